@@ -1,0 +1,335 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This module holds no arithmetic of the FEM method itself: it only lays out
+structured meshes, draws random numbers and builds boundary masks.  Both sides
+(the oracle under ``oracle/`` and the library in ``paper_2111_03541_gb300``)
+receive the same arrays from here.
+
+Random numbers come from one counter-based generator, SplitMix64 (Steele, Lea
+and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+draw ``i`` of stream ``seed`` is ``mix(seed + (i + 1) * 0x9E3779B97F4A7C15)``.
+A uniform double is the top 53 bits times 2^-53; a standard normal comes from
+the Box-Muller transform of two uniforms.
+
+Conventions (all indices 0-based, lexicographic x fastest, then y, then z):
+
+* triangle grid ``n x n`` on the unit square: square (i, j) splits along the
+  diagonal (i, j)->(i+1, j+1) into triangles (v00, v10, v11) and (v00, v11, v01),
+  both counter-clockwise; element id = 2 (j n + i) + t.
+* P2 triangles use the (2n+1)^2 grid of vertices and edge midpoints; local
+  nodes are the three vertices, then the midpoints of edges (0,1), (1,2), (2,0).
+  Edges stay straight: a midpoint sits at the mean of its (jittered) ends.
+* Q1 hexahedra on an ``n^3`` box: local node a = i + 2 j + 4 k sits at the
+  cube corner (i, j, k).
+* jitter moves interior nodes only, each coordinate uniform in [-a h, a h];
+  draw ``node * dim + c`` of the jitter stream.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Seeds of the synthetic workloads.
+SEED_JITTER = 1001
+SEED_COEF = 1002
+SEED_ADVECT = 1003
+SEED_BATCH = 1004
+SEED_GRF = 1005
+SEED_CNN = 1006
+
+
+def splitmix64(seed: int, idx: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for counters ``idx`` of stream ``seed`` (uint64 array)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (idx.astype(np.uint64) + np.uint64(1)) * GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """``n`` doubles in [0, 1) from draws ``offset .. offset+n-1`` of stream ``seed``."""
+    z = splitmix64(seed, np.arange(offset, offset + n, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """``n`` standard normals; normal ``e`` uses draws 2e and 2e+1 (Box-Muller)."""
+    u = uniform(seed, 2 * n, 2 * offset)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def lognormal(seed: int, n: int, sigma: float = 0.5, mu: float = 0.0) -> np.ndarray:
+    """Per-element coefficients exp(mu + sigma z), z standard normal."""
+    return np.exp(mu + sigma * normal(seed, n))
+
+
+# ----------------------------------------------------------------------------
+# meshes
+# ----------------------------------------------------------------------------
+
+def _jitter_grid(coords: np.ndarray, interior: np.ndarray, h: float, alpha: float, seed: int) -> None:
+    if alpha == 0.0:
+        return
+    nn, dim = coords.shape
+    u = uniform(seed, nn * dim).reshape(nn, dim)
+    coords[interior] += (2.0 * u[interior] - 1.0) * (alpha * h)
+
+
+def tri_mesh(n: int, order: int = 1, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
+    """Triangles on the unit square from an ``n x n`` grid.
+
+    Returns ``coords`` (float64 [nn, 2]), ``conn`` (int32 [2 n^2, 3 or 6]) and,
+    for order 2, ``vconn`` (int32 [2 n^2, 3]): the P1 vertex connectivity in the
+    (n+1)^2 vertex numbering together with ``vcoords``.
+    """
+    h = 1.0 / n
+    nv = n + 1
+    jj, ii = np.meshgrid(np.arange(nv), np.arange(nv), indexing="ij")
+    vcoords = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
+    vi, vj = ii.ravel(), jj.ravel()
+    interior = (vi > 0) & (vi < n) & (vj > 0) & (vj < n)
+    _jitter_grid(vcoords, interior, h, jitter, seed)
+
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    v00 = j * nv + i
+    v10 = v00 + 1
+    v01 = v00 + nv
+    v11 = v01 + 1
+    ne = 2 * n * n
+    vconn = np.empty((ne, 3), dtype=np.int32)
+    vconn[0::2] = np.stack([v00, v10, v11], axis=1)
+    vconn[1::2] = np.stack([v00, v11, v01], axis=1)
+    if order == 1:
+        return {"dim": 2, "elem": "P1", "n": n, "coords": vcoords, "conn": vconn}
+
+    # P2: nodes of the (2n+1)^2 grid; vertex (i, j) is fine node (2i, 2j).
+    nf = 2 * n + 1
+    fj, fi = np.meshgrid(np.arange(nf), np.arange(nf), indexing="ij")
+    fi, fj = fi.ravel(), fj.ravel()
+    coords = np.empty((nf * nf, 2), dtype=np.float64)
+    vert = (fi % 2 == 0) & (fj % 2 == 0)
+    coords[vert] = vcoords[(fj[vert] // 2) * nv + fi[vert] // 2]
+
+    def fine(v):  # vertex index -> fine index
+        return (v // nv) * 2 * nf + (v % nv) * 2
+
+    fconn = fine(vconn.astype(np.int64))
+    mids = []
+    for a, b in ((0, 1), (1, 2), (2, 0)):
+        pa, pb = fconn[:, a], fconn[:, b]
+        mi = ((pa % nf) + (pb % nf)) // 2
+        mj = ((pa // nf) + (pb // nf)) // 2
+        m = mj * nf + mi
+        # straight edges: midpoint at the mean of the two ends
+        coords[m] = 0.5 * (coords[pa] + coords[pb])
+        mids.append(m)
+    conn = np.concatenate([fconn, np.stack(mids, axis=1)], axis=1).astype(np.int32)
+    return {"dim": 2, "elem": "P2", "n": n, "coords": coords, "conn": conn,
+            "vcoords": vcoords, "vconn": vconn}
+
+
+def hex_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
+    """Q1 hexahedra on the unit cube from an ``n^3`` grid."""
+    h = 1.0 / n
+    nv = n + 1
+    kk, jj, ii = np.meshgrid(np.arange(nv), np.arange(nv), np.arange(nv), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    coords = np.stack([ii * h, jj * h, kk * h], axis=1).astype(np.float64)
+    interior = (ii > 0) & (ii < n) & (jj > 0) & (jj < n) & (kk > 0) & (kk < n)
+    _jitter_grid(coords, interior, h, jitter, seed)
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    base = ((k.ravel() * nv) + j.ravel()) * nv + i.ravel()
+    conn = np.empty((n ** 3, 8), dtype=np.int32)
+    for a in range(8):
+        di, dj, dk = a & 1, (a >> 1) & 1, (a >> 2) & 1
+        conn[:, a] = base + (dk * nv + dj) * nv + di
+    return {"dim": 3, "elem": "Q1", "n": n, "coords": coords, "conn": conn}
+
+
+# ----------------------------------------------------------------------------
+# boundary data
+# ----------------------------------------------------------------------------
+
+def boundary_nodes(coords: np.ndarray, tol: float = 1e-14) -> np.ndarray:
+    """Boolean mask of nodes on the boundary of the unit square / cube."""
+    return np.any((coords <= tol) | (coords >= 1.0 - tol), axis=1)
+
+
+def thermal_bc(mesh: dict) -> tuple[np.ndarray, np.ndarray]:
+    """Dirichlet u = 0 on the whole boundary: (mask u8 [nn], values f64 [nn])."""
+    m = boundary_nodes(mesh["coords"]).astype(np.uint8)
+    return m, np.zeros(m.shape[0], dtype=np.float64)
+
+
+def elastic_bc(mesh: dict) -> tuple[np.ndarray, np.ndarray]:
+    """Clamp all three displacement components of the nodes on x = 0 (dof 3 node + c)."""
+    clamp = mesh["coords"][:, 0] <= 1e-14
+    m = np.repeat(clamp, 3).astype(np.uint8)
+    return m, np.zeros(m.shape[0], dtype=np.float64)
+
+
+def oseen_bc(mesh: dict) -> tuple[np.ndarray, np.ndarray]:
+    """Lid-driven cavity velocity data plus a pressure pin, dof layout [u1 | u2 | p].
+
+    u = (1, 0) on y = 1 without its two corners, u = 0 on the rest of the
+    boundary; the pressure at vertex (0, 0) is pinned to 0.
+    """
+    c = mesh["coords"]
+    n2 = c.shape[0]
+    n1 = mesh["vcoords"].shape[0]
+    bnd = boundary_nodes(c)
+    lid = (c[:, 1] >= 1.0 - 1e-14) & (c[:, 0] > 1e-14) & (c[:, 0] < 1.0 - 1e-14)
+    mask = np.zeros(2 * n2 + n1, dtype=np.uint8)
+    val = np.zeros(2 * n2 + n1, dtype=np.float64)
+    mask[:n2] = bnd
+    mask[n2:2 * n2] = bnd
+    val[:n2][lid] = 1.0
+    mask[2 * n2] = 1  # pressure pin at vertex 0 = (0, 0)
+    return mask, val
+
+
+def advecting_field(coords: np.ndarray, seed: int = SEED_ADVECT, modes: int = 4) -> np.ndarray:
+    """Divergence-free nodal field a = (d psi/dy, -d psi/dx), max |a| over nodes = 1.
+
+    psi = sum_{kx,ky in 1..modes} c sin(pi kx x + p1) sin(pi ky y + p2) with
+    c ~ N(0, 1) (mode m uses normal m) and phases uniform in [0, 2 pi)
+    (draws 2 modes^2 + 2m and 2 modes^2 + 2m + 1).  Returns float64 [2, nn].
+    """
+    nm = modes * modes
+    amp = normal(seed, nm)
+    ph = uniform(seed, 2 * nm, offset=2 * nm) * (2.0 * np.pi)
+    x, y = coords[:, 0], coords[:, 1]
+    a = np.zeros((2, coords.shape[0]), dtype=np.float64)
+    for m in range(nm):
+        kx, ky = m // modes + 1, m % modes + 1
+        p1, p2 = ph[2 * m], ph[2 * m + 1]
+        sx, cx = np.sin(np.pi * kx * x + p1), np.cos(np.pi * kx * x + p1)
+        sy, cy = np.sin(np.pi * ky * y + p2), np.cos(np.pi * ky * y + p2)
+        a[0] += amp[m] * sx * np.pi * ky * cy
+        a[1] -= amp[m] * np.pi * kx * cx * sy
+    scale = np.sqrt((a * a).sum(axis=0)).max()
+    return a / scale
+
+
+# ----------------------------------------------------------------------------
+# the synthetic workloads
+# ----------------------------------------------------------------------------
+
+def thermal_p1_problem(n: int = 64, jitter: float = 0.2, sigma: float = 0.5,
+                       seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    """2D thermal conduction on jittered P1 triangles (64 x 64 grid: 8192 triangles)."""
+    m = tri_mesh(n, 1, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)
+    m["bc_mask"], m["bc_val"] = thermal_bc(m)
+    m["form"] = "thermal"
+    m["source"] = 1.0
+    return m
+
+
+def thermal_p2_problem(n: int, jitter: float = 0.2, sigma: float = 0.5,
+                       seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    m = tri_mesh(n, 2, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)
+    m["bc_mask"], m["bc_val"] = thermal_bc(m)
+    m["form"] = "thermal"
+    m["source"] = 1.0
+    return m
+
+
+def thermal_q1_problem(n: int, jitter: float = 0.15, sigma: float = 0.5,
+                       seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF,
+                       coef: np.ndarray | None = None) -> dict:
+    m = hex_mesh(n, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma) if coef is None else coef
+    m["bc_mask"], m["bc_val"] = thermal_bc(m)
+    m["form"] = "thermal"
+    m["source"] = 1.0
+    return m
+
+
+def elastic_problem(n: int = 64, jitter: float = 0.15, sigma: float = 0.5, nu: float = 0.3,
+                    seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    """3D linear elasticity on jittered Q1 hexahedra (64^3: 262,144 elements)."""
+    m = hex_mesh(n, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)  # Young's modulus E
+    m["nu"] = nu
+    m["body"] = (0.0, 0.0, -1.0)
+    m["bc_mask"], m["bc_val"] = elastic_bc(m)
+    m["form"] = "elastic"
+    return m
+
+
+def oseen_problem(n: int = 512, viscosity: float = 0.01, rho: float = 1.0,
+                  seed_advect: int = SEED_ADVECT) -> dict:
+    """Picard-linearised flow on Taylor-Hood P2-P1 triangles (512^2 grid: 524,288 elements)."""
+    m = tri_mesh(n, 2, 0.0)
+    m["advect"] = advecting_field(m["coords"], seed_advect)
+    m["viscosity"] = viscosity
+    m["rho"] = rho
+    m["coef"] = np.ones(m["conn"].shape[0], dtype=np.float64)
+    m["bc_mask"], m["bc_val"] = oseen_bc(m)
+    m["form"] = "oseen"
+    return m
+
+
+def batch_specs(n_problems: int = 512, seed: int = SEED_BATCH,
+                lo: float = 1e3, hi: float = 2e5) -> list[dict]:
+    """Element type and grid size of each problem of the batched workload.
+
+    Type: uniform draw 2p < 0.5 -> P1, < 0.8 -> P2, else Q1.  Size: element
+    count log-uniform in [lo, hi] (draw 2p + 1), rounded to the nearest grid:
+    2 n^2 triangles or n^3 hexahedra.
+    """
+    u = uniform(seed, 2 * n_problems)
+    specs = []
+    for p in range(n_problems):
+        t = "P1" if u[2 * p] < 0.5 else ("P2" if u[2 * p] < 0.8 else "Q1")
+        target = math.exp(math.log(lo) + u[2 * p + 1] * (math.log(hi) - math.log(lo)))
+        if t == "Q1":
+            n = max(2, int(round(target ** (1.0 / 3.0))))
+        else:
+            n = max(2, int(round(math.sqrt(target / 2.0))))
+        specs.append({"type": t, "n": n,
+                      "seed_jitter": 1_000_000 + 2 * p, "seed_coef": 1_000_001 + 2 * p})
+    return specs
+
+
+def batch_problem(spec: dict) -> dict:
+    if spec["type"] == "P1":
+        return thermal_p1_problem(spec["n"], 0.2, 0.5, spec["seed_jitter"], spec["seed_coef"])
+    if spec["type"] == "P2":
+        return thermal_p2_problem(spec["n"], 0.2, 0.5, spec["seed_jitter"], spec["seed_coef"])
+    return thermal_q1_problem(spec["n"], 0.15, 0.5, spec["seed_jitter"], spec["seed_coef"])
+
+
+def grf_cells(n: int = 128, corr_len: float = 0.1, sigma: float = 1.0,
+              seed: int = SEED_GRF) -> np.ndarray:
+    """Gaussian random field on the n^3 cells of the unit cube (x fastest).
+
+    Squared-exponential covariance exp(-r^2 / (2 l^2)), sampled by filtering
+    white noise in Fourier space on the periodic n^3 grid, then scaled to
+    standard deviation ``sigma``.  Returns float64 [n^3].
+    """
+    w = normal(seed, n ** 3).reshape(n, n, n)
+    k = 2.0 * np.pi * np.fft.fftfreq(n, d=1.0 / n)
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    filt = np.exp(-0.25 * corr_len ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
+    g = np.fft.ifftn(np.fft.fftn(w) * filt).real
+    g *= sigma / g.std()
+    return g.ravel()
+
+
+def grf_thermal_problem(n: int = 128, system: int = 0) -> dict:
+    """3D thermal conduction on an unjittered Q1 grid with k = exp(GRF), f = 1, u = 0 on the boundary."""
+    k = np.exp(grf_cells(n, seed=SEED_GRF + system))
+    return thermal_q1_problem(n, 0.0, 0.0, coef=k)

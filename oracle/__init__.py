@@ -1,0 +1,274 @@
+"""CPU FP64 oracle of the FEM assembly + Krylov hot path (MetaFEM, arXiv 2111.03541).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it; the product package never imports it.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, single
+thread); this module compiles it with gcc and wraps it with ctypes.  It shares
+no code with the CUDA library: both only receive the arrays made by ``gen``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+LIB = os.path.join(HERE, "_oracle.so")
+
+P1, P2, Q1 = 0, 1, 2
+QTRI3, QTRI6, QHEX8 = 0, 1, 2
+THERMAL, ELASTIC, OSEEN = 0, 1, 2
+ELEM = {"P1": P1, "P2": P2, "Q1": Q1}
+FORM = {"thermal": THERMAL, "elastic": ELASTIC, "oseen": OSEEN}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles oracle.c into _oracle.so (gcc, -O2, no fast-math)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
+                               "-ffp-contract=off", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class Problem(C.Structure):
+    _fields_ = [("form", C.c_int), ("elem", C.c_int), ("quad", C.c_int),
+                ("n_nodes", C.c_int64), ("n_el", C.c_int64), ("n_pnodes", C.c_int64),
+                ("coords", C.c_void_p), ("conn", C.c_void_p), ("pconn", C.c_void_p),
+                ("coef", C.c_void_p), ("nu", C.c_double), ("mu", C.c_double),
+                ("rho", C.c_double), ("source", C.c_void_p), ("fnodal", C.c_void_p),
+                ("advect", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        d, i64, vp, i = C.c_double, C.c_int64, C.c_void_p, C.c_int
+        _lib.or_quad.argtypes = [i, vp, vp]
+        _lib.or_shape.argtypes = [i, vp, vp, vp]
+        _lib.or_elem_measure.argtypes = [i, i, vp]
+        _lib.or_elem_measure.restype = d
+        _lib.or_elem_thermal.argtypes = [i, i, vp, d, d, vp, vp, vp]
+        _lib.or_elem_thermal.restype = d
+        _lib.or_elem_elastic_q1.argtypes = [vp, d, d, vp, vp, vp]
+        _lib.or_elem_elastic_q1.restype = d
+        _lib.or_elem_oseen.argtypes = [vp, vp, d, d, vp, vp, vp, vp]
+        _lib.or_elem_oseen.restype = d
+        _lib.or_assemble.argtypes = [C.POINTER(Problem)] + [C.POINTER(i64)] * 2 + [C.POINTER(vp)] * 5
+        _lib.or_assemble.restype = i
+        _lib.or_free.argtypes = [vp]
+        _lib.or_dirichlet.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+        _lib.or_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
+        _lib.or_pcg.argtypes = [i64, vp, vp, vp, vp, vp, d, i64, C.POINTER(d)]
+        _lib.or_pcg.restype = i64
+        _lib.or_gmres.argtypes = [i64, vp, vp, vp, vp, vp, vp, i, d, i64, C.POINTER(d)]
+        _lib.or_gmres.restype = i64
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data if a is not None else None
+
+
+# ---------------------------------------------------------------------------
+# element level
+# ---------------------------------------------------------------------------
+
+def quad(kind: int) -> tuple[np.ndarray, np.ndarray]:
+    pts = np.zeros((8, 3))
+    w = np.zeros(8)
+    nq = lib().or_quad(kind, _p(pts), _p(w))
+    dim = 3 if kind == QHEX8 else 2
+    return pts.ravel()[: nq * dim].reshape(nq, dim).copy(), w[:nq].copy()
+
+
+def shape(elem: int, xi) -> tuple[np.ndarray, np.ndarray]:
+    dim = 3 if elem == Q1 else 2
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    N = np.zeros(8)
+    dN = np.zeros(24)
+    npe = lib().or_shape(elem, _p(xi), _p(N), _p(dN))
+    return N[:npe].copy(), dN[: npe * dim].reshape(npe, dim).copy()
+
+
+def elem_measure(elem: int, quad_kind: int, X: np.ndarray) -> float:
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    return lib().or_elem_measure(elem, quad_kind, _p(X))
+
+
+def elem_thermal(elem: int, quad_kind: int, X, k: float, f: float = 1.0, fnodal=None):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    npe = X.shape[0]
+    Ke = np.zeros((npe, npe))
+    de = np.zeros(npe)
+    fn = None if fnodal is None else np.ascontiguousarray(fnodal, dtype=np.float64)
+    det = lib().or_elem_thermal(elem, quad_kind, _p(X), k, f, _p(fn), _p(Ke), _p(de))
+    return Ke, de, det
+
+
+def elem_elastic(X, E: float, nu: float, body=(0.0, 0.0, -1.0)):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    b = np.ascontiguousarray(body, dtype=np.float64)
+    Ke = np.zeros((24, 24))
+    de = np.zeros(24)
+    det = lib().or_elem_elastic_q1(_p(X), E, nu, _p(b), _p(Ke), _p(de))
+    return Ke, de, det
+
+
+def elem_oseen(X, aN, mu: float, rho: float):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    aN = np.ascontiguousarray(aN, dtype=np.float64)  # [6][2]
+    A = np.zeros((6, 6))
+    BT = np.zeros((2, 6, 3))
+    B = np.zeros((2, 3, 6))
+    Mp = np.zeros(3)
+    det = lib().or_elem_oseen(_p(X), _p(aN), mu, rho, _p(A), _p(BT), _p(B), _p(Mp))
+    return A, BT, B, Mp, det
+
+
+# ---------------------------------------------------------------------------
+# global level
+# ---------------------------------------------------------------------------
+
+class AssemblyError(RuntimeError):
+    pass
+
+
+def _default_quad(elem: str, form: str) -> int:
+    if elem == "Q1":
+        return QHEX8
+    if form == "oseen":
+        return QTRI6
+    return QTRI3
+
+
+def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: bool = True):
+    """Assembles CSR K and d for a problem dict made by ``gen``.
+
+    Returns dict(row_ptr int64, col int32, val f64, d f64[, pmass f64]).
+    With ``dirichlet`` the strong elimination of ``bc_mask``/``bc_val`` is applied.
+    """
+    form = prob["form"]
+    elem = prob["elem"]
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+
+    coords = arr(prob["coords"], np.float64)
+    conn = arr(prob["conn"], np.int32)
+    coef = arr(prob["coef"], np.float64)
+    pr = Problem()
+    pr.form = FORM[form]
+    pr.elem = ELEM[elem]
+    pr.quad = _default_quad(elem, form) if quad_kind is None else quad_kind
+    pr.n_nodes = coords.shape[0]
+    pr.n_el = conn.shape[0]
+    pr.coords = _p(coords)
+    pr.conn = _p(conn)
+    pr.coef = _p(coef)
+    if form == "thermal":
+        src = arr([prob.get("source", 1.0), 0.0, 0.0], np.float64)
+        pr.source = _p(src)
+        if fnodal is not None:
+            pr.fnodal = _p(arr(fnodal, np.float64))
+    elif form == "elastic":
+        pr.nu = prob["nu"]
+        pr.source = _p(arr(prob["body"], np.float64))
+    else:
+        pconn = arr(prob["vconn"], np.int32)
+        pr.pconn = _p(pconn)
+        pr.n_pnodes = prob["vcoords"].shape[0]
+        pr.mu = prob["viscosity"]
+        pr.rho = prob["rho"]
+        pr.advect = _p(arr(prob["advect"], np.float64))
+    n_rows, nnz = C.c_int64(), C.c_int64()
+    ptrs = [C.c_void_p() for _ in range(5)]
+    rc = lib().or_assemble(C.byref(pr), C.byref(n_rows), C.byref(nnz), *[C.byref(x) for x in ptrs])
+    if rc == -2:
+        raise AssemblyError("element with detJ <= 0")
+    if rc:
+        raise MemoryError("oracle assembly failed")
+    n, z = n_rows.value, nnz.value
+
+    def take(ptr, count, ctype, dt):
+        if not ptr.value:
+            return None
+        a = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=(count,)).astype(dt, copy=True)
+        lib().or_free(ptr)
+        return a
+
+    out = {"row_ptr": take(ptrs[0], n + 1, C.c_int64, np.int64),
+           "col": take(ptrs[1], z, C.c_int32, np.int32),
+           "val": take(ptrs[2], z, C.c_double, np.float64),
+           "d": take(ptrs[3], n, C.c_double, np.float64)}
+    pm = take(ptrs[4], int(pr.n_pnodes), C.c_double, np.float64)
+    if pm is not None:
+        out["pmass"] = pm
+    if dirichlet:
+        apply_dirichlet(out, prob["bc_mask"], prob["bc_val"])
+    return out
+
+
+def apply_dirichlet(sys: dict, mask, bval) -> None:
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    bval = np.ascontiguousarray(bval, dtype=np.float64)
+    n = sys["d"].shape[0]
+    lib().or_dirichlet(n, _p(sys["row_ptr"]), _p(sys["col"]), _p(sys["val"]), _p(sys["d"]),
+                       _p(mask), _p(bval))
+
+
+def spmv(sys: dict, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(sys["row_ptr"].shape[0] - 1)
+    lib().or_spmv(y.shape[0], _p(sys["row_ptr"]), _p(sys["col"]), _p(sys["val"]), _p(x), _p(y))
+    return y
+
+
+def pcg(sys: dict, tol: float = 1e-10, maxit: int = 100000, x0=None):
+    n = sys["d"].shape[0]
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    rr = C.c_double()
+    it = lib().or_pcg(n, _p(sys["row_ptr"]), _p(sys["col"]), _p(sys["val"]), _p(sys["d"]),
+                      _p(x), tol, maxit, C.byref(rr))
+    return x, int(it), rr.value
+
+
+def gmres(sys: dict, pdiag, m: int = 50, tol: float = 1e-8, maxit: int = 20000, x0=None):
+    n = sys["d"].shape[0]
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    pdiag = np.ascontiguousarray(pdiag, dtype=np.float64)
+    rr = C.c_double()
+    it = lib().or_gmres(n, _p(sys["row_ptr"]), _p(sys["col"]), _p(sys["val"]), _p(sys["d"]),
+                        _p(x), _p(pdiag), m, tol, maxit, C.byref(rr))
+    return x, int(it), rr.value
+
+
+def oseen_precond(sys: dict, prob: dict) -> np.ndarray:
+    """Block-diagonal preconditioner diag(diag(A)_u1, diag(A)_u2, diag(M_p) / mu).
+
+    Constrained dofs (velocity Dirichlet nodes, the pinned pressure) keep 1.
+    """
+    n = sys["d"].shape[0]
+    rp, col, val = sys["row_ptr"], sys["col"], sys["val"]
+    diag = np.zeros(n)
+    for i in range(n):
+        s = slice(rp[i], rp[i + 1])
+        hit = np.nonzero(col[s] == i)[0]
+        diag[i] = val[s][hit[0]]
+    n2 = prob["coords"].shape[0]
+    p = diag.copy()
+    p[2 * n2:] = sys["pmass"] / prob["viscosity"]
+    mask = prob["bc_mask"].astype(bool)
+    p[mask] = 1.0
+    return p

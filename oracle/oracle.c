@@ -1,0 +1,703 @@
+/*
+ * CPU FP64 oracle for the FEM assembly + Krylov hot path of MetaFEM
+ * (Xie, Ehmann, Cao, "MetaFEM: A Generic FEM Solver By Meta-expressions",
+ * arXiv 2111.03541).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this file.  The product library never
+ * links, calls or includes it, and it includes nothing of the product.
+ *
+ * Plain, slow, obviously correct: every routine is the definition written out
+ * as nested loops in the order of the paper's sums, double precision
+ * throughout, single threaded.  No blocking, no fusion, no reordering.
+ *
+ * Sign convention: the paper writes the residual of conduction and elasticity
+ * with a minus on the stiffness term (Sec. 4.1, Sec. 4.2), so its tangent
+ * dd/dphi (Eq. "stiffness", Sec. 2.1) is the negative of the positive matrix
+ * returned here; the linear system K x = d is the same after multiplying both
+ * sides by -1.  The flow form of Sec. 4.3 carries +mu(u_ij, u_ij) and is taken
+ * with the paper's own signs.
+ *
+ * Pins: every routine here is checked by tests/test_oracle_pins.py against
+ * closed forms, exact rational integration, invariants and dense solves.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* element kinds */
+enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2 };
+/* quadrature kinds */
+enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2 };
+/* forms */
+enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2 };
+
+/* ------------------------------------------------------------------------ */
+/* Quadrature (Sec. 2.1: each bilinear form is approximated by a weighted     */
+/* sum over integration points w_gamma, x_gamma).                            */
+/* Triangle points are (xi, eta) = (lambda_1, lambda_2) on the reference     */
+/* triangle (0,0),(1,0),(0,1) with weights summing to its area 1/2; hex      */
+/* points live on [-1,1]^3 with weights summing to 8.                        */
+/* ------------------------------------------------------------------------ */
+int or_quad(int kind, double *pts, double *w)
+{
+    if (kind == OR_QTRI3) {
+        /* interior 3-point rule, degree 2: barycentric (2/3,1/6,1/6) and permutations */
+        const double bary[3][3] = {{2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0},
+                                   {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0},
+                                   {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}};
+        for (int q = 0; q < 3; ++q) {
+            pts[2 * q + 0] = bary[q][1];
+            pts[2 * q + 1] = bary[q][2];
+            w[q] = 0.5 / 3.0;
+        }
+        return 3;
+    }
+    if (kind == OR_QTRI6) {
+        /* symmetric 6-point rule, degree 4 (Strang-Fix / Dunavant): two orbits
+         * (a, a, 1-2a) with the closed-form roots of its moment equations. */
+        const double s10 = sqrt(10.0);
+        const double r = sqrt(38.0 - 44.0 * sqrt(2.0 / 5.0));
+        const double a1 = (8.0 - s10 + r) / 18.0;
+        const double a2 = (8.0 - s10 - r) / 18.0;
+        const double t = sqrt(213125.0 - 53320.0 * s10);
+        const double w1 = (620.0 + t) / 3720.0; /* weights normalised to area 1 */
+        const double w2 = (620.0 - t) / 3720.0;
+        const double orb[2] = {a1, a2};
+        const double wo[2] = {w1, w2};
+        int q = 0;
+        for (int o = 0; o < 2; ++o) {
+            const double a = orb[o], b = 1.0 - 2.0 * a;
+            const double bary[3][3] = {{b, a, a}, {a, b, a}, {a, a, b}};
+            for (int p = 0; p < 3; ++p, ++q) {
+                pts[2 * q + 0] = bary[p][1];
+                pts[2 * q + 1] = bary[p][2];
+                w[q] = 0.5 * wo[o];
+            }
+        }
+        return 6;
+    }
+    if (kind == OR_QHEX8) {
+        /* tensor Gauss-Legendre, 2 points per direction at +-1/sqrt(3), weight 1 */
+        const double g = 1.0 / sqrt(3.0);
+        for (int q = 0; q < 8; ++q) {
+            pts[3 * q + 0] = (q & 1) ? g : -g;
+            pts[3 * q + 1] = (q & 2) ? g : -g;
+            pts[3 * q + 2] = (q & 4) ? g : -g;
+            w[q] = 1.0;
+        }
+        return 8;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shape functions N_alpha and reference derivatives dN/dxi (Sec. 2.1:      */
+/* interpolation functions; Sec. 4: Lagrange simplex and cube elements).   */
+/* dN[a*dim + j] = dN_a / dxi_j.                                             */
+/* ------------------------------------------------------------------------ */
+int or_shape(int elem, const double *xi, double *N, double *dN)
+{
+    if (elem == OR_P1) {
+        const double l1 = xi[0], l2 = xi[1], l0 = 1.0 - l1 - l2;
+        N[0] = l0; N[1] = l1; N[2] = l2;
+        dN[0] = -1.0; dN[1] = -1.0;
+        dN[2] = 1.0;  dN[3] = 0.0;
+        dN[4] = 0.0;  dN[5] = 1.0;
+        return 3;
+    }
+    if (elem == OR_P2) {
+        const double l1 = xi[0], l2 = xi[1], l0 = 1.0 - l1 - l2;
+        /* d lambda_k / d xi_j */
+        const double dl[3][2] = {{-1.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}};
+        const double l[3] = {l0, l1, l2};
+        /* vertices: lambda_i (2 lambda_i - 1) */
+        for (int i = 0; i < 3; ++i) {
+            N[i] = l[i] * (2.0 * l[i] - 1.0);
+            for (int j = 0; j < 2; ++j) dN[2 * i + j] = (4.0 * l[i] - 1.0) * dl[i][j];
+        }
+        /* edge midpoints (0,1), (1,2), (2,0): 4 lambda_p lambda_q */
+        const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+        for (int e = 0; e < 3; ++e) {
+            const int p = ep[e][0], q = ep[e][1];
+            N[3 + e] = 4.0 * l[p] * l[q];
+            for (int j = 0; j < 2; ++j)
+                dN[2 * (3 + e) + j] = 4.0 * (dl[p][j] * l[q] + l[p] * dl[q][j]);
+        }
+        return 6;
+    }
+    if (elem == OR_Q1) {
+        /* trilinear: node a = i + 2j + 4k at (2i-1, 2j-1, 2k-1) */
+        for (int a = 0; a < 8; ++a) {
+            const double sa = (a & 1) ? 1.0 : -1.0;
+            const double ta = (a & 2) ? 1.0 : -1.0;
+            const double ua = (a & 4) ? 1.0 : -1.0;
+            const double fx = 1.0 + sa * xi[0], fy = 1.0 + ta * xi[1], fz = 1.0 + ua * xi[2];
+            N[a] = 0.125 * fx * fy * fz;
+            dN[3 * a + 0] = 0.125 * sa * fy * fz;
+            dN[3 * a + 1] = 0.125 * fx * ta * fz;
+            dN[3 * a + 2] = 0.125 * fx * fy * ua;
+        }
+        return 8;
+    }
+    return -1;
+}
+
+static int elem_dim(int elem) { return elem == OR_Q1 ? 3 : 2; }
+static int elem_npe(int elem) { return elem == OR_P1 ? 3 : (elem == OR_P2 ? 6 : 8); }
+
+/* Geometry at one point: J_ij = sum_a x_{a,i} dN_a/dxi_j, detJ, and the
+ * physical gradients grad N_a = J^{-T} gradref N_a (Sec. 2.1: D_lambda N at
+ * x_gamma).  Straight-sided P2 triangles take the affine map of their three
+ * vertices (their isoparametric map is that same affine map).  Returns detJ. */
+static double geometry(int elem, const double *X, const double *xi, double *N, double *gradN)
+{
+    const int dim = elem_dim(elem);
+    const int npe = elem_npe(elem);
+    double dN[8 * 3];
+    or_shape(elem, xi, N, dN);
+    double J[3][3] = {{0}};
+    if (elem == OR_P2) {
+        double Nv[3], dNv[6];
+        or_shape(OR_P1, xi, Nv, dNv);
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j)
+                for (int a = 0; a < 3; ++a) J[i][j] += X[2 * a + i] * dNv[2 * a + j];
+    } else {
+        for (int i = 0; i < dim; ++i)
+            for (int j = 0; j < dim; ++j)
+                for (int a = 0; a < npe; ++a) J[i][j] += X[dim * a + i] * dN[dim * a + j];
+    }
+    double det, Ji[3][3];
+    if (dim == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        Ji[0][0] = J[1][1] / det;  Ji[0][1] = -J[0][1] / det;
+        Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+    } else {
+        /* inverse = adjugate / det */
+        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        Ji[0][0] = c00 / det;
+        Ji[1][0] = c01 / det;
+        Ji[2][0] = c02 / det;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    }
+    /* dN/dx_i = sum_j dN/dxi_j * dxi_j/dx_i, with dxi/dx = J^{-1} */
+    for (int a = 0; a < npe; ++a)
+        for (int i = 0; i < dim; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < dim; ++j) s += dN[dim * a + j] * Ji[j][i];
+            gradN[dim * a + i] = s;
+        }
+    return det;
+}
+
+/* Exported for the geometry pins: sum_q w_q detJ_q (the element measure). */
+double or_elem_measure(int elem, int quad, const double *X)
+{
+    double pts[8 * 3], w[8], N[8], g[24];
+    const int nq = or_quad(quad, pts, w);
+    const int dim = elem_dim(elem);
+    double s = 0.0;
+    for (int q = 0; q < nq; ++q) s += w[q] * geometry(elem, X, pts + dim * q, N, g);
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thermal element (Sec. 4.1: -k(T_,i, T_,i) + (T, s), tangent negated).    */
+/* Ke[a][b] = sum_q w detJ k gradN_a . gradN_b                               */
+/* de[a]    = sum_q w detJ N_a f(x_q), f = fconst or, if fnodal != NULL, the  */
+/* nodal interpolant sum_b fnodal[b] N_b(x_q).  Returns min detJ.            */
+/* ------------------------------------------------------------------------ */
+double or_elem_thermal(int elem, int quad, const double *X, double k, double fconst,
+                       const double *fnodal, double *Ke, double *de)
+{
+    double pts[8 * 3], w[8], N[8], g[24];
+    const int nq = or_quad(quad, pts, w);
+    const int dim = elem_dim(elem), npe = elem_npe(elem);
+    double mindet = 1e300;
+    for (int a = 0; a < npe; ++a) {
+        de[a] = 0.0;
+        for (int b = 0; b < npe; ++b) Ke[a * npe + b] = 0.0;
+    }
+    for (int q = 0; q < nq; ++q) {
+        const double det = geometry(elem, X, pts + dim * q, N, g);
+        if (det < mindet) mindet = det;
+        const double wd = w[q] * det;
+        double f = fconst;
+        if (fnodal) {
+            f = 0.0;
+            for (int b = 0; b < npe; ++b) f += fnodal[b] * N[b];
+        }
+        for (int a = 0; a < npe; ++a) {
+            for (int b = 0; b < npe; ++b) {
+                double dot = 0.0;
+                for (int i = 0; i < dim; ++i) dot += g[dim * a + i] * g[dim * b + i];
+                Ke[a * npe + b] += wd * k * dot;
+            }
+            de[a] += wd * f * N[a];
+        }
+    }
+    return mindet;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Linear elasticity, Q1 (Sec. 4.2: -(d_i,j, sigma_ij), sigma = lambda       */
+/* delta eps_mm + 2 mu eps, lambda = E nu / ((1+nu)(1-2nu)),                 */
+/* mu = E / (2(1+nu))).  With test w = N_a e_c and trial u = N_b e_c':        */
+/* eps(w):sigma(u) = lambda d_c N_a d_c' N_b + mu d_c' N_a d_c N_b            */
+/*                 + mu delta_cc' gradN_a . gradN_b.                         */
+/* Ke[(3a+c)*24 + 3b+c'], de[3a+c] = sum_q w detJ body_c N_a.                */
+/* ------------------------------------------------------------------------ */
+double or_elem_elastic_q1(const double *X, double E, double nu, const double *body,
+                          double *Ke, double *de)
+{
+    double pts[24], w[8], N[8], g[24];
+    const int nq = or_quad(OR_QHEX8, pts, w);
+    const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = E / (2.0 * (1.0 + nu));
+    double mindet = 1e300;
+    memset(Ke, 0, sizeof(double) * 24 * 24);
+    memset(de, 0, sizeof(double) * 24);
+    for (int q = 0; q < nq; ++q) {
+        const double det = geometry(OR_Q1, X, pts + 3 * q, N, g);
+        if (det < mindet) mindet = det;
+        const double wd = w[q] * det;
+        for (int a = 0; a < 8; ++a)
+            for (int c = 0; c < 3; ++c) {
+                for (int b = 0; b < 8; ++b) {
+                    double dot = 0.0;
+                    for (int i = 0; i < 3; ++i) dot += g[3 * a + i] * g[3 * b + i];
+                    for (int cp = 0; cp < 3; ++cp) {
+                        double v = lam * g[3 * a + c] * g[3 * b + cp] + mu * g[3 * a + cp] * g[3 * b + c];
+                        if (c == cp) v += mu * dot;
+                        Ke[(3 * a + c) * 24 + 3 * b + cp] += wd * v;
+                    }
+                }
+                de[3 * a + c] += wd * body[c] * N[a];
+            }
+    }
+    return mindet;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Picard-linearised flow on Taylor-Hood P2-P1 (Sec. 4.3, the NS part of the */
+/* domain form with the advecting velocity a in place of u_j):              */
+/*   mu(u_i,j, u_i,j) - rho(u_i,j, u_i a_j) - (u_i,i, p) + (p, u_i,i).        */
+/* Per component i (the same matrix for i = 1, 2):                           */
+/*   A[a][b]  = sum_q w detJ (mu gradN_a.gradN_b - rho (a_h . gradN_a) N_b)  */
+/* velocity row a, pressure column b:  BT[i][a][b] = -sum_q w detJ d_iN_a M_b */
+/* pressure row a, velocity column b:  B[i][a][b]  = +sum_q w detJ M_a d_iN_b */
+/* pressure mass diagonal Mp[a] = sum_q w detJ M_a^2.                         */
+/* aN is the nodal advecting field [6][2]; a_h = sum_b aN_b N_b.             */
+/* ------------------------------------------------------------------------ */
+double or_elem_oseen(const double *X, const double *aN, double mu, double rho,
+                     double *A, double *BT, double *B, double *Mp)
+{
+    double pts[12], w[6], N[6], g[12], M[3], dM[6];
+    const int nq = or_quad(OR_QTRI6, pts, w);
+    double mindet = 1e300;
+    memset(A, 0, sizeof(double) * 36);
+    memset(BT, 0, sizeof(double) * 2 * 18);
+    memset(B, 0, sizeof(double) * 2 * 18);
+    memset(Mp, 0, sizeof(double) * 3);
+    for (int q = 0; q < nq; ++q) {
+        const double det = geometry(OR_P2, X, pts + 2 * q, N, g);
+        if (det < mindet) mindet = det;
+        or_shape(OR_P1, pts + 2 * q, M, dM);
+        const double wd = w[q] * det;
+        double ah[2] = {0.0, 0.0};
+        for (int b = 0; b < 6; ++b)
+            for (int j = 0; j < 2; ++j) ah[j] += aN[2 * b + j] * N[b];
+        for (int a = 0; a < 6; ++a) {
+            const double adv = ah[0] * g[2 * a] + ah[1] * g[2 * a + 1];
+            for (int b = 0; b < 6; ++b) {
+                const double dot = g[2 * a] * g[2 * b] + g[2 * a + 1] * g[2 * b + 1];
+                A[6 * a + b] += wd * (mu * dot - rho * adv * N[b]);
+            }
+        }
+        for (int i = 0; i < 2; ++i)
+            for (int a = 0; a < 6; ++a)
+                for (int b = 0; b < 3; ++b) BT[18 * i + 3 * a + b] += -wd * g[2 * a + i] * M[b];
+        for (int i = 0; i < 2; ++i)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 6; ++b) B[18 * i + 6 * a + b] += wd * M[a] * g[2 * b + i];
+        for (int a = 0; a < 3; ++a) Mp[a] += wd * M[a] * M[a];
+    }
+    return mindet;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Global assembly (Block B-3/B-4 numbering, Block D-2/D-3 accumulation).    */
+/* Every element emits COO triplets (row, col, value) in element order, local */
+/* row-major order; every dof also emits (g, g, 0) first, so that the        */
+/* diagonal is always present.  A stable sort by (row, col) followed by the  */
+/* sum of duplicates in emission order gives CSR K (ascending columns) and d. */
+/* Dof numbering: thermal node; elasticity 3 node + c; flow [u1 | u2 | p].   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t *row;
+    int32_t *col;
+    double *val;
+    int64_t n, cap;
+} coo_t;
+
+static int coo_push(coo_t *c, int64_t r, int64_t col, double v)
+{
+    if (c->n == c->cap) {
+        int64_t nc = c->cap ? 2 * c->cap : 1 << 16;
+        int64_t *nr = realloc(c->row, sizeof(int64_t) * nc);
+        if (!nr) return -1;
+        c->row = nr;
+        int32_t *ncol = realloc(c->col, sizeof(int32_t) * nc);
+        if (!ncol) return -1;
+        c->col = ncol;
+        double *nv = realloc(c->val, sizeof(double) * nc);
+        if (!nv) return -1;
+        c->val = nv;
+        c->cap = nc;
+    }
+    c->row[c->n] = r;
+    c->col[c->n] = (int32_t)col;
+    c->val[c->n] = v;
+    c->n++;
+    return 0;
+}
+
+/* stable merge sort of an index permutation by (row, col) */
+static const coo_t *g_sort_coo;
+static int key_less(int64_t a, int64_t b)
+{
+    const coo_t *c = g_sort_coo;
+    if (c->row[a] != c->row[b]) return c->row[a] < c->row[b];
+    return c->col[a] < c->col[b];
+}
+static void merge_sort(int64_t *idx, int64_t *tmp, int64_t n)
+{
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) tmp[k++] = key_less(idx[j], idx[i]) ? idx[j++] : idx[i++];
+            while (i < mid) tmp[k++] = idx[i++];
+            while (j < hi) tmp[k++] = idx[j++];
+        }
+        memcpy(idx, tmp, sizeof(int64_t) * n);
+    }
+}
+
+typedef struct {
+    int form, elem, quad;
+    int64_t n_nodes, n_el, n_pnodes;
+    const double *coords;   /* [n_nodes][dim] */
+    const int32_t *conn;    /* [n_el][npe] */
+    const int32_t *pconn;   /* flow: [n_el][3] P1 vertex numbering */
+    const double *coef;     /* [n_el]: k (thermal), E (elasticity) */
+    double nu;              /* Poisson ratio (elasticity) */
+    double mu, rho;         /* flow viscosity, density */
+    const double *source;   /* thermal: source[0]; elasticity: body[3] */
+    const double *fnodal;   /* thermal nodal source or NULL */
+    const double *advect;   /* flow: [2][n_nodes] */
+} or_problem;
+
+int64_t or_ndofs(const or_problem *p)
+{
+    if (p->form == OR_ELASTIC) return 3 * p->n_nodes;
+    if (p->form == OR_OSEEN) return 2 * p->n_nodes + p->n_pnodes;
+    return p->n_nodes;
+}
+
+/* Emits all triplets of one problem; d accumulated in element order too.
+ * Returns 0, or -2 if some element has detJ <= 0, -1 on allocation failure. */
+static int emit(const or_problem *p, coo_t *c, double *d, double *pmass)
+{
+    const int64_t n = or_ndofs(p);
+    const int dim = elem_dim(p->elem), npe = elem_npe(p->elem);
+    for (int64_t g = 0; g < n; ++g)
+        if (coo_push(c, g, g, 0.0)) return -1;
+    double X[8 * 3], Ke[24 * 24], de[24], fn[8];
+    for (int64_t e = 0; e < p->n_el; ++e) {
+        const int32_t *cn = p->conn + e * npe;
+        for (int a = 0; a < npe; ++a)
+            for (int i = 0; i < dim; ++i) X[dim * a + i] = p->coords[(int64_t)cn[a] * dim + i];
+        if (p->form == OR_THERMAL) {
+            if (p->fnodal)
+                for (int a = 0; a < npe; ++a) fn[a] = p->fnodal[cn[a]];
+            const double det = or_elem_thermal(p->elem, p->quad, X, p->coef[e], p->source[0],
+                                               p->fnodal ? fn : NULL, Ke, de);
+            if (!(det > 0.0)) return -2;
+            for (int a = 0; a < npe; ++a) {
+                for (int b = 0; b < npe; ++b)
+                    if (coo_push(c, cn[a], cn[b], Ke[a * npe + b])) return -1;
+                d[cn[a]] += de[a];
+            }
+        } else if (p->form == OR_ELASTIC) {
+            const double det = or_elem_elastic_q1(X, p->coef[e], p->nu, p->source, Ke, de);
+            if (!(det > 0.0)) return -2;
+            for (int a = 0; a < 8; ++a)
+                for (int ci = 0; ci < 3; ++ci) {
+                    for (int b = 0; b < 8; ++b)
+                        for (int cj = 0; cj < 3; ++cj)
+                            if (coo_push(c, 3 * (int64_t)cn[a] + ci, 3 * (int64_t)cn[b] + cj,
+                                         Ke[(3 * a + ci) * 24 + 3 * b + cj]))
+                                return -1;
+                    d[3 * (int64_t)cn[a] + ci] += de[3 * a + ci];
+                }
+        } else {
+            const int32_t *pn = p->pconn + e * 3;
+            double aN[12], A[36], BT[36], B[36], Mp[3];
+            for (int a = 0; a < 6; ++a)
+                for (int j = 0; j < 2; ++j) aN[2 * a + j] = p->advect[j * p->n_nodes + cn[a]];
+            const double det = or_elem_oseen(X, aN, p->mu, p->rho, A, BT, B, Mp);
+            if (!(det > 0.0)) return -2;
+            const int64_t n2 = p->n_nodes;
+            for (int i = 0; i < 2; ++i) {
+                for (int a = 0; a < 6; ++a) {
+                    const int64_t r = i * n2 + cn[a];
+                    for (int b = 0; b < 6; ++b)
+                        if (coo_push(c, r, i * n2 + cn[b], A[6 * a + b])) return -1;
+                    for (int b = 0; b < 3; ++b)
+                        if (coo_push(c, r, 2 * n2 + pn[b], BT[18 * i + 3 * a + b])) return -1;
+                }
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 6; ++b)
+                        if (coo_push(c, 2 * n2 + pn[a], i * n2 + cn[b], B[18 * i + 6 * a + b])) return -1;
+            }
+            if (pmass)
+                for (int a = 0; a < 3; ++a) pmass[pn[a]] += Mp[a];
+        }
+    }
+    return 0;
+}
+
+/* Assembles CSR K and d.  Output arrays are malloc'd here; free with or_free.
+ * pmass_out (flow only, may be NULL) receives a malloc'd [n_pnodes] pressure
+ * mass diagonal.  Returns 0, -1 (allocation) or -2 (detJ <= 0). */
+int or_assemble(const or_problem *p, int64_t *n_rows, int64_t *nnz, int64_t **row_ptr,
+                int32_t **col, double **val, double **d, double **pmass_out)
+{
+    const int64_t n = or_ndofs(p);
+    coo_t c = {0};
+    double *dv = calloc((size_t)n, sizeof(double));
+    double *pm = (p->form == OR_OSEEN) ? calloc((size_t)p->n_pnodes, sizeof(double)) : NULL;
+    if (!dv) return -1;
+    int rc = emit(p, &c, dv, pm);
+    if (rc) {
+        free(c.row); free(c.col); free(c.val); free(dv); free(pm);
+        return rc;
+    }
+    int64_t *idx = malloc(sizeof(int64_t) * c.n), *tmp = malloc(sizeof(int64_t) * c.n);
+    for (int64_t t = 0; t < c.n; ++t) idx[t] = t;
+    g_sort_coo = &c;
+    merge_sort(idx, tmp, c.n);
+    /* count unique (row, col) */
+    int64_t u = 0;
+    for (int64_t t = 0; t < c.n; ++t)
+        if (t == 0 || c.row[idx[t]] != c.row[idx[t - 1]] || c.col[idx[t]] != c.col[idx[t - 1]]) ++u;
+    int64_t *rp = calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t *ci = malloc(sizeof(int32_t) * u);
+    double *vv = malloc(sizeof(double) * u);
+    int64_t k = -1;
+    for (int64_t t = 0; t < c.n; ++t) {
+        const int64_t s = idx[t];
+        if (t == 0 || c.row[s] != c.row[idx[t - 1]] || c.col[s] != c.col[idx[t - 1]]) {
+            ++k;
+            ci[k] = c.col[s];
+            vv[k] = 0.0;
+            rp[c.row[s] + 1]++;
+        }
+        vv[k] += c.val[s]; /* duplicates summed in emission order */
+    }
+    for (int64_t r = 0; r < n; ++r) rp[r + 1] += rp[r];
+    free(idx); free(tmp); free(c.row); free(c.col); free(c.val);
+    *n_rows = n;
+    *nnz = u;
+    *row_ptr = rp;
+    *col = ci;
+    *val = vv;
+    *d = dv;
+    if (pmass_out) *pmass_out = pm; else free(pm);
+    return 0;
+}
+
+void or_free(void *ptr) { free(ptr); }
+
+/* ------------------------------------------------------------------------ */
+/* Strong symmetric Dirichlet elimination (replaces the paper's penalty      */
+/* terms h_penalty, tau, tau^b of Sec. 4.1-4.3).  For a constrained dof g:   */
+/* row g -> identity, d[g] = value; for every other row i: d[i] -= K[i][g]   */
+/* value and K[i][g] = 0.  The pattern is left unchanged (explicit zeros).   */
+/* ------------------------------------------------------------------------ */
+void or_dirichlet(int64_t n, const int64_t *rp, const int32_t *ci, double *val, double *d,
+                  const uint8_t *mask, const double *bval)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask[i]) continue;
+        for (int64_t t = rp[i]; t < rp[i + 1]; ++t) {
+            const int32_t j = ci[t];
+            if (mask[j]) {
+                d[i] -= val[t] * bval[j];
+                val[t] = 0.0;
+            }
+        }
+    }
+    for (int64_t g = 0; g < n; ++g) {
+        if (!mask[g]) continue;
+        for (int64_t t = rp[g]; t < rp[g + 1]; ++t) val[t] = (ci[t] == g) ? 1.0 : 0.0;
+        d[g] = bval[g];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Krylov solvers for Block D-4 (the paper leaves the solver open).          */
+/* ------------------------------------------------------------------------ */
+void or_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+             const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t t = rp[i]; t < rp[i + 1]; ++t) s += val[t] * x[ci[t]];
+        y[i] = s;
+    }
+}
+
+static double dotp(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Jacobi-preconditioned conjugate gradients from x0 = x (in/out); stops when
+ * ||d - K x|| <= tol ||d|| (recursive residual), then reports the true
+ * relative residual.  Returns the iteration count, or -1 if maxit is hit. */
+int64_t or_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+               const double *d, double *x, double tol, int64_t maxit, double *relres)
+{
+    double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    double *p = malloc(sizeof(double) * n), *q = malloc(sizeof(double) * n);
+    double *dinv = malloc(sizeof(double) * n);
+    for (int64_t i = 0; i < n; ++i) {
+        double di = 0.0;
+        for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] == i) di = val[t];
+        dinv[i] = 1.0 / di;
+    }
+    or_spmv(n, rp, ci, val, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = d[i] - q[i];
+    const double dn = sqrt(dotp(n, d, d));
+    for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+    memcpy(p, z, sizeof(double) * n);
+    double rz = dotp(n, r, z);
+    int64_t it = 0, ok = 0;
+    if (sqrt(dotp(n, r, r)) <= tol * dn) ok = 1;
+    while (!ok && it < maxit) {
+        or_spmv(n, rp, ci, val, p, q);
+        const double alpha = rz / dotp(n, p, q);
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+        }
+        ++it;
+        if (sqrt(dotp(n, r, r)) <= tol * dn) { ok = 1; break; }
+        for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+        const double rz1 = dotp(n, r, z);
+        const double beta = rz1 / rz;
+        rz = rz1;
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    }
+    or_spmv(n, rp, ci, val, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = d[i] - q[i];
+    *relres = sqrt(dotp(n, r, r)) / dn;
+    free(r); free(z); free(p); free(q); free(dinv);
+    return ok ? it : -1;
+}
+
+/* Restarted GMRES(m), right preconditioned by the diagonal pdiag
+ * (K P^{-1} y = d, x = P^{-1} y), modified Gram-Schmidt Arnoldi, Givens
+ * rotations on the Hessenberg matrix.  x in/out; stops when the true
+ * relative residual ||d - K x|| / ||d|| (equal to the Arnoldi estimate)
+ * drops to tol.  Returns the total inner iteration count or -1. */
+int64_t or_gmres(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                 const double *d, double *x, const double *pdiag, int m, double tol,
+                 int64_t maxit, double *relres)
+{
+    double *V = malloc(sizeof(double) * n * (m + 1));
+    double *H = calloc((size_t)(m + 1) * m, sizeof(double));
+    double *cs = malloc(sizeof(double) * m), *sn = malloc(sizeof(double) * m);
+    double *s = malloc(sizeof(double) * (m + 1)), *y = malloc(sizeof(double) * m);
+    double *w = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    const double dn = sqrt(dotp(n, d, d));
+    int64_t it = 0;
+    int ok = 0;
+    while (!ok && it < maxit) {
+        or_spmv(n, rp, ci, val, x, w);
+        for (int64_t i = 0; i < n; ++i) V[i] = d[i] - w[i];
+        double beta = sqrt(dotp(n, V, V));
+        if (beta <= tol * dn) { ok = 1; break; }
+        for (int64_t i = 0; i < n; ++i) V[i] /= beta;
+        memset(s, 0, sizeof(double) * (m + 1));
+        s[0] = beta;
+        int j = 0;
+        for (; j < m && it < maxit; ++j) {
+            double *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
+            for (int64_t i = 0; i < n; ++i) z[i] = vj[i] / pdiag[i];
+            or_spmv(n, rp, ci, val, z, vn);
+            for (int k = 0; k <= j; ++k) {
+                const double h = dotp(n, vn, V + (int64_t)k * n);
+                H[k * m + j] = h;
+                for (int64_t i = 0; i < n; ++i) vn[i] -= h * V[(int64_t)k * n + i];
+            }
+            const double hn = sqrt(dotp(n, vn, vn));
+            H[(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                for (int64_t i = 0; i < n; ++i) vn[i] /= hn;
+            for (int k = 0; k < j; ++k) {
+                const double a = H[k * m + j], b = H[(k + 1) * m + j];
+                H[k * m + j] = cs[k] * a + sn[k] * b;
+                H[(k + 1) * m + j] = -sn[k] * a + cs[k] * b;
+            }
+            const double a = H[j * m + j], b = H[(j + 1) * m + j];
+            const double rr = sqrt(a * a + b * b);
+            cs[j] = a / rr;
+            sn[j] = b / rr;
+            H[j * m + j] = rr;
+            H[(j + 1) * m + j] = 0.0;
+            s[j + 1] = -sn[j] * s[j];
+            s[j] = cs[j] * s[j];
+            ++it;
+            if (fabs(s[j + 1]) <= tol * dn) { ++j; ok = 1; break; }
+        }
+        /* back substitution H y = s, then x += P^{-1} V y */
+        for (int k = j - 1; k >= 0; --k) {
+            double t = s[k];
+            for (int l = k + 1; l < j; ++l) t -= H[k * m + l] * y[l];
+            y[k] = t / H[k * m + k];
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int k = 0; k < j; ++k) t += V[(int64_t)k * n + i] * y[k];
+            x[i] += t / pdiag[i];
+        }
+        if (ok) {
+            /* confirm with the true residual */
+            or_spmv(n, rp, ci, val, x, w);
+            for (int64_t i = 0; i < n; ++i) w[i] = d[i] - w[i];
+            if (sqrt(dotp(n, w, w)) > tol * dn) ok = 0;
+        }
+    }
+    or_spmv(n, rp, ci, val, x, w);
+    for (int64_t i = 0; i < n; ++i) w[i] = d[i] - w[i];
+    *relres = sqrt(dotp(n, w, w)) / dn;
+    free(V); free(H); free(cs); free(sn); free(s); free(y); free(w); free(z);
+    return ok ? it : -1;
+}
