@@ -1,0 +1,194 @@
+/*
+ * mf.h -- C ABI of the GB300 (sm_103a) FEM assembly + Krylov library.
+ *
+ * The library builds the global sparse system K x = d of a linearised weak form
+ * on a mesh and solves it, after MetaFEM (Xie, Ehmann, Cao, arXiv 2111.03541):
+ * the problem statement of Sec. 1 fixes K x = d by the forms, the element type
+ * and order, the quadrature and the dof numbering; Sec. 2.2 Block B builds the
+ * dof and sparse-entry maps, Block D-2/D-3 accumulate the residual and the
+ * tangent, Block D-4 solves.  Three hand-lowered forms are provided: thermal
+ * conduction (Sec. 4.1), linear elasticity (Sec. 4.2) and the Picard-linearised
+ * Navier-Stokes domain form on Taylor-Hood elements (Sec. 4.3).
+ *
+ * Conventions shared by every call:
+ *  - Data pointers are DEVICE pointers owned by the caller unless stated.
+ *    The library owns only its opaque handles and the arrays inside them,
+ *    which the matching *_destroy call frees.
+ *  - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream).  Errors found by kernels
+ *    (non-finite coefficient, bad index) are latched in a device status word
+ *    and returned by the next mf_sync_status() or mf_solve().
+ *  - No call aborts, traps or prints.  Invalid arguments return
+ *    MF_ERR_INVALID_ARG without launching anything; mf_last_error() gives a
+ *    thread-local message for the last failure.
+ *  - K is returned positive: the paper's tangent dd/dphi of the conduction
+ *    and elasticity residuals carries the opposite sign; the flow form keeps
+ *    the paper's signs.  All indices are 0-based.
+ *  - Dof numbering (Block B-3): thermal dof = node; elasticity dof =
+ *    3 node + c (node-interleaved); flow dofs [u1 (n_nodes) | u2 (n_nodes) |
+ *    p (n_pnodes)] (variable-major as in Block B-3).
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MF_OK = 0,
+    MF_ERR_INVALID_ARG = 1,  /* bad pointer, size or enum; nothing launched */
+    MF_ERR_BAD_MESH = 2,     /* connectivity out of range, or detJ <= 0 at a point */
+    MF_ERR_NONFINITE = 3,    /* NaN/Inf coefficient, coordinate or residual */
+    MF_ERR_OOM = 4,          /* device allocation failed */
+    MF_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    MF_ERR_NOT_CONVERGED = 6,/* iteration cap reached before the tolerance */
+    MF_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+    MF_ERR_UNSUPPORTED = 8   /* combination not provided (e.g. node valence too high) */
+} mf_status;
+
+typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2 } mf_elem;
+typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2 } mf_form;
+typedef enum { MF_PREC_FP64 = 0, MF_PREC_MIXED = 1 } mf_prec;
+typedef enum { MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1 } mf_solver;
+
+typedef struct mf_mesh mf_mesh;
+typedef struct mf_pattern mf_pattern;
+
+/* Mesh description (Block B-1: elements and their element->control-point map).
+ * coords [n_nodes][dim] f64 AoS; conn [n_elems][npe] int32 with npe = 3 (P1),
+ * 6 (P2: vertices, then midpoints of edges (0,1), (1,2), (2,0)), 8 (Q1: node
+ * a = i + 2j + 4k at reference corner (2i-1, 2j-1, 2k-1)).  Triangles are
+ * counter-clockwise.  For the flow form, pconn [n_elems][3] gives the P1
+ * pressure nodes (the element's vertices in a 0..n_pnodes-1 numbering). */
+typedef struct {
+    int32_t dim;
+    int32_t elem;            /* mf_elem */
+    int64_t n_nodes;
+    int64_t n_elems;
+    const double *coords;
+    const int32_t *conn;
+    int64_t n_pnodes;        /* flow only, else 0 */
+    const int32_t *pconn;    /* flow only, else NULL */
+} mf_mesh_desc;
+
+/* Coefficients of a form (Sec. 4.1-4.3).  elem_coef [n_elems]: the
+ * conductivity k (thermal) or Young's modulus E (elasticity); ignored by the
+ * flow form.  source: thermal f = source[0]; elasticity body force b[3].
+ * advect [2][n_nodes]: nodal advecting velocity of the flow form.  bc_mask
+ * [n_dofs] (u8, nonzero = Dirichlet) and bc_val [n_dofs] f64 may be NULL
+ * (no constraint).  Dirichlet dofs are eliminated symmetrically: row and
+ * column zeroed in the pattern, K[g][g] = 1, d[g] = bc_val[g], and
+ * d[i] -= K[i][g] bc_val[g] on the other rows. */
+typedef struct {
+    const double *elem_coef;
+    double nu;               /* Poisson ratio (elasticity) */
+    double visc;             /* dynamic viscosity mu (flow) */
+    double rho;              /* density (flow) */
+    double source[3];
+    const double *advect;
+    const uint8_t *bc_mask;
+    const double *bc_val;
+} mf_coeffs;
+
+/* CSR view.  row_ptr [n_rows+1] int64, col_idx [nnz] int32 ascending within a
+ * row, the diagonal always present.  Owned by the pattern; values [nnz] is a
+ * caller buffer. */
+typedef struct {
+    int64_t n_rows;
+    int64_t nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    double *values;
+} mf_csr;
+
+typedef struct {
+    int32_t solver;          /* mf_solver */
+    int32_t restart;         /* GMRES restart length m (e.g. 50) */
+    double tol;              /* stop at ||d - K x||_2 <= tol ||d||_2 */
+    int64_t max_iter;
+    const double *precond_diag; /* GMRES: device [n] diagonal P (x = P^-1 y);
+                                   NULL = diag(K).  PCG always uses diag(K). */
+    int32_t check_every;     /* host reads the residual every k iterations (>= 1) */
+} mf_solver_opts;
+
+typedef struct {
+    int64_t iterations;
+    double rel_residual;     /* true ||d - K x|| / ||d|| recomputed at exit */
+    int32_t converged;
+} mf_solve_info;
+
+/* Validates and wraps a mesh (Block B-1).  Checks on the device that every
+ * connectivity entry is in range and detJ > 0 at every quadrature point;
+ * synchronises the stream.  Keeps the caller's device pointers (they must
+ * outlive the handle).  Errors: MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH,
+ * MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_mesh_create(const mf_mesh_desc *desc, void *stream, mf_mesh **out);
+mf_status mf_mesh_destroy(mf_mesh *mesh);
+
+/* Builds the sparsity pattern of a form on a mesh (Block A-3 symbol pairs x
+ * Block B-1 unique control-point pairs -> Block B-4 sparse ids), as CSR with
+ * ascending columns plus the element -> entry maps the assembly uses.  The
+ * flow form has the blocks u1-u1, u2-u2, u-p, p-u and the p-p diagonal; no
+ * u1-u2 block.  Synchronises the stream.  Errors: MF_ERR_INVALID_ARG,
+ * MF_ERR_UNSUPPORTED (more than 64 neighbours or 32 incident elements per
+ * node), MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_pattern_build(const mf_mesh *mesh, int32_t form, void *stream, mf_pattern **out);
+/* Fills n_rows, nnz, row_ptr, col_idx (device pointers owned by the pattern);
+ * values = NULL. */
+mf_status mf_pattern_csr(const mf_pattern *pattern, mf_csr *out);
+/* Copies the pattern's CSR arrays into caller device buffers row_ptr
+ * [n_rows+1] (int64) and col_idx [nnz] (int32), asynchronously on the stream. */
+mf_status mf_pattern_copy_csr(const mf_pattern *pattern, int64_t *row_ptr, int32_t *col_idx, void *stream);
+mf_status mf_pattern_destroy(mf_pattern *pattern);
+
+/* Assembles K and d (Block D-2 residual and D-3 tangent, sparse value and
+ * residual arrays cleared first) for one form: per element quadrature of the
+ * form (Sec. 2.1), then a deterministic fixed-order sum into CSR (no float
+ * atomics: two calls give bit-identical K and d), then the Dirichlet
+ * elimination.  K->values [nnz] and d [n_rows] are caller device buffers.
+ * prec = MF_PREC_MIXED selects the tensor-core element contraction
+ * (elasticity on Q1 only).  Errors: MF_ERR_INVALID_ARG, MF_ERR_UNSUPPORTED,
+ * MF_ERR_CUDA; non-finite coefficients are latched (MF_ERR_NONFINITE). */
+mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
+                      const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d, void *stream);
+
+/* Pressure-mass diagonal of the flow form, out[a] = sum_e sum_q w detJ M_a^2
+ * over P1 pressure node a (for the block-diagonal GMRES preconditioner).
+ * out [n_pnodes] device.  Errors: MF_ERR_INVALID_ARG, MF_ERR_CUDA. */
+mf_status mf_pressure_mass_diag(const mf_mesh *mesh, const mf_pattern *pattern, double *out,
+                                void *stream);
+
+/* Block-diagonal preconditioner of the flow system for GMRES:
+ * out[r] = K[r][r] on velocity rows, p_scale * Mp[n] on the pressure row of
+ * P1 node n (Mp the pressure-mass diagonal), 1 on constrained dofs.
+ * out [n_rows] device.  Errors: MF_ERR_INVALID_ARG, MF_ERR_CUDA. */
+mf_status mf_flow_precond(const mf_mesh *mesh, const mf_pattern *pattern, const mf_csr *K,
+                          const uint8_t *bc_mask, double p_scale, double *out, void *stream);
+
+/* Solves K x = d (Block D-4; the paper leaves the solver open): Jacobi-PCG
+ * (symmetric positive K) or right-preconditioned restarted GMRES(m) with
+ * classical Gram-Schmidt applied twice.  x holds x0 on entry (a warm start
+ * resumes a previous solve) and the solution on exit.  Synchronises the
+ * stream.  Returns MF_ERR_NOT_CONVERGED (x = last iterate, info filled) at
+ * max_iter, MF_ERR_NONFINITE for a non-finite d or a breakdown, and any
+ * latched device error.  info may be NULL. */
+mf_status mf_solve(const mf_csr *K, const double *d, double *x, const mf_solver_opts *opts,
+                   mf_solve_info *info, void *stream);
+
+/* y = K x (device pointers). */
+mf_status mf_spmv(const mf_csr *K, const double *x, double *y, void *stream);
+
+/* Synchronises the stream, returns and clears the latched device status. */
+mf_status mf_sync_status(void *stream);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *mf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MF_H */

@@ -64,6 +64,9 @@ def lib():
         _lib.or_elem_oseen.restype = d
         _lib.or_assemble.argtypes = [C.POINTER(Problem)] + [C.POINTER(i64)] * 2 + [C.POINTER(vp)] * 5
         _lib.or_assemble.restype = i
+        _lib.or_assemble_filtered.argtypes = [C.POINTER(Problem), vp, vp] + [C.POINTER(i64)] * 2 + \
+            [C.POINTER(vp)] * 5
+        _lib.or_assemble_filtered.restype = i
         _lib.or_free.argtypes = [vp]
         _lib.or_dirichlet.argtypes = [i64, vp, vp, vp, vp, vp, vp]
         _lib.or_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
@@ -150,11 +153,15 @@ def _default_quad(elem: str, form: str) -> int:
     return QTRI3
 
 
-def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: bool = True):
+def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: bool = True,
+             keep_nodes=None, keep_pnodes=None):
     """Assembles CSR K and d for a problem dict made by ``gen``.
 
     Returns dict(row_ptr int64, col int32, val f64, d f64[, pmass f64]).
     With ``dirichlet`` the strong elimination of ``bc_mask``/``bc_val`` is applied.
+    ``keep_nodes`` (bool mask over nodes; ``keep_pnodes`` over flow pressure
+    nodes) restricts the work to the elements touching them: only the rows of
+    those nodes are then complete (use ``rows_of``).
     """
     form = prob["form"]
     elem = prob["elem"]
@@ -194,7 +201,13 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
         pr.advect = _p(arr(prob["advect"], np.float64))
     n_rows, nnz = C.c_int64(), C.c_int64()
     ptrs = [C.c_void_p() for _ in range(5)]
-    rc = lib().or_assemble(C.byref(pr), C.byref(n_rows), C.byref(nnz), *[C.byref(x) for x in ptrs])
+    if keep_nodes is None and keep_pnodes is None:
+        rc = lib().or_assemble(C.byref(pr), C.byref(n_rows), C.byref(nnz), *[C.byref(x) for x in ptrs])
+    else:
+        kn = arr(np.zeros(coords.shape[0], np.uint8) if keep_nodes is None else keep_nodes, np.uint8)
+        kp = None if keep_pnodes is None else arr(keep_pnodes, np.uint8)
+        rc = lib().or_assemble_filtered(C.byref(pr), _p(kn), _p(kp), C.byref(n_rows), C.byref(nnz),
+                                        *[C.byref(x) for x in ptrs])
     if rc == -2:
         raise AssemblyError("element with detJ <= 0")
     if rc:
@@ -218,6 +231,12 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
     if dirichlet:
         apply_dirichlet(out, prob["bc_mask"], prob["bc_val"])
     return out
+
+
+def rows_of(sys: dict, rows) -> list[tuple[np.ndarray, np.ndarray]]:
+    """(columns, values) of the given rows of an assembled CSR system."""
+    rp, col, val = sys["row_ptr"], sys["col"], sys["val"]
+    return [(col[rp[r]:rp[r + 1]].copy(), val[rp[r]:rp[r + 1]].copy()) for r in rows]
 
 
 def apply_dirichlet(sys: dict, mask, bval) -> None:

@@ -417,8 +417,12 @@ int64_t or_ndofs(const or_problem *p)
 }
 
 /* Emits all triplets of one problem; d accumulated in element order too.
+ * With a node filter (keep != NULL), only elements with at least one node
+ * marked in keep[] (or, for flow, one vertex marked in pkeep[]) are
+ * evaluated; rows outside the filter are then incomplete and must be ignored.
  * Returns 0, or -2 if some element has detJ <= 0, -1 on allocation failure. */
-static int emit(const or_problem *p, coo_t *c, double *d, double *pmass)
+static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass, const uint8_t *keep,
+                         const uint8_t *pkeep)
 {
     const int64_t n = or_ndofs(p);
     const int dim = elem_dim(p->elem), npe = elem_npe(p->elem);
@@ -427,6 +431,13 @@ static int emit(const or_problem *p, coo_t *c, double *d, double *pmass)
     double X[8 * 3], Ke[24 * 24], de[24], fn[8];
     for (int64_t e = 0; e < p->n_el; ++e) {
         const int32_t *cn = p->conn + e * npe;
+        if (keep) {
+            int hit = 0;
+            for (int a = 0; a < npe; ++a) hit |= keep[cn[a]];
+            if (pkeep && p->pconn)
+                for (int a = 0; a < 3; ++a) hit |= pkeep[p->pconn[e * 3 + a]];
+            if (!hit) continue;
+        }
         for (int a = 0; a < npe; ++a)
             for (int i = 0; i < dim; ++i) X[dim * a + i] = p->coords[(int64_t)cn[a] * dim + i];
         if (p->form == OR_THERMAL) {
@@ -479,18 +490,24 @@ static int emit(const or_problem *p, coo_t *c, double *d, double *pmass)
     return 0;
 }
 
+static int emit(const or_problem *p, coo_t *c, double *d, double *pmass)
+{
+    return emit_filtered(p, c, d, pmass, NULL, NULL);
+}
+
 /* Assembles CSR K and d.  Output arrays are malloc'd here; free with or_free.
  * pmass_out (flow only, may be NULL) receives a malloc'd [n_pnodes] pressure
  * mass diagonal.  Returns 0, -1 (allocation) or -2 (detJ <= 0). */
-int or_assemble(const or_problem *p, int64_t *n_rows, int64_t *nnz, int64_t **row_ptr,
-                int32_t **col, double **val, double **d, double **pmass_out)
+int or_assemble_filtered(const or_problem *p, const uint8_t *keep, const uint8_t *pkeep, int64_t *n_rows,
+                         int64_t *nnz, int64_t **row_ptr, int32_t **col, double **val, double **d,
+                         double **pmass_out)
 {
     const int64_t n = or_ndofs(p);
     coo_t c = {0};
     double *dv = calloc((size_t)n, sizeof(double));
     double *pm = (p->form == OR_OSEEN) ? calloc((size_t)p->n_pnodes, sizeof(double)) : NULL;
     if (!dv) return -1;
-    int rc = emit(p, &c, dv, pm);
+    int rc = emit_filtered(p, &c, dv, pm, keep, pkeep);
     if (rc) {
         free(c.row); free(c.col); free(c.val); free(dv); free(pm);
         return rc;
@@ -527,6 +544,13 @@ int or_assemble(const or_problem *p, int64_t *n_rows, int64_t *nnz, int64_t **ro
     *d = dv;
     if (pmass_out) *pmass_out = pm; else free(pm);
     return 0;
+}
+
+/* The whole system: every element evaluated. */
+int or_assemble(const or_problem *p, int64_t *n_rows, int64_t *nnz, int64_t **row_ptr, int32_t **col,
+                double **val, double **d, double **pmass_out)
+{
+    return or_assemble_filtered(p, NULL, NULL, n_rows, nnz, row_ptr, col, val, d, pmass_out);
 }
 
 void or_free(void *ptr) { free(ptr); }

@@ -1,0 +1,291 @@
+"""Python binding of libmf (GB300 FEM assembly + Krylov hot path of MetaFEM, arXiv 2111.03541).
+
+Argument marshalling only: every step of assembly and solve runs in the CUDA
+kernels of ``libmf.so`` (built in-tree by ``paper_2111_03541_gb300.build``).
+PyTorch provides device memory and streams.  There is no CPU fallback: if the
+library is missing, importing the binding's entry points raises.
+
+The ``mf_*`` functions mirror the C ABI of ``include/mf.h`` one to one.  The
+``Problem`` class is a convenience that moves a problem made by ``gen`` to
+the GPU and keeps its handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "libmf.so")
+
+MF_OK, MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH, MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA, \
+    MF_ERR_NOT_CONVERGED, MF_ERR_TIMEOUT, MF_ERR_UNSUPPORTED = range(9)
+MF_P1_TRI, MF_P2_TRI, MF_Q1_HEX = 0, 1, 2
+MF_FORM_THERMAL, MF_FORM_ELASTIC, MF_FORM_OSEEN = 0, 1, 2
+MF_PREC_FP64, MF_PREC_MIXED = 0, 1
+MF_SOLVER_PCG, MF_SOLVER_GMRES = 0, 1
+
+ELEM = {"P1": MF_P1_TRI, "P2": MF_P2_TRI, "Q1": MF_Q1_HEX}
+FORM = {"thermal": MF_FORM_THERMAL, "elastic": MF_FORM_ELASTIC, "oseen": MF_FORM_OSEEN}
+
+
+class MFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mf status {status}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("elem", C.c_int32), ("n_nodes", C.c_int64), ("n_elems", C.c_int64),
+                ("coords", C.c_void_p), ("conn", C.c_void_p), ("n_pnodes", C.c_int64), ("pconn", C.c_void_p)]
+
+
+class Coeffs(C.Structure):
+    _fields_ = [("elem_coef", C.c_void_p), ("nu", C.c_double), ("visc", C.c_double), ("rho", C.c_double),
+                ("source", C.c_double * 3), ("advect", C.c_void_p), ("bc_mask", C.c_void_p),
+                ("bc_val", C.c_void_p)]
+
+
+class CSR(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("values", C.c_void_p)]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("solver", C.c_int32), ("restart", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int64),
+                ("precond_diag", C.c_void_p), ("check_every", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("rel_residual", C.c_double), ("converged", C.c_int32)]
+
+
+_lib = None
+
+# name -> argtypes (all return mf_status as int, except mf_last_error)
+_SIGS = {
+    "mf_mesh_create": [C.POINTER(MeshDesc), C.c_void_p, C.POINTER(C.c_void_p)],
+    "mf_mesh_destroy": [C.c_void_p],
+    "mf_pattern_build": [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)],
+    "mf_pattern_csr": [C.c_void_p, C.POINTER(CSR)],
+    "mf_pattern_copy_csr": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_pattern_destroy": [C.c_void_p],
+    "mf_assemble": [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Coeffs), C.c_int32, C.POINTER(CSR), C.c_void_p,
+                    C.c_void_p],
+    "mf_pressure_mass_diag": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_flow_precond": [C.c_void_p, C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
+    "mf_solve": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_void_p],
+    "mf_spmv": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_sync_status": [C.c_void_p],
+}
+
+
+def lib() -> C.CDLL:
+    """Loads libmf.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with python -m paper_2111_03541_gb300.build")
+        L = C.CDLL(LIB)
+        for name, argt in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = argt
+            f.restype = C.c_int
+        L.mf_last_error.argtypes = []
+        L.mf_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS) + ["mf_last_error"]
+
+
+def _check(status: int, allow=()) -> int:
+    if status != MF_OK and status not in allow:
+        raise MFError(status, lib().mf_last_error().decode())
+    return status
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one to one
+# ---------------------------------------------------------------------------
+
+def mf_mesh_create(desc: MeshDesc, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().mf_mesh_create(C.byref(desc), _stream(stream), C.byref(h)))
+    return h
+
+
+def mf_mesh_destroy(h) -> None:
+    _check(lib().mf_mesh_destroy(h))
+
+
+def mf_pattern_build(mesh, form: int, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().mf_pattern_build(mesh, form, _stream(stream), C.byref(h)))
+    return h
+
+
+def mf_pattern_csr(pattern) -> CSR:
+    c = CSR()
+    _check(lib().mf_pattern_csr(pattern, C.byref(c)))
+    return c
+
+
+def mf_pattern_copy_csr(pattern, row_ptr, col_idx, stream=None) -> None:
+    _check(lib().mf_pattern_copy_csr(pattern, _ptr(row_ptr), _ptr(col_idx), _stream(stream)))
+
+
+def mf_pattern_destroy(h) -> None:
+    _check(lib().mf_pattern_destroy(h))
+
+
+def mf_assemble(form: int, mesh, pattern, coeffs: Coeffs, prec: int, K: CSR, d, stream=None) -> None:
+    _check(lib().mf_assemble(form, mesh, pattern, C.byref(coeffs), prec, C.byref(K), _ptr(d), _stream(stream)))
+
+
+def mf_pressure_mass_diag(mesh, pattern, out, stream=None) -> None:
+    _check(lib().mf_pressure_mass_diag(mesh, pattern, _ptr(out), _stream(stream)))
+
+
+def mf_flow_precond(mesh, pattern, K: CSR, bc_mask, p_scale: float, out, stream=None) -> None:
+    _check(lib().mf_flow_precond(mesh, pattern, C.byref(K), _ptr(bc_mask), p_scale, _ptr(out), _stream(stream)))
+
+
+def mf_solve(K: CSR, d, x, opts: SolverOpts, stream=None, allow=(MF_ERR_NOT_CONVERGED,)) -> tuple[int, SolveInfo]:
+    info = SolveInfo()
+    st = _check(lib().mf_solve(C.byref(K), _ptr(d), _ptr(x), C.byref(opts), C.byref(info), _stream(stream)), allow)
+    return st, info
+
+
+def mf_spmv(K: CSR, x, y, stream=None) -> None:
+    _check(lib().mf_spmv(C.byref(K), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def mf_sync_status(stream=None) -> None:
+    _check(lib().mf_sync_status(_stream(stream)))
+
+
+def mf_last_error() -> str:
+    return lib().mf_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience: a generated problem on the GPU
+# ---------------------------------------------------------------------------
+
+class Problem:
+    """Device copy of a ``gen`` problem with its mesh and pattern handles.
+
+    ``values``/``d`` are torch tensors (float64) the assembly writes into;
+    ``row_ptr``/``col`` are copies of the pattern's CSR arrays.
+    """
+
+    def __init__(self, prob: dict, device="cuda", stream=None):
+        import numpy as np
+        import torch
+
+        self.prob = prob
+        self.device = torch.device(device)
+        dev = self.device
+
+        def t(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+
+        self.form = FORM[prob["form"]]
+        self.coords = t(prob["coords"], torch.float64)
+        self.conn = t(prob["conn"], torch.int32)
+        self.coef = t(prob["coef"], torch.float64)
+        self.bc_mask = t(prob["bc_mask"], torch.uint8)
+        self.bc_val = t(prob["bc_val"], torch.float64)
+        self.pconn = t(prob["vconn"], torch.int32) if prob["form"] == "oseen" else None
+        self.advect = t(prob["advect"], torch.float64) if prob["form"] == "oseen" else None
+        self.desc = MeshDesc(dim=self.coords.shape[1], elem=ELEM[prob["elem"]], n_nodes=self.coords.shape[0],
+                             n_elems=self.conn.shape[0], coords=_ptr(self.coords), conn=_ptr(self.conn),
+                             n_pnodes=0 if self.pconn is None else prob["vcoords"].shape[0],
+                             pconn=_ptr(self.pconn))
+        self.mesh = mf_mesh_create(self.desc, stream)
+        self.pattern = mf_pattern_build(self.mesh, self.form, stream)
+        self.csr = mf_pattern_csr(self.pattern)
+        self.n = self.csr.n_rows
+        self.nnz = self.csr.nnz
+        self.values = torch.empty(self.nnz, dtype=torch.float64, device=dev)
+        self.d = torch.empty(self.n, dtype=torch.float64, device=dev)
+        self.csr.values = _ptr(self.values)
+        self.coeffs = self.make_coeffs()
+
+    def make_coeffs(self, coef=None, bc=True) -> Coeffs:
+        p = self.prob
+        c = Coeffs()
+        c.elem_coef = _ptr(self.coef if coef is None else coef)
+        c.nu = p.get("nu", 0.0)
+        c.visc = p.get("viscosity", 0.0)
+        c.rho = p.get("rho", 0.0)
+        if p["form"] == "thermal":
+            c.source[0] = p.get("source", 1.0)
+        elif p["form"] == "elastic":
+            for i in range(3):
+                c.source[i] = p["body"][i]
+        c.advect = _ptr(self.advect)
+        if bc:
+            c.bc_mask = _ptr(self.bc_mask)
+            c.bc_val = _ptr(self.bc_val)
+        return c
+
+    def csr_arrays(self, stream=None):
+        import torch
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        ci = torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        mf_pattern_copy_csr(self.pattern, rp, ci, stream)
+        return rp, ci
+
+    def assemble(self, prec: int = MF_PREC_FP64, coeffs: Coeffs | None = None, stream=None):
+        mf_assemble(self.form, self.mesh, self.pattern, coeffs or self.coeffs, prec, self.csr, self.d, stream)
+        return self.values, self.d
+
+    def pressure_mass_diag(self, stream=None):
+        import torch
+        out = torch.empty(self.desc.n_pnodes, dtype=torch.float64, device=self.device)
+        mf_pressure_mass_diag(self.mesh, self.pattern, out, stream)
+        return out
+
+    def flow_precond(self, p_scale: float, stream=None):
+        import torch
+        out = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        mf_flow_precond(self.mesh, self.pattern, self.csr, self.bc_mask, p_scale, out, stream)
+        return out
+
+    def solve(self, x=None, solver=MF_SOLVER_PCG, tol=1e-10, max_iter=100000, restart=50, precond=None,
+              check_every=50, stream=None):
+        import torch
+        if x is None:
+            x = torch.zeros(self.n, dtype=torch.float64, device=self.device)
+        opts = SolverOpts(solver=solver, restart=restart, tol=tol, max_iter=max_iter,
+                          precond_diag=_ptr(precond), check_every=check_every)
+        st, info = mf_solve(self.csr, self.d, x, opts, stream)
+        return x, st, info
+
+    def close(self):
+        if getattr(self, "pattern", None):
+            mf_pattern_destroy(self.pattern)
+            self.pattern = None
+        if getattr(self, "mesh", None):
+            mf_mesh_destroy(self.mesh)
+            self.mesh = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,335 @@
+// C ABI entry points: argument checks, handles, status word, error messages.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "mf_internal.h"
+
+static thread_local char g_msg[512] = "";
+
+mf_status mf_fail(mf_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+mf_status mf_cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return MF_OK;
+    cudaGetLastError();  // clear a non-sticky error
+    if (e == cudaErrorMemoryAllocation) return mf_fail(MF_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return mf_fail(MF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char *mf_last_error(void) { return g_msg; }
+
+// ---------------------------------------------------------------------------
+// device status word: one int per device in a __device__ variable; kernels get
+// its address as an argument (set-up once per device with that device current)
+// ---------------------------------------------------------------------------
+static __device__ int g_status_word;
+static std::mutex g_status_mu;
+static int *g_status_ptr[64];
+
+int *mf_status_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+        g_status_ptr[dev] = static_cast<int *>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+extern "C" mf_status mf_sync_status(void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *w = mf_status_word();
+    if (!w) return mf_fail(MF_ERR_CUDA, "no device status word");
+    int h = 0;
+    MF_CUDA(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (h != 0) {
+        const int zero = 0;
+        MF_CUDA(cudaMemcpyAsync(w, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        return mf_fail(static_cast<mf_status>(h), "device reported status %d", h);
+    }
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int64 counts (three passes: block scan, scan of block
+// totals, add block offsets)
+// ---------------------------------------------------------------------------
+static constexpr int SCAN_T = 512, SCAN_V = 8, SCAN_TILE = SCAN_T * SCAN_V;
+
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *sh, int64_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int64_t before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+    if (total) *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void k_scan_tiles(int64_t *data, int64_t n, int64_t *tile_sums)
+{
+    __shared__ int64_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_V;
+    int64_t v[SCAN_V], s = 0;
+    for (int i = 0; i < SCAN_V; ++i) {
+        v[i] = (base + i < n) ? data[base + i] : 0;
+        s += v[i];
+    }
+    int64_t tot;
+    int64_t run = block_exclusive_scan(s, sh, &tot);
+    for (int i = 0; i < SCAN_V; ++i) {
+        if (base + i < n) data[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_single(int64_t *data, int64_t n, int64_t *total)
+{
+    __shared__ int64_t sh[32];
+    int64_t carry = 0;
+    for (int64_t start = 0; start < n; start += blockDim.x) {
+        const int64_t i = start + threadIdx.x;
+        const int64_t v = i < n ? data[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan(v, sh, &tot);
+        if (i < n) data[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_add(int64_t *data, int64_t n, const int64_t *tile_off)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) data[i] += tile_off[i / SCAN_TILE];
+}
+
+cudaError_t mf_scan_i64(int64_t *d_data, int64_t n, int64_t *d_total, cudaStream_t st)
+{
+    if (n <= SCAN_TILE) {
+        k_scan_single<<<1, 1024, 0, st>>>(d_data, n, d_total);
+        return cudaGetLastError();
+    }
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int64_t *sums = nullptr;
+    cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * tiles, st);
+    if (e != cudaSuccess) return e;
+    k_scan_tiles<<<(unsigned)tiles, SCAN_T, 0, st>>>(d_data, n, sums);
+    e = mf_scan_i64(sums, tiles, d_total, st);
+    if (e == cudaSuccess) {
+        k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_data, n, sums);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(sums, st);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+extern "C" mf_status mf_mesh_create(const mf_mesh_desc *desc, void *stream, mf_mesh **out)
+{
+    g_msg[0] = 0;
+    if (!desc || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: NULL argument");
+    *out = nullptr;
+    if (desc->elem < MF_P1_TRI || desc->elem > MF_Q1_HEX)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: unknown element %d", desc->elem);
+    if (desc->dim != mf_ndim(desc->elem))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: dim %d does not match element", desc->dim);
+    if (desc->n_nodes <= 0 || desc->n_elems <= 0 || !desc->coords || !desc->conn)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: empty mesh or NULL arrays");
+    if (desc->n_nodes > INT32_MAX || desc->n_elems >= (int64_t(1) << 25))
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_mesh_create: at most 2^31-1 nodes and 2^25 elements");
+    if ((desc->pconn == nullptr) != (desc->n_pnodes == 0) || (desc->pconn && desc->elem != MF_P2_TRI))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: pconn/n_pnodes are for P2 flow meshes");
+    mf_mesh *m = new (std::nothrow) mf_mesh();
+    if (!m) return mf_fail(MF_ERR_OOM, "mf_mesh_create: host allocation");
+    m->dim = desc->dim;
+    m->elem = desc->elem;
+    m->npe = mf_npe(desc->elem);
+    m->n_nodes = desc->n_nodes;
+    m->n_elems = desc->n_elems;
+    m->n_pnodes = desc->n_pnodes;
+    m->coords = desc->coords;
+    m->conn = desc->conn;
+    m->pconn = desc->pconn;
+    cudaGetDevice(&m->device);
+    mf_status s = mf_mesh_validate(m, static_cast<cudaStream_t>(stream));
+    if (s != MF_OK) {
+        delete m;
+        return s;
+    }
+    *out = m;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_mesh_destroy(mf_mesh *mesh)
+{
+    delete mesh;
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pattern
+// ---------------------------------------------------------------------------
+extern "C" mf_status mf_pattern_build(const mf_mesh *mesh, int32_t form, void *stream, mf_pattern **out)
+{
+    g_msg[0] = 0;
+    if (!mesh || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_pattern_build: NULL argument");
+    *out = nullptr;
+    if (form == MF_FORM_ELASTIC && mesh->elem != MF_Q1_HEX)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: elasticity is provided on Q1 hexahedra");
+    if (form == MF_FORM_OSEEN && (mesh->elem != MF_P2_TRI || !mesh->pconn))
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: flow needs a P2 mesh with pconn");
+    if (form < MF_FORM_THERMAL || form > MF_FORM_OSEEN)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_pattern_build: unknown form %d", form);
+    mf_pattern *p = new (std::nothrow) mf_pattern();
+    if (!p) return mf_fail(MF_ERR_OOM, "mf_pattern_build: host allocation");
+    p->form = form;
+    p->mesh = mesh;
+    mf_status s = mf_pattern_build_impl(mesh, form, static_cast<cudaStream_t>(stream), p);
+    if (s != MF_OK) {
+        mf_pattern_free(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_pattern_csr(const mf_pattern *pattern, mf_csr *out)
+{
+    if (!pattern || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_pattern_csr: NULL argument");
+    out->n_rows = pattern->n_rows;
+    out->nnz = pattern->nnz;
+    out->row_ptr = pattern->row_ptr;
+    out->col_idx = pattern->col_idx;
+    out->values = nullptr;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_pattern_copy_csr(const mf_pattern *pattern, int64_t *row_ptr, int32_t *col_idx, void *stream)
+{
+    if (!pattern || !row_ptr || !col_idx) return mf_fail(MF_ERR_INVALID_ARG, "mf_pattern_copy_csr: NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MF_CUDA(cudaMemcpyAsync(row_ptr, pattern->row_ptr, sizeof(int64_t) * (pattern->n_rows + 1),
+                            cudaMemcpyDeviceToDevice, st));
+    MF_CUDA(cudaMemcpyAsync(col_idx, pattern->col_idx, sizeof(int32_t) * pattern->nnz, cudaMemcpyDeviceToDevice, st));
+    return MF_OK;
+}
+
+extern "C" mf_status mf_pattern_destroy(mf_pattern *pattern)
+{
+    if (!pattern) return MF_OK;
+    mf_pattern_free(pattern);
+    delete pattern;
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// assembly and solve
+// ---------------------------------------------------------------------------
+static bool csr_ok(const mf_csr *K)
+{
+    return K && K->n_rows > 0 && K->nnz > 0 && K->row_ptr && K->col_idx && K->values;
+}
+
+extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
+                                 const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d,
+                                 void *stream)
+{
+    g_msg[0] = 0;
+    if (!mesh || !pattern || !coeffs || !K || !d || !K->values)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: NULL argument");
+    if (pattern->form != form || pattern->mesh != mesh)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: pattern was built for another form or mesh");
+    if (K->n_rows != pattern->n_rows || K->nnz != pattern->nnz || K->row_ptr != pattern->row_ptr ||
+        K->col_idx != pattern->col_idx)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: K does not carry the pattern's CSR arrays");
+    if (form != MF_FORM_OSEEN && !coeffs->elem_coef)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: elem_coef is NULL");
+    if (form == MF_FORM_OSEEN && !coeffs->advect)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: advect is NULL");
+    if ((coeffs->bc_mask == nullptr) != (coeffs->bc_val == nullptr))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: bc_mask and bc_val go together");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prec == MF_PREC_FP64) return mf_assemble_fp64(form, mesh, pattern, coeffs, K->values, d, st);
+    if (prec == MF_PREC_MIXED) {
+        if (form != MF_FORM_ELASTIC)
+            return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: the mixed path covers Q1 elasticity");
+        return mf_assemble_mixed(form, mesh, pattern, coeffs, K->values, d, st);
+    }
+    return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: unknown precision %d", prec);
+}
+
+extern "C" mf_status mf_pressure_mass_diag(const mf_mesh *mesh, const mf_pattern *pattern, double *out,
+                                           void *stream)
+{
+    g_msg[0] = 0;
+    if (!mesh || !pattern || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_pressure_mass_diag: NULL argument");
+    if (pattern->form != MF_FORM_OSEEN || pattern->mesh != mesh)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_pressure_mass_diag: needs the flow pattern of this mesh");
+    return mf_pmass_impl(mesh, pattern, out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mf_status mf_flow_precond(const mf_mesh *mesh, const mf_pattern *pattern, const mf_csr *K,
+                                     const uint8_t *bc_mask, double p_scale, double *out, void *stream)
+{
+    g_msg[0] = 0;
+    if (!mesh || !pattern || !csr_ok(K) || !out)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_flow_precond: NULL argument");
+    if (pattern->form != MF_FORM_OSEEN || pattern->mesh != mesh || K->row_ptr != pattern->row_ptr)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_flow_precond: needs the flow pattern of this mesh");
+    return mf_flow_precond_impl(mesh, pattern, K, bc_mask, p_scale, out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mf_status mf_solve(const mf_csr *K, const double *d, double *x, const mf_solver_opts *opts,
+                              mf_solve_info *info, void *stream)
+{
+    g_msg[0] = 0;
+    if (!csr_ok(K) || !d || !x || !opts) return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: NULL argument");
+    if (opts->solver != MF_SOLVER_PCG && opts->solver != MF_SOLVER_GMRES)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: unknown solver %d", opts->solver);
+    if (!(opts->tol > 0.0) || opts->max_iter < 0 || (opts->solver == MF_SOLVER_GMRES && opts->restart < 1))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: tol > 0, max_iter >= 0, restart >= 1 required");
+    return mf_solve_impl(K, d, x, opts, info, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mf_status mf_spmv(const mf_csr *K, const double *x, double *y, void *stream)
+{
+    g_msg[0] = 0;
+    if (!csr_ok(K) || !x || !y) return mf_fail(MF_ERR_INVALID_ARG, "mf_spmv: NULL argument");
+    return mf_spmv_impl(K, x, y, static_cast<cudaStream_t>(stream));
+}

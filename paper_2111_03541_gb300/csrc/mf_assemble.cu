@@ -1,0 +1,648 @@
+// FP64 assembly of K and d (MetaFEM Sec. 2.2 Block D-2 / D-3).
+//
+// Two kernels per form.  The element kernel evaluates the quadrature of the
+// form (Sec. 2.1) for one element per thread and writes the element blocks
+// to a scratch array.  The gather kernel then builds every CSR row from the
+// pattern's contribution lists: the contributions of one entry are summed in
+// ascending element order (the paper increments K with atomics in Block D-3;
+// a fixed order makes K bit-reproducible), the strong Dirichlet elimination
+// is applied, and every value of K and d is written exactly once, so no
+// separate clearing pass is needed.
+//
+// Forms (K positive; Sec. 4.1-4.3):
+//   thermal   Ke[a][b] = sum_q w detJ k gradN_a . gradN_b,  de[a] = sum_q w detJ f N_a
+//   elastic   Ke[(a,c),(b,c')] = lambda A_ab[c][c'] + mu A_ab[c'][c] + mu delta_cc' tr A_ab
+//             with A_ab = sum_q w detJ gradN_a gradN_b^T,   de[(a,c)] = body_c sum_q w detJ N_a
+//   flow      A[a][b] = sum_q w detJ (mu gradN_a.gradN_b - rho (a_h.gradN_a) N_b),
+//             B_i[a][b] = sum_q w detJ M_a d_i N_b; the u-p block is -B_i^T.
+#include "mf_internal.h"
+
+namespace {
+
+constexpr double QG = 0.57735026918962576451;  // 2-point Gauss abscissa 1/sqrt(3)
+// symmetric 6-point degree-4 triangle rule (two orbits (a, a, 1-2a)); weights
+// normalised to area 1
+constexpr double T6A1 = 0.44594849091596488632, T6W1 = 0.22338158967801146570;
+constexpr double T6A2 = 0.091576213509770743460, T6W2 = 0.10995174365532186764;
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// reference derivative dN_a/dxi_j of the trilinear basis at Gauss point q
+__device__ __forceinline__ double q1_dref(int q, int a, int j)
+{
+    const double xs[3] = {(q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG};
+    const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+    double v = 0.125 * s[j];
+    for (int i = 0; i < 3; ++i)
+        if (i != j) v *= 1.0 + s[i] * xs[i];
+    return v;
+}
+
+__device__ __forceinline__ double q1_n(int q, int a)
+{
+    const double xs[3] = {(q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG};
+    const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+    return 0.125 * (1.0 + s[0] * xs[0]) * (1.0 + s[1] * xs[1]) * (1.0 + s[2] * xs[2]);
+}
+
+// Jacobian of the trilinear map at Gauss point q, its determinant and inverse
+__device__ __forceinline__ double q1_jac(const double (&x)[8][3], int q, double (&Ji)[3][3])
+{
+    double J[3][3] = {};
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double dn = q1_dref(q, a, j);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) J[i][j] = fma(x[a][i], dn, J[i][j]);
+        }
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double r = 1.0 / det;
+    Ji[0][0] = c00 * r;
+    Ji[1][0] = c01 * r;
+    Ji[2][0] = c02 * r;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+    return det;
+}
+
+// affine triangle from its first three nodes: detJ and grad lambda_k
+__device__ __forceinline__ double tri_affine(const double *__restrict__ X, const int32_t *__restrict__ c,
+                                             double (&gl)[3][2])
+{
+    const double x0 = X[2 * (int64_t)c[0]], y0 = X[2 * (int64_t)c[0] + 1];
+    const double j00 = X[2 * (int64_t)c[1]] - x0, j10 = X[2 * (int64_t)c[1] + 1] - y0;
+    const double j01 = X[2 * (int64_t)c[2]] - x0, j11 = X[2 * (int64_t)c[2] + 1] - y0;
+    const double det = j00 * j11 - j01 * j10;
+    const double r = 1.0 / det;
+    // J^{-1} = [[j11, -j01], [-j10, j00]] / det ; grad lambda = J^{-T} gradref lambda
+    const double i00 = j11 * r, i01 = -j01 * r, i10 = -j10 * r, i11 = j00 * r;
+    gl[1][0] = i00; gl[1][1] = i01;   // gradref lambda_1 = (1, 0)
+    gl[2][0] = i10; gl[2][1] = i11;   // gradref lambda_2 = (0, 1)
+    gl[0][0] = -i00 - i10; gl[0][1] = -i01 - i11;
+    return det;
+}
+
+// P2 basis values and physical gradients at barycentric point l
+__device__ __forceinline__ void p2_basis(const double (&l)[3], const double (&gl)[3][2], double (&N)[6],
+                                         double (&g)[6][2])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        N[i] = l[i] * (2.0 * l[i] - 1.0);
+        g[i][0] = (4.0 * l[i] - 1.0) * gl[i][0];
+        g[i][1] = (4.0 * l[i] - 1.0) * gl[i][1];
+    }
+    const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int p = ep[e][0], q = ep[e][1];
+        N[3 + e] = 4.0 * l[p] * l[q];
+        g[3 + e][0] = 4.0 * (gl[p][0] * l[q] + l[p] * gl[q][0]);
+        g[3 + e][1] = 4.0 * (gl[p][1] * l[q] + l[p] * gl[q][1]);
+    }
+}
+
+__device__ __forceinline__ void tri6_point(int q, double (&l)[3], double &w)
+{
+    const double a = q < 3 ? T6A1 : T6A2;
+    const double b = 1.0 - 2.0 * a;
+    const int k = q % 3;
+    l[0] = (k == 0) ? b : a;
+    l[1] = (k == 1) ? b : a;
+    l[2] = (k == 2) ? b : a;
+    w = 0.5 * (q < 3 ? T6W1 : T6W2);  // reference triangle area 1/2
+}
+
+__device__ __forceinline__ int upair(int a, int b) { return a * (15 - a) / 2 + b; }  // a <= b < 8
+
+// ---------------------------------------------------------------------------
+// element kernels
+// ---------------------------------------------------------------------------
+__global__ void k_elem_thermal_p1(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double gl[3][2];
+    const double det = tri_affine(X, conn + 3 * e, gl);
+    // the integrand is constant: the 3 point weights sum to 1/2
+    const double s = 0.5 * det * k;
+    double *o = out + e * 12;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) o[3 * a + b] = s * (gl[a][0] * gl[b][0] + gl[a][1] * gl[b][1]);
+    // 3-point rule: sum_q w_q lambda_a(q) = 1/6
+    const double l = det * f * (1.0 / 6.0);
+    o[9] = l;
+    o[10] = l;
+    o[11] = l;
+}
+
+__global__ void k_elem_thermal_p2(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double gl[3][2];
+    const double det = tri_affine(X, conn + 6 * e, gl);
+    double Ke[21] = {}, de[6] = {};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        // degree-2 interior rule: (2/3, 1/6, 1/6) and permutations, weight 1/6
+        double l[3] = {1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
+        l[q] = 2.0 / 3.0;
+        double N[6], g[6][2];
+        p2_basis(l, gl, N, g);
+        const double wd = det * (1.0 / 6.0);
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+#pragma unroll
+            for (int b = a; b < 6; ++b, ++t) Ke[t] = fma(wd, g[a][0] * g[b][0] + g[a][1] * g[b][1], Ke[t]);
+            de[a] = fma(wd, N[a], de[a]);
+        }
+    }
+    double *o = out + e * 42;
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = a; b < 6; ++b, ++t) {
+            o[6 * a + b] = k * Ke[t];
+            o[6 * b + a] = k * Ke[t];
+        }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) o[36 + a] = f * de[a];
+}
+
+__global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const double *__restrict__ X,
+                                                         const int32_t *__restrict__ conn,
+                                                         const double *__restrict__ kc, double f,
+                                                         double *__restrict__ out, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double x[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
+    double Ke[36] = {}, m[8] = {};
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+        double Ji[3][3];
+        const double wd = q1_jac(x, q, Ji);  // Gauss weights are 1
+        double g[8][3];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                g[a][i] = q1_dref(q, a, 0) * Ji[0][i] + q1_dref(q, a, 1) * Ji[1][i] + q1_dref(q, a, 2) * Ji[2][i];
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double ga0 = wd * g[a][0], ga1 = wd * g[a][1], ga2 = wd * g[a][2];
+#pragma unroll
+            for (int b = a; b < 8; ++b, ++t) Ke[t] = fma(ga0, g[b][0], fma(ga1, g[b][1], fma(ga2, g[b][2], Ke[t])));
+            m[a] = fma(wd, q1_n(q, a), m[a]);
+        }
+    }
+    double *o = out + e * 72;
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = a; b < 8; ++b, ++t) {
+            o[8 * a + b] = k * Ke[t];
+            o[8 * b + a] = k * Ke[t];
+        }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) o[64 + a] = f * m[a];
+}
+
+// Q1 elasticity, one element per thread.  The scaled gradients
+// sqrt(w detJ) gradN_a(q) of all 8 points go to shared memory (each thread its
+// own column, no synchronisation), then every block pair a <= b contracts
+// them into A_ab and finishes K_ab with lambda, mu.
+constexpr int EL_T = 64;
+
+__global__ void __launch_bounds__(EL_T) k_elem_elastic_q1(int64_t n_el, const double *__restrict__ X,
+                                                          const int32_t *__restrict__ conn,
+                                                          const double *__restrict__ Ec, double nu, double b0,
+                                                          double b1, double b2, double *__restrict__ out,
+                                                          int *status)
+{
+    extern __shared__ double sg[];  // [q][a][i][EL_T]
+    const int tid = threadIdx.x;
+    const int64_t e = (int64_t)blockIdx.x * EL_T + tid;
+    if (e >= n_el) return;
+    const double E = Ec[e];
+    if (!isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = E / (2.0 * (1.0 + nu));
+    double x[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
+    double m[8] = {};
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+        double Ji[3][3];
+        const double wd = q1_jac(x, q, Ji);
+        const double sw = sqrt(wd);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double gi = q1_dref(q, a, 0) * Ji[0][i] + q1_dref(q, a, 1) * Ji[1][i] +
+                                  q1_dref(q, a, 2) * Ji[2][i];
+                sg[((q * 8 + a) * 3 + i) * EL_T + tid] = sw * gi;
+            }
+            m[a] = fma(wd, q1_n(q, a), m[a]);
+        }
+    }
+    double *o = out + e * (36 * 9 + 24);
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) {
+#pragma unroll 1
+        for (int b = a; b < 8; ++b) {
+            double A[3][3] = {};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                double ga[3], gb[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    ga[i] = sg[((q * 8 + a) * 3 + i) * EL_T + tid];
+                    gb[i] = sg[((q * 8 + b) * 3 + i) * EL_T + tid];
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int cp = 0; cp < 3; ++cp) A[c][cp] = fma(ga[c], gb[cp], A[c][cp]);
+            }
+            const double tr = A[0][0] + A[1][1] + A[2][2];
+            double *blk = o + upair(a, b) * 9;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int cp = 0; cp < 3; ++cp)
+                    blk[3 * c + cp] = lam * A[c][cp] + mu * A[cp][c] + (c == cp ? mu * tr : 0.0);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        o[324 + 3 * a + 0] = b0 * m[a];
+        o[324 + 3 * a + 1] = b1 * m[a];
+        o[324 + 3 * a + 2] = b2 * m[a];
+    }
+}
+
+// Taylor-Hood flow, one element per thread: A (6x6) then B_1, B_2 (3x6).
+__global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, const double *__restrict__ X,
+                                                    const int32_t *__restrict__ conn, const double *__restrict__ adv,
+                                                    double mu, double rho, double *__restrict__ out, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const int32_t *c = conn + 6 * e;
+    double gl[3][2];
+    const double det = tri_affine(X, c, gl);
+    double aN[6][2];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        aN[a][0] = adv[c[a]];
+        aN[a][1] = adv[n2 + c[a]];
+        if (!isfinite(aN[a][0]) || !isfinite(aN[a][1])) mf_dev_fail(status, MF_ERR_NONFINITE);
+    }
+    double *o = out + e * 72;
+    {
+        double A[36] = {};
+#pragma unroll 1
+        for (int q = 0; q < 6; ++q) {
+            double l[3], w;
+            tri6_point(q, l, w);
+            double N[6], g[6][2];
+            p2_basis(l, gl, N, g);
+            const double wd = w * det;
+            double ah0 = 0.0, ah1 = 0.0;
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+                ah0 = fma(aN[b][0], N[b], ah0);
+                ah1 = fma(aN[b][1], N[b], ah1);
+            }
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const double adv_a = ah0 * g[a][0] + ah1 * g[a][1];
+#pragma unroll
+                for (int b = 0; b < 6; ++b)
+                    A[6 * a + b] = fma(wd, mu * (g[a][0] * g[b][0] + g[a][1] * g[b][1]) - rho * adv_a * N[b], A[6 * a + b]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 36; ++t) o[t] = A[t];
+    }
+    {
+        double B[36] = {};
+#pragma unroll 1
+        for (int q = 0; q < 6; ++q) {
+            double l[3], w;
+            tri6_point(q, l, w);
+            double N[6], g[6][2];
+            p2_basis(l, gl, N, g);
+            const double wd = w * det;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 6; ++b) B[18 * i + 6 * a + b] = fma(wd * l[a], g[b][i], B[18 * i + 6 * a + b]);
+        }
+#pragma unroll
+        for (int t = 0; t < 36; ++t) o[36 + t] = B[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gather: one warp per row node; lanes over the node's column entries
+// ---------------------------------------------------------------------------
+template <int BS>
+__global__ void __launch_bounds__(256) k_gather(int64_t n_nodes, const int64_t *__restrict__ ptr,
+                                                const int32_t *__restrict__ col, const int64_t *__restrict__ cptr,
+                                                const int32_t *__restrict__ clist, const double *__restrict__ sc,
+                                                int64_t stride, int npe, const uint8_t *__restrict__ mask,
+                                                const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+                                                double *__restrict__ values, double *__restrict__ d)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (n >= n_nodes) return;
+    const int64_t p0 = ptr[n], deg = ptr[n + 1] - p0;
+    bool rm[BS];
+    double lift[BS], dsum[BS];
+    int64_t rbase[BS];
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+        rm[c] = mask ? mask[BS * n + c] != 0 : false;
+        lift[c] = 0.0;
+        dsum[c] = 0.0;
+        rbase[c] = row_ptr[BS * n + c];
+    }
+    for (int64_t k = lane; k < deg; k += 32) {
+        const int64_t p = p0 + k;
+        const int32_t mnode = col[p];
+        double acc[BS][BS];
+#pragma unroll
+        for (int c = 0; c < BS; ++c)
+#pragma unroll
+            for (int cp = 0; cp < BS; ++cp) acc[c][cp] = 0.0;
+        for (int64_t t = cptr[p]; t < cptr[p + 1]; ++t) {
+            const int32_t v = clist[t];
+            const int64_t e = v >> 6;
+            const int a = (v >> 3) & 7, b = v & 7;
+            const double *s = sc + e * stride;
+            if (BS == 1) {
+                acc[0][0] += s[a * npe + b];
+                if (mnode == n) dsum[0] += s[npe * npe + a];
+            } else {
+                if (a <= b) {
+                    const double *blk = s + upair(a, b) * 9;
+#pragma unroll
+                    for (int c = 0; c < BS; ++c)
+#pragma unroll
+                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * c + cp];
+                } else {
+                    const double *blk = s + upair(b, a) * 9;
+#pragma unroll
+                    for (int c = 0; c < BS; ++c)
+#pragma unroll
+                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * cp + c];
+                }
+                if (mnode == n)
+#pragma unroll
+                    for (int c = 0; c < BS; ++c) dsum[c] += s[324 + 3 * a + c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < BS; ++c)
+#pragma unroll
+            for (int cp = 0; cp < BS; ++cp) {
+                double v = acc[c][cp];
+                if (mask) {
+                    const int64_t r = BS * n + c, sdof = BS * (int64_t)mnode + cp;
+                    if (rm[c]) {
+                        v = (r == sdof) ? 1.0 : 0.0;
+                    } else if (mask[sdof]) {
+                        lift[c] -= v * bval[sdof];
+                        v = 0.0;
+                    }
+                }
+                values[rbase[c] + BS * k + cp] = v;
+            }
+    }
+#pragma unroll
+    for (int c = 0; c < BS; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lift[c] += __shfl_xor_sync(0xffffffffu, lift[c], o);
+            dsum[c] += __shfl_xor_sync(0xffffffffu, dsum[c], o);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < BS; ++c) d[BS * n + c] = rm[c] ? bval[BS * n + c] : dsum[c] + lift[c];
+}
+
+// flow rows: u_i(n) = [A over P2-P2 | -B_i^T over P2-P1]; p(n) = [B_1 | B_2 over P1-P2 | diag]
+__global__ void __launch_bounds__(256) k_gather_oseen(int64_t n2, int64_t n1, mf_adj pp, mf_adj pq, mf_adj qp,
+                                                      const double *__restrict__ sc, const uint8_t *__restrict__ mask,
+                                                      const double *__restrict__ bval,
+                                                      const int64_t *__restrict__ row_ptr, double *__restrict__ values,
+                                                      double *__restrict__ d)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= 2 * n2 + n1) return;
+    const bool rm = mask ? mask[r] != 0 : false;
+    const int64_t base = row_ptr[r];
+    double lift = 0.0;
+    auto put = [&](int64_t pos, int64_t sdof, double v) {
+        if (mask) {
+            if (rm) v = (r == sdof) ? 1.0 : 0.0;
+            else if (mask[sdof]) { lift -= v * bval[sdof]; v = 0.0; }
+        }
+        values[pos] = v;
+    };
+    if (r < 2 * n2) {
+        const int i = (int)(r / n2);
+        const int64_t n = r % n2;
+        const int64_t d0 = pp.ptr[n + 1] - pp.ptr[n];
+        for (int64_t k = lane; k < d0; k += 32) {
+            const int64_t p = pp.ptr[n] + k;
+            double acc = 0.0;
+            for (int64_t t = pp.cptr[p]; t < pp.cptr[p + 1]; ++t) {
+                const int32_t v = pp.clist[t];
+                acc += sc[(int64_t)(v >> 6) * 72 + ((v >> 3) & 7) * 6 + (v & 7)];
+            }
+            put(base + k, i * n2 + pp.col[p], acc);
+        }
+        const int64_t d1 = pq.ptr[n + 1] - pq.ptr[n];
+        for (int64_t k = lane; k < d1; k += 32) {
+            const int64_t p = pq.ptr[n] + k;
+            double acc = 0.0;
+            for (int64_t t = pq.cptr[p]; t < pq.cptr[p + 1]; ++t) {
+                const int32_t v = pq.clist[t];  // a: P2 local (velocity row), b: P1 local (pressure col)
+                acc -= sc[(int64_t)(v >> 6) * 72 + 36 + 18 * i + (v & 7) * 6 + ((v >> 3) & 7)];
+            }
+            put(base + d0 + k, 2 * n2 + pq.col[p], acc);
+        }
+    } else {
+        const int64_t n = r - 2 * n2;
+        const int64_t d2 = qp.ptr[n + 1] - qp.ptr[n];
+        for (int i = 0; i < 2; ++i)
+            for (int64_t k = lane; k < d2; k += 32) {
+                const int64_t p = qp.ptr[n] + k;
+                double acc = 0.0;
+                for (int64_t t = qp.cptr[p]; t < qp.cptr[p + 1]; ++t) {
+                    const int32_t v = qp.clist[t];  // a: P1 local (pressure row), b: P2 local (velocity col)
+                    acc += sc[(int64_t)(v >> 6) * 72 + 36 + 18 * i + ((v >> 3) & 7) * 6 + (v & 7)];
+                }
+                put(base + i * d2 + k, i * n2 + qp.col[p], acc);
+            }
+        if (lane == 0) put(base + 2 * d2, r, 0.0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
+    if (lane == 0) d[r] = rm ? bval[r] : lift;
+}
+
+// pressure-mass diagonal: one thread per P1 node, incident elements ascending
+__global__ void k_pmass(int64_t n1, const int64_t *__restrict__ pinc_ptr, const int32_t *__restrict__ pinc,
+                        const int32_t *__restrict__ pconn, const int32_t *__restrict__ conn,
+                        const double *__restrict__ X, double *__restrict__ out)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n1) return;
+    double s = 0.0;
+    for (int64_t t = pinc_ptr[n]; t < pinc_ptr[n + 1]; ++t) {
+        const int64_t e = pinc[t];
+        int a = 0;
+        while (a < 2 && pconn[3 * e + a] != n) ++a;
+        double gl[3][2];
+        const double det = tri_affine(X, conn + 6 * e, gl);
+        double m = 0.0;
+        for (int q = 0; q < 6; ++q) {
+            double l[3], w;
+            tri6_point(q, l, w);
+            m = fma(w * det, l[a] * l[a], m);
+        }
+        s += m;
+    }
+    out[n] = s;
+}
+
+// flow preconditioner: velocity rows diag(K), pressure rows p_scale * Mp (written by k_pmass
+// into out[2 n2 ..] beforehand), constrained dofs 1
+__global__ void k_flow_precond(int64_t n2, int64_t n_rows, const int64_t *__restrict__ rp,
+                               const int32_t *__restrict__ ci, const double *__restrict__ v,
+                               const uint8_t *__restrict__ mask, double p_scale, double *__restrict__ out)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    double val;
+    if (r < 2 * n2) {
+        val = 0.0;
+        for (int64_t t = rp[r]; t < rp[r + 1]; ++t)
+            if (ci[t] == r) val = v[t];
+    } else {
+        val = p_scale * out[r];
+    }
+    if (mask && mask[r]) val = 1.0;
+    out[r] = val;
+}
+
+}  // namespace
+
+mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,
+                               double p_scale, double *out, cudaStream_t st)
+{
+    const int64_t n2 = m->n_nodes;
+    k_pmass<<<nblk(m->n_pnodes, 128), 128, 0, st>>>(m->n_pnodes, p->pinc_ptr, p->pinc, m->pconn, m->conn,
+                                                    m->coords, out + 2 * n2);
+    k_flow_precond<<<nblk(p->n_rows, 256), 256, 0, st>>>(n2, p->n_rows, K->row_ptr, K->col_idx, K->values, mask,
+                                                         p_scale, out);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c, double *values,
+                           double *d, cudaStream_t st)
+{
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_assemble: status word unavailable");
+    const int64_t ne = m->n_elems;
+    if (form == MF_FORM_THERMAL) {
+        const double f = c->source[0];
+        if (m->elem == MF_P1_TRI)
+            k_elem_thermal_p1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
+                                                             status);
+        else if (m->elem == MF_P2_TRI)
+            k_elem_thermal_p2<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
+                                                             status);
+        else
+            k_elem_thermal_q1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
+                                                             status);
+        MF_CUDA(cudaGetLastError());
+        const mf_adj &A = p->adj[0];
+        k_gather<1><<<nblk(A.n_rows * 32, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, A.cptr, A.clist, p->scratch,
+                                                              p->scratch_stride, m->npe, c->bc_mask, c->bc_val,
+                                                              p->row_ptr, values, d);
+    } else if (form == MF_FORM_ELASTIC) {
+        const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;
+        static bool attr_set = false;  // idempotent; set once per process
+        if (!attr_set) {
+            MF_CUDA(cudaFuncSetAttribute(k_elem_elastic_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+        k_elem_elastic_q1<<<nblk(ne, EL_T), EL_T, smem, st>>>(ne, m->coords, m->conn, c->elem_coef, c->nu,
+                                                              c->source[0], c->source[1], c->source[2], p->scratch,
+                                                              status);
+        MF_CUDA(cudaGetLastError());
+        const mf_adj &A = p->adj[0];
+        k_gather<3><<<nblk(A.n_rows * 32, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, A.cptr, A.clist, p->scratch,
+                                                              p->scratch_stride, 8, c->bc_mask, c->bc_val,
+                                                              p->row_ptr, values, d);
+    } else {
+        k_elem_oseen<<<nblk(ne, 128), 128, 0, st>>>(ne, m->n_nodes, m->coords, m->conn, c->advect, c->visc, c->rho,
+                                                    p->scratch, status);
+        MF_CUDA(cudaGetLastError());
+        k_gather_oseen<<<nblk(p->n_rows * 32, 256), 256, 0, st>>>(m->n_nodes, m->n_pnodes, p->adj[0], p->adj[1],
+                                                                  p->adj[2], p->scratch, c->bc_mask, c->bc_val,
+                                                                  p->row_ptr, values, d);
+    }
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st)
+{
+    k_pmass<<<nblk(m->n_pnodes, 128), 128, 0, st>>>(m->n_pnodes, p->pinc_ptr, p->pinc, m->pconn, m->conn,
+                                                    m->coords, out);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}

@@ -1,0 +1,88 @@
+// Internal declarations of the mf library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mf.h"
+
+#define MF_MAX_DEG 64   // neighbours of one node in one adjacency
+#define MF_MAX_INC 32   // elements incident to one node
+
+// Adjacency between a row node space and a column node space (Block B-1: the
+// unique control-point pairs), with, for every node pair, the list of element
+// contributions (e, a, b) in ascending element order.
+struct mf_adj {
+    int64_t n_rows = 0;      // row nodes
+    int64_t n_pairs = 0;     // unique (row node, col node) pairs
+    int64_t *ptr = nullptr;  // [n_rows + 1]
+    int32_t *col = nullptr;  // [n_pairs] ascending per row
+    int64_t *cptr = nullptr; // [n_pairs + 1]
+    int32_t *clist = nullptr;// [n_contrib] packed e * 64 + a * 8 + b
+    int64_t n_contrib = 0;
+};
+
+struct mf_mesh {
+    int dim, elem, npe;
+    int64_t n_nodes, n_elems, n_pnodes;
+    const double *coords;
+    const int32_t *conn;
+    const int32_t *pconn;
+    int device;
+};
+
+struct mf_pattern {
+    int form;
+    const mf_mesh *mesh;
+    int64_t n_rows = 0, nnz = 0;
+    int64_t *row_ptr = nullptr;
+    int32_t *col_idx = nullptr;
+    // adjacencies: [0] row space x row space; flow adds [1] P2 rows x P1
+    // cols and [2] P1 rows x P2 cols
+    mf_adj adj[3];
+    int n_adj = 0;
+    // element-matrix scratch of the FP64 path (doubles per element x n_elems)
+    double *scratch = nullptr;
+    int64_t scratch_stride = 0;
+    // incident elements per row node (ascending), for the mixed path
+    int64_t *inc_ptr = nullptr;
+    int32_t *inc = nullptr;
+    // flow: elements incident to each P1 pressure node, ascending
+    int64_t *pinc_ptr = nullptr;
+    int32_t *pinc = nullptr;
+};
+
+// status word (device) of the current device
+int *mf_status_word();
+mf_status mf_fail(mf_status s, const char *fmt, ...);
+mf_status mf_cuda_check(cudaError_t e, const char *what);
+
+// exclusive scan of n int64 counts in place; total written to *d_total (device)
+cudaError_t mf_scan_i64(int64_t *d_data, int64_t n, int64_t *d_total, cudaStream_t st);
+
+static inline int mf_npe(int elem) { return elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : 8); }
+static inline int mf_ndim(int elem) { return elem == MF_Q1_HEX ? 3 : 2; }
+
+// pattern / assembly entry points implemented in the .cu files
+mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_pattern *p);
+void mf_pattern_free(mf_pattern *p);
+mf_status mf_mesh_validate(const mf_mesh *m, cudaStream_t st);
+mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
+                           double *values, double *d, cudaStream_t st);
+mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
+                            double *values, double *d, cudaStream_t st);
+mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,
+                               double p_scale, double *out, cudaStream_t st);
+mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);
+mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o,
+                        mf_solve_info *info, cudaStream_t st);
+mf_status mf_spmv_impl(const mf_csr *K, const double *x, double *y, cudaStream_t st);
+
+// device status codes are written with atomicCAS(word, 0, code): first error wins
+__device__ __forceinline__ void mf_dev_fail(int *word, int code) { atomicCAS(word, 0, code); }
+
+#define MF_CUDA(call)                                                      \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return mf_cuda_check(e_, #call);            \
+    } while (0)

@@ -1,0 +1,440 @@
+// Mesh validation and sparsity pattern (MetaFEM Sec. 2.2 Block B).
+//
+// Block B-1 collects the unique control-point pairs of every element, Block
+// B-4 gives each (symbol pair, control-point pair) one sparse id.  Here the
+// unique pairs of a row node space and a column node space form an adjacency
+// (CSR over row nodes, ascending columns) built without hashing: per row node
+// the incident elements are gathered and their nodes sorted and de-duplicated
+// in registers.  Each node pair also keeps the list of element contributions
+// (e, a, b) in ascending element order, which fixes the summation order of the
+// assembly.  The dof-level CSR of a form is then laid out from its blocks.
+#include <cstdio>
+
+#include "mf_internal.h"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned nblk(int64_t n, int t = TPB) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// mesh validation: indices in range, finite coordinates, detJ > 0 at every
+// quadrature point of the rules the assembly uses
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double *__restrict__ X,
+                           const int32_t *__restrict__ conn, int64_t n_p, const int32_t *__restrict__ pconn,
+                           int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const int npe = elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : 8);
+    for (int a = 0; a < npe; ++a) {
+        const int32_t v = conn[e * npe + a];
+        if (v < 0 || v >= n_nodes) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
+    }
+    if (pconn)
+        for (int a = 0; a < 3; ++a) {
+            const int32_t v = pconn[e * 3 + a];
+            if (v < 0 || v >= n_p) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
+        }
+    if (elem != MF_Q1_HEX) {
+        const int32_t *c = conn + e * npe;
+        const double x0 = X[2 * c[0]], y0 = X[2 * c[0] + 1];
+        const double x1 = X[2 * c[1]], y1 = X[2 * c[1] + 1];
+        const double x2 = X[2 * c[2]], y2 = X[2 * c[2] + 1];
+        const double det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+        if (!isfinite(det)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
+        if (!(det > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
+        return;
+    }
+    double x[8][3];
+    for (int a = 0; a < 8; ++a)
+        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[e * 8 + a] + i];
+    const double g = 0.57735026918962576451;  // 1/sqrt(3)
+    for (int q = 0; q < 8; ++q) {
+        const double xi[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+        double J[3][3] = {};
+        for (int a = 0; a < 8; ++a) {
+            const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+            const double f[3] = {1.0 + s[0] * xi[0], 1.0 + s[1] * xi[1], 1.0 + s[2] * xi[2]};
+            const double dN[3] = {0.125 * s[0] * f[1] * f[2], 0.125 * f[0] * s[1] * f[2], 0.125 * f[0] * f[1] * s[2]};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) J[i][j] += x[a][i] * dN[j];
+        }
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (!isfinite(det)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
+        if (!(det > 0.0)) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// incidence: elements of every node, ascending
+// ---------------------------------------------------------------------------
+__global__ void k_inc_count(int64_t n_el, int npe, const int32_t *__restrict__ conn, int64_t *cnt)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_el * npe) return;
+    atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[conn[t]]), 1ull);
+}
+
+__global__ void k_inc_fill(int64_t n_el, int npe, const int32_t *__restrict__ conn, const int64_t *ptr,
+                           int64_t *cursor, int32_t *inc)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_el * npe) return;
+    const int32_t v = conn[t];
+    const int64_t pos = ptr[v] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[v]), 1ull);
+    inc[pos] = (int32_t)(t / npe);
+}
+
+__global__ void k_sort_segments_i32(int64_t n, const int64_t *__restrict__ ptr, int32_t *v, int *status)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t b = ptr[r], e = ptr[r + 1];
+    if (e - b > 4 * MF_MAX_INC) { mf_dev_fail(status, MF_ERR_UNSUPPORTED); return; }
+    for (int64_t i = b + 1; i < e; ++i) {  // insertion sort of a short segment
+        const int32_t x = v[i];
+        int64_t j = i - 1;
+        while (j >= b && v[j] > x) { v[j + 1] = v[j]; --j; }
+        v[j + 1] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjacency between row space (conn_r, npe_r) and column space (conn_c, npe_c)
+// ---------------------------------------------------------------------------
+template <bool FILL>
+__global__ void k_adj(int64_t n_rows, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
+                      int npe_c, const int32_t *__restrict__ conn_c, bool self, int64_t *cnt,
+                      const int64_t *__restrict__ ptr, int32_t *col, int *status)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    int32_t nb[MF_MAX_DEG];
+    int deg = 0;
+    if (self) nb[deg++] = (int32_t)r;  // square adjacency: the diagonal is always present
+    const int64_t b = inc_ptr[r], e = inc_ptr[r + 1];
+    if (e - b > MF_MAX_INC) { mf_dev_fail(status, MF_ERR_UNSUPPORTED); return; }
+    for (int64_t t = b; t < e; ++t) {
+        const int32_t el = inc[t];
+        for (int a = 0; a < npe_c; ++a) {
+            const int32_t m = conn_c[(int64_t)el * npe_c + a];
+            int pos = 0;
+            while (pos < deg && nb[pos] < m) ++pos;
+            if (pos < deg && nb[pos] == m) continue;
+            if (deg == MF_MAX_DEG) { mf_dev_fail(status, MF_ERR_UNSUPPORTED); return; }
+            for (int s = deg; s > pos; --s) nb[s] = nb[s - 1];
+            nb[pos] = m;
+            ++deg;
+        }
+    }
+    if (!FILL) {
+        cnt[r] = deg;
+    } else {
+        int32_t *out = col + ptr[r];
+        for (int s = 0; s < deg; ++s) out[s] = nb[s];
+    }
+}
+
+__device__ __forceinline__ int64_t find_pair(const int64_t *ptr, const int32_t *col, int32_t n, int32_t m)
+{
+    int64_t lo = ptr[n], hi = ptr[n + 1] - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < m) lo = mid + 1; else hi = mid;
+    }
+    return lo;  // the pair exists by construction
+}
+
+// contributions: one thread per (element, a in row space, b in column space)
+template <bool FILL>
+__global__ void k_contrib(int64_t n_el, int npe_r, const int32_t *__restrict__ conn_r, int npe_c,
+                          const int32_t *__restrict__ conn_c, const int64_t *__restrict__ ptr,
+                          const int32_t *__restrict__ col, int64_t *cnt, const int64_t *__restrict__ cptr,
+                          int32_t *clist)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int per = npe_r * npe_c;
+    if (t >= n_el * per) return;
+    const int64_t e = t / per;
+    const int a = (int)(t % per) / npe_c, b = (int)(t % per) % npe_c;
+    const int32_t n = conn_r[e * npe_r + a], m = conn_c[e * npe_c + b];
+    const int64_t p = find_pair(ptr, col, n, m);
+    if (!FILL) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[p]), 1ull);
+    } else {
+        const int64_t pos =
+            cptr[p] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[p]), 1ull);
+        clist[pos] = (int32_t)(e * 64 + a * 8 + b);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dof-level CSR of each form
+// ---------------------------------------------------------------------------
+__global__ void k_csr_thermal(int64_t n, const int64_t *__restrict__ ptr, int64_t *row_ptr)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r <= n) row_ptr[r] = ptr[r];
+}
+
+__global__ void k_csr_elastic(int64_t n_nodes, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                              int64_t *row_ptr, int32_t *col_idx)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > 3 * n_nodes) return;
+    if (t == 3 * n_nodes) { row_ptr[t] = 9 * ptr[n_nodes]; return; }
+    const int64_t n = t / 3;
+    const int c = (int)(t % 3);
+    const int64_t deg = ptr[n + 1] - ptr[n];
+    const int64_t base = 9 * ptr[n] + 3 * c * deg;
+    row_ptr[t] = base;
+    for (int64_t k = 0; k < deg; ++k)
+        for (int cp = 0; cp < 3; ++cp) col_idx[base + 3 * k + cp] = 3 * col[ptr[n] + k] + cp;
+}
+
+// flow: rows u_i(n) = [u_i cols over P2-P2 | p cols over P2-P1];
+//       rows p(n)   = [u1 cols over P1-P2 | u2 cols over P1-P2 | p(n)]
+__global__ void k_csr_oseen_len(int64_t n2, int64_t n1, const int64_t *__restrict__ pp, const int64_t *__restrict__ pq,
+                                const int64_t *__restrict__ qp, int64_t *len)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 2 * n2 + n1) return;
+    if (r < 2 * n2) {
+        const int64_t n = r % n2;
+        len[r] = (pp[n + 1] - pp[n]) + (pq[n + 1] - pq[n]);
+    } else {
+        const int64_t n = r - 2 * n2;
+        len[r] = 2 * (qp[n + 1] - qp[n]) + 1;
+    }
+}
+
+__global__ void k_csr_oseen_fill(int64_t n2, int64_t n1, const int64_t *__restrict__ pp, const int32_t *__restrict__ ppc,
+                                 const int64_t *__restrict__ pq, const int32_t *__restrict__ pqc,
+                                 const int64_t *__restrict__ qp, const int32_t *__restrict__ qpc,
+                                 const int64_t *__restrict__ row_ptr, int32_t *col_idx)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 2 * n2 + n1) return;
+    int32_t *out = col_idx + row_ptr[r];
+    if (r < 2 * n2) {
+        const int64_t i = r / n2, n = r % n2;
+        int64_t o = 0;
+        for (int64_t t = pp[n]; t < pp[n + 1]; ++t) out[o++] = (int32_t)(i * n2 + ppc[t]);
+        for (int64_t t = pq[n]; t < pq[n + 1]; ++t) out[o++] = (int32_t)(2 * n2 + pqc[t]);
+    } else {
+        const int64_t n = r - 2 * n2;
+        int64_t o = 0;
+        for (int i = 0; i < 2; ++i)
+            for (int64_t t = qp[n]; t < qp[n + 1]; ++t) out[o++] = (int32_t)(i * n2 + qpc[t]);
+        out[o] = (int32_t)r;
+    }
+}
+
+struct Incidence {
+    int64_t *ptr = nullptr;
+    int32_t *inc = nullptr;
+};
+
+mf_status build_incidence(int64_t n_nodes, int64_t n_el, int npe, const int32_t *conn, cudaStream_t st,
+                          Incidence *out, int *status)
+{
+    int64_t *cursor = nullptr;
+    MF_CUDA(cudaMallocAsync(&out->ptr, sizeof(int64_t) * (n_nodes + 1), st));
+    MF_CUDA(cudaMallocAsync(&out->inc, sizeof(int32_t) * n_el * npe, st));
+    MF_CUDA(cudaMallocAsync(&cursor, sizeof(int64_t) * n_nodes, st));
+    MF_CUDA(cudaMemsetAsync(out->ptr, 0, sizeof(int64_t) * (n_nodes + 1), st));
+    MF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int64_t) * n_nodes, st));
+    k_inc_count<<<nblk(n_el * npe), TPB, 0, st>>>(n_el, npe, conn, out->ptr);
+    MF_CUDA(mf_scan_i64(out->ptr, n_nodes + 1, nullptr, st));
+    k_inc_fill<<<nblk(n_el * npe), TPB, 0, st>>>(n_el, npe, conn, out->ptr, cursor, out->inc);
+    k_sort_segments_i32<<<nblk(n_nodes), TPB, 0, st>>>(n_nodes, out->ptr, out->inc, status);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaFreeAsync(cursor, st));
+    return MF_OK;
+}
+
+mf_status read_i64(const int64_t *d, int64_t *h, cudaStream_t st)
+{
+    MF_CUDA(cudaMemcpyAsync(h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    return MF_OK;
+}
+
+mf_status check_status(int *status, cudaStream_t st, const char *what)
+{
+    int h = 0;
+    MF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        const int zero = 0;
+        MF_CUDA(cudaMemcpyAsync(status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        if (h == MF_ERR_UNSUPPORTED)
+            return mf_fail(MF_ERR_UNSUPPORTED, "%s: node valence above %d elements / %d neighbours", what,
+                           MF_MAX_INC, MF_MAX_DEG);
+        return mf_fail((mf_status)h, "%s: device status %d", what, h);
+    }
+    return MF_OK;
+}
+
+mf_status build_adj(int64_t n_rows, const Incidence &inc, int64_t n_el, int npe_r, const int32_t *conn_r,
+                    int npe_c, const int32_t *conn_c, cudaStream_t st, mf_adj *A, int *status)
+{
+    A->n_rows = n_rows;
+    MF_CUDA(cudaMallocAsync(&A->ptr, sizeof(int64_t) * (n_rows + 1), st));
+    MF_CUDA(cudaMemsetAsync(A->ptr, 0, sizeof(int64_t) * (n_rows + 1), st));
+    const bool self = conn_r == conn_c;
+    k_adj<false><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self, A->ptr,
+                                                   nullptr, nullptr, status);
+    MF_CUDA(cudaGetLastError());
+    mf_status s = check_status(status, st, "mf_pattern_build");
+    if (s != MF_OK) return s;
+    MF_CUDA(mf_scan_i64(A->ptr, n_rows + 1, nullptr, st));
+    s = read_i64(A->ptr + n_rows, &A->n_pairs, st);
+    if (s != MF_OK) return s;
+    MF_CUDA(cudaMallocAsync(&A->col, sizeof(int32_t) * A->n_pairs, st));
+    k_adj<true><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self, nullptr,
+                                                  A->ptr, A->col, status);
+    // contributions of every pair, ascending packed (e, a, b)
+    int64_t *cnt = nullptr;
+    MF_CUDA(cudaMallocAsync(&A->cptr, sizeof(int64_t) * (A->n_pairs + 1), st));
+    MF_CUDA(cudaMallocAsync(&cnt, sizeof(int64_t) * A->n_pairs, st));
+    MF_CUDA(cudaMemsetAsync(A->cptr, 0, sizeof(int64_t) * (A->n_pairs + 1), st));
+    MF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * A->n_pairs, st));
+    const int64_t work = n_el * npe_r * npe_c;
+    k_contrib<false><<<nblk(work), TPB, 0, st>>>(n_el, npe_r, conn_r, npe_c, conn_c, A->ptr, A->col, A->cptr,
+                                                nullptr, nullptr);
+    MF_CUDA(mf_scan_i64(A->cptr, A->n_pairs + 1, nullptr, st));
+    A->n_contrib = work;
+    MF_CUDA(cudaMallocAsync(&A->clist, sizeof(int32_t) * work, st));
+    k_contrib<true><<<nblk(work), TPB, 0, st>>>(n_el, npe_r, conn_r, npe_c, conn_c, A->ptr, A->col, cnt,
+                                               A->cptr, A->clist);
+    k_sort_segments_i32<<<nblk(A->n_pairs), TPB, 0, st>>>(A->n_pairs, A->cptr, A->clist, status);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaFreeAsync(cnt, st));
+    return check_status(status, st, "mf_pattern_build");
+}
+
+void free_inc(Incidence &I, cudaStream_t st)
+{
+    if (I.ptr) cudaFreeAsync(I.ptr, st);
+    if (I.inc) cudaFreeAsync(I.inc, st);
+    I = Incidence();
+}
+
+}  // namespace
+
+mf_status mf_mesh_validate(const mf_mesh *m, cudaStream_t st)
+{
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_mesh_create: status word unavailable");
+    MF_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    k_validate<<<nblk(m->n_elems), TPB, 0, st>>>(m->elem, m->n_elems, m->n_nodes, m->coords, m->conn,
+                                                 m->n_pnodes, m->pconn, status);
+    MF_CUDA(cudaGetLastError());
+    int h = 0;
+    MF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        const int zero = 0;
+        MF_CUDA(cudaMemcpyAsync(status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        return mf_fail((mf_status)h, h == MF_ERR_BAD_MESH
+                                         ? "mf_mesh_create: index out of range or detJ <= 0"
+                                         : "mf_mesh_create: non-finite coordinates");
+    }
+    return MF_OK;
+}
+
+void mf_pattern_free(mf_pattern *p)
+{
+    cudaFree(p->row_ptr);
+    cudaFree(p->col_idx);
+    for (int i = 0; i < 3; ++i) {
+        cudaFree(p->adj[i].ptr);
+        cudaFree(p->adj[i].col);
+        cudaFree(p->adj[i].cptr);
+        cudaFree(p->adj[i].clist);
+        p->adj[i] = mf_adj();
+    }
+    cudaFree(p->scratch);
+    cudaFree(p->inc_ptr);
+    cudaFree(p->inc);
+    cudaFree(p->pinc_ptr);
+    cudaFree(p->pinc);
+    p->pinc_ptr = nullptr;
+    p->pinc = nullptr;
+    p->row_ptr = nullptr;
+    p->col_idx = nullptr;
+    p->scratch = nullptr;
+    p->inc_ptr = nullptr;
+    p->inc = nullptr;
+}
+
+mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_pattern *p)
+{
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_pattern_build: status word unavailable");
+    MF_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    const int npe = m->npe;
+    Incidence incv;
+    mf_status s = build_incidence(m->n_nodes, m->n_elems, npe, m->conn, st, &incv, status);
+    if (s == MF_OK) s = check_status(status, st, "mf_pattern_build");
+    if (s != MF_OK) { free_inc(incv, st); return s; }
+    s = build_adj(m->n_nodes, incv, m->n_elems, npe, m->conn, npe, m->conn, st, &p->adj[0], status);
+    p->n_adj = 1;
+    if (s != MF_OK) { free_inc(incv, st); return s; }
+
+    if (form == MF_FORM_THERMAL) {
+        p->n_rows = m->n_nodes;
+        p->nnz = p->adj[0].n_pairs;
+        MF_CUDA(cudaMallocAsync(&p->row_ptr, sizeof(int64_t) * (p->n_rows + 1), st));
+        MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
+        k_csr_thermal<<<nblk(p->n_rows + 1), TPB, 0, st>>>(p->n_rows, p->adj[0].ptr, p->row_ptr);
+        MF_CUDA(cudaMemcpyAsync(p->col_idx, p->adj[0].col, sizeof(int32_t) * p->nnz, cudaMemcpyDeviceToDevice, st));
+        p->scratch_stride = (int64_t)npe * npe + npe;
+    } else if (form == MF_FORM_ELASTIC) {
+        p->n_rows = 3 * m->n_nodes;
+        p->nnz = 9 * p->adj[0].n_pairs;
+        if (p->nnz >= INT32_MAX) { free_inc(incv, st); return mf_fail(MF_ERR_UNSUPPORTED, "nnz above 2^31"); }
+        MF_CUDA(cudaMallocAsync(&p->row_ptr, sizeof(int64_t) * (p->n_rows + 1), st));
+        MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
+        k_csr_elastic<<<nblk(p->n_rows + 1), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->row_ptr,
+                                                           p->col_idx);
+        p->scratch_stride = 36 * 9 + 24;
+    } else {
+        Incidence incp;
+        s = build_incidence(m->n_pnodes, m->n_elems, 3, m->pconn, st, &incp, status);
+        if (s == MF_OK) s = build_adj(m->n_nodes, incv, m->n_elems, 6, m->conn, 3, m->pconn, st, &p->adj[1], status);
+        if (s == MF_OK) s = build_adj(m->n_pnodes, incp, m->n_elems, 3, m->pconn, 6, m->conn, st, &p->adj[2], status);
+        p->pinc_ptr = incp.ptr;
+        p->pinc = incp.inc;
+        p->n_adj = 3;
+        if (s != MF_OK) { free_inc(incv, st); return s; }
+        const int64_t n2 = m->n_nodes, n1 = m->n_pnodes;
+        p->n_rows = 2 * n2 + n1;
+        MF_CUDA(cudaMallocAsync(&p->row_ptr, sizeof(int64_t) * (p->n_rows + 1), st));
+        MF_CUDA(cudaMemsetAsync(p->row_ptr, 0, sizeof(int64_t) * (p->n_rows + 1), st));
+        k_csr_oseen_len<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[1].ptr, p->adj[2].ptr,
+                                                        p->row_ptr);
+        MF_CUDA(mf_scan_i64(p->row_ptr, p->n_rows + 1, nullptr, st));
+        s = read_i64(p->row_ptr + p->n_rows, &p->nnz, st);
+        if (s != MF_OK) { free_inc(incv, st); return s; }
+        MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
+        k_csr_oseen_fill<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[0].col, p->adj[1].ptr,
+                                                         p->adj[1].col, p->adj[2].ptr, p->adj[2].col, p->row_ptr,
+                                                         p->col_idx);
+        p->scratch_stride = 72;
+    }
+    MF_CUDA(cudaGetLastError());
+    p->inc_ptr = incv.ptr;
+    p->inc = incv.inc;
+    MF_CUDA(cudaMallocAsync(&p->scratch, sizeof(double) * p->scratch_stride * m->n_elems, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    return check_status(status, st, "mf_pattern_build");
+}

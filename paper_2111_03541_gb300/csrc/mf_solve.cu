@@ -1,0 +1,733 @@
+// Krylov solvers for K x = d (MetaFEM Sec. 2.2 Block D-4: "direct or
+// iterative" solver, left open by the paper).
+//
+// Jacobi-PCG runs three kernels per iteration: q = K p with the partial sums
+// of p.q; x += alpha p, r -= alpha q with the partial sums of r.D^-1 r and
+// r.r; p = D^-1 r + beta p.  Each reduction is finished by the last block to
+// arrive, in block order, so results are bit-reproducible and alpha, beta stay
+// on the device.  A CUDA graph holds `check_every` iterations; the host reads
+// the residual between replays, and kernels past convergence return at once.
+//
+// GMRES(m) is right preconditioned by a diagonal P: it runs on K' = K P^-1
+// (columns scaled once) and returns x = P^-1 y.  Arnoldi uses classical
+// Gram-Schmidt applied twice (block dot products and one multi-vector update
+// per pass); the Givens rotations of the Hessenberg column run in a
+// single-thread kernel, so a whole cycle stays on the device.
+#include <cmath>
+
+#include "mf_internal.h"
+
+namespace {
+
+constexpr int RT = 256;       // threads per reduction block
+constexpr int RED_BLOCKS = 1024;  // fixed grid of the reduction kernels (bit-reproducible)
+
+struct PcgState {
+    double rz, pq, rr, dd, tol2, alpha, beta;
+    long long iter, max_iter;
+    int done;         // 1 converged, 2 iteration cap, 3 breakdown / non-finite
+    unsigned ticket;  // last-block counter
+};
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;  // valid in thread 0
+}
+
+// returns true in the one thread (thread 0 of the last block) that may finish
+__device__ bool last_block(unsigned *ticket)
+{
+    __shared__ bool last;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        *ticket = 0;
+        __threadfence();
+        return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// SpMV: W lanes per row
+// ---------------------------------------------------------------------------
+// Every lane of the warp calls the shuffles (full mask): rows past n give 0.
+template <int W>
+__device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                          const double *__restrict__ v, const double *__restrict__ x, int64_t row,
+                                          int sub, bool valid)
+{
+    double s = 0.0;
+    if (valid)
+        for (int64_t t = rp[row] + sub; t < rp[row + 1]; t += W) s = fma(v[t], __ldg(&x[ci[t]]), s);
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, W);
+    return s;
+}
+
+template <int W>
+__global__ void __launch_bounds__(RT) k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                             const double *__restrict__ v, const double *__restrict__ x,
+                                             double *__restrict__ y)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = g / W;
+    const int sub = (int)(g % W);
+    const bool valid = row < n;
+    const double s = row_dot<W>(rp, ci, v, x, row, sub, valid);
+    if (valid && sub == 0) y[row] = s;
+}
+
+// q = K p and partial p.q; grid-stride over rows so the grid is fixed
+template <int W>
+__global__ void __launch_bounds__(RT) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
+                                                 const int32_t *__restrict__ ci, const double *__restrict__ v,
+                                                 const double *__restrict__ p, double *__restrict__ q,
+                                                 double *__restrict__ part, PcgState *S)
+{
+    __shared__ double sh[RT / 32];
+    if (S->done) return;
+    double acc = 0.0;
+    const int64_t rows_per_pass = (int64_t)gridDim.x * blockDim.x / W;
+    const int sub = threadIdx.x % W;
+    // warp-uniform trip count: the loop runs while the warp's first row is in range
+    const int64_t first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / W;
+    for (int64_t off = 0; first + off < n; off += rows_per_pass) {
+        const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W + off;
+        const bool valid = row < n;
+        const double s = row_dot<W>(rp, ci, v, p, row, sub, valid);
+        if (valid && sub == 0) {
+            q[row] = s;
+            acc = fma(p[row], s, acc);
+        }
+    }
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (last_block(&S->ticket)) {
+        double pq = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) pq += part[b];
+        S->pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) S->done = 3;
+        else S->alpha = S->rz / pq;
+    }
+}
+
+// x += alpha p; r -= alpha q; partial r.D^-1 r and r.r
+__global__ void __launch_bounds__(RT) k_pcg_update(int64_t n, const double *__restrict__ dinv,
+                                                   const double *__restrict__ p, const double *__restrict__ q,
+                                                   double *__restrict__ x, double *__restrict__ r,
+                                                   double *__restrict__ part, PcgState *S)
+{
+    __shared__ double sh[RT / 32];
+    if (S->done) return;
+    const double alpha = S->alpha;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rz = fma(ri * dinv[i], ri, rz);
+        rr = fma(ri, ri, rr);
+    }
+    const double bz = block_sum(rz, sh);
+    const double br = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = bz;
+        part[2 * blockIdx.x + 1] = br;
+    }
+    if (last_block(&S->ticket)) {
+        double z = 0.0, s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            z += part[2 * b];
+            s += part[2 * b + 1];
+        }
+        S->iter += 1;
+        S->rr = s;
+        if (!isfinite(s) || !isfinite(z)) S->done = 3;
+        else if (s <= S->tol2 * S->dd) S->done = 1;
+        else if (S->iter >= S->max_iter) S->done = 2;
+        S->beta = z / S->rz;
+        S->rz = z;
+    }
+}
+
+// p = D^-1 r + beta p
+__global__ void __launch_bounds__(RT) k_pcg_dir(int64_t n, const double *__restrict__ dinv,
+                                                const double *__restrict__ r, double *__restrict__ p,
+                                                const PcgState *S)
+{
+    if (S->done) return;
+    const double beta = S->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], dinv[i] * r[i]);
+}
+
+// set-up: dinv = 1 / diag(K); r = d - q (q = K x0); p = D^-1 r; rz, rr, dd
+__global__ void k_diag_inv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ v, double *__restrict__ dinv, int *bad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double di = 0.0;
+    for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
+        if (ci[t] == i) di = v[t];
+    dinv[i] = 1.0 / di;
+    if (!(di != 0.0) || !isfinite(di)) atomicExch(bad, 1);
+}
+
+__global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const double *__restrict__ d, const double *__restrict__ q,
+                                                 const double *__restrict__ dinv, double *__restrict__ r,
+                                                 double *__restrict__ p, double *__restrict__ part, PcgState *S)
+{
+    __shared__ double sh[RT / 32];
+    double rz = 0.0, rr = 0.0, dd = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = d[i] - q[i];
+        r[i] = ri;
+        p[i] = dinv[i] * ri;
+        rz = fma(ri * dinv[i], ri, rz);
+        rr = fma(ri, ri, rr);
+        dd = fma(d[i], d[i], dd);
+    }
+    const double a = block_sum(rz, sh), b = block_sum(rr, sh), c = block_sum(dd, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = a;
+        part[3 * blockIdx.x + 1] = b;
+        part[3 * blockIdx.x + 2] = c;
+    }
+    if (last_block(&S->ticket)) {
+        double z = 0.0, s = 0.0, t = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) {
+            z += part[3 * k];
+            s += part[3 * k + 1];
+            t += part[3 * k + 2];
+        }
+        S->rz = z;
+        S->rr = s;
+        S->dd = t;
+        if (!isfinite(z) || !isfinite(s) || !isfinite(t)) S->done = 3;
+        else if (s <= S->tol2 * t) S->done = 1;
+        else if (S->max_iter == 0) S->done = 2;
+    }
+}
+
+// ||d - K x|| / ||d|| : r_true into part-reduction; also used by GMRES
+__global__ void __launch_bounds__(RT) k_resid_norm(int64_t n, const double *__restrict__ d,
+                                                   const double *__restrict__ kx, double *__restrict__ part,
+                                                   unsigned *ticket, double *out2 /* [2]: rr, dd */)
+{
+    __shared__ double sh[RT / 32];
+    double rr = 0.0, dd = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = d[i] - kx[i];
+        rr = fma(ri, ri, rr);
+        dd = fma(d[i], d[i], dd);
+    }
+    const double a = block_sum(rr, sh), b = block_sum(dd, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+    if (last_block(ticket)) {
+        double s = 0.0, t = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) {
+            s += part[2 * k];
+            t += part[2 * k + 1];
+        }
+        out2[0] = s;
+        out2[1] = t;
+    }
+}
+
+int spmv_width(int64_t n, int64_t nnz)
+{
+    const double avg = (double)nnz / (double)n;
+    return avg <= 8 ? 4 : (avg <= 24 ? 8 : (avg <= 48 ? 16 : 32));
+}
+
+template <int W>
+void launch_spmv(const mf_csr *K, const double *v, const double *x, double *y, cudaStream_t st)
+{
+    k_spmv<W><<<nblk(K->n_rows * W, RT), RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, v, x, y);
+}
+
+void spmv_any(const mf_csr *K, const double *v, const double *x, double *y, cudaStream_t st)
+{
+    switch (spmv_width(K->n_rows, K->nnz)) {
+    case 4: launch_spmv<4>(K, v, x, y, st); break;
+    case 8: launch_spmv<8>(K, v, x, y, st); break;
+    case 16: launch_spmv<16>(K, v, x, y, st); break;
+    default: launch_spmv<32>(K, v, x, y, st); break;
+    }
+}
+
+template <int W>
+void launch_pcg_spmv(const mf_csr *K, const double *p, double *q, double *part, PcgState *S, cudaStream_t st)
+{
+    k_pcg_spmv<W><<<RED_BLOCKS, RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, K->values, p, q, part, S);
+}
+
+// ---------------------------------------------------------------------------
+// GMRES kernels
+// ---------------------------------------------------------------------------
+struct GmState {
+    double beta0, dd, tol2;
+    long long iter, max_iter;
+    int j;           // current Arnoldi column in the cycle
+    int done;        // 1 converged, 2 cap, 3 breakdown
+    int cycle_end;   // 1 when the cycle must stop (converged or j == m)
+    unsigned ticket;
+};
+
+__global__ void k_recip(int64_t n, const double *__restrict__ a, double *__restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = 1.0 / a[i];
+}
+
+__global__ void k_scale_cols(int64_t nnz, const int32_t *__restrict__ ci, const double *__restrict__ v,
+                             const double *__restrict__ pd, double *__restrict__ out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nnz) out[t] = v[t] / pd[ci[t]];
+}
+
+// partial dot products of w with V[0..j] (j+1 vectors), per block
+__global__ void __launch_bounds__(RT) k_block_dots(int64_t n, const double *__restrict__ V, int64_t ldv,
+                                                   const double *__restrict__ w, const GmState *S,
+                                                   double *__restrict__ part /* [grid][m+1] */, int mp1)
+{
+    __shared__ double sh[RT / 32];
+    if (S->cycle_end) return;
+    const int j = S->j;
+    for (int k = 0; k <= j; ++k) {
+        double acc = 0.0;
+        const double *vk = V + (int64_t)k * ldv;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            acc = fma(vk[i], w[i], acc);
+        const double b = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * mp1 + k] = b;
+    }
+}
+
+// h[k] = sum over blocks of part[.][k], in block order; H column j += h (pass 2 adds)
+__global__ void k_reduce_dots(int nb, const double *__restrict__ part, int mp1, const GmState *S, double *h,
+                              double *Hcol_accum, int pass)
+{
+    if (S->cycle_end) return;
+    const int j = S->j;
+    const int k = threadIdx.x;
+    if (k > j) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * mp1 + k];
+    h[k] = s;
+    Hcol_accum[k] = (pass == 0) ? s : Hcol_accum[k] + s;
+}
+
+// w -= V[0..j] h
+__global__ void __launch_bounds__(RT) k_multi_axpy(int64_t n, const double *__restrict__ V, int64_t ldv,
+                                                   const double *__restrict__ h, const GmState *S,
+                                                   double *__restrict__ w)
+{
+    if (S->cycle_end) return;
+    const int j = S->j;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[i];
+        for (int k = 0; k <= j; ++k) s = fma(-h[k], V[(int64_t)k * ldv + i], s);
+        w[i] = s;
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_norm2(int64_t n, const double *__restrict__ w, const GmState *S,
+                                              double *__restrict__ part, unsigned *ticket, double *out)
+{
+    __shared__ double sh[RT / 32];
+    if (S->cycle_end) return;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(w[i], w[i], acc);
+    const double b = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+    if (last_block(ticket)) {
+        double s = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) s += part[k];
+        *out = sqrt(s);
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_scale_vec(int64_t n, const double *__restrict__ w, const double *nrm,
+                                                  const GmState *S, double *__restrict__ out)
+{
+    if (S->cycle_end) return;
+    const double r = 1.0 / *nrm;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = w[i] * r;
+}
+
+// Givens step on Hessenberg column j (stored H[k * m + j]); s = rotated rhs
+__global__ void k_givens(int m, double *H, double *cs, double *sn, double *s, const double *hcol,
+                         const double *hnext, GmState *S)
+{
+    if (S->cycle_end) return;
+    const int j = S->j;
+    for (int k = 0; k <= j; ++k) H[k * m + j] = hcol[k];
+    double hj1 = *hnext;
+    for (int k = 0; k < j; ++k) {
+        const double a = H[k * m + j], b = H[(k + 1) * m + j];
+        H[k * m + j] = cs[k] * a + sn[k] * b;
+        H[(k + 1) * m + j] = -sn[k] * a + cs[k] * b;
+    }
+    const double a = H[j * m + j];
+    const double rr = sqrt(a * a + hj1 * hj1);
+    if (!(rr > 0.0) || !isfinite(rr)) {
+        S->done = 3;
+        S->cycle_end = 1;
+        return;
+    }
+    cs[j] = a / rr;
+    sn[j] = hj1 / rr;
+    H[j * m + j] = rr;
+    s[j + 1] = -sn[j] * s[j];
+    s[j] = cs[j] * s[j];
+    S->iter += 1;
+    S->j = j + 1;
+    if (s[j + 1] * s[j + 1] <= S->tol2 * S->dd) {
+        S->done = 1;
+        S->cycle_end = 1;
+    } else if (S->j == m || S->iter >= S->max_iter) {
+        if (S->iter >= S->max_iter) S->done = 2;
+        S->cycle_end = 1;
+    }
+}
+
+// back substitution H y = s (upper triangular j x j) into y
+__global__ void k_backsolve(int m, const double *H, const double *s, double *y, const GmState *S)
+{
+    const int j = S->j;
+    for (int k = j - 1; k >= 0; --k) {
+        double t = s[k];
+        for (int l = k + 1; l < j; ++l) t -= H[k * m + l] * y[l];
+        y[k] = t / H[k * m + k];
+    }
+}
+
+// x += P^-1 (V y)
+__global__ void __launch_bounds__(RT) k_update_x(int64_t n, const double *__restrict__ V, int64_t ldv,
+                                                 const double *__restrict__ y, const double *__restrict__ pd,
+                                                 const GmState *S, double *__restrict__ x)
+{
+    const int j = S->j;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int k = 0; k < j; ++k) t = fma(V[(int64_t)k * ldv + i], y[k], t);
+        x[i] += pd ? t / pd[i] : t;
+    }
+}
+
+// cycle start: v0 = (d - K x) / beta, s = (beta, 0, ...)
+__global__ void __launch_bounds__(RT) k_gm_start(int64_t n, const double *__restrict__ d,
+                                                 const double *__restrict__ kx, double *__restrict__ v0,
+                                                 double *__restrict__ part, GmState *S, double *s, int m)
+{
+    __shared__ double sh[RT / 32];
+    double rr = 0.0, dd = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = d[i] - kx[i];
+        v0[i] = ri;
+        rr = fma(ri, ri, rr);
+        dd = fma(d[i], d[i], dd);
+    }
+    const double a = block_sum(rr, sh), b = block_sum(dd, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+    if (last_block(&S->ticket)) {
+        double t = 0.0, u = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) {
+            t += part[2 * k];
+            u += part[2 * k + 1];
+        }
+        S->dd = u;
+        S->beta0 = sqrt(t);
+        S->j = 0;
+        S->cycle_end = 0;
+        for (int k = 0; k <= m; ++k) s[k] = 0.0;
+        s[0] = S->beta0;
+        if (!isfinite(t) || !isfinite(u)) { S->done = 3; S->cycle_end = 1; }
+        else if (t <= S->tol2 * u) { S->done = 1; S->cycle_end = 1; }
+        else if (S->iter >= S->max_iter) { S->done = 2; S->cycle_end = 1; }
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_gm_norm_v0(int64_t n, double *__restrict__ v0, const GmState *S)
+{
+    if (S->cycle_end) return;
+    const double r = 1.0 / S->beta0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v0[i] *= r;
+}
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    cudaStream_t st;
+    explicit DevBuf(cudaStream_t s) : st(s) {}
+    cudaError_t alloc(size_t n) { return cudaMallocAsync(&p, sizeof(T) * (n ? n : 1), st); }
+    ~DevBuf() { if (p) cudaFreeAsync(p, st); }
+};
+
+mf_status finish_status(mf_status s, int *status, cudaStream_t st)
+{
+    int h = 0;
+    MF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        const int zero = 0;
+        MF_CUDA(cudaMemcpyAsync(status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        return mf_fail((mf_status)h, "device reported status %d", h);
+    }
+    return s;
+}
+
+mf_status true_residual(const mf_csr *K, const double *d, const double *x, double *tmp, double *part,
+                        unsigned *ticket, double *out2, cudaStream_t st, double *relres)
+{
+    spmv_any(K, K->values, x, tmp, st);
+    k_resid_norm<<<RED_BLOCKS, RT, 0, st>>>(K->n_rows, d, tmp, part, ticket, out2);
+    MF_CUDA(cudaGetLastError());
+    double h[2];
+    MF_CUDA(cudaMemcpyAsync(h, out2, sizeof h, cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    *relres = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+    return MF_OK;
+}
+
+mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o, mf_solve_info *info,
+                    cudaStream_t st)
+{
+    const int64_t n = K->n_rows;
+    DevBuf<double> r(st), p(st), q(st), dinv(st), part(st);
+    DevBuf<PcgState> S(st);
+    DevBuf<int> bad(st);
+    MF_CUDA(r.alloc(n));
+    MF_CUDA(p.alloc(n));
+    MF_CUDA(q.alloc(n));
+    MF_CUDA(dinv.alloc(n));
+    MF_CUDA(part.alloc(3 * RED_BLOCKS + 2));
+    MF_CUDA(S.alloc(1));
+    MF_CUDA(bad.alloc(1));
+    PcgState h{};
+    h.tol2 = o->tol * o->tol;
+    h.max_iter = o->max_iter;
+    MF_CUDA(cudaMemcpyAsync(S.p, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    MF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    k_diag_inv<<<nblk(n, RT), RT, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv.p, bad.p);
+    spmv_any(K, K->values, x, q.p, st);
+    k_pcg_init<<<RED_BLOCKS, RT, 0, st>>>(n, d, q.p, dinv.p, r.p, p.p, part.p, S.p);
+    MF_CUDA(cudaGetLastError());
+    int hb = 0;
+    MF_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (hb) return mf_fail(MF_ERR_NONFINITE, "mf_solve: zero or non-finite diagonal entry");
+
+    const int W = spmv_width(n, K->nnz);
+    const int chunk = o->check_every > 0 ? o->check_every : 50;
+    // capture `chunk` iterations in a graph on a private stream
+    cudaStream_t cs;
+    MF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        for (int it = 0; it < chunk; ++it) {
+            switch (W) {
+            case 4: launch_pcg_spmv<4>(K, p.p, q.p, part.p, S.p, cs); break;
+            case 8: launch_pcg_spmv<8>(K, p.p, q.p, part.p, S.p, cs); break;
+            case 16: launch_pcg_spmv<16>(K, p.p, q.p, part.p, S.p, cs); break;
+            default: launch_pcg_spmv<32>(K, p.p, q.p, part.p, S.p, cs); break;
+            }
+            k_pcg_update<<<RED_BLOCKS, RT, 0, cs>>>(n, dinv.p, p.p, q.p, x, r.p, part.p, S.p);
+            k_pcg_dir<<<RED_BLOCKS, RT, 0, cs>>>(n, dinv.p, r.p, p.p, S.p);
+        }
+        ce = cudaStreamEndCapture(cs, &graph);
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        return mf_cuda_check(ce, "mf_solve: graph capture");
+    }
+    // order the private stream after the set-up work and the caller's stream after the loop
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, st);
+    cudaStreamWaitEvent(cs, ev, 0);
+    mf_status s = MF_OK;
+    for (;;) {
+        MF_CUDA(cudaGraphLaunch(exec, cs));
+        MF_CUDA(cudaMemcpyAsync(&h, S.p, sizeof h, cudaMemcpyDeviceToHost, cs));
+        MF_CUDA(cudaStreamSynchronize(cs));
+        if (h.done) break;
+    }
+    cudaEventRecord(ev, cs);
+    cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+
+    double relres = 0.0;
+    mf_status s2 = true_residual(K, d, x, q.p, part.p, &S.p->ticket, reinterpret_cast<double *>(part.p) + 3 * RED_BLOCKS,
+                                 st, &relres);
+    if (s2 != MF_OK) return s2;
+    if (info) {
+        info->iterations = h.iter;
+        info->rel_residual = relres;
+        info->converged = h.done == 1;
+    }
+    if (h.done == 2) s = mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve: %lld iterations, residual %.3e", h.iter, relres);
+    if (h.done == 3) s = mf_fail(MF_ERR_NONFINITE, "mf_solve: breakdown or non-finite value");
+    return s;
+}
+
+mf_status solve_gmres(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o, mf_solve_info *info,
+                      cudaStream_t st)
+{
+    const int64_t n = K->n_rows;
+    const int m = o->restart;
+    if (m > 1000) return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: restart above 1000");
+    DevBuf<double> V(st), w(st), kv(st), part(st), H(st), cs(st), sn(st), s(st), y(st), h(st), hcol(st), pd(st),
+        nrm(st), ktmp(st);
+    DevBuf<GmState> S(st);
+    const int64_t ldv = n;
+    MF_CUDA(V.alloc((size_t)(m + 1) * n));
+    MF_CUDA(w.alloc(n));
+    MF_CUDA(part.alloc((size_t)RED_BLOCKS * (m + 1) + 2 * RED_BLOCKS + 4));
+    MF_CUDA(H.alloc((size_t)(m + 1) * m));
+    MF_CUDA(cs.alloc(m));
+    MF_CUDA(sn.alloc(m));
+    MF_CUDA(s.alloc(m + 1));
+    MF_CUDA(y.alloc(m));
+    MF_CUDA(h.alloc(m + 1));
+    MF_CUDA(hcol.alloc(m + 1));
+    MF_CUDA(nrm.alloc(1));
+    MF_CUDA(ktmp.alloc(K->nnz));
+    MF_CUDA(S.alloc(1));
+    // K' = K P^-1 (P = precond_diag or diag K)
+    const double *pdiag = o->precond_diag;
+    if (!pdiag) {
+        MF_CUDA(pd.alloc(n));
+        DevBuf<double> dinv(st);
+        DevBuf<int> bad(st);
+        MF_CUDA(dinv.alloc(n));
+        MF_CUDA(bad.alloc(1));
+        MF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+        k_diag_inv<<<nblk(n, RT), RT, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv.p, bad.p);
+        k_recip<<<nblk(n, RT), RT, 0, st>>>(n, dinv.p, pd.p);  // P = diag(K)
+        pdiag = pd.p;
+        int hb = 0;
+        MF_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        if (hb) return mf_fail(MF_ERR_NONFINITE, "mf_solve: zero or non-finite diagonal entry");
+    }
+    k_scale_cols<<<nblk(K->nnz, RT), RT, 0, st>>>(K->nnz, K->col_idx, K->values, pdiag, ktmp.p);
+    mf_csr Kp = *K;
+    Kp.values = ktmp.p;
+    GmState hs{};
+    hs.tol2 = o->tol * o->tol;
+    hs.max_iter = o->max_iter;
+    MF_CUDA(cudaMemcpyAsync(S.p, &hs, sizeof hs, cudaMemcpyHostToDevice, st));
+    double *Vp = V.p;
+    double *partB = part.p + (size_t)RED_BLOCKS * (m + 1);
+    const int chunk = o->check_every > 0 ? o->check_every : 10;
+    for (;;) {
+        // cycle start: r = d - K x (the true residual, with the unscaled K)
+        spmv_any(K, K->values, x, w.p, st);
+        k_gm_start<<<RED_BLOCKS, RT, 0, st>>>(n, d, w.p, Vp, partB, S.p, s.p, m);
+        k_gm_norm_v0<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, S.p);
+        MF_CUDA(cudaGetLastError());
+        for (int j = 0; j < m; ++j) {
+            // w = K' v_j
+            spmv_any(&Kp, Kp.values, Vp + (int64_t)j * ldv, w.p, st);
+            for (int pass = 0; pass < 2; ++pass) {
+                k_block_dots<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, w.p, S.p, part.p, m + 1);
+                k_reduce_dots<<<1, 1024, 0, st>>>(RED_BLOCKS, part.p, m + 1, S.p, h.p, hcol.p, pass);
+                k_multi_axpy<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, h.p, S.p, w.p);
+            }
+            k_norm2<<<RED_BLOCKS, RT, 0, st>>>(n, w.p, S.p, partB, &S.p->ticket, nrm.p);
+            k_scale_vec<<<RED_BLOCKS, RT, 0, st>>>(n, w.p, nrm.p, S.p, Vp + (int64_t)(j + 1) * ldv);
+            k_givens<<<1, 1, 0, st>>>(m, H.p, cs.p, sn.p, s.p, hcol.p, nrm.p, S.p);
+            MF_CUDA(cudaGetLastError());
+            if ((j + 1) % chunk == 0 || j + 1 == m) {
+                MF_CUDA(cudaMemcpyAsync(&hs, S.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+                MF_CUDA(cudaStreamSynchronize(st));
+                if (hs.cycle_end) break;
+            }
+        }
+        k_backsolve<<<1, 1, 0, st>>>(m, H.p, s.p, y.p, S.p);
+        k_update_x<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, y.p, pdiag, S.p, x);
+        MF_CUDA(cudaGetLastError());
+        MF_CUDA(cudaMemcpyAsync(&hs, S.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        if (hs.done) {
+            if (hs.done == 1) {
+                // confirm on the true residual, else restart
+                double rr = 0.0;
+                mf_status t = true_residual(K, d, x, w.p, partB, &S.p->ticket, partB + 2 * RED_BLOCKS, st, &rr);
+                if (t != MF_OK) return t;
+                if (rr > o->tol && hs.iter < o->max_iter) {
+                    hs.done = 0;
+                    MF_CUDA(cudaMemcpyAsync(&S.p->done, &hs.done, sizeof(int), cudaMemcpyHostToDevice, st));
+                    continue;
+                }
+            }
+            break;
+        }
+    }
+    double relres = 0.0;
+    mf_status t = true_residual(K, d, x, w.p, partB, &S.p->ticket, partB + 2 * RED_BLOCKS, st, &relres);
+    if (t != MF_OK) return t;
+    if (info) {
+        info->iterations = hs.iter;
+        info->rel_residual = relres;
+        info->converged = hs.done == 1;
+    }
+    if (hs.done == 2) return mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve: %lld iterations, residual %.3e", hs.iter, relres);
+    if (hs.done == 3) return mf_fail(MF_ERR_NONFINITE, "mf_solve: breakdown or non-finite value");
+    return MF_OK;
+}
+
+}  // namespace
+
+mf_status mf_spmv_impl(const mf_csr *K, const double *x, double *y, cudaStream_t st)
+{
+    spmv_any(K, K->values, x, y, st);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o, mf_solve_info *info,
+                        cudaStream_t st)
+{
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_solve: status word unavailable");
+    mf_status s = (o->solver == MF_SOLVER_PCG) ? solve_pcg(K, d, x, o, info, st) : solve_gmres(K, d, x, o, info, st);
+    if (s == MF_ERR_CUDA || s == MF_ERR_OOM) return s;
+    return finish_status(s, status, st);
+}
