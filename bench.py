@@ -1,0 +1,368 @@
+"""Benchmark: elements assembled per second on 3D Q1 linear elasticity, 64^3 box.
+
+Workload (262,144 jittered Q1 hexahedra, 823,875 dofs, 64,701,513 CSR
+entries, E lognormal(0, 0.5), nu = 0.3, body force (0, 0, -1), clamped at
+x = 0).  One step = one full assembly of K and d on the device: geometry,
+element quadrature, deterministic scatter into CSR, Dirichlet elimination.
+The pattern is built once per mesh beforehand (timed separately and reported).
+Both paths are timed: FP64 and, when the library provides it, the mixed
+tensor-core path; ``value`` is the fastest path whose solution stays within
+1e-8 relative of the FP64 path's.
+
+``--impl reference`` times the CPU FP64 oracle on the same workload (a bounded
+slab of its elements per step) on the host cores.
+
+Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+(N > 1 under torchrun: every rank assembles its own replica; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elements assembled/s (+% HBM roofline), mixed vs FP64 path at <=1e-8 rel err"
+UNIT = "elements/s"
+N_GRID = 64
+WORKLOAD = "3D linear elasticity, Q1 hexahedra on a 64^3 box (262,144 elements, 823,875 dofs), FP64 CSR"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=N_GRID, help="box size n (n^3 elements); 64 is the workload")
+    ap.add_argument("--skip-solve", action="store_true", help="skip the accuracy solves (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 flops per element of the Q1 elasticity kernel's formulation (FMA = 2):
+# per Gauss point 347 (Jacobian 144, cofactors/det/inverse 42, gradients 120,
+# scaling 24, load moments 16) x 8 points, block contractions 36 x 8 x 18 and
+# block finishing 36 x 32, load vector 24.
+FLOPS_PER_ELEMENT_FP64 = 8 * 347 + 36 * 8 * 18 + 36 * 32 + 24
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.file:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def oracle_sample(prob, layers: int):
+    """Oracle assembly restricted to the elements touching the nodes of the
+    first `layers` z-layers of the box; returns (elements evaluated, seconds)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    n = N_GRID
+    keep = np.zeros(prob["coords"].shape[0], np.uint8)
+    keep[: layers * (n + 1) * (n + 1)] = 1
+    ne = int(keep[prob["conn"]].max(axis=1).astype(bool).sum())
+    t = time.perf_counter()
+    oracle.assemble(prob, keep_nodes=keep)
+    return ne, time.perf_counter() - t
+
+
+def cpu_baseline(prob, layers=8):
+    ne, sec = oracle_sample(prob, layers)
+    return {"value": ne / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle FP64 assembly (element matrices, COO sort, sums, Dirichlet) of the {ne} elements "
+                      f"touching the first {layers} node layers of the same 64^3 mesh: {sec:.2f} s, 1 thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import gen
+    prob = gen.elastic_problem(N_GRID)
+    for _ in range(args.warmup):
+        oracle_sample(prob, 1)
+    tot_el, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        ne, s = oracle_sample(prob, 2)
+        tot_el += ne
+        tot_s += s
+    v = tot_el / tot_s
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "elements touching 2 node layers per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "oracle FP64 assembly of the elements touching the first 2 node layers"
+                                       " of the 64^3 mesh per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2111_03541_gb300 as mf
+    from paper_2111_03541_gb300 import build as mfbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mfbuild.build()
+    mf.lib()
+
+    prob = gen.elastic_problem(args.grid)
+    n_el = prob["conn"].shape[0]
+    t0 = time.perf_counter()
+    P = mf.Problem(prob, device=dev)
+    torch.cuda.synchronize()
+    pattern_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def time_path(prec, steps, warmup):
+        for _ in range(warmup):
+            P.assemble(prec)
+        mf.mf_sync_status()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        mf.mf_kernel_times()  # clear
+        mf.mf_set_kernel_timing(True)
+        barrier()
+        for i in range(steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            P.assemble(prec)
+            ends[i].record(stream)
+        barrier()
+        mf.mf_set_kernel_timing(False)
+        kt = mf.mf_kernel_times()
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)], kt
+
+    paths = {}
+    have_mixed = True
+    try:
+        P.assemble(mf.MF_PREC_MIXED)
+        torch.cuda.synchronize()
+    except mf.MFError as e:
+        if e.status != mf.MF_ERR_UNSUPPORTED:
+            raise
+        have_mixed = False
+
+    def kernels(kt):
+        return {k: {"launches": c, "ms_per_launch": t / c} for k, (c, t) in kt.items()}
+
+    sampler = ClockSampler(local)
+    with sampler:
+        ms64, kt64 = time_path(mf.MF_PREC_FP64, args.steps, args.warmup)
+        paths["fp64"] = {"ms_per_step": statistics.mean(ms64), "kernels": kernels(kt64)}
+        if have_mixed:
+            msmx, ktmx = time_path(mf.MF_PREC_MIXED, args.steps, args.warmup)
+            paths["mixed"] = {"ms_per_step": statistics.mean(msmx), "kernels": kernels(ktmx)}
+    clocks = sampler.summary()
+
+    # accuracy of the mixed path: solution against the FP64 path's solution
+    sol = {}
+    if not args.skip_solve:
+        P.assemble(mf.MF_PREC_FP64)
+        t = time.perf_counter()
+        x64, st, info = P.solve(tol=1e-10, max_iter=200000, check_every=100)
+        torch.cuda.synchronize()
+        sol["fp64"] = {"pcg_iterations": int(info.iterations), "rel_residual": info.rel_residual,
+                       "solve_s": time.perf_counter() - t}
+        if have_mixed:
+            P.assemble(mf.MF_PREC_MIXED)
+            t = time.perf_counter()
+            xm, st, info = P.solve(tol=1e-10, max_iter=200000, check_every=100)
+            torch.cuda.synchronize()
+            sol["mixed"] = {"pcg_iterations": int(info.iterations), "rel_residual": info.rel_residual,
+                            "solve_s": time.perf_counter() - t}
+            err = (torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)).item()
+            paths["mixed"]["rel_err_vs_fp64_solution"] = err
+            paths["mixed"]["accurate"] = err <= 1e-8
+    for k, v in paths.items():
+        v["elements_per_s"] = n_el / (v["ms_per_step"] * 1e-3)
+        v["dofs_per_s"] = P.n / (v["ms_per_step"] * 1e-3)
+    best = "mixed" if have_mixed and paths["mixed"].get("accurate") and \
+        paths["mixed"]["ms_per_step"] < paths["fp64"]["ms_per_step"] else "fp64"
+
+    # dominant kernel of the chosen path, timed on the launching stream
+    peaks, peak_src = measured_peaks()
+    alg_bytes = 8 * P.nnz + 8 * P.n + prob["coords"].nbytes + prob["conn"].nbytes + prob["coef"].nbytes + \
+        prob["bc_mask"].nbytes + prob["bc_val"].nbytes
+    ms_best = paths[best]["ms_per_step"]
+    roofline_hbm = {"bound": "hbm", "achieved": alg_bytes / (ms_best * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s"}
+    roofline_hbm["frac"] = roofline_hbm["achieved"] / roofline_hbm["peak"]
+    launches = sum(v["launches"] for v in paths[best]["kernels"].values()) // args.steps
+    if best == "fp64":
+        # the element kernel dominates and is bound by the FP64 pipe
+        kname = "elem_elastic_q1_fp64"
+        ms_el = paths["fp64"]["kernels"][kname]["ms_per_launch"]
+        ach = n_el * FLOPS_PER_ELEMENT_FP64 / (ms_el * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "ms_per_launch": ms_el,
+                    "algorithmic": f"{FLOPS_PER_ELEMENT_FP64} FP64 flops/element x {n_el} elements",
+                    "peak_source": "GB300 nominal dense FP64 rate (measured FMA-loop rate 1.19 TFLOP/s)"}
+    else:
+        kname = max(paths[best]["kernels"], key=lambda k: paths[best]["kernels"][k]["ms_per_launch"])
+        ms_k = paths[best]["kernels"][kname]["ms_per_launch"]
+        roofline = dict(roofline_hbm)
+        roofline.update({"kernel": kname, "ms_per_launch": ms_k, "peak_source": peak_src, "traffic": None})
+
+    # end to end: host buffers in, K and d out, through the C ABI
+    e2e = None if args.no_e2e else e2e_leg(P, prob, mf, stream, args, best)
+
+    out_val = n_el / (ms_best * 1e-3)
+    if dist:
+        t_max = torch.tensor([ms_best], dtype=torch.float64, device=dev)
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        out_val = world * n_el / (t_max.item() * 1e-3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": out_val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_best, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if best == "fp64" else "mixed(bf16 split, f32 acc, f64)",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "path": best, "l2": "flushed between steps (256 MB write)",
+                           "pattern_build_s": pattern_s, "nnz": int(P.nnz), "n_dofs": int(P.n)},
+                "paths": paths, "solve": sol, "hbm": roofline_hbm,
+                "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(prob)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def e2e_leg(P, prob, mf, stream, args, best):
+    import numpy as np
+    import torch
+    prec = mf.MF_PREC_MIXED if best == "mixed" else mf.MF_PREC_FP64
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(prob[k])).pin_memory()
+               for k in ("coords", "conn", "coef", "bc_mask", "bc_val")}
+    dev_in = {"coords": P.coords, "conn": P.conn, "coef": P.coef, "bc_mask": P.bc_mask, "bc_val": P.bc_val}
+    host_K = torch.empty(P.nnz, dtype=torch.float64).pin_memory()
+    host_d = torch.empty(P.n, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = host_K.numel() * 8 + host_d.numel() * 8
+
+    def step():
+        for k, t in host_in.items():
+            dev_in[k].copy_(t, non_blocking=True)
+        P.assemble(prec)
+        host_K.copy_(P.values, non_blocking=True)
+        host_d.copy_(P.d, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(args.steps):
+        step()
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / args.steps
+    return {"value": prob["conn"].shape[0] / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def main():
+    args = parse()
+    if args.grid != N_GRID:
+        global WORKLOAD
+        WORKLOAD = f"3D linear elasticity, Q1 hexahedra on a {args.grid}^3 box (profiling case)"
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -182,6 +182,15 @@ mf_status mf_solve(const mf_csr *K, const double *d, double *x, const mf_solver_
 /* y = K x (device pointers). */
 mf_status mf_spmv(const mf_csr *K, const double *x, double *y, void *stream);
 
+/* Per-kernel timing with CUDA events (tracing).  While enabled, every kernel
+ * launched by mf_assemble is bracketed by two events recorded on the call's
+ * stream.  mf_kernel_times() synchronises those events, writes
+ * "name count total_ms\n" lines (one per kernel name) into buf (NUL
+ * terminated, truncated to len) and clears the counters.  Host-side only; no
+ * effect on results.  Errors: MF_ERR_INVALID_ARG, MF_ERR_CUDA. */
+mf_status mf_set_kernel_timing(int32_t enable);
+mf_status mf_kernel_times(char *buf, size_t len);
+
 /* Synchronises the stream, returns and clears the latched device status. */
 mf_status mf_sync_status(void *stream);
 

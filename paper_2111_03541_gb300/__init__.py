@@ -76,6 +76,8 @@ _SIGS = {
     "mf_solve": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_void_p],
     "mf_spmv": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_sync_status": [C.c_void_p],
+    "mf_set_kernel_timing": [C.c_int32],
+    "mf_kernel_times": [C.c_char_p, C.c_size_t],
 }
 
 
@@ -175,6 +177,21 @@ def mf_spmv(K: CSR, x, y, stream=None) -> None:
 
 def mf_sync_status(stream=None) -> None:
     _check(lib().mf_sync_status(_stream(stream)))
+
+
+def mf_set_kernel_timing(enable: bool) -> None:
+    _check(lib().mf_set_kernel_timing(1 if enable else 0))
+
+
+def mf_kernel_times() -> dict[str, tuple[int, float]]:
+    """{kernel name: (launches, total ms)} since the last read."""
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().mf_kernel_times(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
 
 
 def mf_last_error() -> str:

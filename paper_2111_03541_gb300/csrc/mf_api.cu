@@ -2,8 +2,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "mf_internal.h"
 
@@ -63,6 +66,85 @@ extern "C" mf_status mf_sync_status(void *stream)
         MF_CUDA(cudaStreamSynchronize(st));
         return mf_fail(static_cast<mf_status>(h), "device reported status %d", h);
     }
+    return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing: pairs of events per launch, reduced when read
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_pool;
+std::map<std::string, std::pair<long long, double>> g_prof_acc;
+ProfRec *g_prof_open = nullptr;
+
+cudaEvent_t prof_event()
+{
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+void mf_prof_begin(const char *name, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    g_prof_pending.push_back(ProfRec{name, prof_event(), prof_event()});
+    g_prof_open = &g_prof_pending.back();
+    cudaEventRecord(g_prof_open->a, st);
+}
+
+void mf_prof_end(cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on || !g_prof_open) return;
+    cudaEventRecord(g_prof_open->b, st);
+    g_prof_open = nullptr;
+}
+
+extern "C" mf_status mf_set_kernel_timing(int32_t enable)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = enable != 0;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_kernel_times(char *buf, size_t len)
+{
+    if (!buf || len == 0) return mf_fail(MF_ERR_INVALID_ARG, "mf_kernel_times: empty buffer");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (ProfRec &r : g_prof_pending) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_kernel_times");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &acc = g_prof_acc[r.name];
+        acc.first += 1;
+        acc.second += ms;
+        g_prof_pool.push_back(r.a);
+        g_prof_pool.push_back(r.b);
+    }
+    g_prof_pending.clear();
+    g_prof_open = nullptr;
+    std::string out;
+    char line[256];
+    for (auto &kv : g_prof_acc) {
+        snprintf(line, sizeof line, "%s %lld %.6f\n", kv.first.c_str(), kv.second.first, kv.second.second);
+        out += line;
+    }
+    g_prof_acc.clear();
+    snprintf(buf, len, "%s", out.c_str());
     return MF_OK;
 }
 

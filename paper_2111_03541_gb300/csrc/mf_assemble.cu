@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const dou
 #pragma unroll
         for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
     double Ke[36] = {}, m[8] = {};
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
         double Ji[3][3];
         const double wd = q1_jac(x, q, Ji);  // Gauss weights are 1
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(EL_T) k_elem_elastic_q1(int64_t n_el, const do
 #pragma unroll
         for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
     double m[8] = {};
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
         double Ji[3][3];
         const double wd = q1_jac(x, q, Ji);
@@ -598,6 +598,7 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
     const int64_t ne = m->n_elems;
     if (form == MF_FORM_THERMAL) {
         const double f = c->source[0];
+        mf_prof_begin(m->elem == MF_P1_TRI ? "elem_thermal_p1" : (m->elem == MF_P2_TRI ? "elem_thermal_p2" : "elem_thermal_q1"), st);
         if (m->elem == MF_P1_TRI)
             k_elem_thermal_p1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
                                                              status);
@@ -607,33 +608,40 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         else
             k_elem_thermal_q1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
                                                              status);
+        mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         const mf_adj &A = p->adj[0];
+        mf_prof_begin("gather_scalar", st);
         k_gather<1><<<nblk(A.n_rows * 32, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, A.cptr, A.clist, p->scratch,
                                                               p->scratch_stride, m->npe, c->bc_mask, c->bc_val,
                                                               p->row_ptr, values, d);
+        mf_prof_end(st);
     } else if (form == MF_FORM_ELASTIC) {
         const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;
-        static bool attr_set = false;  // idempotent; set once per process
-        if (!attr_set) {
-            MF_CUDA(cudaFuncSetAttribute(k_elem_elastic_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
-        }
+        MF_CUDA(cudaFuncSetAttribute(k_elem_elastic_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        mf_prof_begin("elem_elastic_q1_fp64", st);
         k_elem_elastic_q1<<<nblk(ne, EL_T), EL_T, smem, st>>>(ne, m->coords, m->conn, c->elem_coef, c->nu,
                                                               c->source[0], c->source[1], c->source[2], p->scratch,
                                                               status);
+        mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         const mf_adj &A = p->adj[0];
+        mf_prof_begin("gather_block3", st);
         k_gather<3><<<nblk(A.n_rows * 32, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, A.cptr, A.clist, p->scratch,
                                                               p->scratch_stride, 8, c->bc_mask, c->bc_val,
                                                               p->row_ptr, values, d);
+        mf_prof_end(st);
     } else {
+        mf_prof_begin("elem_oseen", st);
         k_elem_oseen<<<nblk(ne, 128), 128, 0, st>>>(ne, m->n_nodes, m->coords, m->conn, c->advect, c->visc, c->rho,
                                                     p->scratch, status);
+        mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
+        mf_prof_begin("gather_oseen", st);
         k_gather_oseen<<<nblk(p->n_rows * 32, 256), 256, 0, st>>>(m->n_nodes, m->n_pnodes, p->adj[0], p->adj[1],
                                                                   p->adj[2], p->scratch, c->bc_mask, c->bc_val,
                                                                   p->row_ptr, values, d);
+        mf_prof_end(st);
     }
     MF_CUDA(cudaGetLastError());
     return MF_OK;

@@ -78,6 +78,10 @@ mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_so
                         mf_solve_info *info, cudaStream_t st);
 mf_status mf_spmv_impl(const mf_csr *K, const double *x, double *y, cudaStream_t st);
 
+// kernel timing (tracing): bracket a launch on stream st with events when enabled
+void mf_prof_begin(const char *name, cudaStream_t st);
+void mf_prof_end(cudaStream_t st);
+
 // device status codes are written with atomicCAS(word, 0, code): first error wins
 __device__ __forceinline__ void mf_dev_fail(int *word, int code) { atomicCAS(word, 0, code); }
 
