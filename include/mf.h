@@ -179,6 +179,26 @@ mf_status mf_flow_precond(const mf_mesh *mesh, const mf_pattern *pattern, const 
 mf_status mf_solve(const mf_csr *K, const double *d, double *x, const mf_solver_opts *opts,
                    mf_solve_info *info, void *stream);
 
+/* Jacobi-PCG like mf_solve (same kernels and stopping rule), but it makes no
+ * device allocation: no cudaMalloc, no cudaFree, no graph, stream or event
+ * creation.  It is meant for callers that cannot allocate during a solve, e.g.
+ * a framework that reserved all device memory for its own pool at start-up,
+ * or a latency-critical loop where an allocation would synchronise the device.
+ * The paper has no counterpart; this entry exists for those callers.
+ * Work memory is one file-scope __device__ array holding four vectors of
+ * MF_NOALLOC_MAX_ROWS doubles (about 32 MB), kept by every GPU that loads the
+ * library until the process exits.  Systems with more rows are rejected with
+ * MF_ERR_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (set-up, once per device, with that device current); make that
+ * first call before any stream capture.  Every call shares the array and
+ * keeps the last call's contents (the state is reset at entry), so calls that
+ * overlap on the GPU (several streams or host threads) race: serialise them.
+ * x holds x0 on entry and the solution on exit; info may be NULL.
+ * Synchronises the stream.  Errors: as mf_solve. */
+#define MF_NOALLOC_MAX_ROWS (1 << 20)
+mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, double *x, double tol, int64_t max_iter,
+                               int32_t check_every, mf_solve_info *info, void *stream);
+
 /* y = K x (device pointers). */
 mf_status mf_spmv(const mf_csr *K, const double *x, double *y, void *stream);
 

@@ -74,6 +74,8 @@ _SIGS = {
     "mf_pressure_mass_diag": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_flow_precond": [C.c_void_p, C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
     "mf_solve": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_void_p],
+    "mf_solve_pcg_noalloc": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.c_int32,
+                             C.POINTER(SolveInfo), C.c_void_p],
     "mf_spmv": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_sync_status": [C.c_void_p],
     "mf_set_kernel_timing": [C.c_int32],
@@ -168,6 +170,18 @@ def mf_flow_precond(mesh, pattern, K: CSR, bc_mask, p_scale: float, out, stream=
 def mf_solve(K: CSR, d, x, opts: SolverOpts, stream=None, allow=(MF_ERR_NOT_CONVERGED,)) -> tuple[int, SolveInfo]:
     info = SolveInfo()
     st = _check(lib().mf_solve(C.byref(K), _ptr(d), _ptr(x), C.byref(opts), C.byref(info), _stream(stream)), allow)
+    return st, info
+
+
+MF_NOALLOC_MAX_ROWS = 1 << 20
+
+
+def mf_solve_pcg_noalloc(K: CSR, d, x, tol: float, max_iter: int, check_every: int = 50, stream=None,
+                         allow=(MF_ERR_NOT_CONVERGED,)) -> tuple[int, SolveInfo]:
+    """Jacobi-PCG that makes no device allocation (work vectors in a static device array)."""
+    info = SolveInfo()
+    st = _check(lib().mf_solve_pcg_noalloc(C.byref(K), _ptr(d), _ptr(x), tol, max_iter, check_every,
+                                           C.byref(info), _stream(stream)), allow)
     return st, info
 
 

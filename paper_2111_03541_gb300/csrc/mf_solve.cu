@@ -14,6 +14,7 @@
 // per pass); the Givens rotations of the Hessenberg column run in a
 // single-thread kernel, so a whole cycle stays on the device.
 #include <cmath>
+#include <mutex>
 
 #include "mf_internal.h"
 
@@ -714,6 +715,119 @@ mf_status solve_gmres(const mf_csr *K, const double *d, double *x, const mf_solv
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Jacobi-PCG without any device allocation.
+//
+// For callers that cannot allocate device memory during a solve: a framework
+// that reserved the whole device memory for its own pool at start-up (a
+// cudaMalloc then fails or fragments that pool), or a latency-critical loop
+// where cudaMalloc/cudaFree would synchronise the device.  The work vectors
+// live in one file-scope __device__ array sized for MF_NOALLOC_MAX_ROWS rows;
+// every GPU that loads the library holds it (about 32 MB) until the process
+// exits.  All calls share the array, so calls that overlap on the GPU (other
+// streams, other host threads) race and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t NOALLOC_PART = 3 * RED_BLOCKS + 2;       // block partials + 2 reduction outputs
+constexpr size_t NOALLOC_TAIL = 32;                        // PcgState + breakdown flag
+constexpr size_t NOALLOC_DOUBLES = 4 * (size_t)MF_NOALLOC_MAX_ROWS + NOALLOC_PART + NOALLOC_TAIL;
+static_assert(sizeof(PcgState) + sizeof(int) <= NOALLOC_TAIL * sizeof(double), "tail too small");
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[64];
+
+// Device address of g_noalloc_scratch for the current device (set-up once per
+// device, with that device current; host code must not use the symbol itself).
+mf_status noalloc_base(double **out)
+{
+    int dev = 0;
+    MF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return mf_fail(MF_ERR_UNSUPPORTED, "mf_solve_pcg_noalloc: device index %d", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return mf_cuda_check(e, "mf_solve_pcg_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return MF_OK;
+}
+}  // namespace
+
+extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, double *x, double tol, int64_t max_iter,
+                                          int32_t check_every, mf_solve_info *info, void *stream)
+{
+    if (!K || !d || !x || !K->row_ptr || !K->col_idx || !K->values || K->n_rows <= 0)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: NULL argument");
+    if (K->n_rows > MF_NOALLOC_MAX_ROWS)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: %lld rows exceed MF_NOALLOC_MAX_ROWS = %d",
+                       (long long)K->n_rows, MF_NOALLOC_MAX_ROWS);
+    if (!(tol > 0.0) || max_iter < 0) return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: tol > 0, max_iter >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_solve_pcg_noalloc: status word unavailable");
+    double *base = nullptr;
+    mf_status s = noalloc_base(&base);
+    if (s != MF_OK) return s;
+    const int64_t n = K->n_rows;
+    double *r = base, *p = base + MF_NOALLOC_MAX_ROWS, *q = base + 2 * (size_t)MF_NOALLOC_MAX_ROWS;
+    double *dinv = base + 3 * (size_t)MF_NOALLOC_MAX_ROWS;
+    double *part = base + 4 * (size_t)MF_NOALLOC_MAX_ROWS;
+    PcgState *S = reinterpret_cast<PcgState *>(part + NOALLOC_PART);
+    int *bad = reinterpret_cast<int *>(S + 1);
+
+    // the array keeps the previous call's contents: reset the state and flag
+    PcgState h{};
+    h.tol2 = tol * tol;
+    h.max_iter = max_iter;
+    MF_CUDA(cudaMemcpyAsync(S, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    MF_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    k_diag_inv<<<nblk(n, RT), RT, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv, bad);
+    spmv_any(K, K->values, x, q, st);
+    k_pcg_init<<<RED_BLOCKS, RT, 0, st>>>(n, d, q, dinv, r, p, part, S);
+    MF_CUDA(cudaGetLastError());
+    int hb = 0;
+    MF_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (hb) return mf_fail(MF_ERR_NONFINITE, "mf_solve_pcg_noalloc: zero or non-finite diagonal entry");
+
+    const int W = spmv_width(n, K->nnz);
+    const int chunk = check_every > 0 ? check_every : 50;
+    for (;;) {
+        for (int it = 0; it < chunk; ++it) {
+            switch (W) {
+            case 4: launch_pcg_spmv<4>(K, p, q, part, S, st); break;
+            case 8: launch_pcg_spmv<8>(K, p, q, part, S, st); break;
+            case 16: launch_pcg_spmv<16>(K, p, q, part, S, st); break;
+            default: launch_pcg_spmv<32>(K, p, q, part, S, st); break;
+            }
+            k_pcg_update<<<RED_BLOCKS, RT, 0, st>>>(n, dinv, p, q, x, r, part, S);
+            k_pcg_dir<<<RED_BLOCKS, RT, 0, st>>>(n, dinv, r, p, S);
+        }
+        MF_CUDA(cudaGetLastError());
+        MF_CUDA(cudaMemcpyAsync(&h, S, sizeof h, cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        if (h.done) break;
+    }
+    double relres = 0.0;
+    s = true_residual(K, d, x, q, part, &S->ticket, part + 3 * RED_BLOCKS, st, &relres);
+    if (s != MF_OK) return s;
+    if (info) {
+        info->iterations = h.iter;
+        info->rel_residual = relres;
+        info->converged = h.done == 1;
+    }
+    s = MF_OK;
+    if (h.done == 2) s = mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve_pcg_noalloc: %lld iterations, residual %.3e", h.iter, relres);
+    if (h.done == 3) s = mf_fail(MF_ERR_NONFINITE, "mf_solve_pcg_noalloc: breakdown or non-finite value");
+    return finish_status(s, status, st);
+}
 
 mf_status mf_spmv_impl(const mf_csr *K, const double *x, double *y, cudaStream_t st)
 {
