@@ -252,14 +252,14 @@ def run_ours(args):
     if not args.skip_solve:
         P.assemble(mf.MF_PREC_FP64)
         t = time.perf_counter()
-        x64, st, info = P.solve(tol=1e-10, max_iter=200000, check_every=100)
+        x64, st, info = P.solve(tol=1e-12, max_iter=200000, check_every=100)
         torch.cuda.synchronize()
         sol["fp64"] = {"pcg_iterations": int(info.iterations), "rel_residual": info.rel_residual,
                        "solve_s": time.perf_counter() - t}
         if have_mixed:
             P.assemble(mf.MF_PREC_MIXED)
             t = time.perf_counter()
-            xm, st, info = P.solve(tol=1e-10, max_iter=200000, check_every=100)
+            xm, st, info = P.solve(tol=1e-12, max_iter=200000, check_every=100)
             torch.cuda.synchronize()
             sol["mixed"] = {"pcg_iterations": int(info.iterations), "rel_residual": info.rel_residual,
                             "solve_s": time.perf_counter() - t}

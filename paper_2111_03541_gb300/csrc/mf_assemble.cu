@@ -468,6 +468,103 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n_nodes, const int64_t *
         for (int c = 0; c < BS; ++c) d[BS * n + c] = rm[c] ? bval[BS * n + c] : dsum[c] + lift[c];
 }
 
+// ---------------------------------------------------------------------------
+// elasticity gather: one warp per node, walking the node's incident elements in
+// ascending order.  Each element's 8 blocks (a_n, b) of the node's rows (72
+// values, stored as the upper blocks a <= b) are added into a shared-memory
+// row accumulator at the neighbour slot of node b; after the last element the
+// three CSR rows of the node are written once, coalesced.  T = double (FP64
+// path) or long long (fixed-point mixed path: exact sums, converted once).
+// ---------------------------------------------------------------------------
+constexpr int GEL_WARPS = 8;
+
+template <typename T>
+__device__ __forceinline__ double to_double(T v, int S);
+
+template <>
+__device__ __forceinline__ double to_double<double>(double v, int)
+{
+    return v;
+}
+
+// x * 2^-S for a fixed-point integer x, rounded to nearest even with integer
+// operations only (no FP64 instruction).
+template <>
+__device__ __forceinline__ double to_double<long long>(long long v, int S)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+    unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)u);
+    u <<= lz;  // leading one at bit 63
+    unsigned long long m = u >> 11;  // 53 significant bits
+    const unsigned long long rest = u & 0x7ffull;
+    m += (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
+    const long long ex = 1023 + (63 - lz) - S;
+    if (ex <= 0) return __longlong_as_double((long long)sign);  // below the normal range
+    const unsigned long long bits = ((unsigned long long)ex << 52) + (m - (1ull << 52));
+    return __longlong_as_double((long long)(bits | sign));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
+    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+    const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const int32_t *__restrict__ conn,
+    const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
+    const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+    double *__restrict__ values, double *__restrict__ d)
+{
+    __shared__ T acc_all[GEL_WARPS][MF_MAX_DEG * 9];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t n = (int64_t)blockIdx.x * GEL_WARPS + w;
+    if (n >= n_nodes) return;  // warp-uniform
+    T *acc = acc_all[w];
+    const int64_t p0 = adj_ptr[n];
+    const int deg = (int)(adj_ptr[n + 1] - p0);
+    for (int i = lane; i < 9 * deg; i += 32) acc[i] = T(0);
+    double dsum = 0.0;  // lane c < 3: load of component c
+    __syncwarp();
+    for (int64_t t = inc_ptr[n]; t < inc_ptr[n + 1]; ++t) {
+        const int64_t e = inc[t];
+        const int32_t cn = lane < 8 ? conn[e * 8 + lane] : -1;
+        const unsigned hit = __ballot_sync(0xffffffffu, cn == (int32_t)n);
+        if (hit == 0u) continue;  // cannot happen: incidence lists come from conn
+        const int a = __ffs(hit) - 1;
+        const T *blk = reinterpret_cast<const T *>(sc + e * stride);
+        for (int idx = lane; idx < 72; idx += 32) {
+            const int b = idx / 9, cc = idx - 9 * b;
+            const int c = cc / 3, cp = cc - 3 * c;
+            const T v = (a <= b) ? blk[upair(a, b) * 9 + cc] : blk[upair(b, a) * 9 + 3 * cp + c];
+            const int k = slot[e * 64 + a * 8 + b];
+            acc[k * 9 + cc] += v;
+        }
+        if (lane < 3) dsum += sc[e * stride + 324 + 3 * a + lane];
+        __syncwarp();
+    }
+    const int S = scale ? *scale : 0;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        const int64_t r = 3 * n + c;
+        const bool rm = mask ? mask[r] != 0 : false;
+        const int64_t rb = row_ptr[r];
+        double lift = 0.0;
+        for (int j = lane; j < 3 * deg; j += 32) {
+            const int k = j / 3, cp = j - 3 * k;
+            double v = to_double<T>(acc[k * 9 + 3 * c + cp], S);
+            if (mask) {
+                const int64_t sdof = 3 * (int64_t)adj_col[p0 + k] + cp;
+                if (rm) v = (r == sdof) ? 1.0 : 0.0;
+                else if (mask[sdof]) { lift -= v * bval[sdof]; v = 0.0; }
+            }
+            values[rb + j] = v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
+        const double dc = __shfl_sync(0xffffffffu, dsum, c);
+        if (lane == 0) d[r] = rm ? bval[r] : dc + lift;
+    }
+}
+
 // flow rows: u_i(n) = [A over P2-P2 | -B_i^T over P2-P1]; p(n) = [B_1 | B_2 over P1-P2 | diag]
 __global__ void __launch_bounds__(256) k_gather_oseen(int64_t n2, int64_t n1, mf_adj pp, mf_adj pq, mf_adj qp,
                                                       const double *__restrict__ sc, const uint8_t *__restrict__ mask,
@@ -578,6 +675,21 @@ __global__ void k_flow_precond(int64_t n2, int64_t n_rows, const int64_t *__rest
 
 }  // namespace
 
+void mf_launch_gather_elastic(bool fixed_point, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
+                              double *values, double *d, cudaStream_t st)
+{
+    const mf_adj &A = p->adj[0];
+    const unsigned grid = nblk(m->n_nodes, GEL_WARPS);
+    if (fixed_point)
+        k_gather_el<long long><<<grid, GEL_WARPS * 32, 0, st>>>(
+            m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride,
+            static_cast<const int *>(p->mixed_state), c->bc_mask, c->bc_val, p->row_ptr, values, d);
+    else
+        k_gather_el<double><<<grid, GEL_WARPS * 32, 0, st>>>(
+            m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride, nullptr,
+            c->bc_mask, c->bc_val, p->row_ptr, values, d);
+}
+
 mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,
                                double p_scale, double *out, cudaStream_t st)
 {
@@ -625,11 +737,8 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
                                                               status);
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
-        const mf_adj &A = p->adj[0];
-        mf_prof_begin("gather_block3", st);
-        k_gather<3><<<nblk(A.n_rows * 32, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, A.cptr, A.clist, p->scratch,
-                                                              p->scratch_stride, 8, c->bc_mask, c->bc_val,
-                                                              p->row_ptr, values, d);
+        mf_prof_begin("gather_elastic", st);
+        mf_launch_gather_elastic(false, m, p, c, values, d, st);
         mf_prof_end(st);
     } else {
         mf_prof_begin("elem_oseen", st);

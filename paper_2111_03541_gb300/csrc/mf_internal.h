@@ -50,6 +50,11 @@ struct mf_pattern {
     // flow: elements incident to each P1 pressure node, ascending
     int64_t *pinc_ptr = nullptr;
     int32_t *pinc = nullptr;
+    // elasticity: slot[e][a][b] = position of node conn[e][b] among the sorted
+    // neighbours of node conn[e][a] (u8, n_elems x 64)
+    uint8_t *slot = nullptr;
+    // mixed path: device scalars of the fixed-point scale (see mf_mixed.cu)
+    void *mixed_state = nullptr;
 };
 
 // status word (device) of the current device
@@ -73,6 +78,9 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
                             double *values, double *d, cudaStream_t st);
 mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,
                                double p_scale, double *out, cudaStream_t st);
+// elasticity gather (FP64 sums, or exact int64 fixed-point sums of the mixed path)
+void mf_launch_gather_elastic(bool fixed_point, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
+                              double *values, double *d, cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);
 mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o,
                         mf_solve_info *info, cudaStream_t st);

@@ -1,9 +1,499 @@
-// Mixed-precision element contraction of Q1 elasticity (tensor cores).
+// Mixed-precision assembly of Q1 elasticity (tensor-core element contraction).
+//
+// The element matrix of linear elasticity (Sec. 4.2, -(d_i,j, sigma_ij) with
+// the tangent negated) is, per block pair (a, b) of nodes,
+//   K_ab[c][c'] = lambda A_ab[c][c'] + mu A_ab[c'][c] + mu delta_cc' tr A_ab,
+//   A_ab[c][c'] = sum_q w_q detJ_q d_c N_a(q) d_c' N_b(q).
+// With mu = E / (2 (1 + nu)) and lambda / mu = r = 2 nu / (1 - 2 nu) = p / q
+// (small integers, found on the host), scale the gradients
+//   G[(a,c), q] = sqrt(mu w_q detJ_q / q) d_c N_a(q)          (24 x 8)
+// so that A'' = G G^T and  K_e = p A'' + q swap(A'') + q I tr(A'') exactly.
+//
+// Precision plan (GB300 runs FP64 at 1/58 of FP32):
+//  * geometry (Jacobian, cofactors, detJ, scale, gradients) in double-float
+//    arithmetic (pairs of FP32, ~44 bits), one lane per (element, Gauss point),
+//    from FP64 coordinate differences;
+//  * G is split into 5 BF16 slices of 8 bits with one exponent per row
+//    (Ozaki, Ogita, Oishi & Rump 2012): every slice product summed over the 8
+//    points is an exact integer in FP32, so each level L = s + t of the
+//    slice pairs accumulates exactly on the tensor cores (mma.sync m16n8k16,
+//    bf16 in, fp32 accumulate);
+//  * the levels are combined into 64-bit fixed point at a global scale 2^S
+//    (chosen by a pre-pass so no sum can overflow), the p, q finishing is
+//    integer arithmetic, and the CSR sums of the gather are exact int64 sums
+//    converted once to FP64.
+// The dropped levels (s + t > 4) bound the error at about 2^-40 of the row
+// scale; the solution error against the FP64 path is measured per run.
+#include <cuda_bf16.h>
+
 #include "mf_internal.h"
+
+namespace {
+
+constexpr int MX_WARPS = 4;          // warps per block; each warp: 4 elements
+constexpr int MX_ELEMS = 4 * MX_WARPS;
+constexpr int NSL = 5;               // BF16 slices of G
+constexpr int SL_ROWS = 32;          // 24 rows padded to two m16 tiles
+
+struct MixedState {
+    int S;        // global fixed-point exponent
+    int mx_bits;  // max over elements of max_row sum_q G^2 (float bits, >= 0)
+};
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic: value = h + l with |l| <= ulp(h) / 2
+// ---------------------------------------------------------------------------
+struct f2 {
+    float h, l;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ f2 dadd(f2 a, f2 b)
+{
+    f2 s = two_sum(a.h, b.h);
+    s.l += a.l + b.l;
+    return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ f2 dneg(f2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ f2 dsgn(f2 a, bool neg) { return neg ? dneg(a) : a; }
+__device__ __forceinline__ f2 dsub(f2 a, f2 b) { return dadd(a, dneg(b)); }
+__device__ __forceinline__ f2 dmul(f2 a, f2 b)
+{
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2 dmulf(f2 a, float b)
+{
+    const float p = a.h * b;
+    float e = fmaf(a.h, b, -p);
+    e = fmaf(a.l, b, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2 ddiv(f2 a, f2 b)
+{
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const f2 r = dsub(a, dmulf(b, q1));
+    return fast_two_sum(q1, __fdiv_rn(r.h, b.h));
+}
+__device__ __forceinline__ f2 dsqrt(f2 a)
+{
+    const float s = sqrtf(a.h);
+    const float p = s * s;
+    const float pe = fmaf(s, s, -p);  // s^2 = p + pe exactly
+    const float r = ((a.h - p) - pe) + a.l;
+    return fast_two_sum(s, __fdiv_rn(r, 2.0f * s));
+}
+__device__ __forceinline__ f2 from_double(double x)
+{
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ f2 shfl_xor(f2 v, int m)
+{
+    return {__shfl_xor_sync(0xffffffffu, v.h, m), __shfl_xor_sync(0xffffffffu, v.l, m)};
+}
+__device__ __forceinline__ f2 shfl(f2 v, int src)
+{
+    return {__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
+
+#define DF(x) f2{(float)(x), (float)((x) - (double)(float)(x))}
+
+// 2-point Gauss abscissa G = 1/sqrt(3); factors P = 1 + G, M = 1 - G
+constexpr double GD = 0.57735026918962576450914878050196;
+// d_j N_a(q) = (1/8) s_a^j prod_{k != j} F_k, F_k in {P, M}:  products / 8
+constexpr double KPP = 1.0 / 6.0 + GD / 4.0;   // P^2 / 8
+constexpr double KPM = 1.0 / 12.0;             // P M / 8 = (1 - 1/3) / 8
+constexpr double KMM = 1.0 / 6.0 - GD / 4.0;   // M^2 / 8
+// N_a(q) = (1/8) prod_k F_k: P^3/8, P^2 M/8, P M^2/8, M^3/8 (3, 2, 1, 0 matches)
+constexpr double NP3 = (1.0 + GD) * (1.0 + GD) * (1.0 + GD) / 8.0;
+constexpr double NP2 = (1.0 + GD) * (1.0 + GD) * (1.0 - GD) / 8.0;
+constexpr double NP1 = (1.0 + GD) * (1.0 - GD) * (1.0 - GD) / 8.0;
+constexpr double NP0 = (1.0 - GD) * (1.0 - GD) * (1.0 - GD) / 8.0;
+
+
+__device__ __forceinline__ int f2i_exact(float x)  // |x| < 2^22, integer valued
+{
+    return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------
+// pre-pass: bound of the fixed-point values (FP32 geometry is enough for a bound)
+// ---------------------------------------------------------------------------
+__global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                              const double *__restrict__ Ec, float cmu_q, MixedState *st, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const double E = Ec[e];
+    if (!isfinite(E) || !(E > 0.0)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
+    float x[8][3];
+    const int32_t *cn = conn + 8 * e;
+    for (int a = 0; a < 8; ++a)
+        for (int i = 0; i < 3; ++i) x[a][i] = (float)(X[3 * (int64_t)cn[a] + i] - X[3 * (int64_t)cn[0] + i]);
+    const float g = (float)GD;
+    float rowsum[24] = {};
+    for (int q = 0; q < 8; ++q) {
+        const float xs[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+        float J[3][3] = {}, dN[8][3];
+        for (int a = 0; a < 8; ++a) {
+            const float s[3] = {(a & 1) ? 1.f : -1.f, (a & 2) ? 1.f : -1.f, (a & 4) ? 1.f : -1.f};
+            const float f[3] = {1.f + s[0] * xs[0], 1.f + s[1] * xs[1], 1.f + s[2] * xs[2]};
+            dN[a][0] = 0.125f * s[0] * f[1] * f[2];
+            dN[a][1] = 0.125f * f[0] * s[1] * f[2];
+            dN[a][2] = 0.125f * f[0] * f[1] * s[2];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) J[i][j] += x[a][i] * dN[a][j];
+        }
+        float C[3][3];
+        C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+        const float sc = (float)E * cmu_q / det;  // G^2 = (mu / (q det)) (sum_j dN_j C[c][j])^2
+        for (int a = 0; a < 8; ++a)
+            for (int c = 0; c < 3; ++c) {
+                const float v = dN[a][0] * C[c][0] + dN[a][1] * C[c][1] + dN[a][2] * C[c][2];
+                rowsum[3 * a + c] += sc * v * v;
+            }
+    }
+    float mx = 0.f;
+    for (int r = 0; r < 24; ++r) mx = fmaxf(mx, rowsum[r]);
+    if (!isfinite(mx)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
+    atomicMax(&st->mx_bits, __float_as_int(mx));
+}
+
+// S = floor(62 - log2(8 (p + 4q) Mx 1.25)): every element value |K_e| <=
+// (p + 4q) Mx 2^S and a CSR entry sums at most 8 of them, below 2^62.
+__global__ void k_mixed_scale(MixedState *st, int p, int q)
+{
+    const float mx = __int_as_float(st->mx_bits);
+    st->S = (int)floor(62.0 - log2(8.0 * (p + 4.0 * q) * (double)mx * 1.25));
+}
+
+// ---------------------------------------------------------------------------
+// element kernel
+// ---------------------------------------------------------------------------
+struct WarpSmem {
+    __nv_bfloat16 sl[4][NSL][SL_ROWS][8];  // slices of G per element: [slice][row (a,c)][point]
+    int ex[4][SL_ROWS];                     // row exponents
+    long long A[24][24];                    // fixed-point A'' of the element in progress
+};
+
+__global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
+    int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
+    double cmu_q, int p, int q, double b0, double b1, double b2, const MixedState *__restrict__ st,
+    double *__restrict__ out, int64_t stride, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    WarpSmem &W = reinterpret_cast<WarpSmem *>(smem_raw)[w];
+    const int j = lane >> 3;   // element slot of this lane
+    const int qp = lane & 7;   // Gauss point (and node for loads) of this lane
+    const int gb = lane & ~7;  // first lane of the element group
+    const int64_t e_raw = ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + j;
+    const bool valid = e_raw < n_el;
+    const int64_t e = valid ? e_raw : n_el - 1;
+
+    // padding rows 24..31 of every slice stay zero
+    for (int i = lane; i < 4 * NSL * 8 * 8 / 2; i += 32) {
+        const int el = i / (NSL * 32), r = i % (NSL * 32);
+        reinterpret_cast<uint32_t *>(&W.sl[el][r / 32][24 + (r % 32) / 4][0])[r % 4] = 0u;
+    }
+
+    // --- coordinates: d = x_q - x_0 in FP64, then double-float ---
+    const int32_t *cn = conn + 8 * e;
+    const int64_t n0 = cn[0], nq = cn[qp];
+    f2 d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = from_double(X[3 * nq + i] - X[3 * n0 + i]);
+    // Walsh-Hadamard transform over the 8 corners: lane k of the group gets
+    // H[k] = sum_a (-1)^popcount(k & a) d_a; the trilinear coefficient of the
+    // monomial with index k is (-1)^popcount(k) H[k] / 8.
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const f2 o = shfl_xor(d[i], m);
+            d[i] = (qp & m) ? dsub(o, d[i]) : dadd(d[i], o);
+        }
+    {
+        // pre-scale: k = 1,2,4 (linear) by 1/8; k = 3,5,6 by G/8; k = 7 by 1/24 (G^2 = 1/3)
+        const int pc = __popc(qp);
+        const f2 kf = (pc == 2) ? DF(GD / 8.0) : ((pc == 3) ? DF(1.0 / 24.0) : DF(1.0 / 8.0));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d[i] = dsgn(dmul(d[i], kf), pc & 1);
+    }
+    f2 C1[3], C2[3], C4[3], C3[3], C5[3], C6[3], C7[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        C1[i] = shfl(d[i], gb + 1);  // xi
+        C2[i] = shfl(d[i], gb + 2);  // eta
+        C4[i] = shfl(d[i], gb + 4);  // zeta
+        C3[i] = shfl(d[i], gb + 3);  // xi eta    (x G)
+        C5[i] = shfl(d[i], gb + 5);  // xi zeta   (x G)
+        C6[i] = shfl(d[i], gb + 6);  // eta zeta  (x G)
+        C7[i] = shfl(d[i], gb + 7);  // xi eta zeta (x 1/3)
+    }
+    // --- Jacobian at this lane's Gauss point ---
+    const bool nx = !(qp & 1), ny = !(qp & 2), nz = !(qp & 4);  // sign of xi, eta, zeta is negative
+    f2 J[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        J[i][0] = dadd(dadd(C1[i], dsgn(C3[i], ny)), dadd(dsgn(C5[i], nz), dsgn(C7[i], ny != nz)));
+        J[i][1] = dadd(dadd(C2[i], dsgn(C3[i], nx)), dadd(dsgn(C6[i], nz), dsgn(C7[i], nx != nz)));
+        J[i][2] = dadd(dadd(C4[i], dsgn(C6[i], ny)), dadd(dsgn(C5[i], nx), dsgn(C7[i], nx != ny)));
+    }
+    f2 Cf[3][3];
+    Cf[0][0] = dsub(dmul(J[1][1], J[2][2]), dmul(J[1][2], J[2][1]));
+    Cf[0][1] = dsub(dmul(J[1][2], J[2][0]), dmul(J[1][0], J[2][2]));
+    Cf[0][2] = dsub(dmul(J[1][0], J[2][1]), dmul(J[1][1], J[2][0]));
+    Cf[1][0] = dsub(dmul(J[0][2], J[2][1]), dmul(J[0][1], J[2][2]));
+    Cf[1][1] = dsub(dmul(J[0][0], J[2][2]), dmul(J[0][2], J[2][0]));
+    Cf[1][2] = dsub(dmul(J[0][1], J[2][0]), dmul(J[0][0], J[2][1]));
+    Cf[2][0] = dsub(dmul(J[0][1], J[1][2]), dmul(J[0][2], J[1][1]));
+    Cf[2][1] = dsub(dmul(J[0][2], J[1][0]), dmul(J[0][0], J[1][2]));
+    Cf[2][2] = dsub(dmul(J[0][0], J[1][1]), dmul(J[0][1], J[1][0]));
+    const f2 det = dadd(dadd(dmul(J[0][0], Cf[0][0]), dmul(J[0][1], Cf[0][1])), dmul(J[0][2], Cf[0][2]));
+
+    // --- scale sqrt(mu / (q det)) with mu / q = E cmu / q ---
+    const double E = Ec[e];
+    if (valid && !isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    const f2 sig = dsqrt(ddiv(from_double(E * cmu_q), det));
+    // G[(a,c), qp] = sig sum_j d_j N_a(qp) Cf[c][j], sum-factorised over the
+    // three factor products P^2/8, PM/8, M^2/8
+    f2 Gv[8][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        f2 T[3][3];  // T[j][k]: (sig Cf[c][j]) x {PP, PM, MM}
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            const f2 u = dmul(sig, Cf[c][jj]);
+            T[jj][0] = dmul(u, DF(KPP));
+            T[jj][1] = dmul(u, DF(KPM));
+            T[jj][2] = dmul(u, DF(KMM));
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int match = ~(a ^ qp) & 7;  // bit k: s_a^k equals the sign of the point
+            f2 acc = {0.f, 0.f};
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) {
+                const int others = match & ~(1 << jj) & 7;
+                const int k = 2 - __popc(others);  // 2 matches -> PP, 1 -> PM, 0 -> MM
+                const f2 t = (k == 0) ? T[jj][0] : ((k == 1) ? T[jj][1] : T[jj][2]);
+                acc = dadd(acc, dsgn(t, !((a >> jj) & 1)));
+            }
+            Gv[a][c] = acc;
+        }
+    }
+    // --- load vector: m_a = sum_q detJ_q N_a(q) ---
+    {
+        const f2 n3 = dmul(det, DF(NP3)), n2 = dmul(det, DF(NP2)), n1 = dmul(det, DF(NP1)), n0v = dmul(det, DF(NP0));
+        f2 m[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int mt = __popc(~(a ^ qp) & 7);
+            m[a] = (mt == 3) ? n3 : ((mt == 2) ? n2 : ((mt == 1) ? n1 : n0v));
+        }
+#pragma unroll
+        for (int s = 1; s < 8; s <<= 1)
+#pragma unroll
+            for (int a = 0; a < 8; ++a) m[a] = dadd(m[a], shfl_xor(m[a], s));
+        f2 mine = m[0];
+#pragma unroll
+        for (int a = 1; a < 8; ++a)
+            if (qp == a) mine = m[a];
+        if (valid) {
+            double *dl = out + e * stride + 324 + 3 * qp;
+            const double mv = (double)mine.h + (double)mine.l;
+            dl[0] = b0 * mv;
+            dl[1] = b1 * mv;
+            dl[2] = b2 * mv;
+        }
+    }
+    // --- row exponents (max over the 8 points of the element) and slices ---
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float mx = fabsf(Gv[a][c].h);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+            const int ex = (mx > 0.f) ? (((__float_as_int(mx) >> 23) & 0xff) - 126) : -200;
+            if (qp == 0) W.ex[j][3 * a + c] = ex;
+            // x 2^-ex (exact), then 8-bit digits, rounded to nearest
+            const float s = (mx > 0.f) ? __int_as_float((127 - ex) << 23) : 0.f;
+            float h = Gv[a][c].h * s, l = Gv[a][c].l * s;
+#pragma unroll
+            for (int sl = 0; sl < NSL; ++sl) {
+                h *= 256.f;
+                l *= 256.f;
+                const float dg = rintf(h);
+                const f2 r = two_sum(h - dg, l);
+                h = r.h;
+                l = r.l;
+                W.sl[j][sl][3 * a + c][qp] = __float2bfloat16_rn(dg);
+            }
+        }
+    __syncwarp();
+
+    // --- tensor cores: A'' = G G^T by levels, per element of the warp ---
+    const int g = lane >> 2, t = lane & 3;
+    const int S = st->S;
+#pragma unroll 1
+    for (int el = 0; el < 4; ++el) {
+        const int64_t eo = ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + el;
+        float acc[5][4][4];
+#pragma unroll
+        for (int L = 0; L < 5; ++L)
+#pragma unroll
+            for (int tl = 0; tl < 4; ++tl)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[L][tl][k] = 0.f;
+        auto ld = [&](int sl, int row) -> uint32_t {
+            return *reinterpret_cast<const uint32_t *>(&W.sl[el][sl][row][2 * t]);
+        };
+#pragma unroll
+        for (int L = 0; L < 5; ++L) {
+#pragma unroll
+            for (int s0 = 0; s0 <= L; s0 += 2) {
+                const int s1 = s0 + 1;  // second half of k: slice s1 against slice L - s1
+                const bool two = s1 <= L;
+                uint32_t a[2][4], bf[3][2];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    a[mt][0] = ld(s0, mt * 16 + g);
+                    a[mt][1] = ld(s0, mt * 16 + g + 8);
+                    a[mt][2] = two ? ld(s1, mt * 16 + g) : 0u;
+                    a[mt][3] = two ? ld(s1, mt * 16 + g + 8) : 0u;
+                }
+#pragma unroll
+                for (int nt = 0; nt < 3; ++nt) {
+                    bf[nt][0] = ld(L - s0, nt * 8 + g);
+                    bf[nt][1] = two ? ld(L - s1, nt * 8 + g) : 0u;
+                }
+                mma_bf16(acc[L][0], a[0][0], a[0][1], a[0][2], a[0][3], bf[0][0], bf[0][1]);
+                mma_bf16(acc[L][1], a[0][0], a[0][1], a[0][2], a[0][3], bf[1][0], bf[1][1]);
+                mma_bf16(acc[L][2], a[0][0], a[0][1], a[0][2], a[0][3], bf[2][0], bf[2][1]);
+                mma_bf16(acc[L][3], a[1][0], a[1][1], a[1][2], a[1][3], bf[2][0], bf[2][1]);
+            }
+        }
+        // levels -> 64-bit fixed point at scale 2^S, into shared memory
+        const int tmt[4] = {0, 0, 0, 1}, tnt[4] = {0, 1, 2, 2};
+#pragma unroll
+        for (int tl = 0; tl < 4; ++tl)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int rho = tmt[tl] * 16 + g + 8 * (k >> 1);
+                const int sig2 = tnt[tl] * 8 + 2 * t + (k & 1);
+                if (rho >= 24) continue;
+                long long T = f2i_exact(acc[0][tl][k]);
+#pragma unroll
+                for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][tl][k]);
+                const int sh = W.ex[el][rho] + W.ex[el][sig2] + S - 48;
+                long long v;
+                if (sh >= 0) v = T << sh;
+                else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
+                else v = 0;
+                W.A[rho][sig2] = v;
+                if (tl == 2 && rho < 16) W.A[sig2][rho] = v;  // mirror of the block not computed
+            }
+        __syncwarp();
+        // finishing K = p A + q swap(A) + q I tr(A) on the upper blocks a <= b
+        if (eo < n_el) {
+            long long *o = reinterpret_cast<long long *>(out + eo * stride);
+            for (int idx = lane; idx < 324; idx += 32) {
+                const int blk = idx / 9, cc = idx - 9 * blk;
+                int a = 0, rem = blk;
+                while (rem >= 8 - a) { rem -= 8 - a; ++a; }
+                const int b = a + rem;
+                const int c = cc / 3, cp = cc - 3 * c;
+                long long v = (long long)p * W.A[3 * a + c][3 * b + cp] + (long long)q * W.A[3 * a + cp][3 * b + c];
+                if (c == cp)
+                    v += (long long)q * (W.A[3 * a][3 * b] + W.A[3 * a + 1][3 * b + 1] + W.A[3 * a + 2][3 * b + 2]);
+                o[idx] = v;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
 
 mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c, double *values,
                             double *d, cudaStream_t st)
 {
-    (void)form; (void)m; (void)p; (void)c; (void)values; (void)d; (void)st;
-    return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: mixed path not built");
+    if (form != MF_FORM_ELASTIC || m->elem != MF_Q1_HEX || !p->slot || !p->mixed_state)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: the mixed path covers Q1 elasticity");
+    const double nu = c->nu;
+    if (!(nu > -1.0 && nu < 0.5)) return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: Poisson ratio outside (-1, 0.5)");
+    // lambda / mu = 2 nu / (1 - 2 nu) as a small-integer ratio p / q
+    const double r = 2.0 * nu / (1.0 - 2.0 * nu);
+    int pp = -1, qq = 0;
+    for (int qd = 1; qd <= 64 && pp < 0; ++qd) {
+        const double pn = r * qd;
+        const double pr = nearbyint(pn);
+        if (pr >= 0.0 && pr <= 4096.0 && fabs(pr / qd - r) <= 1e-13 * (1.0 + fabs(r))) {
+            pp = (int)pr;
+            qq = qd;
+        }
+    }
+    if (pp < 0)
+        return mf_fail(MF_ERR_UNSUPPORTED,
+                       "mf_assemble: mixed path needs lambda/mu = 2nu/(1-2nu) to be a ratio p/q with q <= 64");
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_assemble: status word unavailable");
+    const double cmu_q = 1.0 / (2.0 * (1.0 + nu)) / qq;
+    MixedState *ms = static_cast<MixedState *>(p->mixed_state);
+    const int64_t ne = m->n_elems;
+    mf_prof_begin("mixed_bound", st);
+    MF_CUDA(cudaMemsetAsync(ms, 0, sizeof(MixedState), st));
+    k_mixed_bound<<<(unsigned)((ne + 127) / 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, (float)cmu_q,
+                                                                ms, status);
+    k_mixed_scale<<<1, 1, 0, st>>>(ms, pp, qq);
+    mf_prof_end(st);
+    const size_t smem = sizeof(WarpSmem) * MX_WARPS;
+    MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    mf_prof_begin("mixed_elem", st);
+    k_mixed_elem<<<(unsigned)((ne + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
+        ne, m->coords, m->conn, c->elem_coef, cmu_q, pp, qq, c->source[0], c->source[1], c->source[2], ms, p->scratch,
+        p->scratch_stride, status);
+    mf_prof_end(st);
+    MF_CUDA(cudaGetLastError());
+    mf_prof_begin("gather_elastic_fixed", st);
+    mf_launch_gather_elastic(true, m, p, c, values, d, st);
+    mf_prof_end(st);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
 }

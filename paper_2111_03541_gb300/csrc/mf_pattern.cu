@@ -173,6 +173,18 @@ __global__ void k_contrib(int64_t n_el, int npe_r, const int32_t *__restrict__ c
     }
 }
 
+// slot map: position of conn[e][b] among the neighbours of conn[e][a]
+__global__ void k_slot_map(int64_t n_el, const int32_t *__restrict__ conn, const int64_t *__restrict__ ptr,
+                           const int32_t *__restrict__ col, uint8_t *slot)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_el * 64) return;
+    const int64_t e = t >> 6;
+    const int a = (int)(t >> 3) & 7, b = (int)t & 7;
+    const int32_t n = conn[e * 8 + a], m = conn[e * 8 + b];
+    slot[t] = (uint8_t)(find_pair(ptr, col, n, m) - ptr[n]);
+}
+
 // ---------------------------------------------------------------------------
 // dof-level CSR of each form
 // ---------------------------------------------------------------------------
@@ -367,6 +379,10 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->inc);
     cudaFree(p->pinc_ptr);
     cudaFree(p->pinc);
+    cudaFree(p->slot);
+    cudaFree(p->mixed_state);
+    p->slot = nullptr;
+    p->mixed_state = nullptr;
     p->pinc_ptr = nullptr;
     p->pinc = nullptr;
     p->row_ptr = nullptr;
@@ -406,6 +422,9 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
         k_csr_elastic<<<nblk(p->n_rows + 1), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->row_ptr,
                                                            p->col_idx);
+        MF_CUDA(cudaMallocAsync(&p->slot, (size_t)64 * m->n_elems, st));
+        k_slot_map<<<nblk(m->n_elems * 64), TPB, 0, st>>>(m->n_elems, m->conn, p->adj[0].ptr, p->adj[0].col, p->slot);
+        MF_CUDA(cudaMallocAsync(&p->mixed_state, 64, st));
         p->scratch_stride = 36 * 9 + 24;
     } else {
         Incidence incp;

@@ -1,0 +1,114 @@
+"""Mixed-precision (tensor-core) assembly of Q1 elasticity against the oracle.
+
+Contract: the CSR pattern is the same bit for bit; K within 1e-11 row-scaled
+of the FP64 oracle (the slices keep about 40 bits of the scaled gradients);
+the solution of the mixed system within 1e-8 relative of the oracle's
+tightly solved x*; two assemblies bit-identical.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+TOL_K = 1e-11
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2111_03541_gb300 as mf
+    mf.lib()
+    return mf
+
+
+def row_scaled_error(rp, val, ref):
+    n = rp.shape[0] - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    emax = np.zeros(n)
+    rmax = np.zeros(n)
+    np.maximum.at(emax, rows, np.abs(val - ref))
+    np.maximum.at(rmax, rows, np.abs(ref))
+    ok = rmax > 0
+    assert (emax[~ok] == 0).all()
+    return (emax[ok] / rmax[ok]).max()
+
+
+@pytest.mark.parametrize("n,nu", [(5, 0.3), (9, 0.3), (13, 0.3), (6, 0.25), (6, 0.45), (6, 0.0)])
+def test_mixed_values_against_oracle(mf, orc, n, nu):
+    prob = gen.elastic_problem(n, nu=nu)
+    P = mf.Problem(prob)
+    vals, d = P.assemble(mf.MF_PREC_MIXED)
+    mf.mf_sync_status()
+    rp, ci = P.csr_arrays()
+    rp = rp.cpu().numpy()
+    ref = orc.assemble(prob)
+    assert np.array_equal(rp, ref["row_ptr"]) and np.array_equal(ci.cpu().numpy(), ref["col"])
+    err = row_scaled_error(rp, vals.cpu().numpy(), ref["val"])
+    assert err <= TOL_K, err
+    assert np.abs(d.cpu().numpy() - ref["d"]).max() <= 1e-12 * np.abs(ref["d"]).max()
+
+
+def test_mixed_without_dirichlet_keeps_rigid_modes(mf, orc):
+    import torch
+    prob = gen.elastic_problem(6)
+    P = mf.Problem(prob)
+    vals, d = P.assemble(mf.MF_PREC_MIXED, coeffs=P.make_coeffs(bc=False))
+    x = prob["coords"]
+    scale = vals.abs().max().item()
+    for w in np.eye(3):
+        u = torch.from_numpy(np.cross(w, x).ravel()).cuda()
+        y = torch.empty_like(u)
+        mf.mf_spmv(P.csr, u, y)
+        assert y.abs().max().item() <= 1e-11 * scale
+
+
+def test_mixed_solution_within_1e8(mf, orc):
+    import torch
+    prob = gen.elastic_problem(12)
+    P = mf.Problem(prob)
+    P.assemble(mf.MF_PREC_MIXED)
+    x, st, info = P.solve(tol=1e-12, max_iter=100000)
+    assert st == mf.MF_OK
+    ref = orc.assemble(prob)
+    xo, _, rr = orc.pcg(ref, tol=1e-14, maxit=100000)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-8, err
+
+
+def test_mixed_bit_reproducible(mf):
+    import torch
+    P = mf.Problem(gen.elastic_problem(11))
+    v1, d1 = [t.clone() for t in P.assemble(mf.MF_PREC_MIXED)]
+    P.values.zero_()
+    v2, d2 = P.assemble(mf.MF_PREC_MIXED)
+    assert torch.equal(v1, v2) and torch.equal(d1, d2)
+
+
+def test_mixed_full_size_sampled_rows(mf, orc):
+    prob = gen.elastic_problem(64)
+    P = mf.Problem(prob)
+    vals, d = P.assemble(mf.MF_PREC_MIXED)
+    rp, ci = P.csr_arrays()
+    rp, ci, vals = rp.cpu().numpy(), ci.cpu().numpy(), vals.cpu().numpy()
+    nn = prob["coords"].shape[0]
+    nodes = np.unique(np.concatenate([np.random.default_rng(13).integers(0, nn, 30), [1, 66, nn - 2]]))
+    keep = np.zeros(nn, np.uint8)
+    keep[nodes] = 1
+    ref = orc.assemble(prob, keep_nodes=keep)
+    rows = [3 * n + c for n in nodes for c in range(3)]
+    for r, (cols, v) in zip(rows, orc.rows_of(ref, rows)):
+        s = slice(rp[r], rp[r + 1])
+        assert np.array_equal(ci[s], cols)
+        assert np.abs(vals[s] - v).max() <= TOL_K * np.abs(v).max()
+
+
+def test_mixed_refuses_irrational_ratio(mf):
+    prob = gen.elastic_problem(3, nu=0.3141592653589793)
+    P = mf.Problem(prob)
+    with pytest.raises(mf.MFError) as ei:
+        P.assemble(mf.MF_PREC_MIXED)
+    assert ei.value.status == mf.MF_ERR_UNSUPPORTED
