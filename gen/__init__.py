@@ -317,15 +317,17 @@ def grf_cells(n: int = 128, corr_len: float = 0.1, sigma: float = 1.0,
     """Gaussian random field on the n^3 cells of the unit cube (x fastest).
 
     Squared-exponential covariance exp(-r^2 / (2 l^2)), sampled by filtering
-    white noise in Fourier space on the periodic n^3 grid, then scaled to
-    standard deviation ``sigma``.  Returns float64 [n^3].
+    white noise in Fourier space on the periodic n^3 grid.  The filter's
+    point variance sum_k filt(k)^2 / n^3 (Parseval) scales the field to
+    standard deviation ``sigma`` in expectation, so the mean stays a proper
+    zero-mean random component.  Returns float64 [n^3].
     """
     w = normal(seed, n ** 3).reshape(n, n, n)
     k = 2.0 * np.pi * np.fft.fftfreq(n, d=1.0 / n)
     kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
     filt = np.exp(-0.25 * corr_len ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
     g = np.fft.ifftn(np.fft.fftn(w) * filt).real
-    g *= sigma / g.std()
+    g *= sigma / np.sqrt(np.sum(filt ** 2) / n ** 3)
     return g.ravel()
 
 

@@ -211,6 +211,83 @@ mf_status mf_spmv(const mf_csr *K, const double *x, double *y, void *stream);
 mf_status mf_set_kernel_timing(int32_t enable);
 mf_status mf_kernel_times(char *buf, size_t len);
 
+/* ---- Batched assembly (many thermal problems in one launch) -------------
+ * Many independent thermal problems (Sec. 4.1 form) of uneven size and mixed
+ * element order (P1, P2, Q1), each with its own mesh, pattern, coefficients
+ * and output buffers, are assembled by two persistent launches over
+ * (problem, tile) descriptors: element tiles sorted by element type, then node
+ * tiles of the fixed-order gather.  The launches are captured in a CUDA graph
+ * at the first mf_batch_assemble and replayed.  Each problem's K and d are
+ * bitwise equal to mf_assemble's.  Tiling: elements per tile, threads per
+ * element block, nodes per gather tile, resident blocks per SM (grid size). */
+typedef struct mf_batch mf_batch;
+typedef struct {
+    int32_t elem_tile;
+    int32_t elem_block;      /* multiple of 32, <= 256 */
+    int32_t node_tile;
+    int32_t grid_per_sm;
+} mf_batch_tiling;
+/* meshes/patterns [n] (thermal patterns of those meshes), coeffs [n] (host
+ * array of device-pointer structs), values[i] [nnz_i] and d[i] [n_rows_i]
+ * device buffers; all must outlive the batch.  Errors: MF_ERR_INVALID_ARG,
+ * MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, const mf_pattern *const *patterns,
+                          const mf_coeffs *coeffs, double *const *values, double *const *d, mf_batch **out);
+mf_status mf_batch_set_tiling(mf_batch *batch, const mf_batch_tiling *tiling);
+mf_status mf_batch_get_tiling(const mf_batch *batch, mf_batch_tiling *tiling);
+/* Autotuner: times candidate tilings (3 graph replays each) on this batch and
+ * keeps the fastest; with cache_path (a small JSON file, may be NULL) a tiling
+ * found earlier for the same batch signature is reused without timing, and a
+ * new result is stored.  Synchronises the stream. */
+mf_status mf_batch_autotune(mf_batch *batch, const char *cache_path, void *stream, mf_batch_tiling *chosen);
+/* Assembles every problem of the batch (one graph launch, asynchronous). */
+mf_status mf_batch_assemble(mf_batch *batch, void *stream);
+mf_status mf_batch_destroy(mf_batch *batch);
+
+/* ---- Learned preconditioner correction (3D CNN) -------------------------
+ * Not in the paper: a growth line of the hot path.  A 4-layer 3x3x3
+ * convolution network (2 -> 16 -> 16 -> 16 -> 1 channels, ReLU after the first
+ * three, zero padding) on the node grid (nz, ny, nx) of a structured Q1 thermal
+ * problem (node v = (z ny + y) nx + x).  BF16 weights and activations, FP32
+ * accumulation, FP32 master weights and AdamW moments for training.  Inputs
+ * per node: (r / max|r|, log k_nodal / 2) in BF16.  Used as
+ *   z = D^-1 r + max|r| (1 - mask) CNN(r / max|r|, log k)
+ * inside flexible CG, falling back to z = D^-1 r when z . r <= 0.
+ * Parameters: mf_cnn_num_params() floats, layer by layer [w (co, ci, 27) | b (co)],
+ * offset index o = (dz+1) 9 + (dy+1) 3 + (dx+1). */
+typedef struct mf_cnn mf_cnn;
+int64_t mf_cnn_num_params(void);
+/* init: host array of mf_cnn_num_params() floats (initial weights). */
+mf_status mf_cnn_create(const float *init, mf_cnn **out);
+mf_status mf_cnn_destroy(mf_cnn *cnn);
+mf_status mf_cnn_get_params(const mf_cnn *cnn, float *host, int64_t n);
+mf_status mf_cnn_get_grads(const mf_cnn *cnn, float *host, int64_t n);
+/* x: device BF16 [B][nv][2]; y: device FP32 [B][nv]. */
+mf_status mf_cnn_forward(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x, float *y,
+                         void *stream);
+/* Gradients of sum(gy * CNN(x)) into the gradient buffer (read with mf_cnn_get_grads). */
+mf_status mf_cnn_backward(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
+                          const float *gy, void *stream);
+/* One AdamW step (lr > 0; lr = 0 only computes the loss and gradients) on B
+ * samples of systems sharing the pattern of K: kvals[b] the values of system
+ * b, r[b] its residual, x[b] its network input (device pointers); the Jacobi
+ * part uses diag(K_b).  loss (host) = mean_b ||K_b z_b - r_b||^2 / ||r_b||^2. */
+mf_status mf_cnn_train_step(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_t nx, const mf_csr *K,
+                            const double *const *kvals, const double *const *r, const void *const *x,
+                            const uint8_t *mask, float lr, float weight_decay, double *loss, void *stream);
+/* Nodal mean of log k over the cells of the (nz-1)(ny-1)(nx-1) cell grid. */
+mf_status mf_cnn_node_logk(int32_t nz, int32_t ny, int32_t nx, const double *kcell, float *out, void *stream);
+/* Network input from a residual: x [n][2] BF16 = (r / max|r|, logk / 2). */
+mf_status mf_cnn_input(int64_t n, const double *r, const float *logk, void *x_bf16, void *stream);
+/* y = a x + b y on device vectors of length n. */
+mf_status mf_axpby(int64_t n, double a, const double *x, double b, double *y, void *stream);
+/* Flexible CG (Notay 2000, one stored direction) preconditioned by the CNN
+ * correction with the Jacobi fallback; x holds x0 on entry.  fallbacks (may
+ * be NULL) counts the iterations that fell back to Jacobi.  Errors: as mf_solve. */
+mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *x, mf_cnn *cnn, int32_t nz, int32_t ny,
+                           int32_t nx, const float *logk, const uint8_t *mask, double tol, int64_t max_iter,
+                           mf_solve_info *info, int64_t *fallbacks, void *stream);
+
 /* Synchronises the stream, returns and clears the latched device status. */
 mf_status mf_sync_status(void *stream);
 

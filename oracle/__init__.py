@@ -74,6 +74,9 @@ def lib():
         _lib.or_pcg.restype = i64
         _lib.or_gmres.argtypes = [i64, vp, vp, vp, vp, vp, vp, i, d, i64, C.POINTER(d)]
         _lib.or_gmres.restype = i64
+        _lib.or_conv3d_fwd.argtypes = [i64, i64, i64, i, i, vp, vp, vp, i, vp]
+        _lib.or_conv3d_bwd_data.argtypes = [i64, i64, i64, i, i, vp, vp, vp]
+        _lib.or_conv3d_bwd_weight.argtypes = [i64, i64, i64, i, i, vp, vp, vp, vp]
     return _lib
 
 
@@ -291,3 +294,39 @@ def oseen_precond(sys: dict, prob: dict) -> np.ndarray:
     mask = prob["bc_mask"].astype(bool)
     p[mask] = 1.0
     return p
+
+
+# ---------------------------------------------------------------------------
+# 3x3x3 convolution layers (learned preconditioner correction)
+# ---------------------------------------------------------------------------
+
+def conv3d_fwd(x, w, b=None, relu=False):
+    """x [nz, ny, nx, ci], w [co, ci, 27], b [co] -> [nz, ny, nx, co] (zero padding)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    bb = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+    nz, ny, nx, ci = x.shape
+    co = w.shape[0]
+    out = np.zeros((nz, ny, nx, co))
+    lib().or_conv3d_fwd(nz, ny, nx, ci, co, _p(x), _p(w), _p(bb), int(relu), _p(out))
+    return out
+
+
+def conv3d_bwd_data(gout, w, ci):
+    gout = np.ascontiguousarray(gout, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    nz, ny, nx, co = gout.shape
+    gin = np.zeros((nz, ny, nx, ci))
+    lib().or_conv3d_bwd_data(nz, ny, nx, ci, co, _p(gout), _p(w), _p(gin))
+    return gin
+
+
+def conv3d_bwd_weight(x, gout):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    gout = np.ascontiguousarray(gout, dtype=np.float64)
+    nz, ny, nx, ci = x.shape
+    co = gout.shape[3]
+    gw = np.zeros((co, ci, 27))
+    gb = np.zeros(co)
+    lib().or_conv3d_bwd_weight(nz, ny, nx, ci, co, _p(x), _p(gout), _p(gw), _p(gb))
+    return gw, gb

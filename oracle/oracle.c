@@ -725,3 +725,80 @@ int64_t or_gmres(int64_t n, const int64_t *rp, const int32_t *ci, const double *
     free(V); free(H); free(cs); free(sn); free(s); free(y); free(w); free(z);
     return ok ? it : -1;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 3x3x3 convolution layers of the learned preconditioner correction       */
+/* (growth line of the hot path; not in the paper).  Channels-last grids    */
+/* [nz][ny][nx][c], zero padding outside the grid, weights [co][ci][27]     */
+/* with offset index o = (dz+1)*9 + (dy+1)*3 + (dx+1):                      */
+/*   out[v][co] = b[co] + sum_ci sum_o w[co][ci][o] in[v + off(o)][ci].     */
+/* ------------------------------------------------------------------------ */
+static int in_grid(int64_t z, int64_t y, int64_t x, int64_t nz, int64_t ny, int64_t nx)
+{
+    return z >= 0 && z < nz && y >= 0 && y < ny && x >= 0 && x < nx;
+}
+
+void or_conv3d_fwd(int64_t nz, int64_t ny, int64_t nx, int ci_n, int co_n, const double *in, const double *w,
+                   const double *b, int relu, double *out)
+{
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t v = (z * ny + y) * nx + x;
+                for (int co = 0; co < co_n; ++co) {
+                    double s = b ? b[co] : 0.0;
+                    for (int ci = 0; ci < ci_n; ++ci)
+                        for (int o = 0; o < 27; ++o) {
+                            const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+                            if (!in_grid(z + dz, y + dy, x + dx, nz, ny, nx)) continue;
+                            const int64_t u = ((z + dz) * ny + (y + dy)) * nx + (x + dx);
+                            s += w[((int64_t)co * ci_n + ci) * 27 + o] * in[u * ci_n + ci];
+                        }
+                    out[v * co_n + co] = (relu && s < 0.0) ? 0.0 : s;
+                }
+            }
+}
+
+/* gin[u][ci] = sum over (v, o) with u = v + off(o) of w[co][ci][o] gout[v][co] */
+void or_conv3d_bwd_data(int64_t nz, int64_t ny, int64_t nx, int ci_n, int co_n, const double *gout,
+                        const double *w, double *gin)
+{
+    const int64_t nv = nz * ny * nx;
+    for (int64_t i = 0; i < nv * ci_n; ++i) gin[i] = 0.0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t v = (z * ny + y) * nx + x;
+                for (int co = 0; co < co_n; ++co)
+                    for (int ci = 0; ci < ci_n; ++ci)
+                        for (int o = 0; o < 27; ++o) {
+                            const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+                            if (!in_grid(z + dz, y + dy, x + dx, nz, ny, nx)) continue;
+                            const int64_t u = ((z + dz) * ny + (y + dy)) * nx + (x + dx);
+                            gin[u * ci_n + ci] += w[((int64_t)co * ci_n + ci) * 27 + o] * gout[v * co_n + co];
+                        }
+            }
+}
+
+/* gw[co][ci][o] = sum_v gout[v][co] in[v + off(o)][ci];  gb[co] = sum_v gout[v][co] */
+void or_conv3d_bwd_weight(int64_t nz, int64_t ny, int64_t nx, int ci_n, int co_n, const double *in,
+                          const double *gout, double *gw, double *gb)
+{
+    for (int64_t i = 0; i < (int64_t)co_n * ci_n * 27; ++i) gw[i] = 0.0;
+    for (int co = 0; co < co_n; ++co) gb[co] = 0.0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t v = (z * ny + y) * nx + x;
+                for (int co = 0; co < co_n; ++co) {
+                    gb[co] += gout[v * co_n + co];
+                    for (int ci = 0; ci < ci_n; ++ci)
+                        for (int o = 0; o < 27; ++o) {
+                            const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+                            if (!in_grid(z + dz, y + dy, x + dx, nz, ny, nx)) continue;
+                            const int64_t u = ((z + dz) * ny + (y + dy)) * nx + (x + dx);
+                            gw[((int64_t)co * ci_n + ci) * 27 + o] += gout[v * co_n + co] * in[u * ci_n + ci];
+                        }
+                }
+            }
+}

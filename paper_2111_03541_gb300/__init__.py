@@ -55,6 +55,11 @@ class SolverOpts(C.Structure):
                 ("precond_diag", C.c_void_p), ("check_every", C.c_int32)]
 
 
+class BatchTiling(C.Structure):
+    _fields_ = [("elem_tile", C.c_int32), ("elem_block", C.c_int32), ("node_tile", C.c_int32),
+                ("grid_per_sm", C.c_int32)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("rel_residual", C.c_double), ("converged", C.c_int32)]
 
@@ -78,6 +83,28 @@ _SIGS = {
                              C.POINTER(SolveInfo), C.c_void_p],
     "mf_spmv": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_sync_status": [C.c_void_p],
+    "mf_batch_create": [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                        C.POINTER(C.c_void_p)],
+    "mf_batch_set_tiling": [C.c_void_p, C.POINTER(BatchTiling)],
+    "mf_batch_get_tiling": [C.c_void_p, C.POINTER(BatchTiling)],
+    "mf_batch_autotune": [C.c_void_p, C.c_char_p, C.c_void_p, C.POINTER(BatchTiling)],
+    "mf_batch_assemble": [C.c_void_p, C.c_void_p],
+    "mf_batch_destroy": [C.c_void_p],
+    "mf_cnn_create": [C.c_void_p, C.POINTER(C.c_void_p)],
+    "mf_cnn_destroy": [C.c_void_p],
+    "mf_cnn_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
+    "mf_cnn_get_grads": [C.c_void_p, C.c_void_p, C.c_int64],
+    "mf_cnn_forward": [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_cnn_backward": [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_cnn_train_step": [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(CSR), C.c_void_p,
+                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.POINTER(C.c_double),
+                          C.c_void_p],
+    "mf_cnn_node_logk": [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_cnn_input": [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_axpby": [C.c_int64, C.c_double, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
+    "mf_solve_fcg_cnn": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                         C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.POINTER(SolveInfo),
+                         C.POINTER(C.c_int64), C.c_void_p],
     "mf_set_kernel_timing": [C.c_int32],
     "mf_kernel_times": [C.c_char_p, C.c_size_t],
 }
@@ -94,6 +121,8 @@ def lib() -> C.CDLL:
             f = getattr(L, name)
             f.argtypes = argt
             f.restype = C.c_int
+        L.mf_cnn_num_params.argtypes = []
+        L.mf_cnn_num_params.restype = C.c_int64
         L.mf_last_error.argtypes = []
         L.mf_last_error.restype = C.c_char_p
         _lib = L
@@ -101,7 +130,7 @@ def lib() -> C.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return list(_SIGS) + ["mf_last_error"]
+    return list(_SIGS) + ["mf_last_error", "mf_cnn_num_params"]
 
 
 def _check(status: int, allow=()) -> int:
@@ -191,6 +220,113 @@ def mf_spmv(K: CSR, x, y, stream=None) -> None:
 
 def mf_sync_status(stream=None) -> None:
     _check(lib().mf_sync_status(_stream(stream)))
+
+
+def mf_batch_create(problems: list, stream=None) -> C.c_void_p:
+    """Batch of thermal ``Problem`` objects (their mesh, pattern, coefficients and buffers)."""
+    n = len(problems)
+    meshes = (C.c_void_p * n)(*[p.mesh.value for p in problems])
+    pats = (C.c_void_p * n)(*[p.pattern.value for p in problems])
+    coeffs = (Coeffs * n)(*[p.coeffs for p in problems])
+    vals = (C.c_void_p * n)(*[_ptr(p.values) for p in problems])
+    ds = (C.c_void_p * n)(*[_ptr(p.d) for p in problems])
+    h = C.c_void_p()
+    _check(lib().mf_batch_create(n, meshes, pats, coeffs, vals, ds, C.byref(h)))
+    return h
+
+
+def mf_batch_set_tiling(batch, tiling: BatchTiling) -> None:
+    _check(lib().mf_batch_set_tiling(batch, C.byref(tiling)))
+
+
+def mf_batch_get_tiling(batch) -> BatchTiling:
+    t = BatchTiling()
+    _check(lib().mf_batch_get_tiling(batch, C.byref(t)))
+    return t
+
+
+def mf_batch_autotune(batch, cache_path: str | None = None, stream=None) -> BatchTiling:
+    t = BatchTiling()
+    _check(lib().mf_batch_autotune(batch, None if cache_path is None else cache_path.encode(), _stream(stream),
+                                   C.byref(t)))
+    return t
+
+
+def mf_batch_assemble(batch, stream=None) -> None:
+    _check(lib().mf_batch_assemble(batch, _stream(stream)))
+
+
+def mf_batch_destroy(batch) -> None:
+    _check(lib().mf_batch_destroy(batch))
+
+
+def mf_cnn_num_params() -> int:
+    return int(lib().mf_cnn_num_params())
+
+
+def mf_cnn_create(init) -> C.c_void_p:
+    """init: float32 numpy array of mf_cnn_num_params() initial parameters."""
+    import numpy as np
+    init = np.ascontiguousarray(init, dtype=np.float32)
+    h = C.c_void_p()
+    _check(lib().mf_cnn_create(init.ctypes.data, C.byref(h)))
+    return h
+
+
+def mf_cnn_destroy(h) -> None:
+    _check(lib().mf_cnn_destroy(h))
+
+
+def mf_cnn_get_params(h):
+    import numpy as np
+    out = np.empty(mf_cnn_num_params(), dtype=np.float32)
+    _check(lib().mf_cnn_get_params(h, out.ctypes.data, out.size))
+    return out
+
+
+def mf_cnn_get_grads(h):
+    import numpy as np
+    out = np.empty(mf_cnn_num_params(), dtype=np.float32)
+    _check(lib().mf_cnn_get_grads(h, out.ctypes.data, out.size))
+    return out
+
+
+def mf_cnn_forward(h, B, nz, ny, nx, x, y, stream=None) -> None:
+    _check(lib().mf_cnn_forward(h, B, nz, ny, nx, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def mf_cnn_backward(h, B, nz, ny, nx, x, gy, stream=None) -> None:
+    _check(lib().mf_cnn_backward(h, B, nz, ny, nx, _ptr(x), _ptr(gy), _stream(stream)))
+
+
+def mf_cnn_train_step(h, nz, ny, nx, K: CSR, kvals, r, x, mask, lr, weight_decay, stream=None) -> float:
+    B = len(kvals)
+    arr = lambda ts: (C.c_void_p * B)(*[_ptr(t) for t in ts])
+    loss = C.c_double()
+    _check(lib().mf_cnn_train_step(h, B, nz, ny, nx, C.byref(K), arr(kvals), arr(r), arr(x), _ptr(mask),
+                                   lr, weight_decay, C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def mf_cnn_node_logk(nz, ny, nx, kcell, out, stream=None) -> None:
+    _check(lib().mf_cnn_node_logk(nz, ny, nx, _ptr(kcell), _ptr(out), _stream(stream)))
+
+
+def mf_cnn_input(n, r, logk, x, stream=None) -> None:
+    _check(lib().mf_cnn_input(n, _ptr(r), _ptr(logk), _ptr(x), _stream(stream)))
+
+
+def mf_axpby(n, a, x, b, y, stream=None) -> None:
+    _check(lib().mf_axpby(n, a, _ptr(x), b, _ptr(y), _stream(stream)))
+
+
+def mf_solve_fcg_cnn(K: CSR, d, x, cnn, nz, ny, nx, logk, mask, tol, max_iter, stream=None,
+                     allow=(MF_ERR_NOT_CONVERGED,)):
+    info = SolveInfo()
+    fb = C.c_int64()
+    st = _check(lib().mf_solve_fcg_cnn(C.byref(K), _ptr(d), _ptr(x), cnn, nz, ny, nx, _ptr(logk), _ptr(mask), tol,
+                                       max_iter, C.byref(info), C.byref(fb), _stream(stream)), allow)
+    return st, info, fb.value
 
 
 def mf_set_kernel_timing(enable: bool) -> None:

@@ -15,114 +15,11 @@
 //             with A_ab = sum_q w detJ gradN_a gradN_b^T,   de[(a,c)] = body_c sum_q w detJ N_a
 //   flow      A[a][b] = sum_q w detJ (mu gradN_a.gradN_b - rho (a_h.gradN_a) N_b),
 //             B_i[a][b] = sum_q w detJ M_a d_i N_b; the u-p block is -B_i^T.
-#include "mf_internal.h"
+#include "mf_fem.cuh"
 
 namespace {
 
-constexpr double QG = 0.57735026918962576451;  // 2-point Gauss abscissa 1/sqrt(3)
-// symmetric 6-point degree-4 triangle rule (two orbits (a, a, 1-2a)); weights
-// normalised to area 1
-constexpr double T6A1 = 0.44594849091596488632, T6W1 = 0.22338158967801146570;
-constexpr double T6A2 = 0.091576213509770743460, T6W2 = 0.10995174365532186764;
-
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-
-// reference derivative dN_a/dxi_j of the trilinear basis at Gauss point q
-__device__ __forceinline__ double q1_dref(int q, int a, int j)
-{
-    const double xs[3] = {(q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG};
-    const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
-    double v = 0.125 * s[j];
-    for (int i = 0; i < 3; ++i)
-        if (i != j) v *= 1.0 + s[i] * xs[i];
-    return v;
-}
-
-__device__ __forceinline__ double q1_n(int q, int a)
-{
-    const double xs[3] = {(q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG};
-    const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
-    return 0.125 * (1.0 + s[0] * xs[0]) * (1.0 + s[1] * xs[1]) * (1.0 + s[2] * xs[2]);
-}
-
-// Jacobian of the trilinear map at Gauss point q, its determinant and inverse
-__device__ __forceinline__ double q1_jac(const double (&x)[8][3], int q, double (&Ji)[3][3])
-{
-    double J[3][3] = {};
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const double dn = q1_dref(q, a, j);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) J[i][j] = fma(x[a][i], dn, J[i][j]);
-        }
-    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-    const double r = 1.0 / det;
-    Ji[0][0] = c00 * r;
-    Ji[1][0] = c01 * r;
-    Ji[2][0] = c02 * r;
-    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
-    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
-    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
-    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
-    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
-    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
-    return det;
-}
-
-// affine triangle from its first three nodes: detJ and grad lambda_k
-__device__ __forceinline__ double tri_affine(const double *__restrict__ X, const int32_t *__restrict__ c,
-                                             double (&gl)[3][2])
-{
-    const double x0 = X[2 * (int64_t)c[0]], y0 = X[2 * (int64_t)c[0] + 1];
-    const double j00 = X[2 * (int64_t)c[1]] - x0, j10 = X[2 * (int64_t)c[1] + 1] - y0;
-    const double j01 = X[2 * (int64_t)c[2]] - x0, j11 = X[2 * (int64_t)c[2] + 1] - y0;
-    const double det = j00 * j11 - j01 * j10;
-    const double r = 1.0 / det;
-    // J^{-1} = [[j11, -j01], [-j10, j00]] / det ; grad lambda = J^{-T} gradref lambda
-    const double i00 = j11 * r, i01 = -j01 * r, i10 = -j10 * r, i11 = j00 * r;
-    gl[1][0] = i00; gl[1][1] = i01;   // gradref lambda_1 = (1, 0)
-    gl[2][0] = i10; gl[2][1] = i11;   // gradref lambda_2 = (0, 1)
-    gl[0][0] = -i00 - i10; gl[0][1] = -i01 - i11;
-    return det;
-}
-
-// P2 basis values and physical gradients at barycentric point l
-__device__ __forceinline__ void p2_basis(const double (&l)[3], const double (&gl)[3][2], double (&N)[6],
-                                         double (&g)[6][2])
-{
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        N[i] = l[i] * (2.0 * l[i] - 1.0);
-        g[i][0] = (4.0 * l[i] - 1.0) * gl[i][0];
-        g[i][1] = (4.0 * l[i] - 1.0) * gl[i][1];
-    }
-    const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        const int p = ep[e][0], q = ep[e][1];
-        N[3 + e] = 4.0 * l[p] * l[q];
-        g[3 + e][0] = 4.0 * (gl[p][0] * l[q] + l[p] * gl[q][0]);
-        g[3 + e][1] = 4.0 * (gl[p][1] * l[q] + l[p] * gl[q][1]);
-    }
-}
-
-__device__ __forceinline__ void tri6_point(int q, double (&l)[3], double &w)
-{
-    const double a = q < 3 ? T6A1 : T6A2;
-    const double b = 1.0 - 2.0 * a;
-    const int k = q % 3;
-    l[0] = (k == 0) ? b : a;
-    l[1] = (k == 1) ? b : a;
-    l[2] = (k == 2) ? b : a;
-    w = 0.5 * (q < 3 ? T6W1 : T6W2);  // reference triangle area 1/2
-}
-
-__device__ __forceinline__ int upair(int a, int b) { return a * (15 - a) / 2 + b; }  // a <= b < 8
 
 // ---------------------------------------------------------------------------
 // element kernels
@@ -131,62 +28,14 @@ __global__ void k_elem_thermal_p1(int64_t n_el, const double *__restrict__ X, co
                                   const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_el) return;
-    const double k = kc[e];
-    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
-    double gl[3][2];
-    const double det = tri_affine(X, conn + 3 * e, gl);
-    // the integrand is constant: the 3 point weights sum to 1/2
-    const double s = 0.5 * det * k;
-    double *o = out + e * 12;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) o[3 * a + b] = s * (gl[a][0] * gl[b][0] + gl[a][1] * gl[b][1]);
-    // 3-point rule: sum_q w_q lambda_a(q) = 1/6
-    const double l = det * f * (1.0 / 6.0);
-    o[9] = l;
-    o[10] = l;
-    o[11] = l;
+    if (e < n_el) elem_thermal_p1(e, X, conn, kc, f, out, status);
 }
 
 __global__ void k_elem_thermal_p2(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
                                   const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_el) return;
-    const double k = kc[e];
-    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
-    double gl[3][2];
-    const double det = tri_affine(X, conn + 6 * e, gl);
-    double Ke[21] = {}, de[6] = {};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        // degree-2 interior rule: (2/3, 1/6, 1/6) and permutations, weight 1/6
-        double l[3] = {1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
-        l[q] = 2.0 / 3.0;
-        double N[6], g[6][2];
-        p2_basis(l, gl, N, g);
-        const double wd = det * (1.0 / 6.0);
-        int t = 0;
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-#pragma unroll
-            for (int b = a; b < 6; ++b, ++t) Ke[t] = fma(wd, g[a][0] * g[b][0] + g[a][1] * g[b][1], Ke[t]);
-            de[a] = fma(wd, N[a], de[a]);
-        }
-    }
-    double *o = out + e * 42;
-    int t = 0;
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = a; b < 6; ++b, ++t) {
-            o[6 * a + b] = k * Ke[t];
-            o[6 * b + a] = k * Ke[t];
-        }
-#pragma unroll
-    for (int a = 0; a < 6; ++a) o[36 + a] = f * de[a];
+    if (e < n_el) elem_thermal_p2(e, X, conn, kc, f, out, status);
 }
 
 __global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const double *__restrict__ X,
@@ -195,45 +44,7 @@ __global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const dou
                                                          double *__restrict__ out, int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_el) return;
-    const double k = kc[e];
-    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
-    double x[8][3];
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
-    double Ke[36] = {}, m[8] = {};
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        double Ji[3][3];
-        const double wd = q1_jac(x, q, Ji);  // Gauss weights are 1
-        double g[8][3];
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-                g[a][i] = q1_dref(q, a, 0) * Ji[0][i] + q1_dref(q, a, 1) * Ji[1][i] + q1_dref(q, a, 2) * Ji[2][i];
-        int t = 0;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const double ga0 = wd * g[a][0], ga1 = wd * g[a][1], ga2 = wd * g[a][2];
-#pragma unroll
-            for (int b = a; b < 8; ++b, ++t) Ke[t] = fma(ga0, g[b][0], fma(ga1, g[b][1], fma(ga2, g[b][2], Ke[t])));
-            m[a] = fma(wd, q1_n(q, a), m[a]);
-        }
-    }
-    double *o = out + e * 72;
-    int t = 0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = a; b < 8; ++b, ++t) {
-            o[8 * a + b] = k * Ke[t];
-            o[8 * b + a] = k * Ke[t];
-        }
-#pragma unroll
-    for (int a = 0; a < 8; ++a) o[64 + a] = f * m[a];
+    if (e < n_el) elem_thermal_q1(e, X, conn, kc, f, out, status);
 }
 
 // Q1 elasticity, one element per thread.  The scaled gradients
@@ -390,82 +201,9 @@ __global__ void __launch_bounds__(256) k_gather(int64_t n_nodes, const int64_t *
                                                 const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
                                                 double *__restrict__ values, double *__restrict__ d)
 {
-    const int lane = threadIdx.x & 31;
     const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (n >= n_nodes) return;
-    const int64_t p0 = ptr[n], deg = ptr[n + 1] - p0;
-    bool rm[BS];
-    double lift[BS], dsum[BS];
-    int64_t rbase[BS];
-#pragma unroll
-    for (int c = 0; c < BS; ++c) {
-        rm[c] = mask ? mask[BS * n + c] != 0 : false;
-        lift[c] = 0.0;
-        dsum[c] = 0.0;
-        rbase[c] = row_ptr[BS * n + c];
-    }
-    for (int64_t k = lane; k < deg; k += 32) {
-        const int64_t p = p0 + k;
-        const int32_t mnode = col[p];
-        double acc[BS][BS];
-#pragma unroll
-        for (int c = 0; c < BS; ++c)
-#pragma unroll
-            for (int cp = 0; cp < BS; ++cp) acc[c][cp] = 0.0;
-        for (int64_t t = cptr[p]; t < cptr[p + 1]; ++t) {
-            const int32_t v = clist[t];
-            const int64_t e = v >> 6;
-            const int a = (v >> 3) & 7, b = v & 7;
-            const double *s = sc + e * stride;
-            if (BS == 1) {
-                acc[0][0] += s[a * npe + b];
-                if (mnode == n) dsum[0] += s[npe * npe + a];
-            } else {
-                if (a <= b) {
-                    const double *blk = s + upair(a, b) * 9;
-#pragma unroll
-                    for (int c = 0; c < BS; ++c)
-#pragma unroll
-                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * c + cp];
-                } else {
-                    const double *blk = s + upair(b, a) * 9;
-#pragma unroll
-                    for (int c = 0; c < BS; ++c)
-#pragma unroll
-                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * cp + c];
-                }
-                if (mnode == n)
-#pragma unroll
-                    for (int c = 0; c < BS; ++c) dsum[c] += s[324 + 3 * a + c];
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < BS; ++c)
-#pragma unroll
-            for (int cp = 0; cp < BS; ++cp) {
-                double v = acc[c][cp];
-                if (mask) {
-                    const int64_t r = BS * n + c, sdof = BS * (int64_t)mnode + cp;
-                    if (rm[c]) {
-                        v = (r == sdof) ? 1.0 : 0.0;
-                    } else if (mask[sdof]) {
-                        lift[c] -= v * bval[sdof];
-                        v = 0.0;
-                    }
-                }
-                values[rbase[c] + BS * k + cp] = v;
-            }
-    }
-#pragma unroll
-    for (int c = 0; c < BS; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lift[c] += __shfl_xor_sync(0xffffffffu, lift[c], o);
-            dsum[c] += __shfl_xor_sync(0xffffffffu, dsum[c], o);
-        }
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < BS; ++c) d[BS * n + c] = rm[c] ? bval[BS * n + c] : dsum[c] + lift[c];
+    if (n >= n_nodes) return;  // warp-uniform
+    gather_node<BS>(n, threadIdx.x & 31, ptr, col, cptr, clist, sc, stride, npe, mask, bval, row_ptr, values, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,7 +249,7 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
     int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const int32_t *__restrict__ conn,
     const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
-    const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+    int fp, int fq, const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
     double *__restrict__ values, double *__restrict__ d)
 {
     __shared__ T acc_all[GEL_WARPS][MF_MAX_DEG * 9];
@@ -519,26 +257,68 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
     const int64_t n = (int64_t)blockIdx.x * GEL_WARPS + w;
     if (n >= n_nodes) return;  // warp-uniform
     T *acc = acc_all[w];
+    constexpr bool fixed = sizeof(T) == 8 && T(0.5) == T(0);  // integer accumulator
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
     for (int i = lane; i < 9 * deg; i += 32) acc[i] = T(0);
     double dsum = 0.0;  // lane c < 3: load of component c
     __syncwarp();
-    for (int64_t t = inc_ptr[n]; t < inc_ptr[n + 1]; ++t) {
-        const int64_t e = inc[t];
-        const int32_t cn = lane < 8 ? conn[e * 8 + lane] : -1;
-        const unsigned hit = __ballot_sync(0xffffffffu, cn == (int32_t)n);
-        if (hit == 0u) continue;  // cannot happen: incidence lists come from conn
-        const int a = __ffs(hit) - 1;
-        const T *blk = reinterpret_cast<const T *>(sc + e * stride);
-        for (int idx = lane; idx < 72; idx += 32) {
-            const int b = idx / 9, cc = idx - 9 * b;
-            const int c = cc / 3, cp = cc - 3 * c;
-            const T v = (a <= b) ? blk[upair(a, b) * 9 + cc] : blk[upair(b, a) * 9 + 3 * cp + c];
-            const int k = slot[e * 64 + a * 8 + b];
-            acc[k * 9 + cc] += v;
+    const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
+    // incident elements in chunks of 8: element ids and the local index of n
+    // are fetched by lanes 0..7 at once, then the values
+    for (int64_t cb = i0; cb < i1; cb += 8) {
+        const int cnt = (int)min((int64_t)8, i1 - cb);
+        int64_t my_e = 0;
+        int my_a = 0;
+        if (lane < cnt) {
+            my_e = inc[cb + lane];
+            const int32_t *ce = conn + my_e * 8;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (ce[k] == (int32_t)n) my_a = k;
         }
-        if (lane < 3) dsum += sc[e * stride + 324 + 3 * a + lane];
+        if constexpr (fixed) {
+            // exact integer sums: order is irrelevant, so every value of the
+            // chunk streams through shared-memory integer atomics
+            const int items = cnt * 72;
+#pragma unroll 4
+            for (int it = 0; it < (items + 31) / 32; ++it) {  // warp-uniform trip count
+                const int item = lane + 32 * it;
+                const bool act = item < items;
+                const int j = act ? item / 72 : 0;
+                const int64_t e = __shfl_sync(0xffffffffu, my_e, j);
+                const int a = __shfl_sync(0xffffffffu, my_a, j);
+                if (act) {
+                    const int idx = item - 72 * j;
+                    const int b = idx / 9, cc = idx - 9 * b;
+                    const int c = cc / 3, cp = cc - 3 * c;
+                    const T *blk = reinterpret_cast<const T *>(sc + e * stride);
+                    const T v = (a <= b) ? blk[upair(a, b) * 9 + cc] : blk[upair(b, a) * 9 + 3 * cp + c];
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc[slot[e * 64 + a * 8 + b] * 9 + cc]),
+                              (unsigned long long)v);
+                }
+            }
+            for (int j = 0; j < cnt; ++j) {
+                const int64_t e = __shfl_sync(0xffffffffu, my_e, j);
+                const int a = __shfl_sync(0xffffffffu, my_a, j);
+                if (lane < 3) dsum += sc[e * stride + 324 + 3 * a + lane];
+            }
+        } else {
+            // FP64 sums in ascending element order (bit-reproducible)
+            for (int j = 0; j < cnt; ++j) {
+                const int64_t e = __shfl_sync(0xffffffffu, my_e, j);
+                const int a = __shfl_sync(0xffffffffu, my_a, j);
+                const T *blk = reinterpret_cast<const T *>(sc + e * stride);
+                for (int idx = lane; idx < 72; idx += 32) {
+                    const int b = idx / 9, cc = idx - 9 * b;
+                    const int c = cc / 3, cp = cc - 3 * c;
+                    const T v = (a <= b) ? blk[upair(a, b) * 9 + cc] : blk[upair(b, a) * 9 + 3 * cp + c];
+                    acc[slot[e * 64 + a * 8 + b] * 9 + cc] += v;
+                }
+                if (lane < 3) dsum += sc[e * stride + 324 + 3 * a + lane];
+                __syncwarp();
+            }
+        }
         __syncwarp();
     }
     const int S = scale ? *scale : 0;
@@ -550,7 +330,12 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
         double lift = 0.0;
         for (int j = lane; j < 3 * deg; j += 32) {
             const int k = j / 3, cp = j - 3 * k;
-            double v = to_double<T>(acc[k * 9 + 3 * c + cp], S);
+            T kv = acc[k * 9 + 3 * c + cp];
+            if (fq) {  // fixed-point path: K = p A + q A^T + q I tr(A) per node-pair block
+                kv = (T)fp * kv + (T)fq * acc[k * 9 + 3 * cp + c];
+                if (c == cp) kv += (T)fq * (acc[k * 9] + acc[k * 9 + 4] + acc[k * 9 + 8]);
+            }
+            double v = to_double<T>(kv, S);
             if (mask) {
                 const int64_t sdof = 3 * (int64_t)adj_col[p0 + k] + cp;
                 if (rm) v = (r == sdof) ? 1.0 : 0.0;
@@ -675,19 +460,19 @@ __global__ void k_flow_precond(int64_t n2, int64_t n_rows, const int64_t *__rest
 
 }  // namespace
 
-void mf_launch_gather_elastic(bool fixed_point, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
-                              double *values, double *d, cudaStream_t st)
+void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, const mf_mesh *m, const mf_pattern *p,
+                              const mf_coeffs *c, double *values, double *d, cudaStream_t st)
 {
     const mf_adj &A = p->adj[0];
     const unsigned grid = nblk(m->n_nodes, GEL_WARPS);
     if (fixed_point)
         k_gather_el<long long><<<grid, GEL_WARPS * 32, 0, st>>>(
             m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride,
-            static_cast<const int *>(p->mixed_state), c->bc_mask, c->bc_val, p->row_ptr, values, d);
+            static_cast<const int *>(p->mixed_state), fp, fq, c->bc_mask, c->bc_val, p->row_ptr, values, d);
     else
         k_gather_el<double><<<grid, GEL_WARPS * 32, 0, st>>>(
             m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride, nullptr,
-            c->bc_mask, c->bc_val, p->row_ptr, values, d);
+            0, 0, c->bc_mask, c->bc_val, p->row_ptr, values, d);
 }
 
 mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,
@@ -738,7 +523,7 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         mf_prof_begin("gather_elastic", st);
-        mf_launch_gather_elastic(false, m, p, c, values, d, st);
+        mf_launch_gather_elastic(false, 0, 0, m, p, c, values, d, st);
         mf_prof_end(st);
     } else {
         mf_prof_begin("elem_oseen", st);

@@ -1,0 +1,345 @@
+// Batched assembly: many thermal problems of uneven size and mixed element
+// order (P1, P2 triangles, Q1 hexahedra) assembled by persistent launches over
+// (problem, tile) descriptors, replayed from a CUDA graph, with tile shapes
+// picked by a measuring autotuner (results cached in a small JSON file).
+//
+// Every element and every CSR row is computed by the same device routines as
+// the single-problem path (mf_fem.cuh), in the same order, so each problem's
+// K and d are bitwise equal to mf_assemble's.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mf_fem.cuh"
+
+struct BatchProblem {
+    int elem, npe;
+    int64_t n_el, n_nodes;
+    const double *X;
+    const int32_t *conn;
+    const double *kc;
+    double f;
+    double *scratch;
+    int64_t stride;
+    const int64_t *ptr;
+    const int32_t *col;
+    const int64_t *cptr;
+    const int32_t *clist;
+    const uint8_t *mask;
+    const double *bval;
+    const int64_t *row_ptr;
+    double *values;
+    double *d;
+};
+
+struct BatchTile {
+    int32_t prob;
+    int32_t type;
+    int64_t first;
+    int64_t count;
+};
+
+struct mf_batch {
+    int n = 0;
+    std::vector<BatchProblem> host;
+    BatchProblem *dev = nullptr;
+    mf_batch_tiling tiling{};
+    BatchTile *etiles = nullptr, *ntiles = nullptr;
+    int n_etiles = 0, n_ntiles = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int sm_count = 0;
+    std::string signature;
+};
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_batch_elem(const BatchProblem *__restrict__ P,
+                                                    const BatchTile *__restrict__ tiles, int n_tiles, int *status)
+{
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const BatchTile T = tiles[t];
+        const BatchProblem &p = P[T.prob];
+        for (int64_t i = threadIdx.x; i < T.count; i += blockDim.x) {
+            const int64_t e = T.first + i;
+            if (T.type == MF_P1_TRI) elem_thermal_p1(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
+            else if (T.type == MF_P2_TRI) elem_thermal_p2(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
+            else elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_gather(const BatchProblem *__restrict__ P,
+                                                      const BatchTile *__restrict__ tiles, int n_tiles)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const BatchTile T = tiles[t];
+        const BatchProblem &p = P[T.prob];
+        for (int64_t i = warp; i < T.count; i += nw)  // warp-uniform
+            gather_node<1>(T.first + i, lane, p.ptr, p.col, p.cptr, p.clist, p.scratch, p.stride, p.npe, p.mask,
+                           p.bval, p.row_ptr, p.values, p.d);
+    }
+}
+
+void free_tiles(mf_batch *b)
+{
+    cudaFree(b->etiles);
+    cudaFree(b->ntiles);
+    b->etiles = b->ntiles = nullptr;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// element tiles sorted by element type (P1, P2, Q1), node tiles in problem order
+mf_status make_tiles(mf_batch *b, const mf_batch_tiling &t)
+{
+    std::vector<BatchTile> et, nt;
+    for (int type = MF_P1_TRI; type <= MF_Q1_HEX; ++type)
+        for (int i = 0; i < b->n; ++i) {
+            const BatchProblem &p = b->host[i];
+            if (p.elem != type) continue;
+            for (int64_t s = 0; s < p.n_el; s += t.elem_tile)
+                et.push_back(BatchTile{i, type, s, std::min<int64_t>(t.elem_tile, p.n_el - s)});
+        }
+    for (int i = 0; i < b->n; ++i) {
+        const BatchProblem &p = b->host[i];
+        for (int64_t s = 0; s < p.n_nodes; s += t.node_tile)
+            nt.push_back(BatchTile{i, p.elem, s, std::min<int64_t>(t.node_tile, p.n_nodes - s)});
+    }
+    free_tiles(b);
+    MF_CUDA(cudaMalloc(&b->etiles, sizeof(BatchTile) * et.size()));
+    MF_CUDA(cudaMalloc(&b->ntiles, sizeof(BatchTile) * nt.size()));
+    MF_CUDA(cudaMemcpy(b->etiles, et.data(), sizeof(BatchTile) * et.size(), cudaMemcpyHostToDevice));
+    MF_CUDA(cudaMemcpy(b->ntiles, nt.data(), sizeof(BatchTile) * nt.size(), cudaMemcpyHostToDevice));
+    b->n_etiles = (int)et.size();
+    b->n_ntiles = (int)nt.size();
+    b->tiling = t;
+    return MF_OK;
+}
+
+void launch_batch(mf_batch *b, cudaStream_t st, int *status)
+{
+    const mf_batch_tiling &t = b->tiling;
+    const int cap = b->sm_count * t.grid_per_sm;
+    k_batch_elem<<<std::max(1, std::min(b->n_etiles, cap)), t.elem_block, 0, st>>>(b->dev, b->etiles, b->n_etiles,
+                                                                                      status);
+    k_batch_gather<<<std::max(1, std::min(b->n_ntiles, cap)), 256, 0, st>>>(b->dev, b->ntiles, b->n_ntiles);
+}
+
+mf_status capture(mf_batch *b, int *status)
+{
+    cudaStream_t cs;
+    MF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        launch_batch(b, cs, status);
+        e = cudaStreamEndCapture(cs, &b->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return mf_cuda_check(e, "mf_batch: graph capture");
+    return MF_OK;
+}
+
+// tiny flat JSON cache: {"<signature>": [elem_tile, elem_block, node_tile, grid_per_sm], ...}
+bool cache_lookup(const char *path, const std::string &sig, mf_batch_tiling *t)
+{
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    std::string s;
+    char buf[4096];
+    size_t k;
+    while ((k = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, k);
+    fclose(f);
+    const std::string key = "\"" + sig + "\"";
+    const size_t pos = s.find(key);
+    if (pos == std::string::npos) return false;
+    const size_t br = s.find('[', pos);
+    if (br == std::string::npos) return false;
+    int v[4];
+    if (sscanf(s.c_str() + br, "[%d, %d, %d, %d]", &v[0], &v[1], &v[2], &v[3]) != 4) return false;
+    if (v[0] <= 0 || v[1] <= 0 || v[1] % 32 || v[1] > 1024 || v[2] <= 0 || v[3] <= 0) return false;
+    *t = mf_batch_tiling{v[0], v[1], v[2], v[3]};
+    return true;
+}
+
+void cache_store(const char *path, const std::string &sig, const mf_batch_tiling &t)
+{
+    if (!path) return;
+    std::string s;
+    if (FILE *f = fopen(path, "r")) {
+        char buf[4096];
+        size_t k;
+        while ((k = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, k);
+        fclose(f);
+    }
+    char entry[512];
+    snprintf(entry, sizeof entry, "\"%s\": [%d, %d, %d, %d]", sig.c_str(), t.elem_tile, t.elem_block, t.node_tile,
+             t.grid_per_sm);
+    const size_t a = s.find('{'), z = s.rfind('}');
+    std::string body = (a != std::string::npos && z != std::string::npos && z > a) ? s.substr(a + 1, z - a - 1) : "";
+    // drop an older entry of the same signature
+    const std::string key = "\"" + sig + "\"";
+    size_t p = body.find(key);
+    if (p != std::string::npos) {
+        size_t e = body.find(']', p);
+        size_t from = p;
+        while (from > 0 && (body[from - 1] == ' ' || body[from - 1] == ',' || body[from - 1] == '\n')) --from;
+        body.erase(from, e + 1 - from);
+    }
+    while (!body.empty() && (body[0] == ',' || body[0] == '\n' || body[0] == ' ')) body.erase(0, 1);
+    std::string out = "{\n";
+    if (!body.empty()) out += body + ",\n";
+    out += entry;
+    out += "\n}\n";
+    if (FILE *f = fopen(path, "w")) {
+        fputs(out.c_str(), f);
+        fclose(f);
+    }
+}
+
+}  // namespace
+
+extern "C" mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, const mf_pattern *const *patterns,
+                                     const mf_coeffs *coeffs, double *const *values, double *const *d, mf_batch **out)
+{
+    if (!out || n <= 0 || !meshes || !patterns || !coeffs || !values || !d)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_batch_create: NULL argument or empty batch");
+    *out = nullptr;
+    mf_batch *b = new (std::nothrow) mf_batch();
+    if (!b) return mf_fail(MF_ERR_OOM, "mf_batch_create: host allocation");
+    b->n = n;
+    long long cnt[3] = {0, 0, 0}, nodes = 0;
+    for (int i = 0; i < n; ++i) {
+        const mf_mesh *m = meshes[i];
+        const mf_pattern *p = patterns[i];
+        const mf_coeffs &c = coeffs[i];
+        if (!m || !p || p->mesh != m || p->form != MF_FORM_THERMAL || !c.elem_coef || !values[i] || !d[i] ||
+            (c.bc_mask == nullptr) != (c.bc_val == nullptr)) {
+            delete b;
+            return mf_fail(MF_ERR_INVALID_ARG, "mf_batch_create: problem %d is not a thermal mesh/pattern/coeffs", i);
+        }
+        const mf_adj &A = p->adj[0];
+        b->host.push_back(BatchProblem{m->elem, m->npe, m->n_elems, m->n_nodes, m->coords, m->conn, c.elem_coef,
+                                       c.source[0], p->scratch, p->scratch_stride, A.ptr, A.col, A.cptr, A.clist,
+                                       c.bc_mask, c.bc_val, p->row_ptr, values[i], d[i]});
+        cnt[m->elem] += m->n_elems;
+        nodes += m->n_nodes;
+    }
+    char sig[256];
+    snprintf(sig, sizeof sig, "n%d_p1_%lld_p2_%lld_q1_%lld_nodes_%lld", n, cnt[0], cnt[1], cnt[2], nodes);
+    b->signature = sig;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMalloc(&b->dev, sizeof(BatchProblem) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(b->dev, b->host.data(), sizeof(BatchProblem) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->dev);
+        delete b;
+        return mf_cuda_check(e, "mf_batch_create");
+    }
+    mf_status s = make_tiles(b, mf_batch_tiling{1024, 128, 256, 8});
+    if (s != MF_OK) {
+        mf_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_batch_set_tiling(mf_batch *b, const mf_batch_tiling *t)
+{
+    if (!b || !t || t->elem_tile <= 0 || t->elem_block <= 0 || t->elem_block % 32 || t->elem_block > 256 ||
+        t->node_tile <= 0 || t->grid_per_sm <= 0)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_batch_set_tiling: bad tiling");
+    return make_tiles(b, *t);
+}
+
+extern "C" mf_status mf_batch_get_tiling(const mf_batch *b, mf_batch_tiling *t)
+{
+    if (!b || !t) return mf_fail(MF_ERR_INVALID_ARG, "mf_batch_get_tiling: NULL argument");
+    *t = b->tiling;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_batch_assemble(mf_batch *b, void *stream)
+{
+    if (!b) return mf_fail(MF_ERR_INVALID_ARG, "mf_batch_assemble: NULL batch");
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_batch_assemble: status word unavailable");
+    if (!b->exec) {
+        mf_status s = capture(b, status);
+        if (s != MF_OK) return s;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mf_prof_begin("batch_graph", st);
+    MF_CUDA(cudaGraphLaunch(b->exec, st));
+    mf_prof_end(st);
+    return MF_OK;
+}
+
+extern "C" mf_status mf_batch_autotune(mf_batch *b, const char *cache_path, void *stream, mf_batch_tiling *chosen)
+{
+    if (!b) return mf_fail(MF_ERR_INVALID_ARG, "mf_batch_autotune: NULL batch");
+    mf_batch_tiling best{};
+    if (cache_lookup(cache_path, b->signature, &best)) {
+        mf_status s = make_tiles(b, best);
+        if (s == MF_OK && chosen) *chosen = best;
+        return s;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    MF_CUDA(cudaEventCreate(&e0));
+    MF_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    const int etile[] = {256, 1024, 4096};
+    const int eblock[] = {128, 256};
+    const int ntile[] = {64, 512};
+    const int gps[] = {4, 16};
+    for (int a : etile)
+        for (int bb : eblock)
+            for (int c : ntile)
+                for (int g : gps) {
+                    mf_status s = make_tiles(b, mf_batch_tiling{a, bb, c, g});
+                    if (s == MF_OK) s = mf_batch_assemble(b, stream);  // warm-up, captures the graph
+                    if (s != MF_OK) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return s;
+                    }
+                    MF_CUDA(cudaEventRecord(e0, st));
+                    for (int r = 0; r < 3; ++r) MF_CUDA(cudaGraphLaunch(b->exec, st));
+                    MF_CUDA(cudaEventRecord(e1, st));
+                    MF_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = b->tiling;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mf_status s = make_tiles(b, best);
+    if (s != MF_OK) return s;
+    cache_store(cache_path, b->signature, best);
+    if (chosen) *chosen = best;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_batch_destroy(mf_batch *b)
+{
+    if (!b) return MF_OK;
+    free_tiles(b);
+    cudaFree(b->dev);
+    delete b;
+    return MF_OK;
+}

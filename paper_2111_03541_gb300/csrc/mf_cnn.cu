@@ -1,0 +1,768 @@
+// Learned preconditioner correction: a small 3D CNN on the node grid of a
+// structured Q1 thermal problem, trained on the GPU by these kernels and used
+// inside flexible CG (growth line of the hot path; the paper has none).
+//
+// Network: 4 layers of 3x3x3 convolutions, 2 -> 16 -> 16 -> 16 -> 1 channels,
+// ReLU after the first three, zero padding at the grid boundary.  Weights and
+// activations are BF16, every sum accumulates in FP32; the trainer keeps FP32
+// master weights and AdamW moments.  Layout: channels last, node v of a batch
+// grid b at (b * nv + v) * C + c, v = (z * ny + y) * nx + x.
+//
+// Preconditioner (per FCG iteration):
+//   z = D^-1 r + s (1 - mask) CNN(r / s, log k_nodal),  s = max |r|,
+// with the Jacobi step z = D^-1 r whenever z . r <= 0 or z is not finite.
+// Training loss over a batch of residuals r_b of systems K_b:
+//   L = (1/B) sum_b || K_b z_b - r_b ||^2 / || r_b ||^2.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "mf_internal.h"
+
+namespace {
+
+constexpr int NL = 4;
+constexpr int CIN[NL] = {2, 16, 16, 16};
+constexpr int COUT[NL] = {16, 16, 16, 1};
+
+int w_count(int l) { return COUT[l] * CIN[l] * 27; }
+int p_offset_w(int l)
+{
+    int o = 0;
+    for (int i = 0; i < l; ++i) o += w_count(i) + COUT[i];
+    return o;
+}
+int p_offset_b(int l) { return p_offset_w(l) + w_count(l); }
+int p_total() { return p_offset_b(NL - 1) + COUT[NL - 1]; }
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ __forceinline__ bool nb_index(int v, int o, int nz, int ny, int nx, int &u)
+{
+    const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+    const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) return false;
+    u = (zz * ny + yy) * nx + xx;
+    return true;
+}
+
+// forward: one thread per output node, all output channels; weights in smem
+template <int CI, int CO, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(128) k_conv_fwd(int B, int nz, int ny, int nx, const __nv_bfloat16 *__restrict__ in,
+                                                  const __nv_bfloat16 *__restrict__ w, const float *__restrict__ bias,
+                                                  void *__restrict__ out)
+{
+    __shared__ float sw[CO * CI * 27];
+    for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) sw[i] = __bfloat162float(w[i]);
+    __syncthreads();
+    const int nv = nz * ny * nx;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (int64_t)B * nv) return;
+    const int b = (int)(g / nv), v = (int)(g % nv);
+    float acc[CO];
+#pragma unroll
+    for (int co = 0; co < CO; ++co) acc[co] = bias[co];
+    const __nv_bfloat16 *base = in + (int64_t)b * nv * CI;
+#pragma unroll 1
+    for (int o = 0; o < 27; ++o) {
+        int u;
+        if (!nb_index(v, o, nz, ny, nx, u)) continue;
+        float xv[CI];
+#pragma unroll
+        for (int ci = 0; ci < CI; ++ci) xv[ci] = __bfloat162float(base[(int64_t)u * CI + ci]);
+#pragma unroll
+        for (int co = 0; co < CO; ++co)
+#pragma unroll
+            for (int ci = 0; ci < CI; ++ci) acc[co] = fmaf(sw[(co * CI + ci) * 27 + o], xv[ci], acc[co]);
+    }
+    if (OUT_F32) {
+        float *o = static_cast<float *>(out) + g * CO;
+#pragma unroll
+        for (int co = 0; co < CO; ++co) o[co] = RELU ? fmaxf(acc[co], 0.f) : acc[co];
+    } else {
+        __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + g * CO;
+#pragma unroll
+        for (int co = 0; co < CO; ++co) o[co] = __float2bfloat16_rn(RELU ? fmaxf(acc[co], 0.f) : acc[co]);
+    }
+}
+
+// gradient wrt the input: gin[u][ci] = sum_{o, co} w[co][ci][o] gout[u - off(o)][co],
+// where gout is masked by the ReLU of that layer's output (act > 0) when act != NULL
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) k_conv_bwd_data(int B, int nz, int ny, int nx, const float *__restrict__ gout,
+                                                       const __nv_bfloat16 *__restrict__ act,
+                                                       const __nv_bfloat16 *__restrict__ w, float *__restrict__ gin)
+{
+    __shared__ float sw[CO * CI * 27];
+    for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) sw[i] = __bfloat162float(w[i]);
+    __syncthreads();
+    const int nv = nz * ny * nx;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (int64_t)B * nv) return;
+    const int b = (int)(g / nv), u = (int)(g % nv);
+    float acc[CI];
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci) acc[ci] = 0.f;
+#pragma unroll 1
+    for (int o = 0; o < 27; ++o) {
+        int v;
+        if (!nb_index(u, 26 - o, nz, ny, nx, v)) continue;  // v = u - off(o)
+        const int64_t vi = (int64_t)b * nv + v;
+        float gv[CO];
+#pragma unroll
+        for (int co = 0; co < CO; ++co) {
+            gv[co] = gout[vi * CO + co];
+            if (act && !(__bfloat162float(act[vi * CO + co]) > 0.f)) gv[co] = 0.f;
+        }
+#pragma unroll
+        for (int ci = 0; ci < CI; ++ci)
+#pragma unroll
+            for (int co = 0; co < CO; ++co) acc[ci] = fmaf(sw[(co * CI + ci) * 27 + o], gv[co], acc[ci]);
+    }
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci) gin[g * CI + ci] = acc[ci];
+}
+
+// gradient wrt the weights: per block a chunk of nodes, one thread per
+// (co, ci) pair with 27 accumulators; partial sums per block, reduced in order
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) k_conv_bwd_weight(int B, int nz, int ny, int nx, int chunk,
+                                                         const __nv_bfloat16 *__restrict__ in,
+                                                         const float *__restrict__ gout,
+                                                         const __nv_bfloat16 *__restrict__ act,
+                                                         float *__restrict__ part)
+{
+    const int nv = nz * ny * nx;
+    const int64_t total = (int64_t)B * nv;
+    const int pair = threadIdx.x;
+    const bool active = pair < CO * CI;
+    const int co = active ? pair / CI : 0, ci = active ? pair % CI : 0;
+    float acc[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) acc[o] = 0.f;
+    float accb = 0.f;
+    const int64_t g0 = (int64_t)blockIdx.x * chunk, g1 = min(total, g0 + chunk);
+    if (active)
+        for (int64_t g = g0; g < g1; ++g) {
+            float gv = gout[g * CO + co];
+            if (act && !(__bfloat162float(act[g * CO + co]) > 0.f)) gv = 0.f;
+            if (gv == 0.f) continue;
+            if (ci == 0) accb += gv;
+            const int b = (int)(g / nv), v = (int)(g % nv);
+            const __nv_bfloat16 *base = in + (int64_t)b * nv * CI;
+#pragma unroll
+            for (int o = 0; o < 27; ++o) {
+                int u;
+                if (nb_index(v, o, nz, ny, nx, u)) acc[o] = fmaf(gv, __bfloat162float(base[(int64_t)u * CI + ci]), acc[o]);
+            }
+        }
+    const int nw = CO * CI * 27;
+    float *pb = part + (int64_t)blockIdx.x * (nw + CO);
+    if (active) {
+#pragma unroll
+        for (int o = 0; o < 27; ++o) pb[(co * CI + ci) * 27 + o] = acc[o];
+        if (ci == 0) pb[nw + co] = accb;
+    }
+}
+
+__global__ void k_reduce_part(int nblocks, int n, const float *__restrict__ part, float *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * n + i];
+    out[i] = s;
+}
+
+__global__ void k_adamw(int n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                        float *__restrict__ v, float lr, float b1, float b2, float eps, float wd, float c1, float c2,
+                        const int *__restrict__ is_weight, __nv_bfloat16 *__restrict__ pbf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float pi = p[i];
+    if (is_weight[i]) pi -= lr * wd * pi;
+    pi -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pbf[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void k_to_bf16(int n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// ---- preconditioner pieces (FP64 vectors of the Krylov solve) ----
+
+// log k at the nodes: mean of log k over the cells touching each node; the
+// cells form an (nz-1) x (ny-1) x (nx-1) grid
+__global__ void k_node_logk(int nz, int ny, int nx, const double *__restrict__ kcell, float *__restrict__ out)
+{
+    const int nv = nz * ny * nx;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+    double s = 0.0;
+    int c = 0;
+    for (int dz = -1; dz <= 0; ++dz)
+        for (int dy = -1; dy <= 0; ++dy)
+            for (int dx = -1; dx <= 0; ++dx) {
+                const int cz = z + dz, cy = y + dy, cx = x + dx;
+                if (cz < 0 || cz >= nz - 1 || cy < 0 || cy >= ny - 1 || cx < 0 || cx >= nx - 1) continue;
+                s += log(kcell[((int64_t)cz * (ny - 1) + cy) * (nx - 1) + cx]);
+                ++c;
+            }
+    out[v] = c ? (float)(s / c) : 0.f;
+}
+
+// network input [nv][2] = (r / s, log k / 2) in BF16
+__global__ void k_cnn_input(int64_t n, const double *__restrict__ r, const double *__restrict__ s_inv,
+                            const float *__restrict__ logk, __nv_bfloat16 *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[2 * i] = __float2bfloat16_rn((float)(r[i] * *s_inv));
+    x[2 * i + 1] = __float2bfloat16_rn(0.5f * logk[i]);
+}
+
+constexpr int RB = 256, RG = 512;  // reduction block and fixed grid
+
+__device__ double block_sum_d(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;
+}
+
+// partial dot products (a.b) of up to 3 pairs, per block
+__global__ void __launch_bounds__(RB) k_dots(int64_t n, const double *a0, const double *b0, const double *a1,
+                                             const double *b1, const double *a2, const double *b2,
+                                             double *__restrict__ part)
+{
+    __shared__ double sh[RB / 32];
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (a0) s0 = fma(a0[i], b0[i], s0);
+        if (a1) s1 = fma(a1[i], b1[i], s1);
+        if (a2) s2 = fma(a2[i], b2[i], s2);
+    }
+    s0 = block_sum_d(s0, sh);
+    s1 = block_sum_d(s1, sh);
+    s2 = block_sum_d(s2, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = s0;
+        part[3 * blockIdx.x + 1] = s1;
+        part[3 * blockIdx.x + 2] = s2;
+    }
+}
+
+__global__ void __launch_bounds__(RB) k_absmax(int64_t n, const double *__restrict__ a, double *__restrict__ part)
+{
+    __shared__ double sh[RB / 32];
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(a[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = fmax(s, sh[i]);
+        part[blockIdx.x] = s;
+    }
+}
+
+// host helpers: finish reductions on the host (few hundred doubles)
+struct Reducer {
+    double *part = nullptr;
+    std::vector<double> h;
+    cudaStream_t st;
+    cudaError_t init(cudaStream_t s)
+    {
+        st = s;
+        h.resize(3 * RG);
+        return cudaMallocAsync(&part, sizeof(double) * 3 * RG, s);
+    }
+    ~Reducer()
+    {
+        if (part) cudaFreeAsync(part, st);
+    }
+    cudaError_t dots(int64_t n, const double *a0, const double *b0, const double *a1, const double *b1,
+                     const double *a2, const double *b2, double out[3])
+    {
+        k_dots<<<RG, RB, 0, st>>>(n, a0, b0, a1, b1, a2, b2, part);
+        cudaError_t e = cudaMemcpyAsync(h.data(), part, sizeof(double) * 3 * RG, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        out[0] = out[1] = out[2] = 0.0;
+        for (int b = 0; b < RG; ++b)
+            for (int k = 0; k < 3; ++k) out[k] += h[3 * b + k];
+        return e;
+    }
+    cudaError_t absmax(int64_t n, const double *a, double *out)
+    {
+        k_absmax<<<RG, RB, 0, st>>>(n, a, part);
+        cudaError_t e = cudaMemcpyAsync(h.data(), part, sizeof(double) * RG, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        *out = 0.0;
+        for (int b = 0; b < RG; ++b) *out = fmax(*out, h[b]);
+        return e;
+    }
+};
+
+// z = dinv r + s (1 - mask) y    (y: network output, FP32)
+__global__ void k_compose_z(int64_t n, const double *__restrict__ dinv, const double *__restrict__ r,
+                            const float *__restrict__ y, const uint8_t *__restrict__ mask, double s,
+                            double *__restrict__ z)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double corr = (mask && mask[i]) ? 0.0 : s * (double)y[i];
+    z[i] = fma(dinv[i], r[i], corr);
+}
+
+__global__ void k_jacobi(int64_t n, const double *__restrict__ dinv, const double *__restrict__ r,
+                         double *__restrict__ z)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) z[i] = dinv[i] * r[i];
+}
+
+__global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, double b, double *__restrict__ y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = fma(a, x[i], b * y[i]);
+}
+
+__global__ void k_diag_inv2(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, double *__restrict__ dinv)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double di = 0.0;
+    for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
+        if (ci[t] == i) di = v[t];
+    dinv[i] = 1.0 / di;
+}
+
+// training: e = K z - r (q holds K z), partial sums of e.e and r.r per sample
+__global__ void k_train_err(int64_t n, const double *__restrict__ q, const double *__restrict__ r,
+                            double *__restrict__ e)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) e[i] = q[i] - r[i];
+}
+
+// gy = coef s (1 - mask) (K e)   (FP32 gradient of the network output)
+__global__ void k_train_gy(int64_t n, const double *__restrict__ ke, const uint8_t *__restrict__ mask, double coef,
+                           float *__restrict__ gy)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    gy[i] = (mask && mask[i]) ? 0.f : (float)(coef * ke[i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// network object
+// ---------------------------------------------------------------------------
+struct mf_cnn {
+    int np = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, grad, AdamW moments
+    __nv_bfloat16 *pb = nullptr;                                    // BF16 copy used by the kernels
+    int *is_w = nullptr;
+    long long step = 0;
+    // activation workspace (grown on demand)
+    size_t ws_bytes = 0;
+    void *ws = nullptr;
+};
+
+namespace {
+
+template <int CI, int CO, bool RELU, bool F32>
+void fwd_layer(int B, int nz, int ny, int nx, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *b,
+               void *out, cudaStream_t st)
+{
+    const int64_t tot = (int64_t)B * nz * ny * nx;
+    k_conv_fwd<CI, CO, RELU, F32><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, in, w, b, out);
+}
+
+struct Acts {
+    __nv_bfloat16 *a1, *a2, *a3;  // outputs of layers 1..3 (ReLU), BF16
+    float *y;                      // layer 4 output, FP32
+    float *g0, *g1;                // gradient buffers (FP32, 16 channels)
+    float *part;                   // weight-gradient partials
+    int wparts;
+};
+
+mf_status ensure_ws(mf_cnn *c, int B, int nv, bool train, Acts *A, cudaStream_t st)
+{
+    const size_t act = (size_t)B * nv * 16 * sizeof(__nv_bfloat16);
+    const size_t yb = (size_t)B * nv * sizeof(float);
+    const size_t gb = train ? (size_t)B * nv * 16 * sizeof(float) : 0;
+    const int wparts = 1024;
+    const size_t pb = train ? (size_t)wparts * (16 * 16 * 27 + 16) * sizeof(float) : 0;
+    const size_t need = 3 * act + yb + 2 * gb + pb + 4096;
+    if (need > c->ws_bytes) {
+        if (c->ws) cudaFreeAsync(c->ws, st);
+        c->ws = nullptr;
+        MF_CUDA(cudaMallocAsync(&c->ws, need, st));
+        c->ws_bytes = need;
+    }
+    char *q = static_cast<char *>(c->ws);
+    A->a1 = reinterpret_cast<__nv_bfloat16 *>(q);
+    A->a2 = reinterpret_cast<__nv_bfloat16 *>(q + act);
+    A->a3 = reinterpret_cast<__nv_bfloat16 *>(q + 2 * act);
+    A->y = reinterpret_cast<float *>(q + 3 * act);
+    A->g0 = train ? reinterpret_cast<float *>(q + 3 * act + yb) : nullptr;
+    A->g1 = train ? reinterpret_cast<float *>(q + 3 * act + yb + gb) : nullptr;
+    A->part = train ? reinterpret_cast<float *>(q + 3 * act + yb + 2 * gb) : nullptr;
+    A->wparts = wparts;
+    return MF_OK;
+}
+
+void forward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, Acts &A, cudaStream_t st)
+{
+    const __nv_bfloat16 *W = c->pb;
+    const float *P = c->p;
+    fwd_layer<2, 16, true, false>(B, nz, ny, nx, x, W + p_offset_w(0), P + p_offset_b(0), A.a1, st);
+    fwd_layer<16, 16, true, false>(B, nz, ny, nx, A.a1, W + p_offset_w(1), P + p_offset_b(1), A.a2, st);
+    fwd_layer<16, 16, true, false>(B, nz, ny, nx, A.a2, W + p_offset_w(2), P + p_offset_b(2), A.a3, st);
+    fwd_layer<16, 1, false, true>(B, nz, ny, nx, A.a3, W + p_offset_w(3), P + p_offset_b(3), A.y, st);
+}
+
+template <int CI, int CO>
+void bwd_weight(mf_cnn *c, int l, int B, int nz, int ny, int nx, const __nv_bfloat16 *in, const float *gout,
+                const __nv_bfloat16 *act, Acts &A, cudaStream_t st)
+{
+    const int64_t tot = (int64_t)B * nz * ny * nx;
+    const int chunk = (int)((tot + A.wparts - 1) / A.wparts);
+    const int nblocks = (int)((tot + chunk - 1) / chunk);
+    k_conv_bwd_weight<CI, CO><<<nblocks, 256, 0, st>>>(B, nz, ny, nx, chunk, in, gout, act, A.part);
+    const int n = CO * CI * 27 + CO;  // weights then biases, contiguous in the parameter vector
+    k_reduce_part<<<nblk(n, 128), 128, 0, st>>>(nblocks, n, A.part, c->g + p_offset_w(l));
+}
+
+void backward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, const float *gy, Acts &A,
+              cudaStream_t st)
+{
+    const int64_t tot = (int64_t)B * nz * ny * nx;
+    const __nv_bfloat16 *W = c->pb;
+    // layer 4 (no ReLU): dL/dy = gy
+    bwd_weight<16, 1>(c, 3, B, nz, ny, nx, A.a3, gy, nullptr, A, st);
+    k_conv_bwd_data<16, 1><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, gy, nullptr, W + p_offset_w(3), A.g0);
+    // layer 3: gradient wrt a3 is g0, masked by a3 > 0
+    bwd_weight<16, 16>(c, 2, B, nz, ny, nx, A.a2, A.g0, A.a3, A, st);
+    k_conv_bwd_data<16, 16><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, A.g0, A.a3, W + p_offset_w(2), A.g1);
+    // layer 2
+    bwd_weight<16, 16>(c, 1, B, nz, ny, nx, A.a1, A.g1, A.a2, A, st);
+    k_conv_bwd_data<16, 16><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, A.g1, A.a2, W + p_offset_w(1), A.g0);
+    // layer 1 (input gradient not needed)
+    bwd_weight<2, 16>(c, 0, B, nz, ny, nx, x, A.g0, A.a1, A, st);
+}
+
+}  // namespace
+
+extern "C" int64_t mf_cnn_num_params(void) { return p_total(); }
+
+extern "C" mf_status mf_cnn_create(const float *init, mf_cnn **out)
+{
+    if (!init || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_create: NULL argument");
+    *out = nullptr;
+    mf_cnn *c = new (std::nothrow) mf_cnn();
+    if (!c) return mf_fail(MF_ERR_OOM, "mf_cnn_create: host allocation");
+    c->np = p_total();
+    const size_t n = c->np;
+    cudaError_t e = cudaMalloc(&c->p, 4 * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->pb, n * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&c->is_w, n * sizeof(int));
+    if (e != cudaSuccess) {
+        mf_cnn_destroy(c);
+        return mf_cuda_check(e, "mf_cnn_create");
+    }
+    c->g = c->p + n;
+    c->m = c->p + 2 * n;
+    c->v = c->p + 3 * n;
+    std::vector<int> isw(n, 0);
+    for (int l = 0; l < NL; ++l)
+        for (int i = 0; i < w_count(l); ++i) isw[p_offset_w(l) + i] = 1;
+    cudaMemcpy(c->p, init, n * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemset(c->m, 0, 2 * n * sizeof(float));
+    cudaMemcpy(c->is_w, isw.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+    k_to_bf16<<<nblk(n, 256), 256>>>((int)n, c->p, c->pb);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        mf_cnn_destroy(c);
+        return mf_cuda_check(e, "mf_cnn_create");
+    }
+    *out = c;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_destroy(mf_cnn *c)
+{
+    if (!c) return MF_OK;
+    cudaFree(c->p);
+    cudaFree(c->pb);
+    cudaFree(c->is_w);
+    cudaFree(c->ws);
+    delete c;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_get_params(const mf_cnn *c, float *host, int64_t n)
+{
+    if (!c || !host || n != c->np) return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_get_params: bad argument");
+    MF_CUDA(cudaMemcpy(host, c->p, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_get_grads(const mf_cnn *c, float *host, int64_t n)
+{
+    if (!c || !host || n != c->np) return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_get_grads: bad argument");
+    MF_CUDA(cudaMemcpy(host, c->g, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_forward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
+                                    float *y, void *stream)
+{
+    if (!c || !x || !y || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)nz * ny * nx > INT32_MAX / 16)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_forward: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Acts A;
+    mf_status s = ensure_ws(c, B, nz * ny * nx, false, &A, st);
+    if (s != MF_OK) return s;
+    mf_prof_begin("cnn_forward", st);
+    forward(c, B, nz, ny, nx, static_cast<const __nv_bfloat16 *>(x), A, st);
+    mf_prof_end(st);
+    MF_CUDA(cudaMemcpyAsync(y, A.y, sizeof(float) * (size_t)B * nz * ny * nx, cudaMemcpyDeviceToDevice, st));
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_backward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
+                                     const float *gy, void *stream)
+{
+    if (!c || !x || !gy || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_backward: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Acts A;
+    mf_status s = ensure_ws(c, B, nz * ny * nx, true, &A, st);
+    if (s != MF_OK) return s;
+    forward(c, B, nz, ny, nx, static_cast<const __nv_bfloat16 *>(x), A, st);
+    backward(c, B, nz, ny, nx, static_cast<const __nv_bfloat16 *>(x), gy, A, st);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_train_step(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx,
+                                       const mf_csr *K, const double *const *kvals, const double *const *r,
+                                       const void *const *x, const uint8_t *mask, float lr, float weight_decay,
+                                       double *loss, void *stream)
+{
+    if (!c || !K || !kvals || !r || !x || B <= 0 || K->n_rows != (int64_t)nz * ny * nx)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_train_step: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nv = nz * ny * nx;
+    // the batch input: B node grids of 2 channels, gathered into one buffer
+    __nv_bfloat16 *xb = nullptr;
+    double *z = nullptr, *q = nullptr, *e = nullptr, *dinv = nullptr;
+    float *gy = nullptr;
+    MF_CUDA(cudaMallocAsync(&xb, sizeof(__nv_bfloat16) * 2 * (size_t)B * nv, st));
+    MF_CUDA(cudaMallocAsync(&z, sizeof(double) * nv * 4, st));
+    MF_CUDA(cudaMallocAsync(&gy, sizeof(float) * (size_t)B * nv, st));
+    q = z + nv;
+    e = z + 2 * nv;
+    dinv = z + 3 * nv;
+    for (int b = 0; b < B; ++b)
+        MF_CUDA(cudaMemcpyAsync(xb + (size_t)2 * b * nv, x[b], sizeof(__nv_bfloat16) * 2 * nv,
+                                cudaMemcpyDeviceToDevice, st));
+    Acts A;
+    mf_status s = ensure_ws(c, B, nv, true, &A, st);
+    if (s != MF_OK) return s;
+    forward(c, B, nz, ny, nx, xb, A, st);
+    Reducer red;
+    MF_CUDA(red.init(st));
+    double Ltot = 0.0;
+    for (int b = 0; b < B; ++b) {
+        // s_b = max |r_b|; z = D^-1 r + s (1 - mask) y; e = K z - r
+        double smax = 0.0, dd[3];
+        MF_CUDA(red.absmax(nv, r[b], &smax));
+        k_diag_inv2<<<nblk(nv, 256), 256, 0, st>>>(nv, K->row_ptr, K->col_idx, kvals[b], dinv);
+        k_compose_z<<<nblk(nv, 256), 256, 0, st>>>(nv, dinv, r[b], A.y + (size_t)b * nv, mask, smax, z);
+        mf_csr Kb = *K;
+        Kb.values = const_cast<double *>(kvals[b]);
+        mf_spmv_impl(&Kb, z, q, st);
+        k_train_err<<<nblk(nv, 256), 256, 0, st>>>(nv, q, r[b], e);
+        MF_CUDA(red.dots(nv, e, e, r[b], r[b], nullptr, nullptr, dd));
+        const double rr = dd[1] > 0 ? dd[1] : 1.0;
+        Ltot += dd[0] / rr / B;
+        // dL/dz = (2 / (B rr)) K e (K symmetric);  dL/dy = s (1 - mask) dL/dz
+        mf_spmv_impl(&Kb, e, q, st);
+        k_train_gy<<<nblk(nv, 256), 256, 0, st>>>(nv, q, mask, 2.0 * smax / (B * rr), gy + (size_t)b * nv);
+    }
+    backward(c, B, nz, ny, nx, xb, gy, A, st);
+    if (lr > 0.f) {
+        c->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
+        k_adamw<<<nblk(c->np, 256), 256, 0, st>>>(c->np, c->p, c->g, c->m, c->v, lr, b1, b2, 1e-8f, weight_decay, c1,
+                                                  c2, c->is_w, c->pb);
+    }
+    MF_CUDA(cudaGetLastError());
+    cudaFreeAsync(xb, st);
+    cudaFreeAsync(z, st);
+    cudaFreeAsync(gy, st);
+    if (loss) *loss = Ltot;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_node_logk(int32_t nz, int32_t ny, int32_t nx, const double *kcell, float *out,
+                                      void *stream)
+{
+    if (!kcell || !out || nz < 2 || ny < 2 || nx < 2) return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_node_logk");
+    k_node_logk<<<nblk((int64_t)nz * ny * nx, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(nz, ny, nx, kcell,
+                                                                                                  out);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+extern "C" mf_status mf_cnn_input(int64_t n, const double *r, const float *logk, void *x_bf16, void *stream)
+{
+    if (!r || !logk || !x_bf16 || n <= 0) return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_input");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Reducer red;
+    MF_CUDA(red.init(st));
+    double smax = 0.0;
+    MF_CUDA(red.absmax(n, r, &smax));
+    const double sinv = smax > 0 ? 1.0 / smax : 0.0;
+    double *d_sinv = nullptr;
+    MF_CUDA(cudaMallocAsync(&d_sinv, sizeof(double), st));
+    MF_CUDA(cudaMemcpyAsync(d_sinv, &sinv, sizeof(double), cudaMemcpyHostToDevice, st));
+    k_cnn_input<<<nblk(n, 256), 256, 0, st>>>(n, r, d_sinv, logk, static_cast<__nv_bfloat16 *>(x_bf16));
+    cudaFreeAsync(d_sinv, st);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+// y = a x + b y (helper for residual bookkeeping of the training data)
+extern "C" mf_status mf_axpby(int64_t n, double a, const double *x, double b, double *y, void *stream)
+{
+    if (!x || !y || n <= 0) return mf_fail(MF_ERR_INVALID_ARG, "mf_axpby");
+    k_axpby<<<nblk(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, a, x, b, y);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+// Flexible CG (Notay 2000, one stored direction) with the CNN correction.
+extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *x, mf_cnn *c, int32_t nz,
+                                      int32_t ny, int32_t nx, const float *logk, const uint8_t *mask, double tol,
+                                      int64_t max_iter, mf_solve_info *info, int64_t *fallbacks, void *stream)
+{
+    if (!K || !d || !x || !c || !logk || K->n_rows != (int64_t)nz * ny * nx || !(tol > 0))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_fcg_cnn: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = K->n_rows;
+    double *buf = nullptr;
+    MF_CUDA(cudaMallocAsync(&buf, sizeof(double) * 6 * n, st));
+    double *r = buf, *zv = buf + n, *p = buf + 2 * n, *q = buf + 3 * n, *dinv = buf + 4 * n, *qo = buf + 5 * n;
+    __nv_bfloat16 *xin = nullptr;
+    MF_CUDA(cudaMallocAsync(&xin, sizeof(__nv_bfloat16) * 2 * n, st));
+    Acts A;
+    mf_status s = ensure_ws(c, 1, (int)n, false, &A, st);
+    if (s != MF_OK) return s;
+    Reducer red;
+    MF_CUDA(red.init(st));
+    k_diag_inv2<<<nblk(n, 256), 256, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv);
+    // r = d - K x
+    mf_spmv_impl(K, x, q, st);
+    MF_CUDA(cudaMemcpyAsync(r, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -1.0, q, 1.0, r);
+    double dd3[3];
+    MF_CUDA(red.dots(n, d, d, r, r, nullptr, nullptr, dd3));
+    const double dn2 = dd3[0];
+    double rr = dd3[1];
+    int64_t it = 0, fb = 0;
+    double pq_old = 0.0;
+    int done = rr <= tol * tol * dn2 ? 1 : 0;
+    while (!done && it < max_iter) {
+        // z = M(r): Jacobi plus the network correction
+        double smax = 0.0;
+        MF_CUDA(red.absmax(n, r, &smax));
+        const double sinv = smax > 0 ? 1.0 / smax : 0.0;
+        MF_CUDA(cudaMemcpyAsync(q, &sinv, sizeof(double), cudaMemcpyHostToDevice, st));  // q[0] as a scalar slot
+        k_cnn_input<<<nblk(n, 256), 256, 0, st>>>(n, r, q, logk, xin);
+        mf_prof_begin("fcg_cnn_forward", st);
+        forward(c, 1, nz, ny, nx, xin, A, st);
+        mf_prof_end(st);
+        k_compose_z<<<nblk(n, 256), 256, 0, st>>>(n, dinv, r, A.y, mask, smax, zv);
+        double zr[3];
+        MF_CUDA(red.dots(n, zv, r, zv, zv, nullptr, nullptr, zr));
+        if (!(zr[0] > 0.0) || !std::isfinite(zr[0]) || !std::isfinite(zr[1])) {  // descent test failed: Jacobi
+            k_jacobi<<<nblk(n, 256), 256, 0, st>>>(n, dinv, r, zv);
+            ++fb;
+        }
+        // p = z - (z . q_old / p_old . q_old) p_old
+        if (it == 0) {
+            MF_CUDA(cudaMemcpyAsync(p, zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            double zq[3];
+            MF_CUDA(red.dots(n, zv, qo, nullptr, nullptr, nullptr, nullptr, zq));
+            const double beta = -zq[0] / pq_old;
+            k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, 1.0, zv, beta, p);
+        }
+        mf_spmv_impl(K, p, q, st);
+        double pr[3];
+        MF_CUDA(red.dots(n, p, r, p, q, nullptr, nullptr, pr));
+        if (!(pr[1] > 0.0) || !std::isfinite(pr[1])) {
+            done = 3;
+            break;
+        }
+        const double alpha = pr[0] / pr[1];
+        pq_old = pr[1];
+        k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, alpha, p, 1.0, x);
+        k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -alpha, q, 1.0, r);
+        MF_CUDA(cudaMemcpyAsync(qo, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        double rn[3];
+        MF_CUDA(red.dots(n, r, r, nullptr, nullptr, nullptr, nullptr, rn));
+        rr = rn[0];
+        ++it;
+        if (!std::isfinite(rr)) { done = 3; break; }
+        if (rr <= tol * tol * dn2) done = 1;
+    }
+    // true residual
+    mf_spmv_impl(K, x, q, st);
+    MF_CUDA(cudaMemcpyAsync(r, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -1.0, q, 1.0, r);
+    double tr[3];
+    MF_CUDA(red.dots(n, r, r, nullptr, nullptr, nullptr, nullptr, tr));
+    cudaFreeAsync(buf, st);
+    cudaFreeAsync(xin, st);
+    if (info) {
+        info->iterations = it;
+        info->rel_residual = dn2 > 0 ? sqrt(tr[0] / dn2) : sqrt(tr[0]);
+        info->converged = done == 1;
+    }
+    if (fallbacks) *fallbacks = fb;
+    if (done == 3) return mf_fail(MF_ERR_NONFINITE, "mf_solve_fcg_cnn: breakdown");
+    if (done != 1) return mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve_fcg_cnn: %lld iterations", (long long)it);
+    return MF_OK;
+}

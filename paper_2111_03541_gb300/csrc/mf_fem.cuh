@@ -1,0 +1,301 @@
+// Device routines shared by the single-problem and the batched assembly:
+// quadrature constants, reference elements, geometry, and the thermal
+// element kernels of Sec. 4.1 (one element per call, FP64).
+#pragma once
+
+#include "mf_internal.h"
+
+namespace {
+
+constexpr double QG = 0.57735026918962576451;  // 2-point Gauss abscissa 1/sqrt(3)
+// symmetric 6-point degree-4 triangle rule (two orbits (a, a, 1-2a)); weights
+// normalised to area 1
+constexpr double T6A1 = 0.44594849091596488632, T6W1 = 0.22338158967801146570;
+constexpr double T6A2 = 0.091576213509770743460, T6W2 = 0.10995174365532186764;
+
+// reference derivative dN_a/dxi_j of the trilinear basis at Gauss point q
+__device__ __forceinline__ double q1_dref(int q, int a, int j)
+{
+    const double xs[3] = {(q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG};
+    const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+    double v = 0.125 * s[j];
+    for (int i = 0; i < 3; ++i)
+        if (i != j) v *= 1.0 + s[i] * xs[i];
+    return v;
+}
+
+__device__ __forceinline__ double q1_n(int q, int a)
+{
+    const double xs[3] = {(q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG};
+    const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+    return 0.125 * (1.0 + s[0] * xs[0]) * (1.0 + s[1] * xs[1]) * (1.0 + s[2] * xs[2]);
+}
+
+// Jacobian of the trilinear map at Gauss point q, its determinant and inverse
+__device__ __forceinline__ double q1_jac(const double (&x)[8][3], int q, double (&Ji)[3][3])
+{
+    double J[3][3] = {};
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double dn = q1_dref(q, a, j);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) J[i][j] = fma(x[a][i], dn, J[i][j]);
+        }
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double r = 1.0 / det;
+    Ji[0][0] = c00 * r;
+    Ji[1][0] = c01 * r;
+    Ji[2][0] = c02 * r;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+    return det;
+}
+
+// affine triangle from its first three nodes: detJ and grad lambda_k
+__device__ __forceinline__ double tri_affine(const double *__restrict__ X, const int32_t *__restrict__ c,
+                                             double (&gl)[3][2])
+{
+    const double x0 = X[2 * (int64_t)c[0]], y0 = X[2 * (int64_t)c[0] + 1];
+    const double j00 = X[2 * (int64_t)c[1]] - x0, j10 = X[2 * (int64_t)c[1] + 1] - y0;
+    const double j01 = X[2 * (int64_t)c[2]] - x0, j11 = X[2 * (int64_t)c[2] + 1] - y0;
+    const double det = j00 * j11 - j01 * j10;
+    const double r = 1.0 / det;
+    // J^{-1} = [[j11, -j01], [-j10, j00]] / det ; grad lambda = J^{-T} gradref lambda
+    const double i00 = j11 * r, i01 = -j01 * r, i10 = -j10 * r, i11 = j00 * r;
+    gl[1][0] = i00; gl[1][1] = i01;   // gradref lambda_1 = (1, 0)
+    gl[2][0] = i10; gl[2][1] = i11;   // gradref lambda_2 = (0, 1)
+    gl[0][0] = -i00 - i10; gl[0][1] = -i01 - i11;
+    return det;
+}
+
+// P2 basis values and physical gradients at barycentric point l
+__device__ __forceinline__ void p2_basis(const double (&l)[3], const double (&gl)[3][2], double (&N)[6],
+                                         double (&g)[6][2])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        N[i] = l[i] * (2.0 * l[i] - 1.0);
+        g[i][0] = (4.0 * l[i] - 1.0) * gl[i][0];
+        g[i][1] = (4.0 * l[i] - 1.0) * gl[i][1];
+    }
+    const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int p = ep[e][0], q = ep[e][1];
+        N[3 + e] = 4.0 * l[p] * l[q];
+        g[3 + e][0] = 4.0 * (gl[p][0] * l[q] + l[p] * gl[q][0]);
+        g[3 + e][1] = 4.0 * (gl[p][1] * l[q] + l[p] * gl[q][1]);
+    }
+}
+
+__device__ __forceinline__ void tri6_point(int q, double (&l)[3], double &w)
+{
+    const double a = q < 3 ? T6A1 : T6A2;
+    const double b = 1.0 - 2.0 * a;
+    const int k = q % 3;
+    l[0] = (k == 0) ? b : a;
+    l[1] = (k == 1) ? b : a;
+    l[2] = (k == 2) ? b : a;
+    w = 0.5 * (q < 3 ? T6W1 : T6W2);  // reference triangle area 1/2
+}
+
+__device__ __forceinline__ int upair(int a, int b) { return a * (15 - a) / 2 + b; }  // a <= b < 8
+
+__device__ __forceinline__ void elem_thermal_p1(int64_t e, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+{
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double gl[3][2];
+    const double det = tri_affine(X, conn + 3 * e, gl);
+    // the integrand is constant: the 3 point weights sum to 1/2
+    const double s = 0.5 * det * k;
+    double *o = out + e * 12;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) o[3 * a + b] = s * (gl[a][0] * gl[b][0] + gl[a][1] * gl[b][1]);
+    // 3-point rule: sum_q w_q lambda_a(q) = 1/6
+    const double l = det * f * (1.0 / 6.0);
+    o[9] = l;
+    o[10] = l;
+    o[11] = l;
+}
+
+__device__ __forceinline__ void elem_thermal_p2(int64_t e, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+{
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double gl[3][2];
+    const double det = tri_affine(X, conn + 6 * e, gl);
+    double Ke[21] = {}, de[6] = {};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        // degree-2 interior rule: (2/3, 1/6, 1/6) and permutations, weight 1/6
+        double l[3] = {1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
+        l[q] = 2.0 / 3.0;
+        double N[6], g[6][2];
+        p2_basis(l, gl, N, g);
+        const double wd = det * (1.0 / 6.0);
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+#pragma unroll
+            for (int b = a; b < 6; ++b, ++t) Ke[t] = fma(wd, g[a][0] * g[b][0] + g[a][1] * g[b][1], Ke[t]);
+            de[a] = fma(wd, N[a], de[a]);
+        }
+    }
+    double *o = out + e * 42;
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = a; b < 6; ++b, ++t) {
+            o[6 * a + b] = k * Ke[t];
+            o[6 * b + a] = k * Ke[t];
+        }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) o[36 + a] = f * de[a];
+}
+
+__device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restrict__ X,
+                                                         const int32_t *__restrict__ conn,
+                                                         const double *__restrict__ kc, double f,
+                                                         double *__restrict__ out, int *status)
+{
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double x[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
+    double Ke[36] = {}, m[8] = {};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double Ji[3][3];
+        const double wd = q1_jac(x, q, Ji);  // Gauss weights are 1
+        double g[8][3];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                g[a][i] = q1_dref(q, a, 0) * Ji[0][i] + q1_dref(q, a, 1) * Ji[1][i] + q1_dref(q, a, 2) * Ji[2][i];
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double ga0 = wd * g[a][0], ga1 = wd * g[a][1], ga2 = wd * g[a][2];
+#pragma unroll
+            for (int b = a; b < 8; ++b, ++t) Ke[t] = fma(ga0, g[b][0], fma(ga1, g[b][1], fma(ga2, g[b][2], Ke[t])));
+            m[a] = fma(wd, q1_n(q, a), m[a]);
+        }
+    }
+    double *o = out + e * 72;
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = a; b < 8; ++b, ++t) {
+            o[8 * a + b] = k * Ke[t];
+            o[8 * b + a] = k * Ke[t];
+        }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) o[64 + a] = f * m[a];
+}
+
+// One warp builds the BS x BS node-pair blocks of row node n from its
+// contribution lists (ascending elements) and applies the Dirichlet rows.
+template <int BS>
+__device__ __forceinline__ void gather_node(int64_t n, int lane, const int64_t *__restrict__ ptr,
+                                                const int32_t *__restrict__ col, const int64_t *__restrict__ cptr,
+                                                const int32_t *__restrict__ clist, const double *__restrict__ sc,
+                                                int64_t stride, int npe, const uint8_t *__restrict__ mask,
+                                                const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+                                                double *__restrict__ values, double *__restrict__ d)
+{
+    const int64_t p0 = ptr[n], deg = ptr[n + 1] - p0;
+    bool rm[BS];
+    double lift[BS], dsum[BS];
+    int64_t rbase[BS];
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+        rm[c] = mask ? mask[BS * n + c] != 0 : false;
+        lift[c] = 0.0;
+        dsum[c] = 0.0;
+        rbase[c] = row_ptr[BS * n + c];
+    }
+    for (int64_t k = lane; k < deg; k += 32) {
+        const int64_t p = p0 + k;
+        const int32_t mnode = col[p];
+        double acc[BS][BS];
+#pragma unroll
+        for (int c = 0; c < BS; ++c)
+#pragma unroll
+            for (int cp = 0; cp < BS; ++cp) acc[c][cp] = 0.0;
+        for (int64_t t = cptr[p]; t < cptr[p + 1]; ++t) {
+            const int32_t v = clist[t];
+            const int64_t e = v >> 6;
+            const int a = (v >> 3) & 7, b = v & 7;
+            const double *s = sc + e * stride;
+            if (BS == 1) {
+                acc[0][0] += s[a * npe + b];
+                if (mnode == n) dsum[0] += s[npe * npe + a];
+            } else {
+                if (a <= b) {
+                    const double *blk = s + upair(a, b) * 9;
+#pragma unroll
+                    for (int c = 0; c < BS; ++c)
+#pragma unroll
+                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * c + cp];
+                } else {
+                    const double *blk = s + upair(b, a) * 9;
+#pragma unroll
+                    for (int c = 0; c < BS; ++c)
+#pragma unroll
+                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * cp + c];
+                }
+                if (mnode == n)
+#pragma unroll
+                    for (int c = 0; c < BS; ++c) dsum[c] += s[324 + 3 * a + c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < BS; ++c)
+#pragma unroll
+            for (int cp = 0; cp < BS; ++cp) {
+                double v = acc[c][cp];
+                if (mask) {
+                    const int64_t r = BS * n + c, sdof = BS * (int64_t)mnode + cp;
+                    if (rm[c]) {
+                        v = (r == sdof) ? 1.0 : 0.0;
+                    } else if (mask[sdof]) {
+                        lift[c] -= v * bval[sdof];
+                        v = 0.0;
+                    }
+                }
+                values[rbase[c] + BS * k + cp] = v;
+            }
+    }
+#pragma unroll
+    for (int c = 0; c < BS; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lift[c] += __shfl_xor_sync(0xffffffffu, lift[c], o);
+            dsum[c] += __shfl_xor_sync(0xffffffffu, dsum[c], o);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < BS; ++c) d[BS * n + c] = rm[c] ? bval[BS * n + c] : dsum[c] + lift[c];
+}
+
+}  // namespace

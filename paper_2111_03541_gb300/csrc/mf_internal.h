@@ -78,9 +78,10 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
                             double *values, double *d, cudaStream_t st);
 mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,
                                double p_scale, double *out, cudaStream_t st);
-// elasticity gather (FP64 sums, or exact int64 fixed-point sums of the mixed path)
-void mf_launch_gather_elastic(bool fixed_point, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
-                              double *values, double *d, cudaStream_t st);
+// elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64
+// sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
+void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, const mf_mesh *m, const mf_pattern *p,
+                              const mf_coeffs *c, double *values, double *d, cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);
 mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o,
                         mf_solve_info *info, cudaStream_t st);

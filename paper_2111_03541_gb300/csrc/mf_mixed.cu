@@ -19,9 +19,9 @@
 //    slice pairs accumulates exactly on the tensor cores (mma.sync m16n8k16,
 //    bf16 in, fp32 accumulate);
 //  * the levels are combined into 64-bit fixed point at a global scale 2^S
-//    (chosen by a pre-pass so no sum can overflow), the p, q finishing is
-//    integer arithmetic, and the CSR sums of the gather are exact int64 sums
-//    converted once to FP64.
+//    (chosen by a pre-pass so no sum can overflow); the gather sums A'' over
+//    the elements exactly in int64, applies the (linear) p, q finishing once
+//    per CSR block and converts each value once to FP64.
 // The dropped levels (s + t > 4) bound the error at about 2^-40 of the row
 // scale; the solution error against the FP64 path is measured per run.
 #include <cuda_bf16.h>
@@ -206,12 +206,11 @@ __global__ void k_mixed_scale(MixedState *st, int p, int q)
 struct WarpSmem {
     __nv_bfloat16 sl[4][NSL][SL_ROWS][8];  // slices of G per element: [slice][row (a,c)][point]
     int ex[4][SL_ROWS];                     // row exponents
-    long long A[24][24];                    // fixed-point A'' of the element in progress
 };
 
 __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
-    double cmu_q, int p, int q, double b0, double b1, double b2, const MixedState *__restrict__ st,
+    double cmu_q, double b0, double b1, double b2, const MixedState *__restrict__ st,
     double *__restrict__ out, int64_t stride, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -409,43 +408,37 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
                 mma_bf16(acc[L][3], a[1][0], a[1][1], a[1][2], a[1][3], bf[2][0], bf[2][1]);
             }
         }
-        // levels -> 64-bit fixed point at scale 2^S, into shared memory
-        const int tmt[4] = {0, 0, 0, 1}, tnt[4] = {0, 1, 2, 2};
-#pragma unroll
-        for (int tl = 0; tl < 4; ++tl)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int rho = tmt[tl] * 16 + g + 8 * (k >> 1);
-                const int sig2 = tnt[tl] * 8 + 2 * t + (k & 1);
-                if (rho >= 24) continue;
-                long long T = f2i_exact(acc[0][tl][k]);
-#pragma unroll
-                for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][tl][k]);
-                const int sh = W.ex[el][rho] + W.ex[el][sig2] + S - 48;
-                long long v;
-                if (sh >= 0) v = T << sh;
-                else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
-                else v = 0;
-                W.A[rho][sig2] = v;
-                if (tl == 2 && rho < 16) W.A[sig2][rho] = v;  // mirror of the block not computed
-            }
-        __syncwarp();
-        // finishing K = p A + q swap(A) + q I tr(A) on the upper blocks a <= b
+        // levels -> 64-bit fixed point at scale 2^S, written straight to the
+        // element's upper blocks (a <= b); the p, q finishing is linear and is
+        // applied once per CSR block after the exact sums of the gather
         if (eo < n_el) {
             long long *o = reinterpret_cast<long long *>(out + eo * stride);
-            for (int idx = lane; idx < 324; idx += 32) {
-                const int blk = idx / 9, cc = idx - 9 * blk;
-                int a = 0, rem = blk;
-                while (rem >= 8 - a) { rem -= 8 - a; ++a; }
-                const int b = a + rem;
-                const int c = cc / 3, cp = cc - 3 * c;
-                long long v = (long long)p * W.A[3 * a + c][3 * b + cp] + (long long)q * W.A[3 * a + cp][3 * b + c];
-                if (c == cp)
-                    v += (long long)q * (W.A[3 * a][3 * b] + W.A[3 * a + 1][3 * b + 1] + W.A[3 * a + 2][3 * b + 2]);
-                o[idx] = v;
-            }
+            const int tmt[4] = {0, 0, 0, 1}, tnt[4] = {0, 1, 2, 2};
+#pragma unroll
+            for (int tl = 0; tl < 4; ++tl)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int rho = tmt[tl] * 16 + g + 8 * (k >> 1);
+                    const int sig2 = tnt[tl] * 8 + 2 * t + (k & 1);
+                    const int a = rho / 3, b = sig2 / 3;
+                    // an upper block a <= b is complete from the computed tiles:
+                    // (a < b) whole block, (a == b) both triangles (rows >= 24 skipped)
+                    if (rho >= 24 || a > b) continue;
+                    long long T = f2i_exact(acc[0][tl][k]);
+#pragma unroll
+                    for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][tl][k]);
+                    const int sh = W.ex[el][rho] + W.ex[el][sig2] + S - 48;
+                    long long v;
+                    if (sh >= 0) v = T << sh;
+                    else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
+                    else v = 0;
+                    const int base = (a * (15 - a) / 2 + b) * 9;
+                    o[base + 3 * (rho - 3 * a) + (sig2 - 3 * b)] = v;
+                    // diagonal block 5 straddles the tiles: its entries (16, 15) and
+                    // (17, 15) are not computed; they mirror (15, 16) and (15, 17)
+                    if (tl == 2 && a == b) o[base + 3 * (sig2 - 3 * b) + (rho - 3 * a)] = v;
+                }
         }
-        __syncwarp();
     }
 }
 
@@ -487,12 +480,12 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     mf_prof_begin("mixed_elem", st);
     k_mixed_elem<<<(unsigned)((ne + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
-        ne, m->coords, m->conn, c->elem_coef, cmu_q, pp, qq, c->source[0], c->source[1], c->source[2], ms, p->scratch,
+        ne, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms, p->scratch,
         p->scratch_stride, status);
     mf_prof_end(st);
     MF_CUDA(cudaGetLastError());
     mf_prof_begin("gather_elastic_fixed", st);
-    mf_launch_gather_elastic(true, m, p, c, values, d, st);
+    mf_launch_gather_elastic(true, pp, qq, m, p, c, values, d, st);
     mf_prof_end(st);
     MF_CUDA(cudaGetLastError());
     return MF_OK;

@@ -541,3 +541,58 @@ def test_mms_convergence_rate(orc, kind, ns, rate):
         errs.append(_mms_error(orc, prob))
     rates = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log(np.array(ns[1:]) / np.array(ns[:-1]))
     assert rates.min() >= rate, (errs, rates)
+
+
+# ---------------------------------------------------------------------------
+# convolution layers of the learned preconditioner
+# ---------------------------------------------------------------------------
+
+def test_conv3d_fwd_matches_independent_correlation(orc):
+    from scipy.ndimage import correlate
+    rng = np.random.default_rng(21)
+    x = rng.normal(size=(5, 6, 7, 3))
+    w = rng.normal(size=(4, 3, 27))
+    b = rng.normal(size=4)
+    out = orc.conv3d_fwd(x, w, b)
+    ref = np.zeros_like(out)
+    for co in range(4):
+        acc = np.full(x.shape[:3], b[co])
+        for ci in range(3):
+            acc += correlate(x[..., ci], w[co, ci].reshape(3, 3, 3), mode="constant", cval=0.0)
+        ref[..., co] = acc
+    assert np.abs(out - ref).max() < 1e-12
+    r = orc.conv3d_fwd(x, w, b, relu=True)
+    assert np.abs(r - np.maximum(ref, 0.0)).max() < 1e-12
+
+
+def test_conv3d_gradients_central_differences(orc):
+    rng = np.random.default_rng(22)
+    x = rng.normal(size=(4, 5, 3, 2))
+    w = rng.normal(size=(3, 2, 27))
+    b = rng.normal(size=3)
+    g = rng.normal(size=(4, 5, 3, 3))  # loss = sum(g * conv(x))
+
+    def loss(xx, ww, bb):
+        return float(np.sum(g * orc.conv3d_fwd(xx, ww, bb)))
+
+    gin = orc.conv3d_bwd_data(g, w, 2)
+    gw, gb = orc.conv3d_bwd_weight(x, g)
+    h = 1e-6
+    for idx in [(0, 0, 0, 0), (3, 4, 2, 1), (2, 2, 1, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (loss(xp, w, b) - loss(xm, w, b)) / (2 * h)
+        assert abs(fd - gin[idx]) <= 1e-6 * max(1.0, abs(fd))
+    for idx in [(0, 0, 0), (2, 1, 13), (1, 0, 26)]:
+        wp, wm = w.copy(), w.copy()
+        wp[idx] += h
+        wm[idx] -= h
+        fd = (loss(x, wp, b) - loss(x, wm, b)) / (2 * h)
+        assert abs(fd - gw[idx]) <= 1e-6 * max(1.0, abs(fd))
+    for c in range(3):
+        bp, bm = b.copy(), b.copy()
+        bp[c] += h
+        bm[c] -= h
+        fd = (loss(x, w, bp) - loss(x, w, bm)) / (2 * h)
+        assert abs(fd - gb[c]) <= 1e-6 * max(1.0, abs(fd))
