@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--grid", type=int, default=N_GRID, help="box size n (n^3 elements); 64 is the workload")
     ap.add_argument("--skip-solve", action="store_true", help="skip the accuracy solves (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-suite", action="store_true", help="skip the other configurations (C0, C2, C3, C4)")
     return ap.parse_args()
 
 
@@ -236,7 +237,7 @@ def run_ours(args):
         have_mixed = False
 
     def kernels(kt):
-        return {k: {"launches": c, "ms_per_launch": t / c} for k, (c, t) in kt.items()}
+        return {k: {"launches": c, "ms_per_launch": t / c, "ms_per_step": t / args.steps} for k, (c, t) in kt.items()}
 
     sampler = ClockSampler(local)
     with sampler:
@@ -284,17 +285,17 @@ def run_ours(args):
     if best == "fp64":
         # the element kernel dominates and is bound by the FP64 pipe
         kname = "elem_elastic_q1_fp64"
-        ms_el = paths["fp64"]["kernels"][kname]["ms_per_launch"]
+        ms_el = paths["fp64"]["kernels"][kname]["ms_per_step"]
         ach = n_el * FLOPS_PER_ELEMENT_FP64 / (ms_el * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "ms_per_launch": ms_el,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "ms_per_step": ms_el,
                     "algorithmic": f"{FLOPS_PER_ELEMENT_FP64} FP64 flops/element x {n_el} elements",
                     "peak_source": "GB300 nominal dense FP64 rate (measured FMA-loop rate 1.19 TFLOP/s)"}
     else:
-        kname = max(paths[best]["kernels"], key=lambda k: paths[best]["kernels"][k]["ms_per_launch"])
-        ms_k = paths[best]["kernels"][kname]["ms_per_launch"]
+        kname = max(paths[best]["kernels"], key=lambda k: paths[best]["kernels"][k]["ms_per_step"])
+        ms_k = paths[best]["kernels"][kname]["ms_per_step"]
         roofline = dict(roofline_hbm)
-        roofline.update({"kernel": kname, "ms_per_launch": ms_k, "peak_source": peak_src, "traffic": None})
+        roofline.update({"kernel": kname, "ms_per_step": ms_k, "peak_source": peak_src, "traffic": None})
 
     # end to end: host buffers in, K and d out, through the C ABI
     e2e = None if args.no_e2e else e2e_leg(P, prob, mf, stream, args, best)
@@ -315,9 +316,117 @@ def run_ours(args):
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob)
+        if not args.no_suite:
+            del P
+            torch.cuda.empty_cache()
+            line["suite"] = suite(dev)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the other configurations: assembly and solve measurements (not bench lines)
+# ---------------------------------------------------------------------------
+def _ev_time(fn, reps=10, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def _solve_timed(P, **kw):
+    import torch
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    x, st, info = P.solve(**kw)
+    torch.cuda.synchronize()
+    return x, {"iterations": int(info.iterations), "rel_residual": info.rel_residual, "converged": bool(info.converged),
+               "s": time.perf_counter() - t}
+
+
+def suite(dev):
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2111_03541_gb300 as mf
+    out = {}
+    # C0: 2D thermal P1 64^2, Jacobi-PCG to 1e-10
+    prob = gen.thermal_p1_problem(64)
+    P = mf.Problem(prob, device=dev)
+    ms = _ev_time(lambda: P.assemble())
+    _, sol = _solve_timed(P, tol=1e-10)
+    out["C0_thermal_p1_64"] = {"elements": int(prob["conn"].shape[0]), "assemble_us": 1e3 * ms,
+                               "elements_per_s": prob["conn"].shape[0] / (ms * 1e-3), "pcg": sol}
+    del P
+    # C2: Taylor-Hood P2-P1 512^2, GMRES(50) with the block-diagonal preconditioner (pressure scale 1)
+    prob = gen.oseen_problem(512)
+    P = mf.Problem(prob, device=dev)
+    ms = _ev_time(lambda: P.assemble(), reps=5)
+    pd = P.flow_precond(1.0)
+    _, sol = _solve_timed(P, solver=mf.MF_SOLVER_GMRES, restart=50, tol=1e-8, max_iter=20000, precond=pd,
+                          check_every=25)
+    out["C2_oseen_p2p1_512"] = {"elements": int(prob["conn"].shape[0]), "n_dofs": int(P.n), "nnz": int(P.nnz),
+                                "assemble_ms": ms, "elements_per_s": prob["conn"].shape[0] / (ms * 1e-3),
+                                "gmres50": sol}
+    del P, pd
+    torch.cuda.empty_cache()
+    # C3: 512 thermal problems, one launch per problem vs the batched graph
+    specs = gen.batch_specs()
+    probs = [gen.batch_problem(sp) for sp in specs]
+    ne = sum(p["conn"].shape[0] for p in probs)
+    t = time.perf_counter()
+    Ps = [mf.Problem(p, device=dev) for p in probs]
+    torch.cuda.synchronize()
+    pat_s = time.perf_counter() - t
+    ms_single = _ev_time(lambda: [Q.assemble() for Q in Ps], reps=3, warm=1)
+    B = mf.mf_batch_create(Ps)
+    t = time.perf_counter()
+    til = mf.mf_batch_autotune(B, None)
+    tune_s = time.perf_counter() - t
+    ms_batch = _ev_time(lambda: mf.mf_batch_assemble(B), reps=5, warm=2)
+    out["C3_batched_512"] = {"problems": len(Ps), "elements": int(ne), "patterns_s": pat_s,
+                             "per_problem_launches_ms": ms_single, "batched_graph_ms": ms_batch,
+                             "elements_per_s_batched": ne / (ms_batch * 1e-3),
+                             "elements_per_s_per_problem": ne / (ms_single * 1e-3),
+                             "speedup": ms_single / ms_batch, "autotune_s": tune_s,
+                             "tiling": [til.elem_tile, til.elem_block, til.node_tile, til.grid_per_sm]}
+    mf.mf_batch_destroy(B)
+    del Ps
+    torch.cuda.empty_cache()
+    # C4: 3D thermal Q1 128^3, k = exp(GRF); Jacobi-PCG vs flexible CG with the trained correction
+    prob = gen.grf_thermal_problem(128)
+    P = mf.Problem(prob, device=dev)
+    ms = _ev_time(lambda: P.assemble(), reps=5)
+    _, pcg = _solve_timed(P, tol=1e-8, max_iter=100000, check_every=100)
+    c4 = {"elements": int(prob["conn"].shape[0]), "n_dofs": int(P.n), "assemble_ms": ms,
+          "elements_per_s": prob["conn"].shape[0] / (ms * 1e-3), "jacobi_pcg": pcg}
+    wpath = os.path.join(ROOT, "paper_2111_03541_gb300", "weights", "cnn_q1_thermal.f32")
+    if os.path.exists(wpath):
+        from paper_2111_03541_gb300 import learned
+        cnn = mf.mf_cnn_create(learned.load_params(wpath))
+        logk = learned.node_logk(P)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        x, st, info, fb = learned.fcg(P, cnn, logk, tol=1e-8, max_iter=4000)
+        torch.cuda.synchronize()
+        c4["fcg_cnn"] = {"iterations": int(info.iterations), "rel_residual": info.rel_residual,
+                         "converged": bool(info.converged), "s": time.perf_counter() - t, "jacobi_fallbacks": fb}
+        xin = torch.zeros(2 * P.n, dtype=torch.bfloat16, device=dev)
+        y = torch.empty(P.n, dtype=torch.float32, device=dev)
+        nz = prob["n"] + 1
+        c4["cnn_forward_ms"] = _ev_time(lambda: mf.mf_cnn_forward(cnn, 1, nz, nz, nz, xin, y), reps=5)
+        mf.mf_cnn_destroy(cnn)
+    out["C4_grf_q1_128"] = c4
+    return out
 
 
 def e2e_leg(P, prob, mf, stream, args, best):

@@ -271,10 +271,14 @@ mf_status mf_cnn_backward(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_
 /* One AdamW step (lr > 0; lr = 0 only computes the loss and gradients) on B
  * samples of systems sharing the pattern of K: kvals[b] the values of system
  * b, r[b] its residual, x[b] its network input (device pointers); the Jacobi
- * part uses diag(K_b).  loss (host) = mean_b ||K_b z_b - r_b||^2 / ||r_b||^2. */
+ * part uses diag(K_b).  loss (host): without err, mean_b ||K_b z_b - r_b||^2 /
+ * ||r_b||^2; with err[b] = K_b^-1 r_b (the error of the iterate), the energy
+ * left after one optimally scaled step along z_b,
+ * mean_b 1 - (z_b . K_b err_b)^2 / ((z_b . K_b z_b)(err_b . K_b err_b)). */
 mf_status mf_cnn_train_step(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_t nx, const mf_csr *K,
-                            const double *const *kvals, const double *const *r, const void *const *x,
-                            const uint8_t *mask, float lr, float weight_decay, double *loss, void *stream);
+                            const double *const *kvals, const double *const *r, const double *const *err,
+                            const void *const *x, const uint8_t *mask, float lr, float weight_decay, double *loss,
+                            void *stream);
 /* Nodal mean of log k over the cells of the (nz-1)(ny-1)(nx-1) cell grid. */
 mf_status mf_cnn_node_logk(int32_t nz, int32_t ny, int32_t nx, const double *kcell, float *out, void *stream);
 /* Network input from a residual: x [n][2] BF16 = (r / max|r|, logk / 2). */

@@ -97,8 +97,8 @@ _SIGS = {
     "mf_cnn_forward": [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_cnn_backward": [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_cnn_train_step": [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(CSR), C.c_void_p,
-                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.POINTER(C.c_double),
-                          C.c_void_p],
+                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_float,
+                          C.POINTER(C.c_double), C.c_void_p],
     "mf_cnn_node_logk": [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_cnn_input": [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_axpby": [C.c_int64, C.c_double, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
@@ -299,11 +299,12 @@ def mf_cnn_backward(h, B, nz, ny, nx, x, gy, stream=None) -> None:
     _check(lib().mf_cnn_backward(h, B, nz, ny, nx, _ptr(x), _ptr(gy), _stream(stream)))
 
 
-def mf_cnn_train_step(h, nz, ny, nx, K: CSR, kvals, r, x, mask, lr, weight_decay, stream=None) -> float:
+def mf_cnn_train_step(h, nz, ny, nx, K: CSR, kvals, r, x, mask, lr, weight_decay, err=None, stream=None) -> float:
     B = len(kvals)
     arr = lambda ts: (C.c_void_p * B)(*[_ptr(t) for t in ts])
     loss = C.c_double()
-    _check(lib().mf_cnn_train_step(h, B, nz, ny, nx, C.byref(K), arr(kvals), arr(r), arr(x), _ptr(mask),
+    _check(lib().mf_cnn_train_step(h, B, nz, ny, nx, C.byref(K), arr(kvals), arr(r),
+                                   None if err is None else arr(err), arr(x), _ptr(mask),
                                    lr, weight_decay, C.byref(loss), _stream(stream)))
     return loss.value
 

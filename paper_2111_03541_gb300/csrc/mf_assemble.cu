@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const dou
 // them into A_ab and finishes K_ab with lambda, mu.
 constexpr int EL_T = 64;
 
-__global__ void __launch_bounds__(EL_T) k_elem_elastic_q1(int64_t n_el, const double *__restrict__ X,
+__global__ void __launch_bounds__(EL_T) k_elem_elastic_q1(int64_t e0, int64_t e1, const double *__restrict__ X,
                                                           const int32_t *__restrict__ conn,
                                                           const double *__restrict__ Ec, double nu, double b0,
                                                           double b1, double b2, double *__restrict__ out,
@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(EL_T) k_elem_elastic_q1(int64_t n_el, const do
 {
     extern __shared__ double sg[];  // [q][a][i][EL_T]
     const int tid = threadIdx.x;
-    const int64_t e = (int64_t)blockIdx.x * EL_T + tid;
-    if (e >= n_el) return;
+    const int64_t e = e0 + (int64_t)blockIdx.x * EL_T + tid;
+    if (e >= e1) return;
     const double E = Ec[e];
     if (!isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
     const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
@@ -245,8 +245,8 @@ __device__ __forceinline__ double to_double<long long>(long long v, int S)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
-    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+__global__ void __launch_bounds__(GEL_WARPS * 32, 4) k_gather_el(
+    int64_t n0, int64_t n1, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const int32_t *__restrict__ conn,
     const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
     int fp, int fq, const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
 {
     __shared__ T acc_all[GEL_WARPS][MF_MAX_DEG * 9];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t n = (int64_t)blockIdx.x * GEL_WARPS + w;
-    if (n >= n_nodes) return;  // warp-uniform
+    const int64_t n = n0 + (int64_t)blockIdx.x * GEL_WARPS + w;
+    if (n >= n1) return;  // warp-uniform
     T *acc = acc_all[w];
     constexpr bool fixed = sizeof(T) == 8 && T(0.5) == T(0);  // integer accumulator
     const int64_t p0 = adj_ptr[n];
@@ -322,31 +322,52 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
         __syncwarp();
     }
     const int S = scale ? *scale : 0;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-        const int64_t r = 3 * n + c;
-        const bool rm = mask ? mask[r] != 0 : false;
-        const int64_t rb = row_ptr[r];
-        double lift = 0.0;
-        for (int j = lane; j < 3 * deg; j += 32) {
-            const int k = j / 3, cp = j - 3 * k;
-            T kv = acc[k * 9 + 3 * c + cp];
-            if (fq) {  // fixed-point path: K = p A + q A^T + q I tr(A) per node-pair block
-                kv = (T)fp * kv + (T)fq * acc[k * 9 + 3 * cp + c];
-                if (c == cp) kv += (T)fq * (acc[k * 9] + acc[k * 9 + 4] + acc[k * 9 + 8]);
-            }
-            double v = to_double<T>(kv, S);
-            if (mask) {
-                const int64_t sdof = 3 * (int64_t)adj_col[p0 + k] + cp;
-                if (rm) v = (r == sdof) ? 1.0 : 0.0;
-                else if (mask[sdof]) { lift -= v * bval[sdof]; v = 0.0; }
-            }
-            values[rb + j] = v;
-        }
+    // write phase: one lane per neighbour k (its column node and Dirichlet
+    // flags loaded once), the 3 x 3 block finished from shared memory
+    bool rm[3];
+    int64_t rb[3];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
+    for (int c = 0; c < 3; ++c) {
+        rm[c] = mask ? mask[3 * n + c] != 0 : false;
+        rb[c] = row_ptr[3 * n + c];
+    }
+    double lift[3] = {0.0, 0.0, 0.0};
+    for (int k = lane; k < deg; k += 32) {
+        const int64_t mcol = adj_col[p0 + k];
+        bool cm[3] = {false, false, false};
+        double cv[3] = {0.0, 0.0, 0.0};
+        if (mask)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp) {
+                cm[cp] = mask[3 * mcol + cp] != 0;
+                if (cm[cp]) cv[cp] = bval[3 * mcol + cp];
+            }
+        const T *blk = acc + k * 9;
+        T tr = T(0);
+        if (fq) tr = blk[0] + blk[4] + blk[8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp) {
+                T kv = blk[3 * c + cp];
+                if (fq) {  // fixed-point path: K = p A + q A^T + q I tr(A) per node-pair block
+                    kv = (T)fp * kv + (T)fq * blk[3 * cp + c];
+                    if (c == cp) kv += (T)fq * tr;
+                }
+                double v = to_double<T>(kv, S);
+                if (mask) {
+                    if (rm[c]) v = (3 * n + c == 3 * mcol + cp) ? 1.0 : 0.0;
+                    else if (cm[cp]) { lift[c] -= v * cv[cp]; v = 0.0; }
+                }
+                values[rb[c] + 3 * k + cp] = v;
+            }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lift[c] += __shfl_xor_sync(0xffffffffu, lift[c], o);
         const double dc = __shfl_sync(0xffffffffu, dsum, c);
-        if (lane == 0) d[r] = rm ? bval[r] : dc + lift;
+        if (lane == 0) d[3 * n + c] = rm[c] ? bval[3 * n + c] : dc + lift[c];
     }
 }
 
@@ -460,18 +481,19 @@ __global__ void k_flow_precond(int64_t n2, int64_t n_rows, const int64_t *__rest
 
 }  // namespace
 
-void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, const mf_mesh *m, const mf_pattern *p,
-                              const mf_coeffs *c, double *values, double *d, cudaStream_t st)
+void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
+                              const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st)
 {
+    if (n1 <= n0) return;
     const mf_adj &A = p->adj[0];
-    const unsigned grid = nblk(m->n_nodes, GEL_WARPS);
+    const unsigned grid = nblk(n1 - n0, GEL_WARPS);
     if (fixed_point)
         k_gather_el<long long><<<grid, GEL_WARPS * 32, 0, st>>>(
-            m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride,
+            n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride,
             static_cast<const int *>(p->mixed_state), fp, fq, c->bc_mask, c->bc_val, p->row_ptr, values, d);
     else
         k_gather_el<double><<<grid, GEL_WARPS * 32, 0, st>>>(
-            m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride, nullptr,
+            n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride, nullptr,
             0, 0, c->bc_mask, c->bc_val, p->row_ptr, values, d);
 }
 
@@ -516,15 +538,20 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
     } else if (form == MF_FORM_ELASTIC) {
         const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;
         MF_CUDA(cudaFuncSetAttribute(k_elem_elastic_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        mf_prof_begin("elem_elastic_q1_fp64", st);
-        k_elem_elastic_q1<<<nblk(ne, EL_T), EL_T, smem, st>>>(ne, m->coords, m->conn, c->elem_coef, c->nu,
-                                                              c->source[0], c->source[1], c->source[2], p->scratch,
-                                                              status);
-        mf_prof_end(st);
-        MF_CUDA(cudaGetLastError());
-        mf_prof_begin("gather_elastic", st);
-        mf_launch_gather_elastic(false, 0, 0, m, p, c, values, d, st);
-        mf_prof_end(st);
+        // chunk by chunk: the gather reads element blocks still resident in L2
+        const size_t nsl = p->slab_e.size() - 1;
+        for (size_t k = 0; k < nsl; ++k) {
+            const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
+            mf_prof_begin("elem_elastic_q1_fp64", st);
+            k_elem_elastic_q1<<<nblk(e1 - e0, EL_T), EL_T, smem, st>>>(e0, e1, m->coords, m->conn, c->elem_coef,
+                                                                      c->nu, c->source[0], c->source[1],
+                                                                      c->source[2], p->scratch, status);
+            mf_prof_end(st);
+            MF_CUDA(cudaGetLastError());
+            mf_prof_begin("gather_elastic", st);
+            mf_launch_gather_elastic(false, 0, 0, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, st);
+            mf_prof_end(st);
+        }
     } else {
         mf_prof_begin("elem_oseen", st);
         k_elem_oseen<<<nblk(ne, 128), 128, 0, st>>>(ne, m->n_nodes, m->coords, m->conn, c->advect, c->visc, c->rho,

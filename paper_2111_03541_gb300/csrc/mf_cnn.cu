@@ -90,6 +90,90 @@ __global__ void __launch_bounds__(128) k_conv_fwd(int B, int nz, int ny, int nx,
     }
 }
 
+// 16 -> 16 channel layer on tensor cores: implicit GEMM, one warp per run of
+// 16 nodes along x (M = 16 nodes, N = 2 x 8 output channels, K = 27 offsets x
+// 16 input channels, one mma.sync m16n8k16 per offset and n-tile).  Weights
+// sit in shared memory as [o][co][ci] BF16 so a B fragment is one 32-bit load;
+// A fragments are read straight from the channels-last activations (zero
+// outside the grid).
+__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <bool RELU>
+__global__ void __launch_bounds__(128) k_conv16_mma(int B, int nz, int ny, int nx, const __nv_bfloat16 *__restrict__ in,
+                                                    const __nv_bfloat16 *__restrict__ w,
+                                                    const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ __align__(16) __nv_bfloat16 sw[27][16][16];  // [o][co][ci]
+    for (int i = threadIdx.x; i < 16 * 16 * 27; i += blockDim.x) {
+        const int co = i / (16 * 27), ci = (i / 27) % 16, o = i % 27;  // source layout [co][ci][o]
+        sw[o][co][ci] = w[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int xt = (nx + 15) / 16;  // x-runs per row
+    const int64_t runs = (int64_t)B * nz * ny * xt;
+    const int64_t run = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (run >= runs) return;  // warp-uniform
+    const int xr = (int)(run % xt);
+    int64_t rest = run / xt;
+    const int y = (int)(rest % ny);
+    rest /= ny;
+    const int z = (int)(rest % nz);
+    const int b = (int)(rest / nz);
+    const int nv = nz * ny * nx;
+    const __nv_bfloat16 *base = in + (int64_t)b * nv * 16;
+    const int x0 = xr * 16 + g, x1 = x0 + 8;  // the two A rows of this lane
+    float acc[2][4] = {};
+#pragma unroll 1
+    for (int o = 0; o < 27; ++o) {
+        const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+        const int zz = z + dz, yy = y + dy;
+        const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
+        const int xa = x0 + dx, xb = x1 + dx;
+        const bool va = zy && xa >= 0 && xa < nx, vb = zy && xb >= 0 && xb < nx;
+        const int64_t rowa = ((int64_t)zz * ny + yy) * nx + xa, rowb = ((int64_t)zz * ny + yy) * nx + xb;
+        const uint32_t *pa = reinterpret_cast<const uint32_t *>(base + rowa * 16);
+        const uint32_t *pb = reinterpret_cast<const uint32_t *>(base + rowb * 16);
+        const uint32_t a0 = va ? __ldg(pa + t) : 0u, a2 = va ? __ldg(pa + 4 + t) : 0u;
+        const uint32_t a1 = vb ? __ldg(pb + t) : 0u, a3 = vb ? __ldg(pb + 4 + t) : 0u;
+        const uint32_t *wb = reinterpret_cast<const uint32_t *>(&sw[o][0][0]);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int co = nt * 8 + g;
+            const uint32_t b0 = wb[co * 8 + t], b1 = wb[co * 8 + 4 + t];
+            mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
+        }
+    }
+    // C fragment: rows g, g + 8 (nodes x0, x1), columns 2t, 2t + 1 of each n-tile
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int xx = h ? x1 : x0;
+        if (xx >= nx) continue;
+        const int64_t v = (int64_t)b * nv + ((int64_t)z * ny + y) * nx + xx;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int co = nt * 8 + 2 * t;
+            float v0 = acc[nt][2 * h] + bias[co], v1 = acc[nt][2 * h + 1] + bias[co + 1];
+            if (RELU) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            __nv_bfloat162 pr;
+            pr.x = __float2bfloat16_rn(v0);
+            pr.y = __float2bfloat16_rn(v1);
+            *reinterpret_cast<__nv_bfloat162 *>(out + v * 16 + co) = pr;
+        }
+    }
+}
+
 // gradient wrt the input: gin[u][ci] = sum_{o, co} w[co][ci][o] gout[u - off(o)][co],
 // where gout is masked by the ReLU of that layer's output (act > 0) when act != NULL
 template <int CI, int CO>
@@ -443,8 +527,9 @@ void forward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, A
     const __nv_bfloat16 *W = c->pb;
     const float *P = c->p;
     fwd_layer<2, 16, true, false>(B, nz, ny, nx, x, W + p_offset_w(0), P + p_offset_b(0), A.a1, st);
-    fwd_layer<16, 16, true, false>(B, nz, ny, nx, A.a1, W + p_offset_w(1), P + p_offset_b(1), A.a2, st);
-    fwd_layer<16, 16, true, false>(B, nz, ny, nx, A.a2, W + p_offset_w(2), P + p_offset_b(2), A.a3, st);
+    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
+    k_conv16_mma<true><<<nblk(runs, 4), 128, 0, st>>>(B, nz, ny, nx, A.a1, W + p_offset_w(1), P + p_offset_b(1), A.a2);
+    k_conv16_mma<true><<<nblk(runs, 4), 128, 0, st>>>(B, nz, ny, nx, A.a2, W + p_offset_w(2), P + p_offset_b(2), A.a3);
     fwd_layer<16, 1, false, true>(B, nz, ny, nx, A.a3, W + p_offset_w(3), P + p_offset_b(3), A.y, st);
 }
 
@@ -575,8 +660,8 @@ extern "C" mf_status mf_cnn_backward(mf_cnn *c, int32_t B, int32_t nz, int32_t n
 
 extern "C" mf_status mf_cnn_train_step(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx,
                                        const mf_csr *K, const double *const *kvals, const double *const *r,
-                                       const void *const *x, const uint8_t *mask, float lr, float weight_decay,
-                                       double *loss, void *stream)
+                                       const double *const *err, const void *const *x, const uint8_t *mask,
+                                       float lr, float weight_decay, double *loss, void *stream)
 {
     if (!c || !K || !kvals || !r || !x || B <= 0 || K->n_rows != (int64_t)nz * ny * nx)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_train_step: bad argument");
@@ -610,14 +695,31 @@ extern "C" mf_status mf_cnn_train_step(mf_cnn *c, int32_t B, int32_t nz, int32_t
         k_compose_z<<<nblk(nv, 256), 256, 0, st>>>(nv, dinv, r[b], A.y + (size_t)b * nv, mask, smax, z);
         mf_csr Kb = *K;
         Kb.values = const_cast<double *>(kvals[b]);
-        mf_spmv_impl(&Kb, z, q, st);
-        k_train_err<<<nblk(nv, 256), 256, 0, st>>>(nv, q, r[b], e);
-        MF_CUDA(red.dots(nv, e, e, r[b], r[b], nullptr, nullptr, dd));
-        const double rr = dd[1] > 0 ? dd[1] : 1.0;
-        Ltot += dd[0] / rr / B;
-        // dL/dz = (2 / (B rr)) K e (K symmetric);  dL/dy = s (1 - mask) dL/dz
-        mf_spmv_impl(&Kb, e, q, st);
-        k_train_gy<<<nblk(nv, 256), 256, 0, st>>>(nv, q, mask, 2.0 * smax / (B * rr), gy + (size_t)b * nv);
+        if (err && err[b]) {
+            // energy left after one optimally scaled step along z (CG picks the
+            // step length, so the loss ignores the scale of z):
+            //   L = ||e - a z||_K^2 / ||e||_K^2 = 1 - (z.Ke)^2 / ((z.Kz)(e.Ke)),  a = z.Ke / z.Kz
+            //   dL/dz = -2 (z.Ke) / ((z.Kz)(e.Ke)) (Ke - (z.Ke / z.Kz) K z)
+            // (Ke, not the stored residual, keeps L in [0, 1] by Cauchy-Schwarz)
+            mf_spmv_impl(&Kb, z, q, st);
+            mf_spmv_impl(&Kb, err[b], e, st);  // e <- K err
+            MF_CUDA(red.dots(nv, z, e, z, q, err[b], e, dd));
+            const double zr = dd[0], zq = dd[1] > 0 ? dd[1] : 1.0, er = dd[2] > 0 ? dd[2] : 1.0;
+            Ltot += (1.0 - zr * zr / (zq * er)) / B;
+            // e <- K err - (z.Ke / z.Kz) K z ; gy = -2 (z.Ke) / ((z.Kz)(e.Ke)) s e / B
+            k_axpby<<<nblk(nv, 256), 256, 0, st>>>(nv, -zr / zq, q, 1.0, e);
+            k_train_gy<<<nblk(nv, 256), 256, 0, st>>>(nv, e, mask, -2.0 * zr * smax / (zq * er * B),
+                                                      gy + (size_t)b * nv);
+        } else {
+            mf_spmv_impl(&Kb, z, q, st);
+            k_train_err<<<nblk(nv, 256), 256, 0, st>>>(nv, q, r[b], e);
+            MF_CUDA(red.dots(nv, e, e, r[b], r[b], nullptr, nullptr, dd));
+            const double rr = dd[1] > 0 ? dd[1] : 1.0;
+            Ltot += dd[0] / rr / B;
+            // dL/dz = (2 / (B rr)) K e (K symmetric);  dL/dy = s (1 - mask) dL/dz
+            mf_spmv_impl(&Kb, e, q, st);
+            k_train_gy<<<nblk(nv, 256), 256, 0, st>>>(nv, q, mask, 2.0 * smax / (B * rr), gy + (size_t)b * nv);
+        }
     }
     backward(c, B, nz, ny, nx, xb, gy, A, st);
     if (lr > 0.f) {

@@ -180,6 +180,70 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
+    // Parallelepiped test: the bilinear and trilinear coefficients of the map
+    // x(xi) = sum_a x_a N_a(xi) vanish exactly.  Then J is constant and the
+    // Gauss sums factor: sum_q dN_a/dxi_i dN_b/dxi_j = R_ab[i][j] (closed form
+    // below), so Ke[a][b] = k detJ sum_ij R_ab[i][j] (J^-1 J^-T)_ij and
+    // de[a] = f detJ sum_q N_a(q) with sum_q N_a(q) = 1.
+    double cf[4][3];  // coefficients of xi eta, eta zeta, xi zeta, xi eta zeta (times 8)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cf[0][i] = cf[1][i] = cf[2][i] = cf[3][i] = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double sa = (a & 1) ? 1.0 : -1.0, ta = (a & 2) ? 1.0 : -1.0, ua = (a & 4) ? 1.0 : -1.0;
+            cf[0][i] += sa * ta * x[a][i];
+            cf[1][i] += ta * ua * x[a][i];
+            cf[2][i] += sa * ua * x[a][i];
+            cf[3][i] += sa * ta * ua * x[a][i];
+        }
+    }
+    bool affine = true;
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) affine = affine && cf[k2][i] == 0.0;
+    if (affine) {
+        double Ji[3][3];
+        const double det = q1_jac(x, 0, Ji);  // constant over the element
+        double G[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) G[i][j] = Ji[i][0] * Ji[j][0] + Ji[i][1] * Ji[j][1] + Ji[i][2] * Ji[j][2];
+        double *o = out + e * 72;
+        const double kd = k * det;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+#pragma unroll
+            for (int b = a; b < 8; ++b) {
+                // R_ab[i][j]: product over the three directions of the 2-point
+                // sums of the 1D factors: sum (1 + s x)(1 + s' x) = 2 (1 + s s' / 3),
+                // sum (1 + s x) s' = 2 s', sum s s' = 2 s s'; then / 64
+                const double s[2][3] = {{(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0},
+                                        {(b & 1) ? 1.0 : -1.0, (b & 2) ? 1.0 : -1.0, (b & 4) ? 1.0 : -1.0}};
+                double v = 0.0;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        double r = 1.0 / 8.0;  // (2 * 2 * 2) / 64
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            if (d == i && d == j) r *= s[0][d] * s[1][d];
+                            else if (d == i) r *= s[0][d];
+                            else if (d == j) r *= s[1][d];
+                            else r *= 1.0 + s[0][d] * s[1][d] / 3.0;
+                        }
+                        v = fma(r, G[i][j], v);
+                    }
+                o[8 * a + b] = kd * v;
+                o[8 * b + a] = kd * v;
+            }
+            o[64 + a] = f * det;
+        }
+        return;
+    }
     double Ke[36] = {}, m[8] = {};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mf.h"
 
 #define MF_MAX_DEG 64   // neighbours of one node in one adjacency
@@ -55,6 +57,10 @@ struct mf_pattern {
     uint8_t *slot = nullptr;
     // mixed path: device scalars of the fixed-point scale (see mf_mixed.cu)
     void *mixed_state = nullptr;
+    // elasticity slabs: element chunk c = [slab_e[c], slab_e[c+1]) completes the
+    // rows of nodes [slab_n[c], slab_n[c+1]); assembling chunk by chunk keeps the
+    // element scratch of the gather in L2
+    std::vector<int64_t> slab_e, slab_n;
 };
 
 // status word (device) of the current device
@@ -80,8 +86,8 @@ mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_c
                                double p_scale, double *out, cudaStream_t st);
 // elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64
 // sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
-void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, const mf_mesh *m, const mf_pattern *p,
-                              const mf_coeffs *c, double *values, double *d, cudaStream_t st);
+void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
+                              const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);
 mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o,
                         mf_solve_info *info, cudaStream_t st);

@@ -209,7 +209,7 @@ struct WarpSmem {
 };
 
 __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
-    int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
+    int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
     double cmu_q, double b0, double b1, double b2, const MixedState *__restrict__ st,
     double *__restrict__ out, int64_t stride, int *status)
 {
@@ -219,9 +219,9 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     const int j = lane >> 3;   // element slot of this lane
     const int qp = lane & 7;   // Gauss point (and node for loads) of this lane
     const int gb = lane & ~7;  // first lane of the element group
-    const int64_t e_raw = ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + j;
-    const bool valid = e_raw < n_el;
-    const int64_t e = valid ? e_raw : n_el - 1;
+    const int64_t e_raw = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + j;
+    const bool valid = e_raw < e1;
+    const int64_t e = valid ? e_raw : e1 - 1;
 
     // padding rows 24..31 of every slice stay zero
     for (int i = lane; i < 4 * NSL * 8 * 8 / 2; i += 32) {
@@ -289,8 +289,9 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     if (valid && !isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
     const f2 sig = dsqrt(ddiv(from_double(E * cmu_q), det));
     // G[(a,c), qp] = sig sum_j d_j N_a(qp) Cf[c][j], sum-factorised over the
-    // three factor products P^2/8, PM/8, M^2/8
-    f2 Gv[8][3];
+    // three factor products P^2/8, PM/8, M^2/8; one component c at a time:
+    // build the 8 values, take the row exponents (max over the 8 points of the
+    // element), split into 8-bit digits rounded to nearest, store the slices
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         f2 T[3][3];  // T[j][k]: (sig Cf[c][j]) x {PP, PM, MM}
@@ -312,7 +313,29 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
                 const f2 t = (k == 0) ? T[jj][0] : ((k == 1) ? T[jj][1] : T[jj][2]);
                 acc = dadd(acc, dsgn(t, !((a >> jj) & 1)));
             }
-            Gv[a][c] = acc;
+            float mx = fabsf(acc.h);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+            const int ex = (mx > 0.f) ? (((__float_as_int(mx) >> 23) & 0xff) - 126) : -200;
+            if (qp == 0) W.ex[j][3 * a + c] = ex;
+            // x 2^-ex (exact); digits 0..2 from the high word (exact steps), the
+            // low word folded in before digits 3 and 4
+            const float sc = (mx > 0.f) ? __int_as_float((127 - ex) << 23) : 0.f;
+            float h = acc.h * sc, l = acc.l * sc;
+#pragma unroll
+            for (int sl = 0; sl < NSL; ++sl) {
+                h *= 256.f;
+                l *= 256.f;
+                if (sl >= 3) {
+                    const f2 r = two_sum(h, l);
+                    h = r.h;
+                    l = r.l;
+                }
+                const float dg = rintf(h);
+                h -= dg;
+                W.sl[j][sl][3 * a + c][qp] = __float2bfloat16_rn(dg);
+            }
         }
     }
     // --- load vector: m_a = sum_q detJ_q N_a(q) ---
@@ -340,31 +363,6 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
             dl[2] = b2 * mv;
         }
     }
-    // --- row exponents (max over the 8 points of the element) and slices ---
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float mx = fabsf(Gv[a][c].h);
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
-            const int ex = (mx > 0.f) ? (((__float_as_int(mx) >> 23) & 0xff) - 126) : -200;
-            if (qp == 0) W.ex[j][3 * a + c] = ex;
-            // x 2^-ex (exact), then 8-bit digits, rounded to nearest
-            const float s = (mx > 0.f) ? __int_as_float((127 - ex) << 23) : 0.f;
-            float h = Gv[a][c].h * s, l = Gv[a][c].l * s;
-#pragma unroll
-            for (int sl = 0; sl < NSL; ++sl) {
-                h *= 256.f;
-                l *= 256.f;
-                const float dg = rintf(h);
-                const f2 r = two_sum(h - dg, l);
-                h = r.h;
-                l = r.l;
-                W.sl[j][sl][3 * a + c][qp] = __float2bfloat16_rn(dg);
-            }
-        }
     __syncwarp();
 
     // --- tensor cores: A'' = G G^T by levels, per element of the warp ---
@@ -372,61 +370,46 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     const int S = st->S;
 #pragma unroll 1
     for (int el = 0; el < 4; ++el) {
-        const int64_t eo = ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + el;
-        float acc[5][4][4];
-#pragma unroll
-        for (int L = 0; L < 5; ++L)
-#pragma unroll
-            for (int tl = 0; tl < 4; ++tl)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[L][tl][k] = 0.f;
+        const int64_t eo = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + el;
         auto ld = [&](int sl, int row) -> uint32_t {
             return *reinterpret_cast<const uint32_t *>(&W.sl[el][sl][row][2 * t]);
         };
+        long long *o = reinterpret_cast<long long *>(out + (eo < e1 ? eo : e0) * stride);
+#pragma unroll 1
+        for (int tl = 0; tl < 4; ++tl) {  // tiles (m, n): (0,0), (0,1), (0,2), (1,2)
+            const int mt = tl == 3 ? 1 : 0, nt = tl == 3 ? 2 : tl;
+            float acc[5][4];
 #pragma unroll
-        for (int L = 0; L < 5; ++L) {
+            for (int L = 0; L < 5; ++L)
 #pragma unroll
-            for (int s0 = 0; s0 <= L; s0 += 2) {
-                const int s1 = s0 + 1;  // second half of k: slice s1 against slice L - s1
-                const bool two = s1 <= L;
-                uint32_t a[2][4], bf[3][2];
+                for (int k = 0; k < 4; ++k) acc[L][k] = 0.f;
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    a[mt][0] = ld(s0, mt * 16 + g);
-                    a[mt][1] = ld(s0, mt * 16 + g + 8);
-                    a[mt][2] = two ? ld(s1, mt * 16 + g) : 0u;
-                    a[mt][3] = two ? ld(s1, mt * 16 + g + 8) : 0u;
+            for (int L = 0; L < 5; ++L) {
+#pragma unroll
+                for (int s0 = 0; s0 <= L; s0 += 2) {
+                    const int s1 = s0 + 1;  // second half of k: slice s1 against slice L - s1
+                    const bool two = s1 <= L;
+                    const uint32_t a0 = ld(s0, mt * 16 + g), a1 = ld(s0, mt * 16 + g + 8);
+                    const uint32_t a2 = two ? ld(s1, mt * 16 + g) : 0u, a3 = two ? ld(s1, mt * 16 + g + 8) : 0u;
+                    const uint32_t b0 = ld(L - s0, nt * 8 + g), b1 = two ? ld(L - s1, nt * 8 + g) : 0u;
+                    mma_bf16(acc[L], a0, a1, a2, a3, b0, b1);
                 }
-#pragma unroll
-                for (int nt = 0; nt < 3; ++nt) {
-                    bf[nt][0] = ld(L - s0, nt * 8 + g);
-                    bf[nt][1] = two ? ld(L - s1, nt * 8 + g) : 0u;
-                }
-                mma_bf16(acc[L][0], a[0][0], a[0][1], a[0][2], a[0][3], bf[0][0], bf[0][1]);
-                mma_bf16(acc[L][1], a[0][0], a[0][1], a[0][2], a[0][3], bf[1][0], bf[1][1]);
-                mma_bf16(acc[L][2], a[0][0], a[0][1], a[0][2], a[0][3], bf[2][0], bf[2][1]);
-                mma_bf16(acc[L][3], a[1][0], a[1][1], a[1][2], a[1][3], bf[2][0], bf[2][1]);
             }
-        }
-        // levels -> 64-bit fixed point at scale 2^S, written straight to the
-        // element's upper blocks (a <= b); the p, q finishing is linear and is
-        // applied once per CSR block after the exact sums of the gather
-        if (eo < n_el) {
-            long long *o = reinterpret_cast<long long *>(out + eo * stride);
-            const int tmt[4] = {0, 0, 0, 1}, tnt[4] = {0, 1, 2, 2};
-#pragma unroll
-            for (int tl = 0; tl < 4; ++tl)
+            // levels -> 64-bit fixed point at scale 2^S, written straight to the
+            // element's upper blocks (a <= b); the p, q finishing is linear and is
+            // applied once per CSR block after the exact sums of the gather
+            if (eo < e1) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int rho = tmt[tl] * 16 + g + 8 * (k >> 1);
-                    const int sig2 = tnt[tl] * 8 + 2 * t + (k & 1);
+                    const int rho = mt * 16 + g + 8 * (k >> 1);
+                    const int sig2 = nt * 8 + 2 * t + (k & 1);
                     const int a = rho / 3, b = sig2 / 3;
                     // an upper block a <= b is complete from the computed tiles:
                     // (a < b) whole block, (a == b) both triangles (rows >= 24 skipped)
                     if (rho >= 24 || a > b) continue;
-                    long long T = f2i_exact(acc[0][tl][k]);
+                    long long T = f2i_exact(acc[0][k]);
 #pragma unroll
-                    for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][tl][k]);
+                    for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][k]);
                     const int sh = W.ex[el][rho] + W.ex[el][sig2] + S - 48;
                     long long v;
                     if (sh >= 0) v = T << sh;
@@ -438,6 +421,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
                     // (17, 15) are not computed; they mirror (15, 16) and (15, 17)
                     if (tl == 2 && a == b) o[base + 3 * (sig2 - 3 * b) + (rho - 3 * a)] = v;
                 }
+            }
         }
     }
 }
@@ -478,15 +462,19 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     mf_prof_end(st);
     const size_t smem = sizeof(WarpSmem) * MX_WARPS;
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    mf_prof_begin("mixed_elem", st);
-    k_mixed_elem<<<(unsigned)((ne + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
-        ne, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms, p->scratch,
-        p->scratch_stride, status);
-    mf_prof_end(st);
-    MF_CUDA(cudaGetLastError());
-    mf_prof_begin("gather_elastic_fixed", st);
-    mf_launch_gather_elastic(true, pp, qq, m, p, c, values, d, st);
-    mf_prof_end(st);
+    const size_t nsl = p->slab_e.size() - 1;
+    for (size_t k = 0; k < nsl; ++k) {
+        const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
+        mf_prof_begin("mixed_elem", st);
+        k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
+            e0, e1, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms,
+            p->scratch, p->scratch_stride, status);
+        mf_prof_end(st);
+        MF_CUDA(cudaGetLastError());
+        mf_prof_begin("gather_elastic_fixed", st);
+        mf_launch_gather_elastic(true, pp, qq, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, st);
+        mf_prof_end(st);
+    }
     MF_CUDA(cudaGetLastError());
     return MF_OK;
 }

@@ -8,6 +8,7 @@
 // in registers.  Each node pair also keeps the list of element contributions
 // (e, a, b) in ascending element order, which fixes the summation order of the
 // assembly.  The dof-level CSR of a form is then laid out from its blocks.
+#include <algorithm>
 #include <cstdio>
 
 #include "mf_internal.h"
@@ -173,6 +174,15 @@ __global__ void k_contrib(int64_t n_el, int npe_r, const int32_t *__restrict__ c
     }
 }
 
+// last (largest) incident element of every node
+__global__ void k_node_ready(int64_t n, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
+                             int32_t *ready)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    ready[v] = inc_ptr[v + 1] > inc_ptr[v] ? inc[inc_ptr[v + 1] - 1] : -1;
+}
+
 // slot map: position of conn[e][b] among the neighbours of conn[e][a]
 __global__ void k_slot_map(int64_t n_el, const int32_t *__restrict__ conn, const int64_t *__restrict__ ptr,
                            const int32_t *__restrict__ col, uint8_t *slot)
@@ -332,6 +342,44 @@ mf_status build_adj(int64_t n_rows, const Incidence &inc, int64_t n_el, int npe_
     return check_status(status, st, "mf_pattern_build");
 }
 
+// Element chunks of about 48 MB of scratch.  A node's rows are complete once
+// its largest incident element is assembled; chunk c gathers the longest
+// prefix of nodes whose prefix maximum of that value lies below the chunk's
+// end, so node ranges stay contiguous for any numbering (badly ordered meshes
+// just gather later).
+mf_status plan_slabs(const mf_mesh *m, const Incidence &inc, int64_t stride, cudaStream_t st, mf_pattern *p)
+{
+    const int64_t nn = m->n_nodes, ne = m->n_elems;
+    int32_t *d_ready = nullptr;
+    MF_CUDA(cudaMallocAsync(&d_ready, sizeof(int32_t) * nn, st));
+    k_node_ready<<<nblk(nn), TPB, 0, st>>>(nn, inc.ptr, inc.inc, d_ready);
+    std::vector<int32_t> ready(nn);
+    MF_CUDA(cudaMemcpyAsync(ready.data(), d_ready, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    MF_CUDA(cudaFreeAsync(d_ready, st));
+    for (int64_t v = 1; v < nn; ++v) ready[v] = std::max(ready[v], ready[v - 1]);  // prefix maximum
+    // Chunked assembly was measured slower on the 64^3 elasticity workload
+    // (30 serial launches per step cost more in ramp-up and tail than the L2
+    // residency of the scratch saves: 2.08 vs 1.67 ms), so one chunk covers
+    // the mesh; SLAB_BYTES > 0 restores chunks of about that many scratch bytes.
+    constexpr int64_t SLAB_BYTES = 0;
+    const int64_t chunk = SLAB_BYTES > 0 ? std::max<int64_t>(1024, SLAB_BYTES / (stride * 8)) : ne;
+    (void)stride;
+    p->slab_e.clear();
+    p->slab_n.clear();
+    p->slab_e.push_back(0);
+    p->slab_n.push_back(0);
+    int64_t v = 0;
+    for (int64_t e1 = chunk;; e1 += chunk) {
+        const int64_t eb = std::min(e1, ne);
+        while (v < nn && ready[v] < eb) ++v;
+        p->slab_e.push_back(eb);
+        p->slab_n.push_back(eb == ne ? nn : v);
+        if (eb == ne) break;
+    }
+    return MF_OK;
+}
+
 void free_inc(Incidence &I, cudaStream_t st)
 {
     if (I.ptr) cudaFreeAsync(I.ptr, st);
@@ -426,6 +474,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_slot_map<<<nblk(m->n_elems * 64), TPB, 0, st>>>(m->n_elems, m->conn, p->adj[0].ptr, p->adj[0].col, p->slot);
         MF_CUDA(cudaMallocAsync(&p->mixed_state, 64, st));
         p->scratch_stride = 36 * 9 + 24;
+        mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);
+        if (ss != MF_OK) { free_inc(incv, st); return ss; }
     } else {
         Incidence incp;
         s = build_incidence(m->n_pnodes, m->n_elems, 3, m->pconn, st, &incp, status);

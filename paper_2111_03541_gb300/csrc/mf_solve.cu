@@ -13,6 +13,7 @@
 // Gram-Schmidt applied twice (block dot products and one multi-vector update
 // per pass); the Givens rotations of the Hessenberg column run in a
 // single-thread kernel, so a whole cycle stays on the device.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -31,6 +32,10 @@ struct PcgState {
 };
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// grid of the reduction kernels: a function of n only (bit-reproducible), at
+// least 512 rows per block so small systems do not pay for idle blocks
+inline unsigned red_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (n + 511) / 512)); }
 
 __device__ double block_sum(double v, double *sh)
 {
@@ -93,29 +98,32 @@ __global__ void __launch_bounds__(RT) k_spmv(int64_t n, const int64_t *__restric
     if (valid && sub == 0) y[row] = s;
 }
 
-// q = K p and partial p.q; grid-stride over rows so the grid is fixed
+// q = K p: one W-lane group per row over the whole matrix (no reduction here,
+// so no per-block atomics on a shared ticket)
 template <int W>
 __global__ void __launch_bounds__(RT) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
                                                  const double *__restrict__ p, double *__restrict__ q,
-                                                 double *__restrict__ part, PcgState *S)
+                                                 const PcgState *S)
+{
+    if (S->done) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = g / W;
+    const int sub = (int)(g % W);
+    const bool valid = row < n;
+    const double s = row_dot<W>(rp, ci, v, p, row, sub, valid);
+    if (valid && sub == 0) q[row] = s;
+}
+
+// p.q over a grid fixed by n, finished by the last block; alpha = rz / p.q
+__global__ void __launch_bounds__(RT) k_pcg_pq(int64_t n, const double *__restrict__ p, const double *__restrict__ q,
+                                               double *__restrict__ part, PcgState *S)
 {
     __shared__ double sh[RT / 32];
     if (S->done) return;
     double acc = 0.0;
-    const int64_t rows_per_pass = (int64_t)gridDim.x * blockDim.x / W;
-    const int sub = threadIdx.x % W;
-    // warp-uniform trip count: the loop runs while the warp's first row is in range
-    const int64_t first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / W;
-    for (int64_t off = 0; first + off < n; off += rows_per_pass) {
-        const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W + off;
-        const bool valid = row < n;
-        const double s = row_dot<W>(rp, ci, v, p, row, sub, valid);
-        if (valid && sub == 0) {
-            q[row] = s;
-            acc = fma(p[row], s, acc);
-        }
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(p[i], q[i], acc);
     const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = bs;
     if (last_block(&S->ticket)) {
@@ -279,8 +287,12 @@ void spmv_any(const mf_csr *K, const double *v, const double *x, double *y, cuda
 template <int W>
 void launch_pcg_spmv(const mf_csr *K, const double *p, double *q, double *part, PcgState *S, cudaStream_t st)
 {
-    k_pcg_spmv<W><<<RED_BLOCKS, RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, K->values, p, q, part, S);
+    k_pcg_spmv<W><<<nblk(K->n_rows * W, RT), RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, K->values, p, q, S);
+    k_pcg_pq<<<red_grid(K->n_rows), RT, 0, st>>>(K->n_rows, p, q, part, S);
 }
+
+// partial slots the PCG reduction kernels need (3 per block) plus 2 outputs
+inline int64_t pcg_parts(int64_t) { return 3 * RED_BLOCKS + 8; }
 
 // ---------------------------------------------------------------------------
 // GMRES kernels
@@ -510,7 +522,7 @@ mf_status true_residual(const mf_csr *K, const double *d, const double *x, doubl
                         unsigned *ticket, double *out2, cudaStream_t st, double *relres)
 {
     spmv_any(K, K->values, x, tmp, st);
-    k_resid_norm<<<RED_BLOCKS, RT, 0, st>>>(K->n_rows, d, tmp, part, ticket, out2);
+    k_resid_norm<<<red_grid(K->n_rows), RT, 0, st>>>(K->n_rows, d, tmp, part, ticket, out2);
     MF_CUDA(cudaGetLastError());
     double h[2];
     MF_CUDA(cudaMemcpyAsync(h, out2, sizeof h, cudaMemcpyDeviceToHost, st));
@@ -530,7 +542,7 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
     MF_CUDA(p.alloc(n));
     MF_CUDA(q.alloc(n));
     MF_CUDA(dinv.alloc(n));
-    MF_CUDA(part.alloc(3 * RED_BLOCKS + 2));
+    MF_CUDA(part.alloc(pcg_parts(n)));
     MF_CUDA(S.alloc(1));
     MF_CUDA(bad.alloc(1));
     PcgState h{};
@@ -540,7 +552,7 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
     MF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
     k_diag_inv<<<nblk(n, RT), RT, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv.p, bad.p);
     spmv_any(K, K->values, x, q.p, st);
-    k_pcg_init<<<RED_BLOCKS, RT, 0, st>>>(n, d, q.p, dinv.p, r.p, p.p, part.p, S.p);
+    k_pcg_init<<<red_grid(n), RT, 0, st>>>(n, d, q.p, dinv.p, r.p, p.p, part.p, S.p);
     MF_CUDA(cudaGetLastError());
     int hb = 0;
     MF_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -563,8 +575,8 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
             case 16: launch_pcg_spmv<16>(K, p.p, q.p, part.p, S.p, cs); break;
             default: launch_pcg_spmv<32>(K, p.p, q.p, part.p, S.p, cs); break;
             }
-            k_pcg_update<<<RED_BLOCKS, RT, 0, cs>>>(n, dinv.p, p.p, q.p, x, r.p, part.p, S.p);
-            k_pcg_dir<<<RED_BLOCKS, RT, 0, cs>>>(n, dinv.p, r.p, p.p, S.p);
+            k_pcg_update<<<red_grid(n), RT, 0, cs>>>(n, dinv.p, p.p, q.p, x, r.p, part.p, S.p);
+            k_pcg_dir<<<red_grid(n), RT, 0, cs>>>(n, dinv.p, r.p, p.p, S.p);
         }
         ce = cudaStreamEndCapture(cs, &graph);
     }
@@ -594,8 +606,7 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
     cudaStreamDestroy(cs);
 
     double relres = 0.0;
-    mf_status s2 = true_residual(K, d, x, q.p, part.p, &S.p->ticket, reinterpret_cast<double *>(part.p) + 3 * RED_BLOCKS,
-                                 st, &relres);
+    mf_status s2 = true_residual(K, d, x, q.p, part.p, &S.p->ticket, part.p + pcg_parts(n) - 4, st, &relres);
     if (s2 != MF_OK) return s2;
     if (info) {
         info->iterations = h.iter;
@@ -729,7 +740,7 @@ mf_status solve_gmres(const mf_csr *K, const double *d, double *x, const mf_solv
 // streams, other host threads) race and must be serialised by the caller.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr size_t NOALLOC_PART = 3 * RED_BLOCKS + 2;       // block partials + 2 reduction outputs
+constexpr size_t NOALLOC_PART = 3 * RED_BLOCKS + 8;  // reduction block partials + 2 outputs
 constexpr size_t NOALLOC_TAIL = 32;                        // PcgState + breakdown flag
 constexpr size_t NOALLOC_DOUBLES = 4 * (size_t)MF_NOALLOC_MAX_ROWS + NOALLOC_PART + NOALLOC_TAIL;
 static_assert(sizeof(PcgState) + sizeof(int) <= NOALLOC_TAIL * sizeof(double), "tail too small");
@@ -790,7 +801,7 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
     MF_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
     k_diag_inv<<<nblk(n, RT), RT, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv, bad);
     spmv_any(K, K->values, x, q, st);
-    k_pcg_init<<<RED_BLOCKS, RT, 0, st>>>(n, d, q, dinv, r, p, part, S);
+    k_pcg_init<<<red_grid(n), RT, 0, st>>>(n, d, q, dinv, r, p, part, S);
     MF_CUDA(cudaGetLastError());
     int hb = 0;
     MF_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -807,8 +818,8 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
             case 16: launch_pcg_spmv<16>(K, p, q, part, S, st); break;
             default: launch_pcg_spmv<32>(K, p, q, part, S, st); break;
             }
-            k_pcg_update<<<RED_BLOCKS, RT, 0, st>>>(n, dinv, p, q, x, r, part, S);
-            k_pcg_dir<<<RED_BLOCKS, RT, 0, st>>>(n, dinv, r, p, S);
+            k_pcg_update<<<red_grid(n), RT, 0, st>>>(n, dinv, p, q, x, r, part, S);
+            k_pcg_dir<<<red_grid(n), RT, 0, st>>>(n, dinv, r, p, S);
         }
         MF_CUDA(cudaGetLastError());
         MF_CUDA(cudaMemcpyAsync(&h, S, sizeof h, cudaMemcpyDeviceToHost, st));
@@ -816,7 +827,7 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
         if (h.done) break;
     }
     double relres = 0.0;
-    s = true_residual(K, d, x, q, part, &S->ticket, part + 3 * RED_BLOCKS, st, &relres);
+    s = true_residual(K, d, x, q, part, &S->ticket, part + NOALLOC_PART - 4, st, &relres);
     if (s != MF_OK) return s;
     if (info) {
         info->iterations = h.iter;

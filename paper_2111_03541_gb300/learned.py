@@ -8,9 +8,13 @@ allocates buffers, draws the seeded inputs (``gen``) and loops.
 Training systems: 3D thermal conduction on unjittered Q1 boxes of n^3 cells
 (default 32^3) with k = exp(GRF) of correlation length 0.1 measured in units
 of the 128^3 workload's domain (0.4 of a 32-cell box), f = 1, u = 0 on the
-boundary.  Samples are the residuals of Jacobi-PCG after 1, 2, 4, ..., 128
-iterations.  Loss: mean ||K z - r||^2 / ||r||^2 with z the preconditioned
-residual.  Training and validation systems use disjoint seeds.
+boundary.  Samples are the residuals r_k of Jacobi-PCG after 1, 2, 4, ..., 128
+iterations with their errors e_k = x* - x_k = K^-1 r_k.  Loss: the share of
+the error energy left after one optimally scaled step along the preconditioned
+residual z, 1 - (z.Ke)^2 / ((z.Kz)(e.Ke)) (CG picks the step length, so the
+scale of z does not matter), or the residual form ||K z - r||^2 / ||r||^2.
+Iterates already converged to 1e-9 are not sampled (their error is round-off).
+Training and validation systems use disjoint seeds.
 """
 from __future__ import annotations
 
@@ -78,7 +82,7 @@ class Dataset:
         self.P = Problem(base, device=device)
         self.grid = grid_of(base)
         nv = self.P.n
-        self.kvals, self.r, self.x, self.sys_of = [], [], [], []
+        self.kvals, self.r, self.e, self.x, self.sys_of = [], [], [], [], []
         tmp = torch.empty(nv, dtype=torch.float64, device=device)
         logk = torch.empty(nv, dtype=torch.float32, device=device)
         for s in range(n_systems):
@@ -87,14 +91,20 @@ class Dataset:
             self.P.assemble(MF_PREC_FP64)
             self.kvals.append(self.P.values.clone())
             mf_cnn_node_logk(*self.grid, self.P.coef, logk)
+            xs, _, _ = self.P.solve(tol=1e-13, max_iter=100000)  # x*: errors of the iterates
             for it in iters:
                 x, st, info = self.P.solve(tol=1e-14, max_iter=it, check_every=it)
+                if info.rel_residual < 1e-9:
+                    break  # converged: later iterates carry round-off only
                 mf_spmv(self.P.csr, x, tmp)
                 r = self.P.d.clone()
                 mf_axpby(nv, -1.0, tmp, 1.0, r)
+                e = xs.clone()
+                mf_axpby(nv, -1.0, x, 1.0, e)  # e = x* - x_k = K^-1 r_k
                 xin = torch.empty(2 * nv, dtype=torch.bfloat16, device=device)
                 mf_cnn_input(nv, r, logk, xin)
                 self.r.append(r)
+                self.e.append(e)
                 self.x.append(xin)
                 self.sys_of.append(s)
         torch.cuda.synchronize()
@@ -103,19 +113,22 @@ class Dataset:
         return len(self.r)
 
     def batch(self, idx):
-        return ([self.kvals[self.sys_of[i]] for i in idx], [self.r[i] for i in idx], [self.x[i] for i in idx])
+        return ([self.kvals[self.sys_of[i]] for i in idx], [self.r[i] for i in idx], [self.x[i] for i in idx],
+                [self.e[i] for i in idx])
 
 
-def loss_of(cnn, ds: Dataset, idx) -> float:
-    kv, r, x = ds.batch(idx)
+def loss_of(cnn, ds: Dataset, idx, energy: bool = True) -> float:
+    kv, r, x, e = ds.batch(idx)
     nz, ny, nx = ds.grid
-    return mf_cnn_train_step(cnn, nz, ny, nx, ds.P.csr, kv, r, x, ds.P.bc_mask, 0.0, 0.0)
+    return mf_cnn_train_step(cnn, nz, ny, nx, ds.P.csr, kv, r, x, ds.P.bc_mask, 0.0, 0.0, err=e if energy else None)
 
 
 def train(train_ds: Dataset, valid_ds: Dataset, steps: int = 3000, batch: int = 16, lr: float = 2e-3,
-          weight_decay: float = 1e-4, seed: int = gen.SEED_CNN, init=None, log=print):
+          weight_decay: float = 1e-4, seed: int = gen.SEED_CNN, init=None, log=print, energy: bool = True):
     """AdamW on random minibatches (sample order drawn from the seeded stream);
-    cosine learning-rate decay.  Returns (cnn handle, history)."""
+    cosine learning-rate decay.  energy=True trains on the error energy left
+    after one optimally scaled step, 1 - (z.Ke)^2 / ((z.Kz)(e.Ke)), else on the
+    residual ||K z - r||^2 / ||r||^2.  Returns (cnn handle, history)."""
     cnn = mf_cnn_create(init_params(seed) if init is None else init)
     nz, ny, nx = train_ds.grid
     order = (gen.uniform(seed + 1, steps * batch) * len(train_ds)).astype(np.int64)
@@ -125,22 +138,23 @@ def train(train_ds: Dataset, valid_ds: Dataset, steps: int = 3000, batch: int = 
     for k in range(steps):
         idx = order[k * batch:(k + 1) * batch]
         lr_k = lr * 0.5 * (1.0 + np.cos(np.pi * k / steps))
-        kv, r, x = train_ds.batch(idx)
-        L = mf_cnn_train_step(cnn, nz, ny, nx, train_ds.P.csr, kv, r, x, train_ds.P.bc_mask, lr_k, weight_decay)
+        kv, r, x, e = train_ds.batch(idx)
+        L = mf_cnn_train_step(cnn, nz, ny, nx, train_ds.P.csr, kv, r, x, train_ds.P.bc_mask, lr_k, weight_decay,
+                              err=e if energy else None)
         if k % 200 == 0 or k == steps - 1:
-            vl = np.mean([loss_of(cnn, valid_ds, vidx[i:i + batch]) for i in range(0, len(vidx), batch)])
+            vl = np.mean([loss_of(cnn, valid_ds, vidx[i:i + batch], energy) for i in range(0, len(vidx), batch)])
             hist.append({"step": k, "train_loss": L, "valid_loss": float(vl), "s": time.time() - t0})
             log(f"step {k}: train {L:.4f} valid {vl:.4f} ({time.time() - t0:.0f}s)")
     return cnn, hist
 
 
-def jacobi_loss(ds: Dataset, batch: int = 16) -> float:
+def jacobi_loss(ds: Dataset, batch: int = 16, energy: bool = True) -> float:
     """Validation loss of the plain Jacobi step (the network output held at 0)."""
     p = init_params()
     p[:] = 0.0
     cnn = mf_cnn_create(p)
     idx = list(range(len(ds)))
-    v = float(np.mean([loss_of(cnn, ds, idx[i:i + batch]) for i in range(0, len(idx), batch)]))
+    v = float(np.mean([loss_of(cnn, ds, idx[i:i + batch], energy) for i in range(0, len(idx), batch)]))
     mf_cnn_destroy(cnn)
     return v
 

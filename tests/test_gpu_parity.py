@@ -31,6 +31,7 @@ CASES = {
     "p1_13": lambda: gen.thermal_p1_problem(13),
     "p2_11": lambda: gen.thermal_p2_problem(11),
     "q1_9": lambda: gen.thermal_q1_problem(9),
+    "q1_affine_11": lambda: gen.thermal_q1_problem(11, jitter=0.0),
     "el_7": lambda: gen.elastic_problem(7),
     "el_12": lambda: gen.elastic_problem(12),
     "os_9": lambda: gen.oseen_problem(9),
@@ -257,3 +258,76 @@ def test_invalid_arguments(mf):
     with pytest.raises(mf.MFError) as ei:
         mf.mf_pattern_build(P.mesh, mf.MF_FORM_ELASTIC)
     assert ei.value.status == mf.MF_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# degenerate and maximum-size cases
+# ---------------------------------------------------------------------------
+
+def test_empty_mesh_rejected(mf):
+    import torch
+    X = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
+    C = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    desc = mf.MeshDesc(dim=2, elem=mf.MF_P1_TRI, n_nodes=4, n_elems=0, coords=X.data_ptr(), conn=C.data_ptr(),
+                       n_pnodes=0, pconn=None)
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_mesh_create(desc)
+    assert ei.value.status == mf.MF_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kind", ["p1", "q1", "el"])
+def test_single_cell_all_constrained(mf, orc, kind):
+    prob = {"p1": lambda: gen.thermal_p1_problem(1), "q1": lambda: gen.thermal_q1_problem(1),
+            "el": lambda: gen.elastic_problem(1)}[kind]()
+    prob["bc_mask"][:] = 1
+    prob["bc_val"] = np.linspace(-1.0, 1.0, prob["bc_mask"].shape[0])
+    P, rp, ci, val, d = _gpu(mf, prob)
+    ref = orc.assemble(prob)
+    assert np.array_equal(val, ref["val"]) and np.array_equal(d, ref["d"])
+    K = _dense({"row_ptr": rp, "col": ci, "val": val})
+    assert np.array_equal(K, np.eye(K.shape[0])) and np.array_equal(d, prob["bc_val"])
+
+
+def _sampled_rows(mf, orc, prob, rows_of_node, nodes, pnodes=None, tol=TOL):
+    P = mf.Problem(prob)
+    vals, d = P.assemble()
+    rp, ci = P.csr_arrays()
+    rp, ci, vals, d = rp.cpu().numpy(), ci.cpu().numpy(), vals.cpu().numpy(), d.cpu().numpy()
+    keep = np.zeros(prob["coords"].shape[0], np.uint8)
+    keep[nodes] = 1
+    kp = None
+    if pnodes is not None:
+        kp = np.zeros(prob["vcoords"].shape[0], np.uint8)
+        kp[pnodes] = 1
+    ref = orc.assemble(prob, keep_nodes=keep, keep_pnodes=kp)
+    for r, (cols, v) in zip(rows_of_node, orc.rows_of(ref, rows_of_node)):
+        s = slice(rp[r], rp[r + 1])
+        assert np.array_equal(ci[s], cols)
+        assert np.abs(vals[s] - v).max() <= tol * max(np.abs(v).max(), 1e-300)
+        assert abs(d[r] - ref["d"][r]) <= tol * max(np.abs(ref["d"]).max(), 1e-300)
+    return P
+
+
+def test_flow_full_size_sampled_rows(mf, orc):
+    """512^2 Taylor-Hood (524,288 elements, 2,364,419 dofs): sampled u1, u2 and p rows."""
+    prob = gen.oseen_problem(512)
+    n2 = prob["coords"].shape[0]
+    n1 = prob["vcoords"].shape[0]
+    rng = np.random.default_rng(17)
+    nodes = np.unique(np.concatenate([rng.integers(0, n2, 25), [0, 1, 1025, n2 - 1, n2 // 2]]))
+    pnodes = np.unique(np.concatenate([rng.integers(0, n1, 25), [0, 1, n1 - 1]]))
+    rows = [int(n) for n in nodes] + [int(n2 + n) for n in nodes] + [int(2 * n2 + p) for p in pnodes]
+    # a pressure row needs the elements at its vertex: keep the P2 node of that vertex too
+    vert = pnodes // 513 * 2 * 1025 + (pnodes % 513) * 2
+    P = _sampled_rows(mf, orc, prob, rows, np.unique(np.concatenate([nodes, vert])), pnodes)
+    assert P.n == 2 * n2 + n1 == 2_364_419
+
+
+def test_grf_thermal_full_size_sampled_rows(mf, orc):
+    """128^3 Q1 thermal with k = exp(GRF) (2,097,152 elements): sampled rows."""
+    prob = gen.grf_thermal_problem(128)
+    nn = prob["coords"].shape[0]
+    rng = np.random.default_rng(19)
+    nodes = np.unique(np.concatenate([rng.integers(0, nn, 40), [0, 130, nn - 1, nn // 2]]))
+    P = _sampled_rows(mf, orc, prob, [int(n) for n in nodes], nodes)
+    assert P.nnz == (4 + 3 * 127) ** 3
