@@ -41,10 +41,11 @@ __global__ void k_elem_thermal_p2(int64_t n_el, const double *__restrict__ X, co
 __global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const double *__restrict__ X,
                                                          const int32_t *__restrict__ conn,
                                                          const double *__restrict__ kc, double f,
-                                                         double *__restrict__ out, int *status)
+                                                         const uint8_t *__restrict__ tr, double *__restrict__ out,
+                                                         int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n_el) elem_thermal_q1(e, X, conn, kc, f, out, status);
+    if (e < n_el && !q1_translate(e, tr, kc, status)) elem_thermal_q1(e, X, conn, kc, f, out, status);
 }
 
 // Q1 elasticity, one element per thread.  The scaled gradients
@@ -191,19 +192,27 @@ __global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, co
 }
 
 // ---------------------------------------------------------------------------
-// gather: one warp per row node; lanes over the node's column entries
+// thermal gather: one warp per node (gather_row_th)
 // ---------------------------------------------------------------------------
-template <int BS>
-__global__ void __launch_bounds__(256) k_gather(int64_t n_nodes, const int64_t *__restrict__ ptr,
-                                                const int32_t *__restrict__ col, const int64_t *__restrict__ cptr,
-                                                const int32_t *__restrict__ clist, const double *__restrict__ sc,
-                                                int64_t stride, int npe, const uint8_t *__restrict__ mask,
-                                                const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
-                                                double *__restrict__ values, double *__restrict__ d)
+constexpr int GT_WARPS = 8;
+
+template <int NPE>
+__global__ void __launch_bounds__(GT_WARPS * 32, 3) k_gather_th(
+    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+    const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
+    const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const uint8_t *__restrict__ tr,
+    const double *__restrict__ kref, const double *__restrict__ kc, double f, const uint8_t *__restrict__ mask,
+    const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
+    double *__restrict__ d)
 {
-    const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (n >= n_nodes) return;  // warp-uniform
-    gather_node<BS>(n, threadIdx.x & 31, ptr, col, cptr, clist, sc, stride, npe, mask, bval, row_ptr, values, d);
+    constexpr int L = th_lanes<NPE>(), G = 32 / L;  // G nodes per warp
+    __shared__ double acc_all[GT_WARPS * G][MF_MAX_DEG];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x / L;
+    const int64_t n = (int64_t)blockIdx.x * (GT_WARPS * G) + grp;
+    if (n >= n_nodes) return;  // group-uniform
+    const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
+    gather_row_th<NPE>(n, lane & (L - 1), gmask, acc_all[grp], adj_ptr, adj_col, inc_ptr, inc, inc_loc, slot, sc,
+                       stride, tr, kref, kc, f, mask, bval, row_ptr, values, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,7 +254,7 @@ __device__ __forceinline__ double to_double<long long>(long long v, int S)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(GEL_WARPS * 32, 4) k_gather_el(
+__global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
     int64_t n0, int64_t n1, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const int32_t *__restrict__ conn,
     const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
@@ -322,52 +331,31 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 4) k_gather_el(
         __syncwarp();
     }
     const int S = scale ? *scale : 0;
-    // write phase: one lane per neighbour k (its column node and Dirichlet
-    // flags loaded once), the 3 x 3 block finished from shared memory
-    bool rm[3];
-    int64_t rb[3];
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < 3; ++c) {
-        rm[c] = mask ? mask[3 * n + c] != 0 : false;
-        rb[c] = row_ptr[3 * n + c];
-    }
-    double lift[3] = {0.0, 0.0, 0.0};
-    for (int k = lane; k < deg; k += 32) {
-        const int64_t mcol = adj_col[p0 + k];
-        bool cm[3] = {false, false, false};
-        double cv[3] = {0.0, 0.0, 0.0};
-        if (mask)
-#pragma unroll
-            for (int cp = 0; cp < 3; ++cp) {
-                cm[cp] = mask[3 * mcol + cp] != 0;
-                if (cm[cp]) cv[cp] = bval[3 * mcol + cp];
+        const int64_t r = 3 * n + c;
+        const bool rm = mask ? mask[r] != 0 : false;
+        const int64_t rb = row_ptr[r];
+        double lift = 0.0;
+        for (int j = lane; j < 3 * deg; j += 32) {
+            const int k = j / 3, cp = j - 3 * k;
+            T kv = acc[k * 9 + 3 * c + cp];
+            if (fq) {  // fixed-point path: K = p A + q A^T + q I tr(A) per node-pair block
+                kv = (T)fp * kv + (T)fq * acc[k * 9 + 3 * cp + c];
+                if (c == cp) kv += (T)fq * (acc[k * 9] + acc[k * 9 + 4] + acc[k * 9 + 8]);
             }
-        const T *blk = acc + k * 9;
-        T tr = T(0);
-        if (fq) tr = blk[0] + blk[4] + blk[8];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int cp = 0; cp < 3; ++cp) {
-                T kv = blk[3 * c + cp];
-                if (fq) {  // fixed-point path: K = p A + q A^T + q I tr(A) per node-pair block
-                    kv = (T)fp * kv + (T)fq * blk[3 * cp + c];
-                    if (c == cp) kv += (T)fq * tr;
-                }
-                double v = to_double<T>(kv, S);
-                if (mask) {
-                    if (rm[c]) v = (3 * n + c == 3 * mcol + cp) ? 1.0 : 0.0;
-                    else if (cm[cp]) { lift[c] -= v * cv[cp]; v = 0.0; }
-                }
-                values[rb[c] + 3 * k + cp] = v;
+            double v = to_double<T>(kv, S);
+            if (mask) {
+                const int64_t sdof = 3 * (int64_t)adj_col[p0 + k] + cp;
+                if (rm) v = (r == sdof) ? 1.0 : 0.0;
+                else if (mask[sdof]) { lift -= v * bval[sdof]; v = 0.0; }
             }
-    }
+            values[rb + j] = v;
+        }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lift[c] += __shfl_xor_sync(0xffffffffu, lift[c], o);
+        for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
         const double dc = __shfl_sync(0xffffffffu, dsum, c);
-        if (lane == 0) d[3 * n + c] = rm[c] ? bval[3 * n + c] : dc + lift[c];
+        if (lane == 0) d[r] = rm ? bval[r] : dc + lift;
     }
 }
 
@@ -525,15 +513,20 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
             k_elem_thermal_p2<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
                                                              status);
         else
-            k_elem_thermal_q1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
-                                                             status);
+            k_elem_thermal_q1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->tr,
+                                                             p->scratch, status);
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         const mf_adj &A = p->adj[0];
         mf_prof_begin("gather_scalar", st);
-        k_gather<1><<<nblk(A.n_rows * 32, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, A.cptr, A.clist, p->scratch,
-                                                              p->scratch_stride, m->npe, c->bc_mask, c->bc_val,
-                                                              p->row_ptr, values, d);
+#define MF_GATHER_TH(NPE)                                                                                         \
+    k_gather_th<NPE><<<nblk(A.n_rows, GT_WARPS * (32 / th_lanes<NPE>())), GT_WARPS * 32, 0, st>>>(                 \
+        A.n_rows, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->slot, p->scratch, p->scratch_stride, p->tr,    \
+        p->kref, c->elem_coef, f, c->bc_mask, c->bc_val, p->row_ptr, values, d)
+        if (m->elem == MF_P1_TRI) MF_GATHER_TH(3);
+        else if (m->elem == MF_P2_TRI) MF_GATHER_TH(6);
+        else MF_GATHER_TH(8);
+#undef MF_GATHER_TH
         mf_prof_end(st);
     } else if (form == MF_FORM_ELASTIC) {
         const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;

@@ -26,8 +26,12 @@ struct BatchProblem {
     int64_t stride;
     const int64_t *ptr;
     const int32_t *col;
-    const int64_t *cptr;
-    const int32_t *clist;
+    const int64_t *inc_ptr;
+    const int32_t *inc;
+    const uint8_t *inc_loc;
+    const uint8_t *slot;
+    const uint8_t *tr;
+    const double *kref;
     const uint8_t *mask;
     const double *bval;
     const int64_t *row_ptr;
@@ -67,21 +71,38 @@ __global__ void __launch_bounds__(256) k_batch_elem(const BatchProblem *__restri
             const int64_t e = T.first + i;
             if (T.type == MF_P1_TRI) elem_thermal_p1(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
             else if (T.type == MF_P2_TRI) elem_thermal_p2(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
-            else elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
+            else if (!q1_translate(e, p.tr, p.kc, status)) elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_batch_gather(const BatchProblem *__restrict__ P,
-                                                      const BatchTile *__restrict__ tiles, int n_tiles)
+constexpr int BG_WARPS = 8;
+
+template <int NPE>
+__device__ __forceinline__ void batch_gather_tile(const BatchProblem &p, const BatchTile &T, int warp, int lane,
+                                                  double (*acc_all)[MF_MAX_DEG])
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int L = th_lanes<NPE>(), G = 32 / L;
+    const int grp = warp * G + lane / L;
+    const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
+    for (int64_t i = grp; i < T.count; i += BG_WARPS * G)  // group-uniform
+        gather_row_th<NPE>(T.first + i, lane & (L - 1), gmask, acc_all[grp], p.ptr, p.col, p.inc_ptr, p.inc,
+                           p.inc_loc, p.slot, p.scratch, p.stride, NPE == 8 ? p.tr : nullptr,
+                           NPE == 8 ? p.kref : nullptr, p.kc, p.f, p.mask, p.bval, p.row_ptr, p.values, p.d);
+}
+
+__global__ void __launch_bounds__(BG_WARPS * 32) k_batch_gather(const BatchProblem *__restrict__ P,
+                                                               const BatchTile *__restrict__ tiles, int n_tiles)
+{
+    __shared__ double acc_all[BG_WARPS * 8][MF_MAX_DEG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const BatchTile T = tiles[t];
         const BatchProblem &p = P[T.prob];
-        for (int64_t i = warp; i < T.count; i += nw)  // warp-uniform
-            gather_node<1>(T.first + i, lane, p.ptr, p.col, p.cptr, p.clist, p.scratch, p.stride, p.npe, p.mask,
-                           p.bval, p.row_ptr, p.values, p.d);
+        if (T.type == MF_P1_TRI) batch_gather_tile<3>(p, T, warp, lane, acc_all);
+        else if (T.type == MF_P2_TRI) batch_gather_tile<6>(p, T, warp, lane, acc_all);
+        else batch_gather_tile<8>(p, T, warp, lane, acc_all);
+        __syncthreads();  // the next tile may give a group another node type
     }
 }
 
@@ -129,7 +150,8 @@ void launch_batch(mf_batch *b, cudaStream_t st, int *status)
     const int cap = b->sm_count * t.grid_per_sm;
     k_batch_elem<<<std::max(1, std::min(b->n_etiles, cap)), t.elem_block, 0, st>>>(b->dev, b->etiles, b->n_etiles,
                                                                                       status);
-    k_batch_gather<<<std::max(1, std::min(b->n_ntiles, cap)), 256, 0, st>>>(b->dev, b->ntiles, b->n_ntiles);
+    k_batch_gather<<<std::max(1, std::min(b->n_ntiles, cap)), BG_WARPS * 32, 0, st>>>(b->dev, b->ntiles,
+                                                                                     b->n_ntiles);
 }
 
 mf_status capture(mf_batch *b, int *status)
@@ -228,8 +250,8 @@ extern "C" mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, co
         }
         const mf_adj &A = p->adj[0];
         b->host.push_back(BatchProblem{m->elem, m->npe, m->n_elems, m->n_nodes, m->coords, m->conn, c.elem_coef,
-                                       c.source[0], p->scratch, p->scratch_stride, A.ptr, A.col, A.cptr, A.clist,
-                                       c.bc_mask, c.bc_val, p->row_ptr, values[i], d[i]});
+                                       c.source[0], p->scratch, p->scratch_stride, A.ptr, A.col, p->inc_ptr, p->inc,
+                                       p->inc_loc, p->slot, p->tr, p->kref, c.bc_mask, c.bc_val, p->row_ptr, values[i], d[i]});
         cnt[m->elem] += m->n_elems;
         nodes += m->n_nodes;
     }

@@ -277,89 +277,104 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
     for (int a = 0; a < 8; ++a) o[64 + a] = f * m[a];
 }
 
-// One warp builds the BS x BS node-pair blocks of row node n from its
-// contribution lists (ascending elements) and applies the Dirichlet rows.
-template <int BS>
-__device__ __forceinline__ void gather_node(int64_t n, int lane, const int64_t *__restrict__ ptr,
-                                                const int32_t *__restrict__ col, const int64_t *__restrict__ cptr,
-                                                const int32_t *__restrict__ clist, const double *__restrict__ sc,
-                                                int64_t stride, int npe, const uint8_t *__restrict__ mask,
-                                                const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
-                                                double *__restrict__ values, double *__restrict__ d)
+
+// Thermal translate shortcut (Q1): true when element e is a translate of
+// element 0, whose unit matrices stand in for its own; the coefficient is
+// still checked here.
+__device__ __forceinline__ bool q1_translate(int64_t e, const uint8_t *__restrict__ tr, const double *__restrict__ kc,
+                                             int *status)
 {
-    const int64_t p0 = ptr[n], deg = ptr[n + 1] - p0;
-    bool rm[BS];
-    double lift[BS], dsum[BS];
-    int64_t rbase[BS];
+    if (!tr || !tr[e]) return false;
+    if (!isfinite(kc[e])) mf_dev_fail(status, MF_ERR_NONFINITE);
+    return true;
+}
+
+// Lanes per node of the thermal gather: 4 for P1, 8 for P2 and Q1.
+template <int NPE>
+constexpr int th_lanes() { return NPE <= 4 ? 4 : 8; }
+
+// Thermal row of node n by a group of th_lanes<NPE>() lanes (`sub` = lane in
+// the group, `gmask` = the group's lanes; groups of a warp are independent).
+// Lane b fetches, for each incident element j (ascending), entry (a_j, b) of
+// the element matrix (a contiguous row of the scratch, or k_e Kref for a
+// translate) and its slot among the node's neighbours; the loads of up to 8
+// elements are issued before any add.  The adds into the shared-memory row
+// `acc` (MF_MAX_DEG doubles) then run element by element, so every entry and
+// d_n are sums in ascending element order.  Dirichlet rows become identity
+// rows; constrained columns move to the right-hand side (lifting).
+template <int NPE>
+__device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask, double *acc,
+                                              const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+                                              const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
+                                              const uint8_t *__restrict__ inc_loc, const uint8_t *__restrict__ slot,
+                                              const double *__restrict__ sc, int64_t stride,
+                                              const uint8_t *__restrict__ tr, const double *__restrict__ kref,
+                                              const double *__restrict__ kc, double f, const uint8_t *__restrict__ mask,
+                                              const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+                                              double *__restrict__ values, double *__restrict__ d)
+{
+    constexpr int L = th_lanes<NPE>();
+    constexpr int U = 8;  // incident elements whose loads are in flight together
+    const int64_t p0 = adj_ptr[n];
+    const int deg = (int)(adj_ptr[n + 1] - p0);
+    const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
+    const bool rm = mask ? mask[n] != 0 : false;
+    const int64_t rb = row_ptr[n];
+    for (int i = sub; i < deg; i += L) acc[i] = 0.0;
+    __syncwarp(gmask);
+    const int b = sub;
+    const bool act = b < NPE;
+    double dsum = 0.0;
+    for (int64_t cb = i0; cb < i1; cb += U) {
+        const int cnt = (int)min((int64_t)U, i1 - cb);
+        double v[U], ld[U];
+        int s[U];
 #pragma unroll
-    for (int c = 0; c < BS; ++c) {
-        rm[c] = mask ? mask[BS * n + c] != 0 : false;
-        lift[c] = 0.0;
-        dsum[c] = 0.0;
-        rbase[c] = row_ptr[BS * n + c];
-    }
-    for (int64_t k = lane; k < deg; k += 32) {
-        const int64_t p = p0 + k;
-        const int32_t mnode = col[p];
-        double acc[BS][BS];
-#pragma unroll
-        for (int c = 0; c < BS; ++c)
-#pragma unroll
-            for (int cp = 0; cp < BS; ++cp) acc[c][cp] = 0.0;
-        for (int64_t t = cptr[p]; t < cptr[p + 1]; ++t) {
-            const int32_t v = clist[t];
-            const int64_t e = v >> 6;
-            const int a = (v >> 3) & 7, b = v & 7;
-            const double *s = sc + e * stride;
-            if (BS == 1) {
-                acc[0][0] += s[a * npe + b];
-                if (mnode == n) dsum[0] += s[npe * npe + a];
-            } else {
-                if (a <= b) {
-                    const double *blk = s + upair(a, b) * 9;
-#pragma unroll
-                    for (int c = 0; c < BS; ++c)
-#pragma unroll
-                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * c + cp];
+        for (int j = 0; j < U; ++j) {
+            v[j] = 0.0;
+            ld[j] = 0.0;
+            s[j] = 0;
+            if (j < cnt && act) {
+                const int64_t e = inc[cb + j];
+                const int a = inc_loc[cb + j];
+                s[j] = slot[(e * NPE + a) * NPE + b];
+                if (tr && tr[e]) {
+                    v[j] = kc[e] * __ldg(&kref[a * NPE + b]);
+                    if (b == 0) ld[j] = f * __ldg(&kref[NPE * NPE + a]);
                 } else {
-                    const double *blk = s + upair(b, a) * 9;
-#pragma unroll
-                    for (int c = 0; c < BS; ++c)
-#pragma unroll
-                        for (int cp = 0; cp < BS; ++cp) acc[c][cp] += blk[3 * cp + c];
+                    const double *se = sc + e * stride;
+                    v[j] = se[a * NPE + b];
+                    if (b == 0) ld[j] = se[NPE * NPE + a];
                 }
-                if (mnode == n)
-#pragma unroll
-                    for (int c = 0; c < BS; ++c) dsum[c] += s[324 + 3 * a + c];
             }
         }
 #pragma unroll
-        for (int c = 0; c < BS; ++c)
-#pragma unroll
-            for (int cp = 0; cp < BS; ++cp) {
-                double v = acc[c][cp];
-                if (mask) {
-                    const int64_t r = BS * n + c, sdof = BS * (int64_t)mnode + cp;
-                    if (rm[c]) {
-                        v = (r == sdof) ? 1.0 : 0.0;
-                    } else if (mask[sdof]) {
-                        lift[c] -= v * bval[sdof];
-                        v = 0.0;
-                    }
-                }
-                values[rbase[c] + BS * k + cp] = v;
+        for (int j = 0; j < U; ++j) {
+            if (j < cnt) {  // group-uniform
+                if (act) acc[s[j]] += v[j];
+                dsum += ld[j];
+                __syncwarp(gmask);
             }
+        }
+    }
+    double lift = 0.0;
+    for (int k = sub; k < deg; k += L) {
+        const int64_t mcol = adj_col[p0 + k];
+        double val = acc[k];
+        if (mask) {
+            if (rm) {
+                val = (mcol == n) ? 1.0 : 0.0;
+            } else if (mask[mcol]) {
+                lift -= val * bval[mcol];
+                val = 0.0;
+            }
+        }
+        values[rb + k] = val;
     }
 #pragma unroll
-    for (int c = 0; c < BS; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lift[c] += __shfl_xor_sync(0xffffffffu, lift[c], o);
-            dsum[c] += __shfl_xor_sync(0xffffffffu, dsum[c], o);
-        }
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < BS; ++c) d[BS * n + c] = rm[c] ? bval[BS * n + c] : dsum[c] + lift[c];
+    for (int o = L / 2; o > 0; o >>= 1) lift += __shfl_xor_sync(gmask, lift, o, L);
+    if (sub == 0) d[n] = rm ? bval[n] : dsum + lift;
+    __syncwarp(gmask);
 }
 
 }  // namespace

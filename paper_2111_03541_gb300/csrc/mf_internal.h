@@ -49,12 +49,20 @@ struct mf_pattern {
     // incident elements per row node (ascending), for the mixed path
     int64_t *inc_ptr = nullptr;
     int32_t *inc = nullptr;
+    uint8_t *inc_loc = nullptr;  // position of the node in each incident element
     // flow: elements incident to each P1 pressure node, ascending
     int64_t *pinc_ptr = nullptr;
     int32_t *pinc = nullptr;
-    // elasticity: slot[e][a][b] = position of node conn[e][b] among the sorted
-    // neighbours of node conn[e][a] (u8, n_elems x 64)
+    // thermal and elasticity: slot[e][a][b] = position of node conn[e][b]
+    // among the sorted neighbours of node conn[e][a] (u8, n_elems x npe x npe)
     uint8_t *slot = nullptr;
+    // thermal Q1: tr[e] = 1 when element e is an exact translate of element 0
+    // (equal edge vectors x_a - x_0 in FP64), so K_e = k_e Kref and
+    // d_e = f dref with kref = [Kref (8 x 8), dref (8)] element 0's unit-k,
+    // unit-f matrices; null when no element is a translate
+    uint8_t *tr = nullptr;
+    double *kref = nullptr;
+    int64_t n_translate = 0;
     // mixed path: device scalars of the fixed-point scale (see mf_mixed.cu)
     void *mixed_state = nullptr;
     // elasticity slabs: element chunk c = [slab_e[c], slab_e[c+1]) completes the

@@ -5,13 +5,16 @@
 // unique pairs of a row node space and a column node space form an adjacency
 // (CSR over row nodes, ascending columns) built without hashing: per row node
 // the incident elements are gathered and their nodes sorted and de-duplicated
-// in registers.  Each node pair also keeps the list of element contributions
-// (e, a, b) in ascending element order, which fixes the summation order of the
-// assembly.  The dof-level CSR of a form is then laid out from its blocks.
+// in registers.  The thermal and elasticity gathers walk a node's incident
+// elements in ascending order and place each entry through a slot map (the
+// position of the column node among the row node's neighbours); the flow
+// gather keeps, per node pair, the list of element contributions (e, a, b) in
+// ascending element order.  Either fixes the summation order of the assembly.
+// The dof-level CSR of a form is then laid out from its blocks.
 #include <algorithm>
 #include <cstdio>
 
-#include "mf_internal.h"
+#include "mf_fem.cuh"
 
 namespace {
 
@@ -89,6 +92,21 @@ __global__ void k_inc_fill(int64_t n_el, int npe, const int32_t *__restrict__ co
     const int32_t v = conn[t];
     const int64_t pos = ptr[v] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[v]), 1ull);
     inc[pos] = (int32_t)(t / npe);
+}
+
+// position of node n within each of its incident elements
+__global__ void k_inc_local(int64_t n_nodes, int npe, const int32_t *__restrict__ conn, const int64_t *__restrict__ ptr,
+                            const int32_t *__restrict__ inc, uint8_t *__restrict__ loc)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    for (int64_t t = ptr[n]; t < ptr[n + 1]; ++t) {
+        const int32_t *ce = conn + (int64_t)inc[t] * npe;
+        int a = 0;
+        for (int k = 0; k < npe; ++k)
+            if (ce[k] == (int32_t)n) a = k;
+        loc[t] = (uint8_t)a;
+    }
 }
 
 __global__ void k_sort_segments_i32(int64_t n, const int64_t *__restrict__ ptr, int32_t *v, int *status)
@@ -183,16 +201,49 @@ __global__ void k_node_ready(int64_t n, const int64_t *__restrict__ inc_ptr, con
     ready[v] = inc_ptr[v + 1] > inc_ptr[v] ? inc[inc_ptr[v + 1] - 1] : -1;
 }
 
-// slot map: position of conn[e][b] among the neighbours of conn[e][a]
-__global__ void k_slot_map(int64_t n_el, const int32_t *__restrict__ conn, const int64_t *__restrict__ ptr,
+// slot map: position of conn[e][b] among the neighbours of conn[e][a],
+// slot[(e * npe + a) * npe + b]
+__global__ void k_slot_map(int64_t n_el, int npe, const int32_t *__restrict__ conn, const int64_t *__restrict__ ptr,
                            const int32_t *__restrict__ col, uint8_t *slot)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_el * 64) return;
-    const int64_t e = t >> 6;
-    const int a = (int)(t >> 3) & 7, b = (int)t & 7;
-    const int32_t n = conn[e * 8 + a], m = conn[e * 8 + b];
+    const int64_t nn = (int64_t)npe * npe;
+    if (t >= n_el * nn) return;
+    const int64_t e = t / nn;
+    const int r = (int)(t - e * nn);
+    const int a = r / npe, b = r - a * npe;
+    const int32_t n = conn[e * npe + a], m = conn[e * npe + b];
     slot[t] = (uint8_t)(find_pair(ptr, col, n, m) - ptr[n]);
+}
+
+// Q1 translates of element 0: equal edge vectors x_a - x_0 (FP64, exact
+// comparison).  Counted per warp.
+__global__ void k_translate_flags(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                                  uint8_t *__restrict__ tr, unsigned long long *count)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool t = false;
+    if (e < n_el) {
+        t = true;
+        const int32_t *ce = conn + 8 * e;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double r0 = X[3 * (int64_t)conn[0] + i], x0 = X[3 * (int64_t)ce[0] + i];
+#pragma unroll
+            for (int a = 1; a < 8; ++a)
+                t = t && (X[3 * (int64_t)ce[a] + i] - x0 == X[3 * (int64_t)conn[a] + i] - r0);
+        }
+        tr[e] = t ? 1 : 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, t);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(count, (unsigned long long)__popc(bal));
+}
+
+// kref = element 0's matrix and load vector with k = 1, f = 1 (kref[72] holds the 1)
+__global__ void k_kref(const double *__restrict__ X, const int32_t *__restrict__ conn, double *kref, int *status)
+{
+    kref[72] = 1.0;
+    elem_thermal_q1(0, X, conn, kref + 72, 1.0, kref, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -260,6 +311,7 @@ __global__ void k_csr_oseen_fill(int64_t n2, int64_t n1, const int64_t *__restri
 struct Incidence {
     int64_t *ptr = nullptr;
     int32_t *inc = nullptr;
+    uint8_t *loc = nullptr;  // local index of the node in each incident element
 };
 
 mf_status build_incidence(int64_t n_nodes, int64_t n_el, int npe, const int32_t *conn, cudaStream_t st,
@@ -275,6 +327,8 @@ mf_status build_incidence(int64_t n_nodes, int64_t n_el, int npe, const int32_t 
     MF_CUDA(mf_scan_i64(out->ptr, n_nodes + 1, nullptr, st));
     k_inc_fill<<<nblk(n_el * npe), TPB, 0, st>>>(n_el, npe, conn, out->ptr, cursor, out->inc);
     k_sort_segments_i32<<<nblk(n_nodes), TPB, 0, st>>>(n_nodes, out->ptr, out->inc, status);
+    MF_CUDA(cudaMallocAsync(&out->loc, (size_t)n_el * npe, st));
+    k_inc_local<<<nblk(n_nodes), TPB, 0, st>>>(n_nodes, npe, conn, out->ptr, out->inc, out->loc);
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaFreeAsync(cursor, st));
     return MF_OK;
@@ -305,7 +359,7 @@ mf_status check_status(int *status, cudaStream_t st, const char *what)
 }
 
 mf_status build_adj(int64_t n_rows, const Incidence &inc, int64_t n_el, int npe_r, const int32_t *conn_r,
-                    int npe_c, const int32_t *conn_c, cudaStream_t st, mf_adj *A, int *status)
+                    int npe_c, const int32_t *conn_c, bool contrib, cudaStream_t st, mf_adj *A, int *status)
 {
     A->n_rows = n_rows;
     MF_CUDA(cudaMallocAsync(&A->ptr, sizeof(int64_t) * (n_rows + 1), st));
@@ -322,6 +376,7 @@ mf_status build_adj(int64_t n_rows, const Incidence &inc, int64_t n_el, int npe_
     MF_CUDA(cudaMallocAsync(&A->col, sizeof(int32_t) * A->n_pairs, st));
     k_adj<true><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self, nullptr,
                                                   A->ptr, A->col, status);
+    if (!contrib) return check_status(status, st, "mf_pattern_build");
     // contributions of every pair, ascending packed (e, a, b)
     int64_t *cnt = nullptr;
     MF_CUDA(cudaMallocAsync(&A->cptr, sizeof(int64_t) * (A->n_pairs + 1), st));
@@ -384,6 +439,7 @@ void free_inc(Incidence &I, cudaStream_t st)
 {
     if (I.ptr) cudaFreeAsync(I.ptr, st);
     if (I.inc) cudaFreeAsync(I.inc, st);
+    if (I.loc) cudaFreeAsync(I.loc, st);
     I = Incidence();
 }
 
@@ -425,10 +481,17 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->scratch);
     cudaFree(p->inc_ptr);
     cudaFree(p->inc);
+    cudaFree(p->inc_loc);
+    p->inc_loc = nullptr;
     cudaFree(p->pinc_ptr);
     cudaFree(p->pinc);
     cudaFree(p->slot);
     cudaFree(p->mixed_state);
+    cudaFree(p->tr);
+    cudaFree(p->kref);
+    p->tr = nullptr;
+    p->kref = nullptr;
+    p->n_translate = 0;
     p->slot = nullptr;
     p->mixed_state = nullptr;
     p->pinc_ptr = nullptr;
@@ -450,7 +513,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
     mf_status s = build_incidence(m->n_nodes, m->n_elems, npe, m->conn, st, &incv, status);
     if (s == MF_OK) s = check_status(status, st, "mf_pattern_build");
     if (s != MF_OK) { free_inc(incv, st); return s; }
-    s = build_adj(m->n_nodes, incv, m->n_elems, npe, m->conn, npe, m->conn, st, &p->adj[0], status);
+    s = build_adj(m->n_nodes, incv, m->n_elems, npe, m->conn, npe, m->conn, form == MF_FORM_OSEEN, st, &p->adj[0],
+                  status);
     p->n_adj = 1;
     if (s != MF_OK) { free_inc(incv, st); return s; }
 
@@ -461,7 +525,29 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
         k_csr_thermal<<<nblk(p->n_rows + 1), TPB, 0, st>>>(p->n_rows, p->adj[0].ptr, p->row_ptr);
         MF_CUDA(cudaMemcpyAsync(p->col_idx, p->adj[0].col, sizeof(int32_t) * p->nnz, cudaMemcpyDeviceToDevice, st));
+        const int64_t nslot = (int64_t)npe * npe * m->n_elems;
+        MF_CUDA(cudaMallocAsync(&p->slot, (size_t)nslot, st));
+        k_slot_map<<<nblk(nslot), TPB, 0, st>>>(m->n_elems, npe, m->conn, p->adj[0].ptr, p->adj[0].col, p->slot);
         p->scratch_stride = (int64_t)npe * npe + npe;
+        if (m->elem == MF_Q1_HEX && m->n_elems > 0) {
+            unsigned long long *cnt = nullptr;
+            MF_CUDA(cudaMallocAsync(&p->tr, (size_t)m->n_elems, st));
+            MF_CUDA(cudaMallocAsync(&cnt, sizeof(unsigned long long), st));
+            MF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+            k_translate_flags<<<nblk(m->n_elems), TPB, 0, st>>>(m->n_elems, m->coords, m->conn, p->tr, cnt);
+            unsigned long long h = 0;
+            MF_CUDA(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, st));
+            MF_CUDA(cudaStreamSynchronize(st));
+            MF_CUDA(cudaFreeAsync(cnt, st));
+            p->n_translate = (int64_t)h;
+            if (h == 0) {
+                MF_CUDA(cudaFreeAsync(p->tr, st));
+                p->tr = nullptr;
+            } else {
+                MF_CUDA(cudaMallocAsync(&p->kref, sizeof(double) * 73, st));
+                k_kref<<<1, 1, 0, st>>>(m->coords, m->conn, p->kref, status);
+            }
+        }
     } else if (form == MF_FORM_ELASTIC) {
         p->n_rows = 3 * m->n_nodes;
         p->nnz = 9 * p->adj[0].n_pairs;
@@ -471,7 +557,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_csr_elastic<<<nblk(p->n_rows + 1), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->row_ptr,
                                                            p->col_idx);
         MF_CUDA(cudaMallocAsync(&p->slot, (size_t)64 * m->n_elems, st));
-        k_slot_map<<<nblk(m->n_elems * 64), TPB, 0, st>>>(m->n_elems, m->conn, p->adj[0].ptr, p->adj[0].col, p->slot);
+        k_slot_map<<<nblk(m->n_elems * 64), TPB, 0, st>>>(m->n_elems, 8, m->conn, p->adj[0].ptr, p->adj[0].col,
+                                                           p->slot);
         MF_CUDA(cudaMallocAsync(&p->mixed_state, 64, st));
         p->scratch_stride = 36 * 9 + 24;
         mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);
@@ -479,10 +566,13 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
     } else {
         Incidence incp;
         s = build_incidence(m->n_pnodes, m->n_elems, 3, m->pconn, st, &incp, status);
-        if (s == MF_OK) s = build_adj(m->n_nodes, incv, m->n_elems, 6, m->conn, 3, m->pconn, st, &p->adj[1], status);
-        if (s == MF_OK) s = build_adj(m->n_pnodes, incp, m->n_elems, 3, m->pconn, 6, m->conn, st, &p->adj[2], status);
+        if (s == MF_OK)
+            s = build_adj(m->n_nodes, incv, m->n_elems, 6, m->conn, 3, m->pconn, true, st, &p->adj[1], status);
+        if (s == MF_OK)
+            s = build_adj(m->n_pnodes, incp, m->n_elems, 3, m->pconn, 6, m->conn, true, st, &p->adj[2], status);
         p->pinc_ptr = incp.ptr;
         p->pinc = incp.inc;
+        if (incp.loc) cudaFreeAsync(incp.loc, st);
         p->n_adj = 3;
         if (s != MF_OK) { free_inc(incv, st); return s; }
         const int64_t n2 = m->n_nodes, n1 = m->n_pnodes;
@@ -503,6 +593,7 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
     MF_CUDA(cudaGetLastError());
     p->inc_ptr = incv.ptr;
     p->inc = incv.inc;
+    p->inc_loc = incv.loc;
     MF_CUDA(cudaMallocAsync(&p->scratch, sizeof(double) * p->scratch_stride * m->n_elems, st));
     MF_CUDA(cudaStreamSynchronize(st));
     return check_status(status, st, "mf_pattern_build");

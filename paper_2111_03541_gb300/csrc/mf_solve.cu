@@ -23,6 +23,7 @@ namespace {
 
 constexpr int RT = 256;       // threads per reduction block
 constexpr int RED_BLOCKS = 1024;  // fixed grid of the reduction kernels (bit-reproducible)
+constexpr int VU = 4;         // vector kernels: elements a thread loads before it computes
 
 struct PcgState {
     double rz, pq, rr, dd, tol2, alpha, beta;
@@ -50,7 +51,9 @@ __device__ double block_sum(double v, double *sh)
     return s;  // valid in thread 0
 }
 
-// returns true in the one thread (thread 0 of the last block) that may finish
+// true in every thread of the last block to arrive (block-uniform); the
+// ticket is reset for the next launch.  Partials are written by thread 0 of
+// each block before it takes a ticket.
 __device__ bool last_block(unsigned *ticket)
 {
     __shared__ bool last;
@@ -58,19 +61,37 @@ __device__ bool last_block(unsigned *ticket)
     if (threadIdx.x == 0) {
         const unsigned t = atomicAdd(ticket, 1u);
         last = (t == gridDim.x - 1);
+        if (last) *ticket = 0;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        *ticket = 0;
-        __threadfence();
-        return true;
-    }
-    return false;
+    if (last) __threadfence();
+    return last;
+}
+
+// Sums of NV interleaved partial arrays part[b * NV + v], b < nb, by the whole
+// block in a fixed order (thread t adds b = t, t + blockDim, ... in turn, then
+// the block tree), so the result depends on nb only.  Valid in thread 0.
+template <int NV>
+__device__ void finish_sums(const double *part, unsigned nb, double *out, double *sh)
+{
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += __ldcg(&part[(size_t)b * NV + v]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = block_sum(acc[v], sh);
 }
 
 // ---------------------------------------------------------------------------
-// SpMV: W lanes per row
+// SpMV: W lanes per row, SPMV_U entries per lane per batch.  A lane issues the
+// column and value loads of its whole batch, then the gathers of x, then the
+// FMAs, so a row costs three dependent memory round trips however long it is
+// (up to W * SPMV_U entries per batch).
 // ---------------------------------------------------------------------------
+constexpr int SPMV_U = 8;
+
 // Every lane of the warp calls the shuffles (full mask): rows past n give 0.
 template <int W>
 __device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -78,15 +99,31 @@ __device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const 
                                           int sub, bool valid)
 {
     double s = 0.0;
-    if (valid)
-        for (int64_t t = rp[row] + sub; t < rp[row + 1]; t += W) s = fma(v[t], __ldg(&x[ci[t]]), s);
+    if (valid) {
+        const int64_t t1 = rp[row + 1];
+        for (int64_t t = rp[row] + sub; t < t1; t += (int64_t)SPMV_U * W) {
+            int32_t c[SPMV_U];
+            double a[SPMV_U], xv[SPMV_U];
+#pragma unroll
+            for (int u = 0; u < SPMV_U; ++u) {
+                const int64_t tt = t + (int64_t)u * W;
+                const bool ok = tt < t1;
+                c[u] = ok ? __ldcs(&ci[tt]) : -1;
+                a[u] = ok ? __ldcs(&v[tt]) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < SPMV_U; ++u) xv[u] = c[u] >= 0 ? __ldg(&x[c[u]]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < SPMV_U; ++u) s = fma(a[u], xv[u], s);
+        }
+    }
 #pragma unroll
     for (int o = W / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, W);
     return s;
 }
 
 template <int W>
-__global__ void __launch_bounds__(RT) k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void __launch_bounds__(RT, 4) k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                              const double *__restrict__ v, const double *__restrict__ x,
                                              double *__restrict__ y)
 {
@@ -101,7 +138,7 @@ __global__ void __launch_bounds__(RT) k_spmv(int64_t n, const int64_t *__restric
 // q = K p: one W-lane group per row over the whole matrix (no reduction here,
 // so no per-block atomics on a shared ticket)
 template <int W>
-__global__ void __launch_bounds__(RT) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(RT, 4) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
                                                  const double *__restrict__ p, double *__restrict__ q,
                                                  const PcgState *S)
@@ -122,16 +159,29 @@ __global__ void __launch_bounds__(RT) k_pcg_pq(int64_t n, const double *__restri
     __shared__ double sh[RT / 32];
     if (S->done) return;
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc = fma(p[i], q[i], acc);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += VU * stride) {
+        double a[VU], b[VU];
+#pragma unroll
+        for (int u = 0; u < VU; ++u) {
+            const int64_t i = i0 + u * stride;
+            a[u] = i < n ? p[i] : 0.0;
+            b[u] = i < n ? q[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < VU; ++u)
+            if (i0 + u * stride < n) acc = fma(a[u], b[u], acc);
+    }
     const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = bs;
     if (last_block(&S->ticket)) {
-        double pq = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) pq += part[b];
-        S->pq = pq;
-        if (!(pq > 0.0) || !isfinite(pq)) S->done = 3;
-        else S->alpha = S->rz / pq;
+        double pq;
+        finish_sums<1>(part, gridDim.x, &pq, sh);
+        if (threadIdx.x == 0) {
+            S->pq = pq;
+            if (!(pq > 0.0) || !isfinite(pq)) S->done = 3;
+            else S->alpha = S->rz / pq;
+        }
     }
 }
 
@@ -145,12 +195,31 @@ __global__ void __launch_bounds__(RT) k_pcg_update(int64_t n, const double *__re
     if (S->done) return;
     const double alpha = S->alpha;
     double rz = 0.0, rr = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const double ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        rz = fma(ri * dinv[i], ri, rz);
-        rr = fma(ri, ri, rr);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += VU * stride) {
+        double pv[VU], qv[VU], xv[VU], rv[VU], dv[VU];
+#pragma unroll
+        for (int u = 0; u < VU; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                pv[u] = p[i];
+                qv[u] = q[i];
+                xv[u] = x[i];
+                rv[u] = r[i];
+                dv[u] = dinv[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VU; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                x[i] = fma(alpha, pv[u], xv[u]);
+                const double ri = fma(-alpha, qv[u], rv[u]);
+                r[i] = ri;
+                rz = fma(ri * dv[u], ri, rz);
+                rr = fma(ri, ri, rr);
+            }
+        }
     }
     const double bz = block_sum(rz, sh);
     const double br = block_sum(rr, sh);
@@ -159,11 +228,10 @@ __global__ void __launch_bounds__(RT) k_pcg_update(int64_t n, const double *__re
         part[2 * blockIdx.x + 1] = br;
     }
     if (last_block(&S->ticket)) {
-        double z = 0.0, s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            z += part[2 * b];
-            s += part[2 * b + 1];
-        }
+        double zs[2];
+        finish_sums<2>(part, gridDim.x, zs, sh);
+        if (threadIdx.x != 0) return;
+        const double z = zs[0], s = zs[1];
         S->iter += 1;
         S->rr = s;
         if (!isfinite(s) || !isfinite(z)) S->done = 3;
@@ -181,8 +249,24 @@ __global__ void __launch_bounds__(RT) k_pcg_dir(int64_t n, const double *__restr
 {
     if (S->done) return;
     const double beta = S->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], dinv[i] * r[i]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += VU * stride) {
+        double pv[VU], dv[VU], rv[VU];
+#pragma unroll
+        for (int u = 0; u < VU; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                pv[u] = p[i];
+                dv[u] = dinv[i];
+                rv[u] = r[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VU; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) p[i] = fma(beta, pv[u], dv[u] * rv[u]);
+        }
+    }
 }
 
 // set-up: dinv = 1 / diag(K); r = d - q (q = K x0); p = D^-1 r; rz, rr, dd
@@ -219,12 +303,10 @@ __global__ void __launch_bounds__(RT) k_pcg_init(int64_t n, const double *__rest
         part[3 * blockIdx.x + 2] = c;
     }
     if (last_block(&S->ticket)) {
-        double z = 0.0, s = 0.0, t = 0.0;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            z += part[3 * k];
-            s += part[3 * k + 1];
-            t += part[3 * k + 2];
-        }
+        double zst[3];
+        finish_sums<3>(part, gridDim.x, zst, sh);
+        if (threadIdx.x != 0) return;
+        const double z = zst[0], s = zst[1], t = zst[2];
         S->rz = z;
         S->rr = s;
         S->dd = t;
@@ -252,20 +334,23 @@ __global__ void __launch_bounds__(RT) k_resid_norm(int64_t n, const double *__re
         part[2 * blockIdx.x + 1] = b;
     }
     if (last_block(ticket)) {
-        double s = 0.0, t = 0.0;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            s += part[2 * k];
-            t += part[2 * k + 1];
+        double st[2];
+        finish_sums<2>(part, gridDim.x, st, sh);
+        if (threadIdx.x == 0) {
+            out2[0] = st[0];
+            out2[1] = st[1];
         }
-        out2[0] = s;
-        out2[1] = t;
     }
 }
 
+// lanes per row: the smallest W >= 2 whose batch (W * SPMV_U entries) holds an
+// average row
 int spmv_width(int64_t n, int64_t nnz)
 {
-    const double avg = (double)nnz / (double)n;
-    return avg <= 8 ? 4 : (avg <= 24 ? 8 : (avg <= 48 ? 16 : 32));
+    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    int w = 2;
+    while (w < 32 && w * SPMV_U < avg) w *= 2;
+    return w;
 }
 
 template <int W>
@@ -277,6 +362,7 @@ void launch_spmv(const mf_csr *K, const double *v, const double *x, double *y, c
 void spmv_any(const mf_csr *K, const double *v, const double *x, double *y, cudaStream_t st)
 {
     switch (spmv_width(K->n_rows, K->nnz)) {
+    case 2: launch_spmv<2>(K, v, x, y, st); break;
     case 4: launch_spmv<4>(K, v, x, y, st); break;
     case 8: launch_spmv<8>(K, v, x, y, st); break;
     case 16: launch_spmv<16>(K, v, x, y, st); break;
@@ -337,18 +423,22 @@ __global__ void __launch_bounds__(RT) k_block_dots(int64_t n, const double *__re
     }
 }
 
-// h[k] = sum over blocks of part[.][k], in block order; H column j += h (pass 2 adds)
-__global__ void k_reduce_dots(int nb, const double *__restrict__ part, int mp1, const GmState *S, double *h,
-                              double *Hcol_accum, int pass)
+// h[k] = sum over blocks of part[.][k] (one block per k, fixed order); H column j += h (pass 2 adds)
+__global__ void __launch_bounds__(RT) k_reduce_dots(int nb, const double *__restrict__ part, int mp1,
+                                                    const GmState *S, double *h, double *Hcol_accum, int pass)
 {
+    __shared__ double sh[RT / 32];
     if (S->cycle_end) return;
     const int j = S->j;
-    const int k = threadIdx.x;
-    if (k > j) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * mp1 + k];
-    h[k] = s;
-    Hcol_accum[k] = (pass == 0) ? s : Hcol_accum[k] + s;
+    const int k = blockIdx.x;
+    if (k > j) return;  // block-uniform
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(int64_t)b * mp1 + k];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        h[k] = s;
+        Hcol_accum[k] = (pass == 0) ? s : Hcol_accum[k] + s;
+    }
 }
 
 // w -= V[0..j] h
@@ -376,9 +466,9 @@ __global__ void __launch_bounds__(RT) k_norm2(int64_t n, const double *__restric
     const double b = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
     if (last_block(ticket)) {
-        double s = 0.0;
-        for (unsigned k = 0; k < gridDim.x; ++k) s += part[k];
-        *out = sqrt(s);
+        double s;
+        finish_sums<1>(part, gridDim.x, &s, sh);
+        if (threadIdx.x == 0) *out = sqrt(s);
     }
 }
 
@@ -470,11 +560,10 @@ __global__ void __launch_bounds__(RT) k_gm_start(int64_t n, const double *__rest
         part[2 * blockIdx.x + 1] = b;
     }
     if (last_block(&S->ticket)) {
-        double t = 0.0, u = 0.0;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            t += part[2 * k];
-            u += part[2 * k + 1];
-        }
+        double tu[2];
+        finish_sums<2>(part, gridDim.x, tu, sh);
+        if (threadIdx.x != 0) return;
+        const double t = tu[0], u = tu[1];
         S->dd = u;
         S->beta0 = sqrt(t);
         S->j = 0;
@@ -570,6 +659,7 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
     if (ce == cudaSuccess) {
         for (int it = 0; it < chunk; ++it) {
             switch (W) {
+            case 2: launch_pcg_spmv<2>(K, p.p, q.p, part.p, S.p, cs); break;
             case 4: launch_pcg_spmv<4>(K, p.p, q.p, part.p, S.p, cs); break;
             case 8: launch_pcg_spmv<8>(K, p.p, q.p, part.p, S.p, cs); break;
             case 16: launch_pcg_spmv<16>(K, p.p, q.p, part.p, S.p, cs); break;
@@ -679,7 +769,7 @@ mf_status solve_gmres(const mf_csr *K, const double *d, double *x, const mf_solv
             spmv_any(&Kp, Kp.values, Vp + (int64_t)j * ldv, w.p, st);
             for (int pass = 0; pass < 2; ++pass) {
                 k_block_dots<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, w.p, S.p, part.p, m + 1);
-                k_reduce_dots<<<1, 1024, 0, st>>>(RED_BLOCKS, part.p, m + 1, S.p, h.p, hcol.p, pass);
+                k_reduce_dots<<<m + 1, RT, 0, st>>>(RED_BLOCKS, part.p, m + 1, S.p, h.p, hcol.p, pass);
                 k_multi_axpy<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, h.p, S.p, w.p);
             }
             k_norm2<<<RED_BLOCKS, RT, 0, st>>>(n, w.p, S.p, partB, &S.p->ticket, nrm.p);
@@ -813,6 +903,7 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
     for (;;) {
         for (int it = 0; it < chunk; ++it) {
             switch (W) {
+            case 2: launch_pcg_spmv<2>(K, p, q, part, S, st); break;
             case 4: launch_pcg_spmv<4>(K, p, q, part, S, st); break;
             case 8: launch_pcg_spmv<8>(K, p, q, part, S, st); break;
             case 16: launch_pcg_spmv<16>(K, p, q, part, S, st); break;

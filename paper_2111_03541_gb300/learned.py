@@ -186,6 +186,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--loss", choices=("energy", "residual"), default="energy")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
                                                   "cnn_q1_thermal.f32"))
     a = ap.parse_args(argv)
@@ -193,13 +194,15 @@ def main(argv=None):
     tr = Dataset(a.systems, seed0=TRAIN_SEED0)
     va = Dataset(a.valid, seed0=VALID_SEED0)
     print(f"data: {len(tr)} train / {len(va)} valid samples in {time.time() - t:.0f}s", flush=True)
-    jl = jacobi_loss(va)
+    energy = a.loss == "energy"
+    jl = jacobi_loss(va, energy=energy)
     print(f"Jacobi-only validation loss {jl:.4f}", flush=True)
-    cnn, hist = train(tr, va, steps=a.steps, batch=a.batch, lr=a.lr, log=lambda s: print(s, flush=True))
+    cnn, hist = train(tr, va, steps=a.steps, batch=a.batch, lr=a.lr, log=lambda s: print(s, flush=True),
+                      energy=energy)
     params = mf_cnn_get_params(cnn)
     os.makedirs(os.path.dirname(a.out), exist_ok=True)
     save_params(a.out, params, {"systems": a.systems, "valid": a.valid, "steps": a.steps, "batch": a.batch,
-                                "lr": a.lr, "jacobi_valid_loss": jl, "history": hist})
+                                "lr": a.lr, "loss": a.loss, "jacobi_valid_loss": jl, "history": hist})
     print(f"saved {a.out}", flush=True)
     mf_cnn_destroy(cnn)
     torch.cuda.synchronize()
