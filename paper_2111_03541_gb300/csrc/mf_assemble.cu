@@ -25,27 +25,30 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // element kernels
 // ---------------------------------------------------------------------------
 __global__ void k_elem_thermal_p1(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
-                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+                                  const double *__restrict__ kc, double f, const int32_t *__restrict__ map,
+                                  double *__restrict__ out, int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n_el) elem_thermal_p1(e, X, conn, kc, f, out, status);
+    if (e < n_el) elem_thermal_p1(e, X, conn, kc, f, map, out, status);
 }
 
 __global__ void k_elem_thermal_p2(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
-                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+                                  const double *__restrict__ kc, double f, const int32_t *__restrict__ map,
+                                  double *__restrict__ out, int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n_el) elem_thermal_p2(e, X, conn, kc, f, out, status);
+    if (e < n_el) elem_thermal_p2(e, X, conn, kc, f, map, out, status);
 }
 
 __global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const double *__restrict__ X,
                                                          const int32_t *__restrict__ conn,
                                                          const double *__restrict__ kc, double f,
-                                                         const uint8_t *__restrict__ tr, double *__restrict__ out,
+                                                         const uint8_t *__restrict__ tr,
+                                                         const int32_t *__restrict__ map, double *__restrict__ out,
                                                          int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n_el && !q1_translate(e, tr, kc, status)) elem_thermal_q1(e, X, conn, kc, f, out, status);
+    if (e < n_el && !q1_translate(e, tr, kc, status)) elem_thermal_q1(e, X, conn, kc, f, map, out, status);
 }
 
 // Q1 elasticity, one element per thread.  The scaled gradients
@@ -200,8 +203,8 @@ template <int NPE>
 __global__ void __launch_bounds__(GT_WARPS * 32, 3) k_gather_th(
     int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
-    const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const uint8_t *__restrict__ tr,
-    const double *__restrict__ kref, const double *__restrict__ kc, double f, const uint8_t *__restrict__ mask,
+    const uint8_t *__restrict__ inc_slot, const double *__restrict__ sc, const double *__restrict__ kref,
+    const double *__restrict__ kc, double f, const uint8_t *__restrict__ mask,
     const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
     double *__restrict__ d)
 {
@@ -211,8 +214,8 @@ __global__ void __launch_bounds__(GT_WARPS * 32, 3) k_gather_th(
     const int64_t n = (int64_t)blockIdx.x * (GT_WARPS * G) + grp;
     if (n >= n_nodes) return;  // group-uniform
     const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
-    gather_row_th<NPE>(n, lane & (L - 1), gmask, acc_all[grp], adj_ptr, adj_col, inc_ptr, inc, inc_loc, slot, sc,
-                       stride, tr, kref, kc, f, mask, bval, row_ptr, values, d);
+    gather_row_th<NPE>(n, lane & (L - 1), gmask, acc_all[grp], adj_ptr, adj_col, inc_ptr, inc, inc_loc, inc_slot, sc,
+                       kref, kc, f, mask, bval, row_ptr, values, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -507,22 +510,22 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         const double f = c->source[0];
         mf_prof_begin(m->elem == MF_P1_TRI ? "elem_thermal_p1" : (m->elem == MF_P2_TRI ? "elem_thermal_p2" : "elem_thermal_q1"), st);
         if (m->elem == MF_P1_TRI)
-            k_elem_thermal_p1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
-                                                             status);
+            k_elem_thermal_p1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
+                                                             p->scratch, status);
         else if (m->elem == MF_P2_TRI)
-            k_elem_thermal_p2<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->scratch,
-                                                             status);
+            k_elem_thermal_p2<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
+                                                             p->scratch, status);
         else
             k_elem_thermal_q1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->tr,
-                                                             p->scratch, status);
+                                                             p->elem_inc, p->scratch, status);
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         const mf_adj &A = p->adj[0];
         mf_prof_begin("gather_scalar", st);
 #define MF_GATHER_TH(NPE)                                                                                         \
     k_gather_th<NPE><<<nblk(A.n_rows, GT_WARPS * (32 / th_lanes<NPE>())), GT_WARPS * 32, 0, st>>>(                 \
-        A.n_rows, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->slot, p->scratch, p->scratch_stride, p->tr,    \
-        p->kref, c->elem_coef, f, c->bc_mask, c->bc_val, p->row_ptr, values, d)
+        A.n_rows, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->inc_slot, p->scratch, p->kref, c->elem_coef, f,  \
+        c->bc_mask, c->bc_val, p->row_ptr, values, d)
         if (m->elem == MF_P1_TRI) MF_GATHER_TH(3);
         else if (m->elem == MF_P2_TRI) MF_GATHER_TH(6);
         else MF_GATHER_TH(8);

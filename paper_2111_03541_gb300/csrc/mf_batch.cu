@@ -29,7 +29,8 @@ struct BatchProblem {
     const int64_t *inc_ptr;
     const int32_t *inc;
     const uint8_t *inc_loc;
-    const uint8_t *slot;
+    const uint8_t *inc_slot;
+    const int32_t *elem_inc;
     const uint8_t *tr;
     const double *kref;
     const uint8_t *mask;
@@ -69,9 +70,10 @@ __global__ void __launch_bounds__(256) k_batch_elem(const BatchProblem *__restri
         const BatchProblem &p = P[T.prob];
         for (int64_t i = threadIdx.x; i < T.count; i += blockDim.x) {
             const int64_t e = T.first + i;
-            if (T.type == MF_P1_TRI) elem_thermal_p1(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
-            else if (T.type == MF_P2_TRI) elem_thermal_p2(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
-            else if (!q1_translate(e, p.tr, p.kc, status)) elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.scratch, status);
+            if (T.type == MF_P1_TRI) elem_thermal_p1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
+            else if (T.type == MF_P2_TRI) elem_thermal_p2(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
+            else if (!q1_translate(e, p.tr, p.kc, status))
+                elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
         }
     }
 }
@@ -87,8 +89,8 @@ __device__ __forceinline__ void batch_gather_tile(const BatchProblem &p, const B
     const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
     for (int64_t i = grp; i < T.count; i += BG_WARPS * G)  // group-uniform
         gather_row_th<NPE>(T.first + i, lane & (L - 1), gmask, acc_all[grp], p.ptr, p.col, p.inc_ptr, p.inc,
-                           p.inc_loc, p.slot, p.scratch, p.stride, NPE == 8 ? p.tr : nullptr,
-                           NPE == 8 ? p.kref : nullptr, p.kc, p.f, p.mask, p.bval, p.row_ptr, p.values, p.d);
+                           p.inc_loc, p.inc_slot, p.scratch, p.kref, p.kc, p.f, p.mask, p.bval, p.row_ptr, p.values,
+                           p.d);
 }
 
 __global__ void __launch_bounds__(BG_WARPS * 32) k_batch_gather(const BatchProblem *__restrict__ P,
@@ -251,7 +253,8 @@ extern "C" mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, co
         const mf_adj &A = p->adj[0];
         b->host.push_back(BatchProblem{m->elem, m->npe, m->n_elems, m->n_nodes, m->coords, m->conn, c.elem_coef,
                                        c.source[0], p->scratch, p->scratch_stride, A.ptr, A.col, p->inc_ptr, p->inc,
-                                       p->inc_loc, p->slot, p->tr, p->kref, c.bc_mask, c.bc_val, p->row_ptr, values[i], d[i]});
+                                       p->inc_loc, p->inc_slot, p->elem_inc, p->tr, p->kref, c.bc_mask, c.bc_val,
+                                       p->row_ptr, values[i], d[i]});
         cnt[m->elem] += m->n_elems;
         nodes += m->n_nodes;
     }

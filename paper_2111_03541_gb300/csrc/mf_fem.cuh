@@ -110,8 +110,32 @@ __device__ __forceinline__ void tri6_point(int q, double (&l)[3], double &w)
 
 __device__ __forceinline__ int upair(int a, int b) { return a * (15 - a) / 2 + b; }  // a <= b < 8
 
+// Output of a thermal element routine.  With an incidence map, row a of
+// element e goes to incidence entry t = map[e * NPE + a] of node conn[e][a] as
+// [K_e[a][0..NPE), d_e[a]], so that a node's rows are contiguous; without one
+// (map == nullptr), in element order [K_e (NPE x NPE, row-major), d_e (NPE)].
+template <int NPE>
+struct ThOut {
+    int64_t base[NPE];  // offset of row a
+    int64_t ld[NPE];    // offset of load entry a
+    __device__ __forceinline__ ThOut(const int32_t *__restrict__ map, int64_t e)
+    {
+#pragma unroll
+        for (int a = 0; a < NPE; ++a) {
+            if (map) {
+                base[a] = (int64_t)map[e * NPE + a] * (NPE + 1);
+                ld[a] = base[a] + NPE;
+            } else {
+                base[a] = e * (NPE * NPE + NPE) + a * NPE;
+                ld[a] = e * (NPE * NPE + NPE) + NPE * NPE + a;
+            }
+        }
+    }
+};
+
 __device__ __forceinline__ void elem_thermal_p1(int64_t e, const double *__restrict__ X, const int32_t *__restrict__ conn,
-                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+                                  const double *__restrict__ kc, double f, const int32_t *__restrict__ map,
+                                  double *__restrict__ out, int *status)
 {
     const double k = kc[e];
     if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
@@ -119,20 +143,20 @@ __device__ __forceinline__ void elem_thermal_p1(int64_t e, const double *__restr
     const double det = tri_affine(X, conn + 3 * e, gl);
     // the integrand is constant: the 3 point weights sum to 1/2
     const double s = 0.5 * det * k;
-    double *o = out + e * 12;
+    const ThOut<3> W(map, e);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) o[3 * a + b] = s * (gl[a][0] * gl[b][0] + gl[a][1] * gl[b][1]);
+        for (int b = 0; b < 3; ++b) out[W.base[a] + b] = s * (gl[a][0] * gl[b][0] + gl[a][1] * gl[b][1]);
     // 3-point rule: sum_q w_q lambda_a(q) = 1/6
     const double l = det * f * (1.0 / 6.0);
-    o[9] = l;
-    o[10] = l;
-    o[11] = l;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[W.ld[a]] = l;
 }
 
 __device__ __forceinline__ void elem_thermal_p2(int64_t e, const double *__restrict__ X, const int32_t *__restrict__ conn,
-                                  const double *__restrict__ kc, double f, double *__restrict__ out, int *status)
+                                  const double *__restrict__ kc, double f, const int32_t *__restrict__ map,
+                                  double *__restrict__ out, int *status)
 {
     const double k = kc[e];
     if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
@@ -155,23 +179,24 @@ __device__ __forceinline__ void elem_thermal_p2(int64_t e, const double *__restr
             de[a] = fma(wd, N[a], de[a]);
         }
     }
-    double *o = out + e * 42;
+    const ThOut<6> W(map, e);
     int t = 0;
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
         for (int b = a; b < 6; ++b, ++t) {
-            o[6 * a + b] = k * Ke[t];
-            o[6 * b + a] = k * Ke[t];
+            out[W.base[a] + b] = k * Ke[t];
+            out[W.base[b] + a] = k * Ke[t];
         }
 #pragma unroll
-    for (int a = 0; a < 6; ++a) o[36 + a] = f * de[a];
+    for (int a = 0; a < 6; ++a) out[W.ld[a]] = f * de[a];
 }
 
 __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restrict__ X,
                                                          const int32_t *__restrict__ conn,
                                                          const double *__restrict__ kc, double f,
-                                                         double *__restrict__ out, int *status)
+                                                         const int32_t *__restrict__ map, double *__restrict__ out,
+                                                         int *status)
 {
     const double k = kc[e];
     if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
@@ -211,7 +236,7 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) G[i][j] = Ji[i][0] * Ji[j][0] + Ji[i][1] * Ji[j][1] + Ji[i][2] * Ji[j][2];
-        double *o = out + e * 72;
+        const ThOut<8> W(map, e);
         const double kd = k * det;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
@@ -237,10 +262,10 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
                         }
                         v = fma(r, G[i][j], v);
                     }
-                o[8 * a + b] = kd * v;
-                o[8 * b + a] = kd * v;
+                out[W.base[a] + b] = kd * v;
+                out[W.base[b] + a] = kd * v;
             }
-            o[64 + a] = f * det;
+            out[W.ld[a]] = f * det;
         }
         return;
     }
@@ -264,23 +289,23 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
             m[a] = fma(wd, q1_n(q, a), m[a]);
         }
     }
-    double *o = out + e * 72;
+    const ThOut<8> W(map, e);
     int t = 0;
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = a; b < 8; ++b, ++t) {
-            o[8 * a + b] = k * Ke[t];
-            o[8 * b + a] = k * Ke[t];
+            out[W.base[a] + b] = k * Ke[t];
+            out[W.base[b] + a] = k * Ke[t];
         }
 #pragma unroll
-    for (int a = 0; a < 8; ++a) o[64 + a] = f * m[a];
+    for (int a = 0; a < 8; ++a) out[W.ld[a]] = f * m[a];
 }
 
 
 // Thermal translate shortcut (Q1): true when element e is a translate of
-// element 0, whose unit matrices stand in for its own; the coefficient is
-// still checked here.
+// element 0, whose unit matrices stand in for its own (the gather takes k_e
+// from the coefficients); k_e is still checked here.
 __device__ __forceinline__ bool q1_translate(int64_t e, const uint8_t *__restrict__ tr, const double *__restrict__ kc,
                                              int *status)
 {
@@ -295,84 +320,120 @@ constexpr int th_lanes() { return NPE <= 4 ? 4 : 8; }
 
 // Thermal row of node n by a group of th_lanes<NPE>() lanes (`sub` = lane in
 // the group, `gmask` = the group's lanes; groups of a warp are independent).
-// Lane b fetches, for each incident element j (ascending), entry (a_j, b) of
-// the element matrix (a contiguous row of the scratch, or k_e Kref for a
-// translate) and its slot among the node's neighbours; the loads of up to 8
-// elements are issued before any add.  The adds into the shared-memory row
-// `acc` (MF_MAX_DEG doubles) then run element by element, so every entry and
-// d_n are sums in ascending element order.  Dirichlet rows become identity
-// rows; constrained columns move to the right-hand side (lifting).
+// The scratch is in incidence layout: incidence entry t of the node (element
+// e = inc[t], local index a) holds row a of K_e and d_e[a].  A translate
+// (bit 7 of inc_loc) stores nothing: it takes k_e Kref[a][b] and f dref[a].
+// Lane b fetches entry b of each of the node's rows (ascending elements) and
+// its slot among the node's neighbours; the loads of up to 4 rows, the row's
+// columns and their Dirichlet flags do not depend on one another.  The adds
+// into the shared-memory row `acc` (MF_MAX_DEG doubles) run element by
+// element, so every entry is a sum in ascending element order.  d_n: lane j
+// adds the load entries of incidence entries j, j + L, ... in turn, then the
+// group sums its lanes in a fixed tree.  Dirichlet rows become identity rows;
+// constrained columns move to the right-hand side (lifting).  FP64 is the
+// scarce pipe here, so every FP64 instruction of the loop does useful work in
+// all lanes.
 template <int NPE>
 __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask, double *acc,
                                               const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
                                               const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
-                                              const uint8_t *__restrict__ inc_loc, const uint8_t *__restrict__ slot,
-                                              const double *__restrict__ sc, int64_t stride,
-                                              const uint8_t *__restrict__ tr, const double *__restrict__ kref,
-                                              const double *__restrict__ kc, double f, const uint8_t *__restrict__ mask,
+                                              const uint8_t *__restrict__ inc_loc,
+                                              const uint8_t *__restrict__ inc_slot, const double *__restrict__ sc,
+                                              const double *__restrict__ kref, const double *__restrict__ kc,
+                                              double f, const uint8_t *__restrict__ mask,
                                               const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
                                               double *__restrict__ values, double *__restrict__ d)
 {
     constexpr int L = th_lanes<NPE>();
-    constexpr int U = 8;  // incident elements whose loads are in flight together
+    constexpr int U = 4;   // rows whose loads are in flight together
+    constexpr int KM = 4;  // prefetched columns per lane (the rest: plain loop)
+    constexpr int RS = NPE + 1;
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
     const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
     const bool rm = mask ? mask[n] != 0 : false;
     const int64_t rb = row_ptr[n];
+    int32_t mc[KM];
+    unsigned cmask = 0;  // bit i: column sub + L i is constrained
+#pragma unroll
+    for (int i = 0; i < KM; ++i) mc[i] = (sub + L * i < deg) ? adj_col[p0 + sub + L * i] : -1;
+    if (mask)
+#pragma unroll
+        for (int i = 0; i < KM; ++i)
+            if (mc[i] >= 0 && mask[mc[i]]) cmask |= 1u << i;
     for (int i = sub; i < deg; i += L) acc[i] = 0.0;
     __syncwarp(gmask);
     const int b = sub;
     const bool act = b < NPE;
     double dsum = 0.0;
+    // load vector: lane sub takes incidence entries i0 + sub, i0 + sub + L, ...
+    for (int64_t t = i0 + sub; t < i1; t += L) {
+        const int loc = inc_loc[t];
+        dsum += (loc & 0x80) ? f * __ldg(&kref[NPE * NPE + (loc & 0x7f)]) : sc[t * RS + NPE];
+    }
     for (int64_t cb = i0; cb < i1; cb += U) {
         const int cnt = (int)min((int64_t)U, i1 - cb);
-        double v[U], ld[U];
+        double mul[U], val[U];
         int s[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-            v[j] = 0.0;
-            ld[j] = 0.0;
+            mul[j] = 1.0;
+            val[j] = 0.0;
             s[j] = 0;
             if (j < cnt && act) {
-                const int64_t e = inc[cb + j];
-                const int a = inc_loc[cb + j];
-                s[j] = slot[(e * NPE + a) * NPE + b];
-                if (tr && tr[e]) {
-                    v[j] = kc[e] * __ldg(&kref[a * NPE + b]);
-                    if (b == 0) ld[j] = f * __ldg(&kref[NPE * NPE + a]);
+                const int64_t t = cb + j;
+                const int loc = inc_loc[t];
+                s[j] = inc_slot[t * NPE + b];
+                if (loc & 0x80) {
+                    mul[j] = kc[inc[t]];
+                    val[j] = __ldg(&kref[(loc & 0x7f) * NPE + b]);
                 } else {
-                    const double *se = sc + e * stride;
-                    v[j] = se[a * NPE + b];
-                    if (b == 0) ld[j] = se[NPE * NPE + a];
+                    val[j] = sc[t * RS + b];
                 }
             }
         }
 #pragma unroll
         for (int j = 0; j < U; ++j) {
             if (j < cnt) {  // group-uniform
-                if (act) acc[s[j]] += v[j];
-                dsum += ld[j];
+                if (act) acc[s[j]] = fma(mul[j], val[j], acc[s[j]]);  // exact product when mul = 1
                 __syncwarp(gmask);
             }
         }
     }
     double lift = 0.0;
-    for (int k = sub; k < deg; k += L) {
-        const int64_t mcol = adj_col[p0 + k];
-        double val = acc[k];
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+        if (mc[i] < 0) continue;
+        const int k = sub + L * i;
+        double v = acc[k];
         if (mask) {
             if (rm) {
-                val = (mcol == n) ? 1.0 : 0.0;
-            } else if (mask[mcol]) {
-                lift -= val * bval[mcol];
-                val = 0.0;
+                v = (mc[i] == n) ? 1.0 : 0.0;
+            } else if (cmask & (1u << i)) {
+                lift -= v * bval[mc[i]];
+                v = 0.0;
             }
         }
-        values[rb + k] = val;
+        values[rb + k] = v;
+    }
+    for (int k = sub + L * KM; k < deg; k += L) {  // rows longer than L * KM
+        const int64_t mcol = adj_col[p0 + k];
+        double v = acc[k];
+        if (mask) {
+            if (rm) {
+                v = (mcol == n) ? 1.0 : 0.0;
+            } else if (mask[mcol]) {
+                lift -= v * bval[mcol];
+                v = 0.0;
+            }
+        }
+        values[rb + k] = v;
     }
 #pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) lift += __shfl_xor_sync(gmask, lift, o, L);
+    for (int o = L / 2; o > 0; o >>= 1) dsum += __shfl_xor_sync(gmask, dsum, o, L);
+    if (__any_sync(gmask, lift != 0.0))  // rows next to a constrained node only
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) lift += __shfl_xor_sync(gmask, lift, o, L);
     if (sub == 0) d[n] = rm ? bval[n] : dsum + lift;
     __syncwarp(gmask);
 }

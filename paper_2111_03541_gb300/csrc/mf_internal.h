@@ -49,13 +49,20 @@ struct mf_pattern {
     // incident elements per row node (ascending), for the mixed path
     int64_t *inc_ptr = nullptr;
     int32_t *inc = nullptr;
-    uint8_t *inc_loc = nullptr;  // position of the node in each incident element
+    uint8_t *inc_loc = nullptr;  // position of the node in each incident element (thermal
+                                 // Q1: bit 7 set when the element is a translate)
     // flow: elements incident to each P1 pressure node, ascending
     int64_t *pinc_ptr = nullptr;
     int32_t *pinc = nullptr;
-    // thermal and elasticity: slot[e][a][b] = position of node conn[e][b]
-    // among the sorted neighbours of node conn[e][a] (u8, n_elems x npe x npe)
+    // elasticity: slot[e][a][b] = position of node conn[e][b] among the sorted
+    // neighbours of node conn[e][a] (u8, n_elems x 64)
     uint8_t *slot = nullptr;
+    // thermal: inc_slot[t][b] = the same position for incidence entry t of a
+    // node (element inc[t], local index inc_loc[t]) (u8, n_elems x npe x npe);
+    // elem_inc[e][a] = the incidence entry of (e, a): the scratch holds row a
+    // of K_e and d_e[a] there ((npe + 1) doubles per entry)
+    uint8_t *inc_slot = nullptr;
+    int32_t *elem_inc = nullptr;
     // thermal Q1: tr[e] = 1 when element e is an exact translate of element 0
     // (equal edge vectors x_a - x_0 in FP64), so K_e = k_e Kref and
     // d_e = f dref with kref = [Kref (8 x 8), dref (8)] element 0's unit-k,

@@ -201,6 +201,40 @@ __global__ void k_node_ready(int64_t n, const int64_t *__restrict__ inc_ptr, con
     ready[v] = inc_ptr[v + 1] > inc_ptr[v] ? inc[inc_ptr[v + 1] - 1] : -1;
 }
 
+// incidence slot map: for incidence entry t of node n (element e, local a),
+// inc_slot[t * npe + b] = position of conn[e][b] among the neighbours of n
+__global__ void k_inc_slot(int64_t n_nodes, int npe, const int32_t *__restrict__ conn,
+                           const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
+                           const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, uint8_t *inc_slot)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    for (int64_t t = inc_ptr[n]; t < inc_ptr[n + 1]; ++t) {
+        const int32_t *ce = conn + (int64_t)inc[t] * npe;
+        for (int b = 0; b < npe; ++b)
+            inc_slot[t * npe + b] = (uint8_t)(find_pair(ptr, col, (int32_t)n, ce[b]) - ptr[n]);
+    }
+}
+
+// elem_inc[e * npe + a] = incidence entry of (e, a)
+__global__ void k_elem_inc(int64_t n_nodes, int npe, const int64_t *__restrict__ inc_ptr,
+                           const int32_t *__restrict__ inc, const uint8_t *__restrict__ loc, int32_t *elem_inc)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    for (int64_t t = inc_ptr[n]; t < inc_ptr[n + 1]; ++t) elem_inc[(int64_t)inc[t] * npe + loc[t]] = (int32_t)t;
+}
+
+// bit 7 of inc_loc marks incidence entries of translate elements
+__global__ void k_mark_translates(int64_t n_nodes, const int64_t *__restrict__ inc_ptr,
+                                  const int32_t *__restrict__ inc, const uint8_t *__restrict__ tr, uint8_t *loc)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    for (int64_t t = inc_ptr[n]; t < inc_ptr[n + 1]; ++t)
+        if (tr[inc[t]]) loc[t] |= 0x80;
+}
+
 // slot map: position of conn[e][b] among the neighbours of conn[e][a],
 // slot[(e * npe + a) * npe + b]
 __global__ void k_slot_map(int64_t n_el, int npe, const int32_t *__restrict__ conn, const int64_t *__restrict__ ptr,
@@ -243,7 +277,7 @@ __global__ void k_translate_flags(int64_t n_el, const double *__restrict__ X, co
 __global__ void k_kref(const double *__restrict__ X, const int32_t *__restrict__ conn, double *kref, int *status)
 {
     kref[72] = 1.0;
-    elem_thermal_q1(0, X, conn, kref + 72, 1.0, kref, status);
+    elem_thermal_q1(0, X, conn, kref + 72, 1.0, nullptr, kref, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,6 +520,10 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->pinc_ptr);
     cudaFree(p->pinc);
     cudaFree(p->slot);
+    cudaFree(p->inc_slot);
+    p->inc_slot = nullptr;
+    cudaFree(p->elem_inc);
+    p->elem_inc = nullptr;
     cudaFree(p->mixed_state);
     cudaFree(p->tr);
     cudaFree(p->kref);
@@ -525,9 +563,15 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
         k_csr_thermal<<<nblk(p->n_rows + 1), TPB, 0, st>>>(p->n_rows, p->adj[0].ptr, p->row_ptr);
         MF_CUDA(cudaMemcpyAsync(p->col_idx, p->adj[0].col, sizeof(int32_t) * p->nnz, cudaMemcpyDeviceToDevice, st));
-        const int64_t nslot = (int64_t)npe * npe * m->n_elems;
-        MF_CUDA(cudaMallocAsync(&p->slot, (size_t)nslot, st));
-        k_slot_map<<<nblk(nslot), TPB, 0, st>>>(m->n_elems, npe, m->conn, p->adj[0].ptr, p->adj[0].col, p->slot);
+        if ((int64_t)npe * m->n_elems >= INT32_MAX) {
+            free_inc(incv, st);
+            return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: more than 2^31 element-node incidences");
+        }
+        MF_CUDA(cudaMallocAsync(&p->elem_inc, sizeof(int32_t) * npe * m->n_elems, st));
+        k_elem_inc<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, incv.ptr, incv.inc, incv.loc, p->elem_inc);
+        MF_CUDA(cudaMallocAsync(&p->inc_slot, (size_t)npe * npe * m->n_elems, st));
+        k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, m->conn, incv.ptr, incv.inc, p->adj[0].ptr,
+                                                     p->adj[0].col, p->inc_slot);
         p->scratch_stride = (int64_t)npe * npe + npe;
         if (m->elem == MF_Q1_HEX && m->n_elems > 0) {
             unsigned long long *cnt = nullptr;
@@ -546,6 +590,7 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
             } else {
                 MF_CUDA(cudaMallocAsync(&p->kref, sizeof(double) * 73, st));
                 k_kref<<<1, 1, 0, st>>>(m->coords, m->conn, p->kref, status);
+                k_mark_translates<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, incv.ptr, incv.inc, p->tr, incv.loc);
             }
         }
     } else if (form == MF_FORM_ELASTIC) {
