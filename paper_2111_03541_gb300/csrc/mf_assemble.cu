@@ -259,7 +259,7 @@ __device__ __forceinline__ double to_double<long long>(long long v, int S)
 template <typename T>
 __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
     int64_t n0, int64_t n1, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
-    const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const int32_t *__restrict__ conn,
+    const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
     const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
     int fp, int fq, const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
     double *__restrict__ values, double *__restrict__ d)
@@ -273,7 +273,10 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
     for (int i = lane; i < 9 * deg; i += 32) acc[i] = T(0);
-    double dsum = 0.0;  // lane c < 3: load of component c
+    // load vector: lane 3 j + c (j < 8) holds component c of incidence entry
+    // j, j + 8, ... in turn; the 8 partial sums of component c are added in a
+    // fixed tree below
+    double dsum = 0.0;
     __syncwarp();
     const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
     // incident elements in chunks of 8: element ids and the local index of n
@@ -284,10 +287,13 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
         int my_a = 0;
         if (lane < cnt) {
             my_e = inc[cb + lane];
-            const int32_t *ce = conn + my_e * 8;
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (ce[k] == (int32_t)n) my_a = k;
+            my_a = inc_loc[cb + lane];
+        }
+        {
+            const int jd = lane / 3, cd = lane - 3 * (lane / 3);
+            const int64_t ed = __shfl_sync(0xffffffffu, my_e, jd < 8 ? jd : 0);
+            const int ad = __shfl_sync(0xffffffffu, my_a, jd < 8 ? jd : 0);
+            if (jd < cnt) dsum += sc[ed * stride + 324 + 3 * ad + cd];
         }
         if constexpr (fixed) {
             // exact integer sums: order is irrelevant, so every value of the
@@ -310,11 +316,6 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
                               (unsigned long long)v);
                 }
             }
-            for (int j = 0; j < cnt; ++j) {
-                const int64_t e = __shfl_sync(0xffffffffu, my_e, j);
-                const int a = __shfl_sync(0xffffffffu, my_a, j);
-                if (lane < 3) dsum += sc[e * stride + 324 + 3 * a + lane];
-            }
         } else {
             // FP64 sums in ascending element order (bit-reproducible)
             for (int j = 0; j < cnt; ++j) {
@@ -327,12 +328,15 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
                     const T v = (a <= b) ? blk[upair(a, b) * 9 + cc] : blk[upair(b, a) * 9 + 3 * cp + c];
                     acc[slot[e * 64 + a * 8 + b] * 9 + cc] += v;
                 }
-                if (lane < 3) dsum += sc[e * stride + 324 + 3 * a + lane];
                 __syncwarp();
             }
         }
         __syncwarp();
     }
+    // component c of the load: lanes c, c + 3, ..., c + 21 (fixed tree)
+    dsum += __shfl_down_sync(0xffffffffu, dsum, 12);  // lanes c + 3 j, j < 4, take j + 4
+    dsum += __shfl_down_sync(0xffffffffu, dsum, 6);   // j < 2 take j + 2
+    dsum += __shfl_down_sync(0xffffffffu, dsum, 3);   // j = 0 takes j = 1
     const int S = scale ? *scale : 0;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
@@ -355,8 +359,9 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
             }
             values[rb + j] = v;
         }
+        if (__any_sync(0xffffffffu, lift != 0.0))  // rows next to a constrained dof only
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
+            for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
         const double dc = __shfl_sync(0xffffffffu, dsum, c);
         if (lane == 0) d[r] = rm ? bval[r] : dc + lift;
     }
@@ -480,11 +485,11 @@ void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int6
     const unsigned grid = nblk(n1 - n0, GEL_WARPS);
     if (fixed_point)
         k_gather_el<long long><<<grid, GEL_WARPS * 32, 0, st>>>(
-            n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride,
+            n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->slot, p->scratch, p->scratch_stride,
             static_cast<const int *>(p->mixed_state), fp, fq, c->bc_mask, c->bc_val, p->row_ptr, values, d);
     else
         k_gather_el<double><<<grid, GEL_WARPS * 32, 0, st>>>(
-            n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, m->conn, p->slot, p->scratch, p->scratch_stride, nullptr,
+            n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->slot, p->scratch, p->scratch_stride, nullptr,
             0, 0, c->bc_mask, c->bc_val, p->row_ptr, values, d);
 }
 
@@ -534,20 +539,27 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
     } else if (form == MF_FORM_ELASTIC) {
         const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;
         MF_CUDA(cudaFuncSetAttribute(k_elem_elastic_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        // chunk by chunk: the gather reads element blocks still resident in L2
-        const size_t nsl = p->slab_e.size() - 1;
-        for (size_t k = 0; k < nsl; ++k) {
-            const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
-            mf_prof_begin("elem_elastic_q1_fp64", st);
-            k_elem_elastic_q1<<<nblk(e1 - e0, EL_T), EL_T, smem, st>>>(e0, e1, m->coords, m->conn, c->elem_coef,
-                                                                      c->nu, c->source[0], c->source[1],
-                                                                      c->source[2], p->scratch, status);
-            mf_prof_end(st);
-            MF_CUDA(cudaGetLastError());
-            mf_prof_begin("gather_elastic", st);
-            mf_launch_gather_elastic(false, 0, 0, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, st);
-            mf_prof_end(st);
-        }
+        mf_status s = mf_slab_pipeline(
+            p, st,
+            [&](size_t k, cudaStream_t s2) -> mf_status {
+                const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
+                mf_prof_begin("elem_elastic_q1_fp64", s2);
+                k_elem_elastic_q1<<<nblk(e1 - e0, EL_T), EL_T, smem, s2>>>(e0, e1, m->coords, m->conn,
+                                                                          c->elem_coef, c->nu, c->source[0],
+                                                                          c->source[1], c->source[2], p->scratch,
+                                                                          status);
+                mf_prof_end(s2);
+                MF_CUDA(cudaGetLastError());
+                return MF_OK;
+            },
+            [&](size_t k, cudaStream_t s2) -> mf_status {
+                mf_prof_begin("gather_elastic", s2);
+                mf_launch_gather_elastic(false, 0, 0, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, s2);
+                mf_prof_end(s2);
+                MF_CUDA(cudaGetLastError());
+                return MF_OK;
+            });
+        if (s != MF_OK) return s;
     } else {
         mf_prof_begin("elem_oseen", st);
         k_elem_oseen<<<nblk(ne, 128), 128, 0, st>>>(ne, m->n_nodes, m->coords, m->conn, c->advect, c->visc, c->rho,

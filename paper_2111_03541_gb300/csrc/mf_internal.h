@@ -9,6 +9,7 @@
 #include "../../include/mf.h"
 
 #define MF_MAX_DEG 64   // neighbours of one node in one adjacency
+#define MF_SLABS 1      // element chunks of the elasticity assembly (see plan_slabs)
 #define MF_MAX_INC 32   // elements incident to one node
 
 // Adjacency between a row node space and a column node space (Block B-1: the
@@ -76,6 +77,12 @@ struct mf_pattern {
     // rows of nodes [slab_n[c], slab_n[c+1]); assembling chunk by chunk keeps the
     // element scratch of the gather in L2
     std::vector<int64_t> slab_e, slab_n;
+    // with more than one chunk, the gather of chunk k runs on `side` while
+    // chunk k + 1 is computed on the caller's stream (forked and joined by
+    // events, so the pair can be captured in a CUDA graph)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    std::vector<cudaEvent_t> slab_ev;
 };
 
 // status word (device) of the current device
@@ -120,3 +127,34 @@ __device__ __forceinline__ void mf_dev_fail(int *word, int code) { atomicCAS(wor
         cudaError_t e_ = (call);                                           \
         if (e_ != cudaSuccess) return mf_cuda_check(e_, #call);            \
     } while (0)
+
+// Element chunks and their gathers, overlapped across the caller's stream and
+// the pattern's side stream: elem(k, st) is launched for every chunk k in
+// turn, gather(k, s) on the stream s it is given.
+template <typename Elem, typename Gather>
+mf_status mf_slab_pipeline(const mf_pattern *p, cudaStream_t st, Elem elem, Gather gather)
+{
+    const size_t nsl = p->slab_e.size() - 1;
+    const bool two = nsl > 1 && p->side;
+    if (two) {
+        if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+        if (cudaStreamWaitEvent(p->side, p->fork_ev, 0) != cudaSuccess)
+            return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+    }
+    for (size_t k = 0; k < nsl; ++k) {
+        mf_status s = elem(k, st);
+        if (s != MF_OK) return s;
+        if (two) {
+            if (cudaEventRecord(p->slab_ev[k], st) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+            if (cudaStreamWaitEvent(p->side, p->slab_ev[k], 0) != cudaSuccess)
+                return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+        }
+        s = gather(k, two ? p->side : st);
+        if (s != MF_OK) return s;
+    }
+    if (two) {
+        if (cudaEventRecord(p->join_ev, p->side) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+        if (cudaStreamWaitEvent(st, p->join_ev, 0) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+    }
+    return MF_OK;
+}

@@ -462,19 +462,23 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     mf_prof_end(st);
     const size_t smem = sizeof(WarpSmem) * MX_WARPS;
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const size_t nsl = p->slab_e.size() - 1;
-    for (size_t k = 0; k < nsl; ++k) {
-        const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
-        mf_prof_begin("mixed_elem", st);
-        k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
-            e0, e1, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms,
-            p->scratch, p->scratch_stride, status);
-        mf_prof_end(st);
-        MF_CUDA(cudaGetLastError());
-        mf_prof_begin("gather_elastic_fixed", st);
-        mf_launch_gather_elastic(true, pp, qq, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, st);
-        mf_prof_end(st);
-    }
-    MF_CUDA(cudaGetLastError());
-    return MF_OK;
+    return mf_slab_pipeline(
+        p, st,
+        [&](size_t k, cudaStream_t s) -> mf_status {
+            const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
+            mf_prof_begin("mixed_elem", s);
+            k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, s>>>(
+                e0, e1, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms,
+                p->scratch, p->scratch_stride, status);
+            mf_prof_end(s);
+            MF_CUDA(cudaGetLastError());
+            return MF_OK;
+        },
+        [&](size_t k, cudaStream_t s) -> mf_status {
+            mf_prof_begin("gather_elastic_fixed", s);
+            mf_launch_gather_elastic(true, pp, qq, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, s);
+            mf_prof_end(s);
+            MF_CUDA(cudaGetLastError());
+            return MF_OK;
+        });
 }

@@ -447,13 +447,14 @@ mf_status plan_slabs(const mf_mesh *m, const Incidence &inc, int64_t stride, cud
     MF_CUDA(cudaStreamSynchronize(st));
     MF_CUDA(cudaFreeAsync(d_ready, st));
     for (int64_t v = 1; v < nn; ++v) ready[v] = std::max(ready[v], ready[v - 1]);  // prefix maximum
-    // Chunked assembly was measured slower on the 64^3 elasticity workload
-    // (30 serial launches per step cost more in ramp-up and tail than the L2
-    // residency of the scratch saves: 2.08 vs 1.67 ms), so one chunk covers
-    // the mesh; SLAB_BYTES > 0 restores chunks of about that many scratch bytes.
-    constexpr int64_t SLAB_BYTES = 0;
-    const int64_t chunk = SLAB_BYTES > 0 ? std::max<int64_t>(1024, SLAB_BYTES / (stride * 8)) : ne;
+    // MF_SLABS chunks of elements; with more than one, the gather of a chunk
+    // overlaps the element kernel of the next on a second stream.  Measured on
+    // the 64^3 elasticity workload, one chunk is fastest: serial chunks lose
+    // to launch ramp-up and tail (2.08 vs 1.67 ms), and 8 overlapped chunks to
+    // the two kernels slowing each other down, both issue-heavy (mixed path
+    // 1.70 vs 1.59 ms).
     (void)stride;
+    const int64_t chunk = std::max<int64_t>(4096, (ne + MF_SLABS - 1) / MF_SLABS);
     p->slab_e.clear();
     p->slab_n.clear();
     p->slab_e.push_back(0);
@@ -503,6 +504,15 @@ mf_status mf_mesh_validate(const mf_mesh *m, cudaStream_t st)
 
 void mf_pattern_free(mf_pattern *p)
 {
+    if (p->side) cudaStreamSynchronize(p->side);
+    for (cudaEvent_t ev : p->slab_ev)
+        if (ev) cudaEventDestroy(ev);
+    p->slab_ev.clear();
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->join_ev) cudaEventDestroy(p->join_ev);
+    if (p->side) cudaStreamDestroy(p->side);
+    p->fork_ev = p->join_ev = nullptr;
+    p->side = nullptr;
     cudaFree(p->row_ptr);
     cudaFree(p->col_idx);
     for (int i = 0; i < 3; ++i) {
@@ -608,6 +618,13 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         p->scratch_stride = 36 * 9 + 24;
         mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);
         if (ss != MF_OK) { free_inc(incv, st); return ss; }
+        if (p->slab_e.size() > 2) {
+            MF_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+            MF_CUDA(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
+            MF_CUDA(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
+            p->slab_ev.resize(p->slab_e.size() - 1, nullptr);
+            for (cudaEvent_t &ev : p->slab_ev) MF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
     } else {
         Incidence incp;
         s = build_incidence(m->n_pnodes, m->n_elems, 3, m->pconn, st, &incp, status);
