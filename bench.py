@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "elements assembled/s (+% HBM roofline), mixed vs FP64 path at <=1e-8 rel err"
 UNIT = "elements/s"
 N_GRID = 64
+FCG_DIRS = 256  # stored directions of the flexible CG with the learned preconditioner
 WORKLOAD = "3D linear elasticity, Q1 hexahedra on a 64^3 box (262,144 elements, 823,875 dofs), FP64 CSR"
 
 
@@ -416,10 +417,11 @@ def suite(dev):
         logk = learned.node_logk(P)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        x, st, info, fb = learned.fcg(P, cnn, logk, tol=1e-8, max_iter=4000)
+        x, st, info, fb = learned.fcg(P, cnn, logk, tol=1e-8, max_iter=4000, m_dirs=FCG_DIRS)
         torch.cuda.synchronize()
         c4["fcg_cnn"] = {"iterations": int(info.iterations), "rel_residual": info.rel_residual,
-                         "converged": bool(info.converged), "s": time.perf_counter() - t, "jacobi_fallbacks": fb}
+                         "converged": bool(info.converged), "s": time.perf_counter() - t, "jacobi_fallbacks": fb,
+                         "stored_directions": FCG_DIRS}
         xin = torch.zeros(2 * P.n, dtype=torch.bfloat16, device=dev)
         y = torch.empty(P.n, dtype=torch.float32, device=dev)
         nz = prob["n"] + 1

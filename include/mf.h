@@ -285,12 +285,15 @@ mf_status mf_cnn_node_logk(int32_t nz, int32_t ny, int32_t nx, const double *kce
 mf_status mf_cnn_input(int64_t n, const double *r, const float *logk, void *x_bf16, void *stream);
 /* y = a x + b y on device vectors of length n. */
 mf_status mf_axpby(int64_t n, double a, const double *x, double b, double *y, void *stream);
-/* Flexible CG (Notay 2000, one stored direction) preconditioned by the CNN
- * correction with the Jacobi fallback; x holds x0 on entry.  fallbacks (may
- * be NULL) counts the iterations that fell back to Jacobi.  Errors: as mf_solve. */
+/* Flexible CG (Notay 2000) preconditioned by the CNN correction with the
+ * Jacobi fallback, each new direction K-orthogonalised against the last
+ * m_dirs directions (1 <= m_dirs <= 256; 1 is the classic flexible CG); x holds x0 on
+ * entry.  fallbacks (may be NULL) counts the iterations that fell back to
+ * Jacobi.  Work space: (2 m_dirs + 4) vectors of n doubles.  Errors: as
+ * mf_solve, MF_ERR_INVALID_ARG for m_dirs outside [1, 256]. */
 mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *x, mf_cnn *cnn, int32_t nz, int32_t ny,
                            int32_t nx, const float *logk, const uint8_t *mask, double tol, int64_t max_iter,
-                           mf_solve_info *info, int64_t *fallbacks, void *stream);
+                           int32_t m_dirs, mf_solve_info *info, int64_t *fallbacks, void *stream);
 
 /* Synchronises the stream, returns and clears the latched device status. */
 mf_status mf_sync_status(void *stream);

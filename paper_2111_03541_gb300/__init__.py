@@ -103,7 +103,7 @@ _SIGS = {
     "mf_cnn_input": [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_axpby": [C.c_int64, C.c_double, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
     "mf_solve_fcg_cnn": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
-                         C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.POINTER(SolveInfo),
+                         C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.c_int32, C.POINTER(SolveInfo),
                          C.POINTER(C.c_int64), C.c_void_p],
     "mf_set_kernel_timing": [C.c_int32],
     "mf_kernel_times": [C.c_char_p, C.c_size_t],
@@ -321,12 +321,12 @@ def mf_axpby(n, a, x, b, y, stream=None) -> None:
     _check(lib().mf_axpby(n, a, _ptr(x), b, _ptr(y), _stream(stream)))
 
 
-def mf_solve_fcg_cnn(K: CSR, d, x, cnn, nz, ny, nx, logk, mask, tol, max_iter, stream=None,
+def mf_solve_fcg_cnn(K: CSR, d, x, cnn, nz, ny, nx, logk, mask, tol, max_iter, m_dirs=1, stream=None,
                      allow=(MF_ERR_NOT_CONVERGED,)):
     info = SolveInfo()
     fb = C.c_int64()
     st = _check(lib().mf_solve_fcg_cnn(C.byref(K), _ptr(d), _ptr(x), cnn, nz, ny, nx, _ptr(logk), _ptr(mask), tol,
-                                       max_iter, C.byref(info), C.byref(fb), _stream(stream)), allow)
+                                       max_iter, m_dirs, C.byref(info), C.byref(fb), _stream(stream)), allow)
     return st, info, fb.value
 
 

@@ -82,7 +82,7 @@ bool g_prof_on = false;
 std::vector<ProfRec> g_prof_pending;
 std::vector<cudaEvent_t> g_prof_pool;
 std::map<std::string, std::pair<long long, double>> g_prof_acc;
-ProfRec *g_prof_open = nullptr;
+std::vector<size_t> g_prof_open;  // open records (indices), innermost last
 
 cudaEvent_t prof_event()
 {
@@ -102,16 +102,16 @@ void mf_prof_begin(const char *name, cudaStream_t st)
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
     g_prof_pending.push_back(ProfRec{name, prof_event(), prof_event()});
-    g_prof_open = &g_prof_pending.back();
-    cudaEventRecord(g_prof_open->a, st);
+    g_prof_open.push_back(g_prof_pending.size() - 1);
+    cudaEventRecord(g_prof_pending.back().a, st);
 }
 
 void mf_prof_end(cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on || !g_prof_open) return;
-    cudaEventRecord(g_prof_open->b, st);
-    g_prof_open = nullptr;
+    if (!g_prof_on || g_prof_open.empty()) return;
+    cudaEventRecord(g_prof_pending[g_prof_open.back()].b, st);
+    g_prof_open.pop_back();
 }
 
 extern "C" mf_status mf_set_kernel_timing(int32_t enable)
@@ -128,7 +128,10 @@ extern "C" mf_status mf_kernel_times(char *buf, size_t len)
     for (ProfRec &r : g_prof_pending) {
         if (cudaEventSynchronize(r.b) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_kernel_times");
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();  // a record closed after mf_kernel_times: dropped
+            ms = 0.f;
+        }
         auto &acc = g_prof_acc[r.name];
         acc.first += 1;
         acc.second += ms;
@@ -136,7 +139,7 @@ extern "C" mf_status mf_kernel_times(char *buf, size_t len)
         g_prof_pool.push_back(r.b);
     }
     g_prof_pending.clear();
-    g_prof_open = nullptr;
+    g_prof_open.clear();
     std::string out;
     char line[256];
     for (auto &kv : g_prof_acc) {

@@ -13,6 +13,7 @@
 // with the Jacobi step z = D^-1 r whenever z . r <= 0 or z is not finite.
 // Training loss over a batch of residuals r_b of systems K_b:
 //   L = (1/B) sum_b || K_b z_b - r_b ||^2 / || r_b ||^2.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -50,43 +51,86 @@ __device__ __forceinline__ bool nb_index(int v, int o, int nz, int ny, int nx, i
     return true;
 }
 
-// forward: one thread per output node, all output channels; weights in smem
-template <int CI, int CO, bool RELU, bool OUT_F32>
-__global__ void __launch_bounds__(128) k_conv_fwd(int B, int nz, int ny, int nx, const __nv_bfloat16 *__restrict__ in,
-                                                  const __nv_bfloat16 *__restrict__ w, const float *__restrict__ bias,
-                                                  void *__restrict__ out)
+// Forward kernels are persistent (grid-stride over nodes or runs, a few
+// blocks per SM), so each block stages its layer's weights in shared memory
+// once.  Activations are channels-last BF16: a node's 16 channels are 32 bytes,
+// moved as two 16-byte vectors.
+
+// first layer, 2 -> 16 channels, ReLU, BF16 out: one thread per node
+__global__ void __launch_bounds__(256) k_conv_first(int B, int nz, int ny, int nx,
+                                                    const __nv_bfloat16 *__restrict__ in,
+                                                    const __nv_bfloat16 *__restrict__ w,
+                                                    const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out)
 {
-    __shared__ float sw[CO * CI * 27];
-    for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) sw[i] = __bfloat162float(w[i]);
+    __shared__ float sw[27][2][16];  // [o][ci][co]; source layout [co][ci][o]
+    for (int i = threadIdx.x; i < 16 * 2 * 27; i += blockDim.x) {
+        const int co = i / 54, ci = (i / 27) % 2, o = i % 27;
+        sw[o][ci][co] = __bfloat162float(w[i]);
+    }
     __syncthreads();
     const int nv = nz * ny * nx;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= (int64_t)B * nv) return;
-    const int b = (int)(g / nv), v = (int)(g % nv);
-    float acc[CO];
+    const int64_t tot = (int64_t)B * nv;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(g / nv), v = (int)(g - (int64_t)b * nv);
+        const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+        const uint32_t *base = reinterpret_cast<const uint32_t *>(in + (int64_t)b * nv * 2);
+        float acc[16];
 #pragma unroll
-    for (int co = 0; co < CO; ++co) acc[co] = bias[co];
-    const __nv_bfloat16 *base = in + (int64_t)b * nv * CI;
-#pragma unroll 1
-    for (int o = 0; o < 27; ++o) {
-        int u;
-        if (!nb_index(v, o, nz, ny, nx, u)) continue;
-        float xv[CI];
+        for (int co = 0; co < 16; ++co) acc[co] = bias[co];
+#pragma unroll 3
+        for (int o = 0; o < 27; ++o) {
+            const int zz = z + o / 9 - 1, yy = y + (o / 3) % 3 - 1, xx = x + o % 3 - 1;
+            if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
+            const uint32_t raw = __ldg(base + (zz * ny + yy) * nx + xx);
+            const float x0 = __uint_as_float(raw << 16), x1 = __uint_as_float(raw & 0xffff0000u);
 #pragma unroll
-        for (int ci = 0; ci < CI; ++ci) xv[ci] = __bfloat162float(base[(int64_t)u * CI + ci]);
+            for (int co = 0; co < 16; ++co) acc[co] = fmaf(sw[o][0][co], x0, fmaf(sw[o][1][co], x1, acc[co]));
+        }
+        uint32_t pk[8];
 #pragma unroll
-        for (int co = 0; co < CO; ++co)
-#pragma unroll
-            for (int ci = 0; ci < CI; ++ci) acc[co] = fmaf(sw[(co * CI + ci) * 27 + o], xv[ci], acc[co]);
+        for (int k = 0; k < 8; ++k) {
+            __nv_bfloat162 h;
+            h.x = __float2bfloat16_rn(fmaxf(acc[2 * k], 0.f));
+            h.y = __float2bfloat16_rn(fmaxf(acc[2 * k + 1], 0.f));
+            pk[k] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        uint4 *o4 = reinterpret_cast<uint4 *>(out + g * 16);
+        o4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
-    if (OUT_F32) {
-        float *o = static_cast<float *>(out) + g * CO;
+}
+
+// last layer, 16 -> 1 channel, no ReLU, FP32 out: one thread per node
+__global__ void __launch_bounds__(256) k_conv_last(int B, int nz, int ny, int nx,
+                                                   const __nv_bfloat16 *__restrict__ in,
+                                                   const __nv_bfloat16 *__restrict__ w,
+                                                   const float *__restrict__ bias, float *__restrict__ out)
+{
+    __shared__ float sw[27][16];  // [o][ci]; source layout [ci][o]
+    for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) sw[i % 27][i / 27] = __bfloat162float(w[i]);
+    __syncthreads();
+    const int nv = nz * ny * nx;
+    const int64_t tot = (int64_t)B * nv;
+    const float b0 = bias[0];
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(g / nv), v = (int)(g - (int64_t)b * nv);
+        const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+        const uint4 *base = reinterpret_cast<const uint4 *>(in + (int64_t)b * nv * 16);
+        float acc = b0;
+#pragma unroll 3
+        for (int o = 0; o < 27; ++o) {
+            const int zz = z + o / 9 - 1, yy = y + (o / 3) % 3 - 1, xx = x + o % 3 - 1;
+            if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
+            const int64_t u = (int64_t)(zz * ny + yy) * nx + xx;
+            const uint4 lo = __ldg(base + 2 * u), hi = __ldg(base + 2 * u + 1);
+            const uint32_t wds[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-        for (int co = 0; co < CO; ++co) o[co] = RELU ? fmaxf(acc[co], 0.f) : acc[co];
-    } else {
-        __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + g * CO;
-#pragma unroll
-        for (int co = 0; co < CO; ++co) o[co] = __float2bfloat16_rn(RELU ? fmaxf(acc[co], 0.f) : acc[co]);
+            for (int k = 0; k < 8; ++k) {
+                acc = fmaf(sw[o][2 * k], __uint_as_float(wds[k] << 16), acc);
+                acc = fmaf(sw[o][2 * k + 1], __uint_as_float(wds[k] & 0xffff0000u), acc);
+            }
+        }
+        out[g] = acc;
     }
 }
 
@@ -107,7 +151,7 @@ __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1
 }
 
 template <bool RELU>
-__global__ void __launch_bounds__(128) k_conv16_mma(int B, int nz, int ny, int nx, const __nv_bfloat16 *__restrict__ in,
+__global__ void __launch_bounds__(256) k_conv16_mma(int B, int nz, int ny, int nx, const __nv_bfloat16 *__restrict__ in,
                                                     const __nv_bfloat16 *__restrict__ w,
                                                     const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out)
 {
@@ -120,56 +164,68 @@ __global__ void __launch_bounds__(128) k_conv16_mma(int B, int nz, int ny, int n
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int xt = (nx + 15) / 16;  // x-runs per row
     const int64_t runs = (int64_t)B * nz * ny * xt;
-    const int64_t run = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (run >= runs) return;  // warp-uniform
-    const int xr = (int)(run % xt);
-    int64_t rest = run / xt;
-    const int y = (int)(rest % ny);
-    rest /= ny;
-    const int z = (int)(rest % nz);
-    const int b = (int)(rest / nz);
-    const int nv = nz * ny * nx;
-    const __nv_bfloat16 *base = in + (int64_t)b * nv * 16;
-    const int x0 = xr * 16 + g, x1 = x0 + 8;  // the two A rows of this lane
-    float acc[2][4] = {};
+    const int wpb = blockDim.x >> 5;
+    for (int64_t run = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); run < runs;
+         run += (int64_t)gridDim.x * wpb) {  // warp-uniform
+        const int xr = (int)(run % xt);
+        int64_t rest = run / xt;
+        const int y = (int)(rest % ny);
+        rest /= ny;
+        const int z = (int)(rest % nz);
+        const int b = (int)(rest / nz);
+        const int nv = nz * ny * nx;
+        const __nv_bfloat16 *base = in + (int64_t)b * nv * 16;
+        const int x0 = xr * 16 + g, x1 = x0 + 8;  // the two A rows of this lane
+        float acc[2][4] = {};
+        // per (dz, dy) row: the A fragments of the three x offsets are loaded
+        // together, then the six MMAs run
 #pragma unroll 1
-    for (int o = 0; o < 27; ++o) {
-        const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
-        const int zz = z + dz, yy = y + dy;
-        const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
-        const int xa = x0 + dx, xb = x1 + dx;
-        const bool va = zy && xa >= 0 && xa < nx, vb = zy && xb >= 0 && xb < nx;
-        const int64_t rowa = ((int64_t)zz * ny + yy) * nx + xa, rowb = ((int64_t)zz * ny + yy) * nx + xb;
-        const uint32_t *pa = reinterpret_cast<const uint32_t *>(base + rowa * 16);
-        const uint32_t *pb = reinterpret_cast<const uint32_t *>(base + rowb * 16);
-        const uint32_t a0 = va ? __ldg(pa + t) : 0u, a2 = va ? __ldg(pa + 4 + t) : 0u;
-        const uint32_t a1 = vb ? __ldg(pb + t) : 0u, a3 = vb ? __ldg(pb + 4 + t) : 0u;
-        const uint32_t *wb = reinterpret_cast<const uint32_t *>(&sw[o][0][0]);
+        for (int r9 = 0; r9 < 9; ++r9) {
+            const int zz = z + r9 / 3 - 1, yy = y + r9 % 3 - 1;
+            const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
+            const int64_t rowb = ((int64_t)zz * ny + yy) * nx;
+            uint32_t af[3][4];
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int co = nt * 8 + g;
-            const uint32_t b0 = wb[co * 8 + t], b1 = wb[co * 8 + 4 + t];
-            mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
-        }
-    }
-    // C fragment: rows g, g + 8 (nodes x0, x1), columns 2t, 2t + 1 of each n-tile
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int xx = h ? x1 : x0;
-        if (xx >= nx) continue;
-        const int64_t v = (int64_t)b * nv + ((int64_t)z * ny + y) * nx + xx;
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int co = nt * 8 + 2 * t;
-            float v0 = acc[nt][2 * h] + bias[co], v1 = acc[nt][2 * h + 1] + bias[co + 1];
-            if (RELU) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
+            for (int dx = 0; dx < 3; ++dx) {
+                const int xa = x0 + dx - 1, xb = x1 + dx - 1;
+                const bool va = zy && xa >= 0 && xa < nx, vb = zy && xb >= 0 && xb < nx;
+                const uint32_t *pa = reinterpret_cast<const uint32_t *>(base + (rowb + xa) * 16);
+                const uint32_t *pb = reinterpret_cast<const uint32_t *>(base + (rowb + xb) * 16);
+                af[dx][0] = va ? __ldg(pa + t) : 0u;
+                af[dx][2] = va ? __ldg(pa + 4 + t) : 0u;
+                af[dx][1] = vb ? __ldg(pb + t) : 0u;
+                af[dx][3] = vb ? __ldg(pb + 4 + t) : 0u;
             }
-            __nv_bfloat162 pr;
-            pr.x = __float2bfloat16_rn(v0);
-            pr.y = __float2bfloat16_rn(v1);
-            *reinterpret_cast<__nv_bfloat162 *>(out + v * 16 + co) = pr;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const uint32_t *wb = reinterpret_cast<const uint32_t *>(&sw[3 * r9 + dx][0][0]);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const int co = nt * 8 + g;
+                    const uint32_t b0 = wb[co * 8 + t], b1 = wb[co * 8 + 4 + t];
+                    mma16816(acc[nt], af[dx][0], af[dx][1], af[dx][2], af[dx][3], b0, b1);
+                }
+            }
+        }
+        // C fragment: rows g, g + 8 (nodes x0, x1), columns 2t, 2t + 1 of each n-tile
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xx = h ? x1 : x0;
+            if (xx >= nx) continue;
+            const int64_t v = (int64_t)b * nv + ((int64_t)z * ny + y) * nx + xx;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int co = nt * 8 + 2 * t;
+                float v0 = acc[nt][2 * h] + bias[co], v1 = acc[nt][2 * h + 1] + bias[co + 1];
+                if (RELU) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                __nv_bfloat162 pr;
+                pr.x = __float2bfloat16_rn(v0);
+                pr.y = __float2bfloat16_rn(v1);
+                *reinterpret_cast<__nv_bfloat162 *>(out + v * 16 + co) = pr;
+            }
         }
     }
 }
@@ -410,6 +466,68 @@ struct Reducer {
     }
 };
 
+// Flexible CG orthogonalisation on the device: dots of z with the stored
+// K-directions Q[k] (per-block partials, 8 at a time), the coefficients
+// beta_k = -(z . Q[k]) / (P[k] . Q[k]) (one block per k, fixed order), and
+// p = z + sum_k beta_k P[k] (k ascending).
+constexpr int FCG_MAXD = 256;
+
+__global__ void __launch_bounds__(RB) k_fcg_dots(int64_t n, const double *__restrict__ z,
+                                                 const double *__restrict__ Q, int nd, double *__restrict__ part)
+{
+    __shared__ double sh[RB / 32];
+    for (int k0 = 0; k0 < nd; k0 += 8) {
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            const double zi = z[i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k0 + u < nd) acc[u] = fma(zi, Q[(int64_t)(k0 + u) * n + i], acc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (k0 + u >= nd) break;
+            double v = acc[u];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+                part[(int64_t)blockIdx.x * FCG_MAXD + k0 + u] = t;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RB) k_fcg_beta(int nb, const double *__restrict__ part,
+                                                 const double *__restrict__ pq, double *__restrict__ beta)
+{
+    __shared__ double sh[RB / 32];
+    const int k = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(int64_t)b * FCG_MAXD + k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        beta[k] = -t / pq[k];
+    }
+}
+
+__global__ void k_fcg_dir(int64_t n, const double *__restrict__ z, const double *__restrict__ P, int nd,
+                          const double *__restrict__ beta, double *__restrict__ p)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = z[i];
+    for (int k = 0; k < nd; ++k) v = fma(beta[k], P[(int64_t)k * n + i], v);
+    p[i] = v;
+}
+
 // z = dinv r + s (1 - mask) y    (y: network output, FP32)
 __global__ void k_compose_z(int64_t n, const double *__restrict__ dinv, const double *__restrict__ r,
                             const float *__restrict__ y, const uint8_t *__restrict__ mask, double s,
@@ -480,12 +598,17 @@ struct mf_cnn {
 
 namespace {
 
-template <int CI, int CO, bool RELU, bool F32>
-void fwd_layer(int B, int nz, int ny, int nx, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *b,
-               void *out, cudaStream_t st)
+// persistent grid: at most 8 blocks per SM
+unsigned conv_grid(int64_t items, int per_block)
 {
-    const int64_t tot = (int64_t)B * nz * ny * nx;
-    k_conv_fwd<CI, CO, RELU, F32><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, in, w, b, out);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + per_block - 1) / per_block, (int64_t)sms * 8));
 }
 
 struct Acts {
@@ -526,11 +649,22 @@ void forward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, A
 {
     const __nv_bfloat16 *W = c->pb;
     const float *P = c->p;
-    fwd_layer<2, 16, true, false>(B, nz, ny, nx, x, W + p_offset_w(0), P + p_offset_b(0), A.a1, st);
+    const int64_t tot = (int64_t)B * nz * ny * nx;
     const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
-    k_conv16_mma<true><<<nblk(runs, 4), 128, 0, st>>>(B, nz, ny, nx, A.a1, W + p_offset_w(1), P + p_offset_b(1), A.a2);
-    k_conv16_mma<true><<<nblk(runs, 4), 128, 0, st>>>(B, nz, ny, nx, A.a2, W + p_offset_w(2), P + p_offset_b(2), A.a3);
-    fwd_layer<16, 1, false, true>(B, nz, ny, nx, A.a3, W + p_offset_w(3), P + p_offset_b(3), A.y, st);
+    mf_prof_begin("cnn_conv1", st);
+    k_conv_first<<<conv_grid(tot, 256), 256, 0, st>>>(B, nz, ny, nx, x, W + p_offset_w(0), P + p_offset_b(0), A.a1);
+    mf_prof_end(st);
+    mf_prof_begin("cnn_conv2", st);
+    k_conv16_mma<true><<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, A.a1, W + p_offset_w(1), P + p_offset_b(1),
+                                                           A.a2);
+    mf_prof_end(st);
+    mf_prof_begin("cnn_conv3", st);
+    k_conv16_mma<true><<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, A.a2, W + p_offset_w(2), P + p_offset_b(2),
+                                                           A.a3);
+    mf_prof_end(st);
+    mf_prof_begin("cnn_conv4", st);
+    k_conv_last<<<conv_grid(tot, 256), 256, 0, st>>>(B, nz, ny, nx, A.a3, W + p_offset_w(3), P + p_offset_b(3), A.y);
+    mf_prof_end(st);
 }
 
 template <int CI, int CO>
@@ -777,15 +911,23 @@ extern "C" mf_status mf_axpby(int64_t n, double a, const double *x, double b, do
 // Flexible CG (Notay 2000, one stored direction) with the CNN correction.
 extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *x, mf_cnn *c, int32_t nz,
                                       int32_t ny, int32_t nx, const float *logk, const uint8_t *mask, double tol,
-                                      int64_t max_iter, mf_solve_info *info, int64_t *fallbacks, void *stream)
+                                      int64_t max_iter, int32_t m_dirs, mf_solve_info *info, int64_t *fallbacks,
+                                      void *stream)
 {
-    if (!K || !d || !x || !c || !logk || K->n_rows != (int64_t)nz * ny * nx || !(tol > 0))
+    if (!K || !d || !x || !c || !logk || K->n_rows != (int64_t)nz * ny * nx || !(tol > 0) || m_dirs < 1 ||
+        m_dirs > FCG_MAXD)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_fcg_cnn: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = K->n_rows;
+    const int M = m_dirs;
     double *buf = nullptr;
-    MF_CUDA(cudaMallocAsync(&buf, sizeof(double) * 6 * n, st));
-    double *r = buf, *zv = buf + n, *p = buf + 2 * n, *q = buf + 3 * n, *dinv = buf + 4 * n, *qo = buf + 5 * n;
+    MF_CUDA(cudaMallocAsync(&buf, sizeof(double) * (4 + 2 * (size_t)M) * n, st));
+    // P[i], Q[i] = K P[i]: the stored directions, ring buffer of M slots
+    double *r = buf, *zv = buf + n, *dinv = buf + 2 * n, *tmp = buf + 3 * n;
+    double *P = buf + 4 * n, *Q = P + (size_t)M * n;
+    double *small = nullptr;  // [RG * FCG_MAXD] partials, [FCG_MAXD] p.q, [FCG_MAXD] beta
+    MF_CUDA(cudaMallocAsync(&small, sizeof(double) * (RG + 2) * FCG_MAXD, st));
+    double *opart = small, *pq_d = small + (size_t)RG * FCG_MAXD, *beta_d = pq_d + FCG_MAXD;
     __nv_bfloat16 *xin = nullptr;
     MF_CUDA(cudaMallocAsync(&xin, sizeof(__nv_bfloat16) * 2 * n, st));
     Acts A;
@@ -795,26 +937,23 @@ extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *
     MF_CUDA(red.init(st));
     k_diag_inv2<<<nblk(n, 256), 256, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv);
     // r = d - K x
-    mf_spmv_impl(K, x, q, st);
+    mf_spmv_impl(K, x, tmp, st);
     MF_CUDA(cudaMemcpyAsync(r, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -1.0, q, 1.0, r);
+    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -1.0, tmp, 1.0, r);
     double dd3[3];
     MF_CUDA(red.dots(n, d, d, r, r, nullptr, nullptr, dd3));
     const double dn2 = dd3[0];
     double rr = dd3[1];
     int64_t it = 0, fb = 0;
-    double pq_old = 0.0;
     int done = rr <= tol * tol * dn2 ? 1 : 0;
     while (!done && it < max_iter) {
         // z = M(r): Jacobi plus the network correction
         double smax = 0.0;
         MF_CUDA(red.absmax(n, r, &smax));
         const double sinv = smax > 0 ? 1.0 / smax : 0.0;
-        MF_CUDA(cudaMemcpyAsync(q, &sinv, sizeof(double), cudaMemcpyHostToDevice, st));  // q[0] as a scalar slot
-        k_cnn_input<<<nblk(n, 256), 256, 0, st>>>(n, r, q, logk, xin);
-        mf_prof_begin("fcg_cnn_forward", st);
+        MF_CUDA(cudaMemcpyAsync(tmp, &sinv, sizeof(double), cudaMemcpyHostToDevice, st));  // tmp[0] as a scalar slot
+        k_cnn_input<<<nblk(n, 256), 256, 0, st>>>(n, r, tmp, logk, xin);
         forward(c, 1, nz, ny, nx, xin, A, st);
-        mf_prof_end(st);
         k_compose_z<<<nblk(n, 256), 256, 0, st>>>(n, dinv, r, A.y, mask, smax, zv);
         double zr[3];
         MF_CUDA(red.dots(n, zv, r, zv, zv, nullptr, nullptr, zr));
@@ -822,14 +961,19 @@ extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *
             k_jacobi<<<nblk(n, 256), 256, 0, st>>>(n, dinv, r, zv);
             ++fb;
         }
-        // p = z - (z . q_old / p_old . q_old) p_old
-        if (it == 0) {
-            MF_CUDA(cudaMemcpyAsync(p, zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        // p = z - sum_k (z . q_k / p_k . q_k) p_k over the stored directions
+        // (classical Gram-Schmidt: every coefficient from z), on the device
+        const int slot = (int)(it % M);
+        double *p = P + (size_t)slot * n, *q = Q + (size_t)slot * n;
+        const int nst = (int)std::min<int64_t>(it, M);
+        if (nst > 0) {
+            k_fcg_dots<<<RG, RB, 0, st>>>(n, zv, Q, nst, opart);
+            k_fcg_beta<<<nst, RB, 0, st>>>(RG, opart, pq_d, beta_d);
+            k_fcg_dir<<<nblk(n, 256), 256, 0, st>>>(n, zv, P, nst, beta_d, tmp);
+            // the new direction takes the oldest slot only after all coefficients are known
+            MF_CUDA(cudaMemcpyAsync(p, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         } else {
-            double zq[3];
-            MF_CUDA(red.dots(n, zv, qo, nullptr, nullptr, nullptr, nullptr, zq));
-            const double beta = -zq[0] / pq_old;
-            k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, 1.0, zv, beta, p);
+            MF_CUDA(cudaMemcpyAsync(p, zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         }
         mf_spmv_impl(K, p, q, st);
         double pr[3];
@@ -839,10 +983,10 @@ extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *
             break;
         }
         const double alpha = pr[0] / pr[1];
-        pq_old = pr[1];
+        MF_CUDA(cudaMemcpyAsync(pq_d + slot, &pr[1], sizeof(double), cudaMemcpyHostToDevice, st));
+        MF_CUDA(cudaStreamSynchronize(st));  // pr lives on this stack frame
         k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, alpha, p, 1.0, x);
         k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -alpha, q, 1.0, r);
-        MF_CUDA(cudaMemcpyAsync(qo, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         double rn[3];
         MF_CUDA(red.dots(n, r, r, nullptr, nullptr, nullptr, nullptr, rn));
         rr = rn[0];
@@ -851,13 +995,14 @@ extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *
         if (rr <= tol * tol * dn2) done = 1;
     }
     // true residual
-    mf_spmv_impl(K, x, q, st);
+    mf_spmv_impl(K, x, tmp, st);
     MF_CUDA(cudaMemcpyAsync(r, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -1.0, q, 1.0, r);
+    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, -1.0, tmp, 1.0, r);
     double tr[3];
     MF_CUDA(red.dots(n, r, r, nullptr, nullptr, nullptr, nullptr, tr));
     cudaFreeAsync(buf, st);
     cudaFreeAsync(xin, st);
+    cudaFreeAsync(small, st);
     if (info) {
         info->iterations = it;
         info->rel_residual = dn2 > 0 ? sqrt(tr[0] / dn2) : sqrt(tr[0]);

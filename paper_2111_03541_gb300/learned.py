@@ -159,13 +159,16 @@ def jacobi_loss(ds: Dataset, batch: int = 16, energy: bool = True) -> float:
     return v
 
 
-def fcg(P: Problem, cnn, logk, tol: float = 1e-8, max_iter: int = 100000, x=None):
-    """Flexible CG with the network correction on a structured Q1 thermal problem."""
+def fcg(P: Problem, cnn, logk, tol: float = 1e-8, max_iter: int = 100000, x=None, m_dirs: int = 256):
+    """Flexible CG with the network correction on a structured Q1 thermal
+    problem; each direction is K-orthogonalised against the last m_dirs (the
+    network is not a fixed linear operator, and truncated histories of 8 or 32
+    directions stall on the 128^3 workload while 64 and more converge)."""
     import torch
     nz, ny, nx = grid_of(P.prob)
     if x is None:
         x = torch.zeros(P.n, dtype=torch.float64, device=P.device)
-    st, info, fb = mf_solve_fcg_cnn(P.csr, P.d, x, cnn, nz, ny, nx, logk, P.bc_mask, tol, max_iter)
+    st, info, fb = mf_solve_fcg_cnn(P.csr, P.d, x, cnn, nz, ny, nx, logk, P.bc_mask, tol, max_iter, m_dirs)
     return x, st, info, fb
 
 
