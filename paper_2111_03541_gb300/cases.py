@@ -1,0 +1,83 @@
+"""Run one workload's hot path a few times and print per-kernel device times,
+for profiling (ncu, the kernel-timing hooks) without the whole benchmark.
+
+    python -m paper_2111_03541_gb300.cases elastic --n 48 --prec mixed --reps 7
+    python -m paper_2111_03541_gb300.cases thermal-grf --n 128 --reps 4 --pcg-iters 30
+    python -m paper_2111_03541_gb300.cases cnn --n 129 --reps 5
+
+elastic: Q1 elasticity on an n^3 jittered box (gen.elastic_problem), assembled
+reps times after one untimed call.  thermal-grf: Q1 thermal conduction with
+k = exp(GRF) on an n^3 box (gen.grf_thermal_problem), assembled reps times,
+then pcg-iters Jacobi-PCG iterations (graph of 50).  cnn: reps forward passes
+of the preconditioner network on an n^3 node grid (package weights).
+Inputs are the seeded synthetic ones of `gen`; every step runs in libmf.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+
+def _times(mf):
+    return {k: (c, round(t / c, 4)) for k, (c, t) in mf.mf_kernel_times().items()}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn"))
+    ap.add_argument("--n", type=int, default=48)
+    ap.add_argument("--prec", choices=("fp64", "mixed"), default="mixed")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--pcg-iters", type=int, default=0)
+    a = ap.parse_args(argv)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+
+    import gen
+    import paper_2111_03541_gb300 as mf
+    if a.case == "elastic":
+        P = mf.Problem(gen.elastic_problem(a.n))
+        prec = mf.MF_PREC_MIXED if a.prec == "mixed" else mf.MF_PREC_FP64
+        P.assemble(prec)
+        torch.cuda.synchronize()
+        mf.mf_set_kernel_timing(1)
+        for _ in range(a.reps):
+            P.assemble(prec)
+        torch.cuda.synchronize()
+        print("assembly", _times(mf))
+    elif a.case == "thermal-grf":
+        P = mf.Problem(gen.grf_thermal_problem(a.n))
+        P.assemble()
+        torch.cuda.synchronize()
+        mf.mf_set_kernel_timing(1)
+        for _ in range(a.reps):
+            P.assemble()
+        torch.cuda.synchronize()
+        print("assembly", _times(mf))
+        mf.mf_set_kernel_timing(0)
+        if a.pcg_iters > 0:
+            x, st, info = P.solve(tol=1e-8, max_iter=a.pcg_iters, check_every=50)
+            torch.cuda.synchronize()
+            print("pcg iterations", info.iterations, "residual", info.rel_residual)
+    else:
+        from . import learned
+        cnn = mf.mf_cnn_create(learned.load_params(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                                                "cnn_q1_thermal.f32")))
+        nv = a.n ** 3
+        g = torch.Generator(device="cuda").manual_seed(7)
+        xin = torch.randn(2 * nv, device="cuda", generator=g).to(torch.bfloat16)
+        y = torch.empty(nv, dtype=torch.float32, device="cuda")
+        mf.mf_cnn_forward(cnn, 1, a.n, a.n, a.n, xin, y)
+        torch.cuda.synchronize()
+        mf.mf_set_kernel_timing(1)
+        for _ in range(a.reps):
+            mf.mf_cnn_forward(cnn, 1, a.n, a.n, a.n, xin, y)
+        torch.cuda.synchronize()
+        print("cnn forward", _times(mf))
+        mf.mf_cnn_destroy(cnn)
+    mf.mf_set_kernel_timing(0)
+
+
+if __name__ == "__main__":
+    main()
