@@ -257,7 +257,7 @@ __device__ __forceinline__ double to_double<long long>(long long v, int S)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
+__global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
     int64_t n0, int64_t n1, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
     const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
@@ -299,22 +299,32 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
             // exact integer sums: order is irrelevant, so every value of the
             // chunk streams through shared-memory integer atomics
             const int items = cnt * 72;
-#pragma unroll 4
-            for (int it = 0; it < (items + 31) / 32; ++it) {  // warp-uniform trip count
-                const int item = lane + 32 * it;
-                const bool act = item < items;
-                const int j = act ? item / 72 : 0;
-                const int64_t e = __shfl_sync(0xffffffffu, my_e, j);
-                const int a = __shfl_sync(0xffffffffu, my_a, j);
-                if (act) {
-                    const int idx = item - 72 * j;
-                    const int b = idx / 9, cc = idx - 9 * b;
-                    const int c = cc / 3, cp = cc - 3 * c;
-                    const T *blk = reinterpret_cast<const T *>(sc + e * stride);
-                    const T v = (a <= b) ? blk[upair(a, b) * 9 + cc] : blk[upair(b, a) * 9 + 3 * cp + c];
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc[slot[e * 64 + a * 8 + b] * 9 + cc]),
-                              (unsigned long long)v);
+            constexpr int IU = 6;  // items per lane whose loads are in flight together
+            for (int it0 = 0; it0 < (items + 31) / 32; it0 += IU) {  // warp-uniform trip count
+                T v[IU];
+                int ad[IU];
+#pragma unroll
+                for (int u = 0; u < IU; ++u) {
+                    const int item = lane + 32 * (it0 + u);
+                    const bool act = item < items;
+                    const int j = act ? item / 72 : 0;
+                    const int64_t e = __shfl_sync(0xffffffffu, my_e, j);
+                    const int a = __shfl_sync(0xffffffffu, my_a, j);
+                    v[u] = T(0);
+                    ad[u] = -1;
+                    if (act) {
+                        const int idx = item - 72 * j;
+                        const int b = idx / 9, cc = idx - 9 * b;
+                        const int c = cc / 3, cp = cc - 3 * c;
+                        const T *blk = reinterpret_cast<const T *>(sc + e * stride);
+                        v[u] = (a <= b) ? blk[upair(a, b) * 9 + cc] : blk[upair(b, a) * 9 + 3 * cp + c];
+                        ad[u] = slot[e * 64 + a * 8 + b] * 9 + cc;
+                    }
                 }
+#pragma unroll
+                for (int u = 0; u < IU; ++u)
+                    if (ad[u] >= 0)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&acc[ad[u]]), (unsigned long long)v[u]);
             }
         } else {
             // FP64 sums in ascending element order (bit-reproducible)
@@ -338,14 +348,35 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
     dsum += __shfl_down_sync(0xffffffffu, dsum, 6);   // j < 2 take j + 2
     dsum += __shfl_down_sync(0xffffffffu, dsum, 3);   // j = 0 takes j = 1
     const int S = scale ? *scale : 0;
+    // neighbour k's column node and Dirichlet flags, loaded once by lane k
+    // (and k - 32 for rows with more than 32 neighbours), read by shuffle
+    int32_t mcol_l[2] = {0, 0};
+    unsigned cm_l[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        if (k < deg) {
+            mcol_l[h] = adj_col[p0 + k];
+            if (mask)
+#pragma unroll
+                for (int cp = 0; cp < 3; ++cp) cm_l[h] |= (mask[3 * (int64_t)mcol_l[h] + cp] != 0 ? 1u : 0u) << cp;
+        }
+    }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
         const int64_t r = 3 * n + c;
         const bool rm = mask ? mask[r] != 0 : false;
         const int64_t rb = row_ptr[r];
         double lift = 0.0;
-        for (int j = lane; j < 3 * deg; j += 32) {
-            const int k = j / 3, cp = j - 3 * k;
+        for (int j0 = 0; j0 < 3 * deg; j0 += 32) {  // warp-uniform
+            const int j = j0 + lane;
+            const int k = (j < 3 * deg ? j : 0) / 3, cp = j - 3 * (j / 3);
+            const int kk = k & 31;
+            const int32_t mc0 = __shfl_sync(0xffffffffu, mcol_l[0], kk), mc1 = __shfl_sync(0xffffffffu, mcol_l[1], kk);
+            const unsigned f0 = __shfl_sync(0xffffffffu, cm_l[0], kk), f1 = __shfl_sync(0xffffffffu, cm_l[1], kk);
+            if (j >= 3 * deg) continue;
+            const int32_t mcol = k < 32 ? mc0 : mc1;
+            const bool cmk = ((k < 32 ? f0 : f1) >> cp) & 1u;
             T kv = acc[k * 9 + 3 * c + cp];
             if (fq) {  // fixed-point path: K = p A + q A^T + q I tr(A) per node-pair block
                 kv = (T)fp * kv + (T)fq * acc[k * 9 + 3 * cp + c];
@@ -353,9 +384,9 @@ __global__ void __launch_bounds__(GEL_WARPS * 32) k_gather_el(
             }
             double v = to_double<T>(kv, S);
             if (mask) {
-                const int64_t sdof = 3 * (int64_t)adj_col[p0 + k] + cp;
+                const int64_t sdof = 3 * (int64_t)mcol + cp;
                 if (rm) v = (r == sdof) ? 1.0 : 0.0;
-                else if (mask[sdof]) { lift -= v * bval[sdof]; v = 0.0; }
+                else if (cmk) { lift -= v * bval[sdof]; v = 0.0; }
             }
             values[rb + j] = v;
         }
