@@ -35,6 +35,9 @@ def test_batch_matches_single_problem_path_bitwise(mf, orc, tmp_path):
     specs = small_specs()
     assert {s["type"] for s in specs} == {"P1", "P2", "Q1"}
     probs = [gen.batch_problem(s) for s in specs]
+    # unjittered Q1 boxes (every element a translate of element 0) in the mix
+    probs.insert(3, gen.thermal_q1_problem(6, jitter=0.0))
+    probs.append(gen.thermal_q1_problem(9, jitter=0.0))
     single = []
     for pr in probs:
         P = mf.Problem(pr)
@@ -53,7 +56,7 @@ def test_batch_matches_single_problem_path_bitwise(mf, orc, tmp_path):
             assert torch.equal(P.values, v) and torch.equal(P.d, d)
     mf.mf_sync_status()
     # a few problems against the oracle
-    for i in (0, len(probs) // 2, len(probs) - 1):
+    for i in (0, 3, len(probs) // 2, len(probs) - 1):
         ref = orc.assemble(probs[i])
         P = batch_P[i]
         val = P.values.cpu().numpy()

@@ -26,12 +26,27 @@ def mf():
     return mf
 
 
+def _partly_jittered_q1(n):
+    """Unjittered Q1 box whose interior nodes with x < 0.4 are moved: elements
+    away from them stay exact translates of element 0, the others are not."""
+    prob = gen.thermal_q1_problem(n, jitter=0.0)
+    X = prob["coords"].copy()
+    h = 1.0 / n
+    inner = (X[:, 0] > 1e-12) & (X[:, 0] < 0.4) & (np.abs(X[:, 1] - 0.5) < 0.5 - 1e-12) & \
+        (np.abs(X[:, 2] - 0.5) < 0.5 - 1e-12)
+    idx = np.nonzero(inner)[0]
+    X[idx] += 0.15 * h * (2.0 * gen.uniform(4321, 3 * idx.size).reshape(-1, 3) - 1.0)
+    prob["coords"] = X
+    return prob
+
+
 CASES = {
     "p1_64": lambda: gen.thermal_p1_problem(64),
     "p1_13": lambda: gen.thermal_p1_problem(13),
     "p2_11": lambda: gen.thermal_p2_problem(11),
     "q1_9": lambda: gen.thermal_q1_problem(9),
     "q1_affine_11": lambda: gen.thermal_q1_problem(11, jitter=0.0),
+    "q1_partly_translate_10": lambda: _partly_jittered_q1(10),
     "el_7": lambda: gen.elastic_problem(7),
     "el_12": lambda: gen.elastic_problem(12),
     "os_9": lambda: gen.oseen_problem(9),
