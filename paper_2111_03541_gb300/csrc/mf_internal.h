@@ -71,6 +71,12 @@ struct mf_pattern {
     uint8_t *tr = nullptr;
     double *kref = nullptr;
     int64_t n_translate = 0;
+    // elasticity, mixed path: int64 3x3 block accumulator per node pair
+    // (9 x n_pairs; only pairs (n, m) with n <= m are written, the diagonal
+    // blocks as their upper triangles) and, per node pair, the index of the
+    // transposed pair (m, n)
+    long long *kacc = nullptr;
+    int32_t *tpos = nullptr;
     // mixed path: device scalars of the fixed-point scale (see mf_mixed.cu)
     void *mixed_state = nullptr;
     // elasticity slabs: element chunk c = [slab_e[c], slab_e[c+1]) completes the
@@ -108,6 +114,10 @@ mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_c
                                double p_scale, double *out, cudaStream_t st);
 // elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64
 // sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
+// mixed elasticity: CSR rows from the int64 block accumulator (p, q finishing,
+// conversion at scale 2^-S, Dirichlet elimination, loads from the scratch)
+void mf_launch_finish_elastic(int fp, int fq, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
+                              double *values, double *d, cudaStream_t st);
 void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
                               const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);

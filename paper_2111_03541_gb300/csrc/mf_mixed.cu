@@ -19,9 +19,12 @@
 //    slice pairs accumulates exactly on the tensor cores (mma.sync m16n8k16,
 //    bf16 in, fp32 accumulate);
 //  * the levels are combined into 64-bit fixed point at a global scale 2^S
-//    (chosen by a pre-pass so no sum can overflow); the gather sums A'' over
-//    the elements exactly in int64, applies the (linear) p, q finishing once
-//    per CSR block and converts each value once to FP64.
+//    (chosen by a pre-pass so no sum can overflow) and added with integer
+//    atomics into one 3x3 block per node pair (n <= m; the lower pairs are
+//    transposes): integer sums are exact, so the result does not depend on
+//    the order the atomics land in; a node-centric finishing pass applies the
+//    (linear) p, q finishing once per CSR block, converts each value once to
+//    FP64 and eliminates the Dirichlet dofs.
 // The dropped levels (s + t > 4) bound the error at about 2^-40 of the row
 // scale; the solution error against the FP64 path is measured per run.
 #include <cuda_bf16.h>
@@ -206,11 +209,13 @@ __global__ void k_mixed_scale(MixedState *st, int p, int q)
 struct WarpSmem {
     __nv_bfloat16 sl[4][NSL][SL_ROWS][8];  // slices of G per element: [slice][row (a,c)][point]
     int ex[4][SL_ROWS];                     // row exponents
+    int32_t tgt[4][36];                     // accumulator pair of block (a <= b); bit 31: transposed
 };
 
 __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
     double cmu_q, double b0, double b1, double b2, const MixedState *__restrict__ st,
+    const int64_t *__restrict__ adj_ptr, const uint8_t *__restrict__ slot, unsigned long long *__restrict__ kacc,
     double *__restrict__ out, int64_t stride, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -365,6 +370,27 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     }
     __syncwarp();
 
+    // --- accumulator pair of each upper block (a <= b) of the warp's 4 elements:
+    // (n_a, n_b) when n_a <= n_b, else (n_b, n_a) holding the transpose ---
+    for (int i = lane; i < 4 * 36; i += 32) {
+        const int el = i / 36, u = i - 36 * el;
+        int a = 0, rem = u;
+        while (rem >= 8 - a) {
+            rem -= 8 - a;
+            ++a;
+        }
+        const int b = a + rem;
+        const int64_t eo = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + el;
+        int32_t tg = 0;
+        if (eo < e1) {
+            const int32_t na = conn[8 * eo + a], nb = conn[8 * eo + b];
+            tg = na <= nb ? (int32_t)(adj_ptr[na] + slot[eo * 64 + a * 8 + b])
+                          : (int32_t)((adj_ptr[nb] + slot[eo * 64 + b * 8 + a]) | 0x80000000ll);
+        }
+        W.tgt[el][u] = tg;
+    }
+    __syncwarp();
+
     // --- tensor cores: A'' = G G^T by levels, per element of the warp ---
     const int g = lane >> 2, t = lane & 3;
     const int S = st->S;
@@ -374,7 +400,6 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
         auto ld = [&](int sl, int row) -> uint32_t {
             return *reinterpret_cast<const uint32_t *>(&W.sl[el][sl][row][2 * t]);
         };
-        long long *o = reinterpret_cast<long long *>(out + (eo < e1 ? eo : e0) * stride);
 #pragma unroll 1
         for (int tl = 0; tl < 4; ++tl) {  // tiles (m, n): (0,0), (0,1), (0,2), (1,2)
             const int mt = tl == 3 ? 1 : 0, nt = tl == 3 ? 2 : tl;
@@ -395,18 +420,20 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
                     mma_bf16(acc[L], a0, a1, a2, a3, b0, b1);
                 }
             }
-            // levels -> 64-bit fixed point at scale 2^S, written straight to the
-            // element's upper blocks (a <= b); the p, q finishing is linear and is
-            // applied once per CSR block after the exact sums of the gather
+            // levels -> 64-bit fixed point at scale 2^S, added into the node-pair
+            // block accumulator (exact integer sums: any order gives the same
+            // bits); the p, q finishing is linear and is applied once per CSR
+            // block after all elements
             if (eo < e1) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int rho = mt * 16 + g + 8 * (k >> 1);
                     const int sig2 = nt * 8 + 2 * t + (k & 1);
                     const int a = rho / 3, b = sig2 / 3;
-                    // an upper block a <= b is complete from the computed tiles:
-                    // (a < b) whole block, (a == b) both triangles (rows >= 24 skipped)
-                    if (rho >= 24 || a > b) continue;
+                    const int c = rho - 3 * a, cp = sig2 - 3 * b;
+                    // upper blocks a <= b, of a diagonal block its upper triangle;
+                    // the four tiles compute all of them (rows >= 24 are padding)
+                    if (rho >= 24 || a > b || (a == b && c > cp)) continue;
                     long long T = f2i_exact(acc[0][k]);
 #pragma unroll
                     for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][k]);
@@ -415,11 +442,10 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
                     if (sh >= 0) v = T << sh;
                     else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
                     else v = 0;
-                    const int base = (a * (15 - a) / 2 + b) * 9;
-                    o[base + 3 * (rho - 3 * a) + (sig2 - 3 * b)] = v;
-                    // diagonal block 5 straddles the tiles: its entries (16, 15) and
-                    // (17, 15) are not computed; they mirror (15, 16) and (15, 17)
-                    if (tl == 2 && a == b) o[base + 3 * (sig2 - 3 * b) + (rho - 3 * a)] = v;
+                    const int32_t tg = W.tgt[el][a * (15 - a) / 2 + b];
+                    const int64_t pr = tg & 0x7fffffff;
+                    const int q = tg < 0 ? 3 * cp + c : 3 * c + cp;
+                    if (v != 0) atomicAdd(&kacc[pr * 9 + q], (unsigned long long)v);
                 }
             }
         }
@@ -462,23 +488,18 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     mf_prof_end(st);
     const size_t smem = sizeof(WarpSmem) * MX_WARPS;
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return mf_slab_pipeline(
-        p, st,
-        [&](size_t k, cudaStream_t s) -> mf_status {
-            const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
-            mf_prof_begin("mixed_elem", s);
-            k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, s>>>(
-                e0, e1, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms,
-                p->scratch, p->scratch_stride, status);
-            mf_prof_end(s);
-            MF_CUDA(cudaGetLastError());
-            return MF_OK;
-        },
-        [&](size_t k, cudaStream_t s) -> mf_status {
-            mf_prof_begin("gather_elastic_fixed", s);
-            mf_launch_gather_elastic(true, pp, qq, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, s);
-            mf_prof_end(s);
-            MF_CUDA(cudaGetLastError());
-            return MF_OK;
-        });
+    // element blocks go straight into the int64 block accumulator (atomics:
+    // exact, so order-free); the finishing gather then writes each CSR row once
+    MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
+    mf_prof_begin("mixed_elem", st);
+    k_mixed_elem<<<(unsigned)((ne + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
+        0, ne, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms, p->adj[0].ptr,
+        p->slot, reinterpret_cast<unsigned long long *>(p->kacc), p->scratch, p->scratch_stride, status);
+    mf_prof_end(st);
+    MF_CUDA(cudaGetLastError());
+    mf_prof_begin("mixed_finish", st);
+    mf_launch_finish_elastic(pp, qq, m, p, c, values, d, st);
+    mf_prof_end(st);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
 }

@@ -201,6 +201,15 @@ __global__ void k_node_ready(int64_t n, const int64_t *__restrict__ inc_ptr, con
     ready[v] = inc_ptr[v + 1] > inc_ptr[v] ? inc[inc_ptr[v + 1] - 1] : -1;
 }
 
+// tpos[p] = index of the pair (m, n) for the pair p = (n, m)
+__global__ void k_tpos(int64_t n_nodes, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                       int32_t *__restrict__ tpos)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    for (int64_t p = ptr[n]; p < ptr[n + 1]; ++p) tpos[p] = (int32_t)find_pair(ptr, col, col[p], (int32_t)n);
+}
+
 // incidence slot map: for incidence entry t of node n (element e, local a),
 // inc_slot[t * npe + b] = position of conn[e][b] among the neighbours of n
 __global__ void k_inc_slot(int64_t n_nodes, int npe, const int32_t *__restrict__ conn,
@@ -530,6 +539,10 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->pinc_ptr);
     cudaFree(p->pinc);
     cudaFree(p->slot);
+    cudaFree(p->kacc);
+    cudaFree(p->tpos);
+    p->kacc = nullptr;
+    p->tpos = nullptr;
     cudaFree(p->inc_slot);
     p->inc_slot = nullptr;
     cudaFree(p->elem_inc);
@@ -615,6 +628,9 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_slot_map<<<nblk(m->n_elems * 64), TPB, 0, st>>>(m->n_elems, 8, m->conn, p->adj[0].ptr, p->adj[0].col,
                                                            p->slot);
         MF_CUDA(cudaMallocAsync(&p->mixed_state, 64, st));
+        MF_CUDA(cudaMallocAsync(&p->tpos, sizeof(int32_t) * p->adj[0].n_pairs, st));
+        k_tpos<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->tpos);
+        MF_CUDA(cudaMallocAsync(&p->kacc, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
         p->scratch_stride = 36 * 9 + 24;
         mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);
         if (ss != MF_OK) { free_inc(incv, st); return ss; }
