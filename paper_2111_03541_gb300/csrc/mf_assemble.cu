@@ -237,36 +237,19 @@ __device__ __forceinline__ double to_double<double>(double v, int)
     return v;
 }
 
-// x * 2^-S for a fixed-point integer x, rounded to nearest even with integer
-// operations only (no FP64 instruction).
+// x * 2^-S for a fixed-point integer x (mf_fixed_to_double)
 template <>
 __device__ __forceinline__ double to_double<long long>(long long v, int S)
 {
-    if (v == 0) return 0.0;
-    const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
-    unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    const int lz = __clzll((long long)u);
-    u <<= lz;  // leading one at bit 63
-    unsigned long long m = u >> 11;  // 53 significant bits
-    const unsigned long long rest = u & 0x7ffull;
-    m += (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
-    const long long ex = 1023 + (63 - lz) - S;
-    if (ex <= 0) return __longlong_as_double((long long)sign);  // below the normal range
-    const unsigned long long bits = ((unsigned long long)ex << 52) + (m - (1ull << 52));
-    return __longlong_as_double((long long)(bits | sign));
+    return mf_fixed_to_double(v, S);
 }
 
-// ACC = true (mixed path, finishing): the node-pair blocks are not summed from
-// the element scratch but read from the int64 block accumulator the element
-// kernel added into (pairs (n, m) with n <= m; (m, n) is the transpose, a
-// diagonal block its upper triangle); only the loads come from the scratch.
-template <typename T, bool ACC>
+template <typename T>
 __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
     int64_t n0, int64_t n1, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
     const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
-    const long long *__restrict__ kacc, const int32_t *__restrict__ tpos, int fp, int fq,
-    const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+    int fp, int fq, const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
     double *__restrict__ values, double *__restrict__ d)
 {
     __shared__ T acc_all[GEL_WARPS][MF_MAX_DEG * 9];
@@ -277,8 +260,7 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
     constexpr bool fixed = sizeof(T) == 8 && T(0.5) == T(0);  // integer accumulator
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
-    if (!ACC)
-        for (int i = lane; i < 9 * deg; i += 32) acc[i] = T(0);
+    for (int i = lane; i < 9 * deg; i += 32) acc[i] = T(0);
     // load vector: lane 3 j + c (j < 8) holds component c of incidence entry
     // j, j + 8, ... in turn; the 8 partial sums of component c are added in a
     // fixed tree below
@@ -301,9 +283,7 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
             const int ad = __shfl_sync(0xffffffffu, my_a, jd < 8 ? jd : 0);
             if (jd < cnt) dsum += sc[ed * stride + 324 + 3 * ad + cd];
         }
-        if constexpr (ACC) {
-            // blocks come from the accumulator below
-        } else if constexpr (fixed) {
+        if constexpr (fixed) {
             // exact integer sums: order is irrelevant, so every value of the
             // chunk streams through shared-memory integer atomics
             const int items = cnt * 72;
@@ -369,30 +349,6 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
 #pragma unroll
                 for (int cp = 0; cp < 3; ++cp) cm_l[h] |= (mask[3 * (int64_t)mcol_l[h] + cp] != 0 ? 1u : 0u) << cp;
         }
-    }
-    if constexpr (ACC) {
-        // block of neighbour k: its own pair (m > n), the transpose of pair
-        // (m, n) (m < n), or the upper triangle of the diagonal block (m = n)
-        int64_t src_l[2] = {0, 0};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = lane + 32 * h;
-            if (k < deg) src_l[h] = mcol_l[h] < n ? (int64_t)tpos[p0 + k] : p0 + k;
-        }
-        for (int i0 = 0; i0 < 9 * deg; i0 += 32) {  // warp-uniform
-            const int i = i0 + lane;
-            const int k = (i < 9 * deg ? i : 0) / 9, cc = i - 9 * (i / 9);
-            const int kk = k & 31;
-            const int64_t s0 = __shfl_sync(0xffffffffu, src_l[0], kk), s1 = __shfl_sync(0xffffffffu, src_l[1], kk);
-            const int32_t m0 = __shfl_sync(0xffffffffu, mcol_l[0], kk), m1 = __shfl_sync(0xffffffffu, mcol_l[1], kk);
-            if (i >= 9 * deg) continue;
-            const int64_t src = k < 32 ? s0 : s1;
-            const int32_t mcol = k < 32 ? m0 : m1;
-            const int c = cc / 3, cp = cc - 3 * c;
-            const int q = mcol > n ? cc : (mcol < n ? 3 * cp + c : 3 * min(c, cp) + max(c, cp));
-            acc[i] = (T)kacc[src * 9 + q];
-        }
-        __syncwarp();
     }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
@@ -547,26 +503,13 @@ void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int6
     const mf_adj &A = p->adj[0];
     const unsigned grid = nblk(n1 - n0, GEL_WARPS);
     if (fixed_point)
-        k_gather_el<long long, false><<<grid, GEL_WARPS * 32, 0, st>>>(
+        k_gather_el<long long><<<grid, GEL_WARPS * 32, 0, st>>>(
             n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->slot, p->scratch, p->scratch_stride,
-            static_cast<const int *>(p->mixed_state), nullptr, nullptr, fp, fq, c->bc_mask, c->bc_val, p->row_ptr,
-            values, d);
+            static_cast<const int *>(p->mixed_state), fp, fq, c->bc_mask, c->bc_val, p->row_ptr, values, d);
     else
-        k_gather_el<double, false><<<grid, GEL_WARPS * 32, 0, st>>>(
+        k_gather_el<double><<<grid, GEL_WARPS * 32, 0, st>>>(
             n0, n1, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->slot, p->scratch, p->scratch_stride, nullptr,
-            nullptr, nullptr, 0, 0, c->bc_mask, c->bc_val, p->row_ptr, values, d);
-}
-
-void mf_launch_finish_elastic(int fp, int fq, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
-                              double *values, double *d, cudaStream_t st)
-{
-    const mf_adj &A = p->adj[0];
-    const int64_t nn = m->n_nodes;
-    if (nn == 0) return;
-    k_gather_el<long long, true><<<nblk(nn, GEL_WARPS), GEL_WARPS * 32, 0, st>>>(
-        0, nn, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->slot, p->scratch, p->scratch_stride,
-        static_cast<const int *>(p->mixed_state), p->kacc, p->tpos, fp, fq, c->bc_mask, c->bc_val, p->row_ptr,
-        values, d);
+            0, 0, c->bc_mask, c->bc_val, p->row_ptr, values, d);
 }
 
 mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,

@@ -77,6 +77,7 @@ struct mf_pattern {
     // transposed pair (m, n)
     long long *kacc = nullptr;
     int32_t *tpos = nullptr;
+    long long *dacc = nullptr;  // int64 load vector accumulator (3 per node)
     // mixed path: device scalars of the fixed-point scale (see mf_mixed.cu)
     void *mixed_state = nullptr;
     // elasticity slabs: element chunk c = [slab_e[c], slab_e[c+1]) completes the
@@ -114,10 +115,6 @@ mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_c
                                double p_scale, double *out, cudaStream_t st);
 // elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64
 // sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
-// mixed elasticity: CSR rows from the int64 block accumulator (p, q finishing,
-// conversion at scale 2^-S, Dirichlet elimination, loads from the scratch)
-void mf_launch_finish_elastic(int fp, int fq, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
-                              double *values, double *d, cudaStream_t st);
 void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
                               const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);
@@ -167,4 +164,22 @@ mf_status mf_slab_pipeline(const mf_pattern *p, cudaStream_t st, Elem elem, Gath
         if (cudaStreamWaitEvent(st, p->join_ev, 0) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
     }
     return MF_OK;
+}
+
+// x * 2^-S for a fixed-point integer x, rounded to nearest even with integer
+// operations only (no FP64 instruction: FP64 runs at 1/58 of FP32 here).
+__device__ __forceinline__ double mf_fixed_to_double(long long v, int S)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+    unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)u);
+    u <<= lz;  // leading one at bit 63
+    unsigned long long m = u >> 11;  // 53 significant bits
+    const unsigned long long rest = u & 0x7ffull;
+    m += (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
+    const long long ex = 1023 + (63 - lz) - S;
+    if (ex <= 0) return __longlong_as_double((long long)sign);  // below the normal range
+    const unsigned long long bits = ((unsigned long long)ex << 52) + (m - (1ull << 52));
+    return __longlong_as_double((long long)(bits | sign));
 }

@@ -39,8 +39,10 @@ constexpr int NSL = 5;               // BF16 slices of G
 constexpr int SL_ROWS = 32;          // 24 rows padded to two m16 tiles
 
 struct MixedState {
-    int S;        // global fixed-point exponent
-    int mx_bits;  // max over elements of max_row sum_q G^2 (float bits, >= 0)
+    int S;         // global fixed-point exponent of K
+    int mx_bits;   // max over elements of max_row sum_q G^2 (float bits, >= 0)
+    int Sd;        // fixed-point exponent of the load vector d
+    int vol_bits;  // max over elements of sum_q detJ_q (float bits, > 0)
 };
 
 // ---------------------------------------------------------------------------
@@ -159,6 +161,7 @@ __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const 
         for (int i = 0; i < 3; ++i) x[a][i] = (float)(X[3 * (int64_t)cn[a] + i] - X[3 * (int64_t)cn[0] + i]);
     const float g = (float)GD;
     float rowsum[24] = {};
+    float vol = 0.f;
     for (int q = 0; q < 8; ++q) {
         const float xs[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
         float J[3][3] = {}, dN[8][3];
@@ -182,6 +185,7 @@ __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const 
         C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
         C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+        vol += fabsf(det);
         const float sc = (float)E * cmu_q / det;  // G^2 = (mu / (q det)) (sum_j dN_j C[c][j])^2
         for (int a = 0; a < 8; ++a)
             for (int c = 0; c < 3; ++c) {
@@ -193,14 +197,18 @@ __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const 
     for (int r = 0; r < 24; ++r) mx = fmaxf(mx, rowsum[r]);
     if (!isfinite(mx)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
     atomicMax(&st->mx_bits, __float_as_int(mx));
+    atomicMax(&st->vol_bits, __float_as_int(vol));
 }
 
 // S = floor(62 - log2(8 (p + 4q) Mx 1.25)): every element value |K_e| <=
-// (p + 4q) Mx 2^S and a CSR entry sums at most 8 of them, below 2^62.
-__global__ void k_mixed_scale(MixedState *st, int p, int q)
+// (p + 4q) Mx 2^S and a CSR entry sums at most 8 of them, below 2^62.  The
+// load entries are |b_c| sum_q detJ_q N_a(q) <= |b|max vol: Sd likewise.
+__global__ void k_mixed_scale(MixedState *st, int p, int q, double bmax)
 {
     const float mx = __int_as_float(st->mx_bits);
     st->S = (int)floor(62.0 - log2(8.0 * (p + 4.0 * q) * (double)mx * 1.25));
+    const double bv = bmax * (double)__int_as_float(st->vol_bits);
+    st->Sd = bv > 0.0 ? (int)floor(62.0 - log2(8.0 * bv * 1.25)) : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -216,7 +224,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
     double cmu_q, double b0, double b1, double b2, const MixedState *__restrict__ st,
     const int64_t *__restrict__ adj_ptr, const uint8_t *__restrict__ slot, unsigned long long *__restrict__ kacc,
-    double *__restrict__ out, int64_t stride, int *status)
+    unsigned long long *__restrict__ dacc, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -361,11 +369,15 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
         for (int a = 1; a < 8; ++a)
             if (qp == a) mine = m[a];
         if (valid) {
-            double *dl = out + e * stride + 324 + 3 * qp;
+            // d_(3 n + c) += b_c m_a, n = conn[e][a], in fixed point at 2^Sd
             const double mv = (double)mine.h + (double)mine.l;
-            dl[0] = b0 * mv;
-            dl[1] = b1 * mv;
-            dl[2] = b2 * mv;
+            const double scl = ldexp(1.0, st->Sd);
+            const double bb[3] = {b0, b1, b2};
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const long long v = __double2ll_rn(bb[cc] * mv * scl);
+                if (v != 0) atomicAdd(&dacc[3 * (int64_t)nq + cc], (unsigned long long)v);
+            }
         }
     }
     __syncwarp();
@@ -452,6 +464,83 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     }
 }
 
+// ---------------------------------------------------------------------------
+// finishing: one warp per node.  Lane k takes neighbour k's 3x3 block from the
+// accumulator (its own pair (n, m) for m > n, the transpose of (m, n) for
+// m < n, the upper triangle of the diagonal block for m = n), applies
+// K = p A'' + q swap(A'') + q I tr(A'') in int64, converts each value once to
+// FP64 and eliminates the Dirichlet dofs; the three rows are staged in shared
+// memory and written with coalesced stores.
+// ---------------------------------------------------------------------------
+constexpr int FN_WARPS = 8;
+
+__global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
+    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+    const int32_t *__restrict__ tpos, const long long *__restrict__ kacc, const long long *__restrict__ dacc,
+    const MixedState *__restrict__ st, int fp, int fq, const uint8_t *__restrict__ mask,
+    const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
+    double *__restrict__ d)
+{
+    __shared__ double rows_all[FN_WARPS][3][3 * MF_MAX_DEG];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t n = (int64_t)blockIdx.x * FN_WARPS + w;
+    if (n >= n_nodes) return;  // warp-uniform
+    double(*rows)[3 * MF_MAX_DEG] = rows_all[w];
+    const int S = st->S, Sd = st->Sd;
+    const int64_t p0 = adj_ptr[n];
+    const int deg = (int)(adj_ptr[n + 1] - p0);
+    bool rm[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rm[c] = mask ? mask[3 * n + c] != 0 : false;
+    double lift[3] = {0.0, 0.0, 0.0};
+    for (int k = lane; k < deg; k += 32) {
+        const int32_t mcol = adj_col[p0 + k];
+        const int64_t src = mcol < n ? (int64_t)tpos[p0 + k] : p0 + k;
+        const long long *B = kacc + src * 9;
+        long long b[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) b[i] = B[i];
+        long long A[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp)
+                A[c][cp] = mcol > n ? b[3 * c + cp]
+                                    : (mcol < n ? b[3 * cp + c] : b[3 * (c < cp ? c : cp) + (c < cp ? cp : c)]);
+        const long long tr = A[0][0] + A[1][1] + A[2][2];
+        unsigned cm = 0;
+        if (mask)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp) cm |= (mask[3 * (int64_t)mcol + cp] != 0 ? 1u : 0u) << cp;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp) {
+                long long kv = (long long)fp * A[c][cp] + (long long)fq * A[cp][c];
+                if (c == cp) kv += (long long)fq * tr;
+                double v = mf_fixed_to_double(kv, S);
+                if (mask) {
+                    const int64_t sdof = 3 * (int64_t)mcol + cp;
+                    if (rm[c]) v = (3 * n + c == sdof) ? 1.0 : 0.0;
+                    else if ((cm >> cp) & 1u) { lift[c] -= v * bval[sdof]; v = 0.0; }
+                }
+                rows[c][3 * k + cp] = v;
+            }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int64_t r = 3 * n + c;
+        const int64_t rb = row_ptr[r];
+        for (int j = lane; j < 3 * deg; j += 32) values[rb + j] = rows[c][j];
+        double l = lift[c];
+        if (__any_sync(0xffffffffu, l != 0.0))  // rows next to a constrained dof only
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0) d[r] = rm[c] ? bval[r] : mf_fixed_to_double(dacc[r], Sd) + l;
+    }
+}
+
 }  // namespace
 
 mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c, double *values,
@@ -484,21 +573,27 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     MF_CUDA(cudaMemsetAsync(ms, 0, sizeof(MixedState), st));
     k_mixed_bound<<<(unsigned)((ne + 127) / 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, (float)cmu_q,
                                                                 ms, status);
-    k_mixed_scale<<<1, 1, 0, st>>>(ms, pp, qq);
+    const double bmax = fmax(fabs(c->source[0]), fmax(fabs(c->source[1]), fabs(c->source[2])));
+    k_mixed_scale<<<1, 1, 0, st>>>(ms, pp, qq, bmax);
     mf_prof_end(st);
     const size_t smem = sizeof(WarpSmem) * MX_WARPS;
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // element blocks go straight into the int64 block accumulator (atomics:
     // exact, so order-free); the finishing gather then writes each CSR row once
     MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
+    MF_CUDA(cudaMemsetAsync(p->dacc, 0, sizeof(long long) * 3 * m->n_nodes, st));
     mf_prof_begin("mixed_elem", st);
     k_mixed_elem<<<(unsigned)((ne + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
         0, ne, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms, p->adj[0].ptr,
-        p->slot, reinterpret_cast<unsigned long long *>(p->kacc), p->scratch, p->scratch_stride, status);
+        p->slot, reinterpret_cast<unsigned long long *>(p->kacc), reinterpret_cast<unsigned long long *>(p->dacc),
+        status);
     mf_prof_end(st);
     MF_CUDA(cudaGetLastError());
     mf_prof_begin("mixed_finish", st);
-    mf_launch_finish_elastic(pp, qq, m, p, c, values, d, st);
+    if (m->n_nodes > 0)
+        k_mixed_finish<<<(unsigned)((m->n_nodes + FN_WARPS - 1) / FN_WARPS), FN_WARPS * 32, 0, st>>>(
+            m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->tpos, p->kacc, p->dacc, ms, pp, qq, c->bc_mask, c->bc_val,
+            p->row_ptr, values, d);
     mf_prof_end(st);
     MF_CUDA(cudaGetLastError());
     return MF_OK;

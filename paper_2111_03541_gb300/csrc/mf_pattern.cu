@@ -541,6 +541,8 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->slot);
     cudaFree(p->kacc);
     cudaFree(p->tpos);
+    cudaFree(p->dacc);
+    p->dacc = nullptr;
     p->kacc = nullptr;
     p->tpos = nullptr;
     cudaFree(p->inc_slot);
@@ -631,6 +633,7 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         MF_CUDA(cudaMallocAsync(&p->tpos, sizeof(int32_t) * p->adj[0].n_pairs, st));
         k_tpos<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->tpos);
         MF_CUDA(cudaMallocAsync(&p->kacc, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
+        MF_CUDA(cudaMallocAsync(&p->dacc, sizeof(long long) * 3 * m->n_nodes, st));
         p->scratch_stride = 36 * 9 + 24;
         mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);
         if (ss != MF_OK) { free_inc(incv, st); return ss; }
