@@ -558,27 +558,17 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
     } else if (form == MF_FORM_ELASTIC) {
         const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;
         MF_CUDA(cudaFuncSetAttribute(k_elem_elastic_q1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        mf_status s = mf_slab_pipeline(
-            p, st,
-            [&](size_t k, cudaStream_t s2) -> mf_status {
-                const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
-                mf_prof_begin("elem_elastic_q1_fp64", s2);
-                k_elem_elastic_q1<<<nblk(e1 - e0, EL_T), EL_T, smem, s2>>>(e0, e1, m->coords, m->conn,
-                                                                          c->elem_coef, c->nu, c->source[0],
-                                                                          c->source[1], c->source[2], p->scratch,
-                                                                          status);
-                mf_prof_end(s2);
-                MF_CUDA(cudaGetLastError());
-                return MF_OK;
-            },
-            [&](size_t k, cudaStream_t s2) -> mf_status {
-                mf_prof_begin("gather_elastic", s2);
-                mf_launch_gather_elastic(false, 0, 0, p->slab_n[k], p->slab_n[k + 1], m, p, c, values, d, s2);
-                mf_prof_end(s2);
-                MF_CUDA(cudaGetLastError());
-                return MF_OK;
-            });
-        if (s != MF_OK) return s;
+        // one launch pair over the whole mesh: both kernels are bound by the
+        // FP64 pipe, so chunks would not overlap usefully
+        mf_prof_begin("elem_elastic_q1_fp64", st);
+        k_elem_elastic_q1<<<nblk(ne, EL_T), EL_T, smem, st>>>(0, ne, m->coords, m->conn, c->elem_coef, c->nu,
+                                                             c->source[0], c->source[1], c->source[2], p->scratch,
+                                                             status);
+        mf_prof_end(st);
+        MF_CUDA(cudaGetLastError());
+        mf_prof_begin("gather_elastic", st);
+        mf_launch_gather_elastic(false, 0, 0, 0, m->n_nodes, m, p, c, values, d, st);
+        mf_prof_end(st);
     } else {
         mf_prof_begin("elem_oseen", st);
         k_elem_oseen<<<nblk(ne, 128), 128, 0, st>>>(ne, m->n_nodes, m->coords, m->conn, c->advect, c->visc, c->rho,

@@ -9,7 +9,7 @@
 #include "../../include/mf.h"
 
 #define MF_MAX_DEG 64   // neighbours of one node in one adjacency
-#define MF_SLABS 1      // element chunks of the elasticity assembly (see plan_slabs)
+#define MF_SLABS 1      // element chunks of the mixed elasticity assembly (see plan_slabs)
 #define MF_MAX_INC 32   // elements incident to one node
 
 // Adjacency between a row node space and a column node space (Block B-1: the

@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
 constexpr int FN_WARPS = 8;
 
 __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
-    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+    int64_t n_begin, int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int32_t *__restrict__ tpos, const long long *__restrict__ kacc, const long long *__restrict__ dacc,
     const MixedState *__restrict__ st, int fp, int fq, const uint8_t *__restrict__ mask,
     const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
 {
     __shared__ double rows_all[FN_WARPS][3][3 * MF_MAX_DEG];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t n = (int64_t)blockIdx.x * FN_WARPS + w;
+    const int64_t n = n_begin + (int64_t)blockIdx.x * FN_WARPS + w;
     if (n >= n_nodes) return;  // warp-uniform
     double(*rows)[3 * MF_MAX_DEG] = rows_all[w];
     const int S = st->S, Sd = st->Sd;
@@ -582,19 +582,32 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     // exact, so order-free); the finishing gather then writes each CSR row once
     MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
     MF_CUDA(cudaMemsetAsync(p->dacc, 0, sizeof(long long) * 3 * m->n_nodes, st));
-    mf_prof_begin("mixed_elem", st);
-    k_mixed_elem<<<(unsigned)((ne + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, st>>>(
-        0, ne, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms, p->adj[0].ptr,
-        p->slot, reinterpret_cast<unsigned long long *>(p->kacc), reinterpret_cast<unsigned long long *>(p->dacc),
-        status);
-    mf_prof_end(st);
-    MF_CUDA(cudaGetLastError());
-    mf_prof_begin("mixed_finish", st);
-    if (m->n_nodes > 0)
-        k_mixed_finish<<<(unsigned)((m->n_nodes + FN_WARPS - 1) / FN_WARPS), FN_WARPS * 32, 0, st>>>(
-            m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->tpos, p->kacc, p->dacc, ms, pp, qq, c->bc_mask, c->bc_val,
-            p->row_ptr, values, d);
-    mf_prof_end(st);
-    MF_CUDA(cudaGetLastError());
-    return MF_OK;
+    // element chunks on the caller's stream; with more than one chunk the
+    // finishing of the nodes a chunk completes runs on the side stream
+    // (MF_SLABS: one chunk measured fastest)
+    return mf_slab_pipeline(
+        p, st,
+        [&](size_t k, cudaStream_t s2) -> mf_status {
+            const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
+            mf_prof_begin("mixed_elem", s2);
+            k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, s2>>>(
+                e0, e1, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms,
+                p->adj[0].ptr, p->slot, reinterpret_cast<unsigned long long *>(p->kacc),
+                reinterpret_cast<unsigned long long *>(p->dacc), status);
+            mf_prof_end(s2);
+            MF_CUDA(cudaGetLastError());
+            return MF_OK;
+        },
+        [&](size_t k, cudaStream_t s2) -> mf_status {
+            const int64_t n0 = p->slab_n[k], n1 = p->slab_n[k + 1];
+            if (n1 > n0) {
+                mf_prof_begin("mixed_finish", s2);
+                k_mixed_finish<<<(unsigned)((n1 - n0 + FN_WARPS - 1) / FN_WARPS), FN_WARPS * 32, 0, s2>>>(
+                    n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->kacc, p->dacc, ms, pp, qq, c->bc_mask,
+                    c->bc_val, p->row_ptr, values, d);
+                mf_prof_end(s2);
+            }
+            MF_CUDA(cudaGetLastError());
+            return MF_OK;
+        });
 }

@@ -456,12 +456,12 @@ mf_status plan_slabs(const mf_mesh *m, const Incidence &inc, int64_t stride, cud
     MF_CUDA(cudaStreamSynchronize(st));
     MF_CUDA(cudaFreeAsync(d_ready, st));
     for (int64_t v = 1; v < nn; ++v) ready[v] = std::max(ready[v], ready[v - 1]);  // prefix maximum
-    // MF_SLABS chunks of elements; with more than one, the gather of a chunk
-    // overlaps the element kernel of the next on a second stream.  Measured on
-    // the 64^3 elasticity workload, one chunk is fastest: serial chunks lose
-    // to launch ramp-up and tail (2.08 vs 1.67 ms), and 8 overlapped chunks to
-    // the two kernels slowing each other down, both issue-heavy (mixed path
-    // 1.70 vs 1.59 ms).
+    // MF_SLABS chunks of elements; with more than one, the finishing of the
+    // nodes a chunk completes overlaps the element kernel of the next chunk on
+    // a second stream.  Measured on the 64^3 elasticity workload, one chunk is
+    // fastest: 8 overlapped chunks took 1.43 vs 1.32 ms (the element kernel,
+    // bound by instruction issue, slows down next to the finishing pass), and
+    // serial chunks lose to launch ramp-up and tail.
     (void)stride;
     const int64_t chunk = std::max<int64_t>(4096, (ne + MF_SLABS - 1) / MF_SLABS);
     p->slab_e.clear();
