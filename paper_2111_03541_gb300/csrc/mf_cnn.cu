@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_conv_first(int B, int nz, int ny, int n
                                                     const __nv_bfloat16 *__restrict__ w,
                                                     const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out)
 {
-    __shared__ float sw[27][2][16];  // [o][ci][co]; source layout [co][ci][o]
+    __shared__ __align__(16) float sw[27][2][16];  // [o][ci][co]; source layout [co][ci][o]
     for (int i = threadIdx.x; i < 16 * 2 * 27; i += blockDim.x) {
         const int co = i / 54, ci = (i / 27) % 2, o = i % 27;
         sw[o][ci][co] = __bfloat162float(w[i]);
@@ -77,14 +77,32 @@ __global__ void __launch_bounds__(256) k_conv_first(int B, int nz, int ny, int n
         float acc[16];
 #pragma unroll
         for (int co = 0; co < 16; ++co) acc[co] = bias[co];
-#pragma unroll 3
-        for (int o = 0; o < 27; ++o) {
-            const int zz = z + o / 9 - 1, yy = y + (o / 3) % 3 - 1, xx = x + o % 3 - 1;
-            if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
-            const uint32_t raw = __ldg(base + (zz * ny + yy) * nx + xx);
-            const float x0 = __uint_as_float(raw << 16), x1 = __uint_as_float(raw & 0xffff0000u);
+        // the 9 neighbour loads of a z-plane are issued before its FMAs (zero
+        // outside the grid)
+#pragma unroll 1
+        for (int dz = 0; dz < 3; ++dz) {
+            uint32_t raw[9];
 #pragma unroll
-            for (int co = 0; co < 16; ++co) acc[co] = fmaf(sw[o][0][co], x0, fmaf(sw[o][1][co], x1, acc[co]));
+            for (int o = 0; o < 9; ++o) {
+                const int zz = z + dz - 1, yy = y + o / 3 - 1, xx = x + o % 3 - 1;
+                const bool ok = zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+                raw[o] = ok ? __ldg(base + (zz * ny + yy) * nx + xx) : 0u;
+            }
+#pragma unroll
+            for (int o = 0; o < 9; ++o) {
+                const float x0 = __uint_as_float(raw[o] << 16), x1 = __uint_as_float(raw[o] & 0xffff0000u);
+                const int oo = 9 * dz + o;
+                const float4 *w0 = reinterpret_cast<const float4 *>(sw[oo][0]);
+                const float4 *w1 = reinterpret_cast<const float4 *>(sw[oo][1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {  // 16-byte weight reads
+                    const float4 u0 = w0[q], u1 = w1[q];
+                    acc[4 * q] = fmaf(u0.x, x0, fmaf(u1.x, x1, acc[4 * q]));
+                    acc[4 * q + 1] = fmaf(u0.y, x0, fmaf(u1.y, x1, acc[4 * q + 1]));
+                    acc[4 * q + 2] = fmaf(u0.z, x0, fmaf(u1.z, x1, acc[4 * q + 2]));
+                    acc[4 * q + 3] = fmaf(u0.w, x0, fmaf(u1.w, x1, acc[4 * q + 3]));
+                }
+            }
         }
         uint32_t pk[8];
 #pragma unroll
@@ -106,7 +124,7 @@ __global__ void __launch_bounds__(256) k_conv_last(int B, int nz, int ny, int nx
                                                    const __nv_bfloat16 *__restrict__ w,
                                                    const float *__restrict__ bias, float *__restrict__ out)
 {
-    __shared__ float sw[27][16];  // [o][ci]; source layout [ci][o]
+    __shared__ __align__(16) float sw[27][16];  // [o][ci]; source layout [ci][o]
     for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) sw[i % 27][i / 27] = __bfloat162float(w[i]);
     __syncthreads();
     const int nv = nz * ny * nx;
@@ -117,17 +135,30 @@ __global__ void __launch_bounds__(256) k_conv_last(int B, int nz, int ny, int nx
         const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
         const uint4 *base = reinterpret_cast<const uint4 *>(in + (int64_t)b * nv * 16);
         float acc = b0;
-#pragma unroll 3
-        for (int o = 0; o < 27; ++o) {
-            const int zz = z + o / 9 - 1, yy = y + (o / 3) % 3 - 1, xx = x + o % 3 - 1;
-            if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
-            const int64_t u = (int64_t)(zz * ny + yy) * nx + xx;
-            const uint4 lo = __ldg(base + 2 * u), hi = __ldg(base + 2 * u + 1);
-            const uint32_t wds[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        // one z-plane of 9 neighbours (18 16-byte loads) in flight at a time
+#pragma unroll 1
+        for (int dz = 0; dz < 3; ++dz) {
+            uint4 lo[9], hi[9];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                acc = fmaf(sw[o][2 * k], __uint_as_float(wds[k] << 16), acc);
-                acc = fmaf(sw[o][2 * k + 1], __uint_as_float(wds[k] & 0xffff0000u), acc);
+            for (int o = 0; o < 9; ++o) {
+                const int zz = z + dz - 1, yy = y + o / 3 - 1, xx = x + o % 3 - 1;
+                const bool ok = zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+                const int64_t u = (int64_t)(zz * ny + yy) * nx + xx;
+                lo[o] = ok ? __ldg(base + 2 * u) : make_uint4(0u, 0u, 0u, 0u);
+                hi[o] = ok ? __ldg(base + 2 * u + 1) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int o = 0; o < 9; ++o) {
+                const uint32_t wds[8] = {lo[o].x, lo[o].y, lo[o].z, lo[o].w, hi[o].x, hi[o].y, hi[o].z, hi[o].w};
+                const float4 *wo = reinterpret_cast<const float4 *>(sw[9 * dz + o]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {  // 16-byte weight reads
+                    const float4 u = wo[q];
+                    acc = fmaf(u.x, __uint_as_float(wds[2 * q] << 16), acc);
+                    acc = fmaf(u.y, __uint_as_float(wds[2 * q] & 0xffff0000u), acc);
+                    acc = fmaf(u.z, __uint_as_float(wds[2 * q + 1] << 16), acc);
+                    acc = fmaf(u.w, __uint_as_float(wds[2 * q + 1] & 0xffff0000u), acc);
+                }
             }
         }
         out[g] = acc;
