@@ -4,12 +4,17 @@ for profiling (ncu, the kernel-timing hooks) without the whole benchmark.
     python -m paper_2111_03541_gb300.cases elastic --n 48 --prec mixed --reps 7
     python -m paper_2111_03541_gb300.cases thermal-grf --n 128 --reps 4 --pcg-iters 30
     python -m paper_2111_03541_gb300.cases cnn --n 129 --reps 5
+    python -m paper_2111_03541_gb300.cases oseen --n 512 --reps 5
+    python -m paper_2111_03541_gb300.cases batch --reps 5
 
 elastic: Q1 elasticity on an n^3 jittered box (gen.elastic_problem), assembled
 reps times after one untimed call.  thermal-grf: Q1 thermal conduction with
 k = exp(GRF) on an n^3 box (gen.grf_thermal_problem), assembled reps times,
 then pcg-iters Jacobi-PCG iterations (graph of 50).  cnn: reps forward passes
-of the preconditioner network on an n^3 node grid (package weights).
+of the preconditioner network on an n^3 node grid (package weights).  oseen:
+the Taylor-Hood flow form on an n^2 grid (gen.oseen_problem), assembled reps
+times.  batch: the 512-problem thermal batch (gen.batch_specs) in one graph,
+default tiling, reps replays.
 Inputs are the seeded synthetic ones of `gen`; every step runs in libmf.
 """
 from __future__ import annotations
@@ -25,7 +30,7 @@ def _times(mf):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn"))
+    ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn", "oseen", "batch"))
     ap.add_argument("--n", type=int, default=48)
     ap.add_argument("--prec", choices=("fp64", "mixed"), default="mixed")
     ap.add_argument("--reps", type=int, default=5)
@@ -60,6 +65,26 @@ def main(argv=None):
             x, st, info = P.solve(tol=1e-8, max_iter=a.pcg_iters, check_every=50)
             torch.cuda.synchronize()
             print("pcg iterations", info.iterations, "residual", info.rel_residual)
+    elif a.case == "oseen":
+        P = mf.Problem(gen.oseen_problem(a.n))
+        P.assemble()
+        torch.cuda.synchronize()
+        mf.mf_set_kernel_timing(1)
+        for _ in range(a.reps):
+            P.assemble()
+        torch.cuda.synchronize()
+        print("assembly", _times(mf))
+    elif a.case == "batch":
+        Ps = [mf.Problem(gen.batch_problem(sp)) for sp in gen.batch_specs()]
+        B = mf.mf_batch_create(Ps)
+        mf.mf_batch_assemble(B)
+        torch.cuda.synchronize()
+        mf.mf_set_kernel_timing(1)
+        for _ in range(a.reps):
+            mf.mf_batch_assemble(B)
+        torch.cuda.synchronize()
+        print("batch", _times(mf))
+        mf.mf_batch_destroy(B)
     else:
         from . import learned
         cnn = mf.mf_cnn_create(learned.load_params(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",

@@ -386,67 +386,164 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
     }
 }
 
-// flow rows: u_i(n) = [A over P2-P2 | -B_i^T over P2-P1]; p(n) = [B_1 | B_2 over P1-P2 | diag]
-__global__ void __launch_bounds__(256) k_gather_oseen(int64_t n2, int64_t n1, mf_adj pp, mf_adj pq, mf_adj qp,
-                                                      const double *__restrict__ sc, const uint8_t *__restrict__ mask,
-                                                      const double *__restrict__ bval,
-                                                      const int64_t *__restrict__ row_ptr, double *__restrict__ values,
-                                                      double *__restrict__ d)
+// flow rows, node-centric (groups of 16 lanes per node, 2 nodes per warp):
+//   u_i(n) = [A over the P2 neighbours | -B_i^T over the P1 neighbours],
+//   p(n1)  = [B_1 | B_2 over the P2 neighbours | 0 on the diagonal].
+// The element scratch holds A (6 x 6) at 0 and B_i[a1][b2] at 36 + 18 i +
+// 6 a1 + b2.  Each entry is a sum over the incident elements in ascending
+// order (the node's incidence list), the adds into shared-memory rows run
+// element by element; Dirichlet rows become identity rows and constrained
+// columns move to the right-hand side (f = 0, so d is the lifting alone).
+constexpr int GO_GROUPS = 16;  // node groups per block (8 warps)
+
+__device__ __forceinline__ void flow_put(double &v, double &lift, bool rm, int64_t r, int64_t sdof,
+                                         const uint8_t *__restrict__ mask, const double *__restrict__ bval)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (r >= 2 * n2 + n1) return;
-    const bool rm = mask ? mask[r] != 0 : false;
-    const int64_t base = row_ptr[r];
-    double lift = 0.0;
-    auto put = [&](int64_t pos, int64_t sdof, double v) {
-        if (mask) {
-            if (rm) v = (r == sdof) ? 1.0 : 0.0;
-            else if (mask[sdof]) { lift -= v * bval[sdof]; v = 0.0; }
-        }
-        values[pos] = v;
-    };
-    if (r < 2 * n2) {
-        const int i = (int)(r / n2);
-        const int64_t n = r % n2;
-        const int64_t d0 = pp.ptr[n + 1] - pp.ptr[n];
-        for (int64_t k = lane; k < d0; k += 32) {
-            const int64_t p = pp.ptr[n] + k;
-            double acc = 0.0;
-            for (int64_t t = pp.cptr[p]; t < pp.cptr[p + 1]; ++t) {
-                const int32_t v = pp.clist[t];
-                acc += sc[(int64_t)(v >> 6) * 72 + ((v >> 3) & 7) * 6 + (v & 7)];
-            }
-            put(base + k, i * n2 + pp.col[p], acc);
-        }
-        const int64_t d1 = pq.ptr[n + 1] - pq.ptr[n];
-        for (int64_t k = lane; k < d1; k += 32) {
-            const int64_t p = pq.ptr[n] + k;
-            double acc = 0.0;
-            for (int64_t t = pq.cptr[p]; t < pq.cptr[p + 1]; ++t) {
-                const int32_t v = pq.clist[t];  // a: P2 local (velocity row), b: P1 local (pressure col)
-                acc -= sc[(int64_t)(v >> 6) * 72 + 36 + 18 * i + (v & 7) * 6 + ((v >> 3) & 7)];
-            }
-            put(base + d0 + k, 2 * n2 + pq.col[p], acc);
-        }
-    } else {
-        const int64_t n = r - 2 * n2;
-        const int64_t d2 = qp.ptr[n + 1] - qp.ptr[n];
-        for (int i = 0; i < 2; ++i)
-            for (int64_t k = lane; k < d2; k += 32) {
-                const int64_t p = qp.ptr[n] + k;
-                double acc = 0.0;
-                for (int64_t t = qp.cptr[p]; t < qp.cptr[p + 1]; ++t) {
-                    const int32_t v = qp.clist[t];  // a: P1 local (pressure row), b: P2 local (velocity col)
-                    acc += sc[(int64_t)(v >> 6) * 72 + 36 + 18 * i + ((v >> 3) & 7) * 6 + (v & 7)];
-                }
-                put(base + i * d2 + k, i * n2 + qp.col[p], acc);
-            }
-        if (lane == 0) put(base + 2 * d2, r, 0.0);
+    if (mask) {
+        if (rm) v = (r == sdof) ? 1.0 : 0.0;
+        else if (mask[sdof]) { lift -= v * bval[sdof]; v = 0.0; }
     }
+}
+
+__global__ void __launch_bounds__(GO_GROUPS * 16) k_gather_oseen_u(
+    int64_t n2, mf_adj pp, mf_adj pq, const int64_t *__restrict__ inc_ptr, const uint8_t *__restrict__ inc_loc,
+    const int32_t *__restrict__ inc, const uint8_t *__restrict__ slot_pp, const uint8_t *__restrict__ slot_pq,
+    const double *__restrict__ sc, const uint8_t *__restrict__ mask, const double *__restrict__ bval,
+    const int64_t *__restrict__ row_ptr, double *__restrict__ values, double *__restrict__ d)
+{
+    __shared__ double accA_all[GO_GROUPS][MF_MAX_DEG];
+    __shared__ double accB_all[GO_GROUPS][2][MF_MAX_DEG];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 4, sub = threadIdx.x & 15;
+    const unsigned gmask = 0xffffu << (lane & 16);
+    const int64_t n = (int64_t)blockIdx.x * GO_GROUPS + grp;
+    if (n >= n2) return;  // group-uniform
+    double *accA = accA_all[grp];
+    double(*accB)[MF_MAX_DEG] = accB_all[grp];
+    const int64_t pa0 = pp.ptr[n], pb0 = pq.ptr[n];
+    const int da = (int)(pp.ptr[n + 1] - pa0), db = (int)(pq.ptr[n + 1] - pb0);
+    for (int k = sub; k < da; k += 16) accA[k] = 0.0;
+    for (int k = sub; k < db; k += 16) accB[0][k] = accB[1][k] = 0.0;
+    __syncwarp(gmask);
+    // lanes 0..5: A[a][b]; lanes 6..11: B_i[a1][a] with i = (sub - 6) / 3, a1 = (sub - 6) % 3
+    const bool isA = sub < 6, isB = sub >= 6 && sub < 12;
+    const int bi = isB ? (sub - 6) / 3 : 0, ba1 = isB ? (sub - 6) % 3 : 0;
+    const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
+    for (int64_t cb = i0; cb < i1; cb += 4) {
+        const int cnt = (int)min((int64_t)4, i1 - cb);
+        double v[4];
+        int s[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
-    if (lane == 0) d[r] = rm ? bval[r] : lift;
+        for (int j = 0; j < 4; ++j) {
+            v[j] = 0.0;
+            s[j] = 0;
+            if (j < cnt && (isA || isB)) {
+                const int64_t t = cb + j;
+                const double *se = sc + (int64_t)inc[t] * 72;
+                const int a = inc_loc[t];
+                if (isA) {
+                    v[j] = se[6 * a + sub];
+                    s[j] = slot_pp[t * 6 + sub];
+                } else {
+                    v[j] = se[36 + 18 * bi + 6 * ba1 + a];
+                    s[j] = slot_pq[t * 3 + ba1];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < cnt) {  // group-uniform
+                if (isA) accA[s[j]] += v[j];
+                else if (isB) accB[bi][s[j]] -= v[j];
+                __syncwarp(gmask);
+            }
+        }
+    }
+    // rows u_1(n), u_2(n): A part (columns i n2 + m), then -B_i^T (columns 2 n2 + m1)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int64_t r = i * n2 + n;
+        const bool rm = mask ? mask[r] != 0 : false;
+        const int64_t rb = row_ptr[r];
+        double lift = 0.0;
+        for (int k = sub; k < da; k += 16) {
+            double val = accA[k];
+            flow_put(val, lift, rm, r, i * n2 + pp.col[pa0 + k], mask, bval);
+            values[rb + k] = val;
+        }
+        for (int k = sub; k < db; k += 16) {
+            double val = accB[i][k];
+            flow_put(val, lift, rm, r, 2 * n2 + pq.col[pb0 + k], mask, bval);
+            values[rb + da + k] = val;
+        }
+        if (__any_sync(gmask, lift != 0.0))
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) lift += __shfl_xor_sync(gmask, lift, o, 16);
+        if (sub == 0) d[r] = rm ? bval[r] : lift;
+    }
+}
+
+__global__ void __launch_bounds__(GO_GROUPS * 16) k_gather_oseen_p(
+    int64_t n2, int64_t n1, mf_adj qp, const int64_t *__restrict__ pinc_ptr, const int32_t *__restrict__ pinc,
+    const uint8_t *__restrict__ pinc_loc, const uint8_t *__restrict__ pslot, const double *__restrict__ sc,
+    const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+    double *__restrict__ values, double *__restrict__ d)
+{
+    __shared__ double acc_all[GO_GROUPS][2][MF_MAX_DEG];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 4, sub = threadIdx.x & 15;
+    const unsigned gmask = 0xffffu << (lane & 16);
+    const int64_t n = (int64_t)blockIdx.x * GO_GROUPS + grp;
+    if (n >= n1) return;  // group-uniform
+    double(*acc)[MF_MAX_DEG] = acc_all[grp];
+    const int64_t q0 = qp.ptr[n];
+    const int dq = (int)(qp.ptr[n + 1] - q0);
+    for (int k = sub; k < dq; k += 16) acc[0][k] = acc[1][k] = 0.0;
+    __syncwarp(gmask);
+    // lanes 0..11: B_i[a1][b] with i = sub / 6, b = sub % 6
+    const bool act = sub < 12;
+    const int bi = act ? sub / 6 : 0, bb = act ? sub % 6 : 0;
+    const int64_t i0 = pinc_ptr[n], i1 = pinc_ptr[n + 1];
+    for (int64_t cb = i0; cb < i1; cb += 4) {
+        const int cnt = (int)min((int64_t)4, i1 - cb);
+        double v[4];
+        int s[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = 0.0;
+            s[j] = 0;
+            if (j < cnt && act) {
+                const int64_t t = cb + j;
+                v[j] = sc[(int64_t)pinc[t] * 72 + 36 + 18 * bi + 6 * pinc_loc[t] + bb];
+                s[j] = pslot[t * 6 + bb];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < cnt) {  // group-uniform
+                if (act) acc[bi][s[j]] += v[j];
+                __syncwarp(gmask);
+            }
+        }
+    }
+    const int64_t r = 2 * n2 + n;
+    const bool rm = mask ? mask[r] != 0 : false;
+    const int64_t rb = row_ptr[r];
+    double lift = 0.0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        for (int k = sub; k < dq; k += 16) {
+            double val = acc[i][k];
+            flow_put(val, lift, rm, r, i * n2 + qp.col[q0 + k], mask, bval);
+            values[rb + i * dq + k] = val;
+        }
+    if (sub == 0) {
+        double val = 0.0;
+        flow_put(val, lift, rm, r, r, mask, bval);
+        values[rb + 2 * dq] = val;
+    }
+    if (__any_sync(gmask, lift != 0.0))
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) lift += __shfl_xor_sync(gmask, lift, o, 16);
+    if (sub == 0) d[r] = rm ? bval[r] : lift;
 }
 
 // pressure-mass diagonal: one thread per P1 node, incident elements ascending
@@ -576,9 +673,12 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         mf_prof_begin("gather_oseen", st);
-        k_gather_oseen<<<nblk(p->n_rows * 32, 256), 256, 0, st>>>(m->n_nodes, m->n_pnodes, p->adj[0], p->adj[1],
-                                                                  p->adj[2], p->scratch, c->bc_mask, c->bc_val,
-                                                                  p->row_ptr, values, d);
+        k_gather_oseen_u<<<nblk(m->n_nodes, GO_GROUPS), GO_GROUPS * 16, 0, st>>>(
+            m->n_nodes, p->adj[0], p->adj[1], p->inc_ptr, p->inc_loc, p->inc, p->inc_slot, p->inc_slot_pq,
+            p->scratch, c->bc_mask, c->bc_val, p->row_ptr, values, d);
+        k_gather_oseen_p<<<nblk(m->n_pnodes, GO_GROUPS), GO_GROUPS * 16, 0, st>>>(
+            m->n_nodes, m->n_pnodes, p->adj[2], p->pinc_ptr, p->pinc, p->pinc_loc, p->pinc_slot, p->scratch,
+            c->bc_mask, c->bc_val, p->row_ptr, values, d);
         mf_prof_end(st);
     }
     MF_CUDA(cudaGetLastError());

@@ -13,16 +13,12 @@
 #define MF_MAX_INC 32   // elements incident to one node
 
 // Adjacency between a row node space and a column node space (Block B-1: the
-// unique control-point pairs), with, for every node pair, the list of element
-// contributions (e, a, b) in ascending element order.
+// unique control-point pairs).
 struct mf_adj {
     int64_t n_rows = 0;      // row nodes
     int64_t n_pairs = 0;     // unique (row node, col node) pairs
     int64_t *ptr = nullptr;  // [n_rows + 1]
     int32_t *col = nullptr;  // [n_pairs] ascending per row
-    int64_t *cptr = nullptr; // [n_pairs + 1]
-    int32_t *clist = nullptr;// [n_contrib] packed e * 64 + a * 8 + b
-    int64_t n_contrib = 0;
 };
 
 struct mf_mesh {
@@ -52,9 +48,15 @@ struct mf_pattern {
     int32_t *inc = nullptr;
     uint8_t *inc_loc = nullptr;  // position of the node in each incident element (thermal
                                  // Q1: bit 7 set when the element is a translate)
-    // flow: elements incident to each P1 pressure node, ascending
+    // flow: elements incident to each P1 pressure node, ascending, with the
+    // node's local index (0..2) in each
     int64_t *pinc_ptr = nullptr;
     int32_t *pinc = nullptr;
+    uint8_t *pinc_loc = nullptr;
+    // flow slot maps per incidence entry: P2 row x the element's P2 nodes
+    // (inc_slot, 6 per entry), P2 row x its P1 nodes (inc_slot_pq, 3), P1 row
+    // x its P2 nodes (pinc_slot, 6)
+    uint8_t *inc_slot_pq = nullptr, *pinc_slot = nullptr;
     // elasticity: slot[e][a][b] = position of node conn[e][b] among the sorted
     // neighbours of node conn[e][a] (u8, n_elems x 64)
     uint8_t *slot = nullptr;

@@ -5,12 +5,10 @@
 // unique pairs of a row node space and a column node space form an adjacency
 // (CSR over row nodes, ascending columns) built without hashing: per row node
 // the incident elements are gathered and their nodes sorted and de-duplicated
-// in registers.  The thermal and elasticity gathers walk a node's incident
-// elements in ascending order and place each entry through a slot map (the
-// position of the column node among the row node's neighbours); the flow
-// gather keeps, per node pair, the list of element contributions (e, a, b) in
-// ascending element order.  Either fixes the summation order of the assembly.
-// The dof-level CSR of a form is then laid out from its blocks.
+// in registers.  The gathers walk a node's incident elements in ascending
+// order and place each entry through a slot map (the position of the column
+// node among the row node's neighbours), which fixes the summation order of
+// the assembly.  The dof-level CSR of a form is then laid out from its blocks.
 #include <algorithm>
 #include <cstdio>
 
@@ -169,29 +167,6 @@ __device__ __forceinline__ int64_t find_pair(const int64_t *ptr, const int32_t *
     return lo;  // the pair exists by construction
 }
 
-// contributions: one thread per (element, a in row space, b in column space)
-template <bool FILL>
-__global__ void k_contrib(int64_t n_el, int npe_r, const int32_t *__restrict__ conn_r, int npe_c,
-                          const int32_t *__restrict__ conn_c, const int64_t *__restrict__ ptr,
-                          const int32_t *__restrict__ col, int64_t *cnt, const int64_t *__restrict__ cptr,
-                          int32_t *clist)
-{
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int per = npe_r * npe_c;
-    if (t >= n_el * per) return;
-    const int64_t e = t / per;
-    const int a = (int)(t % per) / npe_c, b = (int)(t % per) % npe_c;
-    const int32_t n = conn_r[e * npe_r + a], m = conn_c[e * npe_c + b];
-    const int64_t p = find_pair(ptr, col, n, m);
-    if (!FILL) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[p]), 1ull);
-    } else {
-        const int64_t pos =
-            cptr[p] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[p]), 1ull);
-        clist[pos] = (int32_t)(e * 64 + a * 8 + b);
-    }
-}
-
 // last (largest) incident element of every node
 __global__ void k_node_ready(int64_t n, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
                              int32_t *ready)
@@ -210,18 +185,19 @@ __global__ void k_tpos(int64_t n_nodes, const int64_t *__restrict__ ptr, const i
     for (int64_t p = ptr[n]; p < ptr[n + 1]; ++p) tpos[p] = (int32_t)find_pair(ptr, col, col[p], (int32_t)n);
 }
 
-// incidence slot map: for incidence entry t of node n (element e, local a),
-// inc_slot[t * npe + b] = position of conn[e][b] among the neighbours of n
-__global__ void k_inc_slot(int64_t n_nodes, int npe, const int32_t *__restrict__ conn,
+// incidence slot map: for incidence entry t of row node n (element e),
+// inc_slot[t * npe_c + b] = position of column node conn_c[e][b] among the
+// neighbours of n in the adjacency (ptr, col)
+__global__ void k_inc_slot(int64_t n_nodes, int npe_c, const int32_t *__restrict__ conn_c,
                            const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
                            const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, uint8_t *inc_slot)
 {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= n_nodes) return;
     for (int64_t t = inc_ptr[n]; t < inc_ptr[n + 1]; ++t) {
-        const int32_t *ce = conn + (int64_t)inc[t] * npe;
-        for (int b = 0; b < npe; ++b)
-            inc_slot[t * npe + b] = (uint8_t)(find_pair(ptr, col, (int32_t)n, ce[b]) - ptr[n]);
+        const int32_t *ce = conn_c + (int64_t)inc[t] * npe_c;
+        for (int b = 0; b < npe_c; ++b)
+            inc_slot[t * npe_c + b] = (uint8_t)(find_pair(ptr, col, (int32_t)n, ce[b]) - ptr[n]);
     }
 }
 
@@ -401,8 +377,8 @@ mf_status check_status(int *status, cudaStream_t st, const char *what)
     return MF_OK;
 }
 
-mf_status build_adj(int64_t n_rows, const Incidence &inc, int64_t n_el, int npe_r, const int32_t *conn_r,
-                    int npe_c, const int32_t *conn_c, bool contrib, cudaStream_t st, mf_adj *A, int *status)
+mf_status build_adj(int64_t n_rows, const Incidence &inc, const int32_t *conn_r, int npe_c, const int32_t *conn_c,
+                    cudaStream_t st, mf_adj *A, int *status)
 {
     A->n_rows = n_rows;
     MF_CUDA(cudaMallocAsync(&A->ptr, sizeof(int64_t) * (n_rows + 1), st));
@@ -419,24 +395,6 @@ mf_status build_adj(int64_t n_rows, const Incidence &inc, int64_t n_el, int npe_
     MF_CUDA(cudaMallocAsync(&A->col, sizeof(int32_t) * A->n_pairs, st));
     k_adj<true><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self, nullptr,
                                                   A->ptr, A->col, status);
-    if (!contrib) return check_status(status, st, "mf_pattern_build");
-    // contributions of every pair, ascending packed (e, a, b)
-    int64_t *cnt = nullptr;
-    MF_CUDA(cudaMallocAsync(&A->cptr, sizeof(int64_t) * (A->n_pairs + 1), st));
-    MF_CUDA(cudaMallocAsync(&cnt, sizeof(int64_t) * A->n_pairs, st));
-    MF_CUDA(cudaMemsetAsync(A->cptr, 0, sizeof(int64_t) * (A->n_pairs + 1), st));
-    MF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * A->n_pairs, st));
-    const int64_t work = n_el * npe_r * npe_c;
-    k_contrib<false><<<nblk(work), TPB, 0, st>>>(n_el, npe_r, conn_r, npe_c, conn_c, A->ptr, A->col, A->cptr,
-                                                nullptr, nullptr);
-    MF_CUDA(mf_scan_i64(A->cptr, A->n_pairs + 1, nullptr, st));
-    A->n_contrib = work;
-    MF_CUDA(cudaMallocAsync(&A->clist, sizeof(int32_t) * work, st));
-    k_contrib<true><<<nblk(work), TPB, 0, st>>>(n_el, npe_r, conn_r, npe_c, conn_c, A->ptr, A->col, cnt,
-                                               A->cptr, A->clist);
-    k_sort_segments_i32<<<nblk(A->n_pairs), TPB, 0, st>>>(A->n_pairs, A->cptr, A->clist, status);
-    MF_CUDA(cudaGetLastError());
-    MF_CUDA(cudaFreeAsync(cnt, st));
     return check_status(status, st, "mf_pattern_build");
 }
 
@@ -527,8 +485,6 @@ void mf_pattern_free(mf_pattern *p)
     for (int i = 0; i < 3; ++i) {
         cudaFree(p->adj[i].ptr);
         cudaFree(p->adj[i].col);
-        cudaFree(p->adj[i].cptr);
-        cudaFree(p->adj[i].clist);
         p->adj[i] = mf_adj();
     }
     cudaFree(p->scratch);
@@ -547,6 +503,10 @@ void mf_pattern_free(mf_pattern *p)
     p->tpos = nullptr;
     cudaFree(p->inc_slot);
     p->inc_slot = nullptr;
+    cudaFree(p->inc_slot_pq);
+    cudaFree(p->pinc_slot);
+    cudaFree(p->pinc_loc);
+    p->inc_slot_pq = p->pinc_slot = p->pinc_loc = nullptr;
     cudaFree(p->elem_inc);
     p->elem_inc = nullptr;
     cudaFree(p->mixed_state);
@@ -576,8 +536,7 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
     mf_status s = build_incidence(m->n_nodes, m->n_elems, npe, m->conn, st, &incv, status);
     if (s == MF_OK) s = check_status(status, st, "mf_pattern_build");
     if (s != MF_OK) { free_inc(incv, st); return s; }
-    s = build_adj(m->n_nodes, incv, m->n_elems, npe, m->conn, npe, m->conn, form == MF_FORM_OSEEN, st, &p->adj[0],
-                  status);
+    s = build_adj(m->n_nodes, incv, m->conn, npe, m->conn, st, &p->adj[0], status);
     p->n_adj = 1;
     if (s != MF_OK) { free_inc(incv, st); return s; }
 
@@ -648,13 +607,25 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         Incidence incp;
         s = build_incidence(m->n_pnodes, m->n_elems, 3, m->pconn, st, &incp, status);
         if (s == MF_OK)
-            s = build_adj(m->n_nodes, incv, m->n_elems, 6, m->conn, 3, m->pconn, true, st, &p->adj[1], status);
+            s = build_adj(m->n_nodes, incv, m->conn, 3, m->pconn, st, &p->adj[1], status);
         if (s == MF_OK)
-            s = build_adj(m->n_pnodes, incp, m->n_elems, 3, m->pconn, 6, m->conn, true, st, &p->adj[2], status);
+            s = build_adj(m->n_pnodes, incp, m->pconn, 6, m->conn, st, &p->adj[2], status);
         p->pinc_ptr = incp.ptr;
         p->pinc = incp.inc;
-        if (incp.loc) cudaFreeAsync(incp.loc, st);
+        p->pinc_loc = incp.loc;
         p->n_adj = 3;
+        if (s == MF_OK) {
+            // slots: P2 rows x P2 columns, P2 rows x P1 columns, P1 rows x P2 columns
+            MF_CUDA(cudaMallocAsync(&p->inc_slot, (size_t)36 * m->n_elems, st));
+            MF_CUDA(cudaMallocAsync(&p->inc_slot_pq, (size_t)18 * m->n_elems, st));
+            MF_CUDA(cudaMallocAsync(&p->pinc_slot, (size_t)18 * m->n_elems, st));
+            k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, 6, m->conn, incv.ptr, incv.inc, p->adj[0].ptr,
+                                                         p->adj[0].col, p->inc_slot);
+            k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, 3, m->pconn, incv.ptr, incv.inc, p->adj[1].ptr,
+                                                         p->adj[1].col, p->inc_slot_pq);
+            k_inc_slot<<<nblk(m->n_pnodes), TPB, 0, st>>>(m->n_pnodes, 6, m->conn, incp.ptr, incp.inc,
+                                                          p->adj[2].ptr, p->adj[2].col, p->pinc_slot);
+        }
         if (s != MF_OK) { free_inc(incv, st); return s; }
         const int64_t n2 = m->n_nodes, n1 = m->n_pnodes;
         p->n_rows = 2 * n2 + n1;
