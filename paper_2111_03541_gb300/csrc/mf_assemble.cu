@@ -148,7 +148,10 @@ __global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, co
     }
     double *o = out + e * 72;
     {
-        double A[36] = {};
+        // A = mu D + C: the viscous part D (symmetric, 21 entries) and the
+        // advection part C[a][b] = -rho sum_q w detJ (a_h . grad N_a) N_b are
+        // summed separately, so each FP64 operation does work once
+        double D[21] = {}, Cv[36] = {};
 #pragma unroll 1
         for (int q = 0; q < 6; ++q) {
             double l[3], w;
@@ -162,16 +165,25 @@ __global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, co
                 ah0 = fma(aN[b][0], N[b], ah0);
                 ah1 = fma(aN[b][1], N[b], ah1);
             }
+            const double wrho = wd * rho;
+            int t = 0;
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
-                const double adv_a = ah0 * g[a][0] + ah1 * g[a][1];
 #pragma unroll
-                for (int b = 0; b < 6; ++b)
-                    A[6 * a + b] = fma(wd, mu * (g[a][0] * g[b][0] + g[a][1] * g[b][1]) - rho * adv_a * N[b], A[6 * a + b]);
+                for (int b = a; b < 6; ++b, ++t) D[t] = fma(wd, fma(g[a][0], g[b][0], g[a][1] * g[b][1]), D[t]);
+                const double sa = wrho * fma(ah0, g[a][0], ah1 * g[a][1]);
+#pragma unroll
+                for (int b = 0; b < 6; ++b) Cv[6 * a + b] = fma(-sa, N[b], Cv[6 * a + b]);
             }
         }
+        int t = 0;
 #pragma unroll
-        for (int t = 0; t < 36; ++t) o[t] = A[t];
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = a; b < 6; ++b, ++t) {
+                o[6 * a + b] = fma(mu, D[t], Cv[6 * a + b]);
+                if (b != a) o[6 * b + a] = fma(mu, D[t], Cv[6 * b + a]);
+            }
     }
     {
         double B[36] = {};
@@ -183,11 +195,13 @@ __global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, co
             p2_basis(l, gl, N, g);
             const double wd = w * det;
 #pragma unroll
-            for (int i = 0; i < 2; ++i)
+            for (int a = 0; a < 3; ++a) {
+                const double wl = wd * l[a];
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
+                for (int i = 0; i < 2; ++i)
 #pragma unroll
-                    for (int b = 0; b < 6; ++b) B[18 * i + 6 * a + b] = fma(wd * l[a], g[b][i], B[18 * i + 6 * a + b]);
+                    for (int b = 0; b < 6; ++b) B[18 * i + 6 * a + b] = fma(wl, g[b][i], B[18 * i + 6 * a + b]);
+            }
         }
 #pragma unroll
         for (int t = 0; t < 36; ++t) o[36 + t] = B[t];
