@@ -35,15 +35,19 @@ UNIT = "elements/s"
 N_GRID = 64
 FCG_DIRS = 256  # stored directions of the flexible CG with the learned preconditioner
 
-# DRAM traffic per element of the fixed-point elasticity gather
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu, 48^3 case:
-# 337.08 MB + 187.54 MB for 110,592 elements; it grows in proportion to the
-# elements), with the SHA-256 prefix of the sources that capture was built
-# from: the line reports null traffic once they change.
-GATHER_TRAFFIC = {"kernel": "gather_elastic_fixed", "bytes_per_element": (337.08e6 + 187.54e6) / 110592,
-                  "sources": ("paper_2111_03541_gb300/csrc/mf_assemble.cu", "paper_2111_03541_gb300/csrc/mf_fem.cuh",
-                              "paper_2111_03541_gb300/csrc/mf_internal.h"),
-                  "sha256": "04e633eef10f79f3"}
+# ncu counters of the mixed element kernel (one launch, 48^3 case, 110,592
+# elements; both grow in proportion to the elements): executed warp
+# instructions (smsp__inst_executed.sum = 269,319,252) and DRAM traffic
+# (dram__bytes_read.sum + dram__bytes_write.sum = 140.77 MB + 68.55 MB), with
+# the SHA-256 prefix of the sources that capture was built from: the line
+# reports null for them once those sources change.
+MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 269319252 / 110592,
+                  "bytes_per_element": (140.77e6 + 68.55e6) / 110592,
+                  "sources": ("paper_2111_03541_gb300/csrc/mf_mixed.cu", "paper_2111_03541_gb300/csrc/mf_internal.h"),
+                  "sha256": "926c944429f299fd"}
+# instruction-issue ceiling of GB300: one warp instruction per clock per SM
+# sub-partition, 4 per SM, 152 SMs, 2070 MHz maximum SM clock
+ISSUE_PEAK = 152 * 4 * 2.070e9
 
 
 def sources_hash(files) -> str:
@@ -326,19 +330,24 @@ def run_ours(args):
                     "algorithmic": f"{FLOPS_PER_ELEMENT_FP64} FP64 flops/element x {n_el} elements",
                     "peak_source": "GB300 nominal dense FP64 rate (measured FMA-loop rate 1.19 TFLOP/s)"}
     else:
-        # the gather writes K and d once: 8 nnz + 8 n algorithmic bytes per launch
+        # the mixed path's dominant kernel is the element kernel, bound by
+        # instruction issue (INT/FP32 work of the double-float geometry and the
+        # BF16 split): its executed warp instructions per second against the
+        # issue ceiling
         kname = max(paths[best]["kernels"], key=lambda k: paths[best]["kernels"][k]["ms_per_step"])
-        kk = paths[best]["kernels"][kname]
-        ms_k = kk["ms_per_launch"]
-        kbytes = 8 * P.nnz + 8 * P.n
-        traffic = None
-        if kname == GATHER_TRAFFIC["kernel"] and sources_hash(GATHER_TRAFFIC["sources"]) == GATHER_TRAFFIC["sha256"]:
-            traffic = GATHER_TRAFFIC["bytes_per_element"] * n_el
-        ach = kbytes / (ms_k * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname, "ms_per_launch": ms_k,
-                    "algorithmic": f"8 nnz + 8 n = {kbytes} bytes per launch (K values and d written once)",
-                    "peak_source": peak_src, "assembly": roofline_hbm}
+        ms_k = paths[best]["kernels"][kname]["ms_per_launch"]
+        roofline = {"bound": "alu", "kernel": kname, "ms_per_launch": ms_k, "achieved": None, "peak": None,
+                    "unit": "warp instructions/s", "frac": None, "traffic": None, "assembly": roofline_hbm}
+        ok = kname == MIXED_ELEM_NCU["kernel"] and \
+            sources_hash(MIXED_ELEM_NCU["sources"]) == MIXED_ELEM_NCU["sha256"]
+        if ok:
+            inst = MIXED_ELEM_NCU["inst_per_element"] * n_el
+            ach = inst / (ms_k * 1e-3)
+            roofline.update({"achieved": ach, "peak": ISSUE_PEAK, "frac": ach / ISSUE_PEAK,
+                             "traffic": MIXED_ELEM_NCU["bytes_per_element"] * n_el,
+                             "algorithmic": f"{MIXED_ELEM_NCU['inst_per_element']:.1f} warp instructions per "
+                                            f"element (ncu, 48^3) x {n_el} elements",
+                             "peak_source": "GB300 issue ceiling: 152 SMs x 4 sub-partitions x 2070 MHz"})
 
     # end to end: host buffers in, K and d out, through the C ABI
     e2e = None if args.no_e2e else e2e_leg(P, prob, mf, stream, args, best)
