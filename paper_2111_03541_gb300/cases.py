@@ -8,7 +8,7 @@ for profiling (ncu, the kernel-timing hooks) without the whole benchmark.
     python -m paper_2111_03541_gb300.cases batch --reps 5
 
 elastic: Q1 elasticity on an n^3 jittered box (gen.elastic_problem), assembled
-reps times after one untimed call.  thermal-grf: Q1 thermal conduction with
+reps times after one untimed call, then pcg-iters Jacobi-PCG iterations.  thermal-grf: Q1 thermal conduction with
 k = exp(GRF) on an n^3 box (gen.grf_thermal_problem), assembled reps times,
 then pcg-iters Jacobi-PCG iterations (graph of 50).  cnn: reps forward passes
 of the preconditioner network on an n^3 node grid (package weights).  oseen:
@@ -51,6 +51,11 @@ def main(argv=None):
             P.assemble(prec)
         torch.cuda.synchronize()
         print("assembly", _times(mf))
+        mf.mf_set_kernel_timing(0)
+        if a.pcg_iters > 0:
+            x, st, info = P.solve(tol=1e-12, max_iter=a.pcg_iters, check_every=50)
+            torch.cuda.synchronize()
+            print("pcg iterations", info.iterations, "residual", info.rel_residual)
     elif a.case == "thermal-grf":
         P = mf.Problem(gen.grf_thermal_problem(a.n))
         P.assemble()

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "mf_internal.h"
 
@@ -85,15 +86,14 @@ __device__ void finish_sums(const double *part, unsigned nb, double *out, double
 }
 
 // ---------------------------------------------------------------------------
-// SpMV: W lanes per row, SPMV_U entries per lane per batch.  A lane issues the
+// SpMV: W lanes per row, U entries per lane per batch.  A lane issues the
 // column and value loads of its whole batch, then the gathers of x, then the
 // FMAs, so a row costs three dependent memory round trips however long it is
-// (up to W * SPMV_U entries per batch).
+// (up to W * U entries per batch).
 // ---------------------------------------------------------------------------
-constexpr int SPMV_U = 8;
 
 // Every lane of the warp calls the shuffles (full mask): rows past n give 0.
-template <int W>
+template <int W, int U>
 __device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                           const double *__restrict__ v, const double *__restrict__ x, int64_t row,
                                           int sub, bool valid)
@@ -101,20 +101,20 @@ __device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const 
     double s = 0.0;
     if (valid) {
         const int64_t t1 = rp[row + 1];
-        for (int64_t t = rp[row] + sub; t < t1; t += (int64_t)SPMV_U * W) {
-            int32_t c[SPMV_U];
-            double a[SPMV_U], xv[SPMV_U];
+        for (int64_t t = rp[row] + sub; t < t1; t += (int64_t)U * W) {
+            int32_t c[U];
+            double a[U], xv[U];
 #pragma unroll
-            for (int u = 0; u < SPMV_U; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int64_t tt = t + (int64_t)u * W;
                 const bool ok = tt < t1;
                 c[u] = ok ? __ldcs(&ci[tt]) : -1;
                 a[u] = ok ? __ldcs(&v[tt]) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < SPMV_U; ++u) xv[u] = c[u] >= 0 ? __ldg(&x[c[u]]) : 0.0;
+            for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(&x[c[u]]) : 0.0;
 #pragma unroll
-            for (int u = 0; u < SPMV_U; ++u) s = fma(a[u], xv[u], s);
+            for (int u = 0; u < U; ++u) s = fma(a[u], xv[u], s);
         }
     }
 #pragma unroll
@@ -122,8 +122,8 @@ __device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const 
     return s;
 }
 
-template <int W>
-__global__ void __launch_bounds__(RT, 4) k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+template <int W, int U>
+__global__ void __launch_bounds__(RT, U <= 6 ? 5 : 4) k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                              const double *__restrict__ v, const double *__restrict__ x,
                                              double *__restrict__ y)
 {
@@ -131,14 +131,14 @@ __global__ void __launch_bounds__(RT, 4) k_spmv(int64_t n, const int64_t *__rest
     const int64_t row = g / W;
     const int sub = (int)(g % W);
     const bool valid = row < n;
-    const double s = row_dot<W>(rp, ci, v, x, row, sub, valid);
+    const double s = row_dot<W, U>(rp, ci, v, x, row, sub, valid);
     if (valid && sub == 0) y[row] = s;
 }
 
 // q = K p: one W-lane group per row over the whole matrix (no reduction here,
 // so no per-block atomics on a shared ticket)
-template <int W>
-__global__ void __launch_bounds__(RT, 4) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
+template <int W, int U>
+__global__ void __launch_bounds__(RT, U <= 6 ? 5 : 4) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
                                                  const double *__restrict__ p, double *__restrict__ q,
                                                  const PcgState *S)
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(RT, 4) k_pcg_spmv(int64_t n, const int64_t *__
     const int64_t row = g / W;
     const int sub = (int)(g % W);
     const bool valid = row < n;
-    const double s = row_dot<W>(rp, ci, v, p, row, sub, valid);
+    const double s = row_dot<W, U>(rp, ci, v, p, row, sub, valid);
     if (valid && sub == 0) q[row] = s;
 }
 
@@ -343,37 +343,50 @@ __global__ void __launch_bounds__(RT) k_resid_norm(int64_t n, const double *__re
     }
 }
 
-// lanes per row: the smallest W >= 2 whose batch (W * SPMV_U entries) holds an
-// average row
-int spmv_width(int64_t n, int64_t nnz)
+// SpMV shape: W lanes per row and U entries per lane per batch, the smallest
+// W >= 2 (then U = 6 before 8) whose batch holds an average row: rows stay in
+// one batch while a warp keeps as many rows in flight as it can
+struct SpmvShape {
+    int w, u;
+};
+
+SpmvShape spmv_shape(int64_t n, int64_t nnz)
 {
     const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    int w = 2;
-    while (w < 32 && w * SPMV_U < avg) w *= 2;
-    return w;
+    for (int w = 2; w <= 32; w *= 2) {
+        if (w * 6 >= avg) return {w, 6};
+        if (w * 8 >= avg) return {w, 8};
+    }
+    return {32, 8};
 }
 
-template <int W>
-void launch_spmv(const mf_csr *K, const double *v, const double *x, double *y, cudaStream_t st)
+// calls f(std::integral_constant<int, W>, std::integral_constant<int, U>)
+template <typename F>
+void spmv_dispatch(SpmvShape sh, F &&f)
 {
-    k_spmv<W><<<nblk(K->n_rows * W, RT), RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, v, x, y);
+    using std::integral_constant;
+#define MF_SPMV_CASE(W_, U_) \
+    case W_ * 16 + U_: f(integral_constant<int, W_>(), integral_constant<int, U_>()); break;
+    switch (sh.w * 16 + sh.u) {
+        MF_SPMV_CASE(2, 6) MF_SPMV_CASE(2, 8) MF_SPMV_CASE(4, 6) MF_SPMV_CASE(4, 8) MF_SPMV_CASE(8, 6)
+        MF_SPMV_CASE(8, 8) MF_SPMV_CASE(16, 6) MF_SPMV_CASE(16, 8) MF_SPMV_CASE(32, 6)
+        default: f(integral_constant<int, 32>(), integral_constant<int, 8>()); break;
+    }
+#undef MF_SPMV_CASE
 }
 
 void spmv_any(const mf_csr *K, const double *v, const double *x, double *y, cudaStream_t st)
 {
-    switch (spmv_width(K->n_rows, K->nnz)) {
-    case 2: launch_spmv<2>(K, v, x, y, st); break;
-    case 4: launch_spmv<4>(K, v, x, y, st); break;
-    case 8: launch_spmv<8>(K, v, x, y, st); break;
-    case 16: launch_spmv<16>(K, v, x, y, st); break;
-    default: launch_spmv<32>(K, v, x, y, st); break;
-    }
+    spmv_dispatch(spmv_shape(K->n_rows, K->nnz), [&](auto Wc, auto Uc) {
+        constexpr int W = decltype(Wc)::value, U = decltype(Uc)::value;
+        k_spmv<W, U><<<nblk(K->n_rows * W, RT), RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, v, x, y);
+    });
 }
 
-template <int W>
+template <int W, int U>
 void launch_pcg_spmv(const mf_csr *K, const double *p, double *q, double *part, PcgState *S, cudaStream_t st)
 {
-    k_pcg_spmv<W><<<nblk(K->n_rows * W, RT), RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, K->values, p, q, S);
+    k_pcg_spmv<W, U><<<nblk(K->n_rows * W, RT), RT, 0, st>>>(K->n_rows, K->row_ptr, K->col_idx, K->values, p, q, S);
     k_pcg_pq<<<red_grid(K->n_rows), RT, 0, st>>>(K->n_rows, p, q, part, S);
 }
 
@@ -648,7 +661,7 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
     MF_CUDA(cudaStreamSynchronize(st));
     if (hb) return mf_fail(MF_ERR_NONFINITE, "mf_solve: zero or non-finite diagonal entry");
 
-    const int W = spmv_width(n, K->nnz);
+    const SpmvShape shape = spmv_shape(n, K->nnz);
     const int chunk = o->check_every > 0 ? o->check_every : 50;
     // capture `chunk` iterations in a graph on a private stream
     cudaStream_t cs;
@@ -658,13 +671,9 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
     cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
         for (int it = 0; it < chunk; ++it) {
-            switch (W) {
-            case 2: launch_pcg_spmv<2>(K, p.p, q.p, part.p, S.p, cs); break;
-            case 4: launch_pcg_spmv<4>(K, p.p, q.p, part.p, S.p, cs); break;
-            case 8: launch_pcg_spmv<8>(K, p.p, q.p, part.p, S.p, cs); break;
-            case 16: launch_pcg_spmv<16>(K, p.p, q.p, part.p, S.p, cs); break;
-            default: launch_pcg_spmv<32>(K, p.p, q.p, part.p, S.p, cs); break;
-            }
+            spmv_dispatch(shape, [&](auto Wc, auto Uc) {
+                launch_pcg_spmv<decltype(Wc)::value, decltype(Uc)::value>(K, p.p, q.p, part.p, S.p, cs);
+            });
             k_pcg_update<<<red_grid(n), RT, 0, cs>>>(n, dinv.p, p.p, q.p, x, r.p, part.p, S.p);
             k_pcg_dir<<<red_grid(n), RT, 0, cs>>>(n, dinv.p, r.p, p.p, S.p);
         }
@@ -898,17 +907,13 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
     MF_CUDA(cudaStreamSynchronize(st));
     if (hb) return mf_fail(MF_ERR_NONFINITE, "mf_solve_pcg_noalloc: zero or non-finite diagonal entry");
 
-    const int W = spmv_width(n, K->nnz);
+    const SpmvShape shape = spmv_shape(n, K->nnz);
     const int chunk = check_every > 0 ? check_every : 50;
     for (;;) {
         for (int it = 0; it < chunk; ++it) {
-            switch (W) {
-            case 2: launch_pcg_spmv<2>(K, p, q, part, S, st); break;
-            case 4: launch_pcg_spmv<4>(K, p, q, part, S, st); break;
-            case 8: launch_pcg_spmv<8>(K, p, q, part, S, st); break;
-            case 16: launch_pcg_spmv<16>(K, p, q, part, S, st); break;
-            default: launch_pcg_spmv<32>(K, p, q, part, S, st); break;
-            }
+            spmv_dispatch(shape, [&](auto Wc, auto Uc) {
+                launch_pcg_spmv<decltype(Wc)::value, decltype(Uc)::value>(K, p, q, part, S, st);
+            });
             k_pcg_update<<<red_grid(n), RT, 0, st>>>(n, dinv, p, q, x, r, part, S);
             k_pcg_dir<<<red_grid(n), RT, 0, st>>>(n, dinv, r, p, S);
         }
