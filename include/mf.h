@@ -147,12 +147,17 @@ mf_status mf_pattern_destroy(mf_pattern *pattern);
 
 /* Assembles K and d (Block D-2 residual and D-3 tangent, sparse value and
  * residual arrays cleared first) for one form: per element quadrature of the
- * form (Sec. 2.1), then a deterministic fixed-order sum into CSR (no float
- * atomics: two calls give bit-identical K and d), then the Dirichlet
- * elimination.  K->values [nnz] and d [n_rows] are caller device buffers.
- * prec = MF_PREC_MIXED selects the tensor-core element contraction
- * (elasticity on Q1 only).  Errors: MF_ERR_INVALID_ARG, MF_ERR_UNSUPPORTED,
- * MF_ERR_CUDA; non-finite coefficients are latched (MF_ERR_NONFINITE). */
+ * form (Sec. 2.1), then a deterministic sum into CSR (no float atomics: two
+ * calls give bit-identical K and d), then the Dirichlet elimination.
+ * K->values [nnz] and d [n_rows] are caller device buffers.  prec =
+ * MF_PREC_FP64: FP64 element blocks summed node by node in ascending element
+ * order.  prec = MF_PREC_MIXED (elasticity on Q1 only; needs lambda/mu =
+ * 2nu/(1-2nu) = p/q with q <= 64): tensor-core element contraction on BF16
+ * slices, blocks added as exact 64-bit fixed-point integers (integer atomics,
+ * so the order does not change the bits), converted once to FP64; K within
+ * about 2^-40 of the row scale of the FP64 result.  Errors:
+ * MF_ERR_INVALID_ARG, MF_ERR_UNSUPPORTED, MF_ERR_CUDA; non-finite
+ * coefficients are latched (MF_ERR_NONFINITE). */
 mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
                       const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d, void *stream);
 

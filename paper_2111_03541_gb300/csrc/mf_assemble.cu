@@ -2,12 +2,15 @@
 //
 // Two kernels per form.  The element kernel evaluates the quadrature of the
 // form (Sec. 2.1) for one element per thread and writes the element blocks
-// to a scratch array.  The gather kernel then builds every CSR row from the
-// pattern's contribution lists: the contributions of one entry are summed in
-// ascending element order (the paper increments K with atomics in Block D-3;
-// a fixed order makes K bit-reproducible), the strong Dirichlet elimination
-// is applied, and every value of K and d is written exactly once, so no
-// separate clearing pass is needed.
+// to a scratch array.  The gather kernel then builds every CSR row node by
+// node: it walks the node's incident elements in ascending order and adds
+// their rows into a shared-memory row through the pattern's slot maps, so the
+// contributions of one entry are summed in ascending element order (the
+// paper increments K with atomics in Block D-3; a fixed order makes K
+// bit-reproducible); the strong Dirichlet elimination is applied, and every
+// value of K and d is written exactly once, so no separate clearing pass is
+// needed.  (The mixed elasticity path, mf_mixed.cu, adds exact integer
+// blocks with atomics instead.)
 //
 // Forms (K positive; Sec. 4.1-4.3):
 //   thermal   Ke[a][b] = sum_q w detJ k gradN_a . gradN_b,  de[a] = sum_q w detJ f N_a
