@@ -24,6 +24,19 @@ namespace {
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Reference sums of the flow form's degree-2 parts over the 6-point rule, in
+// barycentric derivatives dN_a/dl_i of the P2 basis (pair p of (i, j):
+// (0,0), (1,1), (2,2), (0,1), (0,2), (1,2); off-diagonal pairs hold ij + ji):
+//   c_Ms[p][a][b] = sum_q w_q (dN_a/dl_i dN_b/dl_j + [i != j] dN_a/dl_j dN_b/dl_i)(q)
+//   c_R[j][a1][b] = sum_q w_q l_a1(q) dN_b/dl_j(q)
+// With G_ij = grad l_i . grad l_j, the viscous block
+// D_ab = det sum_p G_p c_Ms[p][a][b] and the divergence blocks
+// B_i[a1][b] = det sum_j (grad l_j)_i c_R[j][a1][b] are the same finite sums
+// as their quadrature, reordered (the integrands have degree 2).
+__constant__ double c_Ms[6][6][6];
+__constant__ double c_R[3][3][6];
+
+
 // ---------------------------------------------------------------------------
 // element kernels
 // ---------------------------------------------------------------------------
@@ -151,63 +164,62 @@ __global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, co
     }
     double *o = out + e * 72;
     {
-        // A = mu D + C: the viscous part D (symmetric, 21 entries) and the
-        // advection part C[a][b] = -rho sum_q w detJ (a_h . grad N_a) N_b are
-        // summed separately, so each FP64 operation does work once
-        double D[21] = {}, Cv[36] = {};
+        // A = mu D + C: the viscous part D from the reference sums, the
+        // advection part C[a][b] = -rho sum_q w detJ (a_h . grad N_a) N_b by
+        // quadrature (a_h varies over the element)
+        double Cv[36] = {};
 #pragma unroll 1
         for (int q = 0; q < 6; ++q) {
             double l[3], w;
             tri6_point(q, l, w);
             double N[6], g[6][2];
             p2_basis(l, gl, N, g);
-            const double wd = w * det;
+            const double wrho = w * det * rho;
             double ah0 = 0.0, ah1 = 0.0;
 #pragma unroll
             for (int b = 0; b < 6; ++b) {
                 ah0 = fma(aN[b][0], N[b], ah0);
                 ah1 = fma(aN[b][1], N[b], ah1);
             }
-            const double wrho = wd * rho;
-            int t = 0;
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
-#pragma unroll
-                for (int b = a; b < 6; ++b, ++t) D[t] = fma(wd, fma(g[a][0], g[b][0], g[a][1] * g[b][1]), D[t]);
                 const double sa = wrho * fma(ah0, g[a][0], ah1 * g[a][1]);
 #pragma unroll
                 for (int b = 0; b < 6; ++b) Cv[6 * a + b] = fma(-sa, N[b], Cv[6 * a + b]);
             }
         }
-        int t = 0;
+        double Gs[6];
+        Gs[0] = fma(gl[0][0], gl[0][0], gl[0][1] * gl[0][1]);
+        Gs[1] = fma(gl[1][0], gl[1][0], gl[1][1] * gl[1][1]);
+        Gs[2] = fma(gl[2][0], gl[2][0], gl[2][1] * gl[2][1]);
+        Gs[3] = fma(gl[0][0], gl[1][0], gl[0][1] * gl[1][1]);
+        Gs[4] = fma(gl[0][0], gl[2][0], gl[0][1] * gl[2][1]);
+        Gs[5] = fma(gl[1][0], gl[2][0], gl[1][1] * gl[2][1]);
+        const double mdet = mu * det;
 #pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-            for (int b = a; b < 6; ++b, ++t) {
-                o[6 * a + b] = fma(mu, D[t], Cv[6 * a + b]);
-                if (b != a) o[6 * b + a] = fma(mu, D[t], Cv[6 * b + a]);
+            for (int b = a; b < 6; ++b) {
+                double Dab = 0.0;
+#pragma unroll
+                for (int pp = 0; pp < 6; ++pp) Dab = fma(Gs[pp], c_Ms[pp][a][b], Dab);
+                o[6 * a + b] = fma(mdet, Dab, Cv[6 * a + b]);
+                if (b != a) o[6 * b + a] = fma(mdet, Dab, Cv[6 * b + a]);
             }
     }
     {
-        double B[36] = {};
-#pragma unroll 1
-        for (int q = 0; q < 6; ++q) {
-            double l[3], w;
-            tri6_point(q, l, w);
-            double N[6], g[6][2];
-            p2_basis(l, gl, N, g);
-            const double wd = w * det;
+        // B_i[a1][b] = det sum_j (grad l_j)_i c_R[j][a1][b]
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double wl = wd * l[a];
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-                for (int i = 0; i < 2; ++i)
+            for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int b = 0; b < 6; ++b) B[18 * i + 6 * a + b] = fma(wl, g[b][i], B[18 * i + 6 * a + b]);
-            }
-        }
+                for (int b = 0; b < 6; ++b) {
+                    double v = 0.0;
 #pragma unroll
-        for (int t = 0; t < 36; ++t) o[36 + t] = B[t];
+                    for (int j = 0; j < 3; ++j) v = fma(gl[j][i], c_R[j][a][b], v);
+                    o[36 + 18 * i + 6 * a + b] = det * v;
+                }
     }
 }
 
@@ -609,6 +621,40 @@ __global__ void k_flow_precond(int64_t n2, int64_t n_rows, const int64_t *__rest
 }
 
 }  // namespace
+
+// Host: the reference sums of the flow form (see c_Ms, c_R), uploaded to the
+// current device's constant memory.
+mf_status mf_flow_consts_upload()
+{
+    double Ms[6][6][6] = {}, R[3][3][6] = {};
+    const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+    const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    for (int q = 0; q < 6; ++q) {
+        const double a = q < 3 ? T6A1 : T6A2, b = 1.0 - 2.0 * a;
+        const int k = q % 3;
+        const double l[3] = {k == 0 ? b : a, k == 1 ? b : a, k == 2 ? b : a};
+        const double w = 0.5 * (q < 3 ? T6W1 : T6W2);
+        double dN[6][3] = {};  // dN_a / dl_i
+        for (int v = 0; v < 3; ++v) dN[v][v] = 4.0 * l[v] - 1.0;
+        for (int e = 0; e < 3; ++e) {
+            dN[3 + e][ep[e][0]] = 4.0 * l[ep[e][1]];
+            dN[3 + e][ep[e][1]] = 4.0 * l[ep[e][0]];
+        }
+        for (int p = 0; p < 6; ++p)
+            for (int x = 0; x < 6; ++x)
+                for (int y = 0; y < 6; ++y) {
+                    double t = dN[x][pi[p]] * dN[y][pj[p]];
+                    if (pi[p] != pj[p]) t += dN[x][pj[p]] * dN[y][pi[p]];
+                    Ms[p][x][y] += w * t;
+                }
+        for (int j = 0; j < 3; ++j)
+            for (int a1 = 0; a1 < 3; ++a1)
+                for (int y = 0; y < 6; ++y) R[j][a1][y] += w * l[a1] * dN[y][j];
+    }
+    MF_CUDA(cudaMemcpyToSymbol(c_Ms, Ms, sizeof Ms));
+    MF_CUDA(cudaMemcpyToSymbol(c_R, R, sizeof R));
+    return MF_OK;
+}
 
 void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
                               const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st)

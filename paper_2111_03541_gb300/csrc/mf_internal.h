@@ -117,6 +117,9 @@ mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_c
                                double p_scale, double *out, cudaStream_t st);
 // elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64
 // sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
+// reference sums of the flow form in the current device's constant memory
+// (once per flow pattern build)
+mf_status mf_flow_consts_upload();
 void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
                               const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);

@@ -641,6 +641,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
                                                          p->adj[1].col, p->adj[2].ptr, p->adj[2].col, p->row_ptr,
                                                          p->col_idx);
         p->scratch_stride = 72;
+        s = mf_flow_consts_upload();
+        if (s != MF_OK) { free_inc(incv, st); return s; }
     }
     MF_CUDA(cudaGetLastError());
     p->inc_ptr = incv.ptr;
