@@ -36,7 +36,7 @@ namespace {
 constexpr int MX_WARPS = 4;          // warps per block; each warp: 4 elements
 constexpr int MX_ELEMS = 4 * MX_WARPS;
 constexpr int NSL = 5;               // BF16 slices of G
-constexpr int SL_ROWS = 32;          // 24 rows padded to two m16 tiles
+constexpr int SL_ROWS = 24;          // rows (a, c) of G; the second m16 row tile's rows 24..31 are zero
 
 struct MixedState {
     int S;         // global fixed-point exponent of K
@@ -220,7 +220,7 @@ struct WarpSmem {
     int32_t tgt[4][36];                     // accumulator pair of block (a <= b); bit 31: transposed
 };
 
-__global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
+__global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
     int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
     double cmu_q, double b0, double b1, double b2, const MixedState *__restrict__ st,
     const int64_t *__restrict__ adj_ptr, const uint8_t *__restrict__ slot, unsigned long long *__restrict__ kacc,
@@ -235,12 +235,6 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
     const int64_t e_raw = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + j;
     const bool valid = e_raw < e1;
     const int64_t e = valid ? e_raw : e1 - 1;
-
-    // padding rows 24..31 of every slice stay zero
-    for (int i = lane; i < 4 * NSL * 8 * 8 / 2; i += 32) {
-        const int el = i / (NSL * 32), r = i % (NSL * 32);
-        reinterpret_cast<uint32_t *>(&W.sl[el][r / 32][24 + (r % 32) / 4][0])[r % 4] = 0u;
-    }
 
     // --- coordinates: d = x_q - x_0 in FP64, then double-float ---
     const int32_t *cn = conn + 8 * e;
@@ -426,8 +420,9 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_mixed_elem(
                 for (int s0 = 0; s0 <= L; s0 += 2) {
                     const int s1 = s0 + 1;  // second half of k: slice s1 against slice L - s1
                     const bool two = s1 <= L;
-                    const uint32_t a0 = ld(s0, mt * 16 + g), a1 = ld(s0, mt * 16 + g + 8);
-                    const uint32_t a2 = two ? ld(s1, mt * 16 + g) : 0u, a3 = two ? ld(s1, mt * 16 + g + 8) : 0u;
+                    // rows 24..31 (second row tile, fragment rows g + 8) are zero
+                    const uint32_t a0 = ld(s0, mt * 16 + g), a1 = mt ? 0u : ld(s0, g + 8);
+                    const uint32_t a2 = two ? ld(s1, mt * 16 + g) : 0u, a3 = (two && !mt) ? ld(s1, g + 8) : 0u;
                     const uint32_t b0 = ld(L - s0, nt * 8 + g), b1 = two ? ld(L - s1, nt * 8 + g) : 0u;
                     mma_bf16(acc[L], a0, a1, a2, a3, b0, b1);
                 }
