@@ -80,6 +80,9 @@ struct mf_pattern {
     long long *kacc = nullptr;
     int32_t *tpos = nullptr;
     long long *dacc = nullptr;  // int64 load vector accumulator (3 per node)
+    // mixed path: geometry part of the fixed-point bound per element, and the
+    // largest element volume at [n_elems] (see mf_mixed.cu)
+    float *mixed_geo = nullptr;
     // mixed path: device scalars of the fixed-point scale (see mf_mixed.cu)
     void *mixed_state = nullptr;
     // elasticity slabs: element chunk c = [slab_e[c], slab_e[c+1]) completes the
@@ -117,6 +120,8 @@ mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_c
                                double p_scale, double *out, cudaStream_t st);
 // elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64
 // sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
+// mixed elasticity: per-element geometry bound, once per pattern
+mf_status mf_mixed_geometry(const mf_mesh *m, mf_pattern *p, cudaStream_t st);
 // reference sums of the flow form in the current device's constant memory
 // (once per flow pattern build)
 mf_status mf_flow_consts_upload();

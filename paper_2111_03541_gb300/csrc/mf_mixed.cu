@@ -148,13 +148,13 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 // ---------------------------------------------------------------------------
 // pre-pass: bound of the fixed-point values (FP32 geometry is enough for a bound)
 // ---------------------------------------------------------------------------
-__global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
-                              const double *__restrict__ Ec, float cmu_q, MixedState *st, int *status)
+// geometry part of the bound, once per mesh: geo[e] = max_row sum_q G^2 of
+// element e for E cmu / q = 1, and geo[n_el] = max_e sum_q detJ_q (float bits)
+__global__ void k_mixed_geom(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                             float *__restrict__ geo)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_el) return;
-    const double E = Ec[e];
-    if (!isfinite(E) || !(E > 0.0)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
     float x[8][3];
     const int32_t *cn = conn + 8 * e;
     for (int a = 0; a < 8; ++a)
@@ -186,7 +186,7 @@ __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const 
         C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
         vol += fabsf(det);
-        const float sc = (float)E * cmu_q / det;  // G^2 = (mu / (q det)) (sum_j dN_j C[c][j])^2
+        const float sc = 1.0f / det;  // G^2 = (mu / (q det)) (sum_j dN_j C[c][j])^2, mu / q = 1
         for (int a = 0; a < 8; ++a)
             for (int c = 0; c < 3; ++c) {
                 const float v = dN[a][0] * C[c][0] + dN[a][1] * C[c][1] + dN[a][2] * C[c][2];
@@ -195,9 +195,27 @@ __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const 
     }
     float mx = 0.f;
     for (int r = 0; r < 24; ++r) mx = fmaxf(mx, rowsum[r]);
-    if (!isfinite(mx)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
-    atomicMax(&st->mx_bits, __float_as_int(mx));
-    atomicMax(&st->vol_bits, __float_as_int(vol));
+    geo[e] = mx;
+    atomicMax(reinterpret_cast<int *>(geo + n_el), __float_as_int(vol));
+}
+
+// per assembly: the bound max_e E_e cmu / q geo[e] (one atomic per warp)
+__global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ Ec, const float *__restrict__ geo,
+                              float cmu_q, MixedState *st, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float mx = 0.f;
+    if (e < n_el) {
+        const double E = Ec[e];
+        if (!isfinite(E) || !(E > 0.0)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        else mx = (float)E * cmu_q * geo[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) {
+        if (!isfinite(mx)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        else if (mx > 0.f) atomicMax(&st->mx_bits, __float_as_int(mx));
+    }
+    if (e == 0) st->vol_bits = __float_as_int(geo[n_el]);
 }
 
 // S = floor(62 - log2(8 (p + 4q) Mx 1.25)): every element value |K_e| <=
@@ -538,6 +556,16 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
 
 }  // namespace
 
+mf_status mf_mixed_geometry(const mf_mesh *m, mf_pattern *p, cudaStream_t st)
+{
+    const int64_t ne = m->n_elems;
+    MF_CUDA(cudaMallocAsync(&p->mixed_geo, sizeof(float) * (ne + 1), st));
+    MF_CUDA(cudaMemsetAsync(p->mixed_geo + ne, 0, sizeof(float), st));
+    if (ne > 0) k_mixed_geom<<<(unsigned)((ne + 127) / 128), 128, 0, st>>>(ne, m->coords, m->conn, p->mixed_geo);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
 mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c, double *values,
                             double *d, cudaStream_t st)
 {
@@ -566,8 +594,8 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     const int64_t ne = m->n_elems;
     mf_prof_begin("mixed_bound", st);
     MF_CUDA(cudaMemsetAsync(ms, 0, sizeof(MixedState), st));
-    k_mixed_bound<<<(unsigned)((ne + 127) / 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, (float)cmu_q,
-                                                                ms, status);
+    k_mixed_bound<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, c->elem_coef, p->mixed_geo, (float)cmu_q, ms,
+                                                                status);
     const double bmax = fmax(fabs(c->source[0]), fmax(fabs(c->source[1]), fabs(c->source[2])));
     k_mixed_scale<<<1, 1, 0, st>>>(ms, pp, qq, bmax);
     mf_prof_end(st);

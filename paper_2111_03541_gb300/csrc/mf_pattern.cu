@@ -497,6 +497,8 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->slot);
     cudaFree(p->kacc);
     cudaFree(p->tpos);
+    cudaFree(p->mixed_geo);
+    p->mixed_geo = nullptr;
     cudaFree(p->dacc);
     p->dacc = nullptr;
     p->kacc = nullptr;
@@ -589,6 +591,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_slot_map<<<nblk(m->n_elems * 64), TPB, 0, st>>>(m->n_elems, 8, m->conn, p->adj[0].ptr, p->adj[0].col,
                                                            p->slot);
         MF_CUDA(cudaMallocAsync(&p->mixed_state, 64, st));
+        s = mf_mixed_geometry(m, p, st);
+        if (s != MF_OK) { free_inc(incv, st); return s; }
         MF_CUDA(cudaMallocAsync(&p->tpos, sizeof(int32_t) * p->adj[0].n_pairs, st));
         k_tpos<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->tpos);
         MF_CUDA(cudaMallocAsync(&p->kacc, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
