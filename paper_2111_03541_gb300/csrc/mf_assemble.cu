@@ -278,8 +278,8 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
     int64_t n0, int64_t n1, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
     const uint8_t *__restrict__ slot, const double *__restrict__ sc, int64_t stride, const int *__restrict__ scale,
-    int fp, int fq, const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
-    double *__restrict__ values, double *__restrict__ d)
+    int fp, int fq, const uint8_t *__restrict__ mask, const double *__restrict__ bval,
+    const int64_t *__restrict__ row_ptr, double *__restrict__ values, double *__restrict__ d)
 {
     __shared__ T acc_all[GEL_WARPS][MF_MAX_DEG * 9];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -692,7 +692,10 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
     const int64_t ne = m->n_elems;
     if (form == MF_FORM_THERMAL) {
         const double f = c->source[0];
-        mf_prof_begin(m->elem == MF_P1_TRI ? "elem_thermal_p1" : (m->elem == MF_P2_TRI ? "elem_thermal_p2" : "elem_thermal_q1"), st);
+        mf_prof_begin(m->elem == MF_P1_TRI   ? "elem_thermal_p1"
+                      : m->elem == MF_P2_TRI ? "elem_thermal_p2"
+                                             : "elem_thermal_q1",
+                      st);
         if (m->elem == MF_P1_TRI)
             k_elem_thermal_p1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
                                                              p->scratch, status);

@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(256) k_conv_bwd_weight(int B, int nz, int ny, 
 #pragma unroll
             for (int o = 0; o < 27; ++o) {
                 int u;
-                if (nb_index(v, o, nz, ny, nx, u)) acc[o] = fmaf(gv, __bfloat162float(base[(int64_t)u * CI + ci]), acc[o]);
+                if (nb_index(v, o, nz, ny, nx, u))
+                    acc[o] = fmaf(gv, __bfloat162float(base[(int64_t)u * CI + ci]), acc[o]);
             }
         }
     const int nw = CO * CI * 27;

@@ -73,12 +73,14 @@ struct mf_pattern {
     uint8_t *tr = nullptr;
     double *kref = nullptr;
     int64_t n_translate = 0;
-    // elasticity, mixed path: int64 3x3 block accumulator per node pair
-    // (9 x n_pairs; only pairs (n, m) with n <= m are written, the diagonal
-    // blocks as their upper triangles) and, per node pair, the index of the
-    // transposed pair (m, n)
+    // elasticity, mixed path: int64 3x3 block accumulator per upper node pair
+    // (n, m >= n; a diagonal block as its upper triangle), numbered compactly:
+    // upper pair (n, slot k) is block cbase[n] + k; tpos gives, for a lower
+    // pair (n, m < n), the number of the upper pair (m, n) (-1 otherwise)
     long long *kacc = nullptr;
     int32_t *tpos = nullptr;
+    int64_t *cbase = nullptr;
+    int64_t n_upper = 0;
     long long *dacc = nullptr;  // int64 load vector accumulator (3 per node)
     // mixed path: geometry part of the fixed-point bound per element, and the
     // largest element volume at [n_elems] (see mf_mixed.cu)
@@ -153,25 +155,24 @@ mf_status mf_slab_pipeline(const mf_pattern *p, cudaStream_t st, Elem elem, Gath
 {
     const size_t nsl = p->slab_e.size() - 1;
     const bool two = nsl > 1 && p->side;
+    auto fail = [](const char *what) { return mf_cuda_check(cudaGetLastError(), what); };
     if (two) {
-        if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
-        if (cudaStreamWaitEvent(p->side, p->fork_ev, 0) != cudaSuccess)
-            return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+        if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return fail("mf_assemble");
+        if (cudaStreamWaitEvent(p->side, p->fork_ev, 0) != cudaSuccess) return fail("mf_assemble");
     }
     for (size_t k = 0; k < nsl; ++k) {
         mf_status s = elem(k, st);
         if (s != MF_OK) return s;
         if (two) {
-            if (cudaEventRecord(p->slab_ev[k], st) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
-            if (cudaStreamWaitEvent(p->side, p->slab_ev[k], 0) != cudaSuccess)
-                return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+            if (cudaEventRecord(p->slab_ev[k], st) != cudaSuccess) return fail("mf_assemble");
+            if (cudaStreamWaitEvent(p->side, p->slab_ev[k], 0) != cudaSuccess) return fail("mf_assemble");
         }
         s = gather(k, two ? p->side : st);
         if (s != MF_OK) return s;
     }
     if (two) {
-        if (cudaEventRecord(p->join_ev, p->side) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
-        if (cudaStreamWaitEvent(st, p->join_ev, 0) != cudaSuccess) return mf_cuda_check(cudaGetLastError(), "mf_assemble");
+        if (cudaEventRecord(p->join_ev, p->side) != cudaSuccess) return fail("mf_assemble");
+        if (cudaStreamWaitEvent(st, p->join_ev, 0) != cudaSuccess) return fail("mf_assemble");
     }
     return MF_OK;
 }

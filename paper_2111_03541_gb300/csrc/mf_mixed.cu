@@ -239,9 +239,10 @@ struct WarpSmem {
 };
 
 __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
-    int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn, const double *__restrict__ Ec,
+    int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn,
+    const double *__restrict__ Ec,
     double cmu_q, double b0, double b1, double b2, const MixedState *__restrict__ st,
-    const int64_t *__restrict__ adj_ptr, const uint8_t *__restrict__ slot, unsigned long long *__restrict__ kacc,
+    const int64_t *__restrict__ cbase, const uint8_t *__restrict__ slot, unsigned long long *__restrict__ kacc,
     unsigned long long *__restrict__ dacc, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -408,8 +409,8 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
         int32_t tg = 0;
         if (eo < e1) {
             const int32_t na = conn[8 * eo + a], nb = conn[8 * eo + b];
-            tg = na <= nb ? (int32_t)(adj_ptr[na] + slot[eo * 64 + a * 8 + b])
-                          : (int32_t)((adj_ptr[nb] + slot[eo * 64 + b * 8 + a]) | 0x80000000ll);
+            tg = na <= nb ? (int32_t)(cbase[na] + slot[eo * 64 + a * 8 + b])
+                          : (int32_t)((cbase[nb] + slot[eo * 64 + b * 8 + a]) | 0x80000000ll);
         }
         W.tgt[el][u] = tg;
     }
@@ -489,7 +490,8 @@ constexpr int FN_WARPS = 8;
 
 __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
     int64_t n_begin, int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
-    const int32_t *__restrict__ tpos, const long long *__restrict__ kacc, const long long *__restrict__ dacc,
+    const int32_t *__restrict__ tpos, const int64_t *__restrict__ cbase, const long long *__restrict__ kacc,
+    const long long *__restrict__ dacc,
     const MixedState *__restrict__ st, int fp, int fq, const uint8_t *__restrict__ mask,
     const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
     double *__restrict__ d)
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
     double lift[3] = {0.0, 0.0, 0.0};
     for (int k = lane; k < deg; k += 32) {
         const int32_t mcol = adj_col[p0 + k];
-        const int64_t src = mcol < n ? (int64_t)tpos[p0 + k] : p0 + k;
+        const int64_t src = mcol < n ? (int64_t)tpos[p0 + k] : cbase[n] + k;
         const long long *B = kacc + src * 9;
         long long b[9];
 #pragma unroll
@@ -603,7 +605,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // element blocks go straight into the int64 block accumulator (atomics:
     // exact, so order-free); the finishing gather then writes each CSR row once
-    MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
+    MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->n_upper, st));
     MF_CUDA(cudaMemsetAsync(p->dacc, 0, sizeof(long long) * 3 * m->n_nodes, st));
     // element chunks on the caller's stream; with more than one chunk the
     // finishing of the nodes a chunk completes runs on the side stream
@@ -615,7 +617,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
             mf_prof_begin("mixed_elem", s2);
             k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, s2>>>(
                 e0, e1, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms,
-                p->adj[0].ptr, p->slot, reinterpret_cast<unsigned long long *>(p->kacc),
+                p->cbase, p->slot, reinterpret_cast<unsigned long long *>(p->kacc),
                 reinterpret_cast<unsigned long long *>(p->dacc), status);
             mf_prof_end(s2);
             MF_CUDA(cudaGetLastError());
@@ -626,7 +628,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
             if (n1 > n0) {
                 mf_prof_begin("mixed_finish", s2);
                 k_mixed_finish<<<(unsigned)((n1 - n0 + FN_WARPS - 1) / FN_WARPS), FN_WARPS * 32, 0, s2>>>(
-                    n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->kacc, p->dacc, ms, pp, qq, c->bc_mask,
+                    n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->cbase, p->kacc, p->dacc, ms, pp, qq, c->bc_mask,
                     c->bc_val, p->row_ptr, values, d);
                 mf_prof_end(s2);
             }

@@ -176,13 +176,39 @@ __global__ void k_node_ready(int64_t n, const int64_t *__restrict__ inc_ptr, con
     ready[v] = inc_ptr[v + 1] > inc_ptr[v] ? inc[inc_ptr[v + 1] - 1] : -1;
 }
 
-// tpos[p] = index of the pair (m, n) for the pair p = (n, m)
-__global__ void k_tpos(int64_t n_nodes, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                       int32_t *__restrict__ tpos)
+// Upper node pairs (n, m >= n) in a compact numbering: they are the tail of
+// n's sorted neighbour list from the diagonal on, so upper pair (n, slot k)
+// is number cbase[n] + k with cbase[n] = (upper pairs of nodes < n) - the
+// diagonal's slot.  First the count of each node's upper pairs:
+__global__ void k_upper_count(int64_t n_nodes, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                              int64_t *__restrict__ cnt, int64_t *__restrict__ kdiag)
 {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= n_nodes) return;
-    for (int64_t p = ptr[n]; p < ptr[n + 1]; ++p) tpos[p] = (int32_t)find_pair(ptr, col, col[p], (int32_t)n);
+    int64_t kd = 0;
+    for (int64_t p = ptr[n]; p < ptr[n + 1]; ++p)
+        if (col[p] == (int32_t)n) kd = p - ptr[n];
+    kdiag[n] = kd;
+    cnt[n] = (ptr[n + 1] - ptr[n]) - kd;
+}
+
+__global__ void k_upper_base(int64_t n_nodes, const int64_t *__restrict__ scan, int64_t *__restrict__ cbase)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    cbase[n] = scan[n] - cbase[n];  // cbase holds the diagonal slots on entry
+}
+
+// tpos[p] = compact number of the upper pair (m, n) for a lower pair p = (n, m < n)
+__global__ void k_tpos(int64_t n_nodes, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                       const int64_t *__restrict__ cbase, int32_t *__restrict__ tpos)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    for (int64_t p = ptr[n]; p < ptr[n + 1]; ++p) {
+        const int32_t m = col[p];
+        tpos[p] = m < n ? (int32_t)(cbase[m] + (find_pair(ptr, col, m, (int32_t)n) - ptr[m])) : -1;
+    }
 }
 
 // incidence slot map: for incidence entry t of row node n (element e),
@@ -497,6 +523,9 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->slot);
     cudaFree(p->kacc);
     cudaFree(p->tpos);
+    cudaFree(p->cbase);
+    p->cbase = nullptr;
+    p->n_upper = 0;
     cudaFree(p->mixed_geo);
     p->mixed_geo = nullptr;
     cudaFree(p->dacc);
@@ -593,9 +622,23 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         MF_CUDA(cudaMallocAsync(&p->mixed_state, 64, st));
         s = mf_mixed_geometry(m, p, st);
         if (s != MF_OK) { free_inc(incv, st); return s; }
+        {
+            // compact numbering of the upper node pairs (the accumulator's blocks)
+            const int64_t nn = m->n_nodes;
+            int64_t *cnt = nullptr;
+            MF_CUDA(cudaMallocAsync(&cnt, sizeof(int64_t) * (nn + 1), st));
+            MF_CUDA(cudaMallocAsync(&p->cbase, sizeof(int64_t) * (nn + 1), st));
+            MF_CUDA(cudaMemsetAsync(cnt + nn, 0, sizeof(int64_t), st));
+            k_upper_count<<<nblk(nn), TPB, 0, st>>>(nn, p->adj[0].ptr, p->adj[0].col, cnt, p->cbase);
+            MF_CUDA(mf_scan_i64(cnt, nn + 1, nullptr, st));
+            k_upper_base<<<nblk(nn), TPB, 0, st>>>(nn, cnt, p->cbase);
+            s = read_i64(cnt + nn, &p->n_upper, st);
+            MF_CUDA(cudaFreeAsync(cnt, st));
+            if (s != MF_OK) { free_inc(incv, st); return s; }
+        }
         MF_CUDA(cudaMallocAsync(&p->tpos, sizeof(int32_t) * p->adj[0].n_pairs, st));
-        k_tpos<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->tpos);
-        MF_CUDA(cudaMallocAsync(&p->kacc, sizeof(long long) * 9 * p->adj[0].n_pairs, st));
+        k_tpos<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->cbase, p->tpos);
+        MF_CUDA(cudaMallocAsync(&p->kacc, sizeof(long long) * 9 * p->n_upper, st));
         MF_CUDA(cudaMallocAsync(&p->dacc, sizeof(long long) * 3 * m->n_nodes, st));
         p->scratch_stride = 36 * 9 + 24;
         mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);

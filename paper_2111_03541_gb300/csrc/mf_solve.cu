@@ -37,7 +37,10 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // grid of the reduction kernels: a function of n only (bit-reproducible), at
 // least 512 rows per block so small systems do not pay for idle blocks
-inline unsigned red_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (n + 511) / 512)); }
+inline unsigned red_grid(int64_t n)
+{
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (n + 511) / 512));
+}
 
 __device__ double block_sum(double v, double *sh)
 {
@@ -123,7 +126,8 @@ __device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const 
 }
 
 template <int W, int U>
-__global__ void __launch_bounds__(RT, U <= 6 ? 5 : 4) k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void __launch_bounds__(RT, U <= 6 ? 5 : 4) k_spmv(int64_t n, const int64_t *__restrict__ rp,
+                                                             const int32_t *__restrict__ ci,
                                              const double *__restrict__ v, const double *__restrict__ x,
                                              double *__restrict__ y)
 {
@@ -878,7 +882,8 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
     if (K->n_rows > MF_NOALLOC_MAX_ROWS)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: %lld rows exceed MF_NOALLOC_MAX_ROWS = %d",
                        (long long)K->n_rows, MF_NOALLOC_MAX_ROWS);
-    if (!(tol > 0.0) || max_iter < 0) return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: tol > 0, max_iter >= 0");
+    if (!(tol > 0.0) || max_iter < 0)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: tol > 0, max_iter >= 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int *status = mf_status_word();
     if (!status) return mf_fail(MF_ERR_CUDA, "mf_solve_pcg_noalloc: status word unavailable");
@@ -931,7 +936,8 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
         info->converged = h.done == 1;
     }
     s = MF_OK;
-    if (h.done == 2) s = mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve_pcg_noalloc: %lld iterations, residual %.3e", h.iter, relres);
+    if (h.done == 2)
+        s = mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve_pcg_noalloc: %lld iterations, residual %.3e", h.iter, relres);
     if (h.done == 3) s = mf_fail(MF_ERR_NONFINITE, "mf_solve_pcg_noalloc: breakdown or non-finite value");
     return finish_status(s, status, st);
 }
