@@ -24,17 +24,6 @@ namespace {
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Reference sums of the flow form's degree-2 parts over the 6-point rule, in
-// barycentric derivatives dN_a/dl_i of the P2 basis (pair p of (i, j):
-// (0,0), (1,1), (2,2), (0,1), (0,2), (1,2); off-diagonal pairs hold ij + ji):
-//   c_Ms[p][a][b] = sum_q w_q (dN_a/dl_i dN_b/dl_j + [i != j] dN_a/dl_j dN_b/dl_i)(q)
-//   c_R[j][a1][b] = sum_q w_q l_a1(q) dN_b/dl_j(q)
-// With G_ij = grad l_i . grad l_j, the viscous block
-// D_ab = det sum_p G_p c_Ms[p][a][b] and the divergence blocks
-// B_i[a1][b] = det sum_j (grad l_j)_i c_R[j][a1][b] are the same finite sums
-// as their quadrature, reordered (the integrands have degree 2).
-__constant__ double c_Ms[6][6][6];
-__constant__ double c_R[3][3][6];
 
 
 // ---------------------------------------------------------------------------
@@ -622,39 +611,8 @@ __global__ void k_flow_precond(int64_t n2, int64_t n_rows, const int64_t *__rest
 
 }  // namespace
 
-// Host: the reference sums of the flow form (see c_Ms, c_R), uploaded to the
-// current device's constant memory.
-mf_status mf_flow_consts_upload()
-{
-    double Ms[6][6][6] = {}, R[3][3][6] = {};
-    const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
-    const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
-    for (int q = 0; q < 6; ++q) {
-        const double a = q < 3 ? T6A1 : T6A2, b = 1.0 - 2.0 * a;
-        const int k = q % 3;
-        const double l[3] = {k == 0 ? b : a, k == 1 ? b : a, k == 2 ? b : a};
-        const double w = 0.5 * (q < 3 ? T6W1 : T6W2);
-        double dN[6][3] = {};  // dN_a / dl_i
-        for (int v = 0; v < 3; ++v) dN[v][v] = 4.0 * l[v] - 1.0;
-        for (int e = 0; e < 3; ++e) {
-            dN[3 + e][ep[e][0]] = 4.0 * l[ep[e][1]];
-            dN[3 + e][ep[e][1]] = 4.0 * l[ep[e][0]];
-        }
-        for (int p = 0; p < 6; ++p)
-            for (int x = 0; x < 6; ++x)
-                for (int y = 0; y < 6; ++y) {
-                    double t = dN[x][pi[p]] * dN[y][pj[p]];
-                    if (pi[p] != pj[p]) t += dN[x][pj[p]] * dN[y][pi[p]];
-                    Ms[p][x][y] += w * t;
-                }
-        for (int j = 0; j < 3; ++j)
-            for (int a1 = 0; a1 < 3; ++a1)
-                for (int y = 0; y < 6; ++y) R[j][a1][y] += w * l[a1] * dN[y][j];
-    }
-    MF_CUDA(cudaMemcpyToSymbol(c_Ms, Ms, sizeof Ms));
-    MF_CUDA(cudaMemcpyToSymbol(c_R, R, sizeof R));
-    return MF_OK;
-}
+// Host: the reference sums (c_Ms, c_R) in this file's constant memory
+mf_status mf_flow_consts_upload() { return fem_consts_upload(); }
 
 void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
                               const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st)

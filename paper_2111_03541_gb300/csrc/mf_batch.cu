@@ -258,6 +258,13 @@ extern "C" mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, co
         cnt[m->elem] += m->n_elems;
         nodes += m->n_nodes;
     }
+    if (cnt[MF_P2_TRI] > 0) {
+        mf_status su = fem_consts_upload();  // this file's copy of the P2 reference sums
+        if (su != MF_OK) {
+            delete b;
+            return su;
+        }
+    }
     char sig[256];
     snprintf(sig, sizeof sig, "n%d_p1_%lld_p2_%lld_q1_%lld_nodes_%lld", n, cnt[0], cnt[1], cnt[2], nodes);
     b->signature = sig;

@@ -60,6 +60,62 @@ __device__ __forceinline__ double q1_jac(const double (&x)[8][3], int q, double 
     return det;
 }
 
+// Coefficients of the trilinear map x(xi) = sum_a x_a N_a(xi) = sum_S c_S
+// prod_{k in S} xi_k, from a fast Walsh-Hadamard transform over the corners:
+// H[S] = sum_a (-1)^popc(a & S) x_a, c_S = (-1)^popc(S) H[S] / 8 (S a bit set
+// of xi = 1, eta = 2, zeta = 4).  Returns H (the caller tests H[3], H[5],
+// H[6], H[7] = 0 for a parallelepiped).
+__device__ __forceinline__ void q1_wht(const double (&x)[8][3], double (&H)[8][3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double v[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) v[a] = x[a][i];
+#pragma unroll
+        for (int m = 1; m < 8; m <<= 1)
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+                if (!(a & m)) {
+                    const double t = v[a], u = v[a | m];
+                    v[a] = t + u;
+                    v[a | m] = t - u;
+                }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) H[a][i] = v[a];
+    }
+}
+
+// J^-1 and detJ at Gauss point q from the map coefficients c (c[S][i] as
+// above): column j of J is d x / d xi_j = sum_{S containing j} c_S prod_{k in
+// S, k != j} xi_k, three FMAs per entry.
+__device__ __forceinline__ double q1_jac_coef(const double (&c)[8][3], int q, double (&Ji)[3][3])
+{
+    const double xs = (q & 1) ? QG : -QG, ys = (q & 2) ? QG : -QG, zs = (q & 4) ? QG : -QG;
+    double J[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        J[i][0] = fma(zs, fma(ys, c[7][i], c[5][i]), fma(ys, c[3][i], c[1][i]));
+        J[i][1] = fma(zs, fma(xs, c[7][i], c[6][i]), fma(xs, c[3][i], c[2][i]));
+        J[i][2] = fma(ys, fma(xs, c[7][i], c[6][i]), fma(xs, c[5][i], c[4][i]));
+    }
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double r = 1.0 / det;
+    Ji[0][0] = c00 * r;
+    Ji[1][0] = c01 * r;
+    Ji[2][0] = c02 * r;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+    return det;
+}
+
 // affine triangle from its first three nodes: detJ and grad lambda_k
 __device__ __forceinline__ double tri_affine(const double *__restrict__ X, const int32_t *__restrict__ c,
                                              double (&gl)[3][2])
@@ -109,6 +165,53 @@ __device__ __forceinline__ void tri6_point(int q, double (&l)[3], double &w)
 }
 
 __device__ __forceinline__ int upair(int a, int b) { return a * (15 - a) / 2 + b; }  // a <= b < 8
+
+// Reference sums of degree-2 P2 integrands over the 6-point rule, in
+// barycentric derivatives dN_a/dl_i of the P2 basis (pair p of (i, j):
+// (0,0), (1,1), (2,2), (0,1), (0,2), (1,2); off-diagonal pairs hold ij + ji):
+//   c_Ms[p][a][b] = sum_q w_q (dN_a/dl_i dN_b/dl_j + [i != j] dN_a/dl_j dN_b/dl_i)(q)
+//   c_R[j][a1][b] = sum_q w_q l_a1(q) dN_b/dl_j(q)
+// With G_ij = grad l_i . grad l_j, the viscous block
+// D_ab = det sum_p G_p c_Ms[p][a][b] and the divergence blocks
+// B_i[a1][b] = det sum_j (grad l_j)_i c_R[j][a1][b] are the same finite sums
+// as their quadrature, reordered (the integrands have degree 2).
+__constant__ double c_Ms[6][6][6];
+__constant__ double c_R[3][3][6];
+
+// Host: the reference sums, uploaded to this translation unit's copy of c_Ms
+// and c_R on the current device (each file that includes this header and
+// launches a kernel using them uploads its own copy).
+inline mf_status fem_consts_upload()
+{
+    double Ms[6][6][6] = {}, R[3][3][6] = {};
+    const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+    const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    for (int q = 0; q < 6; ++q) {
+        const double a = q < 3 ? T6A1 : T6A2, b = 1.0 - 2.0 * a;
+        const int k = q % 3;
+        const double l[3] = {k == 0 ? b : a, k == 1 ? b : a, k == 2 ? b : a};
+        const double w = 0.5 * (q < 3 ? T6W1 : T6W2);
+        double dN[6][3] = {};  // dN_a / dl_i
+        for (int v = 0; v < 3; ++v) dN[v][v] = 4.0 * l[v] - 1.0;
+        for (int e = 0; e < 3; ++e) {
+            dN[3 + e][ep[e][0]] = 4.0 * l[ep[e][1]];
+            dN[3 + e][ep[e][1]] = 4.0 * l[ep[e][0]];
+        }
+        for (int p = 0; p < 6; ++p)
+            for (int x = 0; x < 6; ++x)
+                for (int y = 0; y < 6; ++y) {
+                    double t = dN[x][pi[p]] * dN[y][pj[p]];
+                    if (pi[p] != pj[p]) t += dN[x][pj[p]] * dN[y][pi[p]];
+                    Ms[p][x][y] += w * t;
+                }
+        for (int j = 0; j < 3; ++j)
+            for (int a1 = 0; a1 < 3; ++a1)
+                for (int y = 0; y < 6; ++y) R[j][a1][y] += w * l[a1] * dN[y][j];
+    }
+    MF_CUDA(cudaMemcpyToSymbol(c_Ms, Ms, sizeof Ms));
+    MF_CUDA(cudaMemcpyToSymbol(c_R, R, sizeof R));
+    return MF_OK;
+}
 
 // Output of a thermal element routine.  With an incidence map, row a of
 // element e goes to incidence entry t = map[e * NPE + a] of node conn[e][a] as
@@ -162,34 +265,32 @@ __device__ __forceinline__ void elem_thermal_p2(int64_t e, const double *__restr
     if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
     double gl[3][2];
     const double det = tri_affine(X, conn + 6 * e, gl);
-    double Ke[21] = {}, de[6] = {};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        // degree-2 interior rule: (2/3, 1/6, 1/6) and permutations, weight 1/6
-        double l[3] = {1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
-        l[q] = 2.0 / 3.0;
-        double N[6], g[6][2];
-        p2_basis(l, gl, N, g);
-        const double wd = det * (1.0 / 6.0);
-        int t = 0;
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-#pragma unroll
-            for (int b = a; b < 6; ++b, ++t) Ke[t] = fma(wd, g[a][0] * g[b][0] + g[a][1] * g[b][1], Ke[t]);
-            de[a] = fma(wd, N[a], de[a]);
-        }
-    }
+    // K_e = k det sum_p G_p c_Ms[p] (the integrand grad N_a . grad N_b has
+    // degree 2: the quadrature sum reordered, see c_Ms); the load of a vertex
+    // node integrates to 0, of an edge node to det / 6 (exact sums of the
+    // degree-2 rule)
+    double Gs[6];
+    Gs[0] = fma(gl[0][0], gl[0][0], gl[0][1] * gl[0][1]);
+    Gs[1] = fma(gl[1][0], gl[1][0], gl[1][1] * gl[1][1]);
+    Gs[2] = fma(gl[2][0], gl[2][0], gl[2][1] * gl[2][1]);
+    Gs[3] = fma(gl[0][0], gl[1][0], gl[0][1] * gl[1][1]);
+    Gs[4] = fma(gl[0][0], gl[2][0], gl[0][1] * gl[2][1]);
+    Gs[5] = fma(gl[1][0], gl[2][0], gl[1][1] * gl[2][1]);
+    const double kd = k * det;
     const ThOut<6> W(map, e);
-    int t = 0;
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
-        for (int b = a; b < 6; ++b, ++t) {
-            out[W.base[a] + b] = k * Ke[t];
-            out[W.base[b] + a] = k * Ke[t];
-        }
+        for (int b = a; b < 6; ++b) {
+            double v = 0.0;
 #pragma unroll
-    for (int a = 0; a < 6; ++a) out[W.ld[a]] = f * de[a];
+            for (int p = 0; p < 6; ++p) v = fma(Gs[p], c_Ms[p][a][b], v);
+            out[W.base[a] + b] = kd * v;
+            out[W.base[b] + a] = kd * v;
+        }
+    const double le = f * det * (1.0 / 6.0);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) out[W.ld[a]] = a < 3 ? 0.0 : le;
 }
 
 __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restrict__ X,
@@ -210,27 +311,19 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
     // Gauss sums factor: sum_q dN_a/dxi_i dN_b/dxi_j = R_ab[i][j] (closed form
     // below), so Ke[a][b] = k detJ sum_ij R_ab[i][j] (J^-1 J^-T)_ij and
     // de[a] = f detJ sum_q N_a(q) with sum_q N_a(q) = 1.
-    double cf[4][3];  // coefficients of xi eta, eta zeta, xi zeta, xi eta zeta (times 8)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        cf[0][i] = cf[1][i] = cf[2][i] = cf[3][i] = 0.0;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const double sa = (a & 1) ? 1.0 : -1.0, ta = (a & 2) ? 1.0 : -1.0, ua = (a & 4) ? 1.0 : -1.0;
-            cf[0][i] += sa * ta * x[a][i];
-            cf[1][i] += ta * ua * x[a][i];
-            cf[2][i] += sa * ua * x[a][i];
-            cf[3][i] += sa * ta * ua * x[a][i];
-        }
-    }
+    double c[8][3];  // map coefficients c_S (q1_wht)
+    q1_wht(x, c);
     bool affine = true;
 #pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2)
+    for (int i = 0; i < 3; ++i)
+        affine = affine && c[3][i] == 0.0 && c[5][i] == 0.0 && c[6][i] == 0.0 && c[7][i] == 0.0;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) affine = affine && cf[k2][i] == 0.0;
+    for (int S = 1; S < 8; ++S)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c[S][i] *= (__popc(S) & 1) ? -0.125 : 0.125;
     if (affine) {
         double Ji[3][3];
-        const double det = q1_jac(x, 0, Ji);  // constant over the element
+        const double det = q1_jac_coef(c, 0, Ji);  // constant over the element
         double G[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -273,7 +366,7 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         double Ji[3][3];
-        const double wd = q1_jac(x, q, Ji);  // Gauss weights are 1
+        const double wd = q1_jac_coef(c, q, Ji);  // Gauss weights are 1
         double g[8][3];
 #pragma unroll
         for (int a = 0; a < 8; ++a)
@@ -301,6 +394,7 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
 #pragma unroll
     for (int a = 0; a < 8; ++a) out[W.ld[a]] = f * m[a];
 }
+
 
 
 // Thermal translate shortcut (Q1): true when element e is a translate of
