@@ -81,11 +81,18 @@ __global__ void __launch_bounds__(EL_T) k_elem_elastic_q1(int64_t e0, int64_t e1
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
+    // map coefficients (q1_wht), so that J at a Gauss point costs 27 FMAs
+    double c[8][3];
+    q1_wht(x, c);
+#pragma unroll
+    for (int S = 1; S < 8; ++S)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c[S][i] *= (__popc(S) & 1) ? -0.125 : 0.125;
     double m[8] = {};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         double Ji[3][3];
-        const double wd = q1_jac(x, q, Ji);
+        const double wd = q1_jac_coef(c, q, Ji);
         const double sw = sqrt(wd);
 #pragma unroll
         for (int a = 0; a < 8; ++a) {

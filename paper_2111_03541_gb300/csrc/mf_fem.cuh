@@ -31,35 +31,6 @@ __device__ __forceinline__ double q1_n(int q, int a)
     return 0.125 * (1.0 + s[0] * xs[0]) * (1.0 + s[1] * xs[1]) * (1.0 + s[2] * xs[2]);
 }
 
-// Jacobian of the trilinear map at Gauss point q, its determinant and inverse
-__device__ __forceinline__ double q1_jac(const double (&x)[8][3], int q, double (&Ji)[3][3])
-{
-    double J[3][3] = {};
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const double dn = q1_dref(q, a, j);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) J[i][j] = fma(x[a][i], dn, J[i][j]);
-        }
-    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-    const double r = 1.0 / det;
-    Ji[0][0] = c00 * r;
-    Ji[1][0] = c01 * r;
-    Ji[2][0] = c02 * r;
-    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
-    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
-    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
-    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
-    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
-    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
-    return det;
-}
-
 // Coefficients of the trilinear map x(xi) = sum_a x_a N_a(xi) = sum_S c_S
 // prod_{k in S} xi_k, from a fast Walsh-Hadamard transform over the corners:
 // H[S] = sum_a (-1)^popc(a & S) x_a, c_S = (-1)^popc(S) H[S] / 8 (S a bit set
