@@ -38,13 +38,14 @@ FCG_DIRS = 256  # stored directions of the flexible CG with the learned precondi
 # ncu counters of the mixed element kernel (one launch, 48^3 case, 110,592
 # elements; both grow in proportion to the elements): executed warp
 # instructions (smsp__inst_executed.sum = 274,102,359) and DRAM traffic
-# (dram__bytes_read.sum + dram__bytes_write.sum = 132.16 MB + 70.18 MB), with
-# the SHA-256 prefix of the sources that capture was built from: the line
-# reports null for them once those sources change.
+# (dram__bytes_read.sum + dram__bytes_write.sum = 132.16 MB + 70.16 MB), with
+# the SHA-256 prefix of the files that hold the kernel's code (mf_mixed.cu and
+# the device helpers it calls): the line reports null for them once those
+# files change.
 MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 274102359 / 110592,
-                  "bytes_per_element": (132.16e6 + 70.18e6) / 110592,
-                  "sources": ("paper_2111_03541_gb300/csrc/mf_mixed.cu", "paper_2111_03541_gb300/csrc/mf_internal.h"),
-                  "sha256": "c1661200c93ebe7e"}
+                  "bytes_per_element": (132.16e6 + 70.16e6) / 110592,
+                  "sources": ("paper_2111_03541_gb300/csrc/mf_mixed.cu", "paper_2111_03541_gb300/csrc/mf_device.cuh"),
+                  "sha256": "8b086cefdef5d448"}
 KERNELS_PER_ASSEMBLY = {"mixed": 4, "fp64": 2}
 # instruction-issue ceiling of GB300: one warp instruction per clock per SM
 # sub-partition, 4 per SM, 152 SMs, 2070 MHz maximum SM clock

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/mf.h"
+#include "mf_device.cuh"
 
 #define MF_MAX_DEG 64   // neighbours of one node in one adjacency
 #define MF_SLABS 1      // element chunks of the mixed elasticity assembly (see plan_slabs)
@@ -138,9 +139,6 @@ mf_status mf_spmv_impl(const mf_csr *K, const double *x, double *y, cudaStream_t
 void mf_prof_begin(const char *name, cudaStream_t st);
 void mf_prof_end(cudaStream_t st);
 
-// device status codes are written with atomicCAS(word, 0, code): first error wins
-__device__ __forceinline__ void mf_dev_fail(int *word, int code) { atomicCAS(word, 0, code); }
-
 #define MF_CUDA(call)                                                      \
     do {                                                                   \
         cudaError_t e_ = (call);                                           \
@@ -175,22 +173,4 @@ mf_status mf_slab_pipeline(const mf_pattern *p, cudaStream_t st, Elem elem, Gath
         if (cudaStreamWaitEvent(st, p->join_ev, 0) != cudaSuccess) return fail("mf_assemble");
     }
     return MF_OK;
-}
-
-// x * 2^-S for a fixed-point integer x, rounded to nearest even with integer
-// operations only (no FP64 instruction: FP64 runs at 1/58 of FP32 here).
-__device__ __forceinline__ double mf_fixed_to_double(long long v, int S)
-{
-    if (v == 0) return 0.0;
-    const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
-    unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    const int lz = __clzll((long long)u);
-    u <<= lz;  // leading one at bit 63
-    unsigned long long m = u >> 11;  // 53 significant bits
-    const unsigned long long rest = u & 0x7ffull;
-    m += (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
-    const long long ex = 1023 + (63 - lz) - S;
-    if (ex <= 0) return __longlong_as_double((long long)sign);  // below the normal range
-    const unsigned long long bits = ((unsigned long long)ex << 52) + (m - (1ull << 52));
-    return __longlong_as_double((long long)(bits | sign));
 }
