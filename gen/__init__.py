@@ -41,6 +41,7 @@ SEED_ADVECT = 1003
 SEED_BATCH = 1004
 SEED_GRF = 1005
 SEED_CNN = 1006
+SEED_FACET = 1007
 
 
 def splitmix64(seed: int, idx: np.ndarray) -> np.ndarray:
@@ -84,7 +85,8 @@ def _jitter_grid(coords: np.ndarray, interior: np.ndarray, h: float, alpha: floa
     coords[interior] += (2.0 * u[interior] - 1.0) * (alpha * h)
 
 
-def tri_mesh(n: int, order: int = 1, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
+def tri_mesh(n: int, order: int = 1, jitter: float = 0.0, seed: int = SEED_JITTER,
+             jitter_all: bool = False) -> dict:
     """Triangles on the unit square from an ``n x n`` grid.
 
     Returns ``coords`` (float64 [nn, 2]), ``conn`` (int32 [2 n^2, 3 or 6]) and,
@@ -97,6 +99,8 @@ def tri_mesh(n: int, order: int = 1, jitter: float = 0.0, seed: int = SEED_JITTE
     vcoords = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
     vi, vj = ii.ravel(), jj.ravel()
     interior = (vi > 0) & (vi < n) & (vj > 0) & (vj < n)
+    if jitter_all:  # boundary nodes move too (facets off the box's sides)
+        interior[:] = True
     _jitter_grid(vcoords, interior, h, jitter, seed)
 
     j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
@@ -138,14 +142,17 @@ def tri_mesh(n: int, order: int = 1, jitter: float = 0.0, seed: int = SEED_JITTE
             "vcoords": vcoords, "vconn": vconn}
 
 
-def hex_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
-    """Q1 hexahedra on the unit cube from an ``n^3`` grid."""
+def hex_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER, jitter_all: bool = False) -> dict:
+    """Q1 hexahedra on the unit cube from an ``n^3`` grid (``jitter_all``:
+    boundary nodes move too, so boundary faces are warped)."""
     h = 1.0 / n
     nv = n + 1
     kk, jj, ii = np.meshgrid(np.arange(nv), np.arange(nv), np.arange(nv), indexing="ij")
     ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
     coords = np.stack([ii * h, jj * h, kk * h], axis=1).astype(np.float64)
     interior = (ii > 0) & (ii < n) & (jj > 0) & (jj < n) & (kk > 0) & (kk < n)
+    if jitter_all:
+        interior[:] = True
     _jitter_grid(coords, interior, h, jitter, seed)
     k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     base = ((k.ravel() * nv) + j.ravel()) * nv + i.ravel()
@@ -219,6 +226,70 @@ def advecting_field(coords: np.ndarray, seed: int = SEED_ADVECT, modes: int = 4)
         a[1] -= amp[m] * np.pi * kx * cx * sy
     scale = np.sqrt((a * a).sum(axis=0)).max()
     return a / scale
+
+
+# Boundary facets are faces of mesh elements, named (element, local face):
+# triangle face f is the edge from vertex f to vertex (f + 1) % 3 (P2 adds the
+# midpoint node 3 + f); hexahedron face 2 d + s is the face where reference
+# coordinate d equals 2 s - 1.
+
+SIDES = ("x0", "x1", "y0", "y1", "z0", "z1")
+
+
+def box_facets(mesh: dict, sides=SIDES) -> tuple[np.ndarray, np.ndarray]:
+    """Facets of the structured mesh on the given sides of the box.
+
+    Returns (element int32 [nf], face uint8 [nf]) side by side in the order
+    given, ascending element ids within a side.  Triangle grid: square (i, j)
+    holds elements 2 (j n + i) (v00, v10, v11) and 2 (j n + i) + 1 (v00, v11,
+    v01); hexahedron (i, j, k) is element (k n + j) n + i.
+    """
+    n = mesh["n"]
+    els, faces = [], []
+    r = np.arange(n)
+    for side in sides:
+        axis, hi = "xyz".index(side[0]), side[1] == "1"
+        if mesh["elem"] == "Q1":
+            k, j, i = np.meshgrid(r, r, r, indexing="ij")
+            idx = (i, j, k)[axis].ravel()
+            e = ((k * n + j) * n + i).ravel()[idx == (n - 1 if hi else 0)]
+            f = 2 * axis + int(hi)
+        else:
+            if axis == 2:
+                raise ValueError("a triangle mesh has no z sides")
+            if axis == 1:  # bottom edge of t = 0 (face 0), top edge of t = 1 (face 1)
+                sq = (n - 1 if hi else 0) * n + r
+                e, f = (2 * sq + 1, 1) if hi else (2 * sq, 0)
+            else:  # right edge of t = 0 (face 1), left edge of t = 1 (face 2)
+                sq = r * n + (n - 1 if hi else 0)
+                e, f = (2 * sq, 1) if hi else (2 * sq + 1, 2)
+        els.append(np.asarray(e, dtype=np.int64))
+        faces.append(np.full(len(els[-1]), f, dtype=np.uint8))
+    if not els:
+        return np.zeros(0, np.int32), np.zeros(0, np.uint8)
+    return np.concatenate(els).astype(np.int32), np.concatenate(faces)
+
+
+def convection_facets(mesh: dict, sides, seed: int = SEED_FACET, h_sigma: float = 0.5) -> dict:
+    """Robin (convection) data on the given sides: per facet h lognormal(0,
+    h_sigma) (draws 2f, 2f + 1 of the normal stream) and T_env uniform in
+    [0.5, 1.5) (draw f of stream seed + 1)."""
+    e, f = box_facets(mesh, sides)
+    nf = e.shape[0]
+    return {"elem": e, "face": f, "h": lognormal(seed, nf, h_sigma), "t_env": 0.5 + uniform(seed + 1, nf)}
+
+
+def traction_facets(mesh: dict, sides, stress=None, seed: int = SEED_FACET) -> dict:
+    """Loaded-boundary data on the given sides: a 3 x 3 stress sigma^l per
+    facet (row-major), the given one on every facet or standard normals
+    (draws 9 f .. 9 f + 8 of stream seed + 2)."""
+    e, f = box_facets(mesh, sides)
+    nf = e.shape[0]
+    if stress is None:
+        s = normal(seed + 2, 9 * nf).reshape(nf, 3, 3)
+    else:
+        s = np.broadcast_to(np.asarray(stress, dtype=np.float64).reshape(1, 3, 3), (nf, 3, 3)).copy()
+    return {"elem": e, "face": f, "stress": s}
 
 
 # ----------------------------------------------------------------------------

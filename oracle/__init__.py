@@ -44,7 +44,9 @@ class Problem(C.Structure):
                 ("coords", C.c_void_p), ("conn", C.c_void_p), ("pconn", C.c_void_p),
                 ("coef", C.c_void_p), ("nu", C.c_double), ("mu", C.c_double),
                 ("rho", C.c_double), ("source", C.c_void_p), ("fnodal", C.c_void_p),
-                ("advect", C.c_void_p)]
+                ("advect", C.c_void_p), ("n_facets", C.c_int64), ("f_elem", C.c_void_p),
+                ("f_face", C.c_void_p), ("f_h", C.c_void_p), ("f_tenv", C.c_void_p),
+                ("f_stress", C.c_void_p)]
 
 
 def lib():
@@ -62,6 +64,10 @@ def lib():
         _lib.or_elem_elastic_q1.restype = d
         _lib.or_elem_oseen.argtypes = [vp, vp, d, d, vp, vp, vp, vp]
         _lib.or_elem_oseen.restype = d
+        _lib.or_facet_nodes.argtypes = [i, i, vp]
+        _lib.or_facet_thermal.argtypes = [i, vp, d, d, vp, vp]
+        _lib.or_facet_thermal.restype = d
+        _lib.or_facet_traction_q1.argtypes = [i, vp, vp, vp]
         _lib.or_assemble.argtypes = [C.POINTER(Problem)] + [C.POINTER(i64)] * 2 + [C.POINTER(vp)] * 5
         _lib.or_assemble.restype = i
         _lib.or_assemble_filtered.argtypes = [C.POINTER(Problem), vp, vp] + [C.POINTER(i64)] * 2 + \
@@ -140,6 +146,34 @@ def elem_oseen(X, aN, mu: float, rho: float):
     return A, BT, B, Mp, det
 
 
+def facet_nodes(elem: int, face: int) -> list[int]:
+    """Local element nodes of a facet, in facet node order."""
+    loc = np.zeros(4, dtype=np.int32)
+    nf = lib().or_facet_nodes(elem, face, _p(loc))
+    if nf < 0:
+        raise ValueError("no such face")
+    return loc[:nf].tolist()
+
+
+def facet_thermal(elem: int, Xf, h: float, t_env: float):
+    """Convection matrix and load of one facet: (Kf, df, measure)."""
+    Xf = np.ascontiguousarray(Xf, dtype=np.float64)
+    nf = Xf.shape[0]
+    Kf = np.zeros((nf, nf))
+    df = np.zeros(nf)
+    meas = lib().or_facet_thermal(elem, _p(Xf), h, t_env, _p(Kf), _p(df))
+    return Kf, df, meas
+
+
+def facet_traction(face: int, Xf, sigma) -> np.ndarray:
+    """Loaded-boundary load of one hexahedron face: [4 facet nodes][3]."""
+    Xf = np.ascontiguousarray(Xf, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64).reshape(9)
+    df = np.zeros((4, 3))
+    lib().or_facet_traction_q1(face, _p(Xf), _p(sg), _p(df))
+    return df
+
+
 # ---------------------------------------------------------------------------
 # global level
 # ---------------------------------------------------------------------------
@@ -164,7 +198,8 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
     With ``dirichlet`` the strong elimination of ``bc_mask``/``bc_val`` is applied.
     ``keep_nodes`` (bool mask over nodes; ``keep_pnodes`` over flow pressure
     nodes) restricts the work to the elements touching them: only the rows of
-    those nodes are then complete (use ``rows_of``).
+    those nodes are then complete (use ``rows_of``).  ``prob["facets"]`` (from
+    ``gen.convection_facets`` / ``gen.traction_facets``) adds the boundary terms.
     """
     form = prob["form"]
     elem = prob["elem"]
@@ -202,6 +237,18 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
         pr.mu = prob["viscosity"]
         pr.rho = prob["rho"]
         pr.advect = _p(arr(prob["advect"], np.float64))
+    fac = prob.get("facets")
+    if fac is not None and len(fac["elem"]) > 0:
+        pr.n_facets = len(fac["elem"])
+        pr.f_elem = _p(arr(fac["elem"], np.int32))
+        pr.f_face = _p(arr(fac["face"], np.uint8))
+        if "h" in fac:
+            pr.f_h = _p(arr(fac["h"], np.float64))
+            pr.f_tenv = _p(arr(fac["t_env"], np.float64))
+        if "stress" in fac:
+            pr.f_stress = _p(arr(fac["stress"], np.float64))
+        if (form == "thermal" and "h" not in fac) or (form == "elastic" and "stress" not in fac):
+            raise ValueError("facet data do not match the form")
     n_rows, nnz = C.c_int64(), C.c_int64()
     ptrs = [C.c_void_p() for _ in range(5)]
     if keep_nodes is None and keep_pnodes is None:
@@ -213,6 +260,8 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
                                         *[C.byref(x) for x in ptrs])
     if rc == -2:
         raise AssemblyError("element with detJ <= 0")
+    if rc == -3:
+        raise AssemblyError("facet outside the mesh, or a form without boundary terms")
     if rc:
         raise MemoryError("oracle assembly failed")
     n, z = n_rows.value, nnz.value

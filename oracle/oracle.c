@@ -336,11 +336,164 @@ double or_elem_oseen(const double *X, const double *aN, double mu, double rho,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Boundary facets (Sec. 2.2: a boundary condition is the domain physics one */
+/* dimension lower; Sec. 4.1 convection h(T, T_env - T); Sec. 4.2 loaded     */
+/* boundary (d_i, sigma^l_ij n_j)).  A facet is local face `face` of an      */
+/* element:                                                                  */
+/*  - triangle face f is the edge from vertex f to vertex (f+1) % 3; P2 adds */
+/*    the midpoint node 3 + f.  Edge parameter t in [0, 1] from vertex f;    */
+/*    the edge is straight, x(t) = x_f + t (x_{f+1} - x_f).                  */
+/*  - hexahedron face 2d + s is the face xi_d = 2s - 1: the element nodes a  */
+/*    with bit d of a equal to s, ascending.  Its parameters (u, v) are the  */
+/*    other two reference coordinates in increasing axis order, so facet     */
+/*    node m sits at (u, v) = (2(m & 1) - 1, 2(m >> 1) - 1) and the face map */
+/*    is the bilinear x(u, v) = sum_m N_m(u, v) x_m.                         */
+/* Quadrature: Gauss-Legendre on the edge with 2 (P1) or 3 (P2) points,     */
+/* exact for N_a N_b on a straight edge; 2 x 2 Gauss on a hexahedron face.   */
+/* ------------------------------------------------------------------------ */
+int or_facet_nodes(int elem, int face, int *loc)
+{
+    if (elem == OR_Q1) {
+        if (face < 0 || face > 5) return -1;
+        const int d = face / 2, s = face % 2;
+        int m = 0;
+        for (int a = 0; a < 8; ++a)
+            if (((a >> d) & 1) == s) loc[m++] = a;
+        return 4;
+    }
+    if (face < 0 || face > 2) return -1;
+    loc[0] = face;
+    loc[1] = (face + 1) % 3;
+    if (elem == OR_P2) {
+        loc[2] = 3 + face;
+        return 3;
+    }
+    return 2;
+}
+
+/* Points and weights of the facet rule: t in [0, 1] (edges) or (u, v) in
+ * [-1, 1]^2 (hexahedron faces). */
+static int facet_quad(int elem, double *pts, double *w)
+{
+    if (elem == OR_P1) {
+        const double g = 0.5 / sqrt(3.0);
+        pts[0] = 0.5 - g; pts[1] = 0.5 + g;
+        w[0] = w[1] = 0.5;
+        return 2;
+    }
+    if (elem == OR_P2) {
+        const double g = 0.5 * sqrt(0.6);
+        pts[0] = 0.5 - g; pts[1] = 0.5; pts[2] = 0.5 + g;
+        w[0] = w[2] = 5.0 / 18.0;
+        w[1] = 8.0 / 18.0;
+        return 3;
+    }
+    const double g = 1.0 / sqrt(3.0);
+    for (int q = 0; q < 4; ++q) {
+        pts[2 * q + 0] = (q & 1) ? g : -g;
+        pts[2 * q + 1] = (q & 2) ? g : -g;
+        w[q] = 1.0;
+    }
+    return 4;
+}
+
+/* Facet shape functions at one point: the trace of the element's basis on
+ * the facet (edge: 1 - t, t [, P2: (1-t)(1-2t), t(2t-1), 4t(1-t)]; face: the
+ * bilinear N_m), and the facet's area vector A = dx/du x dx/dv (faces) or
+ * its length element |dx/dt| (edges, returned in A[0]). */
+static int facet_point(int elem, const double *Xf, const double *p, double *N, double *A)
+{
+    if (elem == OR_P1 || elem == OR_P2) {
+        const double t = p[0];
+        int nf;
+        if (elem == OR_P1) {
+            N[0] = 1.0 - t; N[1] = t;
+            nf = 2;
+        } else {
+            N[0] = (1.0 - t) * (1.0 - 2.0 * t);
+            N[1] = t * (2.0 * t - 1.0);
+            N[2] = 4.0 * t * (1.0 - t);
+            nf = 3;
+        }
+        const double ex = Xf[2] - Xf[0], ey = Xf[3] - Xf[1];
+        A[0] = sqrt(ex * ex + ey * ey);
+        return nf;
+    }
+    const double u = p[0], v = p[1];
+    double xu[3] = {0.0, 0.0, 0.0}, xv[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m < 4; ++m) {
+        const double su = (m & 1) ? 1.0 : -1.0, sv = (m & 2) ? 1.0 : -1.0;
+        N[m] = 0.25 * (1.0 + su * u) * (1.0 + sv * v);
+        const double dNu = 0.25 * su * (1.0 + sv * v), dNv = 0.25 * (1.0 + su * u) * sv;
+        for (int i = 0; i < 3; ++i) {
+            xu[i] += dNu * Xf[3 * m + i];
+            xv[i] += dNv * Xf[3 * m + i];
+        }
+    }
+    A[0] = xu[1] * xv[2] - xu[2] * xv[1];
+    A[1] = xu[2] * xv[0] - xu[0] * xv[2];
+    A[2] = xu[0] * xv[1] - xu[1] * xv[0];
+    return 4;
+}
+
+/* Convection on one facet (Sec. 4.1, h(T, T_env - T), tangent negated):
+ *   Kf[m][m'] = sum_q w_q |J_q| h N_m N_m',  df[m] = sum_q w_q |J_q| h T_env N_m,
+ * |J| the length element (edges) or |A| (faces).  Xf holds the facet nodes'
+ * coordinates in facet node order.  Returns the facet's measure sum_q w |J|. */
+double or_facet_thermal(int elem, const double *Xf, double h, double tenv, double *Kf, double *df)
+{
+    double pts[8], w[4], N[4], A[3];
+    const int nq = facet_quad(elem, pts, w);
+    const int pdim = elem == OR_Q1 ? 2 : 1;
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : 4);
+    for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
+    for (int a = 0; a < nf; ++a) df[a] = 0.0;
+    double meas = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        facet_point(elem, Xf, pts + pdim * q, N, A);
+        const double J = elem == OR_Q1 ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
+        meas += w[q] * J;
+        for (int a = 0; a < nf; ++a) {
+            for (int b = 0; b < nf; ++b) Kf[a * nf + b] += w[q] * J * h * N[a] * N[b];
+            df[a] += w[q] * J * h * tenv * N[a];
+        }
+    }
+    return meas;
+}
+
+/* Loaded boundary on one hexahedron face (Sec. 4.2, (d_i, sigma^l_ij n_j)):
+ *   df[3m + i] = sum_q w_q N_m sigma_ij n_j |A_q|,  n |A| = o A,
+ * with o = +1 or -1 the orientation that makes n the outward normal.  The
+ * reference frame (e_d, e_d1, e_d2), d1 < d2 the face's parameter axes, is
+ * right-handed for d = 0, 2 and left-handed for d = 1, so e_d1 x e_d2 is
+ * +e_d (d = 0, 2) or -e_d (d = 1); the outward reference normal of face
+ * 2d + s is (2s - 1) e_d; a map with detJ > 0 keeps orientation.  sigma is
+ * row-major 3 x 3. */
+void or_facet_traction_q1(int face, const double *Xf, const double *sigma, double *df)
+{
+    double pts[8], w[4], N[4], A[3];
+    const int nq = facet_quad(OR_Q1, pts, w);
+    const int d = face / 2, s = face % 2;
+    const double o = (s ? 1.0 : -1.0) * (d == 1 ? -1.0 : 1.0);
+    for (int a = 0; a < 12; ++a) df[a] = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        facet_point(OR_Q1, Xf, pts + 2 * q, N, A);
+        for (int m = 0; m < 4; ++m)
+            for (int i = 0; i < 3; ++i) {
+                double t = 0.0;
+                for (int j = 0; j < 3; ++j) t += sigma[3 * i + j] * o * A[j];
+                df[3 * m + i] += w[q] * N[m] * t;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Global assembly (Block B-3/B-4 numbering, Block D-2/D-3 accumulation).    */
 /* Every element emits COO triplets (row, col, value) in element order, local */
 /* row-major order; every dof also emits (g, g, 0) first, so that the        */
 /* diagonal is always present.  A stable sort by (row, col) followed by the  */
 /* sum of duplicates in emission order gives CSR K (ascending columns) and d. */
+/* Boundary facets emit after all elements, in facet order.                  */
 /* Dof numbering: thermal node; elasticity 3 node + c; flow [u1 | u2 | p].   */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -407,6 +560,13 @@ typedef struct {
     const double *source;   /* thermal: source[0]; elasticity: body[3] */
     const double *fnodal;   /* thermal nodal source or NULL */
     const double *advect;   /* flow: [2][n_nodes] */
+    /* boundary facets (thermal: convection; elasticity: loaded boundary) */
+    int64_t n_facets;
+    const int32_t *f_elem;  /* [n_facets] parent element */
+    const uint8_t *f_face;  /* [n_facets] local face */
+    const double *f_h;      /* thermal [n_facets]: h */
+    const double *f_tenv;   /* thermal [n_facets]: T_env */
+    const double *f_stress; /* elasticity [n_facets][3][3]: sigma^l */
 } or_problem;
 
 int64_t or_ndofs(const or_problem *p)
@@ -420,7 +580,8 @@ int64_t or_ndofs(const or_problem *p)
  * With a node filter (keep != NULL), only elements with at least one node
  * marked in keep[] (or, for flow, one vertex marked in pkeep[]) are
  * evaluated; rows outside the filter are then incomplete and must be ignored.
- * Returns 0, or -2 if some element has detJ <= 0, -1 on allocation failure. */
+ * Returns 0, or -2 if some element has detJ <= 0, -3 for a facet outside the
+ * mesh or a form without boundary terms, -1 on allocation failure. */
 static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass, const uint8_t *keep,
                          const uint8_t *pkeep)
 {
@@ -487,17 +648,41 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
                 for (int a = 0; a < 3; ++a) pmass[pn[a]] += Mp[a];
         }
     }
+    for (int64_t f = 0; f < p->n_facets; ++f) {
+        const int64_t e = p->f_elem[f];
+        int loc[4];
+        if (e < 0 || e >= p->n_el) return -3;
+        const int nf = or_facet_nodes(p->elem, p->f_face[f], loc);
+        if (nf < 0 || p->form == OR_OSEEN) return -3;
+        int64_t node[4];
+        double Xf[12], Kf[16], df[12];
+        int hit = keep == NULL;
+        for (int m = 0; m < nf; ++m) {
+            node[m] = p->conn[e * npe + loc[m]];
+            if (keep) hit |= keep[node[m]];
+            for (int i = 0; i < dim; ++i) Xf[dim * m + i] = p->coords[node[m] * dim + i];
+        }
+        if (!hit) continue;
+        if (p->form == OR_THERMAL) {
+            or_facet_thermal(p->elem, Xf, p->f_h[f], p->f_tenv[f], Kf, df);
+            for (int a = 0; a < nf; ++a) {
+                for (int b = 0; b < nf; ++b)
+                    if (coo_push(c, node[a], node[b], Kf[a * nf + b])) return -1;
+                d[node[a]] += df[a];
+            }
+        } else {
+            if (p->elem != OR_Q1) return -3;
+            or_facet_traction_q1(p->f_face[f], Xf, p->f_stress + 9 * f, df);
+            for (int a = 0; a < 4; ++a)
+                for (int i = 0; i < 3; ++i) d[3 * node[a] + i] += df[3 * a + i];
+        }
+    }
     return 0;
-}
-
-static int emit(const or_problem *p, coo_t *c, double *d, double *pmass)
-{
-    return emit_filtered(p, c, d, pmass, NULL, NULL);
 }
 
 /* Assembles CSR K and d.  Output arrays are malloc'd here; free with or_free.
  * pmass_out (flow only, may be NULL) receives a malloc'd [n_pnodes] pressure
- * mass diagonal.  Returns 0, -1 (allocation) or -2 (detJ <= 0). */
+ * mass diagonal.  Returns 0, -1 (allocation), -2 (detJ <= 0) or -3 (bad facet). */
 int or_assemble_filtered(const or_problem *p, const uint8_t *keep, const uint8_t *pkeep, int64_t *n_rows,
                          int64_t *nnz, int64_t **row_ptr, int32_t **col, double **val, double **d,
                          double **pmass_out)
