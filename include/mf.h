@@ -161,6 +161,64 @@ mf_status mf_pattern_destroy(mf_pattern *pattern);
 mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
                       const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d, void *stream);
 
+/* ---- Boundary (facet) terms -----------------------------------------------
+ * A boundary condition is the domain physics one dimension lower (Sec. 2.2):
+ * the convection term h(T, T_env - T) of Sec. 4.1 and the loaded boundary
+ * (d_i, sigma^l_ij n_j) of Sec. 4.2, integrated over facets.  A facet is a
+ * local face of a mesh element:
+ *  - triangle face f is the edge from vertex f to vertex (f + 1) % 3; on P2
+ *    the midpoint node 3 + f is its third node.  Edges are straight.
+ *  - hexahedron face 2d + s is the face where reference coordinate d equals
+ *    2s - 1; its nodes are the element nodes a with bit d of a equal to s,
+ *    ascending, and its map is bilinear in the other two reference
+ *    coordinates.  n is the outward unit normal.
+ * Quadrature: Gauss-Legendre with 2 (P1) or 3 (P2) points per edge, exact for
+ * the edge mass matrix; 2 x 2 Gauss on a hexahedron face. */
+typedef struct mf_facets mf_facets;
+
+/* Wraps n_facets facets (elem [n_facets] int32 parent elements, face
+ * [n_facets] u8 local faces; device arrays read during this call only) of a
+ * mesh for a thermal or elasticity pattern.  Builds on the device the facets
+ * incident to every boundary node in ascending facet order and, for the
+ * thermal form, each facet node's position in the node's CSR row.
+ * n_facets = 0 is valid (no boundary terms).  Synchronises the stream.
+ * Errors: MF_ERR_INVALID_ARG (NULL, negative count, flow pattern, pattern of
+ * another mesh), MF_ERR_BAD_MESH (element or face out of range),
+ * MF_ERR_UNSUPPORTED (more than 32 facets at one node), MF_ERR_OOM,
+ * MF_ERR_CUDA. */
+mf_status mf_facets_create(const mf_mesh *mesh, const mf_pattern *pattern, int64_t n_facets,
+                           const int32_t *elem, const uint8_t *face, void *stream, mf_facets **out);
+mf_status mf_facets_destroy(mf_facets *facets);
+
+/* Coefficients of the boundary terms, per facet (device arrays).  Thermal:
+ * h [n_facets] convective coefficient, t_env [n_facets] ambient temperature.
+ * Elasticity: stress [n_facets][3][3] row-major sigma^l, the facet's load
+ * being sigma^l n.  bc_mask / bc_val: the Dirichlet data the system was
+ * assembled with (both NULL: none). */
+typedef struct {
+    const double *h;
+    const double *t_env;
+    const double *stress;
+    const uint8_t *bc_mask;
+    const double *bc_val;
+} mf_facet_coeffs;
+
+/* Adds the boundary terms of the facets to a system assembled by
+ * mf_assemble on the same pattern (values [nnz], d [n_rows], in place):
+ *   thermal     K[a][b] += sum_q w_q |J_q| h N_a N_b,
+ *               d[a]    += sum_q w_q |J_q| h T_env N_a;
+ *   elasticity  d[3a+i] += sum_q w_q N_a sigma_ij (n |J|)_j
+ * over the facets of node a, |J| the facet's length or area element.  Rows
+ * of Dirichlet dofs stay as assembled; a term in the column of a Dirichlet
+ * dof g goes to the right-hand side, d[a] -= term * bc_val[g].  The result is
+ * that of assembling domain and boundary terms together before the
+ * elimination, up to the rounding order.  Each node sums its facets in
+ * ascending facet order: two calls give identical bits.  Errors:
+ * MF_ERR_INVALID_ARG, MF_ERR_CUDA; non-finite coefficients are latched
+ * (MF_ERR_NONFINITE). */
+mf_status mf_assemble_boundary(const mf_facets *facets, const mf_facet_coeffs *coeffs, mf_csr *K, double *d,
+                               void *stream);
+
 /* Pressure-mass diagonal of the flow form, out[a] = sum_e sum_q w detJ M_a^2
  * over P1 pressure node a (for the block-diagonal GMRES preconditioner).
  * out [n_pnodes] device.  Errors: MF_ERR_INVALID_ARG, MF_ERR_CUDA. */

@@ -60,6 +60,11 @@ class BatchTiling(C.Structure):
                 ("grid_per_sm", C.c_int32)]
 
 
+class FacetCoeffs(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("t_env", C.c_void_p), ("stress", C.c_void_p),
+                ("bc_mask", C.c_void_p), ("bc_val", C.c_void_p)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("rel_residual", C.c_double), ("converged", C.c_int32)]
 
@@ -76,6 +81,10 @@ _SIGS = {
     "mf_pattern_destroy": [C.c_void_p],
     "mf_assemble": [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Coeffs), C.c_int32, C.POINTER(CSR), C.c_void_p,
                     C.c_void_p],
+    "mf_facets_create": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.POINTER(C.c_void_p)],
+    "mf_facets_destroy": [C.c_void_p],
+    "mf_assemble_boundary": [C.c_void_p, C.POINTER(FacetCoeffs), C.POINTER(CSR), C.c_void_p, C.c_void_p],
     "mf_pressure_mass_diag": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_flow_precond": [C.c_void_p, C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
     "mf_solve": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_void_p],
@@ -186,6 +195,22 @@ def mf_pattern_destroy(h) -> None:
 
 def mf_assemble(form: int, mesh, pattern, coeffs: Coeffs, prec: int, K: CSR, d, stream=None) -> None:
     _check(lib().mf_assemble(form, mesh, pattern, C.byref(coeffs), prec, C.byref(K), _ptr(d), _stream(stream)))
+
+
+def mf_facets_create(mesh, pattern, elem, face, stream=None) -> C.c_void_p:
+    """elem: int32 device tensor of parent elements, face: uint8 device tensor of local faces."""
+    h = C.c_void_p()
+    n = 0 if elem is None else elem.numel()
+    _check(lib().mf_facets_create(mesh, pattern, n, _ptr(elem), _ptr(face), _stream(stream), C.byref(h)))
+    return h
+
+
+def mf_facets_destroy(h) -> None:
+    _check(lib().mf_facets_destroy(h))
+
+
+def mf_assemble_boundary(facets, coeffs: FacetCoeffs, K: CSR, d, stream=None) -> None:
+    _check(lib().mf_assemble_boundary(facets, C.byref(coeffs), C.byref(K), _ptr(d), _stream(stream)))
 
 
 def mf_pressure_mass_diag(mesh, pattern, out, stream=None) -> None:
@@ -392,6 +417,17 @@ class Problem:
         self.d = torch.empty(self.n, dtype=torch.float64, device=dev)
         self.csr.values = _ptr(self.values)
         self.coeffs = self.make_coeffs()
+        self.facets = None
+        fac = prob.get("facets")
+        if fac is not None:
+            self.f_elem = t(fac["elem"], torch.int32)
+            self.f_face = t(fac["face"], torch.uint8)
+            self.f_h = t(fac["h"], torch.float64) if "h" in fac else None
+            self.f_tenv = t(fac["t_env"], torch.float64) if "t_env" in fac else None
+            self.f_stress = t(np.asarray(fac["stress"]).reshape(-1), torch.float64) if "stress" in fac else None
+            self.facets = mf_facets_create(self.mesh, self.pattern, self.f_elem, self.f_face, stream)
+            self.facet_coeffs = FacetCoeffs(h=_ptr(self.f_h), t_env=_ptr(self.f_tenv), stress=_ptr(self.f_stress),
+                                            bc_mask=_ptr(self.bc_mask), bc_val=_ptr(self.bc_val))
 
     def make_coeffs(self, coef=None, bc=True) -> Coeffs:
         p = self.prob
@@ -419,7 +455,10 @@ class Problem:
         return rp, ci
 
     def assemble(self, prec: int = MF_PREC_FP64, coeffs: Coeffs | None = None, stream=None):
+        """Domain terms, then the boundary terms of ``prob["facets"]`` if any."""
         mf_assemble(self.form, self.mesh, self.pattern, coeffs or self.coeffs, prec, self.csr, self.d, stream)
+        if self.facets:
+            mf_assemble_boundary(self.facets, self.facet_coeffs, self.csr, self.d, stream)
         return self.values, self.d
 
     def pressure_mass_diag(self, stream=None):
@@ -445,6 +484,9 @@ class Problem:
         return x, st, info
 
     def close(self):
+        if getattr(self, "facets", None):
+            mf_facets_destroy(self.facets)
+            self.facets = None
         if getattr(self, "pattern", None):
             mf_pattern_destroy(self.pattern)
             self.pattern = None

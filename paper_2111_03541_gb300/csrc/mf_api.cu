@@ -379,6 +379,59 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
     return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: unknown precision %d", prec);
 }
 
+extern "C" mf_status mf_facets_create(const mf_mesh *mesh, const mf_pattern *pattern, int64_t n_facets,
+                                      const int32_t *elem, const uint8_t *face, void *stream, mf_facets **out)
+{
+    g_msg[0] = 0;
+    if (!mesh || !pattern || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: NULL argument");
+    *out = nullptr;
+    if (pattern->mesh != mesh)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: the pattern was built on another mesh");
+    if (pattern->form != MF_FORM_THERMAL && pattern->form != MF_FORM_ELASTIC)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: boundary terms exist for the thermal and elasticity forms");
+    if (n_facets < 0 || (n_facets > 0 && (!elem || !face)))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: negative count or NULL facet arrays");
+    if (n_facets >= (int64_t(1) << 28))
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: at most 2^28 facets");
+    mf_facets *f = new (std::nothrow) mf_facets();
+    if (!f) return mf_fail(MF_ERR_OOM, "mf_facets_create: host allocation");
+    f->mesh = mesh;
+    f->pattern = pattern;
+    mf_status s = mf_facets_create_impl(mesh, pattern, n_facets, elem, face, static_cast<cudaStream_t>(stream), f);
+    if (s != MF_OK) {
+        mf_facets_free(f);
+        delete f;
+        return s;
+    }
+    *out = f;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_facets_destroy(mf_facets *facets)
+{
+    if (!facets) return MF_OK;
+    mf_facets_free(facets);
+    delete facets;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_assemble_boundary(const mf_facets *facets, const mf_facet_coeffs *coeffs, mf_csr *K,
+                                          double *d, void *stream)
+{
+    g_msg[0] = 0;
+    if (!facets || !coeffs || !K || !d || !K->values)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble_boundary: NULL argument");
+    const mf_pattern *p = facets->pattern;
+    if (K->n_rows != p->n_rows || K->nnz != p->nnz || K->row_ptr != p->row_ptr || K->col_idx != p->col_idx)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble_boundary: K does not carry the facets' pattern");
+    if ((coeffs->bc_mask == nullptr) != (coeffs->bc_val == nullptr))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble_boundary: bc_mask and bc_val go together");
+    if (facets->n_facets == 0) return MF_OK;
+    if (p->form == MF_FORM_THERMAL ? (!coeffs->h || !coeffs->t_env) : !coeffs->stress)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble_boundary: the form's facet coefficients are NULL");
+    return mf_assemble_boundary_impl(facets, coeffs, K->values, d, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" mf_status mf_pressure_mass_diag(const mf_mesh *mesh, const mf_pattern *pattern, double *out,
                                            void *stream)
 {

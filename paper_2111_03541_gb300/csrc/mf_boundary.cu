@@ -1,0 +1,450 @@
+// Boundary (facet) terms: a boundary condition is the domain physics one
+// dimension lower (Sec. 2.2).  Convection h(T, T_env - T) (Sec. 4.1) adds a
+// facet mass matrix to K and a load to d; the loaded boundary
+// (d_i, sigma^l_ij n_j) (Sec. 4.2) adds a load to d.
+//
+// Layout.  A facet set keeps, for every node on some facet (ascending), its
+// incident facets in ascending order with the node's index in each, and for
+// the thermal form the position of every facet node in the node's CSR row.
+// The assembly is node-centric like the domain gather: one thread per
+// boundary node walks its facets in order and updates only its own row, so
+// no atomics are needed and the bits do not depend on the schedule.
+//
+// Geometry.  Edges are straight: |J| = L, and the edge mass matrix and load
+// are L times the closed-form reference integrals (P1: [[1/3, 1/6],
+// [1/6, 1/3]], [1/2, 1/2]; P2: [[4, -1, 2], [-1, 4, 2], [2, 2, 16]] / 30,
+// [1/6, 1/6, 2/3]), which the 2- and 3-point Gauss-Legendre rules integrate
+// exactly.  A hexahedron face x(u, v) = c0 + c1 u + c2 v + c3 uv has the area
+// vector A = x_u x x_v = c1 x c2 + (c1 x c3) u + (c3 x c2) v, linear in
+// (u, v): the convection matrix takes |A| at the 2 x 2 Gauss points, and the
+// traction's integral of N_m A is exact in closed form,
+// int N_m A du dv = c1 x c2 + (c1 x c3) s_u / 3 + (c3 x c2) s_v / 3 for the
+// node at (s_u, s_v).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "mf_internal.h"
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int BND_T = 128;     // threads per block of the boundary kernels
+constexpr int MAX_FINC = 32;   // facets incident to one node
+
+inline unsigned nblk(int64_t n, int t = TPB) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// facet set construction
+// ---------------------------------------------------------------------------
+
+// Local element nodes of facet `face`; returns the node count or 0 for a face
+// the element does not have.
+__device__ __forceinline__ int facet_local(int elem, int face, int (&loc)[4])
+{
+    if (elem == MF_Q1_HEX) {
+        if (face < 0 || face > 5) return 0;
+        const int d = face >> 1, s = face & 1;
+        int m = 0;
+        for (int a = 0; a < 8; ++a)
+            if (((a >> d) & 1) == s) loc[m++] = a;
+        return 4;
+    }
+    if (face < 0 || face > 2) return 0;
+    loc[0] = face;
+    loc[1] = face == 2 ? 0 : face + 1;
+    loc[2] = 3 + face;  // P2 midpoint (unused for P1)
+    return elem == MF_P2_TRI ? 3 : 2;
+}
+
+// Validates the facets, writes their global nodes and counts the facets of
+// every node.
+__global__ void k_facet_nodes(int elem, int npe, int npf, int64_t n_el, const int32_t *__restrict__ conn,
+                              int64_t n_facets, const int32_t *__restrict__ f_elem,
+                              const uint8_t *__restrict__ f_face, int32_t *__restrict__ fnode,
+                              uint8_t *__restrict__ fface, int64_t *__restrict__ cnt, int *status)
+{
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n_facets) return;
+    const int64_t e = f_elem[f];
+    const int face = f_face[f];
+    int loc[4];
+    if (e < 0 || e >= n_el || facet_local(elem, face, loc) != npf) {
+        mf_dev_fail(status, MF_ERR_BAD_MESH);
+        for (int m = 0; m < npf; ++m) fnode[f * npf + m] = -1;
+        return;
+    }
+    fface[f] = (uint8_t)face;
+    for (int m = 0; m < npf; ++m) {
+        const int32_t v = conn[e * npe + loc[m]];
+        fnode[f * npf + m] = v;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[v]), 1ull);
+    }
+}
+
+__global__ void k_flag_nonzero(int64_t n, const int64_t *__restrict__ cnt, int64_t *__restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = cnt[i] > 0 ? 1 : 0;
+}
+
+// boundary node list (ascending, from the scanned flags) and its facet counts
+__global__ void k_compact_nodes(int64_t n, const int64_t *__restrict__ cnt, const int64_t *__restrict__ pos,
+                                int32_t *__restrict__ bnode, int64_t *__restrict__ bcnt, int *status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || cnt[i] == 0) return;
+    if (cnt[i] > MAX_FINC) mf_dev_fail(status, MF_ERR_UNSUPPORTED);
+    bnode[pos[i]] = (int32_t)i;
+    bcnt[pos[i]] = cnt[i];
+}
+
+// incidence entries (facet * 4 + local index) in arrival order
+__global__ void k_facet_fill(int64_t n_entries, int npf, const int32_t *__restrict__ fnode,
+                             const int64_t *__restrict__ pos, const int64_t *__restrict__ bptr,
+                             int64_t *__restrict__ cursor, int64_t *__restrict__ key)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_entries) return;
+    const int64_t b = pos[fnode[t]];
+    const int64_t at = bptr[b] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[b]), 1ull);
+    key[at] = (t / npf) * 4 + (t % npf);
+}
+
+// sorts every node's entries by facet (then local index) and splits the keys;
+// the thermal form also looks up each facet node's slot in the node's row
+__global__ void k_facet_sort_slots(int64_t n_bnodes, int npf, const int64_t *__restrict__ bptr,
+                                   int64_t *__restrict__ key, const int32_t *__restrict__ bnode,
+                                   const int32_t *__restrict__ fnode, const int64_t *__restrict__ row_ptr,
+                                   const int32_t *__restrict__ col, int32_t *__restrict__ binc,
+                                   uint8_t *__restrict__ bloc, uint8_t *__restrict__ bslot, int *status)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bnodes) return;
+    const int64_t lo = bptr[b], hi = bptr[b + 1];
+    if (hi - lo > MAX_FINC) return;  // reported by k_compact_nodes
+    for (int64_t i = lo + 1; i < hi; ++i) {  // insertion sort of a short segment
+        const int64_t x = key[i];
+        int64_t j = i - 1;
+        while (j >= lo && key[j] > x) { key[j + 1] = key[j]; --j; }
+        key[j + 1] = x;
+    }
+    const int32_t r = bnode[b];
+    for (int64_t t = lo; t < hi; ++t) {
+        const int64_t f = key[t] >> 2;
+        binc[t] = (int32_t)f;
+        bloc[t] = (uint8_t)(key[t] & 3);
+        if (!bslot) continue;
+        const int64_t r0 = row_ptr[r], r1 = row_ptr[r + 1];
+        for (int m = 0; m < npf; ++m) {
+            const int32_t c = fnode[f * npf + m];
+            int64_t a = r0, z = r1;  // lower bound of c in the ascending row
+            while (a < z) {
+                const int64_t mid = (a + z) >> 1;
+                if (col[mid] < c) a = mid + 1; else z = mid;
+            }
+            if (a == r1 || col[a] != c || a - r0 > 255) {
+                mf_dev_fail(status, MF_ERR_BAD_MESH);
+                bslot[t * npf + m] = 0;
+            } else {
+                bslot[t * npf + m] = (uint8_t)(a - r0);
+            }
+        }
+    }
+}
+
+mf_status check_status(int *status, cudaStream_t st)
+{
+    int h = 0;
+    MF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (!h) return MF_OK;
+    const int zero = 0;
+    MF_CUDA(cudaMemcpyAsync(status, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (h == MF_ERR_UNSUPPORTED)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: more than %d facets at one node", MAX_FINC);
+    return mf_fail((mf_status)h, "mf_facets_create: facet element or face out of range");
+}
+
+// ---------------------------------------------------------------------------
+// boundary assembly
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// bilinear face coefficients c1, c2, c3 (x = c0 + c1 u + c2 v + c3 uv) of the
+// facet's four nodes, node m at (u, v) = (2(m & 1) - 1, 2(m >> 1) - 1)
+__device__ __forceinline__ void face_coefs(const double *__restrict__ X, const int32_t *fn, double (&c1)[3],
+                                           double (&c2)[3], double (&c3)[3])
+{
+    double x[4][3];
+    for (int m = 0; m < 4; ++m)
+        for (int i = 0; i < 3; ++i) x[m][i] = X[3 * (int64_t)fn[m] + i];
+    for (int i = 0; i < 3; ++i) {
+        c1[i] = 0.25 * ((x[1][i] - x[0][i]) + (x[3][i] - x[2][i]));
+        c2[i] = 0.25 * ((x[2][i] - x[0][i]) + (x[3][i] - x[1][i]));
+        c3[i] = 0.25 * ((x[0][i] - x[1][i]) - (x[2][i] - x[3][i]));
+    }
+}
+
+// Row m of the facet's convection matrix for unit h (row[m']) and the facet
+// load factor for unit h T_env (returned).
+template <int ELEM>
+__device__ __forceinline__ double conv_row(const double *__restrict__ X, const int32_t *fn, int m, double (&row)[4])
+{
+    if (ELEM == MF_P1_TRI || ELEM == MF_P2_TRI) {
+        const double ex = X[2 * (int64_t)fn[1]] - X[2 * (int64_t)fn[0]];
+        const double ey = X[2 * (int64_t)fn[1] + 1] - X[2 * (int64_t)fn[0] + 1];
+        const double L = sqrt(ex * ex + ey * ey);
+        if (ELEM == MF_P1_TRI) {
+            row[0] = L * (m == 0 ? 1.0 / 3.0 : 1.0 / 6.0);
+            row[1] = L * (m == 1 ? 1.0 / 3.0 : 1.0 / 6.0);
+            return 0.5 * L;
+        }
+        // (1/30) [[4, -1, 2], [-1, 4, 2], [2, 2, 16]], load (1/6, 1/6, 2/3)
+        if (m == 2) {
+            row[0] = row[1] = L * (1.0 / 15.0);
+            row[2] = L * (8.0 / 15.0);
+            return L * (2.0 / 3.0);
+        }
+        row[0] = L * (m == 0 ? 2.0 / 15.0 : -1.0 / 30.0);
+        row[1] = L * (m == 1 ? 2.0 / 15.0 : -1.0 / 30.0);
+        row[2] = L * (1.0 / 15.0);
+        return L * (1.0 / 6.0);
+    } else {
+        double c1[3], c2[3], c3[3], P[3], Qu[3], Qv[3];
+        face_coefs(X, fn, c1, c2, c3);
+        cross3(c1, c2, P);
+        cross3(c1, c3, Qu);
+        cross3(c3, c2, Qv);
+        const double g = 0.57735026918962576451;   // 1 / sqrt(3)
+        const double al = 0.5 * (1.0 + g), be = 0.5 * (1.0 - g);  // 1D shape values at +-g
+        for (int k = 0; k < 4; ++k) row[k] = 0.0;
+        double load = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const double u = (q & 1) ? g : -g, v = (q & 2) ? g : -g;
+            const double a0 = P[0] + Qu[0] * u + Qv[0] * v;
+            const double a1 = P[1] + Qu[1] * u + Qv[1] * v;
+            const double a2 = P[2] + Qu[2] * u + Qv[2] * v;
+            const double J = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+            // N_k(q) = n1(k & 1 vs q & 1) n1(k >> 1 vs q >> 1), n1 = al on the
+            // node's own side of the point, be on the other
+            const double nm = ((m & 1) == (q & 1) ? al : be) * ((m >> 1) == (q >> 1) ? al : be);
+            const double jn = J * nm;
+            load += jn;
+            for (int k = 0; k < 4; ++k)
+                row[k] += jn * (((k & 1) == (q & 1) ? al : be) * ((k >> 1) == (q >> 1) ? al : be));
+        }
+        return load;
+    }
+}
+
+template <int ELEM>
+__global__ void __launch_bounds__(BND_T) k_bnd_thermal(int64_t n_bnodes, const int32_t *__restrict__ bnode,
+                                                       const int64_t *__restrict__ bptr,
+                                                       const int32_t *__restrict__ binc,
+                                                       const uint8_t *__restrict__ bloc,
+                                                       const uint8_t *__restrict__ bslot,
+                                                       const int32_t *__restrict__ fnode,
+                                                       const double *__restrict__ X, const double *__restrict__ h,
+                                                       const double *__restrict__ tenv,
+                                                       const uint8_t *__restrict__ mask,
+                                                       const double *__restrict__ bval,
+                                                       const int64_t *__restrict__ row_ptr, double *values,
+                                                       double *d, int *status)
+{
+    constexpr int NPF = ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4);
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bnodes) return;
+    const int32_t r = bnode[b];
+    if (mask && mask[r]) return;  // a Dirichlet row stays the identity
+    double *vrow = values + row_ptr[r];
+    double dr = 0.0;
+    for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
+        const int32_t f = binc[t];
+        const int32_t *fn = fnode + (int64_t)f * NPF;
+        const double hf = h[f], tf = tenv[f];
+        if (!isfinite(hf) || !isfinite(tf)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        double row[4];
+        const double lf = conv_row<ELEM>(X, fn, bloc[t], row);
+        dr += hf * tf * lf;
+        const uint8_t *sl = bslot + t * NPF;
+        for (int k = 0; k < NPF; ++k) {
+            const double v = hf * row[k];
+            const int32_t c = fn[k];
+            if (mask && mask[c]) dr -= v * bval[c];
+            else vrow[sl[k]] += v;
+        }
+    }
+    d[r] += dr;
+}
+
+__global__ void __launch_bounds__(BND_T) k_bnd_traction(int64_t n_bnodes, const int32_t *__restrict__ bnode,
+                                                        const int64_t *__restrict__ bptr,
+                                                        const int32_t *__restrict__ binc,
+                                                        const uint8_t *__restrict__ bloc,
+                                                        const int32_t *__restrict__ fnode,
+                                                        const uint8_t *__restrict__ fface,
+                                                        const double *__restrict__ X,
+                                                        const double *__restrict__ stress,
+                                                        const uint8_t *__restrict__ mask, double *d, int *status)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bnodes) return;
+    const int32_t r = bnode[b];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
+        const int32_t f = binc[t];
+        const int m = bloc[t];
+        double c1[3], c2[3], c3[3], P[3], Qu[3], Qv[3];
+        face_coefs(X, fnode + (int64_t)f * 4, c1, c2, c3);
+        cross3(c1, c2, P);
+        cross3(c1, c3, Qu);
+        cross3(c3, c2, Qv);
+        // outward orientation: (2s - 1), negated for d = 1 (left-handed frame)
+        const int face = fface[f];
+        const double o = ((face & 1) ? 1.0 : -1.0) * ((face >> 1) == 1 ? -1.0 : 1.0);
+        const double su = (m & 1) ? 1.0 / 3.0 : -1.0 / 3.0, sv = (m & 2) ? 1.0 / 3.0 : -1.0 / 3.0;
+        double a[3];
+        for (int i = 0; i < 3; ++i) a[i] = o * (P[i] + Qu[i] * su + Qv[i] * sv);
+        const double *sg = stress + 9 * (int64_t)f;
+        for (int i = 0; i < 3; ++i) {
+            const double s0 = sg[3 * i], s1 = sg[3 * i + 1], s2 = sg[3 * i + 2];
+            if (!isfinite(s0) || !isfinite(s1) || !isfinite(s2)) mf_dev_fail(status, MF_ERR_NONFINITE);
+            acc[i] += s0 * a[0] + s1 * a[1] + s2 * a[2];
+        }
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!(mask && mask[3 * (int64_t)r + i])) d[3 * (int64_t)r + i] += acc[i];
+}
+
+}  // namespace
+
+mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n_facets, const int32_t *elem,
+                                const uint8_t *face, cudaStream_t st, mf_facets *f)
+{
+    f->npf = m->elem == MF_P1_TRI ? 2 : (m->elem == MF_P2_TRI ? 3 : 4);
+    f->n_facets = n_facets;
+    if (n_facets == 0) return MF_OK;
+    if (p->form == MF_FORM_ELASTIC && m->elem != MF_Q1_HEX)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: loaded boundaries are provided on Q1 faces");
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_facets_create: status word unavailable");
+    const int npf = f->npf;
+    const int64_t nn = m->n_nodes, ne = n_facets * npf;
+    int64_t *cnt = nullptr, *pos = nullptr, *key = nullptr, *bcnt = nullptr;
+    auto cleanup = [&]() {
+        cudaFreeAsync(cnt, st);
+        cudaFreeAsync(pos, st);
+        cudaFreeAsync(key, st);
+        cudaFreeAsync(bcnt, st);
+    };
+    auto fail = [&](cudaError_t e, const char *what) {
+        cleanup();
+        return mf_cuda_check(e, what);
+    };
+#define FC(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return fail(e_, #call); \
+    } while (0)
+    FC(cudaMemsetAsync(status, 0, sizeof(int), st));
+    FC(cudaMallocAsync(&f->fnode, sizeof(int32_t) * ne, st));
+    FC(cudaMallocAsync(&f->fface, (size_t)n_facets, st));
+    FC(cudaMallocAsync(&cnt, sizeof(int64_t) * (nn + 1), st));
+    FC(cudaMallocAsync(&pos, sizeof(int64_t) * (nn + 1), st));
+    FC(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (nn + 1), st));
+    k_facet_nodes<<<nblk(n_facets), TPB, 0, st>>>(m->elem, m->npe, npf, m->n_elems, m->conn, n_facets, elem, face,
+                                                 f->fnode, f->fface, cnt, status);
+    FC(cudaGetLastError());
+    {
+        mf_status s = check_status(status, st);
+        if (s != MF_OK) {
+            cleanup();
+            return s;
+        }
+    }
+    k_flag_nonzero<<<nblk(nn + 1), TPB, 0, st>>>(nn + 1, cnt, pos);
+    FC(cudaGetLastError());
+    FC(mf_scan_i64(pos, nn + 1, nullptr, st));
+    int64_t nb = 0;
+    FC(cudaMemcpyAsync(&nb, pos + nn, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    FC(cudaStreamSynchronize(st));
+    f->n_bnodes = nb;
+    FC(cudaMallocAsync(&f->bnode, sizeof(int32_t) * nb, st));
+    FC(cudaMallocAsync(&f->bptr, sizeof(int64_t) * (nb + 1), st));
+    FC(cudaMallocAsync(&bcnt, sizeof(int64_t) * (nb + 1), st));
+    FC(cudaMemsetAsync(bcnt, 0, sizeof(int64_t) * (nb + 1), st));
+    k_compact_nodes<<<nblk(nn), TPB, 0, st>>>(nn, cnt, pos, f->bnode, bcnt, status);
+    FC(cudaGetLastError());
+    FC(mf_scan_i64(bcnt, nb + 1, nullptr, st));
+    FC(cudaMemcpyAsync(f->bptr, bcnt, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToDevice, st));
+    FC(cudaMemsetAsync(bcnt, 0, sizeof(int64_t) * (nb + 1), st));  // now the fill cursors
+    FC(cudaMallocAsync(&key, sizeof(int64_t) * ne, st));
+    FC(cudaMallocAsync(&f->binc, sizeof(int32_t) * ne, st));
+    FC(cudaMallocAsync(&f->bloc, (size_t)ne, st));
+    if (p->form == MF_FORM_THERMAL) FC(cudaMallocAsync(&f->bslot, (size_t)ne * npf, st));
+    k_facet_fill<<<nblk(ne), TPB, 0, st>>>(ne, npf, f->fnode, pos, f->bptr, bcnt, key);
+    FC(cudaGetLastError());
+    k_facet_sort_slots<<<nblk(nb), TPB, 0, st>>>(nb, npf, f->bptr, key, f->bnode, f->fnode, p->row_ptr,
+                                                 p->col_idx, f->binc, f->bloc, f->bslot, status);
+    FC(cudaGetLastError());
+#undef FC
+    mf_status s = check_status(status, st);
+    cleanup();
+    if (s == MF_OK) s = mf_cuda_check(cudaStreamSynchronize(st), "mf_facets_create");
+    return s;
+}
+
+void mf_facets_free(mf_facets *f)
+{
+    cudaFree(f->fnode);
+    cudaFree(f->fface);
+    cudaFree(f->bnode);
+    cudaFree(f->bptr);
+    cudaFree(f->binc);
+    cudaFree(f->bloc);
+    cudaFree(f->bslot);
+    f->fnode = f->bnode = f->binc = nullptr;
+    f->fface = f->bloc = f->bslot = nullptr;
+    f->bptr = nullptr;
+}
+
+mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c, double *values, double *d,
+                                    cudaStream_t st)
+{
+    if (f->n_bnodes == 0) return MF_OK;
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "mf_assemble_boundary: status word unavailable");
+    const mf_mesh *m = f->mesh;
+    const mf_pattern *p = f->pattern;
+    const unsigned g = nblk(f->n_bnodes, BND_T);
+    if (p->form == MF_FORM_THERMAL) {
+        mf_prof_begin("bnd_thermal", st);
+        if (m->elem == MF_P1_TRI)
+            k_bnd_thermal<MF_P1_TRI><<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->bslot,
+                                                         f->fnode, m->coords, c->h, c->t_env, c->bc_mask,
+                                                         c->bc_val, p->row_ptr, values, d, status);
+        else if (m->elem == MF_P2_TRI)
+            k_bnd_thermal<MF_P2_TRI><<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->bslot,
+                                                         f->fnode, m->coords, c->h, c->t_env, c->bc_mask,
+                                                         c->bc_val, p->row_ptr, values, d, status);
+        else
+            k_bnd_thermal<MF_Q1_HEX><<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->bslot,
+                                                         f->fnode, m->coords, c->h, c->t_env, c->bc_mask,
+                                                         c->bc_val, p->row_ptr, values, d, status);
+        mf_prof_end(st);
+    } else {
+        mf_prof_begin("bnd_traction", st);
+        k_bnd_traction<<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->fnode, f->fface,
+                                            m->coords, c->stress, c->bc_mask, d, status);
+        mf_prof_end(st);
+    }
+    return mf_cuda_check(cudaGetLastError(), "mf_assemble_boundary");
+}

@@ -100,6 +100,24 @@ struct mf_pattern {
     std::vector<cudaEvent_t> slab_ev;
 };
 
+// Boundary facets of a mesh for one pattern (thermal or elasticity form): the
+// facets incident to every boundary node, ascending, as a CSR over the
+// boundary nodes.
+struct mf_facets {
+    const mf_mesh *mesh = nullptr;
+    const mf_pattern *pattern = nullptr;
+    int npf = 0;                 // nodes per facet: 2 (P1 edge), 3 (P2 edge), 4 (Q1 face)
+    int64_t n_facets = 0;
+    int32_t *fnode = nullptr;    // [n_facets][npf] global nodes in facet node order
+    uint8_t *fface = nullptr;    // [n_facets] local face of the parent element
+    int64_t n_bnodes = 0;
+    int32_t *bnode = nullptr;    // [n_bnodes] nodes on some facet, ascending
+    int64_t *bptr = nullptr;     // [n_bnodes + 1] offsets into binc / bloc
+    int32_t *binc = nullptr;     // incident facets of each boundary node, ascending
+    uint8_t *bloc = nullptr;     // the node's index within each incident facet
+    uint8_t *bslot = nullptr;    // thermal: [entry][npf] position of facet node m' in the node's row
+};
+
 // status word (device) of the current device
 int *mf_status_word();
 mf_status mf_fail(mf_status s, const char *fmt, ...);
@@ -130,6 +148,11 @@ mf_status mf_mixed_geometry(const mf_mesh *m, mf_pattern *p, cudaStream_t st);
 mf_status mf_flow_consts_upload();
 void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
                               const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st);
+mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n_facets, const int32_t *elem,
+                                const uint8_t *face, cudaStream_t st, mf_facets *f);
+void mf_facets_free(mf_facets *f);
+mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c, double *values, double *d,
+                                    cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);
 mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o,
                         mf_solve_info *info, cudaStream_t st);
