@@ -396,6 +396,73 @@ def _ev_time(fn, reps=10, warm=3):
     return s.elapsed_time(e) / reps
 
 
+def _ev_time_flushed(fn, reps=20, warm=3):
+    """Mean device time of fn with L2 flushed (256 MB write) before every call;
+    only fn sits between the events."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for i, (s, e) in enumerate(evs):
+        flush.fill_(float(i))
+        s.record()
+        fn()
+        e.record()
+    torch.cuda.synchronize()
+    return sum(s.elapsed_time(e) for s, e in evs) / reps
+
+
+def _boundary_case(mf, P, prob, fac, sides, bc_mask, bc_val, hbm_gbs):
+    """Times mf_assemble_boundary alone on an assembled system.  Algorithmic
+    bytes: per boundary node its id, offsets, row start, mask, d (read and
+    write) and coordinates; per incidence entry facet id, local index and row
+    slots; per facet its nodes and coefficients; per touched K entry a read
+    and a write."""
+    import numpy as np
+    import torch
+    dev = P.device
+    e = torch.from_numpy(fac["elem"]).to(dev)
+    f = torch.from_numpy(fac["face"]).to(dev)
+    F = mf.mf_facets_create(P.mesh, P.pattern, e, f)
+    keep = []
+
+    def t(a):
+        x = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).to(dev)
+        keep.append(x)
+        return x.data_ptr()
+    fc = mf.FacetCoeffs(bc_mask=bc_mask.data_ptr(), bc_val=bc_val.data_ptr())
+    thermal = "h" in fac
+    if thermal:
+        fc.h, fc.t_env = t(fac["h"]), t(fac["t_env"])
+    else:
+        fc.stress = t(fac["stress"])
+    ms = _ev_time_flushed(lambda: mf.mf_assemble_boundary(F, fc, P.csr, P.d))
+    mf.mf_sync_status()
+    mf.mf_facets_destroy(F)
+    x = prob["coords"]
+    on = np.zeros(x.shape[0], bool)
+    for sd in sides:
+        ax = "xyz".index(sd[0])
+        on |= (x[:, ax] >= 1.0 - 1e-14) if sd[1] == "1" else (x[:, ax] <= 1e-14)
+    nb = int(on.sum())
+    nf = int(fac["elem"].shape[0])
+    npf, dim = (4, 3) if prob["elem"] == "Q1" else ((2 if prob["elem"] == "P1" else 3), 2)
+    n_inc = nf * npf
+    per_node = 4 + 8 + 8 + (17 if thermal else 51) + 8 * dim
+    per_entry = 4 + 1 + (npf if thermal else 0)
+    per_facet = 4 * npf + (16 if thermal else 73)
+    # touched K entries (thermal): the distinct node pairs of the facets, face-
+    # interior nodes of a structured box side touching 9, edge 6, corner 4
+    touched = 9 * nb if thermal else 0
+    algo = nb * per_node + n_inc * per_entry + nf * per_facet + 16 * touched
+    gbs = algo / (ms * 1e-3) / 1e9
+    return {"facets": nf, "boundary_nodes": nb, "kernel_us": 1e3 * ms, "facets_per_s": nf / (ms * 1e-3),
+            "algorithmic_bytes": algo, "achieved_gbs": gbs, "hbm_frac": gbs / hbm_gbs,
+            "launches": 1, "l2": "flushed before each launch"}
+
+
 def _solve_timed(P, **kw):
     import torch
     torch.cuda.synchronize()
@@ -481,6 +548,22 @@ def suite(dev):
         c4["cnn_forward_ms"] = _ev_time(lambda: mf.mf_cnn_forward(cnn, 1, nz, nz, nz, xin, y), reps=5)
         mf.mf_cnn_destroy(cnn)
     out["C4_grf_q1_128"] = c4
+    # boundary terms: convection on five sides of the C4 mesh (T fixed on x = 0)
+    hbm = measured_peaks()[0]["hbm_gbs"]
+    sides = ("x1", "y0", "y1", "z0", "z1")
+    x0 = torch.from_numpy((prob["coords"][:, 0] <= 1e-14).astype(np.uint8)).to(dev)
+    bv = torch.zeros(P.n, dtype=torch.float64, device=dev)
+    out["B1_convection_q1_128"] = _boundary_case(mf, P, prob, gen.convection_facets(prob, sides), sides, x0, bv,
+                                                 hbm)
+    del P
+    torch.cuda.empty_cache()
+    # loaded boundary: a random stress on five sides of the 64^3 elasticity box (clamped at x = 0)
+    prob = gen.elastic_problem(64)
+    P = mf.Problem(prob, device=dev)
+    P.assemble()
+    out["B2_traction_q1_64"] = _boundary_case(mf, P, prob, gen.traction_facets(prob, sides), sides, P.bc_mask,
+                                              P.bc_val, hbm)
+    del P
     return out
 
 

@@ -124,7 +124,9 @@ typedef struct {
 /* Validates and wraps a mesh (Block B-1).  Checks on the device that every
  * connectivity entry is in range and detJ > 0 at every quadrature point;
  * synchronises the stream.  Keeps the caller's device pointers (they must
- * outlive the handle).  Errors: MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH,
+ * outlive the handle); coordinates and connectivity must not change while
+ * patterns or facet sets of the mesh live (those keep data derived from
+ * them).  Errors: MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH,
  * MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_mesh_create(const mf_mesh_desc *desc, void *stream, mf_mesh **out);
 mf_status mf_mesh_destroy(mf_mesh *mesh);
@@ -180,8 +182,9 @@ typedef struct mf_facets mf_facets;
  * [n_facets] u8 local faces; device arrays read during this call only) of a
  * mesh for a thermal or elasticity pattern.  Builds on the device the facets
  * incident to every boundary node in ascending facet order and, for the
- * thermal form, each facet node's position in the node's CSR row.
- * n_facets = 0 is valid (no boundary terms).  Synchronises the stream.
+ * thermal form, each facet node's position in the node's CSR row, and
+ * keeps each facet's geometry (the coefficient-free factors of the terms
+ * below).  n_facets = 0 is valid (no boundary terms).  Synchronises the stream.
  * Errors: MF_ERR_INVALID_ARG (NULL, negative count, flow pattern, pattern of
  * another mesh), MF_ERR_BAD_MESH (element or face out of range),
  * MF_ERR_UNSUPPORTED (more than 32 facets at one node), MF_ERR_OOM,

@@ -6,6 +6,8 @@ for profiling (ncu, the kernel-timing hooks) without the whole benchmark.
     python -m paper_2111_03541_gb300.cases cnn --n 129 --reps 5
     python -m paper_2111_03541_gb300.cases oseen --n 512 --reps 5
     python -m paper_2111_03541_gb300.cases batch --reps 5
+    python -m paper_2111_03541_gb300.cases convection --n 128 --reps 5
+    python -m paper_2111_03541_gb300.cases traction --n 64 --reps 5
 
 elastic: Q1 elasticity on an n^3 jittered box (gen.elastic_problem), assembled
 reps times after one untimed call, then pcg-iters Jacobi-PCG iterations.  thermal-grf: Q1 thermal conduction with
@@ -14,7 +16,10 @@ then pcg-iters Jacobi-PCG iterations (graph of 50).  cnn: reps forward passes
 of the preconditioner network on an n^3 node grid (package weights).  oseen:
 the Taylor-Hood flow form on an n^2 grid (gen.oseen_problem), assembled reps
 times.  batch: the 512-problem thermal batch (gen.batch_specs) in one graph,
-default tiling, reps replays.
+default tiling, reps replays.  convection: the thermal-grf mesh with T = 0 on
+x = 0 and convection (gen.convection_facets) on the other five sides, the
+boundary terms added reps times.  traction: the elastic mesh with a random
+stress load (gen.traction_facets) on the five sides away from the clamp.
 Inputs are the seeded synthetic ones of `gen`; every step runs in libmf.
 """
 from __future__ import annotations
@@ -30,7 +35,7 @@ def _times(mf):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn", "oseen", "batch"))
+    ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn", "oseen", "batch", "convection", "traction"))
     ap.add_argument("--n", type=int, default=48)
     ap.add_argument("--prec", choices=("fp64", "mixed"), default="mixed")
     ap.add_argument("--reps", type=int, default=5)
@@ -70,6 +75,26 @@ def main(argv=None):
             x, st, info = P.solve(tol=1e-8, max_iter=a.pcg_iters, check_every=50)
             torch.cuda.synchronize()
             print("pcg iterations", info.iterations, "residual", info.rel_residual)
+    elif a.case in ("convection", "traction"):
+        import numpy as np
+        sides = ("x1", "y0", "y1", "z0", "z1")
+        if a.case == "convection":
+            prob = gen.grf_thermal_problem(a.n)
+            left = prob["coords"][:, 0] <= 1e-14
+            prob["bc_mask"] = left.astype(np.uint8)
+            prob["bc_val"] = np.zeros(left.shape[0])
+            prob["facets"] = gen.convection_facets(prob, sides)
+        else:
+            prob = gen.elastic_problem(a.n)
+            prob["facets"] = gen.traction_facets(prob, sides)
+        P = mf.Problem(prob)
+        P.assemble()
+        torch.cuda.synchronize()
+        mf.mf_set_kernel_timing(1)
+        for _ in range(a.reps):
+            mf.mf_assemble_boundary(P.facets, P.facet_coeffs, P.csr, P.d)
+        torch.cuda.synchronize()
+        print("boundary", _times(mf))
     elif a.case == "oseen":
         P = mf.Problem(gen.oseen_problem(a.n))
         P.assemble()

@@ -8,7 +8,11 @@
 // the thermal form the position of every facet node in the node's CSR row.
 // The assembly is node-centric like the domain gather: one thread per
 // boundary node walks its facets in order and updates only its own row, so
-// no atomics are needed and the bits do not depend on the schedule.
+// no atomics are needed and the bits do not depend on the schedule.  The
+// facet geometry of every incidence entry is computed once, when the facet
+// set is made (FP64 runs at 1/58 of the FP32 rate here, and the mesh does not
+// move), so an assembly reads per entry a few cached doubles and the
+// coefficients.
 //
 // Geometry.  Edges are straight: |J| = L, and the edge mass matrix and load
 // are L times the closed-form reference integrals (P1: [[1/3, 1/6],
@@ -117,7 +121,8 @@ __global__ void k_facet_sort_slots(int64_t n_bnodes, int npf, const int64_t *__r
                                    int64_t *__restrict__ key, const int32_t *__restrict__ bnode,
                                    const int32_t *__restrict__ fnode, const int64_t *__restrict__ row_ptr,
                                    const int32_t *__restrict__ col, int32_t *__restrict__ binc,
-                                   uint8_t *__restrict__ bloc, uint8_t *__restrict__ bslot, int *status)
+                                   uint8_t *__restrict__ bloc, uint8_t *__restrict__ bslot,
+                                   int64_t *__restrict__ brow, int *status)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_bnodes) return;
@@ -130,6 +135,7 @@ __global__ void k_facet_sort_slots(int64_t n_bnodes, int npf, const int64_t *__r
         key[j + 1] = x;
     }
     const int32_t r = bnode[b];
+    if (brow) brow[b] = row_ptr[r];
     for (int64_t t = lo; t < hi; ++t) {
         const int64_t f = key[t] >> 2;
         binc[t] = (int32_t)f;
@@ -245,65 +251,26 @@ __device__ __forceinline__ double conv_row(const double *__restrict__ X, const i
     }
 }
 
+// Facet geometry of every incidence entry, once per facet set (the mesh's
+// coordinates do not change while it lives).  Thermal: the entry's row of the
+// unit-h convection matrix and its unit-h T_env load factor, (npf + 1)
+// doubles, and the facet's nodes as the row's columns.  Elasticity: the
+// oriented area moment o int N_m A du dv (3 doubles).
 template <int ELEM>
-__global__ void __launch_bounds__(BND_T) k_bnd_thermal(int64_t n_bnodes, const int32_t *__restrict__ bnode,
-                                                       const int64_t *__restrict__ bptr,
-                                                       const int32_t *__restrict__ binc,
-                                                       const uint8_t *__restrict__ bloc,
-                                                       const uint8_t *__restrict__ bslot,
-                                                       const int32_t *__restrict__ fnode,
-                                                       const double *__restrict__ X, const double *__restrict__ h,
-                                                       const double *__restrict__ tenv,
-                                                       const uint8_t *__restrict__ mask,
-                                                       const double *__restrict__ bval,
-                                                       const int64_t *__restrict__ row_ptr, double *values,
-                                                       double *d, int *status)
+__global__ void k_facet_geometry(int64_t n_entries, const int32_t *__restrict__ binc,
+                                 const uint8_t *__restrict__ bloc, const int32_t *__restrict__ fnode,
+                                 const uint8_t *__restrict__ fface, const double *__restrict__ X, bool traction,
+                                 double *__restrict__ bgeo, int32_t *__restrict__ bcol)
 {
     constexpr int NPF = ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4);
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_bnodes) return;
-    const int32_t r = bnode[b];
-    if (mask && mask[r]) return;  // a Dirichlet row stays the identity
-    double *vrow = values + row_ptr[r];
-    double dr = 0.0;
-    for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
-        const int32_t f = binc[t];
-        const int32_t *fn = fnode + (int64_t)f * NPF;
-        const double hf = h[f], tf = tenv[f];
-        if (!isfinite(hf) || !isfinite(tf)) mf_dev_fail(status, MF_ERR_NONFINITE);
-        double row[4];
-        const double lf = conv_row<ELEM>(X, fn, bloc[t], row);
-        dr += hf * tf * lf;
-        const uint8_t *sl = bslot + t * NPF;
-        for (int k = 0; k < NPF; ++k) {
-            const double v = hf * row[k];
-            const int32_t c = fn[k];
-            if (mask && mask[c]) dr -= v * bval[c];
-            else vrow[sl[k]] += v;
-        }
-    }
-    d[r] += dr;
-}
-
-__global__ void __launch_bounds__(BND_T) k_bnd_traction(int64_t n_bnodes, const int32_t *__restrict__ bnode,
-                                                        const int64_t *__restrict__ bptr,
-                                                        const int32_t *__restrict__ binc,
-                                                        const uint8_t *__restrict__ bloc,
-                                                        const int32_t *__restrict__ fnode,
-                                                        const uint8_t *__restrict__ fface,
-                                                        const double *__restrict__ X,
-                                                        const double *__restrict__ stress,
-                                                        const uint8_t *__restrict__ mask, double *d, int *status)
-{
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_bnodes) return;
-    const int32_t r = bnode[b];
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
-        const int32_t f = binc[t];
-        const int m = bloc[t];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_entries) return;
+    const int32_t f = binc[t];
+    const int m = bloc[t];
+    const int32_t *fn = fnode + (int64_t)f * NPF;
+    if (ELEM == MF_Q1_HEX && traction) {
         double c1[3], c2[3], c3[3], P[3], Qu[3], Qv[3];
-        face_coefs(X, fnode + (int64_t)f * 4, c1, c2, c3);
+        face_coefs(X, fn, c1, c2, c3);
         cross3(c1, c2, P);
         cross3(c1, c3, Qu);
         cross3(c3, c2, Qv);
@@ -311,17 +278,99 @@ __global__ void __launch_bounds__(BND_T) k_bnd_traction(int64_t n_bnodes, const 
         const int face = fface[f];
         const double o = ((face & 1) ? 1.0 : -1.0) * ((face >> 1) == 1 ? -1.0 : 1.0);
         const double su = (m & 1) ? 1.0 / 3.0 : -1.0 / 3.0, sv = (m & 2) ? 1.0 / 3.0 : -1.0 / 3.0;
-        double a[3];
-        for (int i = 0; i < 3; ++i) a[i] = o * (P[i] + Qu[i] * su + Qv[i] * sv);
-        const double *sg = stress + 9 * (int64_t)f;
-        for (int i = 0; i < 3; ++i) {
-            const double s0 = sg[3 * i], s1 = sg[3 * i + 1], s2 = sg[3 * i + 2];
-            if (!isfinite(s0) || !isfinite(s1) || !isfinite(s2)) mf_dev_fail(status, MF_ERR_NONFINITE);
-            acc[i] += s0 * a[0] + s1 * a[1] + s2 * a[2];
+        for (int i = 0; i < 3; ++i) bgeo[3 * t + i] = o * (P[i] + Qu[i] * su + Qv[i] * sv);
+        return;
+    }
+    double row[4];
+    const double lf = conv_row<ELEM>(X, fn, m, row);
+    for (int k = 0; k < NPF; ++k) {
+        bgeo[t * (NPF + 1) + k] = row[k];
+        bcol[t * NPF + k] = fn[k];
+    }
+    bgeo[t * (NPF + 1) + NPF] = lf;
+}
+
+// Convection: one thread per boundary node adds, in ascending facet order,
+// each facet's cached row times h to its own CSR row (or, in a Dirichlet
+// column, moves the term to the right-hand side) and the facet's load to its
+// own d entry.  Each K entry and each d entry has one writer.
+
+template <int NPF>
+__global__ void __launch_bounds__(BND_T) k_bnd_thermal(int64_t n_bnodes, const int32_t *__restrict__ bnode,
+                                                       const int64_t *__restrict__ brow,
+                                                       const int64_t *__restrict__ bptr,
+                                                       const int32_t *__restrict__ binc,
+                                                       const uint8_t *__restrict__ bslot,
+                                                       const double *__restrict__ bgeo,
+                                                       const int32_t *__restrict__ bcol,
+                                                       const double *__restrict__ h, const double *__restrict__ tenv,
+                                                       const uint8_t *__restrict__ mask,
+                                                       const double *__restrict__ bval, double *values, double *d,
+                                                       int *status)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bnodes) return;
+    const int32_t r = bnode[b];
+    if (mask && mask[r]) return;  // a Dirichlet row stays the identity
+    double *vrow = values + brow[b];
+    double dr = 0.0;
+    const int64_t lo = bptr[b], hi = bptr[b + 1];
+    for (int64_t t = lo; t < hi; ++t) {
+        const int32_t f = binc[t];
+        const double hf = h[f], tf = tenv[f];
+        if (!isfinite(hf) || !isfinite(tf)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        const double *g = bgeo + t * (NPF + 1);
+        dr += hf * tf * g[NPF];
+        for (int k = 0; k < NPF; ++k) {
+            const double v = hf * g[k];
+            const int32_t c = bcol[t * NPF + k];
+            if (mask && mask[c]) dr -= v * bval[c];
+            else vrow[bslot[t * NPF + k]] += v;
         }
     }
-    for (int i = 0; i < 3; ++i)
-        if (!(mask && mask[3 * (int64_t)r + i])) d[3 * (int64_t)r + i] += acc[i];
+    d[r] += dr;
+}
+
+// facets whose loads a traction thread issues together
+constexpr int BU = 4;
+
+// Loaded boundary: one thread per (boundary node, component i) adds
+// sum_j sigma^l_ij a_j of the node's facets, in ascending facet order.
+__global__ void __launch_bounds__(BND_T) k_bnd_traction(int64_t n_bnodes, const int32_t *__restrict__ bnode,
+                                                        const int64_t *__restrict__ bptr,
+                                                        const int32_t *__restrict__ binc,
+                                                        const double *__restrict__ bgeo,
+                                                        const double *__restrict__ stress,
+                                                        const uint8_t *__restrict__ mask, double *d, int *status)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= 3 * n_bnodes) return;
+    const int64_t b = g / 3;
+    const int i = (int)(g - 3 * b);
+    const int64_t dof = 3 * (int64_t)bnode[b] + i;
+    if (mask && mask[dof]) return;
+    double acc = 0.0;
+    bool finite = true;
+    const int64_t t1 = bptr[b + 1];
+    for (int64_t t = bptr[b]; t < t1; t += BU) {
+        int32_t f[BU];
+        double a[BU][3], sg[BU][3];
+#pragma unroll
+        for (int u = 0; u < BU; ++u) {
+            f[u] = t + u < t1 ? binc[t + u] : -1;
+            for (int j = 0; j < 3; ++j) a[u][j] = t + u < t1 ? bgeo[3 * (t + u) + j] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < BU; ++u)
+            for (int j = 0; j < 3; ++j) sg[u][j] = f[u] >= 0 ? stress[9 * (int64_t)f[u] + 3 * i + j] : 0.0;
+#pragma unroll
+        for (int u = 0; u < BU; ++u) {
+            finite = finite && isfinite(sg[u][0]) && isfinite(sg[u][1]) && isfinite(sg[u][2]);
+            acc += sg[u][0] * a[u][0] + sg[u][1] * a[u][1] + sg[u][2] * a[u][2];
+        }
+    }
+    if (!finite) mf_dev_fail(status, MF_ERR_NONFINITE);
+    d[dof] += acc;
 }
 
 }  // namespace
@@ -389,11 +438,37 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
     FC(cudaMallocAsync(&key, sizeof(int64_t) * ne, st));
     FC(cudaMallocAsync(&f->binc, sizeof(int32_t) * ne, st));
     FC(cudaMallocAsync(&f->bloc, (size_t)ne, st));
-    if (p->form == MF_FORM_THERMAL) FC(cudaMallocAsync(&f->bslot, (size_t)ne * npf, st));
+    const bool thermal = p->form == MF_FORM_THERMAL;
+    if (thermal) {
+        FC(cudaMallocAsync(&f->bslot, (size_t)ne * npf, st));
+        FC(cudaMallocAsync(&f->bcol, sizeof(int32_t) * ne * npf, st));
+        FC(cudaMallocAsync(&f->brow, sizeof(int64_t) * nb, st));
+        FC(cudaMallocAsync(&f->bgeo, sizeof(double) * ne * (npf + 1), st));
+    } else {
+        FC(cudaMallocAsync(&f->bgeo, sizeof(double) * ne * 3, st));
+    }
     k_facet_fill<<<nblk(ne), TPB, 0, st>>>(ne, npf, f->fnode, pos, f->bptr, bcnt, key);
     FC(cudaGetLastError());
     k_facet_sort_slots<<<nblk(nb), TPB, 0, st>>>(nb, npf, f->bptr, key, f->bnode, f->fnode, p->row_ptr,
-                                                 p->col_idx, f->binc, f->bloc, f->bslot, status);
+                                                 p->col_idx, f->binc, f->bloc, f->bslot, f->brow, status);
+    FC(cudaGetLastError());
+    {
+        // the incidence must be complete before anything follows it
+        mf_status s = check_status(status, st);
+        if (s != MF_OK) {
+            cleanup();
+            return s;
+        }
+    }
+    if (m->elem == MF_P1_TRI)
+        k_facet_geometry<MF_P1_TRI><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
+                                                              false, f->bgeo, f->bcol);
+    else if (m->elem == MF_P2_TRI)
+        k_facet_geometry<MF_P2_TRI><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
+                                                              false, f->bgeo, f->bcol);
+    else
+        k_facet_geometry<MF_Q1_HEX><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
+                                                              !thermal, f->bgeo, f->bcol);
     FC(cudaGetLastError());
 #undef FC
     mf_status s = check_status(status, st);
@@ -411,9 +486,13 @@ void mf_facets_free(mf_facets *f)
     cudaFree(f->binc);
     cudaFree(f->bloc);
     cudaFree(f->bslot);
-    f->fnode = f->bnode = f->binc = nullptr;
+    cudaFree(f->bcol);
+    cudaFree(f->brow);
+    cudaFree(f->bgeo);
+    f->fnode = f->bnode = f->binc = f->bcol = nullptr;
     f->fface = f->bloc = f->bslot = nullptr;
-    f->bptr = nullptr;
+    f->bptr = f->brow = nullptr;
+    f->bgeo = nullptr;
 }
 
 mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c, double *values, double *d,
@@ -424,26 +503,20 @@ mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c
     if (!status) return mf_fail(MF_ERR_CUDA, "mf_assemble_boundary: status word unavailable");
     const mf_mesh *m = f->mesh;
     const mf_pattern *p = f->pattern;
-    const unsigned g = nblk(f->n_bnodes, BND_T);
     if (p->form == MF_FORM_THERMAL) {
         mf_prof_begin("bnd_thermal", st);
-        if (m->elem == MF_P1_TRI)
-            k_bnd_thermal<MF_P1_TRI><<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->bslot,
-                                                         f->fnode, m->coords, c->h, c->t_env, c->bc_mask,
-                                                         c->bc_val, p->row_ptr, values, d, status);
-        else if (m->elem == MF_P2_TRI)
-            k_bnd_thermal<MF_P2_TRI><<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->bslot,
-                                                         f->fnode, m->coords, c->h, c->t_env, c->bc_mask,
-                                                         c->bc_val, p->row_ptr, values, d, status);
-        else
-            k_bnd_thermal<MF_Q1_HEX><<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->bslot,
-                                                         f->fnode, m->coords, c->h, c->t_env, c->bc_mask,
-                                                         c->bc_val, p->row_ptr, values, d, status);
+        const unsigned g = nblk(f->n_bnodes, BND_T);
+#define BND_ARGS f->n_bnodes, f->bnode, f->brow, f->bptr, f->binc, f->bslot, f->bgeo, f->bcol, c->h, c->t_env, \
+                 c->bc_mask, c->bc_val, values, d, status
+        if (m->elem == MF_P1_TRI) k_bnd_thermal<2><<<g, BND_T, 0, st>>>(BND_ARGS);
+        else if (m->elem == MF_P2_TRI) k_bnd_thermal<3><<<g, BND_T, 0, st>>>(BND_ARGS);
+        else k_bnd_thermal<4><<<g, BND_T, 0, st>>>(BND_ARGS);
+#undef BND_ARGS
         mf_prof_end(st);
     } else {
         mf_prof_begin("bnd_traction", st);
-        k_bnd_traction<<<g, BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc, f->bloc, f->fnode, f->fface,
-                                            m->coords, c->stress, c->bc_mask, d, status);
+        k_bnd_traction<<<nblk(3 * f->n_bnodes, BND_T), BND_T, 0, st>>>(f->n_bnodes, f->bnode, f->bptr, f->binc,
+                                                                        f->bgeo, c->stress, c->bc_mask, d, status);
         mf_prof_end(st);
     }
     return mf_cuda_check(cudaGetLastError(), "mf_assemble_boundary");

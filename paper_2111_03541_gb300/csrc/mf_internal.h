@@ -116,6 +116,10 @@ struct mf_facets {
     int32_t *binc = nullptr;     // incident facets of each boundary node, ascending
     uint8_t *bloc = nullptr;     // the node's index within each incident facet
     uint8_t *bslot = nullptr;    // thermal: [entry][npf] position of facet node m' in the node's row
+    int32_t *bcol = nullptr;     // thermal: [entry][npf] facet node m' (the column)
+    int64_t *brow = nullptr;     // thermal: [n_bnodes] start of the node's CSR row
+    double *bgeo = nullptr;      // facet geometry per entry: thermal [entry][npf + 1] unit-h convection
+                                 // row and load factor; elasticity [entry][3] oriented area moment
 };
 
 // status word (device) of the current device
