@@ -21,9 +21,9 @@ LIB = os.path.join(HERE, "_oracle.so")
 
 P1, P2, Q1 = 0, 1, 2
 QTRI3, QTRI6, QHEX8 = 0, 1, 2
-THERMAL, ELASTIC, OSEEN = 0, 1, 2
+THERMAL, ELASTIC, OSEEN, CAPACITY = 0, 1, 2, 3
 ELEM = {"P1": P1, "P2": P2, "Q1": Q1}
-FORM = {"thermal": THERMAL, "elastic": ELASTIC, "oseen": OSEEN}
+FORM = {"thermal": THERMAL, "elastic": ELASTIC, "oseen": OSEEN, "capacity": CAPACITY}
 
 _lib = None
 
@@ -64,6 +64,11 @@ def lib():
         _lib.or_elem_elastic_q1.restype = d
         _lib.or_elem_oseen.argtypes = [vp, vp, d, d, vp, vp, vp, vp]
         _lib.or_elem_oseen.restype = d
+        _lib.or_elem_capacity.argtypes = [i, vp, d, vp]
+        _lib.or_elem_capacity.restype = d
+        _lib.or_genalpha.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, d, d, d, i64, d, i, d,
+                                     vp]
+        _lib.or_genalpha.restype = i
         _lib.or_facet_nodes.argtypes = [i, i, vp]
         _lib.or_facet_thermal.argtypes = [i, vp, d, d, vp, vp]
         _lib.or_facet_thermal.restype = d
@@ -146,6 +151,15 @@ def elem_oseen(X, aN, mu: float, rho: float):
     return A, BT, B, Mp, det
 
 
+def elem_capacity(elem: int, X, C: float):
+    """Capacity matrix C int N_a N_b of one element and its min detJ."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    npe = X.shape[0]
+    Me = np.zeros((npe, npe))
+    det = lib().or_elem_capacity(elem, _p(X), C, _p(Me))
+    return Me, det
+
+
 def facet_nodes(elem: int, face: int) -> list[int]:
     """Local element nodes of a facet, in facet node order."""
     loc = np.zeros(4, dtype=np.int32)
@@ -222,7 +236,7 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
     pr.coords = _p(coords)
     pr.conn = _p(conn)
     pr.coef = _p(coef)
-    if form == "thermal":
+    if form in ("thermal", "capacity"):
         src = arr([prob.get("source", 1.0), 0.0, 0.0], np.float64)
         pr.source = _p(src)
         if fnodal is not None:
@@ -343,6 +357,62 @@ def oseen_precond(sys: dict, prob: dict) -> np.ndarray:
     mask = prob["bc_mask"].astype(bool)
     p[mask] = 1.0
     return p
+
+
+# ---------------------------------------------------------------------------
+# generalised-alpha time stepping
+# ---------------------------------------------------------------------------
+
+def genalpha_params(rho_inf: float) -> dict:
+    """Parameters of the first-order generalised-alpha method (Jansen,
+    Whiting and Hulbert 2000) for the high-frequency spectral radius rho_inf,
+    in the constraint/relaxation notation of Sec. 2.1: b1 = gamma,
+    c1 = alpha_f, c2 = alpha_m; the second-rate level takes b2 = gamma,
+    c3 = alpha_m (it does not enter a first-order residual)."""
+    am = 0.5 * (3.0 - rho_inf) / (1.0 + rho_inf)
+    af = 1.0 / (1.0 + rho_inf)
+    g = 0.5 + am - af
+    return {"b1": g, "b2": g, "c1": af, "c2": am, "c3": am}
+
+
+def capacity(prob: dict, C) -> dict:
+    """Capacity matrix sum_e C_e int N_a N_b of a thermal problem's mesh (no
+    Dirichlet elimination); C is a per-element array."""
+    p = dict(prob, form="capacity", coef=np.ascontiguousarray(C, dtype=np.float64))
+    p.pop("facets", None)
+    return assemble(p, dirichlet=False)
+
+
+def initial_rate(K: dict, M: dict, F, mask, phi0) -> np.ndarray:
+    """Consistent initial rate u0 with M u0 = F - K phi0 on the free rows,
+    u0 = 0 on Dirichlet rows."""
+    r = np.asarray(F, dtype=np.float64) - spmv(K, phi0)
+    Mm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in M.items()}
+    Mm["d"] = r
+    apply_dirichlet(Mm, mask, np.zeros_like(r))
+    u0, _, _ = pcg(Mm, tol=1e-14)
+    return u0
+
+
+def genalpha(K: dict, M: dict, F, mask, bval, phi, u, a, prm: dict, dt: float, steps: int,
+             newton_tol: float = 1e-8, max_newton: int = 10, pcg_tol: float = 1e-13):
+    """Runs or_genalpha; returns (phi, u, a, newton solves per step)."""
+    n = K["d"].shape[0] if "d" in K else K["row_ptr"].shape[0] - 1
+    phi = np.array(phi, dtype=np.float64)
+    u = np.array(u, dtype=np.float64)
+    a = np.array(a, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    bval = np.ascontiguousarray(bval, dtype=np.float64)
+    its = np.zeros(max(steps, 1), dtype=np.int64)
+    rc = lib().or_genalpha(n, _p(K["row_ptr"]), _p(K["col"]), _p(K["val"]), _p(M["val"]), _p(F), _p(mask),
+                           _p(bval), _p(phi), _p(u), _p(a), prm["b1"], prm["b2"], prm["c1"], prm["c2"], prm["c3"],
+                           dt, steps, newton_tol, max_newton, pcg_tol, _p(its))
+    if rc == -4:
+        raise MemoryError("oracle generalised-alpha")
+    if rc:
+        raise RuntimeError("generalised-alpha: a step did not converge")
+    return phi, u, a, its[:steps]
 
 
 # ---------------------------------------------------------------------------

@@ -31,7 +31,7 @@ enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2 };
 /* quadrature kinds */
 enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2 };
 /* forms */
-enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2 };
+enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2, OR_CAPACITY = 3 };
 
 /* ------------------------------------------------------------------------ */
 /* Quadrature (Sec. 2.1: each bilinear form is approximated by a weighted     */
@@ -245,6 +245,29 @@ double or_elem_thermal(int elem, int quad, const double *X, double k, double fco
             }
             de[a] += wd * f * N[a];
         }
+    }
+    return mindet;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Capacity element (Sec. 4.1: -C(T, T_t), the rate term; tangent negated):  */
+/* Me[a][b] = sum_q w detJ C N_a N_b, with a rule exact for N_a N_b on an    */
+/* affine element: the 3-point rule (P1, degree 2), the 6-point rule (P2,    */
+/* degree 4), 2 x 2 x 2 Gauss (Q1).  Returns min detJ.                       */
+/* ------------------------------------------------------------------------ */
+double or_elem_capacity(int elem, const double *X, double C, double *Me)
+{
+    double pts[8 * 3], w[8], N[8], g[24];
+    const int quad = elem == OR_P1 ? OR_QTRI3 : (elem == OR_P2 ? OR_QTRI6 : OR_QHEX8);
+    const int nq = or_quad(quad, pts, w);
+    const int dim = elem_dim(elem), npe = elem_npe(elem);
+    double mindet = 1e300;
+    for (int a = 0; a < npe * npe; ++a) Me[a] = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        const double det = geometry(elem, X, pts + dim * q, N, g);
+        if (det < mindet) mindet = det;
+        for (int a = 0; a < npe; ++a)
+            for (int b = 0; b < npe; ++b) Me[a * npe + b] += w[q] * det * C * N[a] * N[b];
     }
     return mindet;
 }
@@ -572,6 +595,7 @@ typedef struct {
 int64_t or_ndofs(const or_problem *p)
 {
     if (p->form == OR_ELASTIC) return 3 * p->n_nodes;
+    if (p->form == OR_CAPACITY) return p->n_nodes;
     if (p->form == OR_OSEEN) return 2 * p->n_nodes + p->n_pnodes;
     return p->n_nodes;
 }
@@ -612,6 +636,12 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
                     if (coo_push(c, cn[a], cn[b], Ke[a * npe + b])) return -1;
                 d[cn[a]] += de[a];
             }
+        } else if (p->form == OR_CAPACITY) {
+            const double det = or_elem_capacity(p->elem, X, p->coef[e], Ke);
+            if (!(det > 0.0)) return -2;
+            for (int a = 0; a < npe; ++a)
+                for (int b = 0; b < npe; ++b)
+                    if (coo_push(c, cn[a], cn[b], Ke[a * npe + b])) return -1;
         } else if (p->form == OR_ELASTIC) {
             const double det = or_elem_elastic_q1(X, p->coef[e], p->nu, p->source, Ke, de);
             if (!(det > 0.0)) return -2;
@@ -653,7 +683,7 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
         int loc[4];
         if (e < 0 || e >= p->n_el) return -3;
         const int nf = or_facet_nodes(p->elem, p->f_face[f], loc);
-        if (nf < 0 || p->form == OR_OSEEN) return -3;
+        if (nf < 0 || p->form == OR_OSEEN || p->form == OR_CAPACITY) return -3;
         int64_t node[4];
         double Xf[12], Kf[16], df[12];
         int hit = keep == NULL;
@@ -986,4 +1016,109 @@ void or_conv3d_bwd_weight(int64_t nz, int64_t ny, int64_t nx, int ci_n, int co_n
                         }
                 }
             }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Generalised-alpha time stepping (Sec. 2.1, Eq. time_constraints and       */
+/* time_effective; Blocks C and D of Sec. 2.2) of the linear conduction      */
+/* system, maximum derivative order 2: per dof the basic value phi, its rate */
+/* u and its second rate a.  The residual of the form (tangent negated, as   */
+/* K and M here are the positive matrices) at the effective values is        */
+/*   d = F - K phi~ - M u~        (zero on Dirichlet rows),                  */
+/* and the tangent of Block D-3 is T = c1 K + c2 / (b1 dt) M.  K and M share */
+/* the CSR pattern (rp, ci).  Dirichlet dofs keep phi = bval, u = a = 0.     */
+/* Per time step:                                                            */
+/*  C-1  phi += dphi, u += du, a += da (last step's increments);             */
+/*  C-2  da = 0;                                                             */
+/*  C-3  the increments that satisfy the constraints with da = 0:            */
+/*       du = dt (a + b2 da), dphi = dt (u + b1 du);                         */
+/*  D-1  phi~ = phi + c1 dphi, u~ = u + c2 du, a~ = a + c3 da;               */
+/*  D-2  d; stop when ||d|| <= newton_tol ||d_0|| (d_0: the step's first),  */
+/*       or ||d|| <= 1e-13 (||F|| + ||K phi~|| + ||M u~||), the level below  */
+/*       which rounding decides d;                                           */
+/*  D-3/4  T x = d by Jacobi-PCG, dphi += x, and du, da from the             */
+/*       constraints: du = (dphi / dt - u) / b1, da = (du / dt - a) / b2.    */
+/* After the last step the increments are applied (C-1), so phi, u, a hold   */
+/* the values at t = steps dt.  newton_its[m] (may be NULL) counts the       */
+/* solves of step m.  Returns 0, or -1 if a step hit max_newton without      */
+/* converging, -4 on allocation failure.                                     */
+/* ------------------------------------------------------------------------ */
+int or_genalpha(int64_t n, const int64_t *rp, const int32_t *ci, const double *Kv, const double *Mv,
+                const double *F, const uint8_t *mask, const double *bval, double *phi, double *u, double *a,
+                double b1, double b2, double c1, double c2, double c3, double dt, int64_t steps,
+                double newton_tol, int max_newton, double pcg_tol, int64_t *newton_its)
+{
+    const int64_t nnz = rp[n];
+    double *dphi = calloc((size_t)n, sizeof(double)), *du = calloc((size_t)n, sizeof(double));
+    double *da = calloc((size_t)n, sizeof(double)), *pt = malloc(sizeof(double) * n);
+    double *ut = malloc(sizeof(double) * n), *d = malloc(sizeof(double) * n), *x = malloc(sizeof(double) * n);
+    double *Tv = malloc(sizeof(double) * nnz), *zero = calloc((size_t)n, sizeof(double));
+    double *y = malloc(sizeof(double) * n);
+    if (!dphi || !du || !da || !pt || !ut || !d || !x || !Tv || !zero || !y) {
+        free(dphi); free(du); free(da); free(pt); free(ut); free(d); free(x); free(Tv); free(zero); free(y);
+        return -4;
+    }
+    int rc = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (mask[i]) { phi[i] = bval[i]; u[i] = 0.0; a[i] = 0.0; }
+    for (int64_t m = 0; m < steps; ++m) {
+        for (int64_t i = 0; i < n; ++i) {          /* C-1 */
+            phi[i] += dphi[i];
+            u[i] += du[i];
+            a[i] += da[i];
+        }
+        for (int64_t i = 0; i < n; ++i) {          /* C-2, C-3 */
+            da[i] = 0.0;
+            du[i] = mask[i] ? 0.0 : dt * (a[i] + b2 * da[i]);
+            dphi[i] = mask[i] ? 0.0 : dt * (u[i] + b1 * du[i]);
+        }
+        double d0 = -1.0;
+        int it = 0;
+        for (;;) {
+            for (int64_t i = 0; i < n; ++i) {      /* D-1 */
+                pt[i] = phi[i] + c1 * dphi[i];
+                ut[i] = u[i] + c2 * du[i];
+            }
+            or_spmv(n, rp, ci, Kv, pt, d);         /* D-2 */
+            or_spmv(n, rp, ci, Mv, ut, y);
+            double r2 = 0.0, f2 = 0.0, k2 = 0.0, m2 = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                if (!mask[i]) {
+                    f2 += F[i] * F[i];
+                    k2 += d[i] * d[i];
+                    m2 += y[i] * y[i];
+                }
+                d[i] = mask[i] ? 0.0 : F[i] - d[i] - y[i];
+                r2 += d[i] * d[i];
+            }
+            const double r = sqrt(r2);
+            if (d0 < 0.0) d0 = r;
+            /* converged: reduced by newton_tol, or at the rounding floor of
+             * its three terms */
+            if (r <= newton_tol * d0 || r <= 1e-13 * (sqrt(f2) + sqrt(k2) + sqrt(m2))) break;
+            if (it == max_newton) { rc = -1; break; }
+            const double s = c2 / (b1 * dt);       /* D-3 */
+            for (int64_t t = 0; t < nnz; ++t) Tv[t] = c1 * Kv[t] + s * Mv[t];
+            or_dirichlet(n, rp, ci, Tv, d, mask, zero);
+            for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+            double rr;
+            or_pcg(n, rp, ci, Tv, d, x, pcg_tol, 100000, &rr);
+            for (int64_t i = 0; i < n; ++i) {      /* increments from the constraints */
+                if (mask[i]) continue;
+                dphi[i] += x[i];
+                du[i] = (dphi[i] / dt - u[i]) / b1;
+                da[i] = (du[i] / dt - a[i]) / b2;
+            }
+            ++it;
+        }
+        if (newton_its) newton_its[m] = it;
+        if (rc) break;
+    }
+    for (int64_t i = 0; i < n; ++i) {              /* C-1 of the next step */
+        phi[i] += dphi[i];
+        u[i] += du[i];
+        a[i] += da[i];
+    }
+    free(dphi); free(du); free(da); free(pt); free(ut); free(d); free(x); free(Tv); free(zero); free(y);
+    return rc;
 }
