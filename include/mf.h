@@ -51,7 +51,7 @@ typedef enum {
 } mf_status;
 
 typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2 } mf_elem;
-typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2 } mf_form;
+typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2, MF_FORM_CAPACITY = 3 } mf_form;
 typedef enum { MF_PREC_FP64 = 0, MF_PREC_MIXED = 1 } mf_prec;
 typedef enum { MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1 } mf_solver;
 
@@ -162,6 +162,11 @@ mf_status mf_pattern_destroy(mf_pattern *pattern);
  * coefficients are latched (MF_ERR_NONFINITE). */
 mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
                       const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d, void *stream);
+/* form = MF_FORM_CAPACITY (prec FP64, on a thermal pattern) assembles the
+ * capacity matrix of the rate term -C(T, T_t) of Sec. 4.1, K[a][b] =
+ * sum_e C_e int_e N_a N_b with C_e = elem_coef[e], exactly on affine elements
+ * (P1, P2: closed forms; Q1: 2 x 2 x 2 Gauss), and d = 0 (then the Dirichlet
+ * elimination if bc_mask is given). */
 
 /* ---- Boundary (facet) terms -----------------------------------------------
  * A boundary condition is the domain physics one dimension lower (Sec. 2.2):
@@ -221,6 +226,55 @@ typedef struct {
  * (MF_ERR_NONFINITE). */
 mf_status mf_assemble_boundary(const mf_facets *facets, const mf_facet_coeffs *coeffs, mf_csr *K, double *d,
                                void *stream);
+
+/* ---- Generalised-alpha time stepping ---------------------------------------
+ * Sec. 2.1 (Eq. time_constraints, time_effective) and Blocks C, D of Sec. 2.2
+ * for the linear conduction system with capacity: per dof the value phi, its
+ * rate u and second rate a; increments dphi, du, da tied by the constraints
+ * dphi = dt (u + b1 du), du = dt (a + b2 da); residual at the effective
+ * values phi~ = phi + c1 dphi, u~ = u + c2 du (a~ = a + c3 da does not enter
+ * a first-order form):  d = F - K phi~ - M u~;  tangent (Block D-3) T = c1 K +
+ * c2 / (b1 dt) M. */
+typedef struct {
+    double b1, b2, c1, c2, c3;
+} mf_genalpha_params;
+
+/* Parameters of the first-order generalised-alpha method of Jansen, Whiting
+ * and Hulbert (2000) with high-frequency spectral radius rho_inf in [0, 1]:
+ * alpha_m = (3 - rho_inf) / (2 (1 + rho_inf)), alpha_f = 1 / (1 + rho_inf),
+ * gamma = 1/2 + alpha_m - alpha_f; b1 = b2 = gamma, c1 = alpha_f,
+ * c2 = c3 = alpha_m.  Second-order accurate, unconditionally stable.
+ * Errors: MF_ERR_INVALID_ARG. */
+mf_status mf_genalpha_params_from_rho(double rho_inf, mf_genalpha_params *out);
+
+/* Runs `steps` time steps of length dt.  K: CSR of the stiffness (values
+ * with any convection terms, no Dirichlet elimination); M_values [nnz]: the
+ * capacity matrix on the same pattern; F [n]: the load; bc_mask / bc_val
+ * [n] (or NULL): Dirichlet dofs, which keep phi = bc_val and u = a = 0.
+ * phi, u, a [n] (device): the state at t on entry (u should be the
+ * consistent rate, M u = F - K phi on free rows) and at t + steps dt on exit.
+ * Each step: C-1 apply the last increments, C-2 da = 0, C-3 du = dt a,
+ * dphi = dt (u + b1 du); then Newton sub-steps (Block D): residual d at the
+ * effective values, stop when ||d||_2 <= newton_tol ||d_0||_2 (d_0: the
+ * step's first residual) or ||d|| <= 1e-13 (||F|| + ||K phi~|| + ||M u~||)
+ * on the free rows; else solve T x = d by Jacobi-PCG to pcg_tol (relative),
+ * dphi += x, du = (dphi / dt - u) / b1, da = (du / dt - a) / b2.  The norms
+ * are fixed-order sums: runs are bit-reproducible.  newton_its, pcg_its
+ * (host [steps], may be NULL): solves and PCG iterations per step.
+ * Synchronises the stream every sub-step.  Errors: MF_ERR_INVALID_ARG,
+ * MF_ERR_NOT_CONVERGED (a step used max_newton solves, or a PCG solve hit
+ * pcg_max_iter), MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_genalpha_run(const mf_csr *K, const double *M_values, const double *F, const uint8_t *bc_mask,
+                          const double *bc_val, double *phi, double *u, double *a, const mf_genalpha_params *prm,
+                          double dt, int64_t steps, double newton_tol, int32_t max_newton, double pcg_tol,
+                          int64_t pcg_max_iter, int64_t *newton_its, int64_t *pcg_its, void *stream);
+
+/* Consistent initial rate: solves M u = F - K phi on the free rows (u = 0
+ * on Dirichlet rows) by Jacobi-PCG to pcg_tol.  Arguments as
+ * mf_genalpha_run; u [n] device output.  Synchronises the stream.  Errors:
+ * MF_ERR_INVALID_ARG, MF_ERR_NOT_CONVERGED, MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_genalpha_initial_rate(const mf_csr *K, const double *M_values, const double *F, const uint8_t *bc_mask,
+                                   const double *phi, double *u, double pcg_tol, int64_t pcg_max_iter, void *stream);
 
 /* Pressure-mass diagonal of the flow form, out[a] = sum_e sum_q w detJ M_a^2
  * over P1 pressure node a (for the block-diagonal GMRES preconditioner).

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libmf.so")
 MF_OK, MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH, MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA, \
     MF_ERR_NOT_CONVERGED, MF_ERR_TIMEOUT, MF_ERR_UNSUPPORTED = range(9)
 MF_P1_TRI, MF_P2_TRI, MF_Q1_HEX = 0, 1, 2
-MF_FORM_THERMAL, MF_FORM_ELASTIC, MF_FORM_OSEEN = 0, 1, 2
+MF_FORM_THERMAL, MF_FORM_ELASTIC, MF_FORM_OSEEN, MF_FORM_CAPACITY = 0, 1, 2, 3
 MF_PREC_FP64, MF_PREC_MIXED = 0, 1
 MF_SOLVER_PCG, MF_SOLVER_GMRES = 0, 1
 
@@ -65,6 +65,11 @@ class FacetCoeffs(C.Structure):
                 ("bc_mask", C.c_void_p), ("bc_val", C.c_void_p)]
 
 
+class GenAlphaParams(C.Structure):
+    _fields_ = [("b1", C.c_double), ("b2", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+                ("c3", C.c_double)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("rel_residual", C.c_double), ("converged", C.c_int32)]
 
@@ -85,6 +90,12 @@ _SIGS = {
                          C.POINTER(C.c_void_p)],
     "mf_facets_destroy": [C.c_void_p],
     "mf_assemble_boundary": [C.c_void_p, C.POINTER(FacetCoeffs), C.POINTER(CSR), C.c_void_p, C.c_void_p],
+    "mf_genalpha_params_from_rho": [C.c_double, C.POINTER(GenAlphaParams)],
+    "mf_genalpha_run": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                        C.c_void_p, C.POINTER(GenAlphaParams), C.c_double, C.c_int64, C.c_double, C.c_int32,
+                        C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_genalpha_initial_rate": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_double, C.c_int64, C.c_void_p],
     "mf_pressure_mass_diag": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_flow_precond": [C.c_void_p, C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
     "mf_solve": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_void_p],
@@ -211,6 +222,31 @@ def mf_facets_destroy(h) -> None:
 
 def mf_assemble_boundary(facets, coeffs: FacetCoeffs, K: CSR, d, stream=None) -> None:
     _check(lib().mf_assemble_boundary(facets, C.byref(coeffs), C.byref(K), _ptr(d), _stream(stream)))
+
+
+def mf_genalpha_params_from_rho(rho_inf: float) -> GenAlphaParams:
+    p = GenAlphaParams()
+    _check(lib().mf_genalpha_params_from_rho(rho_inf, C.byref(p)))
+    return p
+
+
+def mf_genalpha_run(K: CSR, M_values, F, bc_mask, bc_val, phi, u, a, prm: GenAlphaParams, dt: float, steps: int,
+                    newton_tol: float = 1e-8, max_newton: int = 10, pcg_tol: float = 1e-12,
+                    pcg_max_iter: int = 100000, stream=None, allow=()):
+    """Returns (status, newton solves per step, PCG iterations per step) as numpy arrays."""
+    import numpy as np
+    nits = np.zeros(max(steps, 1), dtype=np.int64)
+    pits = np.zeros(max(steps, 1), dtype=np.int64)
+    st = _check(lib().mf_genalpha_run(C.byref(K), _ptr(M_values), _ptr(F), _ptr(bc_mask), _ptr(bc_val), _ptr(phi),
+                                      _ptr(u), _ptr(a), C.byref(prm), dt, steps, newton_tol, max_newton, pcg_tol,
+                                      pcg_max_iter, nits.ctypes.data, pits.ctypes.data, _stream(stream)), allow)
+    return st, nits[:steps], pits[:steps]
+
+
+def mf_genalpha_initial_rate(K: CSR, M_values, F, bc_mask, phi, u, pcg_tol: float = 1e-13,
+                             pcg_max_iter: int = 100000, stream=None) -> None:
+    _check(lib().mf_genalpha_initial_rate(C.byref(K), _ptr(M_values), _ptr(F), _ptr(bc_mask), _ptr(phi), _ptr(u),
+                                          pcg_tol, pcg_max_iter, _stream(stream)))
 
 
 def mf_pressure_mass_diag(mesh, pattern, out, stream=None) -> None:

@@ -358,8 +358,11 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
     g_msg[0] = 0;
     if (!mesh || !pattern || !coeffs || !K || !d || !K->values)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: NULL argument");
-    if (pattern->form != form || pattern->mesh != mesh)
+    const int pform = form == MF_FORM_CAPACITY ? MF_FORM_THERMAL : form;  // capacity: on a thermal pattern
+    if (pattern->form != pform || pattern->mesh != mesh)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: pattern was built for another form or mesh");
+    if (form == MF_FORM_CAPACITY && prec != MF_PREC_FP64)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: the capacity form is assembled in FP64");
     if (K->n_rows != pattern->n_rows || K->nnz != pattern->nnz || K->row_ptr != pattern->row_ptr ||
         K->col_idx != pattern->col_idx)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: K does not carry the pattern's CSR arrays");
@@ -430,6 +433,47 @@ extern "C" mf_status mf_assemble_boundary(const mf_facets *facets, const mf_face
     if (p->form == MF_FORM_THERMAL ? (!coeffs->h || !coeffs->t_env) : !coeffs->stress)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble_boundary: the form's facet coefficients are NULL");
     return mf_assemble_boundary_impl(facets, coeffs, K->values, d, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mf_status mf_genalpha_params_from_rho(double rho_inf, mf_genalpha_params *out)
+{
+    g_msg[0] = 0;
+    if (!out) return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_params_from_rho: NULL argument");
+    if (!(rho_inf >= 0.0 && rho_inf <= 1.0))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_params_from_rho: rho_inf must lie in [0, 1]");
+    return mf_genalpha_params_from_rho_impl(rho_inf, out);
+}
+
+extern "C" mf_status mf_genalpha_run(const mf_csr *K, const double *M_values, const double *F, const uint8_t *bc_mask,
+                                     const double *bc_val, double *phi, double *u, double *a,
+                                     const mf_genalpha_params *prm, double dt, int64_t steps, double newton_tol,
+                                     int32_t max_newton, double pcg_tol, int64_t pcg_max_iter, int64_t *newton_its,
+                                     int64_t *pcg_its, void *stream)
+{
+    g_msg[0] = 0;
+    if (!csr_ok(K) || !M_values || !F || !phi || !u || !a || !prm)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_run: NULL argument");
+    if ((bc_mask == nullptr) != (bc_val == nullptr))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_run: bc_mask and bc_val go together");
+    if (!(dt > 0.0) || steps < 0 || !(prm->b1 != 0.0) || !(prm->b2 != 0.0) || !(newton_tol > 0.0) ||
+        max_newton < 1 || !(pcg_tol > 0.0) || pcg_max_iter < 1)
+        return mf_fail(MF_ERR_INVALID_ARG,
+                       "mf_genalpha_run: dt > 0, steps >= 0, b1, b2 != 0, tolerances > 0, iteration caps >= 1");
+    return mf_genalpha_run_impl(K, M_values, F, bc_mask, bc_val, phi, u, a, prm, dt, steps, newton_tol, max_newton,
+                                pcg_tol, pcg_max_iter, newton_its, pcg_its, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mf_status mf_genalpha_initial_rate(const mf_csr *K, const double *M_values, const double *F,
+                                              const uint8_t *bc_mask, const double *phi, double *u, double pcg_tol,
+                                              int64_t pcg_max_iter, void *stream)
+{
+    g_msg[0] = 0;
+    if (!csr_ok(K) || !M_values || !F || !phi || !u)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_initial_rate: NULL argument");
+    if (!(pcg_tol > 0.0) || pcg_max_iter < 1)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_initial_rate: pcg_tol > 0 and pcg_max_iter >= 1");
+    return mf_genalpha_initial_rate_impl(K, M_values, F, bc_mask, phi, u, pcg_tol, pcg_max_iter,
+                                         static_cast<cudaStream_t>(stream));
 }
 
 extern "C" mf_status mf_pressure_mass_diag(const mf_mesh *mesh, const mf_pattern *pattern, double *out,

@@ -56,6 +56,18 @@ __global__ void __launch_bounds__(128) k_elem_thermal_q1(int64_t n_el, const dou
     if (e < n_el && !q1_translate(e, tr, kc, status)) elem_thermal_q1(e, X, conn, kc, f, map, out, status);
 }
 
+__global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict__ X,
+                                const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                const uint8_t *__restrict__ tr, const int32_t *__restrict__ map,
+                                double *__restrict__ out, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    if (elem == MF_P1_TRI) elem_capacity_p1(e, X, conn, kc, map, out, status);
+    else if (elem == MF_P2_TRI) elem_capacity_p2(e, X, conn, kc, map, out, status);
+    else if (!q1_translate(e, tr, kc, status)) elem_capacity_q1(e, X, conn, kc, map, out, status);
+}
+
 // Q1 elasticity, one element per thread.  The scaled gradients
 // sqrt(w detJ) gradN_a(q) of all 8 points go to shared memory (each thread its
 // own column, no synchronisation), then every block pair a <= b contracts
@@ -655,13 +667,21 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
     int *status = mf_status_word();
     if (!status) return mf_fail(MF_ERR_CUDA, "mf_assemble: status word unavailable");
     const int64_t ne = m->n_elems;
-    if (form == MF_FORM_THERMAL) {
-        const double f = c->source[0];
-        mf_prof_begin(m->elem == MF_P1_TRI   ? "elem_thermal_p1"
+    if (form == MF_FORM_THERMAL || form == MF_FORM_CAPACITY) {
+        const bool cap = form == MF_FORM_CAPACITY;
+        const double f = cap ? 0.0 : c->source[0];
+        // the translate shortcut of the capacity form takes element 0's unit-C
+        // capacity matrix (and its zero load) stored after the stiffness's
+        const double *kref = (cap && p->kref) ? p->kref + 73 : p->kref;
+        mf_prof_begin(cap ? "elem_capacity"
+                      : m->elem == MF_P1_TRI ? "elem_thermal_p1"
                       : m->elem == MF_P2_TRI ? "elem_thermal_p2"
                                              : "elem_thermal_q1",
                       st);
-        if (m->elem == MF_P1_TRI)
+        if (cap)
+            k_elem_capacity<<<nblk(ne, 128), 128, 0, st>>>(m->elem, ne, m->coords, m->conn, c->elem_coef, p->tr,
+                                                           p->elem_inc, p->scratch, status);
+        else if (m->elem == MF_P1_TRI)
             k_elem_thermal_p1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
                                                              p->scratch, status);
         else if (m->elem == MF_P2_TRI)
@@ -676,7 +696,7 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         mf_prof_begin("gather_scalar", st);
 #define MF_GATHER_TH(NPE)                                                                                         \
     k_gather_th<NPE><<<nblk(A.n_rows, GT_WARPS * (32 / th_lanes<NPE>())), GT_WARPS * 32, 0, st>>>(                 \
-        A.n_rows, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->inc_slot, p->scratch, p->kref, c->elem_coef, f,  \
+        A.n_rows, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->inc_slot, p->scratch, kref, c->elem_coef, f,     \
         c->bc_mask, c->bc_val, p->row_ptr, values, d)
         if (m->elem == MF_P1_TRI) MF_GATHER_TH(3);
         else if (m->elem == MF_P2_TRI) MF_GATHER_TH(6);

@@ -368,6 +368,94 @@ __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restr
 
 
 
+// Capacity (the rate term -C(T, T_t) of Sec. 4.1, tangent negated):
+// M_e[a][b] = C int_e N_a N_b, no load.  P1: C |e| (1 + delta_ab) / 12.  P2:
+// C det R[a][b], R the integrals of the quadratic basis over the reference
+// triangle per unit det = 2|e| (vertices, then the midpoints of edges (0,1),
+// (1,2), (2,0)).  Q1: 2 x 2 x 2 Gauss with detJ from the map coefficients,
+// exact on parallelepipeds.
+__device__ __forceinline__ void elem_capacity_p1(int64_t e, const double *__restrict__ X,
+                                                 const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                                 const int32_t *__restrict__ map, double *__restrict__ out,
+                                                 int *status)
+{
+    const double C = kc[e];
+    if (!isfinite(C)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double gl[3][2];
+    const double s = C * tri_affine(X, conn + 3 * e, gl) * (1.0 / 24.0);
+    const ThOut<3> W(map, e);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) out[W.base[a] + b] = a == b ? 2.0 * s : s;
+        out[W.ld[a]] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void elem_capacity_p2(int64_t e, const double *__restrict__ X,
+                                                 const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                                 const int32_t *__restrict__ map, double *__restrict__ out,
+                                                 int *status)
+{
+    constexpr double R[6][6] = {{6, -1, -1, 0, -4, 0},  {-1, 6, -1, 0, 0, -4},  {-1, -1, 6, -4, 0, 0},
+                                {0, 0, -4, 32, 16, 16}, {-4, 0, 0, 16, 32, 16}, {0, -4, 0, 16, 16, 32}};
+    const double C = kc[e];
+    if (!isfinite(C)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double gl[3][2];
+    const double s = C * tri_affine(X, conn + 6 * e, gl) * (1.0 / 360.0);
+    const ThOut<6> W(map, e);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+#pragma unroll
+        for (int b = 0; b < 6; ++b) out[W.base[a] + b] = s * R[a][b];
+        out[W.ld[a]] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void elem_capacity_q1(int64_t e, const double *__restrict__ X,
+                                                 const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                                 const int32_t *__restrict__ map, double *__restrict__ out,
+                                                 int *status)
+{
+    const double C = kc[e];
+    if (!isfinite(C)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double x[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[8 * e + a] + i];
+    double c[8][3];
+    q1_wht(x, c);
+#pragma unroll
+    for (int S = 1; S < 8; ++S)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c[S][i] *= (__popc(S) & 1) ? -0.125 : 0.125;
+    double Me[36] = {};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double Ji[3][3];
+        const double wd = q1_jac_coef(c, q, Ji);  // Gauss weights are 1
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double na = wd * q1_n(q, a);
+#pragma unroll
+            for (int b = a; b < 8; ++b, ++t) Me[t] = fma(na, q1_n(q, b), Me[t]);
+        }
+    }
+    const ThOut<8> W(map, e);
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+#pragma unroll
+        for (int b = a; b < 8; ++b, ++t) {
+            out[W.base[a] + b] = C * Me[t];
+            out[W.base[b] + a] = C * Me[t];
+        }
+        out[W.ld[a]] = 0.0;
+    }
+}
+
 // Thermal translate shortcut (Q1): true when element e is a translate of
 // element 0, whose unit matrices stand in for its own (the gather takes k_e
 // from the coefficients); k_e is still checked here.

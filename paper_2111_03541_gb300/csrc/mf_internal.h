@@ -70,7 +70,8 @@ struct mf_pattern {
     // thermal Q1: tr[e] = 1 when element e is an exact translate of element 0
     // (equal edge vectors x_a - x_0 in FP64), so K_e = k_e Kref and
     // d_e = f dref with kref = [Kref (8 x 8), dref (8)] element 0's unit-k,
-    // unit-f matrices; null when no element is a translate
+    // unit-f matrices, then [1.0], then [Mref (8 x 8), 0 (8)] its unit-C
+    // capacity matrix at kref + 73; null when no element is a translate
     uint8_t *tr = nullptr;
     double *kref = nullptr;
     int64_t n_translate = 0;
@@ -157,6 +158,14 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
 void mf_facets_free(mf_facets *f);
 mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c, double *values, double *d,
                                     cudaStream_t st);
+mf_status mf_genalpha_params_from_rho_impl(double rho, mf_genalpha_params *out);
+mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *F, const uint8_t *mask,
+                               const double *bval, double *phi, double *u, double *a, const mf_genalpha_params *prm,
+                               double dt, int64_t steps, double newton_tol, int32_t max_newton, double pcg_tol,
+                               int64_t pcg_max_iter, int64_t *newton_its, int64_t *pcg_its, cudaStream_t st);
+mf_status mf_genalpha_initial_rate_impl(const mf_csr *K, const double *Mv, const double *F, const uint8_t *mask,
+                                        const double *phi, double *u, double pcg_tol, int64_t pcg_max_iter,
+                                        cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);
 mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o,
                         mf_solve_info *info, cudaStream_t st);

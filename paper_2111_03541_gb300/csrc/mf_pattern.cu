@@ -284,11 +284,13 @@ __global__ void k_translate_flags(int64_t n_el, const double *__restrict__ X, co
     if ((threadIdx.x & 31) == 0 && bal) atomicAdd(count, (unsigned long long)__popc(bal));
 }
 
-// kref = element 0's matrix and load vector with k = 1, f = 1 (kref[72] holds the 1)
+// kref = element 0's matrix and load vector with k = 1, f = 1 (kref[72] holds
+// the 1), then its capacity matrix with C = 1 and a zero load at kref + 73
 __global__ void k_kref(const double *__restrict__ X, const int32_t *__restrict__ conn, double *kref, int *status)
 {
     kref[72] = 1.0;
     elem_thermal_q1(0, X, conn, kref + 72, 1.0, nullptr, kref, status);
+    elem_capacity_q1(0, X, conn, kref + 72, nullptr, kref + 73, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -607,7 +609,7 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
                 MF_CUDA(cudaFreeAsync(p->tr, st));
                 p->tr = nullptr;
             } else {
-                MF_CUDA(cudaMallocAsync(&p->kref, sizeof(double) * 73, st));
+                MF_CUDA(cudaMallocAsync(&p->kref, sizeof(double) * (73 + 72), st));
                 k_kref<<<1, 1, 0, st>>>(m->coords, m->conn, p->kref, status);
                 k_mark_translates<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, incv.ptr, incv.inc, p->tr, incv.loc);
             }

@@ -1,0 +1,238 @@
+"""Parity of the transient pieces with the CPU FP64 oracle, through the C ABI:
+the capacity matrix C int N_a N_b (MF_FORM_CAPACITY) and generalised-alpha
+time stepping (mf_genalpha_run, mf_genalpha_initial_rate).
+
+Capacity: pattern bit-exact, values row-scaled within 1e-12.  Time stepping:
+both sides solve every Newton step by Jacobi-PCG to a relative residual of
+1e-13, so the states agree to the solves' accuracy: within 1e-10 of the
+state's maximum after the steps run here.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2111_03541_gb300 as mf
+    mf.lib()
+    return mf
+
+
+def _partly_jittered_q1(n):
+    prob = gen.thermal_q1_problem(n, jitter=0.0)
+    X = prob["coords"].copy()
+    h = 1.0 / n
+    inner = (X[:, 0] > 1e-12) & (X[:, 0] < 0.4) & (np.abs(X[:, 1] - 0.5) < 0.5 - 1e-12) & \
+        (np.abs(X[:, 2] - 0.5) < 0.5 - 1e-12)
+    idx = np.nonzero(inner)[0]
+    X[idx] += 0.15 * h * (2.0 * gen.uniform(4321, 3 * idx.size).reshape(-1, 3) - 1.0)
+    prob["coords"] = X
+    return prob
+
+
+CAP = {
+    "p1_20": lambda: gen.thermal_p1_problem(20),
+    "p2_9": lambda: gen.thermal_p2_problem(9),
+    "q1_8": lambda: gen.thermal_q1_problem(8),
+    "q1_affine_11": lambda: gen.thermal_q1_problem(11, jitter=0.0),
+    "q1_partly_translate_10": lambda: _partly_jittered_q1(10),
+}
+
+
+def row_scaled_error(rp, val, ref):
+    n = rp.shape[0] - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    rmax = np.zeros(n)
+    np.maximum.at(rmax, rows, np.abs(ref))
+    emax = np.zeros(n)
+    np.maximum.at(emax, rows, np.abs(val - ref))
+    ok = rmax > 0
+    assert (emax[~ok] == 0).all()
+    return (emax[ok] / rmax[ok]).max()
+
+
+def _capacity_gpu(mf, P, C, bc=False):
+    import torch
+    vals = torch.empty(P.nnz, dtype=torch.float64, device="cuda")
+    d = torch.empty(P.n, dtype=torch.float64, device="cuda")
+    csr = mf.CSR(P.csr.n_rows, P.csr.nnz, P.csr.row_ptr, P.csr.col_idx, vals.data_ptr())
+    Ct = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    coeffs = P.make_coeffs(coef=Ct, bc=bc)
+    mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, coeffs, mf.MF_PREC_FP64, csr, d)
+    return vals, d, csr
+
+
+@pytest.mark.parametrize("case", list(CAP))
+def test_capacity_parity(mf, orc, case):
+    prob = CAP[case]()
+    C = gen.lognormal(77, prob["conn"].shape[0], 0.3)
+    P = mf.Problem(prob)
+    vals, d, _ = _capacity_gpu(mf, P, C)
+    rp, ci = P.csr_arrays()
+    rp, ci = rp.cpu().numpy(), ci.cpu().numpy()
+    ref = orc.capacity(prob, C)
+    assert np.array_equal(rp, ref["row_ptr"]) and np.array_equal(ci, ref["col"])
+    assert row_scaled_error(rp, vals.cpu().numpy(), ref["val"]) <= TOL
+    assert np.abs(d.cpu().numpy()).max() == 0.0
+
+
+def test_capacity_with_dirichlet(mf, orc):
+    prob = gen.thermal_q1_problem(6)
+    prob["bc_val"] = np.where(prob["bc_mask"] > 0, gen.normal(9, prob["bc_mask"].shape[0]), 0.0)
+    C = gen.lognormal(78, prob["conn"].shape[0], 0.3)
+    P = mf.Problem(prob)
+    vals, d, _ = _capacity_gpu(mf, P, C, bc=True)
+    ref = orc.capacity(prob, C)
+    ref["d"] = np.zeros(prob["coords"].shape[0])
+    orc.apply_dirichlet(ref, prob["bc_mask"], prob["bc_val"])
+    rp, _ = P.csr_arrays()
+    assert row_scaled_error(rp.cpu().numpy(), vals.cpu().numpy(), ref["val"]) <= TOL
+    assert np.abs(d.cpu().numpy() - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+
+
+def test_capacity_rejected_in_mixed_precision(mf):
+    import torch
+    P = mf.Problem(gen.thermal_p1_problem(4))
+    C = torch.ones(P.conn.shape[0], dtype=torch.float64, device="cuda")
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, P.make_coeffs(coef=C), mf.MF_PREC_MIXED, P.csr, P.d)
+    assert ei.value.status == mf.MF_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# generalised-alpha
+# ---------------------------------------------------------------------------
+
+def _transient_setup(mf, orc, prob, C):
+    """GPU K (domain + boundary terms, no elimination), M, F and the oracle's."""
+    import torch
+    P = mf.Problem(prob)
+    coeffs = P.make_coeffs(bc=False)
+    mf.mf_assemble(P.form, P.mesh, P.pattern, coeffs, mf.MF_PREC_FP64, P.csr, P.d)
+    if P.facets:
+        fc = mf.FacetCoeffs(h=P.facet_coeffs.h, t_env=P.facet_coeffs.t_env)
+        mf.mf_assemble_boundary(P.facets, fc, P.csr, P.d)
+    Mv, _, _ = _capacity_gpu(mf, P, C)
+    K = orc.assemble(prob, dirichlet=False)
+    M = orc.capacity(prob, C)
+    return P, Mv, K, M
+
+
+def _run_both(mf, orc, prob, C, rho, dt, steps, phi0):
+    import torch
+    P, Mv, K, M = _transient_setup(mf, orc, prob, C)
+    F = K["d"]
+    mask, bval = prob["bc_mask"], prob["bc_val"]
+    # oracle
+    u0o = orc.initial_rate(K, M, F, mask, np.where(mask > 0, bval, phi0))
+    po, uo, ao, itso = orc.genalpha(K, M, F, mask, bval, phi0, u0o, np.zeros_like(F), orc.genalpha_params(rho), dt,
+                                    steps)
+    # GPU
+    phi = torch.from_numpy(np.where(mask > 0, bval, phi0)).cuda()
+    u = torch.empty_like(phi)
+    a = torch.zeros_like(phi)
+    mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, P.bc_mask, phi, u)
+    assert np.abs(u.cpu().numpy() - u0o).max() <= 1e-10 * max(np.abs(u0o).max(), 1e-300)
+    prm = mf.mf_genalpha_params_from_rho(rho)
+    st, nits, pits = mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, a, prm, dt, steps,
+                                        pcg_tol=1e-13)
+    return P, Mv, (phi.cpu().numpy(), u.cpu().numpy(), nits, pits), (po, uo, itso)
+
+
+@pytest.mark.parametrize("kind,rho", [("p1", 0.5), ("p2", 0.0), ("q1", 0.8)])
+def test_genalpha_parity(mf, orc, kind, rho):
+    prob = {"p1": lambda: gen.thermal_p1_problem(16), "p2": lambda: gen.thermal_p2_problem(7),
+            "q1": lambda: gen.thermal_q1_problem(6)}[kind]()
+    left = prob["coords"][:, 0] <= 1e-14
+    prob["bc_mask"] = left.astype(np.uint8)
+    prob["bc_val"] = np.where(left, 0.3, 0.0)
+    sides = ("x1", "y0", "y1") if kind != "q1" else ("x1", "y0", "z1")
+    prob["facets"] = gen.convection_facets(prob, sides)
+    C = gen.lognormal(79, prob["conn"].shape[0], 0.3)
+    x = prob["coords"]
+    phi0 = np.sin(np.pi * x[:, 0]) * np.cos(0.5 * np.pi * x[:, 1])
+    P, Mv, (pg, ug, nits, pits), (po, uo, itso) = _run_both(mf, orc, prob, C, rho, 2e-3, 6, phi0)
+    assert np.array_equal(nits, itso) and (nits == 1).all()
+    assert np.abs(pg - po).max() <= 1e-10 * np.abs(po).max()
+    assert np.abs(ug - uo).max() <= 1e-9 * np.abs(uo).max()
+
+
+def test_genalpha_bit_reproducible(mf, orc):
+    import torch
+    prob = gen.thermal_q1_problem(6)
+    C = np.ones(prob["conn"].shape[0])
+    P, Mv, K, M = _transient_setup(mf, orc, prob, C)
+    prm = mf.mf_genalpha_params_from_rho(0.5)
+    out = []
+    for _ in range(2):
+        phi = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(phi)
+        a = torch.zeros_like(phi)
+        mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, a, prm, 1e-2, 4)
+        out.append((phi.clone(), u.clone()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 1.0])
+def test_genalpha_high_frequency_double_root(mf, rho):
+    # one dof, stiffness 1e8, unit capacity: phi_{n+2} - 2 lam phi_{n+1} + lam^2 phi_n = 0, lam = -rho_inf
+    import torch
+    rp = torch.tensor([0, 1], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([0], dtype=torch.int32, device="cuda")
+    kv = torch.tensor([1e8], dtype=torch.float64, device="cuda")
+    mv = torch.tensor([1.0], dtype=torch.float64, device="cuda")
+    F = torch.zeros(1, dtype=torch.float64, device="cuda")
+    K = mf.CSR(1, 1, rp.data_ptr(), ci.data_ptr(), kv.data_ptr())
+    phi = torch.ones(1, dtype=torch.float64, device="cuda")
+    u = torch.full((1,), -1e8, dtype=torch.float64, device="cuda")
+    a = torch.zeros(1, dtype=torch.float64, device="cuda")
+    prm = mf.mf_genalpha_params_from_rho(rho)
+    seq = []
+    for _ in range(8):
+        mf.mf_genalpha_run(K, mv, F, None, None, phi, u, a, prm, 1.0, 1, pcg_tol=1e-14)
+        seq.append(phi.item())
+    s = np.array(seq)
+    lam = -rho
+    assert np.abs(s[2:] - 2 * lam * s[1:-1] + lam ** 2 * s[:-2]).max() <= 1e-6 * np.abs(s).max()
+
+
+def test_genalpha_steady_state(mf, orc):
+    import torch
+    prob = gen.thermal_p1_problem(12)
+    C = np.ones(prob["conn"].shape[0])
+    P, Mv, K, M = _transient_setup(mf, orc, prob, C)
+    phi = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    u = torch.empty_like(phi)
+    a = torch.zeros_like(phi)
+    mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, P.bc_mask, phi, u)
+    prm = mf.mf_genalpha_params_from_rho(0.0)
+    mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, a, prm, 10.0, 12, pcg_tol=1e-13)
+    ref = orc.assemble(prob)
+    xs, _, _ = orc.pcg(ref, tol=1e-14)
+    assert np.abs(phi.cpu().numpy() - xs).max() <= 1e-10 * np.abs(xs).max()
+
+
+def test_genalpha_invalid_arguments(mf):
+    import torch
+    P = mf.Problem(gen.thermal_p1_problem(4))
+    P.assemble()
+    x = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    prm = mf.mf_genalpha_params_from_rho(0.5)
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_genalpha_run(P.csr, P.values, P.d, None, None, x, x, x, prm, 0.0, 1)
+    assert ei.value.status == mf.MF_ERR_INVALID_ARG
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_genalpha_params_from_rho(1.5)
+    assert ei.value.status == mf.MF_ERR_INVALID_ARG
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_genalpha_run(P.csr, P.values, P.d, P.bc_mask, None, x, x, x, prm, 0.1, 1)
+    assert ei.value.status == mf.MF_ERR_INVALID_ARG
