@@ -463,6 +463,62 @@ def _boundary_case(mf, P, prob, fac, sides, bc_mask, bc_val, hbm_gbs):
             "launches": 1, "l2": "flushed before each launch"}
 
 
+def _transient_case(mf, P, prob, fac, hbm_gbs, rho=0.5, dt=1e-3, steps=5):
+    """Generalised-alpha steps of the conduction system with capacity C = 1
+    and convection facets: K (domain + boundary terms), M and F assembled
+    once, then `steps` steps timed as a whole (Newton residuals, tangents,
+    PCG solves).  The tangent and residual kernels are timed per launch with
+    the library's kernel timing; their algorithmic bytes: tangent K, M values
+    and column (20 B) read and T written (8 B) per entry; residual K, M
+    values and column (20 B) per entry plus F, d, the two effective vectors
+    (32 B) per row."""
+    import numpy as np
+    import torch
+    dev = P.device
+    coeffs = P.make_coeffs(bc=False)
+    mf.mf_assemble(P.form, P.mesh, P.pattern, coeffs, mf.MF_PREC_FP64, P.csr, P.d)
+    e = torch.from_numpy(fac["elem"]).to(dev)
+    f = torch.from_numpy(fac["face"]).to(dev)
+    F_ = mf.mf_facets_create(P.mesh, P.pattern, e, f)
+    h = torch.from_numpy(fac["h"]).to(dev)
+    te = torch.from_numpy(fac["t_env"]).to(dev)
+    mf.mf_assemble_boundary(F_, mf.FacetCoeffs(h=h.data_ptr(), t_env=te.data_ptr()), P.csr, P.d)
+    Cc = torch.ones(P.conn.shape[0], dtype=torch.float64, device=dev)
+    Mv = torch.empty(P.nnz, dtype=torch.float64, device=dev)
+    dz = torch.empty(P.n, dtype=torch.float64, device=dev)
+    csrM = mf.CSR(P.csr.n_rows, P.csr.nnz, P.csr.row_ptr, P.csr.col_idx, Mv.data_ptr())
+    mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, P.make_coeffs(coef=Cc, bc=False), mf.MF_PREC_FP64, csrM,
+                   dz)
+    x = prob["coords"]
+    left = torch.from_numpy((x[:, 0] <= 1e-14).astype(np.uint8)).to(dev)
+    bv = torch.zeros(P.n, dtype=torch.float64, device=dev)
+    phi = torch.zeros(P.n, dtype=torch.float64, device=dev)
+    u = torch.empty_like(phi)
+    a = torch.zeros_like(phi)
+    mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, left, phi, u)
+    prm = mf.mf_genalpha_params_from_rho(rho)
+    mf.mf_set_kernel_timing(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, nits, pits = mf.mf_genalpha_run(P.csr, Mv, P.d, left, bv, phi, u, a, prm, dt, steps, pcg_tol=1e-10)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    kt = mf.mf_kernel_times()
+    mf.mf_set_kernel_timing(0)
+    mf.mf_facets_destroy(F_)
+    nnz, n = int(P.nnz), int(P.n)
+    out = {"steps": steps, "dt": dt, "rho_inf": rho, "ms_per_step": 1e3 * wall / steps,
+           "newton_solves": [int(v) for v in nits], "pcg_iterations": [int(v) for v in pits]}
+    for name, per_entry, per_row in (("ga_tangent", 28, 8), ("ga_residual", 20, 40)):
+        if name in kt:
+            cnt, tot = kt[name]
+            ms = tot / cnt
+            by = per_entry * nnz + per_row * n
+            out[name] = {"launches": cnt, "us": 1e3 * ms, "algorithmic_bytes": by,
+                         "achieved_gbs": by / (ms * 1e-3) / 1e9, "hbm_frac": by / (ms * 1e-3) / 1e9 / hbm_gbs}
+    return out
+
+
 def _solve_timed(P, **kw):
     import torch
     torch.cuda.synchronize()
@@ -555,6 +611,8 @@ def suite(dev):
     bv = torch.zeros(P.n, dtype=torch.float64, device=dev)
     out["B1_convection_q1_128"] = _boundary_case(mf, P, prob, gen.convection_facets(prob, sides), sides, x0, bv,
                                                  hbm)
+    # generalised-alpha transient on the same mesh: capacity 1, convection on five sides, T = 0 on x = 0
+    out["T1_genalpha_q1_128"] = _transient_case(mf, P, prob, gen.convection_facets(prob, sides), hbm)
     del P
     torch.cuda.empty_cache()
     # loaded boundary: a random stress on five sides of the 64^3 elasticity box (clamped at x = 0)

@@ -8,6 +8,7 @@ for profiling (ncu, the kernel-timing hooks) without the whole benchmark.
     python -m paper_2111_03541_gb300.cases batch --reps 5
     python -m paper_2111_03541_gb300.cases convection --n 128 --reps 5
     python -m paper_2111_03541_gb300.cases traction --n 64 --reps 5
+    python -m paper_2111_03541_gb300.cases genalpha --n 96 --reps 3
 
 elastic: Q1 elasticity on an n^3 jittered box (gen.elastic_problem), assembled
 reps times after one untimed call, then pcg-iters Jacobi-PCG iterations.  thermal-grf: Q1 thermal conduction with
@@ -20,6 +21,8 @@ default tiling, reps replays.  convection: the thermal-grf mesh with T = 0 on
 x = 0 and convection (gen.convection_facets) on the other five sides, the
 boundary terms added reps times.  traction: the elastic mesh with a random
 stress load (gen.traction_facets) on the five sides away from the clamp.
+genalpha: the convection case with capacity C = 1, reps generalised-alpha
+steps (rho_inf = 0.5, dt = 1e-3) from T = 0 with the consistent initial rate.
 Inputs are the seeded synthetic ones of `gen`; every step runs in libmf.
 """
 from __future__ import annotations
@@ -35,7 +38,8 @@ def _times(mf):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn", "oseen", "batch", "convection", "traction"))
+    ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn", "oseen", "batch", "convection", "traction",
+                                           "genalpha"))
     ap.add_argument("--n", type=int, default=48)
     ap.add_argument("--prec", choices=("fp64", "mixed"), default="mixed")
     ap.add_argument("--reps", type=int, default=5)
@@ -75,6 +79,32 @@ def main(argv=None):
             x, st, info = P.solve(tol=1e-8, max_iter=a.pcg_iters, check_every=50)
             torch.cuda.synchronize()
             print("pcg iterations", info.iterations, "residual", info.rel_residual)
+    elif a.case == "genalpha":
+        import numpy as np
+        prob = gen.grf_thermal_problem(a.n)
+        left = prob["coords"][:, 0] <= 1e-14
+        prob["bc_mask"] = left.astype(np.uint8)
+        prob["bc_val"] = np.zeros(left.shape[0])
+        prob["facets"] = gen.convection_facets(prob, ("x1", "y0", "y1", "z0", "z1"))
+        P = mf.Problem(prob)
+        mf.mf_assemble(P.form, P.mesh, P.pattern, P.make_coeffs(bc=False), mf.MF_PREC_FP64, P.csr, P.d)
+        mf.mf_assemble_boundary(P.facets, mf.FacetCoeffs(h=P.facet_coeffs.h, t_env=P.facet_coeffs.t_env), P.csr, P.d)
+        Mv = torch.empty(P.nnz, dtype=torch.float64, device="cuda")
+        dz = torch.empty(P.n, dtype=torch.float64, device="cuda")
+        csrM = mf.CSR(P.csr.n_rows, P.csr.nnz, P.csr.row_ptr, P.csr.col_idx, Mv.data_ptr())
+        Cc = torch.ones(P.conn.shape[0], dtype=torch.float64, device="cuda")
+        mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, P.make_coeffs(coef=Cc, bc=False), mf.MF_PREC_FP64,
+                       csrM, dz)
+        phi = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+        u = torch.empty_like(phi)
+        acc = torch.zeros_like(phi)
+        mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, P.bc_mask, phi, u)
+        prm = mf.mf_genalpha_params_from_rho(0.5)
+        mf.mf_set_kernel_timing(1)
+        st, nits, pits = mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, acc, prm, 1e-3, a.reps,
+                                            pcg_tol=1e-10)
+        torch.cuda.synchronize()
+        print("genalpha", _times(mf), "newton", nits.tolist(), "pcg", pits.tolist())
     elif a.case in ("convection", "traction"):
         import numpy as np
         sides = ("x1", "y0", "y1", "z0", "z1")

@@ -7,9 +7,9 @@
 // negated); Block D-3's tangent is T = c1 K + c2 / (b1 dt) M.
 //
 // Every vector update is one elementwise kernel; the residual is one
-// row-parallel pass over K and M (8 lanes per row) that also leaves per-block
-// partial sums of the four norms Newton tests, summed in a fixed order by a
-// one-block kernel, so a run is bit-reproducible; the tangent is one pass over
+// row-parallel pass over K and M (2 lanes per row) that also leaves per-block
+// partial sums of the four norms Newton tests, summed in a fixed order in two
+// levels, so a run is bit-reproducible; the tangent is one pass over
 // the values with the Dirichlet rows and columns set as it goes.  The linear
 // solves are the library's Jacobi-PCG.
 #include <cuda_runtime.h>
@@ -21,8 +21,12 @@
 namespace {
 
 constexpr int TPB = 256;
-constexpr int RL = 8;                 // lanes per row of the row kernels
-constexpr int RPB = TPB / RL;         // rows per block
+// row kernels: lanes per row and entries per lane whose loads are in flight
+// together (measured on the 128^3 Q1 system: the residual, FP64-heavier, is
+// fastest with 2 x 8, the tangent with 4 x 4)
+constexpr int RL = 2, RU = 8;         // residual
+constexpr int TL = 4, TU = 4;         // tangent
+constexpr int RPB = TPB / RL, TPBR = TPB / TL;  // rows per block
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -80,8 +84,9 @@ __device__ __forceinline__ double group_sum(double v)
     return v;
 }
 
-// D-2: d = F - K pt - M ut on free rows (0 on Dirichlet rows), and per block
-// the partial sums of d^2, F^2, (K pt)^2, (M ut)^2 over its free rows.
+// D-2: d = F - K pt - M ut on free rows (0 on Dirichlet rows), one group of
+// RL lanes per row and RPB rows per block, and per block the partial sums of
+// d^2, F^2, (K pt)^2, (M ut)^2 over its free rows.
 __global__ void __launch_bounds__(TPB) k_ga_residual(int64_t n, const int64_t *__restrict__ rp,
                                                      const int32_t *__restrict__ ci, const double *__restrict__ Kv,
                                                      const double *__restrict__ Mv, const double *__restrict__ F,
@@ -94,10 +99,23 @@ __global__ void __launch_bounds__(TPB) k_ga_residual(int64_t n, const int64_t *_
     const int64_t r = (int64_t)blockIdx.x * RPB + g;
     double kp = 0.0, mu = 0.0;
     if (r < n) {
-        for (int64_t t = rp[r] + lane; t < rp[r + 1]; t += RL) {
-            const int32_t c = ci[t];
-            kp = fma(Kv[t], pt[c], kp);
-            mu = fma(Mv[t], ut[c], mu);
+        const int64_t t1 = rp[r + 1];
+        for (int64_t tb = rp[r] + lane; tb < t1; tb += RL * RU) {
+            int32_t c[RU];
+            double kv[RU], mv[RU];
+#pragma unroll
+            for (int j = 0; j < RU; ++j) {
+                const int64_t t = tb + j * RL;
+                c[j] = t < t1 ? ci[t] : -1;
+                kv[j] = t < t1 ? Kv[t] : 0.0;
+                mv[j] = t < t1 ? Mv[t] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < RU; ++j)
+                if (c[j] >= 0) {
+                    kp = fma(kv[j], pt[c[j]], kp);
+                    mu = fma(mv[j], ut[c[j]], mu);
+                }
         }
     }
     kp = group_sum(kp);
@@ -126,12 +144,16 @@ __global__ void __launch_bounds__(TPB) k_ga_residual(int64_t n, const int64_t *_
     }
 }
 
-// fixed-order sum of the block partials: out[k] = sum_b part[4 b + k]
-__global__ void k_ga_norms(int64_t nb, const double *__restrict__ part, double *__restrict__ out)
+// fixed-order sums of nb partial quadruples: block b adds its contiguous
+// chunk of NCHUNK quadruples (thread k its k-th stride, then a fixed tree)
+constexpr int NCHUNK = 4096;
+
+__global__ void k_ga_sum4(int64_t nb, const double *__restrict__ part, double *__restrict__ out)
 {
     __shared__ double sh[TPB][4];
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t b = threadIdx.x; b < nb; b += TPB)
+    const int64_t b0 = (int64_t)blockIdx.x * NCHUNK, b1 = min(nb, b0 + NCHUNK);
+    for (int64_t b = b0 + threadIdx.x; b < b1; b += TPB)
         for (int k = 0; k < 4; ++k) s[k] += part[4 * b + k];
     for (int k = 0; k < 4; ++k) sh[threadIdx.x][k] = s[k];
     __syncthreads();
@@ -140,7 +162,7 @@ __global__ void k_ga_norms(int64_t nb, const double *__restrict__ part, double *
             for (int k = 0; k < 4; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + o][k];
         __syncthreads();
     }
-    if (threadIdx.x < 4) out[threadIdx.x] = sh[0][threadIdx.x];
+    if (threadIdx.x < 4) out[4 * (int64_t)blockIdx.x + threadIdx.x] = sh[0][threadIdx.x];
 }
 
 // D-3: T = c1 K + s M, Dirichlet rows the identity, Dirichlet columns zero
@@ -150,32 +172,50 @@ __global__ void __launch_bounds__(TPB) k_ga_tangent(int64_t n, const int64_t *__
                                                     const double *__restrict__ Mv, double c1, double s,
                                                     const uint8_t *__restrict__ mask, double *__restrict__ Tv)
 {
-    const int lane = threadIdx.x % RL;
-    const int64_t r = (int64_t)blockIdx.x * RPB + threadIdx.x / RL;
+    const int lane = threadIdx.x % TL;
+    const int64_t r = (int64_t)blockIdx.x * TPBR + threadIdx.x / TL;
     if (r >= n) return;
     const bool fixed = mask && mask[r];
-    for (int64_t t = rp[r] + lane; t < rp[r + 1]; t += RL) {
-        const int32_t c = ci[t];
-        double v;
-        if (fixed) v = c == r ? 1.0 : 0.0;
-        else if (mask && mask[c]) v = 0.0;
-        else v = fma(c1, Kv[t], s * Mv[t]);
-        Tv[t] = v;
+    const int64_t t1 = rp[r + 1];
+    for (int64_t tb = rp[r] + lane; tb < t1; tb += TL * TU) {
+        int32_t c[TU];
+        double kv[TU], mv[TU];
+        bool mc[TU];
+#pragma unroll
+        for (int j = 0; j < TU; ++j) {
+            const int64_t t = tb + j * TL;
+            c[j] = t < t1 ? ci[t] : -1;
+            kv[j] = t < t1 ? Kv[t] : 0.0;
+            mv[j] = t < t1 ? Mv[t] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < TU; ++j) mc[j] = mask && c[j] >= 0 && mask[c[j]];
+#pragma unroll
+        for (int j = 0; j < TU; ++j) {
+            if (c[j] < 0) continue;
+            double v;
+            if (fixed) v = c[j] == r ? 1.0 : 0.0;
+            else if (mc[j]) v = 0.0;
+            else v = fma(c1, kv[j], s * mv[j]);
+            Tv[tb + j * TL] = v;
+        }
     }
 }
 
-// D-4: dphi += x and the other increments from the constraints
+// D-4: dphi += x and the other increments from the constraints.  The host
+// passes 1 / dt, 1 / b1, 1 / b2: an FP64 division costs tens of FP64
+// instructions at 1/58 of the FP32 rate here.
 __global__ void k_ga_correct(int64_t n, const uint8_t *__restrict__ mask, const double *__restrict__ x,
                              const double *__restrict__ u, const double *__restrict__ a, double *dphi, double *du,
-                             double *da, double dt, double b1, double b2)
+                             double *da, double idt, double ib1, double ib2)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || (mask && mask[i])) return;
     const double p = dphi[i] + x[i];
-    const double v = (p / dt - u[i]) / b1;
+    const double v = (p * idt - u[i]) * ib1;
     dphi[i] = p;
     du[i] = v;
-    da[i] = (v / dt - a[i]) / b2;
+    da[i] = (v * idt - a[i]) * ib2;
 }
 
 }  // namespace
@@ -200,8 +240,9 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
                                int64_t pcg_max_iter, int64_t *newton_its, int64_t *pcg_its, cudaStream_t st)
 {
     const int64_t n = K->n_rows, nnz = K->nnz;
-    const unsigned gv = nblk(n, TPB), gr = nblk(n, RPB);
-    double *buf = nullptr, *Tv = nullptr, *part = nullptr, *norms = nullptr;
+    const unsigned gv = nblk(n, TPB), gr = nblk(n, RPB), nc = nblk(gr, NCHUNK);
+    if (nc > NCHUNK) return mf_fail(MF_ERR_UNSUPPORTED, "mf_genalpha_run: more than 2^34 rows");
+    double *buf = nullptr, *Tv = nullptr, *part = nullptr, *part2 = nullptr, *norms = nullptr;
     MF_CUDA(cudaMallocAsync(&buf, sizeof(double) * 7 * n, st));
     double *dphi = buf, *du = buf + n, *da = buf + 2 * n, *pt = buf + 3 * n, *ut = buf + 4 * n, *d = buf + 5 * n,
            *x = buf + 6 * n;
@@ -210,11 +251,13 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
         cudaFreeAsync(buf, st);
         cudaFreeAsync(Tv, st);
         cudaFreeAsync(part, st);
+        cudaFreeAsync(part2, st);
         cudaFreeAsync(norms, st);
         return s;
     };
     if (cudaMallocAsync(&Tv, sizeof(double) * nnz, st) != cudaSuccess ||
         cudaMallocAsync(&part, sizeof(double) * 4 * gr, st) != cudaSuccess ||
+        cudaMallocAsync(&part2, sizeof(double) * 4 * nc, st) != cudaSuccess ||
         cudaMallocAsync(&norms, sizeof(double) * 4, st) != cudaSuccess)
         return done(mf_fail(MF_ERR_OOM, "mf_genalpha_run: device allocation"));
     mf_csr T = *K;
@@ -236,7 +279,8 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
             mf_prof_begin("ga_residual", st);
             k_ga_effective<<<gv, TPB, 0, st>>>(n, phi, u, dphi, du, prm->c1, prm->c2, pt, ut);
             k_ga_residual<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, F, mask, pt, ut, d, part);
-            k_ga_norms<<<1, TPB, 0, st>>>(gr, part, norms);
+            k_ga_sum4<<<nc, TPB, 0, st>>>(gr, part, part2);
+            k_ga_sum4<<<1, TPB, 0, st>>>(nc, part2, norms);
             mf_prof_end(st);
             double h[4];
             if (cudaMemcpyAsync(h, norms, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -252,7 +296,8 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
                 break;
             }
             mf_prof_begin("ga_tangent", st);
-            k_ga_tangent<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, prm->c1, s, mask, Tv);
+            k_ga_tangent<<<nblk(n, TPBR), TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, prm->c1, s, mask,
+                                                        Tv);
             mf_prof_end(st);
             if (cudaMemsetAsync(x, 0, sizeof(double) * n, st) != cudaSuccess)
                 return done(mf_cuda_check(cudaGetLastError(), "mf_genalpha_run"));
@@ -263,7 +308,7 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
                 rc = ss;
                 break;
             }
-            k_ga_correct<<<gv, TPB, 0, st>>>(n, mask, x, u, a, dphi, du, da, dt, prm->b1, prm->b2);
+            k_ga_correct<<<gv, TPB, 0, st>>>(n, mask, x, u, a, dphi, du, da, 1.0 / dt, 1.0 / prm->b1, 1.0 / prm->b2);
             ++it;
         }
         if (newton_its) newton_its[m] = it;
@@ -301,7 +346,7 @@ mf_status mf_genalpha_initial_rate_impl(const mf_csr *K, const double *Mv, const
         cudaMemsetAsync(u, 0, sizeof(double) * n, st) != cudaSuccess)
         return done(mf_cuda_check(cudaGetLastError(), "mf_genalpha_initial_rate"));
     k_ga_residual<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, F, mask, phi, zero, rhs, part);
-    k_ga_tangent<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, 0.0, 1.0, mask, Tv);
+    k_ga_tangent<<<nblk(n, TPBR), TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, 0.0, 1.0, mask, Tv);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return done(mf_cuda_check(e, "mf_genalpha_initial_rate"));
     mf_csr T = *K;
