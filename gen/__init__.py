@@ -279,6 +279,18 @@ def convection_facets(mesh: dict, sides, seed: int = SEED_FACET, h_sigma: float 
     return {"elem": e, "face": f, "h": lognormal(seed, nf, h_sigma), "t_env": 0.5 + uniform(seed + 1, nf)}
 
 
+def radiation_facets(mesh: dict, sides, es=None, t_env=None, seed: int = SEED_FACET) -> dict:
+    """Radiation data on the given sides: per facet es = e_m sigma^b
+    (dimensionless; default uniform in [0.5, 1.0), draw f of stream seed + 3)
+    and T_env (default uniform in [1.0, 1.5), draw f of stream seed + 4), or
+    the constants given."""
+    e, f = box_facets(mesh, sides)
+    nf = e.shape[0]
+    es_ = 0.5 + 0.5 * uniform(seed + 3, nf) if es is None else np.full(nf, float(es))
+    te_ = 1.0 + 0.5 * uniform(seed + 4, nf) if t_env is None else np.full(nf, float(t_env))
+    return {"elem": e, "face": f, "es": es_, "t_env": te_}
+
+
 def traction_facets(mesh: dict, sides, stress=None, seed: int = SEED_FACET) -> dict:
     """Loaded-boundary data on the given sides: a 3 x 3 stress sigma^l per
     facet (row-major), the given one on every facet or standard normals

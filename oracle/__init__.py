@@ -49,6 +49,12 @@ class Problem(C.Structure):
                 ("f_stress", C.c_void_p)]
 
 
+class Radiation(C.Structure):
+    _fields_ = [("elem", C.c_int), ("dim", C.c_int), ("npe", C.c_int), ("coords", C.c_void_p),
+                ("conn", C.c_void_p), ("n_facets", C.c_int64), ("f_elem", C.c_void_p), ("f_face", C.c_void_p),
+                ("es", C.c_void_p), ("tenv", C.c_void_p)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -67,7 +73,8 @@ def lib():
         _lib.or_elem_capacity.argtypes = [i, vp, d, vp]
         _lib.or_elem_capacity.restype = d
         _lib.or_genalpha.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, d, d, d, i64, d, i, d,
-                                     vp]
+                                     vp, C.POINTER(Radiation)]
+        _lib.or_facet_radiation.argtypes = [i, vp, d, d, vp, vp, vp]
         _lib.or_genalpha.restype = i
         _lib.or_facet_nodes.argtypes = [i, i, vp]
         _lib.or_facet_thermal.argtypes = [i, vp, d, d, vp, vp]
@@ -394,9 +401,22 @@ def initial_rate(K: dict, M: dict, F, mask, phi0) -> np.ndarray:
     return u0
 
 
+def facet_radiation(elem: int, Xf, es: float, t_env: float, Tf):
+    """Radiation tangent and load of one facet at nodal temperatures Tf: (Kf, rf)."""
+    Xf = np.ascontiguousarray(Xf, dtype=np.float64)
+    Tf = np.ascontiguousarray(Tf, dtype=np.float64)
+    nf = Xf.shape[0]
+    Kf = np.zeros((nf, nf))
+    rf = np.zeros(nf)
+    lib().or_facet_radiation(elem, _p(Xf), es, t_env, _p(Tf), _p(Kf), _p(rf))
+    return Kf, rf
+
+
 def genalpha(K: dict, M: dict, F, mask, bval, phi, u, a, prm: dict, dt: float, steps: int,
-             newton_tol: float = 1e-8, max_newton: int = 10, pcg_tol: float = 1e-13):
-    """Runs or_genalpha; returns (phi, u, a, newton solves per step)."""
+             newton_tol: float = 1e-8, max_newton: int = 10, pcg_tol: float = 1e-13, prob=None, radiation=None):
+    """Runs or_genalpha; returns (phi, u, a, newton solves per step).  With
+    ``radiation`` (dict elem, face, es, t_env of facets of ``prob``'s mesh)
+    the radiation terms enter the residual and the tangent."""
     n = K["d"].shape[0] if "d" in K else K["row_ptr"].shape[0] - 1
     phi = np.array(phi, dtype=np.float64)
     u = np.array(u, dtype=np.float64)
@@ -405,9 +425,23 @@ def genalpha(K: dict, M: dict, F, mask, bval, phi, u, a, prm: dict, dt: float, s
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     bval = np.ascontiguousarray(bval, dtype=np.float64)
     its = np.zeros(max(steps, 1), dtype=np.int64)
+    rad = None
+    keep = []
+    if radiation is not None:
+        def arr(x, dt_):
+            x = np.ascontiguousarray(x, dtype=dt_)
+            keep.append(x)
+            return x
+        X = arr(prob["coords"], np.float64)
+        cn = arr(prob["conn"], np.int32)
+        rad = Radiation(elem=ELEM[prob["elem"]], dim=X.shape[1], npe=cn.shape[1], coords=_p(X), conn=_p(cn),
+                        n_facets=len(radiation["elem"]), f_elem=_p(arr(radiation["elem"], np.int32)),
+                        f_face=_p(arr(radiation["face"], np.uint8)), es=_p(arr(radiation["es"], np.float64)),
+                        tenv=_p(arr(radiation["t_env"], np.float64)))
     rc = lib().or_genalpha(n, _p(K["row_ptr"]), _p(K["col"]), _p(K["val"]), _p(M["val"]), _p(F), _p(mask),
                            _p(bval), _p(phi), _p(u), _p(a), prm["b1"], prm["b2"], prm["c1"], prm["c2"], prm["c3"],
-                           dt, steps, newton_tol, max_newton, pcg_tol, _p(its))
+                           dt, steps, newton_tol, max_newton, pcg_tol, _p(its),
+                           C.byref(rad) if rad is not None else None)
     if rc == -4:
         raise MemoryError("oracle generalised-alpha")
     if rc:

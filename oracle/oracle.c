@@ -510,6 +510,33 @@ void or_facet_traction_q1(int face, const double *Xf, const double *sigma, doubl
     }
 }
 
+/* Radiation on one facet (Sec. 4.1, e_m sigma^b (T, T_env^4 - T^4)) at the
+ * facet nodes' temperatures Tf, es = e_m sigma^b:
+ *   rf[m]      = sum_q w_q |J_q| es N_m (T_env^4 - T_q^4),   T_q = sum_b N_b T_b,
+ *   Kf[m][m'] = sum_q w_q |J_q| 4 es N_m N_m' T_q^3  (= -d rf[m] / d T_m').
+ * Rule and |J| as or_facet_thermal. */
+void or_facet_radiation(int elem, const double *Xf, double es, double tenv, const double *Tf, double *Kf,
+                        double *rf)
+{
+    double pts[8], w[4], N[4], A[3];
+    const int nq = facet_quad(elem, pts, w);
+    const int pdim = elem == OR_Q1 ? 2 : 1;
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : 4);
+    for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
+    for (int a = 0; a < nf; ++a) rf[a] = 0.0;
+    const double te4 = tenv * tenv * tenv * tenv;
+    for (int q = 0; q < nq; ++q) {
+        facet_point(elem, Xf, pts + pdim * q, N, A);
+        const double J = elem == OR_Q1 ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
+        double T = 0.0;
+        for (int b = 0; b < nf; ++b) T += N[b] * Tf[b];
+        for (int a = 0; a < nf; ++a) {
+            rf[a] += w[q] * J * es * N[a] * (te4 - T * T * T * T);
+            for (int b = 0; b < nf; ++b) Kf[a * nf + b] += w[q] * J * 4.0 * es * N[a] * N[b] * T * T * T;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Global assembly (Block B-3/B-4 numbering, Block D-2/D-3 accumulation).    */
 /* Every element emits COO triplets (row, col, value) in element order, local */
@@ -1036,6 +1063,9 @@ void or_conv3d_bwd_weight(int64_t nz, int64_t ny, int64_t nx, int ci_n, int co_n
 /*  D-2  d; stop when ||d|| <= newton_tol ||d_0|| (d_0: the step's first),  */
 /*       or ||d|| <= 1e-13 (||F|| + ||K phi~|| + ||M u~||), the level below  */
 /*       which rounding decides d;                                           */
+/* With radiation facets (rad != NULL, Sec. 4.1 e_m sigma^b (T, T_env^4 -   */
+/* T^4)), F becomes F + R(phi~) (in the rounding floor too) and the tangent  */
+/* gains c1 times the radiation tangent 4 e_m sigma^b int N_a N_b T~^3.      */
 /*  D-3/4  T x = d by Jacobi-PCG, dphi += x, and du, da from the             */
 /*       constraints: du = (dphi / dt - u) / b1, da = (du / dt - a) / b2.    */
 /* After the last step the increments are applied (C-1), so phi, u, a hold   */
@@ -1043,19 +1073,58 @@ void or_conv3d_bwd_weight(int64_t nz, int64_t ny, int64_t nx, int ci_n, int co_n
 /* solves of step m.  Returns 0, or -1 if a step hit max_newton without      */
 /* converging, -4 on allocation failure.                                     */
 /* ------------------------------------------------------------------------ */
+/* Radiation facets of a thermal mesh for or_genalpha (may be absent). */
+typedef struct {
+    int elem, dim, npe;
+    const double *coords;
+    const int32_t *conn;
+    int64_t n_facets;
+    const int32_t *f_elem;
+    const uint8_t *f_face;
+    const double *es;    /* [n_facets] e_m sigma^b */
+    const double *tenv;  /* [n_facets] */
+} or_radiation;
+
+/* Adds the radiation loads at temperatures T to Fe (all rows) and, with
+ * Tv != NULL, scale times the radiation tangent into the CSR values Tv. */
+static void radiation_terms(const or_radiation *rd, const int64_t *rp, const int32_t *ci, const double *T,
+                            double *Fe, double *Tv, double scale)
+{
+    for (int64_t f = 0; f < rd->n_facets; ++f) {
+        int loc[4];
+        const int nf = or_facet_nodes(rd->elem, rd->f_face[f], loc);
+        int64_t node[4];
+        double Xf[12], Tf[4], Kf[16], rf[4];
+        for (int m = 0; m < nf; ++m) {
+            node[m] = rd->conn[(int64_t)rd->f_elem[f] * rd->npe + loc[m]];
+            Tf[m] = T[node[m]];
+            for (int i = 0; i < rd->dim; ++i) Xf[rd->dim * m + i] = rd->coords[node[m] * rd->dim + i];
+        }
+        or_facet_radiation(rd->elem, Xf, rd->es[f], rd->tenv[f], Tf, Kf, rf);
+        for (int a = 0; a < nf; ++a) {
+            Fe[node[a]] += rf[a];
+            if (!Tv) continue;
+            for (int b = 0; b < nf; ++b)
+                for (int64_t t = rp[node[a]]; t < rp[node[a] + 1]; ++t)
+                    if (ci[t] == node[b]) Tv[t] += scale * Kf[a * nf + b];
+        }
+    }
+}
+
 int or_genalpha(int64_t n, const int64_t *rp, const int32_t *ci, const double *Kv, const double *Mv,
                 const double *F, const uint8_t *mask, const double *bval, double *phi, double *u, double *a,
                 double b1, double b2, double c1, double c2, double c3, double dt, int64_t steps,
-                double newton_tol, int max_newton, double pcg_tol, int64_t *newton_its)
+                double newton_tol, int max_newton, double pcg_tol, int64_t *newton_its, const or_radiation *rad)
 {
     const int64_t nnz = rp[n];
     double *dphi = calloc((size_t)n, sizeof(double)), *du = calloc((size_t)n, sizeof(double));
     double *da = calloc((size_t)n, sizeof(double)), *pt = malloc(sizeof(double) * n);
     double *ut = malloc(sizeof(double) * n), *d = malloc(sizeof(double) * n), *x = malloc(sizeof(double) * n);
     double *Tv = malloc(sizeof(double) * nnz), *zero = calloc((size_t)n, sizeof(double));
-    double *y = malloc(sizeof(double) * n);
-    if (!dphi || !du || !da || !pt || !ut || !d || !x || !Tv || !zero || !y) {
+    double *y = malloc(sizeof(double) * n), *Fe = malloc(sizeof(double) * n);
+    if (!dphi || !du || !da || !pt || !ut || !d || !x || !Tv || !zero || !y || !Fe) {
         free(dphi); free(du); free(da); free(pt); free(ut); free(d); free(x); free(Tv); free(zero); free(y);
+        free(Fe);
         return -4;
     }
     int rc = 0;
@@ -1079,16 +1148,18 @@ int or_genalpha(int64_t n, const int64_t *rp, const int32_t *ci, const double *K
                 pt[i] = phi[i] + c1 * dphi[i];
                 ut[i] = u[i] + c2 * du[i];
             }
-            or_spmv(n, rp, ci, Kv, pt, d);         /* D-2 */
+            for (int64_t i = 0; i < n; ++i) Fe[i] = F[i];  /* D-2: loads incl. radiation at phi~ */
+            if (rad) radiation_terms(rad, rp, ci, pt, Fe, NULL, 0.0);
+            or_spmv(n, rp, ci, Kv, pt, d);
             or_spmv(n, rp, ci, Mv, ut, y);
             double r2 = 0.0, f2 = 0.0, k2 = 0.0, m2 = 0.0;
             for (int64_t i = 0; i < n; ++i) {
                 if (!mask[i]) {
-                    f2 += F[i] * F[i];
+                    f2 += Fe[i] * Fe[i];
                     k2 += d[i] * d[i];
                     m2 += y[i] * y[i];
                 }
-                d[i] = mask[i] ? 0.0 : F[i] - d[i] - y[i];
+                d[i] = mask[i] ? 0.0 : Fe[i] - d[i] - y[i];
                 r2 += d[i] * d[i];
             }
             const double r = sqrt(r2);
@@ -1099,6 +1170,7 @@ int or_genalpha(int64_t n, const int64_t *rp, const int32_t *ci, const double *K
             if (it == max_newton) { rc = -1; break; }
             const double s = c2 / (b1 * dt);       /* D-3 */
             for (int64_t t = 0; t < nnz; ++t) Tv[t] = c1 * Kv[t] + s * Mv[t];
+            if (rad) radiation_terms(rad, rp, ci, pt, y, Tv, c1);  /* y: scratch */
             or_dirichlet(n, rp, ci, Tv, d, mask, zero);
             for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
             double rr;
@@ -1120,5 +1192,6 @@ int or_genalpha(int64_t n, const int64_t *rp, const int32_t *ci, const double *K
         a[i] += da[i];
     }
     free(dphi); free(du); free(da); free(pt); free(ut); free(d); free(x); free(Tv); free(zero); free(y);
+    free(Fe);
     return rc;
 }

@@ -1,12 +1,16 @@
 """Pins of the oracle's transient pieces: the capacity matrix C int N_a N_b
-(the rate term -C(T, T_t) of Sec. 4.1) and generalised-alpha time stepping
-(Sec. 2.1 Eq. time_constraints and time_effective, Blocks C and D).
+(the rate term -C(T, T_t) of Sec. 4.1), generalised-alpha time stepping
+(Sec. 2.1 Eq. time_constraints and time_effective, Blocks C and D) and the
+nonlinear radiation term e_m sigma^b (T, T_env^4 - T^4) of Sec. 4.1 inside its
+Newton sub-steps.
 
 Expected values come from exact barycentric integration, Kronecker products of
 1D integrals, the total volume, the double root -rho_inf of the first-order
 generalised-alpha amplification matrix at infinite stiffness (Jansen,
 Whiting and Hulbert 2000), exact solutions of scalar ODEs, the matrix
-exponential of the semi-discrete system, and the steady state.
+exponential of the semi-discrete system, the steady state, closed-form facet
+integrals at constant temperature, central differences of the radiation
+load, and the exact solution of a radiating slab.
 """
 from fractions import Fraction
 from math import factorial
@@ -201,3 +205,86 @@ def test_steady_state_reached(orc):
     ps = np.linalg.solve(Kd, F[free])
     assert np.abs(phi[free] - ps).max() < 1e-10 * np.abs(ps).max()
     assert np.abs(u).max() < 1e-8 * np.abs(ps).max()
+
+
+# ---------------------------------------------------------------------------
+# radiation e_m sigma^b (T, T_env^4 - T^4) (Sec. 4.1) inside the Newton steps
+# ---------------------------------------------------------------------------
+
+def test_radiation_facet_constant_temperature(orc):
+    es, te, T = 0.7, 1.3, 0.9
+    # P1 edge of length 1, P2 edge of length 1.3, Q1 unit square face
+    cases = [(orc.P1, np.array([[0.1, 0.2], [0.7, 1.0]]), 1.0, np.array([0.5, 0.5]),
+              np.array([[1 / 3, 1 / 6], [1 / 6, 1 / 3]])),
+             (orc.P2, np.array([[0.3, -0.2], [-0.9, 0.3], [-0.3, 0.05]]), 1.3, np.array([1 / 6, 1 / 6, 2 / 3]),
+              np.array([[4, -1, 2], [-1, 4, 2], [2, 2, 16]]) / 30.0),
+             (orc.Q1, np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], float), 1.0, np.full(4, 0.25),
+              np.kron(np.array([[2, 1], [1, 2]]) / 6.0, np.array([[2, 1], [1, 2]]) / 6.0))]
+    for elem, X, L, intN, mass in cases:
+        Kf, rf = orc.facet_radiation(elem, X, es, te, np.full(X.shape[0], T))
+        assert np.abs(rf - es * (te ** 4 - T ** 4) * L * intN).max() < 1e-15
+        assert np.abs(Kf - 4 * es * T ** 3 * L * mass).max() < 1e-15
+
+
+def test_radiation_tangent_is_the_derivative(orc):
+    rng = np.random.default_rng(4)
+    X = np.array([[a & 1, (a >> 1) & 1, 0.0] for a in range(4)], float) + rng.uniform(-0.2, 0.2, (4, 3))
+    T = 0.8 + 0.4 * rng.random(4)
+    Kf, rf = orc.facet_radiation(orc.Q1, X, 0.6, 1.2, T)
+    h = 1e-6
+    for b in range(4):
+        e = np.zeros(4)
+        e[b] = h
+        _, rp = orc.facet_radiation(orc.Q1, X, 0.6, 1.2, T + e)
+        _, rm = orc.facet_radiation(orc.Q1, X, 0.6, 1.2, T - e)
+        assert np.abs(-(rp - rm) / (2 * h) - Kf[:, b]).max() < 1e-8 * np.abs(Kf).max()
+
+
+@pytest.mark.parametrize("kind", ["p1", "p2", "q1"])
+def test_radiation_slab_steady_state(orc, kind):
+    # T = T0 on x = 0, k dT/dn = es (T_env^4 - T^4) on x = 1, insulated
+    # elsewhere, no source: T = T0 + b x with k b = es (T_env^4 - (T0 + b)^4)
+    import scipy.optimize
+    prob = {"p1": lambda: gen.thermal_p1_problem(6), "p2": lambda: gen.thermal_p2_problem(4),
+            "q1": lambda: gen.thermal_q1_problem(3)}[kind]()
+    k, es, T0, Te = 1.7, 0.8, 0.4, 1.5
+    prob["coef"] = np.full(prob["conn"].shape[0], k)
+    prob["source"] = 0.0
+    x = prob["coords"]
+    left = x[:, 0] <= 1e-14
+    prob["bc_mask"] = left.astype(np.uint8)
+    prob["bc_val"] = np.where(left, T0, 0.0)
+    K = orc.assemble(prob, dirichlet=False)
+    M = orc.capacity(prob, np.ones(prob["conn"].shape[0]))
+    rad = gen.radiation_facets(prob, ("x1",), es=es, t_env=Te)
+    phi0 = np.where(left, T0, T0)
+    u0 = np.zeros_like(phi0)
+    phi, u, a, its = orc.genalpha(K, M, K["d"], prob["bc_mask"], prob["bc_val"], phi0, u0, np.zeros_like(phi0),
+                                  orc.genalpha_params(0.0), 50.0, 8, prob=prob, radiation=rad)
+    # the physical root: T(1) = T0 + b > 0
+    b = scipy.optimize.brentq(lambda b: k * b - es * (Te ** 4 - (T0 + b) ** 4), -T0, 5.0, xtol=1e-15)
+    assert np.abs(phi - (T0 + b * x[:, 0])).max() < 1e-10
+    assert its.max() <= 8 and its[0] >= 3  # nonlinear: several Newton solves, converging fast
+
+
+def test_radiation_newton_uses_the_exact_tangent(orc):
+    # with the tangent c1 (K + K_rad) + c2 / (b1 dt) M Newton converges
+    # quadratically: a few solves per step (a tangent with the wrong scale on
+    # the radiation part needs 11 or more here)
+    prob = gen.thermal_q1_problem(3)
+    k, T0, Te = 1.7, 0.4, 1.5
+    prob["coef"] = np.full(prob["conn"].shape[0], k)
+    prob["source"] = 0.0
+    x = prob["coords"]
+    left = x[:, 0] <= 1e-14
+    prob["bc_mask"] = left.astype(np.uint8)
+    prob["bc_val"] = np.where(left, T0, 0.0)
+    K = orc.assemble(prob, dirichlet=False)
+    M = orc.capacity(prob, np.ones(prob["conn"].shape[0]))
+    rad = gen.radiation_facets(prob, ("x1", "y1", "z1"), es=0.8, t_env=Te)
+    phi0 = np.full(x.shape[0], T0)
+    u0 = orc.initial_rate(K, M, K["d"], prob["bc_mask"], phi0)
+    phi, u, a, its = orc.genalpha(K, M, K["d"], prob["bc_mask"], prob["bc_val"], phi0, u0, np.zeros_like(phi0),
+                                  orc.genalpha_params(0.5), 0.02, 6, newton_tol=1e-10, max_newton=30, prob=prob,
+                                  radiation=rad)
+    assert its.max() <= 7, its
