@@ -261,19 +261,28 @@ mf_status mf_genalpha_params_from_rho(double rho_inf, mf_genalpha_params *out);
  * dphi += x, du = (dphi / dt - u) / b1, da = (du / dt - a) / b2.  The norms
  * are fixed-order sums: runs are bit-reproducible.  newton_its, pcg_its
  * (host [steps], may be NULL): solves and PCG iterations per step.
+ * Radiation (Sec. 4.1, e_m sigma^b (T, T_env^4 - T^4)): rad (may be NULL) is
+ * a facet set of K's thermal pattern with rad_es [n_facets] = e_m sigma^b
+ * and rad_tenv [n_facets]; the residual then uses F + R(phi~), R_a =
+ * sum_f es int N_a (T_env^4 - T~^4) (facet rule), also inside the rounding
+ * floor, and the tangent gains c1 K_rad, K_rad[a][b] = sum_f 4 es int N_a
+ * N_b T~^3: full Newton.
  * Synchronises the stream every sub-step.  Errors: MF_ERR_INVALID_ARG,
  * MF_ERR_NOT_CONVERGED (a step used max_newton solves, or a PCG solve hit
  * pcg_max_iter), MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_genalpha_run(const mf_csr *K, const double *M_values, const double *F, const uint8_t *bc_mask,
-                          const double *bc_val, double *phi, double *u, double *a, const mf_genalpha_params *prm,
-                          double dt, int64_t steps, double newton_tol, int32_t max_newton, double pcg_tol,
-                          int64_t pcg_max_iter, int64_t *newton_its, int64_t *pcg_its, void *stream);
+                          const double *bc_val, const mf_facets *rad, const double *rad_es, const double *rad_tenv,
+                          double *phi, double *u, double *a, const mf_genalpha_params *prm, double dt,
+                          int64_t steps, double newton_tol, int32_t max_newton, double pcg_tol, int64_t pcg_max_iter,
+                          int64_t *newton_its, int64_t *pcg_its, void *stream);
 
-/* Consistent initial rate: solves M u = F - K phi on the free rows (u = 0
- * on Dirichlet rows) by Jacobi-PCG to pcg_tol.  Arguments as
- * mf_genalpha_run; u [n] device output.  Synchronises the stream.  Errors:
- * MF_ERR_INVALID_ARG, MF_ERR_NOT_CONVERGED, MF_ERR_OOM, MF_ERR_CUDA. */
+/* Consistent initial rate: solves M u = F + R(phi) - K phi on the free rows
+ * (u = 0 on Dirichlet rows; R the radiation loads, if rad is given) by
+ * Jacobi-PCG to pcg_tol.  Arguments as mf_genalpha_run; u [n] device
+ * output.  Synchronises the stream.  Errors: MF_ERR_INVALID_ARG,
+ * MF_ERR_NOT_CONVERGED, MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_genalpha_initial_rate(const mf_csr *K, const double *M_values, const double *F, const uint8_t *bc_mask,
+                                   const mf_facets *rad, const double *rad_es, const double *rad_tenv,
                                    const double *phi, double *u, double pcg_tol, int64_t pcg_max_iter, void *stream);
 
 /* Pressure-mass diagonal of the flow form, out[a] = sum_e sum_q w detJ M_a^2

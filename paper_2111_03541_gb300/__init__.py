@@ -92,10 +92,11 @@ _SIGS = {
     "mf_assemble_boundary": [C.c_void_p, C.POINTER(FacetCoeffs), C.POINTER(CSR), C.c_void_p, C.c_void_p],
     "mf_genalpha_params_from_rho": [C.c_double, C.POINTER(GenAlphaParams)],
     "mf_genalpha_run": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                        C.c_void_p, C.POINTER(GenAlphaParams), C.c_double, C.c_int64, C.c_double, C.c_int32,
-                        C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GenAlphaParams), C.c_double,
+                        C.c_int64, C.c_double, C.c_int32, C.c_double, C.c_int64, C.c_void_p, C.c_void_p,
+                        C.c_void_p],
     "mf_genalpha_initial_rate": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                 C.c_double, C.c_int64, C.c_void_p],
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.c_void_p],
     "mf_pressure_mass_diag": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "mf_flow_precond": [C.c_void_p, C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
     "mf_solve": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_void_p],
@@ -232,21 +233,24 @@ def mf_genalpha_params_from_rho(rho_inf: float) -> GenAlphaParams:
 
 def mf_genalpha_run(K: CSR, M_values, F, bc_mask, bc_val, phi, u, a, prm: GenAlphaParams, dt: float, steps: int,
                     newton_tol: float = 1e-8, max_newton: int = 10, pcg_tol: float = 1e-12,
-                    pcg_max_iter: int = 100000, stream=None, allow=()):
-    """Returns (status, newton solves per step, PCG iterations per step) as numpy arrays."""
+                    pcg_max_iter: int = 100000, stream=None, allow=(), rad=None, rad_es=None, rad_tenv=None):
+    """Returns (status, newton solves per step, PCG iterations per step) as numpy arrays.
+    rad: a facet set handle (radiation), rad_es / rad_tenv: per-facet device tensors."""
     import numpy as np
     nits = np.zeros(max(steps, 1), dtype=np.int64)
     pits = np.zeros(max(steps, 1), dtype=np.int64)
-    st = _check(lib().mf_genalpha_run(C.byref(K), _ptr(M_values), _ptr(F), _ptr(bc_mask), _ptr(bc_val), _ptr(phi),
-                                      _ptr(u), _ptr(a), C.byref(prm), dt, steps, newton_tol, max_newton, pcg_tol,
-                                      pcg_max_iter, nits.ctypes.data, pits.ctypes.data, _stream(stream)), allow)
+    st = _check(lib().mf_genalpha_run(C.byref(K), _ptr(M_values), _ptr(F), _ptr(bc_mask), _ptr(bc_val), rad,
+                                      _ptr(rad_es), _ptr(rad_tenv), _ptr(phi), _ptr(u), _ptr(a), C.byref(prm), dt,
+                                      steps, newton_tol, max_newton, pcg_tol, pcg_max_iter, nits.ctypes.data,
+                                      pits.ctypes.data, _stream(stream)), allow)
     return st, nits[:steps], pits[:steps]
 
 
 def mf_genalpha_initial_rate(K: CSR, M_values, F, bc_mask, phi, u, pcg_tol: float = 1e-13,
-                             pcg_max_iter: int = 100000, stream=None) -> None:
-    _check(lib().mf_genalpha_initial_rate(C.byref(K), _ptr(M_values), _ptr(F), _ptr(bc_mask), _ptr(phi), _ptr(u),
-                                          pcg_tol, pcg_max_iter, _stream(stream)))
+                             pcg_max_iter: int = 100000, stream=None, rad=None, rad_es=None, rad_tenv=None) -> None:
+    _check(lib().mf_genalpha_initial_rate(C.byref(K), _ptr(M_values), _ptr(F), _ptr(bc_mask), rad, _ptr(rad_es),
+                                          _ptr(rad_tenv), _ptr(phi), _ptr(u), pcg_tol, pcg_max_iter,
+                                          _stream(stream)))
 
 
 def mf_pressure_mass_diag(mesh, pattern, out, stream=None) -> None:

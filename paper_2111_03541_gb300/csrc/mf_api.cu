@@ -445,7 +445,8 @@ extern "C" mf_status mf_genalpha_params_from_rho(double rho_inf, mf_genalpha_par
 }
 
 extern "C" mf_status mf_genalpha_run(const mf_csr *K, const double *M_values, const double *F, const uint8_t *bc_mask,
-                                     const double *bc_val, double *phi, double *u, double *a,
+                                     const double *bc_val, const mf_facets *rad, const double *rad_es,
+                                     const double *rad_tenv, double *phi, double *u, double *a,
                                      const mf_genalpha_params *prm, double dt, int64_t steps, double newton_tol,
                                      int32_t max_newton, double pcg_tol, int64_t pcg_max_iter, int64_t *newton_its,
                                      int64_t *pcg_its, void *stream)
@@ -455,25 +456,33 @@ extern "C" mf_status mf_genalpha_run(const mf_csr *K, const double *M_values, co
         return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_run: NULL argument");
     if ((bc_mask == nullptr) != (bc_val == nullptr))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_run: bc_mask and bc_val go together");
+    if (rad && (rad->pattern->row_ptr != K->row_ptr || rad->pattern->form != MF_FORM_THERMAL ||
+                (rad->n_facets > 0 && (!rad_es || !rad_tenv))))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_run: radiation facets need K's thermal pattern, es, t_env");
     if (!(dt > 0.0) || steps < 0 || !(prm->b1 != 0.0) || !(prm->b2 != 0.0) || !(newton_tol > 0.0) ||
         max_newton < 1 || !(pcg_tol > 0.0) || pcg_max_iter < 1)
         return mf_fail(MF_ERR_INVALID_ARG,
                        "mf_genalpha_run: dt > 0, steps >= 0, b1, b2 != 0, tolerances > 0, iteration caps >= 1");
-    return mf_genalpha_run_impl(K, M_values, F, bc_mask, bc_val, phi, u, a, prm, dt, steps, newton_tol, max_newton,
-                                pcg_tol, pcg_max_iter, newton_its, pcg_its, static_cast<cudaStream_t>(stream));
+    return mf_genalpha_run_impl(K, M_values, F, bc_mask, bc_val, rad, rad_es, rad_tenv, phi, u, a, prm, dt, steps,
+                                newton_tol, max_newton, pcg_tol, pcg_max_iter, newton_its, pcg_its,
+                                static_cast<cudaStream_t>(stream));
 }
 
 extern "C" mf_status mf_genalpha_initial_rate(const mf_csr *K, const double *M_values, const double *F,
-                                              const uint8_t *bc_mask, const double *phi, double *u, double pcg_tol,
+                                              const uint8_t *bc_mask, const mf_facets *rad, const double *rad_es,
+                                              const double *rad_tenv, const double *phi, double *u, double pcg_tol,
                                               int64_t pcg_max_iter, void *stream)
 {
     g_msg[0] = 0;
     if (!csr_ok(K) || !M_values || !F || !phi || !u)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_initial_rate: NULL argument");
+    if (rad && (rad->pattern->row_ptr != K->row_ptr || rad->pattern->form != MF_FORM_THERMAL ||
+                (rad->n_facets > 0 && (!rad_es || !rad_tenv))))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_initial_rate: radiation facets need K's thermal pattern");
     if (!(pcg_tol > 0.0) || pcg_max_iter < 1)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_initial_rate: pcg_tol > 0 and pcg_max_iter >= 1");
-    return mf_genalpha_initial_rate_impl(K, M_values, F, bc_mask, phi, u, pcg_tol, pcg_max_iter,
-                                         static_cast<cudaStream_t>(stream));
+    return mf_genalpha_initial_rate_impl(K, M_values, F, bc_mask, rad, rad_es, rad_tenv, phi, u, pcg_tol,
+                                         pcg_max_iter, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" mf_status mf_pressure_mass_diag(const mf_mesh *mesh, const mf_pattern *pattern, double *out,

@@ -251,6 +251,59 @@ __device__ __forceinline__ double conv_row(const double *__restrict__ X, const i
     }
 }
 
+// Facet quadrature (the rule of the convection terms): number of points,
+// weight of point q times |J| at it, and the facet shape value N_b(q).
+// Edges: Gauss-Legendre on t in [0, 1] (2 points for P1, 3 for P2), |J| = L;
+// hexahedron faces: 2 x 2 Gauss on [-1, 1]^2, |J| = |x_u x x_v|.
+template <int ELEM>
+constexpr int facet_nq() { return ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4); }
+
+template <int ELEM>
+__device__ __forceinline__ double facet_shape(int q, int b)
+{
+    if (ELEM == MF_P1_TRI) {
+        const double t = q == 0 ? 0.5 - 0.5 * 0.57735026918962576451 : 0.5 + 0.5 * 0.57735026918962576451;
+        return b == 0 ? 1.0 - t : t;
+    } else if (ELEM == MF_P2_TRI) {
+        const double g = 0.5 * 0.77459666924148337704;  // sqrt(3/5) / 2
+        const double t = q == 0 ? 0.5 - g : (q == 1 ? 0.5 : 0.5 + g);
+        return b == 0 ? (1.0 - t) * (1.0 - 2.0 * t) : (b == 1 ? t * (2.0 * t - 1.0) : 4.0 * t * (1.0 - t));
+    } else {
+        const double al = 0.5 * (1.0 + 0.57735026918962576451), be = 0.5 * (1.0 - 0.57735026918962576451);
+        return ((b & 1) == (q & 1) ? al : be) * ((b >> 1) == (q >> 1) ? al : be);
+    }
+}
+
+template <int ELEM>
+__device__ __forceinline__ void facet_wj(const double *__restrict__ X, const int32_t *fn, double (&wj)[4])
+{
+    if (ELEM == MF_P1_TRI || ELEM == MF_P2_TRI) {
+        const double ex = X[2 * (int64_t)fn[1]] - X[2 * (int64_t)fn[0]];
+        const double ey = X[2 * (int64_t)fn[1] + 1] - X[2 * (int64_t)fn[0] + 1];
+        const double L = sqrt(ex * ex + ey * ey);
+        if (ELEM == MF_P1_TRI) {
+            wj[0] = wj[1] = 0.5 * L;
+        } else {
+            wj[0] = wj[2] = L * (5.0 / 18.0);
+            wj[1] = L * (8.0 / 18.0);
+        }
+    } else {
+        double c1[3], c2[3], c3[3], P[3], Qu[3], Qv[3];
+        face_coefs(X, fn, c1, c2, c3);
+        cross3(c1, c2, P);
+        cross3(c1, c3, Qu);
+        cross3(c3, c2, Qv);
+        const double g = 0.57735026918962576451;
+        for (int q = 0; q < 4; ++q) {
+            const double u = (q & 1) ? g : -g, v = (q & 2) ? g : -g;
+            const double a0 = P[0] + Qu[0] * u + Qv[0] * v;
+            const double a1 = P[1] + Qu[1] * u + Qv[1] * v;
+            const double a2 = P[2] + Qu[2] * u + Qv[2] * v;
+            wj[q] = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+        }
+    }
+}
+
 // Facet geometry of every incidence entry, once per facet set (the mesh's
 // coordinates do not change while it lives).  Thermal: the entry's row of the
 // unit-h convection matrix and its unit-h T_env load factor, (npf + 1)
@@ -260,7 +313,7 @@ template <int ELEM>
 __global__ void k_facet_geometry(int64_t n_entries, const int32_t *__restrict__ binc,
                                  const uint8_t *__restrict__ bloc, const int32_t *__restrict__ fnode,
                                  const uint8_t *__restrict__ fface, const double *__restrict__ X, bool traction,
-                                 double *__restrict__ bgeo, int32_t *__restrict__ bcol)
+                                 double *__restrict__ bgeo, int32_t *__restrict__ bcol, double *__restrict__ bwq)
 {
     constexpr int NPF = ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,6 +341,11 @@ __global__ void k_facet_geometry(int64_t n_entries, const int32_t *__restrict__ 
         bcol[t * NPF + k] = fn[k];
     }
     bgeo[t * (NPF + 1) + NPF] = lf;
+    // per point: w |J| N_m, for the temperature-dependent (radiation) terms
+    constexpr int NQ = facet_nq<ELEM>();
+    double wj[4];
+    facet_wj<ELEM>(X, fn, wj);
+    for (int q = 0; q < NQ; ++q) bwq[t * NQ + q] = wj[q] * facet_shape<ELEM>(q, m);
 }
 
 // Convection: one thread per boundary node adds, in ascending facet order,
@@ -373,7 +431,129 @@ __global__ void __launch_bounds__(BND_T) k_bnd_traction(int64_t n_bnodes, const 
     d[dof] += acc;
 }
 
+// Radiation (Sec. 4.1, e_m sigma^b (T, T_env^4 - T^4)) at nodal temperatures
+// T, one thread per boundary node, its facets in ascending order:
+//   load     R[r] = sum_f es_f sum_q (w |J| N_m)(q) (T_env^4 - T_q^4),
+//   tangent  K_rad[r][c] = sum_f 4 es_f sum_q (w |J| N_m)(q) N_b(q) T_q^3,
+// T_q = sum_b N_b(q) T_b.  The load goes to R[r] (Dirichlet rows untouched);
+// scale times the tangent is added to the node's own CSR row, except in
+// Dirichlet rows and columns.
+template <int ELEM>
+__device__ __forceinline__ void facet_tq(const int32_t *fn, const double *__restrict__ T, double (&tq)[4])
+{
+    constexpr int NPF = ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4);
+    double tb[NPF];
+#pragma unroll
+    for (int b = 0; b < NPF; ++b) tb[b] = T[fn[b]];
+#pragma unroll
+    for (int q = 0; q < facet_nq<ELEM>(); ++q) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < NPF; ++b) v += facet_shape<ELEM>(q, b) * tb[b];
+        tq[q] = v;
+    }
+}
+
+template <int ELEM>
+__global__ void __launch_bounds__(BND_T) k_rad_load(int64_t n_bnodes, const int32_t *__restrict__ bnode,
+                                                    const int64_t *__restrict__ bptr,
+                                                    const int32_t *__restrict__ binc,
+                                                    const double *__restrict__ bwq,
+                                                    const int32_t *__restrict__ fnode,
+                                                    const double *__restrict__ es, const double *__restrict__ tenv,
+                                                    const double *__restrict__ T, const uint8_t *__restrict__ mask,
+                                                    double *__restrict__ R, int *status)
+{
+    constexpr int NPF = ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4), NQ = facet_nq<ELEM>();
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bnodes) return;
+    const int32_t r = bnode[b];
+    if (mask && mask[r]) return;
+    double acc = 0.0;
+    for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
+        const int32_t f = binc[t];
+        const double ef = es[f], te = tenv[f];
+        if (!isfinite(ef) || !isfinite(te)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        const double te4 = (te * te) * (te * te);
+        double tq[4];
+        facet_tq<ELEM>(fnode + (int64_t)f * NPF, T, tq);
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) s += bwq[t * NQ + q] * (te4 - (tq[q] * tq[q]) * (tq[q] * tq[q]));
+        acc += ef * s;
+    }
+    R[r] = acc;
+}
+
+template <int ELEM>
+__global__ void __launch_bounds__(BND_T) k_rad_tangent(int64_t n_bnodes, const int32_t *__restrict__ bnode,
+                                                       const int64_t *__restrict__ brow,
+                                                       const int64_t *__restrict__ bptr,
+                                                       const int32_t *__restrict__ binc,
+                                                       const uint8_t *__restrict__ bslot,
+                                                       const int32_t *__restrict__ bcol,
+                                                       const double *__restrict__ bwq,
+                                                       const int32_t *__restrict__ fnode,
+                                                       const double *__restrict__ es, const double *__restrict__ T,
+                                                       const uint8_t *__restrict__ mask, double scale,
+                                                       double *__restrict__ values)
+{
+    constexpr int NPF = ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4), NQ = facet_nq<ELEM>();
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bnodes) return;
+    const int32_t r = bnode[b];
+    if (mask && mask[r]) return;
+    double *vrow = values + brow[b];
+    for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
+        const int32_t f = binc[t];
+        const double ef4 = 4.0 * es[f] * scale;
+        double tq[4];
+        facet_tq<ELEM>(fnode + (int64_t)f * NPF, T, tq);
+        double wt[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) wt[q] = bwq[t * NQ + q] * (tq[q] * tq[q] * tq[q]);
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int32_t c = bcol[t * NPF + k];
+            if (mask && mask[c]) continue;
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v += wt[q] * facet_shape<ELEM>(q, k);
+            vrow[bslot[t * NPF + k]] += ef4 * v;
+        }
+    }
+}
+
 }  // namespace
+
+mf_status mf_radiation_load(const mf_facets *f, const double *es, const double *tenv, const double *T,
+                            const uint8_t *mask, double *R, cudaStream_t st)
+{
+    if (!f || f->n_bnodes == 0) return MF_OK;
+    int *status = mf_status_word();
+    if (!status) return mf_fail(MF_ERR_CUDA, "radiation: status word unavailable");
+    const unsigned g = nblk(f->n_bnodes, BND_T);
+#define RL_ARGS f->n_bnodes, f->bnode, f->bptr, f->binc, f->bwq, f->fnode, es, tenv, T, mask, R, status
+    if (f->mesh->elem == MF_P1_TRI) k_rad_load<MF_P1_TRI><<<g, BND_T, 0, st>>>(RL_ARGS);
+    else if (f->mesh->elem == MF_P2_TRI) k_rad_load<MF_P2_TRI><<<g, BND_T, 0, st>>>(RL_ARGS);
+    else k_rad_load<MF_Q1_HEX><<<g, BND_T, 0, st>>>(RL_ARGS);
+#undef RL_ARGS
+    return mf_cuda_check(cudaGetLastError(), "radiation load");
+}
+
+mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const double *T, const uint8_t *mask,
+                               double scale, double *values, cudaStream_t st)
+{
+    if (!f || f->n_bnodes == 0) return MF_OK;
+    const unsigned g = nblk(f->n_bnodes, BND_T);
+#define RT_ARGS f->n_bnodes, f->bnode, f->brow, f->bptr, f->binc, f->bslot, f->bcol, f->bwq, f->fnode, es, T, mask, \
+                scale, values
+    if (f->mesh->elem == MF_P1_TRI) k_rad_tangent<MF_P1_TRI><<<g, BND_T, 0, st>>>(RT_ARGS);
+    else if (f->mesh->elem == MF_P2_TRI) k_rad_tangent<MF_P2_TRI><<<g, BND_T, 0, st>>>(RT_ARGS);
+    else k_rad_tangent<MF_Q1_HEX><<<g, BND_T, 0, st>>>(RT_ARGS);
+#undef RT_ARGS
+    return mf_cuda_check(cudaGetLastError(), "radiation tangent");
+}
 
 mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n_facets, const int32_t *elem,
                                 const uint8_t *face, cudaStream_t st, mf_facets *f)
@@ -444,6 +624,7 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
         FC(cudaMallocAsync(&f->bcol, sizeof(int32_t) * ne * npf, st));
         FC(cudaMallocAsync(&f->brow, sizeof(int64_t) * nb, st));
         FC(cudaMallocAsync(&f->bgeo, sizeof(double) * ne * (npf + 1), st));
+        FC(cudaMallocAsync(&f->bwq, sizeof(double) * ne * (npf == 3 ? 3 : (npf == 2 ? 2 : 4)), st));
     } else {
         FC(cudaMallocAsync(&f->bgeo, sizeof(double) * ne * 3, st));
     }
@@ -462,13 +643,13 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
     }
     if (m->elem == MF_P1_TRI)
         k_facet_geometry<MF_P1_TRI><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
-                                                              false, f->bgeo, f->bcol);
+                                                              false, f->bgeo, f->bcol, f->bwq);
     else if (m->elem == MF_P2_TRI)
         k_facet_geometry<MF_P2_TRI><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
-                                                              false, f->bgeo, f->bcol);
+                                                              false, f->bgeo, f->bcol, f->bwq);
     else
         k_facet_geometry<MF_Q1_HEX><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
-                                                              !thermal, f->bgeo, f->bcol);
+                                                              !thermal, f->bgeo, f->bcol, f->bwq);
     FC(cudaGetLastError());
 #undef FC
     mf_status s = check_status(status, st);
@@ -489,6 +670,8 @@ void mf_facets_free(mf_facets *f)
     cudaFree(f->bcol);
     cudaFree(f->brow);
     cudaFree(f->bgeo);
+    cudaFree(f->bwq);
+    f->bwq = nullptr;
     f->fnode = f->bnode = f->binc = f->bcol = nullptr;
     f->fface = f->bloc = f->bslot = nullptr;
     f->bptr = f->brow = nullptr;

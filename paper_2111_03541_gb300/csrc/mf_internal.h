@@ -121,6 +121,7 @@ struct mf_facets {
     int64_t *brow = nullptr;     // thermal: [n_bnodes] start of the node's CSR row
     double *bgeo = nullptr;      // facet geometry per entry: thermal [entry][npf + 1] unit-h convection
                                  // row and load factor; elasticity [entry][3] oriented area moment
+    double *bwq = nullptr;       // thermal: [entry][nq] w_q |J_q| N_m(q) at the facet rule's points
 };
 
 // status word (device) of the current device
@@ -156,14 +157,21 @@ void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int6
 mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n_facets, const int32_t *elem,
                                 const uint8_t *face, cudaStream_t st, mf_facets *f);
 void mf_facets_free(mf_facets *f);
+// radiation terms of a thermal facet set at nodal temperatures T (mf_boundary.cu)
+mf_status mf_radiation_load(const mf_facets *f, const double *es, const double *tenv, const double *T,
+                            const uint8_t *mask, double *R, cudaStream_t st);
+mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const double *T, const uint8_t *mask,
+                               double scale, double *values, cudaStream_t st);
 mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c, double *values, double *d,
                                     cudaStream_t st);
 mf_status mf_genalpha_params_from_rho_impl(double rho, mf_genalpha_params *out);
 mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *F, const uint8_t *mask,
-                               const double *bval, double *phi, double *u, double *a, const mf_genalpha_params *prm,
+                               const double *bval, const mf_facets *rad, const double *rad_es,
+                               const double *rad_tenv, double *phi, double *u, double *a, const mf_genalpha_params *prm,
                                double dt, int64_t steps, double newton_tol, int32_t max_newton, double pcg_tol,
                                int64_t pcg_max_iter, int64_t *newton_its, int64_t *pcg_its, cudaStream_t st);
 mf_status mf_genalpha_initial_rate_impl(const mf_csr *K, const double *Mv, const double *F, const uint8_t *mask,
+                                        const mf_facets *rad, const double *rad_es, const double *rad_tenv,
                                         const double *phi, double *u, double pcg_tol, int64_t pcg_max_iter,
                                         cudaStream_t st);
 mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cudaStream_t st);

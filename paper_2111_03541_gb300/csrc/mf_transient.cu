@@ -84,13 +84,14 @@ __device__ __forceinline__ double group_sum(double v)
     return v;
 }
 
-// D-2: d = F - K pt - M ut on free rows (0 on Dirichlet rows), one group of
+// D-2: d = F + R - K pt - M ut on free rows (0 on Dirichlet rows; R, the
+// radiation loads at pt, may be null), one group of
 // RL lanes per row and RPB rows per block, and per block the partial sums of
-// d^2, F^2, (K pt)^2, (M ut)^2 over its free rows.
+// d^2, (F + R)^2, (K pt)^2, (M ut)^2 over its free rows.
 __global__ void __launch_bounds__(TPB) k_ga_residual(int64_t n, const int64_t *__restrict__ rp,
                                                      const int32_t *__restrict__ ci, const double *__restrict__ Kv,
                                                      const double *__restrict__ Mv, const double *__restrict__ F,
-                                                     const uint8_t *__restrict__ mask,
+                                                     const double *__restrict__ R, const uint8_t *__restrict__ mask,
                                                      const double *__restrict__ pt, const double *__restrict__ ut,
                                                      double *__restrict__ d, double *__restrict__ part)
 {
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(TPB) k_ga_residual(int64_t n, const int64_t *_
         double q[4] = {0.0, 0.0, 0.0, 0.0};
         if (r < n) {
             const bool fixed = mask && mask[r];
-            const double f = F[r];
+            const double f = R ? F[r] + R[r] : F[r];
             const double dr = fixed ? 0.0 : f - kp - mu;
             d[r] = dr;
             if (!fixed) {
@@ -235,7 +236,8 @@ mf_status mf_genalpha_params_from_rho_impl(double rho, mf_genalpha_params *out)
 }
 
 mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *F, const uint8_t *mask,
-                               const double *bval, double *phi, double *u, double *a, const mf_genalpha_params *prm,
+                               const double *bval, const mf_facets *rad, const double *rad_es,
+                               const double *rad_tenv, double *phi, double *u, double *a, const mf_genalpha_params *prm,
                                double dt, int64_t steps, double newton_tol, int32_t max_newton, double pcg_tol,
                                int64_t pcg_max_iter, int64_t *newton_its, int64_t *pcg_its, cudaStream_t st)
 {
@@ -243,9 +245,14 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
     const unsigned gv = nblk(n, TPB), gr = nblk(n, RPB), nc = nblk(gr, NCHUNK);
     if (nc > NCHUNK) return mf_fail(MF_ERR_UNSUPPORTED, "mf_genalpha_run: more than 2^34 rows");
     double *buf = nullptr, *Tv = nullptr, *part = nullptr, *part2 = nullptr, *norms = nullptr;
-    MF_CUDA(cudaMallocAsync(&buf, sizeof(double) * 7 * n, st));
+    const bool hasrad = rad && rad->n_bnodes > 0;
+    MF_CUDA(cudaMallocAsync(&buf, sizeof(double) * 8 * n, st));
     double *dphi = buf, *du = buf + n, *da = buf + 2 * n, *pt = buf + 3 * n, *ut = buf + 4 * n, *d = buf + 5 * n,
-           *x = buf + 6 * n;
+           *x = buf + 6 * n, *R = hasrad ? buf + 7 * n : nullptr;
+    if (hasrad && cudaMemsetAsync(R, 0, sizeof(double) * n, st) != cudaSuccess) {
+        cudaFreeAsync(buf, st);
+        return mf_cuda_check(cudaGetLastError(), "mf_genalpha_run");
+    }
     mf_status rc = MF_OK;
     auto done = [&](mf_status s) {
         cudaFreeAsync(buf, st);
@@ -278,7 +285,11 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
         for (;;) {
             mf_prof_begin("ga_residual", st);
             k_ga_effective<<<gv, TPB, 0, st>>>(n, phi, u, dphi, du, prm->c1, prm->c2, pt, ut);
-            k_ga_residual<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, F, mask, pt, ut, d, part);
+            if (hasrad) {
+                const mf_status rs = mf_radiation_load(rad, rad_es, rad_tenv, pt, mask, R, st);
+                if (rs != MF_OK) return done(rs);
+            }
+            k_ga_residual<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, F, R, mask, pt, ut, d, part);
             k_ga_sum4<<<nc, TPB, 0, st>>>(gr, part, part2);
             k_ga_sum4<<<1, TPB, 0, st>>>(nc, part2, norms);
             mf_prof_end(st);
@@ -298,6 +309,10 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
             mf_prof_begin("ga_tangent", st);
             k_ga_tangent<<<nblk(n, TPBR), TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, prm->c1, s, mask,
                                                         Tv);
+            if (hasrad) {
+                const mf_status rs = mf_radiation_tangent(rad, rad_es, pt, mask, prm->c1, Tv, st);
+                if (rs != MF_OK) return done(rs);
+            }
             mf_prof_end(st);
             if (cudaMemsetAsync(x, 0, sizeof(double) * n, st) != cudaSuccess)
                 return done(mf_cuda_check(cudaGetLastError(), "mf_genalpha_run"));
@@ -322,12 +337,13 @@ mf_status mf_genalpha_run_impl(const mf_csr *K, const double *Mv, const double *
 }
 
 mf_status mf_genalpha_initial_rate_impl(const mf_csr *K, const double *Mv, const double *F, const uint8_t *mask,
+                                        const mf_facets *rad, const double *rad_es, const double *rad_tenv,
                                         const double *phi, double *u, double pcg_tol, int64_t pcg_max_iter,
                                         cudaStream_t st)
 {
-    // M u = F - K phi on the free rows, u = 0 on Dirichlet rows: the residual
-    // kernel with u~ = 0 gives the right-hand side, the tangent kernel with
-    // c1 = 0, s = 1 the matrix
+    // M u = F + R(phi) - K phi on the free rows, u = 0 on Dirichlet rows: the
+    // residual kernel with u~ = 0 gives the right-hand side, the tangent
+    // kernel with c1 = 0, s = 1 the matrix
     const int64_t n = K->n_rows, nnz = K->nnz;
     const unsigned gr = nblk(n, RPB);
     double *buf = nullptr, *Tv = nullptr, *part = nullptr;
@@ -337,15 +353,20 @@ mf_status mf_genalpha_initial_rate_impl(const mf_csr *K, const double *Mv, const
         cudaFreeAsync(part, st);
         return s;
     };
-    if (cudaMallocAsync(&buf, sizeof(double) * 2 * n, st) != cudaSuccess ||
+    const bool hasrad = rad && rad->n_bnodes > 0;
+    if (cudaMallocAsync(&buf, sizeof(double) * 3 * n, st) != cudaSuccess ||
         cudaMallocAsync(&Tv, sizeof(double) * nnz, st) != cudaSuccess ||
         cudaMallocAsync(&part, sizeof(double) * 4 * gr, st) != cudaSuccess)
         return done(mf_fail(MF_ERR_OOM, "mf_genalpha_initial_rate: device allocation"));
-    double *zero = buf, *rhs = buf + n;
-    if (cudaMemsetAsync(zero, 0, sizeof(double) * n, st) != cudaSuccess ||
+    double *zero = buf, *rhs = buf + n, *R = hasrad ? buf + 2 * n : nullptr;
+    if (cudaMemsetAsync(buf, 0, sizeof(double) * 3 * n, st) != cudaSuccess ||
         cudaMemsetAsync(u, 0, sizeof(double) * n, st) != cudaSuccess)
         return done(mf_cuda_check(cudaGetLastError(), "mf_genalpha_initial_rate"));
-    k_ga_residual<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, F, mask, phi, zero, rhs, part);
+    if (hasrad) {
+        const mf_status rs = mf_radiation_load(rad, rad_es, rad_tenv, phi, mask, R, st);
+        if (rs != MF_OK) return done(rs);
+    }
+    k_ga_residual<<<gr, TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, F, R, mask, phi, zero, rhs, part);
     k_ga_tangent<<<nblk(n, TPBR), TPB, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, Mv, 0.0, 1.0, mask, Tv);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return done(mf_cuda_check(e, "mf_genalpha_initial_rate"));

@@ -1,6 +1,7 @@
 """Parity of the transient pieces with the CPU FP64 oracle, through the C ABI:
-the capacity matrix C int N_a N_b (MF_FORM_CAPACITY) and generalised-alpha
-time stepping (mf_genalpha_run, mf_genalpha_initial_rate).
+the capacity matrix C int N_a N_b (MF_FORM_CAPACITY), generalised-alpha time
+stepping (mf_genalpha_run, mf_genalpha_initial_rate) and the nonlinear
+radiation term e_m sigma^b (T, T_env^4 - T^4) in its Newton sub-steps.
 
 Capacity: pattern bit-exact, values row-scaled within 1e-12.  Time stepping:
 both sides solve every Newton step by Jacobi-PCG to a relative residual of
@@ -236,3 +237,96 @@ def test_genalpha_invalid_arguments(mf):
     with pytest.raises(mf.MFError) as ei:
         mf.mf_genalpha_run(P.csr, P.values, P.d, P.bc_mask, None, x, x, x, prm, 0.1, 1)
     assert ei.value.status == mf.MF_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# radiation inside the Newton sub-steps
+# ---------------------------------------------------------------------------
+
+def _oracle_radiation_load(orc, prob, rad, T):
+    elem = {"P1": orc.P1, "P2": orc.P2, "Q1": orc.Q1}[prob["elem"]]
+    R = np.zeros(prob["coords"].shape[0])
+    for e, f, es, te in zip(rad["elem"], rad["face"], rad["es"], rad["t_env"]):
+        nodes = prob["conn"][e][orc.facet_nodes(elem, int(f))]
+        _, rf = orc.facet_radiation(elem, prob["coords"][nodes], es, te, T[nodes])
+        R[nodes] += rf
+    return R
+
+
+def _radiation_case(kind):
+    prob = {"p1": lambda: gen.thermal_p1_problem(10), "p2": lambda: gen.thermal_p2_problem(6),
+            "q1": lambda: gen.thermal_q1_problem(5)}[kind]()
+    prob["source"] = 0.0
+    x = prob["coords"]
+    left = x[:, 0] <= 1e-14
+    prob["bc_mask"] = left.astype(np.uint8)
+    prob["bc_val"] = np.where(left, 1.0, 0.0)
+    sides = ("x1", "y1") if kind != "q1" else ("x1", "y1", "z1")
+    rad = gen.radiation_facets(prob, sides)
+    return prob, rad
+
+
+def _gpu_radiation(mf, P, rad):
+    import torch
+    e = torch.from_numpy(rad["elem"]).cuda()
+    f = torch.from_numpy(rad["face"]).cuda()
+    F = mf.mf_facets_create(P.mesh, P.pattern, e, f)
+    es = torch.from_numpy(rad["es"]).cuda()
+    te = torch.from_numpy(rad["t_env"]).cuda()
+    return F, es, te, (e, f)
+
+
+@pytest.mark.parametrize("kind", ["p1", "p2", "q1"])
+def test_genalpha_radiation_parity(mf, orc, kind):
+    import torch
+    prob, rad = _radiation_case(kind)
+    C = gen.lognormal(80, prob["conn"].shape[0], 0.3)
+    P, Mv, K, M = _transient_setup(mf, orc, prob, C)
+    mask, bval = prob["bc_mask"], prob["bc_val"]
+    # an undamped Newton on T^4 needs a predictor close enough: start at the
+    # Dirichlet value and take steps of 0.01
+    phi0 = np.full(prob["coords"].shape[0], 1.0)
+    prm = orc.genalpha_params(0.5)
+    Fo = K["d"] + _oracle_radiation_load(orc, prob, rad, phi0)
+    u0o = orc.initial_rate(K, M, Fo, mask, phi0)
+    po, uo, ao, itso = orc.genalpha(K, M, K["d"], mask, bval, phi0, u0o, np.zeros_like(phi0), prm, 0.01, 4,
+                                    newton_tol=1e-10, max_newton=30, prob=prob, radiation=rad)
+    Fh, es, te, keep = _gpu_radiation(mf, P, rad)
+    phi = torch.from_numpy(phi0.copy()).cuda()
+    u = torch.empty_like(phi)
+    a = torch.zeros_like(phi)
+    mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, P.bc_mask, phi, u, rad=Fh, rad_es=es, rad_tenv=te)
+    assert np.abs(u.cpu().numpy() - u0o).max() <= 1e-10 * np.abs(u0o).max()
+    st, nits, pits = mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, a,
+                                        mf.mf_genalpha_params_from_rho(0.5), 0.01, 4, newton_tol=1e-10, max_newton=30,
+                                        pcg_tol=1e-13, rad=Fh, rad_es=es, rad_tenv=te)
+    mf.mf_facets_destroy(Fh)
+    assert np.array_equal(nits, itso) and nits.max() > 1  # nonlinear: several solves per step
+    assert np.abs(phi.cpu().numpy() - po).max() <= 1e-10 * np.abs(po).max()
+    assert np.abs(u.cpu().numpy() - uo).max() <= 1e-8 * np.abs(uo).max()
+
+
+@pytest.mark.parametrize("kind", ["p1", "q1"])
+def test_radiation_slab_steady_state_gpu(mf, orc, kind):
+    # T = T0 + b x, k b = es (T_env^4 - (T0 + b)^4)
+    import scipy.optimize
+    import torch
+    prob = gen.thermal_p1_problem(8) if kind == "p1" else gen.thermal_q1_problem(4)
+    k, es, T0, Te = 1.7, 0.8, 0.4, 1.5
+    prob["coef"] = np.full(prob["conn"].shape[0], k)
+    prob["source"] = 0.0
+    x = prob["coords"]
+    left = x[:, 0] <= 1e-14
+    prob["bc_mask"] = left.astype(np.uint8)
+    prob["bc_val"] = np.where(left, T0, 0.0)
+    rad = gen.radiation_facets(prob, ("x1",), es=es, t_env=Te)
+    P, Mv, K, M = _transient_setup(mf, orc, prob, np.ones(prob["conn"].shape[0]))
+    Fh, es_t, te_t, keep = _gpu_radiation(mf, P, rad)
+    phi = torch.full((P.n,), T0, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(phi)
+    a = torch.zeros_like(phi)
+    mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, a, mf.mf_genalpha_params_from_rho(0.0), 50.0, 8,
+                       max_newton=30, pcg_tol=1e-13, rad=Fh, rad_es=es_t, rad_tenv=te_t)
+    mf.mf_facets_destroy(Fh)
+    b = scipy.optimize.brentq(lambda b: k * b - es * (Te ** 4 - (T0 + b) ** 4), -T0, 5.0, xtol=1e-15)
+    assert np.abs(phi.cpu().numpy() - (T0 + b * x[:, 0])).max() < 1e-10
