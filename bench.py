@@ -463,7 +463,7 @@ def _boundary_case(mf, P, prob, fac, sides, bc_mask, bc_val, hbm_gbs):
             "launches": 1, "l2": "flushed before each launch"}
 
 
-def _transient_case(mf, P, prob, fac, hbm_gbs, rho=0.5, dt=1e-3, steps=5):
+def _transient_case(mf, P, prob, fac, hbm_gbs, rho=0.5, dt=1e-3, steps=5, rad=None, t0=0.0):
     """Generalised-alpha steps of the conduction system with capacity C = 1
     and convection facets: K (domain + boundary terms), M and F assembled
     once, then `steps` steps timed as a whole (Newton residuals, tangents,
@@ -471,7 +471,9 @@ def _transient_case(mf, P, prob, fac, hbm_gbs, rho=0.5, dt=1e-3, steps=5):
     the library's kernel timing; their algorithmic bytes: tangent K, M values
     and column (20 B) read and T written (8 B) per entry; residual K, M
     values and column (20 B) per entry plus F, d, the two effective vectors
-    (32 B) per row."""
+    (32 B) per row.  With rad (radiation facet data), those facets radiate
+    (full Newton: several solves per step), T starts at t0 and is held at t0
+    on x = 0."""
     import numpy as np
     import torch
     dev = P.device
@@ -491,21 +493,32 @@ def _transient_case(mf, P, prob, fac, hbm_gbs, rho=0.5, dt=1e-3, steps=5):
                    dz)
     x = prob["coords"]
     left = torch.from_numpy((x[:, 0] <= 1e-14).astype(np.uint8)).to(dev)
-    bv = torch.zeros(P.n, dtype=torch.float64, device=dev)
-    phi = torch.zeros(P.n, dtype=torch.float64, device=dev)
+    bv = torch.full((P.n,), t0, dtype=torch.float64, device=dev)
+    phi = torch.full((P.n,), t0, dtype=torch.float64, device=dev)
     u = torch.empty_like(phi)
     a = torch.zeros_like(phi)
-    mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, left, phi, u)
+    R = None
+    rk = {}
+    if rad is not None:
+        re = torch.from_numpy(rad["elem"]).to(dev)
+        rf = torch.from_numpy(rad["face"]).to(dev)
+        R = mf.mf_facets_create(P.mesh, P.pattern, re, rf)
+        rk = {"rad": R, "rad_es": torch.from_numpy(rad["es"]).to(dev),
+              "rad_tenv": torch.from_numpy(rad["t_env"]).to(dev)}
+    mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, left, phi, u, **rk)
     prm = mf.mf_genalpha_params_from_rho(rho)
     mf.mf_set_kernel_timing(1)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, nits, pits = mf.mf_genalpha_run(P.csr, Mv, P.d, left, bv, phi, u, a, prm, dt, steps, pcg_tol=1e-10)
+    t_start = time.perf_counter()
+    st, nits, pits = mf.mf_genalpha_run(P.csr, Mv, P.d, left, bv, phi, u, a, prm, dt, steps, pcg_tol=1e-10,
+                                        max_newton=30, **rk)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    wall = time.perf_counter() - t_start
     kt = mf.mf_kernel_times()
     mf.mf_set_kernel_timing(0)
     mf.mf_facets_destroy(F_)
+    if R is not None:
+        mf.mf_facets_destroy(R)
     nnz, n = int(P.nnz), int(P.n)
     out = {"steps": steps, "dt": dt, "rho_inf": rho, "ms_per_step": 1e3 * wall / steps,
            "newton_solves": [int(v) for v in nits], "pcg_iterations": [int(v) for v in pits]}
@@ -613,6 +626,10 @@ def suite(dev):
                                                  hbm)
     # generalised-alpha transient on the same mesh: capacity 1, convection on five sides, T = 0 on x = 0
     out["T1_genalpha_q1_128"] = _transient_case(mf, P, prob, gen.convection_facets(prob, sides), hbm)
+    # the same with radiation on the five sides (Newton: several solves per step)
+    out["T2_genalpha_radiation_q1_128"] = _transient_case(mf, P, prob, gen.convection_facets(prob, sides), hbm,
+                                                          dt=1e-3, steps=3, rad=gen.radiation_facets(prob, sides),
+                                                          t0=1.0)
     del P
     torch.cuda.empty_cache()
     # loaded boundary: a random stress on five sides of the 64^3 elasticity box (clamped at x = 0)
