@@ -297,3 +297,24 @@ def test_elastic_traction_full_size_sampled_rows(mf, orc, prec):
     prob["facets"] = gen.traction_facets(prob, ("x1", "y0", "y1", "z0", "z1"))
     nodes = _box_nodes(64, np.random.default_rng(29), 40)
     _sampled(mf, orc, prob, nodes, 3, prec=prec, tol=TOL if prec == 0 else 1e-11)
+
+
+def test_single_element_all_faces(mf, orc):
+    # one hexahedron, convection on all six faces, no Dirichlet: every node
+    # sits on three facets
+    prob = _thermal("Q1", 1, gen.SIDES, dirichlet=None, jitter_all=True)
+    P, rp, ci, val, d = _gpu(mf, prob, bc=False)
+    ref = orc.assemble(prob, dirichlet=False)
+    assert row_scaled_error(rp, val, ref["val"]) <= TOL
+    assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+
+
+def test_facets_on_fully_constrained_rows(mf, orc):
+    # convection on the Dirichlet side itself: rows stay identities, d = bc_val
+    prob = _thermal("P2", 5, ("x0", "x1"), bval_seed=11)
+    P, rp, ci, val, d = _gpu(mf, prob)
+    ref = orc.assemble(prob)
+    assert row_scaled_error(rp, val, ref["val"]) <= TOL
+    assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+    m = prob["bc_mask"] > 0
+    assert np.array_equal(d[m], prob["bc_val"][m])

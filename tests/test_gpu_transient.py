@@ -330,3 +330,84 @@ def test_radiation_slab_steady_state_gpu(mf, orc, kind):
     mf.mf_facets_destroy(Fh)
     b = scipy.optimize.brentq(lambda b: k * b - es * (Te ** 4 - (T0 + b) ** 4), -T0, 5.0, xtol=1e-15)
     assert np.abs(phi.cpu().numpy() - (T0 + b * x[:, 0])).max() < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# degenerate cases
+# ---------------------------------------------------------------------------
+
+def test_genalpha_zero_steps_keeps_the_state(mf, orc):
+    import torch
+    prob = gen.thermal_p1_problem(6)
+    P, Mv, K, M = _transient_setup(mf, orc, prob, np.ones(prob["conn"].shape[0]))
+    phi = torch.linspace(0.0, 1.0, P.n, dtype=torch.float64, device="cuda")
+    u = torch.full_like(phi, 0.25)
+    a = torch.full_like(phi, -0.5)
+    mask = P.bc_mask.bool()
+    p0, u0, a0 = phi.clone(), u.clone(), a.clone()
+    st, nits, pits = mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, a,
+                                        mf.mf_genalpha_params_from_rho(0.5), 0.1, 0)
+    # only the Dirichlet dofs are set (value bc_val, zero rates)
+    assert torch.equal(phi[~mask], p0[~mask]) and torch.equal(u[~mask], u0[~mask]) and torch.equal(a[~mask], a0[~mask])
+    assert torch.equal(phi[mask], P.bc_val[mask]) and (u[mask] == 0).all() and (a[mask] == 0).all()
+
+
+def test_genalpha_without_dirichlet_conserves_heat(mf, orc):
+    # pure Neumann, F = 0: the total heat 1^T M phi is constant in time
+    import torch
+    prob = gen.thermal_q1_problem(5)
+    prob["source"] = 0.0
+    P, Mv, K, M = _transient_setup(mf, orc, prob, gen.lognormal(81, prob["conn"].shape[0], 0.3))
+    x = torch.from_numpy(prob["coords"][:, 0].copy()).cuda()
+    phi = torch.cos(np.pi * x)
+    u = torch.empty_like(phi)
+    a = torch.zeros_like(phi)
+    mf.mf_genalpha_initial_rate(P.csr, Mv, P.d, None, phi, u)
+    Md = _csr_t(P, Mv)
+    h0 = float((Md @ phi.cpu().numpy()).sum())
+    mf.mf_genalpha_run(P.csr, Mv, P.d, None, None, phi, u, a, mf.mf_genalpha_params_from_rho(0.5), 0.05, 5,
+                       pcg_tol=1e-13)
+    h1 = float((Md @ phi.cpu().numpy()).sum())
+    assert abs(h1 - h0) <= 1e-10 * np.abs(Md @ phi.cpu().numpy()).sum()
+
+
+def _csr_t(P, vals):
+    import scipy.sparse as sp
+    rp, ci = P.csr_arrays()
+    return sp.csr_matrix((vals.cpu().numpy(), ci.cpu().numpy(), rp.cpu().numpy()), shape=(P.n, P.n))
+
+
+def test_radiation_with_no_facets_is_linear(mf, orc):
+    # an empty radiation set changes nothing: bit-identical to the run without it
+    import torch
+    prob = gen.thermal_p1_problem(8)
+    P, Mv, K, M = _transient_setup(mf, orc, prob, np.ones(prob["conn"].shape[0]))
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    f = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    R = mf.mf_facets_create(P.mesh, P.pattern, e, f)
+    es = torch.zeros(0, dtype=torch.float64, device="cuda")
+    out = []
+    for rk in ({}, {"rad": R, "rad_es": es, "rad_tenv": es}):
+        phi = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(phi)
+        a = torch.zeros_like(phi)
+        mf.mf_genalpha_run(P.csr, Mv, P.d, P.bc_mask, P.bc_val, phi, u, a, mf.mf_genalpha_params_from_rho(0.5), 0.01,
+                           3, **rk)
+        out.append(phi.clone())
+    mf.mf_facets_destroy(R)
+    assert torch.equal(out[0], out[1])
+
+
+def test_radiation_facets_on_another_pattern_rejected(mf, orc):
+    import torch
+    p1 = gen.thermal_p1_problem(4)
+    P, Mv, K, M = _transient_setup(mf, orc, p1, np.ones(p1["conn"].shape[0]))
+    Q = mf.Problem(gen.thermal_p1_problem(4))
+    rad = gen.radiation_facets(p1, ("x1",))
+    Fh, es, te, keep = _gpu_radiation(mf, Q, rad)
+    x = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_genalpha_run(P.csr, Mv, P.d, None, None, x, x.clone(), x.clone(), mf.mf_genalpha_params_from_rho(0.5),
+                           0.01, 1, rad=Fh, rad_es=es, rad_tenv=te)
+    assert ei.value.status == mf.MF_ERR_INVALID_ARG
+    mf.mf_facets_destroy(Fh)
