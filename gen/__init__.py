@@ -163,6 +163,64 @@ def hex_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER, jitter_all: b
     return {"dim": 3, "elem": "Q1", "n": n, "coords": coords, "conn": conn}
 
 
+def hex20_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
+    """20-node serendipity bricks on the unit cube from an ``n^3`` grid.
+
+    Local nodes: the 8 vertices a = i + 2 j + 4 k at cube corner (i, j, k),
+    then the midpoints of the 12 edges: x edges at (y, z) = (j, k) are
+    8 + j + 2 k, y edges at (x, z) = (i, k) are 12 + i + 2 k, z edges at
+    (x, y) = (i, j) are 16 + i + 2 j.  Global numbering: the (n+1)^3 vertices
+    of ``hex_mesh``, then x, y and z edge midpoints (lexicographic, x
+    fastest).  Edges stay straight: a midpoint sits at the mean of its
+    (jittered) ends.
+    """
+    v = hex_mesh(n, jitter, seed)
+    nv = n + 1
+    X = v["coords"]
+    r = np.arange
+    mids, ids = [], {}
+    base = nv ** 3
+    for axis in range(3):
+        dims = [nv, nv, nv]
+        dims[axis] = n  # segments along the axis
+        k, j, i = np.meshgrid(r(dims[2]), r(dims[1]), r(dims[0]), indexing="ij")
+        i, j, k = i.ravel(), j.ravel(), k.ravel()
+        a = (k * nv + j) * nv + i
+        step = [1, nv, nv * nv][axis]
+        mids.append(0.5 * (X[a] + X[a + step]))
+        ids[axis] = (base, dims)
+        base += a.shape[0]
+    coords = np.concatenate([X] + mids, axis=0)
+    ne = n ** 3
+    kk, jj, ii = np.meshgrid(r(n), r(n), r(n), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    conn = np.empty((ne, 20), dtype=np.int64)
+    conn[:, :8] = v["conn"]
+    for axis in range(3):
+        off, dims = ids[axis]
+        for t in range(4):
+            b0, b1 = t & 1, t >> 1
+            if axis == 0:
+                gi, gj, gk = ii, jj + b0, kk + b1
+            elif axis == 1:
+                gi, gj, gk = ii + b0, jj, kk + b1
+            else:
+                gi, gj, gk = ii + b0, jj + b1, kk
+            conn[:, 8 + 4 * axis + t] = off + (gk * dims[1] + gj) * dims[0] + gi
+    return {"dim": 3, "elem": "Q2S", "n": n, "coords": coords, "conn": conn.astype(np.int32)}
+
+
+def thermal_q2s_problem(n: int, jitter: float = 0.15, sigma: float = 0.5,
+                        seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    """3D thermal conduction on 20-node serendipity bricks (u = 0 on the boundary, f = 1)."""
+    m = hex20_mesh(n, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)
+    m["bc_mask"], m["bc_val"] = thermal_bc(m)
+    m["form"] = "thermal"
+    m["source"] = 1.0
+    return m
+
+
 # ----------------------------------------------------------------------------
 # boundary data
 # ----------------------------------------------------------------------------

@@ -27,9 +27,9 @@
 #include <string.h>
 
 /* element kinds */
-enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2 };
+enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2, OR_Q2S = 3 };
 /* quadrature kinds */
-enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2 };
+enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3 };
 /* forms */
 enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2, OR_CAPACITY = 3 };
 
@@ -77,6 +77,20 @@ int or_quad(int kind, double *pts, double *w)
             }
         }
         return 6;
+    }
+    if (kind == OR_QHEX27) {
+        /* tensor Gauss-Legendre, 3 points per direction at 0, +-sqrt(3/5),
+         * weights 8/9, 5/9; point q = i + 3 j + 9 k */
+        const double g = sqrt(0.6);
+        const double p1[3] = {-g, 0.0, g}, w1[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+        for (int q = 0; q < 27; ++q) {
+            const int i = q % 3, j = (q / 3) % 3, k = q / 9;
+            pts[3 * q + 0] = p1[i];
+            pts[3 * q + 1] = p1[j];
+            pts[3 * q + 2] = p1[k];
+            w[q] = w1[i] * w1[j] * w1[k];
+        }
+        return 27;
     }
     if (kind == OR_QHEX8) {
         /* tensor Gauss-Legendre, 2 points per direction at +-1/sqrt(3), weight 1 */
@@ -141,11 +155,43 @@ int or_shape(int elem, const double *xi, double *N, double *dN)
         }
         return 8;
     }
+    if (elem == OR_Q2S) {
+        /* 20-node serendipity brick.  Vertex a = i + 2j + 4k at
+         * (xa, ya, za) = (2i-1, 2j-1, 2k-1):
+         *   N = (1 + x xa)(1 + y ya)(1 + z za)(x xa + y ya + z za - 2) / 8;
+         * edge midpoints at a zero coordinate, e.g. an x edge at (0, ya, za):
+         *   N = (1 - x^2)(1 + y ya)(1 + z za) / 4;
+         * x edges 8 + j + 2k, y edges 12 + i + 2k, z edges 16 + i + 2j. */
+        const double x = xi[0], y = xi[1], z = xi[2];
+        for (int a = 0; a < 8; ++a) {
+            const double xa = (a & 1) ? 1.0 : -1.0, ya = (a & 2) ? 1.0 : -1.0, za = (a & 4) ? 1.0 : -1.0;
+            const double A = 1.0 + x * xa, B = 1.0 + y * ya, Cz = 1.0 + z * za;
+            const double S = x * xa + y * ya + z * za - 2.0;
+            N[a] = 0.125 * A * B * Cz * S;
+            dN[3 * a + 0] = 0.125 * xa * B * Cz * (S + A);
+            dN[3 * a + 1] = 0.125 * ya * A * Cz * (S + B);
+            dN[3 * a + 2] = 0.125 * za * A * B * (S + Cz);
+        }
+        for (int axis = 0; axis < 3; ++axis)
+            for (int t = 0; t < 4; ++t) {
+                const int a = 8 + 4 * axis + t;
+                /* the two other coordinates in increasing axis order */
+                const int d1 = axis == 0 ? 1 : 0, d2 = axis == 2 ? 1 : 2;
+                const double s1 = (t & 1) ? 1.0 : -1.0, s2 = (t & 2) ? 1.0 : -1.0;
+                const double u = xi[axis], v1 = xi[d1], v2 = xi[d2];
+                const double Q = 1.0 - u * u, P1 = 1.0 + v1 * s1, P2 = 1.0 + v2 * s2;
+                N[a] = 0.25 * Q * P1 * P2;
+                dN[3 * a + axis] = 0.25 * (-2.0 * u) * P1 * P2;
+                dN[3 * a + d1] = 0.25 * Q * s1 * P2;
+                dN[3 * a + d2] = 0.25 * Q * P1 * s2;
+            }
+        return 20;
+    }
     return -1;
 }
 
-static int elem_dim(int elem) { return elem == OR_Q1 ? 3 : 2; }
-static int elem_npe(int elem) { return elem == OR_P1 ? 3 : (elem == OR_P2 ? 6 : 8); }
+static int elem_dim(int elem) { return elem >= OR_Q1 ? 3 : 2; }
+static int elem_npe(int elem) { return elem == OR_P1 ? 3 : (elem == OR_P2 ? 6 : (elem == OR_Q1 ? 8 : 20)); }
 
 /* Geometry at one point: J_ij = sum_a x_{a,i} dN_a/dxi_j, detJ, and the
  * physical gradients grad N_a = J^{-T} gradref N_a (Sec. 2.1: D_lambda N at
@@ -155,7 +201,7 @@ static double geometry(int elem, const double *X, const double *xi, double *N, d
 {
     const int dim = elem_dim(elem);
     const int npe = elem_npe(elem);
-    double dN[8 * 3];
+    double dN[20 * 3];
     or_shape(elem, xi, N, dN);
     double J[3][3] = {{0}};
     if (elem == OR_P2) {
@@ -203,7 +249,7 @@ static double geometry(int elem, const double *X, const double *xi, double *N, d
 /* Exported for the geometry pins: sum_q w_q detJ_q (the element measure). */
 double or_elem_measure(int elem, int quad, const double *X)
 {
-    double pts[8 * 3], w[8], N[8], g[24];
+    double pts[27 * 3], w[27], N[20], g[60];
     const int nq = or_quad(quad, pts, w);
     const int dim = elem_dim(elem);
     double s = 0.0;
@@ -220,7 +266,7 @@ double or_elem_measure(int elem, int quad, const double *X)
 double or_elem_thermal(int elem, int quad, const double *X, double k, double fconst,
                        const double *fnodal, double *Ke, double *de)
 {
-    double pts[8 * 3], w[8], N[8], g[24];
+    double pts[27 * 3], w[27], N[20], g[60];
     const int nq = or_quad(quad, pts, w);
     const int dim = elem_dim(elem), npe = elem_npe(elem);
     double mindet = 1e300;
@@ -253,12 +299,12 @@ double or_elem_thermal(int elem, int quad, const double *X, double k, double fco
 /* Capacity element (Sec. 4.1: -C(T, T_t), the rate term; tangent negated):  */
 /* Me[a][b] = sum_q w detJ C N_a N_b, with a rule exact for N_a N_b on an    */
 /* affine element: the 3-point rule (P1, degree 2), the 6-point rule (P2,    */
-/* degree 4), 2 x 2 x 2 Gauss (Q1).  Returns min detJ.                       */
+/* degree 4), 2 x 2 x 2 Gauss (Q1), 3 x 3 x 3 Gauss (Q2S).  Returns min detJ.*/
 /* ------------------------------------------------------------------------ */
 double or_elem_capacity(int elem, const double *X, double C, double *Me)
 {
-    double pts[8 * 3], w[8], N[8], g[24];
-    const int quad = elem == OR_P1 ? OR_QTRI3 : (elem == OR_P2 ? OR_QTRI6 : OR_QHEX8);
+    double pts[27 * 3], w[27], N[20], g[60];
+    const int quad = elem == OR_P1 ? OR_QTRI3 : (elem == OR_P2 ? OR_QTRI6 : (elem == OR_Q1 ? OR_QHEX8 : OR_QHEX27));
     const int nq = or_quad(quad, pts, w);
     const int dim = elem_dim(elem), npe = elem_npe(elem);
     double mindet = 1e300;
@@ -376,6 +422,7 @@ double or_elem_oseen(const double *X, const double *aN, double mu, double rho,
 /* ------------------------------------------------------------------------ */
 int or_facet_nodes(int elem, int face, int *loc)
 {
+    if (elem == OR_Q2S) return -1; /* no facet terms on serendipity bricks */
     if (elem == OR_Q1) {
         if (face < 0 || face > 5) return -1;
         const int d = face / 2, s = face % 2;
@@ -640,7 +687,7 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
     const int dim = elem_dim(p->elem), npe = elem_npe(p->elem);
     for (int64_t g = 0; g < n; ++g)
         if (coo_push(c, g, g, 0.0)) return -1;
-    double X[8 * 3], Ke[24 * 24], de[24], fn[8];
+    double X[20 * 3], Ke[24 * 24], de[24], fn[20];
     for (int64_t e = 0; e < p->n_el; ++e) {
         const int32_t *cn = p->conn + e * npe;
         if (keep) {
