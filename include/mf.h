@@ -50,7 +50,7 @@ typedef enum {
     MF_ERR_UNSUPPORTED = 8   /* combination not provided (e.g. node valence too high) */
 } mf_status;
 
-typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2 } mf_elem;
+typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2, MF_Q2S_HEX = 3 } mf_elem;
 typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2, MF_FORM_CAPACITY = 3 } mf_form;
 typedef enum { MF_PREC_FP64 = 0, MF_PREC_MIXED = 1 } mf_prec;
 typedef enum { MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1 } mf_solver;
@@ -61,7 +61,12 @@ typedef struct mf_pattern mf_pattern;
 /* Mesh description (Block B-1: elements and their element->control-point map).
  * coords [n_nodes][dim] f64 AoS; conn [n_elems][npe] int32 with npe = 3 (P1),
  * 6 (P2: vertices, then midpoints of edges (0,1), (1,2), (2,0)), 8 (Q1: node
- * a = i + 2j + 4k at reference corner (2i-1, 2j-1, 2k-1)).  Triangles are
+ * a = i + 2j + 4k at reference corner (2i-1, 2j-1, 2k-1)), 20 (Q2S: the
+ * 20-node serendipity brick of the paper's experiments; the 8 vertices as Q1,
+ * then the edge midpoints: x edges 8 + j + 2k at (0, 2j-1, 2k-1), y edges
+ * 12 + i + 2k, z edges 16 + i + 2j; edges straight, midpoints at the mean of
+ * their ends, so the geometry is the vertices' trilinear map; thermal form,
+ * FP64, 3 x 3 x 3 Gauss, up to 128 neighbours per node).  Triangles are
  * counter-clockwise.  For the flow form, pconn [n_elems][3] gives the P1
  * pressure nodes (the element's vertices in a 0..n_pnodes-1 numbering). */
 typedef struct {

@@ -68,6 +68,85 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
     else if (!q1_translate(e, tr, kc, status)) elem_capacity_q1(e, X, conn, kc, map, out, status);
 }
 
+// 20-node serendipity brick, thermal form (Sec. 4.1), 3 x 3 x 3 Gauss: one
+// warp per element.  Lanes q < 27 take the geometry of Gauss point q from the
+// vertices' trilinear map (w detJ and J^-1) into shared memory; lanes a < 20
+// then form the physical gradient of their shape function at every point and
+// store it; finally lane a sums row a of K_e = k sum_q w detJ grad N_a .
+// grad N_b over the 20 gradients in shared memory, and d_e[a] = f sum_q w detJ
+// N_a.  Output as the other thermal elements (incidence layout).
+constexpr int Q2W = 3;  // elements (warps) per block (45 KB of shared memory)
+
+__global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, const double *__restrict__ X,
+                                                               const int32_t *__restrict__ conn,
+                                                               const double *__restrict__ kc, double f,
+                                                               const int32_t *__restrict__ map,
+                                                               double *__restrict__ out, int *status)
+{
+    __shared__ double geo[Q2W][27][10];      // w detJ, J^-1 (row-major)
+    __shared__ double grd[Q2W][27][20][3];   // physical gradients
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * Q2W + w;
+    if (e >= n_el) return;  // warp-uniform
+    const int32_t *ce = conn + e * 20;
+    if (lane < 27) {
+        double x[8][3], c[8][3];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)ce[a] + i];
+        q1_wht(x, c);
+#pragma unroll
+        for (int S = 1; S < 8; ++S)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) c[S][i] *= (__popc(S) & 1) ? -0.125 : 0.125;
+        const double g3 = 0.77459666924148337704;  // sqrt(3/5)
+        const int qi = lane % 3, qj = (lane / 3) % 3, qk = lane / 9;
+        double Ji[3][3];
+        const double det = q1_jac_at(c, (qi - 1) * g3, (qj - 1) * g3, (qk - 1) * g3, Ji);
+        const double w1[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+        geo[w][lane][0] = w1[qi] * w1[qj] * w1[qk] * det;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) geo[w][lane][1 + 3 * i + j] = Ji[i][j];
+    }
+    __syncwarp();
+    const double g3 = 0.77459666924148337704;
+    double m = 0.0;  // sum_q w detJ N_a
+    if (lane < 20) {
+        for (int q = 0; q < 27; ++q) {
+            const double xi[3] = {(q % 3 - 1) * g3, ((q / 3) % 3 - 1) * g3, (q / 9 - 1) * g3};
+            double gr[3];
+            const double N = q2s_shape(lane, xi, gr);
+            const double *G = geo[w][q];
+            m = fma(G[0], N, m);
+            // physical gradient: grad N = J^-T gradref N, (J^-1)_ji at G[1 + 3 j + i]
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                grd[w][q][lane][i] = gr[0] * G[1 + i] + gr[1] * G[4 + i] + gr[2] * G[7 + i];
+        }
+    }
+    __syncwarp();
+    if (lane >= 20) return;
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    double row[20];
+#pragma unroll
+    for (int b = 0; b < 20; ++b) row[b] = 0.0;
+    for (int q = 0; q < 27; ++q) {
+        const double wd = geo[w][q][0];
+        const double ga0 = wd * grd[w][q][lane][0], ga1 = wd * grd[w][q][lane][1], ga2 = wd * grd[w][q][lane][2];
+#pragma unroll
+        for (int b = 0; b < 20; ++b)
+            row[b] = fma(ga0, grd[w][q][b][0], fma(ga1, grd[w][q][b][1], fma(ga2, grd[w][q][b][2], row[b])));
+    }
+    const int64_t base = (int64_t)map[e * 20 + lane] * 21;
+#pragma unroll
+    for (int b = 0; b < 20; ++b) out[base + b] = k * row[b];
+    out[base + 20] = f * m;
+}
+
 // Q1 elasticity, one element per thread.  The scaled gradients
 // sqrt(w detJ) gradN_a(q) of all 8 points go to shared memory (each thread its
 // own column, no synchronisation), then every block pair a <= b contracts
@@ -246,7 +325,7 @@ __global__ void __launch_bounds__(GT_WARPS * 32, 3) k_gather_th(
     double *__restrict__ d)
 {
     constexpr int L = th_lanes<NPE>(), G = 32 / L;  // G nodes per warp
-    __shared__ double acc_all[GT_WARPS * G][MF_MAX_DEG];
+    __shared__ double acc_all[GT_WARPS * G][NPE > 8 ? MF_MAX_DEG_HO : MF_MAX_DEG];
     const int lane = threadIdx.x & 31, grp = threadIdx.x / L;
     const int64_t n = (int64_t)blockIdx.x * (GT_WARPS * G) + grp;
     if (n >= n_nodes) return;  // group-uniform
@@ -676,9 +755,13 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         mf_prof_begin(cap ? "elem_capacity"
                       : m->elem == MF_P1_TRI ? "elem_thermal_p1"
                       : m->elem == MF_P2_TRI ? "elem_thermal_p2"
-                                             : "elem_thermal_q1",
+                      : m->elem == MF_Q1_HEX ? "elem_thermal_q1"
+                                             : "elem_thermal_q2s",
                       st);
-        if (cap)
+        if (m->elem == MF_Q2S_HEX)
+            k_elem_thermal_q2s<<<nblk(ne, Q2W), Q2W * 32, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f,
+                                                                   p->elem_inc, p->scratch, status);
+        else if (cap)
             k_elem_capacity<<<nblk(ne, 128), 128, 0, st>>>(m->elem, ne, m->coords, m->conn, c->elem_coef, p->tr,
                                                            p->elem_inc, p->scratch, status);
         else if (m->elem == MF_P1_TRI)
@@ -700,7 +783,8 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         c->bc_mask, c->bc_val, p->row_ptr, values, d)
         if (m->elem == MF_P1_TRI) MF_GATHER_TH(3);
         else if (m->elem == MF_P2_TRI) MF_GATHER_TH(6);
-        else MF_GATHER_TH(8);
+        else if (m->elem == MF_Q1_HEX) MF_GATHER_TH(8);
+        else MF_GATHER_TH(20);
 #undef MF_GATHER_TH
         mf_prof_end(st);
     } else if (form == MF_FORM_ELASTIC) {

@@ -60,9 +60,9 @@ __device__ __forceinline__ void q1_wht(const double (&x)[8][3], double (&H)[8][3
 // J^-1 and detJ at Gauss point q from the map coefficients c (c[S][i] as
 // above): column j of J is d x / d xi_j = sum_{S containing j} c_S prod_{k in
 // S, k != j} xi_k, three FMAs per entry.
-__device__ __forceinline__ double q1_jac_coef(const double (&c)[8][3], int q, double (&Ji)[3][3])
+__device__ __forceinline__ double q1_jac_at(const double (&c)[8][3], double xs, double ys, double zs,
+                                            double (&Ji)[3][3])
 {
-    const double xs = (q & 1) ? QG : -QG, ys = (q & 2) ? QG : -QG, zs = (q & 4) ? QG : -QG;
     double J[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -85,6 +85,39 @@ __device__ __forceinline__ double q1_jac_coef(const double (&c)[8][3], int q, do
     Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
     Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
     return det;
+}
+
+// q1_jac_at at the 2 x 2 x 2 Gauss point q
+__device__ __forceinline__ double q1_jac_coef(const double (&c)[8][3], int q, double (&Ji)[3][3])
+{
+    return q1_jac_at(c, (q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG, Ji);
+}
+
+// 20-node serendipity brick: shape function a and its reference gradient at
+// xi.  Vertex a = i + 2j + 4k at (2i-1, 2j-1, 2k-1):
+// N = (1 + x xa)(1 + y ya)(1 + z za)(x xa + y ya + z za - 2) / 8; edge
+// midpoints (x edges 8 + j + 2k, y edges 12 + i + 2k, z edges 16 + i + 2j)
+// with zero coordinate along their edge: N = (1 - u^2)(1 + v1 s1)(1 + v2 s2) / 4,
+// v1, v2 the other two coordinates in increasing axis order.
+__device__ __forceinline__ double q2s_shape(int a, const double (&xi)[3], double (&g)[3])
+{
+    if (a < 8) {
+        const double xa = (a & 1) ? 1.0 : -1.0, ya = (a & 2) ? 1.0 : -1.0, za = (a & 4) ? 1.0 : -1.0;
+        const double A = 1.0 + xi[0] * xa, B = 1.0 + xi[1] * ya, Cz = 1.0 + xi[2] * za;
+        const double S = xi[0] * xa + xi[1] * ya + xi[2] * za - 2.0;
+        g[0] = 0.125 * xa * B * Cz * (S + A);
+        g[1] = 0.125 * ya * A * Cz * (S + B);
+        g[2] = 0.125 * za * A * B * (S + Cz);
+        return 0.125 * A * B * Cz * S;
+    }
+    const int axis = (a - 8) >> 2, t = (a - 8) & 3;
+    const int d1 = axis == 0 ? 1 : 0, d2 = axis == 2 ? 1 : 2;
+    const double s1 = (t & 1) ? 1.0 : -1.0, s2 = (t & 2) ? 1.0 : -1.0;
+    const double u = xi[axis], Q = 1.0 - u * u, P1 = 1.0 + xi[d1] * s1, P2 = 1.0 + xi[d2] * s2;
+    g[axis] = -0.5 * u * P1 * P2;
+    g[d1] = 0.25 * Q * s1 * P2;
+    g[d2] = 0.25 * Q * P1 * s2;
+    return 0.25 * Q * P1 * P2;
 }
 
 // affine triangle from its first three nodes: detJ and grad lambda_k
@@ -467,9 +500,10 @@ __device__ __forceinline__ bool q1_translate(int64_t e, const uint8_t *__restric
     return true;
 }
 
-// Lanes per node of the thermal gather: 4 for P1, 8 for P2 and Q1.
+// Lanes per node of the thermal gather: 4 for P1, 8 for P2 and Q1, a warp for
+// the 20-node brick.
 template <int NPE>
-constexpr int th_lanes() { return NPE <= 4 ? 4 : 8; }
+constexpr int th_lanes() { return NPE <= 4 ? 4 : (NPE <= 8 ? 8 : 32); }
 
 // Thermal row of node n by a group of th_lanes<NPE>() lanes (`sub` = lane in
 // the group, `gmask` = the group's lanes; groups of a warp are independent).

@@ -10,6 +10,7 @@
 #include "mf_device.cuh"
 
 #define MF_MAX_DEG 64   // neighbours of one node in one adjacency
+#define MF_MAX_DEG_HO 128  // the same for the 20-node serendipity brick
 #define MF_SLABS 1      // element chunks of the mixed elasticity assembly (see plan_slabs)
 #define MF_MAX_INC 32   // elements incident to one node
 
@@ -132,8 +133,11 @@ mf_status mf_cuda_check(cudaError_t e, const char *what);
 // exclusive scan of n int64 counts in place; total written to *d_total (device)
 cudaError_t mf_scan_i64(int64_t *d_data, int64_t n, int64_t *d_total, cudaStream_t st);
 
-static inline int mf_npe(int elem) { return elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : 8); }
-static inline int mf_ndim(int elem) { return elem == MF_Q1_HEX ? 3 : 2; }
+static inline int mf_npe(int elem)
+{
+    return elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : (elem == MF_Q1_HEX ? 8 : 20));
+}
+static inline int mf_ndim(int elem) { return elem >= MF_Q1_HEX ? 3 : 2; }
 
 // pattern / assembly entry points implemented in the .cu files
 mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_pattern *p);

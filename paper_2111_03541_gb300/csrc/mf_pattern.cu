@@ -30,7 +30,7 @@ __global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_el) return;
-    const int npe = elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : 8);
+    const int npe = elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : (elem == MF_Q1_HEX ? 8 : 20));
     for (int a = 0; a < npe; ++a) {
         const int32_t v = conn[e * npe + a];
         if (v < 0 || v >= n_nodes) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
@@ -40,7 +40,7 @@ __global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double
             const int32_t v = pconn[e * 3 + a];
             if (v < 0 || v >= n_p) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
         }
-    if (elem != MF_Q1_HEX) {
+    if (elem == MF_P1_TRI || elem == MF_P2_TRI) {
         const int32_t *c = conn + e * npe;
         const double x0 = X[2 * c[0]], y0 = X[2 * c[0] + 1];
         const double x1 = X[2 * c[1]], y1 = X[2 * c[1] + 1];
@@ -50,12 +50,26 @@ __global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double
         if (!(det > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
         return;
     }
+    // hexahedra: the trilinear map of the 8 vertices (also the geometry of a
+    // straight-edged serendipity brick) at the 2 x 2 x 2 (Q1) or 3 x 3 x 3
+    // (Q2S) Gauss points
     double x[8][3];
     for (int a = 0; a < 8; ++a)
-        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[e * 8 + a] + i];
+        for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)conn[e * npe + a] + i];
     const double g = 0.57735026918962576451;  // 1/sqrt(3)
-    for (int q = 0; q < 8; ++q) {
-        const double xi[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+    const double g3 = 0.77459666924148337704;  // sqrt(3/5)
+    const int nq = elem == MF_Q1_HEX ? 8 : 27;
+    for (int q = 0; q < nq; ++q) {
+        double xi[3];
+        if (elem == MF_Q1_HEX) {
+            xi[0] = (q & 1) ? g : -g;
+            xi[1] = (q & 2) ? g : -g;
+            xi[2] = (q & 4) ? g : -g;
+        } else {
+            xi[0] = (q % 3 - 1) * g3;
+            xi[1] = ((q / 3) % 3 - 1) * g3;
+            xi[2] = (q / 9 - 1) * g3;
+        }
         double J[3][3] = {};
         for (int a = 0; a < 8; ++a) {
             const double s[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
@@ -124,14 +138,14 @@ __global__ void k_sort_segments_i32(int64_t n, const int64_t *__restrict__ ptr, 
 // ---------------------------------------------------------------------------
 // adjacency between row space (conn_r, npe_r) and column space (conn_c, npe_c)
 // ---------------------------------------------------------------------------
-template <bool FILL>
+template <bool FILL, int MAXD>
 __global__ void k_adj(int64_t n_rows, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
                       int npe_c, const int32_t *__restrict__ conn_c, bool self, int64_t *cnt,
                       const int64_t *__restrict__ ptr, int32_t *col, int *status)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rows) return;
-    int32_t nb[MF_MAX_DEG];
+    int32_t nb[MAXD];
     int deg = 0;
     if (self) nb[deg++] = (int32_t)r;  // square adjacency: the diagonal is always present
     const int64_t b = inc_ptr[r], e = inc_ptr[r + 1];
@@ -143,7 +157,7 @@ __global__ void k_adj(int64_t n_rows, const int64_t *__restrict__ inc_ptr, const
             int pos = 0;
             while (pos < deg && nb[pos] < m) ++pos;
             if (pos < deg && nb[pos] == m) continue;
-            if (deg == MF_MAX_DEG) { mf_dev_fail(status, MF_ERR_UNSUPPORTED); return; }
+            if (deg == MAXD) { mf_dev_fail(status, MF_ERR_UNSUPPORTED); return; }
             for (int s = deg; s > pos; --s) nb[s] = nb[s - 1];
             nb[pos] = m;
             ++deg;
@@ -412,8 +426,14 @@ mf_status build_adj(int64_t n_rows, const Incidence &inc, const int32_t *conn_r,
     MF_CUDA(cudaMallocAsync(&A->ptr, sizeof(int64_t) * (n_rows + 1), st));
     MF_CUDA(cudaMemsetAsync(A->ptr, 0, sizeof(int64_t) * (n_rows + 1), st));
     const bool self = conn_r == conn_c;
-    k_adj<false><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self, A->ptr,
-                                                   nullptr, nullptr, status);
+    // the 20-node brick (npe 20) has up to 81 neighbours per node on a grid
+    const bool wide = npe_c > 8;
+    if (wide)
+        k_adj<false, MF_MAX_DEG_HO><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self,
+                                                                      A->ptr, nullptr, nullptr, status);
+    else
+        k_adj<false, MF_MAX_DEG><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self,
+                                                                   A->ptr, nullptr, nullptr, status);
     MF_CUDA(cudaGetLastError());
     mf_status s = check_status(status, st, "mf_pattern_build");
     if (s != MF_OK) return s;
@@ -421,8 +441,12 @@ mf_status build_adj(int64_t n_rows, const Incidence &inc, const int32_t *conn_r,
     s = read_i64(A->ptr + n_rows, &A->n_pairs, st);
     if (s != MF_OK) return s;
     MF_CUDA(cudaMallocAsync(&A->col, sizeof(int32_t) * A->n_pairs, st));
-    k_adj<true><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self, nullptr,
-                                                  A->ptr, A->col, status);
+    if (wide)
+        k_adj<true, MF_MAX_DEG_HO><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self,
+                                                                     nullptr, A->ptr, A->col, status);
+    else
+        k_adj<true, MF_MAX_DEG><<<nblk(n_rows, 128), 128, 0, st>>>(n_rows, inc.ptr, inc.inc, npe_c, conn_c, self,
+                                                                  nullptr, A->ptr, A->col, status);
     return check_status(status, st, "mf_pattern_build");
 }
 
