@@ -69,12 +69,17 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
 }
 
 // 20-node serendipity brick, thermal form (Sec. 4.1), 3 x 3 x 3 Gauss: one
-// warp per element.  Lanes q < 27 take the geometry of Gauss point q from the
-// vertices' trilinear map (w detJ and J^-1) into shared memory; lanes a < 20
-// then form the physical gradient of their shape function at every point and
-// store it; finally lane a sums row a of K_e = k sum_q w detJ grad N_a .
-// grad N_b over the 20 gradients in shared memory, and d_e[a] = f sum_q w detJ
-// N_a.  Output as the other thermal elements (incidence layout).
+// warp per element, every phase spread over all 32 lanes (the kernel is
+// bound by the FP64 pipe, whose warp instructions cost the same with 20 or
+// 32 lanes active; the shape values and reference gradients at the 27 points
+// come from a table).  (1) lanes q < 27 take the geometry of Gauss point q
+// from the vertices' trilinear map: w detJ, its square root and J^-1; (2) the
+// 540 (node, point) items form sqrt(w detJ) times the physical gradients
+// (detJ > 0 at every point is checked when the mesh is made); (3) the 210
+// pairs a <= b of K_e = k sum_q w detJ grad N_a . grad N_b are spread over the
+// lanes (6 or 7 each) and written to rows a and b; lanes a < 20 add d_e[a] =
+// f sum_q w detJ N_a.  Output as the other thermal elements (incidence
+// layout).
 constexpr int Q2W = 3;  // elements (warps) per block (45 KB of shared memory)
 
 __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, const double *__restrict__ X,
@@ -83,13 +88,14 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
                                                                const int32_t *__restrict__ map,
                                                                double *__restrict__ out, int *status)
 {
-    __shared__ double geo[Q2W][27][10];      // w detJ, J^-1 (row-major)
-    __shared__ double grd[Q2W][27][20][3];   // physical gradients
+    __shared__ double geo[Q2W][27][11];      // w detJ, sqrt(w detJ), J^-1 (row-major)
+    __shared__ double grd[Q2W][27][20][3];   // sqrt(w detJ) times the physical gradients
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * Q2W + w;
     if (e >= n_el) return;  // warp-uniform
     const int32_t *ce = conn + e * 20;
     if (lane < 27) {
+        const double g3 = 0.77459666924148337704;  // sqrt(3/5)
         double x[8][3], c[8][3];
 #pragma unroll
         for (int a = 0; a < 8; ++a)
@@ -100,51 +106,54 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
         for (int S = 1; S < 8; ++S)
 #pragma unroll
             for (int i = 0; i < 3; ++i) c[S][i] *= (__popc(S) & 1) ? -0.125 : 0.125;
-        const double g3 = 0.77459666924148337704;  // sqrt(3/5)
         const int qi = lane % 3, qj = (lane / 3) % 3, qk = lane / 9;
         double Ji[3][3];
         const double det = q1_jac_at(c, (qi - 1) * g3, (qj - 1) * g3, (qk - 1) * g3, Ji);
-        const double w1[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
-        geo[w][lane][0] = w1[qi] * w1[qj] * w1[qk] * det;
+        const double wi = qi == 1 ? 8.0 / 9.0 : 5.0 / 9.0, wj = qj == 1 ? 8.0 / 9.0 : 5.0 / 9.0,
+                     wk = qk == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
+        const double wd = wi * wj * wk * det;
+        geo[w][lane][0] = wd;
+        geo[w][lane][1] = sqrt(wd);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) geo[w][lane][1 + 3 * i + j] = Ji[i][j];
+            for (int j = 0; j < 3; ++j) geo[w][lane][2 + 3 * i + j] = Ji[i][j];
     }
     __syncwarp();
-    const double g3 = 0.77459666924148337704;
-    double m = 0.0;  // sum_q w detJ N_a
-    if (lane < 20) {
-        for (int q = 0; q < 27; ++q) {
-            const double xi[3] = {(q % 3 - 1) * g3, ((q / 3) % 3 - 1) * g3, (q / 9 - 1) * g3};
-            double gr[3];
-            const double N = q2s_shape(lane, xi, gr);
-            const double *G = geo[w][q];
-            m = fma(G[0], N, m);
-            // physical gradient: grad N = J^-T gradref N, (J^-1)_ji at G[1 + 3 j + i]
+    for (int it = lane; it < 540; it += 32) {
+        const int q = it / 20, a = it - 20 * q;
+        const double *T = c_q2s_tab[q][a];
+        const double *G = geo[w][q];
+        const double sw = G[1];
+        // physical gradient: grad N = J^-T gradref N, (J^-1)_ji at G[2 + 3 j + i]
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-                grd[w][q][lane][i] = gr[0] * G[1 + i] + gr[1] * G[4 + i] + gr[2] * G[7 + i];
-        }
+        for (int i = 0; i < 3; ++i) grd[w][q][a][i] = sw * (T[1] * G[2 + i] + T[2] * G[5 + i] + T[3] * G[8 + i]);
     }
     __syncwarp();
-    if (lane >= 20) return;
     const double k = kc[e];
     if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
-    double row[20];
-#pragma unroll
-    for (int b = 0; b < 20; ++b) row[b] = 0.0;
-    for (int q = 0; q < 27; ++q) {
-        const double wd = geo[w][q][0];
-        const double ga0 = wd * grd[w][q][lane][0], ga1 = wd * grd[w][q][lane][1], ga2 = wd * grd[w][q][lane][2];
-#pragma unroll
-        for (int b = 0; b < 20; ++b)
-            row[b] = fma(ga0, grd[w][q][b][0], fma(ga1, grd[w][q][b][1], fma(ga2, grd[w][q][b][2], row[b])));
+    // pair p = lane + 32 t (t < 7, p < 210) of the upper triangle, row-major:
+    // a from the triangular numbering, b = a + offset
+    for (int p = lane; p < 210; p += 32) {
+        int a = 0, rem = p;
+        while (rem >= 20 - a) {
+            rem -= 20 - a;
+            ++a;
+        }
+        const int bb = a + rem;
+        double v = 0.0;
+        for (int q = 0; q < 27; ++q)
+            v = fma(grd[w][q][a][0], grd[w][q][bb][0],
+                    fma(grd[w][q][a][1], grd[w][q][bb][1], fma(grd[w][q][a][2], grd[w][q][bb][2], v)));
+        const double kv = k * v;
+        out[(int64_t)map[e * 20 + a] * 21 + bb] = kv;
+        out[(int64_t)map[e * 20 + bb] * 21 + a] = kv;
     }
-    const int64_t base = (int64_t)map[e * 20 + lane] * 21;
-#pragma unroll
-    for (int b = 0; b < 20; ++b) out[base + b] = k * row[b];
-    out[base + 20] = f * m;
+    if (lane < 20) {
+        double m = 0.0;
+        for (int q = 0; q < 27; ++q) m = fma(geo[w][q][0], c_q2s_tab[q][lane][0], m);
+        out[(int64_t)map[e * 20 + lane] * 21 + 20] = f * m;
+    }
 }
 
 // Q1 elasticity, one element per thread.  The scaled gradients

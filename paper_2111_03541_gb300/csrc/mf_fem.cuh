@@ -93,33 +93,6 @@ __device__ __forceinline__ double q1_jac_coef(const double (&c)[8][3], int q, do
     return q1_jac_at(c, (q & 1) ? QG : -QG, (q & 2) ? QG : -QG, (q & 4) ? QG : -QG, Ji);
 }
 
-// 20-node serendipity brick: shape function a and its reference gradient at
-// xi.  Vertex a = i + 2j + 4k at (2i-1, 2j-1, 2k-1):
-// N = (1 + x xa)(1 + y ya)(1 + z za)(x xa + y ya + z za - 2) / 8; edge
-// midpoints (x edges 8 + j + 2k, y edges 12 + i + 2k, z edges 16 + i + 2j)
-// with zero coordinate along their edge: N = (1 - u^2)(1 + v1 s1)(1 + v2 s2) / 4,
-// v1, v2 the other two coordinates in increasing axis order.
-__device__ __forceinline__ double q2s_shape(int a, const double (&xi)[3], double (&g)[3])
-{
-    if (a < 8) {
-        const double xa = (a & 1) ? 1.0 : -1.0, ya = (a & 2) ? 1.0 : -1.0, za = (a & 4) ? 1.0 : -1.0;
-        const double A = 1.0 + xi[0] * xa, B = 1.0 + xi[1] * ya, Cz = 1.0 + xi[2] * za;
-        const double S = xi[0] * xa + xi[1] * ya + xi[2] * za - 2.0;
-        g[0] = 0.125 * xa * B * Cz * (S + A);
-        g[1] = 0.125 * ya * A * Cz * (S + B);
-        g[2] = 0.125 * za * A * B * (S + Cz);
-        return 0.125 * A * B * Cz * S;
-    }
-    const int axis = (a - 8) >> 2, t = (a - 8) & 3;
-    const int d1 = axis == 0 ? 1 : 0, d2 = axis == 2 ? 1 : 2;
-    const double s1 = (t & 1) ? 1.0 : -1.0, s2 = (t & 2) ? 1.0 : -1.0;
-    const double u = xi[axis], Q = 1.0 - u * u, P1 = 1.0 + xi[d1] * s1, P2 = 1.0 + xi[d2] * s2;
-    g[axis] = -0.5 * u * P1 * P2;
-    g[d1] = 0.25 * Q * s1 * P2;
-    g[d2] = 0.25 * Q * P1 * s2;
-    return 0.25 * Q * P1 * P2;
-}
-
 // affine triangle from its first three nodes: detJ and grad lambda_k
 __device__ __forceinline__ double tri_affine(const double *__restrict__ X, const int32_t *__restrict__ c,
                                              double (&gl)[3][2])
@@ -182,9 +155,41 @@ __device__ __forceinline__ int upair(int a, int b) { return a * (15 - a) / 2 + b
 __constant__ double c_Ms[6][6][6];
 __constant__ double c_R[3][3][6];
 
-// Host: the reference sums, uploaded to this translation unit's copy of c_Ms
-// and c_R on the current device (each file that includes this header and
-// launches a kernel using them uploads its own copy).
+// 20-node serendipity brick: shape function a and its reference gradient at
+// xi.  Vertex a = i + 2j + 4k at (2i-1, 2j-1, 2k-1):
+// N = (1 + x xa)(1 + y ya)(1 + z za)(x xa + y ya + z za - 2) / 8; edge
+// midpoints (x edges 8 + j + 2k, y edges 12 + i + 2k, z edges 16 + i + 2j)
+// with zero coordinate along their edge: N = (1 - u^2)(1 + v1 s1)(1 + v2 s2) / 4,
+// v1, v2 the other two coordinates in increasing axis order.
+__host__ __device__ inline double q2s_shape(int a, const double (&xi)[3], double (&g)[3])
+{
+    if (a < 8) {
+        const double xa = (a & 1) ? 1.0 : -1.0, ya = (a & 2) ? 1.0 : -1.0, za = (a & 4) ? 1.0 : -1.0;
+        const double A = 1.0 + xi[0] * xa, B = 1.0 + xi[1] * ya, Cz = 1.0 + xi[2] * za;
+        const double S = xi[0] * xa + xi[1] * ya + xi[2] * za - 2.0;
+        g[0] = 0.125 * xa * B * Cz * (S + A);
+        g[1] = 0.125 * ya * A * Cz * (S + B);
+        g[2] = 0.125 * za * A * B * (S + Cz);
+        return 0.125 * A * B * Cz * S;
+    }
+    const int axis = (a - 8) >> 2, t = (a - 8) & 3;
+    const int d1 = axis == 0 ? 1 : 0, d2 = axis == 2 ? 1 : 2;
+    const double s1 = (t & 1) ? 1.0 : -1.0, s2 = (t & 2) ? 1.0 : -1.0;
+    const double u = xi[axis], Q = 1.0 - u * u, P1 = 1.0 + xi[d1] * s1, P2 = 1.0 + xi[d2] * s2;
+    g[axis] = -0.5 * u * P1 * P2;
+    g[d1] = 0.25 * Q * s1 * P2;
+    g[d2] = 0.25 * Q * P1 * s2;
+    return 0.25 * Q * P1 * P2;
+}
+
+// 20-node brick at the 27 points of the 3 x 3 x 3 Gauss rule (point q = i +
+// 3 j + 9 k at ((i - 1), (j - 1), (k - 1)) sqrt(3/5)): [q][a] = N_a, then the
+// reference gradient (global memory: lanes read different nodes)
+__device__ double c_q2s_tab[27][20][4];
+
+// Host: the reference sums, uploaded to this translation unit's copy of c_Ms,
+// c_R and c_q2s_tab on the current device (each file that includes this
+// header and launches a kernel using them uploads its own copy).
 inline mf_status fem_consts_upload()
 {
     double Ms[6][6][6] = {}, R[3][3][6] = {};
@@ -214,6 +219,17 @@ inline mf_status fem_consts_upload()
     }
     MF_CUDA(cudaMemcpyToSymbol(c_Ms, Ms, sizeof Ms));
     MF_CUDA(cudaMemcpyToSymbol(c_R, R, sizeof R));
+    static double tab[27][20][4];
+    const double g3 = 0.77459666924148337704;  // sqrt(3/5)
+    for (int q = 0; q < 27; ++q) {
+        const double xi[3] = {(q % 3 - 1) * g3, ((q / 3) % 3 - 1) * g3, (q / 9 - 1) * g3};
+        for (int a = 0; a < 20; ++a) {
+            double g[3];
+            tab[q][a][0] = q2s_shape(a, xi, g);
+            for (int i = 0; i < 3; ++i) tab[q][a][1 + i] = g[i];
+        }
+    }
+    MF_CUDA(cudaMemcpyToSymbol(c_q2s_tab, tab, sizeof tab));
     return MF_OK;
 }
 

@@ -153,8 +153,9 @@ mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_c
 // sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
 // mixed elasticity: per-element geometry bound, once per pattern
 mf_status mf_mixed_geometry(const mf_mesh *m, mf_pattern *p, cudaStream_t st);
-// reference sums of the P2 integrands (flow form, P2 thermal) in the current
-// device's constant memory of mf_assemble.cu (once per such pattern build)
+// reference sums of the P2 integrands (flow form, P2 thermal) and the 20-node
+// brick's reference table, in the current device's copies of mf_assemble.cu
+// (once per such pattern build)
 mf_status mf_flow_consts_upload();
 void mf_launch_gather_elastic(bool fixed_point, int fp, int fq, int64_t n0, int64_t n1, const mf_mesh *m,
                               const mf_pattern *p, const mf_coeffs *c, double *values, double *d, cudaStream_t st);

@@ -614,8 +614,9 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, m->conn, incv.ptr, incv.inc, p->adj[0].ptr,
                                                      p->adj[0].col, p->inc_slot);
         p->scratch_stride = (int64_t)npe * npe + npe;
-        if (m->elem == MF_P2_TRI) {
-            s = mf_flow_consts_upload();  // reference sums of the P2 stiffness
+        if (m->elem == MF_P2_TRI || m->elem == MF_Q2S_HEX) {
+            // reference sums of the P2 stiffness, reference table of the 20-node brick
+            s = mf_flow_consts_upload();
             if (s != MF_OK) { free_inc(incv, st); return s; }
         }
         if (m->elem == MF_Q1_HEX && m->n_elems > 0) {
