@@ -145,3 +145,34 @@ def test_inverted_brick_rejected(mf):
     with pytest.raises(mf.MFError) as ei:
         mf.Problem(prob)
     assert ei.value.status == mf.MF_ERR_BAD_MESH
+
+
+def test_single_brick(mf, orc):
+    prob = gen.thermal_q2s_problem(1, jitter=0.0)
+    P, rp, ci, val, d = _gpu(mf, prob, bc=False)
+    ref = orc.assemble(prob, dirichlet=False)
+    assert np.array_equal(rp, ref["row_ptr"]) and np.array_equal(ci, ref["col"])
+    assert np.diff(rp).min() == 20  # every node couples with all 20
+    assert row_scaled_error(rp, val, ref["val"]) <= TOL
+    assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+
+
+def test_all_constrained(mf, orc):
+    prob = gen.thermal_q2s_problem(2)
+    prob["bc_mask"][:] = 1
+    prob["bc_val"] = np.linspace(-1.0, 1.0, prob["bc_mask"].shape[0])
+    P, rp, ci, val, d = _gpu(mf, prob)
+    ref = orc.assemble(prob)
+    assert np.array_equal(val, ref["val"]) and np.array_equal(d, prob["bc_val"])
+
+
+def test_nan_conductivity_latched(mf):
+    P = mf.Problem(gen.thermal_q2s_problem(2))
+    P.coef[3] = float("nan")
+    P.assemble()
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_sync_status()
+    assert ei.value.status == mf.MF_ERR_NONFINITE
+    P.coef[3] = 1.0
+    P.assemble()
+    mf.mf_sync_status()
