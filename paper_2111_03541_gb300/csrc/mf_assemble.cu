@@ -69,18 +69,19 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
 }
 
 // 20-node serendipity brick, thermal form (Sec. 4.1), 3 x 3 x 3 Gauss: one
-// warp per element, every phase spread over all 32 lanes (the kernel is
-// bound by the FP64 pipe, whose warp instructions cost the same with 20 or
-// 32 lanes active; the shape values and reference gradients at the 27 points
-// come from a table).  (1) lanes q < 27 take the geometry of Gauss point q
-// from the vertices' trilinear map: w detJ, its square root and J^-1; (2) the
-// 540 (node, point) items form sqrt(w detJ) times the physical gradients
-// (detJ > 0 at every point is checked when the mesh is made); (3) the 210
+// warp per element, every phase spread over all 32 lanes.  FP64 is the scarce
+// pipe (1/64 of the FP32 rate here): the shape values and reference gradients
+// at the 27 points come from a table, and everything after the geometry runs
+// in double-float (FP32 pairs, about 48 bits).  (0) lanes < 24 take the
+// vertices' map coefficients; (1) lanes q < 27 the geometry of Gauss point q
+// from the trilinear map: w detJ, and sqrt(w detJ) J^-T as FP32 pairs (detJ
+// > 0 at every point is checked when the mesh is made); (2) the 540 (node,
+// point) items form sqrt(w detJ) times the physical gradients; (3) the 210
 // pairs a <= b of K_e = k sum_q w detJ grad N_a . grad N_b are spread over the
-// lanes (6 or 7 each) and written to rows a and b; lanes a < 20 add d_e[a] =
-// f sum_q w detJ N_a.  Output as the other thermal elements (incidence
-// layout).
-constexpr int Q2W = 3;  // elements (warps) per block (45 KB of shared memory)
+// lanes (6 or 7 each), summed in double-float and written to rows a and b;
+// lanes a < 20 add d_e[a] = f sum_q w detJ N_a (FP64).  Output as the other
+// thermal elements (incidence layout).
+constexpr int Q2W = 3;  // elements (warps) per block (46 KB of shared memory)
 
 __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, const double *__restrict__ X,
                                                                const int32_t *__restrict__ conn,
@@ -88,46 +89,58 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
                                                                const int32_t *__restrict__ map,
                                                                double *__restrict__ out, int *status)
 {
-    __shared__ double geo[Q2W][27][11];      // w detJ, sqrt(w detJ), J^-1 (row-major)
-    __shared__ double grd[Q2W][27][20][3];   // sqrt(w detJ) times the physical gradients
+    __shared__ double wdet[Q2W][27];         // w detJ
+    __shared__ float2 Mq[Q2W][27][9];        // sqrt(w detJ) (J^-1)_ji at [i][j], FP32 pairs
+    __shared__ double cw[Q2W][8][3];         // map coefficients
+    __shared__ float2 grd[Q2W][27][20][3];   // sqrt(w detJ) times the physical gradients, FP32 pairs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * Q2W + w;
     if (e >= n_el) return;  // warp-uniform
     const int32_t *ce = conn + e * 20;
+    if (lane < 24) {  // map coefficient c_S[i], S = lane / 3, i = lane % 3 (q1_wht's, scaled)
+        const int S = lane / 3, i = lane % 3;
+        double v = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double xa = X[3 * (int64_t)ce[a] + i];
+            v += (__popc(a & S) & 1) ? -xa : xa;
+        }
+        cw[w][S][i] = v * ((__popc(S) & 1) ? -0.125 : 0.125);
+    }
+    __syncwarp();
     if (lane < 27) {
         const double g3 = 0.77459666924148337704;  // sqrt(3/5)
-        double x[8][3], c[8][3];
+        double c[8][3];
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int S = 0; S < 8; ++S)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)ce[a] + i];
-        q1_wht(x, c);
-#pragma unroll
-        for (int S = 1; S < 8; ++S)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) c[S][i] *= (__popc(S) & 1) ? -0.125 : 0.125;
+            for (int i = 0; i < 3; ++i) c[S][i] = cw[w][S][i];
         const int qi = lane % 3, qj = (lane / 3) % 3, qk = lane / 9;
         double Ji[3][3];
         const double det = q1_jac_at(c, (qi - 1) * g3, (qj - 1) * g3, (qk - 1) * g3, Ji);
         const double wi = qi == 1 ? 8.0 / 9.0 : 5.0 / 9.0, wj = qj == 1 ? 8.0 / 9.0 : 5.0 / 9.0,
                      wk = qk == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
         const double wd = wi * wj * wk * det;
-        geo[w][lane][0] = wd;
-        geo[w][lane][1] = sqrt(wd);
+        const double sw = sqrt(wd);
+        wdet[w][lane] = wd;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) geo[w][lane][2 + 3 * i + j] = Ji[i][j];
+            for (int j = 0; j < 3; ++j) {
+                const double v = sw * Ji[j][i];
+                const float hi = __double2float_rn(v);
+                Mq[w][lane][3 * i + j] = make_float2(hi, __double2float_rn(v - (double)hi));
+            }
     }
     __syncwarp();
-    for (int it = lane; it < 540; it += 32) {
+    for (int it = lane; it < 540; it += 32) {  // grad N = J^-T gradref N, in FP32 pairs
         const int q = it / 20, a = it - 20 * q;
-        const double *T = c_q2s_tab[q][a];
-        const double *G = geo[w][q];
-        const double sw = G[1];
-        // physical gradient: grad N = J^-T gradref N, (J^-1)_ji at G[2 + 3 j + i]
+        const float2 *T = c_q2s_tabf[q][a];
+        const float2 t0 = T[0], t1 = T[1], t2 = T[2];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) grd[w][q][a][i] = sw * (T[1] * G[2 + i] + T[2] * G[5 + i] + T[3] * G[8 + i]);
+        for (int i = 0; i < 3; ++i)
+            grd[w][q][a][i] = df_add(df_add(df_mul(Mq[w][q][3 * i], t0), df_mul(Mq[w][q][3 * i + 1], t1)),
+                                     df_mul(Mq[w][q][3 * i + 2], t2));
     }
     __syncwarp();
     const double k = kc[e];
@@ -141,17 +154,29 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
             ++a;
         }
         const int bb = a + rem;
-        double v = 0.0;
+        // double-float Gram sum (FP32 pairs, about 48 bits): exact products
+        // of the high parts by FMA, cross terms of the low parts, two-sum
+        // accumulation; the FP64 pipe, 1/64 of the FP32 rate here, stays
+        // free for the geometry
+        float sh = 0.0f, sl = 0.0f;
         for (int q = 0; q < 27; ++q)
-            v = fma(grd[w][q][a][0], grd[w][q][bb][0],
-                    fma(grd[w][q][a][1], grd[w][q][bb][1], fma(grd[w][q][a][2], grd[w][q][bb][2], v)));
-        const double kv = k * v;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float2 x = grd[w][q][a][i], y = grd[w][q][bb][i];
+                const float p = x.x * y.x;
+                const float e = fmaf(x.x, y.x, -p) + fmaf(x.x, y.y, x.y * y.x);
+                const float t = sh + p;  // two-sum of sh and p
+                const float z = t - sh;
+                sl += ((sh - (t - z)) + (p - z)) + e;
+                sh = t;
+            }
+        const double kv = k * ((double)sh + (double)sl);
         out[(int64_t)map[e * 20 + a] * 21 + bb] = kv;
         out[(int64_t)map[e * 20 + bb] * 21 + a] = kv;
     }
     if (lane < 20) {
         double m = 0.0;
-        for (int q = 0; q < 27; ++q) m = fma(geo[w][q][0], c_q2s_tab[q][lane][0], m);
+        for (int q = 0; q < 27; ++q) m = fma(wdet[w][q], c_q2s_tab[q][lane][0], m);
         out[(int64_t)map[e * 20 + lane] * 21 + 20] = f * m;
     }
 }

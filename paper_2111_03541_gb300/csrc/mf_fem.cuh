@@ -182,10 +182,33 @@ __host__ __device__ inline double q2s_shape(int a, const double (&xi)[3], double
     return 0.25 * Q * P1 * P2;
 }
 
+// Double-float arithmetic on FP32 pairs (hi, lo), |lo| <= ulp(hi) / 2, about
+// 48 significant bits (Dekker's product with an FMA, Knuth's two-sum): FP32
+// runs at 64 times the FP64 rate here.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b)
+{
+    const float p = a.x * b.x;
+    const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float z = s - a.x;
+    const float e = ((a.x - (s - z)) + (b.x - z)) + (a.y + b.y);
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+
 // 20-node brick at the 27 points of the 3 x 3 x 3 Gauss rule (point q = i +
 // 3 j + 9 k at ((i - 1), (j - 1), (k - 1)) sqrt(3/5)): [q][a] = N_a, then the
 // reference gradient (global memory: lanes read different nodes)
 __device__ double c_q2s_tab[27][20][4];
+// the reference gradients again, each as an FP32 pair (hi, lo) with hi + lo
+// within 2^-48 of the FP64 value
+__device__ float2 c_q2s_tabf[27][20][3];
 
 // Host: the reference sums, uploaded to this translation unit's copy of c_Ms,
 // c_R and c_q2s_tab on the current device (each file that includes this
@@ -230,6 +253,14 @@ inline mf_status fem_consts_upload()
         }
     }
     MF_CUDA(cudaMemcpyToSymbol(c_q2s_tab, tab, sizeof tab));
+    static float2 tabf[27][20][3];
+    for (int q = 0; q < 27; ++q)
+        for (int a = 0; a < 20; ++a)
+            for (int i = 0; i < 3; ++i) {
+                const float hi = (float)tab[q][a][1 + i];
+                tabf[q][a][i] = make_float2(hi, (float)(tab[q][a][1 + i] - (double)hi));
+            }
+    MF_CUDA(cudaMemcpyToSymbol(c_q2s_tabf, tabf, sizeof tabf));
     return MF_OK;
 }
 
