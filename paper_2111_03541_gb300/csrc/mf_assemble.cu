@@ -76,12 +76,14 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
 // vertices' map coefficients; (1) lanes q < 27 the geometry of Gauss point q
 // from the trilinear map: w detJ, and sqrt(w detJ) J^-T as FP32 pairs (detJ
 // > 0 at every point is checked when the mesh is made); (2) the 540 (node,
-// point) items form sqrt(w detJ) times the physical gradients; (3) the 210
-// pairs a <= b of K_e = k sum_q w detJ grad N_a . grad N_b are spread over the
-// lanes (6 or 7 each), summed in double-float and written to rows a and b;
+// point) items form sqrt(w detJ) times the physical gradients, 9 points at a
+// time (less shared memory, more resident warps); (3) the 210 pairs a <= b of
+// K_e = k sum_q w detJ grad N_a . grad N_b are spread over the lanes (6 or 7
+// each), summed over the chunks in double-float and written to rows a and b;
 // lanes a < 20 add d_e[a] = f sum_q w detJ N_a (FP64).  Output as the other
 // thermal elements (incidence layout).
-constexpr int Q2W = 3;  // elements (warps) per block (46 KB of shared memory)
+constexpr int Q2W = 4;  // elements (warps) per block
+constexpr int QCH = 9;  // Gauss points per chunk of gradients in shared memory
 
 __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, const double *__restrict__ X,
                                                                const int32_t *__restrict__ conn,
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
     __shared__ double wdet[Q2W][27];         // w detJ
     __shared__ float2 Mq[Q2W][27][9];        // sqrt(w detJ) (J^-1)_ji at [i][j], FP32 pairs
     __shared__ double cw[Q2W][8][3];         // map coefficients
-    __shared__ float2 grd[Q2W][27][20][3];   // sqrt(w detJ) times the physical gradients, FP32 pairs
+    __shared__ float2 grd[Q2W][QCH][20][3];  // sqrt(w detJ) times the physical gradients, one chunk of points
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * Q2W + w;
     if (e >= n_el) return;  // warp-uniform
@@ -132,47 +134,60 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
                 Mq[w][lane][3 * i + j] = make_float2(hi, __double2float_rn(v - (double)hi));
             }
     }
-    __syncwarp();
-    for (int it = lane; it < 540; it += 32) {  // grad N = J^-T gradref N, in FP32 pairs
-        const int q = it / 20, a = it - 20 * q;
-        const float2 *T = c_q2s_tabf[q][a];
-        const float2 t0 = T[0], t1 = T[1], t2 = T[2];
+    // pairs p = lane + 32 t (t < 7, p < 210) of the upper triangle, row-major
+    int pa[7], pb[7];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            grd[w][q][a][i] = df_add(df_add(df_mul(Mq[w][q][3 * i], t0), df_mul(Mq[w][q][3 * i + 1], t1)),
-                                     df_mul(Mq[w][q][3 * i + 2], t2));
-    }
-    __syncwarp();
-    const double k = kc[e];
-    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
-    // pair p = lane + 32 t (t < 7, p < 210) of the upper triangle, row-major:
-    // a from the triangular numbering, b = a + offset
-    for (int p = lane; p < 210; p += 32) {
-        int a = 0, rem = p;
+    for (int t = 0; t < 7; ++t) {
+        const int p = lane + 32 * t;
+        int a = 0, rem = p < 210 ? p : 0;
         while (rem >= 20 - a) {
             rem -= 20 - a;
             ++a;
         }
-        const int bb = a + rem;
-        // double-float Gram sum (FP32 pairs, about 48 bits): exact products
-        // of the high parts by FMA, cross terms of the low parts, two-sum
-        // accumulation; the FP64 pipe, 1/64 of the FP32 rate here, stays
-        // free for the geometry
-        float sh = 0.0f, sl = 0.0f;
-        for (int q = 0; q < 27; ++q)
+        pa[t] = p < 210 ? a : -1;
+        pb[t] = a + rem;
+    }
+    float sh[7], sl[7];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float2 x = grd[w][q][a][i], y = grd[w][q][bb][i];
-                const float p = x.x * y.x;
-                const float e = fmaf(x.x, y.x, -p) + fmaf(x.x, y.y, x.y * y.x);
-                const float t = sh + p;  // two-sum of sh and p
-                const float z = t - sh;
-                sl += ((sh - (t - z)) + (p - z)) + e;
-                sh = t;
-            }
-        const double kv = k * ((double)sh + (double)sl);
-        out[(int64_t)map[e * 20 + a] * 21 + bb] = kv;
-        out[(int64_t)map[e * 20 + bb] * 21 + a] = kv;
+    for (int t = 0; t < 7; ++t) sh[t] = sl[t] = 0.0f;
+    for (int q0 = 0; q0 < 27; q0 += QCH) {
+        __syncwarp();  // geometry written / the last chunk's gradients read
+        for (int it = lane; it < QCH * 20; it += 32) {  // grad N = J^-T gradref N, in FP32 pairs
+            const int qq = it / 20, a = it - 20 * qq, q = q0 + qq;
+            const float2 *T = c_q2s_tabf[q][a];
+            const float2 t0 = T[0], t1 = T[1], t2 = T[2];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                grd[w][qq][a][i] = df_add(df_add(df_mul(Mq[w][q][3 * i], t0), df_mul(Mq[w][q][3 * i + 1], t1)),
+                                          df_mul(Mq[w][q][3 * i + 2], t2));
+        }
+        __syncwarp();
+        // double-float Gram sums (exact products of the high parts by FMA,
+        // cross terms of the low parts, two-sum accumulation)
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+            if (pa[t] < 0) continue;
+            for (int qq = 0; qq < QCH; ++qq)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float2 x = grd[w][qq][pa[t]][i], y = grd[w][qq][pb[t]][i];
+                    const float p = x.x * y.x;
+                    const float ep = fmaf(x.x, y.x, -p) + fmaf(x.x, y.y, x.y * y.x);
+                    const float tt = sh[t] + p;  // two-sum of sh and p
+                    const float z = tt - sh[t];
+                    sl[t] += ((sh[t] - (tt - z)) + (p - z)) + ep;
+                    sh[t] = tt;
+                }
+        }
+    }
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        if (pa[t] < 0) continue;
+        const double kv = k * ((double)sh[t] + (double)sl[t]);
+        out[(int64_t)map[e * 20 + pa[t]] * 21 + pb[t]] = kv;
+        out[(int64_t)map[e * 20 + pb[t]] * 21 + pa[t]] = kv;
     }
     if (lane < 20) {
         double m = 0.0;
