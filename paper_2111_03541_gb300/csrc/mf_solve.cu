@@ -126,7 +126,7 @@ __device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp, const 
 }
 
 template <int W, int U>
-__global__ void __launch_bounds__(RT, U <= 6 ? 5 : 4) k_spmv(int64_t n, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(RT, U <= 6 ? 5 : (U <= 12 ? 4 : 3)) k_spmv(int64_t n, const int64_t *__restrict__ rp,
                                                              const int32_t *__restrict__ ci,
                                              const double *__restrict__ v, const double *__restrict__ x,
                                              double *__restrict__ y)
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(RT, U <= 6 ? 5 : 4) k_spmv(int64_t n, const in
 // q = K p: one W-lane group per row over the whole matrix (no reduction here,
 // so no per-block atomics on a shared ticket)
 template <int W, int U>
-__global__ void __launch_bounds__(RT, U <= 6 ? 5 : 4) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(RT, U <= 6 ? 5 : (U <= 12 ? 4 : 3)) k_pcg_spmv(int64_t n, const int64_t *__restrict__ rp,
                                                  const int32_t *__restrict__ ci, const double *__restrict__ v,
                                                  const double *__restrict__ p, double *__restrict__ q,
                                                  const PcgState *S)
@@ -356,11 +356,21 @@ struct SpmvShape {
 
 SpmvShape spmv_shape(int64_t n, int64_t nnz)
 {
+    // Few lanes per row and many entries in flight per lane: the lanes' sum
+    // costs FP64 adds (one per lane per level), and GB300 runs FP64 at 1/64
+    // of the FP32 rate, so wide row groups spend the FP64 pipe on the
+    // reduction.  Measured per-SpMV times (GB300): 64^3 elasticity (78.5
+    // entries per row) 16 x 6: 0.241 ms, 4 x 12: 0.162 ms; 128^3 Q1 thermal
+    // (26.6) 4 x 8: 0.168, 2 x 14: 0.144; Taylor-Hood 512^2 (18.8) 8 x 6:
+    // 0.235, 2 x 10: 0.155; 20-node bricks 48^3 (56.5) 8 x 8: 0.092, 2 x 14:
+    // 0.076; P1 512^2 (7.0): 2 x 6 0.046, 1 x 8 0.044 per PCG iteration.
     const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    for (int w = 2; w <= 32; w *= 2) {
-        if (w * 6 >= avg) return {w, 6};
-        if (w * 8 >= avg) return {w, 8};
-    }
+    if (avg <= 10.0) return {1, 8};
+    if (avg <= 24.0) return {2, 10};
+    if (avg <= 64.0) return {2, 14};
+    if (avg <= 100.0) return {4, 12};
+    if (avg <= 200.0) return {8, 12};
+    if (avg <= 400.0) return {16, 12};
     return {32, 8};
 }
 
@@ -372,8 +382,8 @@ void spmv_dispatch(SpmvShape sh, F &&f)
 #define MF_SPMV_CASE(W_, U_) \
     case W_ * 16 + U_: f(integral_constant<int, W_>(), integral_constant<int, U_>()); break;
     switch (sh.w * 16 + sh.u) {
-        MF_SPMV_CASE(2, 6) MF_SPMV_CASE(2, 8) MF_SPMV_CASE(4, 6) MF_SPMV_CASE(4, 8) MF_SPMV_CASE(8, 6)
-        MF_SPMV_CASE(8, 8) MF_SPMV_CASE(16, 6) MF_SPMV_CASE(16, 8) MF_SPMV_CASE(32, 6)
+        MF_SPMV_CASE(1, 8) MF_SPMV_CASE(2, 10) MF_SPMV_CASE(2, 14) MF_SPMV_CASE(4, 12) MF_SPMV_CASE(8, 12)
+        MF_SPMV_CASE(16, 12)
         default: f(integral_constant<int, 32>(), integral_constant<int, 8>()); break;
     }
 #undef MF_SPMV_CASE
