@@ -221,6 +221,19 @@ def thermal_q2s_problem(n: int, jitter: float = 0.15, sigma: float = 0.5,
     return m
 
 
+def elastic_q2s_problem(n: int, jitter: float = 0.15, sigma: float = 0.5, nu: float = 0.3,
+                        seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    """3D linear elasticity on 20-node serendipity bricks (the element of the
+    cantilever beams, Sec. 4.2): x = 0 clamped, body force (0, 0, -1)."""
+    m = hex20_mesh(n, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)  # Young's modulus E
+    m["nu"] = nu
+    m["body"] = (0.0, 0.0, -1.0)
+    m["bc_mask"], m["bc_val"] = elastic_bc(m)
+    m["form"] = "elastic"
+    return m
+
+
 # ----------------------------------------------------------------------------
 # boundary data
 # ----------------------------------------------------------------------------

@@ -68,6 +68,8 @@ def lib():
         _lib.or_elem_thermal.restype = d
         _lib.or_elem_elastic_q1.argtypes = [vp, d, d, vp, vp, vp]
         _lib.or_elem_elastic_q1.restype = d
+        _lib.or_elem_elastic.argtypes = [i, vp, d, d, vp, vp, vp]
+        _lib.or_elem_elastic.restype = d
         _lib.or_elem_oseen.argtypes = [vp, vp, d, d, vp, vp, vp, vp]
         _lib.or_elem_oseen.restype = d
         _lib.or_elem_capacity.argtypes = [i, vp, d, vp]
@@ -138,12 +140,21 @@ def elem_thermal(elem: int, quad_kind: int, X, k: float, f: float = 1.0, fnodal=
     return Ke, de, det
 
 
-def elem_elastic(X, E: float, nu: float, body=(0.0, 0.0, -1.0)):
+def elem_elastic(X, E: float, nu: float, body=(0.0, 0.0, -1.0), elem: int = None):
+    """Element stiffness [3 npe, 3 npe] (dof 3 a + c), load [3 npe] and min detJ;
+    elem Q1 (the default, 8 nodes) or Q2S (20 nodes)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     b = np.ascontiguousarray(body, dtype=np.float64)
-    Ke = np.zeros((24, 24))
-    de = np.zeros(24)
-    det = lib().or_elem_elastic_q1(_p(X), E, nu, _p(b), _p(Ke), _p(de))
+    if elem is None or elem == Q1:
+        Ke = np.zeros((24, 24))
+        de = np.zeros(24)
+        det = lib().or_elem_elastic_q1(_p(X), E, nu, _p(b), _p(Ke), _p(de))
+        return Ke, de, det
+    if elem != Q2S:
+        raise ValueError("elasticity takes the Q1 or Q2S brick")
+    Ke = np.zeros((60, 60))
+    de = np.zeros(60)
+    det = lib().or_elem_elastic(Q2S, _p(X), E, nu, _p(b), _p(Ke), _p(de))
     return Ke, de, det
 
 
@@ -284,7 +295,7 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
     if rc == -2:
         raise AssemblyError("element with detJ <= 0")
     if rc == -3:
-        raise AssemblyError("facet outside the mesh, or a form without boundary terms")
+        raise AssemblyError("facet outside the mesh, a form without boundary terms, or an element the form does not take")
     if rc:
         raise MemoryError("oracle assembly failed")
     n, z = n_rows.value, nnz.value

@@ -319,42 +319,52 @@ double or_elem_capacity(int elem, const double *X, double C, double *Me)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Linear elasticity, Q1 (Sec. 4.2: -(d_i,j, sigma_ij), sigma = lambda       */
-/* delta eps_mm + 2 mu eps, lambda = E nu / ((1+nu)(1-2nu)),                 */
+/* Linear elasticity on Q1 or Q2S bricks (Sec. 4.2: -(d_i,j, sigma_ij),    */
+/* sigma = lambda delta eps_mm + 2 mu eps, lambda = E nu / ((1+nu)(1-2nu)),  */
 /* mu = E / (2(1+nu))).  With test w = N_a e_c and trial u = N_b e_c':        */
 /* eps(w):sigma(u) = lambda d_c N_a d_c' N_b + mu d_c' N_a d_c N_b            */
 /*                 + mu delta_cc' gradN_a . gradN_b.                         */
-/* Ke[(3a+c)*24 + 3b+c'], de[3a+c] = sum_q w detJ body_c N_a.                */
+/* Rule: 2 x 2 x 2 Gauss (Q1), 3 x 3 x 3 Gauss (Q2S, the cantilever bricks   */
+/* of Sec. 4.2).  With m = 3 npe: Ke[(3a+c)*m + 3b+c'],                      */
+/* de[3a+c] = sum_q w detJ body_c N_a.  Returns min detJ.                    */
 /* ------------------------------------------------------------------------ */
-double or_elem_elastic_q1(const double *X, double E, double nu, const double *body,
-                          double *Ke, double *de)
+double or_elem_elastic(int elem, const double *X, double E, double nu, const double *body,
+                       double *Ke, double *de)
 {
-    double pts[24], w[8], N[8], g[24];
-    const int nq = or_quad(OR_QHEX8, pts, w);
+    double pts[27 * 3], w[27], N[20], g[60];
+    const int nq = or_quad(elem == OR_Q2S ? OR_QHEX27 : OR_QHEX8, pts, w);
+    const int npe = elem_npe(elem), m = 3 * npe;
     const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     const double mu = E / (2.0 * (1.0 + nu));
     double mindet = 1e300;
-    memset(Ke, 0, sizeof(double) * 24 * 24);
-    memset(de, 0, sizeof(double) * 24);
+    memset(Ke, 0, sizeof(double) * m * m);
+    memset(de, 0, sizeof(double) * m);
     for (int q = 0; q < nq; ++q) {
-        const double det = geometry(OR_Q1, X, pts + 3 * q, N, g);
+        const double det = geometry(elem, X, pts + 3 * q, N, g);
         if (det < mindet) mindet = det;
         const double wd = w[q] * det;
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < npe; ++a)
             for (int c = 0; c < 3; ++c) {
-                for (int b = 0; b < 8; ++b) {
+                for (int b = 0; b < npe; ++b) {
                     double dot = 0.0;
                     for (int i = 0; i < 3; ++i) dot += g[3 * a + i] * g[3 * b + i];
                     for (int cp = 0; cp < 3; ++cp) {
                         double v = lam * g[3 * a + c] * g[3 * b + cp] + mu * g[3 * a + cp] * g[3 * b + c];
                         if (c == cp) v += mu * dot;
-                        Ke[(3 * a + c) * 24 + 3 * b + cp] += wd * v;
+                        Ke[(3 * a + c) * m + 3 * b + cp] += wd * v;
                     }
                 }
                 de[3 * a + c] += wd * body[c] * N[a];
             }
     }
     return mindet;
+}
+
+/* The Q1 brick of or_elem_elastic: Ke [24][24], de [24]. */
+double or_elem_elastic_q1(const double *X, double E, double nu, const double *body,
+                          double *Ke, double *de)
+{
+    return or_elem_elastic(OR_Q1, X, E, nu, body, Ke, de);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -679,7 +689,8 @@ int64_t or_ndofs(const or_problem *p)
  * marked in keep[] (or, for flow, one vertex marked in pkeep[]) are
  * evaluated; rows outside the filter are then incomplete and must be ignored.
  * Returns 0, or -2 if some element has detJ <= 0, -3 for a facet outside the
- * mesh or a form without boundary terms, -1 on allocation failure. */
+ * mesh, a form without boundary terms or an element the form does not take,
+ * -1 on allocation failure. */
 static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass, const uint8_t *keep,
                          const uint8_t *pkeep)
 {
@@ -687,7 +698,7 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
     const int dim = elem_dim(p->elem), npe = elem_npe(p->elem);
     for (int64_t g = 0; g < n; ++g)
         if (coo_push(c, g, g, 0.0)) return -1;
-    double X[20 * 3], Ke[24 * 24], de[24], fn[20];
+    double X[20 * 3], Ke[60 * 60], de[60], fn[20];
     for (int64_t e = 0; e < p->n_el; ++e) {
         const int32_t *cn = p->conn + e * npe;
         if (keep) {
@@ -717,14 +728,16 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
                 for (int b = 0; b < npe; ++b)
                     if (coo_push(c, cn[a], cn[b], Ke[a * npe + b])) return -1;
         } else if (p->form == OR_ELASTIC) {
-            const double det = or_elem_elastic_q1(X, p->coef[e], p->nu, p->source, Ke, de);
+            if (p->elem != OR_Q1 && p->elem != OR_Q2S) return -3;
+            const double det = or_elem_elastic(p->elem, X, p->coef[e], p->nu, p->source, Ke, de);
             if (!(det > 0.0)) return -2;
-            for (int a = 0; a < 8; ++a)
+            const int m = 3 * npe;
+            for (int a = 0; a < npe; ++a)
                 for (int ci = 0; ci < 3; ++ci) {
-                    for (int b = 0; b < 8; ++b)
+                    for (int b = 0; b < npe; ++b)
                         for (int cj = 0; cj < 3; ++cj)
                             if (coo_push(c, 3 * (int64_t)cn[a] + ci, 3 * (int64_t)cn[b] + cj,
-                                         Ke[(3 * a + ci) * 24 + 3 * b + cj]))
+                                         Ke[(3 * a + ci) * m + 3 * b + cj]))
                                 return -1;
                     d[3 * (int64_t)cn[a] + ci] += de[3 * a + ci];
                 }
