@@ -95,6 +95,10 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate
 # FMAs and 3 multiplies), the trilinear geometry at 27 points (about 150) and
 # the load vector (540 FMAs); the kernel runs most of them in double-float
 Q2S_FLOPS_PER_ELEMENT = 2 * 210 * 27 * 3 + 540 * (2 * 9 + 3) + 27 * 150 + 2 * 540
+# The same for serendipity elasticity: the 210 pairs sum the nine entries of
+# M_ab (27 points x 9 FMAs), each block is finished with lambda, mu (9 entries
+# x 2 FMAs), plus the gradients, geometry and load vector as above
+Q2S_EL_FLOPS_PER_ELEMENT = 2 * 210 * 27 * 9 + 210 * 9 * 4 + 540 * (2 * 9 + 3) + 27 * 150 + 2 * 540
 
 
 # ---------------------------------------------------------------------------
@@ -655,6 +659,28 @@ def suite(dev):
                                 else flops / (el_ms * 1e-3) / 1e12,
                                 "arithmetic": "geometry and load FP64; gradients and Gram sums in double-float "
                                               "(FP32 pairs, about 48 bits)"}
+    del P
+    torch.cuda.empty_cache()
+    # 20-node serendipity bricks, elasticity (the cantilever element), 48^3
+    prob = gen.elastic_q2s_problem(48)
+    P = mf.Problem(prob, device=dev)
+    ms = _ev_time(lambda: P.assemble(), reps=5)
+    mf.mf_set_kernel_timing(1)
+    P.assemble()
+    torch.cuda.synchronize()
+    kt = mf.mf_kernel_times()
+    mf.mf_set_kernel_timing(0)
+    ne = int(prob["conn"].shape[0])
+    el_ms = kt["elem_elastic_q2s"][1] / kt["elem_elastic_q2s"][0] if "elem_elastic_q2s" in kt else None
+    ga_ms = kt["gather_elastic_q2s"][1] / kt["gather_elastic_q2s"][0] if "gather_elastic_q2s" in kt else None
+    flops = ne * Q2S_EL_FLOPS_PER_ELEMENT
+    out["H2_elastic_q2s_48"] = {"elements": ne, "n_dofs": int(P.n), "nnz": int(P.nnz), "assemble_ms": ms,
+                                "elements_per_s": ne / (ms * 1e-3), "element_kernel_ms": el_ms,
+                                "gather_kernel_ms": ga_ms,
+                                "element_algorithmic_tflops": None if el_ms is None
+                                else flops / (el_ms * 1e-3) / 1e12,
+                                "arithmetic": "geometry and load FP64; gradients and the nine Gram sums per pair "
+                                              "in double-float (FP32 pairs, about 48 bits)"}
     del P
     torch.cuda.empty_cache()
     # loaded boundary: a random stress on five sides of the 64^3 elasticity box (clamped at x = 0)

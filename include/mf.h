@@ -65,8 +65,9 @@ typedef struct mf_pattern mf_pattern;
  * 20-node serendipity brick of the paper's experiments; the 8 vertices as Q1,
  * then the edge midpoints: x edges 8 + j + 2k at (0, 2j-1, 2k-1), y edges
  * 12 + i + 2k, z edges 16 + i + 2j; edges straight, midpoints at the mean of
- * their ends, so the geometry is the vertices' trilinear map; thermal form,
- * FP64, 3 x 3 x 3 Gauss, up to 128 neighbours per node).  Triangles are
+ * their ends, so the geometry is the vertices' trilinear map; thermal and
+ * elasticity forms (Sec. 4.1, Sec. 4.2), FP64, 3 x 3 x 3 Gauss, up to 128
+ * neighbours per node).  Triangles are
  * counter-clockwise.  For the flow form, pconn [n_elems][3] gives the P1
  * pressure nodes (the element's vertices in a 0..n_pnodes-1 numbering). */
 typedef struct {
@@ -140,8 +141,10 @@ mf_status mf_mesh_destroy(mf_mesh *mesh);
  * Block B-1 unique control-point pairs -> Block B-4 sparse ids), as CSR with
  * ascending columns plus the element -> entry maps the assembly uses.  The
  * flow form has the blocks u1-u1, u2-u2, u-p, p-u and the p-p diagonal; no
- * u1-u2 block.  Synchronises the stream.  Errors: MF_ERR_INVALID_ARG,
- * MF_ERR_UNSUPPORTED (more than 64 neighbours or 32 incident elements per
+ * u1-u2 block.  Elasticity takes Q1 and Q2S bricks (dof 3 n + c, 3 x 3
+ * blocks per node pair).  Synchronises the stream.  Errors:
+ * MF_ERR_INVALID_ARG, MF_ERR_UNSUPPORTED (a form the element does not
+ * carry; more than 64 neighbours (128 for Q2S) or 32 incident elements per
  * node), MF_ERR_OOM, MF_ERR_CUDA. */
 mf_status mf_pattern_build(const mf_mesh *mesh, int32_t form, void *stream, mf_pattern **out);
 /* Fills n_rows, nnz, row_ptr, col_idx (device pointers owned by the pattern);

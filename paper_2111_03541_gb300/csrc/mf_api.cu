@@ -294,8 +294,8 @@ extern "C" mf_status mf_pattern_build(const mf_mesh *mesh, int32_t form, void *s
     g_msg[0] = 0;
     if (!mesh || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_pattern_build: NULL argument");
     *out = nullptr;
-    if (form == MF_FORM_ELASTIC && mesh->elem != MF_Q1_HEX)
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: elasticity is provided on Q1 hexahedra");
+    if (form == MF_FORM_ELASTIC && mesh->elem != MF_Q1_HEX && mesh->elem != MF_Q2S_HEX)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: elasticity is provided on Q1 and Q2S bricks");
     if (form == MF_FORM_OSEEN && (mesh->elem != MF_P2_TRI || !mesh->pconn))
         return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: flow needs a P2 mesh with pconn");
     if (form < MF_FORM_THERMAL || form > MF_FORM_OSEEN)
@@ -363,8 +363,9 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: pattern was built for another form or mesh");
     if (form == MF_FORM_CAPACITY && prec != MF_PREC_FP64)
         return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: the capacity form is assembled in FP64");
-    if (mesh->elem == MF_Q2S_HEX && (form != MF_FORM_THERMAL || prec != MF_PREC_FP64))
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: serendipity bricks carry the thermal form in FP64");
+    if (mesh->elem == MF_Q2S_HEX && ((form != MF_FORM_THERMAL && form != MF_FORM_ELASTIC) || prec != MF_PREC_FP64))
+        return mf_fail(MF_ERR_UNSUPPORTED,
+                       "mf_assemble: serendipity bricks carry the thermal and elasticity forms in FP64");
     if (K->n_rows != pattern->n_rows || K->nnz != pattern->nnz || K->row_ptr != pattern->row_ptr ||
         K->col_idx != pattern->col_idx)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: K does not carry the pattern's CSR arrays");

@@ -196,6 +196,142 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
     }
 }
 
+// 20-node serendipity brick, linear elasticity (Sec. 4.2, the element of the
+// cantilever beams), 3 x 3 x 3 Gauss: one block per element.  The geometry
+// and the double-float gradients sqrt(w detJ) grad N_a(q) are formed as in
+// the thermal brick (all 27 points at once, [q][i][a] so that the threads of
+// a warp read consecutive nodes); thread p < 210 then takes the pair a <= b
+// (row-major upper triangle) and sums the nine entries of
+// M_ab[i][j] = sum_q w detJ d_i N_a d_j N_b in double-float, and the block
+// K_ab = lambda M_ab + mu M_ab^T + mu tr(M_ab) I goes to row a (columns of b)
+// and, transposed, to row b.  Row a of element e is incidence entry
+// t = map[e * 20 + a]: [K_ab for b < 20 (3 x 3 each, row-major), d_e(a) (3)].
+constexpr int EQ_T = 224;  // 7 warps: one thread per pair a <= b (210)
+constexpr int EQ_ROW = 20 * 9 + 3;
+
+__global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const double *__restrict__ X,
+                                                           const int32_t *__restrict__ conn,
+                                                           const double *__restrict__ Ec, double nu, double b0,
+                                                           double b1, double b2, const int32_t *__restrict__ map,
+                                                           double *__restrict__ out, int *status)
+{
+    __shared__ double cw[8][3];         // map coefficients
+    __shared__ double wdet[27];         // w detJ
+    __shared__ float2 Mq[27][9];        // sqrt(w detJ) (J^-1)_ji at [i][j], FP32 pairs
+    __shared__ float2 grd[27][3][20];   // sqrt(w detJ) d_i N_a at [q][i][a]
+    __shared__ int32_t tmap[20];
+    const int tid = threadIdx.x;
+    const int64_t e = blockIdx.x;
+    if (e >= n_el) return;  // block-uniform
+    const int32_t *ce = conn + e * 20;
+    if (tid < 24) {  // map coefficient c_S[i], S = tid / 3, i = tid % 3 (q1_wht's, scaled)
+        const int S = tid / 3, i = tid % 3;
+        double v = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double xa = X[3 * (int64_t)ce[a] + i];
+            v += (__popc(a & S) & 1) ? -xa : xa;
+        }
+        cw[S][i] = v * ((__popc(S) & 1) ? -0.125 : 0.125);
+    } else if (tid >= 32 && tid < 52) {
+        tmap[tid - 32] = map[e * 20 + tid - 32];
+    }
+    __syncthreads();
+    if (tid < 27) {
+        const double g3 = 0.77459666924148337704;  // sqrt(3/5)
+        double c[8][3];
+#pragma unroll
+        for (int S = 0; S < 8; ++S)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) c[S][i] = cw[S][i];
+        const int qi = tid % 3, qj = (tid / 3) % 3, qk = tid / 9;
+        double Ji[3][3];
+        const double det = q1_jac_at(c, (qi - 1) * g3, (qj - 1) * g3, (qk - 1) * g3, Ji);
+        const double wi = qi == 1 ? 8.0 / 9.0 : 5.0 / 9.0, wj = qj == 1 ? 8.0 / 9.0 : 5.0 / 9.0,
+                     wk = qk == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
+        const double wd = wi * wj * wk * det;
+        const double sw = sqrt(wd);
+        wdet[tid] = wd;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double v = sw * Ji[j][i];
+                const float hi = __double2float_rn(v);
+                Mq[tid][3 * i + j] = make_float2(hi, __double2float_rn(v - (double)hi));
+            }
+    }
+    __syncthreads();
+    for (int it = tid; it < 27 * 20; it += EQ_T) {  // grad N = J^-T gradref N, in FP32 pairs
+        const int q = it / 20, a = it - 20 * q;
+        const float2 *T = c_q2s_tabf[q][a];
+        const float2 t0 = T[0], t1 = T[1], t2 = T[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            grd[q][i][a] = df_add(df_add(df_mul(Mq[q][3 * i], t0), df_mul(Mq[q][3 * i + 1], t1)),
+                                  df_mul(Mq[q][3 * i + 2], t2));
+    }
+    __syncthreads();
+    if (tid < 210) {
+        int pa = 0, rem = tid;
+        while (rem >= 20 - pa) {
+            rem -= 20 - pa;
+            ++pa;
+        }
+        const int pb = pa + rem;
+        // double-float sums (exact products of the high parts by FMA, cross
+        // terms of the low parts, two-sum accumulation)
+        float sh[9], sl[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sh[k] = sl[k] = 0.0f;
+#pragma unroll 3
+        for (int q = 0; q < 27; ++q) {
+            float2 x[3], y[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                x[i] = grd[q][i][pa];
+                y[i] = grd[q][i][pb];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int k = 3 * i + j;
+                    const float p = x[i].x * y[j].x;
+                    const float ep = fmaf(x[i].x, y[j].x, -p) + fmaf(x[i].x, y[j].y, x[i].y * y[j].x);
+                    const float tt = sh[k] + p;  // two-sum of sh and p
+                    const float z = tt - sh[k];
+                    sl[k] += ((sh[k] - (tt - z)) + (p - z)) + ep;
+                    sh[k] = tt;
+                }
+        }
+        const double E = Ec[e];
+        if (!isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+        const double mu = E / (2.0 * (1.0 + nu));
+        double M[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) M[k] = (double)sh[k] + (double)sl[k];
+        const double mtr = mu * (M[0] + M[4] + M[8]);
+        double *ra = out + (int64_t)tmap[pa] * EQ_ROW + 9 * pb;
+        double *rb = out + (int64_t)tmap[pb] * EQ_ROW + 9 * pa;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double kv = fma(lam, M[3 * i + j], fma(mu, M[3 * j + i], i == j ? mtr : 0.0));
+                ra[3 * i + j] = kv;
+                if (pb != pa) rb[3 * j + i] = kv;
+            }
+    }
+    if (tid < 60) {  // d_e[3 a + c] = b_c sum_q w detJ N_a (FP64)
+        const int a = tid / 3, c = tid - 3 * a;
+        double m = 0.0;
+        for (int q = 0; q < 27; ++q) m = fma(wdet[q], c_q2s_tab[q][a][0], m);
+        out[(int64_t)tmap[a] * EQ_ROW + 180 + c] = (c == 0 ? b0 : (c == 1 ? b1 : b2)) * m;
+    }
+}
+
 // Q1 elasticity, one element per thread.  The scaled gradients
 // sqrt(w detJ) gradN_a(q) of all 8 points go to shared memory (each thread its
 // own column, no synchronisation), then every block pair a <= b contracts
@@ -551,6 +687,114 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
     }
 }
 
+// elasticity gather for the serendipity brick: one warp per node.  Row a of
+// each incident element is incidence entry t (ascending, so the sums run in
+// element order: bit-reproducible); its 180 values are added at the
+// neighbour slot inc_slot[t * 20 + b] of node b in a shared-memory row
+// accumulator (up to MF_MAX_DEG_HO neighbours), the node's three CSR rows are
+// then written once, with Dirichlet elimination and lifting.
+constexpr int GQ_WARPS = 4;
+
+__global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
+    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+    const int64_t *__restrict__ inc_ptr, const uint8_t *__restrict__ inc_slot, const double *__restrict__ sc,
+    const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+    double *__restrict__ values, double *__restrict__ d)
+{
+    constexpr int H = MF_MAX_DEG_HO / 32;
+    __shared__ double acc_all[GQ_WARPS][MF_MAX_DEG_HO * 9];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t n = (int64_t)blockIdx.x * GQ_WARPS + w;
+    if (n >= n_nodes) return;  // warp-uniform
+    double *acc = acc_all[w];
+    const int64_t p0 = adj_ptr[n];
+    const int deg = (int)(adj_ptr[n + 1] - p0);
+    for (int i = lane; i < 9 * deg; i += 32) acc[i] = 0.0;
+    const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
+    double dsum = 0.0;  // lane c < 3: component c of the load, element order
+    if (lane < 3)
+        for (int64_t t = i0; t < i1; ++t) dsum += sc[t * EQ_ROW + 180 + lane];
+    __syncwarp();
+    constexpr int IU = (180 + 31) / 32;  // items per lane and incidence entry
+    for (int64_t cb = i0; cb < i1; cb += 2) {
+        const int cnt = (int)min((int64_t)2, i1 - cb);
+        double v[2][IU];
+        int ad[2][IU];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int u = 0; u < IU; ++u) {
+                const int idx = lane + 32 * u;
+                v[j][u] = 0.0;
+                ad[j][u] = -1;
+                if (j < cnt && idx < 180) {
+                    const int64_t t = cb + j;
+                    const int b = idx / 9;
+                    v[j][u] = sc[t * EQ_ROW + idx];
+                    ad[j][u] = inc_slot[t * 20 + b] * 9 + (idx - 9 * b);
+                }
+            }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int u = 0; u < IU; ++u)
+                if (ad[j][u] >= 0) acc[ad[j][u]] += v[j][u];
+            __syncwarp();
+        }
+    }
+    // neighbour k's column node and Dirichlet flags, loaded by lane k % 32
+    int32_t mcol_l[H];
+    unsigned cm_l[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int k = lane + 32 * h;
+        mcol_l[h] = 0;
+        cm_l[h] = 0u;
+        if (k < deg) {
+            mcol_l[h] = adj_col[p0 + k];
+            if (mask)
+#pragma unroll
+                for (int cp = 0; cp < 3; ++cp) cm_l[h] |= (mask[3 * (int64_t)mcol_l[h] + cp] != 0 ? 1u : 0u) << cp;
+        }
+    }
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        const int64_t r = 3 * n + c;
+        const bool rm = mask ? mask[r] != 0 : false;
+        const int64_t rb = row_ptr[r];
+        double lift = 0.0;
+        for (int j0 = 0; j0 < 3 * deg; j0 += 32) {  // warp-uniform
+            const int j = j0 + lane;
+            const int k = (j < 3 * deg ? j : 0) / 3, cp = j - 3 * (j / 3);
+            const int kk = k & 31, hk = k >> 5;
+            int32_t mcol = 0;
+            unsigned fl = 0u;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {  // every lane takes part in every shuffle
+                const int32_t mc = __shfl_sync(0xffffffffu, mcol_l[h], kk);
+                const unsigned f = __shfl_sync(0xffffffffu, cm_l[h], kk);
+                if (h == hk) {
+                    mcol = mc;
+                    fl = f;
+                }
+            }
+            if (j >= 3 * deg) continue;
+            double v = acc[k * 9 + 3 * c + cp];
+            if (mask) {
+                const int64_t sdof = 3 * (int64_t)mcol + cp;
+                if (rm) v = (r == sdof) ? 1.0 : 0.0;
+                else if ((fl >> cp) & 1u) { lift -= v * bval[sdof]; v = 0.0; }
+            }
+            values[rb + j] = v;
+        }
+        if (__any_sync(0xffffffffu, lift != 0.0))  // rows next to a constrained dof only
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lift += __shfl_xor_sync(0xffffffffu, lift, o);
+        const double dc = __shfl_sync(0xffffffffu, dsum, c);
+        if (lane == 0) d[r] = rm ? bval[r] : dc + lift;
+    }
+}
+
 // flow rows, node-centric (groups of 16 lanes per node, 2 nodes per warp):
 //   u_i(n) = [A over the P2 neighbours | -B_i^T over the P1 neighbours],
 //   p(n1)  = [B_1 | B_2 over the P2 neighbours | 0 on the diagonal].
@@ -835,6 +1079,20 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         else if (m->elem == MF_Q1_HEX) MF_GATHER_TH(8);
         else MF_GATHER_TH(20);
 #undef MF_GATHER_TH
+        mf_prof_end(st);
+    } else if (form == MF_FORM_ELASTIC && m->elem == MF_Q2S_HEX) {
+        mf_prof_begin("elem_elastic_q2s", st);
+        if (ne > 0)
+            k_elem_elastic_q2s<<<(unsigned)ne, EQ_T, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, c->nu,
+                                                              c->source[0], c->source[1], c->source[2], p->elem_inc,
+                                                              p->scratch, status);
+        mf_prof_end(st);
+        MF_CUDA(cudaGetLastError());
+        mf_prof_begin("gather_elastic_q2s", st);
+        const mf_adj &A = p->adj[0];
+        k_gather_el_q2s<<<nblk(m->n_nodes, GQ_WARPS), GQ_WARPS * 32, 0, st>>>(
+            m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc_slot, p->scratch, c->bc_mask, c->bc_val, p->row_ptr, values,
+            d);
         mf_prof_end(st);
     } else if (form == MF_FORM_ELASTIC) {
         const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;

@@ -639,6 +639,28 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
                 k_mark_translates<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, incv.ptr, incv.inc, p->tr, incv.loc);
             }
         }
+    } else if (form == MF_FORM_ELASTIC && m->elem == MF_Q2S_HEX) {
+        // node-interleaved dofs 3 n + c; element rows in the incidence layout
+        // (row a of element e at incidence entry elem_inc[e * 20 + a], 183
+        // values: 20 blocks of 3 x 3, then the load)
+        p->n_rows = 3 * m->n_nodes;
+        p->nnz = 9 * p->adj[0].n_pairs;
+        if (p->nnz >= INT32_MAX || (int64_t)npe * m->n_elems >= INT32_MAX) {
+            free_inc(incv, st);
+            return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: nnz or element-node incidences above 2^31");
+        }
+        MF_CUDA(cudaMallocAsync(&p->row_ptr, sizeof(int64_t) * (p->n_rows + 1), st));
+        MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
+        k_csr_elastic<<<nblk(p->n_rows + 1), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->row_ptr,
+                                                           p->col_idx);
+        MF_CUDA(cudaMallocAsync(&p->elem_inc, sizeof(int32_t) * npe * m->n_elems, st));
+        k_elem_inc<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, incv.ptr, incv.inc, incv.loc, p->elem_inc);
+        MF_CUDA(cudaMallocAsync(&p->inc_slot, (size_t)npe * npe * m->n_elems, st));
+        k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, m->conn, incv.ptr, incv.inc, p->adj[0].ptr,
+                                                     p->adj[0].col, p->inc_slot);
+        p->scratch_stride = (int64_t)npe * (9 * npe + 3);
+        s = mf_flow_consts_upload();  // reference table of the 20-node brick
+        if (s != MF_OK) { free_inc(incv, st); return s; }
     } else if (form == MF_FORM_ELASTIC) {
         p->n_rows = 3 * m->n_nodes;
         p->nnz = 9 * p->adj[0].n_pairs;

@@ -124,7 +124,7 @@ def test_unsupported_combinations(mf):
         mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, P.make_coeffs(coef=C), mf.MF_PREC_FP64, P.csr, P.d)
     assert ei.value.status == mf.MF_ERR_UNSUPPORTED
     with pytest.raises(mf.MFError) as ei:
-        mf.mf_pattern_build(P.mesh, mf.MF_FORM_ELASTIC)
+        mf.mf_pattern_build(P.mesh, mf.MF_FORM_OSEEN)
     assert ei.value.status == mf.MF_ERR_UNSUPPORTED
     e = torch.zeros(1, dtype=torch.int32, device="cuda")
     f = torch.zeros(1, dtype=torch.uint8, device="cuda")
