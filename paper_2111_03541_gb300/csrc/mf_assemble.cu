@@ -71,11 +71,12 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
 // 20-node serendipity brick, thermal form (Sec. 4.1), 3 x 3 x 3 Gauss: one
 // warp per element, every phase spread over all 32 lanes.  FP64 is the scarce
 // pipe (1/64 of the FP32 rate here): the shape values and reference gradients
-// at the 27 points come from a table, and everything after the geometry runs
-// in double-float (FP32 pairs, about 48 bits).  (0) lanes < 24 take the
-// vertices' map coefficients; (1) lanes q < 27 the geometry of Gauss point q
-// from the trilinear map: w detJ, and sqrt(w detJ) J^-T as FP32 pairs (detJ
-// > 0 at every point is checked when the mesh is made); (2) the 540 (node,
+// at the 27 points come from a table, and everything but the map
+// coefficients and the load runs in double-float (FP32 pairs, about 47
+// bits).  (0) lanes < 24 take the vertices' map coefficients; (1) lanes
+// q < 27 the geometry of Gauss point q from the trilinear map (q2s_point_df):
+// w detJ, and sqrt(w detJ) J^-T (detJ > 0 at every point is checked when the
+// mesh is made); (2) the 540 (node,
 // point) items form sqrt(w detJ) times the physical gradients, 9 points at a
 // time (less shared memory, more resident warps); (3) the 210 pairs a <= b of
 // K_e = k sum_q w detJ grad N_a . grad N_b are spread over the lanes (6 or 7
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
 {
     __shared__ double wdet[Q2W][27];         // w detJ
     __shared__ float2 Mq[Q2W][27][9];        // sqrt(w detJ) (J^-1)_ji at [i][j], FP32 pairs
-    __shared__ double cw[Q2W][8][3];         // map coefficients
+    __shared__ float2 cw[Q2W][8][3];         // map coefficients, FP32 pairs
     __shared__ float2 grd[Q2W][QCH][20][3];  // sqrt(w detJ) times the physical gradients, one chunk of points
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * Q2W + w;
@@ -107,32 +108,20 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
             const double xa = X[3 * (int64_t)ce[a] + i];
             v += (__popc(a & S) & 1) ? -xa : xa;
         }
-        cw[w][S][i] = v * ((__popc(S) & 1) ? -0.125 : 0.125);
+        const double cv = v * ((__popc(S) & 1) ? -0.125 : 0.125);
+        const float hi = __double2float_rn(cv);
+        cw[w][S][i] = make_float2(hi, __double2float_rn(cv - (double)hi));
     }
     __syncwarp();
     if (lane < 27) {
-        const double g3 = 0.77459666924148337704;  // sqrt(3/5)
-        double c[8][3];
+        float2 c[8][3], M9[9];
 #pragma unroll
         for (int S = 0; S < 8; ++S)
 #pragma unroll
             for (int i = 0; i < 3; ++i) c[S][i] = cw[w][S][i];
-        const int qi = lane % 3, qj = (lane / 3) % 3, qk = lane / 9;
-        double Ji[3][3];
-        const double det = q1_jac_at(c, (qi - 1) * g3, (qj - 1) * g3, (qk - 1) * g3, Ji);
-        const double wi = qi == 1 ? 8.0 / 9.0 : 5.0 / 9.0, wj = qj == 1 ? 8.0 / 9.0 : 5.0 / 9.0,
-                     wk = qk == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
-        const double wd = wi * wj * wk * det;
-        const double sw = sqrt(wd);
-        wdet[w][lane] = wd;
+        wdet[w][lane] = df_to_double(q2s_point_df(c, lane, M9));
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const double v = sw * Ji[j][i];
-                const float hi = __double2float_rn(v);
-                Mq[w][lane][3 * i + j] = make_float2(hi, __double2float_rn(v - (double)hi));
-            }
+        for (int k = 0; k < 9; ++k) Mq[w][lane][k] = M9[k];
     }
     // pairs p = lane + 32 t (t < 7, p < 210) of the upper triangle, row-major
     int pa[7], pb[7];
@@ -185,7 +174,7 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
 #pragma unroll
     for (int t = 0; t < 7; ++t) {
         if (pa[t] < 0) continue;
-        const double kv = k * ((double)sh[t] + (double)sl[t]);
+        const double kv = k * (f32_to_f64_exact(sh[t]) + f32_to_f64_exact(sl[t]));
         out[(int64_t)map[e * 20 + pa[t]] * 21 + pb[t]] = kv;
         out[(int64_t)map[e * 20 + pb[t]] * 21 + pa[t]] = kv;
     }
@@ -198,14 +187,16 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
 
 // 20-node serendipity brick, linear elasticity (Sec. 4.2, the element of the
 // cantilever beams), 3 x 3 x 3 Gauss: one block per element.  The geometry
-// and the double-float gradients sqrt(w detJ) grad N_a(q) are formed as in
-// the thermal brick (all 27 points at once, [q][i][a] so that the threads of
-// a warp read consecutive nodes); thread p < 210 then takes the pair a <= b
-// (row-major upper triangle) and sums the nine entries of
-// M_ab[i][j] = sum_q w detJ d_i N_a d_j N_b in double-float, and the block
-// K_ab = lambda M_ab + mu M_ab^T + mu tr(M_ab) I goes to row a (columns of b)
-// and, transposed, to row b.  Row a of element e is incidence entry
-// t = map[e * 20 + a]: [K_ab for b < 20 (3 x 3 each, row-major), d_e(a) (3)].
+// (q2s_point_df) and the gradients sqrt(w detJ) grad N_a(q) are formed in
+// double-float as in the thermal brick (all 27 points at once, [q][i][a] so
+// that the threads of a warp read consecutive nodes); thread p < 210 then
+// takes the pair a <= b (row-major upper triangle), sums the nine entries of
+// M_ab[i][j] = sum_q w detJ d_i N_a d_j N_b and finishes
+// K_ab = lambda M_ab + mu M_ab^T + mu tr(M_ab) I, all in double-float (FP64
+// runs at 1/64 of the FP32 rate here; lambda and mu are formed once per
+// element).  Row a of element e is incidence entry t = map[e * 20 + a] of
+// EQ_ROW 8-byte words: K_ab for b < 20 (3 x 3, row-major) as FP32 pairs
+// (hi, lo), then d_e(a) (3 doubles); K_ba = K_ab^T goes to row b.
 constexpr int EQ_T = 224;  // 7 warps: one thread per pair a <= b (210)
 constexpr int EQ_ROW = 20 * 9 + 3;
 
@@ -215,9 +206,10 @@ __global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const d
                                                            double b1, double b2, const int32_t *__restrict__ map,
                                                            double *__restrict__ out, int *status)
 {
-    __shared__ double cw[8][3];         // map coefficients
+    __shared__ float2 cw[8][3];         // map coefficients, FP32 pairs
+    __shared__ float2 lmu[2];           // lambda, mu
     __shared__ double wdet[27];         // w detJ
-    __shared__ float2 Mq[27][9];        // sqrt(w detJ) (J^-1)_ji at [i][j], FP32 pairs
+    __shared__ float2 Mq[27][9];        // sqrt(w detJ) (J^-1)_ji at [i][j]
     __shared__ float2 grd[27][3][20];   // sqrt(w detJ) d_i N_a at [q][i][a]
     __shared__ int32_t tmap[20];
     const int tid = threadIdx.x;
@@ -232,34 +224,31 @@ __global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const d
             const double xa = X[3 * (int64_t)ce[a] + i];
             v += (__popc(a & S) & 1) ? -xa : xa;
         }
-        cw[S][i] = v * ((__popc(S) & 1) ? -0.125 : 0.125);
+        const double cv = v * ((__popc(S) & 1) ? -0.125 : 0.125);
+        const float hi = __double2float_rn(cv);
+        cw[S][i] = make_float2(hi, __double2float_rn(cv - (double)hi));
     } else if (tid >= 32 && tid < 52) {
         tmap[tid - 32] = map[e * 20 + tid - 32];
+    } else if (tid == 64) {
+        const double E = Ec[e];
+        if (!isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        const double lm[2] = {E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), E / (2.0 * (1.0 + nu))};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float hi = __double2float_rn(lm[k]);
+            lmu[k] = make_float2(hi, __double2float_rn(lm[k] - (double)hi));
+        }
     }
     __syncthreads();
     if (tid < 27) {
-        const double g3 = 0.77459666924148337704;  // sqrt(3/5)
-        double c[8][3];
+        float2 c[8][3], M9[9];
 #pragma unroll
         for (int S = 0; S < 8; ++S)
 #pragma unroll
             for (int i = 0; i < 3; ++i) c[S][i] = cw[S][i];
-        const int qi = tid % 3, qj = (tid / 3) % 3, qk = tid / 9;
-        double Ji[3][3];
-        const double det = q1_jac_at(c, (qi - 1) * g3, (qj - 1) * g3, (qk - 1) * g3, Ji);
-        const double wi = qi == 1 ? 8.0 / 9.0 : 5.0 / 9.0, wj = qj == 1 ? 8.0 / 9.0 : 5.0 / 9.0,
-                     wk = qk == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
-        const double wd = wi * wj * wk * det;
-        const double sw = sqrt(wd);
-        wdet[tid] = wd;
+        wdet[tid] = df_to_double(q2s_point_df(c, tid, M9));
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const double v = sw * Ji[j][i];
-                const float hi = __double2float_rn(v);
-                Mq[tid][3 * i + j] = make_float2(hi, __double2float_rn(v - (double)hi));
-            }
+        for (int k = 0; k < 9; ++k) Mq[tid][k] = M9[k];
     }
     __syncthreads();
     for (int it = tid; it < 27 * 20; it += EQ_T) {  // grad N = J^-T gradref N, in FP32 pairs
@@ -279,8 +268,8 @@ __global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const d
             ++pa;
         }
         const int pb = pa + rem;
-        // double-float sums (exact products of the high parts by FMA, cross
-        // terms of the low parts, two-sum accumulation)
+        // double-float sums (exact products of the high parts by FMA,
+        // cross terms of the low parts, two-sum accumulation)
         float sh[9], sl[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) sh[k] = sl[k] = 0.0f;
@@ -305,30 +294,33 @@ __global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const d
                     sh[k] = tt;
                 }
         }
-        const double E = Ec[e];
-        if (!isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
-        const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-        const double mu = E / (2.0 * (1.0 + nu));
-        double M[9];
+        float2 M[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) M[k] = (double)sh[k] + (double)sl[k];
-        const double mtr = mu * (M[0] + M[4] + M[8]);
-        double *ra = out + (int64_t)tmap[pa] * EQ_ROW + 9 * pb;
-        double *rb = out + (int64_t)tmap[pb] * EQ_ROW + 9 * pa;
+        for (int k = 0; k < 9; ++k) {  // renormalise (fast two-sum)
+            const float h = sh[k] + sl[k];
+            M[k] = make_float2(h, sl[k] - (h - sh[k]));
+        }
+        const float2 L = lmu[0], U = lmu[1];
+        const float2 mtr = df_mul(U, df_add(df_add(M[0], M[4]), M[8]));
+        float2 *ra = reinterpret_cast<float2 *>(out + (int64_t)tmap[pa] * EQ_ROW + 9 * pb);
+        float2 *rb = reinterpret_cast<float2 *>(out + (int64_t)tmap[pb] * EQ_ROW + 9 * pa);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                const double kv = fma(lam, M[3 * i + j], fma(mu, M[3 * j + i], i == j ? mtr : 0.0));
+                float2 kv = df_add(df_mul(L, M[3 * i + j]), df_mul(U, M[3 * j + i]));
+                if (i == j) kv = df_add(kv, mtr);
                 ra[3 * i + j] = kv;
                 if (pb != pa) rb[3 * j + i] = kv;
             }
     }
-    if (tid < 60) {  // d_e[3 a + c] = b_c sum_q w detJ N_a (FP64)
-        const int a = tid / 3, c = tid - 3 * a;
+    if (tid < 20) {  // d_e[3 a + c] = b_c sum_q w detJ N_a (FP64)
         double m = 0.0;
-        for (int q = 0; q < 27; ++q) m = fma(wdet[q], c_q2s_tab[q][a][0], m);
-        out[(int64_t)tmap[a] * EQ_ROW + 180 + c] = (c == 0 ? b0 : (c == 1 ? b1 : b2)) * m;
+        for (int q = 0; q < 27; ++q) m = fma(wdet[q], c_q2s_tab[q][tid][0], m);
+        double *o = out + (int64_t)tmap[tid] * EQ_ROW + 180;
+        o[0] = b0 * m;
+        o[1] = b1 * m;
+        o[2] = b2 * m;
     }
 }
 
@@ -689,10 +681,11 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
 
 // elasticity gather for the serendipity brick: one warp per node.  Row a of
 // each incident element is incidence entry t (ascending, so the sums run in
-// element order: bit-reproducible); its 180 values are added at the
-// neighbour slot inc_slot[t * 20 + b] of node b in a shared-memory row
-// accumulator (up to MF_MAX_DEG_HO neighbours), the node's three CSR rows are
-// then written once, with Dirichlet elimination and lifting.
+// element order: bit-reproducible); its 180 values (FP32 pairs) are added in
+// double-float at the neighbour slot inc_slot[t * 20 + b] of node b in a
+// shared-memory row accumulator (up to MF_MAX_DEG_HO neighbours); the node's
+// three CSR rows are then written once in FP64 (one exact conversion and one
+// FP64 add per entry), with Dirichlet elimination and lifting.
 constexpr int GQ_WARPS = 4;
 
 __global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
@@ -702,14 +695,15 @@ __global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
     double *__restrict__ values, double *__restrict__ d)
 {
     constexpr int H = MF_MAX_DEG_HO / 32;
-    __shared__ double acc_all[GQ_WARPS][MF_MAX_DEG_HO * 9];
+    __shared__ float2 acc_all[GQ_WARPS][MF_MAX_DEG_HO * 9];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = (int64_t)blockIdx.x * GQ_WARPS + w;
     if (n >= n_nodes) return;  // warp-uniform
-    double *acc = acc_all[w];
+    float2 *acc = acc_all[w];
+    const float2 *scf = reinterpret_cast<const float2 *>(sc);
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
-    for (int i = lane; i < 9 * deg; i += 32) acc[i] = 0.0;
+    for (int i = lane; i < 9 * deg; i += 32) acc[i] = make_float2(0.0f, 0.0f);
     const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
     double dsum = 0.0;  // lane c < 3: component c of the load, element order
     if (lane < 3)
@@ -718,19 +712,19 @@ __global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
     constexpr int IU = (180 + 31) / 32;  // items per lane and incidence entry
     for (int64_t cb = i0; cb < i1; cb += 2) {
         const int cnt = (int)min((int64_t)2, i1 - cb);
-        double v[2][IU];
+        float2 v[2][IU];
         int ad[2][IU];
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int u = 0; u < IU; ++u) {
                 const int idx = lane + 32 * u;
-                v[j][u] = 0.0;
+                v[j][u] = make_float2(0.0f, 0.0f);
                 ad[j][u] = -1;
                 if (j < cnt && idx < 180) {
                     const int64_t t = cb + j;
                     const int b = idx / 9;
-                    v[j][u] = sc[t * EQ_ROW + idx];
+                    v[j][u] = scf[t * EQ_ROW + idx];
                     ad[j][u] = inc_slot[t * 20 + b] * 9 + (idx - 9 * b);
                 }
             }
@@ -738,7 +732,7 @@ __global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
         for (int j = 0; j < 2; ++j) {
 #pragma unroll
             for (int u = 0; u < IU; ++u)
-                if (ad[j][u] >= 0) acc[ad[j][u]] += v[j][u];
+                if (ad[j][u] >= 0) acc[ad[j][u]] = df_add(acc[ad[j][u]], v[j][u]);
             __syncwarp();
         }
     }
@@ -779,7 +773,7 @@ __global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
                 }
             }
             if (j >= 3 * deg) continue;
-            double v = acc[k * 9 + 3 * c + cp];
+            double v = df_to_double(acc[k * 9 + 3 * c + cp]);
             if (mask) {
                 const int64_t sdof = 3 * (int64_t)mcol + cp;
                 if (rm) v = (r == sdof) ? 1.0 : 0.0;

@@ -3,6 +3,8 @@
 // element kernels of Sec. 4.1 (one element per call, FP64).
 #pragma once
 
+#include <cstring>
+
 #include "mf_internal.h"
 
 namespace {
@@ -185,7 +187,7 @@ __host__ __device__ inline double q2s_shape(int a, const double (&xi)[3], double
 // Double-float arithmetic on FP32 pairs (hi, lo), |lo| <= ulp(hi) / 2, about
 // 48 significant bits (Dekker's product with an FMA, Knuth's two-sum): FP32
 // runs at 64 times the FP64 rate here.
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b)
+__host__ __device__ __forceinline__ float2 df_mul(float2 a, float2 b)
 {
     const float p = a.x * b.x;
     const float e = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p)));
@@ -193,13 +195,106 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b)
     return make_float2(h, e - (h - p));
 }
 
-__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+__host__ __device__ __forceinline__ float2 df_add(float2 a, float2 b)
 {
     const float s = a.x + b.x;
     const float z = s - a.x;
     const float e = ((a.x - (s - z)) + (b.x - z)) + (a.y + b.y);
     const float h = s + e;
     return make_float2(h, e - (h - s));
+}
+
+__host__ __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// 1 / a: an FP32 seed and one Newton step r0 + r0 (1 - a r0), the residual
+// from the exact product a.x r0 (FMA) and the low part
+__host__ __device__ __forceinline__ float2 df_recip(float2 a)
+{
+    const float r0 = 1.0f / a.x;
+    const float ph = a.x * r0;
+    const float pl = fmaf(a.x, r0, -ph);
+    const float e = ((1.0f - ph) - pl) - a.y * r0;
+    const float d = r0 * e;
+    const float h = r0 + d;
+    return make_float2(h, d - (h - r0));
+}
+
+// sqrt(a), a > 0: an FP32 seed and one Newton step s0 + (a - s0^2) / (2 s0)
+__host__ __device__ __forceinline__ float2 df_sqrt(float2 a)
+{
+    const float s0 = sqrtf(a.x);
+    const float ph = s0 * s0;
+    const float pl = fmaf(s0, s0, -ph);
+    const float e = ((a.x - ph) - pl) + a.y;
+    const float d = e * (0.5f / s0);
+    const float h = s0 + d;
+    return make_float2(h, d - (h - s0));
+}
+
+// Exact FP32 -> FP64 conversion by integer operations on the IEEE-754 fields
+// (FP32 subnormals, below 1.2e-38 in magnitude, become zero; infinities and
+// NaN keep their class), and a pair's value as one FP64 add
+__host__ __device__ __forceinline__ double f32_to_f64_exact(float f)
+{
+    unsigned u;
+    memcpy(&u, &f, 4);
+    const unsigned ex = (u >> 23) & 0xffu, sg = u & 0x80000000u, mt = u & 0x7fffffu;
+    unsigned long long b = (unsigned long long)sg << 32;
+    if (ex != 0u)
+        b |= ((unsigned long long)(ex == 0xffu ? 0x7ffu : ex + 896u) << 52) | ((unsigned long long)mt << 29);
+    double r;
+    memcpy(&r, &b, 8);
+    return r;
+}
+
+__host__ __device__ __forceinline__ double df_to_double(float2 a) { return f32_to_f64_exact(a.x) + f32_to_f64_exact(a.y); }
+
+// a b - c d in double-float
+__host__ __device__ __forceinline__ float2 df_det2(float2 a, float2 b, float2 c, float2 d)
+{
+    return df_add(df_mul(a, b), df_neg(df_mul(c, d)));
+}
+
+// Geometry of the 20-node brick (the vertices' trilinear map) at point
+// q = i + 3 j + 9 k of the 3 x 3 x 3 Gauss rule, in double-float: c holds the
+// map coefficients of q1_jac_at as FP32 pairs; the Jacobian, its cofactors
+// and determinant follow q1_jac_at; Mq[3 i + j] = sqrt(w detJ) (J^-1)_ji;
+// returns w detJ.  About 47 bits against FP64's 53, at FP32 issue rates.
+__host__ __device__ __forceinline__ float2 q2s_point_df(const float2 (&c)[8][3], int q, float2 (&Mq)[9])
+{
+    constexpr double G3 = 0.77459666924148337704;  // sqrt(3/5)
+    constexpr double W5 = 5.0 / 9.0, W8 = 8.0 / 9.0;
+    const float2 g = make_float2((float)G3, (float)(G3 - (double)(float)G3));
+    const float2 w5 = make_float2((float)W5, (float)(W5 - (double)(float)W5));
+    const float2 w8 = make_float2((float)W8, (float)(W8 - (double)(float)W8));
+    const int qi = q % 3, qj = (q / 3) % 3, qk = q / 9;
+    const float2 zero = make_float2(0.0f, 0.0f);
+    const float2 xs = qi == 1 ? zero : (qi == 0 ? df_neg(g) : g);
+    const float2 ys = qj == 1 ? zero : (qj == 0 ? df_neg(g) : g);
+    const float2 zs = qk == 1 ? zero : (qk == 0 ? df_neg(g) : g);
+    float2 J[3][3];
+    for (int i = 0; i < 3; ++i) {
+        J[i][0] = df_add(df_mul(zs, df_add(df_mul(ys, c[7][i]), c[5][i])), df_add(df_mul(ys, c[3][i]), c[1][i]));
+        J[i][1] = df_add(df_mul(zs, df_add(df_mul(xs, c[7][i]), c[6][i])), df_add(df_mul(xs, c[3][i]), c[2][i]));
+        J[i][2] = df_add(df_mul(ys, df_add(df_mul(xs, c[7][i]), c[6][i])), df_add(df_mul(xs, c[5][i]), c[4][i]));
+    }
+    float2 C[3][3];  // C[j][i] = detJ (J^-1)_ji
+    C[0][0] = df_det2(J[1][1], J[2][2], J[1][2], J[2][1]);
+    C[1][0] = df_det2(J[1][2], J[2][0], J[1][0], J[2][2]);
+    C[2][0] = df_det2(J[1][0], J[2][1], J[1][1], J[2][0]);
+    C[0][1] = df_det2(J[0][2], J[2][1], J[0][1], J[2][2]);
+    C[1][1] = df_det2(J[0][0], J[2][2], J[0][2], J[2][0]);
+    C[2][1] = df_det2(J[0][1], J[2][0], J[0][0], J[2][1]);
+    C[0][2] = df_det2(J[0][1], J[1][2], J[0][2], J[1][1]);
+    C[1][2] = df_det2(J[0][2], J[1][0], J[0][0], J[1][2]);
+    C[2][2] = df_det2(J[0][0], J[1][1], J[0][1], J[1][0]);
+    const float2 det = df_add(df_add(df_mul(J[0][0], C[0][0]), df_mul(J[0][1], C[1][0])), df_mul(J[0][2], C[2][0]));
+    const float2 wv = df_mul(df_mul(qi == 1 ? w8 : w5, qj == 1 ? w8 : w5), qk == 1 ? w8 : w5);
+    const float2 wd = df_mul(wv, det);
+    const float2 sr = df_mul(df_sqrt(wd), df_recip(det));  // sqrt(w detJ) / detJ
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Mq[3 * i + j] = df_mul(sr, C[j][i]);
+    return wd;
 }
 
 // 20-node brick at the 27 points of the 3 x 3 x 3 Gauss rule (point q = i +
