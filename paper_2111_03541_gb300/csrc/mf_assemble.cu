@@ -73,7 +73,8 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
 // pipe (1/64 of the FP32 rate here): the shape values and reference gradients
 // at the 27 points come from a table, and everything but the map
 // coefficients and the load runs in double-float (FP32 pairs, about 47
-// bits).  (0) lanes < 24 take the vertices' map coefficients; (1) lanes
+// bits).  (0) lanes < 24 load the element's map coefficients (cached by the
+// pattern); (1) lanes
 // q < 27 the geometry of Gauss point q from the trilinear map (q2s_point_df):
 // w detJ, and sqrt(w detJ) J^-T (detJ > 0 at every point is checked when the
 // mesh is made); (2) the 540 (node,
@@ -86,8 +87,7 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
 constexpr int Q2W = 4;  // elements (warps) per block
 constexpr int QCH = 9;  // Gauss points per chunk of gradients in shared memory
 
-__global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, const double *__restrict__ X,
-                                                               const int32_t *__restrict__ conn,
+__global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, const float2 *__restrict__ gmap,
                                                                const double *__restrict__ kc, double f,
                                                                const int32_t *__restrict__ map,
                                                                double *__restrict__ out, int *status)
@@ -99,19 +99,7 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t e = (int64_t)blockIdx.x * Q2W + w;
     if (e >= n_el) return;  // warp-uniform
-    const int32_t *ce = conn + e * 20;
-    if (lane < 24) {  // map coefficient c_S[i], S = lane / 3, i = lane % 3 (q1_wht's, scaled)
-        const int S = lane / 3, i = lane % 3;
-        double v = 0.0;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const double xa = X[3 * (int64_t)ce[a] + i];
-            v += (__popc(a & S) & 1) ? -xa : xa;
-        }
-        const double cv = v * ((__popc(S) & 1) ? -0.125 : 0.125);
-        const float hi = __double2float_rn(cv);
-        cw[w][S][i] = make_float2(hi, __double2float_rn(cv - (double)hi));
-    }
+    if (lane < 24) cw[w][lane / 3][lane % 3] = gmap[e * 24 + lane];  // map coefficient c_S[i], S = lane / 3
     __syncwarp();
     if (lane < 27) {
         float2 c[8][3], M9[9];
@@ -186,8 +174,9 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
 }
 
 // 20-node serendipity brick, linear elasticity (Sec. 4.2, the element of the
-// cantilever beams), 3 x 3 x 3 Gauss: one block per element.  The geometry
-// (q2s_point_df) and the gradients sqrt(w detJ) grad N_a(q) are formed in
+// cantilever beams), 3 x 3 x 3 Gauss: one block per element, from the map
+// coefficients cached by the pattern.  The geometry (q2s_point_df) and the
+// gradients sqrt(w detJ) grad N_a(q) are formed in
 // double-float as in the thermal brick (all 27 points at once, [q][i][a] so
 // that the threads of a warp read consecutive nodes); thread p < 210 then
 // takes the pair a <= b (row-major upper triangle), sums the nine entries of
@@ -200,8 +189,7 @@ __global__ void __launch_bounds__(Q2W * 32) k_elem_thermal_q2s(int64_t n_el, con
 constexpr int EQ_T = 224;  // 7 warps: one thread per pair a <= b (210)
 constexpr int EQ_ROW = 20 * 9 + 3;
 
-__global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const double *__restrict__ X,
-                                                           const int32_t *__restrict__ conn,
+__global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const float2 *__restrict__ gmap,
                                                            const double *__restrict__ Ec, double nu, double b0,
                                                            double b1, double b2, const int32_t *__restrict__ map,
                                                            double *__restrict__ out, int *status)
@@ -209,24 +197,15 @@ __global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const d
     __shared__ float2 cw[8][3];         // map coefficients, FP32 pairs
     __shared__ float2 lmu[2];           // lambda, mu
     __shared__ double wdet[27];         // w detJ
-    __shared__ float2 Mq[27][9];        // sqrt(w detJ) (J^-1)_ji at [i][j]
+    __shared__ float2 Mq[27][9];        // J[q][i][j], then sqrt(w detJ) (J^-1)_ji at [q][3 i + j]
+    __shared__ float2 Cq[27][9];        // cofactors: detJ (J^-1)_ji at [q][3 j + i]
     __shared__ float2 grd[27][3][20];   // sqrt(w detJ) d_i N_a at [q][i][a]
     __shared__ int32_t tmap[20];
     const int tid = threadIdx.x;
     const int64_t e = blockIdx.x;
     if (e >= n_el) return;  // block-uniform
-    const int32_t *ce = conn + e * 20;
-    if (tid < 24) {  // map coefficient c_S[i], S = tid / 3, i = tid % 3 (q1_wht's, scaled)
-        const int S = tid / 3, i = tid % 3;
-        double v = 0.0;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const double xa = X[3 * (int64_t)ce[a] + i];
-            v += (__popc(a & S) & 1) ? -xa : xa;
-        }
-        const double cv = v * ((__popc(S) & 1) ? -0.125 : 0.125);
-        const float hi = __double2float_rn(cv);
-        cw[S][i] = make_float2(hi, __double2float_rn(cv - (double)hi));
+    if (tid < 24) {
+        cw[tid / 3][tid % 3] = gmap[e * 24 + tid];  // map coefficient c_S[i], S = tid / 3
     } else if (tid >= 32 && tid < 52) {
         tmap[tid - 32] = map[e * 20 + tid - 32];
     } else if (tid == 64) {
@@ -239,16 +218,47 @@ __global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const d
             lmu[k] = make_float2(hi, __double2float_rn(lm[k] - (double)hi));
         }
     }
+    // the geometry of q2s_point_df spread over the block in three short
+    // phases (the Jacobian entries, the cofactors, then per point detJ,
+    // sqrt(w detJ) / detJ and the scaled inverse), so that the warps do not
+    // wait on one long dependent chain
+    constexpr double G3 = 0.77459666924148337704;  // sqrt(3/5)
+    constexpr double W5 = 5.0 / 9.0, W8 = 8.0 / 9.0;
+    const float2 g3 = make_float2((float)G3, (float)(G3 - (double)(float)G3));
+    __syncthreads();
+    for (int it = tid; it < 27 * 9; it += EQ_T) {  // J[q][i][j]
+        const int q = it / 9, i = (it - 9 * q) / 3, j = it - 9 * q - 3 * i;
+        const int qd[3] = {q % 3, (q / 3) % 3, q / 9};
+        float2 xyz[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) xyz[d] = qd[d] == 1 ? make_float2(0.0f, 0.0f) : (qd[d] == 0 ? df_neg(g3) : g3);
+        // J[i][0] = z (y c7 + c5) + (y c3 + c1), J[i][1] = z (x c7 + c6) + (x c3 + c2),
+        // J[i][2] = y (x c7 + c6) + (x c5 + c4)
+        const float2 u = j == 2 ? xyz[1] : xyz[2], v = j == 0 ? xyz[1] : xyz[0];
+        const int A = j == 0 ? 5 : 6, B = j == 2 ? 5 : 3, C = j == 0 ? 1 : (j == 1 ? 2 : 4);
+        Mq[q][3 * i + j] = df_add(df_mul(u, df_add(df_mul(v, cw[7][i]), cw[A][i])), df_add(df_mul(v, cw[B][i]), cw[C][i]));
+    }
+    __syncthreads();
+    for (int it = tid; it < 27 * 9; it += EQ_T) {  // Cq[q][3 j + i] = J[i1][j1] J[i2][j2] - J[i1][j2] J[i2][j1]
+        const int q = it / 9, j = (it - 9 * q) / 3, i = it - 9 * q - 3 * j;
+        const int i1 = i == 2 ? 0 : i + 1, i2 = i == 0 ? 2 : i - 1, j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;
+        Cq[q][3 * j + i] = df_det2(Mq[q][3 * i1 + j1], Mq[q][3 * i2 + j2], Mq[q][3 * i1 + j2], Mq[q][3 * i2 + j1]);
+    }
     __syncthreads();
     if (tid < 27) {
-        float2 c[8][3], M9[9];
+        const int q = tid, qi = q % 3, qj = (q / 3) % 3, qk = q / 9;
+        const float2 w5 = make_float2((float)W5, (float)(W5 - (double)(float)W5));
+        const float2 w8 = make_float2((float)W8, (float)(W8 - (double)(float)W8));
+        const float2 det = df_add(df_add(df_mul(Mq[q][0], Cq[q][0]), df_mul(Mq[q][1], Cq[q][3])),
+                                  df_mul(Mq[q][2], Cq[q][6]));
+        const float2 wv = df_mul(df_mul(qi == 1 ? w8 : w5, qj == 1 ? w8 : w5), qk == 1 ? w8 : w5);
+        const float2 wd = df_mul(wv, det);
+        const float2 sr = df_mul(df_sqrt(wd), df_recip(det));  // sqrt(w detJ) / detJ
+        wdet[q] = df_to_double(wd);
 #pragma unroll
-        for (int S = 0; S < 8; ++S)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) c[S][i] = cw[S][i];
-        wdet[tid] = df_to_double(q2s_point_df(c, tid, M9));
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Mq[tid][k] = M9[k];
+            for (int j = 0; j < 3; ++j) Mq[q][3 * i + j] = df_mul(sr, Cq[q][3 * j + i]);
     }
     __syncthreads();
     for (int it = tid; it < 27 * 20; it += EQ_T) {  // grad N = J^-T gradref N, in FP32 pairs
@@ -287,10 +297,11 @@ __global__ void __launch_bounds__(EQ_T) k_elem_elastic_q2s(int64_t n_el, const d
                 for (int j = 0; j < 3; ++j) {
                     const int k = 3 * i + j;
                     const float p = x[i].x * y[j].x;
-                    const float ep = fmaf(x[i].x, y[j].x, -p) + fmaf(x[i].x, y[j].y, x[i].y * y[j].x);
-                    const float tt = sh[k] + p;  // two-sum of sh and p
+                    const float ep = fmaf(x[i].x, y[j].x, -p);  // exact error of p
+                    const float tt = sh[k] + p;                 // two-sum of sh and p
                     const float z = tt - sh[k];
-                    sl[k] += ((sh[k] - (tt - z)) + (p - z)) + ep;
+                    const float es = (sh[k] - (tt - z)) + (p - z);
+                    sl[k] = fmaf(x[i].x, y[j].y, fmaf(x[i].y, y[j].x, sl[k] + (es + ep)));  // + cross terms
                     sh[k] = tt;
                 }
         }
@@ -688,22 +699,37 @@ __global__ void __launch_bounds__(GEL_WARPS * 32, 5) k_gather_el(
 // FP64 add per entry), with Dirichlet elimination and lifting.
 constexpr int GQ_WARPS = 4;
 
-__global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
-    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+// shared memory of one warp of k_gather_el_q2s for rows of up to maxd neighbours
+__host__ __device__ constexpr size_t gq_warp_bytes(int maxd) { return (size_t)maxd * (9 * sizeof(float2) + 8); }
+
+__global__ void __launch_bounds__(GQ_WARPS * 32, 8) k_gather_el_q2s(
+    int64_t n_nodes, int maxd, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int64_t *__restrict__ inc_ptr, const uint8_t *__restrict__ inc_slot, const double *__restrict__ sc,
     const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
     double *__restrict__ values, double *__restrict__ d)
 {
-    constexpr int H = MF_MAX_DEG_HO / 32;
-    __shared__ float2 acc_all[GQ_WARPS][MF_MAX_DEG_HO * 9];
+    extern __shared__ float2 gq_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = (int64_t)blockIdx.x * GQ_WARPS + w;
     if (n >= n_nodes) return;  // warp-uniform
-    float2 *acc = acc_all[w];
+    // per warp: the row accumulator [maxd][9], then the neighbours' column
+    // nodes and Dirichlet flags [maxd] each
+    float2 *acc = reinterpret_cast<float2 *>(reinterpret_cast<char *>(gq_smem) + w * gq_warp_bytes(maxd));
+    int32_t *ncol = reinterpret_cast<int32_t *>(acc + 9 * maxd);
+    int32_t *nflag = ncol + maxd;
     const float2 *scf = reinterpret_cast<const float2 *>(sc);
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
     for (int i = lane; i < 9 * deg; i += 32) acc[i] = make_float2(0.0f, 0.0f);
+    for (int k = lane; k < deg; k += 32) {
+        const int32_t mc = adj_col[p0 + k];
+        int f = 0;
+        if (mask)
+#pragma unroll
+            for (int cp = 0; cp < 3; ++cp) f |= (mask[3 * (int64_t)mc + cp] != 0 ? 1 : 0) << cp;
+        ncol[k] = mc;
+        nflag[k] = f;
+    }
     const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];
     double dsum = 0.0;  // lane c < 3: component c of the load, element order
     if (lane < 3)
@@ -736,48 +762,19 @@ __global__ void __launch_bounds__(GQ_WARPS * 32) k_gather_el_q2s(
             __syncwarp();
         }
     }
-    // neighbour k's column node and Dirichlet flags, loaded by lane k % 32
-    int32_t mcol_l[H];
-    unsigned cm_l[H];
-#pragma unroll
-    for (int h = 0; h < H; ++h) {
-        const int k = lane + 32 * h;
-        mcol_l[h] = 0;
-        cm_l[h] = 0u;
-        if (k < deg) {
-            mcol_l[h] = adj_col[p0 + k];
-            if (mask)
-#pragma unroll
-                for (int cp = 0; cp < 3; ++cp) cm_l[h] |= (mask[3 * (int64_t)mcol_l[h] + cp] != 0 ? 1u : 0u) << cp;
-        }
-    }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
         const int64_t r = 3 * n + c;
         const bool rm = mask ? mask[r] != 0 : false;
         const int64_t rb = row_ptr[r];
         double lift = 0.0;
-        for (int j0 = 0; j0 < 3 * deg; j0 += 32) {  // warp-uniform
-            const int j = j0 + lane;
-            const int k = (j < 3 * deg ? j : 0) / 3, cp = j - 3 * (j / 3);
-            const int kk = k & 31, hk = k >> 5;
-            int32_t mcol = 0;
-            unsigned fl = 0u;
-#pragma unroll
-            for (int h = 0; h < H; ++h) {  // every lane takes part in every shuffle
-                const int32_t mc = __shfl_sync(0xffffffffu, mcol_l[h], kk);
-                const unsigned f = __shfl_sync(0xffffffffu, cm_l[h], kk);
-                if (h == hk) {
-                    mcol = mc;
-                    fl = f;
-                }
-            }
-            if (j >= 3 * deg) continue;
+        for (int j = lane; j < 3 * deg; j += 32) {
+            const int k = j / 3, cp = j - 3 * k;
             double v = df_to_double(acc[k * 9 + 3 * c + cp]);
             if (mask) {
-                const int64_t sdof = 3 * (int64_t)mcol + cp;
+                const int64_t sdof = 3 * (int64_t)ncol[k] + cp;
                 if (rm) v = (r == sdof) ? 1.0 : 0.0;
-                else if ((fl >> cp) & 1u) { lift -= v * bval[sdof]; v = 0.0; }
+                else if ((nflag[k] >> cp) & 1) { lift -= v * bval[sdof]; v = 0.0; }
             }
             values[rb + j] = v;
         }
@@ -1046,8 +1043,8 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
                                              : "elem_thermal_q2s",
                       st);
         if (m->elem == MF_Q2S_HEX)
-            k_elem_thermal_q2s<<<nblk(ne, Q2W), Q2W * 32, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f,
-                                                                   p->elem_inc, p->scratch, status);
+            k_elem_thermal_q2s<<<nblk(ne, Q2W), Q2W * 32, 0, st>>>(ne, p->q2s_map, c->elem_coef, f, p->elem_inc,
+                                                                   p->scratch, status);
         else if (cap)
             k_elem_capacity<<<nblk(ne, 128), 128, 0, st>>>(m->elem, ne, m->coords, m->conn, c->elem_coef, p->tr,
                                                            p->elem_inc, p->scratch, status);
@@ -1077,16 +1074,19 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
     } else if (form == MF_FORM_ELASTIC && m->elem == MF_Q2S_HEX) {
         mf_prof_begin("elem_elastic_q2s", st);
         if (ne > 0)
-            k_elem_elastic_q2s<<<(unsigned)ne, EQ_T, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, c->nu,
-                                                              c->source[0], c->source[1], c->source[2], p->elem_inc,
-                                                              p->scratch, status);
+            k_elem_elastic_q2s<<<(unsigned)ne, EQ_T, 0, st>>>(ne, p->q2s_map, c->elem_coef, c->nu, c->source[0],
+                                                              c->source[1], c->source[2], p->elem_inc, p->scratch,
+                                                              status);
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         mf_prof_begin("gather_elastic_q2s", st);
         const mf_adj &A = p->adj[0];
-        k_gather_el_q2s<<<nblk(m->n_nodes, GQ_WARPS), GQ_WARPS * 32, 0, st>>>(
-            m->n_nodes, A.ptr, A.col, p->inc_ptr, p->inc_slot, p->scratch, c->bc_mask, c->bc_val, p->row_ptr, values,
-            d);
+        const int maxd = A.max_deg > 0 ? A.max_deg : 1;
+        const size_t smem = GQ_WARPS * gq_warp_bytes(maxd);
+        MF_CUDA(cudaFuncSetAttribute(k_gather_el_q2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_gather_el_q2s<<<nblk(m->n_nodes, GQ_WARPS), GQ_WARPS * 32, smem, st>>>(
+            m->n_nodes, maxd, A.ptr, A.col, p->inc_ptr, p->inc_slot, p->scratch, c->bc_mask, c->bc_val, p->row_ptr,
+            values, d);
         mf_prof_end(st);
     } else if (form == MF_FORM_ELASTIC) {
         const size_t smem = sizeof(double) * 8 * 8 * 3 * EL_T;

@@ -21,6 +21,7 @@ struct mf_adj {
     int64_t n_pairs = 0;     // unique (row node, col node) pairs
     int64_t *ptr = nullptr;  // [n_rows + 1]
     int32_t *col = nullptr;  // [n_pairs] ascending per row
+    int32_t max_deg = 0;     // largest row (set where a kernel sizes shared memory by it)
 };
 
 struct mf_mesh {
@@ -76,6 +77,9 @@ struct mf_pattern {
     uint8_t *tr = nullptr;
     double *kref = nullptr;
     int64_t n_translate = 0;
+    // 20-node bricks: the vertices' trilinear-map coefficients of q1_jac_at
+    // per element as FP32 pairs (hi, lo), [n_elems][8][3]
+    float2 *q2s_map = nullptr;
     // elasticity, mixed path: int64 3x3 block accumulator per upper node pair
     // (n, m >= n; a diagonal block as its upper triangle), numbered compactly:
     // upper pair (n, slot k) is block cbase[n] + k; tpos gives, for a lower

@@ -260,6 +260,32 @@ __global__ void k_mark_translates(int64_t n_nodes, const int64_t *__restrict__ i
         if (tr[inc[t]]) loc[t] |= 0x80;
 }
 
+// map coefficients of the 20-node bricks (q1_wht's of the 8 vertices,
+// scaled for q1_jac_at) as FP32 pairs: thread (e, S, i)
+__global__ void k_q2s_map(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                          float2 *__restrict__ out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 24 * n_el) return;
+    const int64_t e = t / 24;
+    const int r = (int)(t - 24 * e), S = r / 3, i = r - 3 * S;
+    double v = 0.0;
+    for (int a = 0; a < 8; ++a) {
+        const double xa = X[3 * (int64_t)conn[20 * e + a] + i];
+        v += (__popc(a & S) & 1) ? -xa : xa;
+    }
+    const double cv = v * ((__popc(S) & 1) ? -0.125 : 0.125);
+    const float hi = __double2float_rn(cv);
+    out[t] = make_float2(hi, __double2float_rn(cv - (double)hi));
+}
+
+// largest row of an adjacency
+__global__ void k_max_deg(int64_t n_rows, const int64_t *__restrict__ ptr, int *out)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n_rows) atomicMax(out, (int)(ptr[r + 1] - ptr[r]));
+}
+
 // slot map: position of conn[e][b] among the neighbours of conn[e][a],
 // slot[(e * npe + a) * npe + b]
 __global__ void k_slot_map(int64_t n_el, int npe, const int32_t *__restrict__ conn, const int64_t *__restrict__ ptr,
@@ -534,6 +560,8 @@ void mf_pattern_free(mf_pattern *p)
     p->side = nullptr;
     cudaFree(p->row_ptr);
     cudaFree(p->col_idx);
+    cudaFree(p->q2s_map);
+    p->q2s_map = nullptr;
     for (int i = 0; i < 3; ++i) {
         cudaFree(p->adj[i].ptr);
         cudaFree(p->adj[i].col);
@@ -619,6 +647,10 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
             s = mf_flow_consts_upload();
             if (s != MF_OK) { free_inc(incv, st); return s; }
         }
+        if (m->elem == MF_Q2S_HEX && m->n_elems > 0) {
+            MF_CUDA(cudaMallocAsync(&p->q2s_map, sizeof(float2) * 24 * m->n_elems, st));
+            k_q2s_map<<<nblk(24 * m->n_elems), TPB, 0, st>>>(m->n_elems, m->coords, m->conn, p->q2s_map);
+        }
         if (m->elem == MF_Q1_HEX && m->n_elems > 0) {
             unsigned long long *cnt = nullptr;
             MF_CUDA(cudaMallocAsync(&p->tr, (size_t)m->n_elems, st));
@@ -659,8 +691,23 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, m->conn, incv.ptr, incv.inc, p->adj[0].ptr,
                                                      p->adj[0].col, p->inc_slot);
         p->scratch_stride = (int64_t)npe * (9 * npe + 3);
+        {
+            int *dmax = nullptr;
+            MF_CUDA(cudaMallocAsync(&dmax, sizeof(int), st));
+            MF_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), st));
+            k_max_deg<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, dmax);
+            int h = 0;
+            MF_CUDA(cudaMemcpyAsync(&h, dmax, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MF_CUDA(cudaStreamSynchronize(st));
+            MF_CUDA(cudaFreeAsync(dmax, st));
+            p->adj[0].max_deg = h;
+        }
         s = mf_flow_consts_upload();  // reference table of the 20-node brick
         if (s != MF_OK) { free_inc(incv, st); return s; }
+        if (m->n_elems > 0) {
+            MF_CUDA(cudaMallocAsync(&p->q2s_map, sizeof(float2) * 24 * m->n_elems, st));
+            k_q2s_map<<<nblk(24 * m->n_elems), TPB, 0, st>>>(m->n_elems, m->coords, m->conn, p->q2s_map);
+        }
     } else if (form == MF_FORM_ELASTIC) {
         p->n_rows = 3 * m->n_nodes;
         p->nnz = 9 * p->adj[0].n_pairs;
