@@ -657,8 +657,8 @@ def suite(dev):
                                 "elements_per_s": ne / (ms * 1e-3), "element_kernel_ms": el_ms,
                                 "element_algorithmic_tflops": None if el_ms is None
                                 else flops / (el_ms * 1e-3) / 1e12,
-                                "arithmetic": "geometry and load FP64; gradients and Gram sums in double-float "
-                                              "(FP32 pairs, about 48 bits)"}
+                                "arithmetic": "map coefficients and load FP64; geometry, gradients and Gram sums "
+                                              "in double-float (FP32 pairs, about 47 bits)"}
     del P
     torch.cuda.empty_cache()
     # 20-node serendipity bricks, elasticity (the cantilever element), 48^3
@@ -679,8 +679,9 @@ def suite(dev):
                                 "gather_kernel_ms": ga_ms,
                                 "element_algorithmic_tflops": None if el_ms is None
                                 else flops / (el_ms * 1e-3) / 1e12,
-                                "arithmetic": "geometry and load FP64; gradients and the nine Gram sums per pair "
-                                              "in double-float (FP32 pairs, about 48 bits)"}
+                                "arithmetic": "map coefficients, load and row sums' conversion FP64; geometry, "
+                                              "gradients, the nine Gram sums per pair, the block finishing and the "
+                                              "row sums in double-float (FP32 pairs, about 47 bits)"}
     del P
     torch.cuda.empty_cache()
     # loaded boundary: a random stress on five sides of the 64^3 elasticity box (clamped at x = 0)
