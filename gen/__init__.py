@@ -210,6 +210,58 @@ def hex20_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
     return {"dim": 3, "elem": "Q2S", "n": n, "coords": coords, "conn": conn.astype(np.int32)}
 
 
+def tet10_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
+    """10-node (quadratic) tetrahedra on the unit cube: each cube of an ``n^3``
+    grid split into the 6 tetrahedra around its main diagonal (Kuhn's
+    subdivision, conforming across cubes), then one node at the midpoint of
+    every edge.  Local nodes: vertices 0..3, then the edges (0,1), (1,2),
+    (2,0), (0,3), (1,3), (2,3).  Global numbering: the (n+1)^3 vertices of
+    ``hex_mesh`` (jittered the same way), then the edge midpoints in the order
+    of their first appearance.  Edges stay straight."""
+    from itertools import permutations
+    base = hex_mesh(n, jitter, seed)
+    X = base["coords"]
+    nv = n + 1
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    c0 = ((k.ravel() * nv) + j.ravel()) * nv + i.ravel()
+    step = (1, nv, nv * nv)
+    tets = []
+    for perm in permutations(range(3)):
+        v = [c0]
+        for ax in perm:
+            v.append(v[-1] + step[ax])
+        t = np.stack(v, axis=1)
+        # the vertex order's orientation follows the permutation's parity
+        odd = sum(1 for a in range(3) for b in range(a + 1, 3) if perm[a] > perm[b]) % 2
+        if odd:
+            t = t[:, [0, 2, 1, 3]]
+        tets.append(t)
+    vt = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int64)
+    ed = [(0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3)]
+    pairs = np.stack([np.sort(vt[:, [p, q]], axis=1) for p, q in ed], axis=1).reshape(-1, 2)
+    key = pairs[:, 0] * X.shape[0] + pairs[:, 1]
+    uniq, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    order = np.argsort(first)           # number the edges by first appearance
+    rank = np.empty_like(order)
+    rank[order] = np.arange(order.shape[0])
+    eid = rank[inv].reshape(-1, 6)
+    ends = pairs[first[order]]
+    coords = np.vstack([X, 0.5 * (X[ends[:, 0]] + X[ends[:, 1]])])
+    conn = np.concatenate([vt, X.shape[0] + eid], axis=1).astype(np.int32)
+    return {"dim": 3, "elem": "P2T", "n": n, "coords": coords, "conn": conn}
+
+
+def thermal_p2t_problem(n: int, jitter: float = 0.1, sigma: float = 0.5,
+                        seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    """3D thermal conduction on quadratic tetrahedra (u = 0 on the boundary, f = 1)."""
+    m = tet10_mesh(n, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)
+    m["bc_mask"], m["bc_val"] = thermal_bc(m)
+    m["form"] = "thermal"
+    m["source"] = 1.0
+    return m
+
+
 def thermal_q2s_problem(n: int, jitter: float = 0.15, sigma: float = 0.5,
                         seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
     """3D thermal conduction on 20-node serendipity bricks (u = 0 on the boundary, f = 1)."""

@@ -19,10 +19,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "_oracle.so")
 
-P1, P2, Q1, Q2S = 0, 1, 2, 3
-QTRI3, QTRI6, QHEX8, QHEX27 = 0, 1, 2, 3
+P1, P2, Q1, Q2S, P2T = 0, 1, 2, 3, 4
+QTRI3, QTRI6, QHEX8, QHEX27, QTET64 = 0, 1, 2, 3, 4
 THERMAL, ELASTIC, OSEEN, CAPACITY = 0, 1, 2, 3
-ELEM = {"P1": P1, "P2": P2, "Q1": Q1, "Q2S": Q2S}
+ELEM = {"P1": P1, "P2": P2, "Q1": Q1, "Q2S": Q2S, "P2T": P2T}
 FORM = {"thermal": THERMAL, "elastic": ELASTIC, "oseen": OSEEN, "capacity": CAPACITY}
 
 _lib = None
@@ -109,15 +109,15 @@ def _p(a: np.ndarray):
 # ---------------------------------------------------------------------------
 
 def quad(kind: int) -> tuple[np.ndarray, np.ndarray]:
-    pts = np.zeros((27, 3))
-    w = np.zeros(27)
+    pts = np.zeros((64, 3))
+    w = np.zeros(64)
     nq = lib().or_quad(kind, _p(pts), _p(w))
-    dim = 3 if kind in (QHEX8, QHEX27) else 2
+    dim = 3 if kind in (QHEX8, QHEX27, QTET64) else 2
     return pts.ravel()[: nq * dim].reshape(nq, dim).copy(), w[:nq].copy()
 
 
 def shape(elem: int, xi) -> tuple[np.ndarray, np.ndarray]:
-    dim = 3 if elem in (Q1, Q2S) else 2
+    dim = 3 if elem in (Q1, Q2S, P2T) else 2
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     N = np.zeros(20)
     dN = np.zeros(60)
@@ -219,6 +219,8 @@ def _default_quad(elem: str, form: str) -> int:
         return QHEX8
     if elem == "Q2S":
         return QHEX27
+    if elem == "P2T":
+        return QTET64
     if form == "oseen":
         return QTRI6
     return QTRI3

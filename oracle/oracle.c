@@ -27,9 +27,9 @@
 #include <string.h>
 
 /* element kinds */
-enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2, OR_Q2S = 3 };
+enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2, OR_Q2S = 3, OR_P2T = 4 };
 /* quadrature kinds */
-enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3 };
+enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3, OR_QTET64 = 4 };
 /* forms */
 enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2, OR_CAPACITY = 3 };
 
@@ -77,6 +77,27 @@ int or_quad(int kind, double *pts, double *w)
             }
         }
         return 6;
+    }
+    if (kind == OR_QTET64) {
+        /* reference tetrahedron x, y, z >= 0, x + y + z <= 1 (volume 1/6) as
+         * the image of the unit cube under x = s, y = t (1 - s),
+         * z = r (1 - s)(1 - t) (Jacobian (1 - s)^2 (1 - t)), with 4-point
+         * Gauss-Legendre in s, t and r: a polynomial of total degree d becomes
+         * one of degree d + 2, d + 1, d in s, t, r, so the rule is exact to
+         * degree 5.  Point q = i + 4 j + 16 k. */
+        const double a = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0));
+        const double b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+        const double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
+        const double x4[4] = {-b, -a, a, b}, w4[4] = {wb, wa, wa, wb};
+        for (int q = 0; q < 64; ++q) {
+            const int i = q % 4, j = (q / 4) % 4, k = q / 16;
+            const double S = 0.5 * (x4[i] + 1.0), T = 0.5 * (x4[j] + 1.0), R = 0.5 * (x4[k] + 1.0);
+            pts[3 * q + 0] = S;
+            pts[3 * q + 1] = T * (1.0 - S);
+            pts[3 * q + 2] = R * (1.0 - S) * (1.0 - T);
+            w[q] = 0.125 * w4[i] * w4[j] * w4[k] * (1.0 - S) * (1.0 - S) * (1.0 - T);
+        }
+        return 64;
     }
     if (kind == OR_QHEX27) {
         /* tensor Gauss-Legendre, 3 points per direction at 0, +-sqrt(3/5),
@@ -155,6 +176,24 @@ int or_shape(int elem, const double *xi, double *N, double *dN)
         }
         return 8;
     }
+    if (elem == OR_P2T) {
+        /* 10-node tetrahedron: lambda = (1 - x - y - z, x, y, z); vertices
+         * lambda_i (2 lambda_i - 1), then the edges (0,1), (1,2), (2,0),
+         * (0,3), (1,3), (2,3): 4 lambda_p lambda_q */
+        const double l[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+        const double dl[4][3] = {{-1.0, -1.0, -1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+        for (int i = 0; i < 4; ++i) {
+            N[i] = l[i] * (2.0 * l[i] - 1.0);
+            for (int j = 0; j < 3; ++j) dN[3 * i + j] = (4.0 * l[i] - 1.0) * dl[i][j];
+        }
+        const int ep[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+        for (int e = 0; e < 6; ++e) {
+            const int p = ep[e][0], q = ep[e][1];
+            N[4 + e] = 4.0 * l[p] * l[q];
+            for (int j = 0; j < 3; ++j) dN[3 * (4 + e) + j] = 4.0 * (dl[p][j] * l[q] + l[p] * dl[q][j]);
+        }
+        return 10;
+    }
     if (elem == OR_Q2S) {
         /* 20-node serendipity brick.  Vertex a = i + 2j + 4k at
          * (xa, ya, za) = (2i-1, 2j-1, 2k-1):
@@ -191,12 +230,16 @@ int or_shape(int elem, const double *xi, double *N, double *dN)
 }
 
 static int elem_dim(int elem) { return elem >= OR_Q1 ? 3 : 2; }
-static int elem_npe(int elem) { return elem == OR_P1 ? 3 : (elem == OR_P2 ? 6 : (elem == OR_Q1 ? 8 : 20)); }
+static int elem_npe(int elem)
+{
+    return elem == OR_P1 ? 3 : (elem == OR_P2 ? 6 : (elem == OR_Q1 ? 8 : (elem == OR_Q2S ? 20 : 10)));
+}
 
 /* Geometry at one point: J_ij = sum_a x_{a,i} dN_a/dxi_j, detJ, and the
  * physical gradients grad N_a = J^{-T} gradref N_a (Sec. 2.1: D_lambda N at
- * x_gamma).  Straight-sided P2 triangles take the affine map of their three
- * vertices (their isoparametric map is that same affine map).  Returns detJ. */
+ * x_gamma).  Straight-sided P2 triangles and tetrahedra take the affine map
+ * of their vertices (their isoparametric map is that same affine map).
+ * Returns detJ. */
 static double geometry(int elem, const double *X, const double *xi, double *N, double *gradN)
 {
     const int dim = elem_dim(elem);
@@ -210,6 +253,9 @@ static double geometry(int elem, const double *X, const double *xi, double *N, d
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j)
                 for (int a = 0; a < 3; ++a) J[i][j] += X[2 * a + i] * dNv[2 * a + j];
+    } else if (elem == OR_P2T) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) J[i][j] = X[3 * (j + 1) + i] - X[i];
     } else {
         for (int i = 0; i < dim; ++i)
             for (int j = 0; j < dim; ++j)
@@ -249,7 +295,7 @@ static double geometry(int elem, const double *X, const double *xi, double *N, d
 /* Exported for the geometry pins: sum_q w_q detJ_q (the element measure). */
 double or_elem_measure(int elem, int quad, const double *X)
 {
-    double pts[27 * 3], w[27], N[20], g[60];
+    double pts[64 * 3], w[64], N[20], g[60];
     const int nq = or_quad(quad, pts, w);
     const int dim = elem_dim(elem);
     double s = 0.0;
@@ -266,7 +312,7 @@ double or_elem_measure(int elem, int quad, const double *X)
 double or_elem_thermal(int elem, int quad, const double *X, double k, double fconst,
                        const double *fnodal, double *Ke, double *de)
 {
-    double pts[27 * 3], w[27], N[20], g[60];
+    double pts[64 * 3], w[64], N[20], g[60];
     const int nq = or_quad(quad, pts, w);
     const int dim = elem_dim(elem), npe = elem_npe(elem);
     double mindet = 1e300;
@@ -299,12 +345,16 @@ double or_elem_thermal(int elem, int quad, const double *X, double k, double fco
 /* Capacity element (Sec. 4.1: -C(T, T_t), the rate term; tangent negated):  */
 /* Me[a][b] = sum_q w detJ C N_a N_b, with a rule exact for N_a N_b on an    */
 /* affine element: the 3-point rule (P1, degree 2), the 6-point rule (P2,    */
-/* degree 4), 2 x 2 x 2 Gauss (Q1), 3 x 3 x 3 Gauss (Q2S).  Returns min detJ.*/
+/* degree 4), 2 x 2 x 2 Gauss (Q1), 3 x 3 x 3 Gauss (Q2S), the 64-point     */
+/* collapsed rule (P2T, degree 5).  Returns min detJ.                       */
 /* ------------------------------------------------------------------------ */
 double or_elem_capacity(int elem, const double *X, double C, double *Me)
 {
-    double pts[27 * 3], w[27], N[20], g[60];
-    const int quad = elem == OR_P1 ? OR_QTRI3 : (elem == OR_P2 ? OR_QTRI6 : (elem == OR_Q1 ? OR_QHEX8 : OR_QHEX27));
+    double pts[64 * 3], w[64], N[20], g[60];
+    const int quad = elem == OR_P1 ? OR_QTRI3
+                     : elem == OR_P2 ? OR_QTRI6
+                     : elem == OR_Q1 ? OR_QHEX8
+                     : elem == OR_Q2S ? OR_QHEX27 : OR_QTET64;
     const int nq = or_quad(quad, pts, w);
     const int dim = elem_dim(elem), npe = elem_npe(elem);
     double mindet = 1e300;
@@ -331,7 +381,7 @@ double or_elem_capacity(int elem, const double *X, double C, double *Me)
 double or_elem_elastic(int elem, const double *X, double E, double nu, const double *body,
                        double *Ke, double *de)
 {
-    double pts[27 * 3], w[27], N[20], g[60];
+    double pts[64 * 3], w[64], N[20], g[60];
     const int nq = or_quad(elem == OR_Q2S ? OR_QHEX27 : OR_QHEX8, pts, w);
     const int npe = elem_npe(elem), m = 3 * npe;
     const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
@@ -432,7 +482,7 @@ double or_elem_oseen(const double *X, const double *aN, double mu, double rho,
 /* ------------------------------------------------------------------------ */
 int or_facet_nodes(int elem, int face, int *loc)
 {
-    if (elem == OR_Q2S) return -1; /* no facet terms on serendipity bricks */
+    if (elem == OR_Q2S || elem == OR_P2T) return -1; /* no facet terms on these elements */
     if (elem == OR_Q1) {
         if (face < 0 || face > 5) return -1;
         const int d = face / 2, s = face % 2;

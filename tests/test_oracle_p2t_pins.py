@@ -1,0 +1,126 @@
+"""Pins of the oracle's 10-node (quadratic) tetrahedron, the quadratic simplex
+of the paper's 3D experiments (Sec. 4.1, Sec. 4.3): basis, the collapsed
+64-point rule, element matrices and assembled systems.
+
+Expected values come from the basis's defining properties (nodal
+interpolation, reproduction of all quadratics), the exact simplex moments
+a! b! c! / (a + b + c + 3)!, the closed-form load moments of quadratic
+simplices (-V/20 at a vertex, V/5 at an edge), invariants of the assembled
+Laplacian (zero row sums, symmetry, one zero eigenvalue per element, linear
+and harmonic quadratic fields in the kernel: straight-edged tetrahedra are
+affine even when jittered), a brute-force pattern and the O(h^3) rate on a
+manufactured solution.
+"""
+import itertools
+from math import factorial
+
+import numpy as np
+import scipy.sparse as sp
+
+import gen
+
+REF = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+EDGES = [(0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3)]
+
+
+def _ref_nodes():
+    return np.vstack([REF] + [0.5 * (REF[p] + REF[q]) for p, q in EDGES])
+
+
+def _tet(seed=3):
+    rng = np.random.default_rng(seed)
+    V = REF * 0.8 + rng.uniform(-0.1, 0.1, (4, 3)) + 0.3
+    return V, np.vstack([V] + [0.5 * (V[p] + V[q]) for p, q in EDGES])
+
+
+def test_basis_interpolates_and_reproduces_quadratics(orc):
+    R = _ref_nodes()
+    Nn = np.array([orc.shape(orc.P2T, r)[0] for r in R])
+    assert np.abs(Nn - np.eye(10)).max() < 1e-15
+    rng = np.random.default_rng(4)
+    for x in rng.dirichlet(np.ones(4), 8)[:, 1:]:
+        N, dN = orc.shape(orc.P2T, x)
+        for i, j, k in itertools.product(range(3), repeat=3):
+            if i + j + k > 2:
+                continue
+            f = R[:, 0] ** i * R[:, 1] ** j * R[:, 2] ** k
+            assert abs(N @ f - x[0] ** i * x[1] ** j * x[2] ** k) < 1e-15
+            g = np.array([i * x[0] ** max(i - 1, 0) * x[1] ** j * x[2] ** k,
+                          j * x[0] ** i * x[1] ** max(j - 1, 0) * x[2] ** k,
+                          k * x[0] ** i * x[1] ** j * x[2] ** max(k - 1, 0)])
+            assert np.abs(dN.T @ f - g).max() < 1e-14
+    x = np.array([0.2, 0.3, 0.1])
+    N, _ = orc.shape(orc.P2T, x)
+    assert abs(N @ (R[:, 0] * R[:, 1] * R[:, 2]) - 0.2 * 0.3 * 0.1) > 1e-3  # a cubic is not
+
+
+def test_collapsed_rule_exact_to_degree_5(orc):
+    pts, w = orc.quad(orc.QTET64)
+    assert pts.shape == (64, 3) and (w > 0).all() and (pts.sum(axis=1) < 1).all() and (pts > 0).all()
+    for a, b, c in itertools.product(range(6), repeat=3):
+        if a + b + c > 5:
+            continue
+        exact = factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + 3)
+        assert abs(np.sum(w * pts[:, 0] ** a * pts[:, 1] ** b * pts[:, 2] ** c) - exact) < 1e-16
+    assert abs(np.sum(w * pts[:, 0] ** 6) - factorial(6) / factorial(9)) > 1e-9
+
+
+def test_element_volume_load_and_stiffness(orc):
+    V, X = _tet()
+    vol = abs(np.linalg.det(V[1:] - V[0])) / 6
+    assert abs(orc.elem_measure(orc.P2T, orc.QTET64, X) - vol) < 1e-16
+    Ke, de, det = orc.elem_thermal(orc.P2T, orc.QTET64, X, k=1.7, f=2.0)
+    assert abs(det - 6 * vol) < 1e-15
+    assert np.abs(de[:4] + 2.0 * vol / 20).max() < 1e-16
+    assert np.abs(de[4:] - 2.0 * vol / 5).max() < 1e-16
+    assert np.abs(Ke - Ke.T).max() < 1e-14
+    assert np.abs(Ke.sum(axis=1)).max() < 1e-14
+    ev = np.linalg.eigvalsh(Ke)
+    assert abs(ev[0]) < 1e-13 and ev[1] > 1e-3 * ev[-1]
+
+
+def _csr(s):
+    n = s["row_ptr"].shape[0] - 1
+    return sp.csr_matrix((s["val"], s["col"], s["row_ptr"]), shape=(n, n))
+
+
+def test_laplacian_invariants_and_harmonic_quadratics(orc):
+    prob = gen.thermal_p2t_problem(3)
+    s = orc.assemble(prob, dirichlet=False)
+    K = _csr(s)
+    scale = np.abs(s["val"]).max()
+    assert np.abs(K @ np.ones(K.shape[0])).max() < 1e-13 * scale
+    assert abs(K - K.T).max() < 1e-14 * scale
+    assert abs(s["d"].sum() - 1.0) < 1e-13
+    prob["coef"] = np.full(prob["conn"].shape[0], 1.3)
+    s = orc.assemble(prob, dirichlet=False)
+    x = prob["coords"]
+    inner = ~gen.boundary_nodes(x)
+    for u in (0.3 + 1.1 * x[:, 0] - 0.7 * x[:, 1] + 0.4 * x[:, 2],
+              x[:, 0] ** 2 + x[:, 1] ** 2 - 2.0 * x[:, 2] ** 2 + 0.5 * x[:, 0] * x[:, 1] - 0.3 * x[:, 1] * x[:, 2]):
+        assert np.abs((_csr(s) @ u)[inner]).max() < 1e-12 * np.abs(s["val"]).max()
+
+
+def test_pattern_matches_brute_force(orc):
+    prob = gen.thermal_p2t_problem(2)
+    s = orc.assemble(prob, dirichlet=False)
+    n = prob["coords"].shape[0]
+    pairs = sorted({(int(a), int(b)) for el in prob["conn"] for a in el for b in el} | {(g, g) for g in range(n)})
+    rows = np.repeat(np.arange(n), np.diff(s["row_ptr"]))
+    assert list(zip(rows.tolist(), s["col"].tolist())) == pairs
+    assert np.diff(s["row_ptr"]).max() == 65
+
+
+def test_mms_third_order(orc):
+    errs = []
+    for n in (2, 4, 8):
+        prob = gen.thermal_p2t_problem(n, jitter=0.1)
+        prob["coef"] = np.ones(prob["conn"].shape[0])
+        c = prob["coords"]
+        u = np.prod(np.sin(np.pi * c), axis=1)
+        s = orc.assemble(prob, fnodal=3 * np.pi ** 2 * u)
+        x, _, rr = orc.pcg(s, tol=1e-13)
+        assert rr <= 1e-12
+        errs.append(np.sqrt(np.mean((x - u) ** 2)))
+    rates = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log(2.0)
+    assert rates.min() >= 2.7, (errs, rates)
