@@ -95,6 +95,11 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate
 # FMAs and 3 multiplies), the trilinear geometry at 27 points (about 150) and
 # the load vector (540 FMAs); the kernel runs most of them in double-float
 Q2S_FLOPS_PER_ELEMENT = 2 * 210 * 27 * 3 + 540 * (2 * 9 + 3) + 27 * 150 + 2 * 540
+# FP64 flops per 10-node tetrahedron (FMA = 2): the contraction of the 6
+# metric entries with the 55 reference tensors, the metric (6 x 3 FMAs), the
+# affine Jacobian, its cofactors, determinant and inverse (about 50), the
+# load (10)
+P2T_FLOPS_PER_ELEMENT = 2 * 6 * 55 + 2 * 6 * 3 + 50 + 10
 # The same for serendipity elasticity: the 210 pairs sum the nine entries of
 # M_ab (27 points x 9 FMAs), each block is finished with lambda, mu (9 entries
 # x 2 FMAs), plus the gradients, geometry and load vector as above
@@ -682,6 +687,33 @@ def suite(dev):
                                 "arithmetic": "map coefficients, load and row sums' conversion FP64; geometry, "
                                               "gradients, the nine Gram sums per pair, the block finishing and the "
                                               "row sums in double-float (FP32 pairs, about 47 bits)"}
+    del P
+    torch.cuda.empty_cache()
+    # quadratic tetrahedra (Kuhn's split of a jittered 48^3 grid), thermal: assembly, then Jacobi-PCG
+    prob = gen.thermal_p2t_problem(48)
+    P = mf.Problem(prob, device=dev)
+    ms = _ev_time(lambda: P.assemble(), reps=5)
+    mf.mf_set_kernel_timing(1)
+    P.assemble()
+    torch.cuda.synchronize()
+    kt = mf.mf_kernel_times()
+    mf.mf_set_kernel_timing(0)
+    ne = int(prob["conn"].shape[0])
+    el_ms = kt["elem_thermal_p2t"][1] / kt["elem_thermal_p2t"][0] if "elem_thermal_p2t" in kt else None
+    ga_ms = kt["gather_scalar"][1] / kt["gather_scalar"][0] if "gather_scalar" in kt else None
+    t0 = time.perf_counter()
+    x, st, info = P.solve(tol=1e-8, max_iter=20000)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    out["H3_thermal_p2t_48"] = {"elements": ne, "n_dofs": int(P.n), "nnz": int(P.nnz), "assemble_ms": ms,
+                                "elements_per_s": ne / (ms * 1e-3), "element_kernel_ms": el_ms,
+                                "gather_kernel_ms": ga_ms,
+                                "element_fp64_tflops": None if el_ms is None
+                                else ne * P2T_FLOPS_PER_ELEMENT / (el_ms * 1e-3) / 1e12,
+                                "fp64_nominal_tflops": FP64_PEAK_TFLOPS,
+                                "jacobi_pcg": {"iterations": int(info.iterations),
+                                               "rel_residual": float(info.rel_residual),
+                                               "converged": bool(info.converged), "s": solve_s}}
     del P
     torch.cuda.empty_cache()
     # loaded boundary: a random stress on five sides of the 64^3 elasticity box (clamped at x = 0)

@@ -50,7 +50,7 @@ typedef enum {
     MF_ERR_UNSUPPORTED = 8   /* combination not provided (e.g. node valence too high) */
 } mf_status;
 
-typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2, MF_Q2S_HEX = 3 } mf_elem;
+typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2, MF_Q2S_HEX = 3, MF_P2_TET = 4 } mf_elem;
 typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2, MF_FORM_CAPACITY = 3 } mf_form;
 typedef enum { MF_PREC_FP64 = 0, MF_PREC_MIXED = 1 } mf_prec;
 typedef enum { MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1 } mf_solver;
@@ -67,7 +67,11 @@ typedef struct mf_pattern mf_pattern;
  * 12 + i + 2k, z edges 16 + i + 2j; edges straight, midpoints at the mean of
  * their ends, so the geometry is the vertices' trilinear map; thermal and
  * elasticity forms (Sec. 4.1, Sec. 4.2), FP64, 3 x 3 x 3 Gauss, up to 128
- * neighbours per node).  Triangles are
+ * neighbours per node), 10 (P2T: the quadratic tetrahedron of the paper's 3D
+ * experiments; vertices 0..3 positively oriented, then the midpoints of
+ * edges (0,1), (1,2), (2,0), (0,3), (1,3), (2,3) at the mean of their ends,
+ * so the geometry is the vertices' affine map; thermal form, FP64, exact
+ * integration, up to 128 neighbours per node).  Triangles are
  * counter-clockwise.  For the flow form, pconn [n_elems][3] gives the P1
  * pressure nodes (the element's vertices in a 0..n_pnodes-1 numbering). */
 typedef struct {

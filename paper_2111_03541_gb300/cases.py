@@ -11,6 +11,7 @@ for profiling (ncu, the kernel-timing hooks) without the whole benchmark.
     python -m paper_2111_03541_gb300.cases genalpha --n 96 --reps 3
     python -m paper_2111_03541_gb300.cases q2s --n 48 --reps 5
     python -m paper_2111_03541_gb300.cases q2s-elastic --n 48 --reps 5
+    python -m paper_2111_03541_gb300.cases p2t --n 48 --reps 5
 
 elastic: Q1 elasticity on an n^3 jittered box (gen.elastic_problem), assembled
 reps times after one untimed call, then pcg-iters Jacobi-PCG iterations.  thermal-grf: Q1 thermal conduction with
@@ -25,7 +26,9 @@ boundary terms added reps times.  traction: the elastic mesh with a random
 stress load (gen.traction_facets) on the five sides away from the clamp.
 q2s: thermal conduction on 20-node serendipity bricks (gen.thermal_q2s_problem),
 assembled reps times.  q2s-elastic: linear elasticity on the same bricks
-(gen.elastic_q2s_problem), assembled reps times.
+(gen.elastic_q2s_problem), assembled reps times.  p2t: thermal conduction on
+quadratic tetrahedra (gen.thermal_p2t_problem: 6 n^3 elements), assembled reps
+times.
 genalpha: the convection case with capacity C = 1, reps generalised-alpha
 steps (rho_inf = 0.5, dt = 1e-3) from T = 0 with the consistent initial rate.
 Inputs are the seeded synthetic ones of `gen`; every step runs in libmf.
@@ -44,7 +47,7 @@ def _times(mf):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("case", choices=("elastic", "thermal-grf", "cnn", "oseen", "batch", "convection", "traction",
-                                           "genalpha", "q2s", "q2s-elastic"))
+                                           "genalpha", "q2s", "q2s-elastic", "p2t"))
     ap.add_argument("--n", type=int, default=48)
     ap.add_argument("--prec", choices=("fp64", "mixed"), default="mixed")
     ap.add_argument("--reps", type=int, default=5)
@@ -70,8 +73,9 @@ def main(argv=None):
             x, st, info = P.solve(tol=1e-12, max_iter=a.pcg_iters, check_every=50)
             torch.cuda.synchronize()
             print("pcg iterations", info.iterations, "residual", info.rel_residual)
-    elif a.case in ("q2s", "q2s-elastic"):
-        P = mf.Problem(gen.thermal_q2s_problem(a.n) if a.case == "q2s" else gen.elastic_q2s_problem(a.n))
+    elif a.case in ("q2s", "q2s-elastic", "p2t"):
+        P = mf.Problem(gen.thermal_q2s_problem(a.n) if a.case == "q2s"
+                       else gen.elastic_q2s_problem(a.n) if a.case == "q2s-elastic" else gen.thermal_p2t_problem(a.n))
         P.assemble()
         torch.cuda.synchronize()
         mf.mf_set_kernel_timing(1)

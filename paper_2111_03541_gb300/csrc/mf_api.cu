@@ -249,7 +249,7 @@ extern "C" mf_status mf_mesh_create(const mf_mesh_desc *desc, void *stream, mf_m
     g_msg[0] = 0;
     if (!desc || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: NULL argument");
     *out = nullptr;
-    if (desc->elem < MF_P1_TRI || desc->elem > MF_Q2S_HEX)
+    if (desc->elem < MF_P1_TRI || desc->elem > MF_P2_TET)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: unknown element %d", desc->elem);
     if (desc->dim != mf_ndim(desc->elem))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: dim %d does not match element", desc->dim);
@@ -366,6 +366,8 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
     if (mesh->elem == MF_Q2S_HEX && ((form != MF_FORM_THERMAL && form != MF_FORM_ELASTIC) || prec != MF_PREC_FP64))
         return mf_fail(MF_ERR_UNSUPPORTED,
                        "mf_assemble: serendipity bricks carry the thermal and elasticity forms in FP64");
+    if (mesh->elem == MF_P2_TET && (form != MF_FORM_THERMAL || prec != MF_PREC_FP64))
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: quadratic tetrahedra carry the thermal form in FP64");
     if (K->n_rows != pattern->n_rows || K->nnz != pattern->nnz || K->row_ptr != pattern->row_ptr ||
         K->col_idx != pattern->col_idx)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: K does not carry the pattern's CSR arrays");
@@ -395,8 +397,8 @@ extern "C" mf_status mf_facets_create(const mf_mesh *mesh, const mf_pattern *pat
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: the pattern was built on another mesh");
     if (pattern->form != MF_FORM_THERMAL && pattern->form != MF_FORM_ELASTIC)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: boundary terms exist for the thermal and elasticity forms");
-    if (mesh->elem == MF_Q2S_HEX)
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: no facet terms on serendipity bricks");
+    if (mesh->elem == MF_Q2S_HEX || mesh->elem == MF_P2_TET)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: no facet terms on serendipity bricks or tetrahedra");
     if (n_facets < 0 || (n_facets > 0 && (!elem || !face)))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: negative count or NULL facet arrays");
     if (n_facets >= (int64_t(1) << 28))

@@ -37,6 +37,47 @@ __global__ void k_elem_thermal_p1(int64_t n_el, const double *__restrict__ X, co
     if (e < n_el) elem_thermal_p1(e, X, conn, kc, f, map, out, status);
 }
 
+// 10-node tetrahedra: one element per thread; its incidence rows go out one
+// row index a at a time through a per-warp stage in shared memory, so that
+// the warp stores whole 96-byte rows (about three per store instruction)
+// instead of 32 scattered words
+__global__ void __launch_bounds__(128) k_elem_thermal_p2t(int64_t n_el, const double *__restrict__ X,
+                                                          const int32_t *__restrict__ conn,
+                                                          const double *__restrict__ kc, double f,
+                                                          const int32_t *__restrict__ map, double *__restrict__ out,
+                                                          int *status)
+{
+    constexpr int RS = mf_th_rs(10);       // 12 words per row
+    __shared__ double stage[4][32][13];    // row of each lane (stride 13: no bank conflicts)
+    __shared__ int32_t rows[4][32][11];    // incidence entries of each lane's element
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float2 G[6];
+    double lv = 0.0, le = 0.0;
+    const bool has = p2t_metric(e, n_el, X, conn, kc, f, G, lv, le, status);
+    if (has)
+#pragma unroll
+        for (int a = 0; a < 10; ++a) rows[w][lane][a] = map[e * 10 + a];
+    // lanes of the warp that hold an element (the last block's tail)
+    const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + 32 * w;
+    const int nl = (int)(n_el - w0 < 32 ? (n_el - w0 > 0 ? n_el - w0 : 0) : 32);
+#pragma unroll 1
+    for (int a = 0; a < 10; ++a) {
+        if (has) {
+#pragma unroll
+            for (int b = 0; b < 10; ++b) stage[w][lane][b] = p2t_entry(G, a, b);
+            stage[w][lane][10] = a < 4 ? lv : le;
+            stage[w][lane][11] = 0.0;
+        }
+        __syncwarp();
+        for (int i = lane; i < nl * RS; i += 32) {
+            const int L = i / RS, j = i - RS * L;
+            out[(int64_t)rows[w][L][a] * RS + j] = stage[w][L][j];
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_elem_thermal_p2(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
                                   const double *__restrict__ kc, double f, const int32_t *__restrict__ map,
                                   double *__restrict__ out, int *status)
@@ -1040,9 +1081,13 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
                       : m->elem == MF_P1_TRI ? "elem_thermal_p1"
                       : m->elem == MF_P2_TRI ? "elem_thermal_p2"
                       : m->elem == MF_Q1_HEX ? "elem_thermal_q1"
+                      : m->elem == MF_P2_TET ? "elem_thermal_p2t"
                                              : "elem_thermal_q2s",
                       st);
-        if (m->elem == MF_Q2S_HEX)
+        if (m->elem == MF_P2_TET)
+            k_elem_thermal_p2t<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
+                                                              p->scratch, status);
+        else if (m->elem == MF_Q2S_HEX)
             k_elem_thermal_q2s<<<nblk(ne, Q2W), Q2W * 32, 0, st>>>(ne, p->q2s_map, c->elem_coef, f, p->elem_inc,
                                                                    p->scratch, status);
         else if (cap)
@@ -1068,6 +1113,7 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         if (m->elem == MF_P1_TRI) MF_GATHER_TH(3);
         else if (m->elem == MF_P2_TRI) MF_GATHER_TH(6);
         else if (m->elem == MF_Q1_HEX) MF_GATHER_TH(8);
+        else if (m->elem == MF_P2_TET) MF_GATHER_TH(10);
         else MF_GATHER_TH(20);
 #undef MF_GATHER_TH
         mf_prof_end(st);

@@ -155,6 +155,14 @@ __device__ __forceinline__ int upair(int a, int b) { return a * (15 - a) / 2 + b
 // B_i[a1][b] = det sum_j (grad l_j)_i c_R[j][a1][b] are the same finite sums
 // as their quadrature, reordered (the integrands have degree 2).
 __constant__ double c_Ms[6][6][6];
+// 10-node tetrahedron (vertices, then edges (0,1), (1,2), (2,0), (0,3),
+// (1,3), (2,3)): c_Mt[u][s] for the pairs u = (a, b), a <= b (row-major) and
+// the entries s = 00, 11, 22, 01, 02, 12 of G = J^-1 J^-T:
+//   c_Mt[u][s] = int_ref d_p N_a d_q N_b (+ d_q N_a d_p N_b for p != q),
+// exact by the 4-point degree-2 rule (the integrand is quadratic), so that
+// K_ab = k detJ sum_s G_s c_Mt[u][s] on the affine element; kept as FP32
+// pairs (hi, lo) for the double-float contraction
+__constant__ float2 c_Mt[55][6];
 __constant__ double c_R[3][3][6];
 
 // 20-node serendipity brick: shape function a and its reference gradient at
@@ -336,6 +344,43 @@ inline mf_status fem_consts_upload()
                 for (int y = 0; y < 6; ++y) R[j][a1][y] += w * l[a1] * dN[y][j];
     }
     MF_CUDA(cudaMemcpyToSymbol(c_Ms, Ms, sizeof Ms));
+    {
+        // 4-point rule on the reference tetrahedron (volume 1/6), degree 2:
+        // barycentric (al, be, be, be) and permutations, weight 1/24 each
+        const double al = (5.0 + 3.0 * sqrt(5.0)) / 20.0, be = (5.0 - sqrt(5.0)) / 20.0;
+        const int ed[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+        const int sp[6] = {0, 1, 2, 0, 0, 1}, sq[6] = {0, 1, 2, 1, 2, 2};
+        double Mt[55][6] = {};
+        for (int q = 0; q < 4; ++q) {
+            double l[4];
+            for (int i = 0; i < 4; ++i) l[i] = i == q ? al : be;
+            double dN[10][4] = {};  // dN_a / dlambda_i
+            for (int v = 0; v < 4; ++v) dN[v][v] = 4.0 * l[v] - 1.0;
+            for (int k = 0; k < 6; ++k) {
+                dN[4 + k][ed[k][0]] = 4.0 * l[ed[k][1]];
+                dN[4 + k][ed[k][1]] = 4.0 * l[ed[k][0]];
+            }
+            double g[10][3];  // reference gradient: lambda_0 = 1 - x - y - z, lambda_{j+1} = x_j
+            for (int a = 0; a < 10; ++a)
+                for (int j = 0; j < 3; ++j) g[a][j] = dN[a][j + 1] - dN[a][0];
+            int u = 0;
+            for (int a = 0; a < 10; ++a)
+                for (int b = a; b < 10; ++b, ++u)
+                    for (int s2 = 0; s2 < 6; ++s2) {
+                        double t = g[a][sp[s2]] * g[b][sq[s2]];
+                        if (sp[s2] != sq[s2]) t += g[a][sq[s2]] * g[b][sp[s2]];
+                        Mt[u][s2] += t / 24.0;
+                    }
+        }
+        float2 Mtf[55][6];
+        for (int u = 0; u < 55; ++u)
+            for (int s2 = 0; s2 < 6; ++s2) {
+                const float hi = (float)Mt[u][s2];
+                Mtf[u][s2] = make_float2(hi, (float)(Mt[u][s2] - (double)hi));
+            }
+        MF_CUDA(cudaMemcpyToSymbol(c_Mt, Mtf, sizeof Mtf));
+
+    }
     MF_CUDA(cudaMemcpyToSymbol(c_R, R, sizeof R));
     static double tab[27][20][4];
     const double g3 = 0.77459666924148337704;  // sqrt(3/5)
@@ -372,7 +417,7 @@ struct ThOut {
 #pragma unroll
         for (int a = 0; a < NPE; ++a) {
             if (map) {
-                base[a] = (int64_t)map[e * NPE + a] * (NPE + 1);
+                base[a] = (int64_t)map[e * NPE + a] * mf_th_rs(NPE);
                 ld[a] = base[a] + NPE;
             } else {
                 base[a] = e * (NPE * NPE + NPE) + a * NPE;
@@ -437,6 +482,68 @@ __device__ __forceinline__ void elem_thermal_p2(int64_t e, const double *__restr
     const double le = f * det * (1.0 / 6.0);
 #pragma unroll
     for (int a = 0; a < 6; ++a) out[W.ld[a]] = a < 3 ? 0.0 : le;
+}
+
+// 10-node tetrahedron, thermal form: the affine map of the vertices, then
+// K_e = k detJ sum_s G_s c_Mt[s] (G = J^-1 J^-T, exact; the contraction in
+// double-float); the load of a vertex node integrates to -f detJ / 120, of an
+// edge node to f detJ / 30 (the moments -V/20 and V/5 of the quadratic
+// simplex, V = detJ / 6).  One thread per element; returns the metric as
+// FP32 pairs and the two load values (vertex, edge); false for a lane
+// without an element.
+__device__ __forceinline__ bool p2t_metric(int64_t e, int64_t n_el, const double *__restrict__ X,
+                                           const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                           double f, float2 (&G)[6], double &lv, double &le, int *status)
+{
+    if (e >= n_el) return false;
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    const int32_t *c = conn + 10 * e;
+    double J[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) J[i][j] = X[3 * (int64_t)c[j + 1] + i] - X[3 * (int64_t)c[0] + i];
+    // inverse by cofactors (as q1_jac_at): Ji[p][i] = d xi_p / d x_i
+    double Ji[3][3];
+    Ji[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    Ji[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    Ji[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * Ji[0][0] + J[0][1] * Ji[1][0] + J[0][2] * Ji[2][0];
+    const double r = 1.0 / det;
+    Ji[0][0] *= r;
+    Ji[1][0] *= r;
+    Ji[2][0] *= r;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+    const int sp[6] = {0, 1, 2, 0, 0, 1}, sq[6] = {0, 1, 2, 1, 2, 2};
+    const double kd = k * det;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const double g =
+            kd * fma(Ji[sp[s]][0], Ji[sq[s]][0], fma(Ji[sp[s]][1], Ji[sq[s]][1], Ji[sp[s]][2] * Ji[sq[s]][2]));
+        const float hi = __double2float_rn(g);
+        G[s] = make_float2(hi, __double2float_rn(g - (double)hi));
+    }
+    lv = -f * det * (1.0 / 120.0);
+    le = f * det * (1.0 / 30.0);
+    return true;
+}
+
+// K_ab of the tetrahedron from its metric: pair u = (min, max) of the upper
+// triangle (row-major), so that K_ab and K_ba are the same bits
+__device__ __forceinline__ double p2t_entry(const float2 (&G)[6], int a, int b)
+{
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    const int u = lo * (19 - lo) / 2 + hi;
+    float2 v = df_mul(G[0], c_Mt[u][0]);
+#pragma unroll
+    for (int s = 1; s < 6; ++s) v = df_add(v, df_mul(G[s], c_Mt[u][s]));
+    return df_to_double(v);
 }
 
 __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restrict__ X,
@@ -645,7 +752,7 @@ __device__ __forceinline__ bool q1_translate(int64_t e, const uint8_t *__restric
 // Lanes per node of the thermal gather: 4 for P1, 8 for P2 and Q1, a warp for
 // the 20-node brick.
 template <int NPE>
-constexpr int th_lanes() { return NPE <= 4 ? 4 : (NPE <= 8 ? 8 : 32); }
+constexpr int th_lanes() { return NPE <= 4 ? 4 : (NPE <= 8 ? 8 : (NPE <= 16 ? 16 : 32)); }
 
 // Thermal row of node n by a group of th_lanes<NPE>() lanes (`sub` = lane in
 // the group, `gmask` = the group's lanes; groups of a warp are independent).
@@ -676,7 +783,7 @@ __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask
     constexpr int L = th_lanes<NPE>();
     constexpr int U = 4;   // rows whose loads are in flight together
     constexpr int KM = 4;  // prefetched columns per lane (the rest: plain loop)
-    constexpr int RS = NPE + 1;
+    constexpr int RS = mf_th_rs(NPE);
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
     const int64_t i0 = inc_ptr[n], i1 = inc_ptr[n + 1];

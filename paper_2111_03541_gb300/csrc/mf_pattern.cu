@@ -30,7 +30,7 @@ __global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_el) return;
-    const int npe = elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : (elem == MF_Q1_HEX ? 8 : 20));
+    const int npe = elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : (elem == MF_Q1_HEX ? 8 : (elem == MF_Q2S_HEX ? 20 : 10)));
     for (int a = 0; a < npe; ++a) {
         const int32_t v = conn[e * npe + a];
         if (v < 0 || v >= n_nodes) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
@@ -46,6 +46,18 @@ __global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double
         const double x1 = X[2 * c[1]], y1 = X[2 * c[1] + 1];
         const double x2 = X[2 * c[2]], y2 = X[2 * c[2] + 1];
         const double det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+        if (!isfinite(det)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
+        if (!(det > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
+        return;
+    }
+    if (elem == MF_P2_TET) {  // the affine map of the 4 vertices
+        const int32_t *c = conn + e * npe;
+        double J[3][3];
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i) J[i][j] = X[3 * (int64_t)c[j + 1] + i] - X[3 * (int64_t)c[0] + i];
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) +
+                           J[0][1] * (J[1][2] * J[2][0] - J[1][0] * J[2][2]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
         if (!isfinite(det)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
         if (!(det > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
         return;
@@ -641,9 +653,9 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         MF_CUDA(cudaMallocAsync(&p->inc_slot, (size_t)npe * npe * m->n_elems, st));
         k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, m->conn, incv.ptr, incv.inc, p->adj[0].ptr,
                                                      p->adj[0].col, p->inc_slot);
-        p->scratch_stride = (int64_t)npe * npe + npe;
-        if (m->elem == MF_P2_TRI || m->elem == MF_Q2S_HEX) {
-            // reference sums of the P2 stiffness, reference table of the 20-node brick
+        p->scratch_stride = (int64_t)npe * mf_th_rs(npe);
+        if (m->elem == MF_P2_TRI || m->elem == MF_Q2S_HEX || m->elem == MF_P2_TET) {
+            // reference sums of the P2 stiffnesses, reference table of the 20-node brick
             s = mf_flow_consts_upload();
             if (s != MF_OK) { free_inc(incv, st); return s; }
         }
