@@ -95,10 +95,11 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate
 # FMAs and 3 multiplies), the trilinear geometry at 27 points (about 150) and
 # the load vector (540 FMAs); the kernel runs most of them in double-float
 Q2S_FLOPS_PER_ELEMENT = 2 * 210 * 27 * 3 + 540 * (2 * 9 + 3) + 27 * 150 + 2 * 540
-# FP64 flops per 10-node tetrahedron (FMA = 2): the contraction of the 6
-# metric entries with the 55 reference tensors, the metric (6 x 3 FMAs), the
+# Algorithmic flops per 10-node tetrahedron (FMA = 2): the contraction of the
+# 6 metric entries with the 55 reference tensors, the metric (6 x 3 FMAs), the
 # affine Jacobian, its cofactors, determinant and inverse (about 50), the
-# load (10)
+# load (10); the kernel forms the metric in FP64 and runs the contraction in
+# double-float, once per row entry (100 a element)
 P2T_FLOPS_PER_ELEMENT = 2 * 6 * 55 + 2 * 6 * 3 + 50 + 10
 # The same for serendipity elasticity: the 210 pairs sum the nine entries of
 # M_ab (27 points x 9 FMAs), each block is finished with lambda, mu (9 entries
@@ -708,9 +709,11 @@ def suite(dev):
     out["H3_thermal_p2t_48"] = {"elements": ne, "n_dofs": int(P.n), "nnz": int(P.nnz), "assemble_ms": ms,
                                 "elements_per_s": ne / (ms * 1e-3), "element_kernel_ms": el_ms,
                                 "gather_kernel_ms": ga_ms,
-                                "element_fp64_tflops": None if el_ms is None
+                                "element_algorithmic_tflops": None if el_ms is None
                                 else ne * P2T_FLOPS_PER_ELEMENT / (el_ms * 1e-3) / 1e12,
-                                "fp64_nominal_tflops": FP64_PEAK_TFLOPS,
+                                "arithmetic": "geometry and metric FP64; the reference-tensor contraction in "
+                                              "double-float (FP32 pairs), one exact conversion per entry",
+                                "element_output_bytes": ne * 10 * 12 * 8,
                                 "jacobi_pcg": {"iterations": int(info.iterations),
                                                "rel_residual": float(info.rel_residual),
                                                "converged": bool(info.converged), "s": solve_s}}
