@@ -363,13 +363,27 @@ def box_facets(mesh: dict, sides=SIDES) -> tuple[np.ndarray, np.ndarray]:
     """Facets of the structured mesh on the given sides of the box.
 
     Returns (element int32 [nf], face uint8 [nf]) side by side in the order
-    given, ascending element ids within a side.  Triangle grid: square (i, j)
+    given, ascending element ids within a side (tetrahedra: the faces whose
+    vertices lie on the side, face i opposite vertex i).  Triangle grid: square (i, j)
     holds elements 2 (j n + i) (v00, v10, v11) and 2 (j n + i) + 1 (v00, v11,
     v01); hexahedron (i, j, k) is element (k n + j) n + i.
     """
     n = mesh["n"]
     els, faces = [], []
     r = np.arange(n)
+    if mesh["elem"] == "P2T":
+        # tetrahedron face i (opposite vertex i) lies on a side when its three
+        # vertices do (boundary nodes are not jittered)
+        X, c = mesh["coords"], mesh["conn"][:, :4]
+        fv = ((1, 2, 3), (0, 3, 2), (0, 1, 3), (0, 2, 1))
+        for side in sides:
+            axis, hi = "xyz".index(side[0]), side[1] == "1"
+            on = np.abs(X[:, axis] - (1.0 if hi else 0.0)) <= 1e-14
+            hit = np.stack([on[c[:, a]] & on[c[:, b]] & on[c[:, d]] for a, b, d in fv], axis=1)
+            e, f = np.nonzero(hit)
+            els.append(e.astype(np.int32))
+            faces.append(f.astype(np.uint8))
+        return np.concatenate(els), np.concatenate(faces)
     for side in sides:
         axis, hi = "xyz".index(side[0]), side[1] == "1"
         if mesh["elem"] == "Q1":

@@ -180,7 +180,7 @@ def elem_capacity(elem: int, X, C: float):
 
 def facet_nodes(elem: int, face: int) -> list[int]:
     """Local element nodes of a facet, in facet node order."""
-    loc = np.zeros(4, dtype=np.int32)
+    loc = np.zeros(6, dtype=np.int32)
     nf = lib().or_facet_nodes(elem, face, _p(loc))
     if nf < 0:
         raise ValueError("no such face")

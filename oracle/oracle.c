@@ -477,12 +477,26 @@ double or_elem_oseen(const double *X, const double *aN, double mu, double rho,
 /*    other two reference coordinates in increasing axis order, so facet     */
 /*    node m sits at (u, v) = (2(m & 1) - 1, 2(m >> 1) - 1) and the face map */
 /*    is the bilinear x(u, v) = sum_m N_m(u, v) x_m.                         */
+/*  - tetrahedron face i (P2T) is opposite vertex i: 3 vertices, then the    */
+/*    midpoints of its edges, the facet basis the P2 triangle's (or_shape    */
+/*    OR_P2) on the reference triangle (xi, eta), the map affine.            */
 /* Quadrature: Gauss-Legendre on the edge with 2 (P1) or 3 (P2) points,     */
-/* exact for N_a N_b on a straight edge; 2 x 2 Gauss on a hexahedron face.   */
+/* exact for N_a N_b on a straight edge; 2 x 2 Gauss on a hexahedron face;   */
+/* the 6-point degree-4 triangle rule on a tetrahedron face (exact for      */
+/* N_a N_b on the flat face).                                               */
 /* ------------------------------------------------------------------------ */
 int or_facet_nodes(int elem, int face, int *loc)
 {
-    if (elem == OR_Q2S || elem == OR_P2T) return -1; /* no facet terms on these elements */
+    if (elem == OR_Q2S) return -1; /* no facet terms on serendipity bricks */
+    if (elem == OR_P2T) {
+        /* face i is opposite vertex i: its vertices in the order that makes
+         * (x1 - x0) x (x2 - x0) point outward for a positively oriented
+         * tetrahedron, then the midpoints of its edges (0,1), (1,2), (2,0) */
+        static const int fl[4][6] = {{1, 2, 3, 5, 9, 8}, {0, 3, 2, 7, 9, 6}, {0, 1, 3, 4, 8, 7}, {0, 2, 1, 6, 5, 4}};
+        if (face < 0 || face > 3) return -1;
+        for (int m = 0; m < 6; ++m) loc[m] = fl[face][m];
+        return 6;
+    }
     if (elem == OR_Q1) {
         if (face < 0 || face > 5) return -1;
         const int d = face / 2, s = face % 2;
@@ -505,6 +519,7 @@ int or_facet_nodes(int elem, int face, int *loc)
  * [-1, 1]^2 (hexahedron faces). */
 static int facet_quad(int elem, double *pts, double *w)
 {
+    if (elem == OR_P2T) return or_quad(OR_QTRI6, pts, w);
     if (elem == OR_P1) {
         const double g = 0.5 / sqrt(3.0);
         pts[0] = 0.5 - g; pts[1] = 0.5 + g;
@@ -549,6 +564,19 @@ static int facet_point(int elem, const double *Xf, const double *p, double *N, d
         A[0] = sqrt(ex * ex + ey * ey);
         return nf;
     }
+    if (elem == OR_P2T) {
+        double dN[12];
+        or_shape(OR_P2, p, N, dN);
+        double e1[3], e2[3];
+        for (int i = 0; i < 3; ++i) {
+            e1[i] = Xf[3 + i] - Xf[i];
+            e2[i] = Xf[6 + i] - Xf[i];
+        }
+        A[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        A[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        A[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        return 6;
+    }
     const double u = p[0], v = p[1];
     double xu[3] = {0.0, 0.0, 0.0}, xv[3] = {0.0, 0.0, 0.0};
     for (int m = 0; m < 4; ++m) {
@@ -572,16 +600,16 @@ static int facet_point(int elem, const double *Xf, const double *p, double *N, d
  * coordinates in facet node order.  Returns the facet's measure sum_q w |J|. */
 double or_facet_thermal(int elem, const double *Xf, double h, double tenv, double *Kf, double *df)
 {
-    double pts[8], w[4], N[4], A[3];
+    double pts[12], w[6], N[6], A[3];
     const int nq = facet_quad(elem, pts, w);
-    const int pdim = elem == OR_Q1 ? 2 : 1;
-    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : 4);
+    const int pdim = (elem == OR_Q1 || elem == OR_P2T) ? 2 : 1;
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : (elem == OR_Q1 ? 4 : 6));
     for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
     for (int a = 0; a < nf; ++a) df[a] = 0.0;
     double meas = 0.0;
     for (int q = 0; q < nq; ++q) {
         facet_point(elem, Xf, pts + pdim * q, N, A);
-        const double J = elem == OR_Q1 ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
+        const double J = (elem == OR_Q1 || elem == OR_P2T) ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
         meas += w[q] * J;
         for (int a = 0; a < nf; ++a) {
             for (int b = 0; b < nf; ++b) Kf[a * nf + b] += w[q] * J * h * N[a] * N[b];
@@ -601,7 +629,7 @@ double or_facet_thermal(int elem, const double *Xf, double h, double tenv, doubl
  * row-major 3 x 3. */
 void or_facet_traction_q1(int face, const double *Xf, const double *sigma, double *df)
 {
-    double pts[8], w[4], N[4], A[3];
+    double pts[12], w[6], N[6], A[3];
     const int nq = facet_quad(OR_Q1, pts, w);
     const int d = face / 2, s = face % 2;
     const double o = (s ? 1.0 : -1.0) * (d == 1 ? -1.0 : 1.0);
@@ -625,16 +653,16 @@ void or_facet_traction_q1(int face, const double *Xf, const double *sigma, doubl
 void or_facet_radiation(int elem, const double *Xf, double es, double tenv, const double *Tf, double *Kf,
                         double *rf)
 {
-    double pts[8], w[4], N[4], A[3];
+    double pts[12], w[6], N[6], A[3];
     const int nq = facet_quad(elem, pts, w);
-    const int pdim = elem == OR_Q1 ? 2 : 1;
-    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : 4);
+    const int pdim = (elem == OR_Q1 || elem == OR_P2T) ? 2 : 1;
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : (elem == OR_Q1 ? 4 : 6));
     for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
     for (int a = 0; a < nf; ++a) rf[a] = 0.0;
     const double te4 = tenv * tenv * tenv * tenv;
     for (int q = 0; q < nq; ++q) {
         facet_point(elem, Xf, pts + pdim * q, N, A);
-        const double J = elem == OR_Q1 ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
+        const double J = (elem == OR_Q1 || elem == OR_P2T) ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
         double T = 0.0;
         for (int b = 0; b < nf; ++b) T += N[b] * Tf[b];
         for (int a = 0; a < nf; ++a) {
@@ -817,12 +845,12 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
     }
     for (int64_t f = 0; f < p->n_facets; ++f) {
         const int64_t e = p->f_elem[f];
-        int loc[4];
+        int loc[6];
         if (e < 0 || e >= p->n_el) return -3;
         const int nf = or_facet_nodes(p->elem, p->f_face[f], loc);
         if (nf < 0 || p->form == OR_OSEEN || p->form == OR_CAPACITY) return -3;
-        int64_t node[4];
-        double Xf[12], Kf[16], df[12];
+        int64_t node[6];
+        double Xf[18], Kf[36], df[18];
         int hit = keep == NULL;
         for (int m = 0; m < nf; ++m) {
             node[m] = p->conn[e * npe + loc[m]];
@@ -1201,10 +1229,10 @@ static void radiation_terms(const or_radiation *rd, const int64_t *rp, const int
                             double *Fe, double *Tv, double scale)
 {
     for (int64_t f = 0; f < rd->n_facets; ++f) {
-        int loc[4];
+        int loc[6];
         const int nf = or_facet_nodes(rd->elem, rd->f_face[f], loc);
-        int64_t node[4];
-        double Xf[12], Tf[4], Kf[16], rf[4];
+        int64_t node[6];
+        double Xf[18], Tf[6], Kf[36], rf[6];
         for (int m = 0; m < nf; ++m) {
             node[m] = rd->conn[(int64_t)rd->f_elem[f] * rd->npe + loc[m]];
             Tf[m] = T[node[m]];

@@ -124,3 +124,59 @@ def test_mms_third_order(orc):
         errs.append(np.sqrt(np.mean((x - u) ** 2)))
     rates = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log(2.0)
     assert rates.min() >= 2.7, (errs, rates)
+
+
+# ---------------------------------------------------------------------------
+# convection on the 6-node faces (Sec. 4.1, h(T, T_env - T) on the surface of
+# the 3D thermal case)
+# ---------------------------------------------------------------------------
+
+# P2 triangle mass matrix times 180 / area (vertices, then the midpoints of
+# edges (0,1), (1,2), (2,0)): the closed form of int N_a N_b
+P2_MASS = np.array([[6, -1, -1, 0, -4, 0], [-1, 6, -1, 0, 0, -4], [-1, -1, 6, -4, 0, 0],
+                    [0, 0, -4, 32, 16, 16], [-4, 0, 0, 16, 32, 16], [0, -4, 0, 16, 16, 32]], float)
+
+
+def test_face_tables_orientation_and_midpoints(orc):
+    V, X = _tet(seed=7)
+    for face in range(4):
+        loc = orc.facet_nodes(orc.P2T, face)
+        assert len(loc) == 6 and face not in loc[:3]
+        Xf = X[loc]
+        n = np.cross(Xf[1] - Xf[0], Xf[2] - Xf[0])
+        assert n @ (Xf[0] - V[face]) > 0  # outward: away from the opposite vertex
+        for m, (p, q) in enumerate(((0, 1), (1, 2), (2, 0))):
+            assert np.abs(Xf[3 + m] - 0.5 * (Xf[p] + Xf[q])).max() < 1e-15
+
+
+def test_face_convection_closed_form(orc):
+    _, X = _tet(seed=8)
+    loc = orc.facet_nodes(orc.P2T, 2)
+    Xf = X[loc]
+    area = 0.5 * np.linalg.norm(np.cross(Xf[1] - Xf[0], Xf[2] - Xf[0]))
+    Kf, df, meas = orc.facet_thermal(orc.P2T, Xf, h=1.7, t_env=0.6)
+    assert abs(meas - area) < 1e-16
+    assert np.abs(Kf - 1.7 * area / 180.0 * P2_MASS).max() < 1e-15
+    assert np.abs(df - 1.7 * 0.6 * area * np.array([0, 0, 0, 1, 1, 1]) / 3.0).max() < 1e-15
+    # radiation at a uniform temperature: load es (T_env^4 - T^4) int N_m,
+    # tangent 4 es T^3 times the mass matrix
+    Kr, rr = orc.facet_radiation(orc.P2T, Xf, 0.8, 1.3, np.full(6, 1.1))
+    assert np.abs(rr - 0.8 * (1.3 ** 4 - 1.1 ** 4) * area * np.array([0, 0, 0, 1, 1, 1]) / 3.0).max() < 1e-14
+    assert np.abs(Kr - 4 * 0.8 * 1.1 ** 3 * area / 180.0 * P2_MASS).max() < 1e-14
+
+
+def test_assembled_convection_on_the_surface(orc):
+    prob = gen.thermal_p2t_problem(3)
+    base = orc.assemble(prob, dirichlet=False)
+    fac = gen.convection_facets(prob, gen.SIDES)
+    fac["h"] = np.full(fac["elem"].shape[0], 2.5)
+    fac["t_env"] = np.full(fac["elem"].shape[0], 0.7)
+    prob["facets"] = fac
+    s = orc.assemble(prob, dirichlet=False)
+    Kc = _csr(s) - _csr(base)
+    one = np.ones(Kc.shape[0])
+    assert abs(one @ Kc @ one - 2.5 * 6.0) < 1e-12          # h times the cube's surface
+    assert abs((s["d"] - base["d"]).sum() - 2.5 * 0.7 * 6.0) < 1e-12
+    x = prob["coords"]
+    assert abs(x[:, 0] @ Kc @ one - 2.5 * 3.0) < 1e-12       # int x over the surface = 3
+    assert abs(Kc - Kc.T).max() < 1e-15
