@@ -191,8 +191,15 @@ mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *patte
  *    2s - 1; its nodes are the element nodes a with bit d of a equal to s,
  *    ascending, and its map is bilinear in the other two reference
  *    coordinates.  n is the outward unit normal.
+ *  - tetrahedron (P2T) face i is the face opposite vertex i; its nodes are
+ *    the three vertices in outward order (1,2,3), (0,3,2), (0,1,3), (0,2,1)
+ *    for i = 0..3, then the midpoints of its edges (0,1), (1,2), (2,0) in
+ *    face order; the face is flat.  Thermal (convection) only.
  * Quadrature: Gauss-Legendre with 2 (P1) or 3 (P2) points per edge, exact for
- * the edge mass matrix; 2 x 2 Gauss on a hexahedron face. */
+ * the edge mass matrix; 2 x 2 Gauss on a hexahedron face; on a tetrahedron
+ * face the exact P2 triangle mass matrix and load.  Serendipity bricks have
+ * no facet terms (MF_ERR_UNSUPPORTED); radiation (mf_genalpha_run) is not
+ * provided on tetrahedron faces (MF_ERR_UNSUPPORTED). */
 typedef struct mf_facets mf_facets;
 
 /* Wraps n_facets facets (elem [n_facets] int32 parent elements, face

@@ -397,8 +397,8 @@ extern "C" mf_status mf_facets_create(const mf_mesh *mesh, const mf_pattern *pat
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: the pattern was built on another mesh");
     if (pattern->form != MF_FORM_THERMAL && pattern->form != MF_FORM_ELASTIC)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: boundary terms exist for the thermal and elasticity forms");
-    if (mesh->elem == MF_Q2S_HEX || mesh->elem == MF_P2_TET)
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: no facet terms on serendipity bricks or tetrahedra");
+    if (mesh->elem == MF_Q2S_HEX)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: no facet terms on serendipity bricks");
     if (n_facets < 0 || (n_facets > 0 && (!elem || !face)))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: negative count or NULL facet arrays");
     if (n_facets >= (int64_t(1) << 28))
@@ -466,6 +466,8 @@ extern "C" mf_status mf_genalpha_run(const mf_csr *K, const double *M_values, co
     if (rad && (rad->pattern->row_ptr != K->row_ptr || rad->pattern->form != MF_FORM_THERMAL ||
                 (rad->n_facets > 0 && (!rad_es || !rad_tenv))))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_run: radiation facets need K's thermal pattern, es, t_env");
+    if (rad && rad->n_facets > 0 && rad->mesh->elem == MF_P2_TET)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_genalpha_run: no radiation on tetrahedron faces");
     if (!(dt > 0.0) || steps < 0 || !(prm->b1 != 0.0) || !(prm->b2 != 0.0) || !(newton_tol > 0.0) ||
         max_newton < 1 || !(pcg_tol > 0.0) || pcg_max_iter < 1)
         return mf_fail(MF_ERR_INVALID_ARG,
@@ -486,6 +488,8 @@ extern "C" mf_status mf_genalpha_initial_rate(const mf_csr *K, const double *M_v
     if (rad && (rad->pattern->row_ptr != K->row_ptr || rad->pattern->form != MF_FORM_THERMAL ||
                 (rad->n_facets > 0 && (!rad_es || !rad_tenv))))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_initial_rate: radiation facets need K's thermal pattern");
+    if (rad && rad->n_facets > 0 && rad->mesh->elem == MF_P2_TET)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_genalpha_initial_rate: no radiation on tetrahedron faces");
     if (!(pcg_tol > 0.0) || pcg_max_iter < 1)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_genalpha_initial_rate: pcg_tol > 0 and pcg_max_iter >= 1");
     return mf_genalpha_initial_rate_impl(K, M_values, F, bc_mask, rad, rad_es, rad_tenv, phi, u, pcg_tol,

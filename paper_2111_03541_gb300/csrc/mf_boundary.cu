@@ -44,8 +44,16 @@ inline unsigned nblk(int64_t n, int t = TPB) { return (unsigned)((n + t - 1) / t
 
 // Local element nodes of facet `face`; returns the node count or 0 for a face
 // the element does not have.
-__device__ __forceinline__ int facet_local(int elem, int face, int (&loc)[4])
+__device__ __forceinline__ int facet_local(int elem, int face, int (&loc)[6])
 {
+    if (elem == MF_P2_TET) {
+        // face i opposite vertex i, vertices ordered outward, then the
+        // midpoints of its edges (0,1), (1,2), (2,0)
+        if (face < 0 || face > 3) return 0;
+        const int fl[4][6] = {{1, 2, 3, 5, 9, 8}, {0, 3, 2, 7, 9, 6}, {0, 1, 3, 4, 8, 7}, {0, 2, 1, 6, 5, 4}};
+        for (int m = 0; m < 6; ++m) loc[m] = fl[face][m];
+        return 6;
+    }
     if (elem == MF_Q1_HEX) {
         if (face < 0 || face > 5) return 0;
         const int d = face >> 1, s = face & 1;
@@ -72,7 +80,7 @@ __global__ void k_facet_nodes(int elem, int npe, int npf, int64_t n_el, const in
     if (f >= n_facets) return;
     const int64_t e = f_elem[f];
     const int face = f_face[f];
-    int loc[4];
+    int loc[6];
     if (e < 0 || e >= n_el || facet_local(elem, face, loc) != npf) {
         mf_dev_fail(status, MF_ERR_BAD_MESH);
         for (int m = 0; m < npf; ++m) fnode[f * npf + m] = -1;
@@ -103,7 +111,7 @@ __global__ void k_compact_nodes(int64_t n, const int64_t *__restrict__ cnt, cons
     bcnt[pos[i]] = cnt[i];
 }
 
-// incidence entries (facet * 4 + local index) in arrival order
+// incidence entries (facet * 8 + local index) in arrival order
 __global__ void k_facet_fill(int64_t n_entries, int npf, const int32_t *__restrict__ fnode,
                              const int64_t *__restrict__ pos, const int64_t *__restrict__ bptr,
                              int64_t *__restrict__ cursor, int64_t *__restrict__ key)
@@ -112,7 +120,7 @@ __global__ void k_facet_fill(int64_t n_entries, int npf, const int32_t *__restri
     if (t >= n_entries) return;
     const int64_t b = pos[fnode[t]];
     const int64_t at = bptr[b] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[b]), 1ull);
-    key[at] = (t / npf) * 4 + (t % npf);
+    key[at] = (t / npf) * 8 + (t % npf);
 }
 
 // sorts every node's entries by facet (then local index) and splits the keys;
@@ -137,9 +145,9 @@ __global__ void k_facet_sort_slots(int64_t n_bnodes, int npf, const int64_t *__r
     const int32_t r = bnode[b];
     if (brow) brow[b] = row_ptr[r];
     for (int64_t t = lo; t < hi; ++t) {
-        const int64_t f = key[t] >> 2;
+        const int64_t f = key[t] >> 3;
         binc[t] = (int32_t)f;
-        bloc[t] = (uint8_t)(key[t] & 3);
+        bloc[t] = (uint8_t)(key[t] & 7);
         if (!bslot) continue;
         const int64_t r0 = row_ptr[r], r1 = row_ptr[r + 1];
         for (int m = 0; m < npf; ++m) {
@@ -202,8 +210,33 @@ __device__ __forceinline__ void face_coefs(const double *__restrict__ X, const i
 // Row m of the facet's convection matrix for unit h (row[m']) and the facet
 // load factor for unit h T_env (returned).
 template <int ELEM>
-__device__ __forceinline__ double conv_row(const double *__restrict__ X, const int32_t *fn, int m, double (&row)[4])
+constexpr int facet_npf() { return ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : (ELEM == MF_Q1_HEX ? 4 : 6)); }
+
+template <int ELEM>
+__device__ __forceinline__ double conv_row(const double *__restrict__ X, const int32_t *fn, int m, double (&row)[6])
 {
+    if (ELEM == MF_P2_TET) {
+        // flat 6-node face of area A: int N_m N_k = A / 180 [6 -1 -1 0 -4 0; ...]
+        // (the P2 triangle's closed form), int N_m = 0 (vertex), A / 3 (edge)
+        double e1[3], e2[3], c[3];
+        for (int i = 0; i < 3; ++i) {
+            e1[i] = X[3 * (int64_t)fn[1] + i] - X[3 * (int64_t)fn[0] + i];
+            e2[i] = X[3 * (int64_t)fn[2] + i] - X[3 * (int64_t)fn[0] + i];
+        }
+        cross3(e1, e2, c);
+        const double A = 0.5 * sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        const double s = A / 180.0;
+        if (m < 3) {
+            for (int k = 0; k < 3; ++k) row[k] = s * (k == m ? 6.0 : -1.0);
+            for (int k = 3; k < 6; ++k) row[k] = 0.0;
+            row[3 + (m + 1) % 3] = -4.0 * s;  // the edge opposite vertex m
+            return 0.0;
+        }
+        for (int k = 0; k < 3; ++k) row[k] = 0.0;
+        row[(m - 3 + 2) % 3] = -4.0 * s;  // the vertex opposite edge m - 3
+        for (int k = 3; k < 6; ++k) row[k] = s * (k == m ? 32.0 : 16.0);
+        return A / 3.0;
+    }
     if (ELEM == MF_P1_TRI || ELEM == MF_P2_TRI) {
         const double ex = X[2 * (int64_t)fn[1]] - X[2 * (int64_t)fn[0]];
         const double ey = X[2 * (int64_t)fn[1] + 1] - X[2 * (int64_t)fn[0] + 1];
@@ -315,7 +348,7 @@ __global__ void k_facet_geometry(int64_t n_entries, const int32_t *__restrict__ 
                                  const uint8_t *__restrict__ fface, const double *__restrict__ X, bool traction,
                                  double *__restrict__ bgeo, int32_t *__restrict__ bcol, double *__restrict__ bwq)
 {
-    constexpr int NPF = ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : 4);
+    constexpr int NPF = facet_npf<ELEM>();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_entries) return;
     const int32_t f = binc[t];
@@ -334,13 +367,14 @@ __global__ void k_facet_geometry(int64_t n_entries, const int32_t *__restrict__ 
         for (int i = 0; i < 3; ++i) bgeo[3 * t + i] = o * (P[i] + Qu[i] * su + Qv[i] * sv);
         return;
     }
-    double row[4];
+    double row[6];
     const double lf = conv_row<ELEM>(X, fn, m, row);
     for (int k = 0; k < NPF; ++k) {
         bgeo[t * (NPF + 1) + k] = row[k];
         bcol[t * NPF + k] = fn[k];
     }
     bgeo[t * (NPF + 1) + NPF] = lf;
+    if (ELEM == MF_P2_TET) return;  // no radiation terms on tetrahedron faces
     // per point: w |J| N_m, for the temperature-dependent (radiation) terms
     constexpr int NQ = facet_nq<ELEM>();
     double wj[4];
@@ -530,6 +564,8 @@ mf_status mf_radiation_load(const mf_facets *f, const double *es, const double *
                             const uint8_t *mask, double *R, cudaStream_t st)
 {
     if (!f || f->n_bnodes == 0) return MF_OK;
+    if (f->mesh->elem == MF_P2_TET)
+        return mf_fail(MF_ERR_UNSUPPORTED, "radiation: not provided on tetrahedron faces");
     int *status = mf_status_word();
     if (!status) return mf_fail(MF_ERR_CUDA, "radiation: status word unavailable");
     const unsigned g = nblk(f->n_bnodes, BND_T);
@@ -545,6 +581,8 @@ mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const doubl
                                double scale, double *values, cudaStream_t st)
 {
     if (!f || f->n_bnodes == 0) return MF_OK;
+    if (f->mesh->elem == MF_P2_TET)
+        return mf_fail(MF_ERR_UNSUPPORTED, "radiation: not provided on tetrahedron faces");
     const unsigned g = nblk(f->n_bnodes, BND_T);
 #define RT_ARGS f->n_bnodes, f->bnode, f->brow, f->bptr, f->binc, f->bslot, f->bcol, f->bwq, f->fnode, es, T, mask, \
                 scale, values
@@ -558,7 +596,7 @@ mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const doubl
 mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n_facets, const int32_t *elem,
                                 const uint8_t *face, cudaStream_t st, mf_facets *f)
 {
-    f->npf = m->elem == MF_P1_TRI ? 2 : (m->elem == MF_P2_TRI ? 3 : 4);
+    f->npf = m->elem == MF_P1_TRI ? 2 : (m->elem == MF_P2_TRI ? 3 : (m->elem == MF_Q1_HEX ? 4 : 6));
     f->n_facets = n_facets;
     if (n_facets == 0) return MF_OK;
     if (p->form == MF_FORM_ELASTIC && m->elem != MF_Q1_HEX)
@@ -624,7 +662,8 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
         FC(cudaMallocAsync(&f->bcol, sizeof(int32_t) * ne * npf, st));
         FC(cudaMallocAsync(&f->brow, sizeof(int64_t) * nb, st));
         FC(cudaMallocAsync(&f->bgeo, sizeof(double) * ne * (npf + 1), st));
-        FC(cudaMallocAsync(&f->bwq, sizeof(double) * ne * (npf == 3 ? 3 : (npf == 2 ? 2 : 4)), st));
+        if (npf <= 4)  // radiation point weights (none on tetrahedron faces)
+            FC(cudaMallocAsync(&f->bwq, sizeof(double) * ne * (npf == 3 ? 3 : (npf == 2 ? 2 : 4)), st));
     } else {
         FC(cudaMallocAsync(&f->bgeo, sizeof(double) * ne * 3, st));
     }
@@ -646,6 +685,9 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
                                                               false, f->bgeo, f->bcol, f->bwq);
     else if (m->elem == MF_P2_TRI)
         k_facet_geometry<MF_P2_TRI><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
+                                                              false, f->bgeo, f->bcol, f->bwq);
+    else if (m->elem == MF_P2_TET)
+        k_facet_geometry<MF_P2_TET><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
                                                               false, f->bgeo, f->bcol, f->bwq);
     else
         k_facet_geometry<MF_Q1_HEX><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
@@ -693,6 +735,7 @@ mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c
                  c->bc_mask, c->bc_val, values, d, status
         if (m->elem == MF_P1_TRI) k_bnd_thermal<2><<<g, BND_T, 0, st>>>(BND_ARGS);
         else if (m->elem == MF_P2_TRI) k_bnd_thermal<3><<<g, BND_T, 0, st>>>(BND_ARGS);
+        else if (m->elem == MF_P2_TET) k_bnd_thermal<6><<<g, BND_T, 0, st>>>(BND_ARGS);
         else k_bnd_thermal<4><<<g, BND_T, 0, st>>>(BND_ARGS);
 #undef BND_ARGS
         mf_prof_end(st);

@@ -194,10 +194,62 @@ def test_unsupported_combinations(mf):
         mf.mf_pattern_build(P.mesh, mf.MF_FORM_ELASTIC)
     assert ei.value.status == mf.MF_ERR_UNSUPPORTED
     e = torch.zeros(1, dtype=torch.int32, device="cuda")
-    f = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    f = torch.full((1,), 4, dtype=torch.uint8, device="cuda")  # a tetrahedron has faces 0..3
     with pytest.raises(mf.MFError) as ei:
         mf.mf_facets_create(P.mesh, P.pattern, e, f)
-    assert ei.value.status == mf.MF_ERR_UNSUPPORTED
+    assert ei.value.status == mf.MF_ERR_BAD_MESH
     with pytest.raises(mf.MFError) as ei:
         mf.mf_batch_create([P])
     assert ei.value.status == mf.MF_ERR_UNSUPPORTED
+
+
+def _p2t_convection(n, sides, dirichlet_x0=True, bval_seed=None):
+    prob = gen.thermal_p2t_problem(n)
+    x = prob["coords"]
+    mask = (np.abs(x[:, 0]) <= 1e-14).astype(np.uint8) if dirichlet_x0 else np.zeros(x.shape[0], np.uint8)
+    prob["bc_mask"] = mask
+    prob["bc_val"] = np.zeros(x.shape[0])
+    if bval_seed is not None:
+        prob["bc_val"] = np.where(mask > 0, gen.normal(bval_seed, x.shape[0]), 0.0)
+    prob["facets"] = gen.convection_facets(prob, sides)
+    return prob
+
+
+@pytest.mark.parametrize("case", ["five_sides_4", "all_sides_lifted_5"])
+def test_convection_on_faces_parity(mf, orc, case):
+    """Convection h(T, T_env - T) on the 6-node faces (the surface terms of the
+    3D thermal case) added to the assembled system, against the oracle."""
+    prob = (_p2t_convection(4, ("x1", "y0", "y1", "z0", "z1")) if case == "five_sides_4"
+            else _p2t_convection(5, gen.SIDES, bval_seed=9))
+    P, rp, ci, val, d = _gpu(mf, prob)
+    ref = orc.assemble(prob)
+    assert np.array_equal(rp, ref["row_ptr"]) and np.array_equal(ci, ref["col"])
+    assert row_scaled_error(rp, val, ref["val"]) <= TOL
+    assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+
+
+def test_convection_on_faces_without_dirichlet_and_reproducible(mf, orc):
+    import torch
+    prob = _p2t_convection(4, gen.SIDES, dirichlet_x0=False)
+    P = mf.Problem(prob)
+    coeffs = P.make_coeffs(bc=False)
+    P.facet_coeffs.bc_mask = None
+    P.facet_coeffs.bc_val = None
+    v1, d1 = [t.clone() for t in P.assemble(coeffs=coeffs)]
+    v2, d2 = P.assemble(coeffs=coeffs)
+    assert torch.equal(v1, v2) and torch.equal(d1, d2)
+    rp, ci = P.csr_arrays()
+    ref = orc.assemble(prob, dirichlet=False)
+    assert row_scaled_error(rp.cpu().numpy(), v1.cpu().numpy(), ref["val"]) <= TOL
+    assert np.abs(d1.cpu().numpy() - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+    # the surface terms alone: the sum of all added entries is sum_f h_f A_f
+    # (the domain rows sum to zero), whose areas add up to the cube's 6
+    fac = prob["facets"]
+    e, f = fac["elem"], fac["face"]
+    X = prob["coords"]
+    fv = ((1, 2, 3), (0, 3, 2), (0, 1, 3), (0, 2, 1))
+    area = np.array([0.5 * np.linalg.norm(np.cross(X[prob["conn"][el][fv[fa][1]]] - X[prob["conn"][el][fv[fa][0]]],
+                                                     X[prob["conn"][el][fv[fa][2]]] - X[prob["conn"][el][fv[fa][0]]]))
+                     for el, fa in zip(e, f)])
+    assert abs(area.sum() - 6.0) < 1e-12
+    assert abs(v1.cpu().numpy().sum() - (fac["h"] * area).sum()) < 1e-11 * (fac["h"] * area).sum()
