@@ -719,6 +719,35 @@ def suite(dev):
                                                "converged": bool(info.converged), "s": solve_s}}
     del P
     torch.cuda.empty_cache()
+    # the 3D thermal case's set-up on quadratic tetrahedra: a heat source and
+    # convection on the whole surface (no Dirichlet data), then Jacobi-PCG
+    prob = gen.thermal_p2t_problem(48)
+    prob["bc_mask"] = np.zeros_like(prob["bc_mask"])
+    prob["bc_val"] = np.zeros_like(prob["bc_val"])
+    prob["facets"] = gen.convection_facets(prob, gen.SIDES)
+    t0 = time.perf_counter()
+    P = mf.Problem(prob, device=dev)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    ms = _ev_time(lambda: P.assemble(), reps=5)
+    mf.mf_set_kernel_timing(1)
+    P.assemble()
+    torch.cuda.synchronize()
+    kt = mf.mf_kernel_times()
+    mf.mf_set_kernel_timing(0)
+    bnd_ms = kt["bnd_thermal"][1] / kt["bnd_thermal"][0] if "bnd_thermal" in kt else None
+    t0 = time.perf_counter()
+    x, st, info = P.solve(tol=1e-8, max_iter=20000)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    out["H4_thermal_p2t_convection_48"] = {
+        "elements": int(prob["conn"].shape[0]), "facets": int(prob["facets"]["elem"].shape[0]),
+        "n_dofs": int(P.n), "mesh_pattern_facets_setup_s": setup_s, "assemble_ms": ms,
+        "boundary_kernel_ms": bnd_ms,
+        "jacobi_pcg": {"iterations": int(info.iterations), "rel_residual": float(info.rel_residual),
+                       "converged": bool(info.converged), "s": solve_s}}
+    del P
+    torch.cuda.empty_cache()
     # loaded boundary: a random stress on five sides of the 64^3 elasticity box (clamped at x = 0)
     prob = gen.elastic_problem(64)
     P = mf.Problem(prob, device=dev)
