@@ -210,6 +210,45 @@ def hex20_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
     return {"dim": 3, "elem": "Q2S", "n": n, "coords": coords, "conn": conn.astype(np.int32)}
 
 
+def quad8_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
+    """8-node serendipity quadrilaterals on the unit square from an ``n x n``
+    grid.  Local nodes: vertices a = i + 2 j at cell corner (i, j), then the
+    midpoints of the x edges (at y = j) 4 + j and of the y edges (at x = i)
+    6 + i.  Global numbering: the (n+1)^2 vertices (x fastest, interior ones
+    jittered as in ``tri_mesh``), then the x-edge midpoints (row by row), then
+    the y-edge midpoints.  Edges stay straight.  Element (i, j) is j n + i."""
+    h = 1.0 / n
+    nv = n + 1
+    jj, ii = np.meshgrid(np.arange(nv), np.arange(nv), indexing="ij")
+    V = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
+    vi, vj = ii.ravel(), jj.ravel()
+    _jitter_grid(V, (vi > 0) & (vi < n) & (vj > 0) & (vj < n), h, jitter, seed)
+    xe = lambda i, j: nv * nv + j * n + i            # x edge from (i, j) to (i + 1, j)
+    ye = lambda i, j: nv * nv + nv * n + j * nv + i  # y edge from (i, j) to (i, j + 1)
+    xi_, xj_ = np.meshgrid(np.arange(n), np.arange(nv), indexing="xy")
+    yi_, yj_ = np.meshgrid(np.arange(nv), np.arange(n), indexing="xy")
+    xa = (xj_ * nv + xi_).ravel()
+    ya = (yj_ * nv + yi_).ravel()
+    coords = np.vstack([V, 0.5 * (V[xa] + V[xa + 1]), 0.5 * (V[ya] + V[ya + nv])])
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    v00 = j * nv + i
+    conn = np.stack([v00, v00 + 1, v00 + nv, v00 + nv + 1, xe(i, j), xe(i, j + 1), ye(i, j), ye(i + 1, j)],
+                    axis=1).astype(np.int32)
+    return {"dim": 2, "elem": "Q2Q", "n": n, "coords": coords, "conn": conn}
+
+
+def thermal_q2q_problem(n: int, jitter: float = 0.2, sigma: float = 0.5,
+                        seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    """2D thermal conduction on 8-node serendipity quadrilaterals (u = 0 on the boundary, f = 1)."""
+    m = quad8_mesh(n, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)
+    m["bc_mask"], m["bc_val"] = thermal_bc(m)
+    m["form"] = "thermal"
+    m["source"] = 1.0
+    return m
+
+
 def tet10_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
     """10-node (quadratic) tetrahedra on the unit cube: each cube of an ``n^3``
     grid split into the 6 tetrahedra around its main diagonal (Kuhn's
@@ -371,6 +410,18 @@ def box_facets(mesh: dict, sides=SIDES) -> tuple[np.ndarray, np.ndarray]:
     n = mesh["n"]
     els, faces = [], []
     r = np.arange(n)
+    if mesh["elem"] == "Q2Q":
+        # element (i, j) = j n + i; edges (0,1|4) y = 0 side, (1,3|7) x = 1,
+        # (3,2|5) y = 1, (2,0|6) x = 0
+        for side in sides:
+            axis, hi = "xyz".index(side[0]), side[1] == "1"
+            if axis == 2:
+                raise ValueError("a quadrilateral mesh has no z sides")
+            k = n - 1 if hi else 0
+            e = (r * n + k) if axis == 0 else (k * n + r)
+            els.append(e.astype(np.int32))
+            faces.append(np.full(n, (1 if hi else 3) if axis == 0 else (2 if hi else 0), np.uint8))
+        return np.concatenate(els), np.concatenate(faces)
     if mesh["elem"] == "P2T":
         # tetrahedron face i (opposite vertex i) lies on a side when its three
         # vertices do (boundary nodes are not jittered)

@@ -19,10 +19,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "_oracle.so")
 
-P1, P2, Q1, Q2S, P2T = 0, 1, 2, 3, 4
-QTRI3, QTRI6, QHEX8, QHEX27, QTET64 = 0, 1, 2, 3, 4
+P1, P2, Q1, Q2S, P2T, Q2Q = 0, 1, 2, 3, 4, 5
+QTRI3, QTRI6, QHEX8, QHEX27, QTET64, QQUAD9 = 0, 1, 2, 3, 4, 5
 THERMAL, ELASTIC, OSEEN, CAPACITY = 0, 1, 2, 3
-ELEM = {"P1": P1, "P2": P2, "Q1": Q1, "Q2S": Q2S, "P2T": P2T}
+ELEM = {"P1": P1, "P2": P2, "Q1": Q1, "Q2S": Q2S, "P2T": P2T, "Q2Q": Q2Q}
 FORM = {"thermal": THERMAL, "elastic": ELASTIC, "oseen": OSEEN, "capacity": CAPACITY}
 
 _lib = None
@@ -221,6 +221,8 @@ def _default_quad(elem: str, form: str) -> int:
         return QHEX27
     if elem == "P2T":
         return QTET64
+    if elem == "Q2Q":
+        return QQUAD9
     if form == "oseen":
         return QTRI6
     return QTRI3

@@ -27,9 +27,9 @@
 #include <string.h>
 
 /* element kinds */
-enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2, OR_Q2S = 3, OR_P2T = 4 };
+enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2, OR_Q2S = 3, OR_P2T = 4, OR_Q2Q = 5 };
 /* quadrature kinds */
-enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3, OR_QTET64 = 4 };
+enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3, OR_QTET64 = 4, OR_QQUAD9 = 5 };
 /* forms */
 enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2, OR_CAPACITY = 3 };
 
@@ -98,6 +98,17 @@ int or_quad(int kind, double *pts, double *w)
             w[q] = 0.125 * w4[i] * w4[j] * w4[k] * (1.0 - S) * (1.0 - S) * (1.0 - T);
         }
         return 64;
+    }
+    if (kind == OR_QQUAD9) {
+        /* [-1, 1]^2, 3 x 3 Gauss-Legendre (0, +-sqrt(3/5); 8/9, 5/9), q = i + 3 j */
+        const double g = sqrt(0.6);
+        const double p1[3] = {-g, 0.0, g}, w1[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+        for (int q = 0; q < 9; ++q) {
+            pts[2 * q + 0] = p1[q % 3];
+            pts[2 * q + 1] = p1[q / 3];
+            w[q] = w1[q % 3] * w1[q / 3];
+        }
+        return 9;
     }
     if (kind == OR_QHEX27) {
         /* tensor Gauss-Legendre, 3 points per direction at 0, +-sqrt(3/5),
@@ -176,6 +187,33 @@ int or_shape(int elem, const double *xi, double *N, double *dN)
         }
         return 8;
     }
+    if (elem == OR_Q2Q) {
+        /* 8-node serendipity quadrilateral on [-1, 1]^2.  Vertex a = i + 2j at
+         * (xa, ya) = (2i-1, 2j-1): N = (1 + x xa)(1 + y ya)(x xa + y ya - 1) / 4;
+         * x edges (at y = ya) 4 + j: N = (1 - x^2)(1 + y ya) / 2;
+         * y edges (at x = xa) 6 + i: N = (1 - y^2)(1 + x xa) / 2. */
+        const double x = xi[0], y = xi[1];
+        for (int a = 0; a < 4; ++a) {
+            const double xa = (a & 1) ? 1.0 : -1.0, ya = (a & 2) ? 1.0 : -1.0;
+            const double A = 1.0 + x * xa, B = 1.0 + y * ya;
+            N[a] = 0.25 * A * B * (x * xa + y * ya - 1.0);
+            dN[2 * a + 0] = 0.25 * xa * B * (2.0 * x * xa + y * ya);
+            dN[2 * a + 1] = 0.25 * ya * A * (x * xa + 2.0 * y * ya);
+        }
+        for (int j = 0; j < 2; ++j) {
+            const double ya = j ? 1.0 : -1.0;
+            N[4 + j] = 0.5 * (1.0 - x * x) * (1.0 + y * ya);
+            dN[2 * (4 + j) + 0] = -x * (1.0 + y * ya);
+            dN[2 * (4 + j) + 1] = 0.5 * ya * (1.0 - x * x);
+        }
+        for (int i = 0; i < 2; ++i) {
+            const double xa = i ? 1.0 : -1.0;
+            N[6 + i] = 0.5 * (1.0 - y * y) * (1.0 + x * xa);
+            dN[2 * (6 + i) + 0] = 0.5 * xa * (1.0 - y * y);
+            dN[2 * (6 + i) + 1] = -y * (1.0 + x * xa);
+        }
+        return 8;
+    }
     if (elem == OR_P2T) {
         /* 10-node tetrahedron: lambda = (1 - x - y - z, x, y, z); vertices
          * lambda_i (2 lambda_i - 1), then the edges (0,1), (1,2), (2,0),
@@ -229,10 +267,10 @@ int or_shape(int elem, const double *xi, double *N, double *dN)
     return -1;
 }
 
-static int elem_dim(int elem) { return elem >= OR_Q1 ? 3 : 2; }
+static int elem_dim(int elem) { return (elem == OR_Q1 || elem == OR_Q2S || elem == OR_P2T) ? 3 : 2; }
 static int elem_npe(int elem)
 {
-    return elem == OR_P1 ? 3 : (elem == OR_P2 ? 6 : (elem == OR_Q1 ? 8 : (elem == OR_Q2S ? 20 : 10)));
+    return elem == OR_P1 ? 3 : (elem == OR_P2 ? 6 : (elem == OR_Q1 || elem == OR_Q2Q ? 8 : (elem == OR_Q2S ? 20 : 10)));
 }
 
 /* Geometry at one point: J_ij = sum_a x_{a,i} dN_a/dxi_j, detJ, and the
@@ -345,8 +383,8 @@ double or_elem_thermal(int elem, int quad, const double *X, double k, double fco
 /* Capacity element (Sec. 4.1: -C(T, T_t), the rate term; tangent negated):  */
 /* Me[a][b] = sum_q w detJ C N_a N_b, with a rule exact for N_a N_b on an    */
 /* affine element: the 3-point rule (P1, degree 2), the 6-point rule (P2,    */
-/* degree 4), 2 x 2 x 2 Gauss (Q1), 3 x 3 x 3 Gauss (Q2S), the 64-point     */
-/* collapsed rule (P2T, degree 5).  Returns min detJ.                       */
+/* degree 4), 2 x 2 x 2 Gauss (Q1), 3 x 3 x 3 Gauss (Q2S), 3 x 3 Gauss      */
+/* (Q2Q), the 64-point collapsed rule (P2T, degree 5).  Returns min detJ.   */
 /* ------------------------------------------------------------------------ */
 double or_elem_capacity(int elem, const double *X, double C, double *Me)
 {
@@ -354,7 +392,8 @@ double or_elem_capacity(int elem, const double *X, double C, double *Me)
     const int quad = elem == OR_P1 ? OR_QTRI3
                      : elem == OR_P2 ? OR_QTRI6
                      : elem == OR_Q1 ? OR_QHEX8
-                     : elem == OR_Q2S ? OR_QHEX27 : OR_QTET64;
+                     : elem == OR_Q2S ? OR_QHEX27
+                     : elem == OR_Q2Q ? OR_QQUAD9 : OR_QTET64;
     const int nq = or_quad(quad, pts, w);
     const int dim = elem_dim(elem), npe = elem_npe(elem);
     double mindet = 1e300;
@@ -505,6 +544,14 @@ int or_facet_nodes(int elem, int face, int *loc)
             if (((a >> d) & 1) == s) loc[m++] = a;
         return 4;
     }
+    if (elem == OR_Q2Q) {
+        /* edges counter-clockwise: (0,1 | 4), (1,3 | 7), (3,2 | 5), (2,0 | 6):
+         * the two vertices, then the midpoint (a straight 3-node edge as P2's) */
+        static const int el[4][3] = {{0, 1, 4}, {1, 3, 7}, {3, 2, 5}, {2, 0, 6}};
+        if (face < 0 || face > 3) return -1;
+        for (int m = 0; m < 3; ++m) loc[m] = el[face][m];
+        return 3;
+    }
     if (face < 0 || face > 2) return -1;
     loc[0] = face;
     loc[1] = (face + 1) % 3;
@@ -519,6 +566,7 @@ int or_facet_nodes(int elem, int face, int *loc)
  * [-1, 1]^2 (hexahedron faces). */
 static int facet_quad(int elem, double *pts, double *w)
 {
+    if (elem == OR_Q2Q) elem = OR_P2;  /* straight 3-node edges */
     if (elem == OR_P2T) return or_quad(OR_QTRI6, pts, w);
     if (elem == OR_P1) {
         const double g = 0.5 / sqrt(3.0);
@@ -548,6 +596,7 @@ static int facet_quad(int elem, double *pts, double *w)
  * its length element |dx/dt| (edges, returned in A[0]). */
 static int facet_point(int elem, const double *Xf, const double *p, double *N, double *A)
 {
+    if (elem == OR_Q2Q) elem = OR_P2;  /* straight 3-node edges */
     if (elem == OR_P1 || elem == OR_P2) {
         const double t = p[0];
         int nf;
@@ -603,7 +652,7 @@ double or_facet_thermal(int elem, const double *Xf, double h, double tenv, doubl
     double pts[12], w[6], N[6], A[3];
     const int nq = facet_quad(elem, pts, w);
     const int pdim = (elem == OR_Q1 || elem == OR_P2T) ? 2 : 1;
-    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : (elem == OR_Q1 ? 4 : 6));
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 || elem == OR_Q2Q ? 3 : (elem == OR_Q1 ? 4 : 6));
     for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
     for (int a = 0; a < nf; ++a) df[a] = 0.0;
     double meas = 0.0;
@@ -656,7 +705,7 @@ void or_facet_radiation(int elem, const double *Xf, double es, double tenv, cons
     double pts[12], w[6], N[6], A[3];
     const int nq = facet_quad(elem, pts, w);
     const int pdim = (elem == OR_Q1 || elem == OR_P2T) ? 2 : 1;
-    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 ? 3 : (elem == OR_Q1 ? 4 : 6));
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 || elem == OR_Q2Q ? 3 : (elem == OR_Q1 ? 4 : 6));
     for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
     for (int a = 0; a < nf; ++a) rf[a] = 0.0;
     const double te4 = tenv * tenv * tenv * tenv;
