@@ -50,7 +50,7 @@ typedef enum {
     MF_ERR_UNSUPPORTED = 8   /* combination not provided (e.g. node valence too high) */
 } mf_status;
 
-typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2, MF_Q2S_HEX = 3, MF_P2_TET = 4 } mf_elem;
+typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2, MF_Q2S_HEX = 3, MF_P2_TET = 4, MF_Q2S_QUAD = 5 } mf_elem;
 typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2, MF_FORM_CAPACITY = 3 } mf_form;
 typedef enum { MF_PREC_FP64 = 0, MF_PREC_MIXED = 1 } mf_prec;
 typedef enum { MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1 } mf_solver;
@@ -71,7 +71,12 @@ typedef struct mf_pattern mf_pattern;
  * experiments; vertices 0..3 positively oriented, then the midpoints of
  * edges (0,1), (1,2), (2,0), (0,3), (1,3), (2,3) at the mean of their ends,
  * so the geometry is the vertices' affine map; thermal form, FP64, exact
- * integration, up to 128 neighbours per node).  Triangles are
+ * integration, up to 128 neighbours per node), 8 (Q2S_QUAD: the 8-node
+ * serendipity quadrilateral of the paper's 2D thermal case; vertices
+ * a = i + 2j at reference corner (2i-1, 2j-1), then the midpoints of the x
+ * edges (at y = 2j-1) 4 + j and of the y edges (at x = 2i-1) 6 + i, at the
+ * mean of their ends, so the geometry is the vertices' bilinear map;
+ * thermal form, FP64, 3 x 3 Gauss).  Triangles are
  * counter-clockwise.  For the flow form, pconn [n_elems][3] gives the P1
  * pressure nodes (the element's vertices in a 0..n_pnodes-1 numbering). */
 typedef struct {
@@ -191,6 +196,9 @@ mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *patte
  *    2s - 1; its nodes are the element nodes a with bit d of a equal to s,
  *    ascending, and its map is bilinear in the other two reference
  *    coordinates.  n is the outward unit normal.
+ *  - quadrilateral (Q2S_QUAD) face f is an edge, counter-clockwise: nodes
+ *    (0, 1, 4), (1, 3, 7), (3, 2, 5), (2, 0, 6) for f = 0..3 (the two ends,
+ *    then the midpoint), integrated as a straight P2 edge.
  *  - tetrahedron (P2T) face i is the face opposite vertex i; its nodes are
  *    the three vertices in outward order (1,2,3), (0,3,2), (0,1,3), (0,2,1)
  *    for i = 0..3, then the midpoints of its edges (0,1), (1,2), (2,0) in

@@ -19,12 +19,12 @@ LIB = os.path.join(HERE, "libmf.so")
 
 MF_OK, MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH, MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA, \
     MF_ERR_NOT_CONVERGED, MF_ERR_TIMEOUT, MF_ERR_UNSUPPORTED = range(9)
-MF_P1_TRI, MF_P2_TRI, MF_Q1_HEX, MF_Q2S_HEX, MF_P2_TET = 0, 1, 2, 3, 4
+MF_P1_TRI, MF_P2_TRI, MF_Q1_HEX, MF_Q2S_HEX, MF_P2_TET, MF_Q2S_QUAD = 0, 1, 2, 3, 4, 5
 MF_FORM_THERMAL, MF_FORM_ELASTIC, MF_FORM_OSEEN, MF_FORM_CAPACITY = 0, 1, 2, 3
 MF_PREC_FP64, MF_PREC_MIXED = 0, 1
 MF_SOLVER_PCG, MF_SOLVER_GMRES = 0, 1
 
-ELEM = {"P1": MF_P1_TRI, "P2": MF_P2_TRI, "Q1": MF_Q1_HEX, "Q2S": MF_Q2S_HEX, "P2T": MF_P2_TET}
+ELEM = {"P1": MF_P1_TRI, "P2": MF_P2_TRI, "Q1": MF_Q1_HEX, "Q2S": MF_Q2S_HEX, "P2T": MF_P2_TET, "Q2Q": MF_Q2S_QUAD}
 FORM = {"thermal": MF_FORM_THERMAL, "elastic": MF_FORM_ELASTIC, "oseen": MF_FORM_OSEEN}
 
 

@@ -249,7 +249,7 @@ extern "C" mf_status mf_mesh_create(const mf_mesh_desc *desc, void *stream, mf_m
     g_msg[0] = 0;
     if (!desc || !out) return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: NULL argument");
     *out = nullptr;
-    if (desc->elem < MF_P1_TRI || desc->elem > MF_P2_TET)
+    if (desc->elem < MF_P1_TRI || desc->elem > MF_Q2S_QUAD)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: unknown element %d", desc->elem);
     if (desc->dim != mf_ndim(desc->elem))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_mesh_create: dim %d does not match element", desc->dim);
@@ -368,6 +368,8 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
                        "mf_assemble: serendipity bricks carry the thermal and elasticity forms in FP64");
     if (mesh->elem == MF_P2_TET && (form != MF_FORM_THERMAL || prec != MF_PREC_FP64))
         return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: quadratic tetrahedra carry the thermal form in FP64");
+    if (mesh->elem == MF_Q2S_QUAD && (form != MF_FORM_THERMAL || prec != MF_PREC_FP64))
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: serendipity quadrilaterals carry the thermal form in FP64");
     if (K->n_rows != pattern->n_rows || K->nnz != pattern->nnz || K->row_ptr != pattern->row_ptr ||
         K->col_idx != pattern->col_idx)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: K does not carry the pattern's CSR arrays");

@@ -78,6 +78,16 @@ __global__ void __launch_bounds__(128) k_elem_thermal_p2t(int64_t n_el, const do
     }
 }
 
+__global__ void __launch_bounds__(128) k_elem_thermal_q2q(int64_t n_el, const double *__restrict__ X,
+                                                          const int32_t *__restrict__ conn,
+                                                          const double *__restrict__ kc, double f,
+                                                          const int32_t *__restrict__ map, double *__restrict__ out,
+                                                          int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_el) elem_thermal_q2q(e, X, conn, kc, f, map, out, status);
+}
+
 __global__ void k_elem_thermal_p2(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
                                   const double *__restrict__ kc, double f, const int32_t *__restrict__ map,
                                   double *__restrict__ out, int *status)
@@ -1082,9 +1092,13 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
                       : m->elem == MF_P2_TRI ? "elem_thermal_p2"
                       : m->elem == MF_Q1_HEX ? "elem_thermal_q1"
                       : m->elem == MF_P2_TET ? "elem_thermal_p2t"
+                      : m->elem == MF_Q2S_QUAD ? "elem_thermal_q2q"
                                              : "elem_thermal_q2s",
                       st);
-        if (m->elem == MF_P2_TET)
+        if (m->elem == MF_Q2S_QUAD)
+            k_elem_thermal_q2q<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
+                                                              p->scratch, status);
+        else if (m->elem == MF_P2_TET)
             k_elem_thermal_p2t<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
                                                               p->scratch, status);
         else if (m->elem == MF_Q2S_HEX)
@@ -1112,7 +1126,7 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         c->bc_mask, c->bc_val, p->row_ptr, values, d)
         if (m->elem == MF_P1_TRI) MF_GATHER_TH(3);
         else if (m->elem == MF_P2_TRI) MF_GATHER_TH(6);
-        else if (m->elem == MF_Q1_HEX) MF_GATHER_TH(8);
+        else if (m->elem == MF_Q1_HEX || m->elem == MF_Q2S_QUAD) MF_GATHER_TH(8);
         else if (m->elem == MF_P2_TET) MF_GATHER_TH(10);
         else MF_GATHER_TH(20);
 #undef MF_GATHER_TH

@@ -250,10 +250,10 @@ extern "C" mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, co
             delete b;
             return mf_fail(MF_ERR_INVALID_ARG, "mf_batch_create: problem %d is not a thermal mesh/pattern/coeffs", i);
         }
-        if (m->elem == MF_Q2S_HEX || m->elem == MF_P2_TET) {
+        if (m->elem == MF_Q2S_HEX || m->elem == MF_P2_TET || m->elem == MF_Q2S_QUAD) {
             delete b;
             return mf_fail(MF_ERR_UNSUPPORTED,
-                           "mf_batch_create: problem %d: serendipity bricks and tetrahedra are not batched", i);
+                           "mf_batch_create: problem %d: serendipity elements and tetrahedra are not batched", i);
         }
         const mf_adj &A = p->adj[0];
         b->host.push_back(BatchProblem{m->elem, m->npe, m->n_elems, m->n_nodes, m->coords, m->conn, c.elem_coef,

@@ -54,6 +54,14 @@ __device__ __forceinline__ int facet_local(int elem, int face, int (&loc)[6])
         for (int m = 0; m < 6; ++m) loc[m] = fl[face][m];
         return 6;
     }
+    if (elem == MF_Q2S_QUAD) {
+        // edges counter-clockwise: the two ends, then the midpoint (a straight
+        // 3-node edge, integrated as a P2 triangle's)
+        if (face < 0 || face > 3) return 0;
+        const int el[4][3] = {{0, 1, 4}, {1, 3, 7}, {3, 2, 5}, {2, 0, 6}};
+        for (int m = 0; m < 3; ++m) loc[m] = el[face][m];
+        return 3;
+    }
     if (elem == MF_Q1_HEX) {
         if (face < 0 || face > 5) return 0;
         const int d = face >> 1, s = face & 1;
@@ -571,7 +579,7 @@ mf_status mf_radiation_load(const mf_facets *f, const double *es, const double *
     const unsigned g = nblk(f->n_bnodes, BND_T);
 #define RL_ARGS f->n_bnodes, f->bnode, f->bptr, f->binc, f->bwq, f->fnode, es, tenv, T, mask, R, status
     if (f->mesh->elem == MF_P1_TRI) k_rad_load<MF_P1_TRI><<<g, BND_T, 0, st>>>(RL_ARGS);
-    else if (f->mesh->elem == MF_P2_TRI) k_rad_load<MF_P2_TRI><<<g, BND_T, 0, st>>>(RL_ARGS);
+    else if (f->mesh->elem == MF_P2_TRI || f->mesh->elem == MF_Q2S_QUAD) k_rad_load<MF_P2_TRI><<<g, BND_T, 0, st>>>(RL_ARGS);
     else k_rad_load<MF_Q1_HEX><<<g, BND_T, 0, st>>>(RL_ARGS);
 #undef RL_ARGS
     return mf_cuda_check(cudaGetLastError(), "radiation load");
@@ -587,7 +595,8 @@ mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const doubl
 #define RT_ARGS f->n_bnodes, f->bnode, f->brow, f->bptr, f->binc, f->bslot, f->bcol, f->bwq, f->fnode, es, T, mask, \
                 scale, values
     if (f->mesh->elem == MF_P1_TRI) k_rad_tangent<MF_P1_TRI><<<g, BND_T, 0, st>>>(RT_ARGS);
-    else if (f->mesh->elem == MF_P2_TRI) k_rad_tangent<MF_P2_TRI><<<g, BND_T, 0, st>>>(RT_ARGS);
+    else if (f->mesh->elem == MF_P2_TRI || f->mesh->elem == MF_Q2S_QUAD)
+        k_rad_tangent<MF_P2_TRI><<<g, BND_T, 0, st>>>(RT_ARGS);
     else k_rad_tangent<MF_Q1_HEX><<<g, BND_T, 0, st>>>(RT_ARGS);
 #undef RT_ARGS
     return mf_cuda_check(cudaGetLastError(), "radiation tangent");
@@ -596,7 +605,7 @@ mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const doubl
 mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n_facets, const int32_t *elem,
                                 const uint8_t *face, cudaStream_t st, mf_facets *f)
 {
-    f->npf = m->elem == MF_P1_TRI ? 2 : (m->elem == MF_P2_TRI ? 3 : (m->elem == MF_Q1_HEX ? 4 : 6));
+    f->npf = m->elem == MF_P1_TRI ? 2 : ((m->elem == MF_P2_TRI || m->elem == MF_Q2S_QUAD) ? 3 : (m->elem == MF_Q1_HEX ? 4 : 6));
     f->n_facets = n_facets;
     if (n_facets == 0) return MF_OK;
     if (p->form == MF_FORM_ELASTIC && m->elem != MF_Q1_HEX)
@@ -683,7 +692,7 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
     if (m->elem == MF_P1_TRI)
         k_facet_geometry<MF_P1_TRI><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
                                                               false, f->bgeo, f->bcol, f->bwq);
-    else if (m->elem == MF_P2_TRI)
+    else if (m->elem == MF_P2_TRI || m->elem == MF_Q2S_QUAD)  // straight 3-node edges
         k_facet_geometry<MF_P2_TRI><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
                                                               false, f->bgeo, f->bcol, f->bwq);
     else if (m->elem == MF_P2_TET)
@@ -734,7 +743,7 @@ mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c
 #define BND_ARGS f->n_bnodes, f->bnode, f->brow, f->bptr, f->binc, f->bslot, f->bgeo, f->bcol, c->h, c->t_env, \
                  c->bc_mask, c->bc_val, values, d, status
         if (m->elem == MF_P1_TRI) k_bnd_thermal<2><<<g, BND_T, 0, st>>>(BND_ARGS);
-        else if (m->elem == MF_P2_TRI) k_bnd_thermal<3><<<g, BND_T, 0, st>>>(BND_ARGS);
+        else if (m->elem == MF_P2_TRI || m->elem == MF_Q2S_QUAD) k_bnd_thermal<3><<<g, BND_T, 0, st>>>(BND_ARGS);
         else if (m->elem == MF_P2_TET) k_bnd_thermal<6><<<g, BND_T, 0, st>>>(BND_ARGS);
         else k_bnd_thermal<4><<<g, BND_T, 0, st>>>(BND_ARGS);
 #undef BND_ARGS

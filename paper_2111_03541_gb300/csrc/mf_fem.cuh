@@ -546,6 +546,91 @@ __device__ __forceinline__ double p2t_entry(const float2 (&G)[6], int a, int b)
     return df_to_double(v);
 }
 
+// 8-node serendipity quadrilateral, thermal form: the vertices' bilinear map
+// at the 3 x 3 Gauss points; reference gradients of the 8-node basis
+// (vertex a at (sa, ta): N = (1 + x sa)(1 + y ta)(x sa + y ta - 1) / 4; x edge
+// 4 + j at y = tj: N = (1 - x^2)(1 + y tj) / 2; y edge 6 + i at x = si:
+// N = (1 - y^2)(1 + x si) / 2); K_e = k sum_q w detJ grad N_a . grad N_b,
+// d_e = f sum_q w detJ N_a.  FP64, one thread per element.
+__device__ __forceinline__ void elem_thermal_q2q(int64_t e, const double *__restrict__ X,
+                                                 const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                                 double f, const int32_t *__restrict__ map, double *__restrict__ out,
+                                                 int *status)
+{
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    const int32_t *c = conn + 8 * e;
+    double x[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) x[a][i] = X[2 * (int64_t)c[a] + i];
+    double K[36] = {}, dl[8] = {};
+    const double g3 = 0.77459666924148337704;  // sqrt(3/5)
+#pragma unroll 1
+    for (int q = 0; q < 9; ++q) {
+        const double xs = (q % 3 - 1) * g3, ys = (q / 3 - 1) * g3;
+        const double w = (q % 3 == 1 ? 8.0 / 9.0 : 5.0 / 9.0) * (q / 3 == 1 ? 8.0 / 9.0 : 5.0 / 9.0);
+        double N[8], dN[8][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double sa = (a & 1) ? 1.0 : -1.0, ta = (a & 2) ? 1.0 : -1.0;
+            const double A = 1.0 + xs * sa, B = 1.0 + ys * ta;
+            N[a] = 0.25 * A * B * (xs * sa + ys * ta - 1.0);
+            dN[a][0] = 0.25 * sa * B * (2.0 * xs * sa + ys * ta);
+            dN[a][1] = 0.25 * ta * A * (xs * sa + 2.0 * ys * ta);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const double t = j ? 1.0 : -1.0;
+            N[4 + j] = 0.5 * (1.0 - xs * xs) * (1.0 + ys * t);
+            dN[4 + j][0] = -xs * (1.0 + ys * t);
+            dN[4 + j][1] = 0.5 * t * (1.0 - xs * xs);
+            N[6 + j] = 0.5 * (1.0 - ys * ys) * (1.0 + xs * t);
+            dN[6 + j][0] = 0.5 * t * (1.0 - ys * ys);
+            dN[6 + j][1] = -ys * (1.0 + xs * t);
+        }
+        // the bilinear map of the vertices: J[i][r] = sum_a x_a,i dN1_a / dxi_r
+        double J[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double sa = (a & 1) ? 1.0 : -1.0, ta = (a & 2) ? 1.0 : -1.0;
+            const double d0 = 0.25 * sa * (1.0 + ta * ys), d1 = 0.25 * ta * (1.0 + sa * xs);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                J[i][0] = fma(x[a][i], d0, J[i][0]);
+                J[i][1] = fma(x[a][i], d1, J[i][1]);
+            }
+        }
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double r = 1.0 / det, wd = w * det;
+        // grad N = J^-T gradref N, J^-1 = [[J11, -J01], [-J10, J00]] / det
+        double g[8][2];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            g[a][0] = (J[1][1] * dN[a][0] - J[1][0] * dN[a][1]) * r;
+            g[a][1] = (J[0][0] * dN[a][1] - J[0][1] * dN[a][0]) * r;
+            dl[a] = fma(wd, N[a], dl[a]);
+        }
+        int u = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = a; b < 8; ++b, ++u) K[u] = fma(wd, fma(g[a][0], g[b][0], g[a][1] * g[b][1]), K[u]);
+    }
+    const ThOut<8> W(map, e);
+    int u = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+#pragma unroll
+        for (int b = a; b < 8; ++b, ++u) {
+            out[W.base[a] + b] = k * K[u];
+            if (b != a) out[W.base[b] + a] = k * K[u];
+        }
+        out[W.ld[a]] = f * dl[a];
+    }
+}
+
 __device__ __forceinline__ void elem_thermal_q1(int64_t e, const double *__restrict__ X,
                                                          const int32_t *__restrict__ conn,
                                                          const double *__restrict__ kc, double f,

@@ -139,9 +139,12 @@ cudaError_t mf_scan_i64(int64_t *d_data, int64_t n, int64_t *d_total, cudaStream
 
 static inline int mf_npe(int elem)
 {
-    return elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : (elem == MF_Q1_HEX ? 8 : (elem == MF_Q2S_HEX ? 20 : 10)));
+    return elem == MF_P1_TRI ? 3
+         : elem == MF_P2_TRI ? 6
+         : (elem == MF_Q1_HEX || elem == MF_Q2S_QUAD) ? 8
+         : elem == MF_Q2S_HEX ? 20 : 10;
 }
-static inline int mf_ndim(int elem) { return elem >= MF_Q1_HEX ? 3 : 2; }
+static inline int mf_ndim(int elem) { return (elem == MF_Q1_HEX || elem == MF_Q2S_HEX || elem == MF_P2_TET) ? 3 : 2; }
 // 8-byte words per incidence row of the thermal scratch: row a of K_e, then
 // d_e[a]; the 10-node tetrahedron's rows are padded to 12 words (96 bytes,
 // three whole 32-byte sectors), so that no sector holds parts of rows that

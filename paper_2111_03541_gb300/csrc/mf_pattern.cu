@@ -30,7 +30,10 @@ __global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_el) return;
-    const int npe = elem == MF_P1_TRI ? 3 : (elem == MF_P2_TRI ? 6 : (elem == MF_Q1_HEX ? 8 : (elem == MF_Q2S_HEX ? 20 : 10)));
+    const int npe = elem == MF_P1_TRI ? 3
+                  : elem == MF_P2_TRI ? 6
+                  : (elem == MF_Q1_HEX || elem == MF_Q2S_QUAD) ? 8
+                  : elem == MF_Q2S_HEX ? 20 : 10;
     for (int a = 0; a < npe; ++a) {
         const int32_t v = conn[e * npe + a];
         if (v < 0 || v >= n_nodes) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
@@ -48,6 +51,29 @@ __global__ void k_validate(int elem, int64_t n_el, int64_t n_nodes, const double
         const double det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
         if (!isfinite(det)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
         if (!(det > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
+        return;
+    }
+    if (elem == MF_Q2S_QUAD) {  // the bilinear map of the 4 vertices at the 3 x 3 Gauss points
+        const int32_t *c = conn + e * npe;
+        double x[4][2];
+        for (int a = 0; a < 4; ++a)
+            for (int i = 0; i < 2; ++i) x[a][i] = X[2 * (int64_t)c[a] + i];
+        const double g3 = 0.77459666924148337704;  // sqrt(3/5)
+        for (int q = 0; q < 9; ++q) {
+            const double xs = (q % 3 - 1) * g3, ys = (q / 3 - 1) * g3;
+            double J[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+            for (int a = 0; a < 4; ++a) {
+                const double sa = (a & 1) ? 1.0 : -1.0, ta = (a & 2) ? 1.0 : -1.0;
+                const double dx = 0.25 * sa * (1.0 + ta * ys), dy = 0.25 * ta * (1.0 + sa * xs);
+                for (int i = 0; i < 2; ++i) {
+                    J[i][0] += x[a][i] * dx;
+                    J[i][1] += x[a][i] * dy;
+                }
+            }
+            const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            if (!isfinite(det)) { mf_dev_fail(status, MF_ERR_NONFINITE); return; }
+            if (!(det > 0.0)) { mf_dev_fail(status, MF_ERR_BAD_MESH); return; }
+        }
         return;
     }
     if (elem == MF_P2_TET) {  // the affine map of the 4 vertices
