@@ -180,3 +180,25 @@ def test_assembled_convection_on_the_surface(orc):
     x = prob["coords"]
     assert abs(x[:, 0] @ Kc @ one - 2.5 * 3.0) < 1e-12       # int x over the surface = 3
     assert abs(Kc - Kc.T).max() < 1e-15
+
+
+def test_capacity_matrix_closed_form(orc):
+    """Consistent mass matrix of the affine 10-node tetrahedron: V / 420 times
+    [6 I - J on the vertices (off-diagonal 1), -4 between a vertex and an edge
+    touching it, -6 between a vertex and the opposite edge, 32 on the edge
+    diagonal, 16 between edges sharing a vertex, 8 between opposite edges]."""
+    V, X = _tet(seed=12)
+    vol = abs(np.linalg.det(V[1:] - V[0])) / 6
+    Me, det = orc.elem_capacity(orc.P2T, X, 1.0)
+    M = np.zeros((10, 10))
+    for a in range(4):
+        for b in range(4):
+            M[a, b] = 6.0 if a == b else 1.0
+    for k, (p, q) in enumerate(EDGES):
+        for a in range(4):
+            M[a, 4 + k] = M[4 + k, a] = -4.0 if a in (p, q) else -6.0
+        for l, (r, t) in enumerate(EDGES):
+            M[4 + k, 4 + l] = 32.0 if k == l else (16.0 if len({p, q} & {r, t}) == 1 else 8.0)
+    assert np.abs(Me - vol / 420.0 * M).max() < 1e-15
+    assert abs(Me.sum() - vol) < 1e-15
+    assert np.abs(Me.sum(axis=1) - vol * np.array([-1 / 20] * 4 + [1 / 5] * 6)).max() < 1e-15

@@ -152,3 +152,17 @@ def test_edges_tables_and_convection(orc):
     tot = sum(orc.facet_thermal(orc.Q2Q, prob["coords"][prob["conn"][el][orc.facet_nodes(orc.Q2Q, int(fa))]],
                                 1.0, 1.0)[2] for el, fa in zip(e, f))
     assert abs(tot - 4.0) < 1e-13
+
+
+def test_capacity_on_a_parallelogram(orc):
+    """Mass matrix of the 8-node element on a parallelogram: total mass the
+    area, row sums the consistent loads (-A/12, A/3), symmetric positive
+    definite."""
+    P = np.array([[0.1, 0.2], [1.3, 0.5], [0.4, 1.1], [1.6, 1.4]])
+    XP = np.vstack([P, 0.5 * (P[0] + P[1]), 0.5 * (P[2] + P[3]), 0.5 * (P[0] + P[2]), 0.5 * (P[1] + P[3])])
+    e1, e2 = P[1] - P[0], P[2] - P[0]
+    A = abs(e1[0] * e2[1] - e1[1] * e2[0])
+    Me, det = orc.elem_capacity(orc.Q2Q, XP, 2.0)
+    assert abs(Me.sum() - 2.0 * A) < 1e-14
+    assert np.abs(Me.sum(axis=1) - 2.0 * A * np.array([-1 / 12] * 4 + [1 / 3] * 4)).max() < 1e-14
+    assert np.abs(Me - Me.T).max() < 1e-15 and np.linalg.eigvalsh(Me)[0] > 0
