@@ -366,10 +366,10 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
     if (mesh->elem == MF_Q2S_HEX && ((form != MF_FORM_THERMAL && form != MF_FORM_ELASTIC) || prec != MF_PREC_FP64))
         return mf_fail(MF_ERR_UNSUPPORTED,
                        "mf_assemble: serendipity bricks carry the thermal and elasticity forms in FP64");
-    if (mesh->elem == MF_P2_TET && (form != MF_FORM_THERMAL || prec != MF_PREC_FP64))
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: quadratic tetrahedra carry the thermal form in FP64");
-    if (mesh->elem == MF_Q2S_QUAD && (form != MF_FORM_THERMAL || prec != MF_PREC_FP64))
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: serendipity quadrilaterals carry the thermal form in FP64");
+    if ((mesh->elem == MF_P2_TET || mesh->elem == MF_Q2S_QUAD) &&
+        ((form != MF_FORM_THERMAL && form != MF_FORM_CAPACITY) || prec != MF_PREC_FP64))
+        return mf_fail(MF_ERR_UNSUPPORTED,
+                       "mf_assemble: tetrahedra and serendipity quadrilaterals carry the thermal and capacity forms in FP64");
     if (K->n_rows != pattern->n_rows || K->nnz != pattern->nnz || K->row_ptr != pattern->row_ptr ||
         K->col_idx != pattern->col_idx)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: K does not carry the pattern's CSR arrays");

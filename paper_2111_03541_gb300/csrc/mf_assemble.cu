@@ -116,6 +116,8 @@ __global__ void k_elem_capacity(int elem, int64_t n_el, const double *__restrict
     if (e >= n_el) return;
     if (elem == MF_P1_TRI) elem_capacity_p1(e, X, conn, kc, map, out, status);
     else if (elem == MF_P2_TRI) elem_capacity_p2(e, X, conn, kc, map, out, status);
+    else if (elem == MF_P2_TET) elem_capacity_p2t(e, X, conn, kc, map, out, status);
+    else if (elem == MF_Q2S_QUAD) elem_capacity_q2q(e, X, conn, kc, map, out, status);
     else if (!q1_translate(e, tr, kc, status)) elem_capacity_q1(e, X, conn, kc, map, out, status);
 }
 
@@ -1095,7 +1097,10 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
                       : m->elem == MF_Q2S_QUAD ? "elem_thermal_q2q"
                                              : "elem_thermal_q2s",
                       st);
-        if (m->elem == MF_Q2S_QUAD)
+        if (cap && (m->elem == MF_Q2S_QUAD || m->elem == MF_P2_TET))
+            k_elem_capacity<<<nblk(ne, 128), 128, 0, st>>>(m->elem, ne, m->coords, m->conn, c->elem_coef, p->tr,
+                                                           p->elem_inc, p->scratch, status);
+        else if (m->elem == MF_Q2S_QUAD)
             k_elem_thermal_q2q<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
                                                               p->scratch, status);
         else if (m->elem == MF_P2_TET)

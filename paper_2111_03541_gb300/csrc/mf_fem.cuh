@@ -779,6 +779,118 @@ __device__ __forceinline__ void elem_capacity_p2(int64_t e, const double *__rest
     }
 }
 
+// 10-node tetrahedron: the consistent mass matrix of the affine element in
+// closed form, C V / 420 [vertex-vertex 6 (diagonal) or 1, vertex-edge -4
+// (the edge touches the vertex) or -6, edge-edge 32 (diagonal), 16 (a shared
+// vertex) or 8], V = detJ / 6; zero load.  Incidence layout (map required).
+__device__ __forceinline__ void elem_capacity_p2t(int64_t e, const double *__restrict__ X,
+                                                  const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                                  const int32_t *__restrict__ map, double *__restrict__ out,
+                                                  int *status)
+{
+    const double C = kc[e];
+    if (!isfinite(C)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    const int32_t *c = conn + 10 * e;
+    double J[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) J[i][j] = X[3 * (int64_t)c[j + 1] + i] - X[3 * (int64_t)c[0] + i];
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) +
+                       J[0][1] * (J[1][2] * J[2][0] - J[1][0] * J[2][2]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    const double s = C * det * (1.0 / 2520.0);
+    const int ep[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+    constexpr int RS = mf_th_rs(10);
+#pragma unroll 1
+    for (int a = 0; a < 10; ++a) {
+        double *row = out + (int64_t)map[e * 10 + a] * RS;
+#pragma unroll
+        for (int b = 0; b < 10; ++b) {
+            double m;
+            if (a < 4 && b < 4) {
+                m = a == b ? 6.0 : 1.0;
+            } else if (a < 4 || b < 4) {
+                const int v = a < 4 ? a : b, k = (a < 4 ? b : a) - 4;
+                m = (ep[k][0] == v || ep[k][1] == v) ? -4.0 : -6.0;
+            } else {
+                const int k = a - 4, l = b - 4;
+                const int sh = (ep[k][0] == ep[l][0]) + (ep[k][0] == ep[l][1]) + (ep[k][1] == ep[l][0]) +
+                               (ep[k][1] == ep[l][1]);
+                m = k == l ? 32.0 : (sh == 1 ? 16.0 : 8.0);
+            }
+            row[b] = s * m;
+        }
+        row[10] = 0.0;
+    }
+}
+
+// 8-node serendipity quadrilateral: C sum_q w detJ N_a N_b at the 3 x 3 Gauss
+// points of the vertices' bilinear map (the basis of elem_thermal_q2q); zero load.
+__device__ __forceinline__ void elem_capacity_q2q(int64_t e, const double *__restrict__ X,
+                                                  const int32_t *__restrict__ conn, const double *__restrict__ kc,
+                                                  const int32_t *__restrict__ map, double *__restrict__ out,
+                                                  int *status)
+{
+    const double C = kc[e];
+    if (!isfinite(C)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    const int32_t *c = conn + 8 * e;
+    double x[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) x[a][i] = X[2 * (int64_t)c[a] + i];
+    double Me[36] = {};
+    const double g3 = 0.77459666924148337704;  // sqrt(3/5)
+#pragma unroll 1
+    for (int q = 0; q < 9; ++q) {
+        const double xs = (q % 3 - 1) * g3, ys = (q / 3 - 1) * g3;
+        const double w = (q % 3 == 1 ? 8.0 / 9.0 : 5.0 / 9.0) * (q / 3 == 1 ? 8.0 / 9.0 : 5.0 / 9.0);
+        double N[8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double sa = (a & 1) ? 1.0 : -1.0, ta = (a & 2) ? 1.0 : -1.0;
+            N[a] = 0.25 * (1.0 + xs * sa) * (1.0 + ys * ta) * (xs * sa + ys * ta - 1.0);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const double t = j ? 1.0 : -1.0;
+            N[4 + j] = 0.5 * (1.0 - xs * xs) * (1.0 + ys * t);
+            N[6 + j] = 0.5 * (1.0 - ys * ys) * (1.0 + xs * t);
+        }
+        double J[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double sa = (a & 1) ? 1.0 : -1.0, ta = (a & 2) ? 1.0 : -1.0;
+            const double d0 = 0.25 * sa * (1.0 + ta * ys), d1 = 0.25 * ta * (1.0 + sa * xs);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                J[i][0] = fma(x[a][i], d0, J[i][0]);
+                J[i][1] = fma(x[a][i], d1, J[i][1]);
+            }
+        }
+        const double wd = w * (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double na = wd * N[a];
+#pragma unroll
+            for (int b = a; b < 8; ++b, ++t) Me[t] = fma(na, N[b], Me[t]);
+        }
+    }
+    const ThOut<8> W(map, e);
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+#pragma unroll
+        for (int b = a; b < 8; ++b, ++t) {
+            out[W.base[a] + b] = C * Me[t];
+            out[W.base[b] + a] = C * Me[t];
+        }
+        out[W.ld[a]] = 0.0;
+    }
+}
+
 __device__ __forceinline__ void elem_capacity_q1(int64_t e, const double *__restrict__ X,
                                                  const int32_t *__restrict__ conn, const double *__restrict__ kc,
                                                  const int32_t *__restrict__ map, double *__restrict__ out,

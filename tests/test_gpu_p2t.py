@@ -187,8 +187,8 @@ def test_unsupported_combinations(mf):
     prob = gen.thermal_p2t_problem(2)
     P = mf.Problem(prob)
     C = torch.ones(P.conn.shape[0], dtype=torch.float64, device="cuda")
-    with pytest.raises(mf.MFError) as ei:
-        mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, P.make_coeffs(coef=C), mf.MF_PREC_FP64, P.csr, P.d)
+    with pytest.raises(mf.MFError) as ei:  # the capacity form is FP64 only
+        mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, P.make_coeffs(coef=C), mf.MF_PREC_MIXED, P.csr, P.d)
     assert ei.value.status == mf.MF_ERR_UNSUPPORTED
     with pytest.raises(mf.MFError) as ei:
         mf.mf_pattern_build(P.mesh, mf.MF_FORM_ELASTIC)
@@ -253,3 +253,21 @@ def test_convection_on_faces_without_dirichlet_and_reproducible(mf, orc):
                      for el, fa in zip(e, f)])
     assert abs(area.sum() - 6.0) < 1e-12
     assert abs(v1.cpu().numpy().sum() - (fac["h"] * area).sum()) < 1e-11 * (fac["h"] * area).sum()
+
+
+def test_capacity_parity(mf, orc):
+    """The capacity form C int N_a N_b (the rate term of Sec. 4.1) against the oracle."""
+    import torch
+    prob = gen.thermal_p2t_problem(4)
+    P = mf.Problem(prob)
+    C = gen.lognormal(77, prob["conn"].shape[0], 0.3)
+    vals = torch.empty(P.nnz, dtype=torch.float64, device="cuda")
+    d = torch.empty(P.n, dtype=torch.float64, device="cuda")
+    csr = mf.CSR(P.csr.n_rows, P.csr.nnz, P.csr.row_ptr, P.csr.col_idx, vals.data_ptr())
+    Ct = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    mf.mf_assemble(mf.MF_FORM_CAPACITY, P.mesh, P.pattern, P.make_coeffs(coef=Ct, bc=False), mf.MF_PREC_FP64, csr, d)
+    rp, ci = P.csr_arrays()
+    ref = orc.capacity(prob, C)
+    assert np.array_equal(rp.cpu().numpy(), ref["row_ptr"]) and np.array_equal(ci.cpu().numpy(), ref["col"])
+    assert row_scaled_error(ref["row_ptr"], vals.cpu().numpy(), ref["val"]) <= TOL
+    assert (d.cpu().numpy() == 0).all()
