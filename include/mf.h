@@ -182,8 +182,9 @@ mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *patte
 /* form = MF_FORM_CAPACITY (prec FP64, on a thermal pattern) assembles the
  * capacity matrix of the rate term -C(T, T_t) of Sec. 4.1, K[a][b] =
  * sum_e C_e int_e N_a N_b with C_e = elem_coef[e], exactly on affine elements
- * (P1, P2: closed forms; Q1: 2 x 2 x 2 Gauss), and d = 0 (then the Dirichlet
- * elimination if bc_mask is given). */
+ * (P1, P2, P2T: closed forms; Q1: 2 x 2 x 2 Gauss; Q2S_QUAD: 3 x 3 Gauss;
+ * not provided on Q2S bricks), and d = 0 (then the Dirichlet elimination if
+ * bc_mask is given). */
 
 /* ---- Boundary (facet) terms -----------------------------------------------
  * A boundary condition is the domain physics one dimension lower (Sec. 2.2):
