@@ -72,6 +72,10 @@ def lib():
         _lib.or_elem_elastic.restype = d
         _lib.or_elem_oseen.argtypes = [vp, vp, d, d, vp, vp, vp, vp]
         _lib.or_elem_oseen.restype = d
+        _lib.or_elem_ns.argtypes = [vp, vp, vp, d, d, d, d, vp, vp]
+        _lib.or_elem_ns.restype = d
+        _lib.or_ns_system.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, d, d, d, d, vp, vp, vp, vp]
+        _lib.or_ns_system.restype = d
         _lib.or_elem_capacity.argtypes = [i, vp, d, vp]
         _lib.or_elem_capacity.restype = d
         _lib.or_genalpha.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, d, d, d, i64, d, i, d,
@@ -167,6 +171,67 @@ def elem_oseen(X, aN, mu: float, rho: float):
     Mp = np.zeros(3)
     det = lib().or_elem_oseen(_p(X), _p(aN), mu, rho, _p(A), _p(BT), _p(B), _p(Mp))
     return A, BT, B, Mp, det
+
+
+def elem_ns(X, U, P, mu: float, rho: float, tau_m: float, tau_c: float):
+    """Steady Navier-Stokes with SUPG on one Taylor-Hood triangle (Sec. 4.3):
+    residual r[15] (velocity dof (a, i) at 2a + i, pressure vertex b at
+    12 + b), tangent Ke[15, 15] by complex step, detJ.  U [6][2], P [3]."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    r = np.zeros(15)
+    Ke = np.zeros((15, 15))
+    det = lib().or_elem_ns(_p(X), _p(U), _p(P), mu, rho, tau_m, tau_c, _p(r), _p(Ke))
+    return r, Ke, det
+
+
+def ns_system(prob: dict, x, tau_m: float, tau_c: float):
+    """Residual R and tangent K (scipy CSR, duplicates summed) of the
+    Navier-Stokes form with SUPG at the state x = [u1 | u2 | p] on a
+    Taylor-Hood problem (``prob`` as gen.oseen_problem: coords, conn, vconn,
+    viscosity, rho).  No Dirichlet elimination."""
+    import scipy.sparse as sp
+    coords = np.ascontiguousarray(prob["coords"], dtype=np.float64)
+    conn = np.ascontiguousarray(prob["conn"], dtype=np.int32)
+    pconn = np.ascontiguousarray(prob["vconn"], dtype=np.int32)
+    n2, n1, ne = coords.shape[0], prob["vcoords"].shape[0], conn.shape[0]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    u1, u2, p = x[:n2].copy(), x[n2:2 * n2].copy(), x[2 * n2:].copy()
+    R = np.zeros(2 * n2 + n1)
+    rows = np.zeros(225 * ne, dtype=np.int64)
+    cols = np.zeros(225 * ne, dtype=np.int32)
+    vals = np.zeros(225 * ne)
+    mindet = lib().or_ns_system(n2, n1, ne, _p(coords), _p(conn), _p(pconn), _p(u1), _p(u2), _p(p),
+                                prob["viscosity"], prob["rho"], tau_m, tau_c, _p(R), _p(rows), _p(cols), _p(vals))
+    if not mindet > 0:
+        raise AssemblyError("element with detJ <= 0")
+    n = 2 * n2 + n1
+    K = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    K.sum_duplicates()
+    return R, K
+
+
+def ns_newton(prob: dict, tau_m: float, tau_c: float, tol: float = 1e-11, maxit: int = 30, x0=None):
+    """Newton-Raphson (Sec. 2.1) on the Navier-Stokes form with SUPG: from
+    x0 (default: the Dirichlet values, zero elsewhere), dofs in bc_mask held
+    at bc_val, K dx = -R on the free dofs (a sparse direct solve) until
+    ||R_free|| <= tol max(1, ||R_free(x0)||).  Returns (x, residual norms)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    mask = np.asarray(prob["bc_mask"]) > 0
+    x = np.where(mask, prob["bc_val"], 0.0) if x0 is None else np.where(mask, prob["bc_val"], x0)
+    free = np.flatnonzero(~mask)
+    hist = []
+    for _ in range(maxit):
+        R, K = ns_system(prob, x, tau_m, tau_c)
+        rn = np.linalg.norm(R[free])
+        hist.append(rn)
+        if rn <= tol * max(1.0, hist[0]):
+            break
+        Kff = K[free][:, free].tocsc()
+        x[free] += spla.spsolve(Kff, -R[free])
+    return x, hist
 
 
 def elem_capacity(elem: int, X, C: float):

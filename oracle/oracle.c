@@ -21,6 +21,7 @@
  * Pins: every routine here is checked by tests/test_oracle_pins.py against
  * closed forms, exact rational integration, invariants and dense solves.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -29,7 +30,7 @@
 /* element kinds */
 enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2, OR_Q2S = 3, OR_P2T = 4, OR_Q2Q = 5 };
 /* quadrature kinds */
-enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3, OR_QTET64 = 4, OR_QQUAD9 = 5 };
+enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3, OR_QTET64 = 4, OR_QQUAD9 = 5, OR_QTRI16 = 6 };
 /* forms */
 enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2, OR_CAPACITY = 3 };
 
@@ -98,6 +99,22 @@ int or_quad(int kind, double *pts, double *w)
             w[q] = 0.125 * w4[i] * w4[j] * w4[k] * (1.0 - S) * (1.0 - S) * (1.0 - T);
         }
         return 64;
+    }
+    if (kind == OR_QTRI16) {
+        /* reference triangle as the image of the unit square under x = s,
+         * y = t (1 - s) (Jacobian 1 - s), 4-point Gauss-Legendre in s and t:
+         * exact to total degree 6.  Point q = i + 4 j. */
+        const double a = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0));
+        const double b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+        const double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
+        const double x4[4] = {-b, -a, a, b}, w4[4] = {wb, wa, wa, wb};
+        for (int q = 0; q < 16; ++q) {
+            const double S = 0.5 * (x4[q % 4] + 1.0), T = 0.5 * (x4[q / 4] + 1.0);
+            pts[2 * q + 0] = S;
+            pts[2 * q + 1] = T * (1.0 - S);
+            w[q] = 0.25 * w4[q % 4] * w4[q / 4] * (1.0 - S);
+        }
+        return 16;
     }
     if (kind == OR_QQUAD9) {
         /* [-1, 1]^2, 3 x 3 Gauss-Legendre (0, +-sqrt(3/5); 8/9, 5/9), q = i + 3 j */
@@ -454,6 +471,142 @@ double or_elem_elastic_q1(const double *X, double E, double nu, const double *bo
                           double *Ke, double *de)
 {
     return or_elem_elastic(OR_Q1, X, E, nu, body, Ke, de);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Steady Navier-Stokes with SUPG on one Taylor-Hood P2-P1 triangle (Sec.    */
+/* 4.3), the domain form as the paper writes it, with test functions v      */
+/* (velocity) and q (pressure):                                             */
+/*   -rho(v_i,j, u_i u_j) - (v_i,i, p) + (q, u_i,i) + mu(v_i,j, u_i,j)        */
+/*   + tau_m rho(v_i,j, Rm_i u_j) + tau_m(q_,i, Rm_i) + tau_c(v_i,i, Rc),     */
+/*   Rc = u_k,k,  Rm_i = rho u_k u_i,k + p_,i - mu u_i,kk.                    */
+/* Element residual r[15]: velocity dof (a, i) at 2a + i (a < 6, i < 2),     */
+/* pressure vertex b at 12 + b; u_i,kk is the constant Laplacian of the P2   */
+/* basis on the affine triangle.  The 16-point rule (degree 6) integrates    */
+/* every term exactly.  Complex arithmetic so that the tangent can be taken  */
+/* by complex-step differentiation (exact to rounding: the residual is a     */
+/* polynomial in the dofs).  Returns detJ.                                   */
+/* ------------------------------------------------------------------------ */
+static double ns_residual(const double *X, const double complex *U, const double complex *P, double mu,
+                          double rho, double tm, double tc, double complex *r)
+{
+    double pts[32], w[16];
+    const int nq = or_quad(OR_QTRI16, pts, w);
+    /* affine map of the vertices: gradients of the barycentrics l0, l1, l2 */
+    const double j00 = X[2] - X[0], j10 = X[3] - X[1], j01 = X[4] - X[0], j11 = X[5] - X[1];
+    const double det = j00 * j11 - j01 * j10;
+    const double gl[3][2] = {{(-j11 + j10) / det, (j01 - j00) / det}, {j11 / det, -j01 / det}, {-j10 / det, j00 / det}};
+    /* P2 basis: vertices l_v (2 l_v - 1), edges (0,1), (1,2), (2,0): 4 l_p l_q;
+     * constant Laplacians */
+    const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    double lap[6];
+    for (int v = 0; v < 3; ++v) lap[v] = 4.0 * (gl[v][0] * gl[v][0] + gl[v][1] * gl[v][1]);
+    for (int e = 0; e < 3; ++e) {
+        const int pp = ep[e][0], qq = ep[e][1];
+        lap[3 + e] = 8.0 * (gl[pp][0] * gl[qq][0] + gl[pp][1] * gl[qq][1]);
+    }
+    for (int k = 0; k < 15; ++k) r[k] = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        const double l[3] = {1.0 - pts[2 * q] - pts[2 * q + 1], pts[2 * q], pts[2 * q + 1]};
+        double N[6], g[6][2];
+        for (int v = 0; v < 3; ++v) {
+            N[v] = l[v] * (2.0 * l[v] - 1.0);
+            for (int k = 0; k < 2; ++k) g[v][k] = (4.0 * l[v] - 1.0) * gl[v][k];
+        }
+        for (int e = 0; e < 3; ++e) {
+            const int pp = ep[e][0], qq = ep[e][1];
+            N[3 + e] = 4.0 * l[pp] * l[qq];
+            for (int k = 0; k < 2; ++k) g[3 + e][k] = 4.0 * (gl[pp][k] * l[qq] + l[pp] * gl[qq][k]);
+        }
+        double complex u[2] = {0.0, 0.0}, du[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, lu[2] = {0.0, 0.0};
+        double complex ph = 0.0, dp[2] = {0.0, 0.0};
+        for (int a = 0; a < 6; ++a)
+            for (int i = 0; i < 2; ++i) {
+                u[i] += N[a] * U[2 * a + i];
+                for (int k = 0; k < 2; ++k) du[i][k] += g[a][k] * U[2 * a + i];
+                lu[i] += lap[a] * U[2 * a + i];
+            }
+        for (int b = 0; b < 3; ++b) {
+            ph += l[b] * P[b];
+            for (int k = 0; k < 2; ++k) dp[k] += gl[b][k] * P[b];
+        }
+        const double complex Rc = du[0][0] + du[1][1];
+        double complex Rm[2];
+        for (int i = 0; i < 2; ++i) Rm[i] = rho * (u[0] * du[i][0] + u[1] * du[i][1]) + dp[i] - mu * lu[i];
+        const double wd = w[q] * det;
+        for (int a = 0; a < 6; ++a) {
+            const double complex adv = g[a][0] * u[0] + g[a][1] * u[1]; /* v_i,j u_j for v = N_a e_i */
+            for (int i = 0; i < 2; ++i) {
+                double complex t = -rho * adv * u[i] - g[a][i] * ph + mu * (g[a][0] * du[i][0] + g[a][1] * du[i][1]);
+                t += tm * rho * adv * Rm[i] + tc * g[a][i] * Rc;
+                r[2 * a + i] += wd * t;
+            }
+        }
+        for (int b = 0; b < 3; ++b)
+            r[12 + b] += wd * (l[b] * Rc + tm * (gl[b][0] * Rm[0] + gl[b][1] * Rm[1]));
+    }
+    return det;
+}
+
+/* Residual r[15] and tangent Ke[15][15] = d r / d (u, p) at the element
+ * state U [6][2] (velocity, node-major), P [3] (vertex pressures), the
+ * tangent column c by a complex step of 1e-30 in dof c.  Returns detJ. */
+double or_elem_ns(const double *X, const double *U, const double *P, double mu, double rho, double tm,
+                  double tc, double *r, double *Ke)
+{
+    double complex Uc[12], Pc[3], rc[15];
+    for (int k = 0; k < 12; ++k) Uc[k] = U[k];
+    for (int k = 0; k < 3; ++k) Pc[k] = P[k];
+    const double det = ns_residual(X, Uc, Pc, mu, rho, tm, tc, rc);
+    for (int k = 0; k < 15; ++k) r[k] = creal(rc[k]);
+    const double h = 1e-30;
+    for (int c = 0; c < 15; ++c) {
+        if (c < 12) Uc[c] += I * h; else Pc[c - 12] += I * h;
+        ns_residual(X, Uc, Pc, mu, rho, tm, tc, rc);
+        for (int k = 0; k < 15; ++k) Ke[15 * k + c] = cimag(rc[k]) / h;
+        if (c < 12) Uc[c] = U[c]; else Pc[c - 12] = P[c - 12];
+    }
+    return det;
+}
+
+/* The global system of the Navier-Stokes form: dofs [u1 (n2) | u2 (n2) |
+ * p (n1)]; R [2 n2 + n1] accumulates the element residuals; the tangent goes
+ * out as 225 triplets per element (rows, cols, vals [n_el * 225], duplicates
+ * to be summed).  Returns the minimum detJ (<= 0: an inverted element). */
+double or_ns_system(int64_t n2, int64_t n1, int64_t n_el, const double *coords, const int32_t *conn,
+                    const int32_t *pconn, const double *u1, const double *u2, const double *p, double mu,
+                    double rho, double tm, double tc, double *R, int64_t *rows, int32_t *cols, double *vals)
+{
+    double mindet = 1e300;
+    for (int64_t k = 0; k < 2 * n2 + n1; ++k) R[k] = 0.0;
+    for (int64_t e = 0; e < n_el; ++e) {
+        const int32_t *cn = conn + 6 * e, *pn = pconn + 3 * e;
+        double X[6], U[12], P[3], r[15], Ke[225];
+        int64_t dof[15];
+        for (int v = 0; v < 3; ++v)
+            for (int i = 0; i < 2; ++i) X[2 * v + i] = coords[2 * (int64_t)cn[v] + i];
+        for (int a = 0; a < 6; ++a) {
+            U[2 * a] = u1[cn[a]];
+            U[2 * a + 1] = u2[cn[a]];
+            dof[2 * a] = cn[a];
+            dof[2 * a + 1] = n2 + cn[a];
+        }
+        for (int b = 0; b < 3; ++b) {
+            P[b] = p[pn[b]];
+            dof[12 + b] = 2 * n2 + pn[b];
+        }
+        const double det = or_elem_ns(X, U, P, mu, rho, tm, tc, r, Ke);
+        if (det < mindet) mindet = det;
+        for (int k = 0; k < 15; ++k) {
+            R[dof[k]] += r[k];
+            for (int c = 0; c < 15; ++c) {
+                rows[225 * e + 15 * k + c] = dof[k];
+                cols[225 * e + 15 * k + c] = (int32_t)dof[c];
+                vals[225 * e + 15 * k + c] = Ke[15 * k + c];
+            }
+        }
+    }
+    return mindet;
 }
 
 /* ------------------------------------------------------------------------ */
