@@ -437,7 +437,7 @@ def box_facets(mesh: dict, sides=SIDES) -> tuple[np.ndarray, np.ndarray]:
         return np.concatenate(els), np.concatenate(faces)
     for side in sides:
         axis, hi = "xyz".index(side[0]), side[1] == "1"
-        if mesh["elem"] == "Q1":
+        if mesh["elem"] in ("Q1", "Q2S"):  # bricks: element (k n + j) n + i, face 2 axis + side
             k, j, i = np.meshgrid(r, r, r, indexing="ij")
             idx = (i, j, k)[axis].ravel()
             e = ((k * n + j) * n + i).ravel()[idx == (n - 1 if hi else 0)]

@@ -86,6 +86,7 @@ def lib():
         _lib.or_facet_thermal.argtypes = [i, vp, d, d, vp, vp]
         _lib.or_facet_thermal.restype = d
         _lib.or_facet_traction_q1.argtypes = [i, vp, vp, vp]
+        _lib.or_facet_traction.argtypes = [i, i, vp, vp, vp]
         _lib.or_assemble.argtypes = [C.POINTER(Problem)] + [C.POINTER(i64)] * 2 + [C.POINTER(vp)] * 5
         _lib.or_assemble.restype = i
         _lib.or_assemble_filtered.argtypes = [C.POINTER(Problem), vp, vp] + [C.POINTER(i64)] * 2 + \
@@ -245,7 +246,7 @@ def elem_capacity(elem: int, X, C: float):
 
 def facet_nodes(elem: int, face: int) -> list[int]:
     """Local element nodes of a facet, in facet node order."""
-    loc = np.zeros(6, dtype=np.int32)
+    loc = np.zeros(8, dtype=np.int32)
     nf = lib().or_facet_nodes(elem, face, _p(loc))
     if nf < 0:
         raise ValueError("no such face")
@@ -262,21 +263,18 @@ def facet_thermal(elem: int, Xf, h: float, t_env: float):
     return Kf, df, meas
 
 
-def facet_traction(face: int, Xf, sigma) -> np.ndarray:
-    """Loaded-boundary load of one hexahedron face: [4 facet nodes][3]."""
+def facet_traction(face: int, Xf, sigma, elem: int = None) -> np.ndarray:
+    """Loaded-boundary load of one brick face: [facet nodes][3] (4 for Q1,
+    the default, 8 for Q2S)."""
     Xf = np.ascontiguousarray(Xf, dtype=np.float64)
     sg = np.ascontiguousarray(sigma, dtype=np.float64).reshape(9)
-    df = np.zeros((4, 3))
-    lib().or_facet_traction_q1(face, _p(Xf), _p(sg), _p(df))
+    if elem is None or elem == Q1:
+        df = np.zeros((4, 3))
+        lib().or_facet_traction_q1(face, _p(Xf), _p(sg), _p(df))
+        return df
+    df = np.zeros((8, 3))
+    lib().or_facet_traction(elem, face, _p(Xf), _p(sg), _p(df))
     return df
-
-
-# ---------------------------------------------------------------------------
-# global level
-# ---------------------------------------------------------------------------
-
-class AssemblyError(RuntimeError):
-    pass
 
 
 def _default_quad(elem: str, form: str) -> int:

@@ -679,7 +679,30 @@ double or_elem_oseen(const double *X, const double *aN, double mu, double rho,
 /* ------------------------------------------------------------------------ */
 int or_facet_nodes(int elem, int face, int *loc)
 {
-    if (elem == OR_Q2S) return -1; /* no facet terms on serendipity bricks */
+    if (elem == OR_Q2S) {
+        /* face 2d + s as on the Q1 brick: its 4 vertices (bit d of a equal to
+         * s, ascending: face node i + 2j with i, j the bits of the face axes
+         * d1 < d2), then, in the 8-node quadrilateral's order, the midpoints
+         * of its d1 edges at bit d2 = j (4 + j) and of its d2 edges at bit
+         * d1 = i (6 + i).  The brick's edge along axis A whose other two
+         * coordinates B < C have bits b, c is node 8 + 4A + b + 2c. */
+        if (face < 0 || face > 5) return -1;
+        const int d = face / 2, s = face % 2;
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        int m = 0;
+        for (int a = 0; a < 8; ++a)
+            if (((a >> d) & 1) == s) loc[m++] = a;
+        for (int k = 0; k < 4; ++k) {
+            const int A = k < 2 ? d1 : d2;            /* the edge's axis */
+            const int other = k < 2 ? d2 : d1, ob = k & 1;
+            int bits[3];
+            bits[d] = s;
+            bits[other] = ob;
+            const int B = A == 0 ? 1 : 0, C = A == 2 ? 1 : 2;
+            loc[4 + k] = 8 + 4 * A + bits[B] + 2 * bits[C];
+        }
+        return 8;
+    }
     if (elem == OR_P2T) {
         /* face i is opposite vertex i: its vertices in the order that makes
          * (x1 - x0) x (x2 - x0) point outward for a positively oriented
@@ -720,6 +743,7 @@ int or_facet_nodes(int elem, int face, int *loc)
 static int facet_quad(int elem, double *pts, double *w)
 {
     if (elem == OR_Q2Q) elem = OR_P2;  /* straight 3-node edges */
+    if (elem == OR_Q2S) return or_quad(OR_QQUAD9, pts, w);  /* 8-node faces: 3 x 3 Gauss */
     if (elem == OR_P2T) return or_quad(OR_QTRI6, pts, w);
     if (elem == OR_P1) {
         const double g = 0.5 / sqrt(3.0);
@@ -781,6 +805,8 @@ static int facet_point(int elem, const double *Xf, const double *p, double *N, d
     }
     const double u = p[0], v = p[1];
     double xu[3] = {0.0, 0.0, 0.0}, xv[3] = {0.0, 0.0, 0.0};
+    double N8[8], dN8[16];
+    if (elem == OR_Q2S) or_shape(OR_Q2Q, p, N8, dN8);  /* the 8-node face basis */
     for (int m = 0; m < 4; ++m) {
         const double su = (m & 1) ? 1.0 : -1.0, sv = (m & 2) ? 1.0 : -1.0;
         N[m] = 0.25 * (1.0 + su * u) * (1.0 + sv * v);
@@ -793,6 +819,10 @@ static int facet_point(int elem, const double *Xf, const double *p, double *N, d
     A[0] = xu[1] * xv[2] - xu[2] * xv[1];
     A[1] = xu[2] * xv[0] - xu[0] * xv[2];
     A[2] = xu[0] * xv[1] - xu[1] * xv[0];
+    if (elem == OR_Q2S) {  /* the map stays the vertices' bilinear one (straight edges) */
+        for (int m = 0; m < 8; ++m) N[m] = N8[m];
+        return 8;
+    }
     return 4;
 }
 
@@ -802,16 +832,16 @@ static int facet_point(int elem, const double *Xf, const double *p, double *N, d
  * coordinates in facet node order.  Returns the facet's measure sum_q w |J|. */
 double or_facet_thermal(int elem, const double *Xf, double h, double tenv, double *Kf, double *df)
 {
-    double pts[12], w[6], N[6], A[3];
+    double pts[18], w[9], N[8], A[3];
     const int nq = facet_quad(elem, pts, w);
-    const int pdim = (elem == OR_Q1 || elem == OR_P2T) ? 2 : 1;
-    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 || elem == OR_Q2Q ? 3 : (elem == OR_Q1 ? 4 : 6));
+    const int pdim = (elem == OR_Q1 || elem == OR_P2T || elem == OR_Q2S) ? 2 : 1;
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 || elem == OR_Q2Q ? 3 : (elem == OR_Q1 ? 4 : (elem == OR_Q2S ? 8 : 6)));
     for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
     for (int a = 0; a < nf; ++a) df[a] = 0.0;
     double meas = 0.0;
     for (int q = 0; q < nq; ++q) {
         facet_point(elem, Xf, pts + pdim * q, N, A);
-        const double J = (elem == OR_Q1 || elem == OR_P2T) ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
+        const double J = (elem == OR_Q1 || elem == OR_P2T || elem == OR_Q2S) ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
         meas += w[q] * J;
         for (int a = 0; a < nf; ++a) {
             for (int b = 0; b < nf; ++b) Kf[a * nf + b] += w[q] * J * h * N[a] * N[b];
@@ -829,22 +859,29 @@ double or_facet_thermal(int elem, const double *Xf, double h, double tenv, doubl
  * +e_d (d = 0, 2) or -e_d (d = 1); the outward reference normal of face
  * 2d + s is (2s - 1) e_d; a map with detJ > 0 keeps orientation.  sigma is
  * row-major 3 x 3. */
-void or_facet_traction_q1(int face, const double *Xf, const double *sigma, double *df)
+void or_facet_traction(int elem, int face, const double *Xf, const double *sigma, double *df)
 {
-    double pts[12], w[6], N[6], A[3];
-    const int nq = facet_quad(OR_Q1, pts, w);
+    double pts[18], w[9], N[8], A[3];
+    const int nq = facet_quad(elem, pts, w);
+    const int nf = elem == OR_Q2S ? 8 : 4;
     const int d = face / 2, s = face % 2;
     const double o = (s ? 1.0 : -1.0) * (d == 1 ? -1.0 : 1.0);
-    for (int a = 0; a < 12; ++a) df[a] = 0.0;
+    for (int a = 0; a < 3 * nf; ++a) df[a] = 0.0;
     for (int q = 0; q < nq; ++q) {
-        facet_point(OR_Q1, Xf, pts + 2 * q, N, A);
-        for (int m = 0; m < 4; ++m)
+        facet_point(elem, Xf, pts + 2 * q, N, A);
+        for (int m = 0; m < nf; ++m)
             for (int i = 0; i < 3; ++i) {
                 double t = 0.0;
                 for (int j = 0; j < 3; ++j) t += sigma[3 * i + j] * o * A[j];
                 df[3 * m + i] += w[q] * N[m] * t;
             }
     }
+}
+
+/* The Q1 face of or_facet_traction: df [4][3]. */
+void or_facet_traction_q1(int face, const double *Xf, const double *sigma, double *df)
+{
+    or_facet_traction(OR_Q1, face, Xf, sigma, df);
 }
 
 /* Radiation on one facet (Sec. 4.1, e_m sigma^b (T, T_env^4 - T^4)) at the
@@ -855,16 +892,16 @@ void or_facet_traction_q1(int face, const double *Xf, const double *sigma, doubl
 void or_facet_radiation(int elem, const double *Xf, double es, double tenv, const double *Tf, double *Kf,
                         double *rf)
 {
-    double pts[12], w[6], N[6], A[3];
+    double pts[18], w[9], N[8], A[3];
     const int nq = facet_quad(elem, pts, w);
-    const int pdim = (elem == OR_Q1 || elem == OR_P2T) ? 2 : 1;
-    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 || elem == OR_Q2Q ? 3 : (elem == OR_Q1 ? 4 : 6));
+    const int pdim = (elem == OR_Q1 || elem == OR_P2T || elem == OR_Q2S) ? 2 : 1;
+    const int nf = elem == OR_P1 ? 2 : (elem == OR_P2 || elem == OR_Q2Q ? 3 : (elem == OR_Q1 ? 4 : (elem == OR_Q2S ? 8 : 6)));
     for (int a = 0; a < nf * nf; ++a) Kf[a] = 0.0;
     for (int a = 0; a < nf; ++a) rf[a] = 0.0;
     const double te4 = tenv * tenv * tenv * tenv;
     for (int q = 0; q < nq; ++q) {
         facet_point(elem, Xf, pts + pdim * q, N, A);
-        const double J = (elem == OR_Q1 || elem == OR_P2T) ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
+        const double J = (elem == OR_Q1 || elem == OR_P2T || elem == OR_Q2S) ? sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) : A[0];
         double T = 0.0;
         for (int b = 0; b < nf; ++b) T += N[b] * Tf[b];
         for (int a = 0; a < nf; ++a) {
@@ -1047,12 +1084,12 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
     }
     for (int64_t f = 0; f < p->n_facets; ++f) {
         const int64_t e = p->f_elem[f];
-        int loc[6];
+        int loc[8];
         if (e < 0 || e >= p->n_el) return -3;
         const int nf = or_facet_nodes(p->elem, p->f_face[f], loc);
         if (nf < 0 || p->form == OR_OSEEN || p->form == OR_CAPACITY) return -3;
-        int64_t node[6];
-        double Xf[18], Kf[36], df[18];
+        int64_t node[8];
+        double Xf[24], Kf[64], df[24];
         int hit = keep == NULL;
         for (int m = 0; m < nf; ++m) {
             node[m] = p->conn[e * npe + loc[m]];
@@ -1068,9 +1105,9 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
                 d[node[a]] += df[a];
             }
         } else {
-            if (p->elem != OR_Q1) return -3;
-            or_facet_traction_q1(p->f_face[f], Xf, p->f_stress + 9 * f, df);
-            for (int a = 0; a < 4; ++a)
+            if (p->elem != OR_Q1 && p->elem != OR_Q2S) return -3;
+            or_facet_traction(p->elem, p->f_face[f], Xf, p->f_stress + 9 * f, df);
+            for (int a = 0; a < nf; ++a)
                 for (int i = 0; i < 3; ++i) d[3 * node[a] + i] += df[3 * a + i];
         }
     }
@@ -1431,10 +1468,10 @@ static void radiation_terms(const or_radiation *rd, const int64_t *rp, const int
                             double *Fe, double *Tv, double scale)
 {
     for (int64_t f = 0; f < rd->n_facets; ++f) {
-        int loc[6];
+        int loc[8];
         const int nf = or_facet_nodes(rd->elem, rd->f_face[f], loc);
-        int64_t node[6];
-        double Xf[18], Tf[6], Kf[36], rf[6];
+        int64_t node[8];
+        double Xf[24], Tf[8], Kf[64], rf[8];
         for (int m = 0; m < nf; ++m) {
             node[m] = rd->conn[(int64_t)rd->f_elem[f] * rd->npe + loc[m]];
             Tf[m] = T[node[m]];
