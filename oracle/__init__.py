@@ -277,6 +277,14 @@ def facet_traction(face: int, Xf, sigma, elem: int = None) -> np.ndarray:
     return df
 
 
+# ---------------------------------------------------------------------------
+# global level
+# ---------------------------------------------------------------------------
+
+class AssemblyError(RuntimeError):
+    pass
+
+
 def _default_quad(elem: str, form: str) -> int:
     if elem == "Q1":
         return QHEX8
