@@ -75,6 +75,8 @@ def lib():
         _lib.or_elem_ns.argtypes = [vp, vp, vp, d, d, d, d, vp, vp]
         _lib.or_elem_ns.restype = d
         _lib.or_ns_system.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, d, d, d, d, vp, vp, vp, vp]
+        _lib.or_elem_ns3.argtypes = [vp, vp, vp, d, d, d, d, vp, vp]
+        _lib.or_elem_ns3.restype = d
         _lib.or_ns_system.restype = d
         _lib.or_elem_capacity.argtypes = [i, vp, d, vp]
         _lib.or_elem_capacity.restype = d
@@ -184,6 +186,20 @@ def elem_ns(X, U, P, mu: float, rho: float, tau_m: float, tau_c: float):
     r = np.zeros(15)
     Ke = np.zeros((15, 15))
     det = lib().or_elem_ns(_p(X), _p(U), _p(P), mu, rho, tau_m, tau_c, _p(r), _p(Ke))
+    return r, Ke, det
+
+
+def elem_ns3(X, U, P, mu: float, rho: float, tau_m: float, tau_c: float):
+    """The Navier-Stokes form with SUPG on one Taylor-Hood tetrahedron:
+    residual r[34] (velocity dof (a, i) at 3a + i, pressure vertex b at
+    30 + b), tangent Ke[34, 34] by complex step, detJ.  X: the 4 vertices;
+    U [10][3]; P [4]."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    r = np.zeros(34)
+    Ke = np.zeros((34, 34))
+    det = lib().or_elem_ns3(_p(X), _p(U), _p(P), mu, rho, tau_m, tau_c, _p(r), _p(Ke))
     return r, Ke, det
 
 

@@ -30,7 +30,7 @@
 /* element kinds */
 enum { OR_P1 = 0, OR_P2 = 1, OR_Q1 = 2, OR_Q2S = 3, OR_P2T = 4, OR_Q2Q = 5 };
 /* quadrature kinds */
-enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3, OR_QTET64 = 4, OR_QQUAD9 = 5, OR_QTRI16 = 6 };
+enum { OR_QTRI3 = 0, OR_QTRI6 = 1, OR_QHEX8 = 2, OR_QHEX27 = 3, OR_QTET64 = 4, OR_QQUAD9 = 5, OR_QTRI16 = 6, OR_QTET125 = 7 };
 /* forms */
 enum { OR_THERMAL = 0, OR_ELASTIC = 1, OR_OSEEN = 2, OR_CAPACITY = 3 };
 
@@ -99,6 +99,23 @@ int or_quad(int kind, double *pts, double *w)
             w[q] = 0.125 * w4[i] * w4[j] * w4[k] * (1.0 - S) * (1.0 - S) * (1.0 - T);
         }
         return 64;
+    }
+    if (kind == OR_QTET125) {
+        /* the collapsed map of OR_QTET64 with 5-point Gauss-Legendre (0,
+         * +-sqrt(5 -+ 2 sqrt(10/7)) / 3): exact to total degree 7.
+         * Point q = i + 5 j + 25 k. */
+        const double a = sqrt(5.0 - 2.0 * sqrt(10.0 / 7.0)) / 3.0, b = sqrt(5.0 + 2.0 * sqrt(10.0 / 7.0)) / 3.0;
+        const double wa = (322.0 + 13.0 * sqrt(70.0)) / 900.0, wb = (322.0 - 13.0 * sqrt(70.0)) / 900.0;
+        const double x5[5] = {-b, -a, 0.0, a, b}, w5[5] = {wb, wa, 128.0 / 225.0, wa, wb};
+        for (int q = 0; q < 125; ++q) {
+            const int i = q % 5, j = (q / 5) % 5, k = q / 25;
+            const double S = 0.5 * (x5[i] + 1.0), T = 0.5 * (x5[j] + 1.0), R = 0.5 * (x5[k] + 1.0);
+            pts[3 * q + 0] = S;
+            pts[3 * q + 1] = T * (1.0 - S);
+            pts[3 * q + 2] = R * (1.0 - S) * (1.0 - T);
+            w[q] = 0.125 * w5[i] * w5[j] * w5[k] * (1.0 - S) * (1.0 - S) * (1.0 - T);
+        }
+        return 125;
     }
     if (kind == OR_QTRI16) {
         /* reference triangle as the image of the unit square under x = s,
@@ -565,6 +582,113 @@ double or_elem_ns(const double *X, const double *U, const double *P, double mu, 
         ns_residual(X, Uc, Pc, mu, rho, tm, tc, rc);
         for (int k = 0; k < 15; ++k) Ke[15 * k + c] = cimag(rc[k]) / h;
         if (c < 12) Uc[c] = U[c]; else Pc[c - 12] = P[c - 12];
+    }
+    return det;
+}
+
+/* The same form on one Taylor-Hood P2-P1 tetrahedron (the 3D flow case of  */
+/* Sec. 4.3): velocity dof (a, i) at 3a + i (a < 10, i < 3), pressure       */
+/* vertex b at 30 + b; the 10-node basis (vertices, then edges (0,1), (1,2), */
+/* (2,0), (0,3), (1,3), (2,3)) on the affine element, its constant          */
+/* Laplacians, and the 125-point rule (exact: every term has degree <= 6).   */
+static double ns3_residual(const double *X, const double complex *U, const double complex *P, double mu,
+                           double rho, double tm, double tc, double complex *r)
+{
+    static double pts[375], w[125];
+    const int nq = or_quad(OR_QTET125, pts, w);
+    double J[3][3], Ji[3][3];
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) J[i][j] = X[3 * (j + 1) + i] - X[i];
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    Ji[0][0] = c00 / det;
+    Ji[1][0] = c01 / det;
+    Ji[2][0] = c02 / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    /* gradients of the barycentrics: l_{p+1} = xi_p, l_0 = 1 - sum */
+    double gl[4][3];
+    for (int k = 0; k < 3; ++k) {
+        gl[1][k] = Ji[0][k];
+        gl[2][k] = Ji[1][k];
+        gl[3][k] = Ji[2][k];
+        gl[0][k] = -(Ji[0][k] + Ji[1][k] + Ji[2][k]);
+    }
+    const int ep[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+    double lap[10];
+    for (int v = 0; v < 4; ++v) lap[v] = 4.0 * (gl[v][0] * gl[v][0] + gl[v][1] * gl[v][1] + gl[v][2] * gl[v][2]);
+    for (int e = 0; e < 6; ++e) {
+        const int pp = ep[e][0], qq = ep[e][1];
+        lap[4 + e] = 8.0 * (gl[pp][0] * gl[qq][0] + gl[pp][1] * gl[qq][1] + gl[pp][2] * gl[qq][2]);
+    }
+    for (int k = 0; k < 34; ++k) r[k] = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        const double l[4] = {1.0 - pts[3 * q] - pts[3 * q + 1] - pts[3 * q + 2], pts[3 * q], pts[3 * q + 1],
+                             pts[3 * q + 2]};
+        double N[10], g[10][3];
+        for (int v = 0; v < 4; ++v) {
+            N[v] = l[v] * (2.0 * l[v] - 1.0);
+            for (int k = 0; k < 3; ++k) g[v][k] = (4.0 * l[v] - 1.0) * gl[v][k];
+        }
+        for (int e = 0; e < 6; ++e) {
+            const int pp = ep[e][0], qq = ep[e][1];
+            N[4 + e] = 4.0 * l[pp] * l[qq];
+            for (int k = 0; k < 3; ++k) g[4 + e][k] = 4.0 * (gl[pp][k] * l[qq] + l[pp] * gl[qq][k]);
+        }
+        double complex u[3] = {0.0, 0.0, 0.0}, du[3][3] = {{0.0}}, lu[3] = {0.0, 0.0, 0.0};
+        double complex ph = 0.0, dp[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 10; ++a)
+            for (int i = 0; i < 3; ++i) {
+                u[i] += N[a] * U[3 * a + i];
+                for (int k = 0; k < 3; ++k) du[i][k] += g[a][k] * U[3 * a + i];
+                lu[i] += lap[a] * U[3 * a + i];
+            }
+        for (int b = 0; b < 4; ++b) {
+            ph += l[b] * P[b];
+            for (int k = 0; k < 3; ++k) dp[k] += gl[b][k] * P[b];
+        }
+        const double complex Rc = du[0][0] + du[1][1] + du[2][2];
+        double complex Rm[3];
+        for (int i = 0; i < 3; ++i)
+            Rm[i] = rho * (u[0] * du[i][0] + u[1] * du[i][1] + u[2] * du[i][2]) + dp[i] - mu * lu[i];
+        const double wd = w[q] * det;
+        for (int a = 0; a < 10; ++a) {
+            const double complex adv = g[a][0] * u[0] + g[a][1] * u[1] + g[a][2] * u[2];
+            for (int i = 0; i < 3; ++i) {
+                double complex t = -rho * adv * u[i] - g[a][i] * ph +
+                                   mu * (g[a][0] * du[i][0] + g[a][1] * du[i][1] + g[a][2] * du[i][2]);
+                t += tm * rho * adv * Rm[i] + tc * g[a][i] * Rc;
+                r[3 * a + i] += wd * t;
+            }
+        }
+        for (int b = 0; b < 4; ++b)
+            r[30 + b] += wd * (l[b] * Rc + tm * (gl[b][0] * Rm[0] + gl[b][1] * Rm[1] + gl[b][2] * Rm[2]));
+    }
+    return det;
+}
+
+/* Residual r[34] and tangent Ke[34][34] (complex step) of ns3_residual at
+ * U [10][3], P [4]; X holds the 4 vertices.  Returns detJ. */
+double or_elem_ns3(const double *X, const double *U, const double *P, double mu, double rho, double tm,
+                   double tc, double *r, double *Ke)
+{
+    double complex Uc[30], Pc[4], rc[34];
+    for (int k = 0; k < 30; ++k) Uc[k] = U[k];
+    for (int k = 0; k < 4; ++k) Pc[k] = P[k];
+    const double det = ns3_residual(X, Uc, Pc, mu, rho, tm, tc, rc);
+    for (int k = 0; k < 34; ++k) r[k] = creal(rc[k]);
+    const double h = 1e-30;
+    for (int c = 0; c < 34; ++c) {
+        if (c < 30) Uc[c] += I * h; else Pc[c - 30] += I * h;
+        ns3_residual(X, Uc, Pc, mu, rho, tm, tc, rc);
+        for (int k = 0; k < 34; ++k) Ke[34 * k + c] = cimag(rc[k]) / h;
+        if (c < 30) Uc[c] = U[c]; else Pc[c - 30] = P[c - 30];
     }
     return det;
 }

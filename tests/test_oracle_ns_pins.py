@@ -83,3 +83,78 @@ def test_newton_converges_quadratically_on_the_cavity(orc):
     # quadratic: once small, each residual is about the square of the previous
     small = [(a, b) for a, b in zip(hist[:-1], hist[1:]) if a < 1e-2 and b > 1e-15]
     assert small and all(b < 50.0 * a * a for a, b in small)
+
+
+# ---------------------------------------------------------------------------
+# the same form on Taylor-Hood tetrahedra (the 3D flow case)
+# ---------------------------------------------------------------------------
+
+def test_tetrahedron_tangent_matches_finite_differences(orc):
+    rng = np.random.default_rng(8)
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float) * 0.9 + rng.uniform(-0.1, 0.1, (4, 3))
+    U, P = rng.normal(size=(10, 3)), rng.normal(size=4)
+    r, Ke, det = orc.elem_ns3(V, U, P, MU, RHO, TM, TC)
+    assert det > 0
+    h = 1e-6
+    for c in (0, 7, 17, 29, 31):
+        Up, Um, Pp, Pm = U.copy(), U.copy(), P.copy(), P.copy()
+        if c < 30:
+            Up.flat[c] += h
+            Um.flat[c] -= h
+        else:
+            Pp[c - 30] += h
+            Pm[c - 30] -= h
+        fd = (orc.elem_ns3(V, Up, Pp, MU, RHO, TM, TC)[0] - orc.elem_ns3(V, Um, Pm, MU, RHO, TM, TC)[0]) / (2 * h)
+        assert np.abs(Ke[:, c] - fd).max() < 1e-7 * np.abs(Ke).max()
+
+
+def test_tetrahedra_poiseuille_is_an_exact_discrete_solution(orc):
+    m = gen.tet10_mesh(2, 0.1)
+    X, c = m["coords"], m["conn"]
+    nv = 27  # the (n + 1)^3 vertices come first: the P1 pressure nodes
+    n2 = X.shape[0]
+    u = np.zeros((n2, 3))
+    u[:, 0] = X[:, 1] * (1.0 - X[:, 1])
+    p = -2.0 * MU * X[:nv, 0] + 0.3
+    R = np.zeros(3 * n2 + nv)
+    scale = 0.0
+    for el in c:
+        r, _, _ = orc.elem_ns3(X[el[:4]], u[el], p[el[:4]], MU, RHO, TM, TC)
+        for a in range(10):
+            for i in range(3):
+                R[i * n2 + el[a]] += r[3 * a + i]
+        for b in range(4):
+            R[3 * n2 + el[b]] += r[30 + b]
+        scale = max(scale, np.abs(orc.elem_ns3(X[el[:4]], np.ones((10, 3)), np.ones(4), MU, RHO, TM, TC)[0]).max())
+    inner = ~gen.boundary_nodes(X)
+    for i in range(3):
+        assert np.abs(R[i * n2:(i + 1) * n2][inner]).max() < 1e-13 * scale
+    assert np.abs(R[3 * n2:]).max() < 1e-13 * scale
+
+
+def test_rotation_covariance(orc):
+    """Rotating the element and the nodal velocities rotates the velocity
+    residual and leaves the pressure residual unchanged (the form is built
+    from vectors and scalars only): catches a dropped or misplaced component."""
+    rng = np.random.default_rng(10)
+    # 2D
+    V, X = _tri(seed=9)
+    U, P = rng.normal(size=(6, 2)), rng.normal(size=3)
+    t = 0.7
+    Q = np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]])
+    r, _, _ = orc.elem_ns(V, U, P, MU, RHO, TM, TC)
+    rq, _, _ = orc.elem_ns(V @ Q.T, U @ Q.T, P, MU, RHO, TM, TC)
+    s = np.abs(r).max()
+    assert np.abs(rq[:12].reshape(6, 2) - r[:12].reshape(6, 2) @ Q.T).max() < 1e-13 * s
+    assert np.abs(rq[12:] - r[12:]).max() < 1e-13 * s
+    # 3D
+    V3 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float) * 0.9 + rng.uniform(-0.1, 0.1, (4, 3))
+    U3, P3 = rng.normal(size=(10, 3)), rng.normal(size=4)
+    Q3, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(Q3) < 0:
+        Q3[:, 0] *= -1.0  # a rotation keeps the vertex order positive
+    r, _, _ = orc.elem_ns3(V3, U3, P3, MU, RHO, TM, TC)
+    rq, _, _ = orc.elem_ns3(V3 @ Q3.T, U3 @ Q3.T, P3, MU, RHO, TM, TC)
+    s = np.abs(r).max()
+    assert np.abs(rq[:30].reshape(10, 3) - r[:30].reshape(10, 3) @ Q3.T).max() < 1e-12 * s
+    assert np.abs(rq[30:] - r[30:]).max() < 1e-12 * s
