@@ -170,11 +170,14 @@ mf_status mf_pattern_destroy(mf_pattern *pattern);
  * calls give bit-identical K and d), then the Dirichlet elimination.
  * K->values [nnz] and d [n_rows] are caller device buffers.  prec =
  * MF_PREC_FP64: FP64 element blocks summed node by node in ascending element
- * order.  prec = MF_PREC_MIXED (elasticity on Q1 only; needs lambda/mu =
- * 2nu/(1-2nu) = p/q with q <= 64): tensor-core element contraction on BF16
- * slices, blocks added as exact 64-bit fixed-point integers (integer atomics,
- * so the order does not change the bits), converted once to FP64; K within
- * about 2^-40 of the row scale of the FP64 result.  Errors:
+ * order.  prec = MF_PREC_MIXED (elasticity on Q1 only, any nu in (-1, 0.5)):
+ * tensor-core element contraction on BF16 slices of the mu-scaled gradients,
+ * blocks added as exact 64-bit fixed-point integers (integer atomics, so the
+ * order does not change the bits) at a scale taken from the current
+ * coordinates and coefficients in every call, then K = r A + A^T + I tr A
+ * per CSR block with r = lambda/mu = 2nu/(1-2nu) as an exact 53-bit
+ * multiplier, converted once to FP64; K within about 2^-40 of the row scale
+ * of the FP64 result.  Errors:
  * MF_ERR_INVALID_ARG, MF_ERR_UNSUPPORTED, MF_ERR_CUDA; non-finite
  * coefficients are latched (MF_ERR_NONFINITE). */
 mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,

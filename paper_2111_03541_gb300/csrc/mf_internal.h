@@ -89,9 +89,6 @@ struct mf_pattern {
     int64_t *cbase = nullptr;
     int64_t n_upper = 0;
     long long *dacc = nullptr;  // int64 load vector accumulator (3 per node)
-    // mixed path: geometry part of the fixed-point bound per element, and the
-    // largest element volume at [n_elems] (see mf_mixed.cu)
-    float *mixed_geo = nullptr;
     // mixed path: device scalars of the fixed-point scale (see mf_mixed.cu)
     void *mixed_state = nullptr;
     // elasticity slabs: element chunk c = [slab_e[c], slab_e[c+1]) completes the
@@ -163,8 +160,6 @@ mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_c
                                double p_scale, double *out, cudaStream_t st);
 // elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64
 // sums of the mixed path's A'' blocks finished as K = fp A + fq (A^T + I tr A)
-// mixed elasticity: per-element geometry bound, once per pattern
-mf_status mf_mixed_geometry(const mf_mesh *m, mf_pattern *p, cudaStream_t st);
 // reference sums of the P2 integrands (flow form, P2 thermal) and the 20-node
 // brick's reference table, in the current device's copies of mf_assemble.cu
 // (once per such pattern build)

@@ -4,30 +4,36 @@
 // the tangent negated) is, per block pair (a, b) of nodes,
 //   K_ab[c][c'] = lambda A_ab[c][c'] + mu A_ab[c'][c] + mu delta_cc' tr A_ab,
 //   A_ab[c][c'] = sum_q w_q detJ_q d_c N_a(q) d_c' N_b(q).
-// With mu = E / (2 (1 + nu)) and lambda / mu = r = 2 nu / (1 - 2 nu) = p / q
-// (small integers, found on the host), scale the gradients
-//   G[(a,c), q] = sqrt(mu w_q detJ_q / q) d_c N_a(q)          (24 x 8)
-// so that A'' = G G^T and  K_e = p A'' + q swap(A'') + q I tr(A'') exactly.
+// With mu_e = E_e / (2 (1 + nu)) and lambda / mu = r = 2 nu / (1 - 2 nu) (the
+// same for every element), scale the gradients
+//   G[(a,c), q] = sqrt(mu_e w_q detJ_q) d_c N_a(q)                  (24 x 8)
+// so that A'' = G G^T and K_e = r A'' + swap(A'') + I tr(A''); that map is
+// linear, so it is applied once per CSR block after the element sums, with r
+// held exactly as a 53-bit integer times a power of two (any nu).
 //
-// Precision plan (GB300 runs FP64 at 1/58 of FP32):
+// Precision plan (GB300 runs FP64 at 1/64 of FP32):
 //  * geometry (Jacobian, cofactors, detJ, scale, gradients) in double-float
 //    arithmetic (pairs of FP32, ~44 bits), one lane per (element, Gauss point),
 //    from FP64 coordinate differences;
-//  * G is split into 5 BF16 slices of 8 bits with one exponent per row
+//  * G is split into 5 BF16 slices of 8 bits with one exponent per element
 //    (Ozaki, Ogita, Oishi & Rump 2012): every slice product summed over the 8
-//    points is an exact integer in FP32, so each level L = s + t of the
-//    slice pairs accumulates exactly on the tensor cores (mma.sync m16n8k16,
-//    bf16 in, fp32 accumulate);
-//  * the levels are combined into 64-bit fixed point at a global scale 2^S
-//    (chosen by a pre-pass so no sum can overflow) and added with integer
-//    atomics into one 3x3 block per node pair (n <= m; the lower pairs are
+//    points is an exact integer in FP32, so each level L = s + t of the slice
+//    pairs accumulates exactly on the tensor cores (mma.sync m16n8k16, bf16
+//    in, fp32 accumulate; fragments by ldmatrix);
+//  * the levels are combined into 64-bit fixed point at a global scale 2^S,
+//    chosen per assembly by an FP32 pre-pass over the current coordinates and
+//    coefficients so that no sum can overflow, and added with integer atomics
+//    into one 3x3 block per node pair (n <= m; the lower pairs are
 //    transposes): integer sums are exact, so the result does not depend on
-//    the order the atomics land in; a node-centric finishing pass applies the
-//    (linear) p, q finishing once per CSR block, converts each value once to
-//    FP64 and eliminates the Dirichlet dofs.
-// The dropped levels (s + t > 4) bound the error at about 2^-40 of the row
-// scale; the solution error against the FP64 path is measured per run.
+//    the order the atomics land in; a node-centric finishing pass applies
+//    r A + A^T + I tr A once per CSR block, converts each value once to FP64
+//    and eliminates the Dirichlet dofs.
+// The dropped levels (s + t > 4) bound the error at about 2^-40 of the
+// element's scale; the solution error against the FP64 path is measured per
+// run.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "mf_internal.h"
 
@@ -146,87 +152,87 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 }
 
 // ---------------------------------------------------------------------------
-// pre-pass: bound of the fixed-point values (FP32 geometry is enough for a bound)
+// pre-pass (per assembly, from the current coordinates and coefficients):
+// bound of the fixed-point values, FP32 geometry is enough for a bound
 // ---------------------------------------------------------------------------
-// geometry part of the bound, once per mesh: geo[e] = max_row sum_q G^2 of
-// element e for E cmu / q = 1, and geo[n_el] = max_e sum_q detJ_q (float bits)
-__global__ void k_mixed_geom(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
-                             float *__restrict__ geo)
+// mx = max over elements of mu_e max_row sum_q G^2 / mu_e-free geometry,
+// vol = max over elements of sum_q |detJ_q| (float bits, atomicMax on
+// non-negative floats orders like the integers)
+__global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
+                              const double *__restrict__ Ec, float cmu, MixedState *st, int *status)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_el) return;
-    float x[8][3];
-    const int32_t *cn = conn + 8 * e;
-    for (int a = 0; a < 8; ++a)
-        for (int i = 0; i < 3; ++i) x[a][i] = (float)(X[3 * (int64_t)cn[a] + i] - X[3 * (int64_t)cn[0] + i]);
-    const float g = (float)GD;
-    float rowsum[24] = {};
-    float vol = 0.f;
-    for (int q = 0; q < 8; ++q) {
-        const float xs[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
-        float J[3][3] = {}, dN[8][3];
-        for (int a = 0; a < 8; ++a) {
-            const float s[3] = {(a & 1) ? 1.f : -1.f, (a & 2) ? 1.f : -1.f, (a & 4) ? 1.f : -1.f};
-            const float f[3] = {1.f + s[0] * xs[0], 1.f + s[1] * xs[1], 1.f + s[2] * xs[2]};
-            dN[a][0] = 0.125f * s[0] * f[1] * f[2];
-            dN[a][1] = 0.125f * f[0] * s[1] * f[2];
-            dN[a][2] = 0.125f * f[0] * f[1] * s[2];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) J[i][j] += x[a][i] * dN[a][j];
-        }
-        float C[3][3];
-        C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-        C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-        C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-        C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-        C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-        C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-        C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-        C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-        C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-        const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-        vol += fabsf(det);
-        const float sc = 1.0f / det;  // G^2 = (mu / (q det)) (sum_j dN_j C[c][j])^2, mu / q = 1
-        for (int a = 0; a < 8; ++a)
-            for (int c = 0; c < 3; ++c) {
-                const float v = dN[a][0] * C[c][0] + dN[a][1] * C[c][1] + dN[a][2] * C[c][2];
-                rowsum[3 * a + c] += sc * v * v;
-            }
-    }
-    float mx = 0.f;
-    for (int r = 0; r < 24; ++r) mx = fmaxf(mx, rowsum[r]);
-    geo[e] = mx;
-    atomicMax(reinterpret_cast<int *>(geo + n_el), __float_as_int(vol));
-}
-
-// per assembly: the bound max_e E_e cmu / q geo[e] (one atomic per warp)
-__global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ Ec, const float *__restrict__ geo,
-                              float cmu_q, MixedState *st, int *status)
-{
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float mx = 0.f;
+    float mx = 0.f, vol = 0.f;
     if (e < n_el) {
+        float x[8][3];
+        const int32_t *cn = conn + 8 * e;
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i) x[a][i] = (float)(X[3 * (int64_t)cn[a] + i] - X[3 * (int64_t)cn[0] + i]);
+        const float g = (float)GD;
+        float rowsum[24] = {};
+        for (int q = 0; q < 8; ++q) {
+            const float xs[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+            float J[3][3] = {}, dN[8][3];
+            for (int a = 0; a < 8; ++a) {
+                const float s[3] = {(a & 1) ? 1.f : -1.f, (a & 2) ? 1.f : -1.f, (a & 4) ? 1.f : -1.f};
+                const float f[3] = {1.f + s[0] * xs[0], 1.f + s[1] * xs[1], 1.f + s[2] * xs[2]};
+                dN[a][0] = 0.125f * s[0] * f[1] * f[2];
+                dN[a][1] = 0.125f * f[0] * s[1] * f[2];
+                dN[a][2] = 0.125f * f[0] * f[1] * s[2];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) J[i][j] += x[a][i] * dN[a][j];
+            }
+            float C[3][3];
+            C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+            C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+            C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+            C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+            C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+            C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+            vol += fabsf(det);
+            const float sc = 1.0f / fabsf(det);  // G^2 = (mu / det) (sum_j dN_j C[c][j])^2 per mu
+            for (int a = 0; a < 8; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    const float v = dN[a][0] * C[c][0] + dN[a][1] * C[c][1] + dN[a][2] * C[c][2];
+                    rowsum[3 * a + c] += sc * v * v;
+                }
+        }
+        for (int r = 0; r < 24; ++r) mx = fmaxf(mx, rowsum[r]);
         const double E = Ec[e];
-        if (!isfinite(E) || !(E > 0.0)) mf_dev_fail(status, MF_ERR_NONFINITE);
-        else mx = (float)E * cmu_q * geo[e];
+        if (!isfinite(E) || !(E > 0.0)) {
+            mf_dev_fail(status, MF_ERR_NONFINITE);
+            mx = 0.f;
+        } else {
+            mx *= (float)E * cmu;
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        vol = fmaxf(vol, __shfl_xor_sync(0xffffffffu, vol, o));
+    }
     if ((threadIdx.x & 31) == 0) {
-        if (!isfinite(mx)) mf_dev_fail(status, MF_ERR_NONFINITE);
-        else if (mx > 0.f) atomicMax(&st->mx_bits, __float_as_int(mx));
+        if (!isfinite(mx) || !isfinite(vol)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        else {
+            if (mx > 0.f) atomicMax(&st->mx_bits, __float_as_int(mx));
+            if (vol > 0.f) atomicMax(&st->vol_bits, __float_as_int(vol));
+        }
     }
-    if (e == 0) st->vol_bits = __float_as_int(geo[n_el]);
 }
 
-// S = floor(62 - log2(8 (p + 4q) Mx 1.25)): every element value |K_e| <=
-// (p + 4q) Mx 2^S and a CSR entry sums at most 8 of them, below 2^62.  The
-// load entries are |b_c| sum_q detJ_q N_a(q) <= |b|max vol: Sd likewise.
-__global__ void k_mixed_scale(MixedState *st, int p, int q, double bmax)
+// S = floor(62 - log2(MF_MAX_INC (|r| + 4) Mx 1.25)): every element value
+// |K_e| <= (|r| + 4) Mx 2^S and a CSR entry sums at most MF_MAX_INC of them,
+// below 2^62.  The load entries are |b_c| sum_q detJ_q N_a(q) <= |b|max vol:
+// Sd likewise.
+__global__ void k_mixed_scale(MixedState *st, double rabs, double bmax)
 {
     const float mx = __int_as_float(st->mx_bits);
-    st->S = (int)floor(62.0 - log2(8.0 * (p + 4.0 * q) * (double)mx * 1.25));
+    st->S = (int)floor(62.0 - log2((double)MF_MAX_INC * (rabs + 4.0) * (double)mx * 1.25));
     const double bv = bmax * (double)__int_as_float(st->vol_bits);
-    st->Sd = bv > 0.0 ? (int)floor(62.0 - log2(8.0 * bv * 1.25)) : 0;
+    st->Sd = bv > 0.0 ? (int)floor(62.0 - log2((double)MF_MAX_INC * bv * 1.25)) : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -234,18 +240,18 @@ __global__ void k_mixed_scale(MixedState *st, int p, int q, double bmax)
 // ---------------------------------------------------------------------------
 struct WarpSmem {
     __nv_bfloat16 sl[4][NSL][SL_ROWS][8];  // slices of G per element: [slice][row (a,c)][point]
-    int ex[4][SL_ROWS];                     // row exponents
+    int ex[4];                              // element exponents
     int32_t tgt[4][36];                     // accumulator pair of block (a <= b); bit 31: transposed
 };
 
-__global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
+__global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
     int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn,
     const double *__restrict__ Ec,
-    double cmu_q, double b0, double b1, double b2, const MixedState *__restrict__ st,
+    double cmu, double b0, double b1, double b2, const MixedState *__restrict__ st,
     const int64_t *__restrict__ cbase, const uint8_t *__restrict__ slot, unsigned long long *__restrict__ kacc,
     unsigned long long *__restrict__ dacc, int *status)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // WarpSmem per warp (16-byte rows)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpSmem &W = reinterpret_cast<WarpSmem *>(smem_raw)[w];
     const int j = lane >> 3;   // element slot of this lane
@@ -310,14 +316,14 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
     Cf[2][2] = dsub(dmul(J[0][0], J[1][1]), dmul(J[0][1], J[1][0]));
     const f2 det = dadd(dadd(dmul(J[0][0], Cf[0][0]), dmul(J[0][1], Cf[0][1])), dmul(J[0][2], Cf[0][2]));
 
-    // --- scale sqrt(mu / (q det)) with mu / q = E cmu / q ---
+    // --- scale sqrt(mu_e / det), mu_e = E cmu ---
     const double E = Ec[e];
     if (valid && !isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
-    const f2 sig = dsqrt(ddiv(from_double(E * cmu_q), det));
+    const f2 sig = dsqrt(ddiv(from_double(E * cmu), det));
     // G[(a,c), qp] = sig sum_j d_j N_a(qp) Cf[c][j], sum-factorised over the
-    // three factor products P^2/8, PM/8, M^2/8; one component c at a time:
-    // build the 8 values, take the row exponents (max over the 8 points of the
-    // element), split into 8-bit digits rounded to nearest, store the slices
+    // three factor products P^2/8, PM/8, M^2/8
+    f2 G[3][8];
+    float gmx = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         f2 T[3][3];  // T[j][k]: (sig Cf[c][j]) x {PP, PM, MM}
@@ -339,16 +345,25 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
                 const f2 t = (k == 0) ? T[jj][0] : ((k == 1) ? T[jj][1] : T[jj][2]);
                 acc = dadd(acc, dsgn(t, !((a >> jj) & 1)));
             }
-            float mx = fabsf(acc.h);
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
-            const int ex = (mx > 0.f) ? (((__float_as_int(mx) >> 23) & 0xff) - 126) : -200;
-            if (qp == 0) W.ex[j][3 * a + c] = ex;
-            // x 2^-ex (exact); digits 0..2 from the high word (exact steps), the
-            // low word folded in before digits 3 and 4
-            const float sc = (mx > 0.f) ? __int_as_float((127 - ex) << 23) : 0.f;
-            float h = acc.h * sc, l = acc.l * sc;
+            G[c][a] = acc;
+            gmx = fmaxf(gmx, fabsf(acc.h));
+        }
+    }
+    // one exponent per element: 2^(ex - 1) <= max |G| < 2^ex; the digits of
+    // every row are taken at that scale (8-bit digits rounded to nearest)
+    gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 1));
+    gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 2));
+    gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 4));
+    const int ex = (gmx > 0.f) ? (((__float_as_int(gmx) >> 23) & 0xff) - 126) : -200;
+    if (qp == 0) W.ex[j] = ex;
+    // x 2^-ex (exact); digits 0..2 from the high word (exact steps), the low
+    // word folded in before digits 3 and 4
+    const float sc = (gmx > 0.f) ? __int_as_float((127 - ex) << 23) : 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            float h = G[c][a].h * sc, l = G[c][a].l * sc;
 #pragma unroll
             for (int sl = 0; sl < NSL; ++sl) {
                 h *= 256.f;
@@ -363,7 +378,6 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
                 W.sl[j][sl][3 * a + c][qp] = __float2bfloat16_rn(dg);
             }
         }
-    }
     // --- load vector: m_a = sum_q detJ_q N_a(q) ---
     {
         const f2 n3 = dmul(det, DF(NP3)), n2 = dmul(det, DF(NP2)), n1 = dmul(det, DF(NP1)), n0v = dmul(det, DF(NP0));
@@ -416,63 +430,90 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
     }
     __syncwarp();
 
-    // --- tensor cores: A'' = G G^T by levels, per element of the warp ---
+    // --- tensor cores: A'' = G G^T by levels, per element of the warp;
+    // fragments by ldmatrix from the slice rows (16 bytes each) ---
     const int g = lane >> 2, t = lane & 3;
     const int S = st->S;
+    const uint32_t sl_base = (uint32_t)__cvta_generic_to_shared(&W.sl[0][0][0][0]);
+    constexpr uint32_t ROWB = 16, SLB = SL_ROWS * ROWB, ELB = NSL * SLB;  // bytes per row, slice, element
 #pragma unroll 1
     for (int el = 0; el < 4; ++el) {
         const int64_t eo = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + el;
-        auto ld = [&](int sl, int row) -> uint32_t {
-            return *reinterpret_cast<const uint32_t *>(&W.sl[el][sl][row][2 * t]);
-        };
+        if (eo >= e1) break;  // warp-uniform
+        const uint32_t eb = sl_base + el * ELB;
+        // fixed-point shift of this element: G G^T = T 2^(2 ex - 48)
+        const int sh = 2 * W.ex[el] + S - 48;
 #pragma unroll 1
         for (int tl = 0; tl < 4; ++tl) {  // tiles (m, n): (0,0), (0,1), (0,2), (1,2)
             const int mt = tl == 3 ? 1 : 0, nt = tl == 3 ? 2 : tl;
+            uint32_t A[3][4], B[NSL][2];
+            // A = slices (s0, s0 + 1) of rows mt 16 + ..; the second row tile
+            // has 8 real rows (16..23), rows 24..31 are zero
+            const int arow = mt ? 16 + (lane & 7) : (lane & 15);
+#pragma unroll
+            for (int sp = 0; sp < 3; ++sp) {  // slice pairs (0,1), (2,3), (4,-)
+                const int s0 = 2 * sp, s1 = s0 + 1 < NSL ? s0 + 1 : s0;
+                if (mt == 0) {
+                    const uint32_t ad = eb + ((lane >> 4) ? s1 : s0) * SLB + arow * ROWB;
+                    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                                 : "=r"(A[sp][0]), "=r"(A[sp][1]), "=r"(A[sp][2]), "=r"(A[sp][3]) : "r"(ad));
+                } else {
+                    // lanes 0..7: slice s0, lanes 8..15: slice s1 (-> a0, a2)
+                    const uint32_t ad = eb + ((lane & 8) ? s1 : s0) * SLB + arow * ROWB;
+                    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                                 : "=r"(A[sp][0]), "=r"(A[sp][2]) : "r"(ad));
+                    A[sp][1] = 0u;
+                    A[sp][3] = 0u;
+                }
+                if (s0 + 1 >= NSL) {  // no slice s0 + 1: the second k half is zero
+                    A[sp][2] = 0u;
+                    A[sp][3] = 0u;
+                }
+            }
+#pragma unroll
+            for (int tp = 0; tp < NSL; ++tp) {  // B pairs (slice t', slice t' - 1), rows nt 8 + ..
+                const int sb = ((lane >> 3) & 1) ? (tp > 0 ? tp - 1 : 0) : tp;
+                const uint32_t ad = eb + sb * SLB + (nt * 8 + (lane & 7)) * ROWB;
+                asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                             : "=r"(B[tp][0]), "=r"(B[tp][1]) : "r"(ad));
+                if (tp == 0) B[tp][1] = 0u;
+            }
             float acc[5][4];
 #pragma unroll
             for (int L = 0; L < 5; ++L)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc[L][k] = 0.f;
+            // level L = sum over s0 = 0, 2, 4 <= L of [slice s0 | s0 + 1] x [slice L - s0 | L - s0 - 1]
 #pragma unroll
-            for (int L = 0; L < 5; ++L) {
+            for (int L = 0; L < 5; ++L)
 #pragma unroll
-                for (int s0 = 0; s0 <= L; s0 += 2) {
-                    const int s1 = s0 + 1;  // second half of k: slice s1 against slice L - s1
-                    const bool two = s1 <= L;
-                    // rows 24..31 (second row tile, fragment rows g + 8) are zero
-                    const uint32_t a0 = ld(s0, mt * 16 + g), a1 = mt ? 0u : ld(s0, g + 8);
-                    const uint32_t a2 = two ? ld(s1, mt * 16 + g) : 0u, a3 = (two && !mt) ? ld(s1, g + 8) : 0u;
-                    const uint32_t b0 = ld(L - s0, nt * 8 + g), b1 = two ? ld(L - s1, nt * 8 + g) : 0u;
-                    mma_bf16(acc[L], a0, a1, a2, a3, b0, b1);
-                }
-            }
+                for (int s0 = 0; s0 <= L; s0 += 2)
+                    mma_bf16(acc[L], A[s0 / 2][0], A[s0 / 2][1], A[s0 / 2][2], A[s0 / 2][3], B[L - s0][0],
+                             s0 + 1 <= L ? B[L - s0][1] : 0u);
             // levels -> 64-bit fixed point at scale 2^S, added into the node-pair
             // block accumulator (exact integer sums: any order gives the same
-            // bits); the p, q finishing is linear and is applied once per CSR
+            // bits); the r finishing is linear and is applied once per CSR
             // block after all elements
-            if (eo < e1) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int rho = mt * 16 + g + 8 * (k >> 1);
-                    const int sig2 = nt * 8 + 2 * t + (k & 1);
-                    const int a = rho / 3, b = sig2 / 3;
-                    const int c = rho - 3 * a, cp = sig2 - 3 * b;
-                    // upper blocks a <= b, of a diagonal block its upper triangle;
-                    // the four tiles compute all of them (rows >= 24 are padding)
-                    if (rho >= 24 || a > b || (a == b && c > cp)) continue;
-                    long long T = f2i_exact(acc[0][k]);
+            for (int k = 0; k < 4; ++k) {
+                const int rho = mt * 16 + g + 8 * (k >> 1);
+                const int sig2 = nt * 8 + 2 * t + (k & 1);
+                const int a = rho / 3, b = sig2 / 3;
+                const int c = rho - 3 * a, cp = sig2 - 3 * b;
+                // upper blocks a <= b, of a diagonal block its upper triangle;
+                // the four tiles compute all of them (rows >= 24 are padding)
+                if (rho >= 24 || a > b || (a == b && c > cp)) continue;
+                long long T = f2i_exact(acc[0][k]);
 #pragma unroll
-                    for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][k]);
-                    const int sh = W.ex[el][rho] + W.ex[el][sig2] + S - 48;
-                    long long v;
-                    if (sh >= 0) v = T << sh;
-                    else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
-                    else v = 0;
-                    const int32_t tg = W.tgt[el][a * (15 - a) / 2 + b];
-                    const int64_t pr = tg & 0x7fffffff;
-                    const int q = tg < 0 ? 3 * cp + c : 3 * c + cp;
-                    if (v != 0) atomicAdd(&kacc[pr * 9 + q], (unsigned long long)v);
-                }
+                for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][k]);
+                long long v;
+                if (sh >= 0) v = T << sh;
+                else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
+                else v = 0;
+                const int32_t tg = W.tgt[el][a * (15 - a) / 2 + b];
+                const int64_t pr = tg & 0x7fffffff;
+                const int q = tg < 0 ? 3 * cp + c : 3 * c + cp;
+                if (v != 0) atomicAdd(&kacc[pr * 9 + q], (unsigned long long)v);
             }
         }
     }
@@ -486,13 +527,29 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
 // FP64 and eliminates the Dirichlet dofs; the three rows are staged in shared
 // memory and written with coalesced stores.
 // ---------------------------------------------------------------------------
+// floor(A R / 2^s), 1 <= s <= 63: bits s .. s + 63 of the 128-bit product
+__device__ __forceinline__ long long mul_r(long long A, long long R, int s)
+{
+    const long long hi = __mul64hi(A, R);
+    const unsigned long long lo = (unsigned long long)A * (unsigned long long)R;
+    return (long long)((lo >> s) | ((unsigned long long)hi << (64 - s)));
+}
+// r A with r = R 2^-s exactly; a short multiplier (|R| < 2^20, e.g. r = 3/2
+// for nu = 0.3) takes one 64 x 32-bit product (|A| < 2^42 then: the scale
+// keeps r A below 2^62)
+__device__ __forceinline__ long long times_r(long long A, long long R, int s)
+{
+    if (R > -(1ll << 20) && R < (1ll << 20)) return (A * R) >> s;
+    return mul_r(A, R, s);
+}
+
 constexpr int FN_WARPS = 8;
 
 __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
     int64_t n_begin, int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int32_t *__restrict__ tpos, const int64_t *__restrict__ cbase, const long long *__restrict__ kacc,
     const long long *__restrict__ dacc,
-    const MixedState *__restrict__ st, int fp, int fq, const uint8_t *__restrict__ mask,
+    const MixedState *__restrict__ st, long long rR, int rs, const uint8_t *__restrict__ mask,
     const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
     double *__restrict__ d)
 {
@@ -531,8 +588,8 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int cp = 0; cp < 3; ++cp) {
-                long long kv = (long long)fp * A[c][cp] + (long long)fq * A[cp][c];
-                if (c == cp) kv += (long long)fq * tr;
+                long long kv = times_r(A[c][cp], rR, rs) + A[cp][c];
+                if (c == cp) kv += tr;
                 double v = mf_fixed_to_double(kv, S);
                 if (mask) {
                     const int64_t sdof = 3 * (int64_t)mcol + cp;
@@ -558,16 +615,6 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
 
 }  // namespace
 
-mf_status mf_mixed_geometry(const mf_mesh *m, mf_pattern *p, cudaStream_t st)
-{
-    const int64_t ne = m->n_elems;
-    MF_CUDA(cudaMallocAsync(&p->mixed_geo, sizeof(float) * (ne + 1), st));
-    MF_CUDA(cudaMemsetAsync(p->mixed_geo + ne, 0, sizeof(float), st));
-    if (ne > 0) k_mixed_geom<<<(unsigned)((ne + 127) / 128), 128, 0, st>>>(ne, m->coords, m->conn, p->mixed_geo);
-    MF_CUDA(cudaGetLastError());
-    return MF_OK;
-}
-
 mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c, double *values,
                             double *d, cudaStream_t st)
 {
@@ -575,31 +622,37 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
         return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: the mixed path covers Q1 elasticity");
     const double nu = c->nu;
     if (!(nu > -1.0 && nu < 0.5)) return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: Poisson ratio outside (-1, 0.5)");
-    // lambda / mu = 2 nu / (1 - 2 nu) as a small-integer ratio p / q
+    // lambda / mu = r = 2 nu / (1 - 2 nu) exactly as rR 2^-rs (a 53-bit integer)
     const double r = 2.0 * nu / (1.0 - 2.0 * nu);
-    int pp = -1, qq = 0;
-    for (int qd = 1; qd <= 64 && pp < 0; ++qd) {
-        const double pn = r * qd;
-        const double pr = nearbyint(pn);
-        if (pr >= 0.0 && pr <= 4096.0 && fabs(pr / qd - r) <= 1e-13 * (1.0 + fabs(r))) {
-            pp = (int)pr;
-            qq = qd;
+    long long rR = 0;
+    int rs = 1;
+    if (r != 0.0) {
+        int ex = 0;
+        const double fr = frexp(r, &ex);  // r = fr 2^ex, 0.5 <= |fr| < 1
+        rR = (long long)ldexp(fr, 53);
+        rs = 53 - ex;
+        while (rs > 1 && (rR & 1) == 0) {
+            rR /= 2;
+            --rs;
         }
+        if (rs > 63) {  // |r| < 2^-11: the bits of r below 2^-63 are dropped (r A is tiny next to A^T)
+            rR /= (1ll << std::min(rs - 63, 62));
+            rs = 63;
+        }
+        if (rs < 1) return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: Poisson ratio out of the mixed path's range");
     }
-    if (pp < 0)
-        return mf_fail(MF_ERR_UNSUPPORTED,
-                       "mf_assemble: mixed path needs lambda/mu = 2nu/(1-2nu) to be a ratio p/q with q <= 64");
     int *status = mf_status_word();
     if (!status) return mf_fail(MF_ERR_CUDA, "mf_assemble: status word unavailable");
-    const double cmu_q = 1.0 / (2.0 * (1.0 + nu)) / qq;
+    const double cmu = 1.0 / (2.0 * (1.0 + nu));
     MixedState *ms = static_cast<MixedState *>(p->mixed_state);
     const int64_t ne = m->n_elems;
     mf_prof_begin("mixed_bound", st);
     MF_CUDA(cudaMemsetAsync(ms, 0, sizeof(MixedState), st));
-    k_mixed_bound<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, c->elem_coef, p->mixed_geo, (float)cmu_q, ms,
-                                                                status);
+    if (ne > 0)
+        k_mixed_bound<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, m->coords, m->conn, c->elem_coef,
+                                                                    (float)cmu, ms, status);
     const double bmax = fmax(fabs(c->source[0]), fmax(fabs(c->source[1]), fabs(c->source[2])));
-    k_mixed_scale<<<1, 1, 0, st>>>(ms, pp, qq, bmax);
+    k_mixed_scale<<<1, 1, 0, st>>>(ms, fabs(r), bmax);
     mf_prof_end(st);
     const size_t smem = sizeof(WarpSmem) * MX_WARPS;
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -616,7 +669,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
             const int64_t e0 = p->slab_e[k], e1 = p->slab_e[k + 1];
             mf_prof_begin("mixed_elem", s2);
             k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, s2>>>(
-                e0, e1, m->coords, m->conn, c->elem_coef, cmu_q, c->source[0], c->source[1], c->source[2], ms,
+                e0, e1, m->coords, m->conn, c->elem_coef, cmu, c->source[0], c->source[1], c->source[2], ms,
                 p->cbase, p->slot, reinterpret_cast<unsigned long long *>(p->kacc),
                 reinterpret_cast<unsigned long long *>(p->dacc), status);
             mf_prof_end(s2);
@@ -628,7 +681,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
             if (n1 > n0) {
                 mf_prof_begin("mixed_finish", s2);
                 k_mixed_finish<<<(unsigned)((n1 - n0 + FN_WARPS - 1) / FN_WARPS), FN_WARPS * 32, 0, s2>>>(
-                    n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->cbase, p->kacc, p->dacc, ms, pp, qq, c->bc_mask,
+                    n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->cbase, p->kacc, p->dacc, ms, rR, rs, c->bc_mask,
                     c->bc_val, p->row_ptr, values, d);
                 mf_prof_end(s2);
             }

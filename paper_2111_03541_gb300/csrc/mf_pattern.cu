@@ -618,8 +618,6 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->cbase);
     p->cbase = nullptr;
     p->n_upper = 0;
-    cudaFree(p->mixed_geo);
-    p->mixed_geo = nullptr;
     cudaFree(p->dacc);
     p->dacc = nullptr;
     p->kacc = nullptr;
@@ -758,8 +756,6 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_slot_map<<<nblk(m->n_elems * 64), TPB, 0, st>>>(m->n_elems, 8, m->conn, p->adj[0].ptr, p->adj[0].col,
                                                            p->slot);
         MF_CUDA(cudaMallocAsync(&p->mixed_state, 64, st));
-        s = mf_mixed_geometry(m, p, st);
-        if (s != MF_OK) { free_inc(incv, st); return s; }
         {
             // compact numbering of the upper node pairs (the accumulator's blocks)
             const int64_t nn = m->n_nodes;

@@ -3,7 +3,10 @@
 Contract: the CSR pattern is the same bit for bit; K within 1e-11 row-scaled
 of the FP64 oracle (the slices keep about 40 bits of the scaled gradients);
 the solution of the mixed system within 1e-8 relative of the oracle's
-tightly solved x*; two assemblies bit-identical.
+tightly solved x*; two assemblies bit-identical.  Any Poisson ratio in
+(-1, 0.5) is accepted (lambda / mu enters once per CSR block as an exact
+53-bit multiplier), and the fixed-point scale follows the coordinates and
+coefficients of each assembly.
 """
 import numpy as np
 import pytest
@@ -37,7 +40,8 @@ def row_scaled_error(rp, val, ref):
     return (emax[ok] / rmax[ok]).max()
 
 
-@pytest.mark.parametrize("n,nu", [(5, 0.3), (9, 0.3), (13, 0.3), (6, 0.25), (6, 0.45), (6, 0.0)])
+@pytest.mark.parametrize("n,nu", [(1, 0.3), (5, 0.3), (9, 0.3), (13, 0.3), (6, 0.25), (6, 0.45), (6, 0.0),
+                                  (6, 0.49), (6, -0.3), (5, 0.3141592653589793), (4, 1e-12)])
 def test_mixed_values_against_oracle(mf, orc, n, nu):
     prob = gen.elastic_problem(n, nu=nu)
     P = mf.Problem(prob)
@@ -106,9 +110,48 @@ def test_mixed_full_size_sampled_rows(mf, orc):
         assert np.abs(vals[s] - v).max() <= TOL_K * np.abs(v).max()
 
 
-def test_mixed_refuses_irrational_ratio(mf):
-    prob = gen.elastic_problem(3, nu=0.3141592653589793)
+def test_mixed_full_32cube(mf, orc):
+    """32^3 = 32,768 elements, every row compared."""
+    prob = gen.elastic_problem(32)
     P = mf.Problem(prob)
-    with pytest.raises(mf.MFError) as ei:
-        P.assemble(mf.MF_PREC_MIXED)
-    assert ei.value.status == mf.MF_ERR_UNSUPPORTED
+    vals, d = P.assemble(mf.MF_PREC_MIXED)
+    mf.mf_sync_status()
+    rp, ci = P.csr_arrays()
+    rp = rp.cpu().numpy()
+    ref = orc.assemble(prob)
+    assert np.array_equal(rp, ref["row_ptr"]) and np.array_equal(ci.cpu().numpy(), ref["col"])
+    assert row_scaled_error(rp, vals.cpu().numpy(), ref["val"]) <= TOL_K
+    assert np.abs(d.cpu().numpy() - ref["d"]).max() <= 1e-12 * np.abs(ref["d"]).max()
+
+
+def test_mixed_lifting_nonzero_dirichlet(mf, orc):
+    """Nonzero prescribed displacements: lifted right-hand side against the oracle."""
+    prob = gen.elastic_problem(7)
+    rng = np.random.default_rng(5)
+    prob["bc_val"] = np.where(prob["bc_mask"] != 0, rng.standard_normal(prob["bc_val"].shape[0]), 0.0)
+    P = mf.Problem(prob)
+    vals, d = P.assemble(mf.MF_PREC_MIXED)
+    mf.mf_sync_status()
+    rp, _ = P.csr_arrays()
+    ref = orc.assemble(prob)
+    assert row_scaled_error(rp.cpu().numpy(), vals.cpu().numpy(), ref["val"]) <= TOL_K
+    assert np.abs(d.cpu().numpy() - ref["d"]).max() <= 1e-10 * np.abs(ref["d"]).max()
+
+
+def test_mixed_scale_follows_moved_coordinates(mf, orc):
+    """The fixed-point scale is taken per assembly: moving the nodes (here a
+    uniform stretch by 3, which scales K by 3) after the pattern was built
+    still gives the oracle's K of the moved mesh."""
+    import torch
+    prob = gen.elastic_problem(6)
+    P = mf.Problem(prob)
+    P.assemble(mf.MF_PREC_MIXED)
+    moved = dict(prob)
+    moved["coords"] = prob["coords"] * 3.0
+    P.coords.copy_(torch.from_numpy(moved["coords"]).to(P.coords.device))
+    vals, d = P.assemble(mf.MF_PREC_MIXED)
+    mf.mf_sync_status()
+    rp, _ = P.csr_arrays()
+    ref = orc.assemble(moved)
+    assert row_scaled_error(rp.cpu().numpy(), vals.cpu().numpy(), ref["val"]) <= TOL_K
+    assert np.abs(d.cpu().numpy() - ref["d"]).max() <= 1e-12 * np.abs(ref["d"]).max()
