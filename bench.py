@@ -35,17 +35,16 @@ UNIT = "elements/s"
 N_GRID = 64
 FCG_DIRS = 256  # stored directions of the flexible CG with the learned preconditioner
 
-# ncu counters of the mixed element kernel (one launch, 48^3 case, 110,592
-# elements; both grow in proportion to the elements): executed warp
-# instructions (smsp__inst_executed.sum = 274,102,359) and DRAM traffic
-# (dram__bytes_read.sum + dram__bytes_write.sum = 132.16 MB + 70.16 MB), with
-# the SHA-256 prefix of the files that hold the kernel's code (mf_mixed.cu and
-# the device helpers it calls): the line reports null for them once those
-# files change.
-MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 274102359 / 110592,
-                  "bytes_per_element": (132.16e6 + 70.16e6) / 110592,
+# ncu counters of the mixed element kernel on a small case (executed warp
+# instructions per element and DRAM bytes per element, both in proportion to
+# the elements), with the SHA-256 prefix of the files that hold the kernel's
+# code: the line reports null for them once those files change.  Capture: 48^3
+# (110,592 elements), smsp__inst_executed.sum = 246,564,942,
+# dram__bytes_read.sum + dram__bytes_write.sum = 132.17 MB + 62.63 MB.
+MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 246564942 / 110592,
+                  "bytes_per_element": (132165632 + 62629120) / 110592,
                   "sources": ("paper_2111_03541_gb300/csrc/mf_mixed.cu", "paper_2111_03541_gb300/csrc/mf_device.cuh"),
-                  "sha256": "8b086cefdef5d448"}
+                  "sha256": "f97c5dce99e42da9"}
 KERNELS_PER_ASSEMBLY = {"mixed": 4, "fp64": 2}
 # instruction-issue ceiling of GB300: one warp instruction per clock per SM
 # sub-partition, 4 per SM, 152 SMs, 2070 MHz maximum SM clock
@@ -192,13 +191,33 @@ def oracle_sample(prob, layers: int):
     return ne, time.perf_counter() - t
 
 
-def cpu_baseline(prob, layers=N_GRID + 1):
-    """The oracle on the host: by default every node layer, i.e. the whole
-    workload (about 10 s on one core)."""
-    ne, sec = oracle_sample(prob, layers)
-    return {"value": ne / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle FP64 assembly (element matrices, COO sort, sums, Dirichlet) of the {ne} elements "
-                      f"touching the first {layers} node layers of the same 64^3 mesh: {sec:.2f} s, 1 thread"}
+def cpu_baseline(prob):
+    """The oracle on the host: the whole workload on all host cores (the
+    OpenMP build of the same oracle source, bit-identical results), and the
+    single-threaded oracle as it stands on one core (about 10 s)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    ne = prob["conn"].shape[0]
+    t = time.perf_counter()
+    oracle.assemble_threads(prob, cores)
+    sec_all = time.perf_counter() - t
+    ne1, sec1 = oracle_sample(prob, N_GRID + 1)
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"value": ne / sec_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle FP64 assembly (element matrices, stable sort by (row, col), sums in emission order, "
+                      f"Dirichlet) of all {ne} elements of the same 64^3 mesh on {cores} threads (OpenMP build of "
+                      f"the same source): {sec_all:.2f} s",
+            "cpu_model": model,
+            "single_core": {"value": ne1 / sec1, "unit": UNIT, "cores": 1,
+                            "sample": f"the single-threaded oracle on the same {ne1} elements: {sec1:.2f} s"}}
 
 
 def run_reference(args):
@@ -330,45 +349,41 @@ def run_ours(args):
     best = "mixed" if have_mixed and paths["mixed"].get("accurate") and \
         paths["mixed"]["ms_per_step"] < paths["fp64"]["ms_per_step"] else "fp64"
 
-    # dominant kernel of the chosen path, timed on the launching stream
+    # dominant kernel of the chosen path, timed on the launching stream.  The
+    # roofline is the assembly's algorithmic bytes (K values written once, d,
+    # coordinates, connectivity, coefficients, Dirichlet data) over that
+    # kernel's time, against the measured HBM copy peak.
     peaks, peak_src = measured_peaks()
     alg_bytes = 8 * P.nnz + 8 * P.n + prob["coords"].nbytes + prob["conn"].nbytes + prob["coef"].nbytes + \
         prob["bc_mask"].nbytes + prob["bc_val"].nbytes
     ms_best = paths[best]["ms_per_step"]
     roofline_hbm = {"bound": "hbm", "achieved": alg_bytes / (ms_best * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s"}
+                    "unit": "GB/s", "algorithmic_bytes": alg_bytes}
     roofline_hbm["frac"] = roofline_hbm["achieved"] / roofline_hbm["peak"]
-    # kernels of ours per assembly (the timing regions group the scale passes):
-    # mixed = bound, scale, element, finishing; FP64 = element, gather
     launches = KERNELS_PER_ASSEMBLY[best]
+    kname = max(paths[best]["kernels"], key=lambda k: paths[best]["kernels"][k]["ms_per_step"])
+    ms_k = paths[best]["kernels"][kname]["ms_per_launch"]
+    ach = alg_bytes / (ms_k * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "ms_per_launch": ms_k,
+                "algorithmic": f"{alg_bytes} B per assembly (8 nnz + 8 n + coordinates, connectivity, coefficients, "
+                               f"Dirichlet mask and values) / the dominant kernel's launch time",
+                "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     if best == "fp64":
-        # the element kernel dominates and is bound by the FP64 pipe
-        kname = "elem_elastic_q1_fp64"
-        ms_el = paths["fp64"]["kernels"][kname]["ms_per_step"]
-        ach = n_el * FLOPS_PER_ELEMENT_FP64 / (ms_el * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "ms_per_step": ms_el,
-                    "algorithmic": f"{FLOPS_PER_ELEMENT_FP64} FP64 flops/element x {n_el} elements",
-                    "peak_source": "GB300 nominal dense FP64 rate (measured FMA-loop rate 1.19 TFLOP/s)"}
-    else:
-        # the mixed path's dominant kernel is the element kernel, bound by
-        # instruction issue (INT/FP32 work of the double-float geometry and the
-        # BF16 split): its executed warp instructions per second against the
-        # issue ceiling
-        kname = max(paths[best]["kernels"], key=lambda k: paths[best]["kernels"][k]["ms_per_step"])
-        ms_k = paths[best]["kernels"][kname]["ms_per_launch"]
-        roofline = {"bound": "alu", "kernel": kname, "ms_per_launch": ms_k, "achieved": None, "peak": None,
-                    "unit": "warp instructions/s", "frac": None, "traffic": None, "assembly": roofline_hbm}
-        ok = kname == MIXED_ELEM_NCU["kernel"] and \
-            sources_hash(MIXED_ELEM_NCU["sources"]) == MIXED_ELEM_NCU["sha256"]
-        if ok:
-            inst = MIXED_ELEM_NCU["inst_per_element"] * n_el
-            ach = inst / (ms_k * 1e-3)
-            roofline.update({"achieved": ach, "peak": ISSUE_PEAK, "frac": ach / ISSUE_PEAK,
-                             "traffic": MIXED_ELEM_NCU["bytes_per_element"] * n_el,
-                             "algorithmic": f"{MIXED_ELEM_NCU['inst_per_element']:.1f} warp instructions per "
-                                            f"element (ncu, 48^3) x {n_el} elements",
-                             "peak_source": "GB300 issue ceiling: 152 SMs x 4 sub-partitions x 2070 MHz"})
+        kel = paths["fp64"]["kernels"].get("elem_elastic_q1_fp64")
+        if kel:
+            tf = n_el * FLOPS_PER_ELEMENT_FP64 / (kel["ms_per_launch"] * 1e-3) / 1e12
+            roofline["fp64_pipe"] = {"achieved_tflops": tf, "peak_tflops": FP64_PEAK_TFLOPS,
+                                     "frac": tf / FP64_PEAK_TFLOPS}
+    elif MIXED_ELEM_NCU and kname == MIXED_ELEM_NCU["kernel"] and \
+            sources_hash(MIXED_ELEM_NCU["sources"]) == MIXED_ELEM_NCU["sha256"]:
+        # explanatory: the element kernel is bound by instruction issue
+        inst = MIXED_ELEM_NCU["inst_per_element"] * n_el
+        roofline["traffic"] = MIXED_ELEM_NCU["bytes_per_element"] * n_el
+        roofline["issue"] = {"warp_instructions": inst, "per_element": MIXED_ELEM_NCU["inst_per_element"],
+                             "achieved": inst / (ms_k * 1e-3), "peak": ISSUE_PEAK,
+                             "frac": inst / (ms_k * 1e-3) / ISSUE_PEAK,
+                             "peak_source": "152 SMs x 4 sub-partitions x 2070 MHz"}
 
     # end to end: host buffers in, K and d out, through the C ABI
     e2e = None if args.no_e2e else e2e_leg(P, prob, mf, stream, args, best)

@@ -18,6 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "_oracle.so")
+LIB_OMP = os.path.join(HERE, "_oracle_omp.so")  # the same source with OpenMP (all-core baseline)
 
 P1, P2, Q1, Q2S, P2T, Q2Q = 0, 1, 2, 3, 4, 5
 QTRI3, QTRI6, QHEX8, QHEX27, QTET64, QQUAD9 = 0, 1, 2, 3, 4, 5
@@ -29,12 +30,20 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compiles oracle.c into _oracle.so (gcc, -O2, no fast-math)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                               "-ffp-contract=off", "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
+    """Compiles oracle.c into _oracle.so (gcc, -O2, no fast-math), and the same
+    source with -fopenmp into _oracle_omp.so for the all-core baseline (skipped
+    when the compiler has no OpenMP)."""
+    for out, extra in ((LIB, []), (LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+            tmp = out + ".%d.tmp" % os.getpid()
+            try:
+                subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
+                                       "-ffp-contract=off", *extra, "-o", tmp, SRC, "-lm"])
+            except subprocess.CalledProcessError:
+                if extra:
+                    continue
+                raise
+            os.replace(tmp, out)
     return LIB
 
 
@@ -405,6 +414,65 @@ def assemble(prob: dict, quad_kind: int | None = None, fnodal=None, dirichlet: b
     pm = take(ptrs[4], int(pr.n_pnodes), C.c_double, np.float64)
     if pm is not None:
         out["pmass"] = pm
+    if dirichlet:
+        apply_dirichlet(out, prob["bc_mask"], prob["bc_val"])
+    return out
+
+
+_lib_omp = None
+
+
+def assemble_threads(prob: dict, threads: int, dirichlet: bool = True) -> dict:
+    """The assembly of ``assemble`` on ``threads`` host threads (OpenMP build
+    of the same source; domain forms without facets).  Bit-identical to
+    ``assemble``; used as the all-core CPU baseline."""
+    global _lib_omp
+    build()
+    if _lib_omp is None:
+        if not os.path.exists(LIB_OMP):
+            raise RuntimeError("no OpenMP build of the oracle")
+        _lib_omp = C.CDLL(LIB_OMP)
+        vp, i64 = C.c_void_p, C.c_int64
+        _lib_omp.or_assemble_threads.argtypes = [C.POINTER(Problem), C.c_int] + [C.POINTER(i64)] * 2 + \
+            [C.POINTER(vp)] * 4
+        _lib_omp.or_assemble_threads.restype = C.c_int
+        _lib_omp.or_free.argtypes = [vp]
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+
+    form, elem = prob["form"], prob["elem"]
+    coords = arr(prob["coords"], np.float64)
+    conn = arr(prob["conn"], np.int32)
+    pr = Problem()
+    pr.form, pr.elem, pr.quad = FORM[form], ELEM[elem], _default_quad(elem, form)
+    pr.n_nodes, pr.n_el = coords.shape[0], conn.shape[0]
+    pr.coords, pr.conn, pr.coef = _p(coords), _p(conn), _p(arr(prob["coef"], np.float64))
+    if form == "elastic":
+        pr.nu = prob["nu"]
+        pr.source = _p(arr(prob["body"], np.float64))
+    else:
+        pr.source = _p(arr([prob.get("source", 1.0), 0.0, 0.0], np.float64))
+    n_rows, nnz = C.c_int64(), C.c_int64()
+    ptrs = [C.c_void_p() for _ in range(4)]
+    rc = _lib_omp.or_assemble_threads(C.byref(pr), int(threads), C.byref(n_rows), C.byref(nnz),
+                                      *[C.byref(x) for x in ptrs])
+    if rc == -2:
+        raise AssemblyError("element with detJ <= 0")
+    if rc:
+        raise AssemblyError("threaded oracle assembly failed (%d)" % rc)
+    n, z = n_rows.value, nnz.value
+
+    def take(ptr, count, ctype, dt):
+        a = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=(count,)).astype(dt, copy=True)
+        _lib_omp.or_free(ptr)
+        return a
+
+    out = {"row_ptr": take(ptrs[0], n + 1, C.c_int64, np.int64), "col": take(ptrs[1], z, C.c_int32, np.int32),
+           "val": take(ptrs[2], z, C.c_double, np.float64), "d": take(ptrs[3], n, C.c_double, np.float64)}
     if dirichlet:
         apply_dirichlet(out, prob["bc_mask"], prob["bc_val"])
     return out

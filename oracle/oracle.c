@@ -1296,6 +1296,181 @@ int or_assemble(const or_problem *p, int64_t *n_rows, int64_t *nnz, int64_t **ro
     return or_assemble_filtered(p, NULL, NULL, n_rows, nnz, row_ptr, col, val, d, pmass_out);
 }
 
+/* ------------------------------------------------------------------------ */
+/* The same assembly on several host threads (the all-core CPU baseline).    */
+/* Compiled with -fopenmp into a second library; without it the pragmas are */
+/* ignored and it runs on one thread.  Element matrices are the same calls   */
+/* as above, each element's triplets land at the position the serial         */
+/* emission gives them, and the stable order by (row, col) is built by a     */
+/* stable counting sort on rows (per-thread counts, chunks in emission       */
+/* order) followed by a stable merge sort of each row by column; duplicates  */
+/* are summed in emission order.  The result equals or_assemble bit for bit. */
+/* Domain forms (thermal, capacity, elasticity) without facets; -3 otherwise.*/
+/* ------------------------------------------------------------------------ */
+static void merge_sort_cols(int64_t *idx, int64_t *tmp, int64_t n, const int32_t *col)
+{
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) tmp[k++] = col[idx[j]] < col[idx[i]] ? idx[j++] : idx[i++];
+            while (i < mid) tmp[k++] = idx[i++];
+            while (j < hi) tmp[k++] = idx[j++];
+        }
+        memcpy(idx, tmp, sizeof(int64_t) * n);
+    }
+}
+
+int or_assemble_threads(const or_problem *p, int threads, int64_t *n_rows, int64_t *nnz, int64_t **row_ptr,
+                        int32_t **col, double **val, double **d)
+{
+    if (p->n_facets > 0 || p->form == OR_OSEEN) return -3;
+    if (p->form == OR_ELASTIC && p->elem != OR_Q1 && p->elem != OR_Q2S) return -3;
+    const int64_t n = or_ndofs(p), ne = p->n_el;
+    const int dim = elem_dim(p->elem), npe = elem_npe(p->elem);
+    const int m = p->form == OR_ELASTIC ? 3 * npe : npe, mm = m * m;
+    const int64_t nt = n + ne * mm; /* triplets: the diagonal, then every element */
+    int64_t *trow = malloc(sizeof(int64_t) * nt);
+    int32_t *tcol = malloc(sizeof(int32_t) * nt);
+    double *tval = malloc(sizeof(double) * nt);
+    double *de_all = malloc(sizeof(double) * (ne * m + 1));
+    double *dv = calloc((size_t)n, sizeof(double));
+    if (!trow || !tcol || !tval || !de_all || !dv) {
+        free(trow); free(tcol); free(tval); free(de_all); free(dv);
+        return -1;
+    }
+    int bad = 0;
+#pragma omp parallel for num_threads(threads) schedule(static)
+    for (int64_t g = 0; g < n; ++g) {
+        trow[g] = g;
+        tcol[g] = (int32_t)g;
+        tval[g] = 0.0;
+    }
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 256)
+    for (int64_t e = 0; e < ne; ++e) {
+        double X[20 * 3], Ke[60 * 60], de[60];
+        const int32_t *cn = p->conn + e * npe;
+        for (int a = 0; a < npe; ++a)
+            for (int i = 0; i < dim; ++i) X[dim * a + i] = p->coords[(int64_t)cn[a] * dim + i];
+        double det;
+        if (p->form == OR_THERMAL) det = or_elem_thermal(p->elem, p->quad, X, p->coef[e], p->source[0], NULL, Ke, de);
+        else if (p->form == OR_CAPACITY) { det = or_elem_capacity(p->elem, X, p->coef[e], Ke); memset(de, 0, sizeof de); }
+        else det = or_elem_elastic(p->elem, X, p->coef[e], p->nu, p->source, Ke, de);
+        if (!(det > 0.0)) {
+#pragma omp atomic write
+            bad = 1;
+        }
+        int64_t t = n + e * mm;
+        for (int a = 0; a < npe; ++a)
+            for (int ci = 0; ci < m / npe; ++ci)
+                for (int b = 0; b < npe; ++b)
+                    for (int cj = 0; cj < m / npe; ++cj) {
+                        const int k = m / npe;
+                        trow[t] = k * (int64_t)cn[a] + ci;
+                        tcol[t] = (int32_t)(k * (int64_t)cn[b] + cj);
+                        tval[t] = Ke[(k * a + ci) * m + k * b + cj];
+                        ++t;
+                    }
+        for (int r = 0; r < m; ++r) de_all[e * m + r] = de[r];
+    }
+    if (bad) {
+        free(trow); free(tcol); free(tval); free(de_all); free(dv);
+        return -2;
+    }
+    /* the load vector in element order, as the serial emission adds it */
+    if (p->form != OR_CAPACITY)
+        for (int64_t e = 0; e < ne; ++e) {
+            const int32_t *cn = p->conn + e * npe;
+            const int k = m / npe;
+            for (int a = 0; a < npe; ++a)
+                for (int ci = 0; ci < k; ++ci) dv[k * (int64_t)cn[a] + ci] += de_all[e * m + k * a + ci];
+        }
+    free(de_all);
+    /* stable counting sort by row: per-thread counts over contiguous chunks */
+    int T = threads > 0 ? threads : 1;
+    int64_t *cnt = calloc((size_t)T * (size_t)(n + 1), sizeof(int64_t));
+    int64_t *rs = calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *perm = malloc(sizeof(int64_t) * nt);
+    if (!cnt || !rs || !perm) {
+        free(cnt); free(rs); free(perm); free(trow); free(tcol); free(tval); free(dv);
+        return -1;
+    }
+    const int64_t chunk = (nt + T - 1) / T;
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+    for (int th = 0; th < T; ++th) {
+        const int64_t lo = th * chunk, hi = lo + chunk < nt ? lo + chunk : nt;
+        int64_t *c = cnt + (size_t)th * (n + 1);
+        for (int64_t t = lo; t < hi; ++t) c[trow[t]]++;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+        int64_t s = rs[r];
+        for (int th = 0; th < T; ++th) {
+            int64_t *c = cnt + (size_t)th * (n + 1);
+            const int64_t v = c[r];
+            c[r] = s;
+            s += v;
+        }
+        rs[r + 1] = s;
+    }
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+    for (int th = 0; th < T; ++th) {
+        const int64_t lo = th * chunk, hi = lo + chunk < nt ? lo + chunk : nt;
+        int64_t *c = cnt + (size_t)th * (n + 1);
+        for (int64_t t = lo; t < hi; ++t) perm[c[trow[t]]++] = t;
+    }
+    free(cnt);
+    /* per row: stable sort by column, then unique columns with sums in
+       emission order */
+    int64_t *ucnt = calloc((size_t)n + 1, sizeof(int64_t));
+#pragma omp parallel num_threads(T)
+    {
+        int64_t cap = 1024;
+        int64_t *tmp = malloc(sizeof(int64_t) * cap);
+#pragma omp for schedule(dynamic, 512)
+        for (int64_t r = 0; r < n; ++r) {
+            const int64_t lo = rs[r], len = rs[r + 1] - lo;
+            if (len > cap) {
+                free(tmp);
+                cap = len;
+                tmp = malloc(sizeof(int64_t) * cap);
+            }
+            merge_sort_cols(perm + lo, tmp, len, tcol);
+            int64_t u = 0;
+            for (int64_t t = 0; t < len; ++t)
+                if (t == 0 || tcol[perm[lo + t]] != tcol[perm[lo + t - 1]]) ++u;
+            ucnt[r + 1] = u;
+        }
+        free(tmp);
+    }
+    for (int64_t r = 0; r < n; ++r) ucnt[r + 1] += ucnt[r];
+    const int64_t u = ucnt[n];
+    int32_t *ci = malloc(sizeof(int32_t) * (u > 0 ? u : 1));
+    double *vv = malloc(sizeof(double) * (u > 0 ? u : 1));
+#pragma omp parallel for num_threads(T) schedule(dynamic, 512)
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t lo = rs[r], len = rs[r + 1] - lo;
+        int64_t k = ucnt[r] - 1;
+        for (int64_t t = 0; t < len; ++t) {
+            const int64_t s = perm[lo + t];
+            if (t == 0 || tcol[s] != tcol[perm[lo + t - 1]]) {
+                ++k;
+                ci[k] = tcol[s];
+                vv[k] = 0.0;
+            }
+            vv[k] += tval[s];
+        }
+    }
+    free(perm); free(rs); free(trow); free(tcol); free(tval);
+    *n_rows = n;
+    *nnz = u;
+    *row_ptr = ucnt;
+    *col = ci;
+    *val = vv;
+    *d = dv;
+    return 0;
+}
+
 void or_free(void *ptr) { free(ptr); }
 
 /* ------------------------------------------------------------------------ */

@@ -31,6 +31,13 @@ mf_status mf_cuda_check(cudaError_t e, const char *what)
 
 extern "C" const char *mf_last_error(void) { return g_msg; }
 
+void mf_clear_error() { g_msg[0] = 0; }
+
+bool mf_csr_ok(const mf_csr *K)
+{
+    return K && K->n_rows > 0 && K->nnz > 0 && K->row_ptr && K->col_idx && K->values;
+}
+
 // ---------------------------------------------------------------------------
 // device status word: one int per device in a __device__ variable; kernels get
 // its address as an argument (set-up once per device with that device current)
@@ -346,10 +353,7 @@ extern "C" mf_status mf_pattern_destroy(mf_pattern *pattern)
 // ---------------------------------------------------------------------------
 // assembly and solve
 // ---------------------------------------------------------------------------
-static bool csr_ok(const mf_csr *K)
-{
-    return K && K->n_rows > 0 && K->nnz > 0 && K->row_ptr && K->col_idx && K->values;
-}
+static bool csr_ok(const mf_csr *K) { return mf_csr_ok(K); }
 
 extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
                                  const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d,

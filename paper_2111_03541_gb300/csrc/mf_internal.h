@@ -130,6 +130,10 @@ struct mf_facets {
 int *mf_status_word();
 mf_status mf_fail(mf_status s, const char *fmt, ...);
 mf_status mf_cuda_check(cudaError_t e, const char *what);
+// clears the calling thread's error message (entry points start with it)
+void mf_clear_error();
+// a CSR system with rows, entries and all three arrays
+bool mf_csr_ok(const mf_csr *K);
 
 // exclusive scan of n int64 counts in place; total written to *d_total (device)
 cudaError_t mf_scan_i64(int64_t *d_data, int64_t n, int64_t *d_total, cudaStream_t st);

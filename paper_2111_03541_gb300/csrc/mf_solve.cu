@@ -887,8 +887,9 @@ mf_status noalloc_base(double **out)
 extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, double *x, double tol, int64_t max_iter,
                                           int32_t check_every, mf_solve_info *info, void *stream)
 {
-    if (!K || !d || !x || !K->row_ptr || !K->col_idx || !K->values || K->n_rows <= 0)
-        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: NULL argument");
+    mf_clear_error();
+    if (!mf_csr_ok(K) || !d || !x)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: NULL argument or an empty system");
     if (K->n_rows > MF_NOALLOC_MAX_ROWS)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_pcg_noalloc: %lld rows exceed MF_NOALLOC_MAX_ROWS = %d",
                        (long long)K->n_rows, MF_NOALLOC_MAX_ROWS);

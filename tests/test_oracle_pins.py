@@ -596,3 +596,21 @@ def test_conv3d_gradients_central_differences(orc):
         bm[c] -= h
         fd = (loss(x, w, bp) - loss(x, w, bm)) / (2 * h)
         assert abs(fd - gb[c]) <= 1e-6 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("make", [lambda: gen.elastic_problem(6), lambda: gen.thermal_q1_problem(5),
+                                  lambda: gen.thermal_p1_problem(9), lambda: gen.thermal_p2_problem(7),
+                                  lambda: gen.elastic_q2s_problem(3), lambda: gen.thermal_p2t_problem(3)],
+                         ids=["elastic_q1", "thermal_q1", "thermal_p1", "thermal_p2", "elastic_q2s", "thermal_p2t"])
+def test_threaded_oracle_is_bit_identical(orc, make):
+    """The all-core build of the oracle (OpenMP, used as the CPU baseline)
+    gives the serial oracle's K and d bit for bit."""
+    import os
+    prob = make()
+    a = orc.assemble(prob)
+    try:
+        b = orc.assemble_threads(prob, max(2, os.cpu_count() or 2))
+    except RuntimeError:
+        pytest.skip("no OpenMP build of the oracle on this host")
+    for k in ("row_ptr", "col", "val", "d"):
+        assert np.array_equal(a[k], b[k]), k

@@ -47,6 +47,38 @@ def test_noalloc_pcg_matches_mf_solve_on_two_calls(mf):
         P.close()
 
 
+def test_noalloc_solve_allocates_no_device_memory(mf):
+    """After a first call (the one-time symbol lookup), a solve leaves the
+    device's free memory and torch's allocator statistics unchanged."""
+    import torch
+    P = mf.Problem(gen.thermal_p1_problem(48))
+    P.assemble()
+    x = torch.zeros(P.n, dtype=torch.float64, device=P.device)
+    mf.mf_solve_pcg_noalloc(P.csr, P.d, x, 1e-10, 100000, 50)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    alloc0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    x.zero_()
+    st, info = mf.mf_solve_pcg_noalloc(P.csr, P.d, x, 1e-10, 100000, 50)
+    torch.cuda.synchronize()
+    assert st == mf.MF_OK and info.converged
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == alloc0
+    assert mf.mf_last_error() == ""
+    P.close()
+
+
+def test_noalloc_rejects_an_empty_system(mf):
+    import torch
+    P = mf.Problem(gen.thermal_p1_problem(4))
+    empty = mf.CSR(n_rows=P.csr.n_rows, nnz=0, row_ptr=P.csr.row_ptr, col_idx=P.csr.col_idx,
+                   values=P.csr.values)
+    x = torch.zeros(P.n, dtype=torch.float64, device=P.device)
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_solve_pcg_noalloc(empty, P.d, x, 1e-10, 10)
+    assert ei.value.status == mf.MF_ERR_INVALID_ARG
+
+
 def test_noalloc_rejects_systems_above_the_limit(mf):
     import torch
     P = mf.Problem(gen.thermal_p1_problem(4))
