@@ -75,6 +75,27 @@ def parse():
     return ap.parse_args()
 
 
+def golden_solution():
+    """The oracle's tight solution of the 64^3 workload at 1,024 sampled dofs
+    (tests/golden, written by a script that calls only the oracle)."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "elastic_q1_64cube_solution.txt")
+    if not os.path.exists(path):
+        return None
+    head, idx, val = {}, [], []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            a, b = line.split()
+            if a.isdigit():
+                idx.append(int(a))
+                val.append(float(b))
+            else:
+                head[a] = float(b)
+    return {"idx": np.array(idx), "val": np.array(val), **head}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -269,6 +290,8 @@ def run_ours(args):
     mfbuild.build()
     mf.lib()
 
+    if world > 1:
+        return run_partitioned(args, mf, gen, dist, world, rank, dev)
     prob = gen.elastic_problem(args.grid)
     n_el = prob["conn"].shape[0]
     t0 = time.perf_counter()
@@ -343,6 +366,23 @@ def run_ours(args):
             err = (torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)).item()
             paths["mixed"]["rel_err_vs_fp64_solution"] = err
             paths["mixed"]["accurate"] = err <= 1e-8
+            # the mixed path's own solve: FP64 refinement around an FP32 inner PCG
+            t = time.perf_counter()
+            xr, st, info = P.solve(solver=mf.MF_SOLVER_PCG_REFINED, tol=1e-12, max_iter=200000, inner_tol=1e-4,
+                                   check_every=100)
+            torch.cuda.synchronize()
+            ref_s = time.perf_counter() - t
+            sol["mixed_refined"] = {"inner_fp32_iterations": int(info.iterations),
+                                    "fp64_refinements": int(info.refinements), "rel_residual": info.rel_residual,
+                                    "solve_s": ref_s,
+                                    "rel_err_vs_fp64_solution":
+                                        (torch.linalg.norm(xr - x64) / torch.linalg.norm(x64)).item()}
+            g = golden_solution()
+            if g is not None and args.grid == N_GRID:
+                xs = xr.cpu().numpy()[g["idx"]]
+                sol["mixed_refined"]["rel_err_vs_oracle_tight_solution_sampled"] = \
+                    float(np.linalg.norm(xs - g["val"]) / np.linalg.norm(g["val"]))
+                sol["mixed_refined"]["oracle_kappa_est_x_relres"] = g["kappa_est"] * g["relres"]
     for k, v in paths.items():
         v["elements_per_s"] = n_el / (v["ms_per_step"] * 1e-3)
         v["dofs_per_s"] = P.n / (v["ms_per_step"] * 1e-3)
@@ -407,6 +447,89 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# N > 1: owner-computes partition of one mesh (weak scaling)
+# ---------------------------------------------------------------------------
+def run_partitioned(args, mf, gen, dist, world, rank, dev):
+    """One 64^3 cube per rank stacked along z (64 x 64 x 64 N elements); rank
+    r owns the node layers of its cube, assembles its elements plus one ghost
+    layer with the library (no exchange: its rows are complete), then the
+    ranks run a distributed Jacobi-PCG: the library's SpMV on the owned rows,
+    a halo exchange of the search direction per iteration (NCCL send/recv)
+    and all-reduced scalars.  value = all elements / the slowest rank's
+    assembly time."""
+    import numpy as np
+    import torch
+
+    from paper_2111_03541_gb300 import partition as pt
+    n = args.grid
+    prob = gen.elastic_box_problem(n, n, n * world)
+    n_el = prob["conn"].shape[0]
+    starts = pt.node_starts(prob["coords"].shape[0], world, (n + 1) * (n + 1))
+    loc = pt.local_problem(prob, starts, rank)
+    P = mf.Problem(loc, device=dev)
+    prec = mf.MF_PREC_MIXED
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        P.assemble(prec)
+    mf.mf_sync_status()
+    starts_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with sampler:
+        dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts_ev[i].record(stream)
+            P.assemble(prec)
+            ends_ev[i].record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+    clocks = sampler.summary()
+    ms_local = statistics.mean(s.elapsed_time(e) for s, e in zip(starts_ev, ends_ev))
+    value, ms_job = job_throughput(dist, ms_local, n_el // world, dev)
+    # distributed Jacobi-PCG on the owned rows
+    k = 3
+    own0, nown = loc["own"]
+    rp_h, _ = P.csr_arrays()
+    rp_h = rp_h.cpu().numpy()
+    r0, r1 = k * own0, k * (own0 + nown)
+    Kown = mf.CSR(n_rows=r1 - r0, nnz=int(rp_h[r1] - rp_h[r0]), row_ptr=P.csr.row_ptr + 8 * r0,
+                  col_idx=P.csr.col_idx, values=P.csr.values)
+    # the diagonal: one entry per row, in row order
+    rows = torch.repeat_interleave(torch.arange(P.n, device=dev), torch.from_numpy(np.diff(rp_h)).to(dev))
+    diag = P.values[rows == P.csr_arrays()[1].to(dev).long()]
+    dinv = (1.0 / diag[r0:r1]).contiguous()
+    ex = pt.HaloExchange(pt.halo_plan(prob["conn"], starts, rank, loc), k, dev)
+    q = torch.empty(r1 - r0, dtype=torch.float64, device=dev)
+
+    def spmv(xl):
+        mf.mf_spmv(Kown, xl, q)
+        return q.clone()
+
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    x, its, rel = pt.dist_pcg(spmv, dinv, P.d[r0:r1].clone(), P.n, slice(r0, r1), ex, 1e-8, 100000)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_job, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "mixed(bf16 split, f32 acc, f64)", "data": "synthetic",
+                "config": {"workload": f"3D linear elasticity, Q1 hexahedra, {n}x{n}x{n * world} box "
+                                       f"({n}^3 cube per rank, {n_el} elements), owner-computes z-slabs with one "
+                                       f"ghost element layer", "path": "mixed",
+                           "l2": "flushed between steps (256 MB write)", "parallelism": f"z-slabs x{world}"},
+                "distributed_pcg": {"iterations": its, "rel_residual": rel, "solve_s": solve_s,
+                                    "tol": 1e-8, "exchange": "halo of the search direction per SpMV (NCCL "
+                                                             "send/recv) + all-reduced scalars"},
+                "e2e": None, "gpu_launches": KERNELS_PER_ASSEMBLY["mixed"] * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------------------

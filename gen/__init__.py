@@ -163,6 +163,26 @@ def hex_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER, jitter_all: b
     return {"dim": 3, "elem": "Q1", "n": n, "coords": coords, "conn": conn}
 
 
+def hex_box_mesh(nx: int, ny: int, nz: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
+    """Q1 hexahedra of side h = 1 / nx on the box [0, 1] x [0, ny h] x [0, nz h]
+    (nx x ny x nz cells, nodes and elements lexicographic with x fastest):
+    ``hex_mesh(n)`` is the case nx = ny = nz = n.  The weak-scaling workload
+    of several ranks stacks their cubes along z."""
+    h = 1.0 / nx
+    kk, jj, ii = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    coords = np.stack([ii * h, jj * h, kk * h], axis=1).astype(np.float64)
+    interior = (ii > 0) & (ii < nx) & (jj > 0) & (jj < ny) & (kk > 0) & (kk < nz)
+    _jitter_grid(coords, interior, h, jitter, seed)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    base = ((k.ravel() * (ny + 1)) + j.ravel()) * (nx + 1) + i.ravel()
+    conn = np.empty((nx * ny * nz, 8), dtype=np.int32)
+    for a in range(8):
+        di, dj, dk = a & 1, (a >> 1) & 1, (a >> 2) & 1
+        conn[:, a] = base + (dk * (ny + 1) + dj) * (nx + 1) + di
+    return {"dim": 3, "elem": "Q1", "n": nx, "coords": coords, "conn": conn}
+
+
 def hex20_mesh(n: int, jitter: float = 0.0, seed: int = SEED_JITTER) -> dict:
     """20-node serendipity bricks on the unit cube from an ``n^3`` grid.
 
@@ -533,6 +553,19 @@ def elastic_problem(n: int = 64, jitter: float = 0.15, sigma: float = 0.5, nu: f
     """3D linear elasticity on jittered Q1 hexahedra (64^3: 262,144 elements)."""
     m = hex_mesh(n, jitter, seed_jitter)
     m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)  # Young's modulus E
+    m["nu"] = nu
+    m["body"] = (0.0, 0.0, -1.0)
+    m["bc_mask"], m["bc_val"] = elastic_bc(m)
+    m["form"] = "elastic"
+    return m
+
+
+def elastic_box_problem(nx: int, ny: int, nz: int, jitter: float = 0.15, sigma: float = 0.5, nu: float = 0.3,
+                        seed_jitter: int = SEED_JITTER, seed_coef: int = SEED_COEF) -> dict:
+    """The elasticity workload of ``elastic_problem`` on an nx x ny x nz box of
+    cubes of side 1 / nx (clamped at x = 0, body force (0, 0, -1))."""
+    m = hex_box_mesh(nx, ny, nz, jitter, seed_jitter)
+    m["coef"] = lognormal(seed_coef, m["conn"].shape[0], sigma)
     m["nu"] = nu
     m["body"] = (0.0, 0.0, -1.0)
     m["bc_mask"], m["bc_val"] = elastic_bc(m)
