@@ -53,10 +53,13 @@ typedef enum {
 typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2, MF_Q2S_HEX = 3, MF_P2_TET = 4, MF_Q2S_QUAD = 5 } mf_elem;
 typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2, MF_FORM_CAPACITY = 3 } mf_form;
 typedef enum { MF_PREC_FP64 = 0, MF_PREC_MIXED = 1 } mf_prec;
-typedef enum { MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1 } mf_solver;
+typedef enum {
+    MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1, MF_SOLVER_PCG_REFINED = 2, MF_SOLVER_GMRES_FLOW_MG = 3
+} mf_solver;
 
 typedef struct mf_mesh mf_mesh;
 typedef struct mf_pattern mf_pattern;
+typedef struct mf_flow_mg mf_flow_mg;
 
 /* Mesh description (Block B-1: elements and their element->control-point map).
  * coords [n_nodes][dim] f64 AoS; conn [n_elems][npe] int32 with npe = 3 (P1),
@@ -128,12 +131,16 @@ typedef struct {
     const double *precond_diag; /* GMRES: device [n] diagonal P (x = P^-1 y);
                                    NULL = diag(K).  PCG always uses diag(K). */
     int32_t check_every;     /* host reads the residual every k iterations (>= 1) */
+    double inner_tol;        /* MF_SOLVER_PCG_REFINED: relative residual of each FP32
+                                inner solve (0: 1e-4) */
+    const mf_flow_mg *flow_mg; /* MF_SOLVER_GMRES_FLOW_MG: the preconditioner hierarchy */
 } mf_solver_opts;
 
 typedef struct {
-    int64_t iterations;
-    double rel_residual;     /* true ||d - K x|| / ||d|| recomputed at exit */
+    int64_t iterations;      /* PCG / GMRES iterations; refined PCG: inner FP32 iterations */
+    double rel_residual;     /* true ||d - K x|| / ||d|| recomputed at exit (FP64) */
     int32_t converged;
+    int64_t refinements;     /* MF_SOLVER_PCG_REFINED: FP64 correction steps */
 } mf_solve_info;
 
 /* Validates and wraps a mesh (Block B-1).  Checks on the device that every
@@ -329,9 +336,36 @@ mf_status mf_pressure_mass_diag(const mf_mesh *mesh, const mf_pattern *pattern, 
 mf_status mf_flow_precond(const mf_mesh *mesh, const mf_pattern *pattern, const mf_csr *K,
                           const uint8_t *bc_mask, double p_scale, double *out, void *stream);
 
+/* Preconditioner of the flow system (Sec. 4.3 Picard form on the Taylor-Hood
+ * P2-P1 split-square grids, dofs [u1 | u2 | p]) for MF_SOLVER_GMRES_FLOW_MG:
+ * the block upper-triangular M = [A B^T; 0 S] applied exactly in its block
+ * structure, S = diag(M_p) / visc (pressure mass over the viscosity, 1 on a
+ * constrained pressure dof), and A^-1 replaced by one geometric multigrid
+ * V-cycle (2 + 2 damped Jacobi sweeps with weight 4 / (3 lambda_max(D^-1 A)),
+ * 60 on the coarsest grid, P2 interpolation between grids and its transpose,
+ * constrained velocity dofs held).  K[l], bc_mask[l] (device, [n_rows of
+ * level l]) are the flow systems assembled by mf_assemble on the grids of
+ * cells[l] cells per side, finest first, each grid halving the previous one
+ * (levels <= 12); pmass (device [n_pnodes]) is mf_pressure_mass_diag of the
+ * finest grid.  The hierarchy copies what it needs (the velocity blocks,
+ * masks); the caller keeps K[0] for the solve.  Synchronises the stream.
+ * Errors: MF_ERR_INVALID_ARG (levels, sizes), MF_ERR_NONFINITE (a zero
+ * diagonal), MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_flow_mg_create(int32_t levels, const mf_csr *const *K, const int64_t *cells,
+                            const uint8_t *const *bc_mask, const double *pmass, double visc, void *stream,
+                            mf_flow_mg **out);
+mf_status mf_flow_mg_destroy(mf_flow_mg *mg);
+
 /* Solves K x = d (Block D-4; the paper leaves the solver open): Jacobi-PCG
- * (symmetric positive K) or right-preconditioned restarted GMRES(m) with
- * classical Gram-Schmidt applied twice.  x holds x0 on entry (a warm start
+ * (symmetric positive K), right-preconditioned restarted GMRES(m) with
+ * classical Gram-Schmidt applied twice, or (MF_SOLVER_PCG_REFINED) FP64
+ * iterative refinement around an FP32 Jacobi-PCG: the residual r = d - K x
+ * is formed in FP64 with K as given, each correction K z = r / ||r|| is
+ * solved on an FP32 copy of K with FP32 vectors to inner_tol, and x += ||r|| z
+ * in FP64, until ||d - K x|| <= tol ||d|| (max_iter caps the inner
+ * iterations; the refinement needs kappa(K) 2^-24 well below 1), or
+ * (MF_SOLVER_GMRES_FLOW_MG) right-preconditioned GMRES(restart) with the
+ * flow hierarchy opts->flow_mg (mf_flow_mg_create).  x holds x0 on entry (a warm start
  * resumes a previous solve) and the solution on exit.  Synchronises the
  * stream.  Returns MF_ERR_NOT_CONVERGED (x = last iterate, info filled) at
  * max_iter, MF_ERR_NONFINITE for a non-finite d or a breakdown, and any

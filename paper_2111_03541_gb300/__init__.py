@@ -22,7 +22,7 @@ MF_OK, MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH, MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR
 MF_P1_TRI, MF_P2_TRI, MF_Q1_HEX, MF_Q2S_HEX, MF_P2_TET, MF_Q2S_QUAD = 0, 1, 2, 3, 4, 5
 MF_FORM_THERMAL, MF_FORM_ELASTIC, MF_FORM_OSEEN, MF_FORM_CAPACITY = 0, 1, 2, 3
 MF_PREC_FP64, MF_PREC_MIXED = 0, 1
-MF_SOLVER_PCG, MF_SOLVER_GMRES = 0, 1
+MF_SOLVER_PCG, MF_SOLVER_GMRES, MF_SOLVER_PCG_REFINED, MF_SOLVER_GMRES_FLOW_MG = 0, 1, 2, 3
 
 ELEM = {"P1": MF_P1_TRI, "P2": MF_P2_TRI, "Q1": MF_Q1_HEX, "Q2S": MF_Q2S_HEX, "P2T": MF_P2_TET, "Q2Q": MF_Q2S_QUAD}
 FORM = {"thermal": MF_FORM_THERMAL, "elastic": MF_FORM_ELASTIC, "oseen": MF_FORM_OSEEN}
@@ -52,7 +52,8 @@ class CSR(C.Structure):
 
 class SolverOpts(C.Structure):
     _fields_ = [("solver", C.c_int32), ("restart", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int64),
-                ("precond_diag", C.c_void_p), ("check_every", C.c_int32)]
+                ("precond_diag", C.c_void_p), ("check_every", C.c_int32), ("inner_tol", C.c_double),
+                ("flow_mg", C.c_void_p)]
 
 
 class BatchTiling(C.Structure):
@@ -71,7 +72,8 @@ class GenAlphaParams(C.Structure):
 
 
 class SolveInfo(C.Structure):
-    _fields_ = [("iterations", C.c_int64), ("rel_residual", C.c_double), ("converged", C.c_int32)]
+    _fields_ = [("iterations", C.c_int64), ("rel_residual", C.c_double), ("converged", C.c_int32),
+                ("refinements", C.c_int64)]
 
 
 _lib = None
@@ -98,6 +100,9 @@ _SIGS = {
     "mf_genalpha_initial_rate": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.c_void_p],
     "mf_pressure_mass_diag": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "mf_flow_mg_create": [C.c_int32, C.POINTER(C.POINTER(CSR)), C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p,
+                          C.c_double, C.c_void_p, C.POINTER(C.c_void_p)],
+    "mf_flow_mg_destroy": [C.c_void_p],
     "mf_flow_precond": [C.c_void_p, C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_double, C.c_void_p, C.c_void_p],
     "mf_solve": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_void_p],
     "mf_solve_pcg_noalloc": [C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_double, C.c_int64, C.c_int32,
@@ -255,6 +260,25 @@ def mf_genalpha_initial_rate(K: CSR, M_values, F, bc_mask, phi, u, pcg_tol: floa
 
 def mf_pressure_mass_diag(mesh, pattern, out, stream=None) -> None:
     _check(lib().mf_pressure_mass_diag(mesh, pattern, _ptr(out), _stream(stream)))
+
+
+def mf_flow_mg_create(systems, cells, bc_masks, pmass, visc: float, stream=None):
+    """systems: CSR structures of the flow systems, finest first; cells: grid
+    cells per side of each; bc_masks: their device masks; pmass: the finest
+    pressure-mass diagonal (device).  Returns the opaque hierarchy handle."""
+    import numpy as np
+    n = len(systems)
+    arr = (C.POINTER(CSR) * n)(*[C.pointer(k) for k in systems])
+    cl = np.ascontiguousarray(cells, dtype=np.int64)
+    masks = (C.c_void_p * n)(*[_ptr(m) for m in bc_masks])
+    out = C.c_void_p()
+    _check(lib().mf_flow_mg_create(n, arr, cl.ctypes.data_as(C.c_void_p), masks, _ptr(pmass), visc,
+                                   _stream(stream), C.byref(out)))
+    return out
+
+
+def mf_flow_mg_destroy(mg) -> None:
+    _check(lib().mf_flow_mg_destroy(mg))
 
 
 def mf_flow_precond(mesh, pattern, K: CSR, bc_mask, p_scale: float, out, stream=None) -> None:
@@ -514,12 +538,13 @@ class Problem:
         return out
 
     def solve(self, x=None, solver=MF_SOLVER_PCG, tol=1e-10, max_iter=100000, restart=50, precond=None,
-              check_every=50, stream=None):
+              check_every=50, inner_tol=0.0, flow_mg=None, stream=None):
         import torch
         if x is None:
             x = torch.zeros(self.n, dtype=torch.float64, device=self.device)
         opts = SolverOpts(solver=solver, restart=restart, tol=tol, max_iter=max_iter,
-                          precond_diag=_ptr(precond), check_every=check_every)
+                          precond_diag=_ptr(precond), check_every=check_every, inner_tol=inner_tol,
+                          flow_mg=flow_mg.value if flow_mg is not None else None)
         st, info = mf_solve(self.csr, self.d, x, opts, stream)
         return x, st, info
 

@@ -528,11 +528,34 @@ extern "C" mf_status mf_solve(const mf_csr *K, const double *d, double *x, const
 {
     g_msg[0] = 0;
     if (!csr_ok(K) || !d || !x || !opts) return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: NULL argument");
-    if (opts->solver != MF_SOLVER_PCG && opts->solver != MF_SOLVER_GMRES)
+    if (opts->solver < MF_SOLVER_PCG || opts->solver > MF_SOLVER_GMRES_FLOW_MG)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: unknown solver %d", opts->solver);
-    if (!(opts->tol > 0.0) || opts->max_iter < 0 || (opts->solver == MF_SOLVER_GMRES && opts->restart < 1))
+    if (opts->solver == MF_SOLVER_GMRES_FLOW_MG && !opts->flow_mg)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: MF_SOLVER_GMRES_FLOW_MG needs opts->flow_mg");
+    const bool gm = opts->solver == MF_SOLVER_GMRES || opts->solver == MF_SOLVER_GMRES_FLOW_MG;
+    if (!(opts->tol > 0.0) || opts->max_iter < 0 || (gm && opts->restart < 1))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: tol > 0, max_iter >= 0, restart >= 1 required");
     return mf_solve_impl(K, d, x, opts, info, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" mf_status mf_flow_mg_create(int32_t levels, const mf_csr *const *K, const int64_t *cells,
+                                       const uint8_t *const *bc_mask, const double *pmass, double visc,
+                                       void *stream, mf_flow_mg **out)
+{
+    g_msg[0] = 0;
+    if (!K || !cells || !bc_mask || !pmass || !out || levels < 1 || levels > 12 || !(visc > 0.0))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_flow_mg_create: NULL argument, levels outside [1, 12] or visc <= 0");
+    for (int l = 0; l < levels; ++l)
+        if (!csr_ok(K[l]) || !bc_mask[l]) return mf_fail(MF_ERR_INVALID_ARG, "mf_flow_mg_create: level %d", l);
+    *out = nullptr;
+    return mf_flow_mg_create_impl(levels, K, cells, bc_mask, pmass, visc, static_cast<cudaStream_t>(stream), out);
+}
+
+extern "C" mf_status mf_flow_mg_destroy(mf_flow_mg *mg)
+{
+    g_msg[0] = 0;
+    mf_flow_mg_destroy_impl(mg);
+    return MF_OK;
 }
 
 extern "C" mf_status mf_spmv(const mf_csr *K, const double *x, double *y, void *stream)

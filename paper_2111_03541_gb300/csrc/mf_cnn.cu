@@ -1039,6 +1039,7 @@ extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *
         info->iterations = it;
         info->rel_residual = dn2 > 0 ? sqrt(tr[0] / dn2) : sqrt(tr[0]);
         info->converged = done == 1;
+        info->refinements = 0;
     }
     if (fallbacks) *fallbacks = fb;
     if (done == 3) return mf_fail(MF_ERR_NONFINITE, "mf_solve_fcg_cnn: breakdown");

@@ -194,6 +194,10 @@ mf_status mf_pmass_impl(const mf_mesh *m, const mf_pattern *p, double *out, cuda
 mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o,
                         mf_solve_info *info, cudaStream_t st);
 mf_status mf_spmv_impl(const mf_csr *K, const double *x, double *y, cudaStream_t st);
+mf_status mf_flow_mg_create_impl(int levels, const mf_csr *const *K, const int64_t *cells,
+                                 const uint8_t *const *bc_mask, const double *pmass, double visc, cudaStream_t st,
+                                 mf_flow_mg **out);
+void mf_flow_mg_destroy_impl(mf_flow_mg *G);
 
 // kernel timing (tracing): bracket a launch on stream st with events when enabled
 void mf_prof_begin(const char *name, cudaStream_t st);

@@ -725,10 +725,302 @@ mf_status solve_pcg(const mf_csr *K, const double *d, double *x, const mf_solver
         info->iterations = h.iter;
         info->rel_residual = relres;
         info->converged = h.done == 1;
+        info->refinements = 0;
     }
     if (h.done == 2) s = mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve: %lld iterations, residual %.3e", h.iter, relres);
     if (h.done == 3) s = mf_fail(MF_ERR_NONFINITE, "mf_solve: breakdown or non-finite value");
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 iterative refinement around an FP32 Jacobi-PCG (the mixed path's
+// solve): the outer residual r = d - K x uses the FP64 K; each correction
+// K32 z = r / ||r|| is solved in FP32 (values and vectors) to a relative
+// residual inner_tol, and x += ||r|| z in FP64.  The refinement converges to
+// K^-1 d as long as kappa(K) 2^-24 stays well below 1.
+// ---------------------------------------------------------------------------
+template <int W, int U>
+__device__ __forceinline__ float row_dot32(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                           const float *__restrict__ v, const float *__restrict__ x, int64_t row,
+                                           int sub, bool valid)
+{
+    float s = 0.f;
+    if (valid) {
+        const int64_t t1 = rp[row + 1];
+        for (int64_t t = rp[row] + sub; t < t1; t += (int64_t)U * W) {
+            int32_t c[U];
+            float a[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t tt = t + (int64_t)u * W;
+                const bool ok = tt < t1;
+                c[u] = ok ? __ldcs(&ci[tt]) : -1;
+                a[u] = ok ? __ldcs(&v[tt]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(&x[c[u]]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) s = fmaf(a[u], xv[u], s);
+        }
+    }
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, W);
+    return s;
+}
+
+template <int W, int U>
+__global__ void __launch_bounds__(RT) k_pcg32_spmv(int64_t n, const int64_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ ci, const float *__restrict__ v,
+                                                   const float *__restrict__ p, float *__restrict__ q,
+                                                   const PcgState *S)
+{
+    if (S->done) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = g / W;
+    const int sub = (int)(g % W);
+    const bool valid = row < n;
+    const float s = row_dot32<W, U>(rp, ci, v, p, row, sub, valid);
+    if (valid && sub == 0) q[row] = s;
+}
+
+__global__ void __launch_bounds__(RT) k_pcg32_pq(int64_t n, const float *__restrict__ p, const float *__restrict__ q,
+                                                 double *__restrict__ part, PcgState *S)
+{
+    __shared__ double sh[RT / 32];
+    if (S->done) return;
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fmaf(p[i], q[i], acc);
+    const double bs = block_sum((double)acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    if (last_block(&S->ticket)) {
+        double pq;
+        finish_sums<1>(part, gridDim.x, &pq, sh);
+        if (threadIdx.x == 0) {
+            S->pq = pq;
+            if (!(pq > 0.0) || !isfinite(pq)) S->done = 3;
+            else S->alpha = S->rz / pq;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_pcg32_update(int64_t n, const float *__restrict__ dinv,
+                                                     const float *__restrict__ p, const float *__restrict__ q,
+                                                     float *__restrict__ x, float *__restrict__ r,
+                                                     double *__restrict__ part, PcgState *S)
+{
+    __shared__ double sh[RT / 32];
+    if (S->done) return;
+    const float alpha = (float)S->alpha;
+    float rz = 0.f, rr = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = fmaf(alpha, p[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rz = fmaf(ri * dinv[i], ri, rz);
+        rr = fmaf(ri, ri, rr);
+    }
+    const double bz = block_sum((double)rz, sh);
+    const double br = block_sum((double)rr, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = bz;
+        part[2 * blockIdx.x + 1] = br;
+    }
+    if (last_block(&S->ticket)) {
+        double zs[2];
+        finish_sums<2>(part, gridDim.x, zs, sh);
+        if (threadIdx.x != 0) return;
+        const double z = zs[0], s2 = zs[1];
+        S->iter += 1;
+        S->rr = s2;
+        if (!isfinite(s2) || !isfinite(z)) S->done = 3;
+        else if (s2 <= S->tol2 * S->dd) S->done = 1;
+        else if (S->iter >= S->max_iter) S->done = 2;
+        S->beta = z / S->rz;
+        S->rz = z;
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_pcg32_dir(int64_t n, const float *__restrict__ dinv,
+                                                  const float *__restrict__ r, float *__restrict__ p,
+                                                  const PcgState *S)
+{
+    if (S->done) return;
+    const float beta = (float)S->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fmaf(beta, p[i], dinv[i] * r[i]);
+}
+
+// K32 = float(K), dinv32 = 1 / diag(K) (rounded once)
+__global__ void k_to_f32(int64_t m, const double *__restrict__ a, float *__restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) b[i] = (float)a[i];
+}
+
+// r = d - K x (FP64) with the partial sums of r.r and d.d; b = r / ||r|| is
+// formed by the next kernel once the norm is known
+__global__ void __launch_bounds__(RT) k_ref_resid(int64_t n, const double *__restrict__ d,
+                                                  const double *__restrict__ kx, double *__restrict__ r,
+                                                  double *__restrict__ part, unsigned *ticket, double *out2)
+{
+    __shared__ double sh[RT / 32];
+    double rr = 0.0, dd = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = d[i] - kx[i];
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+        dd = fma(d[i], d[i], dd);
+    }
+    const double a = block_sum(rr, sh), b = block_sum(dd, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+    if (last_block(ticket)) {
+        double st2[2];
+        finish_sums<2>(part, gridDim.x, st2, sh);
+        if (threadIdx.x == 0) {
+            out2[0] = st2[0];
+            out2[1] = st2[1];
+        }
+    }
+}
+
+// inner start: b = r / ||r||, z = 0, rr = D^-1 b, p = D^-1 b; rz, rr, dd (= b.b)
+__global__ void __launch_bounds__(RT) k_ref_start(int64_t n, const double *__restrict__ r, double inv_nrm,
+                                                  const float *__restrict__ dinv, float *__restrict__ z,
+                                                  float *__restrict__ ri, float *__restrict__ p,
+                                                  double *__restrict__ part, PcgState *S)
+{
+    __shared__ double sh[RT / 32];
+    float rz = 0.f, rr = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float b = (float)(r[i] * inv_nrm);
+        z[i] = 0.f;
+        ri[i] = b;
+        p[i] = dinv[i] * b;
+        rz = fmaf(b * dinv[i], b, rz);
+        rr = fmaf(b, b, rr);
+    }
+    const double a = block_sum((double)rz, sh), c = block_sum((double)rr, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = c;
+    }
+    if (last_block(&S->ticket)) {
+        double zs[2];
+        finish_sums<2>(part, gridDim.x, zs, sh);
+        if (threadIdx.x != 0) return;
+        S->rz = zs[0];
+        S->rr = zs[1];
+        S->dd = zs[1];
+        S->iter = 0;
+        S->done = (!isfinite(zs[0]) || !isfinite(zs[1])) ? 3 : 0;
+    }
+}
+
+// x += s z (FP64 update of the outer iterate)
+__global__ void k_ref_update(int64_t n, double s, const float *__restrict__ z, double *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = fma(s, (double)z[i], x[i]);
+}
+
+template <int W, int U>
+void launch_pcg32_iter(const mf_csr *K, const float *v32, const float *dinv, float *z, float *r, float *p,
+                       float *q, double *part, PcgState *S, cudaStream_t st)
+{
+    const int64_t n = K->n_rows;
+    k_pcg32_spmv<W, U><<<nblk(n * W, RT), RT, 0, st>>>(n, K->row_ptr, K->col_idx, v32, p, q, S);
+    k_pcg32_pq<<<red_grid(n), RT, 0, st>>>(n, p, q, part, S);
+    k_pcg32_update<<<red_grid(n), RT, 0, st>>>(n, dinv, p, q, z, r, part, S);
+    k_pcg32_dir<<<red_grid(n), RT, 0, st>>>(n, dinv, r, p, S);
+}
+
+mf_status solve_refined(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o, mf_solve_info *info,
+                        cudaStream_t st)
+{
+    const int64_t n = K->n_rows, nnz = K->nnz;
+    const double inner_tol = o->inner_tol > 0.0 ? o->inner_tol : 1e-4;
+    DevBuf<double> r64(st), kx(st), part(st), dinv64(st), out2(st);
+    DevBuf<float> v32(st), dinv(st), z(st), r(st), p(st), q(st);
+    DevBuf<PcgState> S(st);
+    DevBuf<int> bad(st);
+    MF_CUDA(r64.alloc(n));
+    MF_CUDA(kx.alloc(n));
+    MF_CUDA(part.alloc(pcg_parts(n)));
+    MF_CUDA(dinv64.alloc(n));
+    MF_CUDA(out2.alloc(2));
+    MF_CUDA(v32.alloc(nnz));
+    MF_CUDA(dinv.alloc(n));
+    MF_CUDA(z.alloc(n));
+    MF_CUDA(r.alloc(n));
+    MF_CUDA(p.alloc(n));
+    MF_CUDA(q.alloc(n));
+    MF_CUDA(S.alloc(1));
+    MF_CUDA(bad.alloc(1));
+    MF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    MF_CUDA(cudaMemsetAsync(S.p, 0, sizeof(PcgState), st));
+    k_diag_inv<<<nblk(n, RT), RT, 0, st>>>(n, K->row_ptr, K->col_idx, K->values, dinv64.p, bad.p);
+    k_to_f32<<<nblk(n, RT), RT, 0, st>>>(n, dinv64.p, dinv.p);
+    k_to_f32<<<nblk(nnz, RT), RT, 0, st>>>(nnz, K->values, v32.p);
+    MF_CUDA(cudaGetLastError());
+    int hb = 0;
+    MF_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (hb) return mf_fail(MF_ERR_NONFINITE, "mf_solve: zero or non-finite diagonal entry");
+    const SpmvShape shape = spmv_shape(n, nnz);
+    const int chunk = o->check_every > 0 ? o->check_every : 50;
+    int64_t inner_total = 0, refinements = 0;
+    double relres = 0.0;
+    int done = 0;  // 1 converged, 2 cap, 3 breakdown
+    for (;;) {
+        spmv_any(K, K->values, x, kx.p, st);
+        k_ref_resid<<<red_grid(n), RT, 0, st>>>(n, d, kx.p, r64.p, part.p, &S.p->ticket, out2.p);
+        MF_CUDA(cudaGetLastError());
+        double h2[2];
+        MF_CUDA(cudaMemcpyAsync(h2, out2.p, sizeof h2, cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        const double rn = sqrt(h2[0]);
+        relres = h2[1] > 0.0 ? rn / sqrt(h2[1]) : rn;
+        if (!isfinite(relres)) { done = 3; break; }
+        if (relres <= o->tol || rn == 0.0) { done = 1; break; }
+        if (inner_total >= o->max_iter) { done = 2; break; }
+        // inner FP32 Jacobi-PCG on K32 z = r / ||r|| from z = 0
+        PcgState hs{};
+        hs.tol2 = inner_tol * inner_tol;
+        hs.max_iter = o->max_iter - inner_total;
+        MF_CUDA(cudaMemcpyAsync(S.p, &hs, sizeof hs, cudaMemcpyHostToDevice, st));
+        k_ref_start<<<red_grid(n), RT, 0, st>>>(n, r64.p, 1.0 / rn, dinv.p, z.p, r.p, p.p, part.p, S.p);
+        MF_CUDA(cudaGetLastError());
+        for (;;) {
+            for (int it = 0; it < chunk; ++it)
+                spmv_dispatch(shape, [&](auto Wc, auto Uc) {
+                    launch_pcg32_iter<decltype(Wc)::value, decltype(Uc)::value>(K, v32.p, dinv.p, z.p, r.p, p.p,
+                                                                                 q.p, part.p, S.p, st);
+                });
+            MF_CUDA(cudaGetLastError());
+            MF_CUDA(cudaMemcpyAsync(&hs, S.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+            MF_CUDA(cudaStreamSynchronize(st));
+            if (hs.done) break;
+        }
+        inner_total += hs.iter;
+        if (hs.done == 3) { done = 3; break; }
+        k_ref_update<<<nblk(n, RT), RT, 0, st>>>(n, rn, z.p, x);
+        ++refinements;
+    }
+    if (info) {
+        info->iterations = inner_total;
+        info->rel_residual = relres;
+        info->converged = done == 1;
+        info->refinements = refinements;
+    }
+    if (done == 2)
+        return mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve: %lld inner iterations, residual %.3e", (long long)inner_total,
+                       relres);
+    if (done == 3) return mf_fail(MF_ERR_NONFINITE, "mf_solve: breakdown or non-finite value");
+    return MF_OK;
 }
 
 mf_status solve_gmres(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o, mf_solve_info *info,
@@ -832,10 +1124,213 @@ mf_status solve_gmres(const mf_csr *K, const double *d, double *x, const mf_solv
         info->iterations = hs.iter;
         info->rel_residual = relres;
         info->converged = hs.done == 1;
+        info->refinements = 0;
     }
     if (hs.done == 2) return mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve: %lld iterations, residual %.3e", hs.iter, relres);
     if (hs.done == 3) return mf_fail(MF_ERR_NONFINITE, "mf_solve: breakdown or non-finite value");
     return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Flow system (Sec. 4.3 Picard form, Taylor-Hood P2-P1, [u1 | u2 | p]):
+// right-preconditioned GMRES(m) with the block upper-triangular
+//   M = [ A  B^T ]      M^-1 [v_u; v_p]:  z_p = S^-1 v_p,
+//       [ 0   S  ]                       z_u = A^-1 (v_u - B^T z_p),
+// S = diag(M_p) / nu (the pressure mass scaled by the viscosity, a spectrally
+// equivalent stand-in for the Schur complement B A^-1 B^T of a viscous flow),
+// and A^-1 (the same matrix for u1 and u2) replaced by one geometric
+// multigrid V-cycle over the structured P2 grids of the hierarchy: damped
+// Jacobi smoothing, P2 interpolation to the finer grid and its transpose
+// back, operators rediscretised by the caller (its assembly on each grid).
+// The preconditioner is a fixed linear operator, so plain right-
+// preconditioned GMRES applies.
+// ---------------------------------------------------------------------------
+
+// rows [0, nv) of K restricted to columns < nv: entry counts, then the fill
+__global__ void k_block_count(int64_t nv, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              int64_t *__restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    int64_t c = 0;
+    for (int64_t t = rp[i]; t < rp[i + 1]; ++t) c += ci[t] < nv;
+    cnt[i] = c;
+}
+__global__ void k_block_fill(int64_t nv, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ v, const int64_t *__restrict__ orp, int32_t *__restrict__ oci,
+                             double *__restrict__ ov)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    int64_t o = orp[i];
+    for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
+        if (ci[t] < nv) {
+            oci[o] = ci[t];
+            ov[o] = v[t];
+            ++o;
+        }
+}
+
+// P2 interpolation from the grid of nc cells per side to the grid of 2 nc
+// (the split-square Taylor-Hood meshes: P2 nodes on the (2n + 1)^2 lattice,
+// x fastest; cell (i, j) split by its diagonal into (v00, v10, v11) and
+// (v00, v11, v01)).  Fine node (fi, fj) sits at (fi / 4, fj / 4) in coarse
+// cell units; row of P: the 6 coarse P2 basis values there (vertices
+// l (2 l - 1), edge midpoints 4 la lb), columns ascending.
+__global__ void k_p2_prolong(int64_t nc, int64_t *__restrict__ prp, int32_t *__restrict__ pci,
+                             double *__restrict__ pv)
+{
+    const int64_t nfs = 4 * nc + 1;  // fine lattice side
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nfs * nfs) return;
+    const int64_t fi = id % nfs, fj = id / nfs;
+    int64_t ic = fi / 4, jc = fj / 4;
+    if (ic == nc) ic = nc - 1;
+    if (jc == nc) jc = nc - 1;
+    const double xi = 0.25 * (double)(fi - 4 * ic), eta = 0.25 * (double)(fj - 4 * jc);
+    const int64_t ncs = 2 * nc + 1;  // coarse lattice side
+    auto node = [&](int64_t a, int64_t b) { return (int32_t)((2 * jc + b) * ncs + 2 * ic + a); };
+    int32_t c[6];
+    double l0, l1, l2;
+    if (xi >= eta) {  // (v00, v10, v11)
+        l0 = 1.0 - xi; l1 = xi - eta; l2 = eta;
+        c[0] = node(0, 0); c[1] = node(2, 0); c[2] = node(2, 2);
+        c[3] = node(1, 0); c[4] = node(2, 1); c[5] = node(1, 1);
+    } else {          // (v00, v11, v01)
+        l0 = 1.0 - eta; l1 = xi; l2 = eta - xi;
+        c[0] = node(0, 0); c[1] = node(2, 2); c[2] = node(0, 2);
+        c[3] = node(1, 1); c[4] = node(1, 2); c[5] = node(0, 1);
+    }
+    double w[6] = {l0 * (2.0 * l0 - 1.0), l1 * (2.0 * l1 - 1.0), l2 * (2.0 * l2 - 1.0), 4.0 * l0 * l1, 4.0 * l1 * l2,
+                   4.0 * l2 * l0};
+    for (int a = 1; a < 6; ++a)  // ascending columns
+        for (int b = a; b > 0 && c[b - 1] > c[b]; --b) {
+            const int32_t tc = c[b]; c[b] = c[b - 1]; c[b - 1] = tc;
+            const double tw = w[b]; w[b] = w[b - 1]; w[b - 1] = tw;
+        }
+    prp[id] = 6 * id;
+    if (id == 0) prp[nfs * nfs] = 6 * nfs * nfs;
+    for (int a = 0; a < 6; ++a) {
+        pci[6 * id + a] = c[a];
+        pv[6 * id + a] = w[a];
+    }
+}
+
+// R = P^T: counts per column, then entries by an atomic cursor, then each
+// row sorted by column (so the result does not depend on the atomics' order)
+__global__ void k_tr_count(int64_t nnz, const int32_t *__restrict__ ci, int64_t *__restrict__ cnt)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nnz) atomicAdd(reinterpret_cast<unsigned long long *>(cnt + ci[t]), 1ull);
+}
+__global__ void k_tr_fill(int64_t nrows, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ v, const int64_t *__restrict__ trp, int64_t *__restrict__ cur,
+                          int32_t *__restrict__ tci, double *__restrict__ tv)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    for (int64_t t = rp[i]; t < rp[i + 1]; ++t) {
+        const int64_t o = trp[ci[t]] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(cur + ci[t]), 1ull);
+        tci[o] = (int32_t)i;
+        tv[o] = v[t];
+    }
+}
+__global__ void k_tr_sort(int64_t n, const int64_t *__restrict__ trp, int32_t *__restrict__ tci,
+                          double *__restrict__ tv)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t a = trp[i] + 1; a < trp[i + 1]; ++a)
+        for (int64_t b = a; b > trp[i] && tci[b - 1] > tci[b]; --b) {
+            const int32_t c = tci[b]; tci[b] = tci[b - 1]; tci[b - 1] = c;
+            const double w = tv[b]; tv[b] = tv[b - 1]; tv[b - 1] = w;
+        }
+}
+
+// sum of squares, finished by the last block
+__global__ void __launch_bounds__(RT) k_sumsq(int64_t n, const double *__restrict__ x, double *__restrict__ part,
+                                              unsigned *ticket, double *out)
+{
+    __shared__ double sh[RT / 32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(x[i], x[i], acc);
+    const double b = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+    if (last_block(ticket)) {
+        double s;
+        finish_sums<1>(part, gridDim.x, &s, sh);
+        if (threadIdx.x == 0) *out = s;
+    }
+}
+
+__global__ void k_fill_pattern(int64_t n, double *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 1.0 + 0.125 * (double)(i % 7) - 0.0625 * (double)(i % 5);
+}
+__global__ void k_scale_into(int64_t n, const double *__restrict__ a, const double *__restrict__ b, double s,
+                             double *__restrict__ out)  // out = s a b
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = s * a[i] * b[i];
+}
+// damped Jacobi step x += w D^-1 (b - A x) (t = A x); constrained rows x = b
+__global__ void k_scal(int64_t n, double s, const double *__restrict__ a, double *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = s * a[i];
+}
+__global__ void k_jacobi(int64_t n, const double *__restrict__ b, const double *__restrict__ t,
+                         const double *__restrict__ dinv, const uint8_t *__restrict__ mask, double w,
+                         double *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[i] = mask[i] ? b[i] : fma(w * dinv[i], b[i] - t[i], x[i]);
+}
+// first sweep from x = 0
+__global__ void k_jacobi0(int64_t n, const double *__restrict__ b, const double *__restrict__ dinv,
+                          const uint8_t *__restrict__ mask, double w, double *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = mask[i] ? b[i] : w * dinv[i] * b[i];
+}
+__global__ void k_resid(int64_t n, const double *__restrict__ b, const double *__restrict__ t, double *__restrict__ r)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = b[i] - t[i];
+}
+__global__ void k_zero_masked(int64_t n, const uint8_t *__restrict__ mask, double *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && mask[i]) x[i] = 0.0;
+}
+__global__ void k_add_unmasked(int64_t n, const uint8_t *__restrict__ mask, const double *__restrict__ t,
+                               double *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !mask[i]) x[i] += t[i];
+}
+// block-triangular pieces: w = [0; 0; S^-1 v_p], rhs_u = v_u - (K w)_u
+__global__ void k_bt_pressure(int64_t nu, int64_t np, const double *__restrict__ v, const double *__restrict__ sinv,
+                              double *__restrict__ w)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nu) w[i] = 0.0;
+    else if (i < nu + np) w[i] = sinv[i - nu] * v[i];
+}
+// S^-1 = nu / Mp on pressure dofs, 1 on constrained ones
+__global__ void k_sinv(int64_t n1, const double *__restrict__ pmass, const uint8_t *__restrict__ pmask, double nu,
+                       double *__restrict__ sinv)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1) sinv[i] = (pmask && pmask[i]) ? 1.0 : nu / pmass[i];
+}
+__global__ void k_axpy_vec(int64_t n, const double *__restrict__ a, double *__restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += a[i];
 }
 
 }  // namespace
@@ -945,12 +1440,326 @@ extern "C" mf_status mf_solve_pcg_noalloc(const mf_csr *K, const double *d, doub
         info->iterations = h.iter;
         info->rel_residual = relres;
         info->converged = h.done == 1;
+        info->refinements = 0;
     }
     s = MF_OK;
     if (h.done == 2)
         s = mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve_pcg_noalloc: %lld iterations, residual %.3e", h.iter, relres);
     if (h.done == 3) s = mf_fail(MF_ERR_NONFINITE, "mf_solve_pcg_noalloc: breakdown or non-finite value");
     return finish_status(s, status, st);
+}
+
+// ---------------------------------------------------------------------------
+// Flow multigrid hierarchy (see the kernels above)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int MG_MAX_LEVELS = 12;
+struct MgLevel {
+    int64_t n = 0, cells = 0;  // velocity dofs of one component (P2 nodes), grid cells per side
+    mf_csr A{};                // the u1-u1 block (equal to the u2-u2 block)
+    double *dinv = nullptr;
+    double omega = 0.0;        // Jacobi damping 4 / (3 lambda_max(D^-1 A))
+    uint8_t *mask = nullptr;   // constrained nodes
+    mf_csr P{}, R{};           // to the next coarser level: P (n x n_coarse) and R = P^T
+    double *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+};
+}  // namespace
+
+struct mf_flow_mg {
+    int levels = 0;
+    MgLevel L[MG_MAX_LEVELS];
+    int64_t n2 = 0, n1 = 0;       // finest: velocity nodes, pressure nodes
+    double *sinv = nullptr;       // [n1]: nu / Mp (1 on a constrained pressure dof)
+    double *w = nullptr, *kw = nullptr;  // [2 n2 + n1] work of the block solve
+    double *part = nullptr, *scal = nullptr;
+    unsigned *ticket = nullptr;
+    int pre = 2, post = 2, coarse = 60;
+};
+
+namespace {
+void mg_free_csr(mf_csr &A)
+{
+    cudaFree(const_cast<int64_t *>(A.row_ptr));
+    cudaFree(const_cast<int32_t *>(A.col_idx));
+    cudaFree(A.values);
+    A = mf_csr{};
+}
+
+mf_status mg_transpose(const mf_csr &P, int64_t ncols, mf_csr &R, cudaStream_t st)
+{
+    int64_t *trp = nullptr, *cur = nullptr;
+    int32_t *tci = nullptr;
+    double *tv = nullptr;
+    MF_CUDA(cudaMallocAsync(&trp, sizeof(int64_t) * (ncols + 1), st));
+    MF_CUDA(cudaMallocAsync(&cur, sizeof(int64_t) * ncols, st));
+    MF_CUDA(cudaMallocAsync(&tci, sizeof(int32_t) * P.nnz, st));
+    MF_CUDA(cudaMallocAsync(&tv, sizeof(double) * P.nnz, st));
+    MF_CUDA(cudaMemsetAsync(trp, 0, sizeof(int64_t) * (ncols + 1), st));
+    MF_CUDA(cudaMemsetAsync(cur, 0, sizeof(int64_t) * ncols, st));
+    k_tr_count<<<nblk(P.nnz, RT), RT, 0, st>>>(P.nnz, P.col_idx, trp);
+    MF_CUDA(mf_scan_i64(trp, ncols + 1, nullptr, st));
+    k_tr_fill<<<nblk(P.n_rows, RT), RT, 0, st>>>(P.n_rows, P.row_ptr, P.col_idx, P.values, trp, cur, tci, tv);
+    k_tr_sort<<<nblk(ncols, RT), RT, 0, st>>>(ncols, trp, tci, tv);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaFreeAsync(cur, st));
+    R = mf_csr{ncols, P.nnz, trp, tci, tv};
+    return MF_OK;
+}
+
+// one V-cycle for A x = b on level l (b, x given for level 0, own vectors below)
+void mg_vcycle(mf_flow_mg &G, int l, const double *b, double *x, cudaStream_t st)
+{
+    MgLevel &L = G.L[l];
+    const unsigned g = nblk(L.n, RT);
+    const int sweeps = (l == G.levels - 1) ? G.coarse : G.pre;
+    k_jacobi0<<<g, RT, 0, st>>>(L.n, b, L.dinv, L.mask, L.omega, x);
+    for (int s = 1; s < sweeps; ++s) {
+        spmv_any(&L.A, L.A.values, x, L.t, st);
+        k_jacobi<<<g, RT, 0, st>>>(L.n, b, L.t, L.dinv, L.mask, L.omega, x);
+    }
+    if (l == G.levels - 1) return;
+    MgLevel &C = G.L[l + 1];
+    spmv_any(&L.A, L.A.values, x, L.t, st);
+    k_resid<<<g, RT, 0, st>>>(L.n, b, L.t, L.r);
+    spmv_any(&L.R, L.R.values, L.r, C.b, st);
+    k_zero_masked<<<nblk(C.n, RT), RT, 0, st>>>(C.n, C.mask, C.b);
+    mg_vcycle(G, l + 1, C.b, C.x, st);
+    spmv_any(&L.P, L.P.values, C.x, L.t, st);
+    k_add_unmasked<<<g, RT, 0, st>>>(L.n, L.mask, L.t, x);
+    for (int s = 0; s < G.post; ++s) {
+        spmv_any(&L.A, L.A.values, x, L.t, st);
+        k_jacobi<<<g, RT, 0, st>>>(L.n, b, L.t, L.dinv, L.mask, L.omega, x);
+    }
+}
+
+// z = M^-1 v for the block upper-triangular M (K: the finest flow system)
+void flow_bt_apply(mf_flow_mg &G, const mf_csr *K, const double *v, double *z, cudaStream_t st)
+{
+    const int64_t nu = 2 * G.n2, nr = nu + G.n1;
+    k_bt_pressure<<<nblk(nr, RT), RT, 0, st>>>(nu, G.n1, v, G.sinv, G.w);
+    spmv_any(K, K->values, G.w, G.kw, st);
+    k_resid<<<nblk(nu, RT), RT, 0, st>>>(nu, v, G.kw, G.kw);  // rhs_u = v_u - (K w)_u
+    mg_vcycle(G, 0, G.kw, z, st);
+    mg_vcycle(G, 0, G.kw + G.n2, z + G.n2, st);
+    cudaMemcpyAsync(z + nu, G.w + nu, sizeof(double) * G.n1, cudaMemcpyDeviceToDevice, st);
+}
+
+mf_status solve_gmres_flow(const mf_csr *K, const double *d, double *x, const mf_solver_opts *o, mf_solve_info *info,
+                           cudaStream_t st)
+{
+    mf_flow_mg &G = *const_cast<mf_flow_mg *>(o->flow_mg);
+    const int64_t n = K->n_rows;
+    if (n != 2 * G.n2 + G.n1) return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: system does not match the hierarchy");
+    const int m = o->restart;
+    if (m > 1000) return mf_fail(MF_ERR_INVALID_ARG, "mf_solve: restart above 1000");
+    DevBuf<double> V(st), w(st), zb(st), tb(st), part(st), H(st), cs(st), sn(st), s(st), y(st), h(st), hcol(st),
+        nrm(st);
+    DevBuf<GmState> S(st);
+    const int64_t ldv = n;
+    MF_CUDA(V.alloc((size_t)(m + 1) * n));
+    MF_CUDA(w.alloc(n));
+    MF_CUDA(zb.alloc(n));
+    MF_CUDA(tb.alloc(n));
+    MF_CUDA(part.alloc((size_t)RED_BLOCKS * (m + 1) + 2 * RED_BLOCKS + 4));
+    MF_CUDA(H.alloc((size_t)(m + 1) * m));
+    MF_CUDA(cs.alloc(m));
+    MF_CUDA(sn.alloc(m));
+    MF_CUDA(s.alloc(m + 1));
+    MF_CUDA(y.alloc(m));
+    MF_CUDA(h.alloc(m + 1));
+    MF_CUDA(hcol.alloc(m + 1));
+    MF_CUDA(nrm.alloc(1));
+    MF_CUDA(S.alloc(1));
+    GmState hs{};
+    hs.tol2 = o->tol * o->tol;
+    hs.max_iter = o->max_iter;
+    MF_CUDA(cudaMemcpyAsync(S.p, &hs, sizeof hs, cudaMemcpyHostToDevice, st));
+    double *Vp = V.p;
+    double *partB = part.p + (size_t)RED_BLOCKS * (m + 1);
+    for (;;) {
+        spmv_any(K, K->values, x, w.p, st);
+        k_gm_start<<<RED_BLOCKS, RT, 0, st>>>(n, d, w.p, Vp, partB, S.p, s.p, m);
+        k_gm_norm_v0<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, S.p);
+        MF_CUDA(cudaGetLastError());
+        MF_CUDA(cudaMemcpyAsync(&hs, S.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        if (!hs.cycle_end)
+            for (int j = 0; j < m; ++j) {
+                // w = K M^-1 v_j
+                flow_bt_apply(G, K, Vp + (int64_t)j * ldv, zb.p, st);
+                spmv_any(K, K->values, zb.p, w.p, st);
+                for (int pass = 0; pass < 2; ++pass) {
+                    k_block_dots<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, w.p, S.p, part.p, m + 1);
+                    k_reduce_dots<<<m + 1, RT, 0, st>>>(RED_BLOCKS, part.p, m + 1, S.p, h.p, hcol.p, pass);
+                    k_multi_axpy<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, h.p, S.p, w.p);
+                }
+                k_norm2<<<RED_BLOCKS, RT, 0, st>>>(n, w.p, S.p, partB, &S.p->ticket, nrm.p);
+                k_scale_vec<<<RED_BLOCKS, RT, 0, st>>>(n, w.p, nrm.p, S.p, Vp + (int64_t)(j + 1) * ldv);
+                k_givens<<<1, 1, 0, st>>>(m, H.p, cs.p, sn.p, s.p, hcol.p, nrm.p, S.p);
+                MF_CUDA(cudaGetLastError());
+                MF_CUDA(cudaMemcpyAsync(&hs, S.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+                MF_CUDA(cudaStreamSynchronize(st));
+                if (hs.cycle_end) break;
+            }
+        // x += M^-1 (V y)
+        k_backsolve<<<1, 1, 0, st>>>(m, H.p, s.p, y.p, S.p);
+        MF_CUDA(cudaMemsetAsync(tb.p, 0, sizeof(double) * n, st));
+        k_update_x<<<RED_BLOCKS, RT, 0, st>>>(n, Vp, ldv, y.p, nullptr, S.p, tb.p);
+        flow_bt_apply(G, K, tb.p, zb.p, st);
+        k_axpy_vec<<<nblk(n, RT), RT, 0, st>>>(n, zb.p, x);
+        MF_CUDA(cudaGetLastError());
+        MF_CUDA(cudaMemcpyAsync(&hs, S.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        if (hs.done) {
+            if (hs.done == 1) {
+                double rr = 0.0;
+                mf_status t = true_residual(K, d, x, w.p, partB, &S.p->ticket, partB + 2 * RED_BLOCKS, st, &rr);
+                if (t != MF_OK) return t;
+                if (rr > o->tol && hs.iter < o->max_iter) {
+                    hs.done = 0;
+                    MF_CUDA(cudaMemcpyAsync(&S.p->done, &hs.done, sizeof(int), cudaMemcpyHostToDevice, st));
+                    continue;
+                }
+            }
+            break;
+        }
+    }
+    double relres = 0.0;
+    mf_status t = true_residual(K, d, x, w.p, partB, &S.p->ticket, partB + 2 * RED_BLOCKS, st, &relres);
+    if (t != MF_OK) return t;
+    if (info) {
+        info->iterations = hs.iter;
+        info->rel_residual = relres;
+        info->converged = hs.done == 1;
+        info->refinements = 0;
+    }
+    if (hs.done == 2) return mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve: %lld iterations, residual %.3e", hs.iter, relres);
+    if (hs.done == 3) return mf_fail(MF_ERR_NONFINITE, "mf_solve: breakdown or non-finite value");
+    return MF_OK;
+}
+}  // namespace
+
+mf_status mf_flow_mg_create_impl(int levels, const mf_csr *const *K, const int64_t *cells,
+                                 const uint8_t *const *bc_mask, const double *pmass, double visc, cudaStream_t st,
+                                 mf_flow_mg **out)
+{
+    mf_flow_mg *G = new (std::nothrow) mf_flow_mg();
+    if (!G) return mf_fail(MF_ERR_OOM, "mf_flow_mg_create: host allocation");
+    auto fail = [&](mf_status s) {
+        mf_flow_mg_destroy_impl(G);
+        return s;
+    };
+    G->levels = levels;
+    for (int l = 0; l < levels; ++l) {
+        const int64_t side = 2 * cells[l] + 1, n2 = side * side;
+        if (K[l]->n_rows <= 2 * n2 || (l > 0 && cells[l - 1] != 2 * cells[l]) || cells[l] < 1)
+            return fail(mf_fail(MF_ERR_INVALID_ARG, "mf_flow_mg_create: level %d does not halve the grid of level "
+                                                   "%d or does not match its system", l, l - 1));
+        MgLevel &L = G->L[l];
+        L.n = n2;
+        L.cells = cells[l];
+        int64_t *rp = nullptr;
+        MF_CUDA(cudaMallocAsync(&rp, sizeof(int64_t) * (n2 + 1), st));
+        MF_CUDA(cudaMemsetAsync(rp + n2, 0, sizeof(int64_t), st));
+        k_block_count<<<nblk(n2, RT), RT, 0, st>>>(n2, K[l]->row_ptr, K[l]->col_idx, rp);
+        MF_CUDA(mf_scan_i64(rp, n2 + 1, nullptr, st));
+        int64_t nnz = 0;
+        MF_CUDA(cudaMemcpyAsync(&nnz, rp + n2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        int32_t *ci = nullptr;
+        double *v = nullptr;
+        MF_CUDA(cudaMallocAsync(&ci, sizeof(int32_t) * nnz, st));
+        MF_CUDA(cudaMallocAsync(&v, sizeof(double) * nnz, st));
+        k_block_fill<<<nblk(n2, RT), RT, 0, st>>>(n2, K[l]->row_ptr, K[l]->col_idx, K[l]->values, rp, ci, v);
+        L.A = mf_csr{n2, nnz, rp, ci, v};
+        MF_CUDA(cudaMallocAsync(&L.dinv, sizeof(double) * n2, st));
+        MF_CUDA(cudaMallocAsync(&L.mask, n2, st));
+        MF_CUDA(cudaMemcpyAsync(L.mask, bc_mask[l], n2, cudaMemcpyDeviceToDevice, st));
+        for (double **p : {&L.x, &L.b, &L.r, &L.t}) MF_CUDA(cudaMallocAsync(p, sizeof(double) * n2, st));
+        int *bad = nullptr;
+        MF_CUDA(cudaMallocAsync(&bad, sizeof(int), st));
+        MF_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        k_diag_inv<<<nblk(n2, RT), RT, 0, st>>>(n2, rp, ci, v, L.dinv, bad);
+        int hb = 0;
+        MF_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MF_CUDA(cudaFreeAsync(bad, st));
+        MF_CUDA(cudaStreamSynchronize(st));
+        if (hb) return fail(mf_fail(MF_ERR_NONFINITE, "mf_flow_mg_create: zero diagonal in level %d", l));
+    }
+    // lambda_max of D^-1 A per level (power iteration, 24 steps) -> omega
+    MF_CUDA(cudaMallocAsync(&G->part, sizeof(double) * (RED_BLOCKS + 8), st));
+    MF_CUDA(cudaMallocAsync(&G->scal, sizeof(double) * 2, st));
+    MF_CUDA(cudaMallocAsync(&G->ticket, sizeof(unsigned), st));
+    MF_CUDA(cudaMemsetAsync(G->ticket, 0, sizeof(unsigned), st));
+    for (int l = 0; l < levels; ++l) {
+        MgLevel &L = G->L[l];
+        const unsigned g = nblk(L.n, RT);
+        k_fill_pattern<<<g, RT, 0, st>>>(L.n, L.x);
+        double lam = 1.0;
+        for (int it = 0; it < 24; ++it) {
+            double h2[2];
+            k_sumsq<<<red_grid(L.n), RT, 0, st>>>(L.n, L.x, G->part, G->ticket, G->scal);
+            spmv_any(&L.A, L.A.values, L.x, L.t, st);
+            k_scale_into<<<g, RT, 0, st>>>(L.n, L.t, L.dinv, 1.0, L.r);  // r = D^-1 A x
+            k_sumsq<<<red_grid(L.n), RT, 0, st>>>(L.n, L.r, G->part, G->ticket, G->scal + 1);
+            MF_CUDA(cudaMemcpyAsync(h2, G->scal, sizeof h2, cudaMemcpyDeviceToHost, st));
+            MF_CUDA(cudaStreamSynchronize(st));
+            if (!(h2[0] > 0.0) || !(h2[1] > 0.0) || !std::isfinite(h2[1])) break;
+            lam = sqrt(h2[1] / h2[0]);
+            k_scal<<<g, RT, 0, st>>>(L.n, 1.0 / sqrt(h2[1]), L.r, L.x);  // x = r / ||r||
+        }
+        L.omega = 4.0 / (3.0 * lam);
+    }
+    // transfers
+    for (int l = 0; l + 1 < levels; ++l) {
+        MgLevel &L = G->L[l], &C = G->L[l + 1];
+        const int64_t nf = L.n;
+        int64_t *prp = nullptr;
+        int32_t *pci = nullptr;
+        double *pv = nullptr;
+        MF_CUDA(cudaMallocAsync(&prp, sizeof(int64_t) * (nf + 1), st));
+        MF_CUDA(cudaMallocAsync(&pci, sizeof(int32_t) * 6 * nf, st));
+        MF_CUDA(cudaMallocAsync(&pv, sizeof(double) * 6 * nf, st));
+        k_p2_prolong<<<nblk(nf, RT), RT, 0, st>>>(C.cells, prp, pci, pv);
+        L.P = mf_csr{nf, 6 * nf, prp, pci, pv};
+        mf_status s = mg_transpose(L.P, C.n, L.R, st);
+        if (s != MF_OK) return fail(s);
+    }
+    // Schur stand-in and work vectors of the finest system
+    G->n2 = G->L[0].n;
+    G->n1 = K[0]->n_rows - 2 * G->n2;
+    MF_CUDA(cudaMallocAsync(&G->sinv, sizeof(double) * G->n1, st));
+    MF_CUDA(cudaMallocAsync(&G->w, sizeof(double) * K[0]->n_rows, st));
+    MF_CUDA(cudaMallocAsync(&G->kw, sizeof(double) * K[0]->n_rows, st));
+    k_sinv<<<nblk(G->n1, RT), RT, 0, st>>>(G->n1, pmass, bc_mask[0] + 2 * G->n2, visc, G->sinv);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaStreamSynchronize(st));
+    *out = G;
+    return MF_OK;
+}
+
+void mf_flow_mg_destroy_impl(mf_flow_mg *G)
+{
+    if (!G) return;
+    for (int l = 0; l < G->levels; ++l) {
+        MgLevel &L = G->L[l];
+        mg_free_csr(L.A);
+        mg_free_csr(L.P);
+        mg_free_csr(L.R);
+        cudaFree(L.dinv);
+        cudaFree(L.mask);
+        cudaFree(L.x);
+        cudaFree(L.b);
+        cudaFree(L.r);
+        cudaFree(L.t);
+    }
+    cudaFree(G->sinv);
+    cudaFree(G->w);
+    cudaFree(G->kw);
+    cudaFree(G->part);
+    cudaFree(G->scal);
+    cudaFree(G->ticket);
+    delete G;
 }
 
 mf_status mf_spmv_impl(const mf_csr *K, const double *x, double *y, cudaStream_t st)
@@ -965,7 +1774,11 @@ mf_status mf_solve_impl(const mf_csr *K, const double *d, double *x, const mf_so
 {
     int *status = mf_status_word();
     if (!status) return mf_fail(MF_ERR_CUDA, "mf_solve: status word unavailable");
-    mf_status s = (o->solver == MF_SOLVER_PCG) ? solve_pcg(K, d, x, o, info, st) : solve_gmres(K, d, x, o, info, st);
+    if (info) info->refinements = 0;
+    mf_status s = (o->solver == MF_SOLVER_PCG)       ? solve_pcg(K, d, x, o, info, st)
+                  : (o->solver == MF_SOLVER_GMRES)   ? solve_gmres(K, d, x, o, info, st)
+                  : (o->solver == MF_SOLVER_GMRES_FLOW_MG) ? solve_gmres_flow(K, d, x, o, info, st)
+                                                     : solve_refined(K, d, x, o, info, st);
     if (s == MF_ERR_CUDA || s == MF_ERR_OOM) return s;
     return finish_status(s, status, st);
 }
