@@ -83,9 +83,13 @@ struct mf_pattern {
     // elasticity, mixed path: int64 3x3 block accumulator per upper node pair
     // (n, m >= n; a diagonal block as its upper triangle), numbered compactly:
     // upper pair (n, slot k) is block cbase[n] + k; tpos gives, for a lower
-    // pair (n, m < n), the number of the upper pair (m, n) (-1 otherwise)
+    // pair (n, m < n), the number of the upper pair (m, n), and for an upper
+    // pair its own number: the block every CSR block of n reads
     long long *kacc = nullptr;
     int32_t *tpos = nullptr;
+    // the accumulator block of each upper block pair (a <= b) of every element
+    // (bit 31: the pair is stored transposed), [n_elems][36]
+    int32_t *etgt = nullptr;
     int64_t *cbase = nullptr;
     int64_t n_upper = 0;
     long long *dacc = nullptr;  // int64 load vector accumulator (3 per node)

@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
     int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn,
     const double *__restrict__ Ec,
     double cmu, double b0, double b1, double b2, const MixedState *__restrict__ st,
-    const int64_t *__restrict__ cbase, const uint8_t *__restrict__ slot, unsigned long long *__restrict__ kacc,
+    const int32_t *__restrict__ etgt, unsigned long long *__restrict__ kacc,
     unsigned long long *__restrict__ dacc, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];  // WarpSmem per warp (16-byte rows)
@@ -409,24 +409,14 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
     }
     __syncwarp();
 
-    // --- accumulator pair of each upper block (a <= b) of the warp's 4 elements:
-    // (n_a, n_b) when n_a <= n_b, else (n_b, n_a) holding the transpose ---
-    for (int i = lane; i < 4 * 36; i += 32) {
-        const int el = i / 36, u = i - 36 * el;
-        int a = 0, rem = u;
-        while (rem >= 8 - a) {
-            rem -= 8 - a;
-            ++a;
+    // --- accumulator block of each upper block pair (a <= b) of the warp's 4
+    // elements (precomputed with the pattern; bit 31: stored transposed) ---
+    {
+        const int64_t ebase = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4;
+        for (int i = lane; i < 4 * 36; i += 32) {
+            const int el = i / 36;
+            W.tgt[el][i - 36 * el] = (ebase + el < e1) ? __ldg(etgt + ebase * 36 + i) : 0;
         }
-        const int b = a + rem;
-        const int64_t eo = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + el;
-        int32_t tg = 0;
-        if (eo < e1) {
-            const int32_t na = conn[8 * eo + a], nb = conn[8 * eo + b];
-            tg = na <= nb ? (int32_t)(cbase[na] + slot[eo * 64 + a * 8 + b])
-                          : (int32_t)((cbase[nb] + slot[eo * 64 + b * 8 + a]) | 0x80000000ll);
-        }
-        W.tgt[el][u] = tg;
     }
     __syncwarp();
 
@@ -567,7 +557,7 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
     double lift[3] = {0.0, 0.0, 0.0};
     for (int k = lane; k < deg; k += 32) {
         const int32_t mcol = adj_col[p0 + k];
-        const int64_t src = mcol < n ? (int64_t)tpos[p0 + k] : cbase[n] + k;
+        const int64_t src = tpos[p0 + k];  // the accumulator block of pair (n, mcol)
         const long long *B = kacc + src * 9;
         long long b[9];
 #pragma unroll
@@ -670,7 +660,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
             mf_prof_begin("mixed_elem", s2);
             k_mixed_elem<<<(unsigned)((e1 - e0 + MX_ELEMS - 1) / MX_ELEMS), MX_WARPS * 32, smem, s2>>>(
                 e0, e1, m->coords, m->conn, c->elem_coef, cmu, c->source[0], c->source[1], c->source[2], ms,
-                p->cbase, p->slot, reinterpret_cast<unsigned long long *>(p->kacc),
+                p->etgt, reinterpret_cast<unsigned long long *>(p->kacc),
                 reinterpret_cast<unsigned long long *>(p->dacc), status);
             mf_prof_end(s2);
             MF_CUDA(cudaGetLastError());

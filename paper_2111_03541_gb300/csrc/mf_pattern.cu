@@ -259,8 +259,29 @@ __global__ void k_tpos(int64_t n_nodes, const int64_t *__restrict__ ptr, const i
     if (n >= n_nodes) return;
     for (int64_t p = ptr[n]; p < ptr[n + 1]; ++p) {
         const int32_t m = col[p];
-        tpos[p] = m < n ? (int32_t)(cbase[m] + (find_pair(ptr, col, m, (int32_t)n) - ptr[m])) : -1;
+        tpos[p] = m < n ? (int32_t)(cbase[m] + (find_pair(ptr, col, m, (int32_t)n) - ptr[m]))
+                        : (int32_t)(cbase[n] + (p - ptr[n]));
     }
+}
+
+// the accumulator block of each upper block pair (a <= b) of every element:
+// (n_a, n_b) when n_a <= n_b, else (n_b, n_a) holding the transpose (bit 31)
+__global__ void k_mixed_etgt(int64_t ne, const int32_t *__restrict__ conn, const int64_t *__restrict__ cbase,
+                             const uint8_t *__restrict__ slot, int32_t *__restrict__ etgt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne * 36) return;
+    const int64_t e = i / 36;
+    const int u = (int)(i - 36 * e);
+    int a = 0, rem = u;
+    while (rem >= 8 - a) {
+        rem -= 8 - a;
+        ++a;
+    }
+    const int b = a + rem;
+    const int32_t na = conn[8 * e + a], nb = conn[8 * e + b];
+    etgt[i] = na <= nb ? (int32_t)(cbase[na] + slot[e * 64 + a * 8 + b])
+                       : (int32_t)((cbase[nb] + slot[e * 64 + b * 8 + a]) | 0x80000000ll);
 }
 
 // incidence slot map: for incidence entry t of row node n (element e),
@@ -615,6 +636,8 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->slot);
     cudaFree(p->kacc);
     cudaFree(p->tpos);
+    cudaFree(p->etgt);
+    p->etgt = nullptr;
     cudaFree(p->cbase);
     p->cbase = nullptr;
     p->n_upper = 0;
@@ -772,6 +795,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         }
         MF_CUDA(cudaMallocAsync(&p->tpos, sizeof(int32_t) * p->adj[0].n_pairs, st));
         k_tpos<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->cbase, p->tpos);
+        MF_CUDA(cudaMallocAsync(&p->etgt, sizeof(int32_t) * 36 * m->n_elems, st));
+        k_mixed_etgt<<<nblk(36 * m->n_elems), TPB, 0, st>>>(m->n_elems, m->conn, p->cbase, p->slot, p->etgt);
         MF_CUDA(cudaMallocAsync(&p->kacc, sizeof(long long) * 9 * p->n_upper, st));
         MF_CUDA(cudaMallocAsync(&p->dacc, sizeof(long long) * 3 * m->n_nodes, st));
         p->scratch_stride = 36 * 9 + 24;
