@@ -15,11 +15,12 @@
 //  * geometry (Jacobian, cofactors, detJ, scale, gradients) in double-float
 //    arithmetic (pairs of FP32, ~44 bits), one lane per (element, Gauss point),
 //    from FP64 coordinate differences;
-//  * G is split into 5 BF16 slices of 8 bits with one exponent per element
+//  * the rows of G are ordered component-major (8 c + a) and split into 5
+//    BF16 slices of 8 bits with one exponent per (element, component)
 //    (Ozaki, Ogita, Oishi & Rump 2012): every slice product summed over the 8
 //    points is an exact integer in FP32, so each level L = s + t of the slice
 //    pairs accumulates exactly on the tensor cores (mma.sync m16n8k16, bf16
-//    in, fp32 accumulate; fragments by ldmatrix);
+//    in, fp32 accumulate; fragments by ldmatrix.trans);
 //  * the levels are combined into 64-bit fixed point at a global scale 2^S,
 //    chosen per assembly by an FP32 pre-pass over the current coordinates and
 //    coefficients so that no sum can overflow, and added with integer atomics
@@ -239,12 +240,12 @@ __global__ void k_mixed_scale(MixedState *st, double rabs, double bmax)
 // element kernel
 // ---------------------------------------------------------------------------
 struct WarpSmem {
-    __nv_bfloat16 sl[4][NSL][SL_ROWS][8];  // slices of G per element: [slice][row (a,c)][point]
-    int ex[4];                              // element exponents
+    __nv_bfloat16 sl[4][NSL][8][SL_ROWS];  // slices of G per element: [slice][point][row (a,c)]
+    int ex[4][3];                           // exponents per (element, component)
     int32_t tgt[4][36];                     // accumulator pair of block (a <= b); bit 31: transposed
 };
 
-__global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
+__global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
     int64_t e0, int64_t e1, const double *__restrict__ X, const int32_t *__restrict__ conn,
     const double *__restrict__ Ec,
     double cmu, double b0, double b1, double b2, const MixedState *__restrict__ st,
@@ -316,68 +317,6 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
     Cf[2][2] = dsub(dmul(J[0][0], J[1][1]), dmul(J[0][1], J[1][0]));
     const f2 det = dadd(dadd(dmul(J[0][0], Cf[0][0]), dmul(J[0][1], Cf[0][1])), dmul(J[0][2], Cf[0][2]));
 
-    // --- scale sqrt(mu_e / det), mu_e = E cmu ---
-    const double E = Ec[e];
-    if (valid && !isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
-    const f2 sig = dsqrt(ddiv(from_double(E * cmu), det));
-    // G[(a,c), qp] = sig sum_j d_j N_a(qp) Cf[c][j], sum-factorised over the
-    // three factor products P^2/8, PM/8, M^2/8
-    f2 G[3][8];
-    float gmx = 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        f2 T[3][3];  // T[j][k]: (sig Cf[c][j]) x {PP, PM, MM}
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-            const f2 u = dmul(sig, Cf[c][jj]);
-            T[jj][0] = dmul(u, DF(KPP));
-            T[jj][1] = dmul(u, DF(KPM));
-            T[jj][2] = dmul(u, DF(KMM));
-        }
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const int match = ~(a ^ qp) & 7;  // bit k: s_a^k equals the sign of the point
-            f2 acc = {0.f, 0.f};
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj) {
-                const int others = match & ~(1 << jj) & 7;
-                const int k = 2 - __popc(others);  // 2 matches -> PP, 1 -> PM, 0 -> MM
-                const f2 t = (k == 0) ? T[jj][0] : ((k == 1) ? T[jj][1] : T[jj][2]);
-                acc = dadd(acc, dsgn(t, !((a >> jj) & 1)));
-            }
-            G[c][a] = acc;
-            gmx = fmaxf(gmx, fabsf(acc.h));
-        }
-    }
-    // one exponent per element: 2^(ex - 1) <= max |G| < 2^ex; the digits of
-    // every row are taken at that scale (8-bit digits rounded to nearest)
-    gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 1));
-    gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 2));
-    gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 4));
-    const int ex = (gmx > 0.f) ? (((__float_as_int(gmx) >> 23) & 0xff) - 126) : -200;
-    if (qp == 0) W.ex[j] = ex;
-    // x 2^-ex (exact); digits 0..2 from the high word (exact steps), the low
-    // word folded in before digits 3 and 4
-    const float sc = (gmx > 0.f) ? __int_as_float((127 - ex) << 23) : 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            float h = G[c][a].h * sc, l = G[c][a].l * sc;
-#pragma unroll
-            for (int sl = 0; sl < NSL; ++sl) {
-                h *= 256.f;
-                l *= 256.f;
-                if (sl >= 3) {
-                    const f2 r = two_sum(h, l);
-                    h = r.h;
-                    l = r.l;
-                }
-                const float dg = rintf(h);
-                h -= dg;
-                W.sl[j][sl][3 * a + c][qp] = __float2bfloat16_rn(dg);
-            }
-        }
     // --- load vector: m_a = sum_q detJ_q N_a(q) ---
     {
         const f2 n3 = dmul(det, DF(NP3)), n2 = dmul(det, DF(NP2)), n1 = dmul(det, DF(NP1)), n0v = dmul(det, DF(NP0));
@@ -409,6 +348,85 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
     }
     __syncwarp();
 
+    // --- scale sqrt(mu_e / det), mu_e = E cmu ---
+    const double E = Ec[e];
+    if (valid && !isfinite(E)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    const f2 sig = dsqrt(ddiv(from_double(E * cmu), det));
+    // rows of G component-major, row 8 c + a:
+    //   G[(c, a), qp] = sig sum_j d_j N_a(qp) Cf[c][j],
+    // sum-factorised over the three factor products P^2/8, PM/8, M^2/8; one
+    // component at a time, each with its own exponent: 2^(ex - 1) <= max over
+    // the element's 8 x 8 values of component c < 2^ex.  The 8-bit digits of
+    // x 2^-ex (exact) are rounded to nearest (magic-number rounding: |x| <
+    // 2^22), digits 0..2 from the high word, the low word folded in before
+    // digits 3 and 4.  A digit is an integer of at most 8 significant bits, so
+    // its bfloat16 is the top half of its float: the 8 rows of a component
+    // pack into one 16-byte store per slice in the [slice][point][row] layout.
+    constexpr float RND = 12582912.0f;  // 1.5 2^23
+    uint32_t *slw = reinterpret_cast<uint32_t *>(&W.sl[j][0][qp][0]);
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {  // rolled: one copy of the code, the cofactor row picked by selects
+        f2 T[3][3];  // T[j][k]: (sig Cf[c][j]) x {PP, PM, MM}
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            const f2 cf = c == 0 ? Cf[0][jj] : (c == 1 ? Cf[1][jj] : Cf[2][jj]);
+            const f2 u = dmul(sig, cf);
+            T[jj][0] = dmul(u, DF(KPP));
+            T[jj][1] = dmul(u, DF(KPM));
+            T[jj][2] = dmul(u, DF(KMM));
+        }
+        f2 G[8];
+        float gmx = 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int match = ~(a ^ qp) & 7;  // bit k: s_a^k equals the sign of the point
+            f2 acc = {0.f, 0.f};
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) {
+                const int others = match & ~(1 << jj) & 7;
+                const int k = 2 - __popc(others);  // 2 matches -> PP, 1 -> PM, 0 -> MM
+                const f2 t = (k == 0) ? T[jj][0] : ((k == 1) ? T[jj][1] : T[jj][2]);
+                acc = jj == 0 ? dsgn(t, !(a & 1)) : dadd(acc, dsgn(t, !((a >> jj) & 1)));
+            }
+            G[a] = acc;
+            gmx = fmaxf(gmx, fabsf(acc.h));
+        }
+        gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 1));
+        gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 2));
+        gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, 4));
+        const int ex = (gmx > 0.f) ? (((__float_as_int(gmx) >> 23) & 0xff) - 126) : -200;
+        if (qp == 0) W.ex[j][c] = ex;
+        const float sc = (gmx > 0.f) ? __int_as_float((127 - ex) << 23) : 0.f;
+        uint32_t pk[NSL][4];
+#pragma unroll
+        for (int pr = 0; pr < 4; ++pr) {
+            float dgt[2][NSL];
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                float h = G[2 * pr + h2].h * sc, l = G[2 * pr + h2].l * sc;
+#pragma unroll
+                for (int sl = 0; sl < NSL; ++sl) {
+                    h *= 256.f;
+                    if (sl >= 3) {
+                        l *= (sl == 3) ? 4294967296.0f : 256.f;  // the low word at the digit's scale
+                        const f2 r = two_sum(h, l);
+                        h = r.h;
+                        l = r.l;
+                    }
+                    const float dg = (h + RND) - RND;
+                    h -= dg;
+                    dgt[h2][sl] = dg;
+                }
+            }
+#pragma unroll
+            for (int sl = 0; sl < NSL; ++sl)
+                pk[sl][pr] = __byte_perm(__float_as_uint(dgt[0][sl]), __float_as_uint(dgt[1][sl]), 0x7632);
+        }
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl)
+            *reinterpret_cast<uint4 *>(slw + sl * (8 * SL_ROWS / 2) + 4 * c) =
+                make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+    }
     // --- accumulator block of each upper block pair (a <= b) of the warp's 4
     // elements (precomputed with the pattern; bit 31: stored transposed) ---
     {
@@ -421,36 +439,82 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
     __syncwarp();
 
     // --- tensor cores: A'' = G G^T by levels, per element of the warp;
-    // fragments by ldmatrix from the slice rows (16 bytes each) ---
+    // fragments by ldmatrix.trans from the [point][row] slice layout ---
     const int g = lane >> 2, t = lane & 3;
     const int S = st->S;
     const uint32_t sl_base = (uint32_t)__cvta_generic_to_shared(&W.sl[0][0][0][0]);
-    constexpr uint32_t ROWB = 16, SLB = SL_ROWS * ROWB, ELB = NSL * SLB;  // bytes per row, slice, element
+    constexpr uint32_t PTB = SL_ROWS * 2, SLB = 8 * PTB, ELB = NSL * SLB;  // bytes per point, slice, element
+    // the accumulator entries of this lane's outputs, the same for every
+    // element.  Output (rho, sig2) of tile (m, n) is A''[(c, a), (c', b)],
+    // c = rho / 8, a = rho % 8, c' = sig2 / 8 = n, b = sig2 % 8; the tiles
+    // cover the component blocks (0,0), (1,0), (0,1), (1,1), (0,2), (1,2) and
+    // (2,2).  Blocks (0,2) and (1,2) are taken whole (their a > b half is the
+    // symmetric (2,0), (2,1) entry of the pair (b, a)), the others on a < b
+    // and, for a = b, on c <= c'.  item: u = block pair (lo, hi) of the
+    // element's nodes (u = lo (15 - lo) / 2 + hi), bits 6..9 the entry (row
+    // component of lo, column component of hi), bits 10..13 the same entry
+    // of the transposed block; 0xffff: not taken.
+    uint32_t item[4][2];
+#pragma unroll
+    for (int tl = 0; tl < 4; ++tl) {  // tiles (m, n): (0,0), (0,1), (0,2), (1,2)
+        const int mt = tl == 3 ? 1 : 0, nt = tl == 3 ? 2 : tl;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int rho = mt * 16 + g + 8 * (k >> 1);
+            const int sig2 = nt * 8 + 2 * t + (k & 1);
+            const int c = rho >> 3, a = rho & 7, cp = sig2 >> 3, b = sig2 & 7;
+            uint32_t it = 0xffffu;
+            if (c < 3) {
+                int lo = a, hi = b, x = c, y = cp;
+                bool ok;
+                if (cp == 2 && c < 2) {
+                    ok = true;
+                    if (a > b) {
+                        lo = b;
+                        hi = a;
+                        x = cp;
+                        y = c;
+                    }
+                } else {
+                    ok = a < b || (a == b && c <= cp);
+                }
+                if (ok) it = (uint32_t)((lo * (15 - lo) / 2 + hi) | ((3 * x + y) << 6) | ((3 * y + x) << 10));
+            }
+            if (k & 1) item[tl][k >> 1] |= it << 16;
+            else item[tl][k >> 1] = it;
+        }
+    }
 #pragma unroll 1
     for (int el = 0; el < 4; ++el) {
         const int64_t eo = e0 + ((int64_t)blockIdx.x * MX_WARPS + w) * 4 + el;
         if (eo >= e1) break;  // warp-uniform
         const uint32_t eb = sl_base + el * ELB;
-        // fixed-point shift of this element: G G^T = T 2^(2 ex - 48)
-        const int sh = 2 * W.ex[el] + S - 48;
+        // fixed-point shift of entry (c, c'): G_c G_c'^T = T 2^(ex_c + ex_c' - 48)
+        const int ex0 = W.ex[el][0], ex1 = W.ex[el][1], ex2 = W.ex[el][2];
 #pragma unroll 1
-        for (int tl = 0; tl < 4; ++tl) {  // tiles (m, n): (0,0), (0,1), (0,2), (1,2)
+        for (int tl = 0; tl < 4; ++tl) {
             const int mt = tl == 3 ? 1 : 0, nt = tl == 3 ? 2 : tl;
+            const int shn = (nt == 0 ? ex0 : (nt == 1 ? ex1 : ex2)) + S - 48;
+            const int sh_lo = (mt ? ex2 : ex0) + shn, sh_hi = ex1 + shn;  // rows c = 2 m, 2 m + 1
+            const uint32_t iw0 = tl == 0 ? item[0][0] : (tl == 1 ? item[1][0] : (tl == 2 ? item[2][0] : item[3][0]));
+            const uint32_t iw1 = tl == 0 ? item[0][1] : (tl == 1 ? item[1][1] : (tl == 2 ? item[2][1] : item[3][1]));
             uint32_t A[3][4], B[NSL][2];
             // A = slices (s0, s0 + 1) of rows mt 16 + ..; the second row tile
             // has 8 real rows (16..23), rows 24..31 are zero
-            const int arow = mt ? 16 + (lane & 7) : (lane & 15);
 #pragma unroll
             for (int sp = 0; sp < 3; ++sp) {  // slice pairs (0,1), (2,3), (4,-)
                 const int s0 = 2 * sp, s1 = s0 + 1 < NSL ? s0 + 1 : s0;
                 if (mt == 0) {
-                    const uint32_t ad = eb + ((lane >> 4) ? s1 : s0) * SLB + arow * ROWB;
-                    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                    // matrices (rows 0-7 | 8-15) x (slice s0 | s1), stored as
+                    // 8 point rows of 8 consecutive G rows
+                    const int mi = lane >> 3;
+                    const uint32_t ad = eb + ((mi >> 1) ? s1 : s0) * SLB + (lane & 7) * PTB + (mi & 1) * 16;
+                    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                                  : "=r"(A[sp][0]), "=r"(A[sp][1]), "=r"(A[sp][2]), "=r"(A[sp][3]) : "r"(ad));
                 } else {
-                    // lanes 0..7: slice s0, lanes 8..15: slice s1 (-> a0, a2)
-                    const uint32_t ad = eb + ((lane & 8) ? s1 : s0) * SLB + arow * ROWB;
-                    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                    // rows 16-23 of slice s0 (-> a0) and s1 (-> a2)
+                    const uint32_t ad = eb + ((lane & 8) ? s1 : s0) * SLB + (lane & 7) * PTB + 32;
+                    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
                                  : "=r"(A[sp][0]), "=r"(A[sp][2]) : "r"(ad));
                     A[sp][1] = 0u;
                     A[sp][3] = 0u;
@@ -463,8 +527,8 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
 #pragma unroll
             for (int tp = 0; tp < NSL; ++tp) {  // B pairs (slice t', slice t' - 1), rows nt 8 + ..
                 const int sb = ((lane >> 3) & 1) ? (tp > 0 ? tp - 1 : 0) : tp;
-                const uint32_t ad = eb + sb * SLB + (nt * 8 + (lane & 7)) * ROWB;
-                asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                const uint32_t ad = eb + sb * SLB + (lane & 7) * PTB + nt * 16;
+                asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
                              : "=r"(B[tp][0]), "=r"(B[tp][1]) : "r"(ad));
                 if (tp == 0) B[tp][1] = 0u;
             }
@@ -486,13 +550,9 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
             // block after all elements
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int rho = mt * 16 + g + 8 * (k >> 1);
-                const int sig2 = nt * 8 + 2 * t + (k & 1);
-                const int a = rho / 3, b = sig2 / 3;
-                const int c = rho - 3 * a, cp = sig2 - 3 * b;
-                // upper blocks a <= b, of a diagonal block its upper triangle;
-                // the four tiles compute all of them (rows >= 24 are padding)
-                if (rho >= 24 || a > b || (a == b && c > cp)) continue;
+                const uint32_t it = ((k >> 1 ? iw1 : iw0) >> (16 * (k & 1))) & 0xffffu;
+                if (it == 0xffffu) continue;
+                const int sh = (k >> 1) ? sh_hi : sh_lo;
                 long long T = f2i_exact(acc[0][k]);
 #pragma unroll
                 for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][k]);
@@ -500,9 +560,9 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
                 if (sh >= 0) v = T << sh;
                 else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
                 else v = 0;
-                const int32_t tg = W.tgt[el][a * (15 - a) / 2 + b];
+                const int32_t tg = W.tgt[el][it & 63];
                 const int64_t pr = tg & 0x7fffffff;
-                const int q = tg < 0 ? 3 * cp + c : 3 * c + cp;
+                const int q = tg < 0 ? (int)(it >> 10) & 15 : (int)(it >> 6) & 15;
                 if (v != 0) atomicAdd(&kacc[pr * 9 + q], (unsigned long long)v);
             }
         }
@@ -512,10 +572,11 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 5) k_mixed_elem(
 // ---------------------------------------------------------------------------
 // finishing: one warp per node.  Lane k takes neighbour k's 3x3 block from the
 // accumulator (its own pair (n, m) for m > n, the transpose of (m, n) for
-// m < n, the upper triangle of the diagonal block for m = n), applies
-// K = p A'' + q swap(A'') + q I tr(A'') in int64, converts each value once to
-// FP64 and eliminates the Dirichlet dofs; the three rows are staged in shared
-// memory and written with coalesced stores.
+// m < n, the upper triangle of the diagonal block for m = n; the load
+// offsets are picked per lane), applies K = r A + A^T + I tr A in int64,
+// converts each value once to FP64 and eliminates the Dirichlet dofs (blocks
+// with no constrained row or column skip those tests); the three rows are
+// staged in shared memory and written with coalesced stores.
 // ---------------------------------------------------------------------------
 // floor(A R / 2^s), 1 <= s <= 63: bits s .. s + 63 of the 128-bit product
 __device__ __forceinline__ long long mul_r(long long A, long long R, int s)
@@ -533,12 +594,23 @@ __device__ __forceinline__ long long times_r(long long A, long long R, int s)
     return mul_r(A, R, s);
 }
 
+// v 2^-S as FP64, rounded to nearest even (values below the normal range
+// flush to signed zero): the hardware conversion of the integer, then the
+// exponent lowered by S
+__device__ __forceinline__ double fixed_to_double(long long v, int S)
+{
+    if (v == 0) return 0.0;
+    const long long bits = __double_as_longlong(__ll2double_rn(v));
+    const long long ex = ((bits >> 52) & 0x7ff) - S;
+    if (ex <= 0) return __longlong_as_double(bits & (1ll << 63));
+    return __longlong_as_double(bits - ((long long)S << 52));
+}
+
 constexpr int FN_WARPS = 8;
 
-__global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
+__global__ void __launch_bounds__(FN_WARPS * 32, 4) k_mixed_finish(
     int64_t n_begin, int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
-    const int32_t *__restrict__ tpos, const int64_t *__restrict__ cbase, const long long *__restrict__ kacc,
-    const long long *__restrict__ dacc,
+    const int32_t *__restrict__ tpos, const long long *__restrict__ kacc, const long long *__restrict__ dacc,
     const MixedState *__restrict__ st, long long rR, int rs, const uint8_t *__restrict__ mask,
     const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
     double *__restrict__ d)
@@ -554,40 +626,54 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
     bool rm[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) rm[c] = mask ? mask[3 * n + c] != 0 : false;
+    const bool rm_any = rm[0] || rm[1] || rm[2];
     double lift[3] = {0.0, 0.0, 0.0};
     for (int k = lane; k < deg; k += 32) {
         const int32_t mcol = adj_col[p0 + k];
         const int64_t src = tpos[p0 + k];  // the accumulator block of pair (n, mcol)
         const long long *B = kacc + src * 9;
-        long long b[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) b[i] = B[i];
+        // A[c][c'] = B[3 c + c'] (m > n), B[3 c' + c] (m < n), the upper
+        // triangle of the diagonal block (m = n): offsets picked per lane
+        const int orient = mcol > n ? 0 : (mcol < n ? 1 : 2);
         long long A[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int cp = 0; cp < 3; ++cp)
-                A[c][cp] = mcol > n ? b[3 * c + cp]
-                                    : (mcol < n ? b[3 * cp + c] : b[3 * (c < cp ? c : cp) + (c < cp ? cp : c)]);
+            for (int cp = 0; cp < 3; ++cp) {
+                const int o0 = 3 * c + cp, o1 = 3 * cp + c, o2 = 3 * (c < cp ? c : cp) + (c < cp ? cp : c);
+                A[c][cp] = B[orient == 0 ? o0 : (orient == 1 ? o1 : o2)];
+            }
         const long long tr = A[0][0] + A[1][1] + A[2][2];
         unsigned cm = 0;
         if (mask)
 #pragma unroll
             for (int cp = 0; cp < 3; ++cp) cm |= (mask[3 * (int64_t)mcol + cp] != 0 ? 1u : 0u) << cp;
+        if (!rm_any && cm == 0) {  // no constrained row or column: the plain block
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int cp = 0; cp < 3; ++cp) {
-                long long kv = times_r(A[c][cp], rR, rs) + A[cp][c];
-                if (c == cp) kv += tr;
-                double v = mf_fixed_to_double(kv, S);
-                if (mask) {
+                for (int cp = 0; cp < 3; ++cp) {
+                    long long kv = times_r(A[c][cp], rR, rs) + A[cp][c];
+                    if (c == cp) kv += tr;
+                    rows[c][3 * k + cp] = fixed_to_double(kv, S);
+                }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int cp = 0; cp < 3; ++cp) {
+                    long long kv = times_r(A[c][cp], rR, rs) + A[cp][c];
+                    if (c == cp) kv += tr;
+                    double v = fixed_to_double(kv, S);
                     const int64_t sdof = 3 * (int64_t)mcol + cp;
                     if (rm[c]) v = (3 * n + c == sdof) ? 1.0 : 0.0;
-                    else if ((cm >> cp) & 1u) { lift[c] -= v * bval[sdof]; v = 0.0; }
+                    else if ((cm >> cp) & 1u) {
+                        lift[c] -= v * bval[sdof];
+                        v = 0.0;
+                    }
+                    rows[c][3 * k + cp] = v;
                 }
-                rows[c][3 * k + cp] = v;
-            }
+        }
     }
     __syncwarp();
 #pragma unroll
@@ -599,7 +685,7 @@ __global__ void __launch_bounds__(FN_WARPS * 32) k_mixed_finish(
         if (__any_sync(0xffffffffu, l != 0.0))  // rows next to a constrained dof only
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-        if (lane == 0) d[r] = rm[c] ? bval[r] : mf_fixed_to_double(dacc[r], Sd) + l;
+        if (lane == 0) d[r] = rm[c] ? bval[r] : fixed_to_double(dacc[r], Sd) + l;
     }
 }
 
@@ -671,7 +757,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
             if (n1 > n0) {
                 mf_prof_begin("mixed_finish", s2);
                 k_mixed_finish<<<(unsigned)((n1 - n0 + FN_WARPS - 1) / FN_WARPS), FN_WARPS * 32, 0, s2>>>(
-                    n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->cbase, p->kacc, p->dacc, ms, rR, rs, c->bc_mask,
+                    n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->kacc, p->dacc, ms, rR, rs, c->bc_mask,
                     c->bc_val, p->row_ptr, values, d);
                 mf_prof_end(s2);
             }

@@ -487,6 +487,22 @@ mf_status read_i64(const int64_t *d, int64_t *h, cudaStream_t st)
     return MF_OK;
 }
 
+// the largest row of an adjacency, to the host (sizes the shared memory of
+// the kernels that stage whole rows)
+mf_status read_max_deg(int64_t n_rows, mf_adj *a, cudaStream_t st)
+{
+    int *dmax = nullptr;
+    MF_CUDA(cudaMallocAsync(&dmax, sizeof(int), st));
+    MF_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), st));
+    if (n_rows > 0) k_max_deg<<<nblk(n_rows), TPB, 0, st>>>(n_rows, a->ptr, dmax);
+    int h = 0;
+    MF_CUDA(cudaMemcpyAsync(&h, dmax, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    MF_CUDA(cudaFreeAsync(dmax, st));
+    a->max_deg = h;
+    return MF_OK;
+}
+
 mf_status check_status(int *status, cudaStream_t st, const char *what)
 {
     int h = 0;
@@ -750,17 +766,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_inc_slot<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, npe, m->conn, incv.ptr, incv.inc, p->adj[0].ptr,
                                                      p->adj[0].col, p->inc_slot);
         p->scratch_stride = (int64_t)npe * (9 * npe + 3);
-        {
-            int *dmax = nullptr;
-            MF_CUDA(cudaMallocAsync(&dmax, sizeof(int), st));
-            MF_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), st));
-            k_max_deg<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, dmax);
-            int h = 0;
-            MF_CUDA(cudaMemcpyAsync(&h, dmax, sizeof(int), cudaMemcpyDeviceToHost, st));
-            MF_CUDA(cudaStreamSynchronize(st));
-            MF_CUDA(cudaFreeAsync(dmax, st));
-            p->adj[0].max_deg = h;
-        }
+        s = read_max_deg(m->n_nodes, &p->adj[0], st);
+        if (s != MF_OK) { free_inc(incv, st); return s; }
         s = mf_flow_consts_upload();  // reference table of the 20-node brick
         if (s != MF_OK) { free_inc(incv, st); return s; }
         if (m->n_elems > 0) {
@@ -793,6 +800,8 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
             MF_CUDA(cudaFreeAsync(cnt, st));
             if (s != MF_OK) { free_inc(incv, st); return s; }
         }
+        s = read_max_deg(m->n_nodes, &p->adj[0], st);
+        if (s != MF_OK) { free_inc(incv, st); return s; }
         MF_CUDA(cudaMallocAsync(&p->tpos, sizeof(int32_t) * p->adj[0].n_pairs, st));
         k_tpos<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, p->adj[0].ptr, p->adj[0].col, p->cbase, p->tpos);
         MF_CUDA(cudaMallocAsync(&p->etgt, sizeof(int32_t) * 36 * m->n_elems, st));
