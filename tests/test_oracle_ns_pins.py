@@ -158,3 +158,112 @@ def test_rotation_covariance(orc):
     s = np.abs(r).max()
     assert np.abs(rq[:30].reshape(10, 3) - r[:30].reshape(10, 3) @ Q3.T).max() < 1e-12 * s
     assert np.abs(rq[30:] - r[30:]).max() < 1e-12 * s
+
+
+# ---------------------------------------------------------------------------
+# the SUPG terms themselves (Sec. 4.3: tau^m rho (v_i,j u_j, R^m_i),
+# tau^m (q_,i, R^m_i), tau^c (v_i,i, R^c)), on fields where the strong
+# residuals have closed forms: u = A x + b (so grad u = A, Laplacian 0) and
+# p = g . x + p0 give R^m = rho A (A x + b) + g and R^c = tr A.  The
+# difference r(tau_m, tau_c) - r(0, 0) is compared with an independent
+# evaluation of those three integrals on a collapsed (Duffy) Gauss-Legendre
+# rule, a different exact rule from the oracle's; the form must also be
+# affine in tau_m and tau_c separately.
+# ---------------------------------------------------------------------------
+
+def _collapsed_rule(dim, n=6):
+    """Points (barycentric coordinates l_1..l_dim of the reference simplex)
+    and weights of the collapsed Gauss-Legendre product rule, exact for
+    polynomials of degree <= 2 n - 2 - dim on the unit simplex of volume
+    1 / dim!."""
+    xg, wg = np.polynomial.legendre.leggauss(n)
+    xg, wg = 0.5 * (xg + 1.0), 0.5 * wg
+    pts, wts = [], []
+    if dim == 2:
+        for s, ws in zip(xg, wg):
+            for t, wt in zip(xg, wg):
+                pts.append((s, t * (1.0 - s)))
+                wts.append(ws * wt * (1.0 - s))
+    else:
+        for s, ws in zip(xg, wg):
+            for t, wt in zip(xg, wg):
+                for v, wv in zip(xg, wg):
+                    pts.append((s, t * (1.0 - s), v * (1.0 - s) * (1.0 - t)))
+                    wts.append(ws * wt * wv * (1.0 - s) ** 2 * (1.0 - t))
+    return np.array(pts), np.array(wts)
+
+
+def _supg_terms(V, A, b, g, rho, tm, tc):
+    """The SUPG part of the residual on the affine Taylor-Hood simplex with
+    vertices V (dim + 1 rows), evaluated independently: velocity rows
+    (node-major, dof (a, i) at dim a + i) then pressure vertex rows."""
+    dim = V.shape[1]
+    E = V[1:] - V[0]                     # columns of the affine map
+    Jm = E.T
+    det = np.linalg.det(Jm)
+    Ginv = np.linalg.inv(Jm)             # rows: gradients of l_1..l_dim
+    gl = np.vstack([-Ginv.sum(axis=0), Ginv])  # gradients of the barycentrics
+    edges = [(0, 1), (1, 2), (2, 0)] if dim == 2 else [(0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3)]
+    nv = dim + 1
+    nn = nv + len(edges)
+    pts, wts = _collapsed_rule(dim)
+    rv = np.zeros((nn, dim))
+    rp = np.zeros(nv)
+    Rc = np.trace(A)
+    for lam, w in zip(pts, wts):
+        l = np.concatenate([[1.0 - lam.sum()], lam])
+        x = V[0] + Jm @ lam
+        u = A @ x + b
+        Rm = rho * (A @ u) + g
+        grads = [(4.0 * l[v] - 1.0) * gl[v] for v in range(nv)]
+        grads += [4.0 * (l[q] * gl[p] + l[p] * gl[q]) for p, q in edges]
+        wd = w * abs(det)
+        for a, gN in enumerate(grads):
+            adv = gN @ u
+            rv[a] += wd * (tm * rho * adv * Rm + tc * gN * Rc)
+        for v in range(nv):
+            rp[v] += wd * tm * (gl[v] @ Rm)
+    return np.concatenate([rv.ravel(), rp])
+
+
+def _linear_state(V, A, b, g, p0):
+    dim = V.shape[1]
+    edges = [(0, 1), (1, 2), (2, 0)] if dim == 2 else [(0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3)]
+    X = np.vstack([V] + [0.5 * (V[p] + V[q]) for p, q in edges])
+    return X @ A.T + b, V @ g + p0
+
+
+def test_supg_terms_against_an_independent_evaluation(orc):
+    rng = np.random.default_rng(21)
+    for dim, elem in ((2, orc.elem_ns), (3, orc.elem_ns3)):
+        V = np.vstack([np.zeros(dim), np.eye(dim)]) * 0.8 + rng.uniform(-0.1, 0.1, (dim + 1, dim))
+        A = rng.normal(size=(dim, dim))  # tr A != 0: the continuity residual is on
+        b, g, p0 = rng.normal(size=dim), rng.normal(size=dim), 0.7
+        U, P = _linear_state(V, A, b, g, p0)
+        tm, tc = 0.037, 0.021
+        r00 = elem(V, U, P, MU, RHO, 0.0, 0.0)[0]
+        rtt = elem(V, U, P, MU, RHO, tm, tc)[0]
+        ref = _supg_terms(V, A, b, g, RHO, tm, tc)
+        scale = np.abs(ref).max()
+        assert scale > 1e-3 and np.abs(ref[:-(dim + 1)]).max() > 1e-3 and np.abs(ref[-(dim + 1):]).max() > 1e-4
+        assert np.abs((rtt - r00) - ref).max() <= 1e-12 * scale
+        # each term on its own (a flipped sign or a dropped rho in one of them fails here)
+        assert np.abs((elem(V, U, P, MU, RHO, tm, 0.0)[0] - r00) - _supg_terms(V, A, b, g, RHO, tm, 0.0)).max() \
+            <= 1e-12 * scale
+        assert np.abs((elem(V, U, P, MU, RHO, 0.0, tc)[0] - r00) - _supg_terms(V, A, b, g, RHO, 0.0, tc)).max() \
+            <= 1e-12 * scale
+
+
+def test_supg_residual_is_affine_in_each_stabilisation_parameter(orc):
+    rng = np.random.default_rng(22)
+    for dim, elem, nu, npr in ((2, orc.elem_ns, 6, 3), (3, orc.elem_ns3, 10, 4)):
+        V = np.vstack([np.zeros(dim), np.eye(dim)]) * 0.9 + rng.uniform(-0.1, 0.1, (dim + 1, dim))
+        U, P = rng.normal(size=(nu, dim)), rng.normal(size=npr)  # a general (quadratic) state
+        r = lambda tm, tc: elem(V, U, P, MU, RHO, tm, tc)[0]
+        r00 = r(0.0, 0.0)
+        dm, dc = r(0.05, 0.0) - r00, r(0.0, 0.04) - r00
+        scale = np.abs(r00).max() + np.abs(dm).max() + np.abs(dc).max()
+        assert np.abs(r(0.1, 0.0) - r00 - 2.0 * dm).max() <= 1e-13 * scale
+        assert np.abs(r(0.0, 0.12) - r00 - 3.0 * dc).max() <= 1e-13 * scale
+        assert np.abs(r(0.05, 0.04) - r00 - dm - dc).max() <= 1e-13 * scale
+        assert np.abs(dm).max() > 1e-6 and np.abs(dc).max() > 1e-6
