@@ -576,6 +576,57 @@ __global__ void __launch_bounds__(GT_WARPS * 32, 3) k_gather_th(
 }
 
 // ---------------------------------------------------------------------------
+// thermal Q1 with translate elements: the gather in double-float.  Every
+// entry of a translate is k_e times a reference entry, so a node's row is a
+// sum of at most 64 such products; they are formed and summed as FP32 pairs
+// (the FP32 pipe runs 64 times the FP64 one here) in the same fixed order as
+// the FP64 gather, and each CSR value is converted once to FP64 by integer
+// operations.  Only rows flagged as next to a constrained node read their
+// columns for the Dirichlet elimination.  Used when every element is a
+// translate; a mesh with other elements takes the FP64 gather.
+// ---------------------------------------------------------------------------
+// the translates' coefficients as pairs, checked finite
+__global__ void k_kc_split(int64_t n_el, const double *__restrict__ kc, const uint8_t *__restrict__ tr,
+                           float2 *__restrict__ kc_df, int *status)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el || !tr[e]) return;
+    const double k = kc[e];
+    if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+    kc_df[e] = f64_to_df(k);
+}
+
+// flag[n] = 1 for every constrained node m and each of its neighbours n
+__global__ void k_mark_bc_rows(int64_t n_nodes, const int64_t *__restrict__ adj_ptr,
+                               const int32_t *__restrict__ adj_col, const uint8_t *__restrict__ mask,
+                               uint8_t *__restrict__ flag)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_nodes || !mask[m]) return;
+    for (int64_t q = adj_ptr[m]; q < adj_ptr[m + 1]; ++q) flag[adj_col[q]] = 1;
+}
+
+constexpr int GD_WARPS = 8;
+
+__global__ void __launch_bounds__(GD_WARPS * 32, 8) k_gather_th_q1df(
+    int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
+    const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
+    const uint8_t *__restrict__ inc_slot, const float2 *__restrict__ kref_df, const float2 *__restrict__ kc_df,
+    float2 f_df, const uint8_t *__restrict__ mask, const uint8_t *__restrict__ bcrow,
+    const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
+    double *__restrict__ d)
+{
+    constexpr int L = 8, G = 4;  // 8 lanes per node, 4 nodes per warp
+    __shared__ float2 acc_all[GD_WARPS * G][MF_MAX_DEG];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x / L;
+    const int64_t n = (int64_t)blockIdx.x * (GD_WARPS * G) + grp;
+    if (n >= n_nodes) return;  // group-uniform
+    const unsigned gmask = 0xffu << (lane & ~(L - 1));
+    gather_row_th_q1df(n, lane & (L - 1), gmask, acc_all[grp], mask != nullptr && bcrow[n] != 0, adj_ptr, adj_col,
+                       inc_ptr, inc, inc_loc, inc_slot, kref_df, kc_df, f_df, mask, bval, row_ptr, values, d);
+}
+
+// ---------------------------------------------------------------------------
 // elasticity gather: one warp per node, walking the node's incident elements in
 // ascending order.  Each element's 8 blocks (a_n, b) of the node's rows (72
 // values, stored as the upper blocks a <= b) are added into a shared-memory
@@ -1118,13 +1169,33 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         else if (m->elem == MF_P2_TRI)
             k_elem_thermal_p2<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->elem_inc,
                                                              p->scratch, status);
-        else
+        else if (!p->kc_df || p->n_translate < ne)
             k_elem_thermal_q1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->tr,
                                                              p->elem_inc, p->scratch, status);
+        // Q1 with translates: their coefficients as pairs for the double-float
+        // gather (the element kernel only runs for the other elements)
+        const bool q1df = m->elem == MF_Q1_HEX && p->kc_df && p->kref_df && p->bcrow && p->n_translate == ne;
+        if (q1df && ne > 0)
+            k_kc_split<<<nblk(ne, 256), 256, 0, st>>>(ne, c->elem_coef, p->tr, p->kc_df, status);
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         const mf_adj &A = p->adj[0];
         mf_prof_begin("gather_scalar", st);
+        if (q1df) {
+            if (c->bc_mask) {
+                MF_CUDA(cudaMemsetAsync(p->bcrow, 0, (size_t)A.n_rows, st));
+                k_mark_bc_rows<<<nblk(A.n_rows, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, c->bc_mask, p->bcrow);
+            }
+            const float fh = (float)f;
+            const float2 f_df = make_float2(fh, (float)(f - (double)fh));  // as f64_to_df
+            k_gather_th_q1df<<<nblk(A.n_rows, GD_WARPS * 4), GD_WARPS * 32, 0, st>>>(
+                A.n_rows, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->inc_slot,
+                cap ? p->kref_df + 73 : p->kref_df, p->kc_df, f_df, c->bc_mask, p->bcrow, c->bc_val, p->row_ptr,
+                values, d);
+            mf_prof_end(st);
+            MF_CUDA(cudaGetLastError());
+            return MF_OK;
+        }
 #define MF_GATHER_TH(NPE)                                                                                         \
     k_gather_th<NPE><<<nblk(A.n_rows, GT_WARPS * (32 / th_lanes<NPE>())), GT_WARPS * 32, 0, st>>>(                 \
         A.n_rows, A.ptr, A.col, p->inc_ptr, p->inc, p->inc_loc, p->inc_slot, p->scratch, kref, c->elem_coef, f,     \

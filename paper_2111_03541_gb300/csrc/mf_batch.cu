@@ -38,6 +38,10 @@ struct BatchProblem {
     const int64_t *row_ptr;
     double *values;
     double *d;
+    // a Q1 mesh of translates: reference entries and coefficients as FP32
+    // pairs (the double-float gather of the single-problem path); else null
+    const float2 *kref_df;
+    float2 *kc_df;
 };
 
 struct BatchTile {
@@ -72,7 +76,11 @@ __global__ void __launch_bounds__(256) k_batch_elem(const BatchProblem *__restri
             const int64_t e = T.first + i;
             if (T.type == MF_P1_TRI) elem_thermal_p1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
             else if (T.type == MF_P2_TRI) elem_thermal_p2(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
-            else if (!q1_translate(e, p.tr, p.kc, status))
+            else if (p.kc_df) {
+                const double k = p.kc[e];
+                if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+                p.kc_df[e] = f64_to_df(k);
+            } else if (!q1_translate(e, p.tr, p.kc, status))
                 elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
         }
     }
@@ -87,6 +95,15 @@ __device__ __forceinline__ void batch_gather_tile(const BatchProblem &p, const B
     constexpr int L = th_lanes<NPE>(), G = 32 / L;
     const int grp = warp * G + lane / L;
     const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
+    if (NPE == 8 && p.kc_df) {  // translates: the single-problem path's double-float row (every row
+                                // takes the Dirichlet branch when there is a mask: the same values)
+        const float2 f_df = f64_to_df(p.f);
+        for (int64_t i = grp; i < T.count; i += BG_WARPS * G)
+            gather_row_th_q1df(T.first + i, lane & (L - 1), gmask, reinterpret_cast<float2 *>(acc_all[grp]),
+                               p.mask != nullptr, p.ptr, p.col, p.inc_ptr, p.inc, p.inc_loc, p.inc_slot, p.kref_df,
+                               p.kc_df, f_df, p.mask, p.bval, p.row_ptr, p.values, p.d);
+        return;
+    }
     for (int64_t i = grp; i < T.count; i += BG_WARPS * G)  // group-uniform
         gather_row_th<NPE>(T.first + i, lane & (L - 1), gmask, acc_all[grp], p.ptr, p.col, p.inc_ptr, p.inc,
                            p.inc_loc, p.inc_slot, p.scratch, p.kref, p.kc, p.f, p.mask, p.bval, p.row_ptr, p.values,
@@ -259,7 +276,11 @@ extern "C" mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, co
         b->host.push_back(BatchProblem{m->elem, m->npe, m->n_elems, m->n_nodes, m->coords, m->conn, c.elem_coef,
                                        c.source[0], p->scratch, p->scratch_stride, A.ptr, A.col, p->inc_ptr, p->inc,
                                        p->inc_loc, p->inc_slot, p->elem_inc, p->tr, p->kref, c.bc_mask, c.bc_val,
-                                       p->row_ptr, values[i], d[i]});
+                                       p->row_ptr, values[i], d[i],
+                                       (m->elem == MF_Q1_HEX && p->kc_df && p->n_translate == m->n_elems)
+                                           ? p->kref_df : nullptr,
+                                       (m->elem == MF_Q1_HEX && p->kref_df && p->n_translate == m->n_elems)
+                                           ? p->kc_df : nullptr});
         cnt[m->elem] += m->n_elems;
         nodes += m->n_nodes;
     }

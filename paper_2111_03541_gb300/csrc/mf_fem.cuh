@@ -257,6 +257,48 @@ __host__ __device__ __forceinline__ double f32_to_f64_exact(float f)
 
 __host__ __device__ __forceinline__ double df_to_double(float2 a) { return f32_to_f64_exact(a.x) + f32_to_f64_exact(a.y); }
 
+// FP64 -> pair: the nearest FP32 and the nearest FP32 of the exact remainder
+__device__ __forceinline__ float2 f64_to_df(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// A normalised pair's value as FP64 by integer operations only (no FP64
+// instruction, so nothing lands on GB300's narrow FP64 pipe): the high word's
+// 24-bit significand followed by the low word's bits aligned below it (those
+// under the 53-bit significand are truncated toward -inf, at most one ulp).
+// A zero or subnormal high word gives a signed zero, an infinite or NaN one
+// its own FP64 value.
+__device__ __forceinline__ double df_to_double_int(float2 a)
+{
+    const unsigned hb = __float_as_uint(a.x);
+    const int eh = (int)((hb >> 23) & 0xffu);
+    if (eh == 0) return __longlong_as_double((long long)((unsigned long long)(hb & 0x80000000u) << 32));
+    if (eh == 0xff) return f32_to_f64_exact(a.x);
+    long long M = (long long)((hb & 0x7fffffu) | 0x800000u) << 29;  // units of 2^(eh - 127 - 52)
+    const unsigned lb = __float_as_uint(a.y);
+    const int el = (int)((lb >> 23) & 0xffu);
+    if (el != 0) {
+        const long long L = (long long)((lb & 0x7fffffu) | 0x800000u);  // units of 2^(el - 150)
+        int sh = eh - 29 - el;  // >= -5 for a normalised pair, |lo| <= ulp(hi) / 2
+        sh = sh < -5 ? -5 : sh;
+        const long long add = sh >= 63 ? 0 : (sh >= 0 ? (L >> sh) : (L << -sh));
+        M = ((hb ^ lb) >> 31) ? M - add : M + add;
+    }
+    long long e = eh - 127 + 1023;
+    if (M >= (1ll << 53)) {
+        M >>= 1;
+        ++e;
+    } else if (M < (1ll << 52)) {
+        M <<= 1;
+        --e;
+    }
+    const unsigned long long bits = ((unsigned long long)(hb >> 31) << 63) | ((unsigned long long)e << 52) |
+                                    ((unsigned long long)M & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
 // a b - c d in double-float
 __host__ __device__ __forceinline__ float2 df_det2(float2 a, float2 b, float2 c, float2 d)
 {
@@ -1068,6 +1110,89 @@ __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) lift += __shfl_xor_sync(gmask, lift, o, L);
     if (sub == 0) d[n] = rm ? bval[n] : dsum + lift;
+    __syncwarp(gmask);
+}
+
+// One node's row of the thermal Q1 form on a mesh whose elements are all
+// translates of element 0, in double-float: every entry of element e is k_e
+// times a reference entry, so the row is a sum of at most 64 products, formed
+// and summed as FP32 pairs (the FP32 pipe runs 64 times the FP64 one on
+// GB300) in the same fixed order as gather_row_th (lane b adds column b of
+// each incident element, elements ascending), then converted once per value
+// to FP64 by integer operations.  L = 8 lanes per node; acc holds MF_MAX_DEG
+// pairs.  near_bc: the node or a neighbour is constrained (only then are the
+// columns read for the Dirichlet elimination; the FP64 lifting lives in that
+// branch alone, so an interior row issues no FP64 instruction).
+__device__ __forceinline__ void gather_row_th_q1df(int64_t n, int sub, unsigned gmask, float2 *acc, bool near_bc,
+                                                   const int64_t *__restrict__ adj_ptr,
+                                                   const int32_t *__restrict__ adj_col,
+                                                   const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
+                                                   const uint8_t *__restrict__ inc_loc,
+                                                   const uint8_t *__restrict__ inc_slot,
+                                                   const float2 *__restrict__ kref_df,
+                                                   const float2 *__restrict__ kc_df, float2 f_df,
+                                                   const uint8_t *__restrict__ mask, const double *__restrict__ bval,
+                                                   const int64_t *__restrict__ row_ptr, double *__restrict__ values,
+                                                   double *__restrict__ d)
+{
+    constexpr int NPE = 8, L = 8, U = 1;  // one element at a time: 32 registers, full occupancy (measured
+                                          // fastest against 2, 4 and 8 elements' loads in flight)
+    const int64_t p0 = adj_ptr[n];
+    const int deg = (int)(adj_ptr[n + 1] - p0);
+    // incidence entries number below 2^31 (checked when the pattern is built)
+    const int32_t i0 = (int32_t)inc_ptr[n], i1 = (int32_t)inc_ptr[n + 1];
+    const int64_t rb = row_ptr[n];
+    for (int i = sub; i < deg; i += L) acc[i] = make_float2(0.f, 0.f);
+    __syncwarp(gmask);
+    // load vector: lane sub takes incidence entries i0 + sub, i0 + sub + L, ...
+    float2 dsum = make_float2(0.f, 0.f);
+    for (int32_t t = i0 + sub; t < i1; t += L)
+        dsum = df_add(dsum, df_mul(f_df, kref_df[NPE * NPE + (inc_loc[t] & 0x7f)]));
+    for (int32_t cb = i0; cb < i1; cb += U) {
+        const int cnt = min(U, i1 - cb);
+        float2 val[U];
+        int s[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            val[j] = make_float2(0.f, 0.f);
+            s[j] = 0;
+            if (j < cnt) {
+                const int32_t t = cb + j;
+                s[j] = inc_slot[(uint32_t)t * NPE + sub];
+                val[j] = df_mul(kc_df[inc[t]], kref_df[(inc_loc[t] & 0x7f) * NPE + sub]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (j < cnt) {  // group-uniform
+                acc[s[j]] = df_add(acc[s[j]], val[j]);
+                __syncwarp(gmask);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1)
+        dsum = df_add(dsum, make_float2(__shfl_xor_sync(gmask, dsum.x, o, L), __shfl_xor_sync(gmask, dsum.y, o, L)));
+    if (!near_bc) {
+        for (int k = sub; k < deg; k += L) values[rb + k] = df_to_double_int(acc[k]);
+        if (sub == 0) d[n] = df_to_double_int(dsum);
+    } else {
+        double lift = 0.0;
+        const bool rm = mask[n] != 0;
+        for (int k = sub; k < deg; k += L) {
+            double v = df_to_double_int(acc[k]);
+            const int32_t mcol = adj_col[p0 + k];
+            if (rm) v = (mcol == n) ? 1.0 : 0.0;
+            else if (mask[mcol]) {
+                lift -= v * bval[mcol];
+                v = 0.0;
+            }
+            values[rb + k] = v;
+        }
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) lift += __shfl_xor_sync(gmask, lift, o, L);
+        if (sub == 0) d[n] = rm ? bval[n] : (lift != 0.0 ? df_to_double_int(dsum) + lift : df_to_double_int(dsum));
+    }
     __syncwarp(gmask);
 }
 

@@ -77,6 +77,13 @@ struct mf_pattern {
     uint8_t *tr = nullptr;
     double *kref = nullptr;
     int64_t n_translate = 0;
+    // the same reference entries as FP32 pairs (hi, lo), the translates'
+    // coefficients as pairs (written per assembly), and per node a flag set
+    // per assembly when the node or a neighbour is constrained (thermal Q1
+    // with translates)
+    float2 *kref_df = nullptr;
+    float2 *kc_df = nullptr;
+    uint8_t *bcrow = nullptr;
     // 20-node bricks: the vertices' trilinear-map coefficients of q1_jac_at
     // per element as FP32 pairs (hi, lo), [n_elems][8][3]
     float2 *q2s_map = nullptr;

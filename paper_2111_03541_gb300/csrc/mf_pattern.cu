@@ -383,6 +383,13 @@ __global__ void k_translate_flags(int64_t n_el, const double *__restrict__ X, co
     if ((threadIdx.x & 31) == 0 && bal) atomicAdd(count, (unsigned long long)__popc(bal));
 }
 
+// the reference entries as FP32 pairs
+__global__ void k_kref_df(const double *__restrict__ kref, float2 *__restrict__ kref_df)
+{
+    const int t = threadIdx.x;
+    if (t < 73 + 72) kref_df[t] = f64_to_df(kref[t]);
+}
+
 // kref = element 0's matrix and load vector with k = 1, f = 1 (kref[72] holds
 // the 1), then its capacity matrix with C = 1 and a zero load at kref + 73
 __global__ void k_kref(const double *__restrict__ X, const int32_t *__restrict__ conn, double *kref, int *status)
@@ -672,8 +679,13 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->mixed_state);
     cudaFree(p->tr);
     cudaFree(p->kref);
+    cudaFree(p->kref_df);
+    cudaFree(p->kc_df);
+    cudaFree(p->bcrow);
     p->tr = nullptr;
     p->kref = nullptr;
+    p->kref_df = p->kc_df = nullptr;
+    p->bcrow = nullptr;
     p->n_translate = 0;
     p->slot = nullptr;
     p->mixed_state = nullptr;
@@ -744,6 +756,10 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
                 MF_CUDA(cudaMallocAsync(&p->kref, sizeof(double) * (73 + 72), st));
                 k_kref<<<1, 1, 0, st>>>(m->coords, m->conn, p->kref, status);
                 k_mark_translates<<<nblk(m->n_nodes), TPB, 0, st>>>(m->n_nodes, incv.ptr, incv.inc, p->tr, incv.loc);
+                MF_CUDA(cudaMallocAsync(&p->kref_df, sizeof(float2) * (73 + 72), st));
+                k_kref_df<<<1, 160, 0, st>>>(p->kref, p->kref_df);
+                MF_CUDA(cudaMallocAsync(&p->kc_df, sizeof(float2) * m->n_elems, st));
+                MF_CUDA(cudaMallocAsync(&p->bcrow, (size_t)m->n_nodes, st));
             }
         }
     } else if (form == MF_FORM_ELASTIC && m->elem == MF_Q2S_HEX) {
