@@ -363,7 +363,10 @@ mf_status mf_flow_mg_destroy(mf_flow_mg *mg);
  * is formed in FP64 with K as given, each correction K z = r / ||r|| is
  * solved on an FP32 copy of K with FP32 vectors to inner_tol, and x += ||r|| z
  * in FP64, until ||d - K x|| <= tol ||d|| (max_iter caps the inner
- * iterations; the refinement needs kappa(K) 2^-24 well below 1), or
+ * iterations; the refinement needs kappa(K) 2^-24 well below 1; three
+ * refinements in a row that do not halve the residual end the solve with
+ * MF_ERR_NOT_CONVERGED: the FP64 residual has reached its rounding floor
+ * above tol), or
  * (MF_SOLVER_GMRES_FLOW_MG) right-preconditioned GMRES(restart) with the
  * flow hierarchy opts->flow_mg (mf_flow_mg_create).  x holds x0 on entry (a warm start
  * resumes a previous solve) and the solution on exit.  Synchronises the

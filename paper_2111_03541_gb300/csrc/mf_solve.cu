@@ -973,8 +973,9 @@ mf_status solve_refined(const mf_csr *K, const double *d, double *x, const mf_so
     const SpmvShape shape = spmv_shape(n, nnz);
     const int chunk = o->check_every > 0 ? o->check_every : 50;
     int64_t inner_total = 0, refinements = 0;
-    double relres = 0.0;
-    int done = 0;  // 1 converged, 2 cap, 3 breakdown
+    double relres = 0.0, prev = 0.0;
+    int stall = 0;  // refinements in a row that did not halve the residual
+    int done = 0;   // 1 converged, 2 cap, 3 breakdown, 4 stagnated
     for (;;) {
         spmv_any(K, K->values, x, kx.p, st);
         k_ref_resid<<<red_grid(n), RT, 0, st>>>(n, d, kx.p, r64.p, part.p, &S.p->ticket, out2.p);
@@ -987,6 +988,11 @@ mf_status solve_refined(const mf_csr *K, const double *d, double *x, const mf_so
         if (!isfinite(relres)) { done = 3; break; }
         if (relres <= o->tol || rn == 0.0) { done = 1; break; }
         if (inner_total >= o->max_iter) { done = 2; break; }
+        // the FP64 residual of a system has a rounding floor: below it the
+        // corrections no longer reduce it, and the loop stops
+        stall = (refinements > 0 && relres > 0.5 * prev) ? stall + 1 : 0;
+        if (stall >= 3) { done = 4; break; }
+        prev = relres;
         // inner FP32 Jacobi-PCG on K32 z = r / ||r|| from z = 0
         PcgState hs{};
         hs.tol2 = inner_tol * inner_tol;
@@ -1020,6 +1026,11 @@ mf_status solve_refined(const mf_csr *K, const double *d, double *x, const mf_so
         return mf_fail(MF_ERR_NOT_CONVERGED, "mf_solve: %lld inner iterations, residual %.3e", (long long)inner_total,
                        relres);
     if (done == 3) return mf_fail(MF_ERR_NONFINITE, "mf_solve: breakdown or non-finite value");
+    if (done == 4)
+        return mf_fail(MF_ERR_NOT_CONVERGED,
+                       "mf_solve: refinement stagnated at residual %.3e after %lld refinements (the rounding floor "
+                       "of the FP64 residual lies above the tolerance)",
+                       relres, (long long)refinements);
     return MF_OK;
 }
 

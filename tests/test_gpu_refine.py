@@ -70,9 +70,21 @@ def test_refined_mixed_64cube_against_golden(mf):
     prob = gen.elastic_problem(64)
     P = mf.Problem(prob)
     P.assemble(mf.MF_PREC_MIXED)
-    x, st, info = P.solve(solver=mf.MF_SOLVER_PCG_REFINED, tol=1e-12, max_iter=200000, inner_tol=1e-4)
-    assert st == mf.MF_OK and info.converged
+    # the FP64 residual of this system has a rounding floor near 2e-12: 1e-11 is reachable
+    x, st, info = P.solve(solver=mf.MF_SOLVER_PCG_REFINED, tol=1e-11, max_iter=200000, inner_tol=1e-4)
+    assert st == mf.MF_OK and info.converged and info.refinements <= 20
     xs = x.cpu().numpy()[np.array(idx)]
     ref = np.array(val)
     err = np.linalg.norm(xs - ref) / np.linalg.norm(ref)
     assert err <= 1e-8, err
+
+
+def test_refinement_stops_at_the_rounding_floor(mf):
+    """A tolerance below the FP64 residual's rounding floor ends in a
+    'stagnated' error after a few refinements, not at the iteration cap."""
+    P = mf.Problem(gen.elastic_problem(16))
+    P.assemble(mf.MF_PREC_MIXED)
+    x, st, info = P.solve(solver=mf.MF_SOLVER_PCG_REFINED, tol=1e-30, max_iter=10 ** 7, inner_tol=1e-4)
+    assert st == mf.MF_ERR_NOT_CONVERGED and not info.converged
+    assert info.refinements <= 40 and info.iterations < 10 ** 6
+    assert info.rel_residual <= 1e-12
