@@ -39,12 +39,13 @@ FCG_DIRS = 256  # stored directions of the flexible CG with the learned precondi
 # instructions per element and DRAM bytes per element, both in proportion to
 # the elements), with the SHA-256 prefix of the files that hold the kernel's
 # code: the line reports null for them once those files change.  Capture: 48^3
-# (110,592 elements), smsp__inst_executed.sum = 246,564,942,
-# dram__bytes_read.sum + dram__bytes_write.sum = 132.17 MB + 62.63 MB.
-MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 246564942 / 110592,
-                  "bytes_per_element": (132165632 + 62629120) / 110592,
+# (110,592 elements), smsp__inst_executed.sum = 236,888,814, DRAM bytes =
+# dram__bytes.sum.per_second x gpu__time_duration.sum = 0.698 TB/s x 288.0 us
+# = 201.1 MB (the same capture gives the finishing kernel's figures).
+MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 236888814 / 110592,
+                  "bytes_per_element": 0.698116e12 * 288.0e-6 / 110592,
                   "sources": ("paper_2111_03541_gb300/csrc/mf_mixed.cu", "paper_2111_03541_gb300/csrc/mf_device.cuh"),
-                  "sha256": "f97c5dce99e42da9"}
+                  "sha256": "ab910985437711a7"}
 KERNELS_PER_ASSEMBLY = {"mixed": 4, "fp64": 2}
 # instruction-issue ceiling of GB300: one warp instruction per clock per SM
 # sub-partition, 4 per SM, 152 SMs, 2070 MHz maximum SM clock
