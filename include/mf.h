@@ -51,7 +51,10 @@ typedef enum {
 } mf_status;
 
 typedef enum { MF_P1_TRI = 0, MF_P2_TRI = 1, MF_Q1_HEX = 2, MF_Q2S_HEX = 3, MF_P2_TET = 4, MF_Q2S_QUAD = 5 } mf_elem;
-typedef enum { MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2, MF_FORM_CAPACITY = 3 } mf_form;
+typedef enum {
+    MF_FORM_THERMAL = 0, MF_FORM_ELASTIC = 1, MF_FORM_OSEEN = 2, MF_FORM_CAPACITY = 3,
+    MF_FORM_NS = 4  /* steady Navier-Stokes with SUPG, Newton tangent (Sec. 4.3) */
+} mf_form;
 typedef enum { MF_PREC_FP64 = 0, MF_PREC_MIXED = 1 } mf_prec;
 typedef enum {
     MF_SOLVER_PCG = 0, MF_SOLVER_GMRES = 1, MF_SOLVER_PCG_REFINED = 2, MF_SOLVER_GMRES_FLOW_MG = 3
@@ -96,7 +99,10 @@ typedef struct {
 /* Coefficients of a form (Sec. 4.1-4.3).  elem_coef [n_elems]: the
  * conductivity k (thermal) or Young's modulus E (elasticity); ignored by the
  * flow form.  source: thermal f = source[0]; elasticity body force b[3].
- * advect [2][n_nodes]: nodal advecting velocity of the flow form.  bc_mask
+ * advect [2][n_nodes]: nodal advecting velocity of the flow form; for the
+ * Navier-Stokes form (MF_FORM_NS) the current state [u1 | u2 | p]
+ * (2 n_nodes + n_pnodes), with the stabilisation parameters tau_m, tau_c of
+ * the SUPG terms (constants, Sec. 4.3).  bc_mask
  * [n_dofs] (u8, nonzero = Dirichlet) and bc_val [n_dofs] f64 may be NULL
  * (no constraint).  Dirichlet dofs are eliminated symmetrically: row and
  * column zeroed in the pattern, K[g][g] = 1, d[g] = bc_val[g], and
@@ -110,6 +116,7 @@ typedef struct {
     const double *advect;
     const uint8_t *bc_mask;
     const double *bc_val;
+    double tau_m, tau_c;     /* SUPG parameters (MF_FORM_NS) */
 } mf_coeffs;
 
 /* CSR view.  row_ptr [n_rows+1] int64, col_idx [nnz] int32 ascending within a
@@ -157,7 +164,9 @@ mf_status mf_mesh_destroy(mf_mesh *mesh);
  * Block B-1 unique control-point pairs -> Block B-4 sparse ids), as CSR with
  * ascending columns plus the element -> entry maps the assembly uses.  The
  * flow form has the blocks u1-u1, u2-u2, u-p, p-u and the p-p diagonal; no
- * u1-u2 block.  Elasticity takes Q1 and Q2S bricks (dof 3 n + c, 3 x 3
+ * u1-u2 block.  The Navier-Stokes form (MF_FORM_NS) has every block: u1-u2
+ * (the convective derivative) and the full P1 x P1 p-p block (the SUPG
+ * pressure term).  Elasticity takes Q1 and Q2S bricks (dof 3 n + c, 3 x 3
  * blocks per node pair).  Synchronises the stream.  Errors:
  * MF_ERR_INVALID_ARG, MF_ERR_UNSUPPORTED (a form the element does not
  * carry; more than 64 neighbours (128 for Q2S) or 32 incident elements per
@@ -189,6 +198,19 @@ mf_status mf_pattern_destroy(mf_pattern *pattern);
  * coefficients are latched (MF_ERR_NONFINITE). */
 mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
                       const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d, void *stream);
+/* form = MF_FORM_NS (prec FP64, on a pattern built for MF_FORM_NS: every
+ * block, u1-u2 and the full p-p block included) linearises the steady
+ * Navier-Stokes form with SUPG at the state x = coeffs->advect (Sec. 4.3
+ * domain form, Newton of Sec. 2.1):
+ *   r_(a,i) = int -rho (grad N_a . u) u_i - d_i N_a p + mu grad N_a . grad u_i
+ *             + tau_m rho (grad N_a . u) Rm_i + tau_c d_i N_a Rc,
+ *   r_b     = int M_b Rc + tau_m grad M_b . Rm,
+ *   Rm = rho (u . grad) u + grad p - mu lap u,  Rc = div u,
+ * K = dr/dx (the tangent, by hand-derived derivatives) and d = -r, so that
+ * K dx = d is the Newton step.  Dirichlet dofs g get the increment data
+ * bc_val[g] - x[g] with the same symmetric elimination as the other forms.
+ * Integrals by a collapsed 4 x 4 Gauss rule, exact for every integrand on
+ * straight-sided triangles. */
 /* form = MF_FORM_CAPACITY (prec FP64, on a thermal pattern) assembles the
  * capacity matrix of the rate term -C(T, T_t) of Sec. 4.1, K[a][b] =
  * sum_e C_e int_e N_a N_b with C_e = elem_coef[e], exactly on affine elements
@@ -375,6 +397,20 @@ mf_status mf_flow_mg_destroy(mf_flow_mg *mg);
  * latched device error.  info may be NULL. */
 mf_status mf_solve(const mf_csr *K, const double *d, double *x, const mf_solver_opts *opts,
                    mf_solve_info *info, void *stream);
+
+/* Newton-Raphson (Sec. 2.1) on the Navier-Stokes form with SUPG: x (device
+ * [2 n_nodes + n_pnodes], the state; entries of Dirichlet dofs are set to
+ * bc_val first) is updated by steps K dx = -r (mf_assemble with MF_FORM_NS,
+ * then mf_solve with *lin, e.g. GMRES) until the residual on the free dofs
+ * satisfies ||r_free|| <= newton_tol max(1, ||r_free(x0)||), at most
+ * max_newton steps.  coeffs->advect is ignored (x is the state).  resid_hist
+ * (host, max_newton + 1 entries, may be NULL) receives ||r_free|| before each
+ * step; *n_steps the number of steps taken.  Synchronises the stream.
+ * Returns MF_ERR_NOT_CONVERGED at max_newton or when a linear solve fails to
+ * converge, and the errors of mf_assemble and mf_solve. */
+mf_status mf_ns_newton(const mf_mesh *mesh, const mf_pattern *pattern, const mf_coeffs *coeffs, double *x,
+                       double newton_tol, int32_t max_newton, const mf_solver_opts *lin, double *resid_hist,
+                       int32_t *n_steps, void *stream);
 
 /* Jacobi-PCG like mf_solve (same kernels and stopping rule), but it makes no
  * device allocation: no cudaMalloc, no cudaFree, no graph, stream or event

@@ -20,12 +20,12 @@ LIB = os.path.join(HERE, "libmf.so")
 MF_OK, MF_ERR_INVALID_ARG, MF_ERR_BAD_MESH, MF_ERR_NONFINITE, MF_ERR_OOM, MF_ERR_CUDA, \
     MF_ERR_NOT_CONVERGED, MF_ERR_TIMEOUT, MF_ERR_UNSUPPORTED = range(9)
 MF_P1_TRI, MF_P2_TRI, MF_Q1_HEX, MF_Q2S_HEX, MF_P2_TET, MF_Q2S_QUAD = 0, 1, 2, 3, 4, 5
-MF_FORM_THERMAL, MF_FORM_ELASTIC, MF_FORM_OSEEN, MF_FORM_CAPACITY = 0, 1, 2, 3
+MF_FORM_THERMAL, MF_FORM_ELASTIC, MF_FORM_OSEEN, MF_FORM_CAPACITY, MF_FORM_NS = 0, 1, 2, 3, 4
 MF_PREC_FP64, MF_PREC_MIXED = 0, 1
 MF_SOLVER_PCG, MF_SOLVER_GMRES, MF_SOLVER_PCG_REFINED, MF_SOLVER_GMRES_FLOW_MG = 0, 1, 2, 3
 
 ELEM = {"P1": MF_P1_TRI, "P2": MF_P2_TRI, "Q1": MF_Q1_HEX, "Q2S": MF_Q2S_HEX, "P2T": MF_P2_TET, "Q2Q": MF_Q2S_QUAD}
-FORM = {"thermal": MF_FORM_THERMAL, "elastic": MF_FORM_ELASTIC, "oseen": MF_FORM_OSEEN}
+FORM = {"thermal": MF_FORM_THERMAL, "elastic": MF_FORM_ELASTIC, "oseen": MF_FORM_OSEEN, "ns": MF_FORM_NS}
 
 
 class MFError(RuntimeError):
@@ -42,7 +42,7 @@ class MeshDesc(C.Structure):
 class Coeffs(C.Structure):
     _fields_ = [("elem_coef", C.c_void_p), ("nu", C.c_double), ("visc", C.c_double), ("rho", C.c_double),
                 ("source", C.c_double * 3), ("advect", C.c_void_p), ("bc_mask", C.c_void_p),
-                ("bc_val", C.c_void_p)]
+                ("bc_val", C.c_void_p), ("tau_m", C.c_double), ("tau_c", C.c_double)]
 
 
 class CSR(C.Structure):
@@ -88,6 +88,8 @@ _SIGS = {
     "mf_pattern_destroy": [C.c_void_p],
     "mf_assemble": [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Coeffs), C.c_int32, C.POINTER(CSR), C.c_void_p,
                     C.c_void_p],
+    "mf_ns_newton": [C.c_void_p, C.c_void_p, C.POINTER(Coeffs), C.c_void_p, C.c_double, C.c_int32,
+                     C.POINTER(SolverOpts), C.c_void_p, C.POINTER(C.c_int32), C.c_void_p],
     "mf_facets_create": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                          C.POINTER(C.c_void_p)],
     "mf_facets_destroy": [C.c_void_p],
@@ -212,6 +214,20 @@ def mf_pattern_destroy(h) -> None:
 
 def mf_assemble(form: int, mesh, pattern, coeffs: Coeffs, prec: int, K: CSR, d, stream=None) -> None:
     _check(lib().mf_assemble(form, mesh, pattern, C.byref(coeffs), prec, C.byref(K), _ptr(d), _stream(stream)))
+
+
+def mf_ns_newton(mesh, pattern, coeffs: Coeffs, x, newton_tol: float, max_newton: int, lin: SolverOpts,
+                 stream=None) -> tuple[int, list[float], int]:
+    """Newton on the Navier-Stokes form: (status, residual norms before each
+    step, steps taken); MF_ERR_NOT_CONVERGED is returned, not raised."""
+    hist = (C.c_double * (max_newton + 1))()
+    steps = C.c_int32(0)
+    st = lib().mf_ns_newton(mesh, pattern, C.byref(coeffs), _ptr(x), newton_tol, max_newton, C.byref(lin),
+                            C.cast(hist, C.c_void_p), C.byref(steps), _stream(stream))
+    if st not in (MF_OK, MF_ERR_NOT_CONVERGED):
+        _check(st)
+    n = min(steps.value + 1, max_newton + 1)  # one norm per evaluated state
+    return st, [hist[i] for i in range(n)], steps.value
 
 
 def mf_facets_create(mesh, pattern, elem, face, stream=None) -> C.c_void_p:
@@ -466,8 +482,14 @@ class Problem:
         self.coef = t(prob["coef"], torch.float64)
         self.bc_mask = t(prob["bc_mask"], torch.uint8)
         self.bc_val = t(prob["bc_val"], torch.float64)
-        self.pconn = t(prob["vconn"], torch.int32) if prob["form"] == "oseen" else None
-        self.advect = t(prob["advect"], torch.float64) if prob["form"] == "oseen" else None
+        flow = prob["form"] in ("oseen", "ns")
+        self.pconn = t(prob["vconn"], torch.int32) if flow else None
+        if prob["form"] == "ns":  # the state [u1 | u2 | p]
+            n_state = 2 * prob["coords"].shape[0] + prob["vcoords"].shape[0]
+            self.advect = t(prob["state"], torch.float64) if "state" in prob else \
+                torch.zeros(n_state, dtype=torch.float64, device=dev)
+        else:
+            self.advect = t(prob["advect"], torch.float64) if flow else None
         self.desc = MeshDesc(dim=self.coords.shape[1], elem=ELEM[prob["elem"]], n_nodes=self.coords.shape[0],
                              n_elems=self.conn.shape[0], coords=_ptr(self.coords), conn=_ptr(self.conn),
                              n_pnodes=0 if self.pconn is None else prob["vcoords"].shape[0],
@@ -506,6 +528,8 @@ class Problem:
             for i in range(3):
                 c.source[i] = p["body"][i]
         c.advect = _ptr(self.advect)
+        c.tau_m = p.get("tau_m", 0.0)
+        c.tau_c = p.get("tau_c", 0.0)
         if bc:
             c.bc_mask = _ptr(self.bc_mask)
             c.bc_val = _ptr(self.bc_val)
@@ -524,6 +548,12 @@ class Problem:
         if self.facets:
             mf_assemble_boundary(self.facets, self.facet_coeffs, self.csr, self.d, stream)
         return self.values, self.d
+
+    def newton(self, tol=1e-11, max_newton=30, lin_tol=1e-13, restart=50, max_iter=200000, stream=None):
+        """Navier-Stokes form: Newton from the current state ``self.advect``
+        (updated in place); returns (status, residual history, steps)."""
+        lin = SolverOpts(solver=MF_SOLVER_GMRES, restart=restart, tol=lin_tol, max_iter=max_iter, check_every=10)
+        return mf_ns_newton(self.mesh, self.pattern, self.coeffs, self.advect, tol, max_newton, lin, stream)
 
     def pressure_mass_diag(self, stream=None):
         import torch

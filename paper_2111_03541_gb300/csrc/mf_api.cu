@@ -303,9 +303,9 @@ extern "C" mf_status mf_pattern_build(const mf_mesh *mesh, int32_t form, void *s
     *out = nullptr;
     if (form == MF_FORM_ELASTIC && mesh->elem != MF_Q1_HEX && mesh->elem != MF_Q2S_HEX)
         return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: elasticity is provided on Q1 and Q2S bricks");
-    if (form == MF_FORM_OSEEN && (mesh->elem != MF_P2_TRI || !mesh->pconn))
+    if ((form == MF_FORM_OSEEN || form == MF_FORM_NS) && (mesh->elem != MF_P2_TRI || !mesh->pconn))
         return mf_fail(MF_ERR_UNSUPPORTED, "mf_pattern_build: flow needs a P2 mesh with pconn");
-    if (form < MF_FORM_THERMAL || form > MF_FORM_OSEEN)
+    if (form < MF_FORM_THERMAL || form > MF_FORM_NS || form == MF_FORM_CAPACITY)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_pattern_build: unknown form %d", form);
     mf_pattern *p = new (std::nothrow) mf_pattern();
     if (!p) return mf_fail(MF_ERR_OOM, "mf_pattern_build: host allocation");
@@ -377,13 +377,17 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
     if (K->n_rows != pattern->n_rows || K->nnz != pattern->nnz || K->row_ptr != pattern->row_ptr ||
         K->col_idx != pattern->col_idx)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: K does not carry the pattern's CSR arrays");
-    if (form != MF_FORM_OSEEN && !coeffs->elem_coef)
+    const bool flow = form == MF_FORM_OSEEN || form == MF_FORM_NS;
+    if (!flow && !coeffs->elem_coef)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: elem_coef is NULL");
-    if (form == MF_FORM_OSEEN && !coeffs->advect)
-        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: advect is NULL");
+    if (flow && !coeffs->advect)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: advect (the advecting field or the state) is NULL");
+    if (form == MF_FORM_NS && prec != MF_PREC_FP64)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_assemble: the Navier-Stokes form is assembled in FP64");
     if ((coeffs->bc_mask == nullptr) != (coeffs->bc_val == nullptr))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: bc_mask and bc_val go together");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (form == MF_FORM_NS) return mf_assemble_ns(mesh, pattern, coeffs, K->values, d, st);
     if (prec == MF_PREC_FP64) return mf_assemble_fp64(form, mesh, pattern, coeffs, K->values, d, st);
     if (prec == MF_PREC_MIXED) {
         if (form != MF_FORM_ELASTIC)
@@ -391,6 +395,24 @@ extern "C" mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pat
         return mf_assemble_mixed(form, mesh, pattern, coeffs, K->values, d, st);
     }
     return mf_fail(MF_ERR_INVALID_ARG, "mf_assemble: unknown precision %d", prec);
+}
+
+extern "C" mf_status mf_ns_newton(const mf_mesh *mesh, const mf_pattern *pattern, const mf_coeffs *coeffs,
+                                  double *x, double newton_tol, int32_t max_newton, const mf_solver_opts *lin,
+                                  double *resid_hist, int32_t *n_steps, void *stream)
+{
+    g_msg[0] = 0;
+    if (!mesh || !pattern || !coeffs || !x || !lin) return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: NULL argument");
+    if (pattern->form != MF_FORM_NS || pattern->mesh != mesh)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: the pattern was not built for MF_FORM_NS on this mesh");
+    if ((coeffs->bc_mask == nullptr) != (coeffs->bc_val == nullptr))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: bc_mask and bc_val go together");
+    if (max_newton < 0 || !(newton_tol >= 0.0))
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: negative step count or tolerance");
+    if (lin->solver != MF_SOLVER_GMRES && lin->solver != MF_SOLVER_PCG)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: the linear solver is GMRES (or PCG)");
+    return mf_ns_newton_impl(mesh, pattern, coeffs, x, newton_tol, max_newton, lin, resid_hist, n_steps,
+                             static_cast<cudaStream_t>(stream));
 }
 
 extern "C" mf_status mf_facets_create(const mf_mesh *mesh, const mf_pattern *pattern, int64_t n_facets,

@@ -41,7 +41,7 @@ struct mf_pattern {
     int32_t *col_idx = nullptr;
     // adjacencies: [0] row space x row space; flow adds [1] P2 rows x P1
     // cols and [2] P1 rows x P2 cols
-    mf_adj adj[3];
+    mf_adj adj[4];
     int n_adj = 0;
     // element-matrix scratch of the FP64 path (doubles per element x n_elems)
     double *scratch = nullptr;
@@ -60,6 +60,9 @@ struct mf_pattern {
     // (inc_slot, 6 per entry), P2 row x its P1 nodes (inc_slot_pq, 3), P1 row
     // x its P2 nodes (pinc_slot, 6)
     uint8_t *inc_slot_pq = nullptr, *pinc_slot = nullptr;
+    // Navier-Stokes: P1 row x the element's P1 nodes (pinc_slot_pp, 3 per
+    // entry) in adj[3] (P1 rows x P1 columns)
+    uint8_t *pinc_slot_pp = nullptr;
     // elasticity: slot[e][a][b] = position of node conn[e][b] among the sorted
     // neighbours of node conn[e][a] (u8, n_elems x 64)
     uint8_t *slot = nullptr;
@@ -171,6 +174,12 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
                            double *values, double *d, cudaStream_t st);
 mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c,
                             double *values, double *d, cudaStream_t st);
+// Navier-Stokes with SUPG (mf_ns.cu): tangent and d = -r at the state c->advect
+mf_status mf_assemble_ns(const mf_mesh *m, const mf_pattern *p, const mf_coeffs *c, double *values, double *d,
+                         cudaStream_t st);
+mf_status mf_ns_newton_impl(const mf_mesh *m, const mf_pattern *p, const mf_coeffs *coeffs, double *x,
+                            double newton_tol, int32_t max_newton, const mf_solver_opts *lin, double *hist,
+                            int32_t *n_steps, cudaStream_t st);
 mf_status mf_flow_precond_impl(const mf_mesh *m, const mf_pattern *p, const mf_csr *K, const uint8_t *mask,
                                double p_scale, double *out, cudaStream_t st);
 // elasticity gather: FP64 sums of element blocks, or (fixed_point) exact int64

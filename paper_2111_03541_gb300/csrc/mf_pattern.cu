@@ -461,6 +461,46 @@ __global__ void k_csr_oseen_fill(int64_t n2, int64_t n1, const int64_t *__restri
     }
 }
 
+// Navier-Stokes rows: a velocity row of P2 node n has [u1: adj0 | u2: n2 +
+// adj0 | p: 2 n2 + adj1], a pressure row of P1 node m [u1: adj2 | u2: n2 +
+// adj2 | p: 2 n2 + adj3] (ascending, the diagonal present in both)
+__global__ void k_csr_ns_len(int64_t n2, int64_t n1, const int64_t *__restrict__ pp, const int64_t *__restrict__ pq,
+                             const int64_t *__restrict__ qp, const int64_t *__restrict__ qq, int64_t *len)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 2 * n2 + n1) return;
+    if (r < 2 * n2) {
+        const int64_t n = r % n2;
+        len[r] = 2 * (pp[n + 1] - pp[n]) + (pq[n + 1] - pq[n]);
+    } else {
+        const int64_t n = r - 2 * n2;
+        len[r] = 2 * (qp[n + 1] - qp[n]) + (qq[n + 1] - qq[n]);
+    }
+}
+
+__global__ void k_csr_ns_fill(int64_t n2, int64_t n1, const int64_t *__restrict__ pp, const int32_t *__restrict__ ppc,
+                              const int64_t *__restrict__ pq, const int32_t *__restrict__ pqc,
+                              const int64_t *__restrict__ qp, const int32_t *__restrict__ qpc,
+                              const int64_t *__restrict__ qq, const int32_t *__restrict__ qqc,
+                              const int64_t *__restrict__ row_ptr, int32_t *col_idx)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 2 * n2 + n1) return;
+    int32_t *out = col_idx + row_ptr[r];
+    int64_t o = 0;
+    if (r < 2 * n2) {
+        const int64_t n = r % n2;
+        for (int i = 0; i < 2; ++i)
+            for (int64_t t = pp[n]; t < pp[n + 1]; ++t) out[o++] = (int32_t)(i * n2 + ppc[t]);
+        for (int64_t t = pq[n]; t < pq[n + 1]; ++t) out[o++] = (int32_t)(2 * n2 + pqc[t]);
+    } else {
+        const int64_t n = r - 2 * n2;
+        for (int i = 0; i < 2; ++i)
+            for (int64_t t = qp[n]; t < qp[n + 1]; ++t) out[o++] = (int32_t)(i * n2 + qpc[t]);
+        for (int64_t t = qq[n]; t < qq[n + 1]; ++t) out[o++] = (int32_t)(2 * n2 + qqc[t]);
+    }
+}
+
 struct Incidence {
     int64_t *ptr = nullptr;
     int32_t *inc = nullptr;
@@ -644,7 +684,7 @@ void mf_pattern_free(mf_pattern *p)
     cudaFree(p->col_idx);
     cudaFree(p->q2s_map);
     p->q2s_map = nullptr;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         cudaFree(p->adj[i].ptr);
         cudaFree(p->adj[i].col);
         p->adj[i] = mf_adj();
@@ -672,6 +712,8 @@ void mf_pattern_free(mf_pattern *p)
     p->inc_slot = nullptr;
     cudaFree(p->inc_slot_pq);
     cudaFree(p->pinc_slot);
+    cudaFree(p->pinc_slot_pp);
+    p->pinc_slot_pp = nullptr;
     cudaFree(p->pinc_loc);
     p->inc_slot_pq = p->pinc_slot = p->pinc_loc = nullptr;
     cudaFree(p->elem_inc);
@@ -841,10 +883,13 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
             s = build_adj(m->n_nodes, incv, m->conn, 3, m->pconn, st, &p->adj[1], status);
         if (s == MF_OK)
             s = build_adj(m->n_pnodes, incp, m->pconn, 6, m->conn, st, &p->adj[2], status);
+        const bool ns = form == MF_FORM_NS;
+        if (s == MF_OK && ns)  // P1 rows x P1 columns: the SUPG pressure block
+            s = build_adj(m->n_pnodes, incp, m->pconn, 3, m->pconn, st, &p->adj[3], status);
         p->pinc_ptr = incp.ptr;
         p->pinc = incp.inc;
         p->pinc_loc = incp.loc;
-        p->n_adj = 3;
+        p->n_adj = ns ? 4 : 3;
         if (s == MF_OK) {
             // slots: P2 rows x P2 columns, P2 rows x P1 columns, P1 rows x P2 columns
             MF_CUDA(cudaMallocAsync(&p->inc_slot, (size_t)36 * m->n_elems, st));
@@ -856,22 +901,37 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
                                                          p->adj[1].col, p->inc_slot_pq);
             k_inc_slot<<<nblk(m->n_pnodes), TPB, 0, st>>>(m->n_pnodes, 6, m->conn, incp.ptr, incp.inc,
                                                           p->adj[2].ptr, p->adj[2].col, p->pinc_slot);
+            if (ns) {
+                MF_CUDA(cudaMallocAsync(&p->pinc_slot_pp, (size_t)9 * m->n_elems, st));
+                k_inc_slot<<<nblk(m->n_pnodes), TPB, 0, st>>>(m->n_pnodes, 3, m->pconn, incp.ptr, incp.inc,
+                                                              p->adj[3].ptr, p->adj[3].col, p->pinc_slot_pp);
+            }
         }
         if (s != MF_OK) { free_inc(incv, st); return s; }
         const int64_t n2 = m->n_nodes, n1 = m->n_pnodes;
         p->n_rows = 2 * n2 + n1;
         MF_CUDA(cudaMallocAsync(&p->row_ptr, sizeof(int64_t) * (p->n_rows + 1), st));
         MF_CUDA(cudaMemsetAsync(p->row_ptr, 0, sizeof(int64_t) * (p->n_rows + 1), st));
-        k_csr_oseen_len<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[1].ptr, p->adj[2].ptr,
-                                                        p->row_ptr);
+        if (ns)
+            k_csr_ns_len<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[1].ptr, p->adj[2].ptr,
+                                                         p->adj[3].ptr, p->row_ptr);
+        else
+            k_csr_oseen_len<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[1].ptr, p->adj[2].ptr,
+                                                            p->row_ptr);
         MF_CUDA(mf_scan_i64(p->row_ptr, p->n_rows + 1, nullptr, st));
         s = read_i64(p->row_ptr + p->n_rows, &p->nnz, st);
         if (s != MF_OK) { free_inc(incv, st); return s; }
         MF_CUDA(cudaMallocAsync(&p->col_idx, sizeof(int32_t) * p->nnz, st));
-        k_csr_oseen_fill<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[0].col, p->adj[1].ptr,
-                                                         p->adj[1].col, p->adj[2].ptr, p->adj[2].col, p->row_ptr,
-                                                         p->col_idx);
-        p->scratch_stride = 72;
+        if (ns)
+            k_csr_ns_fill<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[0].col, p->adj[1].ptr,
+                                                          p->adj[1].col, p->adj[2].ptr, p->adj[2].col, p->adj[3].ptr,
+                                                          p->adj[3].col, p->row_ptr, p->col_idx);
+        else
+            k_csr_oseen_fill<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[0].col, p->adj[1].ptr,
+                                                             p->adj[1].col, p->adj[2].ptr, p->adj[2].col, p->row_ptr,
+                                                             p->col_idx);
+        // Navier-Stokes: residual (15) and tangent (15 x 15) per element
+        p->scratch_stride = ns ? 240 : 72;
         s = mf_flow_consts_upload();
         if (s != MF_OK) { free_inc(incv, st); return s; }
     }
