@@ -697,6 +697,50 @@ def _solve_timed(P, **kw):
                "s": time.perf_counter() - t}
 
 
+def _ns_case(mf, gen, dev):
+    import numpy as np
+    import torch
+    res = {}
+    prob = dict(gen.oseen_problem(512), form="ns", tau_m=0.01, tau_c=0.01)
+    P = mf.Problem(prob, device=dev)
+    ms = _ev_time(lambda: P.assemble(), reps=5)
+    mf.mf_kernel_times()  # clear
+    mf.mf_set_kernel_timing(True)
+    P.assemble()
+    mf.mf_set_kernel_timing(False)
+    kt = {k: round(t / c, 4) for k, (c, t) in mf.mf_kernel_times().items()}
+    res["assembly_512"] = {"elements": int(prob["conn"].shape[0]), "n_dofs": int(P.n), "nnz": int(P.nnz),
+                           "assemble_ms": ms, "elements_per_s": prob["conn"].shape[0] / (ms * 1e-3),
+                           "kernel_ms": kt}
+    del P
+    n, mu = 64, 0.02
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    levels, m = [], n
+    while m >= 4:
+        pr = gen.oseen_problem(m, viscosity=mu, rho=1.0)
+        pr["advect"] = np.zeros_like(pr["advect"])  # Stokes systems for the hierarchy
+        Q = mf.Problem(pr, device=dev)
+        Q.assemble()
+        levels.append(Q)
+        m //= 2
+    mg = mf.mf_flow_mg_create([Q.csr for Q in levels], [Q.prob["n"] for Q in levels], [Q.bc_mask for Q in levels],
+                              levels[0].pressure_mass_diag(), mu)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t
+    P = mf.Problem(dict(gen.oseen_problem(n, viscosity=mu, rho=1.0), form="ns", tau_m=0.01, tau_c=0.01), device=dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    st, hist, steps = P.newton(tol=1e-10, max_newton=20, lin_tol=1e-6, max_iter=20000, flow_mg=mg, check_every=5)
+    torch.cuda.synchronize()
+    res["newton_cavity_64"] = {"n_dofs": int(P.n), "converged": st == mf.MF_OK, "newton_steps": steps,
+                               "residual_history": hist, "s": time.perf_counter() - t, "hierarchy_setup_s": setup_s,
+                               "linear_solver": "GMRES(50) to 1e-6, block-triangular preconditioner over the "
+                                                "Stokes systems of 64^2 .. 4^2"}
+    mf.mf_flow_mg_destroy(mg)
+    return res
+
+
 def suite(dev):
     import numpy as np
     import torch
@@ -739,6 +783,13 @@ def suite(dev):
                                 "hierarchy_setup_s": setup_s,
                                 "hierarchy": "8 grids 512^2 .. 4^2, coarse systems assembled by the library"}
     del P, coarse
+    torch.cuda.empty_cache()
+    # N1: Navier-Stokes with SUPG (Sec. 4.3): the Newton tangent and residual
+    # assembled on the C2 grid (state zero: the cost does not depend on it),
+    # and Newton on the 64^2 lid-driven cavity (mu = 0.02, Re 50) from the
+    # Dirichlet values, GMRES(50) right-preconditioned by the flow hierarchy
+    # built from the grids' Stokes systems
+    out["N1_navier_stokes_supg"] = _ns_case(mf, gen, dev)
     torch.cuda.empty_cache()
     # C3: 512 thermal problems, one launch per problem vs the batched graph
     specs = gen.batch_specs()

@@ -401,7 +401,10 @@ mf_status mf_solve(const mf_csr *K, const double *d, double *x, const mf_solver_
 /* Newton-Raphson (Sec. 2.1) on the Navier-Stokes form with SUPG: x (device
  * [2 n_nodes + n_pnodes], the state; entries of Dirichlet dofs are set to
  * bc_val first) is updated by steps K dx = -r (mf_assemble with MF_FORM_NS,
- * then mf_solve with *lin, e.g. GMRES) until the residual on the free dofs
+ * then mf_solve with *lin: GMRES, or GMRES with a flow hierarchy of
+ * mf_flow_mg_create, e.g. built from the Stokes systems of the grids, whose
+ * block-triangular preconditioner takes the tangent's own velocity-pressure
+ * coupling) until the residual on the free dofs
  * satisfies ||r_free|| <= newton_tol max(1, ||r_free(x0)||), at most
  * max_newton steps.  coeffs->advect is ignored (x is the state).  resid_hist
  * (host, max_newton + 1 entries, may be NULL) receives ||r_free|| before each

@@ -549,10 +549,15 @@ class Problem:
             mf_assemble_boundary(self.facets, self.facet_coeffs, self.csr, self.d, stream)
         return self.values, self.d
 
-    def newton(self, tol=1e-11, max_newton=30, lin_tol=1e-13, restart=50, max_iter=200000, stream=None):
+    def newton(self, tol=1e-11, max_newton=30, lin_tol=1e-13, restart=50, max_iter=200000, flow_mg=None,
+               check_every=10, stream=None):
         """Navier-Stokes form: Newton from the current state ``self.advect``
-        (updated in place); returns (status, residual history, steps)."""
-        lin = SolverOpts(solver=MF_SOLVER_GMRES, restart=restart, tol=lin_tol, max_iter=max_iter, check_every=10)
+        (updated in place); the linear solves are GMRES, with the flow
+        hierarchy ``flow_mg`` as preconditioner when given; returns (status,
+        residual history, steps)."""
+        lin = SolverOpts(solver=MF_SOLVER_GMRES if flow_mg is None else MF_SOLVER_GMRES_FLOW_MG, restart=restart,
+                         tol=lin_tol, max_iter=max_iter, check_every=check_every,
+                         flow_mg=flow_mg.value if flow_mg is not None else None)
         return mf_ns_newton(self.mesh, self.pattern, self.coeffs, self.advect, tol, max_newton, lin, stream)
 
     def pressure_mass_diag(self, stream=None):

@@ -409,8 +409,10 @@ extern "C" mf_status mf_ns_newton(const mf_mesh *mesh, const mf_pattern *pattern
         return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: bc_mask and bc_val go together");
     if (max_newton < 0 || !(newton_tol >= 0.0))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: negative step count or tolerance");
-    if (lin->solver != MF_SOLVER_GMRES && lin->solver != MF_SOLVER_PCG)
-        return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: the linear solver is GMRES (or PCG)");
+    if (lin->solver != MF_SOLVER_GMRES && lin->solver != MF_SOLVER_GMRES_FLOW_MG)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: the linear solver is GMRES or GMRES with the flow hierarchy");
+    if (lin->solver == MF_SOLVER_GMRES_FLOW_MG && !lin->flow_mg)
+        return mf_fail(MF_ERR_INVALID_ARG, "mf_ns_newton: MF_SOLVER_GMRES_FLOW_MG needs lin->flow_mg");
     return mf_ns_newton_impl(mesh, pattern, coeffs, x, newton_tol, max_newton, lin, resid_hist, n_steps,
                              static_cast<cudaStream_t>(stream));
 }
