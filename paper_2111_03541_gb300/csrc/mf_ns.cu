@@ -34,12 +34,16 @@ __device__ __forceinline__ double gl4_w(int i)
     return (i == 0 || i == 3) ? 0.17392742256872679 : 0.3260725774312732;
 }
 
-constexpr int NS_EPB = 8;            // elements per block, 16 threads each
-constexpr int NS_PT = 38;            // doubles of per-point data
+constexpr int NS_EPB = 4;            // elements per block, 16 threads each
+constexpr int NS_PT = 62;            // doubles of per-point data
 constexpr int NS_EL = 240;           // scratch words per element: r (15), K (15 x 15)
 
-// per point: wd, N[6], g[6][2], l[3], u[2], du[2][2], Rm[2], Rc, p, adv[6]
-enum { P_WD = 0, P_N = 1, P_G = 7, P_L = 19, P_U = 22, P_DU = 24, P_RM = 28, P_RC = 30, P_P = 31, P_ADV = 32 };
+// per point: wd, N[6], g[6][2], l[3], u[2], du[2][2], Rm[2], Rc, p, adv[6],
+// dRm[i][j][b] = dRm_i / dU_bj (24)
+enum {
+    P_WD = 0, P_N = 1, P_G = 7, P_L = 19, P_U = 22, P_DU = 24, P_RM = 28, P_RC = 30, P_P = 31, P_ADV = 32,
+    P_DRM = 38
+};
 
 __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n2, const double *__restrict__ X,
                                                          const int32_t *__restrict__ conn,
@@ -63,7 +67,8 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
     const double J01 = X[2 * (int64_t)cn[2]] - x0, J11 = X[2 * (int64_t)cn[2] + 1] - y0;
     const double det = J00 * J11 - J01 * J10;
     if (valid && q == 0 && !(det > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
-    const double gl[3][2] = {{(J10 - J11) / det, (J01 - J00) / det}, {J11 / det, -J01 / det}, {-J10 / det, J00 / det}};
+    const double idet = 1.0 / det;
+    const double gl[3][2] = {{(J10 - J11) * idet, (J01 - J00) * idet}, {J11 * idet, -J01 * idet}, {-J10 * idet, J00 * idet}};
     constexpr int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
     double lap[6];
 #pragma unroll
@@ -147,6 +152,17 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
         }
         o[P_RC] = du[0][0] + du[1][1];
         o[P_P] = ph;
+        // dRm_i / dU_bj = rho (N_b d_j u_i + delta_ij u . g_b) - mu delta_ij lap N_b
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int b = 0; b < 6; ++b) {
+                    const double adv_b = g[b][0] * u[0] + g[b][1] * u[1];
+                    o[P_DRM + 12 * i + 6 * j + b] =
+                        i == j ? rho * (N[b] * du[i][j] + adv_b) - mu * lap[b] : rho * N[b] * du[i][j];
+                }
     }
     __syncthreads();
     // phase 2: thread r < 15 forms row r of the residual and the tangent
@@ -166,52 +182,46 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
             const double adv = o[P_ADV + a], ui = o[P_U + i], rmi = o[P_RM + i], rc = o[P_RC];
             res += wd * (-rho * adv * ui - gai * o[P_P] + mu * (ga0 * o[P_DU + 2 * i] + ga1 * o[P_DU + 2 * i + 1]) +
                          tm * rho * adv * rmi + tc * gai * rc);
+            // K[(a,i),(b,j)] = sum_q wd [ g_a,j N_b (-rho u_i + tm rho Rm_i) + tm rho adv_a dRm_ij(b)
+            //                            + tc g_a,i g_b,j + delta_ij (-rho adv_a N_b + mu g_a . g_b) ]
+            const double A = wd * rho * (tm * rmi - ui);
+            const double c0 = ga0 * A, c1 = ga1 * A;
+            const double T4 = wd * tm * rho * adv, T5 = wd * tc * gai, B = -wd * rho * adv, Mu = wd * mu;
+            const double *dR = o + P_DRM + 12 * i;
 #pragma unroll
             for (int b = 0; b < 6; ++b) {
                 const double Nb = o[P_N + b], gb0 = o[P_G + 2 * b], gb1 = o[P_G + 2 * b + 1];
-                const double dot = ga0 * gb0 + ga1 * gb1;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const double gaj = j ? ga1 : ga0, gbj = j ? gb1 : gb0;
-                    const double dij = (i == j) ? 1.0 : 0.0;
-                    const double dRm = rho * (Nb * o[P_DU + 2 * i + j] + dij * o[P_ADV + b]) - mu * dij * cs[6 + b];
-                    K[2 * b + j] += wd * (-rho * (gaj * Nb * ui + adv * dij * Nb) + mu * dij * dot +
-                                          tm * rho * (gaj * Nb * rmi + adv * dRm) + tc * gai * gbj);
-                }
+                const double diag = B * Nb + Mu * (ga0 * gb0 + ga1 * gb1);
+                K[2 * b] += c0 * Nb + T4 * dR[b] + T5 * gb0 + (i == 0 ? diag : 0.0);
+                K[2 * b + 1] += c1 * Nb + T4 * dR[6 + b] + T5 * gb1 + (i == 1 ? diag : 0.0);
             }
+            const double T6 = wd * gai;
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                K[12 + c] += wd * (-gai * o[P_L + c] + tm * rho * adv * cs[2 * c + i]);
+            for (int c = 0; c < 3; ++c) K[12 + c] += T4 * cs[2 * c + i] - T6 * o[P_L + c];
         }
     } else {
         const int bp = r - 12;
         const double gp0 = cs[2 * bp], gp1 = cs[2 * bp + 1];
+        double area = 0.0;
 #pragma unroll 1
         for (int p = 0; p < 16; ++p) {
             const double *o = pts[le][p];
             const double wd = o[P_WD];
             const double lb = o[P_L + bp];
+            area += wd;
             res += wd * (lb * o[P_RC] + tm * (gp0 * o[P_RM] + gp1 * o[P_RM + 1]));
+            // K[b',(b,j)] = sum_q wd [ l_b' g_b,j + tm sum_i grad l_b',i dRm_ij(b) ]
+            const double L = wd * lb, G0 = wd * tm * gp0, G1 = wd * tm * gp1;
+            const double *dR = o + P_DRM;
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                const double Nb = o[P_N + b];
+            for (int b = 0; b < 6; ++b)
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const double gbj = o[P_G + 2 * b + j];
-                    // sum_i grad l_b',i dRm_i / dU_bj
-                    double s = 0.0;
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const double dij = (i == j) ? 1.0 : 0.0;
-                        const double dRm = rho * (Nb * o[P_DU + 2 * i + j] + dij * o[P_ADV + b]) - mu * dij * cs[6 + b];
-                        s += (i ? gp1 : gp0) * dRm;
-                    }
-                    K[2 * b + j] += wd * (lb * gbj + tm * s);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) K[12 + c] += wd * tm * (gp0 * cs[2 * c] + gp1 * cs[2 * c + 1]);
+                for (int j = 0; j < 2; ++j)
+                    K[2 * b + j] += L * o[P_G + 2 * b + j] + G0 * dR[6 * j + b] + G1 * dR[12 + 6 * j + b];
         }
+        // the pressure-pressure block: tm grad l_b' . grad l_c over the element
+#pragma unroll
+        for (int c = 0; c < 3; ++c) K[12 + c] = area * tm * (gp0 * cs[2 * c] + gp1 * cs[2 * c + 1]);
     }
     double *w = out + e * NS_EL;
     w[r] = res;
