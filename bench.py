@@ -603,7 +603,8 @@ def _boundary_case(mf, P, prob, fac, sides, bc_mask, bc_val, hbm_gbs):
         on |= (x[:, ax] >= 1.0 - 1e-14) if sd[1] == "1" else (x[:, ax] <= 1e-14)
     nb = int(on.sum())
     nf = int(fac["elem"].shape[0])
-    npf, dim = (4, 3) if prob["elem"] == "Q1" else ((2 if prob["elem"] == "P1" else 3), 2)
+    npf, dim = (4, 3) if prob["elem"] == "Q1" else ((8, 3) if prob["elem"] == "Q2S" else
+                                                    ((2 if prob["elem"] == "P1" else 3), 2))
     n_inc = nf * npf
     per_node = 4 + 8 + 8 + (17 if thermal else 51) + 8 * dim
     per_entry = 4 + 1 + (npf if thermal else 0)
@@ -895,6 +896,10 @@ def suite(dev):
                                 "arithmetic": "map coefficients, load and row sums' conversion FP64; geometry, "
                                               "gradients, the nine Gram sums per pair, the block finishing and the "
                                               "row sums in double-float (FP32 pairs, about 47 bits)"}
+    # the cantilever loads (Sec. 4.2) on the bricks' 8-node faces: a random
+    # stress on the five sides away from the clamp
+    out["B3_traction_q2s_48"] = _boundary_case(mf, P, prob, gen.traction_facets(prob, sides), sides, P.bc_mask,
+                                              P.bc_val, hbm)
     del P
     torch.cuda.empty_cache()
     # quadratic tetrahedra (Kuhn's split of a jittered 48^3 grid), thermal: assembly, then Jacobi-PCG

@@ -236,11 +236,17 @@ mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *patte
  *    the three vertices in outward order (1,2,3), (0,3,2), (0,1,3), (0,2,1)
  *    for i = 0..3, then the midpoints of its edges (0,1), (1,2), (2,0) in
  *    face order; the face is flat.  Thermal (convection) only.
+ *  - 20-node brick (Q2S) face 2d + s: its 4 vertices as on the Q1 brick (face
+ *    node i + 2j, i and j the bits of the face axes d1 < d2), then the edge
+ *    midpoints in the 8-node quadrilateral's order: the d1 edges at bit
+ *    d2 = j (4 + j), the d2 edges at bit d1 = i (6 + i); the 8-node
+ *    serendipity basis on the vertices' bilinear map (straight edges).
+ *    Convection and the loaded boundary (the cantilever loads of Sec. 4.2).
  * Quadrature: Gauss-Legendre with 2 (P1) or 3 (P2) points per edge, exact for
- * the edge mass matrix; 2 x 2 Gauss on a hexahedron face; on a tetrahedron
- * face the exact P2 triangle mass matrix and load.  Serendipity bricks have
- * no facet terms (MF_ERR_UNSUPPORTED); radiation (mf_genalpha_run) is not
- * provided on tetrahedron faces (MF_ERR_UNSUPPORTED). */
+ * the edge mass matrix; 2 x 2 Gauss on a Q1 face, 3 x 3 on an 8-node face; on
+ * a tetrahedron face the exact P2 triangle mass matrix and load.  Radiation
+ * (mf_genalpha_run) is not provided on tetrahedron and 8-node brick faces
+ * (MF_ERR_UNSUPPORTED). */
 typedef struct mf_facets mf_facets;
 
 /* Wraps n_facets facets (elem [n_facets] int32 parent elements, face

@@ -427,8 +427,6 @@ extern "C" mf_status mf_facets_create(const mf_mesh *mesh, const mf_pattern *pat
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: the pattern was built on another mesh");
     if (pattern->form != MF_FORM_THERMAL && pattern->form != MF_FORM_ELASTIC)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: boundary terms exist for the thermal and elasticity forms");
-    if (mesh->elem == MF_Q2S_HEX)
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: no facet terms on serendipity bricks");
     if (n_facets < 0 || (n_facets > 0 && (!elem || !face)))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_facets_create: negative count or NULL facet arrays");
     if (n_facets >= (int64_t(1) << 28))

@@ -44,7 +44,7 @@ inline unsigned nblk(int64_t n, int t = TPB) { return (unsigned)((n + t - 1) / t
 
 // Local element nodes of facet `face`; returns the node count or 0 for a face
 // the element does not have.
-__device__ __forceinline__ int facet_local(int elem, int face, int (&loc)[6])
+__device__ __forceinline__ int facet_local(int elem, int face, int (&loc)[8])
 {
     if (elem == MF_P2_TET) {
         // face i opposite vertex i, vertices ordered outward, then the
@@ -62,13 +62,28 @@ __device__ __forceinline__ int facet_local(int elem, int face, int (&loc)[6])
         for (int m = 0; m < 3; ++m) loc[m] = el[face][m];
         return 3;
     }
-    if (elem == MF_Q1_HEX) {
+    if (elem == MF_Q1_HEX || elem == MF_Q2S_HEX) {
         if (face < 0 || face > 5) return 0;
         const int d = face >> 1, s = face & 1;
         int m = 0;
         for (int a = 0; a < 8; ++a)
             if (((a >> d) & 1) == s) loc[m++] = a;
-        return 4;
+        if (elem == MF_Q1_HEX) return 4;
+        // 20-node brick: the vertices as above (face node i + 2j, i and j the
+        // bits of the face axes d1 < d2), then the edge midpoints in the
+        // 8-node quadrilateral's order: the d1 edges at bit d2 = j (4 + j) and
+        // the d2 edges at bit d1 = i (6 + i); the brick's edge along axis A at
+        // bits b, c of its other two axes B < C is node 8 + 4 A + b + 2 c
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        for (int k = 0; k < 4; ++k) {
+            const int A = k < 2 ? d1 : d2, other = k < 2 ? d2 : d1;
+            int bits[3] = {0, 0, 0};
+            bits[d] = s;
+            bits[other] = k & 1;
+            const int B = A == 0 ? 1 : 0, C = A == 2 ? 1 : 2;
+            loc[4 + k] = 8 + 4 * A + bits[B] + 2 * bits[C];
+        }
+        return 8;
     }
     if (face < 0 || face > 2) return 0;
     loc[0] = face;
@@ -88,7 +103,7 @@ __global__ void k_facet_nodes(int elem, int npe, int npf, int64_t n_el, const in
     if (f >= n_facets) return;
     const int64_t e = f_elem[f];
     const int face = f_face[f];
-    int loc[6];
+    int loc[8];
     if (e < 0 || e >= n_el || facet_local(elem, face, loc) != npf) {
         mf_dev_fail(status, MF_ERR_BAD_MESH);
         for (int m = 0; m < npf; ++m) fnode[f * npf + m] = -1;
@@ -218,10 +233,63 @@ __device__ __forceinline__ void face_coefs(const double *__restrict__ X, const i
 // Row m of the facet's convection matrix for unit h (row[m']) and the facet
 // load factor for unit h T_env (returned).
 template <int ELEM>
-constexpr int facet_npf() { return ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : (ELEM == MF_Q1_HEX ? 4 : 6)); }
+constexpr int facet_npf()
+{
+    return ELEM == MF_P1_TRI ? 2 : (ELEM == MF_P2_TRI ? 3 : (ELEM == MF_Q1_HEX ? 4 : (ELEM == MF_Q2S_HEX ? 8 : 6)));
+}
+
+// 8-node serendipity face basis on [-1, 1]^2: vertex m = i + 2 j at
+// (2i - 1, 2j - 1): (1 + su u)(1 + sv v)(su u + sv v - 1) / 4; the
+// midpoint 4 + j of the edge v = 2j - 1: (1 - u^2)(1 + sv v) / 2; the
+// midpoint 6 + i of the edge u = 2i - 1: (1 + su u)(1 - v^2) / 2
+__device__ __forceinline__ double quad8_shape(int m, double u, double v)
+{
+    if (m < 4) {
+        const double su = (m & 1) ? 1.0 : -1.0, sv = (m & 2) ? 1.0 : -1.0;
+        return 0.25 * (1.0 + su * u) * (1.0 + sv * v) * (su * u + sv * v - 1.0);
+    }
+    if (m < 6) return 0.5 * (1.0 - u * u) * (1.0 + (m == 5 ? v : -v));
+    return 0.5 * (1.0 + (m == 7 ? u : -u)) * (1.0 - v * v);
+}
+
+// 3 x 3 Gauss on [-1, 1]: points -sqrt(3/5), 0, sqrt(3/5), weights 5/9, 8/9, 5/9
+__device__ __forceinline__ double g3_x(int i) { return i == 0 ? -0.77459666924148337704 : (i == 1 ? 0.0 : 0.77459666924148337704); }
+__device__ __forceinline__ double g3_w(int i) { return i == 1 ? 8.0 / 9.0 : 5.0 / 9.0; }
+
+// An 8-node brick face (straight edges: the vertices' bilinear map, area
+// vector A(u, v) = P + Qu u + Qv v) on the 3 x 3 rule: the unit-h
+// convection row m (row[k] = int N_m N_k |A|, returned: int N_m |A|), or
+// the area moment int N_m A (mom).
+__device__ __forceinline__ double q2s_face_row(const double *__restrict__ X, const int32_t *fn, int m,
+                                               double (&row)[8], double (&mom)[3])
+{
+    double c1[3], c2[3], c3[3], P[3], Qu[3], Qv[3];
+    face_coefs(X, fn, c1, c2, c3);
+    cross3(c1, c2, P);
+    cross3(c1, c3, Qu);
+    cross3(c3, c2, Qv);
+    for (int k = 0; k < 8; ++k) row[k] = 0.0;
+    mom[0] = mom[1] = mom[2] = 0.0;
+    double load = 0.0;
+    for (int qi = 0; qi < 3; ++qi)
+        for (int qj = 0; qj < 3; ++qj) {
+            const double u = g3_x(qi), v = g3_x(qj), w = g3_w(qi) * g3_w(qj);
+            const double a0 = P[0] + Qu[0] * u + Qv[0] * v;
+            const double a1 = P[1] + Qu[1] * u + Qv[1] * v;
+            const double a2 = P[2] + Qu[2] * u + Qv[2] * v;
+            const double nm = w * quad8_shape(m, u, v);
+            mom[0] += nm * a0;
+            mom[1] += nm * a1;
+            mom[2] += nm * a2;
+            const double jn = nm * sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+            load += jn;
+            for (int k = 0; k < 8; ++k) row[k] += jn * quad8_shape(k, u, v);
+        }
+    return load;
+}
 
 template <int ELEM>
-__device__ __forceinline__ double conv_row(const double *__restrict__ X, const int32_t *fn, int m, double (&row)[6])
+__device__ __forceinline__ double conv_row(const double *__restrict__ X, const int32_t *fn, int m, double (&row)[8])
 {
     if (ELEM == MF_P2_TET) {
         // flat 6-node face of area A: int N_m N_k = A / 180 [6 -1 -1 0 -4 0; ...]
@@ -362,6 +430,22 @@ __global__ void k_facet_geometry(int64_t n_entries, const int32_t *__restrict__ 
     const int32_t f = binc[t];
     const int m = bloc[t];
     const int32_t *fn = fnode + (int64_t)f * NPF;
+    if (ELEM == MF_Q2S_HEX) {
+        double row[8], mom[3];
+        const double lf = q2s_face_row(X, fn, m, row, mom);
+        if (traction) {
+            const int face = fface[f];
+            const double o = ((face & 1) ? 1.0 : -1.0) * ((face >> 1) == 1 ? -1.0 : 1.0);
+            for (int i = 0; i < 3; ++i) bgeo[3 * t + i] = o * mom[i];
+        } else {
+            for (int k = 0; k < 8; ++k) {
+                bgeo[t * 9 + k] = row[k];
+                bcol[t * 8 + k] = fn[k];
+            }
+            bgeo[t * 9 + 8] = lf;
+        }
+        return;  // no radiation terms on the 8-node faces
+    }
     if (ELEM == MF_Q1_HEX && traction) {
         double c1[3], c2[3], c3[3], P[3], Qu[3], Qv[3];
         face_coefs(X, fn, c1, c2, c3);
@@ -375,7 +459,7 @@ __global__ void k_facet_geometry(int64_t n_entries, const int32_t *__restrict__ 
         for (int i = 0; i < 3; ++i) bgeo[3 * t + i] = o * (P[i] + Qu[i] * su + Qv[i] * sv);
         return;
     }
-    double row[6];
+    double row[8];
     const double lf = conv_row<ELEM>(X, fn, m, row);
     for (int k = 0; k < NPF; ++k) {
         bgeo[t * (NPF + 1) + k] = row[k];
@@ -572,8 +656,8 @@ mf_status mf_radiation_load(const mf_facets *f, const double *es, const double *
                             const uint8_t *mask, double *R, cudaStream_t st)
 {
     if (!f || f->n_bnodes == 0) return MF_OK;
-    if (f->mesh->elem == MF_P2_TET)
-        return mf_fail(MF_ERR_UNSUPPORTED, "radiation: not provided on tetrahedron faces");
+    if (f->mesh->elem == MF_P2_TET || f->mesh->elem == MF_Q2S_HEX)
+        return mf_fail(MF_ERR_UNSUPPORTED, "radiation: not provided on tetrahedron and 8-node brick faces");
     int *status = mf_status_word();
     if (!status) return mf_fail(MF_ERR_CUDA, "radiation: status word unavailable");
     const unsigned g = nblk(f->n_bnodes, BND_T);
@@ -589,8 +673,8 @@ mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const doubl
                                double scale, double *values, cudaStream_t st)
 {
     if (!f || f->n_bnodes == 0) return MF_OK;
-    if (f->mesh->elem == MF_P2_TET)
-        return mf_fail(MF_ERR_UNSUPPORTED, "radiation: not provided on tetrahedron faces");
+    if (f->mesh->elem == MF_P2_TET || f->mesh->elem == MF_Q2S_HEX)
+        return mf_fail(MF_ERR_UNSUPPORTED, "radiation: not provided on tetrahedron and 8-node brick faces");
     const unsigned g = nblk(f->n_bnodes, BND_T);
 #define RT_ARGS f->n_bnodes, f->bnode, f->brow, f->bptr, f->binc, f->bslot, f->bcol, f->bwq, f->fnode, es, T, mask, \
                 scale, values
@@ -605,11 +689,13 @@ mf_status mf_radiation_tangent(const mf_facets *f, const double *es, const doubl
 mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n_facets, const int32_t *elem,
                                 const uint8_t *face, cudaStream_t st, mf_facets *f)
 {
-    f->npf = m->elem == MF_P1_TRI ? 2 : ((m->elem == MF_P2_TRI || m->elem == MF_Q2S_QUAD) ? 3 : (m->elem == MF_Q1_HEX ? 4 : 6));
+    f->npf = m->elem == MF_P1_TRI ? 2
+           : ((m->elem == MF_P2_TRI || m->elem == MF_Q2S_QUAD) ? 3
+           : (m->elem == MF_Q1_HEX ? 4 : (m->elem == MF_Q2S_HEX ? 8 : 6)));
     f->n_facets = n_facets;
     if (n_facets == 0) return MF_OK;
-    if (p->form == MF_FORM_ELASTIC && m->elem != MF_Q1_HEX)
-        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: loaded boundaries are provided on Q1 faces");
+    if (p->form == MF_FORM_ELASTIC && m->elem != MF_Q1_HEX && m->elem != MF_Q2S_HEX)
+        return mf_fail(MF_ERR_UNSUPPORTED, "mf_facets_create: loaded boundaries are provided on brick faces");
     int *status = mf_status_word();
     if (!status) return mf_fail(MF_ERR_CUDA, "mf_facets_create: status word unavailable");
     const int npf = f->npf;
@@ -698,6 +784,9 @@ mf_status mf_facets_create_impl(const mf_mesh *m, const mf_pattern *p, int64_t n
     else if (m->elem == MF_P2_TET)
         k_facet_geometry<MF_P2_TET><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
                                                               false, f->bgeo, f->bcol, f->bwq);
+    else if (m->elem == MF_Q2S_HEX)
+        k_facet_geometry<MF_Q2S_HEX><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
+                                                               !thermal, f->bgeo, f->bcol, f->bwq);
     else
         k_facet_geometry<MF_Q1_HEX><<<nblk(ne), TPB, 0, st>>>(ne, f->binc, f->bloc, f->fnode, f->fface, m->coords,
                                                               !thermal, f->bgeo, f->bcol, f->bwq);
@@ -745,6 +834,7 @@ mf_status mf_assemble_boundary_impl(const mf_facets *f, const mf_facet_coeffs *c
         if (m->elem == MF_P1_TRI) k_bnd_thermal<2><<<g, BND_T, 0, st>>>(BND_ARGS);
         else if (m->elem == MF_P2_TRI || m->elem == MF_Q2S_QUAD) k_bnd_thermal<3><<<g, BND_T, 0, st>>>(BND_ARGS);
         else if (m->elem == MF_P2_TET) k_bnd_thermal<6><<<g, BND_T, 0, st>>>(BND_ARGS);
+        else if (m->elem == MF_Q2S_HEX) k_bnd_thermal<8><<<g, BND_T, 0, st>>>(BND_ARGS);
         else k_bnd_thermal<4><<<g, BND_T, 0, st>>>(BND_ARGS);
 #undef BND_ARGS
         mf_prof_end(st);

@@ -318,3 +318,80 @@ def test_facets_on_fully_constrained_rows(mf, orc):
     assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
     m = prob["bc_mask"] > 0
     assert np.array_equal(d[m], prob["bc_val"][m])
+
+
+# ---------------------------------------------------------------------------
+# 8-node faces of the 20-node brick (the cantilever beams' loads, Sec. 4.2;
+# convection, Sec. 4.1): 3 x 3 Gauss on the vertices' bilinear map
+# ---------------------------------------------------------------------------
+_Q2S_EDGES = [(0, 1), (2, 3), (4, 5), (6, 7), (0, 2), (1, 3), (4, 6), (5, 7), (0, 4), (1, 5), (2, 6), (3, 7)]
+
+
+def _warp_hex20(m, amp=0.08, seed=11):
+    """Every vertex jittered (boundary ones too: warped, tilted faces), the
+    edge midpoints moved to the means of their ends (straight edges)."""
+    X = m["coords"].copy()
+    c = m["conn"]
+    verts = np.unique(c[:, :8])
+    h = 1.0 / m["n"]
+    X[verts] += np.random.default_rng(seed).uniform(-amp * h, amp * h, (verts.shape[0], 3))
+    for k, (a, b) in enumerate(_Q2S_EDGES):
+        X[c[:, 8 + k]] = 0.5 * (X[c[:, a]] + X[c[:, b]])
+    return dict(m, coords=X)
+
+
+def _q2s_thermal(n, sides, warp=False):
+    m = gen.hex20_mesh(n, 0.15)
+    if warp:
+        m = _warp_hex20(m)
+    prob = dict(m, form="thermal", source=1.0, coef=gen.lognormal(gen.SEED_COEF, m["conn"].shape[0], 0.5))
+    nn = m["coords"].shape[0]
+    mask = np.zeros(nn, np.uint8)
+    # x = 0 side by the vertices of the x = 0 faces (also when warped)
+    e0, f0 = gen.box_facets(m, ("x0",))
+    for e in e0:
+        mask[m["conn"][e, [0, 2, 4, 6, 12, 14, 16, 18]]] = 1
+    prob["bc_mask"] = mask
+    prob["bc_val"] = np.where(mask > 0, gen.normal(9, nn), 0.0)
+    prob["facets"] = gen.convection_facets(prob, sides)
+    return prob
+
+
+def _q2s_elastic(n, sides, warp=False):
+    prob = gen.elastic_q2s_problem(n)
+    if warp:
+        prob = dict(prob, coords=_warp_hex20(prob)["coords"])
+    prob["facets"] = gen.traction_facets(prob, sides)
+    return prob
+
+
+@pytest.mark.parametrize("warp", [False, True])
+def test_q2s_face_convection_parity(mf, orc, warp):
+    prob = _q2s_thermal(5, ("x1", "y0", "y1", "z0", "z1"), warp=warp)
+    P, rp, ci, val, d = _gpu(mf, prob)
+    ref = orc.assemble(prob)
+    assert np.array_equal(rp, ref["row_ptr"]) and np.array_equal(ci, ref["col"])
+    assert row_scaled_error(rp, val, ref["val"]) <= TOL
+    assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+
+
+@pytest.mark.parametrize("warp", [False, True])
+def test_q2s_face_traction_parity(mf, orc, warp):
+    prob = _q2s_elastic(4, ("x1", "y0", "y1", "z0", "z1"), warp=warp)
+    P, rp, ci, val, d = _gpu(mf, prob)
+    ref = orc.assemble(prob)
+    assert np.array_equal(rp, ref["row_ptr"]) and np.array_equal(ci, ref["col"])
+    assert row_scaled_error(rp, val, ref["val"]) <= TOL
+    assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
+
+
+def test_q2s_uniform_stress_balances_over_the_closed_surface(mf):
+    """A uniform stress on all six sides with no body force and no clamp:
+    the loads sum to zero (int sigma n over a closed surface), per component."""
+    prob = gen.elastic_q2s_problem(3)
+    prob["body"] = (0.0, 0.0, 0.0)
+    prob["bc_mask"] = np.zeros_like(prob["bc_mask"])
+    prob["facets"] = gen.traction_facets(prob, gen.SIDES, stress=np.arange(9.0).reshape(3, 3) - 4.0)
+    P, rp, ci, val, d = _gpu(mf, prob, bc=False)
+    tot = d.reshape(-1, 3).sum(axis=0)
+    assert np.abs(tot).max() <= 1e-12 * np.abs(d).max()
