@@ -504,10 +504,15 @@ mf_status mf_cnn_create(const float *init, mf_cnn **out);
 mf_status mf_cnn_destroy(mf_cnn *cnn);
 mf_status mf_cnn_get_params(const mf_cnn *cnn, float *host, int64_t n);
 mf_status mf_cnn_get_grads(const mf_cnn *cnn, float *host, int64_t n);
-/* x: device BF16 [B][nv][2]; y: device FP32 [B][nv]. */
+/* x: device BF16 [B][nv][2], 4-byte aligned (a node's two channels are read
+ * as one word; MF_ERR_INVALID_ARG otherwise); y: device FP32 [B][nv]. */
 mf_status mf_cnn_forward(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x, float *y,
                          void *stream);
-/* Gradients of sum(gy * CNN(x)) into the gradient buffer (read with mf_cnn_get_grads). */
+/* Gradients of sum(gy * CNN(x)) into the gradient buffer (read with
+ * mf_cnn_get_grads); runs the forward pass first.  All four layers' weight
+ * gradients and the 16-channel input gradients are tensor-core GEMMs over the
+ * nodes (BF16 operands, FP32 accumulation); the gradients passed between
+ * layers are masked by the ReLU and rounded to BF16.  x as mf_cnn_forward. */
 mf_status mf_cnn_backward(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
                           const float *gy, void *stream);
 /* One AdamW step (lr > 0; lr = 0 only computes the loss and gradients) on B

@@ -17,7 +17,9 @@ elastic: Q1 elasticity on an n^3 jittered box (gen.elastic_problem), assembled
 reps times after one untimed call, then pcg-iters Jacobi-PCG iterations.  thermal-grf: Q1 thermal conduction with
 k = exp(GRF) on an n^3 box (gen.grf_thermal_problem), assembled reps times,
 then pcg-iters Jacobi-PCG iterations (graph of 50).  cnn: reps forward passes
-of the preconditioner network on an n^3 node grid (package weights).  oseen:
+of the preconditioner network on an n^3 node grid (package weights); with
+--train also reps backward calls (each a forward and a backward pass,
+random output gradient).  oseen:
 the Taylor-Hood flow form on an n^2 grid (gen.oseen_problem), assembled reps
 times.  batch: the 512-problem thermal batch (gen.batch_specs) in one graph,
 default tiling, reps replays.  convection: the thermal-grf mesh with T = 0 on
@@ -52,6 +54,7 @@ def main(argv=None):
     ap.add_argument("--prec", choices=("fp64", "mixed"), default="mixed")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--pcg-iters", type=int, default=0)
+    ap.add_argument("--train", action="store_true", help="cnn: also time forward + backward passes")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -178,6 +181,16 @@ def main(argv=None):
             mf.mf_cnn_forward(cnn, 1, a.n, a.n, a.n, xin, y)
         torch.cuda.synchronize()
         print("cnn forward", _times(mf))
+        if a.train:
+            gy = torch.randn(nv, device="cuda", generator=g)
+            mf.mf_set_kernel_timing(0)
+            mf.mf_cnn_backward(cnn, 1, a.n, a.n, a.n, xin, gy)
+            torch.cuda.synchronize()
+            mf.mf_set_kernel_timing(1)
+            for _ in range(a.reps):  # the backward call runs its own forward pass first
+                mf.mf_cnn_backward(cnn, 1, a.n, a.n, a.n, xin, gy)
+            torch.cuda.synchronize()
+            print("cnn forward + backward", _times(mf))
         mf.mf_cnn_destroy(cnn)
     mf.mf_set_kernel_timing(0)
 

@@ -261,12 +261,409 @@ __global__ void __launch_bounds__(256) k_conv16_mma(int B, int nz, int ny, int n
     }
 }
 
-// gradient wrt the input: gin[u][ci] = sum_{o, co} w[co][ci][o] gout[u - off(o)][co],
-// where gout is masked by the ReLU of that layer's output (act > 0) when act != NULL
+// Gradient wrt the input of a 16 -> 16 layer on the tensor cores: since the
+// stencil is symmetric (u - off(o) = u + off(26 - o)),
+//   gin[u][ci] = sum_o' sum_co w[co][ci][26 - o'] g[u + off(o')][co]
+// is the forward implicit GEMM of k_conv16_mma with the offsets flipped and
+// the channel roles swapped (16 nodes along x x 16 channels x 27 offsets,
+// BF16 operands, FP32 accumulation); no bias.  The operand g is the previous
+// step's output gradient already masked by its ReLU and rounded to BF16; the
+// result is written the same way for the layer below: out16[u][ci] =
+// bf16(gin[u][ci]) where act[u][ci] > 0 (that layer's ReLU output), else 0.
+__global__ void __launch_bounds__(256) k_conv16_mma_bwd(int B, int nz, int ny, int nx,
+                                                        const __nv_bfloat16 *__restrict__ gin16,
+                                                        const __nv_bfloat16 *__restrict__ w,
+                                                        const __nv_bfloat16 *__restrict__ act,
+                                                        __nv_bfloat16 *__restrict__ out16)
+{
+    __shared__ __align__(16) __nv_bfloat16 sw[27][16][16];  // [o'][ci (output)][co (input)]
+    for (int i = threadIdx.x; i < 16 * 16 * 27; i += blockDim.x) {
+        const int co = i / (16 * 27), ci = (i / 27) % 16, o = i % 27;  // source layout [co][ci][o]
+        sw[26 - o][ci][co] = w[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int xt = (nx + 15) / 16;
+    const int64_t runs = (int64_t)B * nz * ny * xt;
+    const int wpb = blockDim.x >> 5;
+    for (int64_t run = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); run < runs;
+         run += (int64_t)gridDim.x * wpb) {  // warp-uniform
+        const int xr = (int)(run % xt);
+        int64_t rest = run / xt;
+        const int y = (int)(rest % ny);
+        rest /= ny;
+        const int z = (int)(rest % nz);
+        const int b = (int)(rest / nz);
+        const int nv = nz * ny * nx;
+        const __nv_bfloat16 *base = gin16 + (int64_t)b * nv * 16;
+        const int x0 = xr * 16 + g, x1 = x0 + 8;
+        float acc[2][4] = {};
+#pragma unroll 1
+        for (int r9 = 0; r9 < 9; ++r9) {
+            const int zz = z + r9 / 3 - 1, yy = y + r9 % 3 - 1;
+            const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
+            const int64_t rowb = ((int64_t)zz * ny + yy) * nx;
+            uint32_t af[3][4];
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int xa = x0 + dx - 1, xb = x1 + dx - 1;
+                const bool va = zy && xa >= 0 && xa < nx, vb = zy && xb >= 0 && xb < nx;
+                const uint32_t *pa = reinterpret_cast<const uint32_t *>(base + (rowb + xa) * 16);
+                const uint32_t *pb = reinterpret_cast<const uint32_t *>(base + (rowb + xb) * 16);
+                af[dx][0] = va ? __ldg(pa + t) : 0u;
+                af[dx][2] = va ? __ldg(pa + 4 + t) : 0u;
+                af[dx][1] = vb ? __ldg(pb + t) : 0u;
+                af[dx][3] = vb ? __ldg(pb + 4 + t) : 0u;
+            }
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const uint32_t *wb = reinterpret_cast<const uint32_t *>(&sw[3 * r9 + dx][0][0]);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const int ci = nt * 8 + g;
+                    const uint32_t b0 = wb[ci * 8 + t], b1 = wb[ci * 8 + 4 + t];
+                    mma16816(acc[nt], af[dx][0], af[dx][1], af[dx][2], af[dx][3], b0, b1);
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xx = h ? x1 : x0;
+            if (xx >= nx) continue;
+            const int64_t v = (int64_t)b * nv + ((int64_t)z * ny + y) * nx + xx;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int ci = nt * 8 + 2 * t;
+                const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(act + v * 16 + ci);
+                __nv_bfloat162 pr;
+                pr.x = __float2bfloat16_rn(__bfloat162float(m.x) > 0.f ? acc[nt][2 * h] : 0.f);
+                pr.y = __float2bfloat16_rn(__bfloat162float(m.y) > 0.f ? acc[nt][2 * h + 1] : 0.f);
+                *reinterpret_cast<__nv_bfloat162 *>(out16 + v * 16 + ci) = pr;
+            }
+        }
+    }
+}
+
+// Weight gradient of a 16 -> 16 layer on the tensor cores:
+//   dW[co][ci][o] = sum_v g[v][co] in[v + off(o)][ci],   db[co] = sum_v g[v][co],
+// with g the ReLU-masked output gradient in BF16.  For each offset this is a
+// 16 x 16 GEMM whose K dimension runs over nodes: M = co, N = ci, K = the 16
+// nodes of an x-run.  Both operands have the node index as their K index, the
+// strided one of the channels-last layout, so each warp stages the run's g
+// tile (16 nodes x 16 channels) and its input row (the 18 nodes x - 1 .. x + 16
+// of one (dz, dy) neighbour row) in shared memory and transposes them into
+// fragments with ldmatrix.trans.  Block = 9 warps, warp r9 = 3 (dz + 1) +
+// (dy + 1) owns the three offsets (dz, dy, -1..1) and 24 accumulators; the
+// warp with dz = dy = 0 also forms db (one more MMA against a ones operand).
+// Each block walks a contiguous chunk of runs and writes its partial
+// gradient; k_reduce_part sums the partials in block order (deterministic).
+//
+// Shared tiles hold node k's two 16-byte channel halves at k * 32 +
+// ((h ^ (k >> 2 & 1)) * 16), which makes every 8-row ldmatrix phase over
+// consecutive nodes conflict-free.
+__device__ __forceinline__ uint32_t wg_swz(int k, int h) { return (uint32_t)(k * 32 + ((h ^ ((k >> 2) & 1)) << 4)); }
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+// two floats rounded to BF16 in one 32-bit fragment register (lo in bits 0..15)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+constexpr int WG_WARPS = 9;
+
+__global__ void __launch_bounds__(WG_WARPS * 32) k_conv16_mma_wgrad(int B, int nz, int ny, int nx, int64_t chunk,
+                                                                   const __nv_bfloat16 *__restrict__ in,
+                                                                   const __nv_bfloat16 *__restrict__ g16,
+                                                                   float *__restrict__ part)
+{
+    __shared__ __align__(128) unsigned char smem[WG_WARPS][512 + 18 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int dz = warp / 3 - 1, dy = warp % 3 - 1;
+    unsigned char *gt = smem[warp];     // g tile, 16 nodes
+    unsigned char *xt_s = gt + 512;     // input row, 18 nodes
+    const uint32_t gt_a = (uint32_t)__cvta_generic_to_shared(gt);
+    const uint32_t xt_a = gt_a + 512;
+    const int xt = (nx + 15) / 16;
+    const int64_t runs = (int64_t)B * nz * ny * xt;
+    const int nv = nz * ny * nx;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
+    float acc[3][2][4] = {};
+    float accb[4] = {};
+    const uint32_t ones = 0x3f803f80u;  // two BF16 1.0
+    // this lane's ldmatrix row addresses (offset dx added per MMA group)
+    const int a_node = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
+    const int b_node = (lane & 7) + (((lane >> 3) & 1) << 3), b_half = lane >> 4;
+#pragma unroll 1
+    for (int64_t run = r0; run < r1; ++run) {
+        const int xr = (int)(run % xt);
+        int64_t rest = run / xt;
+        const int y = (int)(rest % ny);
+        rest /= ny;
+        const int z = (int)(rest % nz);
+        const int b = (int)(rest / nz);
+        const int64_t bo = (int64_t)b * nv;
+        const int xb = xr * 16;
+        {   // g tile: lane -> (node lane / 2, half lane % 2)
+            const int k = lane >> 1, h = lane & 1, x = xb + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (x < nx) v = __ldg(reinterpret_cast<const uint4 *>(g16 + (bo + ((int64_t)z * ny + y) * nx + x) * 16) + h);
+            *reinterpret_cast<uint4 *>(gt + wg_swz(k, h)) = v;
+        }
+        {   // input row (z + dz, y + dy), nodes xb - 1 .. xb + 16
+            const int zz = z + dz, yy = y + dy;
+            const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
+            const int64_t rowb = bo + ((int64_t)zz * ny + yy) * nx;
+#pragma unroll
+            for (int c = lane; c < 36; c += 32) {
+                const int k = c >> 1, h = c & 1, x = xb - 1 + k;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (zy && x >= 0 && x < nx) v = __ldg(reinterpret_cast<const uint4 *>(in + (rowb + x) * 16) + h);
+                *reinterpret_cast<uint4 *>(xt_s + wg_swz(k, h)) = v;
+            }
+        }
+        __syncwarp();
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4_trans(gt_a + wg_swz(a_node, a_half), a0, a1, a2, a3);
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            uint32_t b00, b01, b10, b11;
+            ldsm_x4_trans(xt_a + wg_swz(b_node + dx, b_half), b00, b01, b10, b11);
+            mma16816(acc[dx][0], a0, a1, a2, a3, b00, b01);
+            mma16816(acc[dx][1], a0, a1, a2, a3, b10, b11);
+        }
+        if (warp == 4) mma16816(accb, a0, a1, a2, a3, ones, ones);
+        __syncwarp();
+    }
+    const int nw = 16 * 16 * 27;
+    float *pb = part + (int64_t)blockIdx.x * (nw + 16);
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+        const int o = 3 * warp + dx;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int ci = nt * 8 + 2 * t;
+            pb[(g * 16 + ci) * 27 + o] = acc[dx][nt][0];
+            pb[(g * 16 + ci + 1) * 27 + o] = acc[dx][nt][1];
+            pb[((g + 8) * 16 + ci) * 27 + o] = acc[dx][nt][2];
+            pb[((g + 8) * 16 + ci + 1) * 27 + o] = acc[dx][nt][3];
+        }
+    }
+    if (warp == 4 && t == 0) {
+        pb[nw + g] = accb[0];
+        pb[nw + g + 8] = accb[2];
+    }
+}
+
+// Weight gradients of the first (2 -> 16) and last (16 -> 1) layers on the
+// tensor cores.  One warp per x-run of 16 nodes takes all nine (dz, dy) rows
+// (one MMA each, 36 accumulators); the offsets along x and the narrow channel
+// side share the MMA's N = 8 columns.  The 8 warps of a block add their
+// accumulators in warp order through shared memory and write one partial per
+// block, summed by k_reduce_part.
+//
+// First layer: dW[co][ci][o] = sum_v g[v][co] x[v + off(o)][ci], ci < 2, with
+// g the ReLU-masked BF16 gradient: M = co, K = nodes (the g tile transposed by
+// ldmatrix.trans), N = 2 dx + ci (6 used); db[co] by an MMA against ones.
+constexpr int WF_WARPS = 8;
+
+__global__ void __launch_bounds__(WF_WARPS * 32) k_wgrad_first(int B, int nz, int ny, int nx, int64_t chunk,
+                                                              const __nv_bfloat16 *__restrict__ xin,
+                                                              const __nv_bfloat16 *__restrict__ g16,
+                                                              float *__restrict__ part)
+{
+    constexpr int NW = 16 * 2 * 27, NP = NW + 16;
+    __shared__ __align__(128) unsigned char gt_s[WF_WARPS][512];
+    __shared__ uint32_t xs[WF_WARPS][9][18];  // both input channels of nodes xb - 1 .. xb + 16, per row
+    __shared__ float red[WF_WARPS][NP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t gt_a = (uint32_t)__cvta_generic_to_shared(gt_s[warp]);
+    const int xt = (nx + 15) / 16;
+    const int64_t runs = (int64_t)B * nz * ny * xt;
+    const int nv = nz * ny * nx;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
+    float acc[9][4] = {};
+    float accb[4] = {};
+    const uint32_t ones = 0x3f803f80u;
+    const int a_node = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
+    const int dx = g >> 1, ci = g & 1;  // this lane's B column n = g
+#pragma unroll 1
+    for (int64_t run = r0 + warp; run < r1; run += WF_WARPS) {
+        const int xr = (int)(run % xt);
+        int64_t rest = run / xt;
+        const int y = (int)(rest % ny);
+        rest /= ny;
+        const int z = (int)(rest % nz);
+        const int b = (int)(rest / nz);
+        const int64_t bo = (int64_t)b * nv;
+        const int xb = xr * 16;
+        {
+            const int k = lane >> 1, h = lane & 1, x = xb + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (x < nx) v = __ldg(reinterpret_cast<const uint4 *>(g16 + (bo + ((int64_t)z * ny + y) * nx + x) * 16) + h);
+            *reinterpret_cast<uint4 *>(gt_s[warp] + wg_swz(k, h)) = v;
+        }
+        for (int c = lane; c < 9 * 18; c += 32) {
+            const int r = c / 18, k = c % 18;
+            const int zz = z + r / 3 - 1, yy = y + r % 3 - 1, x = xb - 1 + k;
+            uint32_t v = 0u;
+            if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && x >= 0 && x < nx)
+                v = __ldg(reinterpret_cast<const uint32_t *>(xin + (bo + ((int64_t)zz * ny + yy) * nx + x) * 2));
+            xs[warp][r][k] = v;
+        }
+        __syncwarp();
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4_trans(gt_a + wg_swz(a_node, a_half), a0, a1, a2, a3);
+        mma16816(accb, a0, a1, a2, a3, ones, ones);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            // B[k][n] = x[xb + k + dx - 1][ci] of row r: shared index k + dx
+            uint32_t b0 = 0u, b1 = 0u;
+            if (g < 6) {
+                const uint32_t *row = xs[warp][r];
+                const uint32_t w0 = row[2 * t + dx], w1 = row[2 * t + 1 + dx];
+                const uint32_t w2 = row[2 * t + 8 + dx], w3 = row[2 * t + 9 + dx];
+                const uint32_t sel = ci ? 0x7632u : 0x5410u;
+                b0 = __byte_perm(w0, w1, sel);
+                b1 = __byte_perm(w2, w3, sel);
+            }
+            mma16816(acc[r], a0, a1, a2, a3, b0, b1);
+        }
+        __syncwarp();
+    }
+    // C[co][n]: c0 = (g, 2t), c1 = (g, 2t + 1), c2 / c3 the same for co = g + 8;
+    // column n = 2 dx + ci, so lanes t < 3 hold dx = t, ci = 0 and 1
+    float *rw = red[warp];
+    if (t < 3) {
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const int o = 3 * r + t;
+            rw[(g * 2 + 0) * 27 + o] = acc[r][0];
+            rw[(g * 2 + 1) * 27 + o] = acc[r][1];
+            rw[((g + 8) * 2 + 0) * 27 + o] = acc[r][2];
+            rw[((g + 8) * 2 + 1) * 27 + o] = acc[r][3];
+        }
+    }
+    if (t == 0) {
+        rw[NW + g] = accb[0];
+        rw[NW + g + 8] = accb[2];
+    }
+    __syncthreads();
+    float *pb = part + (int64_t)blockIdx.x * NP;
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < WF_WARPS; ++w) sum += red[w][i];
+        pb[i] = sum;
+    }
+}
+
+// Last layer: dW[0][ci][o] = sum_u a[u][ci] gy[u - off(o)] (the sum over
+// output nodes v = u - off(o) moved onto the input node u), db = sum_v gy[v]:
+// M = ci, K = nodes (the run's own activation tile, transposed), N = dx (3
+// used), the B column of row (dz, dy) read from gy at (z - dz, y - dy) and
+// rounded to BF16.  The bias sum stays in FP32.
+__global__ void __launch_bounds__(WF_WARPS * 32) k_wgrad_last(int B, int nz, int ny, int nx, int64_t chunk,
+                                                             const __nv_bfloat16 *__restrict__ act,
+                                                             const float *__restrict__ gy, float *__restrict__ part)
+{
+    constexpr int NW = 16 * 27, NP = NW + 1;
+    __shared__ __align__(128) unsigned char at_s[WF_WARPS][512];
+    __shared__ float gs[WF_WARPS][9][18];  // gy at nodes xb - 1 .. xb + 16 of row (z - dz, y - dy)
+    __shared__ float red[WF_WARPS][NP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t at_a = (uint32_t)__cvta_generic_to_shared(at_s[warp]);
+    const int xt = (nx + 15) / 16;
+    const int64_t runs = (int64_t)B * nz * ny * xt;
+    const int nv = nz * ny * nx;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
+    float acc[9][4] = {};
+    float accb = 0.f;
+    const int a_node = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
+#pragma unroll 1
+    for (int64_t run = r0 + warp; run < r1; run += WF_WARPS) {
+        const int xr = (int)(run % xt);
+        int64_t rest = run / xt;
+        const int y = (int)(rest % ny);
+        rest /= ny;
+        const int z = (int)(rest % nz);
+        const int b = (int)(rest / nz);
+        const int64_t bo = (int64_t)b * nv;
+        const int xb = xr * 16;
+        {
+            const int k = lane >> 1, h = lane & 1, x = xb + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (x < nx) v = __ldg(reinterpret_cast<const uint4 *>(act + (bo + ((int64_t)z * ny + y) * nx + x) * 16) + h);
+            *reinterpret_cast<uint4 *>(at_s[warp] + wg_swz(k, h)) = v;
+        }
+        for (int c = lane; c < 9 * 18; c += 32) {
+            const int r = c / 18, k = c % 18;
+            const int zz = z - (r / 3 - 1), yy = y - (r % 3 - 1), x = xb - 1 + k;
+            float v = 0.f;
+            if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && x >= 0 && x < nx)
+                v = __ldg(gy + bo + ((int64_t)zz * ny + yy) * nx + x);
+            gs[warp][r][k] = v;
+        }
+        __syncwarp();
+        if (lane < 16) accb += gs[warp][4][1 + lane];  // the run's own nodes (zero past nx)
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4_trans(at_a + wg_swz(a_node, a_half), a0, a1, a2, a3);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            // B[k][dx] = gy[xb + k - dx + 1] of row r: shared index k - dx + 2
+            uint32_t b0 = 0u, b1 = 0u;
+            if (g < 3) {
+                const float *row = gs[warp][r];
+                const int k0 = 2 * t - g + 2;
+                b0 = pack_bf16(row[k0], row[k0 + 1]);
+                b1 = pack_bf16(row[k0 + 8], row[k0 + 9]);
+            }
+            mma16816(acc[r], a0, a1, a2, a3, b0, b1);
+        }
+        __syncwarp();
+    }
+    // C[ci][dx]: c0 = (g, 2t), c1 = (g, 2t + 1), c2 / c3 the same for ci = g + 8
+    float *rw = red[warp];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int d = 2 * t + j;
+            if (d < 3) {
+                rw[g * 27 + 3 * r + d] = acc[r][j];
+                rw[(g + 8) * 27 + 3 * r + d] = acc[r][2 + j];
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) accb += __shfl_xor_sync(0xffffffffu, accb, off);
+    if (lane == 0) rw[NW] = accb;
+    __syncthreads();
+    float *pb = part + (int64_t)blockIdx.x * NP;
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < WF_WARPS; ++w) sum += red[w][i];
+        pb[i] = sum;
+    }
+}
+
+// gradient wrt the input of the last layer (CO = 1, no ReLU on its output):
+// gin[u][ci] = sum_{o, co} w[co][ci][o] gout[u - off(o)][co], written masked by
+// the ReLU of the layer below (in_act > 0) and rounded to BF16, the operand of
+// that layer's tensor-core passes
 template <int CI, int CO>
 __global__ void __launch_bounds__(128) k_conv_bwd_data(int B, int nz, int ny, int nx, const float *__restrict__ gout,
-                                                       const __nv_bfloat16 *__restrict__ act,
-                                                       const __nv_bfloat16 *__restrict__ w, float *__restrict__ gin)
+                                                       const __nv_bfloat16 *__restrict__ w,
+                                                       const __nv_bfloat16 *__restrict__ in_act,
+                                                       __nv_bfloat16 *__restrict__ gin16)
 {
     __shared__ float sw[CO * CI * 27];
     for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) sw[i] = __bfloat162float(w[i]);
@@ -285,60 +682,15 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(int B, int nz, int ny, in
         const int64_t vi = (int64_t)b * nv + v;
         float gv[CO];
 #pragma unroll
-        for (int co = 0; co < CO; ++co) {
-            gv[co] = gout[vi * CO + co];
-            if (act && !(__bfloat162float(act[vi * CO + co]) > 0.f)) gv[co] = 0.f;
-        }
+        for (int co = 0; co < CO; ++co) gv[co] = gout[vi * CO + co];
 #pragma unroll
         for (int ci = 0; ci < CI; ++ci)
 #pragma unroll
             for (int co = 0; co < CO; ++co) acc[ci] = fmaf(sw[(co * CI + ci) * 27 + o], gv[co], acc[ci]);
     }
 #pragma unroll
-    for (int ci = 0; ci < CI; ++ci) gin[g * CI + ci] = acc[ci];
-}
-
-// gradient wrt the weights: per block a chunk of nodes, one thread per
-// (co, ci) pair with 27 accumulators; partial sums per block, reduced in order
-template <int CI, int CO>
-__global__ void __launch_bounds__(256) k_conv_bwd_weight(int B, int nz, int ny, int nx, int chunk,
-                                                         const __nv_bfloat16 *__restrict__ in,
-                                                         const float *__restrict__ gout,
-                                                         const __nv_bfloat16 *__restrict__ act,
-                                                         float *__restrict__ part)
-{
-    const int nv = nz * ny * nx;
-    const int64_t total = (int64_t)B * nv;
-    const int pair = threadIdx.x;
-    const bool active = pair < CO * CI;
-    const int co = active ? pair / CI : 0, ci = active ? pair % CI : 0;
-    float acc[27];
-#pragma unroll
-    for (int o = 0; o < 27; ++o) acc[o] = 0.f;
-    float accb = 0.f;
-    const int64_t g0 = (int64_t)blockIdx.x * chunk, g1 = min(total, g0 + chunk);
-    if (active)
-        for (int64_t g = g0; g < g1; ++g) {
-            float gv = gout[g * CO + co];
-            if (act && !(__bfloat162float(act[g * CO + co]) > 0.f)) gv = 0.f;
-            if (gv == 0.f) continue;
-            if (ci == 0) accb += gv;
-            const int b = (int)(g / nv), v = (int)(g % nv);
-            const __nv_bfloat16 *base = in + (int64_t)b * nv * CI;
-#pragma unroll
-            for (int o = 0; o < 27; ++o) {
-                int u;
-                if (nb_index(v, o, nz, ny, nx, u))
-                    acc[o] = fmaf(gv, __bfloat162float(base[(int64_t)u * CI + ci]), acc[o]);
-            }
-        }
-    const int nw = CO * CI * 27;
-    float *pb = part + (int64_t)blockIdx.x * (nw + CO);
-    if (active) {
-#pragma unroll
-        for (int o = 0; o < 27; ++o) pb[(co * CI + ci) * 27 + o] = acc[o];
-        if (ci == 0) pb[nw + co] = accb;
-    }
+    for (int ci = 0; ci < CI; ++ci)
+        gin16[g * CI + ci] = __float2bfloat16_rn(__bfloat162float(in_act[g * CI + ci]) > 0.f ? acc[ci] : 0.f);
 }
 
 __global__ void k_reduce_part(int nblocks, int n, const float *__restrict__ part, float *__restrict__ out)
@@ -646,18 +998,21 @@ unsigned conv_grid(int64_t items, int per_block)
 struct Acts {
     __nv_bfloat16 *a1, *a2, *a3;  // outputs of layers 1..3 (ReLU), BF16
     float *y;                      // layer 4 output, FP32
-    float *g0, *g1;                // gradient buffers (FP32, 16 channels)
+    __nv_bfloat16 *gA, *gB;        // ReLU-masked gradients in BF16, 16 channels (tensor-core operands)
     float *part;                   // weight-gradient partials
     int wparts;
 };
 
 mf_status ensure_ws(mf_cnn *c, int B, int nv, bool train, Acts *A, cudaStream_t st)
 {
-    const size_t act = (size_t)B * nv * 16 * sizeof(__nv_bfloat16);
-    const size_t yb = (size_t)B * nv * sizeof(float);
-    const size_t gb = train ? (size_t)B * nv * 16 * sizeof(float) : 0;
+    // every region starts on a 256-byte boundary: the tensor-core kernels move
+    // 16-byte vectors (uint4) and FP32 pairs, whatever B * nv is
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t act = up((size_t)B * nv * 16 * sizeof(__nv_bfloat16));
+    const size_t yb = up((size_t)B * nv * sizeof(float));
+    const size_t gb = train ? act : 0;
     const int wparts = 1024;
-    const size_t pb = train ? (size_t)wparts * (16 * 16 * 27 + 16) * sizeof(float) : 0;
+    const size_t pb = train ? up((size_t)wparts * (16 * 16 * 27 + 16) * sizeof(float)) : 0;
     const size_t need = 3 * act + yb + 2 * gb + pb + 4096;
     if (need > c->ws_bytes) {
         if (c->ws) cudaFreeAsync(c->ws, st);
@@ -670,8 +1025,8 @@ mf_status ensure_ws(mf_cnn *c, int B, int nv, bool train, Acts *A, cudaStream_t 
     A->a2 = reinterpret_cast<__nv_bfloat16 *>(q + act);
     A->a3 = reinterpret_cast<__nv_bfloat16 *>(q + 2 * act);
     A->y = reinterpret_cast<float *>(q + 3 * act);
-    A->g0 = train ? reinterpret_cast<float *>(q + 3 * act + yb) : nullptr;
-    A->g1 = train ? reinterpret_cast<float *>(q + 3 * act + yb + gb) : nullptr;
+    A->gA = train ? reinterpret_cast<__nv_bfloat16 *>(q + 3 * act + yb) : nullptr;
+    A->gB = train ? reinterpret_cast<__nv_bfloat16 *>(q + 3 * act + yb + gb) : nullptr;
     A->part = train ? reinterpret_cast<float *>(q + 3 * act + yb + 2 * gb) : nullptr;
     A->wparts = wparts;
     return MF_OK;
@@ -699,34 +1054,70 @@ void forward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, A
     mf_prof_end(st);
 }
 
-template <int CI, int CO>
-void bwd_weight(mf_cnn *c, int l, int B, int nz, int ny, int nx, const __nv_bfloat16 *in, const float *gout,
-                const __nv_bfloat16 *act, Acts &A, cudaStream_t st)
+// Weight gradient of a 16 -> 16 layer (index l) from its input activations
+// and its ReLU-masked BF16 output gradient, on the tensor cores.
+void bwd_weight16(mf_cnn *c, int l, int B, int nz, int ny, int nx, const __nv_bfloat16 *in,
+                  const __nv_bfloat16 *g16, Acts &A, cudaStream_t st)
 {
-    const int64_t tot = (int64_t)B * nz * ny * nx;
-    const int chunk = (int)((tot + A.wparts - 1) / A.wparts);
-    const int nblocks = (int)((tot + chunk - 1) / chunk);
-    k_conv_bwd_weight<CI, CO><<<nblocks, 256, 0, st>>>(B, nz, ny, nx, chunk, in, gout, act, A.part);
-    const int n = CO * CI * 27 + CO;  // weights then biases, contiguous in the parameter vector
+    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
+    const int64_t chunk = (runs + A.wparts - 1) / A.wparts;
+    const int nblocks = (int)((runs + chunk - 1) / chunk);
+    static const char *names[4] = {"cnn_bwd_weight1", "cnn_bwd_weight2", "cnn_bwd_weight3", "cnn_bwd_weight4"};
+    mf_prof_begin(names[l], st);
+    k_conv16_mma_wgrad<<<nblocks, WG_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, in, g16, A.part);
+    const int n = 16 * 16 * 27 + 16;
     k_reduce_part<<<nblk(n, 128), 128, 0, st>>>(nblocks, n, A.part, c->g + p_offset_w(l));
+    mf_prof_end(st);
+}
+
+// Backward pass.  The gradients entering layers 3, 2 and 1 are kept in BF16,
+// masked by their ReLU (gA, gB, gA), as the tensor-core kernels take them.
+// Weight gradient of the first (2 -> 16, l = 0) or last (16 -> 1, l = 3)
+// layer on the tensor cores.
+void bwd_weight_edge(mf_cnn *c, int l, int B, int nz, int ny, int nx, const __nv_bfloat16 *in,
+                     const __nv_bfloat16 *g16, const float *gy, Acts &A, cudaStream_t st)
+{
+    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
+    const int64_t chunk = (runs + A.wparts - 1) / A.wparts;
+    const int nblocks = (int)((runs + chunk - 1) / chunk);
+    static const char *names[4] = {"cnn_bwd_weight1", "cnn_bwd_weight2", "cnn_bwd_weight3", "cnn_bwd_weight4"};
+    mf_prof_begin(names[l], st);
+    int n;
+    if (l == 0) {
+        k_wgrad_first<<<nblocks, WF_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, in, g16, A.part);
+        n = 16 * 2 * 27 + 16;
+    } else {
+        k_wgrad_last<<<nblocks, WF_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, in, gy, A.part);
+        n = 16 * 27 + 1;
+    }
+    k_reduce_part<<<nblk(n, 128), 128, 0, st>>>(nblocks, n, A.part, c->g + p_offset_w(l));
+    mf_prof_end(st);
 }
 
 void backward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, const float *gy, Acts &A,
               cudaStream_t st)
 {
     const int64_t tot = (int64_t)B * nz * ny * nx;
+    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
     const __nv_bfloat16 *W = c->pb;
-    // layer 4 (no ReLU): dL/dy = gy
-    bwd_weight<16, 1>(c, 3, B, nz, ny, nx, A.a3, gy, nullptr, A, st);
-    k_conv_bwd_data<16, 1><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, gy, nullptr, W + p_offset_w(3), A.g0);
-    // layer 3: gradient wrt a3 is g0, masked by a3 > 0
-    bwd_weight<16, 16>(c, 2, B, nz, ny, nx, A.a2, A.g0, A.a3, A, st);
-    k_conv_bwd_data<16, 16><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, A.g0, A.a3, W + p_offset_w(2), A.g1);
-    // layer 2
-    bwd_weight<16, 16>(c, 1, B, nz, ny, nx, A.a1, A.g1, A.a2, A, st);
-    k_conv_bwd_data<16, 16><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, A.g1, A.a2, W + p_offset_w(1), A.g0);
+    __nv_bfloat16 *gA = A.gA, *gB = A.gB;
+    // layer 4 (no ReLU): dL/dy = gy; gradient wrt a3, masked by a3 > 0 -> gA
+    bwd_weight_edge(c, 3, B, nz, ny, nx, A.a3, nullptr, gy, A, st);
+    mf_prof_begin("cnn_bwd_data4", st);
+    k_conv_bwd_data<16, 1><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, gy, W + p_offset_w(3), A.a3, gA);
+    mf_prof_end(st);
+    // layer 3: input a2; gradient wrt a2, masked by a2 > 0 -> gB
+    bwd_weight16(c, 2, B, nz, ny, nx, A.a2, gA, A, st);
+    mf_prof_begin("cnn_bwd_data3", st);
+    k_conv16_mma_bwd<<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, gA, W + p_offset_w(2), A.a2, gB);
+    mf_prof_end(st);
+    // layer 2: input a1; gradient wrt a1, masked by a1 > 0 -> gA
+    bwd_weight16(c, 1, B, nz, ny, nx, A.a1, gB, A, st);
+    mf_prof_begin("cnn_bwd_data2", st);
+    k_conv16_mma_bwd<<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, gB, W + p_offset_w(1), A.a1, gA);
+    mf_prof_end(st);
     // layer 1 (input gradient not needed)
-    bwd_weight<2, 16>(c, 0, B, nz, ny, nx, x, A.g0, A.a1, A, st);
+    bwd_weight_edge(c, 0, B, nz, ny, nx, x, gA, nullptr, A, st);
 }
 
 }  // namespace
@@ -795,7 +1186,8 @@ extern "C" mf_status mf_cnn_get_grads(const mf_cnn *c, float *host, int64_t n)
 extern "C" mf_status mf_cnn_forward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
                                     float *y, void *stream)
 {
-    if (!c || !x || !y || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)nz * ny * nx > INT32_MAX / 16)
+    if (!c || !x || !y || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)nz * ny * nx > INT32_MAX / 16 ||
+        (reinterpret_cast<uintptr_t>(x) & 3))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_forward: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Acts A;
@@ -812,7 +1204,8 @@ extern "C" mf_status mf_cnn_forward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny
 extern "C" mf_status mf_cnn_backward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
                                      const float *gy, void *stream)
 {
-    if (!c || !x || !gy || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0)
+    if (!c || !x || !gy || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)nz * ny * nx > INT32_MAX / 16 ||
+        (reinterpret_cast<uintptr_t>(x) & 3))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_backward: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Acts A;
