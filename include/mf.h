@@ -505,7 +505,8 @@ mf_status mf_cnn_destroy(mf_cnn *cnn);
 mf_status mf_cnn_get_params(const mf_cnn *cnn, float *host, int64_t n);
 mf_status mf_cnn_get_grads(const mf_cnn *cnn, float *host, int64_t n);
 /* x: device BF16 [B][nv][2], 4-byte aligned (a node's two channels are read
- * as one word; MF_ERR_INVALID_ARG otherwise); y: device FP32 [B][nv]. */
+ * as one word); y: device FP32 [B][nv].  MF_ERR_INVALID_ARG for a misaligned
+ * x or B nv > (2^31 - 1) / 16 (the same bound for training and FCG). */
 mf_status mf_cnn_forward(mf_cnn *cnn, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x, float *y,
                          void *stream);
 /* Gradients of sum(gy * CNN(x)) into the gradient buffer (read with

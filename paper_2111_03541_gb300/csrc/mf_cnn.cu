@@ -41,136 +41,12 @@ int p_total() { return p_offset_b(NL - 1) + COUT[NL - 1]; }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-__device__ __forceinline__ bool nb_index(int v, int o, int nz, int ny, int nx, int &u)
-{
-    const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
-    const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
-    const int zz = z + dz, yy = y + dy, xx = x + dx;
-    if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) return false;
-    u = (zz * ny + yy) * nx + xx;
-    return true;
-}
-
 // Forward kernels are persistent (grid-stride over nodes or runs, a few
 // blocks per SM), so each block stages its layer's weights in shared memory
 // once.  Activations are channels-last BF16: a node's 16 channels are 32 bytes,
 // moved as two 16-byte vectors.
 
-// first layer, 2 -> 16 channels, ReLU, BF16 out: one thread per node
-__global__ void __launch_bounds__(256) k_conv_first(int B, int nz, int ny, int nx,
-                                                    const __nv_bfloat16 *__restrict__ in,
-                                                    const __nv_bfloat16 *__restrict__ w,
-                                                    const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out)
-{
-    __shared__ __align__(16) float sw[27][2][16];  // [o][ci][co]; source layout [co][ci][o]
-    for (int i = threadIdx.x; i < 16 * 2 * 27; i += blockDim.x) {
-        const int co = i / 54, ci = (i / 27) % 2, o = i % 27;
-        sw[o][ci][co] = __bfloat162float(w[i]);
-    }
-    __syncthreads();
-    const int nv = nz * ny * nx;
-    const int64_t tot = (int64_t)B * nv;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(g / nv), v = (int)(g - (int64_t)b * nv);
-        const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
-        const uint32_t *base = reinterpret_cast<const uint32_t *>(in + (int64_t)b * nv * 2);
-        float acc[16];
-#pragma unroll
-        for (int co = 0; co < 16; ++co) acc[co] = bias[co];
-        // the 9 neighbour loads of a z-plane are issued before its FMAs (zero
-        // outside the grid)
-#pragma unroll 1
-        for (int dz = 0; dz < 3; ++dz) {
-            uint32_t raw[9];
-#pragma unroll
-            for (int o = 0; o < 9; ++o) {
-                const int zz = z + dz - 1, yy = y + o / 3 - 1, xx = x + o % 3 - 1;
-                const bool ok = zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-                raw[o] = ok ? __ldg(base + (zz * ny + yy) * nx + xx) : 0u;
-            }
-#pragma unroll
-            for (int o = 0; o < 9; ++o) {
-                const float x0 = __uint_as_float(raw[o] << 16), x1 = __uint_as_float(raw[o] & 0xffff0000u);
-                const int oo = 9 * dz + o;
-                const float4 *w0 = reinterpret_cast<const float4 *>(sw[oo][0]);
-                const float4 *w1 = reinterpret_cast<const float4 *>(sw[oo][1]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {  // 16-byte weight reads
-                    const float4 u0 = w0[q], u1 = w1[q];
-                    acc[4 * q] = fmaf(u0.x, x0, fmaf(u1.x, x1, acc[4 * q]));
-                    acc[4 * q + 1] = fmaf(u0.y, x0, fmaf(u1.y, x1, acc[4 * q + 1]));
-                    acc[4 * q + 2] = fmaf(u0.z, x0, fmaf(u1.z, x1, acc[4 * q + 2]));
-                    acc[4 * q + 3] = fmaf(u0.w, x0, fmaf(u1.w, x1, acc[4 * q + 3]));
-                }
-            }
-        }
-        uint32_t pk[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            __nv_bfloat162 h;
-            h.x = __float2bfloat16_rn(fmaxf(acc[2 * k], 0.f));
-            h.y = __float2bfloat16_rn(fmaxf(acc[2 * k + 1], 0.f));
-            pk[k] = *reinterpret_cast<uint32_t *>(&h);
-        }
-        uint4 *o4 = reinterpret_cast<uint4 *>(out + g * 16);
-        o4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-    }
-}
-
-// last layer, 16 -> 1 channel, no ReLU, FP32 out: one thread per node
-__global__ void __launch_bounds__(256) k_conv_last(int B, int nz, int ny, int nx,
-                                                   const __nv_bfloat16 *__restrict__ in,
-                                                   const __nv_bfloat16 *__restrict__ w,
-                                                   const float *__restrict__ bias, float *__restrict__ out)
-{
-    __shared__ __align__(16) float sw[27][16];  // [o][ci]; source layout [ci][o]
-    for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) sw[i % 27][i / 27] = __bfloat162float(w[i]);
-    __syncthreads();
-    const int nv = nz * ny * nx;
-    const int64_t tot = (int64_t)B * nv;
-    const float b0 = bias[0];
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(g / nv), v = (int)(g - (int64_t)b * nv);
-        const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
-        const uint4 *base = reinterpret_cast<const uint4 *>(in + (int64_t)b * nv * 16);
-        float acc = b0;
-        // one z-plane of 9 neighbours (18 16-byte loads) in flight at a time
-#pragma unroll 1
-        for (int dz = 0; dz < 3; ++dz) {
-            uint4 lo[9], hi[9];
-#pragma unroll
-            for (int o = 0; o < 9; ++o) {
-                const int zz = z + dz - 1, yy = y + o / 3 - 1, xx = x + o % 3 - 1;
-                const bool ok = zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-                const int64_t u = (int64_t)(zz * ny + yy) * nx + xx;
-                lo[o] = ok ? __ldg(base + 2 * u) : make_uint4(0u, 0u, 0u, 0u);
-                hi[o] = ok ? __ldg(base + 2 * u + 1) : make_uint4(0u, 0u, 0u, 0u);
-            }
-#pragma unroll
-            for (int o = 0; o < 9; ++o) {
-                const uint32_t wds[8] = {lo[o].x, lo[o].y, lo[o].z, lo[o].w, hi[o].x, hi[o].y, hi[o].z, hi[o].w};
-                const float4 *wo = reinterpret_cast<const float4 *>(sw[9 * dz + o]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {  // 16-byte weight reads
-                    const float4 u = wo[q];
-                    acc = fmaf(u.x, __uint_as_float(wds[2 * q] << 16), acc);
-                    acc = fmaf(u.y, __uint_as_float(wds[2 * q] & 0xffff0000u), acc);
-                    acc = fmaf(u.z, __uint_as_float(wds[2 * q + 1] << 16), acc);
-                    acc = fmaf(u.w, __uint_as_float(wds[2 * q + 1] & 0xffff0000u), acc);
-                }
-            }
-        }
-        out[g] = acc;
-    }
-}
-
-// 16 -> 16 channel layer on tensor cores: implicit GEMM, one warp per run of
-// 16 nodes along x (M = 16 nodes, N = 2 x 8 output channels, K = 27 offsets x
-// 16 input channels, one mma.sync m16n8k16 per offset and n-tile).  Weights
-// sit in shared memory as [o][co][ci] BF16 so a B fragment is one 32-bit load;
-// A fragments are read straight from the channels-last activations (zero
-// outside the grid).
+// D += A B on one m16n8k16 tile (BF16 operands, FP32 accumulators)
 __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1)
 {
@@ -181,167 +57,190 @@ __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <bool RELU>
-__global__ void __launch_bounds__(256) k_conv16_mma(int B, int nz, int ny, int nx, const __nv_bfloat16 *__restrict__ in,
-                                                    const __nv_bfloat16 *__restrict__ w,
-                                                    const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out)
+// Shared tiles of 16-channel BF16 rows (32 bytes per node or channel row) hold
+// row k's two 16-byte halves at k * 32 + ((h ^ (k >> 2 & 1)) * 16): the 8
+// rows of every ldmatrix phase over consecutive rows then hit distinct banks.
+__device__ __forceinline__ uint32_t wg_swz(int k, int h) { return (uint32_t)(k * 32 + ((h ^ ((k >> 2) & 1)) << 4)); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
 {
-    __shared__ __align__(16) __nv_bfloat16 sw[27][16][16];  // [o][co][ci]
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+// 16-byte global -> shared copy, zero-filled (nothing read) when !valid
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// 16 -> 16 channel layer on tensor cores, forward and input gradient.
+// Implicit GEMM, one warp per x-run of 16 nodes: M = 16 nodes, N = 2 x 8
+// channels, K = 27 offsets x 16 channels (one mma.sync m16n8k16 per offset and
+// n-tile).  The run's 9 neighbour rows (18 nodes each, zero outside the grid)
+// are staged in shared memory by cp.async, the next run's rows in flight while
+// this one computes; A fragments come from them by ldmatrix (row = node, the
+// shift dx is a row offset), B fragments by ldmatrix from the weights, kept
+// per offset as [n][k] rows.
+//   Forward (BWD = false): out[v][co] = ReLU(b[co] + sum_o sum_ci
+//     w[co][ci][o] in[v + off(o)][ci]), n = co, k = ci.
+//   Input gradient (BWD = true): with the stencil symmetric (v - off(o) =
+//     v + off(26 - o)), gin[v][ci] = sum_o sum_co w[co][ci][26 - o]
+//     g[v + off(o)][co] is the same GEMM with n = ci, k = co and the offsets
+//     flipped; g is the output gradient already masked by its ReLU and rounded
+//     to BF16, and the result is written the same way for the layer below:
+//     out[v][ci] = bf16(gin[v][ci]) where act[v][ci] > 0 (its ReLU output), else 0.
+//   Last layer (MODE CV_LAST, 16 -> 1): y[v] = b + sum_o sum_ci w[ci][o]
+//     in[v + off(o)][ci] in FP32 to yout; one n-tile whose column 0 holds the
+//     weights (the other seven are zero).
+constexpr int CV_WARPS = 8;
+constexpr int CV_ROW = 18 * 32;     // one staged neighbour row
+constexpr int CV_RUN = 9 * CV_ROW;  // the 9 (dz, dy) rows of one run
+constexpr int CV_SMEM = 27 * 512 + CV_WARPS * 2 * CV_RUN;
+
+// position of x-run `run` (B * nz * ny * ceil(nx / 16) runs, fewer than 2^31)
+struct RunPos {
+    int b, z, y, xb;
+};
+__device__ __forceinline__ RunPos run_pos(int run, int xt, int ny, int nz)
+{
+    RunPos p;
+    const int row = run / xt;
+    p.xb = (run - row * xt) * 16;
+    const int plane = row / ny;
+    p.y = row - plane * ny;
+    p.b = plane / nz;
+    p.z = plane - p.b * nz;
+    return p;
+}
+
+// stage the 9 neighbour rows of the run at p: nodes xb - 1 .. xb + 16 of rows
+// (z + dz, y + dy), 36 16-byte chunks per row; lane l copies chunk l and,
+// for l < 4, chunk 32 + l
+__device__ __forceinline__ void cv_stage(const RunPos &p, int nz, int ny, int nx, const __nv_bfloat16 *in,
+                                         uint32_t dst, int lane)
+{
+    const int64_t bo = (int64_t)p.b * nz * ny * nx;
+    const int k1 = lane >> 1, k2 = 16 + (lane >> 1), h = lane & 1;
+    const uint32_t s1 = wg_swz(k1, h), s2 = wg_swz(k2, h);
+    const int x1 = p.xb - 1 + k1, x2 = p.xb - 1 + k2;
+    const bool v1 = x1 >= 0 && x1 < nx, v2 = lane < 4 && x2 < nx;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int zz = p.z + r / 3 - 1, yy = p.y + r % 3 - 1;
+        const bool rv = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
+        const __nv_bfloat16 *row = in + (bo + ((int64_t)zz * ny + yy) * nx) * 16 + h * 8;
+        cp_async16(dst + r * CV_ROW + s1, rv && v1 ? row + x1 * 16 : in, rv && v1);
+        if (lane < 4) cp_async16(dst + r * CV_ROW + s2, rv && v2 ? row + x2 * 16 : in, rv && v2);
+    }
+}
+
+enum { CV_FWD = 0, CV_BWD = 1, CV_LAST = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(CV_WARPS * 32, 2) k_conv16_tc(int B, int nz, int ny, int nx,
+                                                               const __nv_bfloat16 *__restrict__ in,
+                                                               const __nv_bfloat16 *__restrict__ w,
+                                                               const float *__restrict__ bias,
+                                                               const __nv_bfloat16 *__restrict__ act,
+                                                               __nv_bfloat16 *__restrict__ out, float *__restrict__ yout)
+{
+    constexpr bool BWD = MODE == CV_BWD, LAST = MODE == CV_LAST;
+    extern __shared__ __align__(128) unsigned char cv_smem[];
     for (int i = threadIdx.x; i < 16 * 16 * 27; i += blockDim.x) {
-        const int co = i / (16 * 27), ci = (i / 27) % 16, o = i % 27;  // source layout [co][ci][o]
-        sw[o][co][ci] = w[i];
+        if (LAST) {  // B rows n = 0..15 of offset o: w[0][k][o] in row 0, zero elsewhere
+            const int o = i / 256, n = (i / 16) % 16, k = i % 16;
+            *reinterpret_cast<__nv_bfloat16 *>(cv_smem + o * 512 + wg_swz(n, k >> 3) + (k & 7) * 2) =
+                n == 0 ? w[k * 27 + o] : __float2bfloat16_rn(0.f);
+        } else {
+            const int co = i / (16 * 27), ci = (i / 27) % 16, o = i % 27;  // source layout [co][ci][o]
+            const int n = BWD ? ci : co, k = BWD ? co : ci, oo = BWD ? 26 - o : o;
+            *reinterpret_cast<__nv_bfloat16 *>(cv_smem + oo * 512 + wg_swz(n, k >> 3) + (k & 7) * 2) = w[i];
+        }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int xt = (nx + 15) / 16;  // x-runs per row
-    const int64_t runs = (int64_t)B * nz * ny * xt;
-    const int wpb = blockDim.x >> 5;
-    for (int64_t run = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); run < runs;
-         run += (int64_t)gridDim.x * wpb) {  // warp-uniform
-        const int xr = (int)(run % xt);
-        int64_t rest = run / xt;
-        const int y = (int)(rest % ny);
-        rest /= ny;
-        const int z = (int)(rest % nz);
-        const int b = (int)(rest / nz);
-        const int nv = nz * ny * nx;
-        const __nv_bfloat16 *base = in + (int64_t)b * nv * 16;
-        const int x0 = xr * 16 + g, x1 = x0 + 8;  // the two A rows of this lane
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t sw_a = (uint32_t)__cvta_generic_to_shared(cv_smem);
+    const uint32_t buf_a = sw_a + 27 * 512 + warp * 2 * CV_RUN;
+    const int xt = (nx + 15) / 16;
+    const int runs = B * nz * ny * xt;
+    const int nv = nz * ny * nx;
+    const int stride = gridDim.x * CV_WARPS;
+    // ldmatrix rows of this lane.  A: (node, channel half) = (lane & 15, lane >> 4)
+    // gives a0..a3; B: matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7),
+    // (n 8-15, k 8-15) give b0, b1 of n-tile 0, then of n-tile 1.
+    const int a_node = lane & 15, a_half = lane >> 4;
+    const int b_n = (lane & 7) + ((lane >> 4) << 3), b_half = (lane >> 3) & 1;
+    int run = blockIdx.x * CV_WARPS + warp;
+    RunPos p = run_pos(run < runs ? run : 0, xt, ny, nz);
+    if (run < runs) cv_stage(p, nz, ny, nx, in, buf_a, lane);
+    cp_async_commit();
+    int cur = 0;
+    for (; run < runs; run += stride) {  // warp-uniform
+        const RunPos pc = p;
+        if (run + stride < runs) {
+            p = run_pos(run + stride, xt, ny, nz);
+            cv_stage(p, nz, ny, nx, in, buf_a + (cur ^ 1) * CV_RUN, lane);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        const uint32_t rb = buf_a + cur * CV_RUN;
         float acc[2][4] = {};
-        // per (dz, dy) row: the A fragments of the three x offsets are loaded
-        // together, then the six MMAs run
-#pragma unroll 1
+#pragma unroll 3
         for (int r9 = 0; r9 < 9; ++r9) {
-            const int zz = z + r9 / 3 - 1, yy = y + r9 % 3 - 1;
-            const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
-            const int64_t rowb = ((int64_t)zz * ny + yy) * nx;
-            uint32_t af[3][4];
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
-                const int xa = x0 + dx - 1, xb = x1 + dx - 1;
-                const bool va = zy && xa >= 0 && xa < nx, vb = zy && xb >= 0 && xb < nx;
-                const uint32_t *pa = reinterpret_cast<const uint32_t *>(base + (rowb + xa) * 16);
-                const uint32_t *pb = reinterpret_cast<const uint32_t *>(base + (rowb + xb) * 16);
-                af[dx][0] = va ? __ldg(pa + t) : 0u;
-                af[dx][2] = va ? __ldg(pa + 4 + t) : 0u;
-                af[dx][1] = vb ? __ldg(pb + t) : 0u;
-                af[dx][3] = vb ? __ldg(pb + 4 + t) : 0u;
-            }
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const uint32_t *wb = reinterpret_cast<const uint32_t *>(&sw[3 * r9 + dx][0][0]);
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const int co = nt * 8 + g;
-                    const uint32_t b0 = wb[co * 8 + t], b1 = wb[co * 8 + 4 + t];
-                    mma16816(acc[nt], af[dx][0], af[dx][1], af[dx][2], af[dx][3], b0, b1);
-                }
+                uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+                ldsm_x4(rb + r9 * CV_ROW + wg_swz(a_node + dx, a_half), a0, a1, a2, a3);
+                ldsm_x4(sw_a + (3 * r9 + dx) * 512 + wg_swz(b_n, b_half), b0, b1, b2, b3);
+                mma16816(acc[0], a0, a1, a2, a3, b0, b1);
+                if (!LAST) mma16816(acc[1], a0, a1, a2, a3, b2, b3);
             }
         }
-        // C fragment: rows g, g + 8 (nodes x0, x1), columns 2t, 2t + 1 of each n-tile
+        // C fragment: rows g, g + 8 (nodes xb + g, xb + g + 8), columns 2t, 2t + 1 of each n-tile
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int xx = h ? x1 : x0;
+            const int xx = pc.xb + g + 8 * h;
             if (xx >= nx) continue;
-            const int64_t v = (int64_t)b * nv + ((int64_t)z * ny + y) * nx + xx;
+            const int64_t v = (int64_t)pc.b * nv + ((int64_t)pc.z * ny + pc.y) * nx + xx;
+            if (LAST) {  // column 0 sits in c0 (node g) and c2 (node g + 8) of the lanes with t = 0
+                if (t == 0) yout[v] = acc[0][2 * h] + bias[0];
+            }
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const int co = nt * 8 + 2 * t;
-                float v0 = acc[nt][2 * h] + bias[co], v1 = acc[nt][2 * h + 1] + bias[co + 1];
-                if (RELU) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
+            for (int nt = 0; nt < (LAST ? 0 : 2); ++nt) {
+                const int n = nt * 8 + 2 * t;
+                float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+                if (BWD) {
+                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(act + v * 16 + n);
+                    v0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
+                    v1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
+                } else {
+                    v0 = fmaxf(v0 + bias[n], 0.f);
+                    v1 = fmaxf(v1 + bias[n + 1], 0.f);
                 }
                 __nv_bfloat162 pr;
                 pr.x = __float2bfloat16_rn(v0);
                 pr.y = __float2bfloat16_rn(v1);
-                *reinterpret_cast<__nv_bfloat162 *>(out + v * 16 + co) = pr;
+                *reinterpret_cast<__nv_bfloat162 *>(out + v * 16 + n) = pr;
             }
         }
+        __syncwarp();  // every lane done with this buffer before it is refilled
+        cur ^= 1;
     }
-}
-
-// Gradient wrt the input of a 16 -> 16 layer on the tensor cores: since the
-// stencil is symmetric (u - off(o) = u + off(26 - o)),
-//   gin[u][ci] = sum_o' sum_co w[co][ci][26 - o'] g[u + off(o')][co]
-// is the forward implicit GEMM of k_conv16_mma with the offsets flipped and
-// the channel roles swapped (16 nodes along x x 16 channels x 27 offsets,
-// BF16 operands, FP32 accumulation); no bias.  The operand g is the previous
-// step's output gradient already masked by its ReLU and rounded to BF16; the
-// result is written the same way for the layer below: out16[u][ci] =
-// bf16(gin[u][ci]) where act[u][ci] > 0 (that layer's ReLU output), else 0.
-__global__ void __launch_bounds__(256) k_conv16_mma_bwd(int B, int nz, int ny, int nx,
-                                                        const __nv_bfloat16 *__restrict__ gin16,
-                                                        const __nv_bfloat16 *__restrict__ w,
-                                                        const __nv_bfloat16 *__restrict__ act,
-                                                        __nv_bfloat16 *__restrict__ out16)
-{
-    __shared__ __align__(16) __nv_bfloat16 sw[27][16][16];  // [o'][ci (output)][co (input)]
-    for (int i = threadIdx.x; i < 16 * 16 * 27; i += blockDim.x) {
-        const int co = i / (16 * 27), ci = (i / 27) % 16, o = i % 27;  // source layout [co][ci][o]
-        sw[26 - o][ci][co] = w[i];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int xt = (nx + 15) / 16;
-    const int64_t runs = (int64_t)B * nz * ny * xt;
-    const int wpb = blockDim.x >> 5;
-    for (int64_t run = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); run < runs;
-         run += (int64_t)gridDim.x * wpb) {  // warp-uniform
-        const int xr = (int)(run % xt);
-        int64_t rest = run / xt;
-        const int y = (int)(rest % ny);
-        rest /= ny;
-        const int z = (int)(rest % nz);
-        const int b = (int)(rest / nz);
-        const int nv = nz * ny * nx;
-        const __nv_bfloat16 *base = gin16 + (int64_t)b * nv * 16;
-        const int x0 = xr * 16 + g, x1 = x0 + 8;
-        float acc[2][4] = {};
-#pragma unroll 1
-        for (int r9 = 0; r9 < 9; ++r9) {
-            const int zz = z + r9 / 3 - 1, yy = y + r9 % 3 - 1;
-            const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
-            const int64_t rowb = ((int64_t)zz * ny + yy) * nx;
-            uint32_t af[3][4];
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const int xa = x0 + dx - 1, xb = x1 + dx - 1;
-                const bool va = zy && xa >= 0 && xa < nx, vb = zy && xb >= 0 && xb < nx;
-                const uint32_t *pa = reinterpret_cast<const uint32_t *>(base + (rowb + xa) * 16);
-                const uint32_t *pb = reinterpret_cast<const uint32_t *>(base + (rowb + xb) * 16);
-                af[dx][0] = va ? __ldg(pa + t) : 0u;
-                af[dx][2] = va ? __ldg(pa + 4 + t) : 0u;
-                af[dx][1] = vb ? __ldg(pb + t) : 0u;
-                af[dx][3] = vb ? __ldg(pb + 4 + t) : 0u;
-            }
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const uint32_t *wb = reinterpret_cast<const uint32_t *>(&sw[3 * r9 + dx][0][0]);
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const int ci = nt * 8 + g;
-                    const uint32_t b0 = wb[ci * 8 + t], b1 = wb[ci * 8 + 4 + t];
-                    mma16816(acc[nt], af[dx][0], af[dx][1], af[dx][2], af[dx][3], b0, b1);
-                }
-            }
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int xx = h ? x1 : x0;
-            if (xx >= nx) continue;
-            const int64_t v = (int64_t)b * nv + ((int64_t)z * ny + y) * nx + xx;
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const int ci = nt * 8 + 2 * t;
-                const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(act + v * 16 + ci);
-                __nv_bfloat162 pr;
-                pr.x = __float2bfloat16_rn(__bfloat162float(m.x) > 0.f ? acc[nt][2 * h] : 0.f);
-                pr.y = __float2bfloat16_rn(__bfloat162float(m.y) > 0.f ? acc[nt][2 * h + 1] : 0.f);
-                *reinterpret_cast<__nv_bfloat162 *>(out16 + v * 16 + ci) = pr;
-            }
-        }
-    }
+    cp_async_wait<0>();
 }
 
 // Weight gradient of a 16 -> 16 layer on the tensor cores:
@@ -351,24 +250,13 @@ __global__ void __launch_bounds__(256) k_conv16_mma_bwd(int B, int nz, int ny, i
 // nodes of an x-run.  Both operands have the node index as their K index, the
 // strided one of the channels-last layout, so each warp stages the run's g
 // tile (16 nodes x 16 channels) and its input row (the 18 nodes x - 1 .. x + 16
-// of one (dz, dy) neighbour row) in shared memory and transposes them into
-// fragments with ldmatrix.trans.  Block = 9 warps, warp r9 = 3 (dz + 1) +
-// (dy + 1) owns the three offsets (dz, dy, -1..1) and 24 accumulators; the
-// warp with dz = dy = 0 also forms db (one more MMA against a ones operand).
-// Each block walks a contiguous chunk of runs and writes its partial
+// of one (dz, dy) neighbour row) in shared memory (swizzled as wg_swz) and
+// transposes them into fragments with ldmatrix.trans.  Block = 9 warps, warp
+// r9 = 3 (dz + 1) + (dy + 1) owns the three offsets (dz, dy, -1..1) and 24
+// accumulators; the warp with dz = dy = 0 also forms db (one more MMA against
+// a ones operand).  Each block walks a contiguous chunk of runs, every warp
+// keeping WG_DEPTH - 1 runs in flight (cp.async), and writes its partial
 // gradient; k_reduce_part sums the partials in block order (deterministic).
-//
-// Shared tiles hold node k's two 16-byte channel halves at k * 32 +
-// ((h ^ (k >> 2 & 1)) * 16), which makes every 8-row ldmatrix phase over
-// consecutive nodes conflict-free.
-__device__ __forceinline__ uint32_t wg_swz(int k, int h) { return (uint32_t)(k * 32 + ((h ^ ((k >> 2) & 1)) << 4)); }
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
 
 // two floats rounded to BF16 in one 32-bit fragment register (lo in bits 0..15)
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -378,58 +266,70 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 constexpr int WG_WARPS = 9;
+constexpr int WG_DEPTH = 4;
+constexpr int WG_STAGE = 512 + 18 * 32;  // g tile + input row
 
-__global__ void __launch_bounds__(WG_WARPS * 32) k_conv16_mma_wgrad(int B, int nz, int ny, int nx, int64_t chunk,
+__global__ void __launch_bounds__(WG_WARPS * 32) k_conv16_mma_wgrad(int B, int nz, int ny, int nx, int chunk,
                                                                    const __nv_bfloat16 *__restrict__ in,
                                                                    const __nv_bfloat16 *__restrict__ g16,
                                                                    float *__restrict__ part)
 {
-    __shared__ __align__(128) unsigned char smem[WG_WARPS][512 + 18 * 32];
+    __shared__ __align__(128) unsigned char smem[WG_WARPS][WG_DEPTH][WG_STAGE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int dz = warp / 3 - 1, dy = warp % 3 - 1;
-    unsigned char *gt = smem[warp];     // g tile, 16 nodes
-    unsigned char *xt_s = gt + 512;     // input row, 18 nodes
-    const uint32_t gt_a = (uint32_t)__cvta_generic_to_shared(gt);
-    const uint32_t xt_a = gt_a + 512;
+    const uint32_t base_a = (uint32_t)__cvta_generic_to_shared(smem[warp][0]);
     const int xt = (nx + 15) / 16;
-    const int64_t runs = (int64_t)B * nz * ny * xt;
-    const int nv = nz * ny * nx;
-    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
+    const int runs = B * nz * ny * xt;
+    const int r0 = blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
+    // this lane's copies: g tile chunk (node lane / 2, half lane % 2); input
+    // row chunks lane and (lane < 4) 32 + lane
+    const int kg = lane >> 1, h = lane & 1, k1 = lane >> 1, k2 = 16 + (lane >> 1);
+    const uint32_t sg = wg_swz(kg, h), s1 = 512 + wg_swz(k1, h), s2 = 512 + wg_swz(k2, h);
+    // runs are staged in order, so their positions advance incrementally
+    RunPos p = run_pos(r0 < runs ? r0 : 0, xt, ny, nz);
+    auto stage = [&](uint32_t dst) {
+        const int64_t bo = (int64_t)p.b * nz * ny * nx;
+        const int xg = p.xb + kg;
+        cp_async16(dst + sg, xg < nx ? g16 + (bo + ((int64_t)p.z * ny + p.y) * nx + xg) * 16 + h * 8 : g16, xg < nx);
+        const int zz = p.z + dz, yy = p.y + dy;
+        const bool rv = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
+        const __nv_bfloat16 *row = in + (bo + ((int64_t)zz * ny + yy) * nx) * 16 + h * 8;
+        const int x1 = p.xb - 1 + k1, x2 = p.xb - 1 + k2;
+        const bool v1 = rv && x1 >= 0 && x1 < nx, v2 = rv && x2 < nx;
+        cp_async16(dst + s1, v1 ? row + x1 * 16 : in, v1);
+        if (lane < 4) cp_async16(dst + s2, v2 ? row + x2 * 16 : in, v2);
+        p.xb += 16;  // next run
+        if (p.xb >= xt * 16) {
+            p.xb = 0;
+            if (++p.y == ny) {
+                p.y = 0;
+                if (++p.z == nz) {
+                    p.z = 0;
+                    ++p.b;
+                }
+            }
+        }
+    };
     float acc[3][2][4] = {};
     float accb[4] = {};
     const uint32_t ones = 0x3f803f80u;  // two BF16 1.0
     // this lane's ldmatrix row addresses (offset dx added per MMA group)
     const int a_node = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
     const int b_node = (lane & 7) + (((lane >> 3) & 1) << 3), b_half = lane >> 4;
-#pragma unroll 1
-    for (int64_t run = r0; run < r1; ++run) {
-        const int xr = (int)(run % xt);
-        int64_t rest = run / xt;
-        const int y = (int)(rest % ny);
-        rest /= ny;
-        const int z = (int)(rest % nz);
-        const int b = (int)(rest / nz);
-        const int64_t bo = (int64_t)b * nv;
-        const int xb = xr * 16;
-        {   // g tile: lane -> (node lane / 2, half lane % 2)
-            const int k = lane >> 1, h = lane & 1, x = xb + k;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (x < nx) v = __ldg(reinterpret_cast<const uint4 *>(g16 + (bo + ((int64_t)z * ny + y) * nx + x) * 16) + h);
-            *reinterpret_cast<uint4 *>(gt + wg_swz(k, h)) = v;
-        }
-        {   // input row (z + dz, y + dy), nodes xb - 1 .. xb + 16
-            const int zz = z + dz, yy = y + dy;
-            const bool zy = zz >= 0 && zz < nz && yy >= 0 && yy < ny;
-            const int64_t rowb = bo + ((int64_t)zz * ny + yy) * nx;
 #pragma unroll
-            for (int c = lane; c < 36; c += 32) {
-                const int k = c >> 1, h = c & 1, x = xb - 1 + k;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (zy && x >= 0 && x < nx) v = __ldg(reinterpret_cast<const uint4 *>(in + (rowb + x) * 16) + h);
-                *reinterpret_cast<uint4 *>(xt_s + wg_swz(k, h)) = v;
-            }
-        }
+    for (int i = 0; i < WG_DEPTH - 1; ++i) {
+        if (r0 + i < r1) stage(base_a + i * WG_STAGE);
+        cp_async_commit();
+    }
+    int slot = 0;
+#pragma unroll 1
+    for (int run = r0; run < r1; ++run) {
+        const int nr = run + WG_DEPTH - 1;
+        if (nr < r1) stage(base_a + ((slot + WG_DEPTH - 1) % WG_DEPTH) * WG_STAGE);
+        cp_async_commit();
+        cp_async_wait<WG_DEPTH - 1>();
         __syncwarp();
+        const uint32_t gt_a = base_a + slot * WG_STAGE, xt_a = gt_a + 512;
         uint32_t a0, a1, a2, a3;
         ldsm_x4_trans(gt_a + wg_swz(a_node, a_half), a0, a1, a2, a3);
 #pragma unroll
@@ -440,8 +340,10 @@ __global__ void __launch_bounds__(WG_WARPS * 32) k_conv16_mma_wgrad(int B, int n
             mma16816(acc[dx][1], a0, a1, a2, a3, b10, b11);
         }
         if (warp == 4) mma16816(accb, a0, a1, a2, a3, ones, ones);
-        __syncwarp();
+        __syncwarp();  // every lane done with this slot before it is refilled
+        slot = (slot + 1) % WG_DEPTH;
     }
+    cp_async_wait<0>();
     const int nw = 16 * 16 * 27;
     float *pb = part + (int64_t)blockIdx.x * (nw + 16);
 #pragma unroll
@@ -465,232 +367,184 @@ __global__ void __launch_bounds__(WG_WARPS * 32) k_conv16_mma_wgrad(int B, int n
 // Weight gradients of the first (2 -> 16) and last (16 -> 1) layers on the
 // tensor cores.  One warp per x-run of 16 nodes takes all nine (dz, dy) rows
 // (one MMA each, 36 accumulators); the offsets along x and the narrow channel
-// side share the MMA's N = 8 columns.  The 8 warps of a block add their
-// accumulators in warp order through shared memory and write one partial per
-// block, summed by k_reduce_part.
+// side share the MMA's N = 8 columns.  Each warp keeps WF_DEPTH - 1 runs in
+// flight (cp.async into its own stages: the 16-channel tile of the run and
+// the nine 18-node rows of the narrow operand, one 32-bit word per node).
+// The 8 warps of a block add their accumulators in warp order through shared
+// memory (reusing the stages) and write one partial per block, summed by
+// k_reduce_part.
 //
 // First layer: dW[co][ci][o] = sum_v g[v][co] x[v + off(o)][ci], ci < 2, with
 // g the ReLU-masked BF16 gradient: M = co, K = nodes (the g tile transposed by
 // ldmatrix.trans), N = 2 dx + ci (6 used); db[co] by an MMA against ones.
-constexpr int WF_WARPS = 8;
-
-__global__ void __launch_bounds__(WF_WARPS * 32) k_wgrad_first(int B, int nz, int ny, int nx, int64_t chunk,
-                                                              const __nv_bfloat16 *__restrict__ xin,
-                                                              const __nv_bfloat16 *__restrict__ g16,
-                                                              float *__restrict__ part)
-{
-    constexpr int NW = 16 * 2 * 27, NP = NW + 16;
-    __shared__ __align__(128) unsigned char gt_s[WF_WARPS][512];
-    __shared__ uint32_t xs[WF_WARPS][9][18];  // both input channels of nodes xb - 1 .. xb + 16, per row
-    __shared__ float red[WF_WARPS][NP];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const uint32_t gt_a = (uint32_t)__cvta_generic_to_shared(gt_s[warp]);
-    const int xt = (nx + 15) / 16;
-    const int64_t runs = (int64_t)B * nz * ny * xt;
-    const int nv = nz * ny * nx;
-    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
-    float acc[9][4] = {};
-    float accb[4] = {};
-    const uint32_t ones = 0x3f803f80u;
-    const int a_node = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
-    const int dx = g >> 1, ci = g & 1;  // this lane's B column n = g
-#pragma unroll 1
-    for (int64_t run = r0 + warp; run < r1; run += WF_WARPS) {
-        const int xr = (int)(run % xt);
-        int64_t rest = run / xt;
-        const int y = (int)(rest % ny);
-        rest /= ny;
-        const int z = (int)(rest % nz);
-        const int b = (int)(rest / nz);
-        const int64_t bo = (int64_t)b * nv;
-        const int xb = xr * 16;
-        {
-            const int k = lane >> 1, h = lane & 1, x = xb + k;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (x < nx) v = __ldg(reinterpret_cast<const uint4 *>(g16 + (bo + ((int64_t)z * ny + y) * nx + x) * 16) + h);
-            *reinterpret_cast<uint4 *>(gt_s[warp] + wg_swz(k, h)) = v;
-        }
-        for (int c = lane; c < 9 * 18; c += 32) {
-            const int r = c / 18, k = c % 18;
-            const int zz = z + r / 3 - 1, yy = y + r % 3 - 1, x = xb - 1 + k;
-            uint32_t v = 0u;
-            if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && x >= 0 && x < nx)
-                v = __ldg(reinterpret_cast<const uint32_t *>(xin + (bo + ((int64_t)zz * ny + yy) * nx + x) * 2));
-            xs[warp][r][k] = v;
-        }
-        __syncwarp();
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4_trans(gt_a + wg_swz(a_node, a_half), a0, a1, a2, a3);
-        mma16816(accb, a0, a1, a2, a3, ones, ones);
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-            // B[k][n] = x[xb + k + dx - 1][ci] of row r: shared index k + dx
-            uint32_t b0 = 0u, b1 = 0u;
-            if (g < 6) {
-                const uint32_t *row = xs[warp][r];
-                const uint32_t w0 = row[2 * t + dx], w1 = row[2 * t + 1 + dx];
-                const uint32_t w2 = row[2 * t + 8 + dx], w3 = row[2 * t + 9 + dx];
-                const uint32_t sel = ci ? 0x7632u : 0x5410u;
-                b0 = __byte_perm(w0, w1, sel);
-                b1 = __byte_perm(w2, w3, sel);
-            }
-            mma16816(acc[r], a0, a1, a2, a3, b0, b1);
-        }
-        __syncwarp();
-    }
-    // C[co][n]: c0 = (g, 2t), c1 = (g, 2t + 1), c2 / c3 the same for co = g + 8;
-    // column n = 2 dx + ci, so lanes t < 3 hold dx = t, ci = 0 and 1
-    float *rw = red[warp];
-    if (t < 3) {
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-            const int o = 3 * r + t;
-            rw[(g * 2 + 0) * 27 + o] = acc[r][0];
-            rw[(g * 2 + 1) * 27 + o] = acc[r][1];
-            rw[((g + 8) * 2 + 0) * 27 + o] = acc[r][2];
-            rw[((g + 8) * 2 + 1) * 27 + o] = acc[r][3];
-        }
-    }
-    if (t == 0) {
-        rw[NW + g] = accb[0];
-        rw[NW + g + 8] = accb[2];
-    }
-    __syncthreads();
-    float *pb = part + (int64_t)blockIdx.x * NP;
-    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
-        float sum = 0.f;
-#pragma unroll
-        for (int w = 0; w < WF_WARPS; ++w) sum += red[w][i];
-        pb[i] = sum;
-    }
-}
-
 // Last layer: dW[0][ci][o] = sum_u a[u][ci] gy[u - off(o)] (the sum over
 // output nodes v = u - off(o) moved onto the input node u), db = sum_v gy[v]:
 // M = ci, K = nodes (the run's own activation tile, transposed), N = dx (3
 // used), the B column of row (dz, dy) read from gy at (z - dz, y - dy) and
-// rounded to BF16.  The bias sum stays in FP32.
-__global__ void __launch_bounds__(WF_WARPS * 32) k_wgrad_last(int B, int nz, int ny, int nx, int64_t chunk,
-                                                             const __nv_bfloat16 *__restrict__ act,
-                                                             const float *__restrict__ gy, float *__restrict__ part)
+// rounded to BF16; the bias sum stays in FP32.
+constexpr int WF_WARPS = 8;
+constexpr int WF_DEPTH = 3;
+constexpr int WF_STAGE = 1280;  // 512-byte tile + 648 bytes of rows, padded to 128 bytes
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, bool valid)
 {
-    constexpr int NW = 16 * 27, NP = NW + 1;
-    __shared__ __align__(128) unsigned char at_s[WF_WARPS][512];
-    __shared__ float gs[WF_WARPS][9][18];  // gy at nodes xb - 1 .. xb + 16 of row (z - dz, y - dy)
-    __shared__ float red[WF_WARPS][NP];
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+template <bool LAST>
+__global__ void __launch_bounds__(WF_WARPS * 32) k_wgrad_edge(int B, int nz, int ny, int nx, int chunk,
+                                                             const __nv_bfloat16 *__restrict__ tile16,
+                                                             const void *__restrict__ narrow,
+                                                             float *__restrict__ part)
+{
+    // tile16: first layer g (masked gradient), last layer a (activations);
+    // narrow: first layer x (BF16 pairs), last layer gy (FP32)
+    constexpr int NW = LAST ? 16 * 27 : 16 * 2 * 27, NP = NW + (LAST ? 1 : 16);
+    constexpr int BUF = WF_WARPS * WF_DEPTH * WF_STAGE > WF_WARPS * NP * 4 ? WF_WARPS * WF_DEPTH * WF_STAGE
+                                                                           : WF_WARPS * NP * 4;
+    __shared__ __align__(128) unsigned char smem[BUF];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const uint32_t at_a = (uint32_t)__cvta_generic_to_shared(at_s[warp]);
+    const uint32_t base_a = (uint32_t)__cvta_generic_to_shared(smem) + warp * WF_DEPTH * WF_STAGE;
+    const unsigned char *base_p = smem + warp * WF_DEPTH * WF_STAGE;
     const int xt = (nx + 15) / 16;
-    const int64_t runs = (int64_t)B * nz * ny * xt;
-    const int nv = nz * ny * nx;
-    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
-    float acc[9][4] = {};
-    float accb = 0.f;
-    const int a_node = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
-#pragma unroll 1
-    for (int64_t run = r0 + warp; run < r1; run += WF_WARPS) {
-        const int xr = (int)(run % xt);
-        int64_t rest = run / xt;
-        const int y = (int)(rest % ny);
-        rest /= ny;
-        const int z = (int)(rest % nz);
-        const int b = (int)(rest / nz);
-        const int64_t bo = (int64_t)b * nv;
-        const int xb = xr * 16;
-        {
-            const int k = lane >> 1, h = lane & 1, x = xb + k;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (x < nx) v = __ldg(reinterpret_cast<const uint4 *>(act + (bo + ((int64_t)z * ny + y) * nx + x) * 16) + h);
-            *reinterpret_cast<uint4 *>(at_s[warp] + wg_swz(k, h)) = v;
-        }
+    const int runs = B * nz * ny * xt;
+    const int r0 = blockIdx.x * chunk, r1 = min(runs, r0 + chunk);
+    const uint32_t *nw32 = static_cast<const uint32_t *>(narrow);
+    const int kg = lane >> 1, h = lane & 1;
+    const uint32_t sg = wg_swz(kg, h);
+    auto stage = [&](int run, uint32_t dst) {
+        const RunPos p = run_pos(run, xt, ny, nz);
+        const int64_t bo = (int64_t)p.b * nz * ny * nx;
+        const int xg = p.xb + kg;
+        cp_async16(dst + sg, xg < nx ? tile16 + (bo + ((int64_t)p.z * ny + p.y) * nx + xg) * 16 + h * 8 : tile16,
+                   xg < nx);
         for (int c = lane; c < 9 * 18; c += 32) {
-            const int r = c / 18, k = c % 18;
-            const int zz = z - (r / 3 - 1), yy = y - (r % 3 - 1), x = xb - 1 + k;
-            float v = 0.f;
-            if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && x >= 0 && x < nx)
-                v = __ldg(gy + bo + ((int64_t)zz * ny + yy) * nx + x);
-            gs[warp][r][k] = v;
+            const int r = c / 18, k = c - r * 18;
+            // first layer: row (z + dz, y + dy); last layer: row (z - dz, y - dy)
+            const int zz = LAST ? p.z - (r / 3 - 1) : p.z + r / 3 - 1;
+            const int yy = LAST ? p.y - (r % 3 - 1) : p.y + r % 3 - 1;
+            const int x = p.xb - 1 + k;
+            const bool v = zz >= 0 && zz < nz && yy >= 0 && yy < ny && x >= 0 && x < nx;
+            cp_async4(dst + 512 + c * 4, v ? nw32 + bo + ((int64_t)zz * ny + yy) * nx + x : nw32, v);
         }
+    };
+    float acc[9][4] = {};
+    float accb[4] = {};
+    float accs = 0.f;
+    const uint32_t ones = 0x3f803f80u;
+    const int a_node = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
+    // first-layer runs go to warps round-robin; a warp's runs: r0 + warp + WF_WARPS i
+#pragma unroll
+    for (int i = 0; i < WF_DEPTH - 1; ++i) {
+        const int run = r0 + warp + i * WF_WARPS;
+        if (run < r1) stage(run, base_a + i * WF_STAGE);
+        cp_async_commit();
+    }
+    int slot = 0;
+#pragma unroll 1
+    for (int run = r0 + warp; run < r1; run += WF_WARPS) {
+        const int nr = run + (WF_DEPTH - 1) * WF_WARPS;
+        if (nr < r1) stage(nr, base_a + ((slot + WF_DEPTH - 1) % WF_DEPTH) * WF_STAGE);
+        cp_async_commit();
+        cp_async_wait<WF_DEPTH - 1>();
         __syncwarp();
-        if (lane < 16) accb += gs[warp][4][1 + lane];  // the run's own nodes (zero past nx)
+        const uint32_t ta = base_a + slot * WF_STAGE;
+        const unsigned char *rows = base_p + slot * WF_STAGE + 512;
         uint32_t a0, a1, a2, a3;
-        ldsm_x4_trans(at_a + wg_swz(a_node, a_half), a0, a1, a2, a3);
+        ldsm_x4_trans(ta + wg_swz(a_node, a_half), a0, a1, a2, a3);
+        if (!LAST) {
+            mma16816(accb, a0, a1, a2, a3, ones, ones);
+            const int dx = g >> 1, ci = g & 1;  // this lane's B column n = g
+            const uint32_t sel = ci ? 0x7632u : 0x5410u;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                // B[k][n] = x[xb + k + dx - 1][ci] of row r: stage index k + dx
+                uint32_t b0 = 0u, b1 = 0u;
+                if (g < 6) {
+                    const uint32_t *row = reinterpret_cast<const uint32_t *>(rows) + r * 18;
+                    b0 = __byte_perm(row[2 * t + dx], row[2 * t + 1 + dx], sel);
+                    b1 = __byte_perm(row[2 * t + 8 + dx], row[2 * t + 9 + dx], sel);
+                }
+                mma16816(acc[r], a0, a1, a2, a3, b0, b1);
+            }
+        } else {
+            if (lane < 16) accs += reinterpret_cast<const float *>(rows)[4 * 18 + 1 + lane];  // own nodes
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                // B[k][dx] = gy[xb + k - dx + 1] of row r: stage index k - dx + 2
+                uint32_t b0 = 0u, b1 = 0u;
+                if (g < 3) {
+                    const float *row = reinterpret_cast<const float *>(rows) + r * 18;
+                    const int k0 = 2 * t - g + 2;
+                    b0 = pack_bf16(row[k0], row[k0 + 1]);
+                    b1 = pack_bf16(row[k0 + 8], row[k0 + 9]);
+                }
+                mma16816(acc[r], a0, a1, a2, a3, b0, b1);
+            }
+        }
+        __syncwarp();  // every lane done with this slot before it is refilled
+        slot = (slot + 1) % WF_DEPTH;
+    }
+    cp_async_wait<0>();
+    __syncthreads();  // the stages become the reduction buffer
+    float *rw = reinterpret_cast<float *>(smem) + warp * NP;
+    if (!LAST) {
+        // C[co][n]: c0 = (g, 2t), c1 = (g, 2t + 1), c2 / c3 the same for co = g + 8;
+        // column n = 2 dx + ci, so lanes t < 3 hold dx = t, ci = 0 and 1
+        if (t < 3) {
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                const int o = 3 * r + t;
+                rw[(g * 2 + 0) * 27 + o] = acc[r][0];
+                rw[(g * 2 + 1) * 27 + o] = acc[r][1];
+                rw[((g + 8) * 2 + 0) * 27 + o] = acc[r][2];
+                rw[((g + 8) * 2 + 1) * 27 + o] = acc[r][3];
+            }
+        }
+        if (t == 0) {
+            rw[NW + g] = accb[0];
+            rw[NW + g + 8] = accb[2];
+        }
+    } else {
+        // C[ci][dx]: c0 = (g, 2t), c1 = (g, 2t + 1), c2 / c3 the same for ci = g + 8
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
-            // B[k][dx] = gy[xb + k - dx + 1] of row r: shared index k - dx + 2
-            uint32_t b0 = 0u, b1 = 0u;
-            if (g < 3) {
-                const float *row = gs[warp][r];
-                const int k0 = 2 * t - g + 2;
-                b0 = pack_bf16(row[k0], row[k0 + 1]);
-                b1 = pack_bf16(row[k0 + 8], row[k0 + 9]);
-            }
-            mma16816(acc[r], a0, a1, a2, a3, b0, b1);
-        }
-        __syncwarp();
-    }
-    // C[ci][dx]: c0 = (g, 2t), c1 = (g, 2t + 1), c2 / c3 the same for ci = g + 8
-    float *rw = red[warp];
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int d = 2 * t + j;
-            if (d < 3) {
-                rw[g * 27 + 3 * r + d] = acc[r][j];
-                rw[(g + 8) * 27 + 3 * r + d] = acc[r][2 + j];
+            for (int j = 0; j < 2; ++j) {
+                const int d = 2 * t + j;
+                if (d < 3) {
+                    rw[g * 27 + 3 * r + d] = acc[r][j];
+                    rw[(g + 8) * 27 + 3 * r + d] = acc[r][2 + j];
+                }
             }
         }
-    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) accb += __shfl_xor_sync(0xffffffffu, accb, off);
-    if (lane == 0) rw[NW] = accb;
+        for (int off = 16; off > 0; off >>= 1) accs += __shfl_xor_sync(0xffffffffu, accs, off);
+        if (lane == 0) rw[NW] = accs;
+    }
     __syncthreads();
+    const float *red = reinterpret_cast<const float *>(smem);
     float *pb = part + (int64_t)blockIdx.x * NP;
     for (int i = threadIdx.x; i < NP; i += blockDim.x) {
         float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < WF_WARPS; ++w) sum += red[w][i];
+        for (int w = 0; w < WF_WARPS; ++w) sum += red[w * NP + i];
         pb[i] = sum;
     }
 }
 
-// gradient wrt the input of the last layer (CO = 1, no ReLU on its output):
-// gin[u][ci] = sum_{o, co} w[co][ci][o] gout[u - off(o)][co], written masked by
-// the ReLU of the layer below (in_act > 0) and rounded to BF16, the operand of
-// that layer's tensor-core passes
-template <int CI, int CO>
-__global__ void __launch_bounds__(128) k_conv_bwd_data(int B, int nz, int ny, int nx, const float *__restrict__ gout,
-                                                       const __nv_bfloat16 *__restrict__ w,
-                                                       const __nv_bfloat16 *__restrict__ in_act,
-                                                       __nv_bfloat16 *__restrict__ gin16)
+// Sum of per-block partials part[b][i], b < nblocks, in two fixed-order
+// levels: slice s (blockIdx.y) adds blocks [s per, (s + 1) per) into
+// tmp[s][i]; k_reduce_part then adds the slices.
+__global__ void k_reduce_split(int nblocks, int n, int per, const float *__restrict__ part, float *__restrict__ tmp)
 {
-    __shared__ float sw[CO * CI * 27];
-    for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) sw[i] = __bfloat162float(w[i]);
-    __syncthreads();
-    const int nv = nz * ny * nx;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= (int64_t)B * nv) return;
-    const int b = (int)(g / nv), u = (int)(g % nv);
-    float acc[CI];
-#pragma unroll
-    for (int ci = 0; ci < CI; ++ci) acc[ci] = 0.f;
-#pragma unroll 1
-    for (int o = 0; o < 27; ++o) {
-        int v;
-        if (!nb_index(u, 26 - o, nz, ny, nx, v)) continue;  // v = u - off(o)
-        const int64_t vi = (int64_t)b * nv + v;
-        float gv[CO];
-#pragma unroll
-        for (int co = 0; co < CO; ++co) gv[co] = gout[vi * CO + co];
-#pragma unroll
-        for (int ci = 0; ci < CI; ++ci)
-#pragma unroll
-            for (int co = 0; co < CO; ++co) acc[ci] = fmaf(sw[(co * CI + ci) * 27 + o], gv[co], acc[ci]);
-    }
-#pragma unroll
-    for (int ci = 0; ci < CI; ++ci)
-        gin16[g * CI + ci] = __float2bfloat16_rn(__bfloat162float(in_act[g * CI + ci]) > 0.f ? acc[ci] : 0.f);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, sl = blockIdx.y;
+    if (i >= n) return;
+    const int b0 = sl * per, b1 = min(nblocks, b0 + per);
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b) s += part[(int64_t)b * n + i];
+    tmp[(int64_t)sl * n + i] = s;
 }
 
 __global__ void k_reduce_part(int nblocks, int n, const float *__restrict__ part, float *__restrict__ out)
@@ -983,7 +837,7 @@ struct mf_cnn {
 namespace {
 
 // persistent grid: at most 8 blocks per SM
-unsigned conv_grid(int64_t items, int per_block)
+int num_sms()
 {
     static int sms = 0;
     if (!sms) {
@@ -992,7 +846,14 @@ unsigned conv_grid(int64_t items, int per_block)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + per_block - 1) / per_block, (int64_t)sms * 8));
+    return sms;
+}
+
+// blocks for items / per_block work units, at most blocks_per_sm per SM
+unsigned conv_grid(int64_t items, int per_block, int blocks_per_sm = 8)
+{
+    return (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((items + per_block - 1) / per_block, (int64_t)num_sms() * blocks_per_sm));
 }
 
 struct Acts {
@@ -1032,26 +893,294 @@ mf_status ensure_ws(mf_cnn *c, int B, int nv, bool train, Acts *A, cudaStream_t 
     return MF_OK;
 }
 
+// First layer, 2 -> 16 channels, ReLU, BF16 out, on the tensor cores.  One
+// warp per x-run of 16 nodes, M = 16 nodes, N = 2 x 8 output channels; K packs
+// two (dz, dy) rows of 8 values each (dx = 0..3 x 2 channels, dx = 3 with zero
+// weight), so 9 rows take 5 m16n8k16 steps per n-tile.  A node's two input
+// channels are one 32-bit word, so every A fragment register is one shared
+// load from the staged rows (18 words per row, nodes xb - 1 .. xb + 16);
+// the B fragments (weights) stay in registers.  Each warp keeps WF_DEPTH - 1
+// runs in flight (cp.async).
+constexpr int C1_ROWW = 18;                // words per staged row
+constexpr int C1_STAGE = 9 * C1_ROWW * 4;  // bytes per run
+
+__global__ void __launch_bounds__(CV_WARPS * 32) k_conv_first_tc(int B, int nz, int ny, int nx,
+                                                                const __nv_bfloat16 *__restrict__ xin,
+                                                                const __nv_bfloat16 *__restrict__ w,
+                                                                const float *__restrict__ bias,
+                                                                __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ __align__(16) uint32_t stg[CV_WARPS][WF_DEPTH][9 * C1_ROWW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // B[k][n]: k = 8 (row parity) + 2 dx + ci, n = co (n-tile nt)
+    uint32_t bw[5][2][2];
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int r = 2 * j + q, co = nt * 8 + g;
+                uint32_t v = 0u;
+                if (r < 9 && t < 3) {
+                    const int o = 3 * r + t;  // source layout [co][ci][o]
+                    v = (uint32_t)__bfloat16_as_ushort(w[(co * 2 + 0) * 27 + o]) |
+                        ((uint32_t)__bfloat16_as_ushort(w[(co * 2 + 1) * 27 + o]) << 16);
+                }
+                bw[j][nt][q] = v;
+            }
+    float bs[2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        bs[nt][0] = bias[nt * 8 + 2 * t];
+        bs[nt][1] = bias[nt * 8 + 2 * t + 1];
+    }
+    const uint32_t base_a = (uint32_t)__cvta_generic_to_shared(stg[warp][0]);
+    const uint32_t *xw = reinterpret_cast<const uint32_t *>(xin);
+    const int xt = (nx + 15) / 16;
+    const int runs = B * nz * ny * xt;
+    const int nv = nz * ny * nx;
+    const int stride = gridDim.x * CV_WARPS;
+    auto stage = [&](const RunPos &p, uint32_t dst) {
+        const int64_t bo = (int64_t)p.b * nv;
+        for (int c = lane; c < 9 * C1_ROWW; c += 32) {
+            const int r = c / C1_ROWW, k = c - r * C1_ROWW;
+            const int zz = p.z + r / 3 - 1, yy = p.y + r % 3 - 1, x = p.xb - 1 + k;
+            const bool v = zz >= 0 && zz < nz && yy >= 0 && yy < ny && x >= 0 && x < nx;
+            cp_async4(dst + c * 4, v ? xw + bo + ((int64_t)zz * ny + yy) * nx + x : xw, v);
+        }
+    };
+    static_assert(WF_DEPTH == 3, "two runs in flight: q0 (computing), q1 (staged)");
+    int run = blockIdx.x * CV_WARPS + warp;
+    RunPos q0 = run_pos(run < runs ? run : 0, xt, ny, nz);
+    if (run < runs) stage(q0, base_a);
+    cp_async_commit();
+    RunPos q1 = run_pos(run + stride < runs ? run + stride : 0, xt, ny, nz);
+    if (run + stride < runs) stage(q1, base_a + C1_STAGE);
+    cp_async_commit();
+    int slot = 0;
+    for (; run < runs; run += stride) {  // warp-uniform
+        const int nr = run + 2 * stride;
+        const int ns = (slot + 2) % 3;
+        RunPos q2 = q1;
+        if (nr < runs) {
+            q2 = run_pos(nr, xt, ny, nz);
+            stage(q2, base_a + ns * C1_STAGE);
+        }
+        cp_async_commit();
+        cp_async_wait<WF_DEPTH - 1>();
+        __syncwarp();
+        const uint32_t *rw = stg[warp][slot];
+        float acc[2][4] = {};
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            // A[m][k]: node m, row 2j (k < 8) or 2j + 1, dx = t, both channels: staged word m + t
+            const uint32_t *r0 = rw + (2 * j) * C1_ROWW, *r1 = rw + (2 * j + 1) * C1_ROWW;
+            const uint32_t a0 = t < 3 ? r0[g + t] : 0u, a1 = t < 3 ? r0[g + 8 + t] : 0u;
+            const uint32_t a2 = (t < 3 && j < 4) ? r1[g + t] : 0u, a3 = (t < 3 && j < 4) ? r1[g + 8 + t] : 0u;
+            mma16816(acc[0], a0, a1, a2, a3, bw[j][0][0], bw[j][0][1]);
+            mma16816(acc[1], a0, a1, a2, a3, bw[j][1][0], bw[j][1][1]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xx = q0.xb + g + 8 * h;
+            if (xx >= nx) continue;
+            const int64_t v = (int64_t)q0.b * nv + ((int64_t)q0.z * ny + q0.y) * nx + xx;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                __nv_bfloat162 pr;
+                pr.x = __float2bfloat16_rn(fmaxf(acc[nt][2 * h] + bs[nt][0], 0.f));
+                pr.y = __float2bfloat16_rn(fmaxf(acc[nt][2 * h + 1] + bs[nt][1], 0.f));
+                *reinterpret_cast<__nv_bfloat162 *>(out + v * 16 + nt * 8 + 2 * t) = pr;
+            }
+        }
+        __syncwarp();  // every lane done with this slot before it is refilled
+        q0 = q1;
+        q1 = q2;
+        slot = (slot + 1) % 3;
+    }
+    cp_async_wait<0>();
+}
+
+// Gradient wrt the input of the last layer (16 -> 1, no ReLU on its output),
+// on the tensor cores: with v - off(o) = v + off(26 - o),
+//   gin[v][ci] = sum_o w[0][ci][o] gy[v - off(o)] = sum_o' w[0][ci][26 - o'] gy[v + off(o')],
+// written masked by the ReLU of the layer below (act > 0) and rounded to BF16.
+// One warp per x-run: M = 16 nodes, N = 2 x 8 channels, K = the 27 offsets o'
+// = 3 r + dx, 15 per m16n8k16 step (5 rows x 3 dx, the 16th column zero), so
+// 2 steps per n-tile; A[m][k] = gy (rounded to BF16) at staged row r, node m +
+// dx; the B fragments stay in registers.  Staging as k_conv_first_tc (FP32
+// words instead of channel pairs).
+__global__ void __launch_bounds__(CV_WARPS * 32) k_conv_bwd_last_tc(int B, int nz, int ny, int nx,
+                                                                   const float *__restrict__ gy,
+                                                                   const __nv_bfloat16 *__restrict__ w,
+                                                                   const __nv_bfloat16 *__restrict__ act,
+                                                                   __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ __align__(16) float stg[CV_WARPS][3][9 * C1_ROWW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // this lane's four K positions per step: 2t, 2t + 1 (registers a0 / a1, b0)
+    // and 2t + 8, 2t + 9 (a2 / a3, b1); position k of step s is o' = 15 s + k
+    // (k < 15), staged at row o' / 3, node offset o' % 3
+    int aoff[2][4];
+    bool aval[2][4];
+    uint32_t bw[2][2][2];
+#pragma unroll
+    for (int st = 0; st < 2; ++st) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 2 * t + (q & 1) + 8 * (q >> 1), op = 15 * st + k;
+            aval[st][q] = k < 15 && op < 27;
+            aoff[st][q] = aval[st][q] ? (op / 3) * C1_ROWW + op % 3 : 0;
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {  // b0 (positions 2t, 2t + 1) and b1 (2t + 8, 2t + 9)
+                const int ci = nt * 8 + g;
+                uint32_t v = 0u;
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    if (aval[st][2 * hh + j]) {
+                        const int op = 15 * st + 2 * t + j + 8 * hh;
+                        v |= (uint32_t)__bfloat16_as_ushort(w[ci * 27 + 26 - op]) << (16 * j);
+                    }
+                bw[st][nt][hh] = v;
+            }
+    }
+    const uint32_t base_a = (uint32_t)__cvta_generic_to_shared(stg[warp][0]);
+    const int xt = (nx + 15) / 16;
+    const int runs = B * nz * ny * xt;
+    const int nv = nz * ny * nx;
+    const int stride = gridDim.x * CV_WARPS;
+    auto stage = [&](const RunPos &p, uint32_t dst) {
+        const int64_t bo = (int64_t)p.b * nv;
+        for (int c = lane; c < 9 * C1_ROWW; c += 32) {
+            const int r = c / C1_ROWW, k = c - r * C1_ROWW;
+            const int zz = p.z + r / 3 - 1, yy = p.y + r % 3 - 1, x = p.xb - 1 + k;
+            const bool v = zz >= 0 && zz < nz && yy >= 0 && yy < ny && x >= 0 && x < nx;
+            cp_async4(dst + c * 4, v ? gy + bo + ((int64_t)zz * ny + yy) * nx + x : gy, v);
+        }
+    };
+    int run = blockIdx.x * CV_WARPS + warp;
+    RunPos q0 = run_pos(run < runs ? run : 0, xt, ny, nz);
+    if (run < runs) stage(q0, base_a);
+    cp_async_commit();
+    RunPos q1 = run_pos(run + stride < runs ? run + stride : 0, xt, ny, nz);
+    if (run + stride < runs) stage(q1, base_a + C1_STAGE);
+    cp_async_commit();
+    int slot = 0;
+    for (; run < runs; run += stride) {  // warp-uniform
+        const int nr = run + 2 * stride;
+        RunPos q2 = q1;
+        if (nr < runs) {
+            q2 = run_pos(nr, xt, ny, nz);
+            stage(q2, base_a + ((slot + 2) % 3) * C1_STAGE);
+        }
+        cp_async_commit();
+        cp_async_wait<2>();
+        __syncwarp();
+        const float *rw = stg[warp][slot];
+        float acc[2][4] = {};
+#pragma unroll
+        for (int st = 0; st < 2; ++st) {
+            uint32_t a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // a0 / a2: node g; a1 / a3: node g + 8 (positions from aoff pairs)
+                const int m = (q & 1) ? g + 8 : g;
+                const int p0 = (q >> 1) * 2;  // first position of the pair
+                const float lo = aval[st][p0] ? rw[aoff[st][p0] + m] : 0.f;
+                const float hi = aval[st][p0 + 1] ? rw[aoff[st][p0 + 1] + m] : 0.f;
+                a[q] = pack_bf16(lo, hi);
+            }
+            mma16816(acc[0], a[0], a[1], a[2], a[3], bw[st][0][0], bw[st][0][1]);
+            mma16816(acc[1], a[0], a[1], a[2], a[3], bw[st][1][0], bw[st][1][1]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xx = q0.xb + g + 8 * h;
+            if (xx >= nx) continue;
+            const int64_t v = (int64_t)q0.b * nv + ((int64_t)q0.z * ny + q0.y) * nx + xx;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int n = nt * 8 + 2 * t;
+                const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(act + v * 16 + n);
+                __nv_bfloat162 pr;
+                pr.x = __float2bfloat16_rn(__bfloat162float(m.x) > 0.f ? acc[nt][2 * h] : 0.f);
+                pr.y = __float2bfloat16_rn(__bfloat162float(m.y) > 0.f ? acc[nt][2 * h + 1] : 0.f);
+                *reinterpret_cast<__nv_bfloat162 *>(out + v * 16 + n) = pr;
+            }
+        }
+        __syncwarp();  // every lane done with this slot before it is refilled
+        q0 = q1;
+        q1 = q2;
+        slot = (slot + 1) % 3;
+    }
+    cp_async_wait<0>();
+}
+
+// One layer with 16 input channels on the tensor cores (mode: a 16 -> 16
+// forward, a 16 -> 16 input gradient, or the 16 -> 1 last layer into yout):
+// persistent, two blocks of CV_WARPS warps per SM.
+void conv16(int mode, int B, int nz, int ny, int nx, const __nv_bfloat16 *in, const __nv_bfloat16 *w,
+            const float *bias, const __nv_bfloat16 *act, __nv_bfloat16 *out, float *yout, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_conv16_tc<CV_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+        cudaFuncSetAttribute(k_conv16_tc<CV_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+        cudaFuncSetAttribute(k_conv16_tc<CV_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+        attr = true;
+    }
+    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
+    const unsigned grid = conv_grid(runs, CV_WARPS, 2);
+    if (mode == CV_BWD)
+        k_conv16_tc<CV_BWD><<<grid, CV_WARPS * 32, CV_SMEM, st>>>(B, nz, ny, nx, in, w, bias, act, out, yout);
+    else if (mode == CV_LAST)
+        k_conv16_tc<CV_LAST><<<grid, CV_WARPS * 32, CV_SMEM, st>>>(B, nz, ny, nx, in, w, bias, act, out, yout);
+    else
+        k_conv16_tc<CV_FWD><<<grid, CV_WARPS * 32, CV_SMEM, st>>>(B, nz, ny, nx, in, w, bias, act, out, yout);
+}
+
 void forward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, Acts &A, cudaStream_t st)
 {
     const __nv_bfloat16 *W = c->pb;
     const float *P = c->p;
-    const int64_t tot = (int64_t)B * nz * ny * nx;
-    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
     mf_prof_begin("cnn_conv1", st);
-    k_conv_first<<<conv_grid(tot, 256), 256, 0, st>>>(B, nz, ny, nx, x, W + p_offset_w(0), P + p_offset_b(0), A.a1);
+    k_conv_first_tc<<<conv_grid(B * nz * ny * ((nx + 15) / 16), CV_WARPS, 3), CV_WARPS * 32, 0, st>>>(
+        B, nz, ny, nx, x, W + p_offset_w(0), P + p_offset_b(0), A.a1);
     mf_prof_end(st);
     mf_prof_begin("cnn_conv2", st);
-    k_conv16_mma<true><<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, A.a1, W + p_offset_w(1), P + p_offset_b(1),
-                                                           A.a2);
+    conv16(CV_FWD, B, nz, ny, nx, A.a1, W + p_offset_w(1), P + p_offset_b(1), nullptr, A.a2, nullptr, st);
     mf_prof_end(st);
     mf_prof_begin("cnn_conv3", st);
-    k_conv16_mma<true><<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, A.a2, W + p_offset_w(2), P + p_offset_b(2),
-                                                           A.a3);
+    conv16(CV_FWD, B, nz, ny, nx, A.a2, W + p_offset_w(2), P + p_offset_b(2), nullptr, A.a3, nullptr, st);
     mf_prof_end(st);
     mf_prof_begin("cnn_conv4", st);
-    k_conv_last<<<conv_grid(tot, 256), 256, 0, st>>>(B, nz, ny, nx, A.a3, W + p_offset_w(3), P + p_offset_b(3), A.y);
+    conv16(CV_LAST, B, nz, ny, nx, A.a3, W + p_offset_w(3), P + p_offset_b(3), nullptr, nullptr, A.y, st);
     mf_prof_end(st);
+}
+
+// Blocks for a weight-gradient kernel: one wave at its occupancy, leaving
+// RED_SLICES rows of the partial buffer for the first reduction level.
+constexpr int RED_SLICES = 16;
+
+template <typename K>
+int wgrad_blocks(K kernel, int threads, int runs, const Acts &A)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ < 1) occ = 1;
+    return std::max(1, std::min({runs, occ * num_sms(), A.wparts - RED_SLICES}));
+}
+
+// out[i] = sum_b part[b][i] over nblocks partials of n values (deterministic)
+void reduce_parts(int nblocks, int n, float *part, float *out, cudaStream_t st)
+{
+    const int per = (nblocks + RED_SLICES - 1) / RED_SLICES;
+    float *tmp = part + (int64_t)nblocks * n;
+    k_reduce_split<<<dim3(nblk(n, 128), RED_SLICES), 128, 0, st>>>(nblocks, n, per, part, tmp);
+    k_reduce_part<<<nblk(n, 128), 128, 0, st>>>(RED_SLICES, n, tmp, out);
 }
 
 // Weight gradient of a 16 -> 16 layer (index l) from its input activations
@@ -1059,62 +1188,61 @@ void forward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, A
 void bwd_weight16(mf_cnn *c, int l, int B, int nz, int ny, int nx, const __nv_bfloat16 *in,
                   const __nv_bfloat16 *g16, Acts &A, cudaStream_t st)
 {
-    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
-    const int64_t chunk = (runs + A.wparts - 1) / A.wparts;
-    const int nblocks = (int)((runs + chunk - 1) / chunk);
+    const int runs = B * nz * ny * ((nx + 15) / 16);
+    const int nb = wgrad_blocks(k_conv16_mma_wgrad, WG_WARPS * 32, runs, A);
+    const int chunk = (runs + nb - 1) / nb;
+    const int nblocks = (runs + chunk - 1) / chunk;
     static const char *names[4] = {"cnn_bwd_weight1", "cnn_bwd_weight2", "cnn_bwd_weight3", "cnn_bwd_weight4"};
     mf_prof_begin(names[l], st);
     k_conv16_mma_wgrad<<<nblocks, WG_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, in, g16, A.part);
-    const int n = 16 * 16 * 27 + 16;
-    k_reduce_part<<<nblk(n, 128), 128, 0, st>>>(nblocks, n, A.part, c->g + p_offset_w(l));
+    reduce_parts(nblocks, 16 * 16 * 27 + 16, A.part, c->g + p_offset_w(l), st);
     mf_prof_end(st);
 }
 
-// Backward pass.  The gradients entering layers 3, 2 and 1 are kept in BF16,
-// masked by their ReLU (gA, gB, gA), as the tensor-core kernels take them.
 // Weight gradient of the first (2 -> 16, l = 0) or last (16 -> 1, l = 3)
 // layer on the tensor cores.
 void bwd_weight_edge(mf_cnn *c, int l, int B, int nz, int ny, int nx, const __nv_bfloat16 *in,
                      const __nv_bfloat16 *g16, const float *gy, Acts &A, cudaStream_t st)
 {
-    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
-    const int64_t chunk = (runs + A.wparts - 1) / A.wparts;
-    const int nblocks = (int)((runs + chunk - 1) / chunk);
+    const int runs = B * nz * ny * ((nx + 15) / 16);
+    const int nb = l == 0 ? wgrad_blocks(k_wgrad_edge<false>, WF_WARPS * 32, runs, A)
+                          : wgrad_blocks(k_wgrad_edge<true>, WF_WARPS * 32, runs, A);
+    const int chunk = (runs + nb - 1) / nb;
+    const int nblocks = (runs + chunk - 1) / chunk;
     static const char *names[4] = {"cnn_bwd_weight1", "cnn_bwd_weight2", "cnn_bwd_weight3", "cnn_bwd_weight4"};
     mf_prof_begin(names[l], st);
     int n;
     if (l == 0) {
-        k_wgrad_first<<<nblocks, WF_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, in, g16, A.part);
+        k_wgrad_edge<false><<<nblocks, WF_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, g16, in, A.part);
         n = 16 * 2 * 27 + 16;
     } else {
-        k_wgrad_last<<<nblocks, WF_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, in, gy, A.part);
+        k_wgrad_edge<true><<<nblocks, WF_WARPS * 32, 0, st>>>(B, nz, ny, nx, chunk, in, gy, A.part);
         n = 16 * 27 + 1;
     }
-    k_reduce_part<<<nblk(n, 128), 128, 0, st>>>(nblocks, n, A.part, c->g + p_offset_w(l));
+    reduce_parts(nblocks, n, A.part, c->g + p_offset_w(l), st);
     mf_prof_end(st);
 }
 
 void backward(mf_cnn *c, int B, int nz, int ny, int nx, const __nv_bfloat16 *x, const float *gy, Acts &A,
               cudaStream_t st)
 {
-    const int64_t tot = (int64_t)B * nz * ny * nx;
-    const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
     const __nv_bfloat16 *W = c->pb;
     __nv_bfloat16 *gA = A.gA, *gB = A.gB;
     // layer 4 (no ReLU): dL/dy = gy; gradient wrt a3, masked by a3 > 0 -> gA
     bwd_weight_edge(c, 3, B, nz, ny, nx, A.a3, nullptr, gy, A, st);
     mf_prof_begin("cnn_bwd_data4", st);
-    k_conv_bwd_data<16, 1><<<nblk(tot, 128), 128, 0, st>>>(B, nz, ny, nx, gy, W + p_offset_w(3), A.a3, gA);
+    k_conv_bwd_last_tc<<<conv_grid(B * nz * ny * ((nx + 15) / 16), CV_WARPS, 3), CV_WARPS * 32, 0, st>>>(
+        B, nz, ny, nx, gy, W + p_offset_w(3), A.a3, gA);
     mf_prof_end(st);
     // layer 3: input a2; gradient wrt a2, masked by a2 > 0 -> gB
     bwd_weight16(c, 2, B, nz, ny, nx, A.a2, gA, A, st);
     mf_prof_begin("cnn_bwd_data3", st);
-    k_conv16_mma_bwd<<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, gA, W + p_offset_w(2), A.a2, gB);
+    conv16(CV_BWD, B, nz, ny, nx, gA, W + p_offset_w(2), nullptr, A.a2, gB, nullptr, st);
     mf_prof_end(st);
     // layer 2: input a1; gradient wrt a1, masked by a1 > 0 -> gA
     bwd_weight16(c, 1, B, nz, ny, nx, A.a1, gB, A, st);
     mf_prof_begin("cnn_bwd_data2", st);
-    k_conv16_mma_bwd<<<conv_grid(runs, 8), 256, 0, st>>>(B, nz, ny, nx, gB, W + p_offset_w(1), A.a1, gA);
+    conv16(CV_BWD, B, nz, ny, nx, gB, W + p_offset_w(1), nullptr, A.a1, gA, nullptr, st);
     mf_prof_end(st);
     // layer 1 (input gradient not needed)
     bwd_weight_edge(c, 0, B, nz, ny, nx, x, gA, nullptr, A, st);
@@ -1186,7 +1314,7 @@ extern "C" mf_status mf_cnn_get_grads(const mf_cnn *c, float *host, int64_t n)
 extern "C" mf_status mf_cnn_forward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
                                     float *y, void *stream)
 {
-    if (!c || !x || !y || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)nz * ny * nx > INT32_MAX / 16 ||
+    if (!c || !x || !y || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)B * nz * ny * nx > INT32_MAX / 16 ||
         (reinterpret_cast<uintptr_t>(x) & 3))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_forward: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1204,7 +1332,7 @@ extern "C" mf_status mf_cnn_forward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny
 extern "C" mf_status mf_cnn_backward(mf_cnn *c, int32_t B, int32_t nz, int32_t ny, int32_t nx, const void *x,
                                      const float *gy, void *stream)
 {
-    if (!c || !x || !gy || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)nz * ny * nx > INT32_MAX / 16 ||
+    if (!c || !x || !gy || B <= 0 || nz <= 0 || ny <= 0 || nx <= 0 || (int64_t)B * nz * ny * nx > INT32_MAX / 16 ||
         (reinterpret_cast<uintptr_t>(x) & 3))
         return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_backward: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1222,7 +1350,8 @@ extern "C" mf_status mf_cnn_train_step(mf_cnn *c, int32_t B, int32_t nz, int32_t
                                        const double *const *err, const void *const *x, const uint8_t *mask,
                                        float lr, float weight_decay, double *loss, void *stream)
 {
-    if (!c || !K || !kvals || !r || !x || B <= 0 || K->n_rows != (int64_t)nz * ny * nx)
+    if (!c || !K || !kvals || !r || !x || B <= 0 || K->n_rows != (int64_t)nz * ny * nx ||
+        (int64_t)B * nz * ny * nx > INT32_MAX / 16)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_cnn_train_step: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nv = nz * ny * nx;
@@ -1340,7 +1469,7 @@ extern "C" mf_status mf_solve_fcg_cnn(const mf_csr *K, const double *d, double *
                                       void *stream)
 {
     if (!K || !d || !x || !c || !logk || K->n_rows != (int64_t)nz * ny * nx || !(tol > 0) || m_dirs < 1 ||
-        m_dirs > FCG_MAXD)
+        m_dirs > FCG_MAXD || (int64_t)nz * ny * nx > INT32_MAX / 16)
         return mf_fail(MF_ERR_INVALID_ARG, "mf_solve_fcg_cnn: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = K->n_rows;
