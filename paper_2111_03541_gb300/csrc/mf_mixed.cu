@@ -553,9 +553,13 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
                 const uint32_t it = ((k >> 1 ? iw1 : iw0) >> (16 * (k & 1))) & 0xffffu;
                 if (it == 0xffffu) continue;
                 const int sh = (k >> 1) ? sh_hi : sh_lo;
-                long long T = f2i_exact(acc[0][k]);
-#pragma unroll
-                for (int L = 1; L < 5; ++L) T = T * 256 + f2i_exact(acc[L][k]);
+                // T = sum_L acc[L] 256^(4 - L): each level is an integer below
+                // 2^22 in magnitude (at most 5 digit products of 2^16, 8 points),
+                // so the pairs (0, 1) and (2, 3) combine exactly in int32 and two
+                // wide multiply-adds finish the int64 value
+                const int hi = f2i_exact(acc[0][k]) * 256 + f2i_exact(acc[1][k]);
+                const int mid = f2i_exact(acc[2][k]) * 256 + f2i_exact(acc[3][k]);
+                const long long T = (long long)hi * 16777216ll + ((long long)mid * 256ll + f2i_exact(acc[4][k]));
                 long long v;
                 if (sh >= 0) v = T << sh;
                 else if (sh > -62) v = (T + (1ll << (-sh - 1))) >> (-sh);
