@@ -131,10 +131,9 @@ constexpr double KPP = 1.0 / 6.0 + GD / 4.0;   // P^2 / 8
 constexpr double KPM = 1.0 / 12.0;             // P M / 8 = (1 - 1/3) / 8
 constexpr double KMM = 1.0 / 6.0 - GD / 4.0;   // M^2 / 8
 // N_a(q) = (1/8) prod_k F_k: P^3/8, P^2 M/8, P M^2/8, M^3/8 (3, 2, 1, 0 matches)
-constexpr double NP3 = (1.0 + GD) * (1.0 + GD) * (1.0 + GD) / 8.0;
-constexpr double NP2 = (1.0 + GD) * (1.0 + GD) * (1.0 - GD) / 8.0;
-constexpr double NP1 = (1.0 + GD) * (1.0 - GD) * (1.0 - GD) / 8.0;
-constexpr double NP0 = (1.0 - GD) * (1.0 - GD) * (1.0 - GD) / 8.0;
+// one axis of N_a at a Gauss point: (1 + s_a s_q G) / 2, signs equal or opposite
+constexpr double NEQ = (1.0 + GD) / 2.0;
+constexpr double NOP = (1.0 - GD) / 2.0;
 
 
 __device__ __forceinline__ int f2i_exact(float x)  // |x| < 2^22, integer valued
@@ -319,21 +318,15 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 6) k_mixed_elem(
 
     // --- load vector: m_a = sum_q detJ_q N_a(q) ---
     {
-        const f2 n3 = dmul(det, DF(NP3)), n2 = dmul(det, DF(NP2)), n1 = dmul(det, DF(NP1)), n0v = dmul(det, DF(NP0));
-        f2 m[8];
+        // N_a(q) is a product over the three axes of (1 + s_a s_q G) / 2, so
+        // three butterflies over the point lanes (one per axis) turn detJ_q in
+        // lane q into m_a in lane a
+        f2 mine = det;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const int mt = __popc(~(a ^ qp) & 7);
-            m[a] = (mt == 3) ? n3 : ((mt == 2) ? n2 : ((mt == 1) ? n1 : n0v));
+        for (int m = 1; m < 8; m <<= 1) {
+            const f2 o = shfl_xor(mine, m);
+            mine = dadd(dmul(mine, DF(NEQ)), dmul(o, DF(NOP)));
         }
-#pragma unroll
-        for (int s = 1; s < 8; s <<= 1)
-#pragma unroll
-            for (int a = 0; a < 8; ++a) m[a] = dadd(m[a], shfl_xor(m[a], s));
-        f2 mine = m[0];
-#pragma unroll
-        for (int a = 1; a < 8; ++a)
-            if (qp == a) mine = m[a];
         if (valid) {
             // d_(3 n + c) += b_c m_a, n = conn[e][a], in fixed point at 2^Sd
             const double mv = (double)mine.h + (double)mine.l;
