@@ -456,12 +456,14 @@ mf_status mf_kernel_times(char *buf, size_t len);
 /* ---- Batched assembly (many thermal problems in one launch) -------------
  * Many independent thermal problems (Sec. 4.1 form) of uneven size and mixed
  * element order (P1, P2, Q1), each with its own mesh, pattern, coefficients
- * and output buffers, are assembled by two persistent launches over
- * (problem, tile) descriptors: element tiles sorted by element type, then node
- * tiles of the fixed-order gather.  The launches are captured in a CUDA graph
- * at the first mf_batch_assemble and replayed.  Each problem's K and d are
- * bitwise equal to mf_assemble's.  Tiling: elements per tile, threads per
- * element block, nodes per gather tile, resident blocks per SM (grid size). */
+ * and output buffers, are assembled by one persistent launch over a queue of
+ * (problem, tile) work items: element tiles sorted by element type, and node
+ * tiles of the fixed-order gather, each problem's node tiles queued after its
+ * element tiles (they wait, bounded, for them: MF_ERR_TIMEOUT in the status
+ * word if the wait gives up).  A counter reset and the launch are captured in
+ * a CUDA graph at the first mf_batch_assemble and replayed.  Each problem's K
+ * and d are bitwise equal to mf_assemble's.  Tiling: elements per tile,
+ * threads per block, nodes per gather tile, blocks per SM (grid size). */
 typedef struct mf_batch mf_batch;
 typedef struct {
     int32_t elem_tile;

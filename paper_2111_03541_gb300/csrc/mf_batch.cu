@@ -1,7 +1,12 @@
 // Batched assembly: many thermal problems of uneven size and mixed element
-// order (P1, P2 triangles, Q1 hexahedra) assembled by persistent launches over
-// (problem, tile) descriptors, replayed from a CUDA graph, with tile shapes
-// picked by a measuring autotuner (results cached in a small JSON file).
+// order (P1, P2 triangles, Q1 hexahedra) assembled by one persistent launch
+// over (problem, tile) work items, replayed from a CUDA graph, with tile
+// shapes picked by a measuring autotuner (results cached in a small JSON
+// file).  Blocks take items from a queue: element tiles (scratch rows) and
+// node tiles (CSR rows gathered from the scratch rows); a problem's node
+// tiles sit about two waves of blocks after its last element tile, so the
+// latency-bound gathers of finished problems overlap the FP64-bound element
+// work of later ones.
 //
 // Every element and every CSR row is computed by the same device routines as
 // the single-problem path (mf_fem.cuh), in the same order, so each problem's
@@ -58,6 +63,10 @@ struct mf_batch {
     mf_batch_tiling tiling{};
     BatchTile *etiles = nullptr, *ntiles = nullptr;
     int n_etiles = 0, n_ntiles = 0;
+    int32_t *items = nullptr;  // queue order: element tile k as k, node tile k as -(k + 1)
+    int32_t *need = nullptr;   // element tiles per problem
+    int *ctr = nullptr;        // finished element tiles per problem, then the queue head
+    int n_items = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int sm_count = 0;
@@ -66,31 +75,27 @@ struct mf_batch {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_batch_elem(const BatchProblem *__restrict__ P,
-                                                    const BatchTile *__restrict__ tiles, int n_tiles, int *status)
+constexpr int BG_WARPS = 8;        // most warps per block (shared row accumulators)
+constexpr int BQ_POLLS = 1 << 22;  // bounded wait of a node tile (about a second of 256 ns naps)
+
+__device__ __forceinline__ void batch_elem_tile(const BatchProblem &p, const BatchTile &T, int *status)
 {
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const BatchTile T = tiles[t];
-        const BatchProblem &p = P[T.prob];
-        for (int64_t i = threadIdx.x; i < T.count; i += blockDim.x) {
-            const int64_t e = T.first + i;
-            if (T.type == MF_P1_TRI) elem_thermal_p1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
-            else if (T.type == MF_P2_TRI) elem_thermal_p2(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
-            else if (p.kc_df) {
-                const double k = p.kc[e];
-                if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
-                p.kc_df[e] = f64_to_df(k);
-            } else if (!q1_translate(e, p.tr, p.kc, status))
-                elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
-        }
+    for (int64_t i = threadIdx.x; i < T.count; i += blockDim.x) {
+        const int64_t e = T.first + i;
+        if (T.type == MF_P1_TRI) elem_thermal_p1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
+        else if (T.type == MF_P2_TRI) elem_thermal_p2(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
+        else if (p.kc_df) {
+            const double k = p.kc[e];
+            if (!isfinite(k)) mf_dev_fail(status, MF_ERR_NONFINITE);
+            p.kc_df[e] = f64_to_df(k);
+        } else if (!q1_translate(e, p.tr, p.kc, status))
+            elem_thermal_q1(e, p.X, p.conn, p.kc, p.f, p.elem_inc, p.scratch, status);
     }
 }
 
-constexpr int BG_WARPS = 8;
-
 template <int NPE>
 __device__ __forceinline__ void batch_gather_tile(const BatchProblem &p, const BatchTile &T, int warp, int lane,
-                                                  double (*acc_all)[MF_MAX_DEG])
+                                                  int nwarps, double (*acc_all)[MF_MAX_DEG])
 {
     constexpr int L = th_lanes<NPE>(), G = 32 / L;
     const int grp = warp * G + lane / L;
@@ -98,30 +103,76 @@ __device__ __forceinline__ void batch_gather_tile(const BatchProblem &p, const B
     if (NPE == 8 && p.kc_df) {  // translates: the single-problem path's double-float row (every row
                                 // takes the Dirichlet branch when there is a mask: the same values)
         const float2 f_df = f64_to_df(p.f);
-        for (int64_t i = grp; i < T.count; i += BG_WARPS * G)
-            gather_row_th_q1df(T.first + i, lane & (L - 1), gmask, reinterpret_cast<float2 *>(acc_all[grp]),
-                               p.mask != nullptr, p.ptr, p.col, p.inc_ptr, p.inc, p.inc_loc, p.inc_slot, p.kref_df,
-                               p.kc_df, f_df, p.mask, p.bval, p.row_ptr, p.values, p.d);
+        for (int64_t i = grp; i < T.count; i += nwarps * G)
+            gather_row_th_q1df<true>(T.first + i, lane & (L - 1), gmask, reinterpret_cast<float2 *>(acc_all[grp]),
+                                     p.mask != nullptr, p.ptr, p.col, p.inc_ptr, p.inc, p.inc_loc, p.inc_slot,
+                                     p.kref_df, p.kc_df, f_df, p.mask, p.bval, p.row_ptr, p.values, p.d);
         return;
     }
-    for (int64_t i = grp; i < T.count; i += BG_WARPS * G)  // group-uniform
-        gather_row_th<NPE>(T.first + i, lane & (L - 1), gmask, acc_all[grp], p.ptr, p.col, p.inc_ptr, p.inc,
-                           p.inc_loc, p.inc_slot, p.scratch, p.kref, p.kc, p.f, p.mask, p.bval, p.row_ptr, p.values,
-                           p.d);
+    for (int64_t i = grp; i < T.count; i += nwarps * G)  // group-uniform
+        gather_row_th<NPE, true>(T.first + i, lane & (L - 1), gmask, acc_all[grp], p.ptr, p.col, p.inc_ptr, p.inc,
+                                 p.inc_loc, p.inc_slot, p.scratch, p.kref, p.kc, p.f, p.mask, p.bval, p.row_ptr,
+                                 p.values, p.d);
 }
 
-__global__ void __launch_bounds__(BG_WARPS * 32) k_batch_gather(const BatchProblem *__restrict__ P,
-                                                               const BatchTile *__restrict__ tiles, int n_tiles)
+// The whole batch in one persistent launch.  A block takes the next queue
+// item (one atomic per item), computes an element tile (then every thread
+// fences its stores and one thread counts the tile for its problem) or a node
+// tile (one thread first waits until all of the problem's element tiles are
+// counted, fences, and the block reads the scratch rows through L2).  Every
+// element tile of a problem comes before its node tiles in the queue, and a
+// block only waits while holding a node tile, so the tiles waited for are
+// held by running blocks that do not wait: no deadlock, whatever the number
+// of resident blocks.  The wait is bounded: after BQ_POLLS polls the launch
+// records MF_ERR_TIMEOUT and goes on.  Registers are capped at 80 per thread
+// (three blocks of 256 per SM): the element routines spill, but the
+// latency-bound gathers keep their occupancy (measured with the 512-problem
+// batch: 254 registers 30.2 ms, 128 23.2 ms, 80 22.3 ms, 64 22.3 ms).
+__global__ void __launch_bounds__(BG_WARPS * 32, 3) k_batch(const BatchProblem *__restrict__ P,
+                                                        const BatchTile *__restrict__ etiles,
+                                                        const BatchTile *__restrict__ ntiles,
+                                                        const int32_t *__restrict__ items, int n_items,
+                                                        const int32_t *__restrict__ need, int *ctr, int n_prob,
+                                                        int *status)
 {
     __shared__ double acc_all[BG_WARPS * 8][MF_MAX_DEG];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const BatchTile T = tiles[t];
-        const BatchProblem &p = P[T.prob];
-        if (T.type == MF_P1_TRI) batch_gather_tile<3>(p, T, warp, lane, acc_all);
-        else if (T.type == MF_P2_TRI) batch_gather_tile<6>(p, T, warp, lane, acc_all);
-        else batch_gather_tile<8>(p, T, warp, lane, acc_all);
-        __syncthreads();  // the next tile may give a group another node type
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int *done = ctr, *head = ctr + n_prob;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();  // every thread has read s_item before it is rewritten
+        if (it >= n_items) break;
+        const int code = items[it];
+        if (code >= 0) {
+            const BatchTile T = etiles[code];
+            batch_elem_tile(P[T.prob], T, status);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&done[T.prob], 1);
+        } else {
+            const BatchTile T = ntiles[-code - 1];
+            if (threadIdx.x == 0) {
+                const int want = need[T.prob];
+                const volatile int *dp = done + T.prob;
+                for (int polls = 0; *dp < want; ++polls) {
+                    if (polls >= BQ_POLLS) {
+                        mf_dev_fail(status, MF_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+            }
+            __syncthreads();
+            const BatchProblem &p = P[T.prob];
+            if (T.type == MF_P1_TRI) batch_gather_tile<3>(p, T, warp, lane, nwarps, acc_all);
+            else if (T.type == MF_P2_TRI) batch_gather_tile<6>(p, T, warp, lane, nwarps, acc_all);
+            else batch_gather_tile<8>(p, T, warp, lane, nwarps, acc_all);
+            __syncthreads();  // the next item may give a group another node type
+        }
     }
 }
 
@@ -129,36 +180,73 @@ void free_tiles(mf_batch *b)
 {
     cudaFree(b->etiles);
     cudaFree(b->ntiles);
+    cudaFree(b->items);
+    cudaFree(b->need);
+    cudaFree(b->ctr);
     b->etiles = b->ntiles = nullptr;
+    b->items = b->need = nullptr;
+    b->ctr = nullptr;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
 }
 
-// element tiles sorted by element type (P1, P2, Q1), node tiles in problem order
+// Work items.  Element tiles sorted by element type (P1, P2, Q1), problems in
+// order within a type; a problem's node tiles go into the queue after the
+// element tile that comes two grids of blocks after its last element tile (so
+// its element tiles are most likely finished when they are taken; one grid
+// and half a grid measured 1% and 2% slower), the rest at the end in the same
+// problem order.
 mf_status make_tiles(mf_batch *b, const mf_batch_tiling &t)
 {
     std::vector<BatchTile> et, nt;
+    std::vector<int> last(b->n, -1), order;
+    std::vector<int32_t> need(b->n, 0);
     for (int type = MF_P1_TRI; type <= MF_Q1_HEX; ++type)
         for (int i = 0; i < b->n; ++i) {
             const BatchProblem &p = b->host[i];
             if (p.elem != type) continue;
-            for (int64_t s = 0; s < p.n_el; s += t.elem_tile)
+            for (int64_t s = 0; s < p.n_el; s += t.elem_tile) {
                 et.push_back(BatchTile{i, type, s, std::min<int64_t>(t.elem_tile, p.n_el - s)});
+                ++need[i];
+            }
+            last[i] = (int)et.size() - 1;
+            order.push_back(i);
         }
-    for (int i = 0; i < b->n; ++i) {
+    std::vector<int> first_nt(b->n, 0), cnt_nt(b->n, 0);
+    for (int i : order) {
         const BatchProblem &p = b->host[i];
+        first_nt[i] = (int)nt.size();
         for (int64_t s = 0; s < p.n_nodes; s += t.node_tile)
             nt.push_back(BatchTile{i, p.elem, s, std::min<int64_t>(t.node_tile, p.n_nodes - s)});
+        cnt_nt[i] = (int)nt.size() - first_nt[i];
     }
+    const int lag = std::max(1, 2 * b->sm_count * t.grid_per_sm);
+    std::vector<int32_t> items;
+    items.reserve(et.size() + nt.size());
+    size_t next = 0;  // next problem (in `order`) whose node tiles are not queued yet
+    auto emit_nodes = [&](int i) {
+        for (int k = 0; k < cnt_nt[i]; ++k) items.push_back(-(first_nt[i] + k) - 1);
+    };
+    for (int k = 0; k < (int)et.size(); ++k) {
+        items.push_back(k);
+        while (next < order.size() && last[order[next]] + lag <= k) emit_nodes(order[next++]);
+    }
+    while (next < order.size()) emit_nodes(order[next++]);
     free_tiles(b);
-    MF_CUDA(cudaMalloc(&b->etiles, sizeof(BatchTile) * et.size()));
-    MF_CUDA(cudaMalloc(&b->ntiles, sizeof(BatchTile) * nt.size()));
+    MF_CUDA(cudaMalloc(&b->etiles, sizeof(BatchTile) * std::max<size_t>(1, et.size())));
+    MF_CUDA(cudaMalloc(&b->ntiles, sizeof(BatchTile) * std::max<size_t>(1, nt.size())));
+    MF_CUDA(cudaMalloc(&b->items, sizeof(int32_t) * std::max<size_t>(1, items.size())));
+    MF_CUDA(cudaMalloc(&b->need, sizeof(int32_t) * b->n));
+    MF_CUDA(cudaMalloc(&b->ctr, sizeof(int) * (b->n + 1)));
     MF_CUDA(cudaMemcpy(b->etiles, et.data(), sizeof(BatchTile) * et.size(), cudaMemcpyHostToDevice));
     MF_CUDA(cudaMemcpy(b->ntiles, nt.data(), sizeof(BatchTile) * nt.size(), cudaMemcpyHostToDevice));
+    MF_CUDA(cudaMemcpy(b->items, items.data(), sizeof(int32_t) * items.size(), cudaMemcpyHostToDevice));
+    MF_CUDA(cudaMemcpy(b->need, need.data(), sizeof(int32_t) * b->n, cudaMemcpyHostToDevice));
     b->n_etiles = (int)et.size();
     b->n_ntiles = (int)nt.size();
+    b->n_items = (int)items.size();
     b->tiling = t;
     return MF_OK;
 }
@@ -166,11 +254,10 @@ mf_status make_tiles(mf_batch *b, const mf_batch_tiling &t)
 void launch_batch(mf_batch *b, cudaStream_t st, int *status)
 {
     const mf_batch_tiling &t = b->tiling;
-    const int cap = b->sm_count * t.grid_per_sm;
-    k_batch_elem<<<std::max(1, std::min(b->n_etiles, cap)), t.elem_block, 0, st>>>(b->dev, b->etiles, b->n_etiles,
-                                                                                      status);
-    k_batch_gather<<<std::max(1, std::min(b->n_ntiles, cap)), BG_WARPS * 32, 0, st>>>(b->dev, b->ntiles,
-                                                                                     b->n_ntiles);
+    const int grid = std::max(1, std::min(b->n_items, b->sm_count * t.grid_per_sm));
+    cudaMemsetAsync(b->ctr, 0, sizeof(int) * (b->n + 1), st);
+    k_batch<<<grid, t.elem_block, 0, st>>>(b->dev, b->etiles, b->ntiles, b->items, b->n_items, b->need, b->ctr, b->n,
+                                           status);
 }
 
 mf_status capture(mf_batch *b, int *status)

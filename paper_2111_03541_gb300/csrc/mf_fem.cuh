@@ -1008,7 +1008,17 @@ constexpr int th_lanes() { return NPE <= 4 ? 4 : (NPE <= 8 ? 8 : (NPE <= 16 ? 16
 // constrained columns move to the right-hand side (lifting).  FP64 is the
 // scarce pipe here, so every FP64 instruction of the loop does useful work in
 // all lanes.
-template <int NPE>
+// Loads of values that the same launch wrote (element rows, coefficient
+// pairs): L2 only when a kernel both writes and reads them (the batch's single
+// persistent launch), plain loads otherwise.
+template <bool L2ONLY, typename T>
+__device__ __forceinline__ T ld_fresh(const T *p)
+{
+    if constexpr (L2ONLY) return __ldcg(p);
+    else return *p;
+}
+
+template <int NPE, bool L2ONLY = false>
 __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask, double *acc,
                                               const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
                                               const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
@@ -1044,7 +1054,7 @@ __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask
     // load vector: lane sub takes incidence entries i0 + sub, i0 + sub + L, ...
     for (int64_t t = i0 + sub; t < i1; t += L) {
         const int loc = inc_loc[t];
-        dsum += (loc & 0x80) ? f * __ldg(&kref[NPE * NPE + (loc & 0x7f)]) : sc[t * RS + NPE];
+        dsum += (loc & 0x80) ? f * __ldg(&kref[NPE * NPE + (loc & 0x7f)]) : ld_fresh<L2ONLY>(&sc[t * RS + NPE]);
     }
     for (int64_t cb = i0; cb < i1; cb += U) {
         const int cnt = (int)min((int64_t)U, i1 - cb);
@@ -1063,7 +1073,7 @@ __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask
                     mul[j] = kc[inc[t]];
                     val[j] = __ldg(&kref[(loc & 0x7f) * NPE + b]);
                 } else {
-                    val[j] = sc[t * RS + b];
+                    val[j] = ld_fresh<L2ONLY>(&sc[t * RS + b]);
                 }
             }
         }
@@ -1123,6 +1133,7 @@ __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask
 // pairs.  near_bc: the node or a neighbour is constrained (only then are the
 // columns read for the Dirichlet elimination; the FP64 lifting lives in that
 // branch alone, so an interior row issues no FP64 instruction).
+template <bool L2ONLY = false>
 __device__ __forceinline__ void gather_row_th_q1df(int64_t n, int sub, unsigned gmask, float2 *acc, bool near_bc,
                                                    const int64_t *__restrict__ adj_ptr,
                                                    const int32_t *__restrict__ adj_col,
@@ -1159,7 +1170,7 @@ __device__ __forceinline__ void gather_row_th_q1df(int64_t n, int sub, unsigned 
             if (j < cnt) {
                 const int32_t t = cb + j;
                 s[j] = inc_slot[(uint32_t)t * NPE + sub];
-                val[j] = df_mul(kc_df[inc[t]], kref_df[(inc_loc[t] & 0x7f) * NPE + sub]);
+                val[j] = df_mul(ld_fresh<L2ONLY>(&kc_df[inc[t]]), kref_df[(inc_loc[t] & 0x7f) * NPE + sub]);
             }
         }
 #pragma unroll
