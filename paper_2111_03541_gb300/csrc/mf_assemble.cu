@@ -626,6 +626,39 @@ __global__ void __launch_bounds__(GD_WARPS * 32, 8) k_gather_th_q1df(
                        inc_ptr, inc, inc_loc, inc_slot, kref_df, kc_df, f_df, mask, bval, row_ptr, values, d);
 }
 
+// Thermal Q1 (or capacity) rows on a lexicographic box of translates of a
+// rectangular cell (box_row_q1): one thread per node; a block's rows are
+// consecutive in the CSR arrays, so they are staged in shared memory and
+// stored with coalesced writes.
+constexpr int QB = 128;  // nodes (threads) per block
+
+__global__ void __launch_bounds__(QB) k_rows_q1box(int n_nodes, int nx1, int ny1, int nz1, mf_box_classes C,
+                                                   int capacity, double f, const double *__restrict__ kc,
+                                                   const uint8_t *__restrict__ mask, const uint8_t *__restrict__ bcrow,
+                                                   const double *__restrict__ bval,
+                                                   const int64_t *__restrict__ row_ptr, double *__restrict__ values,
+                                                   double *__restrict__ d, int64_t n_el, int *status)
+{
+    // the coefficients are read straight from kc: check them here
+    for (int64_t e = (int64_t)blockIdx.x * QB + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * QB)
+        if (!isfinite(kc[e])) mf_dev_fail(status, MF_ERR_NONFINITE);
+    __shared__ double stage[QB * 27];
+    __shared__ double cls[8];
+    if (threadIdx.x < 8) cls[threadIdx.x] = capacity ? C.m_cls[threadIdx.x] : C.k_cls[threadIdx.x];
+    __syncthreads();
+    const int n0 = blockIdx.x * QB, n = n0 + threadIdx.x;
+    const int nend = min(n_nodes, n0 + QB);
+    const int64_t r0 = row_ptr[n0];
+    if (n < n_nodes) {
+        double *row = stage + (row_ptr[n] - r0);
+        d[n] = box_row_q1(n, nx1, ny1, nz1, cls, capacity ? 0.0 : f * C.dref, kc, mask != nullptr && bcrow[n] != 0,
+                          mask, bval, [row](int k, double v) { row[k] = v; });
+    }
+    __syncthreads();
+    const int64_t cnt = row_ptr[nend] - r0;
+    for (int64_t i = threadIdx.x; i < cnt; i += QB) values[r0 + i] = stage[i];
+}
+
 // ---------------------------------------------------------------------------
 // elasticity gather: one warp per node, walking the node's incident elements in
 // ascending order.  Each element's 8 blocks (a_n, b) of the node's rows (72
@@ -1173,9 +1206,12 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
             k_elem_thermal_q1<<<nblk(ne, 128), 128, 0, st>>>(ne, m->coords, m->conn, c->elem_coef, f, p->tr,
                                                              p->elem_inc, p->scratch, status);
         // Q1 with translates: their coefficients as pairs for the double-float
-        // gather (the element kernel only runs for the other elements)
+        // gather (the element kernel only runs for the other elements); a
+        // lexicographic box of a rectangular cell takes its rows straight from
+        // the FP64 coefficients
         const bool q1df = m->elem == MF_Q1_HEX && p->kc_df && p->kref_df && p->bcrow && p->n_translate == ne;
-        if (q1df && ne > 0)
+        const bool q1box = q1df && p->box[0] > 0;
+        if (q1df && !q1box && ne > 0)
             k_kc_split<<<nblk(ne, 256), 256, 0, st>>>(ne, c->elem_coef, p->tr, p->kc_df, status);
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
@@ -1185,6 +1221,15 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
             if (c->bc_mask) {
                 MF_CUDA(cudaMemsetAsync(p->bcrow, 0, (size_t)A.n_rows, st));
                 k_mark_bc_rows<<<nblk(A.n_rows, 256), 256, 0, st>>>(A.n_rows, A.ptr, A.col, c->bc_mask, p->bcrow);
+            }
+            if (q1box) {
+                k_rows_q1box<<<nblk(A.n_rows, QB), QB, 0, st>>>((int)A.n_rows, p->box[0], p->box[1], p->box[2],
+                                                                p->box_cls, cap ? 1 : 0, f, c->elem_coef, c->bc_mask,
+                                                                p->bcrow, c->bc_val, p->row_ptr, values, d, ne,
+                                                                status);
+                mf_prof_end(st);
+                MF_CUDA(cudaGetLastError());
+                return MF_OK;
             }
             const float fh = (float)f;
             const float2 f_df = make_float2(fh, (float)(f - (double)fh));  // as f64_to_df

@@ -47,6 +47,10 @@ struct BatchProblem {
     // pairs (the double-float gather of the single-problem path); else null
     const float2 *kref_df;
     float2 *kc_df;
+    // a lexicographic box of a rectangular cell (every element a translate):
+    // nodes per line (box[0] > 0) and the reference entries by corner class
+    int32_t box[3];
+    mf_box_classes box_cls;
 };
 
 struct BatchTile {
@@ -100,6 +104,16 @@ __device__ __forceinline__ void batch_gather_tile(const BatchProblem &p, const B
     constexpr int L = th_lanes<NPE>(), G = 32 / L;
     const int grp = warp * G + lane / L;
     const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
+    if (NPE == 8 && p.box[0] > 0) {  // box of translates: the single-problem path's row routine, one thread
+                                     // per node (every row checks the mask: the same values)
+        for (int64_t i = threadIdx.x; i < T.count; i += blockDim.x) {
+            const int n = (int)(T.first + i);
+            double *row = p.values + p.row_ptr[n];
+            p.d[n] = box_row_q1(n, p.box[0], p.box[1], p.box[2], p.box_cls.k_cls, p.f * p.box_cls.dref, p.kc,
+                                p.mask != nullptr, p.mask, p.bval, [row](int k, double v) { row[k] = v; });
+        }
+        return;
+    }
     if (NPE == 8 && p.kc_df) {  // translates: the single-problem path's double-float row (every row
                                 // takes the Dirichlet branch when there is a mask: the same values)
         const float2 f_df = f64_to_df(p.f);
@@ -367,7 +381,8 @@ extern "C" mf_status mf_batch_create(int32_t n, const mf_mesh *const *meshes, co
                                        (m->elem == MF_Q1_HEX && p->kc_df && p->n_translate == m->n_elems)
                                            ? p->kref_df : nullptr,
                                        (m->elem == MF_Q1_HEX && p->kref_df && p->n_translate == m->n_elems)
-                                           ? p->kc_df : nullptr});
+                                           ? p->kc_df : nullptr,
+                                       {p->box[0], p->box[1], p->box[2]}, p->box_cls});
         cnt[m->elem] += m->n_elems;
         nodes += m->n_nodes;
     }

@@ -1123,6 +1123,95 @@ __device__ __forceinline__ void gather_row_th(int64_t n, int sub, unsigned gmask
     __syncwarp(gmask);
 }
 
+// One node's row of the thermal Q1 form (or its capacity form: cls = m_cls,
+// zero load) on a lexicographic box of translates of a rectangular cell
+// (mf_pattern::box).  The reference entry of two corners depends only on the
+// axes in which they differ, so entry (n, m) = cls[axes] x (sum of k_e over
+// the elements holding n and m): with the node's 8 incident coefficients k
+// (zero past the box edge), the 27 sums come from 19 FP64 adds (pairs along
+// z, y, x, then faces, then all 8), one product per entry.  The load is f
+// dref times the number of incident elements.  The entries go out in
+// ascending column order through emit(k, value), k = 0, 1, ... over the
+// existing neighbours (slot (dz + 1) 9 + (dy + 1) 3 + (dx + 1) order), so no
+// row is held in registers; the load entry is returned.
+// With near_bc (the node or a neighbour constrained; any row may pass true)
+// Dirichlet rows become identity rows and constrained columns move to the
+// right-hand side (lifting, in ascending column order); other rows give the
+// same values either way.
+template <typename Emit>
+__device__ __forceinline__ double box_row_q1(int n, int nx1, int ny1, int nz1, const double *__restrict__ cls,
+                                             double dref_f, const double *__restrict__ kc, bool near_bc,
+                                             const uint8_t *__restrict__ mask, const double *__restrict__ bval,
+                                             Emit emit)
+{
+    const int S = nx1 * ny1;
+    const int z = n / S, y = (n - z * S) / nx1, x = n - z * S - y * nx1;
+    const int nx = nx1 - 1, ny = ny1 - 1, nz = nz1 - 1;
+    double k[2][2][2];  // [ez][ey][ex]: element (x - 1 + ex, y - 1 + ey, z - 1 + ez)
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int ex = c & 1, ey = (c >> 1) & 1, ez = c >> 2;
+        const int cx = x - 1 + ex, cy = y - 1 + ey, cz = z - 1 + ez;
+        const bool ok = cx >= 0 && cx < nx && cy >= 0 && cy < ny && cz >= 0 && cz < nz;
+        k[ez][ey][ex] = ok ? kc[cx + nx * (cy + ny * cz)] : 0.0;
+        cnt += ok ? 1 : 0;
+    }
+    // s[iz][iy][ix]: index 0 / 1 one element layer (the - / + side), 2 both
+    double sm[3][3][3];
+#pragma unroll
+    for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+        for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+            for (int ex = 0; ex < 2; ++ex) sm[ez][ey][ex] = k[ez][ey][ex];
+#pragma unroll
+    for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+        for (int ex = 0; ex < 2; ++ex) sm[2][ey][ex] = k[0][ey][ex] + k[1][ey][ex];
+#pragma unroll
+    for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+        for (int ex = 0; ex < 2; ++ex) sm[ez][2][ex] = k[ez][0][ex] + k[ez][1][ex];
+#pragma unroll
+    for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+        for (int ey = 0; ey < 2; ++ey) sm[ez][ey][2] = k[ez][ey][0] + k[ez][ey][1];
+#pragma unroll
+    for (int ex = 0; ex < 2; ++ex) sm[2][2][ex] = sm[2][0][ex] + sm[2][1][ex];
+#pragma unroll
+    for (int ey = 0; ey < 2; ++ey) sm[2][ey][2] = sm[2][ey][0] + sm[2][ey][1];
+#pragma unroll
+    for (int ez = 0; ez < 2; ++ez) sm[ez][2][2] = sm[ez][2][0] + sm[ez][2][1];
+    sm[2][2][2] = sm[2][2][0] + sm[2][2][1];
+    int col = 0;
+    const bool chk = near_bc && mask != nullptr;
+    const bool rm = chk ? mask[n] != 0 : false;
+    double lift = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < 27; ++sl) {
+        const int dx = sl % 3 - 1, dy = (sl / 3) % 3 - 1, dz = sl / 9 - 1;
+        const int xx = x + dx, yy = y + dy, zz = z + dz;
+        // neighbour offset -1 -> the - side layer (index 0), +1 -> index 1, 0 -> both (2)
+        const int ix = dx < 0 ? 0 : (dx > 0 ? 1 : 2), iy = dy < 0 ? 0 : (dy > 0 ? 1 : 2),
+                  iz = dz < 0 ? 0 : (dz > 0 ? 1 : 2);
+        const int axes = (dx != 0 ? 1 : 0) | (dy != 0 ? 2 : 0) | (dz != 0 ? 4 : 0);
+        if (xx < 0 || xx > nx || yy < 0 || yy > ny || zz < 0 || zz > nz) continue;
+        double val = cls[axes] * sm[iz][iy][ix];
+        if (chk) {
+            const int mcol = xx + nx1 * (yy + ny1 * zz);
+            if (rm) val = (sl == 13) ? 1.0 : 0.0;
+            else if (mask[mcol]) {
+                lift -= val * bval[mcol];
+                val = 0.0;
+            }
+        }
+        emit(col++, val);
+    }
+    const double dl = dref_f * (double)cnt;
+    return rm ? bval[n] : (lift != 0.0 ? dl + lift : dl);
+}
+
 // One node's row of the thermal Q1 form on a mesh whose elements are all
 // translates of element 0, in double-float: every entry of element e is k_e
 // times a reference entry, so the row is a sum of at most 64 products, formed

@@ -33,6 +33,14 @@ struct mf_mesh {
     int device;
 };
 
+// reference entries of a rectangular Q1 cell by corner class (see
+// mf_pattern::box): conduction k_cls, capacity m_cls, load per corner dref
+struct mf_box_classes {
+    double k_cls[8];
+    double m_cls[8];
+    double dref;
+};
+
 struct mf_pattern {
     int form;
     const mf_mesh *mesh;
@@ -87,6 +95,13 @@ struct mf_pattern {
     float2 *kref_df = nullptr;
     float2 *kc_df = nullptr;
     uint8_t *bcrow = nullptr;
+    // thermal Q1 whose elements are all translates of one rectangular cell,
+    // numbered as a lexicographic box (node (x, y, z) = x + nx1 (y + ny1 z),
+    // the element whose lowest node that is, x fastest): box = {nx1, ny1,
+    // nz1} (else zeros) and the reference entries by class, i.e. by the axes
+    // in which two corners differ (mask dx | dy << 1 | dz << 2)
+    int32_t box[3] = {0, 0, 0};
+    mf_box_classes box_cls{};
     // 20-node bricks: the vertices' trilinear-map coefficients of q1_jac_at
     // per element as FP32 pairs (hi, lo), [n_elems][8][3]
     float2 *q2s_map = nullptr;

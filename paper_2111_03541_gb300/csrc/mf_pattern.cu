@@ -10,6 +10,7 @@
 // node among the row node's neighbours), which fixes the summation order of
 // the assembly.  The dof-level CSR of a form is then laid out from its blocks.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "mf_fem.cuh"
@@ -384,6 +385,21 @@ __global__ void k_translate_flags(int64_t n_el, const double *__restrict__ X, co
 }
 
 // the reference entries as FP32 pairs
+// lexicographic box check: element e = ex + nx (ey + ny ez) must have its
+// local node a at node base(e) + off[a], base(e) = ex + nx1 (ey + ny1 ez)
+__global__ void k_box_check(int64_t n_el, const int32_t *__restrict__ conn, int nx, int ny, int nx1, int ny1,
+                            int4 off_lo, int4 off_hi, int *bad)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+    const int64_t base = ex + (int64_t)nx1 * (ey + (int64_t)ny1 * ez);
+    const int off[8] = {off_lo.x, off_lo.y, off_lo.z, off_lo.w, off_hi.x, off_hi.y, off_hi.z, off_hi.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+        if ((int64_t)conn[8 * e + a] != base + off[a]) *bad = 1;
+}
+
 __global__ void k_kref_df(const double *__restrict__ kref, float2 *__restrict__ kref_df)
 {
     const int t = threadIdx.x;
@@ -637,6 +653,81 @@ mf_status plan_slabs(const mf_mesh *m, const Incidence &inc, int64_t stride, cud
     return MF_OK;
 }
 
+// A thermal Q1 mesh whose elements are all translates: is it a lexicographic
+// box of one rectangular cell?  Element 0's node offsets give the line
+// lengths and the corner -> local index table, a device pass checks every
+// element, and the reference entries (computed in FP64 from element 0) must
+// depend on the pair of corners only through the axes in which they differ,
+// to 1e-14 of the largest entry (true of a rectangular cell; the class
+// values are those of corner 0 with corner mask).  Otherwise box stays zero.
+mf_status detect_box(const mf_mesh *m, mf_pattern *p, cudaStream_t st)
+{
+    p->box[0] = p->box[1] = p->box[2] = 0;
+    int32_t c0[8];
+    MF_CUDA(cudaMemcpyAsync(c0, m->conn, sizeof c0, cudaMemcpyDeviceToHost, st));
+    double kr[73 + 72];
+    MF_CUDA(cudaMemcpyAsync(kr, p->kref, sizeof kr, cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    int32_t lo = c0[0];
+    for (int a = 1; a < 8; ++a) lo = std::min(lo, c0[a]);
+    if (lo != 0) return MF_OK;
+    int32_t srt[8];
+    for (int a = 0; a < 8; ++a) srt[a] = c0[a];
+    std::sort(srt, srt + 8);
+    const int64_t nx1 = srt[2], S = srt[4];
+    if (nx1 < 2 || S % nx1 != 0) return MF_OK;
+    const int64_t want[8] = {0, 1, nx1, nx1 + 1, S, S + 1, S + nx1, S + nx1 + 1};
+    for (int a = 0; a < 8; ++a)
+        if (srt[a] != want[a]) return MF_OK;
+    const int64_t ny1 = S / nx1;
+    if (ny1 < 2 || m->n_nodes % S != 0) return MF_OK;
+    const int64_t nz1 = m->n_nodes / S;
+    if (nz1 < 2 || (nx1 - 1) * (ny1 - 1) * (nz1 - 1) != m->n_elems || m->n_nodes > INT32_MAX) return MF_OK;
+    int corner[8];  // corner bits (x | y << 1 | z << 2) of local node a
+    for (int a = 0; a < 8; ++a) {
+        const int64_t o = c0[a];
+        corner[a] = (int)(o % nx1) | (int)((o / nx1) % ny1) << 1 | (int)(o / S) << 2;
+    }
+    int loc_of[8];
+    for (int a = 0; a < 8; ++a) loc_of[corner[a]] = a;
+    // class constants and their check
+    double kmax = 0.0, mmax = 0.0;
+    for (int i = 0; i < 64; ++i) {
+        kmax = std::max(kmax, std::fabs(kr[i]));
+        mmax = std::max(mmax, std::fabs(kr[73 + i]));
+    }
+    mf_box_classes C{};
+    for (int cm = 0; cm < 8; ++cm) {
+        C.k_cls[cm] = kr[loc_of[0] * 8 + loc_of[cm]];
+        C.m_cls[cm] = kr[73 + loc_of[0] * 8 + loc_of[cm]];
+    }
+    C.dref = kr[64 + loc_of[0]];
+    for (int a = 0; a < 8; ++a) {
+        if (std::fabs(kr[64 + a] - C.dref) > 1e-14 * std::fabs(C.dref)) return MF_OK;
+        for (int b = 0; b < 8; ++b) {
+            const int cm = corner[a] ^ corner[b];
+            if (std::fabs(kr[a * 8 + b] - C.k_cls[cm]) > 1e-14 * kmax) return MF_OK;
+            if (std::fabs(kr[73 + a * 8 + b] - C.m_cls[cm]) > 1e-14 * mmax) return MF_OK;
+        }
+    }
+    int *bad = nullptr;
+    MF_CUDA(cudaMallocAsync(&bad, sizeof(int), st));
+    MF_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    k_box_check<<<nblk(m->n_elems), TPB, 0, st>>>(m->n_elems, m->conn, (int)(nx1 - 1), (int)(ny1 - 1), (int)nx1,
+                                                  (int)ny1, make_int4(c0[0], c0[1], c0[2], c0[3]),
+                                                  make_int4(c0[4], c0[5], c0[6], c0[7]), bad);
+    int hbad = 1;
+    MF_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    MF_CUDA(cudaFreeAsync(bad, st));
+    if (hbad) return MF_OK;
+    p->box[0] = (int32_t)nx1;
+    p->box[1] = (int32_t)ny1;
+    p->box[2] = (int32_t)nz1;
+    p->box_cls = C;
+    return MF_OK;
+}
+
 void free_inc(Incidence &I, cudaStream_t st)
 {
     if (I.ptr) cudaFreeAsync(I.ptr, st);
@@ -729,6 +820,7 @@ void mf_pattern_free(mf_pattern *p)
     p->kref_df = p->kc_df = nullptr;
     p->bcrow = nullptr;
     p->n_translate = 0;
+    p->box[0] = p->box[1] = p->box[2] = 0;
     p->slot = nullptr;
     p->mixed_state = nullptr;
     p->pinc_ptr = nullptr;
@@ -802,6 +894,10 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
                 k_kref_df<<<1, 160, 0, st>>>(p->kref, p->kref_df);
                 MF_CUDA(cudaMallocAsync(&p->kc_df, sizeof(float2) * m->n_elems, st));
                 MF_CUDA(cudaMallocAsync(&p->bcrow, (size_t)m->n_nodes, st));
+                if ((int64_t)h == m->n_elems) {
+                    s = detect_box(m, p, st);
+                    if (s != MF_OK) { free_inc(incv, st); return s; }
+                }
             }
         }
     } else if (form == MF_FORM_ELASTIC && m->elem == MF_Q2S_HEX) {

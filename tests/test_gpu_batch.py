@@ -38,6 +38,9 @@ def test_batch_matches_single_problem_path_bitwise(mf, orc, tmp_path):
     # unjittered Q1 boxes (every element a translate of element 0) in the mix
     probs.insert(3, gen.thermal_q1_problem(6, jitter=0.0))
     probs.append(gen.thermal_q1_problem(9, jitter=0.0))
+    # power-of-two boxes: exact translates of a cubic cell (the box row routine)
+    probs.insert(5, gen.thermal_q1_problem(8, jitter=0.0))
+    probs.append(gen.thermal_q1_problem(16, jitter=0.0))
     single = []
     for pr in probs:
         P = mf.Problem(pr)

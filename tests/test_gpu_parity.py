@@ -40,6 +40,20 @@ def _partly_jittered_q1(n):
     return prob
 
 
+def _box_q1(n, scale=(1.0, 1.0, 1.0), shear=0.0):
+    """Unjittered Q1 box of side h = 1/n, n a power of two so that every
+    element is an exact translate of element 0; ``scale`` stretches the axes
+    by powers of two (a rectangular cell, still exact), ``shear`` adds shear *
+    y to x (a sheared cell: translates, but not class-constant reference
+    entries)."""
+    prob = gen.thermal_q1_problem(n, jitter=0.0)
+    X = prob["coords"].copy()
+    X[:, 0] += shear * X[:, 1]
+    X *= np.asarray(scale)
+    prob["coords"] = X
+    return prob
+
+
 CASES = {
     "p1_64": lambda: gen.thermal_p1_problem(64),
     "p1_13": lambda: gen.thermal_p1_problem(13),
@@ -47,6 +61,9 @@ CASES = {
     "q1_9": lambda: gen.thermal_q1_problem(9),
     "q1_affine_11": lambda: gen.thermal_q1_problem(11, jitter=0.0),
     "q1_partly_translate_10": lambda: _partly_jittered_q1(10),
+    "q1_box_16": lambda: _box_q1(16),
+    "q1_box_rect_8": lambda: _box_q1(8, scale=(1.0, 0.5, 2.0)),
+    "q1_box_sheared_8": lambda: _box_q1(8, shear=0.25),
     "el_7": lambda: gen.elastic_problem(7),
     "el_12": lambda: gen.elastic_problem(12),
     "os_9": lambda: gen.oseen_problem(9),
@@ -88,7 +105,7 @@ def test_pattern_and_values(mf, orc, case):
     assert np.abs(d - ref["d"]).max() <= TOL * np.abs(ref["d"]).max()
 
 
-@pytest.mark.parametrize("case", ["p1_13", "q1_9", "el_7", "os_9"])
+@pytest.mark.parametrize("case", ["p1_13", "q1_9", "q1_box_16", "el_7", "os_9"])
 def test_values_without_dirichlet(mf, orc, case):
     prob = CASES[case]()
     P, rp, ci, val, d = _gpu(mf, prob, bc=False)
@@ -107,8 +124,9 @@ def test_assembly_bit_reproducible(mf, case):
     assert torch.equal(v1, v2) and torch.equal(d1, d2)
 
 
-def test_nonzero_dirichlet_values_lifted(mf, orc):
-    prob = gen.thermal_q1_problem(6)
+@pytest.mark.parametrize("case", ["q1_6", "q1_box_8"])
+def test_nonzero_dirichlet_values_lifted(mf, orc, case):
+    prob = gen.thermal_q1_problem(6) if case == "q1_6" else _box_q1(8)
     rng = np.random.default_rng(7)
     prob["bc_val"] = np.where(prob["bc_mask"] > 0, rng.normal(size=prob["bc_mask"].shape), 0.0)
     P, rp, ci, val, d = _gpu(mf, prob)

@@ -46,6 +46,7 @@ CAP = {
     "q1_8": lambda: gen.thermal_q1_problem(8),
     "q1_affine_11": lambda: gen.thermal_q1_problem(11, jitter=0.0),
     "q1_partly_translate_10": lambda: _partly_jittered_q1(10),
+    "q1_box_16": lambda: gen.thermal_q1_problem(16, jitter=0.0),  # exact translates of a cube: box rows
 }
 
 
@@ -86,8 +87,9 @@ def test_capacity_parity(mf, orc, case):
     assert np.abs(d.cpu().numpy()).max() == 0.0
 
 
-def test_capacity_with_dirichlet(mf, orc):
-    prob = gen.thermal_q1_problem(6)
+@pytest.mark.parametrize("n,jitter", [(6, 0.15), (8, 0.0)])
+def test_capacity_with_dirichlet(mf, orc, n, jitter):
+    prob = gen.thermal_q1_problem(n, jitter=jitter)
     prob["bc_val"] = np.where(prob["bc_mask"] > 0, gen.normal(9, prob["bc_mask"].shape[0]), 0.0)
     C = gen.lognormal(78, prob["conn"].shape[0], 0.3)
     P = mf.Problem(prob)
