@@ -820,8 +820,15 @@ def suite(dev):
     P = mf.Problem(prob, device=dev)
     ms = _ev_time(lambda: P.assemble(), reps=5)
     _, pcg = _solve_timed(P, tol=1e-8, max_iter=100000, check_every=100)
+    # the same algorithmic bytes as the C1 line: K values written once, d,
+    # coordinates, connectivity, coefficients and Dirichlet data, over the
+    # whole assembly's time against the measured copy peak
+    c4_bytes = 8 * P.nnz + 8 * P.n + prob["coords"].nbytes + prob["conn"].nbytes + prob["coef"].nbytes + \
+        prob["bc_mask"].nbytes + prob["bc_val"].nbytes
     c4 = {"elements": int(prob["conn"].shape[0]), "n_dofs": int(P.n), "assemble_ms": ms,
-          "elements_per_s": prob["conn"].shape[0] / (ms * 1e-3), "jacobi_pcg": pcg}
+          "elements_per_s": prob["conn"].shape[0] / (ms * 1e-3), "algorithmic_bytes": int(c4_bytes),
+          "assembly_hbm_frac": c4_bytes / (ms * 1e-3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
+          "jacobi_pcg": pcg}
     wpath = os.path.join(ROOT, "paper_2111_03541_gb300", "weights", "cnn_q1_thermal.f32")
     if os.path.exists(wpath):
         from paper_2111_03541_gb300 import learned
