@@ -1126,13 +1126,14 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_conv_bwd_last_tc(int B, int n
 void conv16(int mode, int B, int nz, int ny, int nx, const __nv_bfloat16 *in, const __nv_bfloat16 *w,
             const float *bias, const __nv_bfloat16 *act, __nv_bfloat16 *out, float *yout, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_conv16_tc<CV_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+    // the attribute is per device: set on every call (a host-side call of a
+    // few microseconds; a failure surfaces as the launch's error)
+    if (mode == CV_BWD)
         cudaFuncSetAttribute(k_conv16_tc<CV_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+    else if (mode == CV_LAST)
         cudaFuncSetAttribute(k_conv16_tc<CV_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
-        attr = true;
-    }
+    else
+        cudaFuncSetAttribute(k_conv16_tc<CV_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
     const int64_t runs = (int64_t)B * nz * ny * ((nx + 15) / 16);
     const unsigned grid = conv_grid(runs, CV_WARPS, 2);
     if (mode == CV_BWD)
