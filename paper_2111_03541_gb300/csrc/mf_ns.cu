@@ -1,7 +1,8 @@
 // Steady Navier-Stokes with SUPG on Taylor-Hood P2-P1 triangles (Sec. 4.3),
 // linearised by Newton-Raphson (Sec. 2.1): the element residual and its
-// tangent in FP64, node-centric gathers into the full-block CSR pattern, and
-// the Newton loop on the device.
+// tangent in double-float (FP32 pairs, about 47 bits: FP32 runs at 64 times
+// the FP64 rate on GB300), node-centric gathers into the full-block CSR
+// pattern in FP64, and the Newton loop on the device.
 //
 // Element form (velocity test N_a e_i, pressure test M_b = l_b):
 //   r_(a,i) = int -rho (g_a . u) u_i - g_a,i p + mu g_a . grad u_i
@@ -17,25 +18,31 @@
 // triangle (xi = s, eta = t (1 - s), weight (1 - s)), exact for polynomials
 // of total degree 6: every integrand on a straight-sided element (the SUPG
 // terms reach degree 6).
-#include "mf_internal.h"
+#include "mf_fem.cuh"
 
 namespace {
+
+// a double constant as an FP32 pair (folded at compile time)
+#define DFC(x) make_float2((float)(x), (float)((x) - (double)(float)(x)))
+
+__device__ __forceinline__ float2 dfma2(float2 a, float2 b, float2 c) { return df_add(df_mul(a, b), c); }
+__device__ __forceinline__ float2 dsub2(float2 a, float2 b) { return df_add(a, df_neg(b)); }
 
 // 4-point Gauss-Legendre on [0, 1]: nodes (1 -+ z) / 2 and half weights of the
 // published rule on [-1, 1] (z = 0.8611363115940526, 0.3399810435848563;
 // weights 0.3478548451374536, 0.6521451548625464)
-__device__ __forceinline__ double gl4_x(int i)
+__device__ __forceinline__ float2 gl4_x(int i)
 {
-    return i == 0 ? 0.06943184420297371 : i == 1 ? 0.33000947820757187 : i == 2 ? 0.6699905217924281
-                                                                                  : 0.9305681557970262;
+    return i == 0 ? DFC(0.06943184420297371)
+                  : i == 1 ? DFC(0.33000947820757187) : i == 2 ? DFC(0.6699905217924281) : DFC(0.9305681557970262);
 }
-__device__ __forceinline__ double gl4_w(int i)
+__device__ __forceinline__ float2 gl4_w(int i)
 {
-    return (i == 0 || i == 3) ? 0.17392742256872679 : 0.3260725774312732;
+    return (i == 0 || i == 3) ? DFC(0.17392742256872679) : DFC(0.3260725774312732);
 }
 
 constexpr int NS_EPB = 4;            // elements per block, 16 threads each
-constexpr int NS_PT = 62;            // doubles of per-point data
+constexpr int NS_PT = 62;            // pairs of per-point data
 constexpr int NS_EL = 240;           // scratch words per element: r (15), K (15 x 15)
 
 // per point: wd, N[6], g[6][2], l[3], u[2], du[2][2], Rm[2], Rc, p, adv[6],
@@ -48,34 +55,41 @@ enum {
 __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n2, const double *__restrict__ X,
                                                          const int32_t *__restrict__ conn,
                                                          const int32_t *__restrict__ pconn,
-                                                         const double *__restrict__ x, double mu, double rho,
-                                                         double tm, double tc, double *__restrict__ out,
+                                                         const double *__restrict__ x, double mu_d, double rho_d,
+                                                         double tm_d, double tc_d, double *__restrict__ out,
                                                          int *status)
 {
-    __shared__ double pts[NS_EPB][16][NS_PT];
-    __shared__ double cst[NS_EPB][12];  // gl[3][2], lap[6]
+    __shared__ float2 pts[NS_EPB][16][NS_PT];
+    __shared__ float2 cst[NS_EPB][12];  // gl[3][2], lap[6]
     const int le = threadIdx.x >> 4, q = threadIdx.x & 15;
     const int64_t e = (int64_t)blockIdx.x * NS_EPB + le;
     const bool valid = e < n_el;
     const int64_t ee = valid ? e : n_el - 1;
     const int32_t *cn = conn + 6 * ee;
     const int32_t *pc = pconn + 3 * ee;
-    // affine map of the vertices: J = [x1 - x0, x2 - x0]; gradients of the
-    // barycentrics l1 = xi, l2 = eta, l0 = 1 - xi - eta
+    const float2 mu = f64_to_df(mu_d), rho = f64_to_df(rho_d), tm = f64_to_df(tm_d), tc = f64_to_df(tc_d);
+    const float2 one = make_float2(1.f, 0.f), two = make_float2(2.f, 0.f), four = make_float2(4.f, 0.f);
+    // affine map of the vertices: J = [x1 - x0, x2 - x0] (differences in FP64,
+    // then pairs); gradients of the barycentrics l1 = xi, l2 = eta, l0 = 1 - xi - eta
     const double x0 = X[2 * (int64_t)cn[0]], y0 = X[2 * (int64_t)cn[0] + 1];
-    const double J00 = X[2 * (int64_t)cn[1]] - x0, J10 = X[2 * (int64_t)cn[1] + 1] - y0;
-    const double J01 = X[2 * (int64_t)cn[2]] - x0, J11 = X[2 * (int64_t)cn[2] + 1] - y0;
-    const double det = J00 * J11 - J01 * J10;
-    if (valid && q == 0 && !(det > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
-    const double idet = 1.0 / det;
-    const double gl[3][2] = {{(J10 - J11) * idet, (J01 - J00) * idet}, {J11 * idet, -J01 * idet}, {-J10 * idet, J00 * idet}};
+    const double J00d = X[2 * (int64_t)cn[1]] - x0, J10d = X[2 * (int64_t)cn[1] + 1] - y0;
+    const double J01d = X[2 * (int64_t)cn[2]] - x0, J11d = X[2 * (int64_t)cn[2] + 1] - y0;
+    if (valid && q == 0 && !(J00d * J11d - J01d * J10d > 0.0)) mf_dev_fail(status, MF_ERR_BAD_MESH);
+    const float2 J00 = f64_to_df(J00d), J10 = f64_to_df(J10d), J01 = f64_to_df(J01d), J11 = f64_to_df(J11d);
+    const float2 det = df_det2(J00, J11, J01, J10);
+    const float2 idet = df_recip(det);
+    const float2 gl[3][2] = {{df_mul(dsub2(J10, J11), idet), df_mul(dsub2(J01, J00), idet)},
+                             {df_mul(J11, idet), df_neg(df_mul(J01, idet))},
+                             {df_neg(df_mul(J10, idet)), df_mul(J00, idet)}};
     constexpr int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
-    double lap[6];
+    float2 lap[6];
 #pragma unroll
-    for (int v = 0; v < 3; ++v) lap[v] = 4.0 * (gl[v][0] * gl[v][0] + gl[v][1] * gl[v][1]);
+    for (int v = 0; v < 3; ++v)
+        lap[v] = df_mul(four, dfma2(gl[v][0], gl[v][0], df_mul(gl[v][1], gl[v][1])));
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-        lap[3 + k] = 8.0 * (gl[ep[k][0]][0] * gl[ep[k][1]][0] + gl[ep[k][0]][1] * gl[ep[k][1]][1]);
+        lap[3 + k] = df_mul(make_float2(8.f, 0.f), dfma2(gl[ep[k][0]][0], gl[ep[k][1]][0],
+                                                         df_mul(gl[ep[k][0]][1], gl[ep[k][1]][1])));
     if (q == 0) {
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
@@ -86,59 +100,64 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
         for (int a = 0; a < 6; ++a) cst[le][6 + a] = lap[a];
     }
     // element state
-    double U[6][2], P[3];
+    float2 U[6][2], P[3];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-        U[a][0] = x[cn[a]];
-        U[a][1] = x[n2 + cn[a]];
+        U[a][0] = f64_to_df(x[cn[a]]);
+        U[a][1] = f64_to_df(x[n2 + cn[a]]);
     }
 #pragma unroll
-    for (int b = 0; b < 3; ++b) P[b] = x[2 * n2 + pc[b]];
+    for (int b = 0; b < 3; ++b) P[b] = f64_to_df(x[2 * n2 + pc[b]]);
     // phase 1: thread q evaluates point q
     {
-        const double s = gl4_x(q >> 2), t = gl4_x(q & 3);
-        const double xi = s, eta = t * (1.0 - s);
-        const double wd = gl4_w(q >> 2) * gl4_w(q & 3) * (1.0 - s) * det;
-        const double l[3] = {1.0 - xi - eta, xi, eta};
-        double N[6], g[6][2];
+        const float2 s = gl4_x(q >> 2), t = gl4_x(q & 3);
+        const float2 oms = dsub2(one, s);
+        const float2 xi = s, eta = df_mul(t, oms);
+        const float2 wd = df_mul(df_mul(df_mul(gl4_w(q >> 2), gl4_w(q & 3)), oms), det);
+        const float2 l[3] = {dsub2(dsub2(one, xi), eta), xi, eta};
+        float2 N[6], g[6][2];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-            N[v] = l[v] * (2.0 * l[v] - 1.0);
-            g[v][0] = (4.0 * l[v] - 1.0) * gl[v][0];
-            g[v][1] = (4.0 * l[v] - 1.0) * gl[v][1];
+            N[v] = df_mul(l[v], dsub2(df_mul(two, l[v]), one));
+            const float2 f = dsub2(df_mul(four, l[v]), one);
+            g[v][0] = df_mul(f, gl[v][0]);
+            g[v][1] = df_mul(f, gl[v][1]);
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int a = ep[k][0], b = ep[k][1];
-            N[3 + k] = 4.0 * l[a] * l[b];
-            g[3 + k][0] = 4.0 * (gl[a][0] * l[b] + l[a] * gl[b][0]);
-            g[3 + k][1] = 4.0 * (gl[a][1] * l[b] + l[a] * gl[b][1]);
+            N[3 + k] = df_mul(four, df_mul(l[a], l[b]));
+            g[3 + k][0] = df_mul(four, dfma2(gl[a][0], l[b], df_mul(l[a], gl[b][0])));
+            g[3 + k][1] = df_mul(four, dfma2(gl[a][1], l[b], df_mul(l[a], gl[b][1])));
         }
-        double u[2] = {0.0, 0.0}, du[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, lu[2] = {0.0, 0.0};
+        const float2 z = make_float2(0.f, 0.f);
+        float2 u[2] = {z, z}, du[2][2] = {{z, z}, {z, z}}, lu[2] = {z, z};
 #pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                u[i] += N[a] * U[a][i];
-                du[i][0] += g[a][0] * U[a][i];
-                du[i][1] += g[a][1] * U[a][i];
-                lu[i] += lap[a] * U[a][i];
+                u[i] = dfma2(N[a], U[a][i], u[i]);
+                du[i][0] = dfma2(g[a][0], U[a][i], du[i][0]);
+                du[i][1] = dfma2(g[a][1], U[a][i], du[i][1]);
+                lu[i] = dfma2(lap[a], U[a][i], lu[i]);
             }
-        double ph = 0.0, dp[2] = {0.0, 0.0};
+        float2 ph = z, dp[2] = {z, z};
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            ph += l[b] * P[b];
-            dp[0] += gl[b][0] * P[b];
-            dp[1] += gl[b][1] * P[b];
+            ph = dfma2(l[b], P[b], ph);
+            dp[0] = dfma2(gl[b][0], P[b], dp[0]);
+            dp[1] = dfma2(gl[b][1], P[b], dp[1]);
         }
-        double *o = pts[le][q];
+        float2 *o = pts[le][q];
         o[P_WD] = wd;
+        float2 adv[6];
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
+            adv[a] = dfma2(g[a][0], u[0], df_mul(g[a][1], u[1]));
             o[P_N + a] = N[a];
             o[P_G + 2 * a] = g[a][0];
             o[P_G + 2 * a + 1] = g[a][1];
-            o[P_ADV + a] = g[a][0] * u[0] + g[a][1] * u[1];
+            o[P_ADV + a] = adv[a];
         }
 #pragma unroll
         for (int v = 0; v < 3; ++v) o[P_L + v] = l[v];
@@ -148,9 +167,11 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
         for (int i = 0; i < 2; ++i) {
             o[P_DU + 2 * i] = du[i][0];
             o[P_DU + 2 * i + 1] = du[i][1];
-            o[P_RM + i] = rho * (u[0] * du[i][0] + u[1] * du[i][1]) + dp[i] - mu * lu[i];
+            // Rm_i = rho (u . grad u_i) + d_i p - mu lap u_i
+            o[P_RM + i] = dsub2(df_add(df_mul(rho, dfma2(u[0], du[i][0], df_mul(u[1], du[i][1]))), dp[i]),
+                                df_mul(mu, lu[i]));
         }
-        o[P_RC] = du[0][0] + du[1][1];
+        o[P_RC] = df_add(du[0][0], du[1][1]);
         o[P_P] = ph;
         // dRm_i / dU_bj = rho (N_b d_j u_i + delta_ij u . g_b) - mu delta_ij lap N_b
 #pragma unroll
@@ -158,75 +179,88 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int b = 0; b < 6; ++b) {
-                    const double adv_b = g[b][0] * u[0] + g[b][1] * u[1];
+                for (int b = 0; b < 6; ++b)
                     o[P_DRM + 12 * i + 6 * j + b] =
-                        i == j ? rho * (N[b] * du[i][j] + adv_b) - mu * lap[b] : rho * N[b] * du[i][j];
-                }
+                        i == j ? dsub2(df_mul(rho, dfma2(N[b], du[i][j], adv[b])), df_mul(mu, lap[b]))
+                               : df_mul(rho, df_mul(N[b], du[i][j]));
     }
     __syncthreads();
     // phase 2: thread r < 15 forms row r of the residual and the tangent
     const int r = q;
     if (!valid || r >= 15) return;
-    const double *cs = cst[le];
-    double res = 0.0, K[15];
+    const float2 *cs = cst[le];
+    const float2 z = make_float2(0.f, 0.f);
+    float2 res = z, K[15];
 #pragma unroll
-    for (int c = 0; c < 15; ++c) K[c] = 0.0;
+    for (int c = 0; c < 15; ++c) K[c] = z;
+    const float2 rtm = df_mul(rho, tm);
     if (r < 12) {
         const int a = r >> 1, i = r & 1;
 #pragma unroll 1
         for (int p = 0; p < 16; ++p) {
-            const double *o = pts[le][p];
-            const double wd = o[P_WD];
-            const double ga0 = o[P_G + 2 * a], ga1 = o[P_G + 2 * a + 1], gai = i ? ga1 : ga0;
-            const double adv = o[P_ADV + a], ui = o[P_U + i], rmi = o[P_RM + i], rc = o[P_RC];
-            res += wd * (-rho * adv * ui - gai * o[P_P] + mu * (ga0 * o[P_DU + 2 * i] + ga1 * o[P_DU + 2 * i + 1]) +
-                         tm * rho * adv * rmi + tc * gai * rc);
+            const float2 *o = pts[le][p];
+            const float2 wd = o[P_WD];
+            const float2 ga0 = o[P_G + 2 * a], ga1 = o[P_G + 2 * a + 1], gai = i ? ga1 : ga0;
+            const float2 adv = o[P_ADV + a], ui = o[P_U + i], rmi = o[P_RM + i], rc = o[P_RC];
+            // -rho adv u_i - g_a,i p + mu (g_a . grad u_i) + tau_m rho adv Rm_i + tau_c g_a,i Rc
+            float2 tt = df_neg(df_mul(rho, df_mul(adv, ui)));
+            tt = dsub2(tt, df_mul(gai, o[P_P]));
+            tt = dfma2(mu, dfma2(ga0, o[P_DU + 2 * i], df_mul(ga1, o[P_DU + 2 * i + 1])), tt);
+            tt = dfma2(rtm, df_mul(adv, rmi), tt);
+            tt = dfma2(tc, df_mul(gai, rc), tt);
+            res = dfma2(wd, tt, res);
             // K[(a,i),(b,j)] = sum_q wd [ g_a,j N_b (-rho u_i + tm rho Rm_i) + tm rho adv_a dRm_ij(b)
             //                            + tc g_a,i g_b,j + delta_ij (-rho adv_a N_b + mu g_a . g_b) ]
-            const double A = wd * rho * (tm * rmi - ui);
-            const double c0 = ga0 * A, c1 = ga1 * A;
-            const double T4 = wd * tm * rho * adv, T5 = wd * tc * gai, B = -wd * rho * adv, Mu = wd * mu;
-            const double *dR = o + P_DRM + 12 * i;
+            const float2 A = df_mul(wd, df_mul(rho, dsub2(df_mul(tm, rmi), ui)));
+            const float2 c0 = df_mul(ga0, A), c1 = df_mul(ga1, A);
+            const float2 T4 = df_mul(wd, df_mul(rtm, adv)), T5 = df_mul(wd, df_mul(tc, gai));
+            const float2 Bn = df_neg(df_mul(wd, df_mul(rho, adv))), Mu = df_mul(wd, mu);
+            const float2 *dR = o + P_DRM + 12 * i;
 #pragma unroll
             for (int b = 0; b < 6; ++b) {
-                const double Nb = o[P_N + b], gb0 = o[P_G + 2 * b], gb1 = o[P_G + 2 * b + 1];
-                const double diag = B * Nb + Mu * (ga0 * gb0 + ga1 * gb1);
-                K[2 * b] += c0 * Nb + T4 * dR[b] + T5 * gb0 + (i == 0 ? diag : 0.0);
-                K[2 * b + 1] += c1 * Nb + T4 * dR[6 + b] + T5 * gb1 + (i == 1 ? diag : 0.0);
+                const float2 Nb = o[P_N + b], gb0 = o[P_G + 2 * b], gb1 = o[P_G + 2 * b + 1];
+                const float2 diag = dfma2(Bn, Nb, df_mul(Mu, dfma2(ga0, gb0, df_mul(ga1, gb1))));
+                float2 k0 = dfma2(c0, Nb, dfma2(T4, dR[b], df_mul(T5, gb0)));
+                float2 k1 = dfma2(c1, Nb, dfma2(T4, dR[6 + b], df_mul(T5, gb1)));
+                if (i == 0) k0 = df_add(k0, diag);
+                else k1 = df_add(k1, diag);
+                K[2 * b] = df_add(K[2 * b], k0);
+                K[2 * b + 1] = df_add(K[2 * b + 1], k1);
             }
-            const double T6 = wd * gai;
+            const float2 T6 = df_mul(wd, gai);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) K[12 + c] += T4 * cs[2 * c + i] - T6 * o[P_L + c];
+            for (int c = 0; c < 3; ++c) K[12 + c] = df_add(K[12 + c], dsub2(df_mul(T4, cs[2 * c + i]), df_mul(T6, o[P_L + c])));
         }
     } else {
         const int bp = r - 12;
-        const double gp0 = cs[2 * bp], gp1 = cs[2 * bp + 1];
-        double area = 0.0;
+        const float2 gp0 = cs[2 * bp], gp1 = cs[2 * bp + 1];
+        float2 area = z;
 #pragma unroll 1
         for (int p = 0; p < 16; ++p) {
-            const double *o = pts[le][p];
-            const double wd = o[P_WD];
-            const double lb = o[P_L + bp];
-            area += wd;
-            res += wd * (lb * o[P_RC] + tm * (gp0 * o[P_RM] + gp1 * o[P_RM + 1]));
+            const float2 *o = pts[le][p];
+            const float2 wd = o[P_WD];
+            const float2 lb = o[P_L + bp];
+            area = df_add(area, wd);
+            res = dfma2(wd, dfma2(lb, o[P_RC], df_mul(tm, dfma2(gp0, o[P_RM], df_mul(gp1, o[P_RM + 1])))), res);
             // K[b',(b,j)] = sum_q wd [ l_b' g_b,j + tm sum_i grad l_b',i dRm_ij(b) ]
-            const double L = wd * lb, G0 = wd * tm * gp0, G1 = wd * tm * gp1;
-            const double *dR = o + P_DRM;
+            const float2 L = df_mul(wd, lb), G0 = df_mul(wd, df_mul(tm, gp0)), G1 = df_mul(wd, df_mul(tm, gp1));
+            const float2 *dR = o + P_DRM;
 #pragma unroll
             for (int b = 0; b < 6; ++b)
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
-                    K[2 * b + j] += L * o[P_G + 2 * b + j] + G0 * dR[6 * j + b] + G1 * dR[12 + 6 * j + b];
+                    K[2 * b + j] = df_add(K[2 * b + j], dfma2(L, o[P_G + 2 * b + j],
+                                                              dfma2(G0, dR[6 * j + b], df_mul(G1, dR[12 + 6 * j + b]))));
         }
         // the pressure-pressure block: tm grad l_b' . grad l_c over the element
 #pragma unroll
-        for (int c = 0; c < 3; ++c) K[12 + c] = area * tm * (gp0 * cs[2 * c] + gp1 * cs[2 * c + 1]);
+        for (int c = 0; c < 3; ++c)
+            K[12 + c] = df_mul(df_mul(area, tm), dfma2(gp0, cs[2 * c], df_mul(gp1, cs[2 * c + 1])));
     }
     double *w = out + e * NS_EL;
-    w[r] = res;
+    w[r] = df_to_double_int(res);
 #pragma unroll
-    for (int c = 0; c < 15; ++c) w[15 + 15 * r + c] = K[c];
+    for (int c = 0; c < 15; ++c) w[15 + 15 * r + c] = df_to_double_int(K[c]);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,4 +1,6 @@
 """Steady Navier-Stokes with SUPG (Sec. 4.3) on the GPU against the oracle.
+The GPU forms the element residual and tangent in double-float (FP32 pairs,
+about 47 bits) and sums them into the CSR rows in FP64.
 
 The oracle's or_ns_system gives the residual R and the tangent K = dR/dx by
 complex-step differentiation of its residual (its own 16-point rule); the
@@ -133,6 +135,8 @@ def test_ns_newton_matches_oracle(mf, orc, n):
     assert hist[0] == pytest.approx(hist_o[0], rel=1e-12)
     x = P.advect.cpu().numpy()
     assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
-    # quadratic: once small, each norm is about the square of the previous
-    small = [(a, b) for a, b in zip(hist[:-1], hist[1:]) if a < 1e-2 and b > 1e-15]
+    # quadratic: once small, each norm is about the square of the previous;
+    # norms below 1e-13 are at the floor of the double-float residual (about
+    # 2^-47 of its terms) and say nothing about the rate
+    small = [(a, b) for a, b in zip(hist[:-1], hist[1:]) if a < 1e-2 and b > 1e-13]
     assert small and all(b < 50.0 * a * a for a, b in small)
