@@ -185,17 +185,28 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
                                : df_mul(rho, df_mul(N[b], du[i][j]));
     }
     __syncthreads();
-    // phase 2: thread r < 15 forms row r of the residual and the tangent
+    // phase 2: thread r < 12 forms velocity row r = (a, i) of the residual and
+    // the tangent and also column (a, i) of the three pressure rows (so the
+    // warps do not run the pressure rows' loop after the velocity rows');
+    // thread 12 + b' forms the pressure residual r_b' and the row's p-p block
     const int r = q;
     if (!valid || r >= 15) return;
     const float2 *cs = cst[le];
     const float2 z = make_float2(0.f, 0.f);
-    float2 res = z, K[15];
+    float2 res = z, K[15], Kp[3] = {z, z, z};
 #pragma unroll
     for (int c = 0; c < 15; ++c) K[c] = z;
     const float2 rtm = df_mul(rho, tm);
+    double *w = out + e * NS_EL;
     if (r < 12) {
         const int a = r >> 1, i = r & 1;
+        // pressure rows' gradients times tau_m
+        float2 tg[3][2];
+#pragma unroll
+        for (int bp = 0; bp < 3; ++bp) {
+            tg[bp][0] = df_mul(tm, cs[2 * bp]);
+            tg[bp][1] = df_mul(tm, cs[2 * bp + 1]);
+        }
 #pragma unroll 1
         for (int p = 0; p < 16; ++p) {
             const float2 *o = pts[le][p];
@@ -230,7 +241,14 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
             const float2 T6 = df_mul(wd, gai);
 #pragma unroll
             for (int c = 0; c < 3; ++c) K[12 + c] = df_add(K[12 + c], dsub2(df_mul(T4, cs[2 * c + i]), df_mul(T6, o[P_L + c])));
+            // K[b',(a,i)] = sum_q wd [ l_b' g_a,i + tm sum_k grad l_b',k dRm_k,i(a) ]
+            const float2 d0 = o[P_DRM + 6 * i + a], d1 = o[P_DRM + 12 + 6 * i + a];
+#pragma unroll
+            for (int bp = 0; bp < 3; ++bp)
+                Kp[bp] = dfma2(wd, dfma2(o[P_L + bp], gai, dfma2(tg[bp][0], d0, df_mul(tg[bp][1], d1))), Kp[bp]);
         }
+#pragma unroll
+        for (int bp = 0; bp < 3; ++bp) w[15 + 15 * (12 + bp) + r] = df_to_double_int(Kp[bp]);
     } else {
         const int bp = r - 12;
         const float2 gp0 = cs[2 * bp], gp1 = cs[2 * bp + 1];
@@ -239,25 +257,19 @@ __global__ void __launch_bounds__(NS_EPB * 16) k_elem_ns(int64_t n_el, int64_t n
         for (int p = 0; p < 16; ++p) {
             const float2 *o = pts[le][p];
             const float2 wd = o[P_WD];
-            const float2 lb = o[P_L + bp];
             area = df_add(area, wd);
-            res = dfma2(wd, dfma2(lb, o[P_RC], df_mul(tm, dfma2(gp0, o[P_RM], df_mul(gp1, o[P_RM + 1])))), res);
-            // K[b',(b,j)] = sum_q wd [ l_b' g_b,j + tm sum_i grad l_b',i dRm_ij(b) ]
-            const float2 L = df_mul(wd, lb), G0 = df_mul(wd, df_mul(tm, gp0)), G1 = df_mul(wd, df_mul(tm, gp1));
-            const float2 *dR = o + P_DRM;
-#pragma unroll
-            for (int b = 0; b < 6; ++b)
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    K[2 * b + j] = df_add(K[2 * b + j], dfma2(L, o[P_G + 2 * b + j],
-                                                              dfma2(G0, dR[6 * j + b], df_mul(G1, dR[12 + 6 * j + b]))));
+            res = dfma2(wd, dfma2(o[P_L + bp], o[P_RC], df_mul(tm, dfma2(gp0, o[P_RM], df_mul(gp1, o[P_RM + 1])))),
+                        res);
         }
         // the pressure-pressure block: tm grad l_b' . grad l_c over the element
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             K[12 + c] = df_mul(df_mul(area, tm), dfma2(gp0, cs[2 * c], df_mul(gp1, cs[2 * c + 1])));
+        w[r] = df_to_double_int(res);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[15 + 15 * r + 12 + c] = df_to_double_int(K[12 + c]);
+        return;
     }
-    double *w = out + e * NS_EL;
     w[r] = df_to_double_int(res);
 #pragma unroll
     for (int c = 0; c < 15; ++c) w[15 + 15 * r + c] = df_to_double_int(K[c]);
