@@ -473,66 +473,107 @@ __global__ void __launch_bounds__(EL_T) k_elem_elastic_q1(int64_t e0, int64_t e1
     }
 }
 
-// Taylor-Hood flow, one element per thread: A (6x6) then B_1, B_2 (3x6).
+// Taylor-Hood flow, one element per thread: A (6x6) then B_1, B_2 (3x6), in
+// double-float (FP32 pairs, about 47 bits): FP64 only for the vertex
+// differences, the finiteness checks and the per-block conversion of the
+// reference sums; each output converts once (integer-only).
+__device__ __forceinline__ float2 dfma_(float2 a, float2 b, float2 c) { return df_add(df_mul(a, b), c); }
+
 __global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, const double *__restrict__ X,
                                                     const int32_t *__restrict__ conn, const double *__restrict__ adv,
-                                                    double mu, double rho, double *__restrict__ out, int *status)
+                                                    double mu_d, double rho_d, double *__restrict__ out, int *status)
 {
+    __shared__ float2 sMs[6][6][6], sR[3][3][6];
+    for (int i = threadIdx.x; i < 216; i += blockDim.x) (&sMs[0][0][0])[i] = f64_to_df((&c_Ms[0][0][0])[i]);
+    for (int i = threadIdx.x; i < 54; i += blockDim.x) (&sR[0][0][0])[i] = f64_to_df((&c_R[0][0][0])[i]);
+    __syncthreads();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_el) return;
     const int32_t *c = conn + 6 * e;
-    double gl[3][2];
-    const double det = tri_affine(X, c, gl);
-    double aN[6][2];
+    const float2 mu = f64_to_df(mu_d), rho = f64_to_df(rho_d);
+    // affine triangle (as tri_affine): J^-1 = [[j11, -j01], [-j10, j00]] / det,
+    // grad lambda = J^-T gradref lambda
+    const double x0 = X[2 * (int64_t)c[0]], y0 = X[2 * (int64_t)c[0] + 1];
+    const float2 j00 = f64_to_df(X[2 * (int64_t)c[1]] - x0), j10 = f64_to_df(X[2 * (int64_t)c[1] + 1] - y0);
+    const float2 j01 = f64_to_df(X[2 * (int64_t)c[2]] - x0), j11 = f64_to_df(X[2 * (int64_t)c[2] + 1] - y0);
+    const float2 det = df_det2(j00, j11, j01, j10);
+    const float2 r = df_recip(det);
+    const float2 i00 = df_mul(j11, r), i01 = df_neg(df_mul(j01, r)), i10 = df_neg(df_mul(j10, r)),
+                 i11 = df_mul(j00, r);
+    const float2 gl[3][2] = {{df_neg(df_add(i00, i10)), df_neg(df_add(i01, i11))}, {i00, i01}, {i10, i11}};
+    float2 aN[6][2];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-        aN[a][0] = adv[c[a]];
-        aN[a][1] = adv[n2 + c[a]];
-        if (!isfinite(aN[a][0]) || !isfinite(aN[a][1])) mf_dev_fail(status, MF_ERR_NONFINITE);
+        const double v0 = adv[c[a]], v1 = adv[n2 + c[a]];
+        if (!isfinite(v0) || !isfinite(v1)) mf_dev_fail(status, MF_ERR_NONFINITE);
+        aN[a][0] = f64_to_df(v0);
+        aN[a][1] = f64_to_df(v1);
     }
     double *o = out + e * 72;
+    const float2 z = make_float2(0.f, 0.f), one = make_float2(1.f, 0.f), two = make_float2(2.f, 0.f),
+                 four = make_float2(4.f, 0.f);
     {
         // A = mu D + C: the viscous part D from the reference sums, the
         // advection part C[a][b] = -rho sum_q w detJ (a_h . grad N_a) N_b by
-        // quadrature (a_h varies over the element)
-        double Cv[36] = {};
+        // the 6-point rule (a_h varies over the element)
+        float2 Cv[36];
+#pragma unroll
+        for (int k = 0; k < 36; ++k) Cv[k] = z;
+        const float2 rdet = df_mul(rho, det);
 #pragma unroll 1
         for (int q = 0; q < 6; ++q) {
-            double l[3], w;
-            tri6_point(q, l, w);
-            double N[6], g[6][2];
-            p2_basis(l, gl, N, g);
-            const double wrho = w * det * rho;
-            double ah0 = 0.0, ah1 = 0.0;
+            const float2 la = q < 3 ? DFC(T6A1) : DFC(T6A2), lb = q < 3 ? DFC(1.0 - 2.0 * T6A1) : DFC(1.0 - 2.0 * T6A2);
+            const int kq = q % 3;
+            const float2 l[3] = {kq == 0 ? lb : la, kq == 1 ? lb : la, kq == 2 ? lb : la};
+            const float2 w = q < 3 ? DFC(0.5 * T6W1) : DFC(0.5 * T6W2);
+            float2 N[6], g[6][2];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                N[i] = df_mul(l[i], df_add(df_mul(two, l[i]), df_neg(one)));
+                const float2 f = df_add(df_mul(four, l[i]), df_neg(one));
+                g[i][0] = df_mul(f, gl[i][0]);
+                g[i][1] = df_mul(f, gl[i][1]);
+            }
+            const int ep[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int pa = ep[k][0], pb = ep[k][1];
+                N[3 + k] = df_mul(four, df_mul(l[pa], l[pb]));
+                g[3 + k][0] = df_mul(four, dfma_(gl[pa][0], l[pb], df_mul(l[pa], gl[pb][0])));
+                g[3 + k][1] = df_mul(four, dfma_(gl[pa][1], l[pb], df_mul(l[pa], gl[pb][1])));
+            }
+            const float2 wrho = df_mul(w, rdet);
+            float2 ah0 = z, ah1 = z;
 #pragma unroll
             for (int b = 0; b < 6; ++b) {
-                ah0 = fma(aN[b][0], N[b], ah0);
-                ah1 = fma(aN[b][1], N[b], ah1);
+                ah0 = dfma_(aN[b][0], N[b], ah0);
+                ah1 = dfma_(aN[b][1], N[b], ah1);
             }
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
-                const double sa = wrho * fma(ah0, g[a][0], ah1 * g[a][1]);
+                const float2 nsa = df_neg(df_mul(wrho, dfma_(ah0, g[a][0], df_mul(ah1, g[a][1]))));
 #pragma unroll
-                for (int b = 0; b < 6; ++b) Cv[6 * a + b] = fma(-sa, N[b], Cv[6 * a + b]);
+                for (int b = 0; b < 6; ++b) Cv[6 * a + b] = dfma_(nsa, N[b], Cv[6 * a + b]);
             }
         }
-        double Gs[6];
-        Gs[0] = fma(gl[0][0], gl[0][0], gl[0][1] * gl[0][1]);
-        Gs[1] = fma(gl[1][0], gl[1][0], gl[1][1] * gl[1][1]);
-        Gs[2] = fma(gl[2][0], gl[2][0], gl[2][1] * gl[2][1]);
-        Gs[3] = fma(gl[0][0], gl[1][0], gl[0][1] * gl[1][1]);
-        Gs[4] = fma(gl[0][0], gl[2][0], gl[0][1] * gl[2][1]);
-        Gs[5] = fma(gl[1][0], gl[2][0], gl[1][1] * gl[2][1]);
-        const double mdet = mu * det;
+        float2 Gs[6];
+        Gs[0] = dfma_(gl[0][0], gl[0][0], df_mul(gl[0][1], gl[0][1]));
+        Gs[1] = dfma_(gl[1][0], gl[1][0], df_mul(gl[1][1], gl[1][1]));
+        Gs[2] = dfma_(gl[2][0], gl[2][0], df_mul(gl[2][1], gl[2][1]));
+        Gs[3] = dfma_(gl[0][0], gl[1][0], df_mul(gl[0][1], gl[1][1]));
+        Gs[4] = dfma_(gl[0][0], gl[2][0], df_mul(gl[0][1], gl[2][1]));
+        Gs[5] = dfma_(gl[1][0], gl[2][0], df_mul(gl[1][1], gl[2][1]));
+        const float2 mdet = df_mul(mu, det);
 #pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
             for (int b = a; b < 6; ++b) {
-                double Dab = 0.0;
+                float2 Dab = z;
 #pragma unroll
-                for (int pp = 0; pp < 6; ++pp) Dab = fma(Gs[pp], c_Ms[pp][a][b], Dab);
-                o[6 * a + b] = fma(mdet, Dab, Cv[6 * a + b]);
-                if (b != a) o[6 * b + a] = fma(mdet, Dab, Cv[6 * b + a]);
+                for (int pp = 0; pp < 6; ++pp) Dab = dfma_(Gs[pp], sMs[pp][a][b], Dab);
+                const float2 vd = df_mul(mdet, Dab);
+                o[6 * a + b] = df_to_double_int(df_add(vd, Cv[6 * a + b]));
+                if (b != a) o[6 * b + a] = df_to_double_int(df_add(vd, Cv[6 * b + a]));
             }
     }
     {
@@ -543,10 +584,10 @@ __global__ void __launch_bounds__(128) k_elem_oseen(int64_t n_el, int64_t n2, co
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 6; ++b) {
-                    double v = 0.0;
+                    float2 v = z;
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) v = fma(gl[j][i], c_R[j][a][b], v);
-                    o[36 + 18 * i + 6 * a + b] = det * v;
+                    for (int j = 0; j < 3; ++j) v = dfma_(gl[j][i], sR[j][a][b], v);
+                    o[36 + 18 * i + 6 * a + b] = df_to_double_int(df_mul(det, v));
                 }
     }
 }

@@ -299,6 +299,9 @@ __device__ __forceinline__ double df_to_double_int(float2 a)
     return __longlong_as_double((long long)bits);
 }
 
+// a double constant as an FP32 pair (folded at compile time)
+#define DFC(x) make_float2((float)(x), (float)((x) - (double)(float)(x)))
+
 // a b - c d in double-float
 __host__ __device__ __forceinline__ float2 df_det2(float2 a, float2 b, float2 c, float2 d)
 {

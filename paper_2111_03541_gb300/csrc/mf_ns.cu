@@ -22,9 +22,6 @@
 
 namespace {
 
-// a double constant as an FP32 pair (folded at compile time)
-#define DFC(x) make_float2((float)(x), (float)((x) - (double)(float)(x)))
-
 __device__ __forceinline__ float2 dfma2(float2 a, float2 b, float2 c) { return df_add(df_mul(a, b), c); }
 __device__ __forceinline__ float2 dsub2(float2 a, float2 b) { return df_add(a, df_neg(b)); }
 
