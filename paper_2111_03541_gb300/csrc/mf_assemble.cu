@@ -986,8 +986,9 @@ __device__ __forceinline__ void flow_put(double &v, double &lift, bool rm, int64
 __global__ void __launch_bounds__(GO_GROUPS * 16) k_gather_oseen_u(
     int64_t n2, mf_adj pp, mf_adj pq, const int64_t *__restrict__ inc_ptr, const uint8_t *__restrict__ inc_loc,
     const int32_t *__restrict__ inc, const uint8_t *__restrict__ slot_pp, const uint8_t *__restrict__ slot_pq,
-    const double *__restrict__ sc, const uint8_t *__restrict__ mask, const double *__restrict__ bval,
-    const int64_t *__restrict__ row_ptr, double *__restrict__ values, double *__restrict__ d)
+    const double *__restrict__ sc, const uint8_t *__restrict__ mask, const uint8_t *__restrict__ bcrow,
+    const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
+    double *__restrict__ d)
 {
     __shared__ double accA_all[GO_GROUPS][MF_MAX_DEG];
     __shared__ double accB_all[GO_GROUPS][2][MF_MAX_DEG];
@@ -1040,17 +1041,19 @@ __global__ void __launch_bounds__(GO_GROUPS * 16) k_gather_oseen_u(
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int64_t r = i * n2 + n;
-        const bool rm = mask ? mask[r] != 0 : false;
+        // the Dirichlet tests (column loads) only on rows next to a constrained dof
+        const uint8_t *mk = (mask && bcrow[r]) ? mask : nullptr;
+        const bool rm = mk ? mk[r] != 0 : false;
         const int64_t rb = row_ptr[r];
         double lift = 0.0;
         for (int k = sub; k < da; k += 16) {
             double val = accA[k];
-            flow_put(val, lift, rm, r, i * n2 + pp.col[pa0 + k], mask, bval);
+            if (mk) flow_put(val, lift, rm, r, i * n2 + pp.col[pa0 + k], mk, bval);
             values[rb + k] = val;
         }
         for (int k = sub; k < db; k += 16) {
             double val = accB[i][k];
-            flow_put(val, lift, rm, r, 2 * n2 + pq.col[pb0 + k], mask, bval);
+            if (mk) flow_put(val, lift, rm, r, 2 * n2 + pq.col[pb0 + k], mk, bval);
             values[rb + da + k] = val;
         }
         if (__any_sync(gmask, lift != 0.0))
@@ -1063,8 +1066,8 @@ __global__ void __launch_bounds__(GO_GROUPS * 16) k_gather_oseen_u(
 __global__ void __launch_bounds__(GO_GROUPS * 16) k_gather_oseen_p(
     int64_t n2, int64_t n1, mf_adj qp, const int64_t *__restrict__ pinc_ptr, const int32_t *__restrict__ pinc,
     const uint8_t *__restrict__ pinc_loc, const uint8_t *__restrict__ pslot, const double *__restrict__ sc,
-    const uint8_t *__restrict__ mask, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
-    double *__restrict__ values, double *__restrict__ d)
+    const uint8_t *__restrict__ mask, const uint8_t *__restrict__ bcrow, const double *__restrict__ bval,
+    const int64_t *__restrict__ row_ptr, double *__restrict__ values, double *__restrict__ d)
 {
     __shared__ double acc_all[GO_GROUPS][2][MF_MAX_DEG];
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 4, sub = threadIdx.x & 15;
@@ -1103,19 +1106,21 @@ __global__ void __launch_bounds__(GO_GROUPS * 16) k_gather_oseen_p(
         }
     }
     const int64_t r = 2 * n2 + n;
-    const bool rm = mask ? mask[r] != 0 : false;
+    // the Dirichlet tests (column loads) only on rows next to a constrained dof
+    const uint8_t *mk = (mask && bcrow[r]) ? mask : nullptr;
+    const bool rm = mk ? mk[r] != 0 : false;
     const int64_t rb = row_ptr[r];
     double lift = 0.0;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
         for (int k = sub; k < dq; k += 16) {
             double val = acc[i][k];
-            flow_put(val, lift, rm, r, i * n2 + qp.col[q0 + k], mask, bval);
+            if (mk) flow_put(val, lift, rm, r, i * n2 + qp.col[q0 + k], mk, bval);
             values[rb + i * dq + k] = val;
         }
     if (sub == 0) {
         double val = 0.0;
-        flow_put(val, lift, rm, r, r, mask, bval);
+        if (mk) flow_put(val, lift, rm, r, r, mk, bval);
         values[rb + 2 * dq] = val;
     }
     if (__any_sync(gmask, lift != 0.0))
@@ -1331,12 +1336,17 @@ mf_status mf_assemble_fp64(int form, const mf_mesh *m, const mf_pattern *p, cons
         mf_prof_end(st);
         MF_CUDA(cudaGetLastError());
         mf_prof_begin("gather_oseen", st);
+        if (c->bc_mask) {  // rows next to a constrained dof: the pattern is structurally symmetric
+            MF_CUDA(cudaMemsetAsync(p->bcrow, 0, (size_t)p->n_rows, st));
+            k_mark_bc_rows<<<nblk(p->n_rows, 256), 256, 0, st>>>(p->n_rows, p->row_ptr, p->col_idx, c->bc_mask,
+                                                                 p->bcrow);
+        }
         k_gather_oseen_u<<<nblk(m->n_nodes, GO_GROUPS), GO_GROUPS * 16, 0, st>>>(
             m->n_nodes, p->adj[0], p->adj[1], p->inc_ptr, p->inc_loc, p->inc, p->inc_slot, p->inc_slot_pq,
-            p->scratch, c->bc_mask, c->bc_val, p->row_ptr, values, d);
+            p->scratch, c->bc_mask, p->bcrow, c->bc_val, p->row_ptr, values, d);
         k_gather_oseen_p<<<nblk(m->n_pnodes, GO_GROUPS), GO_GROUPS * 16, 0, st>>>(
             m->n_nodes, m->n_pnodes, p->adj[2], p->pinc_ptr, p->pinc, p->pinc_loc, p->pinc_slot, p->scratch,
-            c->bc_mask, c->bc_val, p->row_ptr, values, d);
+            c->bc_mask, p->bcrow, c->bc_val, p->row_ptr, values, d);
         mf_prof_end(st);
     }
     MF_CUDA(cudaGetLastError());
