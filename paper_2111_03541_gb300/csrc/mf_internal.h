@@ -91,8 +91,8 @@ struct mf_pattern {
     // the same reference entries as FP32 pairs (hi, lo), the translates'
     // coefficients as pairs (written per assembly), and per node a flag set
     // per assembly when the node or a neighbour is constrained (thermal Q1
-    // with translates; for the Picard flow form bcrow is the same flag per
-    // CSR row: the row or one of its columns constrained)
+    // with translates; for the flow forms bcrow is the same flag per CSR
+    // row: the row or one of its columns constrained)
     float2 *kref_df = nullptr;
     float2 *kc_df = nullptr;
     uint8_t *bcrow = nullptr;

@@ -313,13 +313,24 @@ __device__ __forceinline__ void ns_finish_row(int64_t row, int len, double *acc,
     if (lane == 0) d[row] = rm ? bval[row] - x[row] : -rsum + lift;
 }
 
+// flag[r] = 1 for every constrained dof s and each column r of row s (in a
+// structurally symmetric pattern with its diagonal: the rows holding s)
+__global__ void k_ns_mark_rows(int64_t n_rows, const int64_t *__restrict__ row_ptr,
+                               const int32_t *__restrict__ col_idx, const uint8_t *__restrict__ mask,
+                               uint8_t *__restrict__ flag)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_rows || !mask[s]) return;
+    for (int64_t q = row_ptr[s]; q < row_ptr[s + 1]; ++q) flag[col_idx[q]] = 1;
+}
+
 __global__ void __launch_bounds__(NG_WARPS * 32) k_gather_ns_u(
     int64_t n2, const int64_t *__restrict__ p0ptr, const int64_t *__restrict__ p1ptr,
     const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc, const uint8_t *__restrict__ inc_loc,
     const uint8_t *__restrict__ inc_slot, const uint8_t *__restrict__ inc_slot_pq, const double *__restrict__ sc,
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, const uint8_t *__restrict__ mask,
-    const double *__restrict__ bval, const double *__restrict__ x, double *__restrict__ values,
-    double *__restrict__ d)
+    const uint8_t *__restrict__ bcrow, const double *__restrict__ bval, const double *__restrict__ x,
+    double *__restrict__ values, double *__restrict__ d)
 {
     __shared__ double acc_all[NG_WARPS][NG_ROW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -346,7 +357,9 @@ __global__ void __launch_bounds__(NG_WARPS * 32) k_gather_ns_u(
         if (lane == 0) rsum += E[r];
         __syncwarp();
     }
-    ns_finish_row(row, len, acc, rsum, lane, row_ptr, col_idx, mask, bval, x, values, d);
+    // the Dirichlet tests (column loads) only on rows next to a constrained dof
+    ns_finish_row(row, len, acc, rsum, lane, row_ptr, col_idx, (mask && bcrow[row]) ? mask : nullptr, bval, x,
+                  values, d);
 }
 
 __global__ void __launch_bounds__(NG_WARPS * 32) k_gather_ns_p(
@@ -354,8 +367,8 @@ __global__ void __launch_bounds__(NG_WARPS * 32) k_gather_ns_p(
     const int64_t *__restrict__ pinc_ptr, const int32_t *__restrict__ pinc, const uint8_t *__restrict__ pinc_loc,
     const uint8_t *__restrict__ pinc_slot, const uint8_t *__restrict__ pinc_slot_pp, const double *__restrict__ sc,
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, const uint8_t *__restrict__ mask,
-    const double *__restrict__ bval, const double *__restrict__ x, double *__restrict__ values,
-    double *__restrict__ d)
+    const uint8_t *__restrict__ bcrow, const double *__restrict__ bval, const double *__restrict__ x,
+    double *__restrict__ values, double *__restrict__ d)
 {
     __shared__ double acc_all[NG_WARPS][NG_ROW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -381,7 +394,9 @@ __global__ void __launch_bounds__(NG_WARPS * 32) k_gather_ns_p(
         if (lane == 0) rsum += E[r];
         __syncwarp();
     }
-    ns_finish_row(row, len, acc, rsum, lane, row_ptr, col_idx, mask, bval, x, values, d);
+    // the Dirichlet tests (column loads) only on rows next to a constrained dof
+    ns_finish_row(row, len, acc, rsum, lane, row_ptr, col_idx, (mask && bcrow[row]) ? mask : nullptr, bval, x,
+                  values, d);
 }
 
 // x[g] = bval[g] on the Dirichlet dofs
@@ -434,13 +449,18 @@ mf_status mf_assemble_ns(const mf_mesh *m, const mf_pattern *p, const mf_coeffs 
     mf_prof_end(st);
     MF_CUDA(cudaGetLastError());
     mf_prof_begin("gather_ns", st);
+    if (c->bc_mask) {  // rows next to a constrained dof: the pattern is structurally symmetric
+        MF_CUDA(cudaMemsetAsync(p->bcrow, 0, (size_t)p->n_rows, st));
+        k_ns_mark_rows<<<nsblk(p->n_rows, NR_T), NR_T, 0, st>>>(p->n_rows, p->row_ptr, p->col_idx, c->bc_mask,
+                                                               p->bcrow);
+    }
     k_gather_ns_u<<<nsblk(2 * n2, NG_WARPS), NG_WARPS * 32, 0, st>>>(
         n2, p->adj[0].ptr, p->adj[1].ptr, p->inc_ptr, p->inc, p->inc_loc, p->inc_slot, p->inc_slot_pq, p->scratch,
-        p->row_ptr, p->col_idx, c->bc_mask, c->bc_val, c->advect, values, d);
+        p->row_ptr, p->col_idx, c->bc_mask, p->bcrow, c->bc_val, c->advect, values, d);
     if (n1 > 0)
         k_gather_ns_p<<<nsblk(n1, NG_WARPS), NG_WARPS * 32, 0, st>>>(
             n2, n1, p->adj[2].ptr, p->adj[3].ptr, p->pinc_ptr, p->pinc, p->pinc_loc, p->pinc_slot, p->pinc_slot_pp,
-            p->scratch, p->row_ptr, p->col_idx, c->bc_mask, c->bc_val, c->advect, values, d);
+            p->scratch, p->row_ptr, p->col_idx, c->bc_mask, p->bcrow, c->bc_val, c->advect, values, d);
     mf_prof_end(st);
     MF_CUDA(cudaGetLastError());
     return MF_OK;

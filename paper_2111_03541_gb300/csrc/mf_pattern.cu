@@ -1026,9 +1026,9 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
             k_csr_oseen_fill<<<nblk(p->n_rows), TPB, 0, st>>>(n2, n1, p->adj[0].ptr, p->adj[0].col, p->adj[1].ptr,
                                                              p->adj[1].col, p->adj[2].ptr, p->adj[2].col, p->row_ptr,
                                                              p->col_idx);
-        // Picard flow: per row a flag set per assembly when the row or one of
+        // flow forms: per row a flag set per assembly when the row or one of
         // its columns is constrained (the gathers skip the Dirichlet tests elsewhere)
-        if (!ns) MF_CUDA(cudaMallocAsync(&p->bcrow, (size_t)p->n_rows, st));
+        MF_CUDA(cudaMallocAsync(&p->bcrow, (size_t)p->n_rows, st));
         // Navier-Stokes: residual (15) and tangent (15 x 15) per element
         p->scratch_stride = ns ? 240 : 72;
         s = mf_flow_consts_upload();
