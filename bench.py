@@ -43,9 +43,9 @@ FCG_DIRS = 256  # stored directions of the flexible CG with the learned precondi
 # dram__bytes.sum.per_second x gpu__time_duration.sum = 0.698 TB/s x 288.0 us
 # = 201.1 MB (the same capture gives the finishing kernel's figures).
 MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 215876334 / 110592,
-                  "bytes_per_element": 0.759371e12 * 265.056e-6 / 110592,
+                  "bytes_per_element": 0.762606e12 * 264.0e-6 / 110592,
                   "sources": ("paper_2111_03541_gb300/csrc/mf_mixed.cu", "paper_2111_03541_gb300/csrc/mf_device.cuh"),
-                  "sha256": "b76252edd9c27a98"}
+                  "sha256": "21e9f2f9959965e2"}
 KERNELS_PER_ASSEMBLY = {"mixed": 4, "fp64": 2}
 # instruction-issue ceiling of GB300: one warp instruction per clock per SM
 # sub-partition, 4 per SM, 152 SMs, 2070 MHz maximum SM clock

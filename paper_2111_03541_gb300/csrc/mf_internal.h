@@ -92,7 +92,8 @@ struct mf_pattern {
     // coefficients as pairs (written per assembly), and per node a flag set
     // per assembly when the node or a neighbour is constrained (thermal Q1
     // with translates; for the flow forms bcrow is the same flag per CSR
-    // row: the row or one of its columns constrained)
+    // row: the row or one of its columns constrained; for Q1 elasticity per
+    // node: one of its dofs or a neighbour's constrained)
     float2 *kref_df = nullptr;
     float2 *kc_df = nullptr;
     uint8_t *bcrow = nullptr;

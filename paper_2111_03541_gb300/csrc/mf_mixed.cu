@@ -603,20 +603,34 @@ __device__ __forceinline__ double fixed_to_double(long long v, int S)
     return __longlong_as_double(bits - ((long long)S << 52));
 }
 
+// flag[n] = 1 for every node n holding a constrained dof or adjacent to one
+// (the adjacency includes each node itself)
+__global__ void k_mark_bc_nodes(int64_t n_nodes, const int64_t *__restrict__ adj_ptr,
+                                const int32_t *__restrict__ adj_col, const uint8_t *__restrict__ mask,
+                                uint8_t *__restrict__ flag)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= 3 * n_nodes || !mask[s]) return;
+    const int64_t m = s / 3;
+    for (int64_t q = adj_ptr[m]; q < adj_ptr[m + 1]; ++q) flag[adj_col[q]] = 1;
+}
+
 constexpr int FN_WARPS = 8;
 
 __global__ void __launch_bounds__(FN_WARPS * 32, 4) k_mixed_finish(
     int64_t n_begin, int64_t n_nodes, const int64_t *__restrict__ adj_ptr, const int32_t *__restrict__ adj_col,
     const int32_t *__restrict__ tpos, const long long *__restrict__ kacc, const long long *__restrict__ dacc,
-    const MixedState *__restrict__ st, long long rR, int rs, const uint8_t *__restrict__ mask,
-    const double *__restrict__ bval, const int64_t *__restrict__ row_ptr, double *__restrict__ values,
-    double *__restrict__ d)
+    const MixedState *__restrict__ st, long long rR, int rs, const uint8_t *__restrict__ mask_all,
+    const uint8_t *__restrict__ bcnode, const double *__restrict__ bval, const int64_t *__restrict__ row_ptr,
+    double *__restrict__ values, double *__restrict__ d)
 {
     __shared__ double rows_all[FN_WARPS][3][3 * MF_MAX_DEG];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = n_begin + (int64_t)blockIdx.x * FN_WARPS + w;
     if (n >= n_nodes) return;  // warp-uniform
     double(*rows)[3 * MF_MAX_DEG] = rows_all[w];
+    // the Dirichlet tests only on nodes with a constrained dof at or next to them
+    const uint8_t *mask = (mask_all && bcnode[n]) ? mask_all : nullptr;
     const int S = st->S, Sd = st->Sd;
     const int64_t p0 = adj_ptr[n];
     const int deg = (int)(adj_ptr[n + 1] - p0);
@@ -733,6 +747,11 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     // exact, so order-free); the finishing gather then writes each CSR row once
     MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->n_upper, st));
     MF_CUDA(cudaMemsetAsync(p->dacc, 0, sizeof(long long) * 3 * m->n_nodes, st));
+    if (c->bc_mask) {  // nodes at or next to a constrained dof
+        MF_CUDA(cudaMemsetAsync(p->bcrow, 0, (size_t)m->n_nodes, st));
+        k_mark_bc_nodes<<<(unsigned)((3 * m->n_nodes + 255) / 256), 256, 0, st>>>(m->n_nodes, p->adj[0].ptr,
+                                                                               p->adj[0].col, c->bc_mask, p->bcrow);
+    }
     // element chunks on the caller's stream; with more than one chunk the
     // finishing of the nodes a chunk completes runs on the side stream
     // (MF_SLABS: one chunk measured fastest)
@@ -755,7 +774,7 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
                 mf_prof_begin("mixed_finish", s2);
                 k_mixed_finish<<<(unsigned)((n1 - n0 + FN_WARPS - 1) / FN_WARPS), FN_WARPS * 32, 0, s2>>>(
                     n0, n1, p->adj[0].ptr, p->adj[0].col, p->tpos, p->kacc, p->dacc, ms, rR, rs, c->bc_mask,
-                    c->bc_val, p->row_ptr, values, d);
+                    p->bcrow, c->bc_val, p->row_ptr, values, d);
                 mf_prof_end(s2);
             }
             MF_CUDA(cudaGetLastError());

@@ -962,6 +962,9 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         k_mixed_etgt<<<nblk(36 * m->n_elems), TPB, 0, st>>>(m->n_elems, m->conn, p->cbase, p->slot, p->etgt);
         MF_CUDA(cudaMallocAsync(&p->kacc, sizeof(long long) * 9 * p->n_upper, st));
         MF_CUDA(cudaMallocAsync(&p->dacc, sizeof(long long) * 3 * m->n_nodes, st));
+        // per node a flag set per assembly when one of its dofs or a
+        // neighbour's is constrained (the mixed finishing tests the mask there only)
+        MF_CUDA(cudaMallocAsync(&p->bcrow, (size_t)m->n_nodes, st));
         p->scratch_stride = 36 * 9 + 24;
         mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);
         if (ss != MF_OK) { free_inc(incv, st); return ss; }
