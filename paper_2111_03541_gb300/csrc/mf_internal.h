@@ -132,6 +132,10 @@ struct mf_pattern {
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::vector<cudaEvent_t> slab_ev;
+    // mixed path: the accumulator clears run on clr_side beside the bound
+    // pass (forked and joined by events, capturable in a CUDA graph)
+    cudaStream_t clr_side = nullptr;
+    cudaEvent_t clr_fork = nullptr, clr_join = nullptr;
 };
 
 // Boundary facets of a mesh for one pattern (thermal or elasticity form): the

@@ -733,6 +733,21 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     const double cmu = 1.0 / (2.0 * (1.0 + nu));
     MixedState *ms = static_cast<MixedState *>(p->mixed_state);
     const int64_t ne = m->n_elems;
+    // element blocks go straight into the int64 block accumulator (atomics:
+    // exact, so order-free); the finishing gather then writes each CSR row once.
+    // The accumulator clears (HBM writes) and the node flags run on the
+    // pattern's clear stream beside the bound pass (latency-bound gathers);
+    // the element kernel waits for both.
+    MF_CUDA(cudaEventRecord(p->clr_fork, st));
+    MF_CUDA(cudaStreamWaitEvent(p->clr_side, p->clr_fork, 0));
+    MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->n_upper, p->clr_side));
+    MF_CUDA(cudaMemsetAsync(p->dacc, 0, sizeof(long long) * 3 * m->n_nodes, p->clr_side));
+    if (c->bc_mask) {  // nodes at or next to a constrained dof
+        MF_CUDA(cudaMemsetAsync(p->bcrow, 0, (size_t)m->n_nodes, p->clr_side));
+        k_mark_bc_nodes<<<(unsigned)((3 * m->n_nodes + 255) / 256), 256, 0, p->clr_side>>>(
+            m->n_nodes, p->adj[0].ptr, p->adj[0].col, c->bc_mask, p->bcrow);
+    }
+    MF_CUDA(cudaEventRecord(p->clr_join, p->clr_side));
     mf_prof_begin("mixed_bound", st);
     MF_CUDA(cudaMemsetAsync(ms, 0, sizeof(MixedState), st));
     if (ne > 0)
@@ -741,17 +756,9 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     const double bmax = fmax(fabs(c->source[0]), fmax(fabs(c->source[1]), fabs(c->source[2])));
     k_mixed_scale<<<1, 1, 0, st>>>(ms, fabs(r), bmax);
     mf_prof_end(st);
+    MF_CUDA(cudaStreamWaitEvent(st, p->clr_join, 0));
     const size_t smem = sizeof(WarpSmem) * MX_WARPS;
     MF_CUDA(cudaFuncSetAttribute(k_mixed_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // element blocks go straight into the int64 block accumulator (atomics:
-    // exact, so order-free); the finishing gather then writes each CSR row once
-    MF_CUDA(cudaMemsetAsync(p->kacc, 0, sizeof(long long) * 9 * p->n_upper, st));
-    MF_CUDA(cudaMemsetAsync(p->dacc, 0, sizeof(long long) * 3 * m->n_nodes, st));
-    if (c->bc_mask) {  // nodes at or next to a constrained dof
-        MF_CUDA(cudaMemsetAsync(p->bcrow, 0, (size_t)m->n_nodes, st));
-        k_mark_bc_nodes<<<(unsigned)((3 * m->n_nodes + 255) / 256), 256, 0, st>>>(m->n_nodes, p->adj[0].ptr,
-                                                                               p->adj[0].col, c->bc_mask, p->bcrow);
-    }
     // element chunks on the caller's stream; with more than one chunk the
     // finishing of the nodes a chunk completes runs on the side stream
     // (MF_SLABS: one chunk measured fastest)

@@ -771,6 +771,11 @@ void mf_pattern_free(mf_pattern *p)
     if (p->side) cudaStreamDestroy(p->side);
     p->fork_ev = p->join_ev = nullptr;
     p->side = nullptr;
+    if (p->clr_fork) cudaEventDestroy(p->clr_fork);
+    if (p->clr_join) cudaEventDestroy(p->clr_join);
+    if (p->clr_side) cudaStreamDestroy(p->clr_side);
+    p->clr_fork = p->clr_join = nullptr;
+    p->clr_side = nullptr;
     cudaFree(p->row_ptr);
     cudaFree(p->col_idx);
     cudaFree(p->q2s_map);
@@ -965,6 +970,9 @@ mf_status mf_pattern_build_impl(const mf_mesh *m, int form, cudaStream_t st, mf_
         // per node a flag set per assembly when one of its dofs or a
         // neighbour's is constrained (the mixed finishing tests the mask there only)
         MF_CUDA(cudaMallocAsync(&p->bcrow, (size_t)m->n_nodes, st));
+        MF_CUDA(cudaStreamCreateWithFlags(&p->clr_side, cudaStreamNonBlocking));
+        MF_CUDA(cudaEventCreateWithFlags(&p->clr_fork, cudaEventDisableTiming));
+        MF_CUDA(cudaEventCreateWithFlags(&p->clr_join, cudaEventDisableTiming));
         p->scratch_stride = 36 * 9 + 24;
         mf_status ss = plan_slabs(m, incv, p->scratch_stride, st, p);
         if (ss != MF_OK) { free_inc(incv, st); return ss; }
