@@ -668,9 +668,10 @@ __global__ void __launch_bounds__(GD_WARPS * 32, 8) k_gather_th_q1df(
 }
 
 // Thermal Q1 (or capacity) rows on a lexicographic box of translates of a
-// rectangular cell (box_row_q1): one thread per node; a block's rows are
-// consecutive in the CSR arrays, so they are staged in shared memory and
-// stored with coalesced writes.
+// rectangular cell (box_row_q1): one thread per node; a warp's 32 rows are
+// consecutive in the CSR arrays, so each warp stages them in its part of
+// shared memory and stores them with coalesced writes (no block barrier: a
+// warp with rows next to the constrained boundary delays only itself).
 constexpr int QB = 128;  // nodes (threads) per block
 
 __global__ void __launch_bounds__(QB) k_rows_q1box(int n_nodes, int nx1, int ny1, int nz1, mf_box_classes C,
@@ -687,17 +688,19 @@ __global__ void __launch_bounds__(QB) k_rows_q1box(int n_nodes, int nx1, int ny1
     __shared__ double cls[8];
     if (threadIdx.x < 8) cls[threadIdx.x] = capacity ? C.m_cls[threadIdx.x] : C.k_cls[threadIdx.x];
     __syncthreads();
-    const int n0 = blockIdx.x * QB, n = n0 + threadIdx.x;
-    const int nend = min(n_nodes, n0 + QB);
-    const int64_t r0 = row_ptr[n0];
+    const int lane = threadIdx.x & 31, wbase = blockIdx.x * QB + (threadIdx.x & ~31), n = wbase + lane;
+    if (wbase >= n_nodes) return;  // warp-uniform
+    const int nend = min(n_nodes, wbase + 32);
+    const int64_t r0 = row_ptr[wbase];
+    double *wst = stage + (threadIdx.x & ~31) * 27;  // this warp's 32 rows
     if (n < n_nodes) {
-        double *row = stage + (row_ptr[n] - r0);
+        double *row = wst + (row_ptr[n] - r0);
         d[n] = box_row_q1(n, nx1, ny1, nz1, cls, capacity ? 0.0 : f * C.dref, kc, mask != nullptr && bcrow[n] != 0,
                           mask, bval, [row](int k, double v) { row[k] = v; });
     }
-    __syncthreads();
+    __syncwarp();
     const int64_t cnt = row_ptr[nend] - r0;
-    for (int64_t i = threadIdx.x; i < cnt; i += QB) values[r0 + i] = stage[i];
+    for (int64_t i = lane; i < cnt; i += 32) values[r0 + i] = wst[i];
 }
 
 // ---------------------------------------------------------------------------
