@@ -92,6 +92,37 @@ def test_mixed_bit_reproducible(mf):
     assert torch.equal(v1, v2) and torch.equal(d1, d2)
 
 
+def test_mixed_alternating_coefficients_on_one_pattern(mf):
+    """Re-assembly on one pattern keeps no state from the call before: five
+    calls with two coefficient sets (different Poisson ratio, coefficients,
+    lifting and Dirichlet data; an FP64 call in between) give, bit for bit,
+    what a fresh pattern gives for the same coefficients."""
+    import torch
+    prob = gen.elastic_problem(9)
+    rng = np.random.default_rng(21)
+    prob["bc_val"] = np.where(prob["bc_mask"] != 0, rng.standard_normal(prob["bc_val"].shape[0]), 0.0)
+    P = mf.Problem(prob)
+    coef_b = P.coef * 3.0
+    cA = P.make_coeffs()
+    cB = P.make_coeffs(coef=coef_b, bc=False)
+    cB.nu = 0.45
+
+    def run(Q, c):
+        v, d = Q.assemble(mf.MF_PREC_MIXED, coeffs=c)
+        mf.mf_sync_status()
+        return v.clone(), d.clone()
+
+    seq = [run(P, cA), run(P, cB)]
+    P.assemble(mf.MF_PREC_FP64)
+    seq += [run(P, cA), run(P, cB), run(P, cA)]
+    Q = mf.Problem(prob)
+    fresh_b = run(Q, cB)  # cB names no buffer of P's pattern
+    for k, (v, d) in enumerate(seq):
+        ref = seq[0] if k % 2 == 0 else fresh_b
+        assert torch.equal(v, ref[0]) and torch.equal(d, ref[1]), k
+    assert not torch.equal(seq[0][0], seq[1][0])
+
+
 def test_mixed_full_size_sampled_rows(mf, orc):
     prob = gen.elastic_problem(64)
     P = mf.Problem(prob)
