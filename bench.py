@@ -44,28 +44,34 @@ FCG_DIRS = 256  # stored directions of the flexible CG with the learned precondi
 # = 201.1 MB (the same capture gives the finishing kernel's figures).
 MIXED_ELEM_NCU = {"kernel": "mixed_elem", "inst_per_element": 215876334 / 110592,
                   "bytes_per_element": 0.762606e12 * 264.0e-6 / 110592,
-                  # the element kernel and everything before it (its helpers); the
-                  # finishing kernel and the host code follow the marker
-                  "sources": (("paper_2111_03541_gb300/csrc/mf_mixed.cu", "// finishing: one warp per node"),
+                  # the element kernel and its helpers: the file up to the bound pass,
+                  # and from the element kernel up to the finishing kernel
+                  "sources": (("paper_2111_03541_gb300/csrc/mf_mixed.cu", None, "// pre-pass (per assembly"),
+                              ("paper_2111_03541_gb300/csrc/mf_mixed.cu", "// element kernel",
+                               "// finishing: one warp per node"),
                               "paper_2111_03541_gb300/csrc/mf_device.cuh"),
-                  "sha256": "6210cec16ece14f3"}
+                  "sha256": "2445ca262d27b50c"}
 KERNELS_PER_ASSEMBLY = {"mixed": 4, "fp64": 2}
 # instruction-issue ceiling of GB300: one warp instruction per clock per SM
 # sub-partition, 4 per SM, 152 SMs, 2070 MHz maximum SM clock
 ISSUE_PEAK = 152 * 4 * 2.070e9
 
 
-def sources_hash(files) -> str:
-    """Hash of the source files; an entry (path, marker) takes the file's text
-    up to the marker line only (the part that defines the captured kernel)."""
+def sources_hash(files, root=None) -> str:
+    """Hash of the source files; an entry (path, start, end) takes the file's
+    text from the start marker (None: the beginning) up to the end marker
+    (None: the end), the part that defines the captured kernel."""
     import hashlib
     h = hashlib.sha256()
     for f in files:
-        path, marker = (f, None) if isinstance(f, str) else f
-        with open(os.path.join(ROOT, path), "rb") as fh:
+        path, start, end = (f, None, None) if isinstance(f, str) else f
+        with open(os.path.join(root or ROOT, path), "rb") as fh:
             data = fh.read()
-        if marker is not None:
-            cut = data.find(marker.encode())
+        if start is not None:
+            cut = data.find(start.encode())
+            data = b"" if cut < 0 else data[cut:]
+        if end is not None:
+            cut = data.find(end.encode())
             data = data if cut < 0 else data[:cut]
         h.update(data)
     return h.hexdigest()[:16]

@@ -155,19 +155,34 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 // pre-pass (per assembly, from the current coordinates and coefficients):
 // bound of the fixed-point values, FP32 geometry is enough for a bound
 // ---------------------------------------------------------------------------
+// an FP64 value as FP32 by its bits, toward zero (integer operations only; the
+// FP64 pipe runs at 1/64 of the FP32 rate): |x| below 2^-126 gives a signed
+// zero, above the FP32 range an infinity (the bound then reports non-finite)
+__device__ __forceinline__ float trunc_to_float(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sgn);
+    if (e >= 255) return __uint_as_float(sgn | 0x7f800000u);
+    return __uint_as_float(sgn | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffull));
+}
+
 // mx = max over elements of mu_e max_row sum_q G^2 / mu_e-free geometry,
 // vol = max over elements of sum_q |detJ_q| (float bits, atomicMax on
 // non-negative floats orders like the integers)
 __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
                               const double *__restrict__ Ec, float cmu, MixedState *st, int *status)
 {
+    __shared__ float red[2][8];
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f, vol = 0.f;
     if (e < n_el) {
         float x[8][3];
         const int32_t *cn = conn + 8 * e;
         for (int a = 0; a < 8; ++a)
-            for (int i = 0; i < 3; ++i) x[a][i] = (float)(X[3 * (int64_t)cn[a] + i] - X[3 * (int64_t)cn[0] + i]);
+            for (int i = 0; i < 3; ++i)
+                x[a][i] = trunc_to_float(X[3 * (int64_t)cn[a] + i] - X[3 * (int64_t)cn[0] + i]);
         const float g = (float)GD;
         float rowsum[24] = {};
         for (int q = 0; q < 8; ++q) {
@@ -210,16 +225,29 @@ __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const 
             mx *= (float)E * cmu;
         }
     }
+    // each thread tests its own values (fmaxf drops a NaN next to a number),
+    // then block maxima: one atomic per block and quantity
+    if (!isfinite(mx) || !isfinite(vol)) {
+        mf_dev_fail(status, MF_ERR_NONFINITE);
+        mx = vol = 0.f;
+    }
     for (int o = 16; o > 0; o >>= 1) {
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         vol = fmaxf(vol, __shfl_xor_sync(0xffffffffu, vol, o));
     }
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        if (!isfinite(mx) || !isfinite(vol)) mf_dev_fail(status, MF_ERR_NONFINITE);
-        else {
-            if (mx > 0.f) atomicMax(&st->mx_bits, __float_as_int(mx));
-            if (vol > 0.f) atomicMax(&st->vol_bits, __float_as_int(vol));
+        red[0][w] = mx;
+        red[1][w] = vol;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            mx = fmaxf(mx, red[0][i]);
+            vol = fmaxf(vol, red[1][i]);
         }
+        if (mx > 0.f) atomicMax(&st->mx_bits, __float_as_int(mx));
+        if (vol > 0.f) atomicMax(&st->vol_bits, __float_as_int(vol));
     }
 }
 

@@ -123,6 +123,27 @@ def test_mixed_alternating_coefficients_on_one_pattern(mf):
     assert not torch.equal(seq[0][0], seq[1][0])
 
 
+def test_mixed_nan_coordinate_latched(mf):
+    """A NaN coordinate (one node: its 8 elements, mixed with finite ones in
+    their warps) is reported as MF_ERR_NONFINITE by the fixed-point bound
+    pass, and the next assembly with the coordinate restored is clean."""
+    import torch
+    P = mf.Problem(gen.elastic_problem(6))
+    v0, d0 = [t.clone() for t in P.assemble(mf.MF_PREC_MIXED)]
+    mf.mf_sync_status()
+    node = 3 * 49 + 2 * 7 + 3  # an interior node of the 7 x 7 x 7 node lattice
+    keep = P.coords[node, 1].item()
+    P.coords[node, 1] = float("nan")
+    P.assemble(mf.MF_PREC_MIXED)
+    with pytest.raises(mf.MFError) as ei:
+        mf.mf_sync_status()
+    assert ei.value.status == mf.MF_ERR_NONFINITE
+    P.coords[node, 1] = keep
+    v1, d1 = P.assemble(mf.MF_PREC_MIXED)
+    mf.mf_sync_status()
+    assert torch.equal(v0, v1) and torch.equal(d0, d1)
+
+
 def test_mixed_full_size_sampled_rows(mf, orc):
     prob = gen.elastic_problem(64)
     P = mf.Problem(prob)
