@@ -229,17 +229,26 @@ def oracle_sample(prob, layers: int):
     return ne, time.perf_counter() - t
 
 
+CPU_PCG_ITERS = 20
+
+
 def cpu_baseline(prob):
     """The oracle on the host: the whole workload on all host cores (the
-    OpenMP build of the same oracle source, bit-identical results), and the
-    single-threaded oracle as it stands on one core (about 10 s)."""
+    OpenMP build of the same oracle source, bit-identical results), the
+    single-threaded oracle as it stands on one core (about 10 s), and a
+    bounded sample of the oracle's Jacobi-PCG on the assembled system (one
+    core, as it stands: a fixed number of iterations, about a second)."""
     import oracle
     cores = os.cpu_count() or 1
     ne = prob["conn"].shape[0]
     t = time.perf_counter()
-    oracle.assemble_threads(prob, cores)
+    sys_ = oracle.assemble_threads(prob, cores)
     sec_all = time.perf_counter() - t
     ne1, sec1 = oracle_sample(prob, N_GRID + 1)
+    t = time.perf_counter()
+    oracle.pcg(sys_, tol=1e-300, maxit=CPU_PCG_ITERS)
+    sec_pcg = time.perf_counter() - t
+    nrow, nnz = sys_["d"].shape[0], sys_["col"].shape[0]
     model = ""
     try:
         with open("/proc/cpuinfo") as f:
@@ -255,7 +264,12 @@ def cpu_baseline(prob):
                       f"the same source): {sec_all:.2f} s",
             "cpu_model": model,
             "single_core": {"value": ne1 / sec1, "unit": UNIT, "cores": 1,
-                            "sample": f"the single-threaded oracle on the same {ne1} elements: {sec1:.2f} s"}}
+                            "sample": f"the single-threaded oracle on the same {ne1} elements: {sec1:.2f} s"},
+            "solve": {"kind": "oracle", "cores": 1, "iterations": CPU_PCG_ITERS,
+                      "s_per_iteration": sec_pcg / CPU_PCG_ITERS,
+                      "sample": f"the oracle's Jacobi-PCG (single-threaded, as it stands) on the assembled 64^3 "
+                                f"system ({nrow} rows, {nnz} nonzeros): {CPU_PCG_ITERS} iterations in "
+                                f"{sec_pcg:.2f} s, its set-up (diagonal, first residual) included"}}
 
 
 def run_reference(args):
