@@ -170,11 +170,14 @@ __device__ __forceinline__ float trunc_to_float(double x)
 
 // mx = max over elements of mu_e max_row sum_q G^2 / mu_e-free geometry,
 // vol = max over elements of sum_q |detJ_q| (float bits, atomicMax on
-// non-negative floats orders like the integers)
-__global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const int32_t *__restrict__ conn,
-                              const double *__restrict__ Ec, float cmu, MixedState *st, int *status)
+// non-negative floats orders like the integers); one thread per element
+constexpr int BOUND_THREADS = 256;
+__global__ void __launch_bounds__(BOUND_THREADS) k_mixed_bound(int64_t n_el, const double *__restrict__ X,
+                                                               const int32_t *__restrict__ conn,
+                                                               const double *__restrict__ Ec, float cmu,
+                                                               MixedState *st, int *status)
 {
-    __shared__ float red[2][8];
+    __shared__ float red[2][BOUND_THREADS / 32];
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f, vol = 0.f;
     if (e < n_el) {
@@ -242,7 +245,7 @@ __global__ void k_mixed_bound(int64_t n_el, const double *__restrict__ X, const 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+        for (int i = 1; i < BOUND_THREADS / 32; ++i) {
             mx = fmaxf(mx, red[0][i]);
             vol = fmaxf(vol, red[1][i]);
         }
@@ -779,8 +782,8 @@ mf_status mf_assemble_mixed(int form, const mf_mesh *m, const mf_pattern *p, con
     mf_prof_begin("mixed_bound", st);
     MF_CUDA(cudaMemsetAsync(ms, 0, sizeof(MixedState), st));
     if (ne > 0)
-        k_mixed_bound<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, m->coords, m->conn, c->elem_coef,
-                                                                    (float)cmu, ms, status);
+        k_mixed_bound<<<(unsigned)((ne + BOUND_THREADS - 1) / BOUND_THREADS), BOUND_THREADS, 0, st>>>(
+            ne, m->coords, m->conn, c->elem_coef, (float)cmu, ms, status);
     const double bmax = fmax(fabs(c->source[0]), fmax(fabs(c->source[1]), fabs(c->source[2])));
     k_mixed_scale<<<1, 1, 0, st>>>(ms, fabs(r), bmax);
     mf_prof_end(st);
