@@ -195,7 +195,8 @@ mf_status mf_pattern_destroy(mf_pattern *pattern);
  * multiplier, converted once to FP64; K within about 2^-40 of the row scale
  * of the FP64 result.  Errors:
  * MF_ERR_INVALID_ARG, MF_ERR_UNSUPPORTED, MF_ERR_CUDA; non-finite
- * coefficients are latched (MF_ERR_NONFINITE). */
+ * coefficients (on the mixed path also a non-finite coordinate, found by
+ * the pass that sets the fixed-point scale) are latched (MF_ERR_NONFINITE). */
 mf_status mf_assemble(int32_t form, const mf_mesh *mesh, const mf_pattern *pattern,
                       const mf_coeffs *coeffs, int32_t prec, mf_csr *K, double *d, void *stream);
 /* form = MF_FORM_NS (prec FP64, on a pattern built for MF_FORM_NS: every
