@@ -1323,7 +1323,9 @@ __global__ void k_jacobi0(int64_t n, const double *__restrict__ b, const double 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = mask[i] ? b[i] : w * dinv[i] * b[i];
 }
-__global__ void k_resid(int64_t n, const double *__restrict__ b, const double *__restrict__ t, double *__restrict__ r)
+// r = b - t elementwise; r may be t (the flow preconditioner forms its
+// velocity right-hand side in place), so neither is declared restrict
+__global__ void k_resid(int64_t n, const double *__restrict__ b, const double *t, double *r)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) r[i] = b[i] - t[i];
