@@ -202,3 +202,20 @@ def test_capacity_matrix_closed_form(orc):
     assert np.abs(Me - vol / 420.0 * M).max() < 1e-15
     assert abs(Me.sum() - vol) < 1e-15
     assert np.abs(Me.sum(axis=1) - vol * np.array([-1 / 20] * 4 + [1 / 5] * 6)).max() < 1e-15
+
+
+def test_radiation_tangent_is_the_derivative_on_a_face(orc):
+    """Radiation on a 6-node face with a varying temperature: the tangent is
+    minus the derivative of the load (central differences)."""
+    rng = np.random.default_rng(12)
+    V = np.array([[0.1, 0.0, 0.2], [1.1, 0.2, 0.0], [0.3, 0.9, 0.4]])
+    Xf = np.vstack([V, 0.5 * (V[0] + V[1]), 0.5 * (V[1] + V[2]), 0.5 * (V[2] + V[0])])
+    T = 0.7 + 0.5 * rng.random(6)
+    Kf, _ = orc.facet_radiation(orc.P2T, Xf, 0.8, 1.3, T)
+    h = 1e-6
+    for b in range(6):
+        e = np.zeros(6)
+        e[b] = h
+        _, rp = orc.facet_radiation(orc.P2T, Xf, 0.8, 1.3, T + e)
+        _, rm = orc.facet_radiation(orc.P2T, Xf, 0.8, 1.3, T - e)
+        assert np.abs(-(rp - rm) / (2 * h) - Kf[:, b]).max() < 1e-8 * np.abs(Kf).max()

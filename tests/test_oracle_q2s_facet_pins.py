@@ -86,3 +86,42 @@ def test_flat_face_mass_matrix_by_independent_quadrature(orc):
         A = np.linalg.norm(np.cross(Xf[1] - Xf[0], Xf[2] - Xf[0]))
         Kf, _, _ = orc.facet_thermal(orc.Q2S, Xf, 1.7, 0.4)
         assert np.abs(Kf - 1.7 * A / 4.0 * ref).max() < 1e-14
+
+
+def test_radiation_on_flat_faces_closed_forms(orc):
+    """Radiation e_m sigma^b (T, T_env^4 - T^4) (Sec. 4.1) on a flat 8-node
+    face at a uniform temperature: load es (T_env^4 - T^4) int N_m (-A/12 at
+    the vertices, A/3 at the midpoints), tangent 4 es T^3 times the face mass
+    matrix, i.e. 4 es T^3 / h times the convection matrix of the same face."""
+    V = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], float) @ np.array(
+        [[1.2, 0.1, 0.0], [0.2, 0.9, 0.1], [0.0, 0.1, 1.1]]).T
+    pairs = [(0, 1), (2, 3), (4, 5), (6, 7), (0, 2), (1, 3), (4, 6), (5, 7), (0, 4), (1, 5), (2, 6), (3, 7)]
+    X = np.vstack([V] + [0.5 * (V[p] + V[q]) for p, q in pairs])
+    es, te, T, h = 0.7, 1.3, 0.9, 1.7
+    for face in range(6):
+        Xf = X[orc.facet_nodes(orc.Q2S, face)]
+        A = np.linalg.norm(np.cross(Xf[1] - Xf[0], Xf[2] - Xf[0]))
+        mom = A * np.array([-1 / 12] * 4 + [1 / 3] * 4)
+        Kr, rr = orc.facet_radiation(orc.Q2S, Xf, es, te, np.full(8, T))
+        Kc, _, _ = orc.facet_thermal(orc.Q2S, Xf, h, 0.0)
+        assert np.abs(rr - es * (te ** 4 - T ** 4) * mom).max() < 1e-14
+        assert np.abs(Kr - 4 * es * T ** 3 / h * Kc).max() < 1e-14 * np.abs(Kr).max()
+        assert np.abs(Kr - Kr.T).max() <= 1e-15 * np.abs(Kr).max()  # symmetric up to product order
+
+
+def test_radiation_tangent_is_the_derivative_on_warped_faces(orc):
+    """On the warped faces of a jittered brick, with a varying temperature,
+    the tangent is minus the derivative of the load (central differences)."""
+    _, X = _brick(seed=9, amp=0.15)
+    rng = np.random.default_rng(10)
+    for face in range(6):
+        Xf = X[orc.facet_nodes(orc.Q2S, face)]
+        T = 0.7 + 0.5 * rng.random(8)
+        Kf, _ = orc.facet_radiation(orc.Q2S, Xf, 0.6, 1.2, T)
+        hstep = 1e-6
+        for b in range(8):
+            e = np.zeros(8)
+            e[b] = hstep
+            _, rp = orc.facet_radiation(orc.Q2S, Xf, 0.6, 1.2, T + e)
+            _, rm = orc.facet_radiation(orc.Q2S, Xf, 0.6, 1.2, T - e)
+            assert np.abs(-(rp - rm) / (2 * hstep) - Kf[:, b]).max() < 1e-8 * np.abs(Kf).max()
