@@ -158,7 +158,7 @@ def elem_thermal(elem: int, quad_kind: int, X, k: float, f: float = 1.0, fnodal=
 
 def elem_elastic(X, E: float, nu: float, body=(0.0, 0.0, -1.0), elem: int = None):
     """Element stiffness [3 npe, 3 npe] (dof 3 a + c), load [3 npe] and min detJ;
-    elem Q1 (the default, 8 nodes) or Q2S (20 nodes)."""
+    elem Q1 (the default, 8 nodes), Q2S (20 nodes) or P2T (10 nodes)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     b = np.ascontiguousarray(body, dtype=np.float64)
     if elem is None or elem == Q1:
@@ -166,11 +166,12 @@ def elem_elastic(X, E: float, nu: float, body=(0.0, 0.0, -1.0), elem: int = None
         de = np.zeros(24)
         det = lib().or_elem_elastic_q1(_p(X), E, nu, _p(b), _p(Ke), _p(de))
         return Ke, de, det
-    if elem != Q2S:
-        raise ValueError("elasticity takes the Q1 or Q2S brick")
-    Ke = np.zeros((60, 60))
-    de = np.zeros(60)
-    det = lib().or_elem_elastic(Q2S, _p(X), E, nu, _p(b), _p(Ke), _p(de))
+    if elem not in (Q2S, P2T):
+        raise ValueError("elasticity takes the Q1 or Q2S brick or the P2T tetrahedron")
+    m = 3 * (20 if elem == Q2S else 10)
+    Ke = np.zeros((m, m))
+    de = np.zeros(m)
+    det = lib().or_elem_elastic(elem, _p(X), E, nu, _p(b), _p(Ke), _p(de))
     return Ke, de, det
 
 

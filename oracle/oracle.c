@@ -442,20 +442,23 @@ double or_elem_capacity(int elem, const double *X, double C, double *Me)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Linear elasticity on Q1 or Q2S bricks (Sec. 4.2: -(d_i,j, sigma_ij),    */
+/* Linear elasticity on Q1 or Q2S bricks or P2T tetrahedra (Sec. 4.2:      */
+/* -(d_i,j, sigma_ij),                                                      */
 /* sigma = lambda delta eps_mm + 2 mu eps, lambda = E nu / ((1+nu)(1-2nu)),  */
 /* mu = E / (2(1+nu))).  With test w = N_a e_c and trial u = N_b e_c':        */
 /* eps(w):sigma(u) = lambda d_c N_a d_c' N_b + mu d_c' N_a d_c N_b            */
 /*                 + mu delta_cc' gradN_a . gradN_b.                         */
 /* Rule: 2 x 2 x 2 Gauss (Q1), 3 x 3 x 3 Gauss (Q2S, the cantilever bricks   */
-/* of Sec. 4.2).  With m = 3 npe: Ke[(3a+c)*m + 3b+c'],                      */
+/* of Sec. 4.2), the 64-point collapsed rule (P2T, exact for the degree-2   */
+/* integrands of an affine quadratic tetrahedron).                          */
+/* With m = 3 npe: Ke[(3a+c)*m + 3b+c'],                                     */
 /* de[3a+c] = sum_q w detJ body_c N_a.  Returns min detJ.                    */
 /* ------------------------------------------------------------------------ */
 double or_elem_elastic(int elem, const double *X, double E, double nu, const double *body,
                        double *Ke, double *de)
 {
     double pts[64 * 3], w[64], N[20], g[60];
-    const int nq = or_quad(elem == OR_Q2S ? OR_QHEX27 : OR_QHEX8, pts, w);
+    const int nq = or_quad(elem == OR_Q2S ? OR_QHEX27 : (elem == OR_P2T ? OR_QTET64 : OR_QHEX8), pts, w);
     const int npe = elem_npe(elem), m = 3 * npe;
     const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     const double mu = E / (2.0 * (1.0 + nu));
@@ -1169,7 +1172,7 @@ static int emit_filtered(const or_problem *p, coo_t *c, double *d, double *pmass
                 for (int b = 0; b < npe; ++b)
                     if (coo_push(c, cn[a], cn[b], Ke[a * npe + b])) return -1;
         } else if (p->form == OR_ELASTIC) {
-            if (p->elem != OR_Q1 && p->elem != OR_Q2S) return -3;
+            if (p->elem != OR_Q1 && p->elem != OR_Q2S && p->elem != OR_P2T) return -3;
             const double det = or_elem_elastic(p->elem, X, p->coef[e], p->nu, p->source, Ke, de);
             if (!(det > 0.0)) return -2;
             const int m = 3 * npe;
@@ -1326,7 +1329,7 @@ int or_assemble_threads(const or_problem *p, int threads, int64_t *n_rows, int64
                         int32_t **col, double **val, double **d)
 {
     if (p->n_facets > 0 || p->form == OR_OSEEN) return -3;
-    if (p->form == OR_ELASTIC && p->elem != OR_Q1 && p->elem != OR_Q2S) return -3;
+    if (p->form == OR_ELASTIC && p->elem != OR_Q1 && p->elem != OR_Q2S && p->elem != OR_P2T) return -3;
     const int64_t n = or_ndofs(p), ne = p->n_el;
     const int dim = elem_dim(p->elem), npe = elem_npe(p->elem);
     const int m = p->form == OR_ELASTIC ? 3 * npe : npe, mm = m * m;
