@@ -157,8 +157,12 @@ def test_second_order_scalar(orc, rho):
     assert rates.min() > 1.9, (errs, rates)
 
 
-def _heat_system(orc, n=6):
-    prob = gen.thermal_p1_problem(n)
+def _heat_system(orc, kind="p1"):
+    """Conduction with k = 1, f = 1, u = 0 on the boundary, unassembled
+    Dirichlet rows: P1 triangles, 8-node quadrilaterals or 10-node
+    tetrahedra (the elements of the paper's 2D and 3D thermal cases)."""
+    prob = {"p1": lambda: gen.thermal_p1_problem(6), "q2q": lambda: gen.thermal_q2q_problem(4),
+            "p2t": lambda: gen.thermal_p2t_problem(2)}[kind]()
     prob["coef"] = np.full(prob["conn"].shape[0], 1.0)
     K = orc.assemble(prob, dirichlet=False)
     M = orc.capacity(prob, np.full(prob["conn"].shape[0], 1.0))
@@ -166,12 +170,13 @@ def _heat_system(orc, n=6):
     return prob, K, M, F
 
 
-def test_fe_heat_matches_matrix_exponential(orc):
-    prob, K, M, F = _heat_system(orc)
+@pytest.mark.parametrize("kind", ["p1", "q2q", "p2t"])
+def test_fe_heat_matches_matrix_exponential(orc, kind):
+    prob, K, M, F = _heat_system(orc, kind)
     mask = prob["bc_mask"]
     free = mask == 0
     x = prob["coords"]
-    phi0 = np.where(free, np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]), 0.0)
+    phi0 = np.where(free, np.prod(np.sin(np.pi * x), axis=1), 0.0)
     Kd, Md = _csr(K).toarray()[np.ix_(free, free)], _csr(M).toarray()[np.ix_(free, free)]
     T = 0.05
     # exact semi-discrete solution: phi' = M^-1 (F - K phi)
@@ -193,8 +198,9 @@ def test_fe_heat_matches_matrix_exponential(orc):
     assert rates.min() > 1.9 and errs[-1] < 1e-4, (errs, rates)
 
 
-def test_steady_state_reached(orc):
-    prob, K, M, F = _heat_system(orc)
+@pytest.mark.parametrize("kind", ["p1", "q2q", "p2t"])
+def test_steady_state_reached(orc, kind):
+    prob, K, M, F = _heat_system(orc, kind)
     mask = prob["bc_mask"]
     free = mask == 0
     prm = orc.genalpha_params(0.0)
