@@ -246,13 +246,14 @@ def test_radiation_tangent_is_the_derivative(orc):
         assert np.abs(-(rp - rm) / (2 * h) - Kf[:, b]).max() < 1e-8 * np.abs(Kf).max()
 
 
-@pytest.mark.parametrize("kind", ["p1", "p2", "q1"])
+@pytest.mark.parametrize("kind", ["p1", "p2", "q1", "q2q", "p2t"])
 def test_radiation_slab_steady_state(orc, kind):
     # T = T0 on x = 0, k dT/dn = es (T_env^4 - T^4) on x = 1, insulated
     # elsewhere, no source: T = T0 + b x with k b = es (T_env^4 - (T0 + b)^4)
     import scipy.optimize
     prob = {"p1": lambda: gen.thermal_p1_problem(6), "p2": lambda: gen.thermal_p2_problem(4),
-            "q1": lambda: gen.thermal_q1_problem(3)}[kind]()
+            "q1": lambda: gen.thermal_q1_problem(3), "q2q": lambda: gen.thermal_q2q_problem(3),
+            "p2t": lambda: gen.thermal_p2t_problem(2)}[kind]()
     k, es, T0, Te = 1.7, 0.8, 0.4, 1.5
     prob["coef"] = np.full(prob["conn"].shape[0], k)
     prob["source"] = 0.0
